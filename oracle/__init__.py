@@ -1,0 +1,192 @@
+"""FP64 CPU oracle for the lens ray-trace and Gaussian-kernel reduction.
+
+TEST INFRASTRUCTURE ONLY: the test suite, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` load it. The product path (the CUDA library
+and its Python binding) never imports it and shares no code with it.
+
+The arithmetic lives in ``lensgp_oracle.c`` (plain C, FP64, OpenMP over
+independent rows); this module compiles it with gcc and wraps it with ctypes
+and numpy. Every function cites the passage of Karchev, Coogan & Weniger
+(arXiv:2105.09465) it follows.
+
+Parity status of each function (what pins it, see tests/test_oracle_pins.py):
+  grid_points       — pinned: exact definition, checked element-wise
+  raytrace (SPLE)   — pinned: SIS limit, q=1 power law, SIE artanh closed form,
+                      scipy 2F1, divergence = 2 kappa, zero curl
+  raytrace (shear)  — pinned: linearity and superposition
+  raytrace (tNFW)   — pinned: quadrature of the 3-D profile, NFW limit,
+                      far-field total mass, divergence = 2 kappa
+  raytrace (point)  — pinned: closed form
+  raytrace_vjp      — pinned: FP64 central differences of raytrace
+  kernel_matvec     — pinned: dense long-double brute force, symmetry, PSD,
+                      l -> infinity, two-point value, Riemann-sum integral
+  kernel_matvec_vjp — pinned: FP64 central differences of kernel_matvec
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from pathlib import Path
+
+import numpy as np
+
+HERE = Path(__file__).resolve().parent
+SRC = HERE / "lensgp_oracle.c"
+LIB = HERE / "liblensgp_oracle.so"
+
+_lib = None
+
+
+def build(force: bool = False) -> Path:
+    """Compile the oracle with gcc (FP64, -O2, OpenMP; no FP contraction)."""
+    if force or not LIB.exists() or LIB.stat().st_mtime < SRC.stat().st_mtime:
+        tmp = LIB.with_suffix(".so.tmp")
+        cmd = ["gcc", "-O2", "-fno-fast-math", "-ffp-contract=off", "-fopenmp", "-shared", "-fPIC",
+               "-std=c11", str(SRC), "-o", str(tmp), "-lm"]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"oracle build failed:\n{r.stderr}")
+        os.replace(tmp, LIB)
+    return LIB
+
+
+class OrcGrid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("ss", ctypes.c_int32),
+                ("pix", ctypes.c_float), ("cx", ctypes.c_float), ("cy", ctypes.c_float)]
+
+
+class OrcLens(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_double) for k in ("x0", "y0", "q", "phi", "theta_e", "gamma", "g1", "g2")]
+
+
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_I32 = ctypes.c_int32
+_D = ctypes.c_double
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        L = ctypes.CDLL(str(build()))
+        L.orc_grid_points.argtypes = [ctypes.POINTER(OrcGrid), _P]
+        L.orc_sple_kappa.argtypes = [_D, _D, ctypes.POINTER(OrcLens)]
+        L.orc_sple_kappa.restype = _D
+        L.orc_raytrace.argtypes = [_P, _I64, ctypes.POINTER(OrcLens), _P, _I32, _I32, _P, _P]
+        L.orc_raytrace_vjp.argtypes = [_P, _I64, ctypes.POINTER(OrcLens), _P, _I32, _I32, _P, _P, _P]
+        L.orc_kernel_matvec.argtypes = [_P, _I64, _P, _I64, _P, _D, _D, _P, _P]
+        L.orc_kernel_matvec_rows.argtypes = [_P, _P, _I64, _P, _I64, _P, _D, _D, _P, _P]
+        L.orc_kernel_matvec_vjp.argtypes = [_P, _I64, _P, _I64, _P, _D, _D, _P, _I32, _P, _P, _P, _P, _P]
+        L.orc_num_threads.restype = _I32
+        _lib = L
+    return _lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _pairs(a) -> np.ndarray:
+    """(n, 2) FP64 points; FP32 inputs widen exactly."""
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    assert a.ndim == 2 and a.shape[1] == 2, a.shape
+    return a
+
+
+def _lens(lens) -> OrcLens:
+    """lens: mapping or sequence in the order (x0, y0, q, phi, theta_e, gamma, g1, g2)."""
+    keys = ("x0", "y0", "q", "phi", "theta_e", "gamma", "g1", "g2")
+    vals = [lens[k] for k in keys] if isinstance(lens, dict) else list(lens)
+    return OrcLens(*[float(v) for v in vals])
+
+
+def _subs(sub):
+    if sub is None or len(sub) == 0:
+        return np.zeros((0, 5), np.float64), 0
+    s = np.ascontiguousarray(sub, dtype=np.float64)
+    assert s.ndim == 2 and s.shape[1] == 5
+    return s, s.shape[0]
+
+
+def num_threads() -> int:
+    return int(lib().orc_num_threads())
+
+
+def grid_points(nx, ny, ss, pix, cx=0.0, cy=0.0) -> np.ndarray:
+    """a1: FP32 pixel centres of the (nx ss) x (ny ss) supersampled grid, row-major over y."""
+    g = OrcGrid(nx, ny, ss, pix, cx, cy)
+    out = np.empty((nx * ss * ny * ss, 2), np.float32)
+    lib().orc_grid_points(ctypes.byref(g), _ptr(out))
+    return out
+
+
+def sple_kappa(x, y, lens) -> float:
+    """SPLE convergence (Sec. 2.2)."""
+    L = _lens(lens)
+    return float(lib().orc_sple_kappa(float(x), float(y), ctypes.byref(L)))
+
+
+def raytrace(xi, lens, sub=None, profile=0):
+    """a2-a5: returns (alpha, beta), FP64 (n, 2) arrays."""
+    xi = _pairs(xi)
+    s, ns = _subs(sub)
+    L = _lens(lens)
+    alpha = np.empty(xi.shape, np.float64)
+    beta = np.empty(xi.shape, np.float64)
+    lib().orc_raytrace(_ptr(xi), xi.shape[0], ctypes.byref(L), _ptr(s), ns, profile, _ptr(alpha), _ptr(beta))
+    return alpha, beta
+
+
+def raytrace_vjp(xi, lens, sub, d_beta, profile=0):
+    """Gradient of sum(d_beta * beta) w.r.t. (x0, y0, q, phi, theta_e, g1, g2) and per subhalo
+    (x_h, y_h, kappa_s | theta_pm, theta_s)."""
+    xi = _pairs(xi)
+    s, ns = _subs(sub)
+    L = _lens(lens)
+    db = np.ascontiguousarray(d_beta, dtype=np.float64)
+    d_lens = np.empty(7, np.float64)
+    d_sub = np.empty((ns, 4), np.float64)
+    lib().orc_raytrace_vjp(_ptr(xi), xi.shape[0], ctypes.byref(L), _ptr(s), ns, profile, _ptr(db), _ptr(d_lens),
+                           _ptr(d_sub) if ns else None)
+    return d_lens, d_sub
+
+
+def kernel_matvec(x, y, v, lengthscale, variance=1.0):
+    """a6: (out, absout), FP64, out_i = sum_j var exp(-|x_i-y_j|^2/(2 l^2)) v_j."""
+    x, y = _pairs(x), _pairs(y)
+    v = np.ascontiguousarray(v, dtype=np.float64).reshape(-1)
+    assert v.shape[0] == y.shape[0]
+    out = np.empty(x.shape[0], np.float64)
+    ab = np.empty(x.shape[0], np.float64)
+    lib().orc_kernel_matvec(_ptr(x), x.shape[0], _ptr(y), y.shape[0], _ptr(v), lengthscale, variance, _ptr(out),
+                            _ptr(ab))
+    return out, ab
+
+
+def kernel_matvec_rows(x, rows, y, v, lengthscale, variance=1.0):
+    """a6 on the rows `rows` of x only: (out, absout) of length len(rows)."""
+    x, y = _pairs(x), _pairs(y)
+    rows = np.ascontiguousarray(rows, dtype=np.int64)
+    v = np.ascontiguousarray(v, dtype=np.float64).reshape(-1)
+    out = np.empty(rows.shape[0], np.float64)
+    ab = np.empty(rows.shape[0], np.float64)
+    lib().orc_kernel_matvec_rows(_ptr(x), _ptr(rows), rows.shape[0], _ptr(y), y.shape[0], _ptr(v), lengthscale,
+                                 variance, _ptr(out), _ptr(ab))
+    return out, ab
+
+
+def kernel_matvec_vjp(x, y, v, lengthscale, variance, g, self_kernel=False):
+    """a7: dict with d_v, d_x, d_y (None for a self-kernel), d_len, d_var for Loss = sum_i g_i out_i."""
+    x, y = _pairs(x), _pairs(y)
+    v = np.ascontiguousarray(v, dtype=np.float64).reshape(-1)
+    g = np.ascontiguousarray(g, dtype=np.float64).reshape(-1)
+    n, m = x.shape[0], y.shape[0]
+    d_v = np.empty(m, np.float64)
+    d_x = np.empty((n, 2), np.float64)
+    d_y = None if self_kernel else np.empty((m, 2), np.float64)
+    d_len = np.zeros(1, np.float64)
+    d_var = np.zeros(1, np.float64)
+    lib().orc_kernel_matvec_vjp(_ptr(x), n, _ptr(y), m, _ptr(v), lengthscale, variance, _ptr(g), int(self_kernel),
+                                _ptr(d_v), _ptr(d_x), _ptr(d_y), _ptr(d_len), _ptr(d_var))
+    return {"d_v": d_v, "d_x": d_x, "d_y": d_y, "d_len": float(d_len[0]), "d_var": float(d_var[0])}

@@ -1,0 +1,515 @@
+/*
+ * lensgp ORACLE — plain, slow, FP64 CPU implementation of the lens ray-trace
+ * and Gaussian-kernel reduction of Karchev, Coogan & Weniger (arXiv:2105.09465).
+ *
+ * THIS IS TEST INFRASTRUCTURE. Only the test suite, the smoke check and the
+ * CPU-baseline leg of the benchmark may load it. The CUDA library never calls
+ * it and shares no code, header, table or constant with it.
+ *
+ * Every function states the passage of the paper it follows. Arithmetic is
+ * FP64 throughout; sums over many terms use Neumaier (improved Kahan)
+ * compensation. Parallelism is OpenMP over independent output rows only, so
+ * results do not depend on the thread count.
+ *
+ * Subhalos are not part of the paper (Sec. 2.2 leaves substructure out). They
+ * follow the truncated NFW profile of Baltz, Marshall & Oguri (2009),
+ *   rho(r) = rho_s / [(r/r_s)(1 + r/r_s)^2] * tau^2 / (tau^2 + (r/r_s)^2),
+ * with angular parameters (x_h, y_h, kappa_s, theta_s, tau), kappa_s =
+ * rho_s r_s / Sigma_cr and theta_s = r_s / D_l. A point mass (deflection
+ * theta_pm^2 d/|d|^2) is the second supported profile.
+ */
+#include <math.h>
+#include <omp.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_API __attribute__((visibility("default")))
+
+static const double PI = 3.14159265358979323846264338327950288;
+
+/* Image-plane grid (Sec. 2, Table 1: P are pixel centres; S x S
+ * supersampling of an nx x ny grid of spacing pix is the (nx S) x (ny S) grid
+ * of spacing pix/S). Positions are FP32 values: the FP32 rounding of
+ * cx + (col - (nx S - 1)/2) * h with h = float(pix / S). */
+typedef struct {
+  int32_t nx, ny, ss;
+  float pix, cx, cy;
+} orc_grid;
+
+/* Lens parameters in the order of Sec. 2.2: centre (x0, y0), axis ratio q,
+ * orientation phi (radians), Einstein radius theta_e, 3-D slope gamma, and
+ * external shear (g1, g2). */
+typedef struct {
+  double x0, y0, q, phi, theta_e, gamma, g1, g2;
+} orc_lens;
+
+/* ------------------------------------------------------------------------ */
+/* Compensated summation (Neumaier).                                          */
+typedef struct {
+  double s, c;
+} nsum;
+static inline void ns_add(nsum* a, double x) {
+  double t = a->s + x;
+  if (fabs(a->s) >= fabs(x))
+    a->c += (a->s - t) + x;
+  else
+    a->c += (x - t) + a->s;
+  a->s = t;
+}
+static inline double ns_val(const nsum* a) { return a->s + a->c; }
+
+/* ------------------------------------------------------------------------ */
+/* Forward-mode dual numbers: value plus derivatives with respect to up to
+ * ND parameters. Used for the analytic parameter gradients of the ray-trace. */
+#define ND 8
+typedef struct {
+  double v, d[ND];
+} dn;
+
+static inline dn dn_const(double v) {
+  dn r;
+  memset(&r, 0, sizeof r);
+  r.v = v;
+  return r;
+}
+static inline dn dn_var(double v, int k) {
+  dn r = dn_const(v);
+  r.d[k] = 1.0;
+  return r;
+}
+static inline dn dn_add(dn a, dn b) {
+  for (int k = 0; k < ND; ++k) a.d[k] += b.d[k];
+  a.v += b.v;
+  return a;
+}
+static inline dn dn_sub(dn a, dn b) {
+  for (int k = 0; k < ND; ++k) a.d[k] -= b.d[k];
+  a.v -= b.v;
+  return a;
+}
+static inline dn dn_mul(dn a, dn b) {
+  dn r;
+  r.v = a.v * b.v;
+  for (int k = 0; k < ND; ++k) r.d[k] = a.d[k] * b.v + a.v * b.d[k];
+  return r;
+}
+static inline dn dn_scale(dn a, double s) {
+  a.v *= s;
+  for (int k = 0; k < ND; ++k) a.d[k] *= s;
+  return a;
+}
+static inline dn dn_addc(dn a, double c) {
+  a.v += c;
+  return a;
+}
+/* f(a) with f(a.v) = fv and f'(a.v) = fp. */
+static inline dn dn_chain(dn a, double fv, double fp) {
+  dn r;
+  r.v = fv;
+  for (int k = 0; k < ND; ++k) r.d[k] = fp * a.d[k];
+  return r;
+}
+static inline dn dn_div(dn a, dn b) {
+  dn r;
+  r.v = a.v / b.v;
+  for (int k = 0; k < ND; ++k) r.d[k] = (a.d[k] - r.v * b.d[k]) / b.v;
+  return r;
+}
+static inline dn dn_recip(dn a) { return dn_chain(a, 1.0 / a.v, -1.0 / (a.v * a.v)); }
+static inline dn dn_sqrt(dn a) {
+  double s = sqrt(a.v);
+  return dn_chain(a, s, 0.5 / s);
+}
+static inline dn dn_log(dn a) { return dn_chain(a, log(a.v), 1.0 / a.v); }
+static inline dn dn_powc(dn a, double e) { return dn_chain(a, pow(a.v, e), e * pow(a.v, e - 1.0)); }
+static inline dn dn_cos(dn a) { return dn_chain(a, cos(a.v), -sin(a.v)); }
+static inline dn dn_sin(dn a) { return dn_chain(a, sin(a.v), cos(a.v)); }
+static inline dn dn_acosh(dn a) { return dn_chain(a, acosh(a.v), 1.0 / sqrt(a.v * a.v - 1.0)); }
+static inline dn dn_acos(dn a) { return dn_chain(a, acos(a.v), -1.0 / sqrt(1.0 - a.v * a.v)); }
+
+/* Complex dual: (re, im), each a dual. */
+typedef struct {
+  dn re, im;
+} cdn;
+static inline cdn cdn_mul(cdn a, cdn b) {
+  cdn r;
+  r.re = dn_sub(dn_mul(a.re, b.re), dn_mul(a.im, b.im));
+  r.im = dn_add(dn_mul(a.re, b.im), dn_mul(a.im, b.re));
+  return r;
+}
+static inline cdn cdn_add(cdn a, cdn b) {
+  cdn r = {dn_add(a.re, b.re), dn_add(a.im, b.im)};
+  return r;
+}
+static inline cdn cdn_scale(cdn a, dn s) {
+  cdn r = {dn_mul(a.re, s), dn_mul(a.im, s)};
+  return r;
+}
+static inline cdn cdn_scalec(cdn a, double s) {
+  cdn r = {dn_scale(a.re, s), dn_scale(a.im, s)};
+  return r;
+}
+
+/* ------------------------------------------------------------------------ */
+/* a1: pixel centres (Sec. 2 / Table 1).                                       */
+ORC_API void orc_grid_points(const orc_grid* g, float* xi /* [n][2] */) {
+  const int64_t W = (int64_t)g->nx * g->ss, H = (int64_t)g->ny * g->ss;
+  const float h = g->pix / (float)g->ss;
+  const float c0x = 0.5f * (float)(W - 1), c0y = 0.5f * (float)(H - 1);
+#pragma omp parallel for schedule(static)
+  for (int64_t r = 0; r < H; ++r)
+    for (int64_t c = 0; c < W; ++c) {
+      xi[2 * (r * W + c) + 0] = fmaf((float)c - c0x, h, g->cx);
+      xi[2 * (r * W + c) + 1] = fmaf((float)r - c0y, h, g->cy);
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* a2: SPLE deflection (Sec. 2.2, eq. for the SPLE displacement).
+ *  (u, v) = Rot(phi) (xi - xi0); R_x = sqrt(q) u, R_y = v / sqrt(q);
+ *  e^{i phi_e} = (R_x + i R_y) / R;  z = -(1-q)/(1+q) e^{2 i phi_e};
+ *  alpha' = theta_e 2 sqrt(q)/(1+q) (theta_e/R)^(gamma-2) 2F1(1, (gamma-1)/2;
+ *           (5-gamma)/2; z) e^{i phi_e}, expressed in the (u, v) frame and
+ *  rotated back by Rot(phi)^T.
+ * 2F1(1, a; b; z) = sum_n (a)_n / (b)_n z^n, summed until the term falls
+ * below 1e-17 |F|. The derivative slots of the inputs propagate through.
+ * Returns 0 deflection when R < 1e-12 arcsec (the profile is singular there). */
+static void sple_dual(dn x, dn y, dn x0, dn y0, dn q, dn phi, dn te, double gamma, dn* ax, dn* ay) {
+  dn c = dn_cos(phi), s = dn_sin(phi);
+  dn dx = dn_sub(x, x0), dy = dn_sub(y, y0);
+  dn u = dn_add(dn_mul(c, dx), dn_mul(s, dy));
+  dn v = dn_sub(dn_mul(c, dy), dn_mul(s, dx));
+  dn sq = dn_sqrt(q);
+  dn Rx = dn_mul(sq, u), Ry = dn_div(v, sq);
+  dn R = dn_sqrt(dn_add(dn_mul(Rx, Rx), dn_mul(Ry, Ry)));
+  if (R.v < 1e-12) {
+    *ax = dn_const(0.0);
+    *ay = dn_const(0.0);
+    return;
+  }
+  cdn e = {dn_div(Rx, R), dn_div(Ry, R)};
+  dn f = dn_div(dn_addc(dn_scale(q, -1.0), 1.0), dn_addc(q, 1.0)); /* (1-q)/(1+q) */
+  cdn z = cdn_scale(cdn_mul(e, e), dn_scale(f, -1.0));
+  const double a = 0.5 * (gamma - 1.0), b = 0.5 * (5.0 - gamma);
+  cdn F = {dn_const(1.0), dn_const(0.0)};
+  cdn term = F;
+  for (int n = 1; n < 5000; ++n) {
+    term = cdn_scalec(cdn_mul(term, z), (a + n - 1.0) / (b + n - 1.0));
+    F = cdn_add(F, term);
+    double tm = hypot(term.re.v, term.im.v), fm = hypot(F.re.v, F.im.v);
+    if (tm < 1e-17 * fm) break;
+  }
+  /* prefactor theta_e * 2 sqrt(q)/(1+q) * (theta_e / R)^(gamma - 2) */
+  dn pre = dn_mul(te, dn_div(dn_scale(sq, 2.0), dn_addc(q, 1.0)));
+  pre = dn_mul(pre, dn_powc(dn_div(te, R), gamma - 2.0));
+  cdn ap = cdn_scale(cdn_mul(F, e), pre);
+  /* rotate back: alpha = Rot^T alpha' */
+  *ax = dn_sub(dn_mul(c, ap.re), dn_mul(s, ap.im));
+  *ay = dn_add(dn_mul(s, ap.re), dn_mul(c, ap.im));
+}
+
+/* SPLE convergence, Sec. 2.2: kappa = (3 - gamma)/2 (theta_e / R)^(gamma - 1)
+ * with R the elliptical radius above. Used by the divergence pin. */
+ORC_API double orc_sple_kappa(double x, double y, const orc_lens* L) {
+  double c = cos(L->phi), s = sin(L->phi);
+  double u = c * (x - L->x0) + s * (y - L->y0), v = -s * (x - L->x0) + c * (y - L->y0);
+  double R = sqrt(L->q * u * u + v * v / L->q);
+  return 0.5 * (3.0 - L->gamma) * pow(L->theta_e / R, L->gamma - 1.0);
+}
+
+/* ------------------------------------------------------------------------ */
+/* a4: truncated NFW deflection (Baltz, Marshall & Oguri 2009), in units of
+ * the scale radius: x = R / theta_s,
+ *   g(x) = tau^2/(tau^2+1)^2 [ (tau^2 + 1 + 2(x^2-1)) F(x) + tau pi
+ *          + (tau^2-1) ln tau + sqrt(tau^2+x^2) (-pi + (tau^2-1)/tau L(x)) ],
+ *   F(x) = arccosh(1/x)/sqrt(1-x^2) (x<1), arccos(1/x)/sqrt(x^2-1) (x>1),
+ *   L(x) = ln(x / (sqrt(tau^2+x^2) + tau)),
+ * |alpha| = 4 kappa_s theta_s g(x) / x, directed along xi - xi_h.
+ * Near x = 1 F uses its series in eps = x^2 - 1: sum_n (-eps)^n / (2n+1). */
+static dn tnfw_F(dn x) {
+  dn eps = dn_addc(dn_mul(x, x), -1.0);
+  if (fabs(eps.v) < 1e-3) {
+    dn acc = dn_const(0.0), pw = dn_const(1.0), meps = dn_scale(eps, -1.0);
+    for (int n = 0; n < 12; ++n) {
+      acc = dn_add(acc, dn_scale(pw, 1.0 / (2.0 * n + 1.0)));
+      pw = dn_mul(pw, meps);
+    }
+    return acc;
+  }
+  if (x.v < 1.0) return dn_div(dn_acosh(dn_recip(x)), dn_sqrt(dn_scale(eps, -1.0)));
+  return dn_div(dn_acos(dn_recip(x)), dn_sqrt(eps));
+}
+
+static void tnfw_dual(dn x, dn y, dn xh, dn yh, dn ks, dn ts, double tau, dn* ax, dn* ay) {
+  dn dx = dn_sub(x, xh), dy = dn_sub(y, yh);
+  dn R = dn_sqrt(dn_add(dn_mul(dx, dx), dn_mul(dy, dy)));
+  if (R.v < 1e-15) {
+    *ax = dn_const(0.0);
+    *ay = dn_const(0.0);
+    return;
+  }
+  dn X = dn_div(R, ts);
+  const double t2 = tau * tau;
+  dn st = dn_sqrt(dn_addc(dn_mul(X, X), t2));
+  dn Lx = dn_log(dn_div(X, dn_addc(st, tau)));
+  dn Fx = tnfw_F(X);
+  dn term1 = dn_mul(dn_addc(dn_scale(dn_mul(X, X), 2.0), t2 - 1.0), Fx); /* (tau^2+1+2(x^2-1)) F */
+  dn term2 = dn_const(tau * PI + (t2 - 1.0) * log(tau));
+  dn term3 = dn_mul(st, dn_addc(dn_scale(Lx, (t2 - 1.0) / tau), -PI));
+  dn g = dn_scale(dn_add(dn_add(term1, term2), term3), t2 / ((t2 + 1.0) * (t2 + 1.0)));
+  /* alpha = 4 kappa_s theta_s g / x * d / R = 4 kappa_s g / x^2 * d */
+  dn m = dn_div(dn_scale(dn_mul(ks, g), 4.0), dn_mul(X, X));
+  *ax = dn_mul(m, dx);
+  *ay = dn_mul(m, dy);
+}
+
+static void pointmass_dual(dn x, dn y, dn xh, dn yh, dn tpm, dn* ax, dn* ay) {
+  dn dx = dn_sub(x, xh), dy = dn_sub(y, yh);
+  dn r2 = dn_add(dn_mul(dx, dx), dn_mul(dy, dy));
+  if (r2.v < 1e-30) {
+    *ax = dn_const(0.0);
+    *ay = dn_const(0.0);
+    return;
+  }
+  dn m = dn_div(dn_mul(tpm, tpm), r2);
+  *ax = dn_mul(m, dx);
+  *ay = dn_mul(m, dy);
+}
+
+/* Deflection of subhalo h at (x, y): profile 0 = tNFW record (x, y, kappa_s,
+ * theta_s, tau); profile 1 = point mass record (x, y, theta_pm, -, -).
+ * Derivative slots 0..3 are (x_h, y_h, kappa_s or theta_pm, theta_s) when
+ * `with_grad`. */
+static void sub_dual(double x, double y, const double* rec, int profile, int with_grad, dn* ax, dn* ay) {
+  dn X = dn_const(x), Y = dn_const(y);
+  dn xh = with_grad ? dn_var(rec[0], 0) : dn_const(rec[0]);
+  dn yh = with_grad ? dn_var(rec[1], 1) : dn_const(rec[1]);
+  dn p2 = with_grad ? dn_var(rec[2], 2) : dn_const(rec[2]);
+  dn p3 = with_grad ? dn_var(rec[3], 3) : dn_const(rec[3]);
+  if (profile == 1)
+    pointmass_dual(X, Y, xh, yh, p2, ax, ay);
+  else
+    tnfw_dual(X, Y, xh, yh, p2, p3, rec[4], ax, ay);
+}
+
+/* ------------------------------------------------------------------------ */
+/* a2-a5: ray-trace (eq. for the raytracing equation, Sec. 2.1):
+ *   beta = xi - alpha(xi), alpha = alpha_SPLE + alpha_shear + sum_h alpha_h.
+ * External shear (Sec. 2.2): alpha = [[g1, g2], [g2, -g1]] xi about the origin.
+ * Outputs alpha and beta for n points xi (all FP64; FP32 inputs are widened
+ * exactly by the caller). */
+ORC_API void orc_raytrace(const double* xi, int64_t n, const orc_lens* L, const double* sub, int32_t n_sub,
+                          int32_t profile, double* alpha /*[n][2] or NULL*/, double* beta /*[n][2] or NULL*/) {
+#pragma omp parallel for schedule(dynamic, 256)
+  for (int64_t i = 0; i < n; ++i) {
+    const double x = xi[2 * i], y = xi[2 * i + 1];
+    nsum sx = {0, 0}, sy = {0, 0};
+    dn ax, ay;
+    sple_dual(dn_const(x), dn_const(y), dn_const(L->x0), dn_const(L->y0), dn_const(L->q), dn_const(L->phi),
+              dn_const(L->theta_e), L->gamma, &ax, &ay);
+    ns_add(&sx, ax.v);
+    ns_add(&sy, ay.v);
+    ns_add(&sx, L->g1 * x + L->g2 * y);
+    ns_add(&sy, L->g2 * x - L->g1 * y);
+    for (int32_t h = 0; h < n_sub; ++h) {
+      sub_dual(x, y, sub + 5 * (int64_t)h, profile, 0, &ax, &ay);
+      ns_add(&sx, ax.v);
+      ns_add(&sy, ay.v);
+    }
+    const double axv = ns_val(&sx), ayv = ns_val(&sy);
+    if (alpha) {
+      alpha[2 * i] = axv;
+      alpha[2 * i + 1] = ayv;
+    }
+    if (beta) {
+      beta[2 * i] = x - axv;
+      beta[2 * i + 1] = y - ayv;
+    }
+  }
+}
+
+/* Ray-trace vector-Jacobian product: given d_beta = dLoss/dbeta_i, returns
+ *   d_lens[7] = dLoss/d(x0, y0, q, phi, theta_e, g1, g2)   (slope held fixed,
+ *               as in the paper's fits, Sec. 4.2),
+ *   d_sub[S][4] = dLoss/d(x_h, y_h, kappa_s | theta_pm, theta_s),
+ * with dLoss/dtheta = -sum_i (dalpha_i/dtheta)^T d_beta_i, from forward-mode
+ * dual numbers through the same expressions as orc_raytrace. */
+ORC_API void orc_raytrace_vjp(const double* xi, int64_t n, const orc_lens* L, const double* sub, int32_t n_sub,
+                              int32_t profile, const double* d_beta, double* d_lens /*[7]*/,
+                              double* d_sub /*[S][4] or NULL*/) {
+  nsum acc[7];
+  memset(acc, 0, sizeof acc);
+#pragma omp parallel
+  {
+    nsum loc[7];
+    memset(loc, 0, sizeof loc);
+#pragma omp for schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+      const double x = xi[2 * i], y = xi[2 * i + 1];
+      dn ax, ay;
+      sple_dual(dn_const(x), dn_const(y), dn_var(L->x0, 0), dn_var(L->y0, 1), dn_var(L->q, 2), dn_var(L->phi, 3),
+                dn_var(L->theta_e, 4), L->gamma, &ax, &ay);
+      const double gx = d_beta[2 * i], gy = d_beta[2 * i + 1];
+      for (int k = 0; k < 5; ++k) ns_add(&loc[k], -(ax.d[k] * gx + ay.d[k] * gy));
+      /* shear: dalpha/dg1 = (x, -y), dalpha/dg2 = (y, x) */
+      ns_add(&loc[5], -(x * gx - y * gy));
+      ns_add(&loc[6], -(y * gx + x * gy));
+    }
+#pragma omp critical
+    for (int k = 0; k < 7; ++k) {
+      ns_add(&acc[k], loc[k].s);
+      ns_add(&acc[k], loc[k].c);
+    }
+  }
+  for (int k = 0; k < 7; ++k) d_lens[k] = ns_val(&acc[k]);
+  if (!d_sub) return;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int32_t h = 0; h < n_sub; ++h) {
+    nsum a4[4];
+    memset(a4, 0, sizeof a4);
+    for (int64_t i = 0; i < n; ++i) {
+      dn ax, ay;
+      sub_dual(xi[2 * i], xi[2 * i + 1], sub + 5 * (int64_t)h, profile, 1, &ax, &ay);
+      const double gx = d_beta[2 * i], gy = d_beta[2 * i + 1];
+      for (int k = 0; k < 4; ++k) ns_add(&a4[k], -(ax.d[k] * gx + ay.d[k] * gy));
+    }
+    for (int k = 0; k < 4; ++k) d_sub[4 * (int64_t)h + k] = ns_val(&a4[k]);
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* a6: Gaussian RBF kernel reduction (eq. for the Gaussian RBF, Sec. 3.1, with
+ * isotropic kernel Sigma = l^2 I; Sec. 3.4 evaluates T y as this lazily
+ * reduced sum):
+ *   out_i = sum_j var * exp(-|x_i - y_j|^2 / (2 l^2)) v_j,
+ *   absout_i = sum_j |var * exp(...) v_j|  (the scale of the parity tolerance).
+ * x: n points, y: m points, v: m values (one right-hand side), all FP64. */
+ORC_API void orc_kernel_matvec(const double* x, int64_t n, const double* y, int64_t m, const double* v, double lengthscale,
+                               double variance, double* out, double* absout /* or NULL */) {
+  const double inv2l2 = 1.0 / (2.0 * lengthscale * lengthscale);
+#pragma omp parallel for schedule(dynamic, 64)
+  for (int64_t i = 0; i < n; ++i) {
+    const double xi = x[2 * i], yi = x[2 * i + 1];
+    nsum s = {0, 0}, a = {0, 0};
+    for (int64_t j = 0; j < m; ++j) {
+      const double dx = xi - y[2 * j], dy = yi - y[2 * j + 1];
+      const double kv = variance * exp(-(dx * dx + dy * dy) * inv2l2) * v[j];
+      ns_add(&s, kv);
+      ns_add(&a, fabs(kv));
+    }
+    out[i] = ns_val(&s);
+    if (absout) absout[i] = ns_val(&a);
+  }
+}
+
+/* Same reduction for a subset of rows (sampled parity at full size). */
+ORC_API void orc_kernel_matvec_rows(const double* x, const int64_t* rows, int64_t n_rows, const double* y, int64_t m,
+                                    const double* v, double lengthscale, double variance, double* out, double* absout) {
+  const double inv2l2 = 1.0 / (2.0 * lengthscale * lengthscale);
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int64_t r = 0; r < n_rows; ++r) {
+    const int64_t i = rows[r];
+    const double xi = x[2 * i], yi = x[2 * i + 1];
+    nsum s = {0, 0}, a = {0, 0};
+    for (int64_t j = 0; j < m; ++j) {
+      const double dx = xi - y[2 * j], dy = yi - y[2 * j + 1];
+      const double kv = variance * exp(-(dx * dx + dy * dy) * inv2l2) * v[j];
+      ns_add(&s, kv);
+      ns_add(&a, fabs(kv));
+    }
+    out[r] = ns_val(&s);
+    if (absout) absout[r] = ns_val(&a);
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* a7: gradients of Loss = sum_i g_i out_i through the reduction, by
+ * differentiating the RBF sum term by term (k_ij includes var):
+ *   d_v_j   = sum_i g_i k_ij
+ *   d_x_i   = g_i sum_j k_ij v_j (y_j - x_i) / l^2
+ *   d_y_j   = sum_i g_i k_ij v_j (x_i - y_j) / l^2
+ *   d_len   = sum_ij g_i v_j k_ij |x_i - y_j|^2 / l^3
+ *   d_var   = sum_ij g_i v_j k_ij / var
+ * For a self-kernel (x and y the same point set, `self` != 0) the point
+ * gradient is the sum of both roles and is returned in d_x (d_y unused).
+ * Every output pointer may be NULL. */
+ORC_API void orc_kernel_matvec_vjp(const double* x, int64_t n, const double* y, int64_t m, const double* v,
+                                   double lengthscale, double variance, const double* g, int32_t self, double* d_v,
+                                   double* d_x /*[n][2]*/, double* d_y /*[m][2]*/, double* d_len, double* d_var) {
+  const double l2 = lengthscale * lengthscale, inv2l2 = 1.0 / (2.0 * l2);
+  nsum tl = {0, 0}, tv = {0, 0};
+  /* row pass: d_x (row role), d_len, d_var */
+#pragma omp parallel
+  {
+    nsum ll = {0, 0}, lv = {0, 0};
+#pragma omp for schedule(dynamic, 64)
+    for (int64_t i = 0; i < n; ++i) {
+      const double xi = x[2 * i], yi = x[2 * i + 1];
+      nsum sx = {0, 0}, sy = {0, 0}, sl = {0, 0}, sv = {0, 0};
+      for (int64_t j = 0; j < m; ++j) {
+        const double dx = y[2 * j] - xi, dy = y[2 * j + 1] - yi;
+        const double d2 = dx * dx + dy * dy;
+        const double kv = variance * exp(-d2 * inv2l2) * v[j];
+        ns_add(&sx, kv * dx);
+        ns_add(&sy, kv * dy);
+        ns_add(&sl, kv * d2);
+        ns_add(&sv, kv);
+      }
+      if (d_x) {
+        d_x[2 * i] = g[i] * ns_val(&sx) / l2;
+        d_x[2 * i + 1] = g[i] * ns_val(&sy) / l2;
+      }
+      ns_add(&ll, g[i] * ns_val(&sl) / (l2 * lengthscale));
+      ns_add(&lv, g[i] * ns_val(&sv) / variance);
+    }
+#pragma omp critical
+    {
+      ns_add(&tl, ll.s);
+      ns_add(&tl, ll.c);
+      ns_add(&tv, lv.s);
+      ns_add(&tv, lv.c);
+    }
+  }
+  if (d_len) *d_len = ns_val(&tl);
+  if (d_var) *d_var = ns_val(&tv);
+  /* column pass: d_v, d_y (column role) */
+  double* col = (double*)calloc((size_t)(2 * m), sizeof(double));
+#pragma omp parallel for schedule(dynamic, 64)
+  for (int64_t j = 0; j < m; ++j) {
+    const double yj = y[2 * j], zj = y[2 * j + 1];
+    nsum s = {0, 0}, sx = {0, 0}, sy = {0, 0};
+    for (int64_t i = 0; i < n; ++i) {
+      const double dx = x[2 * i] - yj, dy = x[2 * i + 1] - zj;
+      const double gk = g[i] * variance * exp(-(dx * dx + dy * dy) * inv2l2);
+      ns_add(&s, gk);
+      ns_add(&sx, gk * dx);
+      ns_add(&sy, gk * dy);
+    }
+    if (d_v) d_v[j] = ns_val(&s);
+    col[2 * j] = v[j] * ns_val(&sx) / l2;
+    col[2 * j + 1] = v[j] * ns_val(&sy) / l2;
+  }
+  if (self && d_x) {
+    for (int64_t i = 0; i < n; ++i) {
+      d_x[2 * i] += col[2 * i];
+      d_x[2 * i + 1] += col[2 * i + 1];
+    }
+  } else if (d_y) {
+    memcpy(d_y, col, sizeof(double) * 2 * (size_t)m);
+  }
+  free(col);
+}
+
+/* Number of OpenMP threads the oracle runs with (reported by the benchmark). */
+ORC_API int32_t orc_num_threads(void) {
+  int32_t t = 1;
+#pragma omp parallel
+  {
+#pragma omp single
+    {
+      t = (int32_t)omp_get_num_threads();
+    }
+  }
+  return t;
+}

@@ -1,0 +1,38 @@
+// Internal helpers shared by the CUDA translation units of liblensgp.
+// Not part of the public C ABI (include/lensgp.h is).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+#include "../../include/lensgp.h"
+
+namespace lr {
+
+// Thread-local last-error message, read back through lr_last_error().
+void set_error(const char* fmt, ...);
+
+// Map a CUDA error to LR_ERR_CUDA, recording the failing call.
+lr_status cuda_status(cudaError_t e, const char* what);
+
+#define LR_CHECK_CUDA(call)                                        \
+  do {                                                             \
+    cudaError_t _e = (call);                                       \
+    if (_e != cudaSuccess) return ::lr::cuda_status(_e, #call);    \
+  } while (0)
+
+#define LR_REQUIRE(cond, ...)                                      \
+  do {                                                             \
+    if (!(cond)) {                                                 \
+      ::lr::set_error(__VA_ARGS__);                                \
+      return LR_ERR_INVALID_ARG;                                   \
+    }                                                              \
+  } while (0)
+
+// Hardware exp2 (MUFU.EX2 with flush-to-zero): 2^x, underflows to +0.
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+}  // namespace lr
