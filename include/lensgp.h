@@ -41,6 +41,9 @@ enum {
   LR_ERR_BUSY = 7           /* no free slot right now                            */
 };
 
+/* A CUDA stream (cudaStream_t / CUstream); NULL = the legacy default stream. */
+typedef struct CUstream_st* lr_stream;
+
 /* Message for the most recent failure on this thread ("" if none). */
 const char* lr_last_error(void);
 /* Symbolic name of a status code, e.g. "LR_ERR_INVALID_ARG". */
@@ -56,6 +59,120 @@ const char* lr_status_name(lr_status s);
 lr_status lr_probe_pipe_rates(int32_t device, double* ffma_lanes_per_clk,
                               double* ffma2_lanes_per_clk, double* ex2_per_clk,
                               int32_t* sm_count);
+
+/*
+ * Reads (and with clear != 0 resets) the device fault word of the current
+ * device. Kernels never trap: a bounded wait that runs out records a nonzero
+ * code here (1 = an mbarrier wait for a bulk copy timed out) and the kernel
+ * returns early. Synchronous.
+ */
+lr_status lr_fault_status(int32_t* code, int32_t clear);
+
+/* ------------------------------------------------------------------------ */
+/* Geometry and lens parameters                                               */
+
+/*
+ * Image-plane pixel grid (the pixel centres P of the paper's Table 1).
+ * S x S supersampling of an nx x ny grid of spacing `pix` is the
+ * (nx*ss) x (ny*ss) grid of spacing h = pix/ss (FP32 division). Point k,
+ * with row = k / (nx*ss) and col = k % (nx*ss), sits at the FP32 value
+ *   x = fmaf(col - (nx*ss - 1)/2, h, cx),  y = fmaf(row - (ny*ss - 1)/2, h, cy).
+ * Also used for regular grids of inducing points in the source plane.
+ */
+typedef struct {
+  int32_t nx, ny, ss;
+  float pix, cx, cy;
+} lr_grid;
+
+/*
+ * Lens parameters in the paper's order (Sec. 2.2): SPLE centre (x0, y0),
+ * axis ratio q in (0, 1], orientation phi [rad], Einstein radius theta_e,
+ * 3-D density slope gamma in (1, 3) (2 = isothermal), external shear
+ * (g1, g2) acting about the origin. The SPLE deflection is the
+ * hypergeometric closed form of Sec. 2.2, evaluated as its power series in
+ * e^{2 i phi_e}; axis ratios below ~0.12 need more than 96 terms and are
+ * rejected with LR_ERR_INVALID_ARG.
+ */
+typedef struct {
+  float x0, y0, q, phi, theta_e, gamma, g1, g2;
+} lr_lens;
+
+/*
+ * Subhalo profiles. Records are float[5] per subhalo, device memory,
+ * 16-byte aligned base for the fast staging path (any 4-byte aligned base
+ * works, more slowly):
+ *  LR_PROFILE_TNFW:       (x_h, y_h, kappa_s, theta_s, tau) — truncated NFW
+ *                         of Baltz, Marshall & Oguri (2009), kappa_s =
+ *                         rho_s r_s / Sigma_cr, theta_s = r_s / D_l,
+ *                         tau = r_t / r_s. Substructure is not part of the
+ *                         paper (Sec. 2.2 defers it); this is the standard
+ *                         profile for it.
+ *  LR_PROFILE_POINT_MASS: (x_h, y_h, theta_pm, unused, unused) — deflection
+ *                         theta_pm^2 d / |d|^2.
+ */
+enum { LR_PROFILE_TNFW = 0, LR_PROFILE_POINT_MASS = 1 };
+
+/*
+ * A point set: explicit FP32 positions or a grid, optionally ray-traced
+ * through a lens (then the set is the source-plane positions
+ * beta = xi - alpha(xi) of the image-plane points xi, eq. for the raytracing
+ * equation, Sec. 2.1).
+ *   xy      device float[n][2], or NULL to use `grid`
+ *   grid    used when xy == NULL (then n must equal its point count)
+ *   lens    host pointer; NULL = no ray-trace (positions used as given)
+ *   sub, n_sub, profile   subhalos, used only when lens != NULL
+ */
+typedef struct {
+  const float* xy;
+  lr_grid grid;
+  int64_t n;
+  const lr_lens* lens;
+  const float* sub;
+  int32_t n_sub;
+  int32_t profile;
+} lr_points;
+
+/* ------------------------------------------------------------------------ */
+/* Ray-trace (Sec. 2.1 raytracing equation; Sec. 2.2 lens model)              */
+
+/*
+ * beta_i = xi_i - alpha(xi_i) for every point of `pts` (which must carry a
+ * lens), alpha = alpha_SPLE + alpha_shear + sum_h alpha_h. The subhalo sum is
+ * Kahan-compensated in FP32.
+ *   beta_out   device float[n][2] (required)
+ *   alpha_out  device float[n][2] or NULL
+ * Errors: LR_ERR_INVALID_ARG for NULL/misaligned pointers, n < 0, a grid
+ * whose size differs from n, lens parameters outside their domain or
+ * non-finite. n == 0 is a no-op.
+ */
+lr_status lens_raytrace(const lr_points* pts, float* beta_out, float* alpha_out, lr_stream stream);
+
+/* ------------------------------------------------------------------------ */
+/* Gaussian-kernel reduction (Sec. 3.1 RBF kernel; Sec. 3.4 lazy T y)         */
+
+/*
+ * out_i = sum_j variance * exp(-|x_i - y_j|^2 / (2 lengthscale^2)) v_j
+ * (the RBF covariance of Sec. 3.1 with isotropic kernel Sigma = l^2 I,
+ * reduced lazily without storing the n x m matrix, Sec. 3.4).
+ *   query   the x_i; ray-traced first when query->lens != NULL
+ *   source  the y_j, or NULL for a self-kernel (y = x after ray-tracing)
+ *   v       device float[m][nrhs] (nrhs must be 1 in this version)
+ *   out     device float[n][nrhs]
+ *   beta_out device float[n][2] or NULL: receives the ray-traced query points
+ *   workspace/workspace_bytes: caller-owned device scratch of at least
+ *           lr_matvec_workspace_size() bytes (may be NULL when that is 0)
+ * FP32 arithmetic: distances by FMA, exp through the hardware exp2, per-tile
+ * partial sums merged with Kahan compensation. Deterministic: the same inputs
+ * give bit-identical outputs.
+ * Errors: LR_ERR_INVALID_ARG (pointers, sizes, lengthscale <= 0, variance
+ * not finite, workspace too small), LR_ERR_CUDA (launch failure).
+ */
+lr_status gp_kernel_matvec(const lr_points* query, const lr_points* source, const float* v, int32_t nrhs,
+                           float lengthscale, float variance, float* out, float* beta_out, void* workspace,
+                           size_t workspace_bytes, lr_stream stream);
+
+/* Scratch bytes gp_kernel_matvec needs for these point sets on the current device. */
+lr_status lr_matvec_workspace_size(const lr_points* query, const lr_points* source, int32_t nrhs, size_t* bytes);
 
 #ifdef __cplusplus
 }

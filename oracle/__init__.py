@@ -75,8 +75,7 @@ def lib():
         L.orc_sple_kappa.restype = _D
         L.orc_raytrace.argtypes = [_P, _I64, ctypes.POINTER(OrcLens), _P, _I32, _I32, _P, _P]
         L.orc_raytrace_vjp.argtypes = [_P, _I64, ctypes.POINTER(OrcLens), _P, _I32, _I32, _P, _P, _P]
-        L.orc_kernel_matvec.argtypes = [_P, _I64, _P, _I64, _P, _D, _D, _P, _P]
-        L.orc_kernel_matvec_rows.argtypes = [_P, _P, _I64, _P, _I64, _P, _D, _D, _P, _P]
+        L.orc_kernel_matvec.argtypes = [_P, _I64, _P, _I64, _P, _D, _D, _P, _I64, _P, _P, _P]
         L.orc_kernel_matvec_vjp.argtypes = [_P, _I64, _P, _I64, _P, _D, _D, _P, _I32, _P, _P, _P, _P, _P]
         L.orc_num_threads.restype = _I32
         _lib = L
@@ -152,28 +151,27 @@ def raytrace_vjp(xi, lens, sub, d_beta, profile=0):
     return d_lens, d_sub
 
 
-def kernel_matvec(x, y, v, lengthscale, variance=1.0):
-    """a6: (out, absout), FP64, out_i = sum_j var exp(-|x_i-y_j|^2/(2 l^2)) v_j."""
+def kernel_matvec(x, y, v, lengthscale, variance=1.0, rows=None, with_sens=False):
+    """a6: (out, absout[, sens]), FP64, out_i = sum_j var exp(-|x_i-y_j|^2/(2 l^2)) v_j.
+    With `rows`, only those rows of x are evaluated (sampled parity at full size)."""
     x, y = _pairs(x), _pairs(y)
     v = np.ascontiguousarray(v, dtype=np.float64).reshape(-1)
     assert v.shape[0] == y.shape[0]
-    out = np.empty(x.shape[0], np.float64)
-    ab = np.empty(x.shape[0], np.float64)
-    lib().orc_kernel_matvec(_ptr(x), x.shape[0], _ptr(y), y.shape[0], _ptr(v), lengthscale, variance, _ptr(out),
-                            _ptr(ab))
-    return out, ab
+    if rows is not None:
+        rows = np.ascontiguousarray(rows, dtype=np.int64)
+        assert rows.size == 0 or (rows.min() >= 0 and rows.max() < x.shape[0])
+    cnt = x.shape[0] if rows is None else rows.shape[0]
+    out = np.empty(cnt, np.float64)
+    ab = np.empty(cnt, np.float64)
+    sens = np.empty(cnt, np.float64) if with_sens else None
+    lib().orc_kernel_matvec(_ptr(x), x.shape[0], _ptr(y), y.shape[0], _ptr(v), lengthscale, variance, _ptr(rows),
+                            0 if rows is None else rows.shape[0], _ptr(out), _ptr(ab), _ptr(sens))
+    return (out, ab, sens) if with_sens else (out, ab)
 
 
 def kernel_matvec_rows(x, rows, y, v, lengthscale, variance=1.0):
     """a6 on the rows `rows` of x only: (out, absout) of length len(rows)."""
-    x, y = _pairs(x), _pairs(y)
-    rows = np.ascontiguousarray(rows, dtype=np.int64)
-    v = np.ascontiguousarray(v, dtype=np.float64).reshape(-1)
-    out = np.empty(rows.shape[0], np.float64)
-    ab = np.empty(rows.shape[0], np.float64)
-    lib().orc_kernel_matvec_rows(_ptr(x), _ptr(rows), rows.shape[0], _ptr(y), y.shape[0], _ptr(v), lengthscale,
-                                 variance, _ptr(out), _ptr(ab))
-    return out, ab
+    return kernel_matvec(x, y, v, lengthscale, variance, rows=rows)
 
 
 def kernel_matvec_vjp(x, y, v, lengthscale, variance, g, self_kernel=False):

@@ -382,44 +382,40 @@ ORC_API void orc_raytrace_vjp(const double* xi, int64_t n, const orc_lens* L, co
 /* a6: Gaussian RBF kernel reduction (eq. for the Gaussian RBF, Sec. 3.1, with
  * isotropic kernel Sigma = l^2 I; Sec. 3.4 evaluates T y as this lazily
  * reduced sum):
- *   out_i = sum_j var * exp(-|x_i - y_j|^2 / (2 l^2)) v_j,
- *   absout_i = sum_j |var * exp(...) v_j|  (the scale of the parity tolerance).
- * x: n points, y: m points, v: m values (one right-hand side), all FP64. */
-ORC_API void orc_kernel_matvec(const double* x, int64_t n, const double* y, int64_t m, const double* v, double lengthscale,
-                               double variance, double* out, double* absout /* or NULL */) {
-  const double inv2l2 = 1.0 / (2.0 * lengthscale * lengthscale);
-#pragma omp parallel for schedule(dynamic, 64)
-  for (int64_t i = 0; i < n; ++i) {
-    const double xi = x[2 * i], yi = x[2 * i + 1];
-    nsum s = {0, 0}, a = {0, 0};
-    for (int64_t j = 0; j < m; ++j) {
-      const double dx = xi - y[2 * j], dy = yi - y[2 * j + 1];
-      const double kv = variance * exp(-(dx * dx + dy * dy) * inv2l2) * v[j];
-      ns_add(&s, kv);
-      ns_add(&a, fabs(kv));
-    }
-    out[i] = ns_val(&s);
-    if (absout) absout[i] = ns_val(&a);
+ *   out_i    = sum_j var * exp(-|x_i - y_j|^2 / (2 l^2)) v_j,
+ *   absout_i = sum_j |var exp(...) v_j|           (scale of the parity tolerance)
+ *   sens_i   = sum_j |var exp(...) v_j| |x_i - y_j| / l^2
+ *              (bound on |d out_i / d x| per unit displacement of any point:
+ *               scales the tolerance when the points themselves carry error)
+ * x: n points, y: m points, v: m values (one right-hand side), all FP64.
+ * `rows` (optional) restricts the evaluation to those row indices; outputs
+ * then have n_rows entries. absout and sens may be NULL. */
+static void matvec_row(const double* x, int64_t i, const double* y, int64_t m, const double* v, double inv2l2,
+                       double invl2, double variance, double* out, double* absout, double* sens) {
+  const double xi = x[2 * i], yi = x[2 * i + 1];
+  nsum s = {0, 0}, a = {0, 0}, g = {0, 0};
+  for (int64_t j = 0; j < m; ++j) {
+    const double dx = xi - y[2 * j], dy = yi - y[2 * j + 1];
+    const double d2 = dx * dx + dy * dy;
+    const double kv = variance * exp(-d2 * inv2l2) * v[j];
+    ns_add(&s, kv);
+    ns_add(&a, fabs(kv));
+    ns_add(&g, fabs(kv) * sqrt(d2) * invl2);
   }
+  *out = ns_val(&s);
+  if (absout) *absout = ns_val(&a);
+  if (sens) *sens = ns_val(&g);
 }
 
-/* Same reduction for a subset of rows (sampled parity at full size). */
-ORC_API void orc_kernel_matvec_rows(const double* x, const int64_t* rows, int64_t n_rows, const double* y, int64_t m,
-                                    const double* v, double lengthscale, double variance, double* out, double* absout) {
-  const double inv2l2 = 1.0 / (2.0 * lengthscale * lengthscale);
+ORC_API void orc_kernel_matvec(const double* x, int64_t n, const double* y, int64_t m, const double* v,
+                               double lengthscale, double variance, const int64_t* rows, int64_t n_rows, double* out,
+                               double* absout, double* sens) {
+  const double inv2l2 = 1.0 / (2.0 * lengthscale * lengthscale), invl2 = 1.0 / (lengthscale * lengthscale);
+  const int64_t cnt = rows ? n_rows : n;
 #pragma omp parallel for schedule(dynamic, 16)
-  for (int64_t r = 0; r < n_rows; ++r) {
-    const int64_t i = rows[r];
-    const double xi = x[2 * i], yi = x[2 * i + 1];
-    nsum s = {0, 0}, a = {0, 0};
-    for (int64_t j = 0; j < m; ++j) {
-      const double dx = xi - y[2 * j], dy = yi - y[2 * j + 1];
-      const double kv = variance * exp(-(dx * dx + dy * dy) * inv2l2) * v[j];
-      ns_add(&s, kv);
-      ns_add(&a, fabs(kv));
-    }
-    out[r] = ns_val(&s);
-    if (absout) absout[r] = ns_val(&a);
+  for (int64_t r = 0; r < cnt; ++r) {
+    const int64_t i = rows ? rows[r] : r;
+    matvec_row(x, i, y, m, v, inv2l2, invl2, variance, out + r, absout ? absout + r : NULL, sens ? sens + r : NULL);
   }
 }
 

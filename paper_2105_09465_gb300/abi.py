@@ -1,0 +1,89 @@
+"""ctypes binding of liblensgp.so (the C ABI in include/lensgp.h).
+
+Argument marshalling only: every computation runs in the CUDA library. Tensors
+cross the boundary as raw device pointers, the stream as the current torch
+CUDA stream's handle. Loading fails loudly when the library is missing; there
+is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+from pathlib import Path
+
+from .build import LIB_PATH, build
+
+LR_OK = 0
+LR_ERR_INVALID_ARG = 1
+LR_ERR_CUDA = 2
+LR_ERR_OUT_OF_MEMORY = 3
+LR_ERR_TIMEOUT = 4
+LR_PENDING = 5
+LR_ERR_NOT_FOUND = 6
+LR_ERR_BUSY = 7
+
+LR_PROFILE_TNFW = 0
+LR_PROFILE_POINT_MASS = 1
+
+
+class LensGPError(RuntimeError):
+    def __init__(self, status: int, func: str, msg: str):
+        super().__init__(f"{func} failed with status {status}: {msg}")
+        self.status = status
+
+
+class lr_grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("ss", ctypes.c_int32),
+                ("pix", ctypes.c_float), ("cx", ctypes.c_float), ("cy", ctypes.c_float)]
+
+
+class lr_lens(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_float) for k in ("x0", "y0", "q", "phi", "theta_e", "gamma", "g1", "g2")]
+
+
+class lr_points(ctypes.Structure):
+    _fields_ = [("xy", ctypes.c_void_p), ("grid", lr_grid), ("n", ctypes.c_int64),
+                ("lens", ctypes.POINTER(lr_lens)), ("sub", ctypes.c_void_p), ("n_sub", ctypes.c_int32),
+                ("profile", ctypes.c_int32)]
+
+
+_P = ctypes.c_void_p
+_lib = None
+
+# name -> (restype, argtypes); every symbol include/lensgp.h declares
+SIGNATURES = {
+    "lr_last_error": (ctypes.c_char_p, []),
+    "lr_status_name": (ctypes.c_char_p, [ctypes.c_int32]),
+    "lr_probe_pipe_rates": (ctypes.c_int32, [ctypes.c_int32, _P, _P, _P, _P]),
+    "lr_fault_status": (ctypes.c_int32, [_P, ctypes.c_int32]),
+    "lens_raytrace": (ctypes.c_int32, [ctypes.POINTER(lr_points), _P, _P, _P]),
+    "gp_kernel_matvec": (ctypes.c_int32, [ctypes.POINTER(lr_points), ctypes.POINTER(lr_points), _P, ctypes.c_int32,
+                                          ctypes.c_float, ctypes.c_float, _P, _P, _P, ctypes.c_size_t, _P]),
+    "lr_matvec_workspace_size": (ctypes.c_int32, [ctypes.POINTER(lr_points), ctypes.POINTER(lr_points),
+                                                  ctypes.c_int32, ctypes.POINTER(ctypes.c_size_t)]),
+}
+
+
+def load(path: str | Path | None = None, build_if_missing: bool = True) -> ctypes.CDLL:
+    """Loads (building first if needed) liblensgp.so and declares every entry point."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = Path(path) if path else LIB_PATH
+    if not p.exists():
+        if not build_if_missing:
+            raise FileNotFoundError(f"{p} is missing: build it with paper_2105_09465_gb300.build.build()")
+        build()
+    lib = ctypes.CDLL(str(p))
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def check(status: int, func: str) -> None:
+    if status != LR_OK:
+        msg = load().lr_last_error().decode(errors="replace")
+        raise LensGPError(status, func, msg)

@@ -1,0 +1,141 @@
+"""Python entry points over the C ABI, with torch tensors for device memory.
+
+These functions only marshal arguments: pointers of CUDA tensors, the current
+torch stream and plain structs go to liblensgp.so, which does all the work.
+They raise when CUDA or the library is unavailable (no CPU fallback).
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import torch
+
+from . import abi
+from .workloads import Grid, Lens
+
+
+@dataclass
+class Points:
+    """A point set for the C ABI: explicit (n, 2) float32 CUDA positions or a
+    grid, optionally ray-traced through a lens with subhalos."""
+    xy: torch.Tensor | None = None
+    grid: Grid | None = None
+    lens: Lens | None = None
+    sub: torch.Tensor | None = None   # (S, 5) float32 CUDA
+    profile: int = abi.LR_PROFILE_TNFW
+
+    @property
+    def n(self) -> int:
+        return int(self.xy.shape[0]) if self.xy is not None else self.grid.n
+
+
+def _require_cuda(t: torch.Tensor | None, name: str, shape_tail=None) -> None:
+    if t is None:
+        return
+    if not t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous float32 CUDA tensor")
+    if shape_tail is not None and tuple(t.shape[1:]) != shape_tail:
+        raise ValueError(f"{name} must have shape (n, {', '.join(map(str, shape_tail))})")
+
+
+def _stream_handle(stream: torch.cuda.Stream | None) -> ctypes.c_void_p:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def to_c_points(p: Points | None):
+    """Builds the lr_points struct; returns (struct or None, objects to keep alive)."""
+    if p is None:
+        return None, ()
+    _require_cuda(p.xy, "xy", (2,))
+    _require_cuda(p.sub, "sub", (5,))
+    c = abi.lr_points()
+    keep = []
+    if p.xy is not None:
+        c.xy = p.xy.data_ptr()
+        c.n = p.xy.shape[0]
+    else:
+        c.xy = None
+        c.grid = abi.lr_grid(*p.grid.astuple())
+        c.n = p.grid.n
+    if p.lens is not None:
+        L = abi.lr_lens(*p.lens.astuple())
+        keep.append(L)
+        c.lens = ctypes.pointer(L)
+        c.sub = p.sub.data_ptr() if (p.sub is not None and p.sub.numel()) else None
+        c.n_sub = int(p.sub.shape[0]) if p.sub is not None else 0
+        c.profile = int(p.profile)
+    return c, keep
+
+
+def lens_raytrace(pts: Points, want_alpha: bool = False, stream=None):
+    """beta = xi - alpha(xi) for every point (pts.lens required). Returns beta (and alpha)."""
+    lib = abi.load()
+    c, keep = to_c_points(pts)
+    n = c.n
+    dev = pts.xy.device if pts.xy is not None else torch.device("cuda", torch.cuda.current_device())
+    beta = torch.empty((n, 2), dtype=torch.float32, device=dev)
+    alpha = torch.empty((n, 2), dtype=torch.float32, device=dev) if want_alpha else None
+    st = lib.lens_raytrace(ctypes.byref(c), beta.data_ptr(), alpha.data_ptr() if alpha is not None else None,
+                           _stream_handle(stream))
+    abi.check(st, "lens_raytrace")
+    return (beta, alpha) if want_alpha else beta
+
+
+def matvec_workspace_size(query: Points, source: Points | None) -> int:
+    lib = abi.load()
+    cq, k1 = to_c_points(query)
+    cs, k2 = to_c_points(source)
+    b = ctypes.c_size_t(0)
+    st = lib.lr_matvec_workspace_size(ctypes.byref(cq), ctypes.byref(cs) if cs is not None else None, 1,
+                                      ctypes.byref(b))
+    abi.check(st, "lr_matvec_workspace_size")
+    return int(b.value)
+
+
+def gp_kernel_matvec(query: Points, source: Points | None, v: torch.Tensor, lengthscale: float,
+                     variance: float = 1.0, want_beta: bool = False, out: torch.Tensor | None = None,
+                     workspace: torch.Tensor | None = None, stream=None):
+    """out_i = sum_j variance exp(-|x_i - y_j|^2 / (2 lengthscale^2)) v_j.
+
+    `source=None` is the self-kernel. Returns out (and the ray-traced query
+    points when want_beta and the query carries a lens or a grid)."""
+    lib = abi.load()
+    _require_cuda(v, "v")
+    cq, k1 = to_c_points(query)
+    cs, k2 = to_c_points(source)
+    n = cq.n
+    dev = v.device
+    if out is None:
+        out = torch.empty((n,), dtype=torch.float32, device=dev)
+    beta = torch.empty((n, 2), dtype=torch.float32, device=dev) if want_beta else None
+    b = ctypes.c_size_t(0)
+    abi.check(lib.lr_matvec_workspace_size(ctypes.byref(cq), ctypes.byref(cs) if cs is not None else None, 1,
+                                           ctypes.byref(b)), "lr_matvec_workspace_size")
+    need = int(b.value)
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty((max(need, 1),), dtype=torch.uint8, device=dev)
+    st = lib.gp_kernel_matvec(ctypes.byref(cq), ctypes.byref(cs) if cs is not None else None, v.data_ptr(), 1,
+                              float(lengthscale), float(variance), out.data_ptr(),
+                              beta.data_ptr() if beta is not None else None, workspace.data_ptr(),
+                              workspace.numel(), _stream_handle(stream))
+    abi.check(st, "gp_kernel_matvec")
+    return (out, beta) if want_beta else out
+
+
+def probe_pipe_rates(device: int = 0) -> dict:
+    """Measured per-SM-clock rates: FFMA lanes, FFMA2 lanes, MUFU.EX2; and SM count."""
+    lib = abi.load()
+    a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    n = ctypes.c_int32()
+    abi.check(lib.lr_probe_pipe_rates(device, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(n)),
+              "lr_probe_pipe_rates")
+    return {"ffma_lanes_per_clk": a.value, "ffma2_lanes_per_clk": b.value, "ex2_per_clk": c.value, "sm_count": n.value}
+
+
+def fault_status(clear: bool = False) -> int:
+    lib = abi.load()
+    code = ctypes.c_int32()
+    abi.check(lib.lr_fault_status(ctypes.byref(code), int(clear)), "lr_fault_status")
+    return int(code.value)

@@ -14,6 +14,12 @@ void set_error(const char* fmt, ...);
 // Map a CUDA error to LR_ERR_CUDA, recording the failing call.
 lr_status cuda_status(cudaError_t e, const char* what);
 
+// Device address of the library's fault word on the current device.
+int* fault_ptr();
+
+// Streams cross the ABI as lr_stream (an opaque CUstream_st*).
+inline cudaStream_t as_cuda(lr_stream s) { return reinterpret_cast<cudaStream_t>(s); }
+
 #define LR_CHECK_CUDA(call)                                        \
   do {                                                             \
     cudaError_t _e = (call);                                       \

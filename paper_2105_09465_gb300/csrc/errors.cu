@@ -37,3 +37,37 @@ extern "C" const char* lr_status_name(lr_status s) {
     default: return "LR_UNKNOWN_STATUS";
   }
 }
+
+// ---------------------------------------------------------------------------
+// Device fault word: kernels that give up a bounded wait record a code here
+// (instead of trapping), and the host reads it back with lr_fault_status().
+__device__ int g_lr_fault;
+
+namespace lr {
+
+int* fault_ptr() {
+  static thread_local int cached_dev = -1;
+  static thread_local int* cached = nullptr;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+  if (dev != cached_dev) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_lr_fault) != cudaSuccess) return nullptr;
+    cached = static_cast<int*>(p);
+    cached_dev = dev;
+  }
+  return cached;
+}
+
+}  // namespace lr
+
+extern "C" lr_status lr_fault_status(int32_t* code, int32_t clear) {
+  LR_REQUIRE(code != nullptr, "lr_fault_status: code is NULL");
+  int* p = lr::fault_ptr();
+  if (!p) return lr::cuda_status(cudaGetLastError(), "cudaGetSymbolAddress(g_lr_fault)");
+  int v = 0;
+  LR_CHECK_CUDA(cudaMemcpy(&v, p, sizeof v, cudaMemcpyDeviceToHost));
+  *code = v;
+  if (clear) LR_CHECK_CUDA(cudaMemset(p, 0, sizeof(int)));
+  return LR_OK;
+}

@@ -1,0 +1,366 @@
+// a6: lazily evaluated Gaussian-kernel reduction
+//   out_i = sum_j var * exp(-|x_i - y_j|^2 / (2 l^2)) v_j
+// (RBF covariance with Sigma = l^2 I, Sec. 3.1; T y evaluated without storing
+// T, Sec. 3.4).
+//
+// Work decomposition: the n x m pair space is cut into tasks of
+// (a block of kRowsPerCta query rows) x (a chunk of consecutive source
+// tiles); one CTA per task, scheduled by the hardware. Each thread keeps R
+// query points in registers; source tiles of kTile points are staged in
+// shared memory in a pair-packed layout and streamed with double buffering,
+// so that every instruction of the inner loop works on two sources at once
+// (packed f32x2 add/mul/fma) and each exp is one MUFU.EX2.
+// Per pair: 3 packed-FP32 lane ops (grid sources, uniform y per tile) or 5
+// (explicit sources) plus one exp2.
+// Accuracy: per tile each thread sums <= kTile/2 terms per lane in plain
+// FP32, then folds the tile total into a Kahan-compensated running sum. With
+// several chunks per row the chunk totals are merged by a second kernel in
+// fixed chunk order (Kahan), so results are deterministic.
+#include <math.h>
+
+#include "host.cuh"
+
+namespace lr {
+
+constexpr int kMvThreads = 128;
+constexpr int kMvR = 8;                              // query rows per thread
+constexpr int kRowsPerCta = kMvThreads * kMvR;       // 1024
+constexpr int kTile = 256;                           // source points per tile
+constexpr int kPairs = kTile / 2;                    // = kMvThreads: one pair per loader thread
+static_assert(kPairs == kMvThreads, "one source pair per thread when staging");
+
+struct SrcDesc {
+  const float2* xy;  // explicit source points, or NULL for a grid
+  GridDev g;         // grid description when xy == NULL
+  int64_t m;         // number of source points
+  int32_t segs;      // grid: tiles per grid row
+  int32_t n_tiles;   // total tiles
+};
+
+struct MvArgs {
+  const float2* x;   // query points [n]
+  int64_t n;
+  SrcDesc src;
+  const float* v;    // [m]
+  float neg_c;       // -log2(e) / (2 l^2)
+  float variance;
+  int32_t chunks;    // column chunks per row block
+  float* out;        // [n] when chunks == 1
+  float* partial;    // [chunks][n] when chunks > 1
+};
+
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+
+__device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
+  const float y = x - c;
+  const float t = s + y;
+  c = (t - s) - y;
+  s = t;
+}
+
+// Range of source indices covered by tile t, and (grid) its uniform y.
+__device__ __forceinline__ void tile_range(const SrcDesc& S, int t, int64_t& j0, int& cnt, int& grow) {
+  if (S.xy) {
+    j0 = (int64_t)t * kTile;
+    const int64_t rem = S.m - j0;
+    cnt = rem < kTile ? (int)rem : kTile;
+    grow = 0;
+  } else {
+    grow = t / S.segs;
+    const int seg = t - grow * S.segs;
+    const int c0 = seg * kTile;
+    cnt = min(kTile, S.g.W - c0);
+    j0 = (int64_t)grow * S.g.W + c0;
+  }
+}
+
+// Loads source pair `p` of tile t into registers (zero weight past the end).
+template <bool GRID>
+__device__ __forceinline__ void load_pair(const SrcDesc& S, const float* __restrict__ v, int t, int p, float4& P,
+                                          float2& V) {
+  int64_t j0;
+  int cnt, grow;
+  tile_range(S, t, j0, cnt, grow);
+  const int a = 2 * p, b = 2 * p + 1;
+  if (GRID) {
+    const int c0 = (int)(j0 - (int64_t)grow * S.g.W);
+    const float xa = (a < cnt) ? grid_x(S.g, c0 + a) : 0.f;
+    const float xb = (b < cnt) ? grid_x(S.g, c0 + b) : 0.f;
+    P = make_float4(-xa, -xb, 0.f, 0.f);
+  } else {
+    const float2 pa = (a < cnt) ? __ldg(S.xy + j0 + a) : f2(0.f, 0.f);
+    const float2 pb = (b < cnt) ? __ldg(S.xy + j0 + b) : f2(0.f, 0.f);
+    P = make_float4(-pa.x, -pb.x, -pa.y, -pb.y);
+  }
+  V = f2((a < cnt) ? __ldg(v + j0 + a) : 0.f, (b < cnt) ? __ldg(v + j0 + b) : 0.f);
+}
+
+template <bool GRID>
+__global__ void __launch_bounds__(kMvThreads) matvec_kernel(MvArgs A) {
+  __shared__ __align__(16) float4 sP[2][kPairs];
+  __shared__ __align__(16) float2 sV[2][kPairs];
+
+  const int task = blockIdx.x;
+  const int rb = task / A.chunks;
+  const int chunk = task - rb * A.chunks;
+  const int nt = A.src.n_tiles;
+  const int t0 = (int)((int64_t)chunk * nt / A.chunks);
+  const int t1 = (int)((int64_t)(chunk + 1) * nt / A.chunks);
+  const int tid = threadIdx.x;
+
+  float2 xq[kMvR], yq[kMvR], acc[kMvR];
+  float sum[kMvR], comp[kMvR];
+#pragma unroll
+  for (int r = 0; r < kMvR; ++r) {
+    int64_t i = (int64_t)rb * kRowsPerCta + r * kMvThreads + tid;
+    if (i >= A.n) i = A.n - 1;
+    const float2 p = __ldg(A.x + i);
+    xq[r] = f2(p.x, p.x);
+    yq[r] = f2(p.y, p.y);
+    acc[r] = f2(0.f, 0.f);
+    sum[r] = 0.f;
+    comp[r] = 0.f;
+  }
+  const float2 nc2 = f2(A.neg_c, A.neg_c);
+
+  float4 P;
+  float2 V;
+  if (t0 < t1) {
+    load_pair<GRID>(A.src, A.v, t0, tid, P, V);
+    sP[0][tid] = P;
+    sV[0][tid] = V;
+  }
+  __syncthreads();
+
+  for (int t = t0; t < t1; ++t) {
+    const int buf = (t - t0) & 1;
+    if (t + 1 < t1) load_pair<GRID>(A.src, A.v, t + 1, tid, P, V);  // in flight during compute
+    int64_t j0;
+    int cnt, grow;
+    tile_range(A.src, t, j0, cnt, grow);
+    const int np = (cnt + 1) >> 1;
+    if (GRID) {
+      const float yt = grid_y(A.src.g, grow);
+      float2 dy2c[kMvR];
+#pragma unroll
+      for (int r = 0; r < kMvR; ++r) {
+        const float dy = yq[r].x - yt;
+        const float e = A.neg_c * dy * dy;
+        dy2c[r] = f2(e, e);
+      }
+#pragma unroll 2
+      for (int p = 0; p < np; ++p) {
+        const float4 Q = sP[buf][p];
+        const float2 W = sV[buf][p];
+        const float2 nx = f2(Q.x, Q.y);
+#pragma unroll
+        for (int r = 0; r < kMvR; ++r) {
+          const float2 dx = __fadd2_rn(xq[r], nx);
+          const float2 e = __ffma2_rn(__fmul2_rn(dx, nc2), dx, dy2c[r]);
+          const float2 k = f2(ex2_approx(e.x), ex2_approx(e.y));
+          acc[r] = __ffma2_rn(k, W, acc[r]);
+        }
+      }
+    } else {
+#pragma unroll 2
+      for (int p = 0; p < np; ++p) {
+        const float4 Q = sP[buf][p];
+        const float2 W = sV[buf][p];
+        const float2 nx = f2(Q.x, Q.y), ny = f2(Q.z, Q.w);
+#pragma unroll
+        for (int r = 0; r < kMvR; ++r) {
+          const float2 dx = __fadd2_rn(xq[r], nx);
+          const float2 dy = __fadd2_rn(yq[r], ny);
+          const float2 d2 = __ffma2_rn(dy, dy, __fmul2_rn(dx, dx));
+          const float2 e = __fmul2_rn(d2, nc2);
+          const float2 k = f2(ex2_approx(e.x), ex2_approx(e.y));
+          acc[r] = __ffma2_rn(k, W, acc[r]);
+        }
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < kMvR; ++r) {
+      kahan_add(sum[r], comp[r], acc[r].x + acc[r].y);
+      acc[r] = f2(0.f, 0.f);
+    }
+    if (t + 1 < t1) {
+      sP[buf ^ 1][tid] = P;
+      sV[buf ^ 1][tid] = V;
+    }
+    __syncthreads();
+  }
+
+#pragma unroll
+  for (int r = 0; r < kMvR; ++r) {
+    const int64_t i = (int64_t)rb * kRowsPerCta + r * kMvThreads + tid;
+    if (i < A.n) {
+      const float total = sum[r] - comp[r];
+      if (A.chunks == 1)
+        A.out[i] = A.variance * total;
+      else
+        A.partial[(int64_t)chunk * A.n + i] = total;
+    }
+  }
+}
+
+// Fixed-order compensated merge of the chunk partials.
+__global__ void merge_chunks_kernel(const float* __restrict__ partial, int chunks, int64_t n, float variance,
+                                    float* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float s = 0.f, c = 0.f;
+  for (int k = 0; k < chunks; ++k) kahan_add(s, c, partial[(int64_t)k * n + i]);
+  out[i] = variance * (s - c);
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+
+struct MvPlan {
+  int64_t n, m;
+  bool self;
+  bool q_raytrace, q_grid;   // query needs ray-tracing / grid materialisation
+  bool s_raytrace;           // source needs ray-tracing
+  bool s_grid;               // source read as a grid (no materialisation)
+  int32_t n_tiles, segs, chunks, row_blocks;
+  size_t off_qbeta, off_sbeta, off_partial, bytes;
+};
+
+static lr_status plan_matvec(const lr_points* q, const lr_points* s, int32_t nrhs, bool have_beta_out, MvPlan* P) {
+  lr_status st = validate_points(q, "gp_kernel_matvec(query)", false);
+  if (st != LR_OK) return st;
+  if (s) {
+    st = validate_points(s, "gp_kernel_matvec(source)", false);
+    if (st != LR_OK) return st;
+  }
+  LR_REQUIRE(nrhs == 1, "gp_kernel_matvec: nrhs = %d; this version supports nrhs = 1", nrhs);
+  MvPlan p{};
+  p.n = q->n;
+  p.self = (s == nullptr);
+  p.m = p.self ? q->n : s->n;
+  p.q_raytrace = q->lens != nullptr;
+  p.q_grid = !p.q_raytrace && q->xy == nullptr;
+  p.s_raytrace = !p.self && s->lens != nullptr;
+  p.s_grid = !p.self && !p.s_raytrace && s->xy == nullptr;
+  if (p.s_grid) {
+    const int W = s->grid.nx * s->grid.ss;
+    p.segs = (W + kTile - 1) / kTile;
+    p.n_tiles = (int32_t)((int64_t)p.segs * s->grid.ny * s->grid.ss);
+  } else {
+    p.segs = 0;
+    p.n_tiles = (int32_t)((p.m + kTile - 1) / kTile);
+  }
+  p.row_blocks = (int32_t)((p.n + kRowsPerCta - 1) / kRowsPerCta);
+  // column chunks: enough tasks that every resident CTA slot gets ~8 of them
+  int dev = 0, n_sm = 1, occ = 1;
+  LR_CHECK_CUDA(cudaGetDevice(&dev));
+  LR_CHECK_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
+  LR_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, matvec_kernel<false>, kMvThreads, 0));
+  const int64_t target = 8LL * n_sm * (occ > 0 ? occ : 1);
+  int64_t chunks = 1;
+  if (p.row_blocks > 0 && p.n_tiles > 0) {
+    chunks = (target + p.row_blocks - 1) / p.row_blocks;
+    chunks = chunks < 1 ? 1 : chunks;
+    chunks = chunks > p.n_tiles ? p.n_tiles : chunks;
+  }
+  p.chunks = (int32_t)chunks;
+  size_t off = 0;
+  const bool need_qbuf = (p.q_raytrace || p.q_grid) && !have_beta_out;
+  p.off_qbeta = off;
+  if (need_qbuf) off += align256(sizeof(float2) * (size_t)p.n);
+  p.off_sbeta = off;
+  if (p.s_raytrace) off += align256(sizeof(float2) * (size_t)p.m);
+  p.off_partial = off;
+  if (p.chunks > 1) off += align256(sizeof(float) * (size_t)p.chunks * (size_t)p.n);
+  p.bytes = off;
+  *P = p;
+  return LR_OK;
+}
+
+}  // namespace lr
+
+using namespace lr;
+
+extern "C" lr_status lr_matvec_workspace_size(const lr_points* query, const lr_points* source, int32_t nrhs,
+                                              size_t* bytes) {
+  LR_REQUIRE(bytes != nullptr, "lr_matvec_workspace_size: bytes is NULL");
+  MvPlan P;
+  lr_status st = plan_matvec(query, source, nrhs, false, &P);
+  if (st != LR_OK) return st;
+  *bytes = P.bytes;
+  return LR_OK;
+}
+
+extern "C" lr_status gp_kernel_matvec(const lr_points* query, const lr_points* source, const float* v, int32_t nrhs,
+                                      float lengthscale, float variance, float* out, float* beta_out,
+                                      void* workspace, size_t workspace_bytes, lr_stream stream) {
+  MvPlan P;
+  lr_status st = plan_matvec(query, source, nrhs, beta_out != nullptr, &P);
+  if (st != LR_OK) return st;
+  LR_REQUIRE(isfinite(lengthscale) && lengthscale > 0.f, "gp_kernel_matvec: lengthscale = %g must be > 0",
+             (double)lengthscale);
+  LR_REQUIRE(isfinite(variance), "gp_kernel_matvec: variance is not finite");
+  LR_REQUIRE(out != nullptr || P.n == 0, "gp_kernel_matvec: out is NULL");
+  LR_REQUIRE(v != nullptr || P.m == 0, "gp_kernel_matvec: v is NULL");
+  LR_REQUIRE(((uintptr_t)beta_out & 7u) == 0, "gp_kernel_matvec: beta_out must be 8-byte aligned");
+  LR_REQUIRE(workspace_bytes >= P.bytes, "gp_kernel_matvec: workspace of %zu bytes, %zu needed", workspace_bytes,
+             P.bytes);
+  LR_REQUIRE(P.bytes == 0 || workspace != nullptr, "gp_kernel_matvec: workspace is NULL");
+  LR_REQUIRE(((uintptr_t)workspace & 255u) == 0, "gp_kernel_matvec: workspace must be 256-byte aligned");
+  LR_REQUIRE(P.q_raytrace || P.q_grid || beta_out == nullptr,
+             "gp_kernel_matvec: beta_out given but the query is not ray-traced");
+  cudaStream_t s = as_cuda(stream);
+  if (P.n == 0) return LR_OK;
+  if (P.m == 0) {
+    LR_CHECK_CUDA(cudaMemsetAsync(out, 0, sizeof(float) * (size_t)P.n, s));
+    return LR_OK;
+  }
+  char* ws = static_cast<char*>(workspace);
+  // query points
+  const float2* xq = reinterpret_cast<const float2*>(query->xy);
+  if (P.q_raytrace || P.q_grid) {
+    float2* qb = beta_out ? reinterpret_cast<float2*>(beta_out) : reinterpret_cast<float2*>(ws + P.off_qbeta);
+    st = P.q_raytrace ? launch_raytrace(query, qb, nullptr, s) : launch_grid_points(query->grid, qb, s);
+    if (st != LR_OK) return st;
+    xq = qb;
+  }
+  // source points
+  SrcDesc S{};
+  S.m = P.m;
+  S.n_tiles = P.n_tiles;
+  S.segs = P.segs;
+  if (P.self) {
+    S.xy = xq;
+  } else if (P.s_raytrace) {
+    float2* sb = reinterpret_cast<float2*>(ws + P.off_sbeta);
+    st = launch_raytrace(source, sb, nullptr, s);
+    if (st != LR_OK) return st;
+    S.xy = sb;
+  } else if (P.s_grid) {
+    S.xy = nullptr;
+    S.g = grid_dev(source->grid);
+  } else {
+    S.xy = reinterpret_cast<const float2*>(source->xy);
+  }
+  MvArgs A;
+  A.x = xq;
+  A.n = P.n;
+  A.src = S;
+  A.v = v;
+  A.neg_c = (float)(-1.4426950408889634 / (2.0 * (double)lengthscale * (double)lengthscale));
+  A.variance = variance;
+  A.chunks = P.chunks;
+  A.out = out;
+  A.partial = reinterpret_cast<float*>(ws + P.off_partial);
+  const unsigned grid = (unsigned)((int64_t)P.row_blocks * P.chunks);
+  if (S.xy)
+    matvec_kernel<false><<<grid, kMvThreads, 0, s>>>(A);
+  else
+    matvec_kernel<true><<<grid, kMvThreads, 0, s>>>(A);
+  LR_CHECK_CUDA(cudaGetLastError());
+  if (P.chunks > 1) {
+    merge_chunks_kernel<<<(unsigned)((P.n + 255) / 256), 256, 0, s>>>(A.partial, P.chunks, P.n, variance, out);
+    LR_CHECK_CUDA(cudaGetLastError());
+  }
+  return LR_OK;
+}

@@ -1,0 +1,244 @@
+// a1-a5: pixel-grid generation and the lens ray-trace beta = xi - alpha(xi).
+//
+// One thread per image-plane point. The SPLE and shear terms are evaluated in
+// registers from per-lens constants passed as a kernel parameter; the
+// subhalo records are staged into shared memory in chunks by a bulk
+// asynchronous copy (the TMA engine's 1-D form) and reused by every point of
+// the CTA. Stores are coalesced float2 writes.
+#include <math.h>
+
+#include "host.cuh"
+#include "lens.cuh"
+#include "tma.cuh"
+
+namespace lr {
+
+constexpr int kRtThreads = 256;
+constexpr int kSubChunk = 256;  // subhalos staged per chunk (multiple of 4)
+
+__global__ void grid_points_kernel(GridDev g, int64_t n, float2* out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = grid_point(g, i);
+}
+
+// Converts raw records (5 floats) into the prepared form.
+__device__ __forceinline__ SubRec prep_sub(const float* r, int profile) {
+  SubRec h;
+  h.xh = r[0];
+  h.yh = r[1];
+  if (profile == LR_PROFILE_POINT_MASS) {
+    h.its2 = r[2] * r[2];
+    h.A = h.tau = h.tau2 = h.t2m1_t = h.C = 0.f;
+  } else {
+    const float ks = r[2], ts = r[3], tau = r[4];
+    const float t2 = tau * tau;
+    h.its2 = 1.0f / (ts * ts);
+    h.A = 4.0f * ks * t2 / ((t2 + 1.0f) * (t2 + 1.0f));
+    h.tau = tau;
+    h.tau2 = t2;
+    h.t2m1_t = (t2 - 1.0f) / tau;
+    h.C = tau * kPi + (t2 - 1.0f) * logf(tau);
+  }
+  return h;
+}
+
+// Stages subhalo records [h0, h0 + cnt) into shared memory as SubRec.
+// Returns false (all threads) if the bulk-copy wait timed out.
+__device__ bool stage_subs(const float* __restrict__ sub, int h0, int cnt, int profile, float* raw, SubRec* recs,
+                           uint64_t* bar, uint32_t& phase, bool bulk_ok, int* fault) {
+  const float* src = sub + 5 * (int64_t)h0;
+  const uint32_t bytes = 20u * (uint32_t)cnt;
+  const uint32_t bulk_bytes = bulk_ok ? (bytes & ~15u) : 0u;
+  if (threadIdx.x == 0 && bulk_bytes > 0) {
+    // order this CTA's earlier generic-proxy accesses of `raw` before the async write
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    mbar_expect_tx(bar, bulk_bytes);
+    bulk_g2s(raw, src, bulk_bytes, bar);
+  }
+  // the ragged tail (< 16 B) or everything when unaligned: plain loads
+  for (uint32_t w = bulk_bytes / 4 + threadIdx.x; w < bytes / 4; w += blockDim.x) raw[w] = __ldg(src + w);
+  bool ok = true;
+  if (bulk_bytes > 0) ok = mbar_wait_bounded(bar, phase, fault);
+  phase ^= (bulk_bytes > 0) ? 1u : 0u;
+  __syncthreads();
+  if (__syncthreads_or(!ok)) return false;
+  for (int t = threadIdx.x; t < cnt; t += blockDim.x) recs[t] = prep_sub(raw + 5 * t, profile);
+  __syncthreads();
+  return true;
+}
+
+template <int PROFILE>
+__device__ __forceinline__ void add_subs(const SubRec* recs, int cnt, float x, float y, float& sx, float& cx,
+                                         float& sy, float& cy) {
+#pragma unroll 2
+  for (int t = 0; t < cnt; ++t) {
+    const SubRec h = recs[t];
+    const float dx = x - h.xh, dy = y - h.yh;
+    const float R2 = fmaf(dx, dx, dy * dy);
+    const float m = (PROFILE == LR_PROFILE_POINT_MASS) ? pointmass_m(h, R2) : tnfw_m(h, R2);
+    // Kahan-compensated accumulation over subhalos
+    const float yx = fmaf(m, dx, -cx);
+    const float tx = sx + yx;
+    cx = (tx - sx) - yx;
+    sx = tx;
+    const float yy = fmaf(m, dy, -cy);
+    const float ty = sy + yy;
+    cy = (ty - sy) - yy;
+    sy = ty;
+  }
+}
+
+template <int PROFILE>
+__global__ void __launch_bounds__(kRtThreads) raytrace_kernel(LensConst L, GridDev g, const float2* __restrict__ xi,
+                                                              int64_t n, const float* __restrict__ sub, int n_sub,
+                                                              int bulk_ok, float2* __restrict__ beta,
+                                                              float2* __restrict__ alpha_out, int* fault) {
+  __shared__ __align__(16) float raw[5 * kSubChunk];
+  __shared__ __align__(16) SubRec recs[kSubChunk];
+  __shared__ __align__(8) uint64_t bar;
+  const int64_t i = (int64_t)blockIdx.x * kRtThreads + threadIdx.x;
+  const bool valid = i < n;
+  const int64_t ii = valid ? i : (n - 1);
+  const float2 p = xi ? xi[ii] : grid_point(g, ii);
+
+  float ax, ay;
+  sple_alpha(L, p.x, p.y, ax, ay);
+  // external shear about the origin
+  ax = fmaf(L.g1, p.x, fmaf(L.g2, p.y, ax));
+  ay = fmaf(L.g2, p.x, fmaf(-L.g1, p.y, ay));
+
+  if (n_sub > 0) {
+    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    __syncthreads();
+    uint32_t phase = 0;
+    float sx = 0.f, cx = 0.f, sy = 0.f, cy = 0.f;
+    for (int h0 = 0; h0 < n_sub; h0 += kSubChunk) {
+      const int cnt = min(kSubChunk, n_sub - h0);
+      if (!stage_subs(sub, h0, cnt, PROFILE, raw, recs, &bar, phase, bulk_ok != 0, fault)) return;
+      add_subs<PROFILE>(recs, cnt, p.x, p.y, sx, cx, sy, cy);
+      __syncthreads();
+    }
+    ax += sx - cx;
+    ay += sy - cy;
+  }
+  if (valid) {
+    beta[i] = make_float2(p.x - ax, p.y - ay);
+    if (alpha_out) alpha_out[i] = make_float2(ax, ay);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+
+static bool finitef(float v) { return isfinite(v); }
+
+lr_status make_lens_const(const lr_lens* lens, LensConst* out) {
+  LR_REQUIRE(lens != nullptr, "lens is NULL");
+  const float* f = &lens->x0;
+  for (int k = 0; k < 8; ++k) LR_REQUIRE(finitef(f[k]), "lens parameter %d is not finite", k);
+  LR_REQUIRE(lens->q > 0.f && lens->q <= 1.f, "lens q = %g outside (0, 1]", (double)lens->q);
+  LR_REQUIRE(lens->gamma > 1.f && lens->gamma < 3.f, "lens gamma = %g outside (1, 3)", (double)lens->gamma);
+  LR_REQUIRE(lens->theta_e >= 0.f, "lens theta_e = %g < 0", (double)lens->theta_e);
+  const double q = lens->q, gam = lens->gamma, te = lens->theta_e, phi = lens->phi;
+  LensConst L;
+  memset(&L, 0, sizeof L);
+  L.x0 = lens->x0;
+  L.y0 = lens->y0;
+  L.c = (float)cos(phi);
+  L.s = (float)sin(phi);
+  L.sq = (float)sqrt(q);
+  L.isq = (float)(1.0 / sqrt(q));
+  L.pre = (float)(pow(te, gam - 1.0) * 2.0 * sqrt(q) / (1.0 + q));
+  L.half_expo = (float)(0.5 * (1.0 - gam));
+  L.g1 = lens->g1;
+  L.g2 = lens->g2;
+  // 2F1(1, a; b; -f w) = sum_n c_n (-f)^n w^n, c_n = prod_{k<=n} (a+k-1)/(b+k-1)
+  const double a = 0.5 * (gam - 1.0), b = 0.5 * (5.0 - gam), fq = (1.0 - q) / (1.0 + q);
+  double c = 1.0, fn = 1.0;
+  int n = 0;
+  L.d[0] = 1.0f;
+  for (n = 1; n < kMaxSeriesTerms; ++n) {
+    // tail bound: |d_n| f / (1 - f) (coefficient ratios are below 1 for gamma < 3)
+    if (fq == 0.0 || fabs(c * fn) * fq / (1.0 - fq) < 1e-9) break;
+    c *= (a + n - 1.0) / (b + n - 1.0);
+    fn *= -fq;
+    L.d[n] = (float)(c * fn);
+  }
+  LR_REQUIRE(fq == 0.0 || fabs(c * fn) * fq / (1.0 - fq) < 1e-9,
+             "lens q = %g too small: the deflection series needs more than %d terms", q, kMaxSeriesTerms);
+  L.nterms = n;
+  *out = L;
+  return LR_OK;
+}
+
+int64_t grid_count(const lr_grid& g) { return (int64_t)g.nx * g.ss * (int64_t)g.ny * g.ss; }
+
+lr_status validate_points(const lr_points* p, const char* what, bool need_lens) {
+  LR_REQUIRE(p != nullptr, "%s: point set is NULL", what);
+  LR_REQUIRE(p->n >= 0, "%s: n = %lld < 0", what, (long long)p->n);
+  LR_REQUIRE(p->n < (int64_t(1) << 31), "%s: n = %lld exceeds 2^31 - 1", what, (long long)p->n);
+  if (p->n == 0) {
+    // empty set: positions are never read (an empty tensor has a NULL data pointer)
+  } else if (p->xy == nullptr) {
+    const lr_grid& g = p->grid;
+    LR_REQUIRE(g.nx > 0 && g.ny > 0 && g.ss > 0, "%s: grid dimensions must be positive", what);
+    LR_REQUIRE(isfinite(g.pix) && g.pix > 0.f && isfinite(g.cx) && isfinite(g.cy), "%s: bad grid geometry", what);
+    LR_REQUIRE((int64_t)g.nx * g.ss < (1 << 24) && (int64_t)g.ny * g.ss < (1 << 24),
+               "%s: grid side exceeds 2^24 points", what);
+    LR_REQUIRE(grid_count(g) == p->n, "%s: grid has %lld points but n = %lld", what, (long long)grid_count(g),
+               (long long)p->n);
+  } else {
+    LR_REQUIRE(((uintptr_t)p->xy & 7u) == 0, "%s: xy must be 8-byte aligned", what);
+  }
+  if (need_lens) LR_REQUIRE(p->lens != nullptr, "%s: a lens is required", what);
+  if (p->lens) {
+    LR_REQUIRE(p->n_sub >= 0, "%s: n_sub < 0", what);
+    LR_REQUIRE(p->n_sub == 0 || p->sub != nullptr, "%s: sub is NULL with n_sub = %d", what, p->n_sub);
+    LR_REQUIRE(p->sub == nullptr || ((uintptr_t)p->sub & 3u) == 0, "%s: sub must be 4-byte aligned", what);
+    LR_REQUIRE(p->profile == LR_PROFILE_TNFW || p->profile == LR_PROFILE_POINT_MASS, "%s: unknown profile %d",
+               what, p->profile);
+  }
+  return LR_OK;
+}
+
+lr_status launch_grid_points(const lr_grid& g, float2* out, cudaStream_t s) {
+  const int64_t n = grid_count(g);
+  if (n == 0) return LR_OK;
+  grid_points_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(grid_dev(g), n, out);
+  LR_CHECK_CUDA(cudaGetLastError());
+  return LR_OK;
+}
+
+lr_status launch_raytrace(const lr_points* p, float2* beta, float2* alpha, cudaStream_t s) {
+  LensConst L;
+  lr_status st = make_lens_const(p->lens, &L);
+  if (st != LR_OK) return st;
+  if (p->n == 0) return LR_OK;
+  int* fault = fault_ptr();
+  LR_REQUIRE(fault != nullptr, "could not resolve the device fault word");
+  const GridDev g = p->xy ? GridDev{} : grid_dev(p->grid);
+  const int bulk_ok = (((uintptr_t)p->sub & 15u) == 0) ? 1 : 0;
+  const unsigned blocks = (unsigned)((p->n + kRtThreads - 1) / kRtThreads);
+  const float2* xi = reinterpret_cast<const float2*>(p->xy);
+  const int ns = p->n_sub;
+  if (p->profile == LR_PROFILE_POINT_MASS)
+    raytrace_kernel<LR_PROFILE_POINT_MASS><<<blocks, kRtThreads, 0, s>>>(L, g, xi, p->n, p->sub, ns, bulk_ok, beta,
+                                                                         alpha, fault);
+  else
+    raytrace_kernel<LR_PROFILE_TNFW><<<blocks, kRtThreads, 0, s>>>(L, g, xi, p->n, p->sub, ns, bulk_ok, beta, alpha,
+                                                                   fault);
+  LR_CHECK_CUDA(cudaGetLastError());
+  return LR_OK;
+}
+
+}  // namespace lr
+
+extern "C" lr_status lens_raytrace(const lr_points* pts, float* beta_out, float* alpha_out, lr_stream stream) {
+  lr_status st = lr::validate_points(pts, "lens_raytrace", true);
+  if (st != LR_OK) return st;
+  LR_REQUIRE(beta_out != nullptr || pts->n == 0, "lens_raytrace: beta_out is NULL");
+  LR_REQUIRE(((uintptr_t)beta_out & 7u) == 0 && ((uintptr_t)alpha_out & 7u) == 0,
+             "lens_raytrace: outputs must be 8-byte aligned");
+  return lr::launch_raytrace(pts, reinterpret_cast<float2*>(beta_out), reinterpret_cast<float2*>(alpha_out),
+                             lr::as_cuda(stream));
+}
