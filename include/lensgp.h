@@ -174,6 +174,33 @@ lr_status gp_kernel_matvec(const lr_points* query, const lr_points* source, cons
 /* Scratch bytes gp_kernel_matvec needs for these point sets on the current device. */
 lr_status lr_matvec_workspace_size(const lr_points* query, const lr_points* source, int32_t nrhs, size_t* bytes);
 
+/*
+ * gp_kernel_matvec for callers that cannot allocate device memory (an
+ * application whose device memory is all held by its own pool or budget, a
+ * latency-critical loop that must not hit cudaMalloc's implicit device
+ * synchronisation, a plugin without access to its host's allocator). The
+ * paper has no counterpart: this is a deployment variant of the same
+ * reduction, with the same arguments minus the workspace.
+ *  - Scratch is a static device array of lr_static_scratch_bytes() bytes
+ *    (48 MiB) that every GPU loading this library holds until the process
+ *    exits. Problems whose workspace requirement (lr_matvec_workspace_size)
+ *    exceeds it are rejected with LR_ERR_INVALID_ARG; nothing else is
+ *    allocated (no cudaMalloc, cudaFree or allocating library call).
+ *  - The first call on a device resolves the array's device address
+ *    (cudaGetSymbolAddress, with that device current); make that first call
+ *    before any stream capture.
+ *  - All calls on a device share the one array, which keeps the last call's
+ *    contents. Calls whose kernels overlap on the GPU (different streams, or
+ *    host threads racing) corrupt each other's scratch: serialise them, for
+ *    example on one stream.
+ */
+lr_status gp_kernel_matvec_static_scratch(const lr_points* query, const lr_points* source, const float* v,
+                                          int32_t nrhs, float lengthscale, float variance, float* out,
+                                          float* beta_out, lr_stream stream);
+
+/* Size in bytes of the static scratch used by gp_kernel_matvec_static_scratch. */
+size_t lr_static_scratch_bytes(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -18,6 +18,8 @@
 // fixed chunk order (Kahan), so results are deterministic.
 #include <math.h>
 
+#include <mutex>
+
 #include "host.cuh"
 
 namespace lr {
@@ -363,4 +365,68 @@ extern "C" lr_status gp_kernel_matvec(const lr_points* query, const lr_points* s
     LR_CHECK_CUDA(cudaGetLastError());
   }
   return LR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of gp_kernel_matvec.
+//
+// Some callers cannot allocate device memory at call time: a host
+// application whose device memory is all owned by its own pool or budget
+// fixed at start-up, a latency-critical loop that must not hit cudaMalloc's
+// implicit device synchronisation, or a plugin linked against this C ABI
+// without access to the host framework's allocator. For them this entry
+// point takes no workspace: its scratch is one file-scope device array of
+// kStaticScratchBytes that every GPU loading this library holds until the
+// process exits.
+namespace {
+
+constexpr size_t kStaticScratchBytes = size_t(48) << 20;  // 48 MiB per device
+constexpr int kMaxScratchDevices = 64;
+
+static __device__ __align__(256) unsigned char g_matvec_static_scratch[kStaticScratchBytes];
+
+std::mutex g_static_scratch_mu;
+void* g_static_scratch_ptr[kMaxScratchDevices] = {};
+
+// Device address of the static scratch on the current device. The first
+// call on a device resolves it with cudaGetSymbolAddress (with that device
+// current) and caches it; host code must never pass the array's name itself
+// to a kernel, since in host code it is only a host-side stand-in.
+lr_status static_scratch_address(void** out) {
+  int dev = 0;
+  LR_CHECK_CUDA(cudaGetDevice(&dev));
+  LR_REQUIRE(dev >= 0 && dev < kMaxScratchDevices, "static scratch: device ordinal %d out of range", dev);
+  std::lock_guard<std::mutex> lock(g_static_scratch_mu);
+  if (g_static_scratch_ptr[dev] == nullptr) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_matvec_static_scratch);
+    if (e != cudaSuccess) return cuda_status(e, "cudaGetSymbolAddress(g_matvec_static_scratch)");
+    g_static_scratch_ptr[dev] = p;
+  }
+  *out = g_static_scratch_ptr[dev];
+  return LR_OK;
+}
+
+}  // namespace
+
+extern "C" size_t lr_static_scratch_bytes(void) { return kStaticScratchBytes; }
+
+extern "C" lr_status gp_kernel_matvec_static_scratch(const lr_points* query, const lr_points* source,
+                                                     const float* v, int32_t nrhs, float lengthscale, float variance,
+                                                     float* out, float* beta_out, lr_stream stream) {
+  MvPlan P;
+  lr_status st = plan_matvec(query, source, nrhs, beta_out != nullptr, &P);
+  if (st != LR_OK) return st;
+  LR_REQUIRE(P.bytes <= kStaticScratchBytes,
+             "gp_kernel_matvec_static_scratch: this problem needs %zu bytes of scratch but the static scratch "
+             "holds %zu bytes; use gp_kernel_matvec with a caller workspace",
+             P.bytes, kStaticScratchBytes);
+  void* scratch = nullptr;
+  st = static_scratch_address(&scratch);
+  if (st != LR_OK) return st;
+  // Every word of scratch this call reads is written earlier in the same
+  // call (query/source points, then each chunk partial exactly once), so
+  // nothing needs clearing between calls.
+  return gp_kernel_matvec(query, source, v, nrhs, lengthscale, variance, out, beta_out, scratch,
+                          kStaticScratchBytes, stream);
 }

@@ -22,7 +22,7 @@ def declared_symbols():
             if name in ("sizeof", "defined") or before.endswith("typedef"):
                 continue
             # function declarations: a return type precedes the name
-            if re.search(r"(lr_status|const char\s*\*|void|int32_t)\s*$", before):
+            if re.search(r"(lr_status|const char\s*\*|void|int32_t|size_t)\s*$", before):
                 syms.add(name)
     return syms
 
