@@ -174,6 +174,67 @@ lr_status gp_kernel_matvec(const lr_points* query, const lr_points* source, cons
 /* Scratch bytes gp_kernel_matvec needs for these point sets on the current device. */
 lr_status lr_matvec_workspace_size(const lr_points* query, const lr_points* source, int32_t nrhs, size_t* bytes);
 
+/* ------------------------------------------------------------------------ */
+/* Backward (gradients through the reduction and the ray-trace)               */
+
+/*
+ * Gradient outputs of gp_kernel_matvec_bwd. Every pointer is device memory
+ * owned by the caller, or NULL when that gradient is not wanted; requested
+ * outputs are overwritten (not accumulated).
+ *   d_v            float[m]     dL/dv
+ *   d_x            float[n][2]  dL/d(query points after ray-tracing); for a
+ *                               self-kernel both roles of each point
+ *   d_y            float[m][2]  dL/d(source points): explicit, non-self only
+ *   d_lengthscale  double[1]    dL/dl
+ *   d_variance     double[1]    dL/dvariance
+ *   d_lens         double[7]    dL/d(x0, y0, q, phi, theta_e, g1, g2) of the
+ *                               query's lens (slope held fixed)
+ *   d_sub          double[S][4] dL/d(x_h, y_h, kappa_s | theta_pm, theta_s)
+ */
+typedef struct {
+  float* d_v;
+  float* d_x;
+  float* d_y;
+  double* d_lengthscale;
+  double* d_variance;
+  double* d_lens;
+  double* d_sub;
+} lr_grads;
+
+/*
+ * Vector-Jacobian product of gp_kernel_matvec for Loss = sum_i g_out_i out_i
+ * (g_out: device float[n]), recompute-only: the kernel values are evaluated
+ * again, nothing of size n x m is stored, and the ray-traced points are
+ * recomputed from the lens. Per pair (k_ij = exp(-d_ij^2/(2 l^2))):
+ *   d_v_j = var sum_i k_ij g_i,  d_x_i = var/l^2 g_i sum_j k_ij v_j (y_j - x_i)
+ *   (+ the column role for a self-kernel), d_l = var/l^3 sum g_i v_j k_ij d_ij^2,
+ *   d_var = sum g_i v_j k_ij; then through beta = xi - alpha(xi) to the lens
+ *   and subhalo parameters. Pair sums are FP32 with Kahan-merged tiles;
+ *   parameter and hyperparameter sums are FP64. Deterministic.
+ * Same arguments and conventions as gp_kernel_matvec; workspace of at least
+ * lr_matvec_bwd_workspace_size() bytes, 256-byte aligned.
+ * Errors: LR_ERR_INVALID_ARG also when d_y is requested for grid or
+ * self-kernel sources, lens gradients without a ray-traced query, or a
+ * ray-traced source set distinct from the query.
+ */
+lr_status gp_kernel_matvec_bwd(const lr_points* query, const lr_points* source, const float* v, int32_t nrhs,
+                               float lengthscale, float variance, const float* g_out, const lr_grads* grads,
+                               void* workspace, size_t workspace_bytes, lr_stream stream);
+
+/* Scratch bytes gp_kernel_matvec_bwd needs for these point sets and requested gradients. */
+lr_status lr_matvec_bwd_workspace_size(const lr_points* query, const lr_points* source, int32_t nrhs,
+                                       const lr_grads* grads, size_t* bytes);
+
+/*
+ * Ray-trace backward alone: given d_beta = dL/dbeta (device float[n][2]) for
+ * the points of `pts` (which must carry a lens), writes d_lens (double[7],
+ * dL/d(x0, y0, q, phi, theta_e, g1, g2)) and d_sub (double[S][4]); either may
+ * be NULL. Workspace of lr_raytrace_vjp_workspace_size() bytes.
+ */
+lr_status lens_raytrace_vjp(const lr_points* pts, const float* d_beta, double* d_lens, double* d_sub,
+                            void* workspace, size_t workspace_bytes, lr_stream stream);
+lr_status lr_raytrace_vjp_workspace_size(const lr_points* pts, size_t* bytes);
+
 /*
  * gp_kernel_matvec for callers that cannot allocate device memory (an
  * application whose device memory is all held by its own pool or budget, a

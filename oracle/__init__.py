@@ -74,9 +74,9 @@ def lib():
         L.orc_sple_kappa.argtypes = [_D, _D, ctypes.POINTER(OrcLens)]
         L.orc_sple_kappa.restype = _D
         L.orc_raytrace.argtypes = [_P, _I64, ctypes.POINTER(OrcLens), _P, _I32, _I32, _P, _P]
-        L.orc_raytrace_vjp.argtypes = [_P, _I64, ctypes.POINTER(OrcLens), _P, _I32, _I32, _P, _P, _P]
+        L.orc_raytrace_vjp.argtypes = [_P, _I64, ctypes.POINTER(OrcLens), _P, _I32, _I32, _P, _P, _P, _P, _P]
         L.orc_kernel_matvec.argtypes = [_P, _I64, _P, _I64, _P, _D, _D, _P, _I64, _P, _P, _P]
-        L.orc_kernel_matvec_vjp.argtypes = [_P, _I64, _P, _I64, _P, _D, _D, _P, _I32, _P, _P, _P, _P, _P]
+        L.orc_kernel_matvec_vjp.argtypes = [_P, _I64, _P, _I64, _P, _D, _D, _P, _I32, _P, _P, _P, _P, _P, _P]
         L.orc_num_threads.restype = _I32
         _lib = L
     return _lib
@@ -137,18 +137,21 @@ def raytrace(xi, lens, sub=None, profile=0):
     return alpha, beta
 
 
-def raytrace_vjp(xi, lens, sub, d_beta, profile=0):
+def raytrace_vjp(xi, lens, sub, d_beta, profile=0, with_abs=False):
     """Gradient of sum(d_beta * beta) w.r.t. (x0, y0, q, phi, theta_e, g1, g2) and per subhalo
-    (x_h, y_h, kappa_s | theta_pm, theta_s)."""
+    (x_h, y_h, kappa_s | theta_pm, theta_s). With `with_abs`, also the sums of absolute
+    per-point terms (tolerance scales)."""
     xi = _pairs(xi)
     s, ns = _subs(sub)
     L = _lens(lens)
     db = np.ascontiguousarray(d_beta, dtype=np.float64)
     d_lens = np.empty(7, np.float64)
     d_sub = np.empty((ns, 4), np.float64)
+    a_lens = np.empty(7, np.float64)
+    a_sub = np.empty((ns, 4), np.float64)
     lib().orc_raytrace_vjp(_ptr(xi), xi.shape[0], ctypes.byref(L), _ptr(s), ns, profile, _ptr(db), _ptr(d_lens),
-                           _ptr(d_sub) if ns else None)
-    return d_lens, d_sub
+                           _ptr(d_sub) if ns else None, _ptr(a_lens), _ptr(a_sub) if ns else None)
+    return (d_lens, d_sub, a_lens, a_sub) if with_abs else (d_lens, d_sub)
 
 
 def kernel_matvec(x, y, v, lengthscale, variance=1.0, rows=None, with_sens=False):
@@ -174,8 +177,9 @@ def kernel_matvec_rows(x, rows, y, v, lengthscale, variance=1.0):
     return kernel_matvec(x, y, v, lengthscale, variance, rows=rows)
 
 
-def kernel_matvec_vjp(x, y, v, lengthscale, variance, g, self_kernel=False):
-    """a7: dict with d_v, d_x, d_y (None for a self-kernel), d_len, d_var for Loss = sum_i g_i out_i."""
+def kernel_matvec_vjp(x, y, v, lengthscale, variance, g, self_kernel=False, with_abs=False):
+    """a7: dict with d_v, d_x, d_y (None for a self-kernel), d_len, d_var for Loss = sum_i g_i out_i.
+    With `with_abs`, also the matching sums of absolute terms under keys *_abs."""
     x, y = _pairs(x), _pairs(y)
     v = np.ascontiguousarray(v, dtype=np.float64).reshape(-1)
     g = np.ascontiguousarray(g, dtype=np.float64).reshape(-1)
@@ -185,6 +189,12 @@ def kernel_matvec_vjp(x, y, v, lengthscale, variance, g, self_kernel=False):
     d_y = None if self_kernel else np.empty((m, 2), np.float64)
     d_len = np.zeros(1, np.float64)
     d_var = np.zeros(1, np.float64)
+    sc = [np.empty(m), np.empty((n, 2)), np.empty((m, 2)), np.zeros(1), np.zeros(1)]
+    arr = (ctypes.c_void_p * 5)(*[a.ctypes.data for a in sc]) if with_abs else None
     lib().orc_kernel_matvec_vjp(_ptr(x), n, _ptr(y), m, _ptr(v), lengthscale, variance, _ptr(g), int(self_kernel),
-                                _ptr(d_v), _ptr(d_x), _ptr(d_y), _ptr(d_len), _ptr(d_var))
-    return {"d_v": d_v, "d_x": d_x, "d_y": d_y, "d_len": float(d_len[0]), "d_var": float(d_var[0])}
+                                _ptr(d_v), _ptr(d_x), _ptr(d_y), _ptr(d_len), _ptr(d_var), arr)
+    out = {"d_v": d_v, "d_x": d_x, "d_y": d_y, "d_len": float(d_len[0]), "d_var": float(d_var[0])}
+    if with_abs:
+        out.update({"d_v_abs": sc[0], "d_x_abs": sc[1], "d_y_abs": None if self_kernel else sc[2],
+                    "d_len_abs": float(sc[3][0]), "d_var_abs": float(sc[4][0])})
+    return out

@@ -337,13 +337,16 @@ ORC_API void orc_raytrace(const double* xi, int64_t n, const orc_lens* L, const 
  * dual numbers through the same expressions as orc_raytrace. */
 ORC_API void orc_raytrace_vjp(const double* xi, int64_t n, const orc_lens* L, const double* sub, int32_t n_sub,
                               int32_t profile, const double* d_beta, double* d_lens /*[7]*/,
-                              double* d_sub /*[S][4] or NULL*/) {
-  nsum acc[7];
+                              double* d_sub /*[S][4] or NULL*/, double* d_lens_abs /*[7] or NULL*/,
+                              double* d_sub_abs /*[S][4] or NULL*/) {
+  nsum acc[7], aacc[7];
   memset(acc, 0, sizeof acc);
+  memset(aacc, 0, sizeof aacc);
 #pragma omp parallel
   {
-    nsum loc[7];
+    nsum loc[7], aloc[7];
     memset(loc, 0, sizeof loc);
+    memset(aloc, 0, sizeof aloc);
 #pragma omp for schedule(static)
     for (int64_t i = 0; i < n; ++i) {
       const double x = xi[2 * i], y = xi[2 * i + 1];
@@ -351,30 +354,48 @@ ORC_API void orc_raytrace_vjp(const double* xi, int64_t n, const orc_lens* L, co
       sple_dual(dn_const(x), dn_const(y), dn_var(L->x0, 0), dn_var(L->y0, 1), dn_var(L->q, 2), dn_var(L->phi, 3),
                 dn_var(L->theta_e, 4), L->gamma, &ax, &ay);
       const double gx = d_beta[2 * i], gy = d_beta[2 * i + 1];
-      for (int k = 0; k < 5; ++k) ns_add(&loc[k], -(ax.d[k] * gx + ay.d[k] * gy));
+      double t[7];
+      for (int k = 0; k < 5; ++k) t[k] = -(ax.d[k] * gx + ay.d[k] * gy);
       /* shear: dalpha/dg1 = (x, -y), dalpha/dg2 = (y, x) */
-      ns_add(&loc[5], -(x * gx - y * gy));
-      ns_add(&loc[6], -(y * gx + x * gy));
+      t[5] = -(x * gx - y * gy);
+      t[6] = -(y * gx + x * gy);
+      for (int k = 0; k < 7; ++k) {
+        ns_add(&loc[k], t[k]);
+        ns_add(&aloc[k], fabs(t[k]));
+      }
     }
 #pragma omp critical
     for (int k = 0; k < 7; ++k) {
       ns_add(&acc[k], loc[k].s);
       ns_add(&acc[k], loc[k].c);
+      ns_add(&aacc[k], aloc[k].s);
+      ns_add(&aacc[k], aloc[k].c);
     }
   }
-  for (int k = 0; k < 7; ++k) d_lens[k] = ns_val(&acc[k]);
+  for (int k = 0; k < 7; ++k) {
+    d_lens[k] = ns_val(&acc[k]);
+    if (d_lens_abs) d_lens_abs[k] = ns_val(&aacc[k]);
+  }
   if (!d_sub) return;
 #pragma omp parallel for schedule(dynamic, 1)
   for (int32_t h = 0; h < n_sub; ++h) {
-    nsum a4[4];
+    nsum a4[4], b4[4];
     memset(a4, 0, sizeof a4);
+    memset(b4, 0, sizeof b4);
     for (int64_t i = 0; i < n; ++i) {
       dn ax, ay;
       sub_dual(xi[2 * i], xi[2 * i + 1], sub + 5 * (int64_t)h, profile, 1, &ax, &ay);
       const double gx = d_beta[2 * i], gy = d_beta[2 * i + 1];
-      for (int k = 0; k < 4; ++k) ns_add(&a4[k], -(ax.d[k] * gx + ay.d[k] * gy));
+      for (int k = 0; k < 4; ++k) {
+        const double t = -(ax.d[k] * gx + ay.d[k] * gy);
+        ns_add(&a4[k], t);
+        ns_add(&b4[k], fabs(t));
+      }
     }
-    for (int k = 0; k < 4; ++k) d_sub[4 * (int64_t)h + k] = ns_val(&a4[k]);
+    for (int k = 0; k < 4; ++k) {
+      d_sub[4 * (int64_t)h + k] = ns_val(&a4[k]);
+      if (d_sub_abs) d_sub_abs[4 * (int64_t)h + k] = ns_val(&b4[k]);
+    }
   }
 }
 
@@ -429,20 +450,29 @@ ORC_API void orc_kernel_matvec(const double* x, int64_t n, const double* y, int6
  *   d_var   = sum_ij g_i v_j k_ij / var
  * For a self-kernel (x and y the same point set, `self` != 0) the point
  * gradient is the sum of both roles and is returned in d_x (d_y unused).
+ * `scale` (optional, 5 arrays) receives the matching sums of absolute terms
+ * (the scales of the parity tolerances): |d_v|, |d_x| (per component, both
+ * roles), |d_y|, |d_len|, |d_var| in the order
+ *   scale[0] = d_v_abs[m], scale[1] = d_x_abs[n][2], scale[2] = d_y_abs[m][2],
+ *   scale[3] = d_len_abs[1], scale[4] = d_var_abs[1].
  * Every output pointer may be NULL. */
 ORC_API void orc_kernel_matvec_vjp(const double* x, int64_t n, const double* y, int64_t m, const double* v,
                                    double lengthscale, double variance, const double* g, int32_t self, double* d_v,
-                                   double* d_x /*[n][2]*/, double* d_y /*[m][2]*/, double* d_len, double* d_var) {
+                                   double* d_x /*[n][2]*/, double* d_y /*[m][2]*/, double* d_len, double* d_var,
+                                   double* const* scale /* [5] or NULL */) {
   const double l2 = lengthscale * lengthscale, inv2l2 = 1.0 / (2.0 * l2);
-  nsum tl = {0, 0}, tv = {0, 0};
+  double* s_dv = scale ? scale[0] : NULL;
+  double* s_dx = scale ? scale[1] : NULL;
+  double* s_dy = scale ? scale[2] : NULL;
+  nsum tl = {0, 0}, tv = {0, 0}, tla = {0, 0}, tva = {0, 0};
   /* row pass: d_x (row role), d_len, d_var */
 #pragma omp parallel
   {
-    nsum ll = {0, 0}, lv = {0, 0};
+    nsum ll = {0, 0}, lv = {0, 0}, lla = {0, 0}, lva = {0, 0};
 #pragma omp for schedule(dynamic, 64)
     for (int64_t i = 0; i < n; ++i) {
       const double xi = x[2 * i], yi = x[2 * i + 1];
-      nsum sx = {0, 0}, sy = {0, 0}, sl = {0, 0}, sv = {0, 0};
+      nsum sx = {0, 0}, sy = {0, 0}, sl = {0, 0}, sv = {0, 0}, ax = {0, 0}, ay = {0, 0}, al = {0, 0}, av = {0, 0};
       for (int64_t j = 0; j < m; ++j) {
         const double dx = y[2 * j] - xi, dy = y[2 * j + 1] - yi;
         const double d2 = dx * dx + dy * dy;
@@ -451,13 +481,23 @@ ORC_API void orc_kernel_matvec_vjp(const double* x, int64_t n, const double* y, 
         ns_add(&sy, kv * dy);
         ns_add(&sl, kv * d2);
         ns_add(&sv, kv);
+        ns_add(&ax, fabs(kv * dx));
+        ns_add(&ay, fabs(kv * dy));
+        ns_add(&al, fabs(kv) * d2);
+        ns_add(&av, fabs(kv));
       }
       if (d_x) {
         d_x[2 * i] = g[i] * ns_val(&sx) / l2;
         d_x[2 * i + 1] = g[i] * ns_val(&sy) / l2;
       }
+      if (s_dx) {
+        s_dx[2 * i] = fabs(g[i]) * ns_val(&ax) / l2;
+        s_dx[2 * i + 1] = fabs(g[i]) * ns_val(&ay) / l2;
+      }
       ns_add(&ll, g[i] * ns_val(&sl) / (l2 * lengthscale));
       ns_add(&lv, g[i] * ns_val(&sv) / variance);
+      ns_add(&lla, fabs(g[i]) * ns_val(&al) / (l2 * lengthscale));
+      ns_add(&lva, fabs(g[i]) * ns_val(&av) / fabs(variance));
     }
 #pragma omp critical
     {
@@ -465,34 +505,61 @@ ORC_API void orc_kernel_matvec_vjp(const double* x, int64_t n, const double* y, 
       ns_add(&tl, ll.c);
       ns_add(&tv, lv.s);
       ns_add(&tv, lv.c);
+      ns_add(&tla, lla.s);
+      ns_add(&tla, lla.c);
+      ns_add(&tva, lva.s);
+      ns_add(&tva, lva.c);
     }
   }
   if (d_len) *d_len = ns_val(&tl);
   if (d_var) *d_var = ns_val(&tv);
+  if (scale && scale[3]) *scale[3] = ns_val(&tla);
+  if (scale && scale[4]) *scale[4] = ns_val(&tva);
   /* column pass: d_v, d_y (column role) */
-  double* col = (double*)calloc((size_t)(2 * m), sizeof(double));
+  double* col = (double*)calloc((size_t)(4 * m), sizeof(double));
 #pragma omp parallel for schedule(dynamic, 64)
   for (int64_t j = 0; j < m; ++j) {
     const double yj = y[2 * j], zj = y[2 * j + 1];
-    nsum s = {0, 0}, sx = {0, 0}, sy = {0, 0};
+    nsum s = {0, 0}, sx = {0, 0}, sy = {0, 0}, as = {0, 0}, ax = {0, 0}, ay = {0, 0};
     for (int64_t i = 0; i < n; ++i) {
       const double dx = x[2 * i] - yj, dy = x[2 * i + 1] - zj;
       const double gk = g[i] * variance * exp(-(dx * dx + dy * dy) * inv2l2);
       ns_add(&s, gk);
       ns_add(&sx, gk * dx);
       ns_add(&sy, gk * dy);
+      ns_add(&as, fabs(gk));
+      ns_add(&ax, fabs(gk * dx));
+      ns_add(&ay, fabs(gk * dy));
     }
     if (d_v) d_v[j] = ns_val(&s);
-    col[2 * j] = v[j] * ns_val(&sx) / l2;
-    col[2 * j + 1] = v[j] * ns_val(&sy) / l2;
+    if (s_dv) s_dv[j] = ns_val(&as);
+    col[4 * j] = v[j] * ns_val(&sx) / l2;
+    col[4 * j + 1] = v[j] * ns_val(&sy) / l2;
+    col[4 * j + 2] = fabs(v[j]) * ns_val(&ax) / l2;
+    col[4 * j + 3] = fabs(v[j]) * ns_val(&ay) / l2;
   }
-  if (self && d_x) {
+  if (self) {
     for (int64_t i = 0; i < n; ++i) {
-      d_x[2 * i] += col[2 * i];
-      d_x[2 * i + 1] += col[2 * i + 1];
+      if (d_x) {
+        d_x[2 * i] += col[4 * i];
+        d_x[2 * i + 1] += col[4 * i + 1];
+      }
+      if (s_dx) {
+        s_dx[2 * i] += col[4 * i + 2];
+        s_dx[2 * i + 1] += col[4 * i + 3];
+      }
     }
-  } else if (d_y) {
-    memcpy(d_y, col, sizeof(double) * 2 * (size_t)m);
+  } else {
+    for (int64_t j = 0; j < m; ++j) {
+      if (d_y) {
+        d_y[2 * j] = col[4 * j];
+        d_y[2 * j + 1] = col[4 * j + 1];
+      }
+      if (s_dy) {
+        s_dy[2 * j] = col[4 * j + 2];
+        s_dy[2 * j + 1] = col[4 * j + 3];
+      }
+    }
   }
   free(col);
 }

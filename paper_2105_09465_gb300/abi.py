@@ -46,6 +46,12 @@ class lr_points(ctypes.Structure):
                 ("profile", ctypes.c_int32)]
 
 
+class lr_grads(ctypes.Structure):
+    _fields_ = [("d_v", ctypes.c_void_p), ("d_x", ctypes.c_void_p), ("d_y", ctypes.c_void_p),
+                ("d_lengthscale", ctypes.c_void_p), ("d_variance", ctypes.c_void_p), ("d_lens", ctypes.c_void_p),
+                ("d_sub", ctypes.c_void_p)]
+
+
 _P = ctypes.c_void_p
 _lib = None
 
@@ -64,6 +70,14 @@ SIGNATURES = {
                                                          ctypes.c_int32, ctypes.c_float, ctypes.c_float, _P, _P,
                                                          _P]),
     "lr_static_scratch_bytes": (ctypes.c_size_t, []),
+    "gp_kernel_matvec_bwd": (ctypes.c_int32, [ctypes.POINTER(lr_points), ctypes.POINTER(lr_points), _P,
+                                              ctypes.c_int32, ctypes.c_float, ctypes.c_float, _P,
+                                              ctypes.POINTER(lr_grads), _P, ctypes.c_size_t, _P]),
+    "lr_matvec_bwd_workspace_size": (ctypes.c_int32, [ctypes.POINTER(lr_points), ctypes.POINTER(lr_points),
+                                                      ctypes.c_int32, ctypes.POINTER(lr_grads),
+                                                      ctypes.POINTER(ctypes.c_size_t)]),
+    "lens_raytrace_vjp": (ctypes.c_int32, [ctypes.POINTER(lr_points), _P, _P, _P, _P, ctypes.c_size_t, _P]),
+    "lr_raytrace_vjp_workspace_size": (ctypes.c_int32, [ctypes.POINTER(lr_points), ctypes.POINTER(ctypes.c_size_t)]),
 }
 
 

@@ -124,6 +124,80 @@ def gp_kernel_matvec(query: Points, source: Points | None, v: torch.Tensor, leng
     return (out, beta) if want_beta else out
 
 
+GRADS = ("v", "x", "y", "lengthscale", "variance", "lens", "sub")
+
+
+def gp_kernel_matvec_bwd(query: Points, source: Points | None, v: torch.Tensor, lengthscale: float,
+                         variance: float, g_out: torch.Tensor, want=("v", "x", "lengthscale", "variance"),
+                         workspace: torch.Tensor | None = None, stream=None) -> dict:
+    """Gradients of Loss = sum_i g_out_i out_i (recompute-only backward).
+
+    `want` selects among v, x (query points after ray-tracing), y (explicit
+    non-self sources), lengthscale, variance, lens (7: x0, y0, q, phi,
+    theta_e, g1, g2) and sub (S x 4). Returns a dict of CUDA tensors (the
+    scalar and parameter gradients are float64)."""
+    lib = abi.load()
+    _require_cuda(v, "v")
+    _require_cuda(g_out, "g_out")
+    cq, k1 = to_c_points(query)
+    cs, k2 = to_c_points(source)
+    n, m = cq.n, (cs.n if cs is not None else cq.n)
+    dev = v.device
+    out = {}
+    if "v" in want:
+        out["v"] = torch.empty(m, dtype=torch.float32, device=dev)
+    if "x" in want:
+        out["x"] = torch.empty((n, 2), dtype=torch.float32, device=dev)
+    if "y" in want:
+        out["y"] = torch.empty((m, 2), dtype=torch.float32, device=dev)
+    for k in ("lengthscale", "variance"):
+        if k in want:
+            out[k] = torch.empty(1, dtype=torch.float64, device=dev)
+    if "lens" in want:
+        out["lens"] = torch.empty(7, dtype=torch.float64, device=dev)
+    if "sub" in want:
+        ns = query.sub.shape[0] if query.sub is not None else 0
+        out["sub"] = torch.empty((ns, 4), dtype=torch.float64, device=dev)
+    gr = abi.lr_grads()
+    gr.d_v = out["v"].data_ptr() if "v" in out else None
+    gr.d_x = out["x"].data_ptr() if "x" in out else None
+    gr.d_y = out["y"].data_ptr() if "y" in out else None
+    gr.d_lengthscale = out["lengthscale"].data_ptr() if "lengthscale" in out else None
+    gr.d_variance = out["variance"].data_ptr() if "variance" in out else None
+    gr.d_lens = out["lens"].data_ptr() if "lens" in out else None
+    gr.d_sub = out["sub"].data_ptr() if ("sub" in out and out["sub"].numel()) else None
+    b = ctypes.c_size_t(0)
+    ps = ctypes.byref(cs) if cs is not None else None
+    abi.check(lib.lr_matvec_bwd_workspace_size(ctypes.byref(cq), ps, 1, ctypes.byref(gr), ctypes.byref(b)),
+              "lr_matvec_bwd_workspace_size")
+    need = int(b.value)
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty((max(need, 1),), dtype=torch.uint8, device=dev)
+    st = lib.gp_kernel_matvec_bwd(ctypes.byref(cq), ps, v.data_ptr(), 1, float(lengthscale), float(variance),
+                                  g_out.data_ptr(), ctypes.byref(gr), workspace.data_ptr(), workspace.numel(),
+                                  _stream_handle(stream))
+    abi.check(st, "gp_kernel_matvec_bwd")
+    return out
+
+
+def lens_raytrace_vjp(pts: Points, d_beta: torch.Tensor, stream=None):
+    """(d_lens[7], d_sub[S, 4]) float64 for Loss with dL/dbeta = d_beta."""
+    lib = abi.load()
+    _require_cuda(d_beta, "d_beta", (2,))
+    c, keep = to_c_points(pts)
+    dev = d_beta.device
+    d_lens = torch.empty(7, dtype=torch.float64, device=dev)
+    ns = pts.sub.shape[0] if pts.sub is not None else 0
+    d_sub = torch.empty((ns, 4), dtype=torch.float64, device=dev)
+    b = ctypes.c_size_t(0)
+    abi.check(lib.lr_raytrace_vjp_workspace_size(ctypes.byref(c), ctypes.byref(b)), "lr_raytrace_vjp_workspace_size")
+    ws = torch.empty((max(int(b.value), 1),), dtype=torch.uint8, device=dev)
+    st = lib.lens_raytrace_vjp(ctypes.byref(c), d_beta.data_ptr(), d_lens.data_ptr(),
+                               d_sub.data_ptr() if ns else None, ws.data_ptr(), ws.numel(), _stream_handle(stream))
+    abi.check(st, "lens_raytrace_vjp")
+    return d_lens, d_sub
+
+
 def probe_pipe_rates(device: int = 0) -> dict:
     """Measured per-SM-clock rates: FFMA lanes, FFMA2 lanes, MUFU.EX2; and SM count."""
     lib = abi.load()

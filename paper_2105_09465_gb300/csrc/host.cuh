@@ -11,6 +11,10 @@ lr_status validate_points(const lr_points* p, const char* what, bool need_lens);
 int64_t grid_count(const lr_grid& g);
 lr_status launch_grid_points(const lr_grid& g, float2* out, cudaStream_t s);
 lr_status launch_raytrace(const lr_points* p, float2* beta, float2* alpha, cudaStream_t s);
+lr_status make_lens_grad_const(const lr_lens* lens, LensGradConst* out);
+size_t raytrace_vjp_ws(int64_t n, int32_t n_sub);
+lr_status launch_raytrace_vjp(const lr_points* p, const float2* dbeta, double* d_lens, double* d_sub, void* ws,
+                              cudaStream_t s);
 
 // Rounds a byte count up to a multiple of 256 (workspace sub-allocation).
 inline size_t align256(size_t b) { return (b + 255) & ~size_t(255); }

@@ -138,4 +138,151 @@ __device__ __forceinline__ float pointmass_m(const SubRec& h, float R2) {
   return (R2 > 1e-30f) ? h.its2 / R2 : 0.f;
 }
 
+// Converts a raw subhalo record (5 floats) into the prepared form.
+__device__ __forceinline__ SubRec prep_sub(const float* r, int profile) {
+  SubRec h;
+  h.xh = r[0];
+  h.yh = r[1];
+  if (profile == LR_PROFILE_POINT_MASS) {
+    h.its2 = r[2] * r[2];
+    h.A = h.tau = h.tau2 = h.t2m1_t = h.C = 0.f;
+  } else {
+    const float ks = r[2], ts = r[3], tau = r[4];
+    const float t2 = tau * tau;
+    h.its2 = 1.0f / (ts * ts);
+    h.A = 4.0f * ks * t2 / ((t2 + 1.0f) * (t2 + 1.0f));
+    h.tau = tau;
+    h.tau2 = t2;
+    h.t2m1_t = (t2 - 1.0f) / tau;
+    h.C = tau * kPi + (t2 - 1.0f) * logf(tau);
+  }
+  return h;
+}
+
+// ---------------------------------------------------------------------------
+// Gradients (ray-trace backward). With beta = xi - alpha and G = dL/dbeta,
+// dL/dp = -G . dalpha/dp for every lens or subhalo parameter p.
+
+// tNFW brackets: Gt = B(x)/x^2 (alpha = A Gt d, A = 4 kappa_s tau^2/(tau^2+1)^2)
+// and Ht = g'(x)/(x T) with T = tau^2/(tau^2+1)^2, from
+//   g'(x)/x = T [2F + (tau^2+1)(1-F)/eps - pi/st + (tau^2-1) L/(tau st)],
+// eps = x^2 - 1, (1-F)/eps by its series 1/3 - eps/5 + eps^2/7 - ... near x = 1.
+// Then dalpha/dxi = A [Gt I + (Ht - 2Gt) n n^T] and
+// dalpha/dtheta_s = -A (Ht - 2Gt) d / theta_s.
+__device__ __forceinline__ void tnfw_GH(const SubRec& h, float R2, float& Gt, float& Ht) {
+  const float x2 = R2 * h.its2;
+  if (!(x2 > 1e-20f)) {
+    Gt = 0.f;
+    Ht = 0.f;
+    return;
+  }
+  const float xx = sqrtf(x2);
+  float s;
+  const float F = nfw_F(x2, xx, s);
+  const float st = sqrtf(h.tau2 + x2);
+  const float tp = h.tau + st;
+  const float L = logf(xx / tp);
+  const float t2m1 = h.tau2 - 1.0f;
+  if (x2 < 0.25f) {
+    const float dlx2 = -(h.tau / (1.0f + s) + 1.0f / tp) / tp;
+    const float dl = dlx2 * x2;
+    const float ratio = (dl != 0.f) ? log1pf(dl) / dl : 1.0f;
+    Gt = fmaf(2.0f, F, -kPi / tp) + t2m1 * (F / (1.0f + s) + dlx2 * ratio + L / (h.tau * tp));
+  } else {
+    const float B = fmaf(fmaf(2.0f, x2, t2m1), F, h.C) + st * fmaf(h.t2m1_t, L, -kPi);
+    Gt = B / x2;
+  }
+  const float eps = x2 - 1.0f;
+  float omf;  // (1 - F) / eps
+  if (fabsf(eps) < 0.05f) {
+    float p = 1.0f / 15.0f;
+    p = fmaf(p, -eps, 1.0f / 13.0f);
+    p = fmaf(p, -eps, 1.0f / 11.0f);
+    p = fmaf(p, -eps, 1.0f / 9.0f);
+    p = fmaf(p, -eps, 1.0f / 7.0f);
+    p = fmaf(p, -eps, 1.0f / 5.0f);
+    omf = fmaf(p, -eps, 1.0f / 3.0f);
+  } else {
+    omf = (1.0f - F) / eps;
+  }
+  const float ist = 1.0f / st;
+  Ht = fmaf(2.0f, F, (h.tau2 + 1.0f) * omf) + ist * fmaf(h.t2m1_t, L, -kPi);
+}
+
+// Per-lens constants for the SPLE gradient (host-prepared).
+//  h_n = (n+1) c_{n+1} (-f)^n so that W F'(W) = -f W H(W), dF/df = -W H(W).
+struct LensGradConst {
+  float e;            // (1 - gamma)/2
+  float f;            // (1 - q)/(1 + q)
+  float dlnpre_dq;    // d ln(pre)/dq = 1/(2q) - 1/(1+q)
+  float df_dq;        // -2/(1+q)^2
+  float inv2q;        // 1/(2q)
+  float dlnte;        // (gamma - 1)/theta_e (0 when theta_e == 0)
+  int nterms;
+  int pad_;
+  float hco[kMaxSeriesTerms];
+};
+
+struct cf {
+  float re, im;
+};
+__device__ __forceinline__ cf cmul(cf a, cf b) { return {fmaf(a.re, b.re, -a.im * b.im), fmaf(a.re, b.im, a.im * b.re)}; }
+__device__ __forceinline__ cf cadd(cf a, cf b) { return {a.re + b.re, a.im + b.im}; }
+__device__ __forceinline__ cf cscale(cf a, float s) { return {a.re * s, a.im * s}; }
+__device__ __forceinline__ cf cconj(cf a) { return {a.re, -a.im}; }
+// Re(conj(g) z)
+__device__ __forceinline__ float cdot(cf g, cf z) { return fmaf(g.re, z.re, g.im * z.im); }
+
+// SPLE deflection and the contraction of G = dL/dbeta with -dalpha/dp for
+// p = (x0, y0, q, phi, theta_e). Wirtinger form: alpha' = P F(W) w with
+// w = R_x + i R_y, W = w / conj(w), P = pre (w conj(w))^e; for a real
+// parameter with dw/dp = t: dalpha' = A_w t + A_wb conj(t) (+ explicit terms),
+//   A_w = P ((e+1) F - M),  A_wb = P W (e F + M),  M = f W H(W);
+// alpha = e^{i phi} alpha'.
+__device__ __forceinline__ void sple_vjp(const LensConst& L, const LensGradConst& G, float x, float y, float gx,
+                                         float gy, float out[5]) {
+  const float dx = x - L.x0, dy = y - L.y0;
+  const float u = fmaf(L.c, dx, L.s * dy);
+  const float v = fmaf(L.c, dy, -L.s * dx);
+  const float Rx = L.sq * u, Ry = L.isq * v;
+  const float R2 = fmaf(Rx, Rx, Ry * Ry);
+  if (!(R2 > 1e-24f)) {
+    for (int k = 0; k < 5; ++k) out[k] = 0.f;
+    return;
+  }
+  const float inv = 1.0f / R2;
+  const cf W = {(Rx * Rx - Ry * Ry) * inv, 2.0f * Rx * Ry * inv};
+  cf F = {L.d[L.nterms - 1], 0.f}, H = {G.hco[G.nterms - 1], 0.f};
+  for (int n = L.nterms - 2; n >= 0; --n) F = cadd(cmul(W, F), cf{L.d[n], 0.f});
+  for (int n = G.nterms - 2; n >= 0; --n) H = cadd(cmul(W, H), cf{G.hco[n], 0.f});
+  const float P = L.pre * pow_split(R2, L.half_expo);
+  const cf w = {Rx, Ry};
+  const cf Fw = cmul(F, w);
+  const cf ap = cscale(Fw, P);                    // alpha' (rotated frame)
+  const cf M = cscale(cmul(W, H), G.f);
+  const cf Aw = cscale(cadd(cscale(F, G.e + 1.0f), cscale(M, -1.0f)), P);
+  const cf Awb = cscale(cmul(W, cadd(cscale(F, G.e), M)), P);
+  const cf rot = {L.c, L.s};                      // e^{i phi}
+  const cf g = {gx, gy};
+  const cf gr = cmul(cconj(rot), g);              // conj(e^{i phi})... applied as Re(conj(g) e^{i phi} z) = Re(conj(gr) z)
+  // Re(conj(g) e^{i phi} z) = Re(conj(e^{-i phi} g) z)
+  auto dalpha = [&](cf t) { return cadd(cmul(Aw, t), cmul(Awb, cconj(t))); };
+  const cf tx = {L.sq * L.c, -L.isq * L.s};       // dw/dxi_x
+  const cf ty = {L.sq * L.s, L.isq * L.c};        // dw/dxi_y
+  // x0, y0: dalpha/dx0 = -dalpha/dxi_x, and dL/dp = -Re(conj(g) dalpha/dp)
+  out[0] = cdot(gr, dalpha(tx));
+  out[1] = cdot(gr, dalpha(ty));
+  // q: explicit prefactor and series-coefficient dependence plus dw/dq = conj(w)/(2q)
+  const cf tq = cscale(cconj(w), G.inv2q);
+  const cf dFdf_term = cscale(cmul(cmul(W, H), w), -P * G.df_dq);  // P w dF/df df/dq, dF/df = -W H
+  const cf daq = cadd(cadd(cscale(ap, G.dlnpre_dq), dFdf_term), dalpha(tq));
+  out[2] = -cdot(gr, daq);
+  // phi: dalpha/dphi = i alpha + e^{i phi} dalpha'(dw/dphi), dw/dphi = sq v - i isq u
+  const cf tphi = {L.sq * v, -L.isq * u};
+  const cf daphi = cadd(cf{-ap.im, ap.re}, dalpha(tphi));
+  out[3] = -cdot(gr, daphi);
+  // theta_e: dalpha/dtheta_e = (gamma-1)/theta_e alpha
+  out[4] = -G.dlnte * cdot(gr, ap);
+}
+
 }  // namespace lr

@@ -1,0 +1,562 @@
+// a7: backward of the Gaussian-kernel reduction, recompute-only (k is never
+// stored). For Loss = sum_i g_i out_i with out_i = sum_j var k_ij v_j,
+// k_ij = exp(-|x_i - y_j|^2 / (2 l^2)):
+//   d_x_i = var/l^2 * g_i sum_j k_ij v_j (y_j - x_i)            (row role)
+//         + var/l^2 * v_i sum_j k_ij g_j (y_j - x_i)            (column role, self-kernel)
+//   d_v_j = var sum_i k_ij g_i
+//   d_y_j = var/l^2 * v_j sum_i k_ij g_i (x_i - y_j)            (explicit, non-self sources)
+//   d_l   = var/l^3 * sum_ij g_i v_j k_ij |x_i - y_j|^2
+//   d_var = sum_ij g_i v_j k_ij
+// The row pass runs one sweep over the pairs with the query block in
+// registers (same tiling as the forward pass) and accumulates, per row,
+// A = sum k v, B = sum k v (x_i - y_j), C = sum k v e (e = -log2(e) d^2/(2 l^2))
+// and, for a self-kernel, D = sum k g, E = sum k g (x_i - x_j). Chunk partials
+// are merged in fixed order (Kahan), scalars are reduced in FP64. d_v and d_y
+// of non-self sources are the same reductions with the roles of the two point
+// sets swapped.
+#include <math.h>
+
+#include "host.cuh"
+
+namespace lr {
+
+constexpr int kBwThreads = 128;
+constexpr int kBwR = 4;
+constexpr int kBwRows = kBwThreads * kBwR;  // 512 rows per CTA
+constexpr int kBwTile = 256;
+constexpr int kBwPairs = kBwTile / 2;
+static_assert(kBwPairs == kBwThreads, "one source pair per thread when staging");
+constexpr int kMergeThreads = 256;
+
+struct BwSrc {
+  const float2* xy;  // explicit sources, or NULL for a grid
+  GridDev g;
+  int64_t m;
+  int32_t segs, n_tiles;
+};
+
+struct BwArgs {
+  const float2* x;  // query points [n]
+  int64_t n;
+  BwSrc src;
+  const float* v;   // [m] source weights
+  const float* gs;  // [m] source-side g (self-kernel only: g of the same points)
+  float neg_c;      // -log2(e)/(2 l^2)
+  int32_t chunks;
+  int32_t K;        // quantities per row: 4, or 7 for a self-kernel
+  float* partial;   // [chunks][K][n]
+};
+
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ void kahan(float& s, float& c, float x) {
+  const float y = x - c;
+  const float t = s + y;
+  c = (t - s) - y;
+  s = t;
+}
+
+__device__ __forceinline__ void bw_tile_range(const BwSrc& S, int t, int64_t& j0, int& cnt, int& grow) {
+  if (S.xy) {
+    j0 = (int64_t)t * kBwTile;
+    const int64_t rem = S.m - j0;
+    cnt = rem < kBwTile ? (int)rem : kBwTile;
+    grow = 0;
+  } else {
+    grow = t / S.segs;
+    const int c0 = (t - grow * S.segs) * kBwTile;
+    cnt = min(kBwTile, S.g.W - c0);
+    j0 = (int64_t)grow * S.g.W + c0;
+  }
+}
+
+template <bool GRID, bool SELF>
+__device__ __forceinline__ void bw_load_pair(const BwArgs& A, int t, int p, float4& P, float2& V, float2& Gp) {
+  int64_t j0;
+  int cnt, grow;
+  bw_tile_range(A.src, t, j0, cnt, grow);
+  const int a = 2 * p, b = 2 * p + 1;
+  if (GRID) {
+    const int c0 = (int)(j0 - (int64_t)grow * A.src.g.W);
+    P = make_float4((a < cnt) ? -grid_x(A.src.g, c0 + a) : 0.f, (b < cnt) ? -grid_x(A.src.g, c0 + b) : 0.f, 0.f, 0.f);
+  } else {
+    const float2 pa = (a < cnt) ? __ldg(A.src.xy + j0 + a) : f2(0.f, 0.f);
+    const float2 pb = (b < cnt) ? __ldg(A.src.xy + j0 + b) : f2(0.f, 0.f);
+    P = make_float4(-pa.x, -pb.x, -pa.y, -pb.y);
+  }
+  V = f2((a < cnt) ? __ldg(A.v + j0 + a) : 0.f, (b < cnt) ? __ldg(A.v + j0 + b) : 0.f);
+  if (SELF) Gp = f2((a < cnt) ? __ldg(A.gs + j0 + a) : 0.f, (b < cnt) ? __ldg(A.gs + j0 + b) : 0.f);
+}
+
+template <bool GRID, bool SELF>
+__global__ void __launch_bounds__(kBwThreads) bwd_rows_kernel(BwArgs A) {
+  constexpr int K = SELF ? 7 : 4;
+  __shared__ __align__(16) float4 sP[2][kBwPairs];
+  __shared__ __align__(16) float2 sV[2][kBwPairs];
+  __shared__ __align__(16) float2 sG[SELF ? 2 : 1][kBwPairs];
+
+  const int rb = blockIdx.x / A.chunks;
+  const int chunk = blockIdx.x - rb * A.chunks;
+  const int nt = A.src.n_tiles;
+  const int t0 = (int)((int64_t)chunk * nt / A.chunks);
+  const int t1 = (int)((int64_t)(chunk + 1) * nt / A.chunks);
+  const int tid = threadIdx.x;
+
+  float2 xq[kBwR], yq[kBwR];
+  float2 acc[kBwR][K];
+  float sum[kBwR][K], comp[kBwR][K];
+#pragma unroll
+  for (int r = 0; r < kBwR; ++r) {
+    int64_t i = (int64_t)rb * kBwRows + r * kBwThreads + tid;
+    if (i >= A.n) i = A.n - 1;
+    const float2 p = __ldg(A.x + i);
+    xq[r] = f2(p.x, p.x);
+    yq[r] = f2(p.y, p.y);
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      acc[r][k] = f2(0.f, 0.f);
+      sum[r][k] = 0.f;
+      comp[r][k] = 0.f;
+    }
+  }
+  const float2 nc2 = f2(A.neg_c, A.neg_c);
+
+  float4 P;
+  float2 V, Gp = f2(0.f, 0.f);
+  if (t0 < t1) {
+    bw_load_pair<GRID, SELF>(A, t0, tid, P, V, Gp);
+    sP[0][tid] = P;
+    sV[0][tid] = V;
+    if (SELF) sG[0][tid] = Gp;
+  }
+  __syncthreads();
+
+  for (int t = t0; t < t1; ++t) {
+    const int buf = (t - t0) & 1;
+    if (t + 1 < t1) bw_load_pair<GRID, SELF>(A, t + 1, tid, P, V, Gp);
+    int64_t j0;
+    int cnt, grow;
+    bw_tile_range(A.src, t, j0, cnt, grow);
+    const int np = (cnt + 1) >> 1;
+    float dyr[kBwR];
+    if (GRID) {
+      const float yt = grid_y(A.src.g, grow);
+      float2 dy2c[kBwR];
+#pragma unroll
+      for (int r = 0; r < kBwR; ++r) {
+        dyr[r] = yq[r].x - yt;
+        const float e = A.neg_c * dyr[r] * dyr[r];
+        dy2c[r] = f2(e, e);
+      }
+#pragma unroll 2
+      for (int p = 0; p < np; ++p) {
+        const float4 Q = sP[buf][p];
+        const float2 W = sV[buf][p];
+        const float2 nx = f2(Q.x, Q.y);
+#pragma unroll
+        for (int r = 0; r < kBwR; ++r) {
+          const float2 dx = __fadd2_rn(xq[r], nx);
+          const float2 e = __ffma2_rn(__fmul2_rn(dx, nc2), dx, dy2c[r]);
+          const float2 k = f2(ex2_approx(e.x), ex2_approx(e.y));
+          const float2 kv = __fmul2_rn(k, W);
+          acc[r][0] = __fadd2_rn(acc[r][0], kv);
+          acc[r][1] = __ffma2_rn(kv, dx, acc[r][1]);
+          acc[r][3] = __ffma2_rn(kv, e, acc[r][3]);
+        }
+      }
+    } else {
+#pragma unroll 2
+      for (int p = 0; p < np; ++p) {
+        const float4 Q = sP[buf][p];
+        const float2 W = sV[buf][p];
+        const float2 nx = f2(Q.x, Q.y), ny = f2(Q.z, Q.w);
+        float2 Gq;
+        if (SELF) Gq = sG[buf][p];
+#pragma unroll
+        for (int r = 0; r < kBwR; ++r) {
+          const float2 dx = __fadd2_rn(xq[r], nx);
+          const float2 dy = __fadd2_rn(yq[r], ny);
+          const float2 e = __fmul2_rn(__ffma2_rn(dy, dy, __fmul2_rn(dx, dx)), nc2);
+          const float2 k = f2(ex2_approx(e.x), ex2_approx(e.y));
+          const float2 kv = __fmul2_rn(k, W);
+          acc[r][0] = __fadd2_rn(acc[r][0], kv);
+          acc[r][1] = __ffma2_rn(kv, dx, acc[r][1]);
+          acc[r][2] = __ffma2_rn(kv, dy, acc[r][2]);
+          acc[r][3] = __ffma2_rn(kv, e, acc[r][3]);
+          if (SELF) {
+            const float2 kg = __fmul2_rn(k, Gq);
+            acc[r][4] = __fadd2_rn(acc[r][4], kg);
+            acc[r][5] = __ffma2_rn(kg, dx, acc[r][5]);
+            acc[r][6] = __ffma2_rn(kg, dy, acc[r][6]);
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < kBwR; ++r) {
+      if (GRID) acc[r][2] = f2(dyr[r] * acc[r][0].x, dyr[r] * acc[r][0].y);  // uniform y on a grid row
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        kahan(sum[r][k], comp[r][k], acc[r][k].x + acc[r][k].y);
+        acc[r][k] = f2(0.f, 0.f);
+      }
+    }
+    if (t + 1 < t1) {
+      sP[buf ^ 1][tid] = P;
+      sV[buf ^ 1][tid] = V;
+      if (SELF) sG[buf ^ 1][tid] = Gp;
+    }
+    __syncthreads();
+  }
+
+#pragma unroll
+  for (int r = 0; r < kBwR; ++r) {
+    const int64_t i = (int64_t)rb * kBwRows + r * kBwThreads + tid;
+    if (i < A.n) {
+#pragma unroll
+      for (int k = 0; k < K; ++k) A.partial[((int64_t)chunk * K + k) * A.n + i] = sum[r][k] - comp[r][k];
+    }
+  }
+}
+
+struct MergeArgs {
+  const float* partial;
+  int32_t chunks, K;
+  int64_t n;
+  const float* g;      // [n] dL/dout
+  const float* vrow;   // [n] v of the query points (self-kernel column role)
+  float var, inv_l2, dl_scale;  // dl_scale = -var / (neg_c_abs...) see host
+  float2* d_x;         // [n] or NULL
+  float* d_v;          // [n] (self-kernel) or NULL
+  double* scal_part;   // [blocks][2]: d_len, d_var partials
+};
+
+// Per-row merge of chunk partials, the per-row gradients, and per-block FP64
+// partials of the two scalar gradients.
+__global__ void __launch_bounds__(kMergeThreads) bwd_merge_kernel(MergeArgs M) {
+  __shared__ double red[2][kMergeThreads / 32];
+  const int64_t i = (int64_t)blockIdx.x * kMergeThreads + threadIdx.x;
+  double sl = 0.0, sv = 0.0;
+  if (i < M.n) {
+    float s[7], c[7];
+    for (int k = 0; k < M.K; ++k) {
+      s[k] = 0.f;
+      c[k] = 0.f;
+      for (int ch = 0; ch < M.chunks; ++ch) kahan(s[k], c[k], M.partial[((int64_t)ch * M.K + k) * M.n + i]);
+      s[k] -= c[k];
+    }
+    const float gi = M.g[i];
+    float ddx = gi * s[1], ddy = gi * s[2];
+    if (M.K == 7) {
+      const float vi = M.vrow[i];
+      ddx = fmaf(vi, s[5], ddx);
+      ddy = fmaf(vi, s[6], ddy);
+      if (M.d_v) M.d_v[i] = M.var * s[4];
+    }
+    // sums were taken over (x_i - y_j); the gradient wants (y_j - x_i)
+    if (M.d_x) M.d_x[i] = make_float2(-M.var * M.inv_l2 * ddx, -M.var * M.inv_l2 * ddy);
+    sl = (double)gi * (double)s[3] * (double)M.dl_scale;
+    sv = (double)gi * (double)s[0];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    sl += __shfl_xor_sync(0xffffffffu, sl, o);
+    sv += __shfl_xor_sync(0xffffffffu, sv, o);
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) {
+    red[0][w] = sl;
+    red[1][w] = sv;
+  }
+  __syncthreads();
+  if (threadIdx.x < 2) {
+    double t = 0.0;
+    for (int k = 0; k < kMergeThreads / 32; ++k) t += red[threadIdx.x][k];
+    M.scal_part[(int64_t)blockIdx.x * 2 + threadIdx.x] = t;
+  }
+}
+
+__global__ void bwd_scalar_final_kernel(const double* __restrict__ part, int nblk, double* d_len, double* d_var) {
+  if (threadIdx.x == 0 && d_len) {
+    double s = 0.0;
+    for (int b = 0; b < nblk; ++b) s += part[2 * b];
+    *d_len = s;
+  }
+  if (threadIdx.x == 1 && d_var) {
+    double s = 0.0;
+    for (int b = 0; b < nblk; ++b) s += part[2 * b + 1];
+    *d_var = s;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+
+struct RowPlan {
+  int32_t n_tiles, segs, chunks, row_blocks, K;
+  size_t partial_bytes, scal_bytes;
+  int64_t merge_blocks;
+};
+
+static lr_status plan_rows(int64_t n, int64_t m, bool grid, const lr_grid* g, bool self, RowPlan* R) {
+  RowPlan p{};
+  p.K = self ? 7 : 4;
+  if (grid) {
+    const int W = g->nx * g->ss;
+    p.segs = (W + kBwTile - 1) / kBwTile;
+    p.n_tiles = (int32_t)((int64_t)p.segs * g->ny * g->ss);
+  } else {
+    p.n_tiles = (int32_t)((m + kBwTile - 1) / kBwTile);
+  }
+  p.row_blocks = (int32_t)((n + kBwRows - 1) / kBwRows);
+  int dev = 0, n_sm = 1, occ = 1;
+  LR_CHECK_CUDA(cudaGetDevice(&dev));
+  LR_CHECK_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
+  if (self)
+    LR_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, bwd_rows_kernel<false, true>, kBwThreads, 0));
+  else
+    LR_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, bwd_rows_kernel<false, false>, kBwThreads, 0));
+  const int64_t target = 8LL * n_sm * (occ > 0 ? occ : 1);
+  int64_t chunks = 1;
+  if (p.row_blocks > 0 && p.n_tiles > 0) {
+    chunks = (target + p.row_blocks - 1) / p.row_blocks;
+    if (chunks < 1) chunks = 1;
+    if (chunks > p.n_tiles) chunks = p.n_tiles;
+  }
+  p.chunks = (int32_t)chunks;
+  p.partial_bytes = align256(sizeof(float) * (size_t)p.chunks * p.K * (size_t)n);
+  p.merge_blocks = (n + kMergeThreads - 1) / kMergeThreads;
+  p.scal_bytes = align256(sizeof(double) * 2 * (size_t)(p.merge_blocks > 0 ? p.merge_blocks : 1));
+  *R = p;
+  return LR_OK;
+}
+
+static lr_status launch_rows(const float2* x, int64_t n, const float2* ys, const lr_grid* yg, int64_t m,
+                             const float* v, const float* gs, const float* g, const float* vrow, float ell, float var,
+                             bool self, float2* d_x, float* d_v, double* d_len, double* d_var, char* ws,
+                             cudaStream_t s) {
+  RowPlan R;
+  lr_status st = plan_rows(n, m, ys == nullptr, yg, self, &R);
+  if (st != LR_OK) return st;
+  BwArgs A;
+  A.x = x;
+  A.n = n;
+  A.src.xy = ys;
+  A.src.g = ys ? GridDev{} : grid_dev(*yg);
+  A.src.m = m;
+  A.src.segs = R.segs;
+  A.src.n_tiles = R.n_tiles;
+  A.v = v;
+  A.gs = gs;
+  const double c = 1.4426950408889634 / (2.0 * (double)ell * (double)ell);
+  A.neg_c = (float)(-c);
+  A.chunks = R.chunks;
+  A.K = R.K;
+  A.partial = reinterpret_cast<float*>(ws);
+  const unsigned grid = (unsigned)((int64_t)R.row_blocks * R.chunks);
+  if (ys == nullptr)
+    bwd_rows_kernel<true, false><<<grid, kBwThreads, 0, s>>>(A);
+  else if (self)
+    bwd_rows_kernel<false, true><<<grid, kBwThreads, 0, s>>>(A);
+  else
+    bwd_rows_kernel<false, false><<<grid, kBwThreads, 0, s>>>(A);
+  LR_CHECK_CUDA(cudaGetLastError());
+  MergeArgs M;
+  M.partial = A.partial;
+  M.chunks = R.chunks;
+  M.K = R.K;
+  M.n = n;
+  M.g = g;
+  M.vrow = vrow;
+  M.var = var;
+  M.inv_l2 = (float)(1.0 / ((double)ell * ell));
+  // sum k v d^2 = -C / c; d_len = var/l^3 * sum g_i (sum_j k v d^2)
+  M.dl_scale = (float)(-(double)var / (c * (double)ell * ell * ell));
+  M.d_x = d_x;
+  M.d_v = d_v;
+  M.scal_part = reinterpret_cast<double*>(ws + R.partial_bytes);
+  bwd_merge_kernel<<<(unsigned)R.merge_blocks, kMergeThreads, 0, s>>>(M);
+  LR_CHECK_CUDA(cudaGetLastError());
+  if (d_len || d_var) {
+    bwd_scalar_final_kernel<<<1, 32, 0, s>>>(M.scal_part, (int)R.merge_blocks, d_len, d_var);
+    LR_CHECK_CUDA(cudaGetLastError());
+  }
+  return LR_OK;
+}
+
+static size_t rows_ws(int64_t n, int64_t m, bool grid, const lr_grid* g, bool self, lr_status* st) {
+  RowPlan R;
+  *st = plan_rows(n, m, grid, g, self, &R);
+  return R.partial_bytes + R.scal_bytes;
+}
+
+struct BwPlan {
+  int64_t n, m;
+  bool self, q_raytrace, q_grid, s_raytrace, s_grid;
+  bool want_lens;       // lens / subhalo gradients of the query's lens
+  bool need_dx;         // d_x needed (requested or for the lens gradient)
+  size_t off_qbeta, off_sbeta, off_rows, off_dx, off_sgrid, off_swap, off_swaprows, off_vjp, bytes;
+};
+
+static lr_status plan_bwd(const lr_points* q, const lr_points* s, const lr_grads* gr, BwPlan* P) {
+  lr_status st = validate_points(q, "gp_kernel_matvec_bwd(query)", false);
+  if (st != LR_OK) return st;
+  if (s) {
+    st = validate_points(s, "gp_kernel_matvec_bwd(source)", false);
+    if (st != LR_OK) return st;
+  }
+  LR_REQUIRE(gr != nullptr, "gp_kernel_matvec_bwd: grads is NULL");
+  BwPlan p{};
+  p.n = q->n;
+  p.self = s == nullptr;
+  p.m = p.self ? q->n : s->n;
+  p.q_raytrace = q->lens != nullptr;
+  p.q_grid = !p.q_raytrace && q->xy == nullptr;
+  p.s_raytrace = !p.self && s->lens != nullptr;
+  p.s_grid = !p.self && !p.s_raytrace && s->xy == nullptr;
+  LR_REQUIRE(!p.s_raytrace, "gp_kernel_matvec_bwd: a ray-traced source set distinct from the query is not supported");
+  LR_REQUIRE(!(gr->d_y && (p.self || p.s_grid)),
+             "gp_kernel_matvec_bwd: d_y applies to explicit non-self source points only");
+  p.want_lens = (gr->d_lens || gr->d_sub);
+  LR_REQUIRE(!p.want_lens || p.q_raytrace, "gp_kernel_matvec_bwd: lens gradients need a ray-traced query");
+  p.need_dx = gr->d_x || p.want_lens;
+  size_t off = 0;
+  p.off_qbeta = off;
+  if (p.q_raytrace || p.q_grid) off += align256(8 * (size_t)p.n);
+  p.off_sbeta = off;
+  p.off_rows = off;
+  {
+    size_t b = rows_ws(p.n, p.m, p.s_grid, p.s_grid ? &s->grid : nullptr, p.self, &st);
+    if (st != LR_OK) return st;
+    off += b;
+  }
+  p.off_dx = off;
+  if (p.need_dx && !gr->d_x) off += align256(8 * (size_t)p.n);
+  p.off_sgrid = off;
+  p.off_swap = off;
+  p.off_swaprows = off;
+  if (!p.self && gr->d_v) {
+    if (p.s_grid) off += align256(8 * (size_t)p.m);
+    p.off_swap = off;
+    // forward reduction with roles swapped: query = sources (explicit), source = query points (explicit)
+    lr_points qs{}, ss{};
+    qs.xy = reinterpret_cast<const float*>(uintptr_t(256));
+    qs.n = p.m;
+    ss.xy = reinterpret_cast<const float*>(uintptr_t(256));
+    ss.n = p.n;
+    size_t b = 0;
+    st = lr_matvec_workspace_size(&qs, &ss, 1, &b);
+    if (st != LR_OK) return st;
+    off += align256(b);
+  }
+  p.off_swaprows = off;
+  if (!p.self && gr->d_y) {
+    size_t b = rows_ws(p.m, p.n, false, nullptr, false, &st);
+    if (st != LR_OK) return st;
+    off += b;
+  }
+  p.off_vjp = off;
+  if (p.want_lens) off += raytrace_vjp_ws(p.n, q->n_sub);
+  p.bytes = off;
+  *P = p;
+  return LR_OK;
+}
+
+}  // namespace lr
+
+using namespace lr;
+
+extern "C" lr_status lr_matvec_bwd_workspace_size(const lr_points* query, const lr_points* source, int32_t nrhs,
+                                                  const lr_grads* grads, size_t* bytes) {
+  LR_REQUIRE(bytes != nullptr, "lr_matvec_bwd_workspace_size: bytes is NULL");
+  LR_REQUIRE(nrhs == 1, "lr_matvec_bwd_workspace_size: nrhs = %d; this version supports nrhs = 1", nrhs);
+  BwPlan P;
+  lr_status st = plan_bwd(query, source, grads, &P);
+  if (st != LR_OK) return st;
+  *bytes = P.bytes;
+  return LR_OK;
+}
+
+extern "C" lr_status gp_kernel_matvec_bwd(const lr_points* query, const lr_points* source, const float* v,
+                                          int32_t nrhs, float lengthscale, float variance, const float* g_out,
+                                          const lr_grads* grads, void* workspace, size_t workspace_bytes,
+                                          lr_stream stream) {
+  LR_REQUIRE(nrhs == 1, "gp_kernel_matvec_bwd: nrhs = %d; this version supports nrhs = 1", nrhs);
+  BwPlan P;
+  lr_status st = plan_bwd(query, source, grads, &P);
+  if (st != LR_OK) return st;
+  LR_REQUIRE(isfinite(lengthscale) && lengthscale > 0.f, "gp_kernel_matvec_bwd: lengthscale must be > 0");
+  LR_REQUIRE(isfinite(variance), "gp_kernel_matvec_bwd: variance is not finite");
+  LR_REQUIRE(g_out != nullptr || P.n == 0, "gp_kernel_matvec_bwd: g_out is NULL");
+  LR_REQUIRE(v != nullptr || P.m == 0, "gp_kernel_matvec_bwd: v is NULL");
+  LR_REQUIRE(workspace_bytes >= P.bytes, "gp_kernel_matvec_bwd: workspace of %zu bytes, %zu needed",
+             workspace_bytes, P.bytes);
+  LR_REQUIRE(P.bytes == 0 || workspace != nullptr, "gp_kernel_matvec_bwd: workspace is NULL");
+  LR_REQUIRE(((uintptr_t)workspace & 255u) == 0, "gp_kernel_matvec_bwd: workspace must be 256-byte aligned");
+  const lr_grads& G = *grads;
+  LR_REQUIRE(((uintptr_t)G.d_x & 7u) == 0 && ((uintptr_t)G.d_y & 7u) == 0 && ((uintptr_t)G.d_lens & 7u) == 0 &&
+                 ((uintptr_t)G.d_sub & 7u) == 0 && ((uintptr_t)G.d_lengthscale & 7u) == 0 &&
+                 ((uintptr_t)G.d_variance & 7u) == 0,
+             "gp_kernel_matvec_bwd: gradient outputs must be 8-byte aligned");
+  cudaStream_t s = as_cuda(stream);
+  char* ws = static_cast<char*>(workspace);
+  if (P.n == 0 || P.m == 0) {
+    // every gradient is an empty sum
+    if (G.d_v && P.m) LR_CHECK_CUDA(cudaMemsetAsync(G.d_v, 0, 4 * (size_t)P.m, s));
+    if (G.d_x && P.n) LR_CHECK_CUDA(cudaMemsetAsync(G.d_x, 0, 8 * (size_t)P.n, s));
+    if (G.d_y && P.m) LR_CHECK_CUDA(cudaMemsetAsync(G.d_y, 0, 8 * (size_t)P.m, s));
+    if (G.d_lengthscale) LR_CHECK_CUDA(cudaMemsetAsync(G.d_lengthscale, 0, 8, s));
+    if (G.d_variance) LR_CHECK_CUDA(cudaMemsetAsync(G.d_variance, 0, 8, s));
+    if (G.d_lens) LR_CHECK_CUDA(cudaMemsetAsync(G.d_lens, 0, 56, s));
+    if (G.d_sub && query->n_sub) LR_CHECK_CUDA(cudaMemsetAsync(G.d_sub, 0, 32 * (size_t)query->n_sub, s));
+    return LR_OK;
+  }
+  // query points (recomputed: nothing from the forward pass is stored)
+  const float2* xq = reinterpret_cast<const float2*>(query->xy);
+  if (P.q_raytrace || P.q_grid) {
+    float2* qb = reinterpret_cast<float2*>(ws + P.off_qbeta);
+    st = P.q_raytrace ? launch_raytrace(query, qb, nullptr, s) : launch_grid_points(query->grid, qb, s);
+    if (st != LR_OK) return st;
+    xq = qb;
+  }
+  const float2* ys = P.self ? xq : (P.s_grid ? nullptr : reinterpret_cast<const float2*>(source->xy));
+  const lr_grid* yg = P.s_grid ? &source->grid : nullptr;
+  float2* dx = P.need_dx ? (G.d_x ? reinterpret_cast<float2*>(G.d_x) : reinterpret_cast<float2*>(ws + P.off_dx))
+                         : nullptr;
+  // row pass: d_x (both roles for a self-kernel), self d_v, d_l, d_var
+  st = launch_rows(xq, P.n, ys, yg, P.m, v, P.self ? g_out : nullptr, g_out, v, lengthscale, variance, P.self, dx,
+                   P.self ? G.d_v : nullptr, G.d_lengthscale, G.d_variance, ws + P.off_rows, s);
+  if (st != LR_OK) return st;
+  // d_v of non-self sources: sum_i var k_ij g_i, the forward reduction with the point sets swapped
+  if (!P.self && G.d_v) {
+    const float* ypts = source->xy;
+    if (P.s_grid) {
+      float2* gp = reinterpret_cast<float2*>(ws + P.off_sgrid);
+      st = launch_grid_points(source->grid, gp, s);
+      if (st != LR_OK) return st;
+      ypts = reinterpret_cast<const float*>(gp);
+    }
+    lr_points qs{}, ss{};
+    qs.xy = ypts;
+    qs.n = P.m;
+    ss.xy = reinterpret_cast<const float*>(xq);
+    ss.n = P.n;
+    size_t b = 0;
+    st = lr_matvec_workspace_size(&qs, &ss, 1, &b);
+    if (st != LR_OK) return st;
+    st = gp_kernel_matvec(&qs, &ss, g_out, 1, lengthscale, variance, G.d_v, nullptr, ws + P.off_swap, b, stream);
+    if (st != LR_OK) return st;
+  }
+  // d_y of explicit non-self sources: the row pass with the point sets swapped
+  if (!P.self && G.d_y) {
+    st = launch_rows(reinterpret_cast<const float2*>(source->xy), P.m, xq, nullptr, P.n, g_out, nullptr, v, g_out,
+                     lengthscale, variance, false, reinterpret_cast<float2*>(G.d_y), nullptr, nullptr, nullptr,
+                     ws + P.off_swaprows, s);
+    if (st != LR_OK) return st;
+  }
+  // lens and subhalo gradients through the ray-trace
+  if (P.want_lens) {
+    st = launch_raytrace_vjp(query, dx, G.d_lens, G.d_sub, ws + P.off_vjp, s);
+    if (st != LR_OK) return st;
+  }
+  return LR_OK;
+}

@@ -9,7 +9,7 @@
 
 #include "host.cuh"
 #include "lens.cuh"
-#include "tma.cuh"
+#include "subs.cuh"
 
 namespace lr {
 
@@ -19,52 +19,6 @@ constexpr int kSubChunk = 256;  // subhalos staged per chunk (multiple of 4)
 __global__ void grid_points_kernel(GridDev g, int64_t n, float2* out) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) out[i] = grid_point(g, i);
-}
-
-// Converts raw records (5 floats) into the prepared form.
-__device__ __forceinline__ SubRec prep_sub(const float* r, int profile) {
-  SubRec h;
-  h.xh = r[0];
-  h.yh = r[1];
-  if (profile == LR_PROFILE_POINT_MASS) {
-    h.its2 = r[2] * r[2];
-    h.A = h.tau = h.tau2 = h.t2m1_t = h.C = 0.f;
-  } else {
-    const float ks = r[2], ts = r[3], tau = r[4];
-    const float t2 = tau * tau;
-    h.its2 = 1.0f / (ts * ts);
-    h.A = 4.0f * ks * t2 / ((t2 + 1.0f) * (t2 + 1.0f));
-    h.tau = tau;
-    h.tau2 = t2;
-    h.t2m1_t = (t2 - 1.0f) / tau;
-    h.C = tau * kPi + (t2 - 1.0f) * logf(tau);
-  }
-  return h;
-}
-
-// Stages subhalo records [h0, h0 + cnt) into shared memory as SubRec.
-// Returns false (all threads) if the bulk-copy wait timed out.
-__device__ bool stage_subs(const float* __restrict__ sub, int h0, int cnt, int profile, float* raw, SubRec* recs,
-                           uint64_t* bar, uint32_t& phase, bool bulk_ok, int* fault) {
-  const float* src = sub + 5 * (int64_t)h0;
-  const uint32_t bytes = 20u * (uint32_t)cnt;
-  const uint32_t bulk_bytes = bulk_ok ? (bytes & ~15u) : 0u;
-  if (threadIdx.x == 0 && bulk_bytes > 0) {
-    // order this CTA's earlier generic-proxy accesses of `raw` before the async write
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    mbar_expect_tx(bar, bulk_bytes);
-    bulk_g2s(raw, src, bulk_bytes, bar);
-  }
-  // the ragged tail (< 16 B) or everything when unaligned: plain loads
-  for (uint32_t w = bulk_bytes / 4 + threadIdx.x; w < bytes / 4; w += blockDim.x) raw[w] = __ldg(src + w);
-  bool ok = true;
-  if (bulk_bytes > 0) ok = mbar_wait_bounded(bar, phase, fault);
-  phase ^= (bulk_bytes > 0) ? 1u : 0u;
-  __syncthreads();
-  if (__syncthreads_or(!ok)) return false;
-  for (int t = threadIdx.x; t < cnt; t += blockDim.x) recs[t] = prep_sub(raw + 5 * t, profile);
-  __syncthreads();
-  return true;
 }
 
 template <int PROFILE>

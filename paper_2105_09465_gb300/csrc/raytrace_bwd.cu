@@ -1,0 +1,274 @@
+// Ray-trace backward (vector-Jacobian product of a2-a5): given G = dL/dbeta
+// for every image-plane point, returns dL/d(x0, y0, q, phi, theta_e, g1, g2)
+// of the lens and dL/d(x_h, y_h, kappa_s | theta_pm, theta_s) of every
+// subhalo, with dL/dp = -sum_i G_i . dalpha_i/dp (beta = xi - alpha).
+//
+// One CTA covers kVjThreads x kVjPpt points (each thread keeps kVjPpt points
+// and their G in registers). Lens terms are summed per thread, reduced across
+// the CTA in FP64 and written as one partial per CTA. Subhalo records are
+// staged in shared memory like the forward pass; for each subhalo a thread
+// sums over its points, the warp reduces with shuffles, and the CTA combines
+// its warps in fixed order. A final kernel adds the per-CTA partials in fixed
+// order in FP64, so results are deterministic.
+#include <math.h>
+
+#include "host.cuh"
+#include "subs.cuh"
+
+namespace lr {
+
+constexpr int kVjThreads = 256;
+constexpr int kVjPpt = 8;
+constexpr int kVjPoints = kVjThreads * kVjPpt;  // points per CTA
+constexpr int kVjChunk = 128;                   // subhalos staged per chunk
+constexpr int kVjWarps = kVjThreads / 32;
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <int PROFILE>
+__global__ void __launch_bounds__(kVjThreads) raytrace_vjp_kernel(LensConst L, LensGradConst LG, GridDev g,
+                                                                  const float2* __restrict__ xi, int64_t n,
+                                                                  const float* __restrict__ sub, int n_sub,
+                                                                  int bulk_ok, const float2* __restrict__ dbeta,
+                                                                  double* __restrict__ lens_part,
+                                                                  float* __restrict__ sub_part, int* fault) {
+  __shared__ __align__(16) float raw[5 * kVjChunk];
+  __shared__ __align__(16) SubRec recs[kVjChunk];
+  __shared__ float2 extra[kVjChunk];  // tNFW: (4T, 1/theta_s); point mass: (0, theta_pm)
+  __shared__ float red[kVjWarps][kVjChunk][4];
+  __shared__ double lred[kVjWarps][7];
+  __shared__ __align__(8) uint64_t bar;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t base = (int64_t)blockIdx.x * kVjPoints;
+
+  float px[kVjPpt], py[kVjPpt], gx[kVjPpt], gy[kVjPpt];
+#pragma unroll
+  for (int k = 0; k < kVjPpt; ++k) {
+    const int64_t i = base + k * kVjThreads + tid;
+    if (i < n) {
+      const float2 p = xi ? xi[i] : grid_point(g, i);
+      const float2 d = dbeta[i];
+      px[k] = p.x;
+      py[k] = p.y;
+      gx[k] = d.x;
+      gy[k] = d.y;
+    } else {  // zero gradient: contributes exactly nothing
+      px[k] = py[k] = gx[k] = gy[k] = 0.f;
+    }
+  }
+
+  // ---- main lens and shear
+  float la[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+  for (int k = 0; k < kVjPpt; ++k) {
+    float o5[5];
+    sple_vjp(L, LG, px[k], py[k], gx[k], gy[k], o5);
+#pragma unroll
+    for (int t = 0; t < 5; ++t) la[t] += o5[t];
+    la[5] -= fmaf(gx[k], px[k], -gy[k] * py[k]);  // dalpha/dg1 = (x, -y)
+    la[6] -= fmaf(gx[k], py[k], gy[k] * px[k]);   // dalpha/dg2 = (y, x)
+  }
+#pragma unroll
+  for (int t = 0; t < 7; ++t) {
+    const double s = warp_sum_d((double)la[t]);
+    if (lane == 0) lred[warp][t] = s;
+  }
+  __syncthreads();
+  if (tid < 7) {
+    double s = 0.0;
+    for (int w = 0; w < kVjWarps; ++w) s += lred[w][tid];
+    lens_part[(int64_t)blockIdx.x * 7 + tid] = s;
+  }
+
+  // ---- subhalos
+  if (n_sub == 0) return;
+  if (tid == 0) mbar_init(&bar, 1);
+  __syncthreads();
+  uint32_t phase = 0;
+  for (int h0 = 0; h0 < n_sub; h0 += kVjChunk) {
+    const int cnt = min(kVjChunk, n_sub - h0);
+    if (!stage_subs(sub, h0, cnt, PROFILE, raw, recs, &bar, phase, bulk_ok != 0, fault)) return;
+    for (int t = tid; t < cnt; t += kVjThreads) {
+      const float* r = raw + 5 * t;
+      if (PROFILE == LR_PROFILE_POINT_MASS) {
+        extra[t] = make_float2(0.f, r[2]);
+      } else {
+        const float t2 = r[4] * r[4];
+        extra[t] = make_float2(4.0f * t2 / ((t2 + 1.0f) * (t2 + 1.0f)), 1.0f / r[3]);
+      }
+    }
+    __syncthreads();
+    for (int h = 0; h < cnt; ++h) {
+      const SubRec rec = recs[h];
+      const float2 ex = extra[h];
+      float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+#pragma unroll
+      for (int k = 0; k < kVjPpt; ++k) {
+        const float dx = px[k] - rec.xh, dy = py[k] - rec.yh;
+        const float R2 = fmaf(dx, dx, dy * dy);
+        if (!(R2 > 1e-30f)) continue;
+        const float dg = fmaf(dx, gx[k], dy * gy[k]);
+        const float iR2 = 1.0f / R2;
+        if (PROFILE == LR_PROFILE_POINT_MASS) {
+          const float m = rec.its2 * iR2;
+          const float q = 2.0f * dg * iR2;
+          a0 += m * fmaf(-q, dx, gx[k]);
+          a1 += m * fmaf(-q, dy, gy[k]);
+          a2 -= 2.0f * ex.y * dg * iR2;
+        } else {
+          float Gt, Ht;
+          tnfw_GH(rec, R2, Gt, Ht);
+          const float hg = Ht - 2.0f * Gt;
+          const float q = hg * dg * iR2;
+          a0 += rec.A * fmaf(Gt, gx[k], q * dx);
+          a1 += rec.A * fmaf(Gt, gy[k], q * dy);
+          a2 -= ex.x * Gt * dg;
+          a3 += rec.A * hg * dg * ex.y;
+        }
+      }
+      a0 = warp_sum(a0);
+      a1 = warp_sum(a1);
+      a2 = warp_sum(a2);
+      a3 = warp_sum(a3);
+      if (lane == 0) {
+        red[warp][h][0] = a0;
+        red[warp][h][1] = a1;
+        red[warp][h][2] = a2;
+        red[warp][h][3] = a3;
+      }
+    }
+    __syncthreads();
+    for (int t = tid; t < 4 * cnt; t += kVjThreads) {
+      float s = 0.f;
+      for (int w = 0; w < kVjWarps; ++w) s += red[w][t >> 2][t & 3];
+      sub_part[((int64_t)blockIdx.x * n_sub + h0) * 4 + t] = s;
+    }
+    __syncthreads();
+  }
+}
+
+// Fixed-order FP64 sum of the per-CTA partials.
+__global__ void vjp_final_kernel(const double* __restrict__ lens_part, const float* __restrict__ sub_part, int nblk,
+                                 int n_sub, double* __restrict__ d_lens, double* __restrict__ d_sub) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < 7 && d_lens) {
+    double s = 0.0;
+    for (int b = 0; b < nblk; ++b) s += lens_part[(int64_t)b * 7 + t];
+    d_lens[t] = s;
+  }
+  if (t < 4 * n_sub && d_sub) {
+    double s = 0.0;
+    for (int b = 0; b < nblk; ++b) s += (double)sub_part[(int64_t)b * n_sub * 4 + t];
+    d_sub[t] = s;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+
+lr_status make_lens_grad_const(const lr_lens* lens, LensGradConst* out) {
+  const double q = lens->q, gam = lens->gamma, te = lens->theta_e;
+  LensGradConst G;
+  memset(&G, 0, sizeof G);
+  G.e = (float)(0.5 * (1.0 - gam));
+  const double f = (1.0 - q) / (1.0 + q);
+  G.f = (float)f;
+  G.dlnpre_dq = (float)(0.5 / q - 1.0 / (1.0 + q));
+  G.df_dq = (float)(-2.0 / ((1.0 + q) * (1.0 + q)));
+  G.inv2q = (float)(0.5 / q);
+  G.dlnte = te > 0.0 ? (float)((gam - 1.0) / te) : 0.f;
+  // h_n = (n+1) c_{n+1} (-f)^n, c_n = prod_{k<=n} (a+k-1)/(b+k-1)
+  const double a = 0.5 * (gam - 1.0), b = 0.5 * (5.0 - gam);
+  double c = 1.0, fn = 1.0;  // c_{n+1}, (-f)^n
+  int n = 0;
+  for (n = 0; n < kMaxSeriesTerms; ++n) {
+    c *= (a + n) / (b + n);  // c_{n+1}
+    const double hn = (n + 1.0) * c * fn;
+    G.hco[n] = (float)hn;
+    // tail bound for sum_{k>n} |h_k|: |h_n| f (n+2)/(n+1) / (1 - f)^2
+    if (f == 0.0 || fabs(hn) * f * (n + 2.0) / (n + 1.0) / ((1.0 - f) * (1.0 - f)) < 1e-9) {
+      ++n;
+      break;
+    }
+    fn *= -f;
+  }
+  LR_REQUIRE(n <= kMaxSeriesTerms, "lens q = %g too small for the gradient series", q);
+  G.nterms = n < 1 ? 1 : n;
+  *out = G;
+  return LR_OK;
+}
+
+size_t raytrace_vjp_ws(int64_t n, int32_t n_sub) {
+  const int64_t nblk = (n + kVjPoints - 1) / kVjPoints;
+  return align256(sizeof(double) * 7 * (size_t)nblk) + align256(sizeof(float) * 4 * (size_t)n_sub * (size_t)nblk);
+}
+
+lr_status launch_raytrace_vjp(const lr_points* p, const float2* dbeta, double* d_lens, double* d_sub, void* ws,
+                              cudaStream_t s) {
+  LensConst L;
+  lr_status st = make_lens_const(p->lens, &L);
+  if (st != LR_OK) return st;
+  LensGradConst G;
+  st = make_lens_grad_const(p->lens, &G);
+  if (st != LR_OK) return st;
+  const int64_t nblk = (p->n + kVjPoints - 1) / kVjPoints;
+  if (nblk == 0) {
+    if (d_lens) LR_CHECK_CUDA(cudaMemsetAsync(d_lens, 0, 7 * sizeof(double), s));
+    if (d_sub && p->n_sub) LR_CHECK_CUDA(cudaMemsetAsync(d_sub, 0, 4 * sizeof(double) * p->n_sub, s));
+    return LR_OK;
+  }
+  int* fault = fault_ptr();
+  LR_REQUIRE(fault != nullptr, "could not resolve the device fault word");
+  double* lens_part = static_cast<double*>(ws);
+  float* sub_part = reinterpret_cast<float*>(static_cast<char*>(ws) + align256(sizeof(double) * 7 * (size_t)nblk));
+  const GridDev g = p->xy ? GridDev{} : grid_dev(p->grid);
+  const int bulk_ok = (((uintptr_t)p->sub & 15u) == 0) ? 1 : 0;
+  const float2* xi = reinterpret_cast<const float2*>(p->xy);
+  if (p->profile == LR_PROFILE_POINT_MASS)
+    raytrace_vjp_kernel<LR_PROFILE_POINT_MASS><<<(unsigned)nblk, kVjThreads, 0, s>>>(
+        L, G, g, xi, p->n, p->sub, p->n_sub, bulk_ok, dbeta, lens_part, sub_part, fault);
+  else
+    raytrace_vjp_kernel<LR_PROFILE_TNFW><<<(unsigned)nblk, kVjThreads, 0, s>>>(
+        L, G, g, xi, p->n, p->sub, p->n_sub, bulk_ok, dbeta, lens_part, sub_part, fault);
+  LR_CHECK_CUDA(cudaGetLastError());
+  const int nt = 4 * p->n_sub > 7 ? 4 * p->n_sub : 7;
+  vjp_final_kernel<<<(nt + 255) / 256, 256, 0, s>>>(lens_part, sub_part, (int)nblk, p->n_sub, d_lens,
+                                                     p->n_sub ? d_sub : nullptr);
+  LR_CHECK_CUDA(cudaGetLastError());
+  return LR_OK;
+}
+
+}  // namespace lr
+
+extern "C" lr_status lr_raytrace_vjp_workspace_size(const lr_points* pts, size_t* bytes) {
+  LR_REQUIRE(bytes != nullptr, "lr_raytrace_vjp_workspace_size: bytes is NULL");
+  lr_status st = lr::validate_points(pts, "lr_raytrace_vjp_workspace_size", true);
+  if (st != LR_OK) return st;
+  *bytes = lr::raytrace_vjp_ws(pts->n, pts->n_sub);
+  return LR_OK;
+}
+
+extern "C" lr_status lens_raytrace_vjp(const lr_points* pts, const float* d_beta, double* d_lens, double* d_sub,
+                                       void* workspace, size_t workspace_bytes, lr_stream stream) {
+  lr_status st = lr::validate_points(pts, "lens_raytrace_vjp", true);
+  if (st != LR_OK) return st;
+  LR_REQUIRE(d_beta != nullptr || pts->n == 0, "lens_raytrace_vjp: d_beta is NULL");
+  LR_REQUIRE(((uintptr_t)d_beta & 7u) == 0, "lens_raytrace_vjp: d_beta must be 8-byte aligned");
+  LR_REQUIRE(((uintptr_t)d_lens & 7u) == 0 && ((uintptr_t)d_sub & 7u) == 0,
+             "lens_raytrace_vjp: gradient outputs must be 8-byte aligned");
+  const size_t need = lr::raytrace_vjp_ws(pts->n, pts->n_sub);
+  LR_REQUIRE(workspace_bytes >= need, "lens_raytrace_vjp: workspace of %zu bytes, %zu needed", workspace_bytes, need);
+  LR_REQUIRE(need == 0 || workspace != nullptr, "lens_raytrace_vjp: workspace is NULL");
+  LR_REQUIRE(((uintptr_t)workspace & 255u) == 0, "lens_raytrace_vjp: workspace must be 256-byte aligned");
+  return lr::launch_raytrace_vjp(pts, reinterpret_cast<const float2*>(d_beta), d_lens, d_sub, workspace,
+                                 lr::as_cuda(stream));
+}
