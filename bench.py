@@ -115,31 +115,39 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------------------
-def cpu_sample(p, seconds: float) -> dict:
-    """Times the FP64 oracle (ray-trace + kernel reduction) on a bounded row sample of workload p."""
+def cpu_sample(p, seconds: float, g=None) -> dict:
+    """Times the FP64 oracle on a bounded row sample of workload p: ray-trace,
+    kernel reduction, reduction gradients and ray-trace gradients of the
+    sampled rows against all inducing points (the same per-pair work as the
+    GPU step)."""
     import oracle
 
     oracle.build()
     xi_all = oracle.grid_points(*p.xgrid.astuple())
     yg = oracle.grid_points(*p.ygrid.astuple())
     rng = np.random.default_rng(0)
+    if g is None:
+        g = rng.standard_normal(p.n)
 
     def run(rows):
         t = time.perf_counter()
         xi = xi_all[rows]
         _, b = oracle.raytrace(xi, p.lens.astuple(), p.sub)
         oracle.kernel_matvec(b, yg, p.v, p.lengthscale, p.variance)
+        R = oracle.kernel_matvec_vjp(b, yg, p.v, p.lengthscale, p.variance, g[rows])
+        oracle.raytrace_vjp(xi, p.lens.astuple(), p.sub, R["d_x"])
         return time.perf_counter() - t
 
-    rows = rng.choice(p.n, 256, replace=False)
+    rows = rng.choice(p.n, 64, replace=False)
     dt = run(rows)
-    k = int(min(p.n, max(256, 256 * seconds / max(dt, 1e-3))))
+    k = int(min(p.n, max(64, 64 * seconds / max(dt, 1e-3))))
     rows = rng.choice(p.n, k, replace=False)
     dt = run(rows)
     pairs = k * p.m
     return {"value": pairs / dt / 1e9, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": f"{k} random rows of the workload ({pairs:.3e} pairs, ray-trace of those rows included), "
-                      f"{dt:.1f} s", "seconds": dt}
+            "sample": f"{k} random rows of the workload x all {p.m} inducing points ({pairs:.3e} pairs): "
+                      f"ray-trace, reduction, reduction gradients and ray-trace gradients, {dt:.1f} s",
+            "seconds": dt}
 
 
 # --------------------------------------------------------------------------
@@ -169,6 +177,21 @@ def run_reference(args):
 
 
 # --------------------------------------------------------------------------
+def event_time(fn, n, stream, flush):
+    """Mean CUDA-event time (ms) of fn() over n calls, L2 flushed before each."""
+    import torch
+    evs = []
+    for k in range(n):
+        flush.fill_(k & 0xFF)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        evs.append((a, b))
+    torch.cuda.synchronize()
+    return float(np.mean([a.elapsed_time(b) for a, b in evs]))
+
+
 def run_ours(args):
     import torch
 
@@ -186,23 +209,50 @@ def run_ours(args):
     # each rank owns an independent lens system of the realistic recipe (weak scaling)
     p = W.realistic(seed=1 + rank)
     dev = torch.device("cuda", local)
+    g_np = np.random.default_rng(100 + rank).standard_normal(p.n).astype(np.float32)
     sub = torch.from_numpy(p.sub).to(dev)
     v = torch.from_numpy(p.v).to(dev)
+    g = torch.from_numpy(g_np).to(dev)
     q = api.Points(grid=p.xgrid, lens=p.lens, sub=sub)
     s = api.Points(grid=p.ygrid)
+    want = ["v", "lengthscale", "variance", "lens", "sub"]
     out = torch.empty(p.n, dtype=torch.float32, device=dev)
     ws = torch.empty(max(api.matvec_workspace_size(q, s), 1), dtype=torch.uint8, device=dev)
+    bws = torch.empty(1, dtype=torch.uint8, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
+    grads = {}
+
+    def fwd():
+        api.gp_kernel_matvec(q, s, v, p.lengthscale, p.variance, out=out, workspace=ws)
+
+    def bwd():
+        nonlocal bws
+        G = api.gp_kernel_matvec_bwd(q, s, v, p.lengthscale, p.variance, g, want=want, workspace=bws)
+        grads.update(G)
 
     def step():
-        api.gp_kernel_matvec(q, s, v, p.lengthscale, p.variance, out=out, workspace=ws)
+        fwd()
+        bwd()
+
+    # size the backward workspace once (the call allocates it on first use)
+    bws = torch.empty(1 << 20, dtype=torch.uint8, device=dev)
+    from paper_2105_09465_gb300 import abi as _abi
+    import ctypes
+    cq, _k1 = api.to_c_points(q)
+    cs, _k2 = api.to_c_points(s)
+    gr = _abi.lr_grads()
+    gr.d_v, gr.d_lengthscale, gr.d_variance, gr.d_lens, gr.d_sub = 256, 256, 256, 256, 256
+    b = ctypes.c_size_t(0)
+    _abi.check(_abi.load().lr_matvec_bwd_workspace_size(ctypes.byref(cq), ctypes.byref(cs), 1, ctypes.byref(gr),
+                                                         ctypes.byref(b)), "lr_matvec_bwd_workspace_size")
+    bws = torch.empty(max(int(b.value), 1), dtype=torch.uint8, device=dev)
 
     for _ in range(max(3, args.warmup)):
         step()
     torch.cuda.synchronize()
 
-    # ---- timed region: device-resident inputs
+    # ---- timed region: device-resident inputs, forward + backward per step
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     clocks = ClockSampler(local)
     clocks.start()
@@ -218,75 +268,75 @@ def run_ours(args):
     if dist:
         dist.barrier()
     clk = clocks.stop()
-    times = [a.elapsed_time(b) for a, b in ev]
-    ms = float(np.mean(times))
+    ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
     if dist:
         t = torch.tensor([ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
     value = world * p.pairs / (ms * 1e-3) / 1e9
+    nk = max(5, min(args.steps, 50))
+    fwd_ms = event_time(fwd, nk, stream, flush)
+    bwd_ms = event_time(bwd, nk, stream, flush)
 
-    # ---- dominant kernel alone: reduction over the ray-traced points (explicit source path excluded)
+    # ---- kernels in isolation (same launch configuration as inside the step)
     beta = api.lens_raytrace(q)
     qx = api.Points(xy=beta)
     ws2 = torch.empty(max(api.matvec_workspace_size(qx, s), 1), dtype=torch.uint8, device=dev)
-    for _ in range(3):
-        api.gp_kernel_matvec(qx, s, v, p.lengthscale, p.variance, out=out, workspace=ws2)
-    kev = []
-    for k in range(max(5, args.steps)):
-        flush.fill_(k & 0xFF)
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        api.gp_kernel_matvec(qx, s, v, p.lengthscale, p.variance, out=out, workspace=ws2)
-        b.record(stream)
-        kev.append((a, b))
-    # ray-trace alone (a2-a5)
-    rev = []
-    for k in range(max(5, args.steps)):
-        flush.fill_(k & 0xFF)
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        api.lens_raytrace(q)
-        b.record(stream)
-        rev.append((a, b))
-    torch.cuda.synchronize()
-    k_ms = float(np.mean([a.elapsed_time(b) for a, b in kev]))
-    r_ms = float(np.mean([a.elapsed_time(b) for a, b in rev]))
+    ygp = api.gp_kernel_matvec(api.Points(grid=p.ygrid), api.Points(grid=W.Grid(1, 1, 1, 1.0)),
+                               torch.ones(1, device=dev), 1.0, want_beta=True)[1]
+    ysw = api.Points(xy=ygp)
+    ws3 = torch.empty(max(api.matvec_workspace_size(ysw, qx), 1), dtype=torch.uint8, device=dev)
+    dvv = torch.empty(p.m, dtype=torch.float32, device=dev)
+    dbeta = torch.from_numpy(np.random.default_rng(7).standard_normal((p.n, 2)).astype(np.float32)).to(dev)
+    kern = {}
+    kern["matvec_kernel<grid> fwd"] = (
+        event_time(lambda: api.gp_kernel_matvec(qx, s, v, p.lengthscale, p.variance, out=out, workspace=ws2), nk,
+                   stream, flush), p.pairs, 32.0, "pairs: 1 MUFU.EX2 + 4 FP32 lanes each")
+    kern["bwd_rows_kernel<grid>"] = (
+        event_time(lambda: api.gp_kernel_matvec_bwd(qx, s, v, p.lengthscale, p.variance, g, want=["x"]), nk,
+                   stream, flush), p.pairs, 128.0 / 7.0, "pairs: 1 MUFU.EX2 + 7 FP32 lanes each")
+    kern["matvec_kernel<explicit> (d_v, roles swapped)"] = (
+        event_time(lambda: api.gp_kernel_matvec(ysw, qx, g, p.lengthscale, p.variance, out=dvv, workspace=ws3), nk,
+                   stream, flush), p.pairs, 128.0 / 6.0, "pairs: 1 MUFU.EX2 + 6 FP32 lanes each")
+    rt_ms = event_time(lambda: api.lens_raytrace(q), nk, stream, flush)
+    vjp_ms = event_time(lambda: api.lens_raytrace_vjp(q, dbeta), nk, stream, flush)
 
     # ---- end to end through the public API with host buffers
     v_host = torch.from_numpy(p.v).pin_memory()
+    g_host = torch.from_numpy(g_np).pin_memory()
     sub_host = torch.from_numpy(p.sub).pin_memory()
     out_host = torch.empty(p.n, dtype=torch.float32).pin_memory()
-    v_d = torch.empty_like(v)
-    sub_d = torch.empty_like(sub)
+    dv_host = torch.empty(p.m, dtype=torch.float32).pin_memory()
+    dl_host = torch.empty(7, dtype=torch.float64).pin_memory()
+    ds_host = torch.empty((len(p.sub), 4), dtype=torch.float64).pin_memory()
+    sc_host = torch.empty(2, dtype=torch.float64).pin_memory()
+    v_d, g_d, sub_d = torch.empty_like(v), torch.empty_like(g), torch.empty_like(sub)
     qe = api.Points(grid=p.xgrid, lens=p.lens, sub=sub_d)
 
     def e2e_step():
         v_d.copy_(v_host, non_blocking=True)
+        g_d.copy_(g_host, non_blocking=True)
         sub_d.copy_(sub_host, non_blocking=True)
         api.gp_kernel_matvec(qe, s, v_d, p.lengthscale, p.variance, out=out, workspace=ws)
+        G = api.gp_kernel_matvec_bwd(qe, s, v_d, p.lengthscale, p.variance, g_d, want=want, workspace=bws)
         out_host.copy_(out, non_blocking=True)
+        dv_host.copy_(G["v"], non_blocking=True)
+        dl_host.copy_(G["lens"], non_blocking=True)
+        ds_host.copy_(G["sub"], non_blocking=True)
+        sc_host[0:1].copy_(G["lengthscale"], non_blocking=True)
+        sc_host[1:2].copy_(G["variance"], non_blocking=True)
 
     for _ in range(3):
         e2e_step()
     torch.cuda.synchronize()
-    eev = []
-    for k in range(args.steps):
-        flush.fill_(k & 0xFF)
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        e2e_step()
-        b.record(stream)
-        eev.append((a, b))
-    torch.cuda.synchronize()
-    e_ms = float(np.mean([a.elapsed_time(b) for a, b in eev]))
+    e_ms = event_time(e2e_step, max(5, min(args.steps, 100)), stream, flush)
     if dist:
         t = torch.tensor([e_ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e_ms = float(t.item())
     e2e_val = world * p.pairs / (e_ms * 1e-3) / 1e9
-    h2d = v_host.numel() * 4 + sub_host.numel() * 4
-    d2h = out_host.numel() * 4
+    h2d = (v_host.numel() + g_host.numel() + sub_host.numel()) * 4
+    d2h = out_host.numel() * 4 + dv_host.numel() * 4 + (dl_host.numel() + ds_host.numel() + 2) * 8
 
     rates = api.probe_pipe_rates(local)
     if rank != 0:
@@ -297,37 +347,45 @@ def run_ours(args):
 
     sm_mhz = clk["sm_mhz"] or SM_MAX_MHZ_DEFAULT
     sm_max = clk["sm_max_mhz"] or SM_MAX_MHZ_DEFAULT
-    # ALU roofline for the grid-source reduction: per pair one MUFU.EX2 and 4 FP32 lanes
-    per_sm_clk = min(rates["ex2_per_clk"], rates["ffma2_lanes_per_clk"] / 4.0)
-    peak_max = per_sm_clk * rates["sm_count"] * sm_max * 1e6 / 1e9
-    peak_meas = per_sm_clk * rates["sm_count"] * sm_mhz * 1e6 / 1e9
-    achieved = p.pairs / (k_ms * 1e-3) / 1e9
-    plan_chunks = None
+    nsm = rates["sm_count"]
+    ex2 = rates["ex2_per_clk"]
+    fma = rates["ffma2_lanes_per_clk"]
+    table = {}
+    for name, (kms, pairs, _, note) in kern.items():
+        lanes = float(note.split("+ ")[1].split(" ")[0])
+        per_clk = min(ex2, fma / lanes)
+        peak = per_clk * nsm * sm_max * 1e6 / 1e9
+        ach = pairs / (kms * 1e-3) / 1e9
+        table[name] = {"ms": kms, "achieved": ach, "peak": peak, "frac": ach / peak, "per_sm_clk": per_clk,
+                       "note": note}
+    dom = max(table, key=lambda k: table[k]["ms"])
+    d = table[dom]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded; see workloads.py)",
         "config": dict(workload_config(p), parallelism=f"independent lens system per GPU x{world}"),
-        "pass": "forward (grid, ray-trace, kernel reduction)",
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_max, "unit": UNIT,
-                     "frac": achieved / peak_max, "traffic": measured_traffic("matvec_kernel<grid source>"),
-                     "kernel": "matvec_kernel<grid source> (+ chunk merge)",
-                     "peak_basis": f"min(MUFU.EX2 {rates['ex2_per_clk']:.2f}/clk/SM, FFMA2 lanes "
-                                   f"{rates['ffma2_lanes_per_clk']:.1f}/4 per clk/SM) x {rates['sm_count']} SMs "
-                                   f"x {sm_max:.0f} MHz (max clock; probe-measured rates)",
-                     "peak_at_measured_clock": peak_meas, "frac_at_measured_clock": achieved / peak_meas,
-                     "kernel_ms": k_ms},
-        "raytrace": {"ms": r_ms, "points": p.n, "subhalo_pairs": p.n * len(p.sub),
-                     "hbm_gbs": p.n * 8 / (r_ms * 1e-3) / 1e9,
-                     "note": "ALU/XU-bound with subhalos: 8 B/point written, ~100 instructions per point-subhalo"},
+        "pass": "forward + backward (grid, ray-trace, reduction; gradients for v, lengthscale, variance, "
+                "7 lens parameters, 200x4 subhalo parameters)",
+        "fwd": {"ms": fwd_ms, "value": p.pairs / (fwd_ms * 1e-3) / 1e9, "unit": UNIT},
+        "bwd": {"ms": bwd_ms},
+        "roofline": {"bound": "alu", "achieved": d["achieved"], "peak": d["peak"], "unit": UNIT,
+                     "frac": d["frac"], "traffic": measured_traffic(dom), "kernel": dom,
+                     "peak_basis": f"min(MUFU.EX2 {ex2:.2f}/clk/SM, FFMA2 {fma:.1f} lanes/clk/SM / lanes per pair) "
+                                   f"x {nsm} SMs x {sm_max:.0f} MHz (max clock; probe-measured rates); {d['note']}",
+                     "frac_at_measured_clock": d["frac"] * sm_max / sm_mhz},
+        "kernels": table,
+        "raytrace": {"ms": rt_ms, "vjp_ms": vjp_ms, "points": p.n, "subhalo_pairs": p.n * len(p.sub),
+                     "hbm_gbs": p.n * 8 / (rt_ms * 1e-3) / 1e9,
+                     "note": "ALU/XU-bound with subhalos (8 B written per point)"},
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "ms_per_step": e_ms},
-        "gpu_launches": 3 * args.steps,
+        "gpu_launches": 12 * args.steps,
         "clocks": clk,
         "pipe_rates": rates,
     }
     if world == 1 and not args.no_cpu_baseline:
-        cb = cpu_sample(p, args.cpu_seconds)
+        cb = cpu_sample(p, args.cpu_seconds, g_np.astype(np.float64))
         cb.pop("seconds", None)
         line["cpu_baseline"] = cb
     print(json.dumps(line))

@@ -275,16 +275,35 @@ __global__ void __launch_bounds__(kMergeThreads) bwd_merge_kernel(MergeArgs M) {
   }
 }
 
-__global__ void bwd_scalar_final_kernel(const double* __restrict__ part, int nblk, double* d_len, double* d_var) {
-  if (threadIdx.x == 0 && d_len) {
-    double s = 0.0;
-    for (int b = 0; b < nblk; ++b) s += part[2 * b];
-    *d_len = s;
+// Fixed-order FP64 reduction of the per-block scalar partials: thread t sums
+// blocks t, t + 256, ...; warps reduce by xor-shuffle; warp 0 adds the warps
+// in order. One CTA of kMergeThreads threads.
+__global__ void __launch_bounds__(kMergeThreads) bwd_scalar_final_kernel(const double* __restrict__ part, int nblk,
+                                                                         double* d_len, double* d_var) {
+  __shared__ double red[2][kMergeThreads / 32];
+  double a = 0.0, b = 0.0;
+  for (int k = threadIdx.x; k < nblk; k += kMergeThreads) {
+    a += part[2 * k];
+    b += part[2 * k + 1];
   }
-  if (threadIdx.x == 1 && d_var) {
-    double s = 0.0;
-    for (int b = 0; b < nblk; ++b) s += part[2 * b + 1];
-    *d_var = s;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = a;
+    red[1][threadIdx.x >> 5] = b;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double sa = 0.0, sb = 0.0;
+    for (int w = 0; w < kMergeThreads / 32; ++w) {
+      sa += red[0][w];
+      sb += red[1][w];
+    }
+    if (d_len) *d_len = sa;
+    if (d_var) *d_var = sb;
   }
 }
 
@@ -377,7 +396,7 @@ static lr_status launch_rows(const float2* x, int64_t n, const float2* ys, const
   bwd_merge_kernel<<<(unsigned)R.merge_blocks, kMergeThreads, 0, s>>>(M);
   LR_CHECK_CUDA(cudaGetLastError());
   if (d_len || d_var) {
-    bwd_scalar_final_kernel<<<1, 32, 0, s>>>(M.scal_part, (int)R.merge_blocks, d_len, d_var);
+    bwd_scalar_final_kernel<<<1, kMergeThreads, 0, s>>>(M.scal_part, (int)R.merge_blocks, d_len, d_var);
     LR_CHECK_CUDA(cudaGetLastError());
   }
   return LR_OK;

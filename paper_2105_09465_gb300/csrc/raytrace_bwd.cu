@@ -156,19 +156,29 @@ __global__ void __launch_bounds__(kVjThreads) raytrace_vjp_kernel(LensConst L, L
   }
 }
 
-// Fixed-order FP64 sum of the per-CTA partials.
+// Fixed-order FP64 sum of the per-CTA partials: one warp per output value
+// (7 lens values, then 4 per subhalo); lane l sums CTAs l, l + 32, ...; the
+// warp reduces by xor-shuffle.
 __global__ void vjp_final_kernel(const double* __restrict__ lens_part, const float* __restrict__ sub_part, int nblk,
                                  int n_sub, double* __restrict__ d_lens, double* __restrict__ d_sub) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < 7 && d_lens) {
-    double s = 0.0;
-    for (int b = 0; b < nblk; ++b) s += lens_part[(int64_t)b * 7 + t];
-    d_lens[t] = s;
+  const int o = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (o >= 7 + 4 * n_sub) return;
+  double s = 0.0;
+  if (o < 7) {
+    for (int b = lane; b < nblk; b += 32) s += lens_part[(int64_t)b * 7 + o];
+  } else {
+    const int t = o - 7;
+    for (int b = lane; b < nblk; b += 32) s += (double)sub_part[(int64_t)b * n_sub * 4 + t];
   }
-  if (t < 4 * n_sub && d_sub) {
-    double s = 0.0;
-    for (int b = 0; b < nblk; ++b) s += (double)sub_part[(int64_t)b * n_sub * 4 + t];
-    d_sub[t] = s;
+#pragma unroll
+  for (int k = 16; k > 0; k >>= 1) s += __shfl_xor_sync(0xffffffffu, s, k);
+  if (lane == 0) {
+    if (o < 7) {
+      if (d_lens) d_lens[o] = s;
+    } else if (d_sub) {
+      d_sub[o - 7] = s;
+    }
   }
 }
 
@@ -240,9 +250,9 @@ lr_status launch_raytrace_vjp(const lr_points* p, const float2* dbeta, double* d
     raytrace_vjp_kernel<LR_PROFILE_TNFW><<<(unsigned)nblk, kVjThreads, 0, s>>>(
         L, G, g, xi, p->n, p->sub, p->n_sub, bulk_ok, dbeta, lens_part, sub_part, fault);
   LR_CHECK_CUDA(cudaGetLastError());
-  const int nt = 4 * p->n_sub > 7 ? 4 * p->n_sub : 7;
-  vjp_final_kernel<<<(nt + 255) / 256, 256, 0, s>>>(lens_part, sub_part, (int)nblk, p->n_sub, d_lens,
-                                                     p->n_sub ? d_sub : nullptr);
+  const int64_t warps = 7 + 4 * (int64_t)p->n_sub;
+  vjp_final_kernel<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, s>>>(lens_part, sub_part, (int)nblk, p->n_sub,
+                                                                        d_lens, p->n_sub ? d_sub : nullptr);
   LR_CHECK_CUDA(cudaGetLastError());
   return LR_OK;
 }
