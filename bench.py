@@ -38,6 +38,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serving-requests", type=int, default=32)
+    ap.add_argument("--serving-iters", type=int, default=50)
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="target oracle CPU time for cpu_baseline")
     return ap.parse_args()
 
@@ -177,6 +180,74 @@ def run_reference(args):
 
 
 # --------------------------------------------------------------------------
+def run_serving(n_req: int, iters: int) -> dict:
+    """Serving trace (sides 64-512 px at 2x2, 0-500 subhalos, 128x128 inducing
+    grid, `iters` fwd+bwd+update iterations each) through the session engine:
+    all requests at t = 0 with continuous batching (16 slots) and one at a
+    time (1 slot, per-request launches), then Poisson arrivals at 70 % of the
+    measured batched capacity."""
+    import threading as th
+
+    from paper_2105_09465_gb300 import workloads as W
+    from paper_2105_09465_gb300.serving import Session
+
+    trace = W.serving_trace(seed=3, n_requests=n_req, iters=iters)
+    rng = np.random.default_rng(33)
+    datas = [rng.standard_normal(r["problem"].n).astype(np.float32) for r in trace]
+    pairs = sum(r["problem"].n * r["problem"].m for r in trace) * iters
+    step = 1e-3
+
+    def pct(lat):
+        return {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+                "mean_s": float(np.mean(lat))}
+
+    out = {"trace": f"{n_req} requests (seed 3): square images of side U{{64,128,256,384,512}} px at 2x2, "
+                    f"0-500 tNFW subhalos, 128x128 inducing grid, {iters} iterations of ray-trace + reduction + "
+                    f"backward + update each; {pairs:.3e} pairs of forward+backward work",
+           "unit": UNIT}
+    with Session(max_slots=2) as S:  # warm-up (module load, pools)
+        p = trace[0]["problem"]
+        S.poll(S.submit(p, datas[0], 2, step))
+    for mode, slots in (("batched", 16), ("unbatched", 1)):
+        with Session(max_slots=slots) as S:
+            t0 = time.perf_counter()
+            ts = [S.submit(r["problem"], d, iters, step) for r, d in zip(trace, datas)]
+            res = [S.poll(t, timeout_s=600, want=()) for t in ts]
+            wall = time.perf_counter() - t0
+            st = S.stats()
+        assert all(r.status == 0 for r in res), [r.status for r in res]
+        lat = [r.latency for r in res]
+        out[mode] = {"value": pairs / wall / 1e9, "wall_s": wall, "req_per_s": n_req / wall,
+                     "batched_launches": st["launches"], "iterations": st["iterations"], **pct(lat)}
+    out["speedup_batched_vs_unbatched"] = out["batched"]["value"] / out["unbatched"]["value"]
+    # Poisson arrivals at 70 % of the measured batched capacity
+    rate = 0.7 * out["batched"]["req_per_s"]
+    arr = np.cumsum(np.random.default_rng(5).exponential(1.0 / rate, n_req))
+    with Session(max_slots=16) as S:
+        tickets = [None] * n_req
+        t0 = time.perf_counter()
+
+        def feeder():
+            for k, (r, d) in enumerate(zip(trace, datas)):
+                dt = arr[k] - (time.perf_counter() - t0)
+                if dt > 0:
+                    time.sleep(dt)
+                tickets[k] = S.submit(r["problem"], d, iters, step)
+
+        f = th.Thread(target=feeder)
+        f.start()
+        res = []
+        for k in range(n_req):
+            while tickets[k] is None:
+                time.sleep(0.0005)
+            res.append(S.poll(tickets[k], timeout_s=600, want=()))
+        f.join()
+        wall = time.perf_counter() - t0
+    out["poisson_70pct"] = {"rate_req_per_s": rate, "value": pairs / wall / 1e9, "wall_s": wall,
+                            **pct([r.latency for r in res])}
+    return out
+
+
 def event_time(fn, n, stream, flush):
     """Mean CUDA-event time (ms) of fn() over n calls, L2 flushed before each."""
     import torch
@@ -384,6 +455,10 @@ def run_ours(args):
         "clocks": clk,
         "pipe_rates": rates,
     }
+    if world == 1 and not args.no_serving:
+        line["serving"] = run_serving(args.serving_requests, args.serving_iters)
+        line["p50_latency_s"] = line["serving"]["batched"]["p50_s"]
+        line["p99_latency_s"] = line["serving"]["batched"]["p99_s"]
     if world == 1 and not args.no_cpu_baseline:
         cb = cpu_sample(p, args.cpu_seconds, g_np.astype(np.float64))
         cb.pop("seconds", None)

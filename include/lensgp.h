@@ -235,6 +235,83 @@ lr_status lens_raytrace_vjp(const lr_points* pts, const float* d_beta, double* d
                             void* workspace, size_t workspace_bytes, lr_stream stream);
 lr_status lr_raytrace_vjp_workspace_size(const lr_points* pts, size_t* bytes);
 
+/* ------------------------------------------------------------------------ */
+/* Serving: device-resident request loop with continuous batching             */
+
+/*
+ * A session owns a worker thread, a CUDA stream and a device memory pool on
+ * one GPU. Requests (lens systems) are submitted from host memory and
+ * admitted, first come first served, while fewer than max_slots requests are
+ * active and their device state fits in hbm_budget_bytes (state is held from
+ * admission until the result is polled). Each admitted request runs `iters`
+ * iterations of: ray-trace its image grid, out = K(beta, y) v over its
+ * inducing grid, residual g = out - data, the full backward pass of
+ * L = 0.5 |out - data|^2 (dL/dv, dL/dbeta, lens, subhalo, length-scale and
+ * variance gradients), and v <- v - step dL/dv. Between iterations the
+ * worker admits new requests; one iteration of ALL active requests is one
+ * batched kernel launch per stage, so requests of different sizes share
+ * launches and overlap on the device. A request is summed in an order fixed
+ * by its own sizes: its results are bit-identical alone or in any mix.
+ */
+typedef struct lr_session lr_session;
+
+typedef struct {
+  size_t hbm_budget_bytes; /* device memory admitted requests may hold; 0 = 120 GiB */
+  int32_t max_slots;       /* requests iterating at once (1 = one at a time) */
+  int32_t device;          /* CUDA device ordinal */
+} lr_session_cfg;
+
+typedef struct {
+  lr_grid grid;         /* image-plane grid, ray-traced through `lens` */
+  lr_lens lens;
+  const float* sub;     /* HOST float[n_sub][5] subhalo records (copied at submit) */
+  int32_t n_sub;
+  int32_t profile;      /* LR_PROFILE_TNFW or LR_PROFILE_POINT_MASS */
+  lr_grid ygrid;        /* source-plane inducing grid */
+  const float* v0;      /* HOST float[m]: initial source weights (copied) */
+  const float* data;    /* HOST float[n]: observed fluxes (copied) */
+  float lengthscale, variance;
+  float step;           /* gradient step on v */
+  int32_t iters;        /* >= 1 */
+} lr_request;
+
+typedef struct {
+  float* out;           /* HOST float[n] or NULL: K v of the last iteration */
+  float* v;             /* HOST float[m] or NULL: v after the last update */
+  double* d_lens;       /* HOST double[7] or NULL: lens gradient of the last iteration */
+  double* d_sub;        /* HOST double[n_sub][4] or NULL */
+  double d_lengthscale; /* filled in */
+  double d_variance;
+  double loss;          /* 0.5 |out - data|^2 of the last iteration */
+  double t_submit_s, t_admit_s, t_done_s; /* session clock (s): submit, admission, GPU completion */
+} lr_result;
+
+typedef struct {
+  int64_t pending, active, held; /* held: finished, result not yet polled */
+  size_t used_bytes;
+  uint64_t iterations;           /* batched iterations run */
+  uint64_t launches;             /* batched kernel launches issued */
+} lr_session_stats;
+
+lr_status solve_session_create(const lr_session_cfg* cfg, lr_session** out);
+/* Copies the request in and queues it; *ticket identifies it. LR_ERR_OUT_OF_MEMORY
+ * if its device state alone exceeds the budget; LR_ERR_INVALID_ARG on bad input. */
+lr_status solve_session_submit(lr_session* s, const lr_request* req, uint64_t* ticket);
+/* Waits up to timeout_us for the ticket (0: do not wait). LR_OK: result
+ * copied into *out and the request's device state released; LR_PENDING (no
+ * wait) or LR_ERR_TIMEOUT: not finished; LR_ERR_NOT_FOUND: unknown ticket;
+ * any other status: the request failed (message in lr_last_error). One
+ * poller per ticket. */
+lr_status solve_session_poll(lr_session* s, uint64_t ticket, lr_result* out, int64_t timeout_us);
+/* Removes a request that has not been admitted yet (LR_ERR_BUSY otherwise). */
+lr_status solve_session_cancel(lr_session* s, uint64_t ticket);
+/* Host-side fault injection: the next batched iteration is abandoned as if a
+ * launch had failed; its requests fail with LR_ERR_CUDA, the session goes on. */
+lr_status solve_session_inject_fault(lr_session* s);
+lr_status solve_session_stats(lr_session* s, lr_session_stats* out);
+/* Stops the worker after its current iteration and frees everything. */
+lr_status solve_session_destroy(lr_session* s);
+
 /*
  * gp_kernel_matvec for callers that cannot allocate device memory (an
  * application whose device memory is all held by its own pool or budget, a

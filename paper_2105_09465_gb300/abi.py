@@ -52,6 +52,29 @@ class lr_grads(ctypes.Structure):
                 ("d_sub", ctypes.c_void_p)]
 
 
+class lr_session_cfg(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_slots", ctypes.c_int32), ("device", ctypes.c_int32)]
+
+
+class lr_request(ctypes.Structure):
+    _fields_ = [("grid", lr_grid), ("lens", lr_lens), ("sub", ctypes.c_void_p), ("n_sub", ctypes.c_int32),
+                ("profile", ctypes.c_int32), ("ygrid", lr_grid), ("v0", ctypes.c_void_p), ("data", ctypes.c_void_p),
+                ("lengthscale", ctypes.c_float), ("variance", ctypes.c_float), ("step", ctypes.c_float),
+                ("iters", ctypes.c_int32)]
+
+
+class lr_result(ctypes.Structure):
+    _fields_ = [("out", ctypes.c_void_p), ("v", ctypes.c_void_p), ("d_lens", ctypes.c_void_p),
+                ("d_sub", ctypes.c_void_p), ("d_lengthscale", ctypes.c_double), ("d_variance", ctypes.c_double),
+                ("loss", ctypes.c_double), ("t_submit_s", ctypes.c_double), ("t_admit_s", ctypes.c_double),
+                ("t_done_s", ctypes.c_double)]
+
+
+class lr_session_stats(ctypes.Structure):
+    _fields_ = [("pending", ctypes.c_int64), ("active", ctypes.c_int64), ("held", ctypes.c_int64),
+                ("used_bytes", ctypes.c_size_t), ("iterations", ctypes.c_uint64), ("launches", ctypes.c_uint64)]
+
+
 _P = ctypes.c_void_p
 _lib = None
 
@@ -78,6 +101,13 @@ SIGNATURES = {
                                                       ctypes.POINTER(ctypes.c_size_t)]),
     "lens_raytrace_vjp": (ctypes.c_int32, [ctypes.POINTER(lr_points), _P, _P, _P, _P, ctypes.c_size_t, _P]),
     "lr_raytrace_vjp_workspace_size": (ctypes.c_int32, [ctypes.POINTER(lr_points), ctypes.POINTER(ctypes.c_size_t)]),
+    "solve_session_create": (ctypes.c_int32, [ctypes.POINTER(lr_session_cfg), ctypes.POINTER(ctypes.c_void_p)]),
+    "solve_session_submit": (ctypes.c_int32, [_P, ctypes.POINTER(lr_request), ctypes.POINTER(ctypes.c_uint64)]),
+    "solve_session_poll": (ctypes.c_int32, [_P, ctypes.c_uint64, ctypes.POINTER(lr_result), ctypes.c_int64]),
+    "solve_session_cancel": (ctypes.c_int32, [_P, ctypes.c_uint64]),
+    "solve_session_inject_fault": (ctypes.c_int32, [_P]),
+    "solve_session_stats": (ctypes.c_int32, [_P, ctypes.POINTER(lr_session_stats)]),
+    "solve_session_destroy": (ctypes.c_int32, [_P]),
 }
 
 

@@ -20,36 +20,13 @@
 
 #include <mutex>
 
+#include "batch.cuh"
 #include "host.cuh"
+#include "problems.cuh"
 
 namespace lr {
 
-constexpr int kMvThreads = 128;
-constexpr int kMvR = 8;                              // query rows per thread
-constexpr int kRowsPerCta = kMvThreads * kMvR;       // 1024
-constexpr int kTile = 256;                           // source points per tile
-constexpr int kPairs = kTile / 2;                    // = kMvThreads: one pair per loader thread
 static_assert(kPairs == kMvThreads, "one source pair per thread when staging");
-
-struct SrcDesc {
-  const float2* xy;  // explicit source points, or NULL for a grid
-  GridDev g;         // grid description when xy == NULL
-  int64_t m;         // number of source points
-  int32_t segs;      // grid: tiles per grid row
-  int32_t n_tiles;   // total tiles
-};
-
-struct MvArgs {
-  const float2* x;   // query points [n]
-  int64_t n;
-  SrcDesc src;
-  const float* v;    // [m]
-  float neg_c;       // -log2(e) / (2 l^2)
-  float variance;
-  int32_t chunks;    // column chunks per row block
-  float* out;        // [n] when chunks == 1
-  float* partial;    // [chunks][n] when chunks > 1
-};
 
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
 
@@ -97,14 +74,10 @@ __device__ __forceinline__ void load_pair(const SrcDesc& S, const float* __restr
   V = f2((a < cnt) ? __ldg(v + j0 + a) : 0.f, (b < cnt) ? __ldg(v + j0 + b) : 0.f);
 }
 
+// One task: kRowsPerCta query rows x one chunk of source tiles.
 template <bool GRID>
-__global__ void __launch_bounds__(kMvThreads) matvec_kernel(MvArgs A) {
-  __shared__ __align__(16) float4 sP[2][kPairs];
-  __shared__ __align__(16) float2 sV[2][kPairs];
-
-  const int task = blockIdx.x;
-  const int rb = task / A.chunks;
-  const int chunk = task - rb * A.chunks;
+__device__ __forceinline__ void matvec_body(const MvArgs& A, int rb, int chunk, float4 (*sP)[kPairs],
+                                            float2 (*sV)[kPairs]) {
   const int nt = A.src.n_tiles;
   const int t0 = (int)((int64_t)chunk * nt / A.chunks);
   const int t1 = (int)((int64_t)(chunk + 1) * nt / A.chunks);
@@ -205,18 +178,109 @@ __global__ void __launch_bounds__(kMvThreads) matvec_kernel(MvArgs A) {
   }
 }
 
+template <bool GRID>
+__global__ void __launch_bounds__(kMvThreads) matvec_kernel(const __grid_constant__ MvArgs A) {
+  __shared__ __align__(16) float4 sP[2][kPairs];
+  __shared__ __align__(16) float2 sV[2][kPairs];
+  const int rb = blockIdx.x / A.chunks;
+  matvec_body<GRID>(A, rb, blockIdx.x - rb * A.chunks, sP, sV);
+}
+
+// Batched form: CTA b runs task b of its problem; every problem of one
+// launch has the same source kind (grid or explicit).
+template <bool GRID>
+__global__ void __launch_bounds__(kMvThreads) matvec_batched_kernel(const __grid_constant__ Batch<MvArgs> B) {
+  __shared__ __align__(16) float4 sP[2][kPairs];
+  __shared__ __align__(16) float2 sV[2][kPairs];
+  const int k = batch_find(B, blockIdx.x);
+  const MvArgs& A = B.p[k];
+  const int local = blockIdx.x - B.start[k];
+  const int rb = local / A.chunks;
+  matvec_body<GRID>(A, rb, local - rb * A.chunks, sP, sV);
+}
+
 // Fixed-order compensated merge of the chunk partials.
-__global__ void merge_chunks_kernel(const float* __restrict__ partial, int chunks, int64_t n, float variance,
-                                    float* __restrict__ out) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void merge_body(const float* __restrict__ partial, int chunks, int64_t n, float variance,
+                                           float* __restrict__ out, int64_t i) {
   if (i >= n) return;
   float s = 0.f, c = 0.f;
   for (int k = 0; k < chunks; ++k) kahan_add(s, c, partial[(int64_t)k * n + i]);
   out[i] = variance * (s - c);
 }
 
+__global__ void merge_chunks_kernel(const float* __restrict__ partial, int chunks, int64_t n, float variance,
+                                    float* __restrict__ out) {
+  merge_body(partial, chunks, n, variance, out, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+__global__ void merge_batched_kernel(const __grid_constant__ Batch<MergeP> B) {
+  const int k = batch_find(B, blockIdx.x);
+  const MergeP& M = B.p[k];
+  merge_body(M.partial, M.chunks, M.n, M.variance, M.out,
+             (int64_t)(blockIdx.x - B.start[k]) * blockDim.x + threadIdx.x);
+}
+
 // ---------------------------------------------------------------------------
 // Host side
+
+int32_t plan_chunks(int64_t row_blocks, int64_t n_tiles, int occupancy, int n_sm) {
+  const int64_t target = 8LL * n_sm * (occupancy > 0 ? occupancy : 1);
+  int64_t chunks = 1;
+  if (row_blocks > 0 && n_tiles > 0) {
+    chunks = (target + row_blocks - 1) / row_blocks;
+    if (chunks < 1) chunks = 1;
+    if (chunks > n_tiles) chunks = n_tiles;
+  }
+  return (int32_t)chunks;
+}
+
+lr_status launch_matvec_batched(const MvArgs* p, int count, cudaStream_t s) {
+  for (int kind = 0; kind < 2; ++kind) {  // 0: explicit sources, 1: grid sources
+    Batch<MvArgs> B;
+    B.count = 0;
+    int64_t tot = 0;
+    for (int i = 0; i <= count; ++i) {
+      const bool flush = (i == count) || B.count == kMaxBatch;
+      if (flush && B.count > 0) {
+        B.start[B.count] = (int32_t)tot;
+        if (tot > 0) {
+          if (kind)
+            matvec_batched_kernel<true><<<(unsigned)tot, kMvThreads, 0, s>>>(B);
+          else
+            matvec_batched_kernel<false><<<(unsigned)tot, kMvThreads, 0, s>>>(B);
+          LR_CHECK_CUDA(cudaGetLastError());
+        }
+        B.count = 0;
+        tot = 0;
+      }
+      if (i == count) break;
+      if ((p[i].src.xy == nullptr) != (kind == 1)) continue;
+      B.p[B.count] = p[i];
+      B.start[B.count] = (int32_t)tot;
+      tot += (int64_t)((p[i].n + kRowsPerCta - 1) / kRowsPerCta) * p[i].chunks;
+      ++B.count;
+    }
+  }
+  return LR_OK;
+}
+
+lr_status launch_merge_batched(const MergeP* p, int count, cudaStream_t s) {
+  for (int b0 = 0; b0 < count; b0 += kMaxBatch) {
+    Batch<MergeP> B;
+    B.count = count - b0 < kMaxBatch ? count - b0 : kMaxBatch;
+    int64_t tot = 0;
+    for (int k = 0; k < B.count; ++k) {
+      B.p[k] = p[b0 + k];
+      B.start[k] = (int32_t)tot;
+      tot += (p[b0 + k].n + 255) / 256;
+    }
+    B.start[B.count] = (int32_t)tot;
+    if (tot == 0) continue;
+    merge_batched_kernel<<<(unsigned)tot, 256, 0, s>>>(B);
+    LR_CHECK_CUDA(cudaGetLastError());
+  }
+  return LR_OK;
+}
 
 struct MvPlan {
   int64_t n, m;
@@ -253,18 +317,11 @@ static lr_status plan_matvec(const lr_points* q, const lr_points* s, int32_t nrh
     p.n_tiles = (int32_t)((p.m + kTile - 1) / kTile);
   }
   p.row_blocks = (int32_t)((p.n + kRowsPerCta - 1) / kRowsPerCta);
-  // column chunks: enough tasks that every resident CTA slot gets ~8 of them
   int dev = 0, n_sm = 1, occ = 1;
   LR_CHECK_CUDA(cudaGetDevice(&dev));
   LR_CHECK_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
   LR_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, matvec_kernel<false>, kMvThreads, 0));
-  const int64_t target = 8LL * n_sm * (occ > 0 ? occ : 1);
-  int64_t chunks = 1;
-  if (p.row_blocks > 0 && p.n_tiles > 0) {
-    chunks = (target + p.row_blocks - 1) / p.row_blocks;
-    chunks = chunks < 1 ? 1 : chunks;
-    chunks = chunks > p.n_tiles ? p.n_tiles : chunks;
-  }
+  const int64_t chunks = plan_chunks(p.row_blocks, p.n_tiles, occ, n_sm);
   p.chunks = (int32_t)chunks;
   size_t off = 0;
   const bool need_qbuf = (p.q_raytrace || p.q_grid) && !have_beta_out;
@@ -276,6 +333,52 @@ static lr_status plan_matvec(const lr_points* q, const lr_points* s, int32_t nrh
   if (p.chunks > 1) off += align256(sizeof(float) * (size_t)p.chunks * (size_t)p.n);
   p.bytes = off;
   *P = p;
+  return LR_OK;
+}
+
+// Problem descriptor for a forward reduction of explicit query points against
+// explicit (ys) or grid (yg) sources, planned exactly as gp_kernel_matvec
+// plans it. With partial == NULL only *partial_bytes is filled in.
+lr_status make_mv_problem(const float2* x, int64_t n, const float2* ys, const lr_grid* yg, int64_t m, const float* v,
+                          float ell, float var, float* out, float* partial, MvArgs* A, MergeP* M,
+                          size_t* partial_bytes) {
+  lr_points q{}, src{};
+  q.xy = x ? reinterpret_cast<const float*>(x) : reinterpret_cast<const float*>(uintptr_t(256));
+  q.n = n;
+  if (ys || !yg) {
+    src.xy = ys ? reinterpret_cast<const float*>(ys) : reinterpret_cast<const float*>(uintptr_t(256));
+  } else {
+    src.grid = *yg;
+  }
+  src.n = m;
+  MvPlan P;
+  lr_status st = plan_matvec(&q, &src, 1, false, &P);
+  if (st != LR_OK) return st;
+  *partial_bytes = P.chunks > 1 ? align256(sizeof(float) * (size_t)P.chunks * (size_t)n) : 0;
+  if (A) {
+    MvArgs a{};
+    a.x = x;
+    a.n = n;
+    a.src.xy = ys;
+    a.src.g = ys ? GridDev{} : grid_dev(*yg);
+    a.src.m = m;
+    a.src.segs = P.segs;
+    a.src.n_tiles = P.n_tiles;
+    a.v = v;
+    a.neg_c = (float)(-1.4426950408889634 / (2.0 * (double)ell * (double)ell));
+    a.variance = var;
+    a.chunks = P.chunks;
+    a.out = out;
+    a.partial = partial;
+    *A = a;
+  }
+  if (M) {
+    M->partial = partial;
+    M->chunks = P.chunks;
+    M->n = n;
+    M->variance = var;
+    M->out = out;
+  }
   return LR_OK;
 }
 

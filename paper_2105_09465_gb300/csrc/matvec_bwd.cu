@@ -17,35 +17,11 @@
 #include <math.h>
 
 #include "host.cuh"
+#include "problems.cuh"
 
 namespace lr {
 
-constexpr int kBwThreads = 128;
-constexpr int kBwR = 4;
-constexpr int kBwRows = kBwThreads * kBwR;  // 512 rows per CTA
-constexpr int kBwTile = 256;
-constexpr int kBwPairs = kBwTile / 2;
 static_assert(kBwPairs == kBwThreads, "one source pair per thread when staging");
-constexpr int kMergeThreads = 256;
-
-struct BwSrc {
-  const float2* xy;  // explicit sources, or NULL for a grid
-  GridDev g;
-  int64_t m;
-  int32_t segs, n_tiles;
-};
-
-struct BwArgs {
-  const float2* x;  // query points [n]
-  int64_t n;
-  BwSrc src;
-  const float* v;   // [m] source weights
-  const float* gs;  // [m] source-side g (self-kernel only: g of the same points)
-  float neg_c;      // -log2(e)/(2 l^2)
-  int32_t chunks;
-  int32_t K;        // quantities per row: 4, or 7 for a self-kernel
-  float* partial;   // [chunks][K][n]
-};
 
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
 __device__ __forceinline__ void kahan(float& s, float& c, float x) {
@@ -87,15 +63,18 @@ __device__ __forceinline__ void bw_load_pair(const BwArgs& A, int t, int p, floa
   if (SELF) Gp = f2((a < cnt) ? __ldg(A.gs + j0 + a) : 0.f, (b < cnt) ? __ldg(A.gs + j0 + b) : 0.f);
 }
 
-template <bool GRID, bool SELF>
-__global__ void __launch_bounds__(kBwThreads) bwd_rows_kernel(BwArgs A) {
-  constexpr int K = SELF ? 7 : 4;
-  __shared__ __align__(16) float4 sP[2][kBwPairs];
-  __shared__ __align__(16) float2 sV[2][kBwPairs];
-  __shared__ __align__(16) float2 sG[SELF ? 2 : 1][kBwPairs];
+struct BwSmem {
+  float4 sP[2][kBwPairs];
+  float2 sV[2][kBwPairs];
+  float2 sG[2][kBwPairs];
+};
 
-  const int rb = blockIdx.x / A.chunks;
-  const int chunk = blockIdx.x - rb * A.chunks;
+template <bool GRID, bool SELF>
+__device__ __forceinline__ void bwd_rows_body(const BwArgs& A, int rb, int chunk, BwSmem& sm) {
+  constexpr int K = SELF ? 7 : 4;
+  float4 (*sP)[kBwPairs] = sm.sP;
+  float2 (*sV)[kBwPairs] = sm.sV;
+  float2 (*sG)[kBwPairs] = sm.sG;
   const int nt = A.src.n_tiles;
   const int t0 = (int)((int64_t)chunk * nt / A.chunks);
   const int t1 = (int)((int64_t)(chunk + 1) * nt / A.chunks);
@@ -218,23 +197,30 @@ __global__ void __launch_bounds__(kBwThreads) bwd_rows_kernel(BwArgs A) {
   }
 }
 
-struct MergeArgs {
-  const float* partial;
-  int32_t chunks, K;
-  int64_t n;
-  const float* g;      // [n] dL/dout
-  const float* vrow;   // [n] v of the query points (self-kernel column role)
-  float var, inv_l2, dl_scale;  // dl_scale = -var / (neg_c_abs...) see host
-  float2* d_x;         // [n] or NULL
-  float* d_v;          // [n] (self-kernel) or NULL
-  double* scal_part;   // [blocks][2]: d_len, d_var partials
-};
+template <bool GRID, bool SELF>
+__global__ void __launch_bounds__(kBwThreads) bwd_rows_kernel(const __grid_constant__ BwArgs A) {
+  __shared__ __align__(16) BwSmem sm;
+  const int rb = blockIdx.x / A.chunks;
+  bwd_rows_body<GRID, SELF>(A, rb, blockIdx.x - rb * A.chunks, sm);
+}
+
+// Batched form; every problem of one launch has the same kind (grid,
+// explicit, or explicit self-kernel).
+template <bool GRID, bool SELF>
+__global__ void __launch_bounds__(kBwThreads) bwd_rows_batched_kernel(const __grid_constant__ Batch<BwArgs> B) {
+  __shared__ __align__(16) BwSmem sm;
+  const int k = batch_find(B, blockIdx.x);
+  const BwArgs& A = B.p[k];
+  const int local = blockIdx.x - B.start[k];
+  const int rb = local / A.chunks;
+  bwd_rows_body<GRID, SELF>(A, rb, local - rb * A.chunks, sm);
+}
 
 // Per-row merge of chunk partials, the per-row gradients, and per-block FP64
 // partials of the two scalar gradients.
-__global__ void __launch_bounds__(kMergeThreads) bwd_merge_kernel(MergeArgs M) {
+__device__ __forceinline__ void bwd_merge_body(const MergeArgs& M, int64_t blk) {
   __shared__ double red[2][kMergeThreads / 32];
-  const int64_t i = (int64_t)blockIdx.x * kMergeThreads + threadIdx.x;
+  const int64_t i = blk * kMergeThreads + threadIdx.x;
   double sl = 0.0, sv = 0.0;
   if (i < M.n) {
     float s[7], c[7];
@@ -271,15 +257,24 @@ __global__ void __launch_bounds__(kMergeThreads) bwd_merge_kernel(MergeArgs M) {
   if (threadIdx.x < 2) {
     double t = 0.0;
     for (int k = 0; k < kMergeThreads / 32; ++k) t += red[threadIdx.x][k];
-    M.scal_part[(int64_t)blockIdx.x * 2 + threadIdx.x] = t;
+    M.scal_part[blk * 2 + threadIdx.x] = t;
   }
+}
+
+__global__ void __launch_bounds__(kMergeThreads) bwd_merge_kernel(const __grid_constant__ MergeArgs M) {
+  bwd_merge_body(M, blockIdx.x);
+}
+
+__global__ void __launch_bounds__(kMergeThreads) bwd_merge_batched_kernel(const __grid_constant__ Batch<MergeArgs> B) {
+  const int k = batch_find(B, blockIdx.x);
+  bwd_merge_body(B.p[k], blockIdx.x - B.start[k]);
 }
 
 // Fixed-order FP64 reduction of the per-block scalar partials: thread t sums
 // blocks t, t + 256, ...; warps reduce by xor-shuffle; warp 0 adds the warps
 // in order. One CTA of kMergeThreads threads.
-__global__ void __launch_bounds__(kMergeThreads) bwd_scalar_final_kernel(const double* __restrict__ part, int nblk,
-                                                                         double* d_len, double* d_var) {
+__device__ __forceinline__ void scalar_final_body(const double* __restrict__ part, int nblk, double* d_len,
+                                                  double* d_var) {
   __shared__ double red[2][kMergeThreads / 32];
   double a = 0.0, b = 0.0;
   for (int k = threadIdx.x; k < nblk; k += kMergeThreads) {
@@ -305,6 +300,82 @@ __global__ void __launch_bounds__(kMergeThreads) bwd_scalar_final_kernel(const d
     if (d_len) *d_len = sa;
     if (d_var) *d_var = sb;
   }
+}
+
+__global__ void __launch_bounds__(kMergeThreads) bwd_scalar_final_kernel(const double* __restrict__ part, int nblk,
+                                                                         double* d_len, double* d_var) {
+  scalar_final_body(part, nblk, d_len, d_var);
+}
+
+__global__ void __launch_bounds__(kMergeThreads) scalar_batched_kernel(const __grid_constant__ Batch<ScalP> B) {
+  const ScalP& P = B.p[blockIdx.x];
+  scalar_final_body(P.part, P.nblk, P.d_len, P.d_var);
+}
+
+lr_status launch_bwd_rows_batched(const BwArgs* p, int count, cudaStream_t s) {
+  for (int kind = 0; kind < 3; ++kind) {  // 0: grid, 1: explicit, 2: explicit self-kernel
+    Batch<BwArgs> B;
+    B.count = 0;
+    int64_t tot = 0;
+    for (int i = 0; i <= count; ++i) {
+      const bool flush = (i == count) || B.count == kMaxBatch;
+      if (flush && B.count > 0) {
+        B.start[B.count] = (int32_t)tot;
+        if (tot > 0) {
+          if (kind == 0)
+            bwd_rows_batched_kernel<true, false><<<(unsigned)tot, kBwThreads, 0, s>>>(B);
+          else if (kind == 1)
+            bwd_rows_batched_kernel<false, false><<<(unsigned)tot, kBwThreads, 0, s>>>(B);
+          else
+            bwd_rows_batched_kernel<false, true><<<(unsigned)tot, kBwThreads, 0, s>>>(B);
+          LR_CHECK_CUDA(cudaGetLastError());
+        }
+        B.count = 0;
+        tot = 0;
+      }
+      if (i == count) break;
+      const int pk = p[i].src.xy == nullptr ? 0 : (p[i].gs != nullptr ? 2 : 1);
+      if (pk != kind) continue;
+      B.p[B.count] = p[i];
+      B.start[B.count] = (int32_t)tot;
+      tot += (int64_t)((p[i].n + kBwRows - 1) / kBwRows) * p[i].chunks;
+      ++B.count;
+    }
+  }
+  return LR_OK;
+}
+
+lr_status launch_bwd_merge_batched(const MergeArgs* p, int count, cudaStream_t s) {
+  for (int b0 = 0; b0 < count; b0 += kMaxBatch) {
+    Batch<MergeArgs> B;
+    B.count = count - b0 < kMaxBatch ? count - b0 : kMaxBatch;
+    int64_t tot = 0;
+    for (int k = 0; k < B.count; ++k) {
+      B.p[k] = p[b0 + k];
+      B.start[k] = (int32_t)tot;
+      tot += (p[b0 + k].n + kMergeThreads - 1) / kMergeThreads;
+    }
+    B.start[B.count] = (int32_t)tot;
+    if (tot == 0) continue;
+    bwd_merge_batched_kernel<<<(unsigned)tot, kMergeThreads, 0, s>>>(B);
+    LR_CHECK_CUDA(cudaGetLastError());
+  }
+  return LR_OK;
+}
+
+lr_status launch_scalar_batched(const ScalP* p, int count, cudaStream_t s) {
+  for (int b0 = 0; b0 < count; b0 += kMaxBatch) {
+    Batch<ScalP> B;
+    B.count = count - b0 < kMaxBatch ? count - b0 : kMaxBatch;
+    for (int k = 0; k < B.count; ++k) {
+      B.p[k] = p[b0 + k];
+      B.start[k] = k;
+    }
+    B.start[B.count] = B.count;
+    scalar_batched_kernel<<<(unsigned)B.count, kMergeThreads, 0, s>>>(B);
+    LR_CHECK_CUDA(cudaGetLastError());
+  }
+  return LR_OK;
 }
 
 // ---------------------------------------------------------------------------
@@ -334,14 +405,8 @@ static lr_status plan_rows(int64_t n, int64_t m, bool grid, const lr_grid* g, bo
     LR_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, bwd_rows_kernel<false, true>, kBwThreads, 0));
   else
     LR_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, bwd_rows_kernel<false, false>, kBwThreads, 0));
-  const int64_t target = 8LL * n_sm * (occ > 0 ? occ : 1);
-  int64_t chunks = 1;
-  if (p.row_blocks > 0 && p.n_tiles > 0) {
-    chunks = (target + p.row_blocks - 1) / p.row_blocks;
-    if (chunks < 1) chunks = 1;
-    if (chunks > p.n_tiles) chunks = p.n_tiles;
-  }
-  p.chunks = (int32_t)chunks;
+  const int32_t chunks = plan_chunks(p.row_blocks, p.n_tiles, occ, n_sm);
+  p.chunks = chunks;
   p.partial_bytes = align256(sizeof(float) * (size_t)p.chunks * p.K * (size_t)n);
   p.merge_blocks = (n + kMergeThreads - 1) / kMergeThreads;
   p.scal_bytes = align256(sizeof(double) * 2 * (size_t)(p.merge_blocks > 0 ? p.merge_blocks : 1));
@@ -399,6 +464,55 @@ static lr_status launch_rows(const float2* x, int64_t n, const float2* ys, const
     bwd_scalar_final_kernel<<<1, kMergeThreads, 0, s>>>(M.scal_part, (int)R.merge_blocks, d_len, d_var);
     LR_CHECK_CUDA(cudaGetLastError());
   }
+  return LR_OK;
+}
+
+// Problem descriptors for the non-self row pass (d_x, d_l, d_var) of explicit
+// query points against grid (yg) or explicit (ys) sources, planned as
+// gp_kernel_matvec_bwd plans it; ws receives the partials. With ws == NULL
+// only *bytes is filled in.
+lr_status make_rows_problem(const float2* x, int64_t n, const float2* ys, const lr_grid* yg, int64_t m,
+                            const float* v, const float* g, float ell, float var, float2* dx, double* d_len,
+                            double* d_var, char* ws, BwArgs* A, MergeArgs* M, ScalP* S, size_t* bytes) {
+  RowPlan R;
+  lr_status st = plan_rows(n, m, ys == nullptr, yg, false, &R);
+  if (st != LR_OK) return st;
+  *bytes = R.partial_bytes + R.scal_bytes;
+  if (!ws) return LR_OK;
+  BwArgs a{};
+  a.x = x;
+  a.n = n;
+  a.src.xy = ys;
+  a.src.g = ys ? GridDev{} : grid_dev(*yg);
+  a.src.m = m;
+  a.src.segs = R.segs;
+  a.src.n_tiles = R.n_tiles;
+  a.v = v;
+  a.gs = nullptr;
+  const double c = 1.4426950408889634 / (2.0 * (double)ell * (double)ell);
+  a.neg_c = (float)(-c);
+  a.chunks = R.chunks;
+  a.K = R.K;
+  a.partial = reinterpret_cast<float*>(ws);
+  *A = a;
+  MergeArgs mm{};
+  mm.partial = a.partial;
+  mm.chunks = R.chunks;
+  mm.K = R.K;
+  mm.n = n;
+  mm.g = g;
+  mm.vrow = v;
+  mm.var = var;
+  mm.inv_l2 = (float)(1.0 / ((double)ell * ell));
+  mm.dl_scale = (float)(-(double)var / (c * (double)ell * ell * ell));
+  mm.d_x = dx;
+  mm.d_v = nullptr;
+  mm.scal_part = reinterpret_cast<double*>(ws + R.partial_bytes);
+  *M = mm;
+  S->part = mm.scal_part;
+  S->nblk = (int32_t)R.merge_blocks;
+  S->d_len = d_len;
+  S->d_var = d_var;
   return LR_OK;
 }
 

@@ -1,0 +1,163 @@
+// Problem descriptors of the kernels, shared by the single-problem entry
+// points and the batched launches of the serving engine, plus the host-side
+// launch helpers for batches.
+#pragma once
+#include "batch.cuh"
+#include "grid.cuh"
+#include "lens.cuh"
+
+namespace lr {
+
+// ---- forward reduction (matvec.cu)
+constexpr int kMvThreads = 128;
+constexpr int kMvR = 8;                         // query rows per thread
+constexpr int kRowsPerCta = kMvThreads * kMvR;  // 1024
+constexpr int kTile = 256;                      // source points per tile
+constexpr int kPairs = kTile / 2;               // = kMvThreads: one pair per loader thread
+
+struct SrcDesc {
+  const float2* xy;  // explicit source points, or NULL for a grid
+  GridDev g;         // grid description when xy == NULL
+  int64_t m;         // number of source points
+  int32_t segs;      // grid: tiles per grid row
+  int32_t n_tiles;   // total tiles
+};
+
+struct MvArgs {
+  const float2* x;   // query points [n]
+  int64_t n;
+  SrcDesc src;
+  const float* v;    // [m]
+  float neg_c;       // -log2(e) / (2 l^2)
+  float variance;
+  int32_t chunks;    // column chunks per row block
+  float* out;        // [n] when chunks == 1
+  float* partial;    // [chunks][n] when chunks > 1
+};
+
+struct MergeP {
+  const float* partial;
+  int32_t chunks;
+  int64_t n;
+  float variance;
+  float* out;
+};
+
+
+// ---- backward row pass (matvec_bwd.cu)
+constexpr int kBwThreads = 128;
+constexpr int kBwR = 4;
+constexpr int kBwRows = kBwThreads * kBwR;  // 512 rows per CTA
+constexpr int kBwTile = 256;
+constexpr int kBwPairs = kBwTile / 2;
+constexpr int kMergeThreads = 256;
+
+struct BwSrc {
+  const float2* xy;  // explicit sources, or NULL for a grid
+  GridDev g;
+  int64_t m;
+  int32_t segs, n_tiles;
+};
+
+struct BwArgs {
+  const float2* x;  // query points [n]
+  int64_t n;
+  BwSrc src;
+  const float* v;   // [m] source weights
+  const float* gs;  // [m] source-side g (self-kernel only: g of the same points)
+  float neg_c;      // -log2(e)/(2 l^2)
+  int32_t chunks;
+  int32_t K;        // quantities per row: 4, or 7 for a self-kernel
+  float* partial;   // [chunks][K][n]
+};
+
+struct MergeArgs {
+  const float* partial;
+  int32_t chunks, K;
+  int64_t n;
+  const float* g;      // [n] dL/dout
+  const float* vrow;   // [n] v of the query points (self-kernel column role)
+  float var, inv_l2, dl_scale;  // dl_scale = -var / (neg_c_abs...) see host
+  float2* d_x;         // [n] or NULL
+  float* d_v;          // [n] (self-kernel) or NULL
+  double* scal_part;   // [blocks][2]: d_len, d_var partials
+};
+
+struct ScalP {
+  const double* part;
+  int32_t nblk;
+  double* d_len;
+  double* d_var;
+};
+
+// ---- ray-trace and its backward (raytrace.cu, raytrace_bwd.cu)
+struct RtP {
+  LensConst L;
+  GridDev g;
+  const float2* xi;  // explicit points, or NULL for the grid
+  int64_t n;
+  const float* sub;
+  int32_t n_sub, bulk_ok, profile;
+  float2* beta;
+  float2* alpha;
+};
+
+struct VjpP {
+  LensConst L;
+  LensGradConst LG;
+  GridDev g;
+  const float2* xi;
+  int64_t n;
+  const float* sub;
+  int32_t n_sub, bulk_ok, profile;
+  const float2* dbeta;
+  double* lens_part;
+  float* sub_part;
+};
+
+struct VjpFinalP {
+  const double* lens_part;
+  const float* sub_part;
+  int32_t nblk, n_sub;
+  double* d_lens;
+  double* d_sub;
+};
+
+// out[i] = a[i] - alpha * b[i]
+struct AxpyP {
+  const float* a;
+  const float* b;
+  float* out;
+  int64_t n;
+  float alpha;
+};
+
+// Batched launch helpers: each splits `count` problems into launches of at
+// most kMaxBatch problems, all on stream s.
+lr_status launch_matvec_batched(const MvArgs* p, int count, cudaStream_t s);
+lr_status launch_merge_batched(const MergeP* p, int count, cudaStream_t s);
+lr_status launch_raytrace_batched(const RtP* p, int count, cudaStream_t s);
+lr_status launch_bwd_rows_batched(const BwArgs* p, int count, cudaStream_t s);
+lr_status launch_bwd_merge_batched(const MergeArgs* p, int count, cudaStream_t s);
+lr_status launch_scalar_batched(const ScalP* p, int count, cudaStream_t s);
+lr_status launch_vjp_batched(const VjpP* p, int count, cudaStream_t s);
+lr_status launch_vjp_final_batched(const VjpFinalP* p, int count, cudaStream_t s);
+
+// Problem constructors (planned exactly as the single-problem entry points).
+lr_status make_mv_problem(const float2* x, int64_t n, const float2* ys, const lr_grid* yg, int64_t m, const float* v,
+                          float ell, float var, float* out, float* partial, MvArgs* A, MergeP* M,
+                          size_t* partial_bytes);
+lr_status make_rows_problem(const float2* x, int64_t n, const float2* ys, const lr_grid* yg, int64_t m,
+                            const float* v, const float* g, float ell, float var, float2* dx, double* d_len,
+                            double* d_var, char* ws, BwArgs* A, MergeArgs* M, ScalP* S, size_t* bytes);
+lr_status make_rt_problem(const lr_points* p, float2* beta, float2* alpha, RtP* R);
+lr_status make_vjp_problem(const lr_points* p, const float2* dbeta, double* d_lens, double* d_sub, void* ws, VjpP* V,
+                           VjpFinalP* F);
+
+// Column chunks for a reduction of row_blocks x n_tiles tasks: enough that
+// every resident CTA slot (occupancy x SMs) receives about 8 tasks. Depends
+// only on the problem's own sizes, so a problem is summed in the same order
+// alone or inside a batch.
+int32_t plan_chunks(int64_t row_blocks, int64_t n_tiles, int occupancy, int n_sm);
+
+}  // namespace lr

@@ -8,6 +8,7 @@
 #include <math.h>
 
 #include "host.cuh"
+#include "problems.cuh"
 #include "lens.cuh"
 #include "subs.cuh"
 
@@ -42,15 +43,18 @@ __device__ __forceinline__ void add_subs(const SubRec* recs, int cnt, float x, f
   }
 }
 
+struct RtSmem {
+  float raw[5 * kSubChunk];
+  SubRec recs[kSubChunk];
+  uint64_t bar;
+};
+
 template <int PROFILE>
-__global__ void __launch_bounds__(kRtThreads) raytrace_kernel(LensConst L, GridDev g, const float2* __restrict__ xi,
-                                                              int64_t n, const float* __restrict__ sub, int n_sub,
-                                                              int bulk_ok, float2* __restrict__ beta,
-                                                              float2* __restrict__ alpha_out, int* fault) {
-  __shared__ __align__(16) float raw[5 * kSubChunk];
-  __shared__ __align__(16) SubRec recs[kSubChunk];
-  __shared__ __align__(8) uint64_t bar;
-  const int64_t i = (int64_t)blockIdx.x * kRtThreads + threadIdx.x;
+__device__ __forceinline__ void raytrace_body(const LensConst& L, const GridDev& g, const float2* __restrict__ xi,
+                                              int64_t n, const float* __restrict__ sub, int n_sub, int bulk_ok,
+                                              float2* __restrict__ beta, float2* __restrict__ alpha_out, int* fault,
+                                              int64_t blk, RtSmem& sm) {
+  const int64_t i = blk * kRtThreads + threadIdx.x;
   const bool valid = i < n;
   const int64_t ii = valid ? i : (n - 1);
   const float2 p = xi ? xi[ii] : grid_point(g, ii);
@@ -62,14 +66,14 @@ __global__ void __launch_bounds__(kRtThreads) raytrace_kernel(LensConst L, GridD
   ay = fmaf(L.g2, p.x, fmaf(-L.g1, p.y, ay));
 
   if (n_sub > 0) {
-    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    if (threadIdx.x == 0) mbar_init(&sm.bar, 1);
     __syncthreads();
     uint32_t phase = 0;
     float sx = 0.f, cx = 0.f, sy = 0.f, cy = 0.f;
     for (int h0 = 0; h0 < n_sub; h0 += kSubChunk) {
       const int cnt = min(kSubChunk, n_sub - h0);
-      if (!stage_subs(sub, h0, cnt, PROFILE, raw, recs, &bar, phase, bulk_ok != 0, fault)) return;
-      add_subs<PROFILE>(recs, cnt, p.x, p.y, sx, cx, sy, cy);
+      if (!stage_subs(sub, h0, cnt, PROFILE, sm.raw, sm.recs, &sm.bar, phase, bulk_ok != 0, fault)) return;
+      add_subs<PROFILE>(sm.recs, cnt, p.x, p.y, sx, cx, sy, cy);
       __syncthreads();
     }
     ax += sx - cx;
@@ -79,6 +83,50 @@ __global__ void __launch_bounds__(kRtThreads) raytrace_kernel(LensConst L, GridD
     beta[i] = make_float2(p.x - ax, p.y - ay);
     if (alpha_out) alpha_out[i] = make_float2(ax, ay);
   }
+}
+
+template <int PROFILE>
+__global__ void __launch_bounds__(kRtThreads) raytrace_kernel(const __grid_constant__ LensConst L, GridDev g,
+                                                              const float2* __restrict__ xi, int64_t n,
+                                                              const float* __restrict__ sub, int n_sub, int bulk_ok,
+                                                              float2* __restrict__ beta,
+                                                              float2* __restrict__ alpha_out, int* fault) {
+  __shared__ __align__(16) RtSmem sm;
+  raytrace_body<PROFILE>(L, g, xi, n, sub, n_sub, bulk_ok, beta, alpha_out, fault, blockIdx.x, sm);
+}
+
+__global__ void __launch_bounds__(kRtThreads) raytrace_batched_kernel(const __grid_constant__ Batch<RtP> B,
+                                                                      int* fault) {
+  __shared__ __align__(16) RtSmem sm;
+  const int k = batch_find(B, blockIdx.x);
+  const RtP& P = B.p[k];
+  const int64_t blk = blockIdx.x - B.start[k];
+  if (P.profile == LR_PROFILE_POINT_MASS)
+    raytrace_body<LR_PROFILE_POINT_MASS>(P.L, P.g, P.xi, P.n, P.sub, P.n_sub, P.bulk_ok, P.beta, P.alpha, fault,
+                                         blk, sm);
+  else
+    raytrace_body<LR_PROFILE_TNFW>(P.L, P.g, P.xi, P.n, P.sub, P.n_sub, P.bulk_ok, P.beta, P.alpha, fault, blk,
+                                   sm);
+}
+
+lr_status launch_raytrace_batched(const RtP* p, int count, cudaStream_t s) {
+  int* fault = fault_ptr();
+  LR_REQUIRE(fault != nullptr, "could not resolve the device fault word");
+  for (int b0 = 0; b0 < count; b0 += kMaxBatch) {
+    Batch<RtP> B;
+    B.count = count - b0 < kMaxBatch ? count - b0 : kMaxBatch;
+    int64_t tot = 0;
+    for (int k = 0; k < B.count; ++k) {
+      B.p[k] = p[b0 + k];
+      B.start[k] = (int32_t)tot;
+      tot += (p[b0 + k].n + kRtThreads - 1) / kRtThreads;
+    }
+    B.start[B.count] = (int32_t)tot;
+    if (tot == 0) continue;
+    raytrace_batched_kernel<<<(unsigned)tot, kRtThreads, 0, s>>>(B, fault);
+    LR_CHECK_CUDA(cudaGetLastError());
+  }
+  return LR_OK;
 }
 
 // ---------------------------------------------------------------------------
@@ -182,6 +230,23 @@ lr_status launch_raytrace(const lr_points* p, float2* beta, float2* alpha, cudaS
     raytrace_kernel<LR_PROFILE_TNFW><<<blocks, kRtThreads, 0, s>>>(L, g, xi, p->n, p->sub, ns, bulk_ok, beta, alpha,
                                                                    fault);
   LR_CHECK_CUDA(cudaGetLastError());
+  return LR_OK;
+}
+
+lr_status make_rt_problem(const lr_points* p, float2* beta, float2* alpha, RtP* R) {
+  RtP r{};
+  lr_status st = make_lens_const(p->lens, &r.L);
+  if (st != LR_OK) return st;
+  r.g = p->xy ? GridDev{} : grid_dev(p->grid);
+  r.xi = reinterpret_cast<const float2*>(p->xy);
+  r.n = p->n;
+  r.sub = p->sub;
+  r.n_sub = p->n_sub;
+  r.bulk_ok = (((uintptr_t)p->sub & 15u) == 0) ? 1 : 0;
+  r.profile = p->profile;
+  r.beta = beta;
+  r.alpha = alpha;
+  *R = r;
   return LR_OK;
 }
 

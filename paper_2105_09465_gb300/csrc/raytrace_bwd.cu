@@ -13,6 +13,7 @@
 #include <math.h>
 
 #include "host.cuh"
+#include "problems.cuh"
 #include "subs.cuh"
 
 namespace lr {
@@ -34,21 +35,29 @@ __device__ __forceinline__ double warp_sum_d(double v) {
   return v;
 }
 
+struct VjSmem {
+  float raw[5 * kVjChunk];
+  SubRec recs[kVjChunk];
+  float2 extra[kVjChunk];  // tNFW: (4T, 1/theta_s); point mass: (0, theta_pm)
+  float red[kVjWarps][kVjChunk][4];
+  double lred[kVjWarps][7];
+  uint64_t bar;
+};
+
 template <int PROFILE>
-__global__ void __launch_bounds__(kVjThreads) raytrace_vjp_kernel(LensConst L, LensGradConst LG, GridDev g,
-                                                                  const float2* __restrict__ xi, int64_t n,
-                                                                  const float* __restrict__ sub, int n_sub,
-                                                                  int bulk_ok, const float2* __restrict__ dbeta,
-                                                                  double* __restrict__ lens_part,
-                                                                  float* __restrict__ sub_part, int* fault) {
-  __shared__ __align__(16) float raw[5 * kVjChunk];
-  __shared__ __align__(16) SubRec recs[kVjChunk];
-  __shared__ float2 extra[kVjChunk];  // tNFW: (4T, 1/theta_s); point mass: (0, theta_pm)
-  __shared__ float red[kVjWarps][kVjChunk][4];
-  __shared__ double lred[kVjWarps][7];
-  __shared__ __align__(8) uint64_t bar;
+__device__ __forceinline__ void vjp_body(const LensConst& L, const LensGradConst& LG, const GridDev& g,
+                                         const float2* __restrict__ xi, int64_t n, const float* __restrict__ sub,
+                                         int n_sub, int bulk_ok, const float2* __restrict__ dbeta,
+                                         double* __restrict__ lens_part, float* __restrict__ sub_part, int* fault,
+                                         int64_t blk, VjSmem& sm) {
+  float* raw = sm.raw;
+  SubRec* recs = sm.recs;
+  float2* extra = sm.extra;
+  float (*red)[kVjChunk][4] = sm.red;
+  double (*lred)[7] = sm.lred;
+  uint64_t& bar = sm.bar;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int64_t base = (int64_t)blockIdx.x * kVjPoints;
+  const int64_t base = blk * kVjPoints;
 
   float px[kVjPpt], py[kVjPpt], gx[kVjPpt], gy[kVjPpt];
 #pragma unroll
@@ -86,7 +95,7 @@ __global__ void __launch_bounds__(kVjThreads) raytrace_vjp_kernel(LensConst L, L
   if (tid < 7) {
     double s = 0.0;
     for (int w = 0; w < kVjWarps; ++w) s += lred[w][tid];
-    lens_part[(int64_t)blockIdx.x * 7 + tid] = s;
+    lens_part[blk * 7 + tid] = s;
   }
 
   // ---- subhalos
@@ -150,18 +159,44 @@ __global__ void __launch_bounds__(kVjThreads) raytrace_vjp_kernel(LensConst L, L
     for (int t = tid; t < 4 * cnt; t += kVjThreads) {
       float s = 0.f;
       for (int w = 0; w < kVjWarps; ++w) s += red[w][t >> 2][t & 3];
-      sub_part[((int64_t)blockIdx.x * n_sub + h0) * 4 + t] = s;
+      sub_part[(blk * n_sub + h0) * 4 + t] = s;
     }
     __syncthreads();
   }
 }
 
+template <int PROFILE>
+__global__ void __launch_bounds__(kVjThreads) raytrace_vjp_kernel(const __grid_constant__ LensConst L,
+                                                                  const __grid_constant__ LensGradConst LG, GridDev g,
+                                                                  const float2* __restrict__ xi, int64_t n,
+                                                                  const float* __restrict__ sub, int n_sub,
+                                                                  int bulk_ok, const float2* __restrict__ dbeta,
+                                                                  double* __restrict__ lens_part,
+                                                                  float* __restrict__ sub_part, int* fault) {
+  __shared__ __align__(16) VjSmem sm;
+  vjp_body<PROFILE>(L, LG, g, xi, n, sub, n_sub, bulk_ok, dbeta, lens_part, sub_part, fault, blockIdx.x, sm);
+}
+
+__global__ void __launch_bounds__(kVjThreads) vjp_batched_kernel(const __grid_constant__ Batch<VjpP> B, int* fault) {
+  __shared__ __align__(16) VjSmem sm;
+  const int k = batch_find(B, blockIdx.x);
+  const VjpP& P = B.p[k];
+  const int64_t blk = blockIdx.x - B.start[k];
+  if (P.profile == LR_PROFILE_POINT_MASS)
+    vjp_body<LR_PROFILE_POINT_MASS>(P.L, P.LG, P.g, P.xi, P.n, P.sub, P.n_sub, P.bulk_ok, P.dbeta, P.lens_part,
+                                    P.sub_part, fault, blk, sm);
+  else
+    vjp_body<LR_PROFILE_TNFW>(P.L, P.LG, P.g, P.xi, P.n, P.sub, P.n_sub, P.bulk_ok, P.dbeta, P.lens_part,
+                              P.sub_part, fault, blk, sm);
+}
+
 // Fixed-order FP64 sum of the per-CTA partials: one warp per output value
 // (7 lens values, then 4 per subhalo); lane l sums CTAs l, l + 32, ...; the
 // warp reduces by xor-shuffle.
-__global__ void vjp_final_kernel(const double* __restrict__ lens_part, const float* __restrict__ sub_part, int nblk,
-                                 int n_sub, double* __restrict__ d_lens, double* __restrict__ d_sub) {
-  const int o = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+__device__ __forceinline__ void vjp_final_body(const double* __restrict__ lens_part,
+                                               const float* __restrict__ sub_part, int nblk, int n_sub,
+                                               double* __restrict__ d_lens, double* __restrict__ d_sub, int64_t blk) {
+  const int o = (int)((blk * blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
   if (o >= 7 + 4 * n_sub) return;
   double s = 0.0;
@@ -180,6 +215,54 @@ __global__ void vjp_final_kernel(const double* __restrict__ lens_part, const flo
       d_sub[o - 7] = s;
     }
   }
+}
+
+__global__ void vjp_final_kernel(const double* __restrict__ lens_part, const float* __restrict__ sub_part, int nblk,
+                                 int n_sub, double* __restrict__ d_lens, double* __restrict__ d_sub) {
+  vjp_final_body(lens_part, sub_part, nblk, n_sub, d_lens, d_sub, blockIdx.x);
+}
+
+__global__ void vjp_final_batched_kernel(const __grid_constant__ Batch<VjpFinalP> B) {
+  const int k = batch_find(B, blockIdx.x);
+  const VjpFinalP& P = B.p[k];
+  vjp_final_body(P.lens_part, P.sub_part, P.nblk, P.n_sub, P.d_lens, P.d_sub, blockIdx.x - B.start[k]);
+}
+
+lr_status launch_vjp_batched(const VjpP* p, int count, cudaStream_t s) {
+  int* fault = fault_ptr();
+  LR_REQUIRE(fault != nullptr, "could not resolve the device fault word");
+  for (int b0 = 0; b0 < count; b0 += kMaxBatch) {
+    Batch<VjpP> B;
+    B.count = count - b0 < kMaxBatch ? count - b0 : kMaxBatch;
+    int64_t tot = 0;
+    for (int k = 0; k < B.count; ++k) {
+      B.p[k] = p[b0 + k];
+      B.start[k] = (int32_t)tot;
+      tot += (p[b0 + k].n + kVjPoints - 1) / kVjPoints;
+    }
+    B.start[B.count] = (int32_t)tot;
+    if (tot == 0) continue;
+    vjp_batched_kernel<<<(unsigned)tot, kVjThreads, 0, s>>>(B, fault);
+    LR_CHECK_CUDA(cudaGetLastError());
+  }
+  return LR_OK;
+}
+
+lr_status launch_vjp_final_batched(const VjpFinalP* p, int count, cudaStream_t s) {
+  for (int b0 = 0; b0 < count; b0 += kMaxBatch) {
+    Batch<VjpFinalP> B;
+    B.count = count - b0 < kMaxBatch ? count - b0 : kMaxBatch;
+    int64_t tot = 0;
+    for (int k = 0; k < B.count; ++k) {
+      B.p[k] = p[b0 + k];
+      B.start[k] = (int32_t)tot;
+      tot += ((7 + 4 * (int64_t)p[b0 + k].n_sub) * 32 + 255) / 256;
+    }
+    B.start[B.count] = (int32_t)tot;
+    vjp_final_batched_kernel<<<(unsigned)tot, 256, 0, s>>>(B);
+    LR_CHECK_CUDA(cudaGetLastError());
+  }
+  return LR_OK;
 }
 
 // ---------------------------------------------------------------------------
@@ -254,6 +337,36 @@ lr_status launch_raytrace_vjp(const lr_points* p, const float2* dbeta, double* d
   vjp_final_kernel<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, s>>>(lens_part, sub_part, (int)nblk, p->n_sub,
                                                                         d_lens, p->n_sub ? d_sub : nullptr);
   LR_CHECK_CUDA(cudaGetLastError());
+  return LR_OK;
+}
+
+// Problem descriptors for the ray-trace VJP; ws (raytrace_vjp_ws bytes) holds
+// the per-CTA partials.
+lr_status make_vjp_problem(const lr_points* p, const float2* dbeta, double* d_lens, double* d_sub, void* ws, VjpP* V,
+                           VjpFinalP* F) {
+  VjpP v{};
+  lr_status st = make_lens_const(p->lens, &v.L);
+  if (st != LR_OK) return st;
+  st = make_lens_grad_const(p->lens, &v.LG);
+  if (st != LR_OK) return st;
+  const int64_t nblk = (p->n + kVjPoints - 1) / kVjPoints;
+  v.g = p->xy ? GridDev{} : grid_dev(p->grid);
+  v.xi = reinterpret_cast<const float2*>(p->xy);
+  v.n = p->n;
+  v.sub = p->sub;
+  v.n_sub = p->n_sub;
+  v.bulk_ok = (((uintptr_t)p->sub & 15u) == 0) ? 1 : 0;
+  v.profile = p->profile;
+  v.dbeta = dbeta;
+  v.lens_part = static_cast<double*>(ws);
+  v.sub_part = reinterpret_cast<float*>(static_cast<char*>(ws) + align256(sizeof(double) * 7 * (size_t)nblk));
+  *V = v;
+  F->lens_part = v.lens_part;
+  F->sub_part = v.sub_part;
+  F->nblk = (int32_t)nblk;
+  F->n_sub = p->n_sub;
+  F->d_lens = d_lens;
+  F->d_sub = p->n_sub ? d_sub : nullptr;
   return LR_OK;
 }
 

@@ -1,0 +1,182 @@
+"""Serving engine: results against the oracle and against the single-problem
+entry points, bit-identical alone vs in a mix vs one-at-a-time, admission by
+device-memory budget, poll/timeout/cancel semantics and host-side fault
+injection."""
+import time
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2105_09465_gb300 import abi, api, workloads as W
+from paper_2105_09465_gb300.serving import Session
+from tests.gpu_util import dev, host, need_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    need_gpu()
+
+
+def problem(seed, side, n_sub, yside=32):
+    rng = np.random.default_rng(seed)
+    lens = W.draw_lens(rng)
+    sub = W.draw_subhalos(rng, n_sub, lens, 1e7, 1e10)
+    g = W.Grid(side, side, 2, 0.05)
+    yg = W.inducing_grid(g, yside)
+    ell = float(np.float32(yg.pix * 4.0 / 3.0))
+    p = W.Problem(f"s{seed}", g, lens, sub, 0, yg, ell, 1.0, W.draw_v(rng, yg.n), seed)
+    data = rng.standard_normal(p.n).astype(np.float32)
+    return p, data
+
+
+def test_matches_oracle_iterations(orc):
+    p, data = problem(1, 16, 6, 12)
+    iters, step = 3, 0.05
+    with Session(max_slots=4) as S:
+        t = S.submit(p, data, iters, step)
+        R = S.poll(t)
+    assert R.status == abi.LR_OK
+    xi = orc.grid_points(*p.xgrid.astuple())
+    yg = orc.grid_points(*p.ygrid.astuple())
+    v = p.v.astype(np.float64)
+    for _ in range(iters):
+        _, b = orc.raytrace(xi, p.lens.astuple(), p.sub)
+        out, _ = orc.kernel_matvec(b, yg, v, p.lengthscale, p.variance)
+        g = out - data
+        G = orc.kernel_matvec_vjp(b, yg, v, p.lengthscale, p.variance, g)
+        dl, ds = orc.raytrace_vjp(xi, p.lens.astuple(), p.sub, G["d_x"])
+        v = v - step * G["d_v"]
+    scale = lambda a: np.max(np.abs(a))
+    np.testing.assert_allclose(R.out, out, atol=1e-4 * scale(out))
+    np.testing.assert_allclose(R.v, v, atol=1e-4 * scale(v))
+    np.testing.assert_allclose(R.d_lens, dl, atol=1e-3 * scale(dl))
+    np.testing.assert_allclose(R.d_sub, ds, atol=1e-3 * scale(ds))
+    assert abs(R.d_lengthscale - G["d_len"]) <= 1e-3 * abs(G["d_len"])
+    assert abs(R.d_variance - G["d_var"]) <= 1e-3 * abs(G["d_var"])
+    assert abs(R.loss - 0.5 * np.sum((out - data) ** 2)) <= 1e-4 * R.loss
+
+
+def test_one_iteration_equals_single_problem_calls():
+    """Batched launches inside the engine give exactly what the single-problem
+    entry points give for the same iteration."""
+    p, data = problem(2, 24, 9, 32)
+    with Session(max_slots=4) as S:
+        t = S.submit(p, data, 1, 0.0)
+        R = S.poll(t)
+    q = api.Points(grid=p.xgrid, lens=p.lens, sub=dev(p.sub))
+    s = api.Points(grid=p.ygrid)
+    out = api.gp_kernel_matvec(q, s, dev(p.v), p.lengthscale, p.variance)
+    g = out - dev(data)
+    G = api.gp_kernel_matvec_bwd(q, s, dev(p.v), p.lengthscale, p.variance, g,
+                                 want=["v", "lengthscale", "variance", "lens", "sub"])
+    assert np.array_equal(R.out, host(out).astype(np.float32))
+    assert np.array_equal(R.v, p.v)
+    assert np.array_equal(R.d_lens, host(G["lens"]))
+    assert np.array_equal(R.d_sub, host(G["sub"]))
+    assert R.d_lengthscale == G["lengthscale"].item() and R.d_variance == G["variance"].item()
+
+
+def run(reqs, max_slots, iters=4, step=0.02, budget=0):
+    with Session(max_slots=max_slots, hbm_budget_bytes=budget) as S:
+        ts = [S.submit(p, d, iters, step) for p, d in reqs]
+        return [S.poll(t) for t in ts]
+
+
+def same(a, b):
+    return (np.array_equal(a.out, b.out) and np.array_equal(a.v, b.v) and np.array_equal(a.d_lens, b.d_lens)
+            and np.array_equal(a.d_sub, b.d_sub) and a.d_lengthscale == b.d_lengthscale
+            and a.d_variance == b.d_variance)
+
+
+def test_alone_vs_mix_vs_one_at_a_time_bit_identical():
+    reqs = [problem(10 + k, side, ns, ys) for k, (side, ns, ys) in
+            enumerate([(16, 0, 32), (40, 25, 64), (24, 7, 32), (64, 40, 128), (32, 3, 16), (20, 12, 48)])]
+    mix = run(reqs, max_slots=8)
+    fifo = run(reqs, max_slots=1)
+    alone = [run([r], max_slots=1)[0] for r in reqs[:3]]
+    for k in range(len(reqs)):
+        assert mix[k].status == abi.LR_OK
+        assert same(mix[k], fifo[k]), k
+    for k in range(3):
+        assert same(mix[k], alone[k]), k
+
+
+def test_more_requests_than_one_batched_launch():
+    """17+ active requests split every stage into several batched launches."""
+    reqs = [problem(40 + k, 12 + (k % 5) * 4, k % 4, 16) for k in range(20)]
+    mix = run(reqs, max_slots=20, iters=2)
+    fifo = run(reqs, max_slots=1, iters=2)
+    for a, b in zip(mix, fifo):
+        assert a.status == abi.LR_OK and same(a, b)
+
+
+def test_admission_respects_memory_budget():
+    reqs = [problem(60 + k, 48, 10, 64) for k in range(6)]
+    # footprint of one request: measure with a generous session and its stats
+    with Session(max_slots=1) as S:
+        t = S.submit(*reqs[0], 2, 0.01)
+        peak = 0
+        while True:
+            peak = max(peak, S.stats()["used_bytes"])
+            st = S.poll_status(t, 0.0)
+            if st != abi.LR_PENDING:
+                break
+            time.sleep(0.001)
+        S.poll(t)
+    one = peak
+    assert one > 0
+    budget = int(2.5 * one)
+    with Session(max_slots=8, hbm_budget_bytes=budget) as S:
+        ts = [S.submit(p, d, 6, 0.01) for p, d in reqs]
+        seen_active = 0
+        for _ in range(2000):
+            st = S.stats()
+            assert st["used_bytes"] <= budget
+            seen_active = max(seen_active, st["active"])
+            if st["pending"] == 0 and st["active"] == 0:
+                break
+            time.sleep(0.002)
+        res = [S.poll(t) for t in ts]
+    assert all(r.status == abi.LR_OK for r in res)
+    assert seen_active <= 2
+
+
+def test_request_larger_than_budget_is_rejected():
+    p, data = problem(70, 64, 5, 64)
+    with Session(max_slots=2, hbm_budget_bytes=1 << 20) as S:
+        with pytest.raises(abi.LensGPError) as e:
+            S.submit(p, data, 2, 0.0)
+        assert e.value.status == abi.LR_ERR_OUT_OF_MEMORY
+
+
+def test_poll_pending_timeout_and_cancel():
+    big, bd = problem(80, 200, 50, 128)
+    small, sd = problem(81, 16, 2, 16)
+    with Session(max_slots=1) as S:
+        t1 = S.submit(big, bd, 40, 0.0)
+        t2 = S.submit(small, sd, 2, 0.0)
+        assert S.poll_status(t1, 0.0) == abi.LR_PENDING
+        assert S.poll_status(t1, 0.001) == abi.LR_ERR_TIMEOUT
+        assert S.cancel(t2) == abi.LR_OK  # still queued behind t1 (one slot)
+        assert S.lib.solve_session_poll(S.h, t2, abi.lr_result(), 0) == abi.LR_ERR_NOT_FOUND
+        r1 = S.poll(t1)
+        assert r1.status == abi.LR_OK
+        assert S.cancel(t1) == abi.LR_ERR_NOT_FOUND
+
+
+def test_fault_injection_fails_the_iteration_and_the_session_recovers():
+    a, ad = problem(90, 24, 4, 32)
+    c, cd = problem(91, 24, 4, 32)
+    with Session(max_slots=4) as S:
+        S.inject_fault()
+        ta = S.submit(a, ad, 3, 0.0)
+        ra = S.poll(ta)
+        assert ra.status == abi.LR_ERR_CUDA
+        tc = S.submit(c, cd, 3, 0.0)
+        rc = S.poll(tc)
+        assert rc.status == abi.LR_OK
+        assert S.stats()["used_bytes"] == 0
+    assert api.fault_status() == 0  # no device-side fault was recorded
