@@ -190,6 +190,11 @@ lr_status lr_matvec_workspace_size(const lr_points* query, const lr_points* sour
  *   d_lens         double[7]    dL/d(x0, y0, q, phi, theta_e, g1, g2) of the
  *                               query's lens (slope held fixed)
  *   d_sub          double[S][4] dL/d(x_h, y_h, kappa_s | theta_pm, theta_s)
+ * and one optional INPUT:
+ *   beta_in        float[n][2]  the query's ray-traced points as the forward
+ *                               pass produced them (gp_kernel_matvec's
+ *                               beta_out); when given they are used instead of
+ *                               being recomputed
  */
 typedef struct {
   float* d_v;
@@ -199,6 +204,7 @@ typedef struct {
   double* d_variance;
   double* d_lens;
   double* d_sub;
+  const float* beta_in;
 } lr_grads;
 
 /*

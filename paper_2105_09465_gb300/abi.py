@@ -49,7 +49,7 @@ class lr_points(ctypes.Structure):
 class lr_grads(ctypes.Structure):
     _fields_ = [("d_v", ctypes.c_void_p), ("d_x", ctypes.c_void_p), ("d_y", ctypes.c_void_p),
                 ("d_lengthscale", ctypes.c_void_p), ("d_variance", ctypes.c_void_p), ("d_lens", ctypes.c_void_p),
-                ("d_sub", ctypes.c_void_p)]
+                ("d_sub", ctypes.c_void_p), ("beta_in", ctypes.c_void_p)]
 
 
 class lr_session_cfg(ctypes.Structure):

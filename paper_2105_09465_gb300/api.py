@@ -96,11 +96,12 @@ def matvec_workspace_size(query: Points, source: Points | None) -> int:
 
 def gp_kernel_matvec(query: Points, source: Points | None, v: torch.Tensor, lengthscale: float,
                      variance: float = 1.0, want_beta: bool = False, out: torch.Tensor | None = None,
-                     workspace: torch.Tensor | None = None, stream=None):
+                     workspace: torch.Tensor | None = None, stream=None, beta: torch.Tensor | None = None):
     """out_i = sum_j variance exp(-|x_i - y_j|^2 / (2 lengthscale^2)) v_j.
 
     `source=None` is the self-kernel. Returns out (and the ray-traced query
-    points when want_beta and the query carries a lens or a grid)."""
+    points when want_beta and the query carries a lens or a grid). `beta`, if
+    given, is an (n, 2) float32 buffer that receives the ray-traced points."""
     lib = abi.load()
     _require_cuda(v, "v")
     cq, k1 = to_c_points(query)
@@ -109,7 +110,9 @@ def gp_kernel_matvec(query: Points, source: Points | None, v: torch.Tensor, leng
     dev = v.device
     if out is None:
         out = torch.empty((n,), dtype=torch.float32, device=dev)
-    beta = torch.empty((n, 2), dtype=torch.float32, device=dev) if want_beta else None
+    if beta is None and want_beta:
+        beta = torch.empty((n, 2), dtype=torch.float32, device=dev)
+    _require_cuda(beta, "beta", (2,))
     b = ctypes.c_size_t(0)
     abi.check(lib.lr_matvec_workspace_size(ctypes.byref(cq), ctypes.byref(cs) if cs is not None else None, 1,
                                            ctypes.byref(b)), "lr_matvec_workspace_size")
@@ -129,13 +132,15 @@ GRADS = ("v", "x", "y", "lengthscale", "variance", "lens", "sub")
 
 def gp_kernel_matvec_bwd(query: Points, source: Points | None, v: torch.Tensor, lengthscale: float,
                          variance: float, g_out: torch.Tensor, want=("v", "x", "lengthscale", "variance"),
-                         workspace: torch.Tensor | None = None, stream=None) -> dict:
+                         workspace: torch.Tensor | None = None, stream=None, beta: torch.Tensor | None = None) -> dict:
     """Gradients of Loss = sum_i g_out_i out_i (recompute-only backward).
 
     `want` selects among v, x (query points after ray-tracing), y (explicit
     non-self sources), lengthscale, variance, lens (7: x0, y0, q, phi,
-    theta_e, g1, g2) and sub (S x 4). Returns a dict of CUDA tensors (the
-    scalar and parameter gradients are float64)."""
+    theta_e, g1, g2) and sub (S x 4). `beta` (optional) passes the query's
+    ray-traced points from the forward pass instead of recomputing them.
+    Returns a dict of CUDA tensors (the scalar and parameter gradients are
+    float64)."""
     lib = abi.load()
     _require_cuda(v, "v")
     _require_cuda(g_out, "g_out")
@@ -166,6 +171,9 @@ def gp_kernel_matvec_bwd(query: Points, source: Points | None, v: torch.Tensor, 
     gr.d_variance = out["variance"].data_ptr() if "variance" in out else None
     gr.d_lens = out["lens"].data_ptr() if "lens" in out else None
     gr.d_sub = out["sub"].data_ptr() if ("sub" in out and out["sub"].numel()) else None
+    if beta is not None:
+        _require_cuda(beta, "beta", (2,))
+        gr.beta_in = beta.data_ptr()
     b = ctypes.c_size_t(0)
     ps = ctypes.byref(cs) if cs is not None else None
     abi.check(lib.lr_matvec_bwd_workspace_size(ctypes.byref(cq), ps, 1, ctypes.byref(gr), ctypes.byref(b)),

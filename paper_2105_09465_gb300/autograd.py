@@ -27,14 +27,14 @@ class RaytraceKernelMatvec(torch.autograd.Function):
         q = api.Points(grid=xgrid, lens=lens, sub=sub.detach().contiguous() if sub is not None else None,
                        profile=profile)
         s = api.Points(grid=ygrid) if ygrid is not None else None
-        out = api.gp_kernel_matvec(q, s, v.detach().contiguous(), ell, var)
-        ctx.save_for_backward(v, sub if sub is not None else torch.empty(0))
+        out, beta = api.gp_kernel_matvec(q, s, v.detach().contiguous(), ell, var, want_beta=True)
+        ctx.save_for_backward(v, sub if sub is not None else torch.empty(0), beta)
         ctx.meta = (q, s, ell, var, lens_params.dtype, lens_params.device)
         return out
 
     @staticmethod
     def backward(ctx, grad_out):
-        v, sub = ctx.saved_tensors
+        v, sub, beta = ctx.saved_tensors
         q, s, ell, var, ldtype, ldev = ctx.meta
         need = ctx.needs_input_grad
         want = []
@@ -51,7 +51,7 @@ class RaytraceKernelMatvec(torch.autograd.Function):
         if not want:
             return (None,) * 8
         G = api.gp_kernel_matvec_bwd(q, s, v.detach().contiguous(), ell, var, grad_out.contiguous().float(),
-                                     want=want)
+                                     want=want, beta=beta)
         gv = G.get("v")
         gl = None
         if "lens" in G:

@@ -79,13 +79,25 @@ __device__ __forceinline__ void sple_alpha(const LensConst& L, float x, float y,
   ay = fmaf(L.s, apx, L.c * apy);
 }
 
+// Fast FP32 helpers for the subhalo terms (hardware reciprocal, reciprocal
+// square root and log2; each within a few ulp, far inside the 1e-6 arcsec
+// deflection budget of a subhalo whose deflection is at most ~0.1 arcsec).
+__device__ __forceinline__ float fsqrt_pos(float x) { return x * rsqrtf(x); }  // x > 0
+__device__ __forceinline__ float fdiv(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ float frcp(float b) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(b));
+  return r;
+}
+__device__ __forceinline__ float flog(float x) { return __logf(x); }
+
 // F(x) of the NFW family as a function of x^2 (x = R / theta_s):
 //   arccosh(1/x)/sqrt(1-x^2) for x < 1, arccos(1/x)/sqrt(x^2-1) for x > 1,
 // with its series sum_n (-eps)^n/(2n+1), eps = x^2 - 1, near x = 1.
 // Also returns s = sqrt(|1 - x^2|).
 __device__ __forceinline__ float nfw_F(float x2, float xx, float& s) {
   const float eps = x2 - 1.0f;
-  s = sqrtf(fabsf(eps));
+  s = fsqrt_pos(fmaxf(fabsf(eps), 1e-30f));
   if (fabsf(eps) < 0.05f) {
     const float m = -eps;
     float p = 1.0f / 15.0f;
@@ -97,8 +109,9 @@ __device__ __forceinline__ float nfw_F(float x2, float xx, float& s) {
     p = fmaf(p, m, 1.0f / 3.0f);
     return fmaf(p, m, 1.0f);
   }
-  if (eps < 0.f) return logf((1.0f + s) / xx) / s;  // arccosh(1/x) = ln((1 + s)/x)
-  return atanf(s) / s;                              // arccos(1/x) = arctan(s)
+  const float is = frcp(s);
+  if (eps < 0.f) return flog((1.0f + s) * frcp(xx)) * is;  // arccosh(1/x) = ln((1 + s)/x)
+  return atanf(s) * is;                                    // arccos(1/x) = arctan(s)
 }
 
 // a4: truncated-NFW deflection per unit offset: alpha = m * (dx, dy) with
@@ -111,24 +124,25 @@ __device__ __forceinline__ float nfw_F(float x2, float xx, float& s) {
 __device__ __forceinline__ float tnfw_m(const SubRec& h, float R2) {
   const float x2 = R2 * h.its2;
   if (!(x2 > 1e-20f)) return 0.f;
-  const float xx = sqrtf(x2);
+  const float xx = fsqrt_pos(x2);
   float s;
   const float F = nfw_F(x2, xx, s);
-  const float st = sqrtf(h.tau2 + x2);
+  const float st = fsqrt_pos(h.tau2 + x2);
   const float tp = h.tau + st;
-  const float L = logf(xx / tp);
+  const float itp = frcp(tp);
+  const float L = flog(xx * itp);
   float G;
   if (x2 < 0.25f) {
-    const float dlx2 = -(h.tau / (1.0f + s) + 1.0f / tp) / tp;
+    const float is1 = frcp(1.0f + s);
+    const float dlx2 = -fmaf(h.tau, is1, itp) * itp;
     const float dl = dlx2 * x2;
-    const float ratio = (dl != 0.f) ? log1pf(dl) / dl : 1.0f;
+    const float ratio = (dl != 0.f) ? fdiv(log1pf(dl), dl) : 1.0f;
     const float t2m1 = h.tau2 - 1.0f;
-    G = fmaf(2.0f, F, -kPi / tp) +
-        t2m1 * (F / (1.0f + s) + dlx2 * ratio + L / (h.tau * tp));
+    G = fmaf(2.0f, F, -kPi * itp) + t2m1 * (F * is1 + dlx2 * ratio + L * frcp(h.tau) * itp);
   } else {
     const float t2m1 = h.tau2 - 1.0f;
     const float B = fmaf(fmaf(2.0f, x2, t2m1), F, h.C) + st * fmaf(h.t2m1_t, L, -kPi);
-    G = B / x2;
+    G = B * frcp(x2);
   }
   return h.A * G;
 }
@@ -176,21 +190,23 @@ __device__ __forceinline__ void tnfw_GH(const SubRec& h, float R2, float& Gt, fl
     Ht = 0.f;
     return;
   }
-  const float xx = sqrtf(x2);
+  const float xx = fsqrt_pos(x2);
   float s;
   const float F = nfw_F(x2, xx, s);
-  const float st = sqrtf(h.tau2 + x2);
+  const float st = fsqrt_pos(h.tau2 + x2);
   const float tp = h.tau + st;
-  const float L = logf(xx / tp);
+  const float itp = frcp(tp);
+  const float L = flog(xx * itp);
   const float t2m1 = h.tau2 - 1.0f;
   if (x2 < 0.25f) {
-    const float dlx2 = -(h.tau / (1.0f + s) + 1.0f / tp) / tp;
+    const float is1 = frcp(1.0f + s);
+    const float dlx2 = -fmaf(h.tau, is1, itp) * itp;
     const float dl = dlx2 * x2;
-    const float ratio = (dl != 0.f) ? log1pf(dl) / dl : 1.0f;
-    Gt = fmaf(2.0f, F, -kPi / tp) + t2m1 * (F / (1.0f + s) + dlx2 * ratio + L / (h.tau * tp));
+    const float ratio = (dl != 0.f) ? fdiv(log1pf(dl), dl) : 1.0f;
+    Gt = fmaf(2.0f, F, -kPi * itp) + t2m1 * (F * is1 + dlx2 * ratio + L * frcp(h.tau) * itp);
   } else {
     const float B = fmaf(fmaf(2.0f, x2, t2m1), F, h.C) + st * fmaf(h.t2m1_t, L, -kPi);
-    Gt = B / x2;
+    Gt = B * frcp(x2);
   }
   const float eps = x2 - 1.0f;
   float omf;  // (1 - F) / eps
@@ -203,9 +219,9 @@ __device__ __forceinline__ void tnfw_GH(const SubRec& h, float R2, float& Gt, fl
     p = fmaf(p, -eps, 1.0f / 5.0f);
     omf = fmaf(p, -eps, 1.0f / 3.0f);
   } else {
-    omf = (1.0f - F) / eps;
+    omf = (1.0f - F) * frcp(eps);
   }
-  const float ist = 1.0f / st;
+  const float ist = frcp(st);
   Ht = fmaf(2.0f, F, (h.tau2 + 1.0f) * omf) + ist * fmaf(h.t2m1_t, L, -kPi);
 }
 

@@ -54,18 +54,32 @@ __device__ __forceinline__ void tile_range(const SrcDesc& S, int t, int64_t& j0,
 }
 
 // Loads source pair `p` of tile t into registers (zero weight past the end).
+// Grid tiles are cut into sub-segments of kSeg columns; grid abscissae are
+// stored as sc (x_j - o) relative to the sub-segment's centre column o, which
+// keeps every scaled coordinate of a contributing pair small (FP32 error
+// ~1e-6 of a kernel length) while letting one FMA form the exponent.
+constexpr int kSeg = 16;
+
+__device__ __forceinline__ float seg_origin(const GridDev& g, int c0, int sg) {
+  return grid_x(g, c0 + kSeg * sg + kSeg / 2);
+}
+
 template <bool GRID>
-__device__ __forceinline__ void load_pair(const SrcDesc& S, const float* __restrict__ v, int t, int p, float4& P,
-                                          float2& V) {
+__device__ __forceinline__ void load_pair(const SrcDesc& S, const float* __restrict__ v, float sc, int t, int p,
+                                          float4& P, float2& V) {
   int64_t j0;
   int cnt, grow;
   tile_range(S, t, j0, cnt, grow);
   const int a = 2 * p, b = 2 * p + 1;
   if (GRID) {
     const int c0 = (int)(j0 - (int64_t)grow * S.g.W);
-    const float xa = (a < cnt) ? grid_x(S.g, c0 + a) : 0.f;
-    const float xb = (b < cnt) ? grid_x(S.g, c0 + b) : 0.f;
-    P = make_float4(-xa, -xb, 0.f, 0.f);
+    const float o = seg_origin(S.g, c0, a / kSeg);
+    const float xa = (a < cnt) ? sc * (grid_x(S.g, c0 + a) - o) : 0.f;
+    const float xb = (b < cnt) ? sc * (grid_x(S.g, c0 + b) - o) : 0.f;
+    // (x', v) of the pair in one 16-byte word: one shared load per pair
+    P = make_float4(-xa, -xb, (a < cnt) ? __ldg(v + j0 + a) : 0.f, (b < cnt) ? __ldg(v + j0 + b) : 0.f);
+    V = f2(0.f, 0.f);
+    return;
   } else {
     const float2 pa = (a < cnt) ? __ldg(S.xy + j0 + a) : f2(0.f, 0.f);
     const float2 pb = (b < cnt) ? __ldg(S.xy + j0 + b) : f2(0.f, 0.f);
@@ -75,16 +89,25 @@ __device__ __forceinline__ void load_pair(const SrcDesc& S, const float* __restr
 }
 
 // One task: kRowsPerCta query rows x one chunk of source tiles.
+// Per-thread Kahan running sums live in shared memory (touched once per tile),
+// which keeps them out of the register budget of the inner loop.
+struct MvSmem {
+  float4 sP[2][kPairs];
+  float2 sV[2][kPairs];
+  float ksum[kMvR][kMvThreads];
+  float kcomp[kMvR][kMvThreads];
+};
+
 template <bool GRID>
-__device__ __forceinline__ void matvec_body(const MvArgs& A, int rb, int chunk, float4 (*sP)[kPairs],
-                                            float2 (*sV)[kPairs]) {
+__device__ __forceinline__ void matvec_body(const MvArgs& A, int rb, int chunk, MvSmem& sm) {
+  float4 (*sP)[kPairs] = sm.sP;
+  float2 (*sV)[kPairs] = sm.sV;
   const int nt = A.src.n_tiles;
   const int t0 = (int)((int64_t)chunk * nt / A.chunks);
   const int t1 = (int)((int64_t)(chunk + 1) * nt / A.chunks);
   const int tid = threadIdx.x;
 
   float2 xq[kMvR], yq[kMvR], acc[kMvR];
-  float sum[kMvR], comp[kMvR];
 #pragma unroll
   for (int r = 0; r < kMvR; ++r) {
     int64_t i = (int64_t)rb * kRowsPerCta + r * kMvThreads + tid;
@@ -93,15 +116,15 @@ __device__ __forceinline__ void matvec_body(const MvArgs& A, int rb, int chunk, 
     xq[r] = f2(p.x, p.x);
     yq[r] = f2(p.y, p.y);
     acc[r] = f2(0.f, 0.f);
-    sum[r] = 0.f;
-    comp[r] = 0.f;
+    sm.ksum[r][tid] = 0.f;
+    sm.kcomp[r][tid] = 0.f;
   }
   const float2 nc2 = f2(A.neg_c, A.neg_c);
 
   float4 P;
   float2 V;
   if (t0 < t1) {
-    load_pair<GRID>(A.src, A.v, t0, tid, P, V);
+    load_pair<GRID>(A.src, A.v, A.sc, t0, tid, P, V);
     sP[0][tid] = P;
     sV[0][tid] = V;
   }
@@ -109,31 +132,43 @@ __device__ __forceinline__ void matvec_body(const MvArgs& A, int rb, int chunk, 
 
   for (int t = t0; t < t1; ++t) {
     const int buf = (t - t0) & 1;
-    if (t + 1 < t1) load_pair<GRID>(A.src, A.v, t + 1, tid, P, V);  // in flight during compute
+    if (t + 1 < t1) load_pair<GRID>(A.src, A.v, A.sc, t + 1, tid, P, V);  // in flight during compute
     int64_t j0;
     int cnt, grow;
     tile_range(A.src, t, j0, cnt, grow);
     const int np = (cnt + 1) >> 1;
     if (GRID) {
+      // exponent -(sc^2)(dx^2 + dy^2) = -(dx'^2 + dy'^2) with tile-local scaled dx'
       const float yt = grid_y(A.src.g, grow);
-      float2 dy2c[kMvR];
+      const int c0 = (int)(j0 - (int64_t)grow * A.src.g.W);
+      float2 dy2[kMvR];
 #pragma unroll
       for (int r = 0; r < kMvR; ++r) {
-        const float dy = yq[r].x - yt;
-        const float e = A.neg_c * dy * dy;
-        dy2c[r] = f2(e, e);
+        const float dy = A.sc * (yq[r].x - yt);
+        dy2[r] = f2(dy * dy, dy * dy);
       }
-#pragma unroll 2
-      for (int p = 0; p < np; ++p) {
-        const float4 Q = sP[buf][p];
-        const float2 W = sV[buf][p];
-        const float2 nx = f2(Q.x, Q.y);
+      const int nsg = (cnt + kSeg - 1) / kSeg;
+      for (int sg = 0; sg < nsg; ++sg) {
+        const float o = seg_origin(A.src.g, c0, sg);
+        float2 qx[kMvR];
 #pragma unroll
         for (int r = 0; r < kMvR; ++r) {
-          const float2 dx = __fadd2_rn(xq[r], nx);
-          const float2 e = __ffma2_rn(__fmul2_rn(dx, nc2), dx, dy2c[r]);
-          const float2 k = f2(ex2_approx(e.x), ex2_approx(e.y));
-          acc[r] = __ffma2_rn(k, W, acc[r]);
+          const float q = A.sc * (xq[r].x - o);
+          qx[r] = f2(q, q);
+        }
+#pragma unroll
+        for (int pp = 0; pp < kSeg / 2; ++pp) {
+          const int p = sg * (kSeg / 2) + pp;
+          const float4 Q = sP[buf][p];
+          const float2 W = f2(Q.z, Q.w);
+          const float2 nx = f2(Q.x, Q.y);
+#pragma unroll
+          for (int r = 0; r < kMvR; ++r) {
+            const float2 dx = __fadd2_rn(qx[r], nx);
+            const float2 t = __ffma2_rn(dx, dx, dy2[r]);
+            const float2 k = f2(ex2_approx(-t.x), ex2_approx(-t.y));
+            acc[r] = __ffma2_rn(k, W, acc[r]);
+          }
         }
       }
     } else {
@@ -155,7 +190,10 @@ __device__ __forceinline__ void matvec_body(const MvArgs& A, int rb, int chunk, 
     }
 #pragma unroll
     for (int r = 0; r < kMvR; ++r) {
-      kahan_add(sum[r], comp[r], acc[r].x + acc[r].y);
+      float su = sm.ksum[r][tid], co = sm.kcomp[r][tid];
+      kahan_add(su, co, acc[r].x + acc[r].y);
+      sm.ksum[r][tid] = su;
+      sm.kcomp[r][tid] = co;
       acc[r] = f2(0.f, 0.f);
     }
     if (t + 1 < t1) {
@@ -169,7 +207,7 @@ __device__ __forceinline__ void matvec_body(const MvArgs& A, int rb, int chunk, 
   for (int r = 0; r < kMvR; ++r) {
     const int64_t i = (int64_t)rb * kRowsPerCta + r * kMvThreads + tid;
     if (i < A.n) {
-      const float total = sum[r] - comp[r];
+      const float total = sm.ksum[r][tid] - sm.kcomp[r][tid];
       if (A.chunks == 1)
         A.out[i] = A.variance * total;
       else
@@ -180,23 +218,21 @@ __device__ __forceinline__ void matvec_body(const MvArgs& A, int rb, int chunk, 
 
 template <bool GRID>
 __global__ void __launch_bounds__(kMvThreads) matvec_kernel(const __grid_constant__ MvArgs A) {
-  __shared__ __align__(16) float4 sP[2][kPairs];
-  __shared__ __align__(16) float2 sV[2][kPairs];
+  __shared__ __align__(16) MvSmem sm;
   const int rb = blockIdx.x / A.chunks;
-  matvec_body<GRID>(A, rb, blockIdx.x - rb * A.chunks, sP, sV);
+  matvec_body<GRID>(A, rb, blockIdx.x - rb * A.chunks, sm);
 }
 
 // Batched form: CTA b runs task b of its problem; every problem of one
 // launch has the same source kind (grid or explicit).
 template <bool GRID>
 __global__ void __launch_bounds__(kMvThreads) matvec_batched_kernel(const __grid_constant__ Batch<MvArgs> B) {
-  __shared__ __align__(16) float4 sP[2][kPairs];
-  __shared__ __align__(16) float2 sV[2][kPairs];
+  __shared__ __align__(16) MvSmem sm;
   const int k = batch_find(B, blockIdx.x);
   const MvArgs& A = B.p[k];
   const int local = blockIdx.x - B.start[k];
   const int rb = local / A.chunks;
-  matvec_body<GRID>(A, rb, local - rb * A.chunks, sP, sV);
+  matvec_body<GRID>(A, rb, local - rb * A.chunks, sm);
 }
 
 // Fixed-order compensated merge of the chunk partials.
@@ -366,6 +402,7 @@ lr_status make_mv_problem(const float2* x, int64_t n, const float2* ys, const lr
     a.src.n_tiles = P.n_tiles;
     a.v = v;
     a.neg_c = (float)(-1.4426950408889634 / (2.0 * (double)ell * (double)ell));
+    a.sc = (float)sqrt(1.4426950408889634 / (2.0 * (double)ell * (double)ell));
     a.variance = var;
     a.chunks = P.chunks;
     a.out = out;
@@ -453,6 +490,7 @@ extern "C" lr_status gp_kernel_matvec(const lr_points* query, const lr_points* s
   A.src = S;
   A.v = v;
   A.neg_c = (float)(-1.4426950408889634 / (2.0 * (double)lengthscale * (double)lengthscale));
+  A.sc = (float)sqrt(1.4426950408889634 / (2.0 * (double)lengthscale * (double)lengthscale));
   A.variance = variance;
   A.chunks = P.chunks;
   A.out = out;

@@ -22,6 +22,7 @@
 namespace lr {
 
 static_assert(kBwPairs == kBwThreads, "one source pair per thread when staging");
+constexpr int kBwSeg = 16;  // grid sub-segment (columns) of the tile-local coordinates
 
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
 __device__ __forceinline__ void kahan(float& s, float& c, float x) {
@@ -52,8 +53,11 @@ __device__ __forceinline__ void bw_load_pair(const BwArgs& A, int t, int p, floa
   bw_tile_range(A.src, t, j0, cnt, grow);
   const int a = 2 * p, b = 2 * p + 1;
   if (GRID) {
+    // scaled tile-local abscissae (see the forward pass)
     const int c0 = (int)(j0 - (int64_t)grow * A.src.g.W);
-    P = make_float4((a < cnt) ? -grid_x(A.src.g, c0 + a) : 0.f, (b < cnt) ? -grid_x(A.src.g, c0 + b) : 0.f, 0.f, 0.f);
+    const float o = grid_x(A.src.g, c0 + kBwSeg * (a / kBwSeg) + kBwSeg / 2);
+    P = make_float4((a < cnt) ? -A.sc * (grid_x(A.src.g, c0 + a) - o) : 0.f,
+                    (b < cnt) ? -A.sc * (grid_x(A.src.g, c0 + b) - o) : 0.f, 0.f, 0.f);
   } else {
     const float2 pa = (a < cnt) ? __ldg(A.src.xy + j0 + a) : f2(0.f, 0.f);
     const float2 pb = (b < cnt) ? __ldg(A.src.xy + j0 + b) : f2(0.f, 0.f);
@@ -67,9 +71,12 @@ struct BwSmem {
   float4 sP[2][kBwPairs];
   float2 sV[2][kBwPairs];
   float2 sG[2][kBwPairs];
+  float dvred[kBwThreads / 32][kBwTile];  // fused d_v: per-warp sums of k g per source
+  float ksum[kBwR][7][kBwThreads];         // per-thread Kahan running sums (touched once per tile)
+  float kcomp[kBwR][7][kBwThreads];
 };
 
-template <bool GRID, bool SELF>
+template <bool GRID, bool SELF, bool DV>
 __device__ __forceinline__ void bwd_rows_body(const BwArgs& A, int rb, int chunk, BwSmem& sm) {
   constexpr int K = SELF ? 7 : 4;
   float4 (*sP)[kBwPairs] = sm.sP;
@@ -80,9 +87,8 @@ __device__ __forceinline__ void bwd_rows_body(const BwArgs& A, int rb, int chunk
   const int t1 = (int)((int64_t)(chunk + 1) * nt / A.chunks);
   const int tid = threadIdx.x;
 
-  float2 xq[kBwR], yq[kBwR];
+  float2 xq[kBwR], yq[kBwR], gq[kBwR];
   float2 acc[kBwR][K];
-  float sum[kBwR][K], comp[kBwR][K];
 #pragma unroll
   for (int r = 0; r < kBwR; ++r) {
     int64_t i = (int64_t)rb * kBwRows + r * kBwThreads + tid;
@@ -90,11 +96,17 @@ __device__ __forceinline__ void bwd_rows_body(const BwArgs& A, int rb, int chunk
     const float2 p = __ldg(A.x + i);
     xq[r] = f2(p.x, p.x);
     yq[r] = f2(p.y, p.y);
+    {
+      // rows past n carry g = 0 so that they add nothing to the fused d_v
+      const int64_t i0 = (int64_t)rb * kBwRows + r * kBwThreads + tid;
+      const float gv = (DV && i0 < A.n) ? __ldg(A.grow + i0) : 0.f;
+      gq[r] = f2(gv, gv);
+    }
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       acc[r][k] = f2(0.f, 0.f);
-      sum[r][k] = 0.f;
-      comp[r][k] = 0.f;
+      sm.ksum[r][k][tid] = 0.f;
+      sm.kcomp[r][k][tid] = 0.f;
     }
   }
   const float2 nc2 = f2(A.neg_c, A.neg_c);
@@ -118,28 +130,77 @@ __device__ __forceinline__ void bwd_rows_body(const BwArgs& A, int rb, int chunk
     const int np = (cnt + 1) >> 1;
     float dyr[kBwR];
     if (GRID) {
+      // t = sc^2 d^2 = dx'^2 + dy'^2 in scaled tile-local coordinates, k = 2^-t;
+      // B accumulates k v dx' (= sc k v dx) and C accumulates k v t (= c k v d^2)
       const float yt = grid_y(A.src.g, grow);
-      float2 dy2c[kBwR];
+      const int c0 = (int)(j0 - (int64_t)grow * A.src.g.W);
+      float2 dy2[kBwR];
 #pragma unroll
       for (int r = 0; r < kBwR; ++r) {
         dyr[r] = yq[r].x - yt;
-        const float e = A.neg_c * dyr[r] * dyr[r];
-        dy2c[r] = f2(e, e);
+        const float d = A.sc * dyr[r];
+        dy2[r] = f2(d * d, d * d);
       }
-#pragma unroll 2
-      for (int p = 0; p < np; ++p) {
-        const float4 Q = sP[buf][p];
-        const float2 W = sV[buf][p];
-        const float2 nx = f2(Q.x, Q.y);
+      constexpr bool fuse_dv = DV;
+      const int nsg = (cnt + kBwSeg - 1) / kBwSeg;
+      for (int sg = 0; sg < nsg; ++sg) {
+        const float o = grid_x(A.src.g, c0 + kBwSeg * sg + kBwSeg / 2);
+        float2 qx[kBwR];
 #pragma unroll
         for (int r = 0; r < kBwR; ++r) {
-          const float2 dx = __fadd2_rn(xq[r], nx);
-          const float2 e = __ffma2_rn(__fmul2_rn(dx, nc2), dx, dy2c[r]);
-          const float2 k = f2(ex2_approx(e.x), ex2_approx(e.y));
-          const float2 kv = __fmul2_rn(k, W);
-          acc[r][0] = __fadd2_rn(acc[r][0], kv);
-          acc[r][1] = __ffma2_rn(kv, dx, acc[r][1]);
-          acc[r][3] = __ffma2_rn(kv, e, acc[r][3]);
+          const float q = A.sc * (xq[r].x - o);
+          qx[r] = f2(q, q);
+        }
+        float kgs[kBwSeg];  // fused d_v: per-thread sums of k g over its rows, per source of the sub-segment
+#pragma unroll
+        for (int pp = 0; pp < kBwSeg / 2; ++pp) {
+          const int p = sg * (kBwSeg / 2) + pp;
+          const float4 Q = sP[buf][p];
+          const float2 W = sV[buf][p];
+          const float2 nx = f2(Q.x, Q.y);
+          float2 kg = f2(0.f, 0.f);
+#pragma unroll
+          for (int r = 0; r < kBwR; ++r) {
+            const float2 dx = __fadd2_rn(qx[r], nx);
+            const float2 t = __ffma2_rn(dx, dx, dy2[r]);
+            const float2 k = f2(ex2_approx(-t.x), ex2_approx(-t.y));
+            const float2 kv = __fmul2_rn(k, W);
+            acc[r][0] = __fadd2_rn(acc[r][0], kv);
+            acc[r][1] = __ffma2_rn(kv, dx, acc[r][1]);
+            acc[r][3] = __ffma2_rn(kv, t, acc[r][3]);
+            if (fuse_dv) kg = __ffma2_rn(k, gq[r], kg);
+          }
+          kgs[2 * pp] = kg.x;
+          kgs[2 * pp + 1] = kg.y;
+        }
+        if (fuse_dv) {
+          // warp reduce-scatter of the 16 per-lane sums: after the halving
+          // stages lane L holds the warp total of source (L >> 1) & 15
+          const int lane = tid & 31;
+#pragma unroll
+          for (int h = kBwSeg / 2, m = 16; h >= 1; h >>= 1, m >>= 1) {
+            const bool upper = (lane & m) != 0;
+#pragma unroll
+            for (int i = 0; i < h; ++i) {
+              const float lo = kgs[i], hi = kgs[i + h];
+              const float send = upper ? lo : hi;
+              const float keep = upper ? hi : lo;
+              kgs[i] = keep + __shfl_xor_sync(0xffffffffu, send, m);
+            }
+          }
+          kgs[0] += __shfl_xor_sync(0xffffffffu, kgs[0], 1);
+          if ((lane & 1) == 0) sm.dvred[tid >> 5][sg * kBwSeg + ((lane >> 1) & 15)] = kgs[0];
+        }
+      }
+      if (fuse_dv) {
+        __syncthreads();
+        // combine the warps in order; row block rb owns these columns of dv_part
+        float* dst = A.dv_part + (int64_t)rb * A.src.m + j0;
+        for (int j = tid; j < cnt; j += kBwThreads) {
+          float sdv = sm.dvred[0][j];
+#pragma unroll
+          for (int w = 1; w < kBwThreads / 32; ++w) sdv += sm.dvred[w][j];
+          dst[j] = sdv;
         }
       }
     } else {
@@ -175,7 +236,10 @@ __device__ __forceinline__ void bwd_rows_body(const BwArgs& A, int rb, int chunk
       if (GRID) acc[r][2] = f2(dyr[r] * acc[r][0].x, dyr[r] * acc[r][0].y);  // uniform y on a grid row
 #pragma unroll
       for (int k = 0; k < K; ++k) {
-        kahan(sum[r][k], comp[r][k], acc[r][k].x + acc[r][k].y);
+        float su = sm.ksum[r][k][tid], co = sm.kcomp[r][k][tid];
+        kahan(su, co, acc[r][k].x + acc[r][k].y);
+        sm.ksum[r][k][tid] = su;
+        sm.kcomp[r][k][tid] = co;
         acc[r][k] = f2(0.f, 0.f);
       }
     }
@@ -192,28 +256,28 @@ __device__ __forceinline__ void bwd_rows_body(const BwArgs& A, int rb, int chunk
     const int64_t i = (int64_t)rb * kBwRows + r * kBwThreads + tid;
     if (i < A.n) {
 #pragma unroll
-      for (int k = 0; k < K; ++k) A.partial[((int64_t)chunk * K + k) * A.n + i] = sum[r][k] - comp[r][k];
+      for (int k = 0; k < K; ++k) A.partial[((int64_t)chunk * K + k) * A.n + i] = sm.ksum[r][k][tid] - sm.kcomp[r][k][tid];
     }
   }
 }
 
-template <bool GRID, bool SELF>
+template <bool GRID, bool SELF, bool DV>
 __global__ void __launch_bounds__(kBwThreads) bwd_rows_kernel(const __grid_constant__ BwArgs A) {
   __shared__ __align__(16) BwSmem sm;
   const int rb = blockIdx.x / A.chunks;
-  bwd_rows_body<GRID, SELF>(A, rb, blockIdx.x - rb * A.chunks, sm);
+  bwd_rows_body<GRID, SELF, DV>(A, rb, blockIdx.x - rb * A.chunks, sm);
 }
 
 // Batched form; every problem of one launch has the same kind (grid,
 // explicit, or explicit self-kernel).
-template <bool GRID, bool SELF>
+template <bool GRID, bool SELF, bool DV>
 __global__ void __launch_bounds__(kBwThreads) bwd_rows_batched_kernel(const __grid_constant__ Batch<BwArgs> B) {
   __shared__ __align__(16) BwSmem sm;
   const int k = batch_find(B, blockIdx.x);
   const BwArgs& A = B.p[k];
   const int local = blockIdx.x - B.start[k];
   const int rb = local / A.chunks;
-  bwd_rows_body<GRID, SELF>(A, rb, local - rb * A.chunks, sm);
+  bwd_rows_body<GRID, SELF, DV>(A, rb, local - rb * A.chunks, sm);
 }
 
 // Per-row merge of chunk partials, the per-row gradients, and per-block FP64
@@ -231,7 +295,7 @@ __device__ __forceinline__ void bwd_merge_body(const MergeArgs& M, int64_t blk) 
       s[k] -= c[k];
     }
     const float gi = M.g[i];
-    float ddx = gi * s[1], ddy = gi * s[2];
+    float ddx = gi * s[1] * M.b_scale, ddy = gi * s[2];
     if (M.K == 7) {
       const float vi = M.vrow[i];
       ddx = fmaf(vi, s[5], ddx);
@@ -312,8 +376,42 @@ __global__ void __launch_bounds__(kMergeThreads) scalar_batched_kernel(const __g
   scalar_final_body(P.part, P.nblk, P.d_len, P.d_var);
 }
 
+__device__ __forceinline__ void dv_merge_body(const DvMergeP& P, int64_t j) {
+  if (j >= P.m) return;
+  float s = 0.f, c = 0.f;
+  for (int rb = 0; rb < P.row_blocks; ++rb) kahan(s, c, P.dv_part[(int64_t)rb * P.m + j]);
+  P.d_v[j] = P.var * (s - c);
+}
+
+__global__ void dv_merge_kernel(const __grid_constant__ DvMergeP P) {
+  dv_merge_body(P, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+__global__ void dv_merge_batched_kernel(const __grid_constant__ Batch<DvMergeP> B) {
+  const int k = batch_find(B, blockIdx.x);
+  dv_merge_body(B.p[k], (int64_t)(blockIdx.x - B.start[k]) * blockDim.x + threadIdx.x);
+}
+
+lr_status launch_dv_merge_batched(const DvMergeP* p, int count, cudaStream_t s) {
+  for (int b0 = 0; b0 < count; b0 += kMaxBatch) {
+    Batch<DvMergeP> B;
+    B.count = count - b0 < kMaxBatch ? count - b0 : kMaxBatch;
+    int64_t tot = 0;
+    for (int k = 0; k < B.count; ++k) {
+      B.p[k] = p[b0 + k];
+      B.start[k] = (int32_t)tot;
+      tot += (p[b0 + k].m + 255) / 256;
+    }
+    B.start[B.count] = (int32_t)tot;
+    if (tot == 0) continue;
+    dv_merge_batched_kernel<<<(unsigned)tot, 256, 0, s>>>(B);
+    LR_CHECK_CUDA(cudaGetLastError());
+  }
+  return LR_OK;
+}
+
 lr_status launch_bwd_rows_batched(const BwArgs* p, int count, cudaStream_t s) {
-  for (int kind = 0; kind < 3; ++kind) {  // 0: grid, 1: explicit, 2: explicit self-kernel
+  for (int kind = 0; kind < 4; ++kind) {  // 0: grid, 1: explicit, 2: explicit self-kernel, 3: grid + fused d_v
     Batch<BwArgs> B;
     B.count = 0;
     int64_t tot = 0;
@@ -323,18 +421,20 @@ lr_status launch_bwd_rows_batched(const BwArgs* p, int count, cudaStream_t s) {
         B.start[B.count] = (int32_t)tot;
         if (tot > 0) {
           if (kind == 0)
-            bwd_rows_batched_kernel<true, false><<<(unsigned)tot, kBwThreads, 0, s>>>(B);
+            bwd_rows_batched_kernel<true, false, false><<<(unsigned)tot, kBwThreads, 0, s>>>(B);
           else if (kind == 1)
-            bwd_rows_batched_kernel<false, false><<<(unsigned)tot, kBwThreads, 0, s>>>(B);
+            bwd_rows_batched_kernel<false, false, false><<<(unsigned)tot, kBwThreads, 0, s>>>(B);
+          else if (kind == 2)
+            bwd_rows_batched_kernel<false, true, false><<<(unsigned)tot, kBwThreads, 0, s>>>(B);
           else
-            bwd_rows_batched_kernel<false, true><<<(unsigned)tot, kBwThreads, 0, s>>>(B);
+            bwd_rows_batched_kernel<true, false, true><<<(unsigned)tot, kBwThreads, 0, s>>>(B);
           LR_CHECK_CUDA(cudaGetLastError());
         }
         B.count = 0;
         tot = 0;
       }
       if (i == count) break;
-      const int pk = p[i].src.xy == nullptr ? 0 : (p[i].gs != nullptr ? 2 : 1);
+      const int pk = p[i].src.xy == nullptr ? (p[i].dv_part ? 3 : 0) : (p[i].gs != nullptr ? 2 : 1);
       if (pk != kind) continue;
       B.p[B.count] = p[i];
       B.start[B.count] = (int32_t)tot;
@@ -383,7 +483,7 @@ lr_status launch_scalar_batched(const ScalP* p, int count, cudaStream_t s) {
 
 struct RowPlan {
   int32_t n_tiles, segs, chunks, row_blocks, K;
-  size_t partial_bytes, scal_bytes;
+  size_t partial_bytes, scal_bytes, dv_bytes;  // dv_bytes: fused d_v partials (grid sources)
   int64_t merge_blocks;
 };
 
@@ -402,68 +502,16 @@ static lr_status plan_rows(int64_t n, int64_t m, bool grid, const lr_grid* g, bo
   LR_CHECK_CUDA(cudaGetDevice(&dev));
   LR_CHECK_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
   if (self)
-    LR_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, bwd_rows_kernel<false, true>, kBwThreads, 0));
+    LR_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, bwd_rows_kernel<false, true, false>, kBwThreads, 0));
   else
-    LR_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, bwd_rows_kernel<false, false>, kBwThreads, 0));
+    LR_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, bwd_rows_kernel<false, false, false>, kBwThreads, 0));
   const int32_t chunks = plan_chunks(p.row_blocks, p.n_tiles, occ, n_sm);
   p.chunks = chunks;
   p.partial_bytes = align256(sizeof(float) * (size_t)p.chunks * p.K * (size_t)n);
   p.merge_blocks = (n + kMergeThreads - 1) / kMergeThreads;
   p.scal_bytes = align256(sizeof(double) * 2 * (size_t)(p.merge_blocks > 0 ? p.merge_blocks : 1));
+  p.dv_bytes = grid ? align256(sizeof(float) * (size_t)p.row_blocks * (size_t)m) : 0;
   *R = p;
-  return LR_OK;
-}
-
-static lr_status launch_rows(const float2* x, int64_t n, const float2* ys, const lr_grid* yg, int64_t m,
-                             const float* v, const float* gs, const float* g, const float* vrow, float ell, float var,
-                             bool self, float2* d_x, float* d_v, double* d_len, double* d_var, char* ws,
-                             cudaStream_t s) {
-  RowPlan R;
-  lr_status st = plan_rows(n, m, ys == nullptr, yg, self, &R);
-  if (st != LR_OK) return st;
-  BwArgs A;
-  A.x = x;
-  A.n = n;
-  A.src.xy = ys;
-  A.src.g = ys ? GridDev{} : grid_dev(*yg);
-  A.src.m = m;
-  A.src.segs = R.segs;
-  A.src.n_tiles = R.n_tiles;
-  A.v = v;
-  A.gs = gs;
-  const double c = 1.4426950408889634 / (2.0 * (double)ell * (double)ell);
-  A.neg_c = (float)(-c);
-  A.chunks = R.chunks;
-  A.K = R.K;
-  A.partial = reinterpret_cast<float*>(ws);
-  const unsigned grid = (unsigned)((int64_t)R.row_blocks * R.chunks);
-  if (ys == nullptr)
-    bwd_rows_kernel<true, false><<<grid, kBwThreads, 0, s>>>(A);
-  else if (self)
-    bwd_rows_kernel<false, true><<<grid, kBwThreads, 0, s>>>(A);
-  else
-    bwd_rows_kernel<false, false><<<grid, kBwThreads, 0, s>>>(A);
-  LR_CHECK_CUDA(cudaGetLastError());
-  MergeArgs M;
-  M.partial = A.partial;
-  M.chunks = R.chunks;
-  M.K = R.K;
-  M.n = n;
-  M.g = g;
-  M.vrow = vrow;
-  M.var = var;
-  M.inv_l2 = (float)(1.0 / ((double)ell * ell));
-  // sum k v d^2 = -C / c; d_len = var/l^3 * sum g_i (sum_j k v d^2)
-  M.dl_scale = (float)(-(double)var / (c * (double)ell * ell * ell));
-  M.d_x = d_x;
-  M.d_v = d_v;
-  M.scal_part = reinterpret_cast<double*>(ws + R.partial_bytes);
-  bwd_merge_kernel<<<(unsigned)R.merge_blocks, kMergeThreads, 0, s>>>(M);
-  LR_CHECK_CUDA(cudaGetLastError());
-  if (d_len || d_var) {
-    bwd_scalar_final_kernel<<<1, kMergeThreads, 0, s>>>(M.scal_part, (int)R.merge_blocks, d_len, d_var);
-    LR_CHECK_CUDA(cudaGetLastError());
-  }
   return LR_OK;
 }
 
@@ -473,11 +521,14 @@ static lr_status launch_rows(const float2* x, int64_t n, const float2* ys, const
 // only *bytes is filled in.
 lr_status make_rows_problem(const float2* x, int64_t n, const float2* ys, const lr_grid* yg, int64_t m,
                             const float* v, const float* g, float ell, float var, float2* dx, double* d_len,
-                            double* d_var, char* ws, BwArgs* A, MergeArgs* M, ScalP* S, size_t* bytes) {
+                            double* d_var, float* d_v, char* ws, BwArgs* A, MergeArgs* M, ScalP* S, DvMergeP* D,
+                            size_t* bytes) {
   RowPlan R;
-  lr_status st = plan_rows(n, m, ys == nullptr, yg, false, &R);
+  const bool grid = ys == nullptr;
+  lr_status st = plan_rows(n, m, grid, yg, false, &R);
   if (st != LR_OK) return st;
-  *bytes = R.partial_bytes + R.scal_bytes;
+  const bool fuse = grid && d_v != nullptr;
+  *bytes = R.partial_bytes + R.scal_bytes + (fuse ? R.dv_bytes : 0);
   if (!ws) return LR_OK;
   BwArgs a{};
   a.x = x;
@@ -491,9 +542,12 @@ lr_status make_rows_problem(const float2* x, int64_t n, const float2* ys, const 
   a.gs = nullptr;
   const double c = 1.4426950408889634 / (2.0 * (double)ell * (double)ell);
   a.neg_c = (float)(-c);
+  a.sc = (float)sqrt(c);
   a.chunks = R.chunks;
   a.K = R.K;
   a.partial = reinterpret_cast<float*>(ws);
+  a.grow = fuse ? g : nullptr;
+  a.dv_part = fuse ? reinterpret_cast<float*>(ws + R.partial_bytes + R.scal_bytes) : nullptr;
   *A = a;
   MergeArgs mm{};
   mm.partial = a.partial;
@@ -504,7 +558,10 @@ lr_status make_rows_problem(const float2* x, int64_t n, const float2* ys, const 
   mm.vrow = v;
   mm.var = var;
   mm.inv_l2 = (float)(1.0 / ((double)ell * ell));
-  mm.dl_scale = (float)(-(double)var / (c * (double)ell * ell * ell));
+  // grid path: C = sum k v c d^2 (positive), B in coordinates scaled by sc;
+  // explicit path: C = sum k v e with e = -c d^2, B unscaled
+  mm.dl_scale = (float)((grid ? 1.0 : -1.0) * (double)var / (c * (double)ell * ell * ell));
+  mm.b_scale = grid ? (float)(1.0 / sqrt(c)) : 1.0f;
   mm.d_x = dx;
   mm.d_v = nullptr;
   mm.scal_part = reinterpret_cast<double*>(ws + R.partial_bytes);
@@ -513,13 +570,101 @@ lr_status make_rows_problem(const float2* x, int64_t n, const float2* ys, const 
   S->nblk = (int32_t)R.merge_blocks;
   S->d_len = d_len;
   S->d_var = d_var;
+  if (D) {
+    D->dv_part = a.dv_part;
+    D->row_blocks = R.row_blocks;
+    D->m = m;
+    D->var = var;
+    D->d_v = fuse ? d_v : nullptr;
+  }
   return LR_OK;
 }
 
-static size_t rows_ws(int64_t n, int64_t m, bool grid, const lr_grid* g, bool self, lr_status* st) {
+static lr_status launch_rows(const float2* x, int64_t n, const float2* ys, const lr_grid* yg, int64_t m,
+                             const float* v, const float* gs, const float* g, const float* vrow, float ell, float var,
+                             bool self, float2* d_x, float* d_v, double* d_len, double* d_var, char* ws,
+                             cudaStream_t s) {
+  if (!self) {
+    // grid sources fuse d_v into the row pass; explicit sources leave d_v to the caller
+    BwArgs A;
+    MergeArgs M;
+    ScalP S;
+    DvMergeP D;
+    size_t b = 0;
+    lr_status st = make_rows_problem(x, n, ys, yg, m, v, g, ell, var, d_x, d_len, d_var, ys == nullptr ? d_v : nullptr,
+                                     ws, &A, &M, &S, &D, &b);
+    if (st != LR_OK) return st;
+    const unsigned grid = (unsigned)(((n + kBwRows - 1) / kBwRows) * A.chunks);
+    if (ys == nullptr && A.dv_part)
+      bwd_rows_kernel<true, false, true><<<grid, kBwThreads, 0, s>>>(A);
+    else if (ys == nullptr)
+      bwd_rows_kernel<true, false, false><<<grid, kBwThreads, 0, s>>>(A);
+    else
+      bwd_rows_kernel<false, false, false><<<grid, kBwThreads, 0, s>>>(A);
+    LR_CHECK_CUDA(cudaGetLastError());
+    bwd_merge_kernel<<<(unsigned)S.nblk, kMergeThreads, 0, s>>>(M);
+    LR_CHECK_CUDA(cudaGetLastError());
+    if (d_len || d_var) {
+      bwd_scalar_final_kernel<<<1, kMergeThreads, 0, s>>>(S.part, S.nblk, d_len, d_var);
+      LR_CHECK_CUDA(cudaGetLastError());
+    }
+    if (A.dv_part) {
+      dv_merge_kernel<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(D);
+      LR_CHECK_CUDA(cudaGetLastError());
+    }
+    return LR_OK;
+  }
+  RowPlan R;
+  lr_status st = plan_rows(n, m, false, yg, true, &R);
+  if (st != LR_OK) return st;
+  BwArgs A{};
+  A.x = x;
+  A.n = n;
+  A.src.xy = ys;
+  A.src.m = m;
+  A.src.segs = R.segs;
+  A.src.n_tiles = R.n_tiles;
+  A.v = v;
+  A.gs = gs;
+  const double c = 1.4426950408889634 / (2.0 * (double)ell * (double)ell);
+  A.neg_c = (float)(-c);
+  A.sc = (float)sqrt(c);
+  A.chunks = R.chunks;
+  A.K = R.K;
+  A.partial = reinterpret_cast<float*>(ws);
+  A.grow = nullptr;
+  A.dv_part = nullptr;
+  const unsigned grid = (unsigned)((int64_t)R.row_blocks * R.chunks);
+  bwd_rows_kernel<false, true, false><<<grid, kBwThreads, 0, s>>>(A);
+  LR_CHECK_CUDA(cudaGetLastError());
+  MergeArgs M{};
+  M.partial = A.partial;
+  M.chunks = R.chunks;
+  M.K = R.K;
+  M.n = n;
+  M.g = g;
+  M.vrow = vrow;
+  M.var = var;
+  M.inv_l2 = (float)(1.0 / ((double)ell * ell));
+  // explicit path: C = sum k v e with e = -c d^2; d_len = var/l^3 sum g_i (sum_j k v d^2)
+  M.dl_scale = (float)(-(double)var / (c * (double)ell * ell * ell));
+  M.b_scale = 1.0f;
+  M.d_x = d_x;
+  M.d_v = d_v;
+  M.scal_part = reinterpret_cast<double*>(ws + R.partial_bytes);
+  bwd_merge_kernel<<<(unsigned)R.merge_blocks, kMergeThreads, 0, s>>>(M);
+  LR_CHECK_CUDA(cudaGetLastError());
+  if (d_len || d_var) {
+    bwd_scalar_final_kernel<<<1, kMergeThreads, 0, s>>>(M.scal_part, (int)R.merge_blocks, d_len, d_var);
+    LR_CHECK_CUDA(cudaGetLastError());
+  }
+  return LR_OK;
+}
+
+static size_t rows_ws(int64_t n, int64_t m, bool grid, const lr_grid* g, bool self, bool fuse_dv, lr_status* st) {
   RowPlan R;
   *st = plan_rows(n, m, grid, g, self, &R);
-  return R.partial_bytes + R.scal_bytes;
+  return R.partial_bytes + R.scal_bytes + (fuse_dv ? R.dv_bytes : 0);
 }
 
 struct BwPlan {
@@ -552,13 +697,15 @@ static lr_status plan_bwd(const lr_points* q, const lr_points* s, const lr_grads
   p.want_lens = (gr->d_lens || gr->d_sub);
   LR_REQUIRE(!p.want_lens || p.q_raytrace, "gp_kernel_matvec_bwd: lens gradients need a ray-traced query");
   p.need_dx = gr->d_x || p.want_lens;
+  LR_REQUIRE(gr->beta_in == nullptr || p.q_raytrace, "gp_kernel_matvec_bwd: beta_in given but the query is not ray-traced");
+  LR_REQUIRE(((uintptr_t)gr->beta_in & 7u) == 0, "gp_kernel_matvec_bwd: beta_in must be 8-byte aligned");
   size_t off = 0;
   p.off_qbeta = off;
-  if (p.q_raytrace || p.q_grid) off += align256(8 * (size_t)p.n);
+  if ((p.q_raytrace && !gr->beta_in) || p.q_grid) off += align256(8 * (size_t)p.n);
   p.off_sbeta = off;
   p.off_rows = off;
   {
-    size_t b = rows_ws(p.n, p.m, p.s_grid, p.s_grid ? &s->grid : nullptr, p.self, &st);
+    size_t b = rows_ws(p.n, p.m, p.s_grid, p.s_grid ? &s->grid : nullptr, p.self, p.s_grid && gr->d_v != nullptr, &st);
     if (st != LR_OK) return st;
     off += b;
   }
@@ -567,8 +714,7 @@ static lr_status plan_bwd(const lr_points* q, const lr_points* s, const lr_grads
   p.off_sgrid = off;
   p.off_swap = off;
   p.off_swaprows = off;
-  if (!p.self && gr->d_v) {
-    if (p.s_grid) off += align256(8 * (size_t)p.m);
+  if (!p.self && gr->d_v && !p.s_grid) {
     p.off_swap = off;
     // forward reduction with roles swapped: query = sources (explicit), source = query points (explicit)
     lr_points qs{}, ss{};
@@ -583,7 +729,7 @@ static lr_status plan_bwd(const lr_points* q, const lr_points* s, const lr_grads
   }
   p.off_swaprows = off;
   if (!p.self && gr->d_y) {
-    size_t b = rows_ws(p.m, p.n, false, nullptr, false, &st);
+    size_t b = rows_ws(p.m, p.n, false, nullptr, false, false, &st);
     if (st != LR_OK) return st;
     off += b;
   }
@@ -643,9 +789,11 @@ extern "C" lr_status gp_kernel_matvec_bwd(const lr_points* query, const lr_point
     if (G.d_sub && query->n_sub) LR_CHECK_CUDA(cudaMemsetAsync(G.d_sub, 0, 32 * (size_t)query->n_sub, s));
     return LR_OK;
   }
-  // query points (recomputed: nothing from the forward pass is stored)
+  // query points: the forward's ray-traced points when given, else recomputed
   const float2* xq = reinterpret_cast<const float2*>(query->xy);
-  if (P.q_raytrace || P.q_grid) {
+  if (P.q_raytrace && G.beta_in) {
+    xq = reinterpret_cast<const float2*>(G.beta_in);
+  } else if (P.q_raytrace || P.q_grid) {
     float2* qb = reinterpret_cast<float2*>(ws + P.off_qbeta);
     st = P.q_raytrace ? launch_raytrace(query, qb, nullptr, s) : launch_grid_points(query->grid, qb, s);
     if (st != LR_OK) return st;
@@ -657,17 +805,12 @@ extern "C" lr_status gp_kernel_matvec_bwd(const lr_points* query, const lr_point
                          : nullptr;
   // row pass: d_x (both roles for a self-kernel), self d_v, d_l, d_var
   st = launch_rows(xq, P.n, ys, yg, P.m, v, P.self ? g_out : nullptr, g_out, v, lengthscale, variance, P.self, dx,
-                   P.self ? G.d_v : nullptr, G.d_lengthscale, G.d_variance, ws + P.off_rows, s);
+                   (P.self || P.s_grid) ? G.d_v : nullptr, G.d_lengthscale, G.d_variance, ws + P.off_rows, s);
   if (st != LR_OK) return st;
-  // d_v of non-self sources: sum_i var k_ij g_i, the forward reduction with the point sets swapped
-  if (!P.self && G.d_v) {
+  // d_v of explicit non-self sources: sum_i var k_ij g_i, the forward reduction
+  // with the point sets swapped (grid sources have it fused into the row pass)
+  if (!P.self && !P.s_grid && G.d_v) {
     const float* ypts = source->xy;
-    if (P.s_grid) {
-      float2* gp = reinterpret_cast<float2*>(ws + P.off_sgrid);
-      st = launch_grid_points(source->grid, gp, s);
-      if (st != LR_OK) return st;
-      ypts = reinterpret_cast<const float*>(gp);
-    }
     lr_points qs{}, ss{};
     qs.xy = ypts;
     qs.n = P.m;

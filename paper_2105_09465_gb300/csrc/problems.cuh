@@ -29,6 +29,7 @@ struct MvArgs {
   SrcDesc src;
   const float* v;    // [m]
   float neg_c;       // -log2(e) / (2 l^2)
+  float sc;          // sqrt(log2(e) / (2 l^2)): scale of the tile-local grid coordinates
   float variance;
   int32_t chunks;    // column chunks per row block
   float* out;        // [n] when chunks == 1
@@ -66,9 +67,22 @@ struct BwArgs {
   const float* v;   // [m] source weights
   const float* gs;  // [m] source-side g (self-kernel only: g of the same points)
   float neg_c;      // -log2(e)/(2 l^2)
+  float sc;         // sqrt(log2(e)/(2 l^2)): scale of the tile-local grid coordinates
   int32_t chunks;
   int32_t K;        // quantities per row: 4, or 7 for a self-kernel
   float* partial;   // [chunks][K][n]
+  // grid sources only: fused column reduction for dL/dv
+  const float* grow;  // [n] g of the query rows, or NULL (no fused d_v)
+  float* dv_part;     // [row blocks][m] per-row-block sums of k_ij g_i
+};
+
+// Fixed-order merge of the fused d_v partials: d_v_j = var sum_rb dv_part[rb][j].
+struct DvMergeP {
+  const float* dv_part;
+  int32_t row_blocks;
+  int64_t m;
+  float var;
+  float* d_v;
 };
 
 struct MergeArgs {
@@ -77,7 +91,8 @@ struct MergeArgs {
   int64_t n;
   const float* g;      // [n] dL/dout
   const float* vrow;   // [n] v of the query points (self-kernel column role)
-  float var, inv_l2, dl_scale;  // dl_scale = -var / (neg_c_abs...) see host
+  float var, inv_l2, dl_scale;  // d_x scale var/l^2 and d_len scale (sign per accumulation form)
+  float b_scale;                // 1, or 1/sc when B was accumulated in scaled grid coordinates
   float2* d_x;         // [n] or NULL
   float* d_v;          // [n] (self-kernel) or NULL
   double* scal_part;   // [blocks][2]: d_len, d_var partials
@@ -140,6 +155,7 @@ lr_status launch_raytrace_batched(const RtP* p, int count, cudaStream_t s);
 lr_status launch_bwd_rows_batched(const BwArgs* p, int count, cudaStream_t s);
 lr_status launch_bwd_merge_batched(const MergeArgs* p, int count, cudaStream_t s);
 lr_status launch_scalar_batched(const ScalP* p, int count, cudaStream_t s);
+lr_status launch_dv_merge_batched(const DvMergeP* p, int count, cudaStream_t s);
 lr_status launch_vjp_batched(const VjpP* p, int count, cudaStream_t s);
 lr_status launch_vjp_final_batched(const VjpFinalP* p, int count, cudaStream_t s);
 
@@ -149,7 +165,8 @@ lr_status make_mv_problem(const float2* x, int64_t n, const float2* ys, const lr
                           size_t* partial_bytes);
 lr_status make_rows_problem(const float2* x, int64_t n, const float2* ys, const lr_grid* yg, int64_t m,
                             const float* v, const float* g, float ell, float var, float2* dx, double* d_len,
-                            double* d_var, char* ws, BwArgs* A, MergeArgs* M, ScalP* S, size_t* bytes);
+                            double* d_var, float* d_v, char* ws, BwArgs* A, MergeArgs* M, ScalP* S, DvMergeP* D,
+                            size_t* bytes);
 lr_status make_rt_problem(const lr_points* p, float2* beta, float2* alpha, RtP* R);
 lr_status make_vjp_problem(const lr_points* p, const float2* dbeta, double* d_lens, double* d_sub, void* ws, VjpP* V,
                            VjpFinalP* F);

@@ -12,7 +12,7 @@
 // requests while slots (max_slots) and the device-memory budget allow, then
 // runs ONE iteration for every active request with one batched launch per
 // stage (ray-trace, reduction, merge, residual, backward rows, merge,
-// scalars, swapped reduction, merge, ray-trace VJP, final sums, update):
+// scalars, d_v merge, ray-trace VJP, final sums, update):
 // requests of different sizes share the launches and their CTAs overlap on
 // the device. A request that reaches its iteration count leaves the batch;
 // a host callback on the stream timestamps its completion. Every request is
@@ -74,16 +74,16 @@ struct Req {
   int64_t n = 0, m = 0;
   // device memory (one allocation) and the offsets of its parts
   size_t bytes = 0;
-  size_t o_beta, o_out, o_data, o_g, o_dx, o_v, o_dv, o_ypts, o_sub, o_dlens, o_dsub, o_scal, o_fwd, o_rows, o_swp,
-      o_vjp;
+  size_t o_beta, o_out, o_data, o_g, o_dx, o_v, o_dv, o_sub, o_dlens, o_dsub, o_scal, o_fwd, o_rows, o_vjp;
   char* dmem = nullptr;
   // problem descriptors of the batched stages
   RtP rt;
-  MvArgs fwd, swp;
-  MergeP fwd_m, swp_m;
+  MvArgs fwd;
+  MergeP fwd_m;
   BwArgs rows;
   MergeArgs rows_m;
   ScalP scal;
+  DvMergeP dvm;
   VjpP vjp;
   VjpFinalP vfin;
   AxpyP resid, upd;
@@ -135,15 +135,14 @@ size_t carve(size_t& off, size_t bytes) {
 // Sizes the request's device state (same plans as the single-problem calls).
 lr_status size_request(Req* r) {
   const int64_t n = r->n, m = r->m;
-  size_t fwd_b = 0, rows_b = 0, swp_b = 0;
+  size_t fwd_b = 0, rows_b = 0;
   lr_status st = make_mv_problem(nullptr, n, nullptr, &r->ygrid, m, nullptr, r->ell, r->var, nullptr, nullptr,
                                  nullptr, nullptr, &fwd_b);
   if (st != LR_OK) return st;
+  // d_v fused into the row pass (grid sources)
   st = make_rows_problem(nullptr, n, nullptr, &r->ygrid, m, nullptr, nullptr, r->ell, r->var, nullptr, nullptr,
-                         nullptr, nullptr, nullptr, nullptr, nullptr, &rows_b);
-  if (st != LR_OK) return st;
-  st = make_mv_problem(nullptr, m, reinterpret_cast<const float2*>(uintptr_t(256)), nullptr, n, nullptr, r->ell,
-                       r->var, nullptr, nullptr, nullptr, nullptr, &swp_b);
+                         nullptr, reinterpret_cast<float*>(uintptr_t(256)), nullptr, nullptr, nullptr, nullptr,
+                         nullptr, &rows_b);
   if (st != LR_OK) return st;
   size_t off = 0;
   r->o_beta = carve(off, 8 * n);
@@ -153,14 +152,12 @@ lr_status size_request(Req* r) {
   r->o_dx = carve(off, 8 * n);
   r->o_v = carve(off, 4 * m);
   r->o_dv = carve(off, 4 * m);
-  r->o_ypts = carve(off, 8 * m);
   r->o_sub = carve(off, 20 * (size_t)r->n_sub);
   r->o_dlens = carve(off, 7 * 8);
   r->o_dsub = carve(off, 32 * (size_t)r->n_sub);
   r->o_scal = carve(off, 16);
   r->o_fwd = carve(off, fwd_b);
   r->o_rows = carve(off, rows_b);
-  r->o_swp = carve(off, swp_b);
   r->o_vjp = carve(off, raytrace_vjp_ws(n, r->n_sub));
   r->bytes = off;
   return LR_OK;
@@ -179,7 +176,6 @@ lr_status init_request(lr_session* S, Req* r) {
   float2* dx = reinterpret_cast<float2*>(d + r->o_dx);
   float* v = reinterpret_cast<float*>(d + r->o_v);
   float* dv = reinterpret_cast<float*>(d + r->o_dv);
-  float2* ypts = reinterpret_cast<float2*>(d + r->o_ypts);
   float* sub = r->n_sub ? reinterpret_cast<float*>(d + r->o_sub) : nullptr;
   double* dlens = reinterpret_cast<double*>(d + r->o_dlens);
   double* dsub = reinterpret_cast<double*>(d + r->o_dsub);
@@ -188,8 +184,7 @@ lr_status init_request(lr_session* S, Req* r) {
   LR_CHECK_CUDA(cudaMemcpyAsync(data, r->data.data(), 4 * r->n, cudaMemcpyHostToDevice, S->stream));
   if (r->n_sub)
     LR_CHECK_CUDA(cudaMemcpyAsync(sub, r->sub.data(), 20 * (size_t)r->n_sub, cudaMemcpyHostToDevice, S->stream));
-  lr_status st = launch_grid_points(r->ygrid, ypts, S->stream);
-  if (st != LR_OK) return st;
+  lr_status st;
   lr_points P{};
   P.xy = nullptr;
   P.grid = r->grid;
@@ -204,11 +199,8 @@ lr_status init_request(lr_session* S, Req* r) {
                             reinterpret_cast<float*>(d + r->o_fwd), &r->fwd, &r->fwd_m, &b)) != LR_OK)
     return st;
   r->resid = AxpyP{out, data, g, r->n, 1.0f};
-  if ((st = make_rows_problem(beta, r->n, nullptr, &r->ygrid, r->m, v, g, r->ell, r->var, dx, scal, scal + 1,
-                              d + r->o_rows, &r->rows, &r->rows_m, &r->scal, &b)) != LR_OK)
-    return st;
-  if ((st = make_mv_problem(ypts, r->m, beta, nullptr, r->n, g, r->ell, r->var, dv,
-                            reinterpret_cast<float*>(d + r->o_swp), &r->swp, &r->swp_m, &b)) != LR_OK)
+  if ((st = make_rows_problem(beta, r->n, nullptr, &r->ygrid, r->m, v, g, r->ell, r->var, dx, scal, scal + 1, dv,
+                              d + r->o_rows, &r->rows, &r->rows_m, &r->scal, &r->dvm, &b)) != LR_OK)
     return st;
   if ((st = make_vjp_problem(&P, dx, dlens, dsub, d + r->o_vjp, &r->vjp, &r->vfin)) != LR_OK) return st;
   r->upd = AxpyP{v, dv, v, r->m, r->step};
@@ -218,8 +210,9 @@ lr_status init_request(lr_session* S, Req* r) {
 // One batched iteration over `act`.
 lr_status run_iteration(lr_session* S, const std::vector<Req*>& act) {
   std::vector<RtP> rt;
-  std::vector<MvArgs> fwd, swp;
-  std::vector<MergeP> fwd_m, swp_m;
+  std::vector<MvArgs> fwd;
+  std::vector<MergeP> fwd_m;
+  std::vector<DvMergeP> dvm;
   std::vector<AxpyP> resid, upd;
   std::vector<BwArgs> rows;
   std::vector<MergeArgs> rows_m;
@@ -234,8 +227,7 @@ lr_status run_iteration(lr_session* S, const std::vector<Req*>& act) {
     rows.push_back(r->rows);
     rows_m.push_back(r->rows_m);
     scal.push_back(r->scal);
-    swp.push_back(r->swp);
-    if (r->swp.chunks > 1) swp_m.push_back(r->swp_m);
+    dvm.push_back(r->dvm);
     vjp.push_back(r->vjp);
     vfin.push_back(r->vfin);
     upd.push_back(r->upd);
@@ -250,13 +242,12 @@ lr_status run_iteration(lr_session* S, const std::vector<Req*>& act) {
   if ((st = launch_bwd_rows_batched(rows.data(), n, s)) != LR_OK) return st;
   if ((st = launch_bwd_merge_batched(rows_m.data(), n, s)) != LR_OK) return st;
   if ((st = launch_scalar_batched(scal.data(), n, s)) != LR_OK) return st;
-  if ((st = launch_matvec_batched(swp.data(), n, s)) != LR_OK) return st;
-  if ((st = launch_merge_batched(swp_m.data(), (int)swp_m.size(), s)) != LR_OK) return st;
+  if ((st = launch_dv_merge_batched(dvm.data(), n, s)) != LR_OK) return st;
   if ((st = launch_vjp_batched(vjp.data(), n, s)) != LR_OK) return st;
   if ((st = launch_vjp_final_batched(vfin.data(), n, s)) != LR_OK) return st;
   if ((st = launch_axpy_batched(upd.data(), n, s)) != LR_OK) return st;
   const int groups = (n + kMaxBatch - 1) / kMaxBatch;
-  S->launches += (uint64_t)groups * (10 + (fwd_m.empty() ? 0 : 1) + (swp_m.empty() ? 0 : 1));
+  S->launches += (uint64_t)groups * (10 + (fwd_m.empty() ? 0 : 1));
   return LR_OK;
 }
 
