@@ -67,18 +67,30 @@ __device__ __forceinline__ void bw_load_pair(const BwArgs& A, int t, int p, floa
   if (SELF) Gp = f2((a < cnt) ? __ldg(A.gs + j0 + a) : 0.f, (b < cnt) ? __ldg(A.gs + j0 + b) : 0.f);
 }
 
+template <int R, int K>
 struct BwSmem {
   float4 sP[2][kBwPairs];
   float2 sV[2][kBwPairs];
   float2 sG[2][kBwPairs];
   float dvred[kBwThreads / 32][kBwTile];  // fused d_v: per-warp sums of k g per source
-  float ksum[kBwR][7][kBwThreads];         // per-thread Kahan running sums (touched once per tile)
-  float kcomp[kBwR][7][kBwThreads];
+  float ksum[R][K][kBwThreads];            // per-thread Kahan running sums (touched once per tile)
+  float kcomp[R][K][kBwThreads];
 };
 
 template <bool GRID, bool SELF, bool DV>
-__device__ __forceinline__ void bwd_rows_body(const BwArgs& A, int rb, int chunk, BwSmem& sm) {
-  constexpr int K = SELF ? 7 : 4;
+struct BwCfg {
+  static constexpr int R = DV ? kBwRdv : kBwR;
+  static constexpr int K = SELF ? 7 : 4;
+  static constexpr int ROWS = kBwThreads * R;
+  using Smem = BwSmem<R, K>;
+};
+
+template <bool GRID, bool SELF, bool DV>
+__device__ __forceinline__ void bwd_rows_body(const BwArgs& A, int rb, int chunk,
+                                              typename BwCfg<GRID, SELF, DV>::Smem& sm) {
+  constexpr int kBwR = BwCfg<GRID, SELF, DV>::R;
+  constexpr int kBwRows = BwCfg<GRID, SELF, DV>::ROWS;
+  constexpr int K = BwCfg<GRID, SELF, DV>::K;
   float4 (*sP)[kBwPairs] = sm.sP;
   float2 (*sV)[kBwPairs] = sm.sV;
   float2 (*sG)[kBwPairs] = sm.sG;
@@ -263,7 +275,7 @@ __device__ __forceinline__ void bwd_rows_body(const BwArgs& A, int rb, int chunk
 
 template <bool GRID, bool SELF, bool DV>
 __global__ void __launch_bounds__(kBwThreads) bwd_rows_kernel(const __grid_constant__ BwArgs A) {
-  __shared__ __align__(16) BwSmem sm;
+  __shared__ __align__(16) typename BwCfg<GRID, SELF, DV>::Smem sm;
   const int rb = blockIdx.x / A.chunks;
   bwd_rows_body<GRID, SELF, DV>(A, rb, blockIdx.x - rb * A.chunks, sm);
 }
@@ -272,7 +284,7 @@ __global__ void __launch_bounds__(kBwThreads) bwd_rows_kernel(const __grid_const
 // explicit, or explicit self-kernel).
 template <bool GRID, bool SELF, bool DV>
 __global__ void __launch_bounds__(kBwThreads) bwd_rows_batched_kernel(const __grid_constant__ Batch<BwArgs> B) {
-  __shared__ __align__(16) BwSmem sm;
+  __shared__ __align__(16) typename BwCfg<GRID, SELF, DV>::Smem sm;
   const int k = batch_find(B, blockIdx.x);
   const BwArgs& A = B.p[k];
   const int local = blockIdx.x - B.start[k];
@@ -438,7 +450,7 @@ lr_status launch_bwd_rows_batched(const BwArgs* p, int count, cudaStream_t s) {
       if (pk != kind) continue;
       B.p[B.count] = p[i];
       B.start[B.count] = (int32_t)tot;
-      tot += (int64_t)((p[i].n + kBwRows - 1) / kBwRows) * p[i].chunks;
+      tot += (int64_t)((p[i].n + p[i].rows_per_cta - 1) / p[i].rows_per_cta) * p[i].chunks;
       ++B.count;
     }
   }
@@ -482,14 +494,16 @@ lr_status launch_scalar_batched(const ScalP* p, int count, cudaStream_t s) {
 // Host side
 
 struct RowPlan {
-  int32_t n_tiles, segs, chunks, row_blocks, K;
+  int32_t n_tiles, segs, chunks, row_blocks, K, rows_per_cta;
   size_t partial_bytes, scal_bytes, dv_bytes;  // dv_bytes: fused d_v partials (grid sources)
   int64_t merge_blocks;
 };
 
-static lr_status plan_rows(int64_t n, int64_t m, bool grid, const lr_grid* g, bool self, RowPlan* R) {
+static lr_status plan_rows(int64_t n, int64_t m, bool grid, const lr_grid* g, bool self, bool fuse_dv, RowPlan* R) {
   RowPlan p{};
   p.K = self ? 7 : 4;
+  const bool dv = grid && fuse_dv;
+  p.rows_per_cta = dv ? BwCfg<true, false, true>::ROWS : kBwRows;
   if (grid) {
     const int W = g->nx * g->ss;
     p.segs = (W + kBwTile - 1) / kBwTile;
@@ -497,12 +511,14 @@ static lr_status plan_rows(int64_t n, int64_t m, bool grid, const lr_grid* g, bo
   } else {
     p.n_tiles = (int32_t)((m + kBwTile - 1) / kBwTile);
   }
-  p.row_blocks = (int32_t)((n + kBwRows - 1) / kBwRows);
+  p.row_blocks = (int32_t)((n + p.rows_per_cta - 1) / p.rows_per_cta);
   int dev = 0, n_sm = 1, occ = 1;
   LR_CHECK_CUDA(cudaGetDevice(&dev));
   LR_CHECK_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
   if (self)
     LR_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, bwd_rows_kernel<false, true, false>, kBwThreads, 0));
+  else if (dv)
+    LR_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, bwd_rows_kernel<true, false, true>, kBwThreads, 0));
   else
     LR_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, bwd_rows_kernel<false, false, false>, kBwThreads, 0));
   const int32_t chunks = plan_chunks(p.row_blocks, p.n_tiles, occ, n_sm);
@@ -525,9 +541,9 @@ lr_status make_rows_problem(const float2* x, int64_t n, const float2* ys, const 
                             size_t* bytes) {
   RowPlan R;
   const bool grid = ys == nullptr;
-  lr_status st = plan_rows(n, m, grid, yg, false, &R);
-  if (st != LR_OK) return st;
   const bool fuse = grid && d_v != nullptr;
+  lr_status st = plan_rows(n, m, grid, yg, false, fuse, &R);
+  if (st != LR_OK) return st;
   *bytes = R.partial_bytes + R.scal_bytes + (fuse ? R.dv_bytes : 0);
   if (!ws) return LR_OK;
   BwArgs a{};
@@ -545,6 +561,7 @@ lr_status make_rows_problem(const float2* x, int64_t n, const float2* ys, const 
   a.sc = (float)sqrt(c);
   a.chunks = R.chunks;
   a.K = R.K;
+  a.rows_per_cta = R.rows_per_cta;
   a.partial = reinterpret_cast<float*>(ws);
   a.grow = fuse ? g : nullptr;
   a.dv_part = fuse ? reinterpret_cast<float*>(ws + R.partial_bytes + R.scal_bytes) : nullptr;
@@ -594,7 +611,7 @@ static lr_status launch_rows(const float2* x, int64_t n, const float2* ys, const
     lr_status st = make_rows_problem(x, n, ys, yg, m, v, g, ell, var, d_x, d_len, d_var, ys == nullptr ? d_v : nullptr,
                                      ws, &A, &M, &S, &D, &b);
     if (st != LR_OK) return st;
-    const unsigned grid = (unsigned)(((n + kBwRows - 1) / kBwRows) * A.chunks);
+    const unsigned grid = (unsigned)(((n + A.rows_per_cta - 1) / A.rows_per_cta) * A.chunks);
     if (ys == nullptr && A.dv_part)
       bwd_rows_kernel<true, false, true><<<grid, kBwThreads, 0, s>>>(A);
     else if (ys == nullptr)
@@ -615,7 +632,7 @@ static lr_status launch_rows(const float2* x, int64_t n, const float2* ys, const
     return LR_OK;
   }
   RowPlan R;
-  lr_status st = plan_rows(n, m, false, yg, true, &R);
+  lr_status st = plan_rows(n, m, false, yg, true, false, &R);
   if (st != LR_OK) return st;
   BwArgs A{};
   A.x = x;
@@ -631,6 +648,7 @@ static lr_status launch_rows(const float2* x, int64_t n, const float2* ys, const
   A.sc = (float)sqrt(c);
   A.chunks = R.chunks;
   A.K = R.K;
+  A.rows_per_cta = R.rows_per_cta;
   A.partial = reinterpret_cast<float*>(ws);
   A.grow = nullptr;
   A.dv_part = nullptr;
@@ -663,7 +681,7 @@ static lr_status launch_rows(const float2* x, int64_t n, const float2* ys, const
 
 static size_t rows_ws(int64_t n, int64_t m, bool grid, const lr_grid* g, bool self, bool fuse_dv, lr_status* st) {
   RowPlan R;
-  *st = plan_rows(n, m, grid, g, self, &R);
+  *st = plan_rows(n, m, grid, g, self, fuse_dv, &R);
   return R.partial_bytes + R.scal_bytes + (fuse_dv ? R.dv_bytes : 0);
 }
 

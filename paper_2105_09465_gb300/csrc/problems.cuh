@@ -47,8 +47,9 @@ struct MergeP {
 
 // ---- backward row pass (matvec_bwd.cu)
 constexpr int kBwThreads = 128;
-constexpr int kBwR = 4;
+constexpr int kBwR = 4;                     // rows per thread
 constexpr int kBwRows = kBwThreads * kBwR;  // 512 rows per CTA
+constexpr int kBwRdv = 8;                   // rows per thread with the fused d_v reduction
 constexpr int kBwTile = 256;
 constexpr int kBwPairs = kBwTile / 2;
 constexpr int kMergeThreads = 256;
@@ -70,6 +71,7 @@ struct BwArgs {
   float sc;         // sqrt(log2(e)/(2 l^2)): scale of the tile-local grid coordinates
   int32_t chunks;
   int32_t K;        // quantities per row: 4, or 7 for a self-kernel
+  int32_t rows_per_cta;  // kBwThreads x (kBwR, or kBwRdv with the fused d_v)
   float* partial;   // [chunks][K][n]
   // grid sources only: fused column reduction for dL/dv
   const float* grow;  // [n] g of the query rows, or NULL (no fused d_v)
