@@ -147,6 +147,16 @@ typedef struct {
  */
 lr_status lens_raytrace(const lr_points* pts, float* beta_out, float* alpha_out, lr_stream stream);
 
+/*
+ * Lens Jacobian and magnification (Sec. 2.1, lens-Jacobian and magnification
+ * equations): for every point of `pts` (which must carry a lens),
+ *   jac_out[i] = d beta / d xi = I - d alpha / d xi, row-major float[4]
+ *                (A_xx, A_xy, A_yx, A_yy), A_xy = d beta_x / d y,
+ *   mu_out[i]  = 1 / det(jac) (signed; infinite on critical curves).
+ * Either output may be NULL. jac_out must be 16-byte aligned.
+ */
+lr_status lens_jacobian(const lr_points* pts, float* jac_out, float* mu_out, lr_stream stream);
+
 /* ------------------------------------------------------------------------ */
 /* Gaussian-kernel reduction (Sec. 3.1 RBF kernel; Sec. 3.4 lazy T y)         */
 

@@ -75,6 +75,7 @@ def lib():
         L.orc_sple_kappa.restype = _D
         L.orc_raytrace.argtypes = [_P, _I64, ctypes.POINTER(OrcLens), _P, _I32, _I32, _P, _P]
         L.orc_raytrace_vjp.argtypes = [_P, _I64, ctypes.POINTER(OrcLens), _P, _I32, _I32, _P, _P, _P, _P, _P]
+        L.orc_lens_jacobian.argtypes = [_P, _I64, ctypes.POINTER(OrcLens), _P, _I32, _I32, _P, _P]
         L.orc_kernel_matvec.argtypes = [_P, _I64, _P, _I64, _P, _D, _D, _P, _I64, _P, _P, _P]
         L.orc_kernel_matvec_vjp.argtypes = [_P, _I64, _P, _I64, _P, _D, _D, _P, _I32, _P, _P, _P, _P, _P, _P]
         L.orc_num_threads.restype = _I32
@@ -152,6 +153,17 @@ def raytrace_vjp(xi, lens, sub, d_beta, profile=0, with_abs=False):
     lib().orc_raytrace_vjp(_ptr(xi), xi.shape[0], ctypes.byref(L), _ptr(s), ns, profile, _ptr(db), _ptr(d_lens),
                            _ptr(d_sub) if ns else None, _ptr(a_lens), _ptr(a_sub) if ns else None)
     return (d_lens, d_sub, a_lens, a_sub) if with_abs else (d_lens, d_sub)
+
+
+def lens_jacobian(xi, lens, sub=None, profile=0):
+    """(jac (n, 2, 2) = d beta / d xi, mu (n,) = 1/det) from the paper's lens-Jacobian definition."""
+    xi = _pairs(xi)
+    s, ns = _subs(sub)
+    L = _lens(lens)
+    jac = np.empty((xi.shape[0], 4), np.float64)
+    mu = np.empty(xi.shape[0], np.float64)
+    lib().orc_lens_jacobian(_ptr(xi), xi.shape[0], ctypes.byref(L), _ptr(s), ns, profile, _ptr(jac), _ptr(mu))
+    return jac.reshape(-1, 2, 2), mu
 
 
 def kernel_matvec(x, y, v, lengthscale, variance=1.0, rows=None, with_sens=False):

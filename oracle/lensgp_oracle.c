@@ -122,7 +122,11 @@ static inline dn dn_sqrt(dn a) {
   return dn_chain(a, s, 0.5 / s);
 }
 static inline dn dn_log(dn a) { return dn_chain(a, log(a.v), 1.0 / a.v); }
-static inline dn dn_powc(dn a, double e) { return dn_chain(a, pow(a.v, e), e * pow(a.v, e - 1.0)); }
+static inline dn dn_powc(dn a, double e) {
+  /* a^0 is the constant 1 (also at a = 0, where e a^(e-1) would be 0 * inf) */
+  if (e == 0.0) return dn_const(1.0);
+  return dn_chain(a, pow(a.v, e), e * pow(a.v, e - 1.0));
+}
 static inline dn dn_cos(dn a) { return dn_chain(a, cos(a.v), -sin(a.v)); }
 static inline dn dn_sin(dn a) { return dn_chain(a, sin(a.v), cos(a.v)); }
 static inline dn dn_acosh(dn a) { return dn_chain(a, acosh(a.v), 1.0 / sqrt(a.v * a.v - 1.0)); }
@@ -396,6 +400,53 @@ ORC_API void orc_raytrace_vjp(const double* xi, int64_t n, const orc_lens* L, co
       d_sub[4 * (int64_t)h + k] = ns_val(&a4[k]);
       if (d_sub_abs) d_sub_abs[4 * (int64_t)h + k] = ns_val(&b4[k]);
     }
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Lens Jacobian and magnification (Sec. 2.1, lens-Jacobian and magnification
+ * equations): A = d beta / d xi = I - d alpha / d xi, mu = 1 / det A.
+ * d alpha / d xi comes from forward-mode dual numbers in (x, y) through the
+ * same deflection expressions as orc_raytrace (slots 0 and 1).
+ * jac: [n][4] = (A_xx, A_xy, A_yx, A_yy) with A_xy = d beta_x / d y. */
+ORC_API void orc_lens_jacobian(const double* xi, int64_t n, const orc_lens* L, const double* sub, int32_t n_sub,
+                               int32_t profile, double* jac /*[n][4]*/, double* mu /*[n] or NULL*/) {
+#pragma omp parallel for schedule(dynamic, 256)
+  for (int64_t i = 0; i < n; ++i) {
+    const double x = xi[2 * i], y = xi[2 * i + 1];
+    dn X = dn_var(x, 0), Y = dn_var(y, 1);
+    nsum a[4];
+    memset(a, 0, sizeof a);
+    dn ax, ay;
+    sple_dual(X, Y, dn_const(L->x0), dn_const(L->y0), dn_const(L->q), dn_const(L->phi), dn_const(L->theta_e),
+              L->gamma, &ax, &ay);
+    ns_add(&a[0], ax.d[0]);
+    ns_add(&a[1], ax.d[1]);
+    ns_add(&a[2], ay.d[0]);
+    ns_add(&a[3], ay.d[1]);
+    /* shear: d alpha / d xi = [[g1, g2], [g2, -g1]] */
+    ns_add(&a[0], L->g1);
+    ns_add(&a[1], L->g2);
+    ns_add(&a[2], L->g2);
+    ns_add(&a[3], -L->g1);
+    for (int32_t h = 0; h < n_sub; ++h) {
+      const double* rec = sub + 5 * (int64_t)h;
+      dn hx, hy;
+      if (profile == 1)
+        pointmass_dual(X, Y, dn_const(rec[0]), dn_const(rec[1]), dn_const(rec[2]), &hx, &hy);
+      else
+        tnfw_dual(X, Y, dn_const(rec[0]), dn_const(rec[1]), dn_const(rec[2]), dn_const(rec[3]), rec[4], &hx, &hy);
+      ns_add(&a[0], hx.d[0]);
+      ns_add(&a[1], hx.d[1]);
+      ns_add(&a[2], hy.d[0]);
+      ns_add(&a[3], hy.d[1]);
+    }
+    const double j00 = 1.0 - ns_val(&a[0]), j01 = -ns_val(&a[1]), j10 = -ns_val(&a[2]), j11 = 1.0 - ns_val(&a[3]);
+    jac[4 * i] = j00;
+    jac[4 * i + 1] = j01;
+    jac[4 * i + 2] = j10;
+    jac[4 * i + 3] = j11;
+    if (mu) mu[i] = 1.0 / (j00 * j11 - j01 * j10);
   }
 }
 

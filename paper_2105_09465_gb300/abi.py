@@ -85,6 +85,7 @@ SIGNATURES = {
     "lr_probe_pipe_rates": (ctypes.c_int32, [ctypes.c_int32, _P, _P, _P, _P]),
     "lr_fault_status": (ctypes.c_int32, [_P, ctypes.c_int32]),
     "lens_raytrace": (ctypes.c_int32, [ctypes.POINTER(lr_points), _P, _P, _P]),
+    "lens_jacobian": (ctypes.c_int32, [ctypes.POINTER(lr_points), _P, _P, _P]),
     "gp_kernel_matvec": (ctypes.c_int32, [ctypes.POINTER(lr_points), ctypes.POINTER(lr_points), _P, ctypes.c_int32,
                                           ctypes.c_float, ctypes.c_float, _P, _P, _P, ctypes.c_size_t, _P]),
     "lr_matvec_workspace_size": (ctypes.c_int32, [ctypes.POINTER(lr_points), ctypes.POINTER(lr_points),

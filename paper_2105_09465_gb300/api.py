@@ -83,6 +83,18 @@ def lens_raytrace(pts: Points, want_alpha: bool = False, stream=None):
     return (beta, alpha) if want_alpha else beta
 
 
+def lens_jacobian(pts: Points, stream=None):
+    """(jac (n, 2, 2) = d beta / d xi, mu (n,) magnification) for every point (pts.lens required)."""
+    lib = abi.load()
+    c, keep = to_c_points(pts)
+    dev = pts.xy.device if pts.xy is not None else torch.device("cuda", torch.cuda.current_device())
+    jac = torch.empty((c.n, 4), dtype=torch.float32, device=dev)
+    mu = torch.empty(c.n, dtype=torch.float32, device=dev)
+    abi.check(lib.lens_jacobian(ctypes.byref(c), jac.data_ptr(), mu.data_ptr(), _stream_handle(stream)),
+              "lens_jacobian")
+    return jac.view(-1, 2, 2), mu
+
+
 def matvec_workspace_size(query: Points, source: Points | None) -> int:
     lib = abi.load()
     cq, k1 = to_c_points(query)

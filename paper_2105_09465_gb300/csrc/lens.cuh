@@ -323,4 +323,38 @@ __device__ __forceinline__ void sple_vjp(const LensConst& L, const LensGradConst
   out[4] = -G.dlnte * cdot(gr, ap);
 }
 
+// SPLE deflection Jacobian d alpha / d xi at (x, y), row-major
+// (J[0] = d ax/dx, J[1] = d ax/dy, J[2] = d ay/dx, J[3] = d ay/dy), from the
+// Wirtinger derivatives used by sple_vjp: d alpha = e^{i phi} (A_w t + A_wb conj(t)).
+__device__ __forceinline__ void sple_jacobian(const LensConst& L, const LensGradConst& G, float x, float y,
+                                              float J[4]) {
+  const float dx = x - L.x0, dy = y - L.y0;
+  const float u = fmaf(L.c, dx, L.s * dy);
+  const float v = fmaf(L.c, dy, -L.s * dx);
+  const float Rx = L.sq * u, Ry = L.isq * v;
+  const float R2 = fmaf(Rx, Rx, Ry * Ry);
+  if (!(R2 > 1e-24f)) {
+    J[0] = J[1] = J[2] = J[3] = 0.f;
+    return;
+  }
+  const float inv = 1.0f / R2;
+  const cf W = {(Rx * Rx - Ry * Ry) * inv, 2.0f * Rx * Ry * inv};
+  cf F = {L.d[L.nterms - 1], 0.f}, H = {G.hco[G.nterms - 1], 0.f};
+  for (int n = L.nterms - 2; n >= 0; --n) F = cadd(cmul(W, F), cf{L.d[n], 0.f});
+  for (int n = G.nterms - 2; n >= 0; --n) H = cadd(cmul(W, H), cf{G.hco[n], 0.f});
+  const float P = L.pre * pow_split(R2, L.half_expo);
+  const cf M = cscale(cmul(W, H), G.f);
+  const cf Aw = cscale(cadd(cscale(F, G.e + 1.0f), cscale(M, -1.0f)), P);
+  const cf Awb = cscale(cmul(W, cadd(cscale(F, G.e), M)), P);
+  const cf rot = {L.c, L.s};
+  const cf tx = {L.sq * L.c, -L.isq * L.s};
+  const cf ty = {L.sq * L.s, L.isq * L.c};
+  const cf jx = cmul(rot, cadd(cmul(Aw, tx), cmul(Awb, cconj(tx))));
+  const cf jy = cmul(rot, cadd(cmul(Aw, ty), cmul(Awb, cconj(ty))));
+  J[0] = jx.re;
+  J[1] = jy.re;
+  J[2] = jx.im;
+  J[3] = jy.im;
+}
+
 }  // namespace lr

@@ -19,7 +19,7 @@
 namespace lr {
 
 constexpr int kVjThreads = 256;
-constexpr int kVjPpt = 8;
+constexpr int kVjPpt = 4;  // 1024 points per CTA: ~4 CTAs per SM on the realistic workload
 constexpr int kVjPoints = kVjThreads * kVjPpt;  // points per CTA
 constexpr int kVjChunk = 128;                   // subhalos staged per chunk
 constexpr int kVjWarps = kVjThreads / 32;

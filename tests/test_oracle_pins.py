@@ -395,3 +395,45 @@ def test_printed_lenses_divergence_and_shear(orc, name):
     kap = np.array([orc.sple_kappa(p[0], p[1], L) for p in x])
     np.testing.assert_allclose(div, 2 * kap, rtol=2e-6)
     np.testing.assert_allclose(curl, 0.0, atol=2e-6 * np.max(kap))
+
+
+# ---------------------------------------------------------------- lens Jacobian / magnification
+def test_jacobian_sis_magnification_closed_form(orc):
+    """SIS: det(d beta / d xi) = 1 - theta_E / R (tangential eigenvalue; radial is 1)."""
+    x = pts(200, 3.0)
+    x = x[np.hypot(x[:, 0], x[:, 1]) > 0.05]
+    jac, mu = orc.lens_jacobian(x, lens(theta_e=1.3))
+    R = np.hypot(x[:, 0], x[:, 1])
+    np.testing.assert_allclose(1.0 / mu, 1 - 1.3 / R, rtol=1e-11, atol=1e-13)
+    # radial direction is an eigenvector with eigenvalue 1
+    n = x / R[:, None]
+    np.testing.assert_allclose(np.einsum("nij,nj->ni", jac, n), n, atol=1e-12)
+
+
+def test_jacobian_point_mass_closed_form(orc):
+    """Point mass: mu = (1 - theta^4 / R^4)^-1."""
+    x = pts(100, 1.0) + 0.02
+    sub = np.array([[0.0, 0.0, 0.4, 0.0, 0.0]])
+    _, mu = orc.lens_jacobian(x, lens(theta_e=0.0), sub, profile=1)
+    R = np.hypot(x[:, 0], x[:, 1])
+    np.testing.assert_allclose(mu, 1.0 / (1 - 0.4 ** 4 / R ** 4), rtol=1e-10)
+
+
+@pytest.mark.parametrize("name", ["hoags_object", "arp142"])
+def test_jacobian_trace_and_symmetry_and_shear(orc, name):
+    """Paper's lens-Jacobian form: A = (1 - kappa) I - [[g1, g2], [g2, -g1]]_local, i.e.
+    tr A = 2 - 2 kappa and A symmetric; with subhalos also against finite differences of beta."""
+    L = paper_lenses()[name]
+    x = pts(120, 2.5)
+    x = x[np.hypot(x[:, 0] - L["x0"], x[:, 1] - L["y0"]) > 0.2]
+    sub = np.array([[0.4, 0.3, 0.02, 0.25, 10.0], [-0.5, 0.9, 0.015, 0.4, 4.0]])
+    jac, mu = orc.lens_jacobian(x, L)
+    kap = np.array([orc.sple_kappa(p[0], p[1], L) for p in x])
+    np.testing.assert_allclose(jac[:, 0, 0] + jac[:, 1, 1], 2 - 2 * kap, rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(jac[:, 0, 1], jac[:, 1, 0], atol=1e-12)
+    jac2, _ = orc.lens_jacobian(x, L, sub)
+    h = 1e-6
+    bx = (orc.raytrace(x + [h, 0], L, sub)[1] - orc.raytrace(x - [h, 0], L, sub)[1]) / (2 * h)
+    by = (orc.raytrace(x + [0, h], L, sub)[1] - orc.raytrace(x - [0, h], L, sub)[1]) / (2 * h)
+    np.testing.assert_allclose(jac2[:, :, 0], bx, atol=1e-7)
+    np.testing.assert_allclose(jac2[:, :, 1], by, atol=1e-7)
