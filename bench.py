@@ -272,9 +272,9 @@ def event_time(fn, n, stream, flush):
 def run_ours(args):
     import torch
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    from paper_2105_09465_gb300 import replicas
+
+    rank, local, world = replicas.world()
     torch.cuda.set_device(local)
     dist = None
     if world > 1:
@@ -284,7 +284,7 @@ def run_ours(args):
     from paper_2105_09465_gb300 import api, workloads as W
 
     # each rank owns an independent lens system of the realistic recipe (weak scaling)
-    p = W.realistic(seed=1 + rank)
+    p = W.realistic(seed=replicas.rank_seed(rank))
     dev = torch.device("cuda", local)
     g_np = np.random.default_rng(100 + rank).standard_normal(p.n).astype(np.float32)
     sub = torch.from_numpy(p.sub).to(dev)
@@ -346,12 +346,8 @@ def run_ours(args):
     if dist:
         dist.barrier()
     clk = clocks.stop()
-    ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * p.pairs / (ms * 1e-3) / 1e9
+    ms = replicas.max_over_ranks(float(np.mean([a.elapsed_time(b) for a, b in ev])), dev)
+    value = replicas.aggregate_rate(p.pairs, ms * 1e-3, world) / 1e9
     nk = max(5, min(args.steps, 50))
     fwd_ms = event_time(fwd, nk, stream, flush)
     bwd_ms = event_time(bwd, nk, stream, flush)
@@ -405,12 +401,8 @@ def run_ours(args):
     for _ in range(3):
         e2e_step()
     torch.cuda.synchronize()
-    e_ms = event_time(e2e_step, max(5, min(args.steps, 100)), stream, flush)
-    if dist:
-        t = torch.tensor([e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e_ms = float(t.item())
-    e2e_val = world * p.pairs / (e_ms * 1e-3) / 1e9
+    e_ms = replicas.max_over_ranks(event_time(e2e_step, max(5, min(args.steps, 100)), stream, flush), dev)
+    e2e_val = replicas.aggregate_rate(p.pairs, e_ms * 1e-3, world) / 1e9
     h2d = (v_host.numel() + g_host.numel() + sub_host.numel()) * 4
     d2h = out_host.numel() * 4 + dv_host.numel() * 4 + (dl_host.numel() + ds_host.numel() + 2) * 8
 

@@ -181,6 +181,22 @@ lr_status gp_kernel_matvec(const lr_points* query, const lr_points* source, cons
                            float lengthscale, float variance, float* out, float* beta_out, void* workspace,
                            size_t workspace_bytes, lr_stream stream);
 
+/*
+ * Multi-layer reduction (Sec. 3.1, sum of RBF layers with fixed length
+ * scales and per-layer variances): with L = n_layers in [1, 4],
+ *   out_i = sum_l variances[l] sum_j exp(-|x_i - y_j|^2 / (2 lengthscales[l]^2)) v[l][j].
+ * The pair distance is formed once for all layers. lengthscales and
+ * variances are HOST float[L]; v is device float[L][m] (layer-major).
+ * Sources may be explicit or a grid, or NULL for a self-kernel (the paper's
+ * image-plane GP); they may not carry a lens. Other arguments as
+ * gp_kernel_matvec; workspace of lr_matvec_layers_workspace_size() bytes.
+ */
+lr_status gp_kernel_matvec_layers(const lr_points* query, const lr_points* source, int32_t n_layers,
+                                  const float* lengthscales, const float* variances, const float* v, float* out,
+                                  float* beta_out, void* workspace, size_t workspace_bytes, lr_stream stream);
+lr_status lr_matvec_layers_workspace_size(const lr_points* query, const lr_points* source, int32_t n_layers,
+                                          size_t* bytes);
+
 /* Scratch bytes gp_kernel_matvec needs for these point sets on the current device. */
 lr_status lr_matvec_workspace_size(const lr_points* query, const lr_points* source, int32_t nrhs, size_t* bytes);
 

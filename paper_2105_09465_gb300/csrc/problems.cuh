@@ -49,7 +49,7 @@ struct MergeP {
 constexpr int kBwThreads = 128;
 constexpr int kBwR = 4;                     // rows per thread
 constexpr int kBwRows = kBwThreads * kBwR;  // 512 rows per CTA
-constexpr int kBwRdv = 8;                   // rows per thread with the fused d_v reduction
+constexpr int kBwRdv = 8;                   // rows per thread with the fused d_v reduction                   // rows per thread with the fused d_v reduction                   // rows per thread with the fused d_v reduction                   // rows per thread with the fused d_v reduction                   // rows per thread with the fused d_v reduction
 constexpr int kBwTile = 256;
 constexpr int kBwPairs = kBwTile / 2;
 constexpr int kMergeThreads = 256;
