@@ -197,6 +197,34 @@ lr_status gp_kernel_matvec_layers(const lr_points* query, const lr_points* sourc
 lr_status lr_matvec_layers_workspace_size(const lr_points* query, const lr_points* source, int32_t n_layers,
                                           size_t* bytes);
 
+/* ------------------------------------------------------------------------ */
+/* Pixel windows (Sec. 3.2) and the windowed transmission (Sec. 3.5)          */
+
+/*
+ * Window covariances of a W x H grid of projected pixel centres p (device
+ * float[W*H][2], row-major over grid y, e.g. lens_raytrace of an lr_grid):
+ * a_i / b_i = half the vector between the two centres adjacent along grid
+ * x / y (the vector to the single neighbour at the border), and
+ *   z[i] = (Zxx, Zxy, Zyy) of Z_i = (a_i a_i^T + b_i b_i^T) / (4 pi)
+ * (window-kernel equation). z: device float[W*H][3].
+ */
+lr_status gp_pixel_shapes(const float* p, int32_t W, int32_t H, float* z, lr_stream stream);
+
+/*
+ * Windowed (non-stationary) transmission reduction (transmission equation
+ * with Sigma = l^2 I):
+ *   out_i = sum_k G(p_i - q_k, Z_i + (l^2/2) I) v_k,
+ *   G(d, C) = exp(-d^T C^-1 d / 2) / (2 pi sqrt(det C)),
+ * for n query points p (device float[n][2]) with window covariances z
+ * (device float[n][3], from gp_pixel_shapes; zeros give point pixels) and
+ * sources q (explicit or grid, no lens). The caller folds the transmission
+ * weights A_k into v_k. Workspace of lr_windowed_workspace_size() bytes.
+ */
+lr_status gp_windowed_matvec(const float* p, const float* z, int64_t n, const lr_points* source, const float* v,
+                             float lengthscale, float* out, void* workspace, size_t workspace_bytes,
+                             lr_stream stream);
+lr_status lr_windowed_workspace_size(int64_t n, const lr_points* source, size_t* bytes);
+
 /* Scratch bytes gp_kernel_matvec needs for these point sets on the current device. */
 lr_status lr_matvec_workspace_size(const lr_points* query, const lr_points* source, int32_t nrhs, size_t* bytes);
 

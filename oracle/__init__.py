@@ -76,6 +76,8 @@ def lib():
         L.orc_raytrace.argtypes = [_P, _I64, ctypes.POINTER(OrcLens), _P, _I32, _I32, _P, _P]
         L.orc_raytrace_vjp.argtypes = [_P, _I64, ctypes.POINTER(OrcLens), _P, _I32, _I32, _P, _P, _P, _P, _P]
         L.orc_lens_jacobian.argtypes = [_P, _I64, ctypes.POINTER(OrcLens), _P, _I32, _I32, _P, _P]
+        L.orc_pixel_shapes.argtypes = [_P, _I32, _I32, _P]
+        L.orc_windowed_matvec.argtypes = [_P, _P, _I64, _P, _I64, _P, _D, _P, _P, _P]
         L.orc_kernel_matvec.argtypes = [_P, _I64, _P, _I64, _P, _D, _D, _P, _I64, _P, _P, _P]
         L.orc_kernel_matvec_vjp.argtypes = [_P, _I64, _P, _I64, _P, _D, _D, _P, _I32, _P, _P, _P, _P, _P, _P]
         L.orc_num_threads.restype = _I32
@@ -114,7 +116,7 @@ def num_threads() -> int:
 
 
 def grid_points(nx, ny, ss, pix, cx=0.0, cy=0.0) -> np.ndarray:
-    """a1: FP32 pixel centres of the (nx ss) x (ny ss) supersampled grid, row-major over y."""
+    """FP32 pixel centres of the (nx ss) x (ny ss) supersampled grid, row-major over y."""
     g = OrcGrid(nx, ny, ss, pix, cx, cy)
     out = np.empty((nx * ss * ny * ss, 2), np.float32)
     lib().orc_grid_points(ctypes.byref(g), _ptr(out))
@@ -128,7 +130,7 @@ def sple_kappa(x, y, lens) -> float:
 
 
 def raytrace(xi, lens, sub=None, profile=0):
-    """a2-a5: returns (alpha, beta), FP64 (n, 2) arrays."""
+    """Ray-trace beta = xi - alpha(xi): returns (alpha, beta), FP64 (n, 2) arrays."""
     xi = _pairs(xi)
     s, ns = _subs(sub)
     L = _lens(lens)
@@ -166,8 +168,30 @@ def lens_jacobian(xi, lens, sub=None, profile=0):
     return jac.reshape(-1, 2, 2), mu
 
 
+def pixel_shapes(p, W, H):
+    """(W*H, 3) window covariances (Zxx, Zxy, Zyy) of a W x H grid of projected pixel centres."""
+    p = _pairs(p)
+    assert p.shape[0] == W * H
+    z = np.empty((W * H, 3), np.float64)
+    lib().orc_pixel_shapes(_ptr(p), W, H, _ptr(z))
+    return z
+
+
+def windowed_matvec(p, z, q, v, lengthscale, dense=False):
+    """(out, absout[, T]) of out_i = sum_k G(p_i - q_k, Z_i + l^2/2 I) v_k."""
+    p, q = _pairs(p), _pairs(q)
+    z = np.ascontiguousarray(z, np.float64)
+    v = None if v is None else np.ascontiguousarray(v, np.float64).reshape(-1)
+    n, m = p.shape[0], q.shape[0]
+    out = np.empty(n, np.float64)
+    ab = np.empty(n, np.float64)
+    T = np.empty((n, m), np.float64) if dense else None
+    lib().orc_windowed_matvec(_ptr(p), _ptr(z), n, _ptr(q), m, _ptr(v), lengthscale, _ptr(out), _ptr(ab), _ptr(T))
+    return (out, ab, T) if dense else (out, ab)
+
+
 def kernel_matvec(x, y, v, lengthscale, variance=1.0, rows=None, with_sens=False):
-    """a6: (out, absout[, sens]), FP64, out_i = sum_j var exp(-|x_i-y_j|^2/(2 l^2)) v_j.
+    """Gaussian-kernel reduction: (out, absout[, sens]), FP64, out_i = sum_j var exp(-|x_i-y_j|^2/(2 l^2)) v_j.
     With `rows`, only those rows of x are evaluated (sampled parity at full size)."""
     x, y = _pairs(x), _pairs(y)
     v = np.ascontiguousarray(v, dtype=np.float64).reshape(-1)
@@ -185,12 +209,12 @@ def kernel_matvec(x, y, v, lengthscale, variance=1.0, rows=None, with_sens=False
 
 
 def kernel_matvec_rows(x, rows, y, v, lengthscale, variance=1.0):
-    """a6 on the rows `rows` of x only: (out, absout) of length len(rows)."""
+    """The reduction on the rows `rows` of x only: (out, absout) of length len(rows)."""
     return kernel_matvec(x, y, v, lengthscale, variance, rows=rows)
 
 
 def kernel_matvec_vjp(x, y, v, lengthscale, variance, g, self_kernel=False, with_abs=False):
-    """a7: dict with d_v, d_x, d_y (None for a self-kernel), d_len, d_var for Loss = sum_i g_i out_i.
+    """Reduction gradients: dict with d_v, d_x, d_y (None for a self-kernel), d_len, d_var for Loss = sum_i g_i out_i.
     With `with_abs`, also the matching sums of absolute terms under keys *_abs."""
     x, y = _pairs(x), _pairs(y)
     v = np.ascontiguousarray(v, dtype=np.float64).reshape(-1)

@@ -156,7 +156,7 @@ static inline cdn cdn_scalec(cdn a, double s) {
 }
 
 /* ------------------------------------------------------------------------ */
-/* a1: pixel centres (Sec. 2 / Table 1).                                       */
+/* Pixel centres (Sec. 2 / Table 1).                                       */
 ORC_API void orc_grid_points(const orc_grid* g, float* xi /* [n][2] */) {
   const int64_t W = (int64_t)g->nx * g->ss, H = (int64_t)g->ny * g->ss;
   const float h = g->pix / (float)g->ss;
@@ -170,7 +170,7 @@ ORC_API void orc_grid_points(const orc_grid* g, float* xi /* [n][2] */) {
 }
 
 /* ------------------------------------------------------------------------ */
-/* a2: SPLE deflection (Sec. 2.2, eq. for the SPLE displacement).
+/* SPLE deflection (Sec. 2.2, eq. for the SPLE displacement).
  *  (u, v) = Rot(phi) (xi - xi0); R_x = sqrt(q) u, R_y = v / sqrt(q);
  *  e^{i phi_e} = (R_x + i R_y) / R;  z = -(1-q)/(1+q) e^{2 i phi_e};
  *  alpha' = theta_e 2 sqrt(q)/(1+q) (theta_e/R)^(gamma-2) 2F1(1, (gamma-1)/2;
@@ -223,7 +223,7 @@ ORC_API double orc_sple_kappa(double x, double y, const orc_lens* L) {
 }
 
 /* ------------------------------------------------------------------------ */
-/* a4: truncated NFW deflection (Baltz, Marshall & Oguri 2009), in units of
+/* Truncated NFW deflection (Baltz, Marshall & Oguri 2009), in units of
  * the scale radius: x = R / theta_s,
  *   g(x) = tau^2/(tau^2+1)^2 [ (tau^2 + 1 + 2(x^2-1)) F(x) + tau pi
  *          + (tau^2-1) ln tau + sqrt(tau^2+x^2) (-pi + (tau^2-1)/tau L(x)) ],
@@ -298,7 +298,7 @@ static void sub_dual(double x, double y, const double* rec, int profile, int wit
 }
 
 /* ------------------------------------------------------------------------ */
-/* a2-a5: ray-trace (eq. for the raytracing equation, Sec. 2.1):
+/* Ray-trace (eq. for the raytracing equation, Sec. 2.1):
  *   beta = xi - alpha(xi), alpha = alpha_SPLE + alpha_shear + sum_h alpha_h.
  * External shear (Sec. 2.2): alpha = [[g1, g2], [g2, -g1]] xi about the origin.
  * Outputs alpha and beta for n points xi (all FP64; FP32 inputs are widened
@@ -451,7 +451,7 @@ ORC_API void orc_lens_jacobian(const double* xi, int64_t n, const orc_lens* L, c
 }
 
 /* ------------------------------------------------------------------------ */
-/* a6: Gaussian RBF kernel reduction (eq. for the Gaussian RBF, Sec. 3.1, with
+/* Gaussian RBF kernel reduction (eq. for the Gaussian RBF, Sec. 3.1, with
  * isotropic kernel Sigma = l^2 I; Sec. 3.4 evaluates T y as this lazily
  * reduced sum):
  *   out_i    = sum_j var * exp(-|x_i - y_j|^2 / (2 l^2)) v_j,
@@ -492,7 +492,61 @@ ORC_API void orc_kernel_matvec(const double* x, int64_t n, const double* y, int6
 }
 
 /* ------------------------------------------------------------------------ */
-/* a7: gradients of Loss = sum_i g_i out_i through the reduction, by
+/* Pixel windows (Sec. 3.2, the window-kernel equation and its footnote): the
+ * projected pixel centres p form a W x H grid (row-major over grid y). The
+ * axes of pixel i are a_i = half the vector between the two centres adjacent
+ * along grid x, b_i the same along grid y; at the border of the grid, where
+ * one neighbour is missing, the vector to the single neighbour. The window
+ * covariance is Z_i = (a a^T + b b^T) / (4 pi); output (Zxx, Zxy, Zyy). */
+ORC_API void orc_pixel_shapes(const double* p, int32_t W, int32_t H, double* z) {
+#pragma omp parallel for schedule(static)
+  for (int64_t r = 0; r < H; ++r)
+    for (int64_t c = 0; c < W; ++c) {
+      const int64_t i = r * W + c;
+      const int64_t cl = c > 0 ? i - 1 : i, cr = c + 1 < W ? i + 1 : i;
+      const int64_t rd = r > 0 ? i - W : i, ru = r + 1 < H ? i + W : i;
+      const double sa = (cr - cl == 2) ? 0.5 : 1.0, sb = (ru - rd == 2 * W) ? 0.5 : 1.0;
+      const double ax = sa * (p[2 * cr] - p[2 * cl]), ay = sa * (p[2 * cr + 1] - p[2 * cl + 1]);
+      const double bx = sb * (p[2 * ru] - p[2 * rd]), by = sb * (p[2 * ru + 1] - p[2 * rd + 1]);
+      const double k = 1.0 / (4.0 * PI);
+      z[3 * i] = k * (ax * ax + bx * bx);
+      z[3 * i + 1] = k * (ax * ay + bx * by);
+      z[3 * i + 2] = k * (ay * ay + by * by);
+    }
+}
+
+/* Windowed transmission (Sec. 3.5, the transmission equation, with
+ * Sigma = l^2 I): T_ik = A_k G(p_i - q_k, Z_i + Sigma / 2), reduced as
+ *   out_i = sum_k G(p_i - q_k, Z_i + Sigma / 2) v_k,
+ * G(d, C) = exp(-d^T C^-1 d / 2) / (2 pi sqrt(det C)); the caller folds the
+ * weights A_k into v_k. absout_i = sum_k |G v_k|. With T != NULL (tiny
+ * sizes only) also writes the dense G matrix [n][m]. */
+ORC_API void orc_windowed_matvec(const double* p, const double* z, int64_t n, const double* q, int64_t m,
+                                 const double* v, double lengthscale, double* out, double* absout, double* T) {
+  const double half_s = 0.5 * lengthscale * lengthscale;
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int64_t i = 0; i < n; ++i) {
+    const double cxx = z[3 * i] + half_s, cxy = z[3 * i + 1], cyy = z[3 * i + 2] + half_s;
+    const double det = cxx * cyy - cxy * cxy;
+    const double ixx = cyy / det, ixy = -cxy / det, iyy = cxx / det;
+    const double norm = 1.0 / (2.0 * PI * sqrt(det));
+    nsum s = {0, 0}, a = {0, 0};
+    for (int64_t k = 0; k < m; ++k) {
+      const double dx = p[2 * i] - q[2 * k], dy = p[2 * i + 1] - q[2 * k + 1];
+      const double g = norm * exp(-0.5 * (ixx * dx * dx + 2.0 * ixy * dx * dy + iyy * dy * dy));
+      if (T) T[i * m + k] = g;
+      if (v) {
+        ns_add(&s, g * v[k]);
+        ns_add(&a, fabs(g * v[k]));
+      }
+    }
+    if (out) out[i] = ns_val(&s);
+    if (absout) absout[i] = ns_val(&a);
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Gradients of Loss = sum_i g_i out_i through the reduction, by
  * differentiating the RBF sum term by term (k_ij includes var):
  *   d_v_j   = sum_i g_i k_ij
  *   d_x_i   = g_i sum_j k_ij v_j (y_j - x_i) / l^2

@@ -94,6 +94,11 @@ SIGNATURES = {
                                                          ctypes.c_int32, ctypes.c_float, ctypes.c_float, _P, _P,
                                                          _P]),
     "lr_static_scratch_bytes": (ctypes.c_size_t, []),
+    "gp_pixel_shapes": (ctypes.c_int32, [_P, ctypes.c_int32, ctypes.c_int32, _P, _P]),
+    "gp_windowed_matvec": (ctypes.c_int32, [_P, _P, ctypes.c_int64, ctypes.POINTER(lr_points), _P, ctypes.c_float, _P,
+                                            _P, ctypes.c_size_t, _P]),
+    "lr_windowed_workspace_size": (ctypes.c_int32, [ctypes.c_int64, ctypes.POINTER(lr_points),
+                                                    ctypes.POINTER(ctypes.c_size_t)]),
     "gp_kernel_matvec_layers": (ctypes.c_int32, [ctypes.POINTER(lr_points), ctypes.POINTER(lr_points), ctypes.c_int32,
                                                  _P, _P, _P, _P, _P, _P, ctypes.c_size_t, _P]),
     "lr_matvec_layers_workspace_size": (ctypes.c_int32, [ctypes.POINTER(lr_points), ctypes.POINTER(lr_points),

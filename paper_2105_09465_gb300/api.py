@@ -167,6 +167,34 @@ def gp_kernel_matvec_layers(query: Points, source: Points | None, v: torch.Tenso
     return (out, beta) if want_beta else out
 
 
+def pixel_shapes(p: torch.Tensor, W: int, H: int, stream=None) -> torch.Tensor:
+    """(W*H, 3) window covariances (Zxx, Zxy, Zyy) of a W x H grid of projected pixel centres p."""
+    lib = abi.load()
+    _require_cuda(p, "p", (2,))
+    z = torch.empty((p.shape[0], 3), dtype=torch.float32, device=p.device)
+    abi.check(lib.gp_pixel_shapes(p.data_ptr(), W, H, z.data_ptr(), _stream_handle(stream)), "gp_pixel_shapes")
+    return z
+
+
+def gp_windowed_matvec(p: torch.Tensor, z: torch.Tensor, source: Points, v: torch.Tensor, lengthscale: float,
+                       stream=None) -> torch.Tensor:
+    """out_i = sum_k G(p_i - q_k, Z_i + l^2/2 I) v_k (windowed transmission)."""
+    lib = abi.load()
+    _require_cuda(p, "p", (2,))
+    _require_cuda(z, "z", (3,))
+    _require_cuda(v, "v")
+    cs, k = to_c_points(source)
+    n = p.shape[0]
+    out = torch.empty(n, dtype=torch.float32, device=p.device)
+    b = ctypes.c_size_t(0)
+    abi.check(lib.lr_windowed_workspace_size(n, ctypes.byref(cs), ctypes.byref(b)), "lr_windowed_workspace_size")
+    ws = torch.empty(max(int(b.value), 1), dtype=torch.uint8, device=p.device)
+    st = lib.gp_windowed_matvec(p.data_ptr(), z.data_ptr(), n, ctypes.byref(cs), v.data_ptr(), float(lengthscale),
+                                out.data_ptr(), ws.data_ptr(), ws.numel(), _stream_handle(stream))
+    abi.check(st, "gp_windowed_matvec")
+    return out
+
+
 GRADS = ("v", "x", "y", "lengthscale", "variance", "lens", "sub")
 
 

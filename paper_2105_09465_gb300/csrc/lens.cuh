@@ -49,7 +49,7 @@ __device__ __forceinline__ float pow_split(float R2, float e) {
   return ldexpf(exp2f(r), (int)n);
 }
 
-// a2: SPLE deflection at (x, y).
+// SPLE deflection at (x, y).
 __device__ __forceinline__ void sple_alpha(const LensConst& L, float x, float y, float& ax, float& ay) {
   const float dx = x - L.x0, dy = y - L.y0;
   const float u = fmaf(L.c, dx, L.s * dy);
@@ -136,7 +136,7 @@ __device__ __forceinline__ float nfw_F(float x2, float xx, float& s) {
   return atan_over(s, is);                                 // arccos(1/x) = arctan(s)
 }
 
-// a4: truncated-NFW deflection per unit offset: alpha = m * (dx, dy) with
+// Truncated-NFW deflection per unit offset: alpha = m * (dx, dy) with
 // m = A * B(x)/x^2 where B is the bracket of the enclosed-mass function.
 // For x < 0.5 the bracket is evaluated in a rearranged form whose terms are
 // all O(x^2) (the direct form cancels catastrophically as x -> 0):

@@ -1,4 +1,4 @@
-// a6: lazily evaluated Gaussian-kernel reduction
+// Lazily evaluated Gaussian-kernel reduction
 //   out_i = sum_j var * exp(-|x_i - y_j|^2 / (2 l^2)) v_j
 // (RBF covariance with Sigma = l^2 I, Sec. 3.1; T y evaluated without storing
 // T, Sec. 3.4).

@@ -1,4 +1,4 @@
-// a7: backward of the Gaussian-kernel reduction, recompute-only (k is never
+// Backward of the Gaussian-kernel reduction, recompute-only (k is never
 // stored). For Loss = sum_i g_i out_i with out_i = sum_j var k_ij v_j,
 // k_ij = exp(-|x_i - y_j|^2 / (2 l^2)):
 //   d_x_i = var/l^2 * g_i sum_j k_ij v_j (y_j - x_i)            (row role)

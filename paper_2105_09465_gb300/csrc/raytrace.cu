@@ -1,4 +1,4 @@
-// a1-a5: pixel-grid generation and the lens ray-trace beta = xi - alpha(xi).
+// Pixel-grid generation and the lens ray-trace beta = xi - alpha(xi).
 //
 // One thread per image-plane point. The SPLE and shear terms are evaluated in
 // registers from per-lens constants passed as a kernel parameter; the

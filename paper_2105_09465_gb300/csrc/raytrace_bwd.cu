@@ -1,4 +1,4 @@
-// Ray-trace backward (vector-Jacobian product of a2-a5): given G = dL/dbeta
+// Ray-trace backward (vector-Jacobian product of the deflection sum): given G = dL/dbeta
 // for every image-plane point, returns dL/d(x0, y0, q, phi, theta_e, g1, g2)
 // of the lens and dL/d(x_h, y_h, kappa_s | theta_pm, theta_s) of every
 // subhalo, with dL/dp = -sum_i G_i . dalpha_i/dp (beta = xi - alpha).

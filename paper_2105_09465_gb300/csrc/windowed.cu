@@ -1,0 +1,316 @@
+// Pixel windows and the windowed (non-stationary) transmission reduction of
+// the paper's image-plane model (Sec. 3.2 window-function and window-kernel
+// equations, Sec. 3.5 transmission equation):
+//   Z_i = (a_i a_i^T + b_i b_i^T) / (4 pi)   from the projected pixel grid,
+//   out_i = sum_k G(p_i - q_k, Z_i + (l^2/2) I) v_k,
+//   G(d, C) = exp(-d^T C^-1 d / 2) / (2 pi sqrt(det C)),
+// with the transmission weights A_k folded into v_k by the caller. Each
+// query row carries its own 2x2 inverse covariance (three coefficients,
+// pre-scaled for exp2) and normalisation; per pair the exponent is a
+// quadratic form in (dx, dy). Same tiling, chunking and fixed-order merge as
+// the stationary reduction.
+#include <math.h>
+
+#include "host.cuh"
+#include "problems.cuh"
+
+namespace lr {
+
+constexpr int kWnThreads = 128;
+constexpr int kWnR = 4;
+constexpr int kWnRows = kWnThreads * kWnR;
+constexpr int kWnTile = 256;
+constexpr int kWnPairs = kWnTile / 2;
+static_assert(kWnPairs == kWnThreads, "one source pair per thread when staging");
+
+__global__ void pixel_shapes_kernel(const float2* __restrict__ p, int32_t W, int32_t H, float* __restrict__ z) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (int64_t)W * H) return;
+  const int32_t r = (int32_t)(i / W), c = (int32_t)(i - (int64_t)r * W);
+  const int64_t cl = c > 0 ? i - 1 : i, cr = c + 1 < W ? i + 1 : i;
+  const int64_t rd = r > 0 ? i - W : i, ru = r + 1 < H ? i + W : i;
+  const float sa = (cr - cl == 2) ? 0.5f : 1.0f, sb = (ru - rd == 2 * (int64_t)W) ? 0.5f : 1.0f;
+  const float2 pl = p[cl], pr = p[cr], pd = p[rd], pu = p[ru];
+  const float ax = sa * (pr.x - pl.x), ay = sa * (pr.y - pl.y);
+  const float bx = sb * (pu.x - pd.x), by = sb * (pu.y - pd.y);
+  const float k = 0.0795774715459477f;  // 1 / (4 pi)
+  z[3 * i] = k * fmaf(ax, ax, bx * bx);
+  z[3 * i + 1] = k * fmaf(ax, ay, bx * by);
+  z[3 * i + 2] = k * fmaf(ay, ay, by * by);
+}
+
+struct WnArgs {
+  const float2* p;
+  const float* z;
+  int64_t n;
+  const float2* q;  // explicit sources, or NULL for the grid
+  GridDev g;
+  int64_t m;
+  int32_t segs, n_tiles, chunks;
+  const float* v;
+  float half_s;     // l^2 / 2
+  float* out;
+  float* partial;
+};
+
+__device__ __forceinline__ float2 wf2(float a, float b) { return make_float2(a, b); }
+
+__device__ __forceinline__ void wn_tile(const WnArgs& A, int t, int64_t& j0, int& cnt, int& grow) {
+  if (A.q) {
+    j0 = (int64_t)t * kWnTile;
+    const int64_t rem = A.m - j0;
+    cnt = rem < kWnTile ? (int)rem : kWnTile;
+    grow = 0;
+  } else {
+    grow = t / A.segs;
+    const int c0 = (t - grow * A.segs) * kWnTile;
+    cnt = min(kWnTile, A.g.W - c0);
+    j0 = (int64_t)grow * A.g.W + c0;
+  }
+}
+
+template <bool GRID>
+__device__ __forceinline__ void wn_load(const WnArgs& A, int t, int p, float4& P, float2& V) {
+  int64_t j0;
+  int cnt, grow;
+  wn_tile(A, t, j0, cnt, grow);
+  const int a = 2 * p, b = 2 * p + 1;
+  if (GRID) {
+    const int c0 = (int)(j0 - (int64_t)grow * A.g.W);
+    P = make_float4((a < cnt) ? -grid_x(A.g, c0 + a) : 0.f, (b < cnt) ? -grid_x(A.g, c0 + b) : 0.f, 0.f, 0.f);
+  } else {
+    const float2 qa = (a < cnt) ? __ldg(A.q + j0 + a) : wf2(0.f, 0.f);
+    const float2 qb = (b < cnt) ? __ldg(A.q + j0 + b) : wf2(0.f, 0.f);
+    P = make_float4(-qa.x, -qb.x, -qa.y, -qb.y);
+  }
+  V = wf2((a < cnt) ? __ldg(A.v + j0 + a) : 0.f, (b < cnt) ? __ldg(A.v + j0 + b) : 0.f);
+}
+
+template <bool GRID>
+__global__ void __launch_bounds__(kWnThreads) windowed_kernel(const __grid_constant__ WnArgs A) {
+  __shared__ __align__(16) float4 sP[2][kWnPairs];
+  __shared__ __align__(16) float2 sV[2][kWnPairs];
+  __shared__ float ksum[kWnR][kWnThreads], kcomp[kWnR][kWnThreads];
+  const int rb = blockIdx.x / A.chunks;
+  const int chunk = blockIdx.x - rb * A.chunks;
+  const int t0 = (int)((int64_t)chunk * A.n_tiles / A.chunks);
+  const int t1 = (int)((int64_t)(chunk + 1) * A.n_tiles / A.chunks);
+  const int tid = threadIdx.x;
+  // per row: exponent = dx (mxx dx + mxy2 dy) + myy dy^2 with the inverse
+  // covariance pre-scaled by -log2(e)/2
+  float2 xq[kWnR], yq[kWnR], mxx[kWnR], mxy2[kWnR], myy[kWnR], acc[kWnR];
+  float norm[kWnR];
+#pragma unroll
+  for (int r = 0; r < kWnR; ++r) {
+    int64_t i = (int64_t)rb * kWnRows + r * kWnThreads + tid;
+    if (i >= A.n) i = A.n - 1;
+    const float2 pp = __ldg(A.p + i);
+    const float cxx = __ldg(A.z + 3 * i) + A.half_s, cxy = __ldg(A.z + 3 * i + 1),
+                cyy = __ldg(A.z + 3 * i + 2) + A.half_s;
+    const float det = fmaf(cxx, cyy, -cxy * cxy);
+    const float s = -0.72134752044448170f / det;  // -log2(e) / (2 det)
+    xq[r] = wf2(pp.x, pp.x);
+    yq[r] = wf2(pp.y, pp.y);
+    mxx[r] = wf2(s * cyy, s * cyy);
+    mxy2[r] = wf2(-2.0f * s * cxy, -2.0f * s * cxy);
+    myy[r] = wf2(s * cxx, s * cxx);
+    norm[r] = 0.15915494309189535f * rsqrtf(det);  // 1 / (2 pi sqrt(det))
+    acc[r] = wf2(0.f, 0.f);
+    ksum[r][tid] = 0.f;
+    kcomp[r][tid] = 0.f;
+  }
+  float4 P;
+  float2 V;
+  if (t0 < t1) {
+    wn_load<GRID>(A, t0, tid, P, V);
+    sP[0][tid] = P;
+    sV[0][tid] = V;
+  }
+  __syncthreads();
+  for (int t = t0; t < t1; ++t) {
+    const int buf = (t - t0) & 1;
+    if (t + 1 < t1) wn_load<GRID>(A, t + 1, tid, P, V);
+    int64_t j0;
+    int cnt, grow;
+    wn_tile(A, t, j0, cnt, grow);
+    const int np = (cnt + 1) >> 1;
+    if (GRID) {
+      // uniform y on a grid row: the dy terms are per row and tile
+      const float yt = grid_y(A.g, grow);
+      float2 cy[kWnR], ey[kWnR];
+#pragma unroll
+      for (int r = 0; r < kWnR; ++r) {
+        const float dy = yq[r].x - yt;
+        cy[r] = wf2(mxy2[r].x * dy, mxy2[r].x * dy);
+        ey[r] = wf2(myy[r].x * dy * dy, myy[r].x * dy * dy);
+      }
+#pragma unroll 2
+      for (int p = 0; p < np; ++p) {
+        const float4 Q = sP[buf][p];
+        const float2 W = sV[buf][p];
+        const float2 nx = wf2(Q.x, Q.y);
+#pragma unroll
+        for (int r = 0; r < kWnR; ++r) {
+          const float2 dx = __fadd2_rn(xq[r], nx);
+          const float2 u = __ffma2_rn(mxx[r], dx, cy[r]);
+          const float2 e = __ffma2_rn(dx, u, ey[r]);
+          const float2 k = wf2(ex2_approx(e.x), ex2_approx(e.y));
+          acc[r] = __ffma2_rn(k, W, acc[r]);
+        }
+      }
+    } else {
+#pragma unroll 2
+      for (int p = 0; p < np; ++p) {
+        const float4 Q = sP[buf][p];
+        const float2 W = sV[buf][p];
+        const float2 nx = wf2(Q.x, Q.y), ny = wf2(Q.z, Q.w);
+#pragma unroll
+        for (int r = 0; r < kWnR; ++r) {
+          const float2 dx = __fadd2_rn(xq[r], nx);
+          const float2 dy = __fadd2_rn(yq[r], ny);
+          const float2 u = __ffma2_rn(mxx[r], dx, __fmul2_rn(mxy2[r], dy));
+          const float2 e = __ffma2_rn(dx, u, __fmul2_rn(__fmul2_rn(myy[r], dy), dy));
+          const float2 k = wf2(ex2_approx(e.x), ex2_approx(e.y));
+          acc[r] = __ffma2_rn(k, W, acc[r]);
+        }
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < kWnR; ++r) {
+      const float y = (acc[r].x + acc[r].y) - kcomp[r][tid];
+      const float s = ksum[r][tid] + y;
+      kcomp[r][tid] = (s - ksum[r][tid]) - y;
+      ksum[r][tid] = s;
+      acc[r] = wf2(0.f, 0.f);
+    }
+    if (t + 1 < t1) {
+      sP[buf ^ 1][tid] = P;
+      sV[buf ^ 1][tid] = V;
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int r = 0; r < kWnR; ++r) {
+    const int64_t i = (int64_t)rb * kWnRows + r * kWnThreads + tid;
+    if (i < A.n) {
+      const float total = norm[r] * (ksum[r][tid] - kcomp[r][tid]);
+      if (A.chunks == 1)
+        A.out[i] = total;
+      else
+        A.partial[(int64_t)chunk * A.n + i] = total;
+    }
+  }
+}
+
+__global__ void windowed_merge_kernel(const float* __restrict__ partial, int chunks, int64_t n,
+                                      float* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float s = 0.f, c = 0.f;
+  for (int k = 0; k < chunks; ++k) {
+    const float y = partial[(int64_t)k * n + i] - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+  out[i] = s - c;
+}
+
+struct WnPlan {
+  int32_t n_tiles, segs, chunks, row_blocks;
+  size_t bytes;
+};
+
+static lr_status plan_windowed(int64_t n, const lr_points* s, WnPlan* P) {
+  lr_status st = validate_points(s, "gp_windowed_matvec(source)", false);
+  if (st != LR_OK) return st;
+  LR_REQUIRE(s->lens == nullptr, "gp_windowed_matvec: sources must not carry a lens");
+  LR_REQUIRE(n >= 0 && n < (int64_t(1) << 31), "gp_windowed_matvec: n out of range");
+  WnPlan p{};
+  if (s->xy == nullptr) {
+    const int W = s->grid.nx * s->grid.ss;
+    p.segs = (W + kWnTile - 1) / kWnTile;
+    p.n_tiles = (int32_t)((int64_t)p.segs * s->grid.ny * s->grid.ss);
+  } else {
+    p.n_tiles = (int32_t)((s->n + kWnTile - 1) / kWnTile);
+  }
+  p.row_blocks = (int32_t)((n + kWnRows - 1) / kWnRows);
+  int dev = 0, n_sm = 1, occ = 1;
+  LR_CHECK_CUDA(cudaGetDevice(&dev));
+  LR_CHECK_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
+  LR_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, windowed_kernel<false>, kWnThreads, 0));
+  p.chunks = plan_chunks(p.row_blocks, p.n_tiles, occ, n_sm);
+  p.bytes = p.chunks > 1 ? align256(4 * (size_t)p.chunks * (size_t)n) : 0;
+  *P = p;
+  return LR_OK;
+}
+
+}  // namespace lr
+
+using namespace lr;
+
+extern "C" lr_status gp_pixel_shapes(const float* p, int32_t W, int32_t H, float* z, lr_stream stream) {
+  LR_REQUIRE(W >= 1 && H >= 1 && (int64_t)W * H < (int64_t(1) << 31), "gp_pixel_shapes: bad grid %d x %d", W, H);
+  LR_REQUIRE(p != nullptr && z != nullptr, "gp_pixel_shapes: NULL pointer");
+  LR_REQUIRE(((uintptr_t)p & 7u) == 0 && ((uintptr_t)z & 3u) == 0, "gp_pixel_shapes: misaligned pointer");
+  const int64_t n = (int64_t)W * H;
+  pixel_shapes_kernel<<<(unsigned)((n + 255) / 256), 256, 0, as_cuda(stream)>>>(reinterpret_cast<const float2*>(p),
+                                                                                  W, H, z);
+  LR_CHECK_CUDA(cudaGetLastError());
+  return LR_OK;
+}
+
+extern "C" lr_status lr_windowed_workspace_size(int64_t n, const lr_points* source, size_t* bytes) {
+  LR_REQUIRE(bytes != nullptr, "lr_windowed_workspace_size: bytes is NULL");
+  WnPlan P;
+  lr_status st = plan_windowed(n, source, &P);
+  if (st != LR_OK) return st;
+  *bytes = P.bytes;
+  return LR_OK;
+}
+
+extern "C" lr_status gp_windowed_matvec(const float* p, const float* z, int64_t n, const lr_points* source,
+                                        const float* v, float lengthscale, float* out, void* workspace,
+                                        size_t workspace_bytes, lr_stream stream) {
+  WnPlan P;
+  lr_status st = plan_windowed(n, source, &P);
+  if (st != LR_OK) return st;
+  LR_REQUIRE(isfinite(lengthscale) && lengthscale > 0.f, "gp_windowed_matvec: lengthscale must be > 0");
+  LR_REQUIRE(n == 0 || (p != nullptr && z != nullptr && out != nullptr), "gp_windowed_matvec: NULL pointer");
+  LR_REQUIRE(((uintptr_t)p & 7u) == 0 && ((uintptr_t)z & 3u) == 0, "gp_windowed_matvec: misaligned p or z");
+  LR_REQUIRE(v != nullptr || source->n == 0, "gp_windowed_matvec: v is NULL");
+  LR_REQUIRE(workspace_bytes >= P.bytes && (P.bytes == 0 || workspace != nullptr),
+             "gp_windowed_matvec: workspace of %zu bytes, %zu needed", workspace_bytes, P.bytes);
+  LR_REQUIRE(((uintptr_t)workspace & 255u) == 0, "gp_windowed_matvec: workspace must be 256-byte aligned");
+  cudaStream_t s = as_cuda(stream);
+  if (n == 0) return LR_OK;
+  if (source->n == 0) {
+    LR_CHECK_CUDA(cudaMemsetAsync(out, 0, 4 * (size_t)n, s));
+    return LR_OK;
+  }
+  WnArgs A{};
+  A.p = reinterpret_cast<const float2*>(p);
+  A.z = z;
+  A.n = n;
+  A.q = reinterpret_cast<const float2*>(source->xy);
+  A.g = source->xy ? GridDev{} : grid_dev(source->grid);
+  A.m = source->n;
+  A.segs = P.segs;
+  A.n_tiles = P.n_tiles;
+  A.chunks = P.chunks;
+  A.v = v;
+  A.half_s = 0.5f * lengthscale * lengthscale;
+  A.out = out;
+  A.partial = static_cast<float*>(workspace);
+  const unsigned grid = (unsigned)((int64_t)P.row_blocks * P.chunks);
+  if (A.q)
+    windowed_kernel<false><<<grid, kWnThreads, 0, s>>>(A);
+  else
+    windowed_kernel<true><<<grid, kWnThreads, 0, s>>>(A);
+  LR_CHECK_CUDA(cudaGetLastError());
+  if (P.chunks > 1) {
+    windowed_merge_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(A.partial, P.chunks, n, out);
+    LR_CHECK_CUDA(cudaGetLastError());
+  }
+  return LR_OK;
+}

@@ -1,4 +1,4 @@
-"""Parity of the CUDA backward pass (a7) with the FP64 oracle's analytic
+"""Parity of the CUDA backward pass with the FP64 oracle's analytic
 gradients: the reduction alone on explicit points, grid inducing points, the
 self-kernel; the ray-trace vector-Jacobian product alone; and the whole
 fused chain down to the lens and subhalo parameters."""

@@ -1,4 +1,4 @@
-"""Parity of the CUDA kernel reduction (a6) with the FP64 oracle, on explicit
+"""Parity of the CUDA kernel reduction with the FP64 oracle, on explicit
 points, grid inducing points, the self-kernel and the fused ray-trace path."""
 import numpy as np
 import pytest

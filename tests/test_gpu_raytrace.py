@@ -1,4 +1,4 @@
-"""Parity of the CUDA ray-trace (a1-a5) with the FP64 oracle."""
+"""Parity of the CUDA ray-trace with the FP64 oracle."""
 import math
 
 import numpy as np

@@ -24,7 +24,7 @@ def pts(n, hw=3.0, rng=RNG):
     return rng.uniform(-hw, hw, size=(n, 2))
 
 
-# ---------------------------------------------------------------- a1: grid
+# ---------------------------------------------------------------- pixel grid
 def test_grid_points_definition(orc):
     xi = orc.grid_points(3, 2, 2, 0.05, 0.25, -0.5).astype(np.float64)
     assert xi.shape == (6 * 4, 2)
@@ -51,7 +51,7 @@ def test_grid_points_are_fp32_values(orc):
     np.testing.assert_allclose(g[..., 0] + g[:, ::-1, 0], 0.2, atol=1e-7)
 
 
-# ---------------------------------------------------------------- a2: SPLE
+# ---------------------------------------------------------------- SPLE
 def test_sis_constant_magnitude(orc):
     """q = 1, gamma = 2: |alpha| = theta_E everywhere, radial."""
     x = pts(500)
@@ -135,7 +135,7 @@ def test_sple_zero_at_centre(orc):
     assert np.all(a == 0.0)
 
 
-# ---------------------------------------------------------------- a3: shear
+# ---------------------------------------------------------------- external shear
 def test_shear_linear_symmetric_traceless(orc):
     L = lens(theta_e=0.0, g1=0.03, g2=-0.02)
     x1, x2 = pts(50), pts(50)
@@ -162,7 +162,7 @@ def test_superposition(orc):
     np.testing.assert_allclose(full, main + shear + s0 + s1, atol=1e-14)
 
 
-# ---------------------------------------------------------------- a4: subhalos
+# ---------------------------------------------------------------- subhalos
 def _tnfw_rho(r, ks, ts, tau):
     """3-D truncated NFW density in units of Sigma_cr per arcsec (theta_s = r_s)."""
     t = r / ts
@@ -238,7 +238,7 @@ def test_point_mass(orc):
     np.testing.assert_allclose(a, 0.05 ** 2 * d / (d ** 2).sum(1)[:, None], rtol=1e-13)
 
 
-# ---------------------------------------------------------------- a2-a5 gradients
+# ---------------------------------------------------------------- ray-trace gradients
 @pytest.mark.parametrize("profile", [0, 1])
 def test_raytrace_vjp_against_central_differences(orc, profile):
     rng = np.random.default_rng(7)
@@ -264,7 +264,7 @@ def test_raytrace_vjp_against_central_differences(orc, profile):
             np.testing.assert_allclose(d_sub[hh, k], fd, rtol=1e-6, atol=1e-7)
 
 
-# ---------------------------------------------------------------- a6: kernel reduction
+# ---------------------------------------------------------------- kernel reduction
 def test_matvec_brute_force_long_double(orc):
     rng = np.random.default_rng(3)
     x, y = rng.uniform(-0.2, 0.2, (37, 2)), rng.uniform(-0.2, 0.2, (53, 2))
@@ -315,7 +315,7 @@ def test_matvec_rows_matches_full(orc):
     np.testing.assert_array_equal(a2, ab[rows])
 
 
-# ---------------------------------------------------------------- a7: gradients
+# ---------------------------------------------------------------- reduction gradients
 @pytest.mark.parametrize("self_kernel", [False, True])
 def test_matvec_vjp_against_central_differences(orc, self_kernel):
     rng = np.random.default_rng(8)
@@ -437,3 +437,64 @@ def test_jacobian_trace_and_symmetry_and_shear(orc, name):
     by = (orc.raytrace(x + [0, h], L, sub)[1] - orc.raytrace(x - [0, h], L, sub)[1]) / (2 * h)
     np.testing.assert_allclose(jac2[:, :, 0], bx, atol=1e-7)
     np.testing.assert_allclose(jac2[:, :, 1], by, atol=1e-7)
+
+
+# ---------------------------------------------------------------- pixel windows (next: windowed kernel)
+def test_pixel_window_normalisation_appendix_c(orc):
+    """App. C: the window with Z = (a a^T + b b^T)/4pi has integral of w^2 equal to
+    1/|det(a, b)| (the inverse projected pixel area); checked by 2-D quadrature."""
+    rng = np.random.default_rng(21)
+    a, b = rng.normal(0, 0.05, 2), rng.normal(0, 0.05, 2)
+    grid = np.array([[i * a + j * b for i in range(3)] for j in range(3)]).reshape(-1, 2)
+    z = orc.pixel_shapes(grid, 3, 3)[4]  # centre pixel: both neighbours present
+    Z = np.array([[z[0], z[1]], [z[1], z[2]]])
+    Zi = np.linalg.inv(Z)
+    L = 8 * np.sqrt(np.max(np.linalg.eigvalsh(Z)))
+    h = L / 400
+    xs = np.arange(-L, L, h)
+    X, Y = np.meshgrid(xs, xs)
+    r = np.stack([X, Y], -1)
+    w = np.exp(-0.5 * np.einsum("...i,ij,...j", r, Zi, r)) / (2 * np.pi * np.sqrt(np.linalg.det(Z)))
+    np.testing.assert_allclose((w ** 2).sum() * h * h, 1 / abs(a[0] * b[1] - a[1] * b[0]), rtol=1e-6)
+    np.testing.assert_allclose(w.sum() * h * h, 1.0, rtol=1e-6)
+
+
+def test_pixel_shapes_border_uses_the_single_neighbour(orc):
+    grid = np.array([[c * 0.1, r * 0.2] for r in range(2) for c in range(3)])
+    z = orc.pixel_shapes(grid, 3, 2)
+    k = 1 / (4 * np.pi)
+    for i in range(6):
+        np.testing.assert_allclose(z[i], [k * 0.01, 0.0, k * 0.04], atol=1e-15)
+
+
+def test_windowed_point_limit_is_the_rbf_kernel(orc):
+    """Z_i -> 0: G(d, l^2/2 I) = exp(-d^2/l^2)/(pi l^2), the RBF with length l/sqrt2."""
+    rng = np.random.default_rng(22)
+    p, q, v = rng.uniform(-0.3, 0.3, (20, 2)), rng.uniform(-0.3, 0.3, (30, 2)), rng.standard_normal(30)
+    out, _ = orc.windowed_matvec(p, np.zeros((20, 3)), q, v, 0.1)
+    ref, _ = orc.kernel_matvec(p, q, v, 0.1 / np.sqrt(2), 1 / (np.pi * 0.01))
+    np.testing.assert_allclose(out, ref, rtol=1e-12)
+
+
+def test_transmission_factorises_the_windowed_covariance(orc):
+    """Sec. 3.5: with A_k = |2 pi Sigma|^(1/4) / sqrt(n_q) on a dense grid,
+    sum_k T_ik T_jk -> |2 pi Sigma|^(1/2) G(p_i - p_j, Z_i + Sigma + Z_j) = K_ij / var (eq. covariance)."""
+    rng = np.random.default_rng(23)
+    ell = 0.1
+    p = rng.uniform(-0.1, 0.1, (5, 2))
+    z = np.abs(rng.normal(0, 1e-3, (5, 3)))
+    z[:, 1] = 0.3 * np.sqrt(z[:, 0] * z[:, 2])
+    h = 0.008
+    g = np.arange(-0.7, 0.7 + h / 2, h)
+    Q = np.stack(np.meshgrid(g, g), -1).reshape(-1, 2)
+    _, _, T = orc.windowed_matvec(p, z, Q, None, ell, dense=True)
+    S = ell * ell
+    A2 = 2 * np.pi * S * h * h  # A_k^2 = |2 pi Sigma|^(1/2) / n_q with |2 pi Sigma|^(1/2) = 2 pi l^2
+    lhs = A2 * T @ T.T
+    ref = np.empty((5, 5))
+    for i in range(5):
+        for j in range(5):
+            C = np.array([[z[i, 0] + z[j, 0] + S, z[i, 1] + z[j, 1]], [z[i, 1] + z[j, 1], z[i, 2] + z[j, 2] + S]])
+            d = p[i] - p[j]
+            ref[i, j] = 2 * np.pi * S * np.exp(-0.5 * d @ np.linalg.solve(C, d)) / (2 * np.pi * np.sqrt(np.linalg.det(C)))
+    np.testing.assert_allclose(lhs, ref, rtol=1e-6)
