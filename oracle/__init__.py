@@ -78,6 +78,7 @@ def lib():
         L.orc_lens_jacobian.argtypes = [_P, _I64, ctypes.POINTER(OrcLens), _P, _I32, _I32, _P, _P]
         L.orc_pixel_shapes.argtypes = [_P, _I32, _I32, _P]
         L.orc_windowed_matvec.argtypes = [_P, _P, _I64, _P, _I64, _P, _D, _P, _P, _P]
+        L.orc_knn_r2.argtypes = [_P, _I64, _I32, _P, _I64, _P]
         L.orc_kernel_matvec.argtypes = [_P, _I64, _P, _I64, _P, _D, _D, _P, _I64, _P, _P, _P]
         L.orc_kernel_matvec_vjp.argtypes = [_P, _I64, _P, _I64, _P, _D, _D, _P, _I32, _P, _P, _P, _P, _P, _P]
         L.orc_num_threads.restype = _I32
@@ -188,6 +189,31 @@ def windowed_matvec(p, z, q, v, lengthscale, dense=False):
     T = np.empty((n, m), np.float64) if dense else None
     lib().orc_windowed_matvec(_ptr(p), _ptr(z), n, _ptr(q), m, _ptr(v), lengthscale, _ptr(out), _ptr(ab), _ptr(T))
     return (out, ab, T) if dense else (out, ab)
+
+
+def knn_r2(q, k, rows=None):
+    """Squared distance from each point (or each listed row) of q to its k-th
+    closest other point of q, FP64 (k <= 64)."""
+    q = _pairs(q)
+    assert 1 <= k <= 64
+    r = None if rows is None else np.ascontiguousarray(rows, np.int64)
+    n = q.shape[0] if r is None else len(r)
+    out = np.empty(n, np.float64)
+    lib().orc_knn_r2(_ptr(q), q.shape[0], k, _ptr(r), n, _ptr(out))
+    return out
+
+
+def knn_density(q, k=20, rows=None):
+    """Inducing-point density rho = k / (pi r_k^2) (Sec. 3.5 footnote)."""
+    return k / (np.pi * knn_r2(q, k, rows))
+
+
+def transmission_weights(q, lengthscale, k=20, rows=None, density=None):
+    """A_k = |2 pi Sigma|^(1/4) / sqrt(rho(q_k)) with Sigma = l^2 I in two
+    dimensions, i.e. sqrt(2 pi l^2 / rho) (Sec. 3.5). `density` overrides
+    the k-nearest-neighbour estimate."""
+    rho = knn_density(q, k, rows) if density is None else np.asarray(density, np.float64)
+    return np.sqrt(2.0 * np.pi * lengthscale ** 2 / rho)
 
 
 def kernel_matvec(x, y, v, lengthscale, variance=1.0, rows=None, with_sens=False):

@@ -545,6 +545,36 @@ ORC_API void orc_windowed_matvec(const double* p, const double* z, int64_t n, co
   }
 }
 
+/* Inducing-point density (Sec. 3.5, footnote to the factorisation of the
+ * covariance): rho(q_k) = k / (pi r_k^2) with r_k the distance from q_k to the
+ * k-th closest OTHER point of the set (the point itself excluded by index;
+ * coincident points count at distance 0). Writes r_k^2 for the rows listed
+ * in `rows` (all m points when rows == NULL). Plain definition: every
+ * squared distance in FP64, then the k-th smallest by repeated selection of
+ * a bounded sorted list. */
+ORC_API void orc_knn_r2(const double* q, int64_t m, int32_t k, const int64_t* rows, int64_t n_rows, double* r2) {
+  const int64_t n = rows ? n_rows : m;
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int64_t t = 0; t < n; ++t) {
+    const int64_t i = rows ? rows[t] : t;
+    double best[64];
+    int32_t have = 0;
+    for (int64_t j = 0; j < m; ++j) {
+      if (j == i) continue;
+      const double dx = q[2 * i] - q[2 * j], dy = q[2 * i + 1] - q[2 * j + 1];
+      const double d2 = dx * dx + dy * dy;
+      if (have == k && d2 >= best[k - 1]) continue;
+      int32_t pos = have < k ? have++ : k - 1;
+      while (pos > 0 && best[pos - 1] > d2) {
+        best[pos] = best[pos - 1];
+        --pos;
+      }
+      best[pos] = d2;
+    }
+    r2[t] = have == k ? best[k - 1] : INFINITY;
+  }
+}
+
 /* ------------------------------------------------------------------------ */
 /* Gradients of Loss = sum_i g_i out_i through the reduction, by
  * differentiating the RBF sum term by term (k_ij includes var):

@@ -498,3 +498,62 @@ def test_transmission_factorises_the_windowed_covariance(orc):
             d = p[i] - p[j]
             ref[i, j] = 2 * np.pi * S * np.exp(-0.5 * d @ np.linalg.solve(C, d)) / (2 * np.pi * np.sqrt(np.linalg.det(C)))
     np.testing.assert_allclose(lhs, ref, rtol=1e-6)
+
+
+# ---------------------------------------------------------------- inducing-point density
+def _lattice(side, h):
+    g = (np.arange(side) - (side - 1) / 2) * h
+    return np.stack(np.meshgrid(g, g), -1).reshape(-1, 2)
+
+
+@pytest.mark.parametrize("k,shell", [(1, 1), (4, 1), (5, 2), (8, 2), (12, 4), (13, 5), (20, 5), (24, 8), (28, 9)])
+def test_knn_radius_on_the_square_lattice(orc, k, shell):
+    """Neighbour shells of the square lattice (spacing h, interior points):
+    4 at h^2, 4 at 2h^2, 4 at 4h^2, 8 at 5h^2, 4 at 8h^2, 4 at 9h^2, so the
+    k-th closest other point sits at shell * h^2 (k = 20 -> r^2 = 5 h^2)."""
+    side, h = 15, 0.1
+    q = _lattice(side, h)
+    inner = [r * side + c for r in range(4, side - 4) for c in range(4, side - 4)]
+    r2 = orc.knn_r2(q, k, inner)
+    np.testing.assert_allclose(r2, shell * h * h, rtol=1e-12)
+
+
+def test_knn_radius_matches_a_full_sort(orc):
+    """Brute force by a library sort of every row of the distance matrix
+    (self excluded), on random points with coincident pairs."""
+    rng = np.random.default_rng(31)
+    q = rng.uniform(-1, 1, (300, 2))
+    q[50:60] = q[40:50]  # ten coincident pairs
+    d2 = ((q[:, None, :] - q[None, :, :]) ** 2).sum(-1)
+    np.fill_diagonal(d2, np.inf)
+    srt = np.sort(d2, axis=1)
+    for k in (1, 2, 7, 20, 33):
+        np.testing.assert_array_equal(orc.knn_r2(q, k), srt[:, k - 1])
+    assert np.all(orc.knn_r2(q, 1)[40:60] == 0.0)
+
+
+def test_knn_density_of_a_uniform_lattice_corner_and_interior(orc):
+    """rho = k / (pi r_k^2): 20 / (5 pi h^2) in the lattice interior. The
+    corner point sees one quadrant, squared distances (a^2 + b^2) h^2 over
+    a, b >= 0 not both zero, whose 20th smallest is 20 h^2."""
+    side, h = 15, 0.1
+    q = _lattice(side, h)
+    rho = orc.knn_density(q, 20, [side * 7 + 7, 0])
+    c = np.sort([(a * a + b * b) for a in range(side) for b in range(side) if a or b])[19]
+    np.testing.assert_allclose(rho, [20 / (np.pi * 5 * h * h), 20 / (np.pi * c * h * h)], rtol=1e-12)
+
+
+def test_transmission_weights_reproduce_the_rbf_kernel(orc):
+    """Sec. 3.5: with A_k = |2 pi Sigma|^(1/4) / sqrt(rho) and the exact
+    density 1/h^2 of a fine lattice, sum_k A_k^2 G(p_i - q_k, Sigma/2)
+    G(p_j - q_k, Sigma/2) equals exp(-|p_i - p_j|^2 / (2 l^2)), the unit
+    variance Gaussian RBF (Sec. 3.1)."""
+    rng = np.random.default_rng(37)
+    ell, h = 0.1, 0.02
+    p = rng.uniform(-0.15, 0.15, (6, 2))
+    Q = _lattice(101, h)
+    A = orc.transmission_weights(Q, ell, density=np.full(len(Q), 1 / (h * h)))
+    _, _, T = orc.windowed_matvec(p, np.zeros((6, 3)), Q, None, ell, dense=True)
+    lhs = (T * A) @ (T * A).T
+    d2 = ((p[:, None, :] - p[None, :, :]) ** 2).sum(-1)
+    np.testing.assert_allclose(lhs, np.exp(-d2 / (2 * ell * ell)), rtol=1e-9)
