@@ -225,6 +225,25 @@ lr_status gp_windowed_matvec(const float* p, const float* z, int64_t n, const lr
                              lr_stream stream);
 lr_status lr_windowed_workspace_size(int64_t n, const lr_points* source, size_t* bytes);
 
+/*
+ * Inducing-point density (Sec. 3.5, footnote to the covariance factorisation)
+ * and the transmission weights it sets, for m points q (device float[m][2]):
+ *   r2_out[i] = r_k(q_i)^2, the squared distance to the k-th closest OTHER
+ *               point of q (the point itself excluded by index; coincident
+ *               points count at distance 0), FP32;
+ *   a_out[i]  = A_i = |2 pi Sigma|^(1/4) / sqrt(rho_i) with rho_i = k / (pi r2_i)
+ *               and Sigma = lengthscale^2 I, i.e. pi l sqrt(2 r2_i / k).
+ * Either output may be NULL (not both); lengthscale is read only for a_out.
+ * 1 <= k <= 32 and m >= k + 1, else LR_ERR_INVALID_ARG. Workspace of
+ * lr_knn_workspace_size(m) bytes, 256-byte aligned, owned by the caller.
+ * Cost grows with the number of points per occupied cell of a uniform grid
+ * over the bounding box: far outliers that stretch the box make it slower,
+ * never wrong.
+ */
+lr_status gp_knn_density(const float* q, int64_t m, int32_t k, float lengthscale, float* r2_out, float* a_out,
+                         void* workspace, size_t workspace_bytes, lr_stream stream);
+lr_status lr_knn_workspace_size(int64_t m, size_t* bytes);
+
 /* Scratch bytes gp_kernel_matvec needs for these point sets on the current device. */
 lr_status lr_matvec_workspace_size(const lr_points* query, const lr_points* source, int32_t nrhs, size_t* bytes);
 

@@ -97,6 +97,9 @@ SIGNATURES = {
     "gp_pixel_shapes": (ctypes.c_int32, [_P, ctypes.c_int32, ctypes.c_int32, _P, _P]),
     "gp_windowed_matvec": (ctypes.c_int32, [_P, _P, ctypes.c_int64, ctypes.POINTER(lr_points), _P, ctypes.c_float, _P,
                                             _P, ctypes.c_size_t, _P]),
+    "gp_knn_density": (ctypes.c_int32, [_P, ctypes.c_int64, ctypes.c_int32, ctypes.c_float, _P, _P, _P,
+                                        ctypes.c_size_t, _P]),
+    "lr_knn_workspace_size": (ctypes.c_int32, [ctypes.c_int64, ctypes.POINTER(ctypes.c_size_t)]),
     "lr_windowed_workspace_size": (ctypes.c_int32, [ctypes.c_int64, ctypes.POINTER(lr_points),
                                                     ctypes.POINTER(ctypes.c_size_t)]),
     "gp_kernel_matvec_layers": (ctypes.c_int32, [ctypes.POINTER(lr_points), ctypes.POINTER(lr_points), ctypes.c_int32,

@@ -195,6 +195,29 @@ def gp_windowed_matvec(p: torch.Tensor, z: torch.Tensor, source: Points, v: torc
     return out
 
 
+def knn_density(q: torch.Tensor, k: int = 20, lengthscale: float | None = None, want_r2: bool = True,
+                workspace: torch.Tensor | None = None, stream=None):
+    """k-th-neighbour squared radius r2 (and, with a lengthscale, the
+    transmission weights A = pi l sqrt(2 r2 / k)) of every point of q.
+    Returns r2, A or (r2, A)."""
+    lib = abi.load()
+    _require_cuda(q, "q", (2,))
+    m = q.shape[0]
+    b = ctypes.c_size_t(0)
+    abi.check(lib.lr_knn_workspace_size(m, ctypes.byref(b)), "lr_knn_workspace_size")
+    if workspace is None or workspace.numel() < b.value:
+        workspace = torch.empty(max(int(b.value), 1), dtype=torch.uint8, device=q.device)
+    r2 = torch.empty(m, dtype=torch.float32, device=q.device) if want_r2 else None
+    a = torch.empty(m, dtype=torch.float32, device=q.device) if lengthscale is not None else None
+    st = lib.gp_knn_density(q.data_ptr(), m, int(k), float(lengthscale or 0.0),
+                            r2.data_ptr() if r2 is not None else None, a.data_ptr() if a is not None else None,
+                            workspace.data_ptr(), workspace.numel(), _stream_handle(stream))
+    abi.check(st, "gp_knn_density")
+    if r2 is not None and a is not None:
+        return r2, a
+    return r2 if r2 is not None else a
+
+
 GRADS = ("v", "x", "y", "lengthscale", "variance", "lens", "sub")
 
 
