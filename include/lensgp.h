@@ -158,12 +158,12 @@ lr_status lens_raytrace(const lr_points* pts, float* beta_out, float* alpha_out,
 lr_status lens_jacobian(const lr_points* pts, float* jac_out, float* mu_out, lr_stream stream);
 
 /* ------------------------------------------------------------------------ */
-/* Gaussian-kernel reduction (Sec. 3.1 RBF kernel; Sec. 3.4 lazy T y)         */
+/* Gaussian-kernel reduction (Sec. 3.1 RBF kernel; Sec. 3.3 lazy T y)         */
 
 /*
  * out_i = sum_j variance * exp(-|x_i - y_j|^2 / (2 lengthscale^2)) v_j
  * (the RBF covariance of Sec. 3.1 with isotropic kernel Sigma = l^2 I,
- * reduced lazily without storing the n x m matrix, Sec. 3.4).
+ * reduced lazily without storing the n x m matrix, Sec. 3.3).
  *   query   the x_i; ray-traced first when query->lens != NULL
  *   source  the y_j, or NULL for a self-kernel (y = x after ray-tracing)
  *   v       device float[m][nrhs] (nrhs must be 1 in this version)
@@ -198,7 +198,7 @@ lr_status lr_matvec_layers_workspace_size(const lr_points* query, const lr_point
                                           size_t* bytes);
 
 /* ------------------------------------------------------------------------ */
-/* Pixel windows (Sec. 3.2) and the windowed transmission (Sec. 3.5)          */
+/* Pixel windows (Sec. 3.2) and the windowed transmission (Sec. 3.4)          */
 
 /*
  * Window covariances of a W x H grid of projected pixel centres p (device
@@ -226,7 +226,7 @@ lr_status gp_windowed_matvec(const float* p, const float* z, int64_t n, const lr
 lr_status lr_windowed_workspace_size(int64_t n, const lr_points* source, size_t* bytes);
 
 /*
- * Inducing-point density (Sec. 3.5, footnote to the covariance factorisation)
+ * Inducing-point density (Sec. 3.4, footnote to the covariance factorisation)
  * and the transmission weights it sets, for m points q (device float[m][2]):
  *   r2_out[i] = r_k(q_i)^2, the squared distance to the k-th closest OTHER
  *               point of q (the point itself excluded by index; coincident

@@ -204,13 +204,13 @@ def knn_r2(q, k, rows=None):
 
 
 def knn_density(q, k=20, rows=None):
-    """Inducing-point density rho = k / (pi r_k^2) (Sec. 3.5 footnote)."""
+    """Inducing-point density rho = k / (pi r_k^2) (Sec. 3.4 footnote)."""
     return k / (np.pi * knn_r2(q, k, rows))
 
 
 def transmission_weights(q, lengthscale, k=20, rows=None, density=None):
     """A_k = |2 pi Sigma|^(1/4) / sqrt(rho(q_k)) with Sigma = l^2 I in two
-    dimensions, i.e. sqrt(2 pi l^2 / rho) (Sec. 3.5). `density` overrides
+    dimensions, i.e. sqrt(2 pi l^2 / rho) (Sec. 3.4). `density` overrides
     the k-nearest-neighbour estimate."""
     rho = knn_density(q, k, rows) if density is None else np.asarray(density, np.float64)
     return np.sqrt(2.0 * np.pi * lengthscale ** 2 / rho)

@@ -452,7 +452,7 @@ ORC_API void orc_lens_jacobian(const double* xi, int64_t n, const orc_lens* L, c
 
 /* ------------------------------------------------------------------------ */
 /* Gaussian RBF kernel reduction (eq. for the Gaussian RBF, Sec. 3.1, with
- * isotropic kernel Sigma = l^2 I; Sec. 3.4 evaluates T y as this lazily
+ * isotropic kernel Sigma = l^2 I; Sec. 3.3 evaluates T y as this lazily
  * reduced sum):
  *   out_i    = sum_j var * exp(-|x_i - y_j|^2 / (2 l^2)) v_j,
  *   absout_i = sum_j |var exp(...) v_j|           (scale of the parity tolerance)
@@ -515,7 +515,7 @@ ORC_API void orc_pixel_shapes(const double* p, int32_t W, int32_t H, double* z) 
     }
 }
 
-/* Windowed transmission (Sec. 3.5, the transmission equation, with
+/* Windowed transmission (Sec. 3.4, the transmission equation, with
  * Sigma = l^2 I): T_ik = A_k G(p_i - q_k, Z_i + Sigma / 2), reduced as
  *   out_i = sum_k G(p_i - q_k, Z_i + Sigma / 2) v_k,
  * G(d, C) = exp(-d^T C^-1 d / 2) / (2 pi sqrt(det C)); the caller folds the
@@ -545,7 +545,7 @@ ORC_API void orc_windowed_matvec(const double* p, const double* z, int64_t n, co
   }
 }
 
-/* Inducing-point density (Sec. 3.5, footnote to the factorisation of the
+/* Inducing-point density (Sec. 3.4, footnote to the factorisation of the
  * covariance): rho(q_k) = k / (pi r_k^2) with r_k the distance from q_k to the
  * k-th closest OTHER point of the set (the point itself excluded by index;
  * coincident points count at distance 0). Writes r_k^2 for the rows listed

@@ -1,4 +1,4 @@
-// Inducing-point density by the k-th nearest neighbour (Sec. 3.5, footnote to
+// Inducing-point density by the k-th nearest neighbour (Sec. 3.4, footnote to
 // the factorisation of the covariance) and the transmission weights it sets:
 //   rho(q_i) = k / (pi r_k(q_i)^2),  A_i = |2 pi Sigma|^(1/4) / sqrt(rho)
 //                                        = pi l sqrt(2 r_k^2 / k)   (Sigma = l^2 I).

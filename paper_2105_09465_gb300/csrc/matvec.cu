@@ -1,7 +1,7 @@
 // Lazily evaluated Gaussian-kernel reduction
 //   out_i = sum_j var * exp(-|x_i - y_j|^2 / (2 l^2)) v_j
 // (RBF covariance with Sigma = l^2 I, Sec. 3.1; T y evaluated without storing
-// T, Sec. 3.4).
+// T, Sec. 3.3).
 //
 // Work decomposition: the n x m pair space is cut into tasks of
 // (a block of kRowsPerCta query rows) x (a chunk of consecutive source

@@ -1,6 +1,6 @@
 // Pixel windows and the windowed (non-stationary) transmission reduction of
 // the paper's image-plane model (Sec. 3.2 window-function and window-kernel
-// equations, Sec. 3.5 transmission equation):
+// equations, Sec. 3.4 transmission equation):
 //   Z_i = (a_i a_i^T + b_i b_i^T) / (4 pi)   from the projected pixel grid,
 //   out_i = sum_k G(p_i - q_k, Z_i + (l^2/2) I) v_k,
 //   G(d, C) = exp(-d^T C^-1 d / 2) / (2 pi sqrt(det C)),

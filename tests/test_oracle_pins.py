@@ -477,7 +477,7 @@ def test_windowed_point_limit_is_the_rbf_kernel(orc):
 
 
 def test_transmission_factorises_the_windowed_covariance(orc):
-    """Sec. 3.5: with A_k = |2 pi Sigma|^(1/4) / sqrt(n_q) on a dense grid,
+    """Sec. 3.4: with A_k = |2 pi Sigma|^(1/4) / sqrt(n_q) on a dense grid,
     sum_k T_ik T_jk -> |2 pi Sigma|^(1/2) G(p_i - p_j, Z_i + Sigma + Z_j) = K_ij / var (eq. covariance)."""
     rng = np.random.default_rng(23)
     ell = 0.1
@@ -544,7 +544,7 @@ def test_knn_density_of_a_uniform_lattice_corner_and_interior(orc):
 
 
 def test_transmission_weights_reproduce_the_rbf_kernel(orc):
-    """Sec. 3.5: with A_k = |2 pi Sigma|^(1/4) / sqrt(rho) and the exact
+    """Sec. 3.4: with A_k = |2 pi Sigma|^(1/4) / sqrt(rho) and the exact
     density 1/h^2 of a fine lattice, sum_k A_k^2 G(p_i - q_k, Sigma/2)
     G(p_j - q_k, Sigma/2) equals exp(-|p_i - p_j|^2 / (2 l^2)), the unit
     variance Gaussian RBF (Sec. 3.1)."""
