@@ -244,6 +244,78 @@ lr_status gp_knn_density(const float* q, int64_t m, int32_t k, float lengthscale
                          void* workspace, size_t workspace_bytes, lr_stream stream);
 lr_status lr_knn_workspace_size(int64_t m, size_t* bytes);
 
+/* ------------------------------------------------------------------------ */
+/* Likelihood and ELBO terms (Sec. 3.3 generative model, Sec. 3.6 ELBO,       */
+/* Sec. 3.7 mean-field proposal, Sec. 4.2 partial MVN proposal)               */
+/*
+ * The loss of one reparameterised draw is
+ *   nll(d | f) - ln p(y | alpha) + ln q(y)          (minus the ELBO estimate).
+ * Every scalar below is an FP64 sum taken in an order fixed by the sizes
+ * alone (bit-reproducible). Scalars are written to DEVICE memory. The
+ * functions taking a workspace need lr_elbo_workspace_size() bytes, 256-byte
+ * aligned; one workspace serves one call at a time on a stream.
+ */
+size_t lr_elbo_workspace_size(void);
+
+/*
+ * Gaussian pixel likelihood of supersampled model fluxes f (device float[n]):
+ * the model of pixel p is the mean of its ss x ss subpixels (grid != NULL,
+ * f in grid-point order, n = (nx ss)(ny ss); grid == NULL: one value per
+ * pixel), and
+ *   nll = sum_p (m_p - d_p)^2 / (2 s_p^2) + ln s_p  +  (P/2) ln 2 pi,
+ * s_p = sigma[p] (device float[P]) or sigma0 when sigma == NULL.
+ * Optional outputs: g_out[n] = d nll / d f = (m_p - d_p) / (s_p^2 ss^2) for
+ * every subpixel of p, model_out[P] = m_p. nll_out: device double[1].
+ */
+lr_status gp_gaussian_nll(const float* f, int64_t n, const lr_grid* grid, const float* data, const float* sigma,
+                          float sigma0, float* g_out, float* model_out, double* nll_out, void* workspace,
+                          size_t workspace_bytes, lr_stream stream);
+
+/*
+ * Diagonal-normal proposal of m source parameters (Sec. 3.7) with prior
+ * y ~ N(0, alpha^2 I) (Sec. 3.3): y_out = mu + sd * eps and
+ *   terms_out[0] = -ln p(y | alpha) = sum y^2 / (2 alpha^2) + m ln alpha + (m/2) ln 2 pi,
+ *   terms_out[1] = ln q(y) = sum (-eps^2 / 2 - ln sd) - (m/2) ln 2 pi.
+ * All arrays device float[m]; terms_out device double[2].
+ */
+lr_status gp_diag_normal_draw(const float* mu, const float* sd, const float* eps, int64_t m, float alpha,
+                              float* y_out, double* terms_out, void* workspace, size_t workspace_bytes,
+                              lr_stream stream);
+
+/*
+ * Gradients of  Loss = L(y) + w_prior (-ln p(y | alpha)) + w_q ln q(y)  with
+ * dL/dy = d_y, through y = mu + sd eps at fixed eps:
+ *   d_mu = d_y + w_prior y / alpha^2,   d_sd = d_mu * eps - w_q / sd,
+ *   d_alpha (device double[1]) = w_prior (m / alpha - sum y^2 / alpha^3).
+ */
+lr_status gp_diag_normal_vjp(const float* mu, const float* sd, const float* eps, int64_t m, float alpha,
+                             const float* d_y, double w_prior, double w_q, float* d_mu, float* d_sd,
+                             double* d_alpha, void* workspace, size_t workspace_bytes, lr_stream stream);
+
+/*
+ * Partial multivariate-normal proposal over D lens parameters and M
+ * source-plane parameters (Sec. 4.2): x = mu + L_full eps with
+ *   L_full = [[L, 0], [C, diag(sd)]],
+ * L device float[D][D] row-major (lower triangle read, positive diagonal),
+ * C device float[M][D], sd device float[M], mu, eps, x_out device float[D+M];
+ *   logq_out (device double[1]) = ln N(x | mu, L_full L_full^T)
+ *            = -|eps|^2 / 2 - sum ln L_ii - sum ln sd - ((D+M)/2) ln 2 pi.
+ * 1 <= D <= 32.
+ */
+lr_status gp_partial_mvn_draw(const float* mu, const float* L, const float* C, const float* sd, const float* eps,
+                              int32_t D, int64_t M, float* x_out, double* logq_out, void* workspace,
+                              size_t workspace_bytes, lr_stream stream);
+
+/*
+ * Gradients of Loss = L(x) + w_q ln q(x) with dL/dx = d_x (device float[D+M])
+ * at fixed eps: d_mu = d_x; d_L[i][j] = d_x[i] eps[j] for j <= i (0 above the
+ * diagonal) minus w_q / L_ii on it; d_C[j][l] = d_x[D+j] eps[l];
+ * d_sd[j] = d_x[D+j] eps[D+j] - w_q / sd[j]. No workspace.
+ */
+lr_status gp_partial_mvn_vjp(const float* L, const float* sd, const float* eps, int32_t D, int64_t M,
+                             const float* d_x, double w_q, float* d_mu, float* d_L, float* d_C, float* d_sd,
+                             lr_stream stream);
+
 /* Scratch bytes gp_kernel_matvec needs for these point sets on the current device. */
 lr_status lr_matvec_workspace_size(const lr_points* query, const lr_points* source, int32_t nrhs, size_t* bytes);
 

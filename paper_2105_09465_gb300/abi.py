@@ -100,6 +100,17 @@ SIGNATURES = {
     "gp_knn_density": (ctypes.c_int32, [_P, ctypes.c_int64, ctypes.c_int32, ctypes.c_float, _P, _P, _P,
                                         ctypes.c_size_t, _P]),
     "lr_knn_workspace_size": (ctypes.c_int32, [ctypes.c_int64, ctypes.POINTER(ctypes.c_size_t)]),
+    "lr_elbo_workspace_size": (ctypes.c_size_t, []),
+    "gp_gaussian_nll": (ctypes.c_int32, [_P, ctypes.c_int64, ctypes.POINTER(lr_grid), _P, _P, ctypes.c_float, _P, _P,
+                                         _P, _P, ctypes.c_size_t, _P]),
+    "gp_diag_normal_draw": (ctypes.c_int32, [_P, _P, _P, ctypes.c_int64, ctypes.c_float, _P, _P, _P, ctypes.c_size_t,
+                                             _P]),
+    "gp_diag_normal_vjp": (ctypes.c_int32, [_P, _P, _P, ctypes.c_int64, ctypes.c_float, _P, ctypes.c_double,
+                                            ctypes.c_double, _P, _P, _P, _P, ctypes.c_size_t, _P]),
+    "gp_partial_mvn_draw": (ctypes.c_int32, [_P, _P, _P, _P, _P, ctypes.c_int32, ctypes.c_int64, _P, _P, _P,
+                                             ctypes.c_size_t, _P]),
+    "gp_partial_mvn_vjp": (ctypes.c_int32, [_P, _P, _P, ctypes.c_int32, ctypes.c_int64, _P, ctypes.c_double, _P, _P,
+                                            _P, _P, _P]),
     "lr_windowed_workspace_size": (ctypes.c_int32, [ctypes.c_int64, ctypes.POINTER(lr_points),
                                                     ctypes.POINTER(ctypes.c_size_t)]),
     "gp_kernel_matvec_layers": (ctypes.c_int32, [ctypes.POINTER(lr_points), ctypes.POINTER(lr_points), ctypes.c_int32,

@@ -218,6 +218,103 @@ def knn_density(q: torch.Tensor, k: int = 20, lengthscale: float | None = None, 
     return r2 if r2 is not None else a
 
 
+# ---------------------------------------------------------------- likelihood and ELBO terms
+def _elbo_ws(device) -> torch.Tensor:
+    return torch.empty(int(abi.load().lr_elbo_workspace_size()), dtype=torch.uint8, device=device)
+
+
+def _f32(t: torch.Tensor | None, name: str, n: int | None = None):
+    if t is None:
+        return None
+    _require_cuda(t, name)
+    if n is not None and t.numel() != n:
+        raise ValueError(f"{name}: {t.numel()} elements, {n} expected")
+    return t.data_ptr()
+
+
+def gaussian_nll(f: torch.Tensor, data: torch.Tensor, sigma: torch.Tensor | float, grid=None, want_g: bool = True,
+                 want_model: bool = False, stream=None):
+    """(nll: float64 0-d device tensor, g, model) of the Gaussian pixel
+    likelihood of supersampled fluxes f (grid: the supersampled Grid, or None
+    for one value per pixel)."""
+    lib = abi.load()
+    n = f.numel()
+    P = data.numel()
+    dev_ = f.device
+    nll = torch.empty((), dtype=torch.float64, device=dev_)
+    g = torch.empty(n, dtype=torch.float32, device=dev_) if want_g else None
+    model = torch.empty(P, dtype=torch.float32, device=dev_) if want_model else None
+    sig_t = sigma if isinstance(sigma, torch.Tensor) else None
+    cg = ctypes.byref(abi.lr_grid(*grid.astuple())) if grid is not None else None
+    ws = _elbo_ws(dev_)
+    st = lib.gp_gaussian_nll(_f32(f, "f"), n, cg, _f32(data, "data"), _f32(sig_t, "sigma", P),
+                             float(0.0 if sig_t is not None else sigma), g.data_ptr() if g is not None else None,
+                             model.data_ptr() if model is not None else None, nll.data_ptr(), ws.data_ptr(),
+                             ws.numel(), _stream_handle(stream))
+    abi.check(st, "gp_gaussian_nll")
+    return nll, g, model
+
+
+def diag_normal_draw(mu, sd, eps, alpha: float, stream=None):
+    """(y, terms[2] float64 = [-ln p(y | alpha), ln q(y)])."""
+    lib = abi.load()
+    m = mu.numel()
+    y = torch.empty(m, dtype=torch.float32, device=mu.device)
+    terms = torch.empty(2, dtype=torch.float64, device=mu.device)
+    ws = _elbo_ws(mu.device)
+    st = lib.gp_diag_normal_draw(_f32(mu, "mu"), _f32(sd, "sd", m), _f32(eps, "eps", m), m, float(alpha),
+                                 y.data_ptr(), terms.data_ptr(), ws.data_ptr(), ws.numel(), _stream_handle(stream))
+    abi.check(st, "gp_diag_normal_draw")
+    return y, terms
+
+
+def diag_normal_vjp(mu, sd, eps, alpha: float, d_y, w_prior: float = 1.0, w_q: float = 1.0, stream=None):
+    """(d_mu, d_sd, d_alpha float64 0-d)."""
+    lib = abi.load()
+    m = mu.numel()
+    d_mu = torch.empty(m, dtype=torch.float32, device=mu.device)
+    d_sd = torch.empty(m, dtype=torch.float32, device=mu.device)
+    d_a = torch.empty((), dtype=torch.float64, device=mu.device)
+    ws = _elbo_ws(mu.device)
+    st = lib.gp_diag_normal_vjp(_f32(mu, "mu"), _f32(sd, "sd", m), _f32(eps, "eps", m), m, float(alpha),
+                                _f32(d_y, "d_y", m), float(w_prior), float(w_q), d_mu.data_ptr(), d_sd.data_ptr(),
+                                d_a.data_ptr(), ws.data_ptr(), ws.numel(), _stream_handle(stream))
+    abi.check(st, "gp_diag_normal_vjp")
+    return d_mu, d_sd, d_a
+
+
+def partial_mvn_draw(mu, L, C, sd, eps, stream=None):
+    """(x[D+M], logq float64 0-d) of the partial MVN proposal."""
+    lib = abi.load()
+    D = L.shape[0]
+    M = sd.numel()
+    x = torch.empty(D + M, dtype=torch.float32, device=mu.device)
+    lq = torch.empty((), dtype=torch.float64, device=mu.device)
+    ws = _elbo_ws(mu.device)
+    st = lib.gp_partial_mvn_draw(_f32(mu, "mu", D + M), _f32(L, "L", D * D), _f32(C, "C", M * D), _f32(sd, "sd"),
+                                 _f32(eps, "eps", D + M), D, M, x.data_ptr(), lq.data_ptr(), ws.data_ptr(),
+                                 ws.numel(), _stream_handle(stream))
+    abi.check(st, "gp_partial_mvn_draw")
+    return x, lq
+
+
+def partial_mvn_vjp(L, sd, eps, d_x, w_q: float = 1.0, stream=None):
+    """(d_mu[D+M], d_L[D, D], d_C[M, D], d_sd[M])."""
+    lib = abi.load()
+    D = L.shape[0]
+    M = sd.numel()
+    dv_ = L.device
+    d_mu = torch.empty(D + M, dtype=torch.float32, device=dv_)
+    d_L = torch.empty((D, D), dtype=torch.float32, device=dv_)
+    d_C = torch.empty((M, D), dtype=torch.float32, device=dv_)
+    d_sd = torch.empty(M, dtype=torch.float32, device=dv_)
+    st = lib.gp_partial_mvn_vjp(_f32(L, "L", D * D), _f32(sd, "sd"), _f32(eps, "eps", D + M), D, M,
+                                _f32(d_x, "d_x", D + M), float(w_q), d_mu.data_ptr(), d_L.data_ptr(),
+                                d_C.data_ptr(), d_sd.data_ptr(), _stream_handle(stream))
+    abi.check(st, "gp_partial_mvn_vjp")
+    return d_mu, d_L, d_C, d_sd
+
+
 GRADS = ("v", "x", "y", "lengthscale", "variance", "lens", "sub")
 
 
