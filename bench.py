@@ -39,6 +39,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-extensions", action="store_true", help="skip timing the kernels beyond the fused step")
     ap.add_argument("--serving-requests", type=int, default=32)
     ap.add_argument("--serving-iters", type=int, default=50)
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="target oracle CPU time for cpu_baseline")
@@ -269,6 +270,69 @@ def event_time(fn, n, stream, flush):
     return float(np.mean([a.elapsed_time(b) for a, b in evs]))
 
 
+def run_extensions(p, dev, rates, sm_max, flush, stream) -> dict:
+    """Kernels beyond the fused step, each timed alone on realistic-shaped
+    inputs (same lens, same inducing grid): windowed transmission over the
+    ray-traced pixel centres, three image-plane layers, k-NN density, lens
+    Jacobian, likelihood and ELBO terms."""
+    import torch
+
+    from paper_2105_09465_gb300 import api, workloads as W
+
+    ex2, fma, nsm = rates["ex2_per_clk"], rates["ffma2_lanes_per_clk"], rates["sm_count"]
+
+    def roof(pairs, ms, n_ex2, lanes):
+        per_clk = min(ex2 / n_ex2, fma / lanes)
+        peak = per_clk * nsm * sm_max * 1e6 / 1e9
+        ach = pairs / (ms * 1e-3) / 1e9
+        return {"ms": ms, "achieved": ach, "peak": peak, "unit": UNIT, "frac": ach / peak,
+                "basis": f"{n_ex2} MUFU.EX2 + {lanes} FP32 lanes per pair"}
+
+    nk = 20
+    out = {}
+    sub = torch.from_numpy(p.sub).to(dev)
+    pix = W.Grid(p.xgrid.nx, p.xgrid.ny, 1, p.xgrid.pix)
+    bp = api.lens_raytrace(api.Points(grid=pix, lens=p.lens, sub=sub))
+    z = api.pixel_shapes(bp, pix.nx, pix.ny)
+    s = api.Points(grid=p.ygrid)
+    v = torch.from_numpy(p.v).to(dev)
+    ms = event_time(lambda: api.gp_windowed_matvec(bp, z, s, v, p.lengthscale), nk, stream, flush)
+    out["windowed_matvec<grid>"] = dict(roof(pix.n * p.m, ms, 1, 4), n=pix.n, m=p.m,
+                                        workload=f"{pix.nx}x{pix.ny} ray-traced pixel centres with their "
+                                                 f"window covariances x {p.ygrid.nx}x{p.ygrid.ny} grid")
+    out["pixel_shapes"] = {"ms": event_time(lambda: api.pixel_shapes(bp, pix.nx, pix.ny), nk, stream, flush)}
+    # three image-plane layers (the paper's 10 / 4.47 / 2 mas ratios) on the supersampled points
+    beta = api.lens_raytrace(api.Points(grid=p.xgrid, lens=p.lens, sub=sub))
+    vl = torch.randn((3, p.m), generator=torch.Generator().manual_seed(5)).to(dev)
+    ls = [p.lengthscale, p.lengthscale * 0.447, p.lengthscale * 0.2]
+    ms = event_time(lambda: api.gp_kernel_matvec_layers(api.Points(xy=beta), s, vl, ls, [1.0, 0.5, 0.25]), nk,
+                    stream, flush)
+    out["matvec_layers<grid> x3"] = dict(roof(p.pairs, ms, 3, 10), layers=3,
+                                         note="pairs counted once; 3 exponentials per pair")
+    out["knn_density k=20"] = {"ms": event_time(lambda: api.knn_density(beta, 20, lengthscale=p.lengthscale), nk,
+                                                stream, flush), "points": p.n}
+    qj = api.Points(grid=p.xgrid, lens=p.lens, sub=sub)
+    out["lens_jacobian"] = {"ms": event_time(lambda: api.lens_jacobian(qj), nk, stream, flush), "points": p.n,
+                            "subhalo_pairs": p.n * len(p.sub)}
+    f = torch.randn(p.n, device=dev)
+    d = torch.randn(p.xgrid.nx * p.xgrid.ny, device=dev)
+    out["gaussian_nll"] = {"ms": event_time(lambda: api.gaussian_nll(f, d, 0.1, grid=p.xgrid), nk, stream, flush),
+                           "pixels": int(d.numel()), "subpixels": p.n}
+    m3 = 3 * p.n
+    mu, sd, eps = torch.randn(m3, device=dev), torch.rand(m3, device=dev) + 0.01, torch.randn(m3, device=dev)
+    out["diag_normal_draw+vjp"] = {
+        "ms": event_time(lambda: (api.diag_normal_draw(mu, sd, eps, 1.0), api.diag_normal_vjp(mu, sd, eps, 1.0, eps)),
+                         nk, stream, flush), "params": m3}
+    D, M = 7, p.m
+    L = (torch.eye(D) * 0.01).to(dev)
+    C = torch.randn((M, D), device=dev) * 0.01
+    sd2, e2 = torch.rand(M, device=dev) + 0.01, torch.randn(D + M, device=dev)
+    out["partial_mvn_draw+vjp"] = {
+        "ms": event_time(lambda: (api.partial_mvn_draw(e2, L, C, sd2, e2), api.partial_mvn_vjp(L, sd2, e2, e2)), nk,
+                         stream, flush), "D": D, "M": M}
+    return out
+
+
 def run_ours(args):
     import torch
 
@@ -453,6 +517,8 @@ def run_ours(args):
         "clocks": clk,
         "pipe_rates": rates,
     }
+    if not args.no_extensions:
+        line["extensions"] = run_extensions(p, dev, rates, sm_max, flush, stream)
     if world == 1 and not args.no_serving:
         line["serving"] = run_serving(args.serving_requests, args.serving_iters)
         line["p50_latency_s"] = line["serving"]["batched"]["p50_s"]
