@@ -429,10 +429,12 @@ def run_ours(args):
     kern = {}
     kern["matvec_kernel<grid> fwd"] = (
         event_time(lambda: api.gp_kernel_matvec(qx, s, v, p.lengthscale, p.variance, out=out, workspace=ws2), nk,
-                   stream, flush), p.pairs, 32.0, "pairs: 1 MUFU.EX2 + 3 FP32 lanes each")
+                   stream, flush), p.pairs, 32.0, "pairs: 1 MUFU.EX2 + 2 FP32 lanes each (split exponent)")
     kern["bwd_rows_kernel<grid, fused d_v>"] = (
         event_time(lambda: api.gp_kernel_matvec_bwd(qx, s, v, p.lengthscale, p.variance, g, want=["x", "v"]), nk,
-                   stream, flush), p.pairs, 128.0 / 6.5, "pairs: 1 MUFU.EX2 + 6.5 FP32 lanes each")
+                   stream, flush), p.pairs, 128.0 / 5.7,
+        "pairs: 1 MUFU.EX2 + 5.7 FP32 lanes each (split exponent: 5 per pair, 0.56 per-sub-segment moments, "
+        "0.12 d_v reduce-scatter)")
     rt_ms = event_time(lambda: api.lens_raytrace(q), nk, stream, flush)
     vjp_ms = event_time(lambda: api.lens_raytrace_vjp(q, dbeta), nk, stream, flush)
 

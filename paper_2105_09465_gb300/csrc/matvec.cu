@@ -10,8 +10,8 @@
 // shared memory in a pair-packed layout and streamed with double buffering,
 // so that every instruction of the inner loop works on two sources at once
 // (packed f32x2 add/mul/fma) and each exp is one MUFU.EX2.
-// Per pair: 3 packed-FP32 lane ops (grid sources, uniform y per tile) or 5
-// (explicit sources) plus one exp2.
+// Per pair: 2 packed-FP32 lane ops (grid sources: uniform y per tile and a
+// split exponent) or 5 (explicit sources) plus one exp2.
 // Accuracy: per tile each thread sums <= kTile/2 terms per lane in plain
 // FP32, then folds the tile total into a Kahan-compensated running sum. With
 // several chunks per row the chunk totals are merged by a second kernel in
@@ -54,19 +54,21 @@ __device__ __forceinline__ void tile_range(const SrcDesc& S, int t, int64_t& j0,
 }
 
 // Loads source pair `p` of tile t into registers (zero weight past the end).
-// Grid tiles are cut into sub-segments of kSeg columns; grid abscissae are
-// stored as sc (x_j - o) relative to the sub-segment's centre column o, which
-// keeps every scaled coordinate of a contributing pair small (FP32 error
-// ~1e-6 of a kernel length) while letting one FMA form the exponent.
-constexpr int kSeg = 16;
+// Grid tiles are cut into sub-segments of kSeg columns. A grid source is
+// stored as its scaled abscissa x' = sc (x_j - o), relative to the
+// sub-segment's centre column o, and its weight folded with the source half
+// of the split exponent, v~ = v 2^-x'^2 (exponent splitting below). The split
+// is used only when |x'| <= kSplitXMax inside a sub-segment, so that
+// v~ >= 2^-30 v and the split terms stay small; otherwise (-x', v) is stored.
+constexpr int kSeg = kSplitSeg;
 
 __device__ __forceinline__ float seg_origin(const GridDev& g, int c0, int sg) {
   return grid_x(g, c0 + kSeg * sg + kSeg / 2);
 }
 
 template <bool GRID>
-__device__ __forceinline__ void load_pair(const SrcDesc& S, const float* __restrict__ v, float sc, int t, int p,
-                                          float4& P, float2& V) {
+__device__ __forceinline__ void load_pair(const SrcDesc& S, const float* __restrict__ v, float sc, bool split, int t,
+                                          int p, float4& P, float2& V) {
   int64_t j0;
   int cnt, grow;
   tile_range(S, t, j0, cnt, grow);
@@ -76,8 +78,14 @@ __device__ __forceinline__ void load_pair(const SrcDesc& S, const float* __restr
     const float o = seg_origin(S.g, c0, a / kSeg);
     const float xa = (a < cnt) ? sc * (grid_x(S.g, c0 + a) - o) : 0.f;
     const float xb = (b < cnt) ? sc * (grid_x(S.g, c0 + b) - o) : 0.f;
-    // (x', v) of the pair in one 16-byte word: one shared load per pair
-    P = make_float4(-xa, -xb, (a < cnt) ? __ldg(v + j0 + a) : 0.f, (b < cnt) ? __ldg(v + j0 + b) : 0.f);
+    float va = (a < cnt) ? __ldg(v + j0 + a) : 0.f;
+    float vb = (b < cnt) ? __ldg(v + j0 + b) : 0.f;
+    // (x', v~) of the pair in one 16-byte word (one shared load per pair);
+    // the unsplit form stores (-x', v)
+    if (split)
+      P = make_float4(xa, xb, va * ex2_approx(-xa * xa), vb * ex2_approx(-xb * xb));
+    else
+      P = make_float4(-xa, -xb, va, vb);
     V = f2(0.f, 0.f);
     return;
   } else {
@@ -124,7 +132,7 @@ __device__ __forceinline__ void matvec_body(const MvArgs& A, int rb, int chunk, 
   float4 P;
   float2 V;
   if (t0 < t1) {
-    load_pair<GRID>(A.src, A.v, A.sc, t0, tid, P, V);
+    load_pair<GRID>(A.src, A.v, A.sc, A.split != 0, t0, tid, P, V);
     sP[0][tid] = P;
     sV[0][tid] = V;
   }
@@ -132,42 +140,76 @@ __device__ __forceinline__ void matvec_body(const MvArgs& A, int rb, int chunk, 
 
   for (int t = t0; t < t1; ++t) {
     const int buf = (t - t0) & 1;
-    if (t + 1 < t1) load_pair<GRID>(A.src, A.v, A.sc, t + 1, tid, P, V);  // in flight during compute
+    if (t + 1 < t1) load_pair<GRID>(A.src, A.v, A.sc, A.split != 0, t + 1, tid, P, V);  // in flight during compute
     int64_t j0;
     int cnt, grow;
     tile_range(A.src, t, j0, cnt, grow);
     const int np = (cnt + 1) >> 1;
     if (GRID) {
-      // exponent -(sc^2)(dx^2 + dy^2) = -(dx'^2 + dy'^2) with tile-local scaled dx'
+      // Exponent splitting: with scaled tile-local q = sc (x_i - o),
+      // x' = sc (x_j - o) and dy' = sc (y_i - y_t),
+      //   -(q - x')^2 - dy'^2 = [2 q x' - q^2 - dy'^2] - x'^2,
+      // so k v = 2^(2 q x' + a_i) * v~ with a_i = -(q^2 + dy'^2) per row and
+      // v~ = v 2^-x'^2 per source: ONE packed FMA forms the exponent of two
+      // pairs and one more accumulates. The bracket is at most x'^2 <= 30.25,
+      // so 2^bracket cannot overflow; for the pairs that contribute, its FP32
+      // error is a few 1e-6 absolute (a relative error of k below 1e-5).
       const float yt = grid_y(A.src.g, grow);
       const int c0 = (int)(j0 - (int64_t)grow * A.src.g.W);
-      float2 dy2[kMvR];
+      float dy2[kMvR];
 #pragma unroll
       for (int r = 0; r < kMvR; ++r) {
         const float dy = A.sc * (yq[r].x - yt);
-        dy2[r] = f2(dy * dy, dy * dy);
+        dy2[r] = dy * dy;
       }
       const int nsg = (cnt + kSeg - 1) / kSeg;
-      for (int sg = 0; sg < nsg; ++sg) {
-        const float o = seg_origin(A.src.g, c0, sg);
-        float2 qx[kMvR];
-#pragma unroll
-        for (int r = 0; r < kMvR; ++r) {
-          const float q = A.sc * (xq[r].x - o);
-          qx[r] = f2(q, q);
-        }
-#pragma unroll
-        for (int pp = 0; pp < kSeg / 2; ++pp) {
-          const int p = sg * (kSeg / 2) + pp;
-          const float4 Q = sP[buf][p];
-          const float2 W = f2(Q.z, Q.w);
-          const float2 nx = f2(Q.x, Q.y);
+      if (!A.split) {
+        // unsplit: dx' = q - x', exponent -(dx'^2 + dy'^2)
+        for (int sg = 0; sg < nsg; ++sg) {
+          const float o = seg_origin(A.src.g, c0, sg);
+          float2 qx[kMvR], d2[kMvR];
 #pragma unroll
           for (int r = 0; r < kMvR; ++r) {
-            const float2 dx = __fadd2_rn(qx[r], nx);
-            const float2 t = __ffma2_rn(dx, dx, dy2[r]);
-            const float2 k = f2(ex2_approx(-t.x), ex2_approx(-t.y));
-            acc[r] = __ffma2_rn(k, W, acc[r]);
+            const float q = A.sc * (xq[r].x - o);
+            qx[r] = f2(q, q);
+            d2[r] = f2(dy2[r], dy2[r]);
+          }
+#pragma unroll
+          for (int pp = 0; pp < kSeg / 2; ++pp) {
+            const float4 Q = sP[buf][sg * (kSeg / 2) + pp];
+            const float2 W = f2(Q.z, Q.w);
+            const float2 nx = f2(Q.x, Q.y);
+#pragma unroll
+            for (int r = 0; r < kMvR; ++r) {
+              const float2 dx = __fadd2_rn(qx[r], nx);
+              const float2 t = __ffma2_rn(dx, dx, d2[r]);
+              const float2 k = f2(ex2_approx(-t.x), ex2_approx(-t.y));
+              acc[r] = __ffma2_rn(k, W, acc[r]);
+            }
+          }
+        }
+      } else {
+        for (int sg = 0; sg < nsg; ++sg) {
+          const float o = seg_origin(A.src.g, c0, sg);
+          float2 q2[kMvR], ar[kMvR];
+#pragma unroll
+          for (int r = 0; r < kMvR; ++r) {
+            const float q = A.sc * (xq[r].x - o);
+            const float a = -fmaf(q, q, dy2[r]);
+            q2[r] = f2(2.f * q, 2.f * q);
+            ar[r] = f2(a, a);
+          }
+#pragma unroll
+          for (int pp = 0; pp < kSeg / 2; ++pp) {
+            const float4 Q = sP[buf][sg * (kSeg / 2) + pp];
+            const float2 W = f2(Q.z, Q.w);
+            const float2 X = f2(Q.x, Q.y);
+#pragma unroll
+            for (int r = 0; r < kMvR; ++r) {
+              const float2 e = __ffma2_rn(q2[r], X, ar[r]);
+              const float2 k = f2(ex2_approx(e.x), ex2_approx(e.y));
+              acc[r] = __ffma2_rn(k, W, acc[r]);
+            }
           }
         }
       }
@@ -403,6 +445,7 @@ lr_status make_mv_problem(const float2* x, int64_t n, const float2* ys, const lr
     a.v = v;
     a.neg_c = (float)(-1.4426950408889634 / (2.0 * (double)ell * (double)ell));
     a.sc = (float)sqrt(1.4426950408889634 / (2.0 * (double)ell * (double)ell));
+    a.split = ys ? 0 : grid_split_ok(a.src.g, a.sc);
     a.variance = var;
     a.chunks = P.chunks;
     a.out = out;
@@ -491,6 +534,7 @@ extern "C" lr_status gp_kernel_matvec(const lr_points* query, const lr_points* s
   A.v = v;
   A.neg_c = (float)(-1.4426950408889634 / (2.0 * (double)lengthscale * (double)lengthscale));
   A.sc = (float)sqrt(1.4426950408889634 / (2.0 * (double)lengthscale * (double)lengthscale));
+  A.split = S.xy ? 0 : grid_split_ok(S.g, A.sc);
   A.variance = variance;
   A.chunks = P.chunks;
   A.out = out;

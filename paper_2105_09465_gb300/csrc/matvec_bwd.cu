@@ -46,7 +46,7 @@ __device__ __forceinline__ void bw_tile_range(const BwSrc& S, int t, int64_t& j0
   }
 }
 
-template <bool GRID, bool SELF>
+template <bool GRID, bool SELF, bool SPLIT>
 __device__ __forceinline__ void bw_load_pair(const BwArgs& A, int t, int p, float4& P, float2& V, float2& Gp) {
   int64_t j0;
   int cnt, grow;
@@ -56,8 +56,18 @@ __device__ __forceinline__ void bw_load_pair(const BwArgs& A, int t, int p, floa
     // scaled tile-local abscissae (see the forward pass)
     const int c0 = (int)(j0 - (int64_t)grow * A.src.g.W);
     const float o = grid_x(A.src.g, c0 + kBwSeg * (a / kBwSeg) + kBwSeg / 2);
-    P = make_float4((a < cnt) ? -A.sc * (grid_x(A.src.g, c0 + a) - o) : 0.f,
-                    (b < cnt) ? -A.sc * (grid_x(A.src.g, c0 + b) - o) : 0.f, 0.f, 0.f);
+    const float xa = (a < cnt) ? A.sc * (grid_x(A.src.g, c0 + a) - o) : 0.f;
+    const float xb = (b < cnt) ? A.sc * (grid_x(A.src.g, c0 + b) - o) : 0.f;
+    if (SPLIT) {
+      // split exponent: v~ = v 2^-x'^2 and its first two x' moments
+      const float va = (a < cnt) ? __ldg(A.v + j0 + a) * ex2_approx(-xa * xa) : 0.f;
+      const float vb = (b < cnt) ? __ldg(A.v + j0 + b) * ex2_approx(-xb * xb) : 0.f;
+      P = make_float4(xa, xb, va, vb);
+      V = f2(va * xa, vb * xb);
+      Gp = f2(va * xa * xa, vb * xb * xb);
+      return;
+    }
+    P = make_float4(-xa, -xb, 0.f, 0.f);
   } else {
     const float2 pa = (a < cnt) ? __ldg(A.src.xy + j0 + a) : f2(0.f, 0.f);
     const float2 pb = (b < cnt) ? __ldg(A.src.xy + j0 + b) : f2(0.f, 0.f);
@@ -85,7 +95,7 @@ struct BwCfg {
   using Smem = BwSmem<R, K>;
 };
 
-template <bool GRID, bool SELF, bool DV>
+template <bool GRID, bool SELF, bool DV, bool SPLIT>
 __device__ __forceinline__ void bwd_rows_body(const BwArgs& A, int rb, int chunk,
                                               typename BwCfg<GRID, SELF, DV>::Smem& sm) {
   constexpr int kBwR = BwCfg<GRID, SELF, DV>::R;
@@ -126,16 +136,16 @@ __device__ __forceinline__ void bwd_rows_body(const BwArgs& A, int rb, int chunk
   float4 P;
   float2 V, Gp = f2(0.f, 0.f);
   if (t0 < t1) {
-    bw_load_pair<GRID, SELF>(A, t0, tid, P, V, Gp);
+    bw_load_pair<GRID, SELF, SPLIT>(A, t0, tid, P, V, Gp);
     sP[0][tid] = P;
     sV[0][tid] = V;
-    if (SELF) sG[0][tid] = Gp;
+    if (SELF || SPLIT) sG[0][tid] = Gp;
   }
   __syncthreads();
 
   for (int t = t0; t < t1; ++t) {
     const int buf = (t - t0) & 1;
-    if (t + 1 < t1) bw_load_pair<GRID, SELF>(A, t + 1, tid, P, V, Gp);
+    if (t + 1 < t1) bw_load_pair<GRID, SELF, SPLIT>(A, t + 1, tid, P, V, Gp);
     int64_t j0;
     int cnt, grow;
     bw_tile_range(A.src, t, j0, cnt, grow);
@@ -155,6 +165,71 @@ __device__ __forceinline__ void bwd_rows_body(const BwArgs& A, int rb, int chunk
       }
       constexpr bool fuse_dv = DV;
       const int nsg = (cnt + kBwSeg - 1) / kBwSeg;
+      if (SPLIT) {
+      for (int sg = 0; sg < nsg; ++sg) {
+        // Split exponent (see the forward pass): k v = 2^(2 q x' + a_i) v~.
+        // Per pair one packed FMA forms the exponent and three accumulate the
+        // x' moments S0 = sum k~ v~, S1 = sum k~ v~ x', S2 = sum k~ v~ x'^2 of
+        // the sub-segment, from which, with dx' = q - x',
+        //   sum k v = S0, sum k v dx' = q S0 - S1,
+        //   sum k v (dx'^2 + dy'^2) = (q^2 + dy'^2) S0 - 2 q S1 + S2;
+        // the fused d_v sums k~ g and scales by 2^-x'^2 per source at the end.
+        const float o = grid_x(A.src.g, c0 + kBwSeg * sg + kBwSeg / 2);
+        float2 q2[kBwR], ar[kBwR], S0[kBwR], S1[kBwR], S2[kBwR];
+#pragma unroll
+        for (int r = 0; r < kBwR; ++r) {
+          const float q = A.sc * (xq[r].x - o);
+          const float a = -fmaf(q, q, dy2[r].x);
+          q2[r] = f2(2.f * q, 2.f * q);
+          ar[r] = f2(a, a);
+          S0[r] = S1[r] = S2[r] = f2(0.f, 0.f);
+        }
+        float kgs[kBwSeg];
+#pragma unroll
+        for (int pp = 0; pp < kBwSeg / 2; ++pp) {
+          const int p = sg * (kBwSeg / 2) + pp;
+          const float4 Q = sP[buf][p];
+          const float2 X = f2(Q.x, Q.y), W0 = f2(Q.z, Q.w);
+          const float2 W1 = sV[buf][p], W2 = sG[buf][p];
+          float2 kg = f2(0.f, 0.f);
+#pragma unroll
+          for (int r = 0; r < kBwR; ++r) {
+            const float2 e = __ffma2_rn(q2[r], X, ar[r]);
+            const float2 k = f2(ex2_approx(e.x), ex2_approx(e.y));
+            S0[r] = __ffma2_rn(k, W0, S0[r]);
+            S1[r] = __ffma2_rn(k, W1, S1[r]);
+            S2[r] = __ffma2_rn(k, W2, S2[r]);
+            if (fuse_dv) kg = __ffma2_rn(k, gq[r], kg);
+          }
+          kgs[2 * pp] = kg.x;
+          kgs[2 * pp + 1] = kg.y;
+        }
+#pragma unroll
+        for (int r = 0; r < kBwR; ++r) {
+          const float q = 0.5f * q2[r].x;
+          const float s0 = S0[r].x + S0[r].y, s1 = S1[r].x + S1[r].y, s2 = S2[r].x + S2[r].y;
+          acc[r][0].x += s0;
+          acc[r][1].x += fmaf(q, s0, -s1);
+          acc[r][3].x += fmaf(fmaf(q, q, dy2[r].x), s0, fmaf(-2.f * q, s1, s2));
+        }
+        if (fuse_dv) {
+          const int lane = tid & 31;
+#pragma unroll
+          for (int h = kBwSeg / 2, m = 16; h >= 1; h >>= 1, m >>= 1) {
+            const bool upper = (lane & m) != 0;
+#pragma unroll
+            for (int i = 0; i < h; ++i) {
+              const float lo = kgs[i], hi = kgs[i + h];
+              const float send = upper ? lo : hi;
+              const float keep = upper ? hi : lo;
+              kgs[i] = keep + __shfl_xor_sync(0xffffffffu, send, m);
+            }
+          }
+          kgs[0] += __shfl_xor_sync(0xffffffffu, kgs[0], 1);
+          if ((lane & 1) == 0) sm.dvred[tid >> 5][sg * kBwSeg + ((lane >> 1) & 15)] = kgs[0];
+        }
+      }
+      } else {
       for (int sg = 0; sg < nsg; ++sg) {
         const float o = grid_x(A.src.g, c0 + kBwSeg * sg + kBwSeg / 2);
         float2 qx[kBwR];
@@ -204,6 +279,7 @@ __device__ __forceinline__ void bwd_rows_body(const BwArgs& A, int rb, int chunk
           if ((lane & 1) == 0) sm.dvred[tid >> 5][sg * kBwSeg + ((lane >> 1) & 15)] = kgs[0];
         }
       }
+      }
       if (fuse_dv) {
         __syncthreads();
         // combine the warps in order; row block rb owns these columns of dv_part
@@ -212,6 +288,11 @@ __device__ __forceinline__ void bwd_rows_body(const BwArgs& A, int rb, int chunk
           float sdv = sm.dvred[0][j];
 #pragma unroll
           for (int w = 1; w < kBwThreads / 32; ++w) sdv += sm.dvred[w][j];
+          if (SPLIT) {
+            const float4 Q = sP[buf][j >> 1];
+            const float xj = (j & 1) ? Q.y : Q.x;
+            sdv *= ex2_approx(-xj * xj);
+          }
           dst[j] = sdv;
         }
       }
@@ -258,7 +339,7 @@ __device__ __forceinline__ void bwd_rows_body(const BwArgs& A, int rb, int chunk
     if (t + 1 < t1) {
       sP[buf ^ 1][tid] = P;
       sV[buf ^ 1][tid] = V;
-      if (SELF) sG[buf ^ 1][tid] = Gp;
+      if (SELF || SPLIT) sG[buf ^ 1][tid] = Gp;
     }
     __syncthreads();
   }
@@ -273,23 +354,23 @@ __device__ __forceinline__ void bwd_rows_body(const BwArgs& A, int rb, int chunk
   }
 }
 
-template <bool GRID, bool SELF, bool DV>
+template <bool GRID, bool SELF, bool DV, bool SPLIT = false>
 __global__ void __launch_bounds__(kBwThreads) bwd_rows_kernel(const __grid_constant__ BwArgs A) {
   __shared__ __align__(16) typename BwCfg<GRID, SELF, DV>::Smem sm;
   const int rb = blockIdx.x / A.chunks;
-  bwd_rows_body<GRID, SELF, DV>(A, rb, blockIdx.x - rb * A.chunks, sm);
+  bwd_rows_body<GRID, SELF, DV, SPLIT>(A, rb, blockIdx.x - rb * A.chunks, sm);
 }
 
-// Batched form; every problem of one launch has the same kind (grid,
-// explicit, or explicit self-kernel).
-template <bool GRID, bool SELF, bool DV>
+// Batched form; every problem of one launch has the same kind (grid with or
+// without the split exponent and fused d_v, explicit, explicit self-kernel).
+template <bool GRID, bool SELF, bool DV, bool SPLIT = false>
 __global__ void __launch_bounds__(kBwThreads) bwd_rows_batched_kernel(const __grid_constant__ Batch<BwArgs> B) {
   __shared__ __align__(16) typename BwCfg<GRID, SELF, DV>::Smem sm;
   const int k = batch_find(B, blockIdx.x);
   const BwArgs& A = B.p[k];
   const int local = blockIdx.x - B.start[k];
   const int rb = local / A.chunks;
-  bwd_rows_body<GRID, SELF, DV>(A, rb, local - rb * A.chunks, sm);
+  bwd_rows_body<GRID, SELF, DV, SPLIT>(A, rb, local - rb * A.chunks, sm);
 }
 
 // Per-row merge of chunk partials, the per-row gradients, and per-block FP64
@@ -423,7 +504,9 @@ lr_status launch_dv_merge_batched(const DvMergeP* p, int count, cudaStream_t s) 
 }
 
 lr_status launch_bwd_rows_batched(const BwArgs* p, int count, cudaStream_t s) {
-  for (int kind = 0; kind < 4; ++kind) {  // 0: grid, 1: explicit, 2: explicit self-kernel, 3: grid + fused d_v
+  // kinds: 0 grid, 1 explicit, 2 explicit self-kernel, 3 grid + fused d_v,
+  // 4 grid split, 5 grid split + fused d_v
+  for (int kind = 0; kind < 6; ++kind) {
     Batch<BwArgs> B;
     B.count = 0;
     int64_t tot = 0;
@@ -438,15 +521,21 @@ lr_status launch_bwd_rows_batched(const BwArgs* p, int count, cudaStream_t s) {
             bwd_rows_batched_kernel<false, false, false><<<(unsigned)tot, kBwThreads, 0, s>>>(B);
           else if (kind == 2)
             bwd_rows_batched_kernel<false, true, false><<<(unsigned)tot, kBwThreads, 0, s>>>(B);
-          else
+          else if (kind == 3)
             bwd_rows_batched_kernel<true, false, true><<<(unsigned)tot, kBwThreads, 0, s>>>(B);
+          else if (kind == 4)
+            bwd_rows_batched_kernel<true, false, false, true><<<(unsigned)tot, kBwThreads, 0, s>>>(B);
+          else
+            bwd_rows_batched_kernel<true, false, true, true><<<(unsigned)tot, kBwThreads, 0, s>>>(B);
           LR_CHECK_CUDA(cudaGetLastError());
         }
         B.count = 0;
         tot = 0;
       }
       if (i == count) break;
-      const int pk = p[i].src.xy == nullptr ? (p[i].dv_part ? 3 : 0) : (p[i].gs != nullptr ? 2 : 1);
+      const bool dvk = p[i].dv_part != nullptr;
+      const int pk = p[i].src.xy == nullptr ? (p[i].split ? (dvk ? 5 : 4) : (dvk ? 3 : 0))
+                                            : (p[i].gs != nullptr ? 2 : 1);
       if (pk != kind) continue;
       B.p[B.count] = p[i];
       B.start[B.count] = (int32_t)tot;
@@ -517,8 +606,14 @@ static lr_status plan_rows(int64_t n, int64_t m, bool grid, const lr_grid* g, bo
   LR_CHECK_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
   if (self)
     LR_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, bwd_rows_kernel<false, true, false>, kBwThreads, 0));
-  else if (dv)
+  else if (dv) {
+    // the split and unsplit variants: plan for the lower occupancy of the two
+    int occ2 = 1;
     LR_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, bwd_rows_kernel<true, false, true>, kBwThreads, 0));
+    LR_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, bwd_rows_kernel<true, false, true, true>,
+                                                                kBwThreads, 0));
+    occ = occ < occ2 ? occ : occ2;
+  }
   else
     LR_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, bwd_rows_kernel<false, false, false>, kBwThreads, 0));
   const int32_t chunks = plan_chunks(p.row_blocks, p.n_tiles, occ, n_sm);
@@ -559,6 +654,7 @@ lr_status make_rows_problem(const float2* x, int64_t n, const float2* ys, const 
   const double c = 1.4426950408889634 / (2.0 * (double)ell * (double)ell);
   a.neg_c = (float)(-c);
   a.sc = (float)sqrt(c);
+  a.split = ys ? 0 : grid_split_ok(a.src.g, a.sc);
   a.chunks = R.chunks;
   a.K = R.K;
   a.rows_per_cta = R.rows_per_cta;
@@ -612,8 +708,12 @@ static lr_status launch_rows(const float2* x, int64_t n, const float2* ys, const
                                      ws, &A, &M, &S, &D, &b);
     if (st != LR_OK) return st;
     const unsigned grid = (unsigned)(((n + A.rows_per_cta - 1) / A.rows_per_cta) * A.chunks);
-    if (ys == nullptr && A.dv_part)
+    if (ys == nullptr && A.dv_part && A.split)
+      bwd_rows_kernel<true, false, true, true><<<grid, kBwThreads, 0, s>>>(A);
+    else if (ys == nullptr && A.dv_part)
       bwd_rows_kernel<true, false, true><<<grid, kBwThreads, 0, s>>>(A);
+    else if (ys == nullptr && A.split)
+      bwd_rows_kernel<true, false, false, true><<<grid, kBwThreads, 0, s>>>(A);
     else if (ys == nullptr)
       bwd_rows_kernel<true, false, false><<<grid, kBwThreads, 0, s>>>(A);
     else
@@ -646,6 +746,7 @@ static lr_status launch_rows(const float2* x, int64_t n, const float2* ys, const
   const double c = 1.4426950408889634 / (2.0 * (double)ell * (double)ell);
   A.neg_c = (float)(-c);
   A.sc = (float)sqrt(c);
+  A.split = 0;
   A.chunks = R.chunks;
   A.K = R.K;
   A.rows_per_cta = R.rows_per_cta;

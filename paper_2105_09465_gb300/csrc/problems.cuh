@@ -8,6 +8,19 @@
 
 namespace lr {
 
+// ---- exponent splitting of grid-source tiles (matvec.cu, matvec_bwd.cu)
+// A grid tile is cut into sub-segments of kSplitSeg columns with scaled
+// abscissae x' = sc (x_j - o) about each sub-segment's centre o. Splitting
+// the exponent as [2 q x' - q^2 - dy'^2] - x'^2 is exact in real arithmetic;
+// in FP32 it needs |x'| bounded, which holds when the length scale is not
+// much below the grid spacing (l >= 1.24 h). Otherwise the kernels use the
+// unsplit form.
+constexpr int kSplitSeg = 16;
+constexpr float kSplitXMax = 5.5f;
+inline int32_t grid_split_ok(const GridDev& g, float sc) {
+  return sc * g.h * (float)(kSplitSeg / 2) <= kSplitXMax ? 1 : 0;
+}
+
 // ---- forward reduction (matvec.cu)
 constexpr int kMvThreads = 128;
 constexpr int kMvR = 8;                         // query rows per thread
@@ -30,6 +43,7 @@ struct MvArgs {
   const float* v;    // [m]
   float neg_c;       // -log2(e) / (2 l^2)
   float sc;          // sqrt(log2(e) / (2 l^2)): scale of the tile-local grid coordinates
+  int32_t split;     // grid sources: split exponent (grid_split_ok)
   float variance;
   int32_t chunks;    // column chunks per row block
   float* out;        // [n] when chunks == 1
@@ -49,7 +63,7 @@ struct MergeP {
 constexpr int kBwThreads = 128;
 constexpr int kBwR = 4;                     // rows per thread
 constexpr int kBwRows = kBwThreads * kBwR;  // 512 rows per CTA
-constexpr int kBwRdv = 8;                   // rows per thread with the fused d_v reduction                   // rows per thread with the fused d_v reduction                   // rows per thread with the fused d_v reduction                   // rows per thread with the fused d_v reduction                   // rows per thread with the fused d_v reduction
+constexpr int kBwRdv = 8;                   // rows per thread with the fused d_v reduction
 constexpr int kBwTile = 256;
 constexpr int kBwPairs = kBwTile / 2;
 constexpr int kMergeThreads = 256;
@@ -69,6 +83,7 @@ struct BwArgs {
   const float* gs;  // [m] source-side g (self-kernel only: g of the same points)
   float neg_c;      // -log2(e)/(2 l^2)
   float sc;         // sqrt(log2(e)/(2 l^2)): scale of the tile-local grid coordinates
+  int32_t split;    // grid sources: split exponent (grid_split_ok)
   int32_t chunks;
   int32_t K;        // quantities per row: 4, or 7 for a self-kernel
   int32_t rows_per_cta;  // kBwThreads x (kBwR, or kBwRdv with the fused d_v)

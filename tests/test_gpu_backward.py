@@ -65,6 +65,17 @@ def test_reduction_grid_source(orc, gw, gh):
                     rng.standard_normal(4099).astype(np.float32), 0.053, 0.7, False, grid=g)
 
 
+@pytest.mark.parametrize("ratio", [0.5, 1.2, 1.25, 1.5, 4.0])
+def test_reduction_grid_lengthscale_to_spacing(orc, ratio):
+    """Both forms of the grid path (split exponent from 1.24 grid spacings up)."""
+    rng = np.random.default_rng(int(ratio * 10))
+    g = W.Grid(260, 30, 1, 0.04)
+    yg = orc.grid_points(*g.astuple())
+    x = np.stack([rng.uniform(-5.6, 5.6, 2999), rng.uniform(-0.7, 0.7, 2999)], -1).astype(np.float32)
+    check_reduction(orc, x, yg, rng.standard_normal(g.n).astype(np.float32),
+                    rng.standard_normal(2999).astype(np.float32), ratio * 0.04, 0.8, False, grid=g)
+
+
 def test_reduction_self_kernel(orc):
     rng = np.random.default_rng(5)
     x = pts(rng, 6000, 1.0)

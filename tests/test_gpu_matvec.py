@@ -41,6 +41,21 @@ def test_grid_source(orc, gw, gh):
     assert_matvec_close(got, ref, ab)
 
 
+@pytest.mark.parametrize("ratio", [0.3, 0.9, 1.2, 1.25, 1.5, 4.0])
+def test_grid_source_lengthscale_to_spacing(orc, ratio):
+    """Length scales below and above 1.24 grid spacings: the grid path splits
+    the exponent only above that (both forms are covered)."""
+    rng = np.random.default_rng(int(ratio * 100))
+    g = W.Grid(300, 40, 1, 0.04, 0.0, 0.0)
+    yg = orc.grid_points(*g.astuple())
+    x = np.stack([rng.uniform(-6.5, 6.5, 3001), rng.uniform(-0.9, 0.9, 3001)], -1).astype(np.float32)
+    v = rng.standard_normal(g.n).astype(np.float32)
+    ell = ratio * 0.04
+    got = host(api.gp_kernel_matvec(api.Points(xy=dev(x)), api.Points(grid=g), dev(v), ell, 0.9))
+    ref, ab = orc.kernel_matvec(x, yg, v, ell, 0.9)
+    assert_matvec_close(got, ref, ab)
+
+
 def test_self_kernel_explicit(orc):
     rng = np.random.default_rng(3)
     x = pts(rng, 6000, 1.0)
