@@ -335,11 +335,16 @@ lr_status lr_matvec_workspace_size(const lr_points* query, const lr_points* sour
  *   d_lens         double[7]    dL/d(x0, y0, q, phi, theta_e, g1, g2) of the
  *                               query's lens (slope held fixed)
  *   d_sub          double[S][4] dL/d(x_h, y_h, kappa_s | theta_pm, theta_s)
- * and one optional INPUT:
+ * and two optional INPUTS:
  *   beta_in        float[n][2]  the query's ray-traced points as the forward
  *                               pass produced them (gp_kernel_matvec's
  *                               beta_out); when given they are used instead of
  *                               being recomputed
+ *   moments_in     float[4][n]  the row moments gp_kernel_matvec_train wrote
+ *                               for the same query, source, v and length
+ *                               scale (non-self sources only); when given the
+ *                               row sums are not recomputed and only the
+ *                               column sums for d_v (and d_y) sweep the pairs
  */
 typedef struct {
   float* d_v;
@@ -350,7 +355,27 @@ typedef struct {
   double* d_lens;
   double* d_sub;
   const float* beta_in;
+  const float* moments_in;
 } lr_grads;
+
+/*
+ * Forward pass of a training step: out exactly as gp_kernel_matvec computes
+ * it, plus the per-row sums the backward pass needs that do not depend on
+ * dL/dout, written to moments_out (device float[4][n], owned by the caller):
+ *   A_i = sum_j k_ij v_j,  B_i = sum_j k_ij v_j (x_i - y_j)  (two rows, in the
+ *   library's internal coordinate scaling),  C_i = sum_j k_ij v_j d_ij^2
+ *   (internal scaling).
+ * Pass them unchanged as grads->moments_in to gp_kernel_matvec_bwd with the
+ * same arguments. The pair sweep costs a few more FP32 operations per pair
+ * than gp_kernel_matvec and saves the backward's row sweep. Sources: grid or
+ * explicit, not a self-kernel (source != NULL) and not ray-traced. Workspace
+ * of lr_matvec_train_workspace_size() bytes, 256-byte aligned.
+ */
+lr_status gp_kernel_matvec_train(const lr_points* query, const lr_points* source, const float* v, int32_t nrhs,
+                                 float lengthscale, float variance, float* out, float* beta_out, float* moments_out,
+                                 void* workspace, size_t workspace_bytes, lr_stream stream);
+lr_status lr_matvec_train_workspace_size(const lr_points* query, const lr_points* source, int32_t nrhs,
+                                         size_t* bytes);
 
 /*
  * Vector-Jacobian product of gp_kernel_matvec for Loss = sum_i g_out_i out_i

@@ -49,7 +49,8 @@ class lr_points(ctypes.Structure):
 class lr_grads(ctypes.Structure):
     _fields_ = [("d_v", ctypes.c_void_p), ("d_x", ctypes.c_void_p), ("d_y", ctypes.c_void_p),
                 ("d_lengthscale", ctypes.c_void_p), ("d_variance", ctypes.c_void_p), ("d_lens", ctypes.c_void_p),
-                ("d_sub", ctypes.c_void_p), ("beta_in", ctypes.c_void_p)]
+                ("d_sub", ctypes.c_void_p), ("beta_in", ctypes.c_void_p),
+                ("moments_in", ctypes.c_void_p)]
 
 
 class lr_session_cfg(ctypes.Structure):
@@ -100,6 +101,11 @@ SIGNATURES = {
     "gp_knn_density": (ctypes.c_int32, [_P, ctypes.c_int64, ctypes.c_int32, ctypes.c_float, _P, _P, _P,
                                         ctypes.c_size_t, _P]),
     "lr_knn_workspace_size": (ctypes.c_int32, [ctypes.c_int64, ctypes.POINTER(ctypes.c_size_t)]),
+    "gp_kernel_matvec_train": (ctypes.c_int32, [ctypes.POINTER(lr_points), ctypes.POINTER(lr_points), _P,
+                                                ctypes.c_int32, ctypes.c_float, ctypes.c_float, _P, _P, _P, _P,
+                                                ctypes.c_size_t, _P]),
+    "lr_matvec_train_workspace_size": (ctypes.c_int32, [ctypes.POINTER(lr_points), ctypes.POINTER(lr_points),
+                                                        ctypes.c_int32, ctypes.POINTER(ctypes.c_size_t)]),
     "lr_elbo_workspace_size": (ctypes.c_size_t, []),
     "gp_gaussian_nll": (ctypes.c_int32, [_P, ctypes.c_int64, ctypes.POINTER(lr_grid), _P, _P, ctypes.c_float, _P, _P,
                                          _P, _P, ctypes.c_size_t, _P]),

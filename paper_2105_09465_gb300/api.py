@@ -318,17 +318,60 @@ def partial_mvn_vjp(L, sd, eps, d_x, w_q: float = 1.0, stream=None):
 GRADS = ("v", "x", "y", "lengthscale", "variance", "lens", "sub")
 
 
+def train_workspace_size(query: Points, source: Points) -> int:
+    lib = abi.load()
+    cq, k1 = to_c_points(query)
+    cs, k2 = to_c_points(source)
+    b = ctypes.c_size_t(0)
+    ps = ctypes.byref(cs) if cs is not None else None
+    abi.check(lib.lr_matvec_train_workspace_size(ctypes.byref(cq), ps, 1, ctypes.byref(b)),
+              "lr_matvec_train_workspace_size")
+    return int(b.value)
+
+
+def gp_kernel_matvec_train(query: Points, source: Points, v: torch.Tensor, lengthscale: float, variance: float = 1.0,
+                           out: torch.Tensor | None = None, beta: torch.Tensor | None = None,
+                           moments: torch.Tensor | None = None, workspace: torch.Tensor | None = None, stream=None):
+    """Forward of a training step: (out, moments). out equals gp_kernel_matvec's;
+    moments (4, n) are the row sums to pass to gp_kernel_matvec_bwd(moments=...).
+    `beta` optionally receives the ray-traced query points."""
+    lib = abi.load()
+    _require_cuda(v, "v")
+    cq, k1 = to_c_points(query)
+    cs, k2 = to_c_points(source)
+    n = cq.n
+    dev = v.device
+    out = torch.empty((n,), dtype=torch.float32, device=dev) if out is None else out
+    moments = torch.empty((4, n), dtype=torch.float32, device=dev) if moments is None else moments
+    _require_cuda(beta, "beta", (2,))
+    b = ctypes.c_size_t(0)
+    ps = ctypes.byref(cs) if cs is not None else None
+    abi.check(lib.lr_matvec_train_workspace_size(ctypes.byref(cq), ps, 1, ctypes.byref(b)),
+              "lr_matvec_train_workspace_size")
+    need = int(b.value)
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty((max(need, 1),), dtype=torch.uint8, device=dev)
+    st = lib.gp_kernel_matvec_train(ctypes.byref(cq), ps, v.data_ptr(), 1, float(lengthscale),
+                                    float(variance), out.data_ptr(), beta.data_ptr() if beta is not None else None,
+                                    moments.data_ptr(), workspace.data_ptr(), workspace.numel(),
+                                    _stream_handle(stream))
+    abi.check(st, "gp_kernel_matvec_train")
+    return out, moments
+
+
 def gp_kernel_matvec_bwd(query: Points, source: Points | None, v: torch.Tensor, lengthscale: float,
                          variance: float, g_out: torch.Tensor, want=("v", "x", "lengthscale", "variance"),
-                         workspace: torch.Tensor | None = None, stream=None, beta: torch.Tensor | None = None) -> dict:
+                         workspace: torch.Tensor | None = None, stream=None, beta: torch.Tensor | None = None,
+                         moments: torch.Tensor | None = None) -> dict:
     """Gradients of Loss = sum_i g_out_i out_i (recompute-only backward).
 
     `want` selects among v, x (query points after ray-tracing), y (explicit
     non-self sources), lengthscale, variance, lens (7: x0, y0, q, phi,
     theta_e, g1, g2) and sub (S x 4). `beta` (optional) passes the query's
-    ray-traced points from the forward pass instead of recomputing them.
-    Returns a dict of CUDA tensors (the scalar and parameter gradients are
-    float64)."""
+    ray-traced points from the forward pass instead of recomputing them;
+    `moments` (optional) the row sums of gp_kernel_matvec_train, which leaves
+    only the column sums to sweep. Returns a dict of CUDA tensors (the scalar
+    and parameter gradients are float64)."""
     lib = abi.load()
     _require_cuda(v, "v")
     _require_cuda(g_out, "g_out")
@@ -362,6 +405,11 @@ def gp_kernel_matvec_bwd(query: Points, source: Points | None, v: torch.Tensor, 
     if beta is not None:
         _require_cuda(beta, "beta", (2,))
         gr.beta_in = beta.data_ptr()
+    if moments is not None:
+        _require_cuda(moments, "moments")
+        if moments.numel() != 4 * n:
+            raise ValueError("moments must hold 4 x n values")
+        gr.moments_in = moments.data_ptr()
     b = ctypes.c_size_t(0)
     ps = ctypes.byref(cs) if cs is not None else None
     abi.check(lib.lr_matvec_bwd_workspace_size(ctypes.byref(cq), ps, 1, ctypes.byref(gr), ctypes.byref(b)),

@@ -32,6 +32,25 @@ __device__ __forceinline__ void kahan(float& s, float& c, float x) {
   s = t;
 }
 
+// Warp reduce-scatter of the kBwSeg per-lane sums kgs[] of one sub-segment:
+// after the halving stages lane L holds the warp total of source (L >> 1) & 15,
+// which the even lanes store to dvred_w[source].
+__device__ __forceinline__ void warp_reduce_scatter(float (&kgs)[kBwSeg], int lane, float* dvred_w) {
+#pragma unroll
+  for (int h = kBwSeg / 2, m = 16; h >= 1; h >>= 1, m >>= 1) {
+    const bool upper = (lane & m) != 0;
+#pragma unroll
+    for (int i = 0; i < h; ++i) {
+      const float lo = kgs[i], hi = kgs[i + h];
+      const float send = upper ? lo : hi;
+      const float keep = upper ? hi : lo;
+      kgs[i] = keep + __shfl_xor_sync(0xffffffffu, send, m);
+    }
+  }
+  kgs[0] += __shfl_xor_sync(0xffffffffu, kgs[0], 1);
+  if ((lane & 1) == 0) dvred_w[(lane >> 1) & 15] = kgs[0];
+}
+
 __device__ __forceinline__ void bw_tile_range(const BwSrc& S, int t, int64_t& j0, int& cnt, int& grow) {
   if (S.xy) {
     j0 = (int64_t)t * kBwTile;
@@ -89,7 +108,7 @@ struct BwSmem {
 
 template <bool GRID, bool SELF, bool DV>
 struct BwCfg {
-  static constexpr int R = DV ? kBwRdv : kBwR;
+  static constexpr int R = DV ? kBwRdv : (GRID ? kBwRgrid : kBwR);
   static constexpr int K = SELF ? 7 : 4;
   static constexpr int ROWS = kBwThreads * R;
   using Smem = BwSmem<R, K>;
@@ -212,22 +231,7 @@ __device__ __forceinline__ void bwd_rows_body(const BwArgs& A, int rb, int chunk
           acc[r][1].x += fmaf(q, s0, -s1);
           acc[r][3].x += fmaf(fmaf(q, q, dy2[r].x), s0, fmaf(-2.f * q, s1, s2));
         }
-        if (fuse_dv) {
-          const int lane = tid & 31;
-#pragma unroll
-          for (int h = kBwSeg / 2, m = 16; h >= 1; h >>= 1, m >>= 1) {
-            const bool upper = (lane & m) != 0;
-#pragma unroll
-            for (int i = 0; i < h; ++i) {
-              const float lo = kgs[i], hi = kgs[i + h];
-              const float send = upper ? lo : hi;
-              const float keep = upper ? hi : lo;
-              kgs[i] = keep + __shfl_xor_sync(0xffffffffu, send, m);
-            }
-          }
-          kgs[0] += __shfl_xor_sync(0xffffffffu, kgs[0], 1);
-          if ((lane & 1) == 0) sm.dvred[tid >> 5][sg * kBwSeg + ((lane >> 1) & 15)] = kgs[0];
-        }
+        if (fuse_dv) warp_reduce_scatter(kgs, tid & 31, &sm.dvred[tid >> 5][sg * kBwSeg]);
       }
       } else {
       for (int sg = 0; sg < nsg; ++sg) {
@@ -260,24 +264,7 @@ __device__ __forceinline__ void bwd_rows_body(const BwArgs& A, int rb, int chunk
           kgs[2 * pp] = kg.x;
           kgs[2 * pp + 1] = kg.y;
         }
-        if (fuse_dv) {
-          // warp reduce-scatter of the 16 per-lane sums: after the halving
-          // stages lane L holds the warp total of source (L >> 1) & 15
-          const int lane = tid & 31;
-#pragma unroll
-          for (int h = kBwSeg / 2, m = 16; h >= 1; h >>= 1, m >>= 1) {
-            const bool upper = (lane & m) != 0;
-#pragma unroll
-            for (int i = 0; i < h; ++i) {
-              const float lo = kgs[i], hi = kgs[i + h];
-              const float send = upper ? lo : hi;
-              const float keep = upper ? hi : lo;
-              kgs[i] = keep + __shfl_xor_sync(0xffffffffu, send, m);
-            }
-          }
-          kgs[0] += __shfl_xor_sync(0xffffffffu, kgs[0], 1);
-          if ((lane & 1) == 0) sm.dvred[tid >> 5][sg * kBwSeg + ((lane >> 1) & 15)] = kgs[0];
-        }
+        if (fuse_dv) warp_reduce_scatter(kgs, tid & 31, &sm.dvred[tid >> 5][sg * kBwSeg]);
       }
       }
       if (fuse_dv) {
@@ -371,6 +358,153 @@ __global__ void __launch_bounds__(kBwThreads) bwd_rows_batched_kernel(const __gr
   const int local = blockIdx.x - B.start[k];
   const int rb = local / A.chunks;
   bwd_rows_body<GRID, SELF, DV, SPLIT>(A, rb, local - rb * A.chunks, sm);
+}
+
+// ---------------------------------------------------------------------------
+// d_v alone for grid sources: dv_part[rb][j] = sum over the rows i of row
+// block rb of k_ij g_i. This is the column half of the backward pass when the
+// row sums (A, B, C) come from the training forward (gp_kernel_matvec_train),
+// so per pair only the exponent, one exp2 and one accumulation remain:
+// 2 FP32 lanes with the split exponent (k = k~ 2^-x'^2, the per-source
+// factor applied once per tile), 3 without.
+constexpr int kDvR = 8;
+constexpr int kDvRows = kBwThreads * kDvR;
+
+struct DvSmem {
+  float2 sX[2][kBwPairs];
+  float dvred[kBwThreads / 32][kBwTile];
+};
+
+template <bool SPLIT>
+__device__ __forceinline__ void dv_load_pair(const BwArgs& A, int t, int p, float2& X) {
+  int64_t j0;
+  int cnt, grow;
+  bw_tile_range(A.src, t, j0, cnt, grow);
+  const int a = 2 * p, b = 2 * p + 1;
+  const int c0 = (int)(j0 - (int64_t)grow * A.src.g.W);
+  const float o = grid_x(A.src.g, c0 + kBwSeg * (a / kBwSeg) + kBwSeg / 2);
+  const float xa = (a < cnt) ? A.sc * (grid_x(A.src.g, c0 + a) - o) : 0.f;
+  const float xb = (b < cnt) ? A.sc * (grid_x(A.src.g, c0 + b) - o) : 0.f;
+  X = SPLIT ? f2(xa, xb) : f2(-xa, -xb);
+}
+
+template <bool SPLIT>
+__device__ __forceinline__ void dv_rows_body(const BwArgs& A, int rb, int chunk, DvSmem& sm) {
+  const int nt = A.src.n_tiles;
+  const int t0 = (int)((int64_t)chunk * nt / A.chunks);
+  const int t1 = (int)((int64_t)(chunk + 1) * nt / A.chunks);
+  const int tid = threadIdx.x;
+  float xq[kDvR], yq[kDvR];
+  float2 gq[kDvR];
+#pragma unroll
+  for (int r = 0; r < kDvR; ++r) {
+    const int64_t i0 = (int64_t)rb * kDvRows + r * kBwThreads + tid;
+    const int64_t i = i0 < A.n ? i0 : A.n - 1;
+    const float2 p = __ldg(A.x + i);
+    xq[r] = p.x;
+    yq[r] = p.y;
+    const float gv = i0 < A.n ? __ldg(A.grow + i0) : 0.f;  // rows past n add nothing
+    gq[r] = f2(gv, gv);
+  }
+  float2 X = f2(0.f, 0.f);
+  if (t0 < t1) {
+    dv_load_pair<SPLIT>(A, t0, tid, X);
+    sm.sX[0][tid] = X;
+  }
+  __syncthreads();
+  for (int t = t0; t < t1; ++t) {
+    const int buf = (t - t0) & 1;
+    if (t + 1 < t1) dv_load_pair<SPLIT>(A, t + 1, tid, X);
+    int64_t j0;
+    int cnt, grow;
+    bw_tile_range(A.src, t, j0, cnt, grow);
+    const float yt = grid_y(A.src.g, grow);
+    const int c0 = (int)(j0 - (int64_t)grow * A.src.g.W);
+    float dy2[kDvR];
+#pragma unroll
+    for (int r = 0; r < kDvR; ++r) {
+      const float d = A.sc * (yq[r] - yt);
+      dy2[r] = d * d;
+    }
+    const int nsg = (cnt + kBwSeg - 1) / kBwSeg;
+    for (int sg = 0; sg < nsg; ++sg) {
+      const float o = grid_x(A.src.g, c0 + kBwSeg * sg + kBwSeg / 2);
+      float2 qa[kDvR], qb[kDvR];  // split: (2q, -(q^2 + dy'^2)); unsplit: (q, dy'^2)
+#pragma unroll
+      for (int r = 0; r < kDvR; ++r) {
+        const float q = A.sc * (xq[r] - o);
+        if (SPLIT) {
+          const float a = -fmaf(q, q, dy2[r]);
+          qa[r] = f2(2.f * q, 2.f * q);
+          qb[r] = f2(a, a);
+        } else {
+          qa[r] = f2(q, q);
+          qb[r] = f2(dy2[r], dy2[r]);
+        }
+      }
+      float kgs[kBwSeg];
+#pragma unroll
+      for (int pp = 0; pp < kBwSeg / 2; ++pp) {
+        const float2 Xp = sm.sX[buf][sg * (kBwSeg / 2) + pp];
+        float2 kg = f2(0.f, 0.f);
+#pragma unroll
+        for (int r = 0; r < kDvR; ++r) {
+          float2 k;
+          if (SPLIT) {
+            const float2 e = __ffma2_rn(qa[r], Xp, qb[r]);
+            k = f2(ex2_approx(e.x), ex2_approx(e.y));
+          } else {
+            const float2 dx = __fadd2_rn(qa[r], Xp);
+            const float2 tt = __ffma2_rn(dx, dx, qb[r]);
+            k = f2(ex2_approx(-tt.x), ex2_approx(-tt.y));
+          }
+          kg = __ffma2_rn(k, gq[r], kg);
+        }
+        kgs[2 * pp] = kg.x;
+        kgs[2 * pp + 1] = kg.y;
+      }
+      warp_reduce_scatter(kgs, tid & 31, &sm.dvred[tid >> 5][sg * kBwSeg]);
+    }
+    __syncthreads();
+    // combine the warps in order; row block rb owns these columns of dv_part
+    float* dst = A.dv_part + (int64_t)rb * A.src.m + j0;
+    for (int j = tid; j < cnt; j += kBwThreads) {
+      float sdv = sm.dvred[0][j];
+#pragma unroll
+      for (int w = 1; w < kBwThreads / 32; ++w) sdv += sm.dvred[w][j];
+      if (SPLIT) {
+        const float2 Xp = sm.sX[buf][j >> 1];
+        const float xj = (j & 1) ? Xp.y : Xp.x;
+        sdv *= ex2_approx(-xj * xj);
+      }
+      dst[j] = sdv;
+    }
+    if (t + 1 < t1) sm.sX[buf ^ 1][tid] = X;
+    __syncthreads();
+  }
+}
+
+template <bool SPLIT>
+__global__ void __launch_bounds__(kBwThreads) dv_rows_kernel(const __grid_constant__ BwArgs A) {
+  __shared__ __align__(16) DvSmem sm;
+  const int rb = blockIdx.x / A.chunks;
+  dv_rows_body<SPLIT>(A, rb, blockIdx.x - rb * A.chunks, sm);
+}
+
+// Training forward: fixed-order merge of the row-pass chunk partials into the
+// per-row moments (A, B_x, B_y, C) and out = var A.
+__global__ void moments_merge_kernel(const float* __restrict__ partial, int chunks, int64_t n, float var,
+                                     float* __restrict__ out, float* __restrict__ mom) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    float s = 0.f, c = 0.f;
+    for (int ch = 0; ch < chunks; ++ch) kahan(s, c, partial[((int64_t)ch * 4 + k) * n + i]);
+    s -= c;
+    mom[(int64_t)k * n + i] = s;
+    if (k == 0) out[i] = var * s;
+  }
 }
 
 // Per-row merge of chunk partials, the per-row gradients, and per-block FP64
@@ -592,7 +726,7 @@ static lr_status plan_rows(int64_t n, int64_t m, bool grid, const lr_grid* g, bo
   RowPlan p{};
   p.K = self ? 7 : 4;
   const bool dv = grid && fuse_dv;
-  p.rows_per_cta = dv ? BwCfg<true, false, true>::ROWS : kBwRows;
+  p.rows_per_cta = dv ? BwCfg<true, false, true>::ROWS : (grid ? BwCfg<true, false, false>::ROWS : kBwRows);
   if (grid) {
     const int W = g->nx * g->ss;
     p.segs = (W + kBwTile - 1) / kBwTile;
@@ -614,8 +748,15 @@ static lr_status plan_rows(int64_t n, int64_t m, bool grid, const lr_grid* g, bo
                                                                 kBwThreads, 0));
     occ = occ < occ2 ? occ : occ2;
   }
-  else
+  else if (grid) {
+    int occ2 = 1;
+    LR_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, bwd_rows_kernel<true, false, false>, kBwThreads, 0));
+    LR_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, bwd_rows_kernel<true, false, false, true>,
+                                                                kBwThreads, 0));
+    occ = occ < occ2 ? occ : occ2;
+  } else {
     LR_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, bwd_rows_kernel<false, false, false>, kBwThreads, 0));
+  }
   const int32_t chunks = plan_chunks(p.row_blocks, p.n_tiles, occ, n_sm);
   p.chunks = chunks;
   p.partial_bytes = align256(sizeof(float) * (size_t)p.chunks * p.K * (size_t)n);
@@ -624,6 +765,30 @@ static lr_status plan_rows(int64_t n, int64_t m, bool grid, const lr_grid* g, bo
   p.dv_bytes = grid ? align256(sizeof(float) * (size_t)p.row_blocks * (size_t)m) : 0;
   *R = p;
   return LR_OK;
+}
+
+// Merge of non-self row-pass partials [chunks][4][n] (A, B_x, B_y, C) into
+// d_x and the FP64 block partials of d_l and d_var.
+static MergeArgs row_merge_args(bool grid, float ell, float var, const float* partial, int32_t chunks, int64_t n,
+                                const float* g, const float* vrow, float2* dx, double* scal_part) {
+  const double c = 1.4426950408889634 / (2.0 * (double)ell * (double)ell);
+  MergeArgs mm{};
+  mm.partial = partial;
+  mm.chunks = chunks;
+  mm.K = 4;
+  mm.n = n;
+  mm.g = g;
+  mm.vrow = vrow;
+  mm.var = var;
+  mm.inv_l2 = (float)(1.0 / ((double)ell * ell));
+  // grid path: C = sum k v c d^2 (positive), B in coordinates scaled by sc;
+  // explicit path: C = sum k v e with e = -c d^2, B unscaled
+  mm.dl_scale = (float)((grid ? 1.0 : -1.0) * (double)var / (c * (double)ell * ell * ell));
+  mm.b_scale = grid ? (float)(1.0 / sqrt(c)) : 1.0f;
+  mm.d_x = dx;
+  mm.d_v = nullptr;
+  mm.scal_part = scal_part;
+  return mm;
 }
 
 // Problem descriptors for the non-self row pass (d_x, d_l, d_var) of explicit
@@ -662,24 +827,8 @@ lr_status make_rows_problem(const float2* x, int64_t n, const float2* ys, const 
   a.grow = fuse ? g : nullptr;
   a.dv_part = fuse ? reinterpret_cast<float*>(ws + R.partial_bytes + R.scal_bytes) : nullptr;
   *A = a;
-  MergeArgs mm{};
-  mm.partial = a.partial;
-  mm.chunks = R.chunks;
-  mm.K = R.K;
-  mm.n = n;
-  mm.g = g;
-  mm.vrow = v;
-  mm.var = var;
-  mm.inv_l2 = (float)(1.0 / ((double)ell * ell));
-  // grid path: C = sum k v c d^2 (positive), B in coordinates scaled by sc;
-  // explicit path: C = sum k v e with e = -c d^2, B unscaled
-  mm.dl_scale = (float)((grid ? 1.0 : -1.0) * (double)var / (c * (double)ell * ell * ell));
-  mm.b_scale = grid ? (float)(1.0 / sqrt(c)) : 1.0f;
-  mm.d_x = dx;
-  mm.d_v = nullptr;
-  mm.scal_part = reinterpret_cast<double*>(ws + R.partial_bytes);
-  *M = mm;
-  S->part = mm.scal_part;
+  *M = row_merge_args(grid, ell, var, a.partial, R.chunks, n, g, v, dx, reinterpret_cast<double*>(ws + R.partial_bytes));
+  S->part = M->scal_part;
   S->nblk = (int32_t)R.merge_blocks;
   S->d_len = d_len;
   S->d_var = d_var;
@@ -780,6 +929,77 @@ static lr_status launch_rows(const float2* x, int64_t n, const float2* ys, const
   return LR_OK;
 }
 
+// Plan of the d_v-only pass over grid sources (dv_rows_kernel).
+static lr_status plan_dv(int64_t n, const lr_grid* g, RowPlan* R) {
+  RowPlan p{};
+  p.K = 0;
+  p.rows_per_cta = kDvRows;
+  const int W = g->nx * g->ss;
+  p.segs = (W + kBwTile - 1) / kBwTile;
+  p.n_tiles = (int32_t)((int64_t)p.segs * g->ny * g->ss);
+  p.row_blocks = (int32_t)((n + kDvRows - 1) / kDvRows);
+  int dev = 0, n_sm = 1, occ = 1, occ2 = 1;
+  LR_CHECK_CUDA(cudaGetDevice(&dev));
+  LR_CHECK_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
+  LR_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, dv_rows_kernel<true>, kBwThreads, 0));
+  LR_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, dv_rows_kernel<false>, kBwThreads, 0));
+  p.chunks = plan_chunks(p.row_blocks, p.n_tiles, occ < occ2 ? occ : occ2, n_sm);
+  const int64_t m = (int64_t)W * g->ny * g->ss;
+  p.dv_bytes = align256(sizeof(float) * (size_t)p.row_blocks * (size_t)m);
+  *R = p;
+  return LR_OK;
+}
+
+// d_v of grid sources from the d_v-only pass: dv_part, then the fixed-order
+// merge over row blocks. ws: the plan's dv_bytes.
+static lr_status launch_dv(const float2* x, int64_t n, const lr_grid* yg, const float* g, float ell, float var,
+                           float* d_v, char* ws, cudaStream_t s) {
+  RowPlan R;
+  lr_status st = plan_dv(n, yg, &R);
+  if (st != LR_OK) return st;
+  BwArgs A{};
+  A.x = x;
+  A.n = n;
+  A.src.xy = nullptr;
+  A.src.g = grid_dev(*yg);
+  A.src.m = (int64_t)A.src.g.W * A.src.g.H;
+  A.src.segs = R.segs;
+  A.src.n_tiles = R.n_tiles;
+  const double c = 1.4426950408889634 / (2.0 * (double)ell * (double)ell);
+  A.neg_c = (float)(-c);
+  A.sc = (float)sqrt(c);
+  A.split = grid_split_ok(A.src.g, A.sc);
+  A.chunks = R.chunks;
+  A.rows_per_cta = kDvRows;
+  A.grow = g;
+  A.dv_part = reinterpret_cast<float*>(ws);
+  const unsigned grid = (unsigned)((int64_t)R.row_blocks * R.chunks);
+  if (A.split)
+    dv_rows_kernel<true><<<grid, kBwThreads, 0, s>>>(A);
+  else
+    dv_rows_kernel<false><<<grid, kBwThreads, 0, s>>>(A);
+  LR_CHECK_CUDA(cudaGetLastError());
+  DvMergeP D{A.dv_part, R.row_blocks, A.src.m, var, d_v};
+  dv_merge_kernel<<<(unsigned)((A.src.m + 255) / 256), 256, 0, s>>>(D);
+  LR_CHECK_CUDA(cudaGetLastError());
+  return LR_OK;
+}
+
+// Row gradients from the training forward's moments: d_x, d_l, d_var.
+// ws: the scalar partials (merge blocks x 2 doubles).
+static lr_status launch_moment_rows(const float* mom, int64_t n, bool grid, const float* g, const float* v, float ell,
+                                    float var, float2* d_x, double* d_len, double* d_var, char* ws, cudaStream_t s) {
+  const int64_t nblk = (n + kMergeThreads - 1) / kMergeThreads;
+  MergeArgs M = row_merge_args(grid, ell, var, mom, 1, n, g, v, d_x, reinterpret_cast<double*>(ws));
+  bwd_merge_kernel<<<(unsigned)nblk, kMergeThreads, 0, s>>>(M);
+  LR_CHECK_CUDA(cudaGetLastError());
+  if (d_len || d_var) {
+    bwd_scalar_final_kernel<<<1, kMergeThreads, 0, s>>>(M.scal_part, (int32_t)nblk, d_len, d_var);
+    LR_CHECK_CUDA(cudaGetLastError());
+  }
+  return LR_OK;
+}
+
 static size_t rows_ws(int64_t n, int64_t m, bool grid, const lr_grid* g, bool self, bool fuse_dv, lr_status* st) {
   RowPlan R;
   *st = plan_rows(n, m, grid, g, self, fuse_dv, &R);
@@ -791,7 +1011,8 @@ struct BwPlan {
   bool self, q_raytrace, q_grid, s_raytrace, s_grid;
   bool want_lens;       // lens / subhalo gradients of the query's lens
   bool need_dx;         // d_x needed (requested or for the lens gradient)
-  size_t off_qbeta, off_sbeta, off_rows, off_dx, off_sgrid, off_swap, off_swaprows, off_vjp, bytes;
+  bool moments;         // row sums given by the training forward
+  size_t off_qbeta, off_sbeta, off_rows, off_dv, off_dx, off_sgrid, off_swap, off_swaprows, off_vjp, bytes;
 };
 
 static lr_status plan_bwd(const lr_points* q, const lr_points* s, const lr_grads* gr, BwPlan* P) {
@@ -818,12 +1039,25 @@ static lr_status plan_bwd(const lr_points* q, const lr_points* s, const lr_grads
   p.need_dx = gr->d_x || p.want_lens;
   LR_REQUIRE(gr->beta_in == nullptr || p.q_raytrace, "gp_kernel_matvec_bwd: beta_in given but the query is not ray-traced");
   LR_REQUIRE(((uintptr_t)gr->beta_in & 7u) == 0, "gp_kernel_matvec_bwd: beta_in must be 8-byte aligned");
+  p.moments = gr->moments_in != nullptr;
+  LR_REQUIRE(!p.moments || !p.self, "gp_kernel_matvec_bwd: moments_in applies to non-self sources only");
+  LR_REQUIRE(((uintptr_t)gr->moments_in & 3u) == 0, "gp_kernel_matvec_bwd: moments_in must be 4-byte aligned");
   size_t off = 0;
   p.off_qbeta = off;
   if ((p.q_raytrace && !gr->beta_in) || p.q_grid) off += align256(8 * (size_t)p.n);
   p.off_sbeta = off;
   p.off_rows = off;
-  {
+  if (p.moments) {
+    // scalar partials of the moment merge, then the d_v-only pass of grid sources
+    off += align256(sizeof(double) * 2 * (size_t)((p.n + kMergeThreads - 1) / kMergeThreads + 1));
+    p.off_dv = off;
+    if (p.s_grid && gr->d_v && p.n > 0) {
+      RowPlan R;
+      st = plan_dv(p.n, &s->grid, &R);
+      if (st != LR_OK) return st;
+      off += R.dv_bytes;
+    }
+  } else {
     size_t b = rows_ws(p.n, p.m, p.s_grid, p.s_grid ? &s->grid : nullptr, p.self, p.s_grid && gr->d_v != nullptr, &st);
     if (st != LR_OK) return st;
     off += b;
@@ -922,10 +1156,22 @@ extern "C" lr_status gp_kernel_matvec_bwd(const lr_points* query, const lr_point
   const lr_grid* yg = P.s_grid ? &source->grid : nullptr;
   float2* dx = P.need_dx ? (G.d_x ? reinterpret_cast<float2*>(G.d_x) : reinterpret_cast<float2*>(ws + P.off_dx))
                          : nullptr;
-  // row pass: d_x (both roles for a self-kernel), self d_v, d_l, d_var
-  st = launch_rows(xq, P.n, ys, yg, P.m, v, P.self ? g_out : nullptr, g_out, v, lengthscale, variance, P.self, dx,
-                   (P.self || P.s_grid) ? G.d_v : nullptr, G.d_lengthscale, G.d_variance, ws + P.off_rows, s);
-  if (st != LR_OK) return st;
+  if (P.moments) {
+    // row gradients from the training forward's moments; d_v of grid sources
+    // from the d_v-only sweep
+    st = launch_moment_rows(G.moments_in, P.n, P.s_grid, g_out, v, lengthscale, variance, dx, G.d_lengthscale,
+                            G.d_variance, ws + P.off_rows, s);
+    if (st != LR_OK) return st;
+    if (P.s_grid && G.d_v) {
+      st = launch_dv(xq, P.n, yg, g_out, lengthscale, variance, G.d_v, ws + P.off_dv, s);
+      if (st != LR_OK) return st;
+    }
+  } else {
+    // row pass: d_x (both roles for a self-kernel), self d_v, d_l, d_var
+    st = launch_rows(xq, P.n, ys, yg, P.m, v, P.self ? g_out : nullptr, g_out, v, lengthscale, variance, P.self, dx,
+                     (P.self || P.s_grid) ? G.d_v : nullptr, G.d_lengthscale, G.d_variance, ws + P.off_rows, s);
+    if (st != LR_OK) return st;
+  }
   // d_v of explicit non-self sources: sum_i var k_ij g_i, the forward reduction
   // with the point sets swapped (grid sources have it fused into the row pass)
   if (!P.self && !P.s_grid && G.d_v) {
@@ -953,5 +1199,115 @@ extern "C" lr_status gp_kernel_matvec_bwd(const lr_points* query, const lr_point
     st = launch_raytrace_vjp(query, dx, G.d_lens, G.d_sub, ws + P.off_vjp, s);
     if (st != LR_OK) return st;
   }
+  return LR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Training forward: the non-self row pass with the source weights v gives the
+// per-row moments (A, B_x, B_y, C); out = var A. One sweep over the pairs
+// serves the forward output and the row half of the backward.
+namespace lr {
+
+struct TrainPlan {
+  int64_t n, m;
+  bool q_raytrace, q_grid, s_grid;
+  RowPlan R;
+  size_t off_qbeta, off_rows, bytes;
+};
+
+static lr_status plan_train(const lr_points* q, const lr_points* s, TrainPlan* T) {
+  lr_status st = validate_points(q, "gp_kernel_matvec_train(query)", false);
+  if (st != LR_OK) return st;
+  LR_REQUIRE(s != nullptr, "gp_kernel_matvec_train: a self-kernel (source == NULL) is not supported");
+  st = validate_points(s, "gp_kernel_matvec_train(source)", false);
+  if (st != LR_OK) return st;
+  LR_REQUIRE(s->lens == nullptr, "gp_kernel_matvec_train: ray-traced sources are not supported");
+  TrainPlan p{};
+  p.n = q->n;
+  p.m = s->n;
+  p.q_raytrace = q->lens != nullptr;
+  p.q_grid = !p.q_raytrace && q->xy == nullptr;
+  p.s_grid = s->xy == nullptr;
+  size_t off = 0;
+  p.off_qbeta = off;
+  if (p.q_raytrace || p.q_grid) off += align256(8 * (size_t)p.n);
+  p.off_rows = off;
+  if (p.n > 0 && p.m > 0) {
+    st = plan_rows(p.n, p.m, p.s_grid, p.s_grid ? &s->grid : nullptr, false, false, &p.R);
+    if (st != LR_OK) return st;
+    off += p.R.partial_bytes + p.R.scal_bytes;
+  }
+  p.bytes = off;
+  *T = p;
+  return LR_OK;
+}
+
+}  // namespace lr
+
+extern "C" lr_status lr_matvec_train_workspace_size(const lr_points* query, const lr_points* source, int32_t nrhs,
+                                                    size_t* bytes) {
+  LR_REQUIRE(bytes != nullptr, "lr_matvec_train_workspace_size: bytes is NULL");
+  LR_REQUIRE(nrhs == 1, "lr_matvec_train_workspace_size: nrhs = %d; this version supports nrhs = 1", nrhs);
+  TrainPlan T;
+  lr_status st = plan_train(query, source, &T);
+  if (st != LR_OK) return st;
+  *bytes = T.bytes;
+  return LR_OK;
+}
+
+extern "C" lr_status gp_kernel_matvec_train(const lr_points* query, const lr_points* source, const float* v,
+                                            int32_t nrhs, float lengthscale, float variance, float* out,
+                                            float* beta_out, float* moments_out, void* workspace,
+                                            size_t workspace_bytes, lr_stream stream) {
+  LR_REQUIRE(nrhs == 1, "gp_kernel_matvec_train: nrhs = %d; this version supports nrhs = 1", nrhs);
+  TrainPlan T;
+  lr_status st = plan_train(query, source, &T);
+  if (st != LR_OK) return st;
+  LR_REQUIRE(isfinite(lengthscale) && lengthscale > 0.f, "gp_kernel_matvec_train: lengthscale must be > 0");
+  LR_REQUIRE(isfinite(variance), "gp_kernel_matvec_train: variance is not finite");
+  LR_REQUIRE(T.n == 0 || (out != nullptr && moments_out != nullptr),
+             "gp_kernel_matvec_train: out and moments_out are required");
+  LR_REQUIRE(v != nullptr || T.m == 0, "gp_kernel_matvec_train: v is NULL");
+  LR_REQUIRE(beta_out == nullptr || T.q_raytrace || T.q_grid,
+             "gp_kernel_matvec_train: beta_out needs a ray-traced or grid query");
+  LR_REQUIRE(((uintptr_t)beta_out & 7u) == 0 && ((uintptr_t)out & 3u) == 0 && ((uintptr_t)moments_out & 3u) == 0,
+             "gp_kernel_matvec_train: misaligned output");
+  LR_REQUIRE(workspace_bytes >= T.bytes && (T.bytes == 0 || workspace != nullptr),
+             "gp_kernel_matvec_train: workspace of %zu bytes, %zu needed", workspace_bytes, T.bytes);
+  LR_REQUIRE(((uintptr_t)workspace & 255u) == 0, "gp_kernel_matvec_train: workspace must be 256-byte aligned");
+  cudaStream_t s = as_cuda(stream);
+  char* ws = static_cast<char*>(workspace);
+  if (T.n == 0) return LR_OK;
+  const float2* xq = reinterpret_cast<const float2*>(query->xy);
+  if (T.q_raytrace || T.q_grid) {
+    float2* qb = beta_out ? reinterpret_cast<float2*>(beta_out) : reinterpret_cast<float2*>(ws + T.off_qbeta);
+    st = T.q_raytrace ? launch_raytrace(query, qb, nullptr, s) : launch_grid_points(query->grid, qb, s);
+    if (st != LR_OK) return st;
+    xq = qb;
+  }
+  if (T.m == 0) {
+    LR_CHECK_CUDA(cudaMemsetAsync(out, 0, 4 * (size_t)T.n, s));
+    LR_CHECK_CUDA(cudaMemsetAsync(moments_out, 0, 16 * (size_t)T.n, s));
+    return LR_OK;
+  }
+  BwArgs A;
+  MergeArgs M;
+  ScalP S;
+  size_t b = 0;
+  const float2* ys = T.s_grid ? nullptr : reinterpret_cast<const float2*>(source->xy);
+  st = make_rows_problem(xq, T.n, ys, T.s_grid ? &source->grid : nullptr, T.m, v, nullptr, lengthscale, variance,
+                         nullptr, nullptr, nullptr, nullptr, ws + T.off_rows, &A, &M, &S, nullptr, &b);
+  if (st != LR_OK) return st;
+  const unsigned grid = (unsigned)(((T.n + A.rows_per_cta - 1) / A.rows_per_cta) * A.chunks);
+  if (T.s_grid && A.split)
+    bwd_rows_kernel<true, false, false, true><<<grid, kBwThreads, 0, s>>>(A);
+  else if (T.s_grid)
+    bwd_rows_kernel<true, false, false><<<grid, kBwThreads, 0, s>>>(A);
+  else
+    bwd_rows_kernel<false, false, false><<<grid, kBwThreads, 0, s>>>(A);
+  LR_CHECK_CUDA(cudaGetLastError());
+  moments_merge_kernel<<<(unsigned)((T.n + 255) / 256), 256, 0, s>>>(A.partial, A.chunks, T.n, variance, out,
+                                                                       moments_out);
+  LR_CHECK_CUDA(cudaGetLastError());
   return LR_OK;
 }

@@ -64,6 +64,7 @@ constexpr int kBwThreads = 128;
 constexpr int kBwR = 4;                     // rows per thread
 constexpr int kBwRows = kBwThreads * kBwR;  // 512 rows per CTA
 constexpr int kBwRdv = 8;                   // rows per thread with the fused d_v reduction
+constexpr int kBwRgrid = 4;                 // rows per thread, grid sources without d_v (training forward)
 constexpr int kBwTile = 256;
 constexpr int kBwPairs = kBwTile / 2;
 constexpr int kMergeThreads = 256;

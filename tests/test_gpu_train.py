@@ -1,0 +1,108 @@
+"""Parity of the training forward (gp_kernel_matvec_train: out plus the row
+moments) and of the backward pass fed those moments, against the FP64
+oracle, for grid sources on both sides of the split-exponent bound, explicit
+sources and the fused ray-traced chain."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2105_09465_gb300 import abi, api, workloads as W
+from tests.gpu_util import assert_matvec_close, dev, host, need_gpu
+from tests.test_gpu_backward import close, fused_chain
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    need_gpu()
+
+
+def grid_case(ratio, seed):
+    rng = np.random.default_rng(seed)
+    g = W.Grid(260, 30, 1, 0.04)
+    x = np.stack([rng.uniform(-5.6, 5.6, 2999), rng.uniform(-0.7, 0.7, 2999)], -1).astype(np.float32)
+    return g, x, rng.standard_normal(g.n).astype(np.float32), rng.standard_normal(2999).astype(np.float32), ratio * 0.04
+
+
+@pytest.mark.parametrize("ratio", [0.5, 1.2, 1.25, 1.5, 4.0])
+def test_grid_source(orc, ratio):
+    g, x, v, gout, ell = grid_case(ratio, int(10 * ratio))
+    yg = orc.grid_points(*g.astuple())
+    q, s = api.Points(xy=dev(x)), api.Points(grid=g)
+    out, mom = api.gp_kernel_matvec_train(q, s, dev(v), ell, 0.8)
+    ref, ab = orc.kernel_matvec(x, yg, v, ell, 0.8)
+    assert_matvec_close(host(out), ref, ab, what="train forward")
+    G = api.gp_kernel_matvec_bwd(q, s, dev(v), ell, 0.8, dev(gout), want=["v", "x", "lengthscale", "variance"],
+                                 moments=mom)
+    R = orc.kernel_matvec_vjp(x, yg, v, ell, 0.8, gout.astype(np.float64), False, with_abs=True)
+    close(host(G["v"]), R["d_v"], R["d_v_abs"], what="d_v")
+    close(host(G["x"]), R["d_x"], R["d_x_abs"], what="d_x")
+    close(host(G["lengthscale"]), [R["d_len"]], [R["d_len_abs"]], what="d_len")
+    close(host(G["variance"]), [R["d_var"]], [R["d_var_abs"]], what="d_var")
+
+
+@pytest.mark.parametrize("n,m", [(1, 1), (700, 5003), (3001, 2500)])
+def test_explicit_sources(orc, n, m):
+    rng = np.random.default_rng(n + m)
+    x, y = rng.uniform(-0.5, 0.5, (n, 2)).astype(np.float32), rng.uniform(-0.5, 0.5, (m, 2)).astype(np.float32)
+    v, gout = rng.standard_normal(m).astype(np.float32), rng.standard_normal(n).astype(np.float32)
+    q, s = api.Points(xy=dev(x)), api.Points(xy=dev(y))
+    out, mom = api.gp_kernel_matvec_train(q, s, dev(v), 0.05, 1.3)
+    ref, ab = orc.kernel_matvec(x, y, v, 0.05, 1.3)
+    assert_matvec_close(host(out), ref, ab, what="train forward")
+    want = ["v", "x", "y", "lengthscale", "variance"]
+    G = api.gp_kernel_matvec_bwd(q, s, dev(v), 0.05, 1.3, dev(gout), want=want, moments=mom)
+    R = orc.kernel_matvec_vjp(x, y, v, 0.05, 1.3, gout.astype(np.float64), False, with_abs=True)
+    for k, rk in (("v", "d_v"), ("x", "d_x"), ("y", "d_y")):
+        close(host(G[k]), R[rk], R[rk + "_abs"], what=rk)
+    close(host(G["lengthscale"]), [R["d_len"]], [R["d_len_abs"]], what="d_len")
+    close(host(G["variance"]), [R["d_var"]], [R["d_var_abs"]], what="d_var")
+
+
+def test_fused_chain_with_moments(orc):
+    """Ray-traced query (lens, shear, 200 tNFW) against grid inducing points:
+    train forward, then the backward with the forward's points and moments,
+    down to the lens and subhalo parameters."""
+    p = W.realistic(seed=51, side=80, ss=2, n_sub=200)
+    g = np.random.default_rng(3).standard_normal(p.n).astype(np.float32)
+    q = api.Points(grid=p.xgrid, lens=p.lens, sub=dev(p.sub))
+    s = api.Points(grid=p.ygrid)
+    beta = torch.empty((p.n, 2), device="cuda")
+    out, mom = api.gp_kernel_matvec_train(q, s, dev(p.v), p.lengthscale, p.variance, beta=beta)
+    want = ["v", "x", "lengthscale", "variance", "lens", "sub"]
+    G = api.gp_kernel_matvec_bwd(q, s, dev(p.v), p.lengthscale, p.variance, dev(g), want=want, beta=beta,
+                                 moments=mom)
+    xi, bref, yg = fused_chain(orc, p)
+    ref, ab, sens = orc.kernel_matvec(bref, yg, p.v, p.lengthscale, p.variance, with_sens=True)
+    delta = 1e-6 + np.spacing(np.abs(bref).max().astype(np.float32))
+    assert_matvec_close(host(out), ref, ab, sens=sens, delta=delta, what="fused train forward")
+    R = orc.kernel_matvec_vjp(bref, yg, p.v, p.lengthscale, p.variance, g.astype(np.float64), with_abs=True)
+    rl, rs, _, _ = orc.raytrace_vjp(xi, p.lens.astuple(), p.sub, R["d_x"], 0, with_abs=True)
+    close(host(G["v"]), R["d_v"], R["d_v_abs"], rel=1e-4, what="d_v")
+    close(host(G["x"]), R["d_x"], R["d_x_abs"], rel=1e-4, what="d_x")
+    close(host(G["lengthscale"]), [R["d_len"]], [R["d_len_abs"]], rel=1e-4, what="d_len")
+    close(host(G["variance"]), [R["d_var"]], [R["d_var_abs"]], rel=1e-4, what="d_var")
+    _, _, al2, asub2 = orc.raytrace_vjp(xi, p.lens.astuple(), p.sub, R["d_x_abs"], 0, with_abs=True)
+    close(host(G["lens"]), rl, al2, rel=2e-4, what="d_lens")
+    close(host(G["sub"]), rs, asub2, rel=2e-4, what="d_sub")
+
+
+def test_deterministic_and_self_kernel_rejected():
+    p = W.realistic(seed=52, side=40, ss=2, n_sub=30)
+    q, s = api.Points(grid=p.xgrid, lens=p.lens, sub=dev(p.sub)), api.Points(grid=p.ygrid)
+    g = dev(np.random.default_rng(0).standard_normal(p.n))
+    a_out, a_mom = api.gp_kernel_matvec_train(q, s, dev(p.v), p.lengthscale, 1.0)
+    b_out, b_mom = api.gp_kernel_matvec_train(q, s, dev(p.v), p.lengthscale, 1.0)
+    assert torch.equal(a_out, b_out) and torch.equal(a_mom, b_mom)
+    want = ["v", "x", "lengthscale", "variance", "lens", "sub"]
+    ga = api.gp_kernel_matvec_bwd(q, s, dev(p.v), p.lengthscale, 1.0, g, want=want, moments=a_mom)
+    gb = api.gp_kernel_matvec_bwd(q, s, dev(p.v), p.lengthscale, 1.0, g, want=want, moments=a_mom)
+    for k in want:
+        assert torch.equal(ga[k], gb[k]), k
+    x = dev(np.zeros((8, 2)))
+    with pytest.raises(abi.LensGPError, match="self-kernel"):
+        api.gp_kernel_matvec_train(api.Points(xy=x), None, dev(np.ones(8)), 0.1, 1.0)
+    with pytest.raises(abi.LensGPError, match="non-self"):
+        api.gp_kernel_matvec_bwd(api.Points(xy=x), None, dev(np.ones(8)), 0.1, 1.0, dev(np.ones(8)),
+                                 moments=torch.zeros((4, 8), device="cuda"))
