@@ -142,7 +142,7 @@ struct VjpP {
   const float2* xi;
   int64_t n;
   const float* sub;
-  int32_t n_sub, bulk_ok, profile;
+  int32_t n_sub, profile;
   const float2* dbeta;
   double* lens_part;
   float* sub_part;

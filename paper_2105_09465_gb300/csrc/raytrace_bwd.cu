@@ -3,32 +3,27 @@
 // of the lens and dL/d(x_h, y_h, kappa_s | theta_pm, theta_s) of every
 // subhalo, with dL/dp = -sum_i G_i . dalpha_i/dp (beta = xi - alpha).
 //
-// One CTA covers kVjThreads x kVjPpt points (each thread keeps kVjPpt points
-// and their G in registers). Lens terms are summed per thread, reduced across
-// the CTA in FP64 and written as one partial per CTA. Subhalo records are
-// staged in shared memory like the forward pass; for each subhalo a thread
-// sums over its points, the warp reduces with shuffles, and the CTA combines
-// its warps in fixed order. A final kernel adds the per-CTA partials in fixed
-// order in FP64, so results are deterministic.
+// The grid has at most one CTA per resident slot; CTA b takes the contiguous
+// point range [b n / nblk, (b + 1) n / nblk), so every CTA does the same work
+// to within one point and no wave is left partly empty. Points and their G
+// are staged through shared memory in tiles; each thread OWNS one subhalo
+// (threads loop over subhalo groups when there are more) and sweeps the
+// tile's points, reading each point as a shared-memory broadcast, so the
+// subhalo sums need no cross-thread reduction at all. The lens and shear
+// terms are per point: the thread that stages a point also evaluates them.
+// Per-CTA partials (FP64 lens terms, Kahan-compensated FP32 subhalo terms)
+// are added in fixed order by a final kernel, so results are deterministic.
 #include <math.h>
 
 #include "host.cuh"
 #include "problems.cuh"
-#include "subs.cuh"
 
 namespace lr {
 
 constexpr int kVjThreads = 256;
-constexpr int kVjPpt = 4;  // 1024 points per CTA: ~4 CTAs per SM on the realistic workload
-constexpr int kVjPoints = kVjThreads * kVjPpt;  // points per CTA
-constexpr int kVjChunk = 128;                   // subhalos staged per chunk
+constexpr int kVjTile = 256;  // points staged per tile
 constexpr int kVjWarps = kVjThreads / 32;
 
-__device__ __forceinline__ float warp_sum(float v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
 __device__ __forceinline__ double warp_sum_d(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -36,132 +31,124 @@ __device__ __forceinline__ double warp_sum_d(double v) {
 }
 
 struct VjSmem {
-  float raw[5 * kVjChunk];
-  SubRec recs[kVjChunk];
-  float2 extra[kVjChunk];  // tNFW: (4T, 1/theta_s); point mass: (0, theta_pm)
-  float red[kVjWarps][kVjChunk][4];
+  float4 pts[2][kVjTile];  // (x, y, G_x, G_y)
   double lred[kVjWarps][7];
-  uint64_t bar;
 };
+
+__device__ __forceinline__ void vj_kahan(float& s, float& c, float x) {
+  const float y = x - c;
+  const float t = s + y;
+  c = (t - s) - y;
+  s = t;
+}
 
 template <int PROFILE>
 __device__ __forceinline__ void vjp_body(const LensConst& L, const LensGradConst& LG, const GridDev& g,
                                          const float2* __restrict__ xi, int64_t n, const float* __restrict__ sub,
-                                         int n_sub, int bulk_ok, const float2* __restrict__ dbeta,
-                                         double* __restrict__ lens_part, float* __restrict__ sub_part, int* fault,
-                                         int64_t blk, VjSmem& sm) {
-  float* raw = sm.raw;
-  SubRec* recs = sm.recs;
-  float2* extra = sm.extra;
-  float (*red)[kVjChunk][4] = sm.red;
-  double (*lred)[7] = sm.lred;
-  uint64_t& bar = sm.bar;
+                                         int n_sub, const float2* __restrict__ dbeta, double* __restrict__ lens_part,
+                                         float* __restrict__ sub_part, int64_t blk, int64_t nblk, VjSmem& sm) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int64_t base = blk * kVjPoints;
+  const int64_t p0 = blk * n / nblk, p1 = (blk + 1) * n / nblk;
+  const int ntiles = (int)((p1 - p0 + kVjTile - 1) / kVjTile);
+  float la[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  const int ngroups = n_sub > 0 ? (n_sub + kVjThreads - 1) / kVjThreads : 1;
 
-  float px[kVjPpt], py[kVjPpt], gx[kVjPpt], gy[kVjPpt];
+  // stage point p0 + k kVjTile + tid; the first subhalo group also takes the
+  // point's lens and shear terms
+  auto load = [&](int k, bool lens_terms) -> float4 {
+    const int64_t i = p0 + (int64_t)k * kVjTile + tid;
+    if (i >= p1) return make_float4(0.f, 0.f, 0.f, 0.f);  // zero gradient: contributes nothing
+    const float2 p = xi ? xi[i] : grid_point(g, i);
+    const float2 d = dbeta[i];
+    if (lens_terms) {
+      float o5[5];
+      sple_vjp(L, LG, p.x, p.y, d.x, d.y, o5);
 #pragma unroll
-  for (int k = 0; k < kVjPpt; ++k) {
-    const int64_t i = base + k * kVjThreads + tid;
-    if (i < n) {
-      const float2 p = xi ? xi[i] : grid_point(g, i);
-      const float2 d = dbeta[i];
-      px[k] = p.x;
-      py[k] = p.y;
-      gx[k] = d.x;
-      gy[k] = d.y;
-    } else {  // zero gradient: contributes exactly nothing
-      px[k] = py[k] = gx[k] = gy[k] = 0.f;
+      for (int t = 0; t < 5; ++t) la[t] += o5[t];
+      la[5] -= fmaf(d.x, p.x, -d.y * p.y);  // dalpha/dg1 = (x, -y)
+      la[6] -= fmaf(d.x, p.y, d.y * p.x);   // dalpha/dg2 = (y, x)
+    }
+    return make_float4(p.x, p.y, d.x, d.y);
+  };
+
+  for (int grp = 0; grp < ngroups; ++grp) {
+    const int h = grp * kVjThreads + tid;
+    const bool own = h < n_sub;
+    SubRec rec{};
+    float2 ex = make_float2(0.f, 0.f);  // tNFW: (4T, 1/theta_s); point mass: (0, theta_pm)
+    if (own) {
+      const float* r = sub + 5 * (int64_t)h;
+      rec = prep_sub(r, PROFILE);
+      if (PROFILE == LR_PROFILE_POINT_MASS) {
+        ex = make_float2(0.f, __ldg(r + 2));
+      } else {
+        const float tau = __ldg(r + 4), t2 = tau * tau;
+        ex = make_float2(4.0f * t2 / ((t2 + 1.0f) * (t2 + 1.0f)), 1.0f / __ldg(r + 3));
+      }
+    }
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f, c0 = 0.f, c1 = 0.f, c2 = 0.f, c3 = 0.f;
+    float4 P = ntiles > 0 ? load(0, grp == 0) : make_float4(0.f, 0.f, 0.f, 0.f);
+    sm.pts[0][tid] = P;
+    __syncthreads();
+    for (int k = 0; k < ntiles; ++k) {
+      const int buf = k & 1;
+      if (k + 1 < ntiles) P = load(k + 1, grp == 0);
+      const int cnt = (int)min((int64_t)kVjTile, p1 - p0 - (int64_t)k * kVjTile);
+      if (own) {
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+#pragma unroll 4
+        for (int j = 0; j < cnt; ++j) {
+          const float4 Q = sm.pts[buf][j];
+          const float dx = Q.x - rec.xh, dy = Q.y - rec.yh;
+          const float R2 = fmaf(dx, dx, dy * dy);
+          if (!(R2 > 1e-30f)) continue;
+          const float dg = fmaf(dx, Q.z, dy * Q.w);
+          const float iR2 = 1.0f / R2;
+          if (PROFILE == LR_PROFILE_POINT_MASS) {
+            const float m = rec.its2 * iR2;
+            const float q = 2.0f * dg * iR2;
+            a0 += m * fmaf(-q, dx, Q.z);
+            a1 += m * fmaf(-q, dy, Q.w);
+            a2 -= 2.0f * ex.y * dg * iR2;
+          } else {
+            float Gt, Ht;
+            tnfw_GH(rec, R2, Gt, Ht);
+            const float hg = Ht - 2.0f * Gt;
+            const float q = hg * dg * iR2;
+            a0 += rec.A * fmaf(Gt, Q.z, q * dx);
+            a1 += rec.A * fmaf(Gt, Q.w, q * dy);
+            a2 -= ex.x * Gt * dg;
+            a3 += rec.A * hg * dg * ex.y;
+          }
+        }
+        vj_kahan(s0, c0, a0);
+        vj_kahan(s1, c1, a1);
+        vj_kahan(s2, c2, a2);
+        vj_kahan(s3, c3, a3);
+      }
+      if (k + 1 < ntiles) sm.pts[buf ^ 1][tid] = P;
+      __syncthreads();
+    }
+    if (own) {
+      float* o = sub_part + (blk * n_sub + h) * 4;
+      o[0] = s0 - c0;
+      o[1] = s1 - c1;
+      o[2] = s2 - c2;
+      o[3] = s3 - c3;
     }
   }
 
-  // ---- main lens and shear
-  float la[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-  for (int k = 0; k < kVjPpt; ++k) {
-    float o5[5];
-    sple_vjp(L, LG, px[k], py[k], gx[k], gy[k], o5);
-#pragma unroll
-    for (int t = 0; t < 5; ++t) la[t] += o5[t];
-    la[5] -= fmaf(gx[k], px[k], -gy[k] * py[k]);  // dalpha/dg1 = (x, -y)
-    la[6] -= fmaf(gx[k], py[k], gy[k] * px[k]);   // dalpha/dg2 = (y, x)
-  }
+  // lens terms: warp shuffles then the warps in fixed order, FP64
 #pragma unroll
   for (int t = 0; t < 7; ++t) {
-    const double s = warp_sum_d((double)la[t]);
-    if (lane == 0) lred[warp][t] = s;
+    const double v = warp_sum_d((double)la[t]);
+    if (lane == 0) sm.lred[warp][t] = v;
   }
   __syncthreads();
   if (tid < 7) {
-    double s = 0.0;
-    for (int w = 0; w < kVjWarps; ++w) s += lred[w][tid];
-    lens_part[blk * 7 + tid] = s;
-  }
-
-  // ---- subhalos
-  if (n_sub == 0) return;
-  if (tid == 0) mbar_init(&bar, 1);
-  __syncthreads();
-  uint32_t phase = 0;
-  for (int h0 = 0; h0 < n_sub; h0 += kVjChunk) {
-    const int cnt = min(kVjChunk, n_sub - h0);
-    if (!stage_subs(sub, h0, cnt, PROFILE, raw, recs, &bar, phase, bulk_ok != 0, fault)) return;
-    for (int t = tid; t < cnt; t += kVjThreads) {
-      const float* r = raw + 5 * t;
-      if (PROFILE == LR_PROFILE_POINT_MASS) {
-        extra[t] = make_float2(0.f, r[2]);
-      } else {
-        const float t2 = r[4] * r[4];
-        extra[t] = make_float2(4.0f * t2 / ((t2 + 1.0f) * (t2 + 1.0f)), 1.0f / r[3]);
-      }
-    }
-    __syncthreads();
-    for (int h = 0; h < cnt; ++h) {
-      const SubRec rec = recs[h];
-      const float2 ex = extra[h];
-      float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-#pragma unroll
-      for (int k = 0; k < kVjPpt; ++k) {
-        const float dx = px[k] - rec.xh, dy = py[k] - rec.yh;
-        const float R2 = fmaf(dx, dx, dy * dy);
-        if (!(R2 > 1e-30f)) continue;
-        const float dg = fmaf(dx, gx[k], dy * gy[k]);
-        const float iR2 = 1.0f / R2;
-        if (PROFILE == LR_PROFILE_POINT_MASS) {
-          const float m = rec.its2 * iR2;
-          const float q = 2.0f * dg * iR2;
-          a0 += m * fmaf(-q, dx, gx[k]);
-          a1 += m * fmaf(-q, dy, gy[k]);
-          a2 -= 2.0f * ex.y * dg * iR2;
-        } else {
-          float Gt, Ht;
-          tnfw_GH(rec, R2, Gt, Ht);
-          const float hg = Ht - 2.0f * Gt;
-          const float q = hg * dg * iR2;
-          a0 += rec.A * fmaf(Gt, gx[k], q * dx);
-          a1 += rec.A * fmaf(Gt, gy[k], q * dy);
-          a2 -= ex.x * Gt * dg;
-          a3 += rec.A * hg * dg * ex.y;
-        }
-      }
-      a0 = warp_sum(a0);
-      a1 = warp_sum(a1);
-      a2 = warp_sum(a2);
-      a3 = warp_sum(a3);
-      if (lane == 0) {
-        red[warp][h][0] = a0;
-        red[warp][h][1] = a1;
-        red[warp][h][2] = a2;
-        red[warp][h][3] = a3;
-      }
-    }
-    __syncthreads();
-    for (int t = tid; t < 4 * cnt; t += kVjThreads) {
-      float s = 0.f;
-      for (int w = 0; w < kVjWarps; ++w) s += red[w][t >> 2][t & 3];
-      sub_part[(blk * n_sub + h0) * 4 + t] = s;
-    }
-    __syncthreads();
+    double v = 0.0;
+    for (int w = 0; w < kVjWarps; ++w) v += sm.lred[w][tid];
+    lens_part[blk * 7 + tid] = v;
   }
 }
 
@@ -170,24 +157,44 @@ __global__ void __launch_bounds__(kVjThreads) raytrace_vjp_kernel(const __grid_c
                                                                   const __grid_constant__ LensGradConst LG, GridDev g,
                                                                   const float2* __restrict__ xi, int64_t n,
                                                                   const float* __restrict__ sub, int n_sub,
-                                                                  int bulk_ok, const float2* __restrict__ dbeta,
+                                                                  const float2* __restrict__ dbeta,
                                                                   double* __restrict__ lens_part,
-                                                                  float* __restrict__ sub_part, int* fault) {
+                                                                  float* __restrict__ sub_part) {
   __shared__ __align__(16) VjSmem sm;
-  vjp_body<PROFILE>(L, LG, g, xi, n, sub, n_sub, bulk_ok, dbeta, lens_part, sub_part, fault, blockIdx.x, sm);
+  vjp_body<PROFILE>(L, LG, g, xi, n, sub, n_sub, dbeta, lens_part, sub_part, blockIdx.x, gridDim.x, sm);
 }
 
-__global__ void __launch_bounds__(kVjThreads) vjp_batched_kernel(const __grid_constant__ Batch<VjpP> B, int* fault) {
+__global__ void __launch_bounds__(kVjThreads) vjp_batched_kernel(const __grid_constant__ Batch<VjpP> B) {
   __shared__ __align__(16) VjSmem sm;
   const int k = batch_find(B, blockIdx.x);
   const VjpP& P = B.p[k];
   const int64_t blk = blockIdx.x - B.start[k];
+  const int64_t nblk = B.start[k + 1] - B.start[k];
   if (P.profile == LR_PROFILE_POINT_MASS)
-    vjp_body<LR_PROFILE_POINT_MASS>(P.L, P.LG, P.g, P.xi, P.n, P.sub, P.n_sub, P.bulk_ok, P.dbeta, P.lens_part,
-                                    P.sub_part, fault, blk, sm);
+    vjp_body<LR_PROFILE_POINT_MASS>(P.L, P.LG, P.g, P.xi, P.n, P.sub, P.n_sub, P.dbeta, P.lens_part, P.sub_part,
+                                    blk, nblk, sm);
   else
-    vjp_body<LR_PROFILE_TNFW>(P.L, P.LG, P.g, P.xi, P.n, P.sub, P.n_sub, P.bulk_ok, P.dbeta, P.lens_part,
-                              P.sub_part, fault, blk, sm);
+    vjp_body<LR_PROFILE_TNFW>(P.L, P.LG, P.g, P.xi, P.n, P.sub, P.n_sub, P.dbeta, P.lens_part, P.sub_part, blk,
+                              nblk, sm);
+}
+
+// CTAs of the VJP for n points: one per resident slot of the device at most
+// (and at most one per kVjTile points), so a launch is a single full wave.
+int64_t vjp_blocks(int64_t n) {
+  if (n <= 0) return 0;
+  static int slots[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
+  if (slots[dev] == 0) {
+    int n_sm = 1, occ = 1;
+    if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) n_sm = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, raytrace_vjp_kernel<LR_PROFILE_TNFW>, kVjThreads, 0) !=
+        cudaSuccess)
+      occ = 1;
+    slots[dev] = (occ > 0 ? occ : 1) * n_sm;
+  }
+  const int64_t nb = (n + kVjTile - 1) / kVjTile;
+  return nb < slots[dev] ? nb : slots[dev];
 }
 
 // Fixed-order FP64 sum of the per-CTA partials: one warp per output value
@@ -229,8 +236,6 @@ __global__ void vjp_final_batched_kernel(const __grid_constant__ Batch<VjpFinalP
 }
 
 lr_status launch_vjp_batched(const VjpP* p, int count, cudaStream_t s) {
-  int* fault = fault_ptr();
-  LR_REQUIRE(fault != nullptr, "could not resolve the device fault word");
   for (int b0 = 0; b0 < count; b0 += kMaxBatch) {
     Batch<VjpP> B;
     B.count = count - b0 < kMaxBatch ? count - b0 : kMaxBatch;
@@ -238,11 +243,11 @@ lr_status launch_vjp_batched(const VjpP* p, int count, cudaStream_t s) {
     for (int k = 0; k < B.count; ++k) {
       B.p[k] = p[b0 + k];
       B.start[k] = (int32_t)tot;
-      tot += (p[b0 + k].n + kVjPoints - 1) / kVjPoints;
+      tot += vjp_blocks(p[b0 + k].n);
     }
     B.start[B.count] = (int32_t)tot;
     if (tot == 0) continue;
-    vjp_batched_kernel<<<(unsigned)tot, kVjThreads, 0, s>>>(B, fault);
+    vjp_batched_kernel<<<(unsigned)tot, kVjThreads, 0, s>>>(B);
     LR_CHECK_CUDA(cudaGetLastError());
   }
   return LR_OK;
@@ -301,7 +306,7 @@ lr_status make_lens_grad_const(const lr_lens* lens, LensGradConst* out) {
 }
 
 size_t raytrace_vjp_ws(int64_t n, int32_t n_sub) {
-  const int64_t nblk = (n + kVjPoints - 1) / kVjPoints;
+  const int64_t nblk = vjp_blocks(n);
   return align256(sizeof(double) * 7 * (size_t)nblk) + align256(sizeof(float) * 4 * (size_t)n_sub * (size_t)nblk);
 }
 
@@ -313,25 +318,22 @@ lr_status launch_raytrace_vjp(const lr_points* p, const float2* dbeta, double* d
   LensGradConst G;
   st = make_lens_grad_const(p->lens, &G);
   if (st != LR_OK) return st;
-  const int64_t nblk = (p->n + kVjPoints - 1) / kVjPoints;
+  const int64_t nblk = vjp_blocks(p->n);
   if (nblk == 0) {
     if (d_lens) LR_CHECK_CUDA(cudaMemsetAsync(d_lens, 0, 7 * sizeof(double), s));
     if (d_sub && p->n_sub) LR_CHECK_CUDA(cudaMemsetAsync(d_sub, 0, 4 * sizeof(double) * p->n_sub, s));
     return LR_OK;
   }
-  int* fault = fault_ptr();
-  LR_REQUIRE(fault != nullptr, "could not resolve the device fault word");
   double* lens_part = static_cast<double*>(ws);
   float* sub_part = reinterpret_cast<float*>(static_cast<char*>(ws) + align256(sizeof(double) * 7 * (size_t)nblk));
   const GridDev g = p->xy ? GridDev{} : grid_dev(p->grid);
-  const int bulk_ok = (((uintptr_t)p->sub & 15u) == 0) ? 1 : 0;
   const float2* xi = reinterpret_cast<const float2*>(p->xy);
   if (p->profile == LR_PROFILE_POINT_MASS)
     raytrace_vjp_kernel<LR_PROFILE_POINT_MASS><<<(unsigned)nblk, kVjThreads, 0, s>>>(
-        L, G, g, xi, p->n, p->sub, p->n_sub, bulk_ok, dbeta, lens_part, sub_part, fault);
+        L, G, g, xi, p->n, p->sub, p->n_sub, dbeta, lens_part, sub_part);
   else
     raytrace_vjp_kernel<LR_PROFILE_TNFW><<<(unsigned)nblk, kVjThreads, 0, s>>>(
-        L, G, g, xi, p->n, p->sub, p->n_sub, bulk_ok, dbeta, lens_part, sub_part, fault);
+        L, G, g, xi, p->n, p->sub, p->n_sub, dbeta, lens_part, sub_part);
   LR_CHECK_CUDA(cudaGetLastError());
   const int64_t warps = 7 + 4 * (int64_t)p->n_sub;
   vjp_final_kernel<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, s>>>(lens_part, sub_part, (int)nblk, p->n_sub,
@@ -349,13 +351,12 @@ lr_status make_vjp_problem(const lr_points* p, const float2* dbeta, double* d_le
   if (st != LR_OK) return st;
   st = make_lens_grad_const(p->lens, &v.LG);
   if (st != LR_OK) return st;
-  const int64_t nblk = (p->n + kVjPoints - 1) / kVjPoints;
+  const int64_t nblk = vjp_blocks(p->n);
   v.g = p->xy ? GridDev{} : grid_dev(p->grid);
   v.xi = reinterpret_cast<const float2*>(p->xy);
   v.n = p->n;
   v.sub = p->sub;
   v.n_sub = p->n_sub;
-  v.bulk_ok = (((uintptr_t)p->sub & 15u) == 0) ? 1 : 0;
   v.profile = p->profile;
   v.dbeta = dbeta;
   v.lens_part = static_cast<double*>(ws);
