@@ -82,14 +82,27 @@ __device__ __forceinline__ void sple_alpha(const LensConst& L, float x, float y,
 // Fast FP32 helpers for the subhalo terms (hardware reciprocal, reciprocal
 // square root and log2; each within a few ulp, far inside the 1e-6 arcsec
 // deflection budget of a subhalo whose deflection is at most ~0.1 arcsec).
-__device__ __forceinline__ float fsqrt_pos(float x) { return x * rsqrtf(x); }  // x > 0
+// The .ftz forms flush subnormal inputs, which none of these arguments are
+// (they are squared distances and ratios of order 1e-20 and up), and so skip
+// the subnormal handling the non-ftz forms carry.
+__device__ __forceinline__ float frsqrt(float x) {
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float fsqrt_pos(float x) { return x * frsqrt(x); }  // x > 0
 __device__ __forceinline__ float fdiv(float a, float b) { return __fdividef(a, b); }
 __device__ __forceinline__ float frcp(float b) {
   float r;
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(b));
   return r;
 }
-__device__ __forceinline__ float flog(float x) { return __logf(x); }
+// ln x = log2(x) ln 2
+__device__ __forceinline__ float flog(float x) {
+  float r;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r * 0.69314718055994531f;
+}
 
 // arctan(s) / s for s > 0, given is = 1/s. With t = min(s, 1/s) and u = t^2,
 // arctan(t) = t P(u), where P is a degree-8 polynomial fitted for this
@@ -109,7 +122,7 @@ __device__ __forceinline__ float atan_over(float s, float is) {
   p = fmaf(p, u, 1.999261826e-01f);
   p = fmaf(p, u, -3.333307207e-01f);
   p = fmaf(p, u, 1.0f);
-  const float at = t * p;
+  const float at = __fmul_rn(t, p);  // not contracted: the same rounding in every caller
   return (s <= 1.0f ? at : 1.57079632679f - at) * is;
 }
 
@@ -160,10 +173,11 @@ __device__ __forceinline__ float tnfw_m(const SubRec& h, float R2) {
     const float dl = dlx2 * x2;
     const float ratio = (dl != 0.f) ? fdiv(log1pf(dl), dl) : 1.0f;
     const float t2m1 = h.tau2 - 1.0f;
-    G = fmaf(2.0f, F, -kPi * itp) + t2m1 * (F * is1 + dlx2 * ratio + L * frcp(h.tau) * itp);
+    G = fmaf(t2m1, fmaf(F, is1, fmaf(dlx2, ratio, __fmul_rn(__fmul_rn(L, frcp(h.tau)), itp))),
+             fmaf(2.0f, F, __fmul_rn(-kPi, itp)));
   } else {
     const float t2m1 = h.tau2 - 1.0f;
-    const float B = fmaf(fmaf(2.0f, x2, t2m1), F, h.C) + st * fmaf(h.t2m1_t, L, -kPi);
+    const float B = fmaf(st, fmaf(h.t2m1_t, L, -kPi), fmaf(fmaf(2.0f, x2, t2m1), F, h.C));
     G = B * frcp(x2);
   }
   return h.A * G;
@@ -171,7 +185,27 @@ __device__ __forceinline__ float tnfw_m(const SubRec& h, float R2) {
 
 // Point mass: alpha = theta_pm^2 (dx, dy) / R^2.
 __device__ __forceinline__ float pointmass_m(const SubRec& h, float R2) {
-  return (R2 > 1e-30f) ? h.its2 / R2 : 0.f;
+  return (R2 > 1e-30f) ? h.its2 * frcp(R2) : 0.f;
+}
+
+// The far side of the tNFW profile, x^2 - 1 >= 0.05 (arccos form of F,
+// direct bracket), as straight-line code so that several pairs can be
+// interleaved; there it evaluates exactly the operations of tnfw_m /
+// tnfw_GH, so the results are bitwise the same. Other x^2 give a finite
+// value that the caller replaces.
+__device__ __forceinline__ bool tnfw_is_far(float x2) { return x2 - 1.0f >= 0.05f; }
+
+__device__ __forceinline__ float tnfw_m_far(const SubRec& h, float x2) {
+  const float xx = fsqrt_pos(x2);
+  const float eps = fmaxf(x2 - 1.0f, 0.05f);
+  const float s = fsqrt_pos(eps);
+  const float F = atan_over(s, frcp(s));
+  const float st = fsqrt_pos(h.tau2 + x2);
+  const float itp = frcp(h.tau + st);
+  const float L = flog(xx * itp);
+  const float t2m1 = h.tau2 - 1.0f;
+  const float B = fmaf(st, fmaf(h.t2m1_t, L, -kPi), fmaf(fmaf(2.0f, x2, t2m1), F, h.C));
+  return h.A * (B * frcp(x2));
 }
 
 // Converts a raw subhalo record (5 floats) into the prepared form.
@@ -190,7 +224,7 @@ __device__ __forceinline__ SubRec prep_sub(const float* r, int profile) {
     h.tau = tau;
     h.tau2 = t2;
     h.t2m1_t = (t2 - 1.0f) / tau;
-    h.C = tau * kPi + (t2 - 1.0f) * logf(tau);
+    h.C = fmaf(t2 - 1.0f, logf(tau), __fmul_rn(tau, kPi));  // explicit rounding: the same in every kernel
   }
   return h;
 }
@@ -225,9 +259,10 @@ __device__ __forceinline__ void tnfw_GH(const SubRec& h, float R2, float& Gt, fl
     const float dlx2 = -fmaf(h.tau, is1, itp) * itp;
     const float dl = dlx2 * x2;
     const float ratio = (dl != 0.f) ? fdiv(log1pf(dl), dl) : 1.0f;
-    Gt = fmaf(2.0f, F, -kPi * itp) + t2m1 * (F * is1 + dlx2 * ratio + L * frcp(h.tau) * itp);
+    Gt = fmaf(t2m1, fmaf(F, is1, fmaf(dlx2, ratio, __fmul_rn(__fmul_rn(L, frcp(h.tau)), itp))),
+              fmaf(2.0f, F, __fmul_rn(-kPi, itp)));
   } else {
-    const float B = fmaf(fmaf(2.0f, x2, t2m1), F, h.C) + st * fmaf(h.t2m1_t, L, -kPi);
+    const float B = fmaf(st, fmaf(h.t2m1_t, L, -kPi), fmaf(fmaf(2.0f, x2, t2m1), F, h.C));
     Gt = B * frcp(x2);
   }
   const float eps = x2 - 1.0f;
@@ -244,7 +279,24 @@ __device__ __forceinline__ void tnfw_GH(const SubRec& h, float R2, float& Gt, fl
     omf = (1.0f - F) * frcp(eps);
   }
   const float ist = frcp(st);
-  Ht = fmaf(2.0f, F, (h.tau2 + 1.0f) * omf) + ist * fmaf(h.t2m1_t, L, -kPi);
+  Ht = fmaf(ist, fmaf(h.t2m1_t, L, -kPi), fmaf(2.0f, F, __fmul_rn(h.tau2 + 1.0f, omf)));
+}
+
+// tnfw_GH on the far side (see tnfw_m_far).
+__device__ __forceinline__ void tnfw_GH_far(const SubRec& h, float x2, float& Gt, float& Ht) {
+  const float xx = fsqrt_pos(x2);
+  const float eps = fmaxf(x2 - 1.0f, 0.05f);
+  const float s = fsqrt_pos(eps);
+  const float F = atan_over(s, frcp(s));
+  const float st = fsqrt_pos(h.tau2 + x2);
+  const float itp = frcp(h.tau + st);
+  const float L = flog(xx * itp);
+  const float t2m1 = h.tau2 - 1.0f;
+  const float B = fmaf(st, fmaf(h.t2m1_t, L, -kPi), fmaf(fmaf(2.0f, x2, t2m1), F, h.C));
+  Gt = B * frcp(x2);
+  const float omf = (1.0f - F) * frcp(eps);
+  const float ist = frcp(st);
+  Ht = fmaf(ist, fmaf(h.t2m1_t, L, -kPi), fmaf(2.0f, F, __fmul_rn(h.tau2 + 1.0f, omf)));
 }
 
 // Per-lens constants for the SPLE gradient (host-prepared).

@@ -22,11 +22,37 @@ __global__ void grid_points_kernel(GridDev g, int64_t n, float2* out) {
   if (i < n) out[i] = grid_point(g, i);
 }
 
+__device__ __forceinline__ void kahan2(float m, float dx, float dy, float& sx, float& cx, float& sy, float& cy) {
+  const float yx = fmaf(m, dx, -cx);
+  const float tx = sx + yx;
+  cx = (tx - sx) - yx;
+  sx = tx;
+  const float yy = fmaf(m, dy, -cy);
+  const float ty = sy + yy;
+  cy = (ty - sy) - yy;
+  sy = ty;
+}
+
 template <int PROFILE>
 __device__ __forceinline__ void add_subs(const SubRec* recs, int cnt, float x, float y, float& sx, float& cx,
                                          float& sy, float& cy) {
-#pragma unroll 2
-  for (int t = 0; t < cnt; ++t) {
+  int t = 0;
+  if (PROFILE == LR_PROFILE_TNFW) {
+    // two subhalos per step on the straight-line far-side form (the rare
+    // near pairs are redone by the general form); same sums, same order
+    for (; t + 1 < cnt; t += 2) {
+      const SubRec ha = recs[t], hb = recs[t + 1];
+      const float dxa = x - ha.xh, dya = y - ha.yh, dxb = x - hb.xh, dyb = y - hb.yh;
+      const float R2a = fmaf(dxa, dxa, dya * dya), R2b = fmaf(dxb, dxb, dyb * dyb);
+      const float x2a = R2a * ha.its2, x2b = R2b * hb.its2;
+      float ma = tnfw_m_far(ha, x2a), mb = tnfw_m_far(hb, x2b);
+      if (!tnfw_is_far(x2a)) ma = tnfw_m(ha, R2a);
+      if (!tnfw_is_far(x2b)) mb = tnfw_m(hb, R2b);
+      kahan2(ma, dxa, dya, sx, cx, sy, cy);
+      kahan2(mb, dxb, dyb, sx, cx, sy, cy);
+    }
+  }
+  for (; t < cnt; ++t) {
     const SubRec h = recs[t];
     const float dx = x - h.xh, dy = y - h.yh;
     const float R2 = fmaf(dx, dx, dy * dy);

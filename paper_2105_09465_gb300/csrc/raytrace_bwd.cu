@@ -35,6 +35,19 @@ struct VjSmem {
   double lred[kVjWarps][7];
 };
 
+// One tNFW pair's terms of the four subhalo sums (with explicit roundings,
+// so every caller and every kernel that inlines it sums the same values).
+__device__ __forceinline__ void vj_accum(const SubRec& rec, float2 ex, float dx, float dy, float gx, float gy,
+                                         float R2, float Gt, float Ht, float& a0, float& a1, float& a2, float& a3) {
+  const float dg = fmaf(dx, gx, __fmul_rn(dy, gy));
+  const float hg = fmaf(-2.0f, Gt, Ht);
+  const float q = __fmul_rn(__fmul_rn(hg, dg), frcp(R2));
+  a0 = fmaf(rec.A, fmaf(Gt, gx, __fmul_rn(q, dx)), a0);
+  a1 = fmaf(rec.A, fmaf(Gt, gy, __fmul_rn(q, dy)), a1);
+  a2 = fmaf(-__fmul_rn(ex.x, Gt), dg, a2);
+  a3 = fmaf(__fmul_rn(__fmul_rn(rec.A, hg), dg), ex.y, a3);
+}
+
 __device__ __forceinline__ void vj_kahan(float& s, float& c, float x) {
   const float y = x - c;
   const float t = s + y;
@@ -96,30 +109,43 @@ __device__ __forceinline__ void vjp_body(const LensConst& L, const LensGradConst
       const int cnt = (int)min((int64_t)kVjTile, p1 - p0 - (int64_t)k * kVjTile);
       if (own) {
         float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-#pragma unroll 4
-        for (int j = 0; j < cnt; ++j) {
+        int j = 0;
+        if (PROFILE == LR_PROFILE_TNFW) {
+          // two points per step on the straight-line far-side form (the rare
+          // near pairs are redone by the general form); same sums, same order
+          for (; j + 1 < cnt; j += 2) {
+            const float4 Qa = sm.pts[buf][j], Qb = sm.pts[buf][j + 1];
+            const float dxa = Qa.x - rec.xh, dya = Qa.y - rec.yh, dxb = Qb.x - rec.xh, dyb = Qb.y - rec.yh;
+            const float R2a = fmaf(dxa, dxa, dya * dya), R2b = fmaf(dxb, dxb, dyb * dyb);
+            const float x2a = R2a * rec.its2, x2b = R2b * rec.its2;
+            float Ga, Ha, Gb, Hb;
+            tnfw_GH_far(rec, x2a, Ga, Ha);
+            tnfw_GH_far(rec, x2b, Gb, Hb);
+            if (!tnfw_is_far(x2a)) tnfw_GH(rec, R2a, Ga, Ha);
+            if (!tnfw_is_far(x2b)) tnfw_GH(rec, R2b, Gb, Hb);
+            if (R2a > 1e-30f) vj_accum(rec, ex, dxa, dya, Qa.z, Qa.w, R2a, Ga, Ha, a0, a1, a2, a3);
+            if (R2b > 1e-30f) vj_accum(rec, ex, dxb, dyb, Qb.z, Qb.w, R2b, Gb, Hb, a0, a1, a2, a3);
+          }
+        }
+        for (; j < cnt; ++j) {
           const float4 Q = sm.pts[buf][j];
           const float dx = Q.x - rec.xh, dy = Q.y - rec.yh;
           const float R2 = fmaf(dx, dx, dy * dy);
           if (!(R2 > 1e-30f)) continue;
-          const float dg = fmaf(dx, Q.z, dy * Q.w);
-          const float iR2 = 1.0f / R2;
-          if (PROFILE == LR_PROFILE_POINT_MASS) {
-            const float m = rec.its2 * iR2;
-            const float q = 2.0f * dg * iR2;
-            a0 += m * fmaf(-q, dx, Q.z);
-            a1 += m * fmaf(-q, dy, Q.w);
-            a2 -= 2.0f * ex.y * dg * iR2;
-          } else {
+          if (PROFILE == LR_PROFILE_TNFW) {
             float Gt, Ht;
             tnfw_GH(rec, R2, Gt, Ht);
-            const float hg = Ht - 2.0f * Gt;
-            const float q = hg * dg * iR2;
-            a0 += rec.A * fmaf(Gt, Q.z, q * dx);
-            a1 += rec.A * fmaf(Gt, Q.w, q * dy);
-            a2 -= ex.x * Gt * dg;
-            a3 += rec.A * hg * dg * ex.y;
+            vj_accum(rec, ex, dx, dy, Q.z, Q.w, R2, Gt, Ht, a0, a1, a2, a3);
+            continue;
           }
+          // point mass
+          const float dg = fmaf(dx, Q.z, dy * Q.w);
+          const float iR2 = frcp(R2);
+          const float m = rec.its2 * iR2;
+          const float q = 2.0f * dg * iR2;
+          a0 += m * fmaf(-q, dx, Q.z);
+          a1 += m * fmaf(-q, dy, Q.w);
+          a2 -= 2.0f * ex.y * dg * iR2;
         }
         vj_kahan(s0, c0, a0);
         vj_kahan(s1, c1, a1);
