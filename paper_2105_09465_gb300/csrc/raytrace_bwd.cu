@@ -20,8 +20,8 @@
 
 namespace lr {
 
-constexpr int kVjThreads = 256;
-constexpr int kVjTile = 256;  // points staged per tile
+constexpr int kVjThreads = 128;
+constexpr int kVjTile = kVjThreads;  // points staged per tile (one per thread)
 constexpr int kVjWarps = kVjThreads / 32;
 
 __device__ __forceinline__ double warp_sum_d(double v) {
