@@ -297,7 +297,7 @@ def run_extensions(p, dev, rates, sm_max, flush, stream) -> dict:
     s = api.Points(grid=p.ygrid)
     v = torch.from_numpy(p.v).to(dev)
     ms = event_time(lambda: api.gp_windowed_matvec(bp, z, s, v, p.lengthscale), nk, stream, flush)
-    out["windowed_matvec<grid>"] = dict(roof(pix.n * p.m, ms, 1, 4), n=pix.n, m=p.m,
+    out["windowed_matvec<grid>"] = dict(roof(pix.n * p.m, ms, 1, 3), n=pix.n, m=p.m,
                                         workload=f"{pix.nx}x{pix.ny} ray-traced pixel centres with their "
                                                  f"window covariances x {p.ygrid.nx}x{p.ygrid.ny} grid")
     out["pixel_shapes"] = {"ms": event_time(lambda: api.pixel_shapes(bp, pix.nx, pix.ny), nk, stream, flush)}

@@ -22,6 +22,7 @@ constexpr int kWnRows = kWnThreads * kWnR;
 constexpr int kWnTile = 256;
 constexpr int kWnPairs = kWnTile / 2;
 static_assert(kWnPairs == kWnThreads, "one source pair per thread when staging");
+constexpr int kWnSeg = 16;  // grid sub-segment (columns) of the tile-local abscissae
 
 __global__ void pixel_shapes_kernel(const float2* __restrict__ p, int32_t W, int32_t H, float* __restrict__ z) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -76,8 +77,10 @@ __device__ __forceinline__ void wn_load(const WnArgs& A, int t, int p, float4& P
   wn_tile(A, t, j0, cnt, grow);
   const int a = 2 * p, b = 2 * p + 1;
   if (GRID) {
+    // abscissae relative to the centre column of their 16-column sub-segment
     const int c0 = (int)(j0 - (int64_t)grow * A.g.W);
-    P = make_float4((a < cnt) ? -grid_x(A.g, c0 + a) : 0.f, (b < cnt) ? -grid_x(A.g, c0 + b) : 0.f, 0.f, 0.f);
+    const float o = grid_x(A.g, c0 + kWnSeg * (a / kWnSeg) + kWnSeg / 2);
+    P = make_float4((a < cnt) ? grid_x(A.g, c0 + a) - o : 0.f, (b < cnt) ? grid_x(A.g, c0 + b) - o : 0.f, 0.f, 0.f);
   } else {
     const float2 qa = (a < cnt) ? __ldg(A.q + j0 + a) : wf2(0.f, 0.f);
     const float2 qb = (b < cnt) ? __ldg(A.q + j0 + b) : wf2(0.f, 0.f);
@@ -135,27 +138,48 @@ __global__ void __launch_bounds__(kWnThreads) windowed_kernel(const __grid_const
     wn_tile(A, t, j0, cnt, grow);
     const int np = (cnt + 1) >> 1;
     if (GRID) {
-      // uniform y on a grid row: the dy terms are per row and tile
+      // Uniform y on a grid row: completing the square in dx,
+      //   -e = -mxx (dx + kap dy)^2 + lam dy^2,  kap = mxy2 / (2 mxx),
+      //   lam = mxy2^2 / (4 mxx) - myy >= 0,
+      // so with s = sqrt(-mxx) and w = s ((x_i - o) + kap dy) - s (x_j - o)
+      // the pair needs one packed FMA for w of two pairs, one for
+      // t = w^2 + lam dy^2, the exp2 of -t and one packed FMA to accumulate.
       const float yt = grid_y(A.g, grow);
-      float2 cy[kWnR], ey[kWnR];
+      const int c0 = (int)(j0 - (int64_t)grow * A.g.W);
+      float kdy[kWnR], sr[kWnR];
+      float2 t0[kWnR], ns[kWnR];
 #pragma unroll
       for (int r = 0; r < kWnR; ++r) {
-        const float dy = yq[r].x - yt;
-        cy[r] = wf2(mxy2[r].x * dy, mxy2[r].x * dy);
-        ey[r] = wf2(myy[r].x * dy * dy, myy[r].x * dy * dy);
+        const float a2 = mxx[r].x, dy = yq[r].x - yt;
+        const float kap = mxy2[r].x / (2.0f * a2);
+        const float lam = fmaxf(fmaf(mxy2[r].x, kap * 0.5f, -myy[r].x), 0.f);
+        sr[r] = sqrtf(-a2);
+        kdy[r] = kap * dy;
+        t0[r] = wf2(lam * dy * dy, lam * dy * dy);
+        ns[r] = wf2(-sr[r], -sr[r]);
       }
-#pragma unroll 2
-      for (int p = 0; p < np; ++p) {
-        const float4 Q = sP[buf][p];
-        const float2 W = sV[buf][p];
-        const float2 nx = wf2(Q.x, Q.y);
+      const int nsg = (cnt + kWnSeg - 1) / kWnSeg;
+      for (int sg = 0; sg < nsg; ++sg) {
+        const float o = grid_x(A.g, c0 + kWnSeg * sg + kWnSeg / 2);
+        float2 qc[kWnR];
 #pragma unroll
         for (int r = 0; r < kWnR; ++r) {
-          const float2 dx = __fadd2_rn(xq[r], nx);
-          const float2 u = __ffma2_rn(mxx[r], dx, cy[r]);
-          const float2 e = __ffma2_rn(dx, u, ey[r]);
-          const float2 k = wf2(ex2_approx(e.x), ex2_approx(e.y));
-          acc[r] = __ffma2_rn(k, W, acc[r]);
+          const float q = sr[r] * ((xq[r].x - o) + kdy[r]);  // small terms first: no large-ulp rounding
+          qc[r] = wf2(q, q);
+        }
+#pragma unroll
+        for (int pp = 0; pp < kWnSeg / 2; ++pp) {
+          const int p = sg * (kWnSeg / 2) + pp;
+          const float4 Q = sP[buf][p];
+          const float2 W = sV[buf][p];
+          const float2 X = wf2(Q.x, Q.y);
+#pragma unroll
+          for (int r = 0; r < kWnR; ++r) {
+            const float2 w = __ffma2_rn(ns[r], X, qc[r]);
+            const float2 t = __ffma2_rn(w, w, t0[r]);
+            const float2 k = wf2(ex2_approx(-t.x), ex2_approx(-t.y));
+            acc[r] = __ffma2_rn(k, W, acc[r]);
+          }
         }
       }
     } else {

@@ -60,3 +60,21 @@ def test_zero_windows_reduce_to_the_point_kernel():
     a = host(api.gp_windowed_matvec(dev(x), dev(z), api.Points(xy=dev(x)), dev(v), 0.08))
     b = host(api.gp_kernel_matvec(api.Points(xy=dev(x)), None, dev(v), 0.08 / np.sqrt(2.0), 1.0 / (np.pi * 0.0064)))
     np.testing.assert_allclose(a, b, rtol=1e-5, atol=1e-5 * np.abs(b).max())
+
+
+def test_windowed_grid_realistic_scales(orc):
+    """Pixel windows of a lensed 120 x 120 image at the realistic pixel size
+    (0.05 arcsec) against a 128 x 128 source grid over the field padded by 20 %,
+    length scale 4/3 of its spacing: the grid path's completed square at the
+    workload's coordinate magnitudes."""
+    p = W.realistic(seed=11, side=120, ss=1, n_sub=0)
+    g = p.xgrid
+    _, b = orc.raytrace(orc.grid_points(*g.astuple()), p.lens.astuple())
+    b = b.astype(np.float32)
+    zr = orc.pixel_shapes(b, g.nx, g.ny).astype(np.float32)
+    yg = p.ygrid
+    q = orc.grid_points(*yg.astuple())
+    v = np.random.default_rng(12).standard_normal(len(q)).astype(np.float32)
+    got = host(api.gp_windowed_matvec(dev(b), dev(zr), api.Points(grid=yg), dev(v), p.lengthscale))
+    ref, ab = orc.windowed_matvec(b, zr, q, v, p.lengthscale)
+    assert_matvec_close(got, ref, ab, what="windowed (realistic grid)")
