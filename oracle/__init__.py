@@ -79,6 +79,8 @@ def lib():
         L.orc_pixel_shapes.argtypes = [_P, _I32, _I32, _P]
         L.orc_windowed_matvec.argtypes = [_P, _P, _I64, _P, _I64, _P, _D, _P, _P, _P]
         L.orc_knn_r2.argtypes = [_P, _I64, _I32, _P, _I64, _P]
+        L.orc_windowed_vjp.argtypes = [_P, _P, _I64, _P, _I64, _P, _D, _P] + [_P] * 10
+        L.orc_pixel_shapes_vjp.argtypes = [_P, _I32, _I32, _P, _P]
         L.orc_kernel_matvec.argtypes = [_P, _I64, _P, _I64, _P, _D, _D, _P, _I64, _P, _P, _P]
         L.orc_kernel_matvec_vjp.argtypes = [_P, _I64, _P, _I64, _P, _D, _D, _P, _I32, _P, _P, _P, _P, _P, _P]
         L.orc_num_threads.restype = _I32
@@ -189,6 +191,37 @@ def windowed_matvec(p, z, q, v, lengthscale, dense=False):
     T = np.empty((n, m), np.float64) if dense else None
     lib().orc_windowed_matvec(_ptr(p), _ptr(z), n, _ptr(q), m, _ptr(v), lengthscale, _ptr(out), _ptr(ab), _ptr(T))
     return (out, ab, T) if dense else (out, ab)
+
+
+def windowed_vjp(p, z, q, v, lengthscale, g, with_abs=False):
+    """Gradients of Loss = sum_i g_i out_i through windowed_matvec: dict with
+    d_v (m), d_p (n, 2), d_q (m, 2), d_z (n, 3: Zxx, Zxy, Zyy; the off-diagonal
+    entry counted in both positions), d_len; with_abs adds *_abs scales."""
+    p, q = _pairs(p), _pairs(q)
+    z = np.ascontiguousarray(z, np.float64)
+    v = np.ascontiguousarray(v, np.float64).reshape(-1)
+    g = np.ascontiguousarray(g, np.float64).reshape(-1)
+    n, m = p.shape[0], q.shape[0]
+    R = {"d_v": np.empty(m), "d_p": np.empty((n, 2)), "d_q": np.empty((m, 2)), "d_z": np.empty((n, 3)),
+         "d_len": np.empty(1)}
+    A = {k + "_abs": np.empty_like(a) for k, a in R.items()} if with_abs else {}
+    ab = [A.get(k + "_abs") for k in ("d_v", "d_p", "d_q", "d_z", "d_len")]
+    lib().orc_windowed_vjp(_ptr(p), _ptr(z), n, _ptr(q), m, _ptr(v), lengthscale, _ptr(g), _ptr(R["d_v"]),
+                           _ptr(R["d_p"]), _ptr(R["d_q"]), _ptr(R["d_z"]), _ptr(R["d_len"]), *map(_ptr, ab))
+    R["d_len"] = float(R["d_len"][0])
+    if with_abs:
+        A["d_len_abs"] = float(A["d_len_abs"][0])
+        R.update(A)
+    return R
+
+
+def pixel_shapes_vjp(p, W, H, dz):
+    """dL/dp (W*H, 2) through pixel_shapes given dL/dZ (W*H, 3)."""
+    p = _pairs(p)
+    dz = np.ascontiguousarray(dz, np.float64)
+    dp = np.empty((W * H, 2), np.float64)
+    lib().orc_pixel_shapes_vjp(_ptr(p), W, H, _ptr(dz), _ptr(dp))
+    return dp
 
 
 def knn_r2(q, k, rows=None):

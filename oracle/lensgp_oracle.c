@@ -545,6 +545,127 @@ ORC_API void orc_windowed_matvec(const double* p, const double* z, int64_t n, co
   }
 }
 
+/* Gradients of Loss = sum_i g_i out_i through the windowed transmission
+ * reduction (out_i = sum_k G(p_i - q_k, C_i) v_k, C_i = Z_i + (l^2/2) I), by
+ * differentiating each Gaussian term: with d = p_i - q_k, M = C_i^-1 and
+ * u = M d,
+ *   dG/dp_i = -G u,  dG/dq_k = G u,  dG/dC_i = G (u u^T - M) / 2,
+ * and dC_i/dl = l I. Outputs (each may be NULL):
+ *   d_v[m], d_p[n][2], d_q[m][2], d_z[n][3] (dL/d(Zxx, Zxy, Zyy), the
+ *   off-diagonal entry counted in both symmetric positions), d_len[1];
+ * abs_* (same shapes, optional) receive the sums of absolute terms. */
+ORC_API void orc_windowed_vjp(const double* p, const double* z, int64_t n, const double* q, int64_t m,
+                              const double* v, double lengthscale, const double* g, double* d_v, double* d_p,
+                              double* d_q, double* d_z, double* d_len, double* abs_v, double* abs_p, double* abs_q,
+                              double* abs_z, double* abs_len) {
+  const double half_s = 0.5 * lengthscale * lengthscale;
+  double* dq_acc = (double*)calloc((size_t)(3 * m + 1), sizeof(double));
+  double* dq_abs = (double*)calloc((size_t)(3 * m + 1), sizeof(double));
+  nsum len = {0, 0}, len_a = {0, 0};
+  for (int64_t i = 0; i < n; ++i) {
+    const double cxx = z[3 * i] + half_s, cxy = z[3 * i + 1], cyy = z[3 * i + 2] + half_s;
+    const double det = cxx * cyy - cxy * cxy;
+    const double mxx = cyy / det, mxy = -cxy / det, myy = cxx / det;
+    const double norm = 1.0 / (2.0 * PI * sqrt(det));
+    nsum px = {0, 0}, py = {0, 0}, zxx = {0, 0}, zxy = {0, 0}, zyy = {0, 0};
+    double apx = 0, apy = 0, azxx = 0, azxy = 0, azyy = 0;
+    for (int64_t k = 0; k < m; ++k) {
+      const double dx = p[2 * i] - q[2 * k], dy = p[2 * i + 1] - q[2 * k + 1];
+      const double ux = mxx * dx + mxy * dy, uy = mxy * dx + myy * dy;
+      const double G = norm * exp(-0.5 * (dx * ux + dy * uy));
+      const double gG = g[i] * G, gGv = gG * v[k];
+      /* row role */
+      ns_add(&px, -gGv * ux);
+      ns_add(&py, -gGv * uy);
+      apx += fabs(gGv * ux);
+      apy += fabs(gGv * uy);
+      const double cx = 0.5 * gGv * (ux * ux - mxx), cxy2 = 0.5 * gGv * (ux * uy - mxy),
+                   cy = 0.5 * gGv * (uy * uy - myy);
+      ns_add(&zxx, cx);
+      ns_add(&zxy, 2.0 * cxy2);
+      ns_add(&zyy, cy);
+      azxx += fabs(cx);
+      azxy += 2.0 * fabs(cxy2);
+      azyy += fabs(cy);
+      ns_add(&len, lengthscale * (cx + cy));
+      ns_add(&len_a, lengthscale * (fabs(cx) + fabs(cy)));
+      /* column role (sequential over i: fixed order) */
+      dq_acc[k] += gG;
+      dq_acc[m + k] += gGv * ux;
+      dq_acc[2 * m + k] += gGv * uy;
+      dq_abs[k] += fabs(gG);
+      dq_abs[m + k] += fabs(gGv * ux);
+      dq_abs[2 * m + k] += fabs(gGv * uy);
+    }
+    if (d_p) {
+      d_p[2 * i] = ns_val(&px);
+      d_p[2 * i + 1] = ns_val(&py);
+    }
+    if (abs_p) {
+      abs_p[2 * i] = apx;
+      abs_p[2 * i + 1] = apy;
+    }
+    if (d_z) {
+      d_z[3 * i] = ns_val(&zxx);
+      d_z[3 * i + 1] = ns_val(&zxy);
+      d_z[3 * i + 2] = ns_val(&zyy);
+    }
+    if (abs_z) {
+      abs_z[3 * i] = azxx;
+      abs_z[3 * i + 1] = azxy;
+      abs_z[3 * i + 2] = azyy;
+    }
+  }
+  for (int64_t k = 0; k < m; ++k) {
+    if (d_v) d_v[k] = dq_acc[k];
+    if (abs_v) abs_v[k] = dq_abs[k];
+    if (d_q) {
+      d_q[2 * k] = dq_acc[m + k];
+      d_q[2 * k + 1] = dq_acc[2 * m + k];
+    }
+    if (abs_q) {
+      abs_q[2 * k] = dq_abs[m + k];
+      abs_q[2 * k + 1] = dq_abs[2 * m + k];
+    }
+  }
+  if (d_len) *d_len = ns_val(&len);
+  if (abs_len) *abs_len = ns_val(&len_a);
+  free(dq_acc);
+  free(dq_abs);
+}
+
+/* Gradient of Loss through the pixel windows: given dL/dZ (n x 3, the
+ * off-diagonal entry counted in both positions as above), returns dL/dp
+ * (n x 2) for the W x H grid of projected centres of orc_pixel_shapes, by
+ * differentiating Z_i = (a a^T + b b^T)/(4 pi) and scattering the window
+ * vectors' gradients onto the neighbours they are differences of. */
+ORC_API void orc_pixel_shapes_vjp(const double* p, int32_t W, int32_t H, const double* dz, double* dp) {
+  (void)p;
+  memset(dp, 0, sizeof(double) * 2 * (size_t)W * (size_t)H);
+  for (int64_t r = 0; r < H; ++r)
+    for (int64_t c = 0; c < W; ++c) {
+      const int64_t i = r * W + c;
+      const int64_t cl = c > 0 ? i - 1 : i, cr = c + 1 < W ? i + 1 : i;
+      const int64_t rd = r > 0 ? i - W : i, ru = r + 1 < H ? i + W : i;
+      const double sa = (cr - cl == 2) ? 0.5 : 1.0, sb = (ru - rd == 2 * W) ? 0.5 : 1.0;
+      const double ax = sa * (p[2 * cr] - p[2 * cl]), ay = sa * (p[2 * cr + 1] - p[2 * cl + 1]);
+      const double bx = sb * (p[2 * ru] - p[2 * rd]), by = sb * (p[2 * ru + 1] - p[2 * rd + 1]);
+      const double k = 1.0 / (4.0 * PI);
+      const double gxx = dz[3 * i], gxy = dz[3 * i + 1], gyy = dz[3 * i + 2];
+      /* Zxy = k (ax ay + bx by); its gradient gxy already counts both positions */
+      const double dax = k * (2.0 * gxx * ax + gxy * ay), day = k * (gxy * ax + 2.0 * gyy * ay);
+      const double dbx = k * (2.0 * gxx * bx + gxy * by), dby = k * (gxy * bx + 2.0 * gyy * by);
+      dp[2 * cr] += sa * dax;
+      dp[2 * cr + 1] += sa * day;
+      dp[2 * cl] -= sa * dax;
+      dp[2 * cl + 1] -= sa * day;
+      dp[2 * ru] += sb * dbx;
+      dp[2 * ru + 1] += sb * dby;
+      dp[2 * rd] -= sb * dbx;
+      dp[2 * rd + 1] -= sb * dby;
+    }
+}
+
 /* Inducing-point density (Sec. 3.4, footnote to the factorisation of the
  * covariance): rho(q_k) = k / (pi r_k^2) with r_k the distance from q_k to the
  * k-th closest OTHER point of the set (the point itself excluded by index;

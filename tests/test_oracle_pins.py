@@ -557,3 +557,43 @@ def test_transmission_weights_reproduce_the_rbf_kernel(orc):
     lhs = (T * A) @ (T * A).T
     d2 = ((p[:, None, :] - p[None, :, :]) ** 2).sum(-1)
     np.testing.assert_allclose(lhs, np.exp(-d2 / (2 * ell * ell)), rtol=1e-9)
+
+
+# ---------------------------------------------------------------- windowed reduction gradients
+def _cd(f, x, h):
+    x = np.array(x, np.float64)
+    out = np.zeros_like(x)
+    for i in np.ndindex(x.shape):
+        a, b = x.copy(), x.copy()
+        a[i] += h
+        b[i] -= h
+        out[i] = (f(a) - f(b)) / (2 * h)
+    return out
+
+
+def test_windowed_vjp_by_central_differences(orc):
+    """Every gradient of sum_i g_i out_i through the windowed transmission,
+    against FP64 central differences of the forward oracle."""
+    rng = np.random.default_rng(41)
+    n, m, ell = 5, 7, 0.07
+    p = rng.uniform(-0.1, 0.1, (n, 2))
+    q = rng.uniform(-0.1, 0.1, (m, 2))
+    z = np.stack([rng.uniform(1e-4, 4e-4, n), rng.uniform(-5e-5, 5e-5, n), rng.uniform(1e-4, 4e-4, n)], -1)
+    v, g = rng.normal(size=m), rng.normal(size=n)
+    L = lambda p_, z_, q_, v_, l_: g @ orc.windowed_matvec(p_, z_, q_, v_, l_)[0]
+    R = orc.windowed_vjp(p, z, q, v, ell, g)
+    np.testing.assert_allclose(R["d_p"], _cd(lambda a: L(a, z, q, v, ell), p, 1e-6), rtol=1e-6, atol=1e-6)
+    np.testing.assert_allclose(R["d_q"], _cd(lambda a: L(p, z, a, v, ell), q, 1e-6), rtol=1e-6, atol=1e-6)
+    np.testing.assert_allclose(R["d_v"], _cd(lambda a: L(p, z, q, a, ell), v, 1e-4), rtol=1e-8)
+    np.testing.assert_allclose(R["d_z"], _cd(lambda a: L(p, a, q, v, ell), z, 1e-8), rtol=1e-5, atol=1e-3)
+    assert R["d_len"] == pytest.approx(_cd(lambda a: L(p, z, q, v, a[0]), [ell], 1e-7)[0], rel=1e-6)
+
+
+def test_pixel_shapes_vjp_by_central_differences(orc):
+    rng = np.random.default_rng(43)
+    W, H = 5, 4
+    g = (np.arange(W) - 2.0) * 0.05
+    P = np.stack(np.meshgrid(g, (np.arange(H) - 1.5) * 0.05), -1).reshape(-1, 2) + rng.normal(0, 0.01, (W * H, 2))
+    dz = rng.normal(size=(W * H, 3))
+    f = lambda a: np.sum(dz * orc.pixel_shapes(a, W, H))
+    np.testing.assert_allclose(orc.pixel_shapes_vjp(P, W, H, dz), _cd(f, P, 1e-6), rtol=1e-7, atol=1e-9)
