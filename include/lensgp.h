@@ -226,6 +226,35 @@ lr_status gp_windowed_matvec(const float* p, const float* z, int64_t n, const lr
 lr_status lr_windowed_workspace_size(int64_t n, const lr_points* source, size_t* bytes);
 
 /*
+ * Gradients of Loss = sum_i g_i out_i through gp_windowed_matvec
+ * (recompute-only). With d = p_i - q_k, C_i = Z_i + (l^2/2) I, M = C_i^-1,
+ * u = M d and G = G(d, C_i):
+ *   d_p[i] = -g_i sum_k v_k G u,          d_q[k] = v_k sum_i g_i G u,
+ *   d_v[k] = sum_i g_i G,
+ *   d_z[i] = g_i sum_k v_k G (u u^T - M)/2 as (xx, 2 xy, yy): the gradient
+ *            with respect to (Zxx, Zxy, Zyy), the off-diagonal entry
+ *            counted in both symmetric positions,
+ *   d_lengthscale = l sum_i tr(d_z-matrix_i)  (device double[1]).
+ * Sources must be explicit points (grid sources: use the stationary
+ * reduction, which is what the windowed form reduces to without windows).
+ * For an image-plane layer with q = p the total gradient of a point is
+ * d_p + d_q + gp_pixel_shapes_vjp(d_z). Every output may be NULL; the row
+ * sweep runs for d_p, d_z or d_lengthscale, the column sweep for d_v or d_q.
+ * Workspace of lr_windowed_bwd_workspace_size() bytes, 256-byte aligned.
+ */
+lr_status gp_windowed_matvec_bwd(const float* p, const float* z, int64_t n, const lr_points* source, const float* v,
+                                 float lengthscale, const float* g, float* d_v, float* d_p, float* d_q, float* d_z,
+                                 double* d_lengthscale, void* workspace, size_t workspace_bytes, lr_stream stream);
+lr_status lr_windowed_bwd_workspace_size(int64_t n, const lr_points* source, size_t* bytes);
+
+/*
+ * Gradient through gp_pixel_shapes: dp (device float[W*H][2], overwritten)
+ * = dL/dp given dz = dL/d(Zxx, Zxy, Zyy) (device float[W*H][3], off-diagonal
+ * counted in both positions) for the W x H grid of projected centres p.
+ */
+lr_status gp_pixel_shapes_vjp(const float* p, int32_t W, int32_t H, const float* dz, float* dp, lr_stream stream);
+
+/*
  * Inducing-point density (Sec. 3.4, footnote to the covariance factorisation)
  * and the transmission weights it sets, for m points q (device float[m][2]):
  *   r2_out[i] = r_k(q_i)^2, the squared distance to the k-th closest OTHER

@@ -117,6 +117,11 @@ SIGNATURES = {
                                              ctypes.c_size_t, _P]),
     "gp_partial_mvn_vjp": (ctypes.c_int32, [_P, _P, _P, ctypes.c_int32, ctypes.c_int64, _P, ctypes.c_double, _P, _P,
                                             _P, _P, _P]),
+    "gp_windowed_matvec_bwd": (ctypes.c_int32, [_P, _P, ctypes.c_int64, ctypes.POINTER(lr_points), _P, ctypes.c_float,
+                                                _P, _P, _P, _P, _P, _P, _P, ctypes.c_size_t, _P]),
+    "lr_windowed_bwd_workspace_size": (ctypes.c_int32, [ctypes.c_int64, ctypes.POINTER(lr_points),
+                                                        ctypes.POINTER(ctypes.c_size_t)]),
+    "gp_pixel_shapes_vjp": (ctypes.c_int32, [_P, ctypes.c_int32, ctypes.c_int32, _P, _P, _P]),
     "lr_windowed_workspace_size": (ctypes.c_int32, [ctypes.c_int64, ctypes.POINTER(lr_points),
                                                     ctypes.POINTER(ctypes.c_size_t)]),
     "gp_kernel_matvec_layers": (ctypes.c_int32, [ctypes.POINTER(lr_points), ctypes.POINTER(lr_points), ctypes.c_int32,

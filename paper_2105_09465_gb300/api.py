@@ -315,6 +315,43 @@ def partial_mvn_vjp(L, sd, eps, d_x, w_q: float = 1.0, stream=None):
     return d_mu, d_L, d_C, d_sd
 
 
+def gp_windowed_matvec_bwd(p: torch.Tensor, z: torch.Tensor, source: Points, v: torch.Tensor, lengthscale: float,
+                           g: torch.Tensor, want=("v", "p", "q", "z", "lengthscale"), stream=None) -> dict:
+    """Gradients of sum_i g_i out_i through gp_windowed_matvec (explicit sources)."""
+    lib = abi.load()
+    _require_cuda(p, "p", (2,))
+    _require_cuda(z, "z", (3,))
+    _require_cuda(v, "v")
+    _require_cuda(g, "g")
+    cs, k = to_c_points(source)
+    n, m = p.shape[0], cs.n
+    dev_ = p.device
+    shapes = {"v": (m,), "p": (n, 2), "q": (m, 2), "z": (n, 3)}
+    out = {key: torch.empty(shapes[key], dtype=torch.float32, device=dev_) for key in want if key in shapes}
+    if "lengthscale" in want:
+        out["lengthscale"] = torch.empty(1, dtype=torch.float64, device=dev_)
+    b = ctypes.c_size_t(0)
+    abi.check(lib.lr_windowed_bwd_workspace_size(n, ctypes.byref(cs), ctypes.byref(b)), "lr_windowed_bwd_workspace_size")
+    ws = torch.empty(max(int(b.value), 1), dtype=torch.uint8, device=dev_)
+    ptr = lambda key: out[key].data_ptr() if key in out else None
+    st = lib.gp_windowed_matvec_bwd(p.data_ptr(), z.data_ptr(), n, ctypes.byref(cs), v.data_ptr(), float(lengthscale),
+                                    g.data_ptr(), ptr("v"), ptr("p"), ptr("q"), ptr("z"), ptr("lengthscale"),
+                                    ws.data_ptr(), ws.numel(), _stream_handle(stream))
+    abi.check(st, "gp_windowed_matvec_bwd")
+    return out
+
+
+def pixel_shapes_vjp(p: torch.Tensor, W: int, H: int, dz: torch.Tensor, stream=None) -> torch.Tensor:
+    """dL/dp (W*H, 2) through pixel_shapes given dL/dZ (W*H, 3)."""
+    lib = abi.load()
+    _require_cuda(p, "p", (2,))
+    _require_cuda(dz, "dz", (3,))
+    dp = torch.empty_like(p)
+    abi.check(lib.gp_pixel_shapes_vjp(p.data_ptr(), W, H, dz.data_ptr(), dp.data_ptr(), _stream_handle(stream)),
+              "gp_pixel_shapes_vjp")
+    return dp
+
+
 GRADS = ("v", "x", "y", "lengthscale", "variance", "lens", "sub")
 
 

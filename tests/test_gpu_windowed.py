@@ -78,3 +78,39 @@ def test_windowed_grid_realistic_scales(orc):
     got = host(api.gp_windowed_matvec(dev(b), dev(zr), api.Points(grid=yg), dev(v), p.lengthscale))
     ref, ab = orc.windowed_matvec(b, zr, q, v, p.lengthscale)
     assert_matvec_close(got, ref, ab, what="windowed (realistic grid)")
+
+
+def _close(got, ref, scale, rel, what):
+    got, ref, scale = (np.asarray(a, np.float64) for a in (got, ref, scale))
+    bad = np.abs(got - ref) > rel * scale + 1e-30
+    assert not bad.any(), (what, int(bad.sum()), float(np.max(np.abs(got - ref) / (scale + 1e-300))))
+
+
+@pytest.mark.parametrize("self_points", [False, True])
+def test_windowed_backward(orc, self_points):
+    """Every gradient of sum_i g_i out_i against the FP64 oracle, on a lensed
+    pixel grid with its windows; sources explicit or the pixels themselves
+    (the image-plane layer)."""
+    g_, b = lensed_grid(orc, side=50)
+    zr = orc.pixel_shapes(b, g_.nx, g_.ny).astype(np.float32)
+    rng = np.random.default_rng(21)
+    q = b if self_points else rng.uniform(-1.2, 1.2, (2000, 2)).astype(np.float32)
+    v = rng.standard_normal(len(q)).astype(np.float32)
+    gout = rng.standard_normal(len(b)).astype(np.float32)
+    ell = 0.05
+    G = api.gp_windowed_matvec_bwd(dev(b), dev(zr), api.Points(xy=dev(q)), dev(v), ell, dev(gout))
+    R = orc.windowed_vjp(b, zr, q, v, ell, gout, with_abs=True)
+    rel = 2e-5  # of the sum of |terms|, the reduction tolerance
+    _close(host(G["v"]), R["d_v"], R["d_v_abs"], rel, "d_v")
+    _close(host(G["p"]), R["d_p"], R["d_p_abs"], rel, "d_p")
+    _close(host(G["q"]), R["d_q"], R["d_q_abs"], rel, "d_q")
+    _close(host(G["z"]), R["d_z"], R["d_z_abs"], rel, "d_z")
+    _close(host(G["lengthscale"]), [R["d_len"]], [R["d_len_abs"]], rel, "d_len")
+
+
+def test_pixel_shapes_vjp(orc):
+    g_, b = lensed_grid(orc, side=40)
+    dz = np.random.default_rng(22).standard_normal((len(b), 3)).astype(np.float32)
+    got = host(api.pixel_shapes_vjp(dev(b), g_.nx, g_.ny, dev(dz)))
+    ref = orc.pixel_shapes_vjp(b, g_.nx, g_.ny, dz)
+    np.testing.assert_allclose(got, ref, rtol=1e-4, atol=1e-5 * np.abs(ref).max())
