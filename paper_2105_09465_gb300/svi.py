@@ -1,0 +1,134 @@
+"""One stochastic-variational-inference step of the paper's lensed-GP model,
+composed from the library's kernels (Sec. 3.3 generative model, Sec. 3.4
+transmission, Sec. 3.6 ELBO, Sec. 4.2 proposals).
+
+Model for one draw:
+  theta (7 lens and shear parameters) and the source-plane layer y_sp are
+  drawn jointly from the partial multivariate-normal proposal; every
+  image-plane layer y_l from its diagonal-normal proposal;
+  beta = ray-trace of the pixel centres through theta;
+  f = T_sp y_sp + sum_l T_l y_l with
+    T_sp: the stationary reduction of beta against the source grid
+          (length scale sigma_sp / sqrt(2), weights A |pi Sigma|^-1/2 y_sp,
+          A from the grid's exact density),
+    T_l:  the windowed reduction of beta against beta itself (the
+          image-plane layer), windows from the projected pixel grid, weights
+          A_k y_l with A_k from the k = 20 nearest-neighbour density;
+  loss = nll(d | f) - ln p(y | alpha) + ln q, minus the ELBO estimate.
+The lens priors are uniform (constant inside their domain) and left out;
+the transmission weights A_k are held fixed within a step.
+
+Every numerical step runs in the library's CUDA kernels; this module only
+orders the calls and moves the 7 drawn lens parameters to the host, where
+the ray-trace takes them as a parameter struct.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import torch
+
+from . import api
+from .workloads import Grid, Lens
+
+N_LENS = 7  # x0, y0, q, phi, theta_e, g1, g2 (the slope is held fixed)
+
+
+@dataclass
+class ModelConfig:
+    pixels: Grid                 # image pixel centres (ss = 1)
+    source_grid: Grid            # source-plane inducing points
+    sigma_sp: float              # source-plane layer kernel size
+    sigma_layers: list[float]    # image-plane layer kernel sizes
+    alpha_sp: float              # prior scale of y_sp
+    alpha_layers: list[float]    # prior scales of the image-plane layers
+    noise: float                 # pixel noise standard deviation
+    gamma: float = 2.0           # fixed SPLE slope
+    knn_k: int = 20
+
+
+@dataclass
+class Guide:
+    """Variational parameters (Table 2): partial MVN over (theta, y_sp),
+    diagonal normals over the image-plane layers. All float32 CUDA."""
+    mu: torch.Tensor             # (7 + M,)
+    L: torch.Tensor              # (7, 7) lower triangular, positive diagonal
+    C: torch.Tensor              # (M, 7)
+    sd_sp: torch.Tensor          # (M,)
+    mu_layers: list[torch.Tensor] = field(default_factory=list)
+    sd_layers: list[torch.Tensor] = field(default_factory=list)
+
+
+def lens_from(theta: list[float], gamma: float) -> Lens:
+    x0, y0, q, phi, te, g1, g2 = theta
+    return Lens(x0, y0, q, phi, te, gamma, g1, g2)
+
+
+def loss_and_grads(cfg: ModelConfig, guide: Guide, data: torch.Tensor, eps_sp: torch.Tensor,
+                   eps_layers: list[torch.Tensor]) -> tuple[float, dict]:
+    """Loss of one reparameterised draw (given the standard-normal draws) and
+    its gradients with respect to every guide parameter."""
+    dev = data.device
+    M = guide.sd_sp.numel()
+    # ---- draws and their log densities
+    x, logq_sp = api.partial_mvn_draw(guide.mu, guide.L, guide.C, guide.sd_sp, eps_sp)
+    theta = x[:N_LENS].double().cpu().tolist()
+    y_sp = x[N_LENS:].contiguous()
+    lens = lens_from(theta, cfg.gamma)
+    ys, terms = [], []
+    for mu, sd, e, a in zip(guide.mu_layers, guide.sd_layers, eps_layers, cfg.alpha_layers):
+        y, t = api.diag_normal_draw(mu, sd, e, a)
+        ys.append(y)
+        terms.append(t)
+    ones_sp = torch.ones(M, device=dev)
+    _, prior_sp = api.diag_normal_draw(y_sp, ones_sp, torch.zeros(M, device=dev), cfg.alpha_sp)
+
+    # ---- forward
+    pix = api.Points(grid=cfg.pixels, lens=lens)
+    beta = api.lens_raytrace(pix)
+    h = cfg.source_grid.pix / cfg.source_grid.ss
+    a_sp = math.sqrt(2.0 * math.pi) * cfg.sigma_sp * h / (math.pi * cfg.sigma_sp ** 2)  # A |pi Sigma|^-1/2
+    src = api.Points(grid=cfg.source_grid)
+    w_sp = (a_sp * y_sp).contiguous()
+    f = api.gp_kernel_matvec(api.Points(xy=beta), src, w_sp, cfg.sigma_sp / math.sqrt(2.0), 1.0)
+    z = api.pixel_shapes(beta, cfg.pixels.nx, cfg.pixels.ny)
+    self_pts = api.Points(xy=beta)
+    a_layers, w_layers = [], []
+    for y, s in zip(ys, cfg.sigma_layers):
+        a_k = api.knn_density(beta, cfg.knn_k, lengthscale=s, want_r2=False)
+        w = (a_k * y).contiguous()
+        f = f + api.gp_windowed_matvec(beta, z, self_pts, w, s)
+        a_layers.append(a_k)
+        w_layers.append(w)
+    nll, g, _ = api.gaussian_nll(f.contiguous(), data, cfg.noise)
+
+    # ---- backward
+    d_beta = torch.zeros_like(beta)
+    d_z = torch.zeros_like(z)
+    grads = {"layers_mu": [], "layers_sd": []}
+    for y, s, a_k, w, mu, sd, e, al in zip(ys, cfg.sigma_layers, a_layers, w_layers, guide.mu_layers,
+                                           guide.sd_layers, eps_layers, cfg.alpha_layers):
+        G = api.gp_windowed_matvec_bwd(beta, z, self_pts, w, s, g, want=("v", "p", "q", "z"))
+        d_beta += G["p"] + G["q"]
+        d_z += G["z"]
+        d_y = (a_k * G["v"]).contiguous()
+        d_mu, d_sd, _ = api.diag_normal_vjp(mu, sd, e, al, d_y, 1.0, 1.0)
+        grads["layers_mu"].append(d_mu)
+        grads["layers_sd"].append(d_sd)
+    d_beta += api.pixel_shapes_vjp(beta, cfg.pixels.nx, cfg.pixels.ny, d_z.contiguous())
+    Gs = api.gp_kernel_matvec_bwd(api.Points(xy=beta), src, w_sp, cfg.sigma_sp / math.sqrt(2.0), 1.0, g,
+                                  want=("v", "x"))
+    d_beta += Gs["x"]
+    d_lens, _ = api.lens_raytrace_vjp(pix, d_beta.contiguous())
+    # the source-plane layer's prior: d(-ln p)/dy_sp = y_sp / alpha^2
+    d_ysp = a_sp * Gs["v"] + y_sp / (cfg.alpha_sp ** 2)
+    d_x = torch.cat([d_lens.float(), d_ysp]).contiguous()
+    d_mu, d_L, d_C, d_sd = api.partial_mvn_vjp(guide.L, guide.sd_sp, eps_sp, d_x, 1.0)
+    grads.update(mu=d_mu, L=d_L, C=d_C, sd_sp=d_sd, d_lens=d_lens, d_beta=d_beta)
+
+    loss = float(nll) + float(prior_sp[0]) + float(logq_sp)
+    for t in terms:
+        tt = t.cpu()
+        loss += float(tt[0]) + float(tt[1])
+    return loss, grads

@@ -104,3 +104,38 @@ def test_partial_mvn_vjp_by_central_differences():
     np.testing.assert_allclose(d_L, np.tril(cdiff(lambda z: loss(mu, z, C, sd), L)), rtol=1e-6, atol=1e-9)
     np.testing.assert_allclose(d_C, cdiff(lambda z: loss(mu, L, z, sd), C), rtol=1e-7, atol=1e-9)
     np.testing.assert_allclose(d_sd, cdiff(lambda z: loss(mu, L, C, z), sd), rtol=1e-7)
+
+
+def test_svi_step_gradients_by_central_differences(orc):
+    """The oracle's composed SVI loss (ray-trace, both GP layers, windows,
+    likelihood, prior and proposal terms) against its own analytic
+    gradients, weights held fixed: lens means, source weights, scale
+    parameters and image-plane layer parameters."""
+    from oracle import svi
+    from tests.svi_case import case
+    cfg, guide, data, eps_sp, eps_l = case()
+    g64 = {k: (np.asarray(v, np.float64) if not isinstance(v, list) else [np.asarray(x, np.float64) for x in v])
+           for k, v in guide.items()}
+    loss, G = svi.loss_and_grads(orc, cfg, g64, data, eps_sp, eps_l)
+    A = G["A"]
+
+    def L_of(key, idx, val, sub=None):
+        gg = {k: (v.copy() if not isinstance(v, list) else [x.copy() for x in v]) for k, v in g64.items()}
+        arr = gg[key] if sub is None else gg[key][sub]
+        arr[idx] = val
+        return svi.loss_and_grads(orc, cfg, gg, data, eps_sp, eps_l, A_fixed=A)[0]
+
+    def fd(key, idx, h, sub=None):
+        base = (g64[key] if sub is None else g64[key][sub])[idx]
+        return (L_of(key, idx, base + h, sub) - L_of(key, idx, base - h, sub)) / (2 * h)
+
+    for j in range(7):
+        assert G["mu"][j] == pytest.approx(fd("mu", j, 1e-6), rel=2e-5, abs=1e-3), f"mu[{j}]"
+    for j in (7, 50, 200):
+        assert G["mu"][j] == pytest.approx(fd("mu", j, 1e-5), rel=1e-6, abs=1e-6), f"mu[{j}]"
+    assert G["L"][4, 4] == pytest.approx(fd("L", (4, 4), 1e-6), rel=2e-5)
+    assert G["C"][10, 2] == pytest.approx(fd("C", (10, 2), 1e-6), rel=2e-5, abs=1e-6)
+    assert G["sd_sp"][3] == pytest.approx(fd("sd_sp", 3, 1e-6), rel=1e-6)
+    for j in (0, 300):
+        assert G["layers_mu"][0][j] == pytest.approx(fd("mu_layers", j, 1e-5, sub=0), rel=1e-6, abs=1e-6)
+        assert G["layers_sd"][0][j] == pytest.approx(fd("sd_layers", j, 1e-7, sub=0), rel=1e-5, abs=1e-5)
