@@ -301,6 +301,40 @@ def run_extensions(p, dev, rates, sm_max, flush, stream) -> dict:
                                         workload=f"{pix.nx}x{pix.ny} ray-traced pixel centres with their "
                                                  f"window covariances x {p.ygrid.nx}x{p.ygrid.ny} grid")
     out["pixel_shapes"] = {"ms": event_time(lambda: api.pixel_shapes(bp, pix.nx, pix.ny), nk, stream, flush)}
+    # the image-plane layer: the pixels' own windowed reduction (explicit sources = the pixels)
+    vp = torch.randn(pix.n, generator=torch.Generator().manual_seed(6)).to(dev)
+    gp = torch.randn(pix.n, generator=torch.Generator().manual_seed(7)).to(dev)
+    selfp = api.Points(xy=bp)
+    ms = event_time(lambda: api.gp_windowed_matvec(bp, z, selfp, vp, 0.05), 5, stream, flush)
+    out["windowed_matvec<explicit> image-plane layer"] = dict(roof(pix.n * pix.n, ms, 1, 8), n=pix.n, m=pix.n)
+    ms = event_time(lambda: api.gp_windowed_matvec_bwd(bp, z, selfp, vp, 0.05, gp), 3, stream, flush)
+    out["windowed backward (rows + columns) image-plane layer"] = dict(
+        roof(2 * pix.n * pix.n, ms, 1, 15), note="two sweeps; pairs counted per sweep; ~17 and ~13 lanes per pair")
+    # one SVI step of the model at this size (host waits included: wall clock)
+    import time
+    from paper_2105_09465_gb300 import svi
+    mc = svi.ModelConfig(pixels=pix, source_grid=p.ygrid, sigma_sp=p.lengthscale * 1.4142135, sigma_layers=[0.05],
+                         alpha_sp=1.0, alpha_layers=[0.5], noise=0.1, gamma=p.lens.gamma)
+    M = p.m
+    th = torch.tensor([p.lens.x0, p.lens.y0, p.lens.q, p.lens.phi, p.lens.theta_e, p.lens.g1, p.lens.g2])
+    gd = svi.Guide(mu=torch.cat([th, torch.zeros(M)]).to(dev), L=(torch.eye(7) * 1e-3).to(dev),
+                   C=torch.zeros((M, 7), device=dev), sd_sp=torch.full((M,), 0.05, device=dev),
+                   mu_layers=[torch.zeros(pix.n, device=dev)], sd_layers=[torch.full((pix.n,), 0.01, device=dev)])
+    gen = torch.Generator().manual_seed(8)
+    data = torch.randn(pix.n, generator=gen).to(dev)
+    e_sp = torch.randn(7 + M, generator=gen).to(dev)
+    e_l = [torch.randn(pix.n, generator=gen).to(dev)]
+    for _ in range(2):
+        svi.loss_and_grads(mc, gd, data, e_sp, e_l)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(5):
+        svi.loss_and_grads(mc, gd, data, e_sp, e_l)
+    torch.cuda.synchronize()
+    out["svi_step"] = {"ms": (time.perf_counter() - t0) / 5 * 1e3,
+                       "workload": f"{pix.nx}x{pix.ny} pixels, {p.ygrid.nx}x{p.ygrid.ny} source grid, one "
+                                   "image-plane layer: draws, ray-trace, both layers, likelihood and every gradient",
+                       "timing": "wall clock around the call (it waits for the 7 drawn lens parameters)"}
     # three image-plane layers (the paper's 10 / 4.47 / 2 mas ratios) on the supersampled points
     beta = api.lens_raytrace(api.Points(grid=p.xgrid, lens=p.lens, sub=sub))
     vl = torch.randn((3, p.m), generator=torch.Generator().manual_seed(5)).to(dev)
