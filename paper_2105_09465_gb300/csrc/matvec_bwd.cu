@@ -491,20 +491,37 @@ __global__ void __launch_bounds__(kBwThreads) dv_rows_kernel(const __grid_consta
   dv_rows_body<SPLIT>(A, rb, blockIdx.x - rb * A.chunks, sm);
 }
 
+template <bool SPLIT>
+__global__ void __launch_bounds__(kBwThreads) dv_rows_batched_kernel(const __grid_constant__ Batch<BwArgs> B) {
+  __shared__ __align__(16) DvSmem sm;
+  const int k = batch_find(B, blockIdx.x);
+  const BwArgs& A = B.p[k];
+  const int local = blockIdx.x - B.start[k];
+  const int rb = local / A.chunks;
+  dv_rows_body<SPLIT>(A, rb, local - rb * A.chunks, sm);
+}
+
 // Training forward: fixed-order merge of the row-pass chunk partials into the
 // per-row moments (A, B_x, B_y, C) and out = var A.
-__global__ void moments_merge_kernel(const float* __restrict__ partial, int chunks, int64_t n, float var,
-                                     float* __restrict__ out, float* __restrict__ mom) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+__device__ __forceinline__ void moments_merge_body(const MomMergeP& P, int64_t i) {
+  if (i >= P.n) return;
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     float s = 0.f, c = 0.f;
-    for (int ch = 0; ch < chunks; ++ch) kahan(s, c, partial[((int64_t)ch * 4 + k) * n + i]);
+    for (int ch = 0; ch < P.chunks; ++ch) kahan(s, c, P.partial[((int64_t)ch * 4 + k) * P.n + i]);
     s -= c;
-    mom[(int64_t)k * n + i] = s;
-    if (k == 0) out[i] = var * s;
+    P.mom[(int64_t)k * P.n + i] = s;
+    if (k == 0) P.out[i] = P.var * s;
   }
+}
+
+__global__ void moments_merge_kernel(const __grid_constant__ MomMergeP P) {
+  moments_merge_body(P, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+__global__ void moments_merge_batched_kernel(const __grid_constant__ Batch<MomMergeP> B) {
+  const int k = batch_find(B, blockIdx.x);
+  moments_merge_body(B.p[k], (int64_t)(blockIdx.x - B.start[k]) * blockDim.x + threadIdx.x);
 }
 
 // Per-row merge of chunk partials, the per-row gradients, and per-block FP64
@@ -708,6 +725,54 @@ lr_status launch_scalar_batched(const ScalP* p, int count, cudaStream_t s) {
     }
     B.start[B.count] = B.count;
     scalar_batched_kernel<<<(unsigned)B.count, kMergeThreads, 0, s>>>(B);
+    LR_CHECK_CUDA(cudaGetLastError());
+  }
+  return LR_OK;
+}
+
+lr_status launch_dv_rows_batched(const BwArgs* p, int count, cudaStream_t s) {
+  for (int kind = 0; kind < 2; ++kind) {  // 0: unsplit, 1: split exponent
+    Batch<BwArgs> B;
+    B.count = 0;
+    int64_t tot = 0;
+    for (int i = 0; i <= count; ++i) {
+      const bool flush = (i == count) || B.count == kMaxBatch;
+      if (flush && B.count > 0) {
+        B.start[B.count] = (int32_t)tot;
+        if (tot > 0) {
+          if (kind == 1)
+            dv_rows_batched_kernel<true><<<(unsigned)tot, kBwThreads, 0, s>>>(B);
+          else
+            dv_rows_batched_kernel<false><<<(unsigned)tot, kBwThreads, 0, s>>>(B);
+          LR_CHECK_CUDA(cudaGetLastError());
+        }
+        B.count = 0;
+        tot = 0;
+      }
+      if (i == count) break;
+      if ((p[i].split ? 1 : 0) != kind) continue;
+      B.p[B.count] = p[i];
+      B.start[B.count] = (int32_t)tot;
+      tot += (int64_t)((p[i].n + kDvRows - 1) / kDvRows) * p[i].chunks;
+      ++B.count;
+    }
+  }
+  return LR_OK;
+}
+
+lr_status launch_moments_merge_batched(const MomMergeP* p, int count, cudaStream_t s) {
+  for (int b0 = 0; b0 < count; b0 += kMaxBatch) {
+    Batch<MomMergeP> B;
+    B.count = count - b0 < kMaxBatch ? count - b0 : kMaxBatch;
+    int64_t tot = 0;
+    for (int k = 0; k < B.count; ++k) {
+      B.p[k] = p[b0 + k];
+      B.start[k] = (int32_t)tot;
+      tot += (p[b0 + k].n + 255) / 256;
+    }
+    B.start[B.count] = (int32_t)tot;
+    if (tot == 0) continue;
+    moments_merge_batched_kernel<<<(unsigned)tot, 256, 0, s>>>(B);
     LR_CHECK_CUDA(cudaGetLastError());
   }
   return LR_OK;
@@ -950,51 +1015,100 @@ static lr_status plan_dv(int64_t n, const lr_grid* g, RowPlan* R) {
   return LR_OK;
 }
 
+lr_status make_train_problem(const float2* x, int64_t n, const float2* ys, const lr_grid* yg, int64_t m,
+                             const float* v, float ell, float var, float* out, float* mom, char* ws, BwArgs* A,
+                             MomMergeP* MM, size_t* bytes) {
+  BwArgs a;
+  MergeArgs M;
+  ScalP S;
+  lr_status st = make_rows_problem(x, n, ys, yg, m, v, nullptr, ell, var, nullptr, nullptr, nullptr, nullptr, ws,
+                                   ws ? &a : nullptr, ws ? &M : nullptr, ws ? &S : nullptr, nullptr, bytes);
+  if (st != LR_OK || !ws) return st;
+  *A = a;
+  MM->partial = a.partial;
+  MM->chunks = a.chunks;
+  MM->n = n;
+  MM->var = var;
+  MM->out = out;
+  MM->mom = mom;
+  return LR_OK;
+}
+
+lr_status make_moment_rows_problem(const float* mom, int64_t n, bool grid, const float* g, const float* v, float ell,
+                                   float var, float2* dx, double* d_len, double* d_var, char* ws, MergeArgs* M,
+                                   ScalP* S, size_t* bytes) {
+  const int64_t nblk = (n + kMergeThreads - 1) / kMergeThreads;
+  *bytes = align256(sizeof(double) * 2 * (size_t)(nblk + 1));
+  if (!ws) return LR_OK;
+  *M = row_merge_args(grid, ell, var, mom, 1, n, g, v, dx, reinterpret_cast<double*>(ws));
+  S->part = M->scal_part;
+  S->nblk = (int32_t)nblk;
+  S->d_len = d_len;
+  S->d_var = d_var;
+  return LR_OK;
+}
+
+lr_status make_dv_problem(const float2* x, int64_t n, const lr_grid* yg, const float* g, float ell, float var,
+                          float* d_v, char* ws, BwArgs* A, DvMergeP* D, size_t* bytes) {
+  RowPlan R;
+  lr_status st = plan_dv(n, yg, &R);
+  if (st != LR_OK) return st;
+  *bytes = R.dv_bytes;
+  if (!ws) return LR_OK;
+  BwArgs a{};
+  a.x = x;
+  a.n = n;
+  a.src.xy = nullptr;
+  a.src.g = grid_dev(*yg);
+  a.src.m = (int64_t)a.src.g.W * a.src.g.H;
+  a.src.segs = R.segs;
+  a.src.n_tiles = R.n_tiles;
+  const double c = 1.4426950408889634 / (2.0 * (double)ell * (double)ell);
+  a.neg_c = (float)(-c);
+  a.sc = (float)sqrt(c);
+  a.split = grid_split_ok(a.src.g, a.sc);
+  a.chunks = R.chunks;
+  a.rows_per_cta = kDvRows;
+  a.grow = g;
+  a.dv_part = reinterpret_cast<float*>(ws);
+  *A = a;
+  *D = DvMergeP{a.dv_part, R.row_blocks, a.src.m, var, d_v};
+  return LR_OK;
+}
+
 // d_v of grid sources from the d_v-only pass: dv_part, then the fixed-order
 // merge over row blocks. ws: the plan's dv_bytes.
 static lr_status launch_dv(const float2* x, int64_t n, const lr_grid* yg, const float* g, float ell, float var,
                            float* d_v, char* ws, cudaStream_t s) {
-  RowPlan R;
-  lr_status st = plan_dv(n, yg, &R);
+  BwArgs A;
+  DvMergeP D;
+  size_t b = 0;
+  lr_status st = make_dv_problem(x, n, yg, g, ell, var, d_v, ws, &A, &D, &b);
   if (st != LR_OK) return st;
-  BwArgs A{};
-  A.x = x;
-  A.n = n;
-  A.src.xy = nullptr;
-  A.src.g = grid_dev(*yg);
-  A.src.m = (int64_t)A.src.g.W * A.src.g.H;
-  A.src.segs = R.segs;
-  A.src.n_tiles = R.n_tiles;
-  const double c = 1.4426950408889634 / (2.0 * (double)ell * (double)ell);
-  A.neg_c = (float)(-c);
-  A.sc = (float)sqrt(c);
-  A.split = grid_split_ok(A.src.g, A.sc);
-  A.chunks = R.chunks;
-  A.rows_per_cta = kDvRows;
-  A.grow = g;
-  A.dv_part = reinterpret_cast<float*>(ws);
-  const unsigned grid = (unsigned)((int64_t)R.row_blocks * R.chunks);
+  const unsigned grid = (unsigned)(((n + kDvRows - 1) / kDvRows) * A.chunks);
   if (A.split)
     dv_rows_kernel<true><<<grid, kBwThreads, 0, s>>>(A);
   else
     dv_rows_kernel<false><<<grid, kBwThreads, 0, s>>>(A);
   LR_CHECK_CUDA(cudaGetLastError());
-  DvMergeP D{A.dv_part, R.row_blocks, A.src.m, var, d_v};
-  dv_merge_kernel<<<(unsigned)((A.src.m + 255) / 256), 256, 0, s>>>(D);
+  dv_merge_kernel<<<(unsigned)((D.m + 255) / 256), 256, 0, s>>>(D);
   LR_CHECK_CUDA(cudaGetLastError());
   return LR_OK;
 }
 
 // Row gradients from the training forward's moments: d_x, d_l, d_var.
-// ws: the scalar partials (merge blocks x 2 doubles).
+// ws: the scalar partials (make_moment_rows_problem's bytes).
 static lr_status launch_moment_rows(const float* mom, int64_t n, bool grid, const float* g, const float* v, float ell,
                                     float var, float2* d_x, double* d_len, double* d_var, char* ws, cudaStream_t s) {
-  const int64_t nblk = (n + kMergeThreads - 1) / kMergeThreads;
-  MergeArgs M = row_merge_args(grid, ell, var, mom, 1, n, g, v, d_x, reinterpret_cast<double*>(ws));
-  bwd_merge_kernel<<<(unsigned)nblk, kMergeThreads, 0, s>>>(M);
+  MergeArgs M;
+  ScalP S;
+  size_t b = 0;
+  lr_status st = make_moment_rows_problem(mom, n, grid, g, v, ell, var, d_x, d_len, d_var, ws, &M, &S, &b);
+  if (st != LR_OK) return st;
+  bwd_merge_kernel<<<(unsigned)S.nblk, kMergeThreads, 0, s>>>(M);
   LR_CHECK_CUDA(cudaGetLastError());
   if (d_len || d_var) {
-    bwd_scalar_final_kernel<<<1, kMergeThreads, 0, s>>>(M.scal_part, (int32_t)nblk, d_len, d_var);
+    bwd_scalar_final_kernel<<<1, kMergeThreads, 0, s>>>(S.part, S.nblk, d_len, d_var);
     LR_CHECK_CUDA(cudaGetLastError());
   }
   return LR_OK;
@@ -1291,12 +1405,11 @@ extern "C" lr_status gp_kernel_matvec_train(const lr_points* query, const lr_poi
     return LR_OK;
   }
   BwArgs A;
-  MergeArgs M;
-  ScalP S;
+  MomMergeP MM;
   size_t b = 0;
   const float2* ys = T.s_grid ? nullptr : reinterpret_cast<const float2*>(source->xy);
-  st = make_rows_problem(xq, T.n, ys, T.s_grid ? &source->grid : nullptr, T.m, v, nullptr, lengthscale, variance,
-                         nullptr, nullptr, nullptr, nullptr, ws + T.off_rows, &A, &M, &S, nullptr, &b);
+  st = make_train_problem(xq, T.n, ys, T.s_grid ? &source->grid : nullptr, T.m, v, lengthscale, variance, out,
+                          moments_out, ws + T.off_rows, &A, &MM, &b);
   if (st != LR_OK) return st;
   const unsigned grid = (unsigned)(((T.n + A.rows_per_cta - 1) / A.rows_per_cta) * A.chunks);
   if (T.s_grid && A.split)
@@ -1306,8 +1419,7 @@ extern "C" lr_status gp_kernel_matvec_train(const lr_points* query, const lr_poi
   else
     bwd_rows_kernel<false, false, false><<<grid, kBwThreads, 0, s>>>(A);
   LR_CHECK_CUDA(cudaGetLastError());
-  moments_merge_kernel<<<(unsigned)((T.n + 255) / 256), 256, 0, s>>>(A.partial, A.chunks, T.n, variance, out,
-                                                                       moments_out);
+  moments_merge_kernel<<<(unsigned)((T.n + 255) / 256), 256, 0, s>>>(MM);
   LR_CHECK_CUDA(cudaGetLastError());
   return LR_OK;
 }

@@ -103,6 +103,16 @@ struct DvMergeP {
   float* d_v;
 };
 
+// training forward: merge of the row-pass partials into out and the moments
+struct MomMergeP {
+  const float* partial;  // [chunks][4][n]
+  int32_t chunks;
+  int64_t n;
+  float var;
+  float* out;            // [n]
+  float* mom;            // [4][n]
+};
+
 struct MergeArgs {
   const float* partial;
   int32_t chunks, K;
@@ -174,6 +184,19 @@ lr_status launch_bwd_rows_batched(const BwArgs* p, int count, cudaStream_t s);
 lr_status launch_bwd_merge_batched(const MergeArgs* p, int count, cudaStream_t s);
 lr_status launch_scalar_batched(const ScalP* p, int count, cudaStream_t s);
 lr_status launch_dv_merge_batched(const DvMergeP* p, int count, cudaStream_t s);
+lr_status launch_dv_rows_batched(const BwArgs* p, int count, cudaStream_t s);
+lr_status launch_moments_merge_batched(const MomMergeP* p, int count, cudaStream_t s);
+// Training-step problems against grid sources (gp_kernel_matvec_train and
+// gp_kernel_matvec_bwd with moments plan them the same way). With ws == NULL
+// only *bytes is filled in.
+lr_status make_train_problem(const float2* x, int64_t n, const float2* ys, const lr_grid* yg, int64_t m,
+                             const float* v, float ell, float var, float* out, float* mom, char* ws, BwArgs* A,
+                             MomMergeP* MM, size_t* bytes);
+lr_status make_moment_rows_problem(const float* mom, int64_t n, bool grid, const float* g, const float* v, float ell,
+                                   float var, float2* dx, double* d_len, double* d_var, char* ws, MergeArgs* M,
+                                   ScalP* S, size_t* bytes);
+lr_status make_dv_problem(const float2* x, int64_t n, const lr_grid* yg, const float* g, float ell, float var,
+                          float* d_v, char* ws, BwArgs* A, DvMergeP* D, size_t* bytes);
 lr_status launch_vjp_batched(const VjpP* p, int count, cudaStream_t s);
 lr_status launch_vjp_final_batched(const VjpFinalP* p, int count, cudaStream_t s);
 

@@ -2,8 +2,9 @@
 //
 // A request is one lens system (image grid, lens, subhalos, inducing grid,
 // source weights v and observed fluxes d) plus a number of iterations. Each
-// iteration ray-traces the image, reduces the kernel (out = K v), forms the
-// residual g = out - d, runs the full backward pass (dL/dv, dL/dbeta, lens,
+// iteration ray-traces the image, reduces the kernel (out = K v, with the
+// row moments of the training forward), forms the residual g = out - d, runs
+// the full backward pass (dL/dv, dL/dbeta, lens,
 // subhalo and hyperparameter gradients of L = 0.5 |out - d|^2) and takes a
 // gradient step v <- v - step dL/dv. All of a request's state stays on the
 // device from admission to completion.
@@ -11,8 +12,8 @@
 // A worker thread owns the GPU side. Between iterations it admits pending
 // requests while slots (max_slots) and the device-memory budget allow, then
 // runs ONE iteration for every active request with one batched launch per
-// stage (ray-trace, reduction, merge, residual, backward rows, merge,
-// scalars, d_v merge, ray-trace VJP, final sums, update):
+// stage (ray-trace, training forward, moments merge, residual, row-gradient
+// merge, scalars, d_v sweep, d_v merge, ray-trace VJP, final sums, update):
 // requests of different sizes share the launches and their CTAs overlap on
 // the device. A request that reaches its iteration count leaves the batch;
 // a host callback on the stream timestamps its completion. Every request is
@@ -74,15 +75,16 @@ struct Req {
   int64_t n = 0, m = 0;
   // device memory (one allocation) and the offsets of its parts
   size_t bytes = 0;
-  size_t o_beta, o_out, o_data, o_g, o_dx, o_v, o_dv, o_sub, o_dlens, o_dsub, o_scal, o_fwd, o_rows, o_vjp;
+  size_t o_beta, o_out, o_data, o_g, o_dx, o_v, o_dv, o_sub, o_dlens, o_dsub, o_scal, o_mom, o_train, o_mrows,
+      o_dvp, o_vjp;
   char* dmem = nullptr;
   // problem descriptors of the batched stages
   RtP rt;
-  MvArgs fwd;
-  MergeP fwd_m;
-  BwArgs rows;
-  MergeArgs rows_m;
+  BwArgs train;     // training forward: out and the row moments
+  MomMergeP tmerge;
+  MergeArgs mrows;  // row gradients from the moments
   ScalP scal;
+  BwArgs dv;        // d_v sweep
   DvMergeP dvm;
   VjpP vjp;
   VjpFinalP vfin;
@@ -135,14 +137,14 @@ size_t carve(size_t& off, size_t bytes) {
 // Sizes the request's device state (same plans as the single-problem calls).
 lr_status size_request(Req* r) {
   const int64_t n = r->n, m = r->m;
-  size_t fwd_b = 0, rows_b = 0;
-  lr_status st = make_mv_problem(nullptr, n, nullptr, &r->ygrid, m, nullptr, r->ell, r->var, nullptr, nullptr,
-                                 nullptr, nullptr, &fwd_b);
+  size_t train_b = 0, mrows_b = 0, dv_b = 0;
+  lr_status st = make_train_problem(nullptr, n, nullptr, &r->ygrid, m, nullptr, r->ell, r->var, nullptr, nullptr,
+                                    nullptr, nullptr, nullptr, &train_b);
   if (st != LR_OK) return st;
-  // d_v fused into the row pass (grid sources)
-  st = make_rows_problem(nullptr, n, nullptr, &r->ygrid, m, nullptr, nullptr, r->ell, r->var, nullptr, nullptr,
-                         nullptr, reinterpret_cast<float*>(uintptr_t(256)), nullptr, nullptr, nullptr, nullptr,
-                         nullptr, &rows_b);
+  st = make_moment_rows_problem(nullptr, n, true, nullptr, nullptr, r->ell, r->var, nullptr, nullptr, nullptr,
+                                nullptr, nullptr, nullptr, &mrows_b);
+  if (st != LR_OK) return st;
+  st = make_dv_problem(nullptr, n, &r->ygrid, nullptr, r->ell, r->var, nullptr, nullptr, nullptr, nullptr, &dv_b);
   if (st != LR_OK) return st;
   size_t off = 0;
   r->o_beta = carve(off, 8 * n);
@@ -156,8 +158,10 @@ lr_status size_request(Req* r) {
   r->o_dlens = carve(off, 7 * 8);
   r->o_dsub = carve(off, 32 * (size_t)r->n_sub);
   r->o_scal = carve(off, 16);
-  r->o_fwd = carve(off, fwd_b);
-  r->o_rows = carve(off, rows_b);
+  r->o_mom = carve(off, 16 * n);
+  r->o_train = carve(off, train_b);
+  r->o_mrows = carve(off, mrows_b);
+  r->o_dvp = carve(off, dv_b);
   r->o_vjp = carve(off, raytrace_vjp_ws(n, r->n_sub));
   r->bytes = off;
   return LR_OK;
@@ -195,12 +199,16 @@ lr_status init_request(lr_session* S, Req* r) {
   P.profile = r->profile;
   if ((st = make_rt_problem(&P, beta, nullptr, &r->rt)) != LR_OK) return st;
   size_t b = 0;
-  if ((st = make_mv_problem(beta, r->n, nullptr, &r->ygrid, r->m, v, r->ell, r->var, out,
-                            reinterpret_cast<float*>(d + r->o_fwd), &r->fwd, &r->fwd_m, &b)) != LR_OK)
+  float* mom = reinterpret_cast<float*>(d + r->o_mom);
+  if ((st = make_train_problem(beta, r->n, nullptr, &r->ygrid, r->m, v, r->ell, r->var, out, mom, d + r->o_train,
+                               &r->train, &r->tmerge, &b)) != LR_OK)
     return st;
   r->resid = AxpyP{out, data, g, r->n, 1.0f};
-  if ((st = make_rows_problem(beta, r->n, nullptr, &r->ygrid, r->m, v, g, r->ell, r->var, dx, scal, scal + 1, dv,
-                              d + r->o_rows, &r->rows, &r->rows_m, &r->scal, &r->dvm, &b)) != LR_OK)
+  if ((st = make_moment_rows_problem(mom, r->n, true, g, v, r->ell, r->var, dx, scal, scal + 1, d + r->o_mrows,
+                                     &r->mrows, &r->scal, &b)) != LR_OK)
+    return st;
+  if ((st = make_dv_problem(beta, r->n, &r->ygrid, g, r->ell, r->var, dv, d + r->o_dvp, &r->dv, &r->dvm, &b)) !=
+      LR_OK)
     return st;
   if ((st = make_vjp_problem(&P, dx, dlens, dsub, d + r->o_vjp, &r->vjp, &r->vfin)) != LR_OK) return st;
   r->upd = AxpyP{v, dv, v, r->m, r->step};
@@ -210,23 +218,22 @@ lr_status init_request(lr_session* S, Req* r) {
 // One batched iteration over `act`.
 lr_status run_iteration(lr_session* S, const std::vector<Req*>& act) {
   std::vector<RtP> rt;
-  std::vector<MvArgs> fwd;
-  std::vector<MergeP> fwd_m;
+  std::vector<BwArgs> train, dvs;
+  std::vector<MomMergeP> tmerge;
   std::vector<DvMergeP> dvm;
   std::vector<AxpyP> resid, upd;
-  std::vector<BwArgs> rows;
-  std::vector<MergeArgs> rows_m;
+  std::vector<MergeArgs> mrows;
   std::vector<ScalP> scal;
   std::vector<VjpP> vjp;
   std::vector<VjpFinalP> vfin;
   for (Req* r : act) {
     rt.push_back(r->rt);
-    fwd.push_back(r->fwd);
-    if (r->fwd.chunks > 1) fwd_m.push_back(r->fwd_m);
+    train.push_back(r->train);
+    tmerge.push_back(r->tmerge);
     resid.push_back(r->resid);
-    rows.push_back(r->rows);
-    rows_m.push_back(r->rows_m);
+    mrows.push_back(r->mrows);
     scal.push_back(r->scal);
+    dvs.push_back(r->dv);
     dvm.push_back(r->dvm);
     vjp.push_back(r->vjp);
     vfin.push_back(r->vfin);
@@ -236,18 +243,18 @@ lr_status run_iteration(lr_session* S, const std::vector<Req*>& act) {
   cudaStream_t s = S->stream;
   lr_status st;
   if ((st = launch_raytrace_batched(rt.data(), n, s)) != LR_OK) return st;
-  if ((st = launch_matvec_batched(fwd.data(), n, s)) != LR_OK) return st;
-  if ((st = launch_merge_batched(fwd_m.data(), (int)fwd_m.size(), s)) != LR_OK) return st;
+  if ((st = launch_bwd_rows_batched(train.data(), n, s)) != LR_OK) return st;
+  if ((st = launch_moments_merge_batched(tmerge.data(), n, s)) != LR_OK) return st;
   if ((st = launch_axpy_batched(resid.data(), n, s)) != LR_OK) return st;
-  if ((st = launch_bwd_rows_batched(rows.data(), n, s)) != LR_OK) return st;
-  if ((st = launch_bwd_merge_batched(rows_m.data(), n, s)) != LR_OK) return st;
+  if ((st = launch_bwd_merge_batched(mrows.data(), n, s)) != LR_OK) return st;
   if ((st = launch_scalar_batched(scal.data(), n, s)) != LR_OK) return st;
+  if ((st = launch_dv_rows_batched(dvs.data(), n, s)) != LR_OK) return st;
   if ((st = launch_dv_merge_batched(dvm.data(), n, s)) != LR_OK) return st;
   if ((st = launch_vjp_batched(vjp.data(), n, s)) != LR_OK) return st;
   if ((st = launch_vjp_final_batched(vfin.data(), n, s)) != LR_OK) return st;
   if ((st = launch_axpy_batched(upd.data(), n, s)) != LR_OK) return st;
   const int groups = (n + kMaxBatch - 1) / kMaxBatch;
-  S->launches += (uint64_t)groups * (10 + (fwd_m.empty() ? 0 : 1));
+  S->launches += (uint64_t)groups * 11;
   return LR_OK;
 }
 

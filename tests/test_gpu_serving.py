@@ -68,10 +68,10 @@ def test_one_iteration_equals_single_problem_calls():
         R = S.poll(t)
     q = api.Points(grid=p.xgrid, lens=p.lens, sub=dev(p.sub))
     s = api.Points(grid=p.ygrid)
-    out = api.gp_kernel_matvec(q, s, dev(p.v), p.lengthscale, p.variance)
+    out, mom = api.gp_kernel_matvec_train(q, s, dev(p.v), p.lengthscale, p.variance)
     g = out - dev(data)
     G = api.gp_kernel_matvec_bwd(q, s, dev(p.v), p.lengthscale, p.variance, g,
-                                 want=["v", "lengthscale", "variance", "lens", "sub"])
+                                 want=["v", "lengthscale", "variance", "lens", "sub"], moments=mom)
     assert np.array_equal(R.out, host(out).astype(np.float32))
     assert np.array_equal(R.v, p.v)
     assert np.array_equal(R.d_lens, host(G["lens"]))
