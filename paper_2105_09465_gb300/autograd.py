@@ -27,14 +27,21 @@ class RaytraceKernelMatvec(torch.autograd.Function):
         q = api.Points(grid=xgrid, lens=lens, sub=sub.detach().contiguous() if sub is not None else None,
                        profile=profile)
         s = api.Points(grid=ygrid) if ygrid is not None else None
-        out, beta = api.gp_kernel_matvec(q, s, v.detach().contiguous(), ell, var, want_beta=True)
-        ctx.save_for_backward(v, sub if sub is not None else torch.empty(0), beta)
+        if s is not None:
+            # training forward: also keeps the row moments, so the backward
+            # sweeps the pairs only for d_v
+            beta = torch.empty((q.n, 2), dtype=torch.float32, device=v.device)
+            out, mom = api.gp_kernel_matvec_train(q, s, v.detach().contiguous(), ell, var, beta=beta)
+        else:
+            out, beta = api.gp_kernel_matvec(q, s, v.detach().contiguous(), ell, var, want_beta=True)
+            mom = torch.empty(0, device=v.device)
+        ctx.save_for_backward(v, sub if sub is not None else torch.empty(0), beta, mom)
         ctx.meta = (q, s, ell, var, lens_params.dtype, lens_params.device)
         return out
 
     @staticmethod
     def backward(ctx, grad_out):
-        v, sub, beta = ctx.saved_tensors
+        v, sub, beta, mom = ctx.saved_tensors
         q, s, ell, var, ldtype, ldev = ctx.meta
         need = ctx.needs_input_grad
         want = []
@@ -51,7 +58,7 @@ class RaytraceKernelMatvec(torch.autograd.Function):
         if not want:
             return (None,) * 8
         G = api.gp_kernel_matvec_bwd(q, s, v.detach().contiguous(), ell, var, grad_out.contiguous().float(),
-                                     want=want, beta=beta)
+                                     want=want, beta=beta, moments=mom if mom.numel() else None)
         gv = G.get("v")
         gl = None
         if "lens" in G:
