@@ -345,6 +345,19 @@ lr_status gp_partial_mvn_vjp(const float* L, const float* sd, const float* eps, 
                              const float* d_x, double w_q, float* d_mu, float* d_L, float* d_C, float* d_sd,
                              lr_stream stream);
 
+/*
+ * Diagnostic: the number of (query, source) pairs the grid-source kernels
+ * actually evaluate for query points x (device float[n][2]; ray-traced points
+ * of query_grid, or explicit points when query_grid is NULL) against
+ * source_grid with this length scale, for row blocks of rows_per_cta rows
+ * (1024: gp_kernel_matvec and the d_v sweep; 512: gp_kernel_matvec_train).
+ * Pairs left out are exactly those whose FP32 exp2 flushes to 0, so every
+ * result equals the full n x m evaluation. Synchronises the stream; allocates
+ * a small temporary buffer.
+ */
+lr_status lr_grid_pairs_evaluated(const float* x, int64_t n, const lr_grid* query_grid, const lr_grid* source_grid,
+                                  float lengthscale, int32_t rows_per_cta, int64_t* pairs, lr_stream stream);
+
 /* Scratch bytes gp_kernel_matvec needs for these point sets on the current device. */
 lr_status lr_matvec_workspace_size(const lr_points* query, const lr_points* source, int32_t nrhs, size_t* bytes);
 

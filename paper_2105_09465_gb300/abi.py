@@ -106,6 +106,8 @@ SIGNATURES = {
                                                 ctypes.c_size_t, _P]),
     "lr_matvec_train_workspace_size": (ctypes.c_int32, [ctypes.POINTER(lr_points), ctypes.POINTER(lr_points),
                                                         ctypes.c_int32, ctypes.POINTER(ctypes.c_size_t)]),
+    "lr_grid_pairs_evaluated": (ctypes.c_int32, [_P, ctypes.c_int64, ctypes.POINTER(lr_grid), ctypes.POINTER(lr_grid),
+                                                 ctypes.c_float, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64), _P]),
     "lr_elbo_workspace_size": (ctypes.c_size_t, []),
     "gp_gaussian_nll": (ctypes.c_int32, [_P, ctypes.c_int64, ctypes.POINTER(lr_grid), _P, _P, ctypes.c_float, _P, _P,
                                          _P, _P, ctypes.c_size_t, _P]),

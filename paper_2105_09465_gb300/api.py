@@ -55,6 +55,8 @@ def to_c_points(p: Points | None):
     if p.xy is not None:
         c.xy = p.xy.data_ptr()
         c.n = p.xy.shape[0]
+        if p.grid is not None:  # explicit points laid out on this grid (row-block order only)
+            c.grid = abi.lr_grid(*p.grid.astuple())
     else:
         c.xy = None
         c.grid = abi.lr_grid(*p.grid.astuple())
@@ -353,6 +355,19 @@ def pixel_shapes_vjp(p: torch.Tensor, W: int, H: int, dz: torch.Tensor, stream=N
 
 
 GRADS = ("v", "x", "y", "lengthscale", "variance", "lens", "sub")
+
+
+def grid_pairs_evaluated(x: torch.Tensor, query_grid: Grid | None, source_grid: Grid, lengthscale: float,
+                         rows_per_cta: int = 1024, stream=None) -> int:
+    """Pairs the grid-source kernels evaluate (the rest are exactly zero)."""
+    lib = abi.load()
+    _require_cuda(x, "x", (2,))
+    qg = ctypes.byref(abi.lr_grid(*query_grid.astuple())) if query_grid is not None else None
+    out = ctypes.c_int64(0)
+    abi.check(lib.lr_grid_pairs_evaluated(x.data_ptr(), x.shape[0], qg, ctypes.byref(abi.lr_grid(*source_grid.astuple())),
+                                          float(lengthscale), int(rows_per_cta), ctypes.byref(out),
+                                          _stream_handle(stream)), "lr_grid_pairs_evaluated")
+    return int(out.value)
 
 
 def train_workspace_size(query: Points, source: Points) -> int:

@@ -19,4 +19,15 @@ lr_status launch_raytrace_vjp(const lr_points* p, const float2* dbeta, double* d
 // Rounds a byte count up to a multiple of 256 (workspace sub-allocation).
 inline size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
+// Image-grid layout of a query point set, or NULL: the grid itself for a
+// grid query, and for explicit points the grid they carry when its point
+// count matches (points laid out row-major on that grid, e.g. ray-traced
+// pixels). Only the order of rows in row blocks depends on it.
+inline const lr_grid* query_layout(const lr_points* q) {
+  const lr_grid& g = q->grid;
+  if (q->xy == nullptr) return &g;
+  if (g.nx > 0 && g.ny > 0 && g.ss > 0 && (int64_t)g.nx * g.ss * g.ny * g.ss == q->n) return &g;
+  return nullptr;
+}
+
 }  // namespace lr

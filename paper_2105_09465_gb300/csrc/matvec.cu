@@ -110,16 +110,23 @@ template <bool GRID>
 __device__ __forceinline__ void matvec_body(const MvArgs& A, int rb, int chunk, MvSmem& sm) {
   float4 (*sP)[kPairs] = sm.sP;
   float2 (*sV)[kPairs] = sm.sV;
-  const int nt = A.src.n_tiles;
-  const int t0 = (int)((int64_t)chunk * nt / A.chunks);
-  const int t1 = (int)((int64_t)(chunk + 1) * nt / A.chunks);
+  // grid sources with row-block info: chunks split the block's active tile range
+  RowBlockInfo B{};
+  int lo = 0, hi = A.src.n_tiles;
+  if (GRID && A.info) {
+    B = A.info[rb];
+    lo = B.t_lo;
+    hi = B.t_hi > B.t_lo ? B.t_hi : B.t_lo;
+  }
+  const int t0 = lo + (int)((int64_t)chunk * (hi - lo) / A.chunks);
+  const int t1 = lo + (int)((int64_t)(chunk + 1) * (hi - lo) / A.chunks);
   const int tid = threadIdx.x;
 
   float2 xq[kMvR], yq[kMvR], acc[kMvR];
 #pragma unroll
   for (int r = 0; r < kMvR; ++r) {
-    int64_t i = (int64_t)rb * kRowsPerCta + r * kMvThreads + tid;
-    if (i >= A.n) i = A.n - 1;
+    const int64_t ir = map_row(A.map, A.n, kRowsPerCta, rb, r * kMvThreads + tid);
+    const int64_t i = ir >= 0 ? ir : 0;  // padding rows compute on row 0 and are not written
     const float2 p = __ldg(A.x + i);
     xq[r] = f2(p.x, p.x);
     yq[r] = f2(p.y, p.y);
@@ -166,6 +173,9 @@ __device__ __forceinline__ void matvec_body(const MvArgs& A, int rb, int chunk, 
       if (!A.split) {
         // unsplit: dx' = q - x', exponent -(dx'^2 + dy'^2)
         for (int sg = 0; sg < nsg; ++sg) {
+          if (A.info && seg_far(B, grid_x(A.src.g, c0 + kSeg * sg),
+                                grid_x(A.src.g, c0 + min(kSeg * sg + kSeg, cnt) - 1), yt, A.sc))
+            continue;  // every pair's exp2 flushes to 0
           const float o = seg_origin(A.src.g, c0, sg);
           float2 qx[kMvR], d2[kMvR];
 #pragma unroll
@@ -190,6 +200,9 @@ __device__ __forceinline__ void matvec_body(const MvArgs& A, int rb, int chunk, 
         }
       } else {
         for (int sg = 0; sg < nsg; ++sg) {
+          if (A.info && seg_far(B, grid_x(A.src.g, c0 + kSeg * sg),
+                                grid_x(A.src.g, c0 + min(kSeg * sg + kSeg, cnt) - 1), yt, A.sc))
+            continue;  // every pair's exp2 flushes to 0
           const float o = seg_origin(A.src.g, c0, sg);
           float2 q2[kMvR], ar[kMvR];
 #pragma unroll
@@ -247,8 +260,8 @@ __device__ __forceinline__ void matvec_body(const MvArgs& A, int rb, int chunk, 
 
 #pragma unroll
   for (int r = 0; r < kMvR; ++r) {
-    const int64_t i = (int64_t)rb * kRowsPerCta + r * kMvThreads + tid;
-    if (i < A.n) {
+    const int64_t i = map_row(A.map, A.n, kRowsPerCta, rb, r * kMvThreads + tid);
+    if (i >= 0) {
       const float total = sm.ksum[r][tid] - sm.kcomp[r][tid];
       if (A.chunks == 1)
         A.out[i] = A.variance * total;
@@ -335,7 +348,7 @@ lr_status launch_matvec_batched(const MvArgs* p, int count, cudaStream_t s) {
       if ((p[i].src.xy == nullptr) != (kind == 1)) continue;
       B.p[B.count] = p[i];
       B.start[B.count] = (int32_t)tot;
-      tot += (int64_t)((p[i].n + kRowsPerCta - 1) / kRowsPerCta) * p[i].chunks;
+      tot += row_block_count(p[i].map, p[i].n, kRowsPerCta) * p[i].chunks;
       ++B.count;
     }
   }
@@ -367,7 +380,8 @@ struct MvPlan {
   bool s_raytrace;           // source needs ray-tracing
   bool s_grid;               // source read as a grid (no materialisation)
   int32_t n_tiles, segs, chunks, row_blocks;
-  size_t off_qbeta, off_sbeta, off_partial, bytes;
+  RowMap map;                // row blocks: image tiles of a grid query, else index order
+  size_t off_qbeta, off_sbeta, off_partial, off_info, bytes;
 };
 
 static lr_status plan_matvec(const lr_points* q, const lr_points* s, int32_t nrhs, bool have_beta_out, MvPlan* P) {
@@ -394,7 +408,9 @@ static lr_status plan_matvec(const lr_points* q, const lr_points* s, int32_t nrh
     p.segs = 0;
     p.n_tiles = (int32_t)((p.m + kTile - 1) / kTile);
   }
-  p.row_blocks = (int32_t)((p.n + kRowsPerCta - 1) / kRowsPerCta);
+  const lr_grid* layout = query_layout(q);
+  p.map = layout ? make_row_map(layout, kRowsPerCta) : RowMap{};
+  p.row_blocks = (int32_t)row_block_count(p.map, p.n, kRowsPerCta);
   int dev = 0, n_sm = 1, occ = 1;
   LR_CHECK_CUDA(cudaGetDevice(&dev));
   LR_CHECK_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
@@ -409,6 +425,8 @@ static lr_status plan_matvec(const lr_points* q, const lr_points* s, int32_t nrh
   if (p.s_raytrace) off += align256(sizeof(float2) * (size_t)p.m);
   p.off_partial = off;
   if (p.chunks > 1) off += align256(sizeof(float) * (size_t)p.chunks * (size_t)p.n);
+  p.off_info = off;
+  if (p.s_grid) off += row_info_bytes(p.map, p.n, kRowsPerCta);
   p.bytes = off;
   *P = p;
   return LR_OK;
@@ -450,6 +468,8 @@ lr_status make_mv_problem(const float2* x, int64_t n, const float2* ys, const lr
     a.chunks = P.chunks;
     a.out = out;
     a.partial = partial;
+    a.map = RowMap{};
+    a.info = nullptr;
     *A = a;
   }
   if (M) {
@@ -539,6 +559,14 @@ extern "C" lr_status gp_kernel_matvec(const lr_points* query, const lr_points* s
   A.chunks = P.chunks;
   A.out = out;
   A.partial = reinterpret_cast<float*>(ws + P.off_partial);
+  A.map = P.map;
+  A.info = nullptr;
+  if (P.s_grid) {
+    // row-block boxes: the exactly-zero pairs are left out
+    RowInfoP R{xq, P.n, P.map, kRowsPerCta, P.segs, S.g, A.sc, reinterpret_cast<RowBlockInfo*>(ws + P.off_info)};
+    if ((st = launch_row_info(R, s)) != LR_OK) return st;
+    A.info = R.info;
+  }
   const unsigned grid = (unsigned)((int64_t)P.row_blocks * P.chunks);
   if (S.xy)
     matvec_kernel<false><<<grid, kMvThreads, 0, s>>>(A);

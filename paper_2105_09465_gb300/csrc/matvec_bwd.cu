@@ -123,24 +123,30 @@ __device__ __forceinline__ void bwd_rows_body(const BwArgs& A, int rb, int chunk
   float4 (*sP)[kBwPairs] = sm.sP;
   float2 (*sV)[kBwPairs] = sm.sV;
   float2 (*sG)[kBwPairs] = sm.sG;
-  const int nt = A.src.n_tiles;
-  const int t0 = (int)((int64_t)chunk * nt / A.chunks);
-  const int t1 = (int)((int64_t)(chunk + 1) * nt / A.chunks);
+  // grid sources with row-block info: chunks split the block's active tile range
+  RowBlockInfo B{};
+  int lo = 0, hi = A.src.n_tiles;
+  if (GRID && A.info) {
+    B = A.info[rb];
+    lo = B.t_lo;
+    hi = B.t_hi > B.t_lo ? B.t_hi : B.t_lo;
+  }
+  const int t0 = lo + (int)((int64_t)chunk * (hi - lo) / A.chunks);
+  const int t1 = lo + (int)((int64_t)(chunk + 1) * (hi - lo) / A.chunks);
   const int tid = threadIdx.x;
 
   float2 xq[kBwR], yq[kBwR], gq[kBwR];
   float2 acc[kBwR][K];
 #pragma unroll
   for (int r = 0; r < kBwR; ++r) {
-    int64_t i = (int64_t)rb * kBwRows + r * kBwThreads + tid;
-    if (i >= A.n) i = A.n - 1;
+    const int64_t ir = map_row(A.map, A.n, kBwRows, rb, r * kBwThreads + tid);
+    const int64_t i = ir >= 0 ? ir : 0;  // padding rows compute on row 0 and are not written
     const float2 p = __ldg(A.x + i);
     xq[r] = f2(p.x, p.x);
     yq[r] = f2(p.y, p.y);
     {
-      // rows past n carry g = 0 so that they add nothing to the fused d_v
-      const int64_t i0 = (int64_t)rb * kBwRows + r * kBwThreads + tid;
-      const float gv = (DV && i0 < A.n) ? __ldg(A.grow + i0) : 0.f;
+      // padding rows carry g = 0 so that they add nothing to the fused d_v
+      const float gv = (DV && ir >= 0) ? __ldg(A.grow + ir) : 0.f;
       gq[r] = f2(gv, gv);
     }
 #pragma unroll
@@ -186,6 +192,12 @@ __device__ __forceinline__ void bwd_rows_body(const BwArgs& A, int rb, int chunk
       const int nsg = (cnt + kBwSeg - 1) / kBwSeg;
       if (SPLIT) {
       for (int sg = 0; sg < nsg; ++sg) {
+        if (A.info && seg_far(B, grid_x(A.src.g, c0 + kBwSeg * sg),
+                              grid_x(A.src.g, c0 + min(kBwSeg * sg + kBwSeg, cnt) - 1), yt, A.sc)) {
+          // every pair's exp2 flushes to 0: nothing to add, zero column sums
+          if (fuse_dv && (tid & 31) < kBwSeg) sm.dvred[tid >> 5][sg * kBwSeg + (tid & 31)] = 0.f;
+          continue;
+        }
         // Split exponent (see the forward pass): k v = 2^(2 q x' + a_i) v~.
         // Per pair one packed FMA forms the exponent and three accumulate the
         // x' moments S0 = sum k~ v~, S1 = sum k~ v~ x', S2 = sum k~ v~ x'^2 of
@@ -235,6 +247,11 @@ __device__ __forceinline__ void bwd_rows_body(const BwArgs& A, int rb, int chunk
       }
       } else {
       for (int sg = 0; sg < nsg; ++sg) {
+        if (A.info && seg_far(B, grid_x(A.src.g, c0 + kBwSeg * sg),
+                              grid_x(A.src.g, c0 + min(kBwSeg * sg + kBwSeg, cnt) - 1), yt, A.sc)) {
+          if (fuse_dv && (tid & 31) < kBwSeg) sm.dvred[tid >> 5][sg * kBwSeg + (tid & 31)] = 0.f;
+          continue;
+        }
         const float o = grid_x(A.src.g, c0 + kBwSeg * sg + kBwSeg / 2);
         float2 qx[kBwR];
 #pragma unroll
@@ -333,8 +350,8 @@ __device__ __forceinline__ void bwd_rows_body(const BwArgs& A, int rb, int chunk
 
 #pragma unroll
   for (int r = 0; r < kBwR; ++r) {
-    const int64_t i = (int64_t)rb * kBwRows + r * kBwThreads + tid;
-    if (i < A.n) {
+    const int64_t i = map_row(A.map, A.n, kBwRows, rb, r * kBwThreads + tid);
+    if (i >= 0) {
 #pragma unroll
       for (int k = 0; k < K; ++k) A.partial[((int64_t)chunk * K + k) * A.n + i] = sm.ksum[r][k][tid] - sm.kcomp[r][k][tid];
     }
@@ -390,20 +407,26 @@ __device__ __forceinline__ void dv_load_pair(const BwArgs& A, int t, int p, floa
 
 template <bool SPLIT>
 __device__ __forceinline__ void dv_rows_body(const BwArgs& A, int rb, int chunk, DvSmem& sm) {
-  const int nt = A.src.n_tiles;
-  const int t0 = (int)((int64_t)chunk * nt / A.chunks);
-  const int t1 = (int)((int64_t)(chunk + 1) * nt / A.chunks);
+  RowBlockInfo B{};
+  int lo = 0, hi = A.src.n_tiles;
+  if (A.info) {
+    B = A.info[rb];
+    lo = B.t_lo;
+    hi = B.t_hi > B.t_lo ? B.t_hi : B.t_lo;
+  }
+  const int t0 = lo + (int)((int64_t)chunk * (hi - lo) / A.chunks);
+  const int t1 = lo + (int)((int64_t)(chunk + 1) * (hi - lo) / A.chunks);
   const int tid = threadIdx.x;
   float xq[kDvR], yq[kDvR];
   float2 gq[kDvR];
 #pragma unroll
   for (int r = 0; r < kDvR; ++r) {
-    const int64_t i0 = (int64_t)rb * kDvRows + r * kBwThreads + tid;
-    const int64_t i = i0 < A.n ? i0 : A.n - 1;
+    const int64_t ir = map_row(A.map, A.n, kDvRows, rb, r * kBwThreads + tid);
+    const int64_t i = ir >= 0 ? ir : 0;
     const float2 p = __ldg(A.x + i);
     xq[r] = p.x;
     yq[r] = p.y;
-    const float gv = i0 < A.n ? __ldg(A.grow + i0) : 0.f;  // rows past n add nothing
+    const float gv = ir >= 0 ? __ldg(A.grow + ir) : 0.f;  // padding rows add nothing
     gq[r] = f2(gv, gv);
   }
   float2 X = f2(0.f, 0.f);
@@ -428,6 +451,12 @@ __device__ __forceinline__ void dv_rows_body(const BwArgs& A, int rb, int chunk,
     }
     const int nsg = (cnt + kBwSeg - 1) / kBwSeg;
     for (int sg = 0; sg < nsg; ++sg) {
+      if (A.info && seg_far(B, grid_x(A.src.g, c0 + kBwSeg * sg),
+                            grid_x(A.src.g, c0 + min(kBwSeg * sg + kBwSeg, cnt) - 1), yt, A.sc)) {
+        // every pair's exp2 flushes to 0: zero column sums for this sub-segment
+        if ((tid & 31) < kBwSeg) sm.dvred[tid >> 5][sg * kBwSeg + (tid & 31)] = 0.f;
+        continue;
+      }
       const float o = grid_x(A.src.g, c0 + kBwSeg * sg + kBwSeg / 2);
       float2 qa[kDvR], qb[kDvR];  // split: (2q, -(q^2 + dy'^2)); unsplit: (q, dy'^2)
 #pragma unroll
@@ -622,8 +651,18 @@ __global__ void __launch_bounds__(kMergeThreads) scalar_batched_kernel(const __g
 
 __device__ __forceinline__ void dv_merge_body(const DvMergeP& P, int64_t j) {
   if (j >= P.m) return;
+  // with row-block info, a row block wrote source j only when j's tile is in
+  // its active range; elsewhere its sum is exactly 0 and is not read
+  int t = 0;
+  if (P.info) {
+    const int64_t r = j / P.W;
+    t = (int)(r * P.segs + (j - r * P.W) / kBwTile);
+  }
   float s = 0.f, c = 0.f;
-  for (int rb = 0; rb < P.row_blocks; ++rb) kahan(s, c, P.dv_part[(int64_t)rb * P.m + j]);
+  for (int rb = 0; rb < P.row_blocks; ++rb) {
+    if (P.info && !(P.info[rb].t_lo <= t && t < P.info[rb].t_hi)) continue;
+    kahan(s, c, P.dv_part[(int64_t)rb * P.m + j]);
+  }
   P.d_v[j] = P.var * (s - c);
 }
 
@@ -690,7 +729,7 @@ lr_status launch_bwd_rows_batched(const BwArgs* p, int count, cudaStream_t s) {
       if (pk != kind) continue;
       B.p[B.count] = p[i];
       B.start[B.count] = (int32_t)tot;
-      tot += (int64_t)((p[i].n + p[i].rows_per_cta - 1) / p[i].rows_per_cta) * p[i].chunks;
+      tot += row_block_count(p[i].map, p[i].n, p[i].rows_per_cta) * p[i].chunks;
       ++B.count;
     }
   }
@@ -753,7 +792,7 @@ lr_status launch_dv_rows_batched(const BwArgs* p, int count, cudaStream_t s) {
       if ((p[i].split ? 1 : 0) != kind) continue;
       B.p[B.count] = p[i];
       B.start[B.count] = (int32_t)tot;
-      tot += (int64_t)((p[i].n + kDvRows - 1) / kDvRows) * p[i].chunks;
+      tot += row_block_count(p[i].map, p[i].n, kDvRows) * p[i].chunks;
       ++B.count;
     }
   }
@@ -783,11 +822,14 @@ lr_status launch_moments_merge_batched(const MomMergeP* p, int count, cudaStream
 
 struct RowPlan {
   int32_t n_tiles, segs, chunks, row_blocks, K, rows_per_cta;
+  RowMap map;                                  // row blocks: image tiles of a grid query, else index order
   size_t partial_bytes, scal_bytes, dv_bytes;  // dv_bytes: fused d_v partials (grid sources)
+  size_t info_bytes;                           // grid sources: row-block boxes
   int64_t merge_blocks;
 };
 
-static lr_status plan_rows(int64_t n, int64_t m, bool grid, const lr_grid* g, bool self, bool fuse_dv, RowPlan* R) {
+static lr_status plan_rows(int64_t n, int64_t m, bool grid, const lr_grid* g, bool self, bool fuse_dv,
+                           const lr_grid* qgrid, RowPlan* R) {
   RowPlan p{};
   p.K = self ? 7 : 4;
   const bool dv = grid && fuse_dv;
@@ -799,7 +841,9 @@ static lr_status plan_rows(int64_t n, int64_t m, bool grid, const lr_grid* g, bo
   } else {
     p.n_tiles = (int32_t)((m + kBwTile - 1) / kBwTile);
   }
-  p.row_blocks = (int32_t)((n + p.rows_per_cta - 1) / p.rows_per_cta);
+  p.map = (grid && qgrid) ? make_row_map(qgrid, p.rows_per_cta) : RowMap{};
+  p.row_blocks = (int32_t)row_block_count(p.map, n, p.rows_per_cta);
+  p.info_bytes = grid ? row_info_bytes(p.map, n, p.rows_per_cta) : 0;
   int dev = 0, n_sm = 1, occ = 1;
   LR_CHECK_CUDA(cudaGetDevice(&dev));
   LR_CHECK_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
@@ -860,16 +904,17 @@ static MergeArgs row_merge_args(bool grid, float ell, float var, const float* pa
 // query points against grid (yg) or explicit (ys) sources, planned as
 // gp_kernel_matvec_bwd plans it; ws receives the partials. With ws == NULL
 // only *bytes is filled in.
-lr_status make_rows_problem(const float2* x, int64_t n, const float2* ys, const lr_grid* yg, int64_t m,
-                            const float* v, const float* g, float ell, float var, float2* dx, double* d_len,
+lr_status make_rows_problem(const float2* x, int64_t n, const lr_grid* qgrid, const float2* ys, const lr_grid* yg,
+                            int64_t m, const float* v, const float* g, float ell, float var, float2* dx, double* d_len,
                             double* d_var, float* d_v, char* ws, BwArgs* A, MergeArgs* M, ScalP* S, DvMergeP* D,
-                            size_t* bytes) {
+                            RowInfoP* RI, size_t* bytes) {
   RowPlan R;
   const bool grid = ys == nullptr;
   const bool fuse = grid && d_v != nullptr;
-  lr_status st = plan_rows(n, m, grid, yg, false, fuse, &R);
+  lr_status st = plan_rows(n, m, grid, yg, false, fuse, qgrid, &R);
   if (st != LR_OK) return st;
-  *bytes = R.partial_bytes + R.scal_bytes + (fuse ? R.dv_bytes : 0);
+  const size_t off_info = R.partial_bytes + R.scal_bytes + (fuse ? R.dv_bytes : 0);
+  *bytes = off_info + R.info_bytes;
   if (!ws) return LR_OK;
   BwArgs a{};
   a.x = x;
@@ -891,7 +936,12 @@ lr_status make_rows_problem(const float2* x, int64_t n, const float2* ys, const 
   a.partial = reinterpret_cast<float*>(ws);
   a.grow = fuse ? g : nullptr;
   a.dv_part = fuse ? reinterpret_cast<float*>(ws + R.partial_bytes + R.scal_bytes) : nullptr;
+  a.map = R.map;
+  a.info = grid ? reinterpret_cast<const RowBlockInfo*>(ws + off_info) : nullptr;
   *A = a;
+  if (RI)
+    *RI = RowInfoP{x, n, R.map, R.rows_per_cta, R.segs, a.src.g, a.sc,
+                   grid ? reinterpret_cast<RowBlockInfo*>(ws + off_info) : nullptr};
   *M = row_merge_args(grid, ell, var, a.partial, R.chunks, n, g, v, dx, reinterpret_cast<double*>(ws + R.partial_bytes));
   S->part = M->scal_part;
   S->nblk = (int32_t)R.merge_blocks;
@@ -903,13 +953,16 @@ lr_status make_rows_problem(const float2* x, int64_t n, const float2* ys, const 
     D->m = m;
     D->var = var;
     D->d_v = fuse ? d_v : nullptr;
+    D->info = a.info;
+    D->W = grid ? a.src.g.W : 0;
+    D->segs = R.segs;
   }
   return LR_OK;
 }
 
-static lr_status launch_rows(const float2* x, int64_t n, const float2* ys, const lr_grid* yg, int64_t m,
-                             const float* v, const float* gs, const float* g, const float* vrow, float ell, float var,
-                             bool self, float2* d_x, float* d_v, double* d_len, double* d_var, char* ws,
+static lr_status launch_rows(const float2* x, int64_t n, const lr_grid* qgrid, const float2* ys, const lr_grid* yg,
+                             int64_t m, const float* v, const float* gs, const float* g, const float* vrow, float ell,
+                             float var, bool self, float2* d_x, float* d_v, double* d_len, double* d_var, char* ws,
                              cudaStream_t s) {
   if (!self) {
     // grid sources fuse d_v into the row pass; explicit sources leave d_v to the caller
@@ -917,11 +970,13 @@ static lr_status launch_rows(const float2* x, int64_t n, const float2* ys, const
     MergeArgs M;
     ScalP S;
     DvMergeP D;
+    RowInfoP RI;
     size_t b = 0;
-    lr_status st = make_rows_problem(x, n, ys, yg, m, v, g, ell, var, d_x, d_len, d_var, ys == nullptr ? d_v : nullptr,
-                                     ws, &A, &M, &S, &D, &b);
+    lr_status st = make_rows_problem(x, n, qgrid, ys, yg, m, v, g, ell, var, d_x, d_len, d_var,
+                                     ys == nullptr ? d_v : nullptr, ws, &A, &M, &S, &D, &RI, &b);
     if (st != LR_OK) return st;
-    const unsigned grid = (unsigned)(((n + A.rows_per_cta - 1) / A.rows_per_cta) * A.chunks);
+    if (RI.info && (st = launch_row_info(RI, s)) != LR_OK) return st;
+    const unsigned grid = (unsigned)(row_block_count(A.map, n, A.rows_per_cta) * A.chunks);
     if (ys == nullptr && A.dv_part && A.split)
       bwd_rows_kernel<true, false, true, true><<<grid, kBwThreads, 0, s>>>(A);
     else if (ys == nullptr && A.dv_part)
@@ -946,7 +1001,7 @@ static lr_status launch_rows(const float2* x, int64_t n, const float2* ys, const
     return LR_OK;
   }
   RowPlan R;
-  lr_status st = plan_rows(n, m, false, yg, true, false, &R);
+  lr_status st = plan_rows(n, m, false, yg, true, false, nullptr, &R);
   if (st != LR_OK) return st;
   BwArgs A{};
   A.x = x;
@@ -995,14 +1050,16 @@ static lr_status launch_rows(const float2* x, int64_t n, const float2* ys, const
 }
 
 // Plan of the d_v-only pass over grid sources (dv_rows_kernel).
-static lr_status plan_dv(int64_t n, const lr_grid* g, RowPlan* R) {
+static lr_status plan_dv(int64_t n, const lr_grid* g, const lr_grid* qgrid, RowPlan* R) {
   RowPlan p{};
   p.K = 0;
   p.rows_per_cta = kDvRows;
   const int W = g->nx * g->ss;
   p.segs = (W + kBwTile - 1) / kBwTile;
   p.n_tiles = (int32_t)((int64_t)p.segs * g->ny * g->ss);
-  p.row_blocks = (int32_t)((n + kDvRows - 1) / kDvRows);
+  p.map = qgrid ? make_row_map(qgrid, kDvRows) : RowMap{};
+  p.row_blocks = (int32_t)row_block_count(p.map, n, kDvRows);
+  p.info_bytes = row_info_bytes(p.map, n, kDvRows);
   int dev = 0, n_sm = 1, occ = 1, occ2 = 1;
   LR_CHECK_CUDA(cudaGetDevice(&dev));
   LR_CHECK_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
@@ -1015,14 +1072,14 @@ static lr_status plan_dv(int64_t n, const lr_grid* g, RowPlan* R) {
   return LR_OK;
 }
 
-lr_status make_train_problem(const float2* x, int64_t n, const float2* ys, const lr_grid* yg, int64_t m,
-                             const float* v, float ell, float var, float* out, float* mom, char* ws, BwArgs* A,
-                             MomMergeP* MM, size_t* bytes) {
+lr_status make_train_problem(const float2* x, int64_t n, const lr_grid* qgrid, const float2* ys, const lr_grid* yg,
+                             int64_t m, const float* v, float ell, float var, float* out, float* mom, char* ws,
+                             BwArgs* A, MomMergeP* MM, RowInfoP* RI, size_t* bytes) {
   BwArgs a;
   MergeArgs M;
   ScalP S;
-  lr_status st = make_rows_problem(x, n, ys, yg, m, v, nullptr, ell, var, nullptr, nullptr, nullptr, nullptr, ws,
-                                   ws ? &a : nullptr, ws ? &M : nullptr, ws ? &S : nullptr, nullptr, bytes);
+  lr_status st = make_rows_problem(x, n, qgrid, ys, yg, m, v, nullptr, ell, var, nullptr, nullptr, nullptr, nullptr,
+                                   ws, ws ? &a : nullptr, ws ? &M : nullptr, ws ? &S : nullptr, nullptr, RI, bytes);
   if (st != LR_OK || !ws) return st;
   *A = a;
   MM->partial = a.partial;
@@ -1048,12 +1105,13 @@ lr_status make_moment_rows_problem(const float* mom, int64_t n, bool grid, const
   return LR_OK;
 }
 
-lr_status make_dv_problem(const float2* x, int64_t n, const lr_grid* yg, const float* g, float ell, float var,
-                          float* d_v, char* ws, BwArgs* A, DvMergeP* D, size_t* bytes) {
+lr_status make_dv_problem(const float2* x, int64_t n, const lr_grid* qgrid, const lr_grid* yg, const float* g,
+                          float ell, float var, float* d_v, char* ws, BwArgs* A, DvMergeP* D, RowInfoP* RI,
+                          size_t* bytes) {
   RowPlan R;
-  lr_status st = plan_dv(n, yg, &R);
+  lr_status st = plan_dv(n, yg, qgrid, &R);
   if (st != LR_OK) return st;
-  *bytes = R.dv_bytes;
+  *bytes = R.dv_bytes + R.info_bytes;
   if (!ws) return LR_OK;
   BwArgs a{};
   a.x = x;
@@ -1071,21 +1129,27 @@ lr_status make_dv_problem(const float2* x, int64_t n, const lr_grid* yg, const f
   a.rows_per_cta = kDvRows;
   a.grow = g;
   a.dv_part = reinterpret_cast<float*>(ws);
+  a.map = R.map;
+  RowBlockInfo* info = reinterpret_cast<RowBlockInfo*>(ws + R.dv_bytes);
+  a.info = info;
   *A = a;
-  *D = DvMergeP{a.dv_part, R.row_blocks, a.src.m, var, d_v};
+  *D = DvMergeP{a.dv_part, R.row_blocks, a.src.m, var, d_v, info, a.src.g.W, R.segs};
+  if (RI) *RI = RowInfoP{x, n, R.map, kDvRows, R.segs, a.src.g, a.sc, info};
   return LR_OK;
 }
 
 // d_v of grid sources from the d_v-only pass: dv_part, then the fixed-order
 // merge over row blocks. ws: the plan's dv_bytes.
-static lr_status launch_dv(const float2* x, int64_t n, const lr_grid* yg, const float* g, float ell, float var,
-                           float* d_v, char* ws, cudaStream_t s) {
+static lr_status launch_dv(const float2* x, int64_t n, const lr_grid* qgrid, const lr_grid* yg, const float* g,
+                           float ell, float var, float* d_v, char* ws, cudaStream_t s) {
   BwArgs A;
   DvMergeP D;
+  RowInfoP RI;
   size_t b = 0;
-  lr_status st = make_dv_problem(x, n, yg, g, ell, var, d_v, ws, &A, &D, &b);
+  lr_status st = make_dv_problem(x, n, qgrid, yg, g, ell, var, d_v, ws, &A, &D, &RI, &b);
   if (st != LR_OK) return st;
-  const unsigned grid = (unsigned)(((n + kDvRows - 1) / kDvRows) * A.chunks);
+  if ((st = launch_row_info(RI, s)) != LR_OK) return st;
+  const unsigned grid = (unsigned)(row_block_count(A.map, n, kDvRows) * A.chunks);
   if (A.split)
     dv_rows_kernel<true><<<grid, kBwThreads, 0, s>>>(A);
   else
@@ -1114,10 +1178,11 @@ static lr_status launch_moment_rows(const float* mom, int64_t n, bool grid, cons
   return LR_OK;
 }
 
-static size_t rows_ws(int64_t n, int64_t m, bool grid, const lr_grid* g, bool self, bool fuse_dv, lr_status* st) {
+static size_t rows_ws(int64_t n, int64_t m, bool grid, const lr_grid* g, bool self, bool fuse_dv,
+                      const lr_grid* qgrid, lr_status* st) {
   RowPlan R;
-  *st = plan_rows(n, m, grid, g, self, fuse_dv, &R);
-  return R.partial_bytes + R.scal_bytes + (fuse_dv ? R.dv_bytes : 0);
+  *st = plan_rows(n, m, grid, g, self, fuse_dv, qgrid, &R);
+  return R.partial_bytes + R.scal_bytes + (fuse_dv ? R.dv_bytes : 0) + R.info_bytes;
 }
 
 struct BwPlan {
@@ -1154,6 +1219,7 @@ static lr_status plan_bwd(const lr_points* q, const lr_points* s, const lr_grads
   LR_REQUIRE(gr->beta_in == nullptr || p.q_raytrace, "gp_kernel_matvec_bwd: beta_in given but the query is not ray-traced");
   LR_REQUIRE(((uintptr_t)gr->beta_in & 7u) == 0, "gp_kernel_matvec_bwd: beta_in must be 8-byte aligned");
   p.moments = gr->moments_in != nullptr;
+  const lr_grid* qg = query_layout(q);  // row blocks follow the image tiles
   LR_REQUIRE(!p.moments || !p.self, "gp_kernel_matvec_bwd: moments_in applies to non-self sources only");
   LR_REQUIRE(((uintptr_t)gr->moments_in & 3u) == 0, "gp_kernel_matvec_bwd: moments_in must be 4-byte aligned");
   size_t off = 0;
@@ -1167,12 +1233,13 @@ static lr_status plan_bwd(const lr_points* q, const lr_points* s, const lr_grads
     p.off_dv = off;
     if (p.s_grid && gr->d_v && p.n > 0) {
       RowPlan R;
-      st = plan_dv(p.n, &s->grid, &R);
+      st = plan_dv(p.n, &s->grid, qg, &R);
       if (st != LR_OK) return st;
-      off += R.dv_bytes;
+      off += R.dv_bytes + R.info_bytes;
     }
   } else {
-    size_t b = rows_ws(p.n, p.m, p.s_grid, p.s_grid ? &s->grid : nullptr, p.self, p.s_grid && gr->d_v != nullptr, &st);
+    size_t b = rows_ws(p.n, p.m, p.s_grid, p.s_grid ? &s->grid : nullptr, p.self, p.s_grid && gr->d_v != nullptr, qg,
+                       &st);
     if (st != LR_OK) return st;
     off += b;
   }
@@ -1196,7 +1263,7 @@ static lr_status plan_bwd(const lr_points* q, const lr_points* s, const lr_grads
   }
   p.off_swaprows = off;
   if (!p.self && gr->d_y) {
-    size_t b = rows_ws(p.m, p.n, false, nullptr, false, false, &st);
+    size_t b = rows_ws(p.m, p.n, false, nullptr, false, false, nullptr, &st);
     if (st != LR_OK) return st;
     off += b;
   }
@@ -1268,6 +1335,7 @@ extern "C" lr_status gp_kernel_matvec_bwd(const lr_points* query, const lr_point
   }
   const float2* ys = P.self ? xq : (P.s_grid ? nullptr : reinterpret_cast<const float2*>(source->xy));
   const lr_grid* yg = P.s_grid ? &source->grid : nullptr;
+  const lr_grid* qgrid = query_layout(query);
   float2* dx = P.need_dx ? (G.d_x ? reinterpret_cast<float2*>(G.d_x) : reinterpret_cast<float2*>(ws + P.off_dx))
                          : nullptr;
   if (P.moments) {
@@ -1277,12 +1345,13 @@ extern "C" lr_status gp_kernel_matvec_bwd(const lr_points* query, const lr_point
                             G.d_variance, ws + P.off_rows, s);
     if (st != LR_OK) return st;
     if (P.s_grid && G.d_v) {
-      st = launch_dv(xq, P.n, yg, g_out, lengthscale, variance, G.d_v, ws + P.off_dv, s);
+      st = launch_dv(xq, P.n, qgrid, yg, g_out, lengthscale, variance, G.d_v, ws + P.off_dv, s);
       if (st != LR_OK) return st;
     }
   } else {
     // row pass: d_x (both roles for a self-kernel), self d_v, d_l, d_var
-    st = launch_rows(xq, P.n, ys, yg, P.m, v, P.self ? g_out : nullptr, g_out, v, lengthscale, variance, P.self, dx,
+    st = launch_rows(xq, P.n, qgrid, ys, yg, P.m, v, P.self ? g_out : nullptr, g_out, v, lengthscale, variance, P.self,
+                     dx,
                      (P.self || P.s_grid) ? G.d_v : nullptr, G.d_lengthscale, G.d_variance, ws + P.off_rows, s);
     if (st != LR_OK) return st;
   }
@@ -1303,7 +1372,8 @@ extern "C" lr_status gp_kernel_matvec_bwd(const lr_points* query, const lr_point
   }
   // d_y of explicit non-self sources: the row pass with the point sets swapped
   if (!P.self && G.d_y) {
-    st = launch_rows(reinterpret_cast<const float2*>(source->xy), P.m, xq, nullptr, P.n, g_out, nullptr, v, g_out,
+    st = launch_rows(reinterpret_cast<const float2*>(source->xy), P.m, nullptr, xq, nullptr, P.n, g_out, nullptr, v,
+                     g_out,
                      lengthscale, variance, false, reinterpret_cast<float2*>(G.d_y), nullptr, nullptr, nullptr,
                      ws + P.off_swaprows, s);
     if (st != LR_OK) return st;
@@ -1347,9 +1417,9 @@ static lr_status plan_train(const lr_points* q, const lr_points* s, TrainPlan* T
   if (p.q_raytrace || p.q_grid) off += align256(8 * (size_t)p.n);
   p.off_rows = off;
   if (p.n > 0 && p.m > 0) {
-    st = plan_rows(p.n, p.m, p.s_grid, p.s_grid ? &s->grid : nullptr, false, false, &p.R);
+    st = plan_rows(p.n, p.m, p.s_grid, p.s_grid ? &s->grid : nullptr, false, false, query_layout(q), &p.R);
     if (st != LR_OK) return st;
-    off += p.R.partial_bytes + p.R.scal_bytes;
+    off += p.R.partial_bytes + p.R.scal_bytes + p.R.info_bytes;
   }
   p.bytes = off;
   *T = p;
@@ -1408,10 +1478,13 @@ extern "C" lr_status gp_kernel_matvec_train(const lr_points* query, const lr_poi
   MomMergeP MM;
   size_t b = 0;
   const float2* ys = T.s_grid ? nullptr : reinterpret_cast<const float2*>(source->xy);
-  st = make_train_problem(xq, T.n, ys, T.s_grid ? &source->grid : nullptr, T.m, v, lengthscale, variance, out,
-                          moments_out, ws + T.off_rows, &A, &MM, &b);
+  RowInfoP RI;
+  st = make_train_problem(xq, T.n, query_layout(query), ys,
+                          T.s_grid ? &source->grid : nullptr, T.m, v, lengthscale, variance, out, moments_out,
+                          ws + T.off_rows, &A, &MM, &RI, &b);
   if (st != LR_OK) return st;
-  const unsigned grid = (unsigned)(((T.n + A.rows_per_cta - 1) / A.rows_per_cta) * A.chunks);
+  if (RI.info && (st = launch_row_info(RI, s)) != LR_OK) return st;
+  const unsigned grid = (unsigned)(row_block_count(A.map, T.n, A.rows_per_cta) * A.chunks);
   if (T.s_grid && A.split)
     bwd_rows_kernel<true, false, false, true><<<grid, kBwThreads, 0, s>>>(A);
   else if (T.s_grid)

@@ -5,6 +5,7 @@
 #include "batch.cuh"
 #include "grid.cuh"
 #include "lens.cuh"
+#include "rowmap.cuh"
 
 namespace lr {
 
@@ -19,6 +20,23 @@ constexpr int kSplitSeg = 16;
 constexpr float kSplitXMax = 5.5f;
 inline int32_t grid_split_ok(const GridDev& g, float sc) {
   return sc * g.h * (float)(kSplitSeg / 2) <= kSplitXMax ? 1 : 0;
+}
+
+// ---- row-block boxes for grid sources (rowmap.cu)
+struct RowInfoP {
+  const float2* x;  // query points
+  int64_t n;
+  RowMap map;
+  int32_t rows_per_cta, segs;
+  GridDev g;        // source grid
+  float sc;
+  RowBlockInfo* info;  // [row blocks]
+};
+lr_status launch_row_info(const RowInfoP& P, cudaStream_t s);
+lr_status launch_row_info_batched(const RowInfoP* p, int count, cudaStream_t s);
+inline size_t row_info_bytes(const RowMap& m, int64_t n, int rows_per_cta) {
+  const size_t b = sizeof(RowBlockInfo) * (size_t)(row_block_count(m, n, rows_per_cta) + 1);
+  return (b + 255) & ~size_t(255);
 }
 
 // ---- forward reduction (matvec.cu)
@@ -46,6 +64,8 @@ struct MvArgs {
   int32_t split;     // grid sources: split exponent (grid_split_ok)
   float variance;
   int32_t chunks;    // column chunks per row block
+  RowMap map;        // order of the query rows in row blocks
+  const RowBlockInfo* info;  // grid sources: per-row-block box and active tiles, or NULL (no skipping)
   float* out;        // [n] when chunks == 1
   float* partial;    // [chunks][n] when chunks > 1
 };
@@ -86,6 +106,8 @@ struct BwArgs {
   float sc;         // sqrt(log2(e)/(2 l^2)): scale of the tile-local grid coordinates
   int32_t split;    // grid sources: split exponent (grid_split_ok)
   int32_t chunks;
+  RowMap map;       // order of the query rows in row blocks
+  const RowBlockInfo* info;  // grid sources: per-row-block box and active tiles, or NULL (no skipping)
   int32_t K;        // quantities per row: 4, or 7 for a self-kernel
   int32_t rows_per_cta;  // kBwThreads x (kBwR, or kBwRdv with the fused d_v)
   float* partial;   // [chunks][K][n]
@@ -101,6 +123,8 @@ struct DvMergeP {
   int64_t m;
   float var;
   float* d_v;
+  const RowBlockInfo* info;  // row blocks' active tile ranges, or NULL (every row block wrote every source)
+  int32_t W, segs;           // source grid width and tiles per grid row (with info)
 };
 
 // training forward: merge of the row-pass partials into out and the moments
@@ -189,14 +213,15 @@ lr_status launch_moments_merge_batched(const MomMergeP* p, int count, cudaStream
 // Training-step problems against grid sources (gp_kernel_matvec_train and
 // gp_kernel_matvec_bwd with moments plan them the same way). With ws == NULL
 // only *bytes is filled in.
-lr_status make_train_problem(const float2* x, int64_t n, const float2* ys, const lr_grid* yg, int64_t m,
-                             const float* v, float ell, float var, float* out, float* mom, char* ws, BwArgs* A,
-                             MomMergeP* MM, size_t* bytes);
+lr_status make_train_problem(const float2* x, int64_t n, const lr_grid* qgrid, const float2* ys, const lr_grid* yg,
+                             int64_t m, const float* v, float ell, float var, float* out, float* mom, char* ws,
+                             BwArgs* A, MomMergeP* MM, RowInfoP* RI, size_t* bytes);
 lr_status make_moment_rows_problem(const float* mom, int64_t n, bool grid, const float* g, const float* v, float ell,
                                    float var, float2* dx, double* d_len, double* d_var, char* ws, MergeArgs* M,
                                    ScalP* S, size_t* bytes);
-lr_status make_dv_problem(const float2* x, int64_t n, const lr_grid* yg, const float* g, float ell, float var,
-                          float* d_v, char* ws, BwArgs* A, DvMergeP* D, size_t* bytes);
+lr_status make_dv_problem(const float2* x, int64_t n, const lr_grid* qgrid, const lr_grid* yg, const float* g,
+                          float ell, float var, float* d_v, char* ws, BwArgs* A, DvMergeP* D, RowInfoP* RI,
+                          size_t* bytes);
 lr_status launch_vjp_batched(const VjpP* p, int count, cudaStream_t s);
 lr_status launch_vjp_final_batched(const VjpFinalP* p, int count, cudaStream_t s);
 
@@ -204,10 +229,10 @@ lr_status launch_vjp_final_batched(const VjpFinalP* p, int count, cudaStream_t s
 lr_status make_mv_problem(const float2* x, int64_t n, const float2* ys, const lr_grid* yg, int64_t m, const float* v,
                           float ell, float var, float* out, float* partial, MvArgs* A, MergeP* M,
                           size_t* partial_bytes);
-lr_status make_rows_problem(const float2* x, int64_t n, const float2* ys, const lr_grid* yg, int64_t m,
-                            const float* v, const float* g, float ell, float var, float2* dx, double* d_len,
+lr_status make_rows_problem(const float2* x, int64_t n, const lr_grid* qgrid, const float2* ys, const lr_grid* yg,
+                            int64_t m, const float* v, const float* g, float ell, float var, float2* dx, double* d_len,
                             double* d_var, float* d_v, char* ws, BwArgs* A, MergeArgs* M, ScalP* S, DvMergeP* D,
-                            size_t* bytes);
+                            RowInfoP* RI, size_t* bytes);
 lr_status make_rt_problem(const lr_points* p, float2* beta, float2* alpha, RtP* R);
 lr_status make_vjp_problem(const lr_points* p, const float2* dbeta, double* d_lens, double* d_sub, void* ws, VjpP* V,
                            VjpFinalP* F);

@@ -86,6 +86,7 @@ struct Req {
   ScalP scal;
   BwArgs dv;        // d_v sweep
   DvMergeP dvm;
+  RowInfoP tinfo, dinfo;  // row-block boxes of the training forward and the d_v sweep
   VjpP vjp;
   VjpFinalP vfin;
   AxpyP resid, upd;
@@ -138,13 +139,14 @@ size_t carve(size_t& off, size_t bytes) {
 lr_status size_request(Req* r) {
   const int64_t n = r->n, m = r->m;
   size_t train_b = 0, mrows_b = 0, dv_b = 0;
-  lr_status st = make_train_problem(nullptr, n, nullptr, &r->ygrid, m, nullptr, r->ell, r->var, nullptr, nullptr,
-                                    nullptr, nullptr, nullptr, &train_b);
+  lr_status st = make_train_problem(nullptr, n, &r->grid, nullptr, &r->ygrid, m, nullptr, r->ell, r->var, nullptr,
+                                    nullptr, nullptr, nullptr, nullptr, nullptr, &train_b);
   if (st != LR_OK) return st;
   st = make_moment_rows_problem(nullptr, n, true, nullptr, nullptr, r->ell, r->var, nullptr, nullptr, nullptr,
                                 nullptr, nullptr, nullptr, &mrows_b);
   if (st != LR_OK) return st;
-  st = make_dv_problem(nullptr, n, &r->ygrid, nullptr, r->ell, r->var, nullptr, nullptr, nullptr, nullptr, &dv_b);
+  st = make_dv_problem(nullptr, n, &r->grid, &r->ygrid, nullptr, r->ell, r->var, nullptr, nullptr, nullptr, nullptr,
+                       nullptr, &dv_b);
   if (st != LR_OK) return st;
   size_t off = 0;
   r->o_beta = carve(off, 8 * n);
@@ -200,15 +202,15 @@ lr_status init_request(lr_session* S, Req* r) {
   if ((st = make_rt_problem(&P, beta, nullptr, &r->rt)) != LR_OK) return st;
   size_t b = 0;
   float* mom = reinterpret_cast<float*>(d + r->o_mom);
-  if ((st = make_train_problem(beta, r->n, nullptr, &r->ygrid, r->m, v, r->ell, r->var, out, mom, d + r->o_train,
-                               &r->train, &r->tmerge, &b)) != LR_OK)
+  if ((st = make_train_problem(beta, r->n, &r->grid, nullptr, &r->ygrid, r->m, v, r->ell, r->var, out, mom,
+                               d + r->o_train, &r->train, &r->tmerge, &r->tinfo, &b)) != LR_OK)
     return st;
   r->resid = AxpyP{out, data, g, r->n, 1.0f};
   if ((st = make_moment_rows_problem(mom, r->n, true, g, v, r->ell, r->var, dx, scal, scal + 1, d + r->o_mrows,
                                      &r->mrows, &r->scal, &b)) != LR_OK)
     return st;
-  if ((st = make_dv_problem(beta, r->n, &r->ygrid, g, r->ell, r->var, dv, d + r->o_dvp, &r->dv, &r->dvm, &b)) !=
-      LR_OK)
+  if ((st = make_dv_problem(beta, r->n, &r->grid, &r->ygrid, g, r->ell, r->var, dv, d + r->o_dvp, &r->dv, &r->dvm,
+                            &r->dinfo, &b)) != LR_OK)
     return st;
   if ((st = make_vjp_problem(&P, dx, dlens, dsub, d + r->o_vjp, &r->vjp, &r->vfin)) != LR_OK) return st;
   r->upd = AxpyP{v, dv, v, r->m, r->step};
@@ -218,6 +220,7 @@ lr_status init_request(lr_session* S, Req* r) {
 // One batched iteration over `act`.
 lr_status run_iteration(lr_session* S, const std::vector<Req*>& act) {
   std::vector<RtP> rt;
+  std::vector<RowInfoP> infos;
   std::vector<BwArgs> train, dvs;
   std::vector<MomMergeP> tmerge;
   std::vector<DvMergeP> dvm;
@@ -228,6 +231,8 @@ lr_status run_iteration(lr_session* S, const std::vector<Req*>& act) {
   std::vector<VjpFinalP> vfin;
   for (Req* r : act) {
     rt.push_back(r->rt);
+    infos.push_back(r->tinfo);
+    infos.push_back(r->dinfo);
     train.push_back(r->train);
     tmerge.push_back(r->tmerge);
     resid.push_back(r->resid);
@@ -243,6 +248,7 @@ lr_status run_iteration(lr_session* S, const std::vector<Req*>& act) {
   cudaStream_t s = S->stream;
   lr_status st;
   if ((st = launch_raytrace_batched(rt.data(), n, s)) != LR_OK) return st;
+  if ((st = launch_row_info_batched(infos.data(), (int)infos.size(), s)) != LR_OK) return st;
   if ((st = launch_bwd_rows_batched(train.data(), n, s)) != LR_OK) return st;
   if ((st = launch_moments_merge_batched(tmerge.data(), n, s)) != LR_OK) return st;
   if ((st = launch_axpy_batched(resid.data(), n, s)) != LR_OK) return st;
@@ -254,7 +260,7 @@ lr_status run_iteration(lr_session* S, const std::vector<Req*>& act) {
   if ((st = launch_vjp_final_batched(vfin.data(), n, s)) != LR_OK) return st;
   if ((st = launch_axpy_batched(upd.data(), n, s)) != LR_OK) return st;
   const int groups = (n + kMaxBatch - 1) / kMaxBatch;
-  S->launches += (uint64_t)groups * 11;
+  S->launches += (uint64_t)groups * 11 + (uint64_t)((2 * n + kMaxBatch - 1) / kMaxBatch);
   return LR_OK;
 }
 

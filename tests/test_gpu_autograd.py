@@ -32,8 +32,12 @@ def test_autograd_matches_direct_backward():
     g = dev(np.random.default_rng(1).standard_normal(p.n))
     (out * g).sum().backward()
     q = api.Points(grid=p.xgrid, lens=p.lens, sub=sub.detach())
-    G = api.gp_kernel_matvec_bwd(q, api.Points(grid=p.ygrid), v.detach(), p.lengthscale, 1.3, g,
-                                 want=["v", "lens", "sub", "lengthscale", "variance"])
+    s = api.Points(grid=p.ygrid)
+    # the wrapper's path: training forward (row moments), then the backward with them
+    beta = torch.empty((p.n, 2), device="cuda")
+    _, mom = api.gp_kernel_matvec_train(q, s, v.detach(), p.lengthscale, 1.3, beta=beta)
+    G = api.gp_kernel_matvec_bwd(q, s, v.detach(), p.lengthscale, 1.3, g,
+                                 want=["v", "lens", "sub", "lengthscale", "variance"], beta=beta, moments=mom)
     assert torch.equal(v.grad, G["v"])
     assert torch.equal(lens.grad[[0, 1, 2, 3, 4, 6, 7]], G["lens"].cpu())
     assert lens.grad[5] == 0

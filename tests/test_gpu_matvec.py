@@ -153,3 +153,30 @@ def test_deterministic_and_stream_ordered(orc):
 
 def test_no_fault_recorded():
     assert api.fault_status() == 0
+
+
+def test_evaluated_pairs_bounds():
+    """The grid kernels leave out only pairs beyond the exact-zero radius: none
+    for a length scale as large as the field, most for the realistic one."""
+    p = W.realistic(seed=3, side=80, ss=2, n_sub=0)
+    beta = api.lens_raytrace(api.Points(grid=p.xgrid, lens=p.lens))
+    full = p.n * p.m
+    assert api.grid_pairs_evaluated(beta, p.xgrid, p.ygrid, 100.0, 1024) == full
+    some = api.grid_pairs_evaluated(beta, p.xgrid, p.ygrid, p.lengthscale, 1024)
+    assert 0 < some < full
+    # explicit order (no layout) evaluates at least as many pairs as image tiles
+    assert api.grid_pairs_evaluated(beta, None, p.ygrid, p.lengthscale, 1024) >= some
+
+
+def test_grid_source_with_image_layout(orc):
+    """Explicit ray-traced pixels that carry their image grid (row blocks in
+    image tiles, pairs beyond the exact-zero radius left out) against the oracle."""
+    p = W.realistic(seed=5, side=64, ss=2, n_sub=10)
+    # the oracle's ray-traced points, rounded to FP32, feed both sides
+    _, bref = orc.raytrace(orc.grid_points(*p.xgrid.astuple()), p.lens.astuple(), p.sub)
+    b = bref.astype(np.float32)
+    yg = orc.grid_points(*p.ygrid.astuple())
+    got = host(api.gp_kernel_matvec(api.Points(xy=dev(b), grid=p.xgrid), api.Points(grid=p.ygrid), dev(p.v),
+                                    p.lengthscale, p.variance))
+    ref, ab = orc.kernel_matvec(b, yg, p.v, p.lengthscale, p.variance)
+    assert_matvec_close(got, ref, ab, what="grid source, image layout")
