@@ -314,8 +314,8 @@ __global__ void merge_batched_kernel(const __grid_constant__ Batch<MergeP> B) {
 // ---------------------------------------------------------------------------
 // Host side
 
-int32_t plan_chunks(int64_t row_blocks, int64_t n_tiles, int occupancy, int n_sm) {
-  const int64_t target = 8LL * n_sm * (occupancy > 0 ? occupancy : 1);
+int32_t plan_chunks(int64_t row_blocks, int64_t n_tiles, int occupancy, int n_sm, int waves) {
+  const int64_t target = (int64_t)waves * n_sm * (occupancy > 0 ? occupancy : 1);
   int64_t chunks = 1;
   if (row_blocks > 0 && n_tiles > 0) {
     chunks = (target + row_blocks - 1) / row_blocks;
@@ -415,7 +415,7 @@ static lr_status plan_matvec(const lr_points* q, const lr_points* s, int32_t nrh
   LR_CHECK_CUDA(cudaGetDevice(&dev));
   LR_CHECK_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
   LR_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, matvec_kernel<false>, kMvThreads, 0));
-  const int64_t chunks = plan_chunks(p.row_blocks, p.n_tiles, occ, n_sm);
+  const int64_t chunks = plan_chunks(p.row_blocks, p.n_tiles, occ, n_sm, p.s_grid ? kSkipWaves : kChunkWaves);
   p.chunks = (int32_t)chunks;
   size_t off = 0;
   const bool need_qbuf = (p.q_raytrace || p.q_grid) && !have_beta_out;

@@ -866,7 +866,7 @@ static lr_status plan_rows(int64_t n, int64_t m, bool grid, const lr_grid* g, bo
   } else {
     LR_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, bwd_rows_kernel<false, false, false>, kBwThreads, 0));
   }
-  const int32_t chunks = plan_chunks(p.row_blocks, p.n_tiles, occ, n_sm);
+  const int32_t chunks = plan_chunks(p.row_blocks, p.n_tiles, occ, n_sm, grid ? kSkipWaves : kChunkWaves);
   p.chunks = chunks;
   p.partial_bytes = align256(sizeof(float) * (size_t)p.chunks * p.K * (size_t)n);
   p.merge_blocks = (n + kMergeThreads - 1) / kMergeThreads;
@@ -1065,7 +1065,7 @@ static lr_status plan_dv(int64_t n, const lr_grid* g, const lr_grid* qgrid, RowP
   LR_CHECK_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
   LR_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, dv_rows_kernel<true>, kBwThreads, 0));
   LR_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, dv_rows_kernel<false>, kBwThreads, 0));
-  p.chunks = plan_chunks(p.row_blocks, p.n_tiles, occ < occ2 ? occ : occ2, n_sm);
+  p.chunks = plan_chunks(p.row_blocks, p.n_tiles, occ < occ2 ? occ : occ2, n_sm, kSkipWaves);
   const int64_t m = (int64_t)W * g->ny * g->ss;
   p.dv_bytes = align256(sizeof(float) * (size_t)p.row_blocks * (size_t)m);
   *R = p;

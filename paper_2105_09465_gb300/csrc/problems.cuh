@@ -241,6 +241,11 @@ lr_status make_vjp_problem(const lr_points* p, const float2* dbeta, double* d_le
 // every resident CTA slot (occupancy x SMs) receives about 8 tasks. Depends
 // only on the problem's own sizes, so a problem is summed in the same order
 // alone or inside a batch.
-int32_t plan_chunks(int64_t row_blocks, int64_t n_tiles, int occupancy, int n_sm);
+// Column chunks per row block so that there are about `waves` tasks per
+// resident CTA slot. Grid sources that leave out exactly-zero pairs have
+// smaller tasks, so they plan fewer (kSkipWaves).
+constexpr int kChunkWaves = 8;
+constexpr int kSkipWaves = 3;
+int32_t plan_chunks(int64_t row_blocks, int64_t n_tiles, int occupancy, int n_sm, int waves = kChunkWaves);
 
 }  // namespace lr
