@@ -29,6 +29,16 @@ sys.path.insert(0, str(ROOT))
 METRIC = "Gpair-evals/s fused raytrace+GP kernel matvec (fwd, fwd+bwd); p50/p99 req latency"
 UNIT = "Gpair/s"
 SM_MAX_MHZ_DEFAULT = 2070.0
+# Work per point-subhalo pair of the far-side tNFW form (x^2 >= 1.05, nearly
+# every pair), counted operation by operation from the kernels' source (FP32
+# lanes; packed f32x2 operations count 2 lanes for 2 pairs):
+# forward: 2 offsets, 3 for R^2 and x^2, 23 for the shared far terms (arctan
+# polynomial 12), 7 for the mass bracket, 2 to accumulate both components,
+# 1.25 for the Kahan fold after every 8 subhalos;
+# backward: 5 + 23, 13 for the G and H brackets, 1 for 1/R^2, 16 for the four
+# subhalo sums, 0.6 for the Kahan folds. MUFU: 2 rsqrt, 1 rcp, 1 lg2 each.
+RT_MUFU, RT_LANES = 4, 38.3
+VJ_MUFU, VJ_LANES = 4, 58.6
 
 
 def parse():
@@ -271,6 +281,20 @@ def event_time(fn, n, stream, flush):
     return float(np.mean([a.elapsed_time(b) for a, b in evs]))
 
 
+def kernel_time(fn, n, stream, flush, kernel):
+    """Mean device time (ms) of one library kernel alone over n calls of fn
+    (the library's launch timer: CUDA events around that kernel's launches on
+    its stream), and the mean CUDA-event time of the whole call."""
+    from paper_2105_09465_gb300 import api
+    api.kernel_timer_enable(True)
+    call_ms = event_time(fn, n, stream, flush)
+    api.kernel_timer_enable(False)
+    cnt, tot, dropped = api.kernel_timer_read(kernel)
+    if cnt != n or dropped:
+        raise RuntimeError(f"launch timer saw {cnt} launches of {kernel} for {n} calls ({dropped} dropped)")
+    return tot / cnt, call_ms
+
+
 def run_extensions(p, dev, rates, sm_max, flush, stream) -> dict:
     """Kernels beyond the fused step, each timed alone on realistic-shaped
     inputs (same lens, same inducing grid): windowed transmission over the
@@ -469,6 +493,18 @@ def run_ours(args):
     fwd_ms = event_time(fwd, nk, stream, flush)
     bwd_ms = event_time(bwd, nk, stream, flush)
 
+    # ---- where the step's time goes: the launch timer around each heavy
+    # kernel over nk directly launched steps
+    api.kernel_timer_enable(True)
+    direct_ms = event_time(step, nk, stream, flush)
+    api.kernel_timer_enable(False)
+    breakdown = {}
+    for kname in ("raytrace", "train_rows", "dv_rows", "raytrace_vjp"):
+        cnt, tot, _ = api.kernel_timer_read(kname)
+        breakdown[kname] = tot / cnt if cnt else None
+    breakdown["other launches and gaps"] = direct_ms - sum(v for v in breakdown.values() if v)
+    breakdown["step (direct launches, timer on)"] = direct_ms
+
     # ---- kernels in isolation (same launch configuration as inside the step)
     # Each entry: (ms, pairs, pairs per SM clock at the binding pipe, note, in the step?).
     beta = api.lens_raytrace(q)
@@ -481,24 +517,37 @@ def run_ours(args):
     dbeta = torch.from_numpy(np.random.default_rng(7).standard_normal((p.n, 2)).astype(np.float32)).to(dev)
     kern = {}
     kern["bwd_rows_kernel<grid, split> (training forward: out + row moments)"] = (
-        event_time(lambda: api.gp_kernel_matvec_train(qx, s, v, p.lengthscale, p.variance, out=out, moments=mom2,
-                                                      workspace=ws2), nk, stream, flush), ev[512], 128.0 / 4.6,
-        "pairs: 1 MUFU.EX2 + 4.6 FP32 lanes each (split exponent: 4 per pair, 0.56 per-sub-segment moment "
-        "conversion)", True)
+        *kernel_time(lambda: api.gp_kernel_matvec_train(qx, s, v, p.lengthscale, p.variance, out=out, moments=mom2,
+                                                        workspace=ws2), nk, stream, flush, "train_rows"),
+        ev[512], 1, 4.6, "pairs: 1 MUFU.EX2 + 4.6 FP32 lanes each (split exponent: 4 per pair, 0.56 "
+        "per-sub-segment moment conversion)", True)
     kern["dv_rows_kernel<split> (backward: d_v)"] = (
-        event_time(lambda: api.gp_kernel_matvec_bwd(qx, s, v, p.lengthscale, p.variance, g, want=["v"],
-                                                    moments=mom2), nk, stream, flush), ev[1024], 32.0,
-        "pairs: 1 MUFU.EX2 + 2.1 FP32 lanes each (split exponent: 2 per pair, 0.12 d_v reduce-scatter)", True)
+        *kernel_time(lambda: api.gp_kernel_matvec_bwd(qx, s, v, p.lengthscale, p.variance, g, want=["v"],
+                                                      moments=mom2), nk, stream, flush, "dv_rows"),
+        ev[1024], 1, 2.1, "pairs: 1 MUFU.EX2 + 2.1 FP32 lanes each (split exponent: 2 per pair, 0.12 d_v "
+        "reduce-scatter)", True)
     kern["matvec_kernel<grid> (inference forward, not in the step)"] = (
-        event_time(lambda: api.gp_kernel_matvec(qx, s, v, p.lengthscale, p.variance, out=out, workspace=ws3), nk,
-                   stream, flush), ev[1024], 32.0, "pairs: 1 MUFU.EX2 + 2 FP32 lanes each (split exponent)", False)
+        *kernel_time(lambda: api.gp_kernel_matvec(qx, s, v, p.lengthscale, p.variance, out=out, workspace=ws3), nk,
+                     stream, flush, "matvec"),
+        ev[1024], 1, 2.0, "pairs: 1 MUFU.EX2 + 2 FP32 lanes each (split exponent)", False)
     kern["bwd_rows_kernel<grid, split, fused d_v> (backward without moments, not in the step)"] = (
-        event_time(lambda: api.gp_kernel_matvec_bwd(qx, s, v, p.lengthscale, p.variance, g, want=["x", "v"]), nk,
-                   stream, flush), ev[1024], 128.0 / 5.7,
-        "pairs: 1 MUFU.EX2 + 5.7 FP32 lanes each (split exponent: 5 per pair, 0.56 per-sub-segment moments, "
-        "0.12 d_v reduce-scatter)", False)
-    rt_ms = event_time(lambda: api.lens_raytrace(q), nk, stream, flush)
-    vjp_ms = event_time(lambda: api.lens_raytrace_vjp(q, dbeta), nk, stream, flush)
+        *kernel_time(lambda: api.gp_kernel_matvec_bwd(qx, s, v, p.lengthscale, p.variance, g, want=["x", "v"]), nk,
+                     stream, flush, "bwd_rows"),
+        ev[1024], 1, 5.7, "pairs: 1 MUFU.EX2 + 5.7 FP32 lanes each (split exponent: 5 per pair, 0.56 "
+        "per-sub-segment moments, 0.12 d_v reduce-scatter)", False)
+    rt_ms, rt_call_ms = kernel_time(lambda: api.lens_raytrace(q), nk, stream, flush, "raytrace")
+    vjp_ms, vjp_call_ms = kernel_time(lambda: api.lens_raytrace_vjp(q, dbeta), nk, stream, flush, "raytrace_vjp")
+    # the ray-trace kernels' unit is the point-subhalo pair; counts are those
+    # of the far-side tNFW form that nearly every pair takes
+    sub_pairs = p.n * len(p.sub)
+    kern["raytrace_kernel<tNFW> (forward ray-trace; unit: point-subhalo pair)"] = (
+        rt_ms, rt_call_ms, sub_pairs, RT_MUFU, RT_LANES,
+        f"pairs: {RT_MUFU} MUFU + {RT_LANES} FP32 lanes each (far-side tNFW mass and its Kahan sum; the SPLE and "
+        "shear terms, once per point, are not counted)", True)
+    kern["raytrace_vjp_kernel<tNFW> (ray-trace backward; unit: point-subhalo pair)"] = (
+        vjp_ms, vjp_call_ms, sub_pairs, VJ_MUFU, VJ_LANES,
+        f"pairs: {VJ_MUFU} MUFU + {VJ_LANES} FP32 lanes each (far-side tNFW G and H brackets and the four subhalo "
+        "sums; the per-point SPLE and shear gradient terms are not counted)", True)
 
     # ---- end to end through the public API with host buffers
     v_host = torch.from_numpy(p.v).pin_memory()
@@ -548,14 +597,17 @@ def run_ours(args):
     ex2 = rates["ex2_per_clk"]
     fma = rates["ffma2_lanes_per_clk"]
     table = {}
-    for name, (kms, pairs, _, note, in_step) in kern.items():
-        lanes = float(note.split("+ ")[1].split(" ")[0])
-        lanes = max(lanes, fma / ex2)  # the XU pipe bounds below 4 lanes
-        per_clk = min(ex2, fma / lanes)
+    for name, (kms, call_ms, pairs, mufu, lanes, note, in_step) in kern.items():
+        # MUFU (XU pipe, measured at its EX2 rate) or the FP32 FMA pipe binds
+        per_clk = min(ex2 / mufu, fma / lanes)
         peak = per_clk * nsm * sm_max * 1e6 / 1e9
         ach = pairs / (kms * 1e-3) / 1e9
-        table[name] = {"ms": kms, "achieved": ach, "peak": peak, "frac": ach / peak, "per_sm_clk": per_clk,
-                       "pairs_evaluated": pairs, "pairs_logical": p.pairs, "note": note, "in_step": in_step}
+        table[name] = {"ms": kms, "call_ms": call_ms, "achieved": ach, "peak": peak, "frac": ach / peak,
+                       "per_sm_clk": per_clk, "pairs_evaluated": pairs,
+                       "pairs_logical": p.pairs if "raytrace" not in name else pairs, "note": note,
+                       "in_step": in_step,
+                       "timing": "kernel alone (launch-timer events around its launches); call_ms: the whole "
+                                 "entry point (row-block pre-pass and merges included)"}
     dom = max((k for k in table if table[k]["in_step"]), key=lambda k: table[k]["ms"])
     d = table[dom]
     line = {
@@ -574,11 +626,14 @@ def run_ours(args):
                           "evaluating all of them; the roofline counts evaluated pairs"},
         "roofline": {"bound": "alu", "achieved": d["achieved"], "peak": d["peak"], "unit": UNIT,
                      "frac": d["frac"], "traffic": measured_traffic(dom), "kernel": dom,
-                     "peak_basis": f"min(MUFU.EX2 {ex2:.2f}/clk/SM, FFMA2 {fma:.1f} lanes/clk/SM / lanes per pair) "
+                     "peak_basis": f"min(MUFU {ex2:.2f}/clk/SM / MUFU per pair, FFMA2 {fma:.1f} lanes/clk/SM / lanes "
+                                   f"per pair) "
                                    f"x {nsm} SMs x {sm_max:.0f} MHz (max clock; probe-measured rates); {d['note']}",
                      "frac_at_measured_clock": d["frac"] * sm_max / sm_mhz},
         "kernels": table,
-        "raytrace": {"ms": rt_ms, "vjp_ms": vjp_ms, "points": p.n, "subhalo_pairs": p.n * len(p.sub),
+        "step_breakdown_ms": breakdown,
+        "raytrace": {"ms": rt_ms, "vjp_ms": vjp_ms, "vjp_call_ms": vjp_call_ms, "points": p.n,
+                     "subhalo_pairs": p.n * len(p.sub),
                      "hbm_gbs": p.n * 8 / (rt_ms * 1e-3) / 1e9,
                      "note": "ALU/XU-bound with subhalos (8 B written per point)"},
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,

@@ -68,6 +68,33 @@ lr_status lr_probe_pipe_rates(int32_t device, double* ffma_lanes_per_clk,
  */
 lr_status lr_fault_status(int32_t* code, int32_t clear);
 
+/*
+ * Launch timer: device time of the library's pair-sweep kernels alone,
+ * without the pre-pass and merge launches of the same entry point (the
+ * denominator of a per-kernel roofline). lr_kernel_timer_enable(1) makes the
+ * current device the timed one and clears earlier records; from then on each
+ * launch of a kernel below, from any single-problem entry point on that
+ * device, records a CUDA event before and after it on its stream (not while
+ * the stream is capturing a graph, and not past 8192 launches: those count as
+ * dropped). lr_kernel_timer_enable(0) stops recording and keeps the records.
+ * lr_kernel_timer_read waits for the recorded events of `kernel` and returns
+ * the launch count and the summed milliseconds (and, if `dropped` is not NULL,
+ * the number of launches that were not recorded). Host-thread safe; timing is
+ * for profiling runs, since each record adds two event records to the stream.
+ */
+enum {
+  LR_KT_MATVEC = 0,       /* gp_kernel_matvec pair sweep (matvec_kernel)                */
+  LR_KT_TRAIN_ROWS = 1,   /* gp_kernel_matvec_train pair sweep (out + row moments)      */
+  LR_KT_BWD_ROWS = 2,     /* gp_kernel_matvec_bwd row sweep without moments             */
+  LR_KT_DV_ROWS = 3,      /* gp_kernel_matvec_bwd d_v sweep (grid sources)              */
+  LR_KT_RAYTRACE = 4,     /* lens_raytrace                                              */
+  LR_KT_RAYTRACE_VJP = 5, /* lens_raytrace_vjp                                          */
+  LR_KT_WINDOWED = 6,     /* gp_windowed_matvec pair sweep                              */
+  LR_KT_COUNT = 7
+};
+lr_status lr_kernel_timer_enable(int32_t enable);
+lr_status lr_kernel_timer_read(int32_t kernel, int64_t* launches, double* total_ms, int64_t* dropped);
+
 /* ------------------------------------------------------------------------ */
 /* Geometry and lens parameters                                               */
 

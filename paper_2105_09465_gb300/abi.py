@@ -85,6 +85,8 @@ SIGNATURES = {
     "lr_status_name": (ctypes.c_char_p, [ctypes.c_int32]),
     "lr_probe_pipe_rates": (ctypes.c_int32, [ctypes.c_int32, _P, _P, _P, _P]),
     "lr_fault_status": (ctypes.c_int32, [_P, ctypes.c_int32]),
+    "lr_kernel_timer_enable": (ctypes.c_int32, [ctypes.c_int32]),
+    "lr_kernel_timer_read": (ctypes.c_int32, [ctypes.c_int32, _P, _P, _P]),
     "lens_raytrace": (ctypes.c_int32, [ctypes.POINTER(lr_points), _P, _P, _P]),
     "lens_jacobian": (ctypes.c_int32, [ctypes.POINTER(lr_points), _P, _P, _P]),
     "gp_kernel_matvec": (ctypes.c_int32, [ctypes.POINTER(lr_points), ctypes.POINTER(lr_points), _P, ctypes.c_int32,

@@ -504,6 +504,27 @@ def probe_pipe_rates(device: int = 0) -> dict:
     return {"ffma_lanes_per_clk": a.value, "ffma2_lanes_per_clk": b.value, "ex2_per_clk": c.value, "sm_count": n.value}
 
 
+# Kernel ids of the launch timer (LR_KT_* in the C header).
+TIMED_KERNELS = {"matvec": 0, "train_rows": 1, "bwd_rows": 2, "dv_rows": 3, "raytrace": 4, "raytrace_vjp": 5,
+                 "windowed": 6}
+
+
+def kernel_timer_enable(enable: bool = True) -> None:
+    """Start (clearing earlier records) or stop the library's launch timer on
+    the current device: CUDA events around each pair-sweep launch."""
+    abi.check(abi.load().lr_kernel_timer_enable(int(enable)), "lr_kernel_timer_enable")
+
+
+def kernel_timer_read(kernel: str) -> tuple[int, float, int]:
+    """(launches, summed device milliseconds, launches not recorded) of one
+    timed kernel since the timer was last enabled; waits for its events."""
+    lib = abi.load()
+    n, ms, dropped = ctypes.c_int64(), ctypes.c_double(), ctypes.c_int64()
+    abi.check(lib.lr_kernel_timer_read(TIMED_KERNELS[kernel], ctypes.byref(n), ctypes.byref(ms), ctypes.byref(dropped)),
+              "lr_kernel_timer_read")
+    return int(n.value), float(ms.value), int(dropped.value)
+
+
 def fault_status(clear: bool = False) -> int:
     lib = abi.load()
     code = ctypes.c_int32()

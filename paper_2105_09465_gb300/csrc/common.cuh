@@ -17,6 +17,12 @@ lr_status cuda_status(cudaError_t e, const char* what);
 // Device address of the library's fault word on the current device.
 int* fault_ptr();
 
+// Launch timer (lr_kernel_timer_enable): events on stream s before and after
+// one launch of kernel id (an LR_KT_* value). No-ops while the timer is off or
+// s is capturing a graph.
+void ktimer_begin(int id, cudaStream_t s);
+void ktimer_end(int id, cudaStream_t s);
+
 // Streams cross the ABI as lr_stream (an opaque CUstream_st*).
 inline cudaStream_t as_cuda(lr_stream s) { return reinterpret_cast<cudaStream_t>(s); }
 

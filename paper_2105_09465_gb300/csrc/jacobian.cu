@@ -58,7 +58,8 @@ __global__ void __launch_bounds__(kJThreads) lens_jacobian_kernel(const __grid_c
           J[3] += fmaf(q, dy * dy, m);
         } else {
           float Gt, Ht;
-          tnfw_GH(h, R2, Gt, Ht);
+          float ix2_unused;
+          tnfw_GH(h, R2, Gt, Ht, ix2_unused);
           const float a = h.A * Gt, q = h.A * (Ht - 2.0f * Gt) * iR2;
           J[0] += fmaf(q, dx * dx, a);
           J[1] += q * dx * dy;

@@ -103,6 +103,14 @@ __device__ __forceinline__ float flog(float x) {
   asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
   return r * 0.69314718055994531f;
 }
+// ln(x) / 2 = log2(x) ln(2) / 2
+constexpr float kHalfLn2 = 0.34657359027997265f;
+__device__ __forceinline__ float flg2(float x) {
+  float r;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float flog_half(float x) { return __fmul_rn(flg2(x), kHalfLn2); }
 
 // arctan(s) / s for s > 0, given is = 1/s. With t = min(s, 1/s) and u = t^2,
 // arctan(t) = t P(u), where P is a degree-8 polynomial fitted for this
@@ -110,20 +118,39 @@ __device__ __forceinline__ float flog(float x) {
 // monomial basis, iteratively reweighted toward equal relative ripple:
 // relative error 1.5e-8 in exact arithmetic, ~2e-7 after FP32 rounding);
 // arctan(s) = pi/2 - arctan(1/s) for s > 1.
+// Every operation is an explicitly rounded intrinsic (never contracted), so
+// atan_over2 below, the same steps on packed f32x2 pairs, gives the same bits.
+__device__ constexpr float kAtanP[9] = {2.849667566e-03f, -1.606774889e-02f, 4.269010574e-02f, -7.504177094e-02f,
+                             1.064087972e-01f, -1.420363039e-01f, 1.999261826e-01f,  -3.333307207e-01f,
+                             1.0f};
+constexpr float kHalfPi = 1.57079632679f;
+
 __device__ __forceinline__ float atan_over(float s, float is) {
   const float t = fminf(s, is);
-  const float u = t * t;
-  float p = 2.849667566e-03f;
-  p = fmaf(p, u, -1.606774889e-02f);
-  p = fmaf(p, u, 4.269010574e-02f);
-  p = fmaf(p, u, -7.504177094e-02f);
-  p = fmaf(p, u, 1.064087972e-01f);
-  p = fmaf(p, u, -1.420363039e-01f);
-  p = fmaf(p, u, 1.999261826e-01f);
-  p = fmaf(p, u, -3.333307207e-01f);
-  p = fmaf(p, u, 1.0f);
-  const float at = __fmul_rn(t, p);  // not contracted: the same rounding in every caller
-  return (s <= 1.0f ? at : 1.57079632679f - at) * is;
+  const float u = __fmul_rn(t, t);
+  float p = kAtanP[0];
+#pragma unroll
+  for (int k = 1; k < 9; ++k) p = __fmaf_rn(p, u, kAtanP[k]);
+  const float at = __fmul_rn(t, p);
+  return __fmul_rn(s <= 1.0f ? at : __fsub_rn(kHalfPi, at), is);
+}
+
+// ---- packed f32x2 forms: each lane rounds exactly as the scalar
+// intrinsic it mirrors (a - b is b * (-1) + a with one rounding)
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, f2(-1.0f), a); }
+__device__ __forceinline__ float2 frsqrt2(float2 x) { return make_float2(frsqrt(x.x), frsqrt(x.y)); }
+__device__ __forceinline__ float2 frcp2(float2 x) { return make_float2(frcp(x.x), frcp(x.y)); }
+
+__device__ __forceinline__ float2 atan_over2(float2 s, float2 is) {
+  const float2 t = make_float2(fminf(s.x, is.x), fminf(s.y, is.y));
+  const float2 u = __fmul2_rn(t, t);
+  float2 p = f2(kAtanP[0]);
+#pragma unroll
+  for (int k = 1; k < 9; ++k) p = __ffma2_rn(p, u, f2(kAtanP[k]));
+  const float2 at = __fmul2_rn(t, p);
+  const float2 alt = sub2(f2(kHalfPi), at);
+  return __fmul2_rn(make_float2(s.x <= 1.0f ? at.x : alt.x, s.y <= 1.0f ? at.y : alt.y), is);
 }
 
 // F(x) of the NFW family as a function of x^2 (x = R / theta_s):
@@ -156,8 +183,12 @@ __device__ __forceinline__ float nfw_F(float x2, float xx, float& s) {
 //   B/x^2 = -pi/(tau+st) + 2F + (tau^2-1) [F/(1+s) + log1p(dl)/x^2 + L/(tau (tau+st))],
 //   dl = -x^2 [tau/(1+s) + 1/(tau+st)]/(tau+st),  st = sqrt(tau^2+x^2),
 // otherwise B = (tau^2-1+2x^2) F + C + st (-pi + (tau^2-1)/tau L).
+__device__ __forceinline__ float tnfw_m_far(const SubRec& h, float x2);
+__device__ __forceinline__ bool tnfw_is_far(float x2);
+
 __device__ __forceinline__ float tnfw_m(const SubRec& h, float R2) {
-  const float x2 = R2 * h.its2;
+  const float x2 = __fmul_rn(R2, h.its2);
+  if (tnfw_is_far(x2)) return tnfw_m_far(h, x2);
   if (!(x2 > 1e-20f)) return 0.f;
   const float xx = fsqrt_pos(x2);
   float s;
@@ -190,22 +221,110 @@ __device__ __forceinline__ float pointmass_m(const SubRec& h, float R2) {
 
 // The far side of the tNFW profile, x^2 - 1 >= 0.05 (arccos form of F,
 // direct bracket), as straight-line code so that several pairs can be
-// interleaved; there it evaluates exactly the operations of tnfw_m /
-// tnfw_GH, so the results are bitwise the same. Other x^2 give a finite
-// value that the caller replaces.
-__device__ __forceinline__ bool tnfw_is_far(float x2) { return x2 - 1.0f >= 0.05f; }
+// interleaved. tnfw_m and tnfw_GH return exactly these values for far x^2
+// (they call the same code), so a pair gives the same bits on either path.
+// Other x^2 give a finite value that the caller replaces.
+//
+// Four MUFU operations per pair: one reciprocal square root gives both
+// s = sqrt(eps) and 1/s (and 1/eps = (1/s)^2), one gives st = sqrt(tau^2 + x^2)
+// and 1/st, one reciprocal of x^2 (tau + st) gives both 1/(tau + st) and
+// 1/x^2, and ln(x/(tau + st)) = ln(x^2/(tau + st)^2)/2 needs no sqrt(x^2).
+// Valid while x^2 (tau + st) stays finite in FP32 (x^2 < ~1e24).
+__device__ __forceinline__ bool tnfw_is_far(float x2) { return __fadd_rn(x2, -1.0f) >= 0.05f; }
+
+// Every step below is an explicitly rounded intrinsic, and the *2 forms
+// repeat the same steps on packed f32x2 pairs, so a pair gives the same bits
+// whether it is evaluated alone or packed with another. x2 must itself come
+// from __fmul_rn (not a contractible product).
+struct TnfwFar {
+  float F, is, st, ist, ix2, L;
+};
+
+__device__ __forceinline__ TnfwFar tnfw_far_terms(const SubRec& h, float x2) {
+  TnfwFar t;
+  const float eps = fmaxf(__fadd_rn(x2, -1.0f), 0.05f);
+  t.is = frsqrt(eps);
+  const float s = __fmul_rn(eps, t.is);
+  t.F = atan_over(s, t.is);
+  const float u = __fadd_rn(h.tau2, x2);
+  t.ist = frsqrt(u);
+  t.st = __fmul_rn(u, t.ist);
+  const float tp = __fadd_rn(h.tau, t.st);
+  const float r = frcp(__fmul_rn(x2, tp));
+  const float itp = __fmul_rn(x2, r);
+  t.ix2 = __fmul_rn(tp, r);
+  t.L = flog_half(__fmul_rn(__fmul_rn(x2, itp), itp));
+  return t;
+}
 
 __device__ __forceinline__ float tnfw_m_far(const SubRec& h, float x2) {
-  const float xx = fsqrt_pos(x2);
-  const float eps = fmaxf(x2 - 1.0f, 0.05f);
-  const float s = fsqrt_pos(eps);
-  const float F = atan_over(s, frcp(s));
-  const float st = fsqrt_pos(h.tau2 + x2);
-  const float itp = frcp(h.tau + st);
-  const float L = flog(xx * itp);
-  const float t2m1 = h.tau2 - 1.0f;
-  const float B = fmaf(st, fmaf(h.t2m1_t, L, -kPi), fmaf(fmaf(2.0f, x2, t2m1), F, h.C));
-  return h.A * (B * frcp(x2));
+  const TnfwFar t = tnfw_far_terms(h, x2);
+  const float t2m1 = __fadd_rn(h.tau2, -1.0f);
+  const float B = __fmaf_rn(t.st, __fmaf_rn(h.t2m1_t, t.L, -kPi),
+                            __fmaf_rn(__fmaf_rn(2.0f, x2, t2m1), t.F, h.C));
+  return __fmul_rn(h.A, __fmul_rn(B, t.ix2));
+}
+
+// Two records (or one record twice) with every field as a packed pair.
+struct SubRec2 {
+  float2 xh, yh, its2, A, tau, tau2, t2m1_t, C;
+};
+
+__device__ __forceinline__ SubRec2 sub_pair(const SubRec& a, const SubRec& b) {
+  SubRec2 r;
+  r.xh = make_float2(a.xh, b.xh);
+  r.yh = make_float2(a.yh, b.yh);
+  r.its2 = make_float2(a.its2, b.its2);
+  r.A = make_float2(a.A, b.A);
+  r.tau = make_float2(a.tau, b.tau);
+  r.tau2 = make_float2(a.tau2, b.tau2);
+  r.t2m1_t = make_float2(a.t2m1_t, b.t2m1_t);
+  r.C = make_float2(a.C, b.C);
+  return r;
+}
+
+__device__ __forceinline__ SubRec sub_lane(const SubRec2& r, int k) {
+  SubRec h;
+  h.xh = k ? r.xh.y : r.xh.x;
+  h.yh = k ? r.yh.y : r.yh.x;
+  h.its2 = k ? r.its2.y : r.its2.x;
+  h.A = k ? r.A.y : r.A.x;
+  h.tau = k ? r.tau.y : r.tau.x;
+  h.tau2 = k ? r.tau2.y : r.tau2.x;
+  h.t2m1_t = k ? r.t2m1_t.y : r.t2m1_t.x;
+  h.C = k ? r.C.y : r.C.x;
+  return h;
+}
+
+struct TnfwFar2 {
+  float2 F, is, st, ist, ix2, L;
+};
+
+__device__ __forceinline__ TnfwFar2 tnfw_far_terms2(const SubRec2& h, float2 x2) {
+  TnfwFar2 t;
+  const float2 e = __fadd2_rn(x2, f2(-1.0f));
+  const float2 eps = make_float2(fmaxf(e.x, 0.05f), fmaxf(e.y, 0.05f));
+  t.is = frsqrt2(eps);
+  const float2 s = __fmul2_rn(eps, t.is);
+  t.F = atan_over2(s, t.is);
+  const float2 u = __fadd2_rn(h.tau2, x2);
+  t.ist = frsqrt2(u);
+  t.st = __fmul2_rn(u, t.ist);
+  const float2 tp = __fadd2_rn(h.tau, t.st);
+  const float2 r = frcp2(__fmul2_rn(x2, tp));
+  const float2 itp = __fmul2_rn(x2, r);
+  t.ix2 = __fmul2_rn(tp, r);
+  const float2 a = __fmul2_rn(__fmul2_rn(x2, itp), itp);
+  t.L = __fmul2_rn(make_float2(flg2(a.x), flg2(a.y)), f2(kHalfLn2));
+  return t;
+}
+
+__device__ __forceinline__ float2 tnfw_m_far2(const SubRec2& h, float2 x2) {
+  const TnfwFar2 t = tnfw_far_terms2(h, x2);
+  const float2 t2m1 = __fadd2_rn(h.tau2, f2(-1.0f));
+  const float2 B = __ffma2_rn(t.st, __ffma2_rn(h.t2m1_t, t.L, f2(-kPi)),
+                              __ffma2_rn(__ffma2_rn(f2(2.0f), x2, t2m1), t.F, h.C));
+  return __fmul2_rn(h.A, __fmul2_rn(B, t.ix2));
 }
 
 // Converts a raw subhalo record (5 floats) into the prepared form.
@@ -239,13 +358,22 @@ __device__ __forceinline__ SubRec prep_sub(const float* r, int profile) {
 // eps = x^2 - 1, (1-F)/eps by its series 1/3 - eps/5 + eps^2/7 - ... near x = 1.
 // Then dalpha/dxi = A [Gt I + (Ht - 2Gt) n n^T] and
 // dalpha/dtheta_s = -A (Ht - 2Gt) d / theta_s.
-__device__ __forceinline__ void tnfw_GH(const SubRec& h, float R2, float& Gt, float& Ht) {
-  const float x2 = R2 * h.its2;
+__device__ __forceinline__ void tnfw_GH_far(const SubRec& h, float x2, float& Gt, float& Ht, float& ix2);
+
+// Also returns ix2 = 1/x^2 (0 at x = 0).
+__device__ __forceinline__ void tnfw_GH(const SubRec& h, float R2, float& Gt, float& Ht, float& ix2) {
+  const float x2 = __fmul_rn(R2, h.its2);
+  if (tnfw_is_far(x2)) {
+    tnfw_GH_far(h, x2, Gt, Ht, ix2);
+    return;
+  }
   if (!(x2 > 1e-20f)) {
     Gt = 0.f;
     Ht = 0.f;
+    ix2 = 0.f;
     return;
   }
+  ix2 = frcp(x2);
   const float xx = fsqrt_pos(x2);
   float s;
   const float F = nfw_F(x2, xx, s);
@@ -263,7 +391,7 @@ __device__ __forceinline__ void tnfw_GH(const SubRec& h, float R2, float& Gt, fl
               fmaf(2.0f, F, __fmul_rn(-kPi, itp)));
   } else {
     const float B = fmaf(st, fmaf(h.t2m1_t, L, -kPi), fmaf(fmaf(2.0f, x2, t2m1), F, h.C));
-    Gt = B * frcp(x2);
+    Gt = B * ix2;
   }
   const float eps = x2 - 1.0f;
   float omf;  // (1 - F) / eps
@@ -282,21 +410,27 @@ __device__ __forceinline__ void tnfw_GH(const SubRec& h, float R2, float& Gt, fl
   Ht = fmaf(ist, fmaf(h.t2m1_t, L, -kPi), fmaf(2.0f, F, __fmul_rn(h.tau2 + 1.0f, omf)));
 }
 
-// tnfw_GH on the far side (see tnfw_m_far).
-__device__ __forceinline__ void tnfw_GH_far(const SubRec& h, float x2, float& Gt, float& Ht) {
-  const float xx = fsqrt_pos(x2);
-  const float eps = fmaxf(x2 - 1.0f, 0.05f);
-  const float s = fsqrt_pos(eps);
-  const float F = atan_over(s, frcp(s));
-  const float st = fsqrt_pos(h.tau2 + x2);
-  const float itp = frcp(h.tau + st);
-  const float L = flog(xx * itp);
-  const float t2m1 = h.tau2 - 1.0f;
-  const float B = fmaf(st, fmaf(h.t2m1_t, L, -kPi), fmaf(fmaf(2.0f, x2, t2m1), F, h.C));
-  Gt = B * frcp(x2);
-  const float omf = (1.0f - F) * frcp(eps);
-  const float ist = frcp(st);
-  Ht = fmaf(ist, fmaf(h.t2m1_t, L, -kPi), fmaf(2.0f, F, __fmul_rn(h.tau2 + 1.0f, omf)));
+// tnfw_GH on the far side (see tnfw_m_far), with 1/eps = (1/s)^2.
+__device__ __forceinline__ void tnfw_GH_far(const SubRec& h, float x2, float& Gt, float& Ht, float& ix2) {
+  const TnfwFar t = tnfw_far_terms(h, x2);
+  const float t2m1 = __fadd_rn(h.tau2, -1.0f);
+  const float lp = __fmaf_rn(h.t2m1_t, t.L, -kPi);
+  const float B = __fmaf_rn(t.st, lp, __fmaf_rn(__fmaf_rn(2.0f, x2, t2m1), t.F, h.C));
+  Gt = __fmul_rn(B, t.ix2);
+  ix2 = t.ix2;
+  const float omf = __fmul_rn(__fsub_rn(1.0f, t.F), __fmul_rn(t.is, t.is));
+  Ht = __fmaf_rn(t.ist, lp, __fmaf_rn(2.0f, t.F, __fmul_rn(__fadd_rn(h.tau2, 1.0f), omf)));
+}
+
+__device__ __forceinline__ void tnfw_GH_far2(const SubRec2& h, float2 x2, float2& Gt, float2& Ht, float2& ix2) {
+  const TnfwFar2 t = tnfw_far_terms2(h, x2);
+  const float2 t2m1 = __fadd2_rn(h.tau2, f2(-1.0f));
+  const float2 lp = __ffma2_rn(h.t2m1_t, t.L, f2(-kPi));
+  const float2 B = __ffma2_rn(t.st, lp, __ffma2_rn(__ffma2_rn(f2(2.0f), x2, t2m1), t.F, h.C));
+  Gt = __fmul2_rn(B, t.ix2);
+  ix2 = t.ix2;
+  const float2 omf = __fmul2_rn(sub2(f2(1.0f), t.F), __fmul2_rn(t.is, t.is));
+  Ht = __ffma2_rn(t.ist, lp, __ffma2_rn(f2(2.0f), t.F, __fmul2_rn(__fadd2_rn(h.tau2, f2(1.0f)), omf)));
 }
 
 // Per-lens constants for the SPLE gradient (host-prepared).

@@ -568,11 +568,13 @@ extern "C" lr_status gp_kernel_matvec(const lr_points* query, const lr_points* s
     A.info = R.info;
   }
   const unsigned grid = (unsigned)((int64_t)P.row_blocks * P.chunks);
+  ktimer_begin(LR_KT_MATVEC, s);
   if (S.xy)
     matvec_kernel<false><<<grid, kMvThreads, 0, s>>>(A);
   else
     matvec_kernel<true><<<grid, kMvThreads, 0, s>>>(A);
   LR_CHECK_CUDA(cudaGetLastError());
+  ktimer_end(LR_KT_MATVEC, s);
   if (P.chunks > 1) {
     merge_chunks_kernel<<<(unsigned)((P.n + 255) / 256), 256, 0, s>>>(A.partial, P.chunks, P.n, variance, out);
     LR_CHECK_CUDA(cudaGetLastError());

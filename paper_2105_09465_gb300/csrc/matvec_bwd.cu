@@ -554,11 +554,13 @@ __global__ void moments_merge_batched_kernel(const __grid_constant__ Batch<MomMe
 }
 
 // Per-row merge of chunk partials, the per-row gradients, and per-block FP64
-// partials of the two scalar gradients.
+// partials of the two scalar gradients. The per-row products and the warp
+// sums (a 32-term pairwise tree) stay in FP32; the warps' sums are added in
+// FP64 (FP64 arithmetic runs at a small fraction of the FP32 rate).
 __device__ __forceinline__ void bwd_merge_body(const MergeArgs& M, int64_t blk) {
-  __shared__ double red[2][kMergeThreads / 32];
+  __shared__ float red[2][kMergeThreads / 32];
   const int64_t i = blk * kMergeThreads + threadIdx.x;
-  double sl = 0.0, sv = 0.0;
+  float sl = 0.f, sv = 0.f;
   if (i < M.n) {
     float s[7], c[7];
     for (int k = 0; k < M.K; ++k) {
@@ -577,8 +579,8 @@ __device__ __forceinline__ void bwd_merge_body(const MergeArgs& M, int64_t blk) 
     }
     // sums were taken over (x_i - y_j); the gradient wants (y_j - x_i)
     if (M.d_x) M.d_x[i] = make_float2(-M.var * M.inv_l2 * ddx, -M.var * M.inv_l2 * ddy);
-    sl = (double)gi * (double)s[3] * (double)M.dl_scale;
-    sv = (double)gi * (double)s[0];
+    sl = __fmul_rn(__fmul_rn(gi, s[3]), M.dl_scale);
+    sv = __fmul_rn(gi, s[0]);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -593,7 +595,7 @@ __device__ __forceinline__ void bwd_merge_body(const MergeArgs& M, int64_t blk) 
   __syncthreads();
   if (threadIdx.x < 2) {
     double t = 0.0;
-    for (int k = 0; k < kMergeThreads / 32; ++k) t += red[threadIdx.x][k];
+    for (int k = 0; k < kMergeThreads / 32; ++k) t += (double)red[threadIdx.x][k];
     M.scal_part[blk * 2 + threadIdx.x] = t;
   }
 }
@@ -649,30 +651,48 @@ __global__ void __launch_bounds__(kMergeThreads) scalar_batched_kernel(const __g
   scalar_final_body(P.part, P.nblk, P.d_len, P.d_var);
 }
 
-__device__ __forceinline__ void dv_merge_body(const DvMergeP& P, int64_t j) {
-  if (j >= P.m) return;
-  // with row-block info, a row block wrote source j only when j's tile is in
-  // its active range; elsewhere its sum is exactly 0 and is not read
-  int t = 0;
-  if (P.info) {
-    const int64_t r = j / P.W;
-    t = (int)(r * P.segs + (j - r * P.W) / kBwTile);
-  }
+// d_v merge: a CTA of kDvMergeCols x kDvMergeGroups threads takes
+// kDvMergeCols consecutive sources; thread group y sums the row blocks
+// y, y + kDvMergeGroups, ... (Kahan), and the groups' sums are added in
+// group order, so the result is deterministic. With row-block info, a row
+// block wrote source j only when j's tile is in its active range; elsewhere
+// its sum is exactly 0 and is not read.
+constexpr int kDvMergeCols = 32, kDvMergeGroups = 8;
+
+__device__ __forceinline__ void dv_merge_body(const DvMergeP& P, int64_t blk) {
+  __shared__ float part[kDvMergeGroups][kDvMergeCols];
+  const int x = threadIdx.x % kDvMergeCols, y = threadIdx.x / kDvMergeCols;
+  const int64_t j = blk * kDvMergeCols + x;
   float s = 0.f, c = 0.f;
-  for (int rb = 0; rb < P.row_blocks; ++rb) {
-    if (P.info && !(P.info[rb].t_lo <= t && t < P.info[rb].t_hi)) continue;
-    kahan(s, c, P.dv_part[(int64_t)rb * P.m + j]);
+  if (j < P.m) {
+    int t = 0;
+    if (P.info) {
+      const int64_t r = j / P.W;
+      t = (int)(r * P.segs + (j - r * P.W) / kBwTile);
+    }
+    for (int rb = y; rb < P.row_blocks; rb += kDvMergeGroups) {
+      if (P.info && !(P.info[rb].t_lo <= t && t < P.info[rb].t_hi)) continue;
+      kahan(s, c, P.dv_part[(int64_t)rb * P.m + j]);
+    }
   }
-  P.d_v[j] = P.var * (s - c);
+  part[y][x] = s - c;
+  __syncthreads();
+  if (y == 0 && j < P.m) {
+    float t = 0.f, cc = 0.f;
+#pragma unroll
+    for (int k = 0; k < kDvMergeGroups; ++k) kahan(t, cc, part[k][x]);
+    P.d_v[j] = P.var * (t - cc);
+  }
 }
 
-__global__ void dv_merge_kernel(const __grid_constant__ DvMergeP P) {
-  dv_merge_body(P, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+__global__ void __launch_bounds__(kDvMergeCols * kDvMergeGroups) dv_merge_kernel(const __grid_constant__ DvMergeP P) {
+  dv_merge_body(P, blockIdx.x);
 }
 
-__global__ void dv_merge_batched_kernel(const __grid_constant__ Batch<DvMergeP> B) {
+__global__ void __launch_bounds__(kDvMergeCols * kDvMergeGroups)
+    dv_merge_batched_kernel(const __grid_constant__ Batch<DvMergeP> B) {
   const int k = batch_find(B, blockIdx.x);
-  dv_merge_body(B.p[k], (int64_t)(blockIdx.x - B.start[k]) * blockDim.x + threadIdx.x);
+  dv_merge_body(B.p[k], blockIdx.x - B.start[k]);
 }
 
 lr_status launch_dv_merge_batched(const DvMergeP* p, int count, cudaStream_t s) {
@@ -683,11 +703,11 @@ lr_status launch_dv_merge_batched(const DvMergeP* p, int count, cudaStream_t s) 
     for (int k = 0; k < B.count; ++k) {
       B.p[k] = p[b0 + k];
       B.start[k] = (int32_t)tot;
-      tot += (p[b0 + k].m + 255) / 256;
+      tot += (p[b0 + k].m + kDvMergeCols - 1) / kDvMergeCols;
     }
     B.start[B.count] = (int32_t)tot;
     if (tot == 0) continue;
-    dv_merge_batched_kernel<<<(unsigned)tot, 256, 0, s>>>(B);
+    dv_merge_batched_kernel<<<(unsigned)tot, kDvMergeCols * kDvMergeGroups, 0, s>>>(B);
     LR_CHECK_CUDA(cudaGetLastError());
   }
   return LR_OK;
@@ -977,6 +997,7 @@ static lr_status launch_rows(const float2* x, int64_t n, const lr_grid* qgrid, c
     if (st != LR_OK) return st;
     if (RI.info && (st = launch_row_info(RI, s)) != LR_OK) return st;
     const unsigned grid = (unsigned)(row_block_count(A.map, n, A.rows_per_cta) * A.chunks);
+    ktimer_begin(LR_KT_BWD_ROWS, s);
     if (ys == nullptr && A.dv_part && A.split)
       bwd_rows_kernel<true, false, true, true><<<grid, kBwThreads, 0, s>>>(A);
     else if (ys == nullptr && A.dv_part)
@@ -988,6 +1009,7 @@ static lr_status launch_rows(const float2* x, int64_t n, const lr_grid* qgrid, c
     else
       bwd_rows_kernel<false, false, false><<<grid, kBwThreads, 0, s>>>(A);
     LR_CHECK_CUDA(cudaGetLastError());
+    ktimer_end(LR_KT_BWD_ROWS, s);
     bwd_merge_kernel<<<(unsigned)S.nblk, kMergeThreads, 0, s>>>(M);
     LR_CHECK_CUDA(cudaGetLastError());
     if (d_len || d_var) {
@@ -995,7 +1017,7 @@ static lr_status launch_rows(const float2* x, int64_t n, const lr_grid* qgrid, c
       LR_CHECK_CUDA(cudaGetLastError());
     }
     if (A.dv_part) {
-      dv_merge_kernel<<<(unsigned)((m + 255) / 256), 256, 0, s>>>(D);
+      dv_merge_kernel<<<(unsigned)((m + kDvMergeCols - 1) / kDvMergeCols), kDvMergeCols * kDvMergeGroups, 0, s>>>(D);
       LR_CHECK_CUDA(cudaGetLastError());
     }
     return LR_OK;
@@ -1023,8 +1045,10 @@ static lr_status launch_rows(const float2* x, int64_t n, const lr_grid* qgrid, c
   A.grow = nullptr;
   A.dv_part = nullptr;
   const unsigned grid = (unsigned)((int64_t)R.row_blocks * R.chunks);
+  ktimer_begin(LR_KT_BWD_ROWS, s);
   bwd_rows_kernel<false, true, false><<<grid, kBwThreads, 0, s>>>(A);
   LR_CHECK_CUDA(cudaGetLastError());
+  ktimer_end(LR_KT_BWD_ROWS, s);
   MergeArgs M{};
   M.partial = A.partial;
   M.chunks = R.chunks;
@@ -1150,12 +1174,14 @@ static lr_status launch_dv(const float2* x, int64_t n, const lr_grid* qgrid, con
   if (st != LR_OK) return st;
   if ((st = launch_row_info(RI, s)) != LR_OK) return st;
   const unsigned grid = (unsigned)(row_block_count(A.map, n, kDvRows) * A.chunks);
+  ktimer_begin(LR_KT_DV_ROWS, s);
   if (A.split)
     dv_rows_kernel<true><<<grid, kBwThreads, 0, s>>>(A);
   else
     dv_rows_kernel<false><<<grid, kBwThreads, 0, s>>>(A);
   LR_CHECK_CUDA(cudaGetLastError());
-  dv_merge_kernel<<<(unsigned)((D.m + 255) / 256), 256, 0, s>>>(D);
+  ktimer_end(LR_KT_DV_ROWS, s);
+  dv_merge_kernel<<<(unsigned)((D.m + kDvMergeCols - 1) / kDvMergeCols), kDvMergeCols * kDvMergeGroups, 0, s>>>(D);
   LR_CHECK_CUDA(cudaGetLastError());
   return LR_OK;
 }
@@ -1485,6 +1511,7 @@ extern "C" lr_status gp_kernel_matvec_train(const lr_points* query, const lr_poi
   if (st != LR_OK) return st;
   if (RI.info && (st = launch_row_info(RI, s)) != LR_OK) return st;
   const unsigned grid = (unsigned)(row_block_count(A.map, T.n, A.rows_per_cta) * A.chunks);
+  ktimer_begin(LR_KT_TRAIN_ROWS, s);
   if (T.s_grid && A.split)
     bwd_rows_kernel<true, false, false, true><<<grid, kBwThreads, 0, s>>>(A);
   else if (T.s_grid)
@@ -1492,6 +1519,7 @@ extern "C" lr_status gp_kernel_matvec_train(const lr_points* query, const lr_poi
   else
     bwd_rows_kernel<false, false, false><<<grid, kBwThreads, 0, s>>>(A);
   LR_CHECK_CUDA(cudaGetLastError());
+  ktimer_end(LR_KT_TRAIN_ROWS, s);
   moments_merge_kernel<<<(unsigned)((T.n + 255) / 256), 256, 0, s>>>(MM);
   LR_CHECK_CUDA(cudaGetLastError());
   return LR_OK;

@@ -177,6 +177,7 @@ struct VjpP {
   int64_t n;
   const float* sub;
   int32_t n_sub, profile;
+  int32_t phases;  // slots per subhalo (see vjp_phases)
   const float2* dbeta;
   double* lens_part;
   float* sub_part;
@@ -185,7 +186,7 @@ struct VjpP {
 struct VjpFinalP {
   const double* lens_part;
   const float* sub_part;
-  int32_t nblk, n_sub;
+  int32_t nblk, n_sub, phases;
   double* d_lens;
   double* d_sub;
 };

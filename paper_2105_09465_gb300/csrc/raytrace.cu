@@ -22,56 +22,64 @@ __global__ void grid_points_kernel(GridDev g, int64_t n, float2* out) {
   if (i < n) out[i] = grid_point(g, i);
 }
 
-__device__ __forceinline__ void kahan2(float m, float dx, float dy, float& sx, float& cx, float& sy, float& cy) {
-  const float yx = fmaf(m, dx, -cx);
-  const float tx = sx + yx;
-  cx = (tx - sx) - yx;
-  sx = tx;
-  const float yy = fmaf(m, dy, -cy);
-  const float ty = sy + yy;
-  cy = (ty - sy) - yy;
-  sy = ty;
+constexpr int kRtFold = 8;  // subhalos summed plainly before a Kahan fold
+
+__device__ __forceinline__ void kahan(float& s, float& c, float x) {
+  const float y = __fsub_rn(x, c);
+  const float t = __fadd_rn(s, y);
+  c = __fsub_rn(__fsub_rn(t, s), y);
+  s = t;
 }
 
+// Deflection of the staged subhalos at (x, y), added to the Kahan sums
+// (sx, cx), (sy, cy). Blocks of kRtFold subhalos are summed plainly in two
+// packed lanes (even and odd subhalos) and folded into the Kahan sums; the
+// fold order is fixed, so every kernel that calls this gets the same bits.
 template <int PROFILE>
-__device__ __forceinline__ void add_subs(const SubRec* recs, int cnt, float x, float y, float& sx, float& cx,
+__device__ __forceinline__ void add_subs(const SubRec2* recs2, int cnt, float x, float y, float& sx, float& cx,
                                          float& sy, float& cy) {
-  int t = 0;
-  if (PROFILE == LR_PROFILE_TNFW) {
-    // two subhalos per step on the straight-line far-side form (the rare
-    // near pairs are redone by the general form); same sums, same order
-    for (; t + 1 < cnt; t += 2) {
-      const SubRec ha = recs[t], hb = recs[t + 1];
-      const float dxa = x - ha.xh, dya = y - ha.yh, dxb = x - hb.xh, dyb = y - hb.yh;
-      const float R2a = fmaf(dxa, dxa, dya * dya), R2b = fmaf(dxb, dxb, dyb * dyb);
-      const float x2a = R2a * ha.its2, x2b = R2b * hb.its2;
-      float ma = tnfw_m_far(ha, x2a), mb = tnfw_m_far(hb, x2b);
-      if (!tnfw_is_far(x2a)) ma = tnfw_m(ha, R2a);
-      if (!tnfw_is_far(x2b)) mb = tnfw_m(hb, R2b);
-      kahan2(ma, dxa, dya, sx, cx, sy, cy);
-      kahan2(mb, dxb, dyb, sx, cx, sy, cy);
+  const float2 X = f2(x), Y = f2(y);
+  for (int t0 = 0; t0 < cnt; t0 += kRtFold) {
+    const int t1 = min(cnt, t0 + kRtFold);
+    float2 ax = f2(0.f), ay = f2(0.f);
+    int t = t0;
+    if (PROFILE == LR_PROFILE_TNFW) {
+      // two subhalos per step on the packed far-side form (the rare near
+      // pairs are redone by the general form, which gives the same bits for
+      // far pairs)
+      for (; t + 1 < t1; t += 2) {
+        const SubRec2 H = recs2[t >> 1];
+        const float2 dx = sub2(X, H.xh), dy = sub2(Y, H.yh);
+        const float2 R2 = __ffma2_rn(dx, dx, __fmul2_rn(dy, dy));
+        const float2 x2 = __fmul2_rn(R2, H.its2);
+        float2 m = tnfw_m_far2(H, x2);
+        if (!tnfw_is_far(x2.x)) m.x = tnfw_m(sub_lane(H, 0), R2.x);
+        if (!tnfw_is_far(x2.y)) m.y = tnfw_m(sub_lane(H, 1), R2.y);
+        ax = __ffma2_rn(m, dx, ax);
+        ay = __ffma2_rn(m, dy, ay);
+      }
     }
-  }
-  for (; t < cnt; ++t) {
-    const SubRec h = recs[t];
-    const float dx = x - h.xh, dy = y - h.yh;
-    const float R2 = fmaf(dx, dx, dy * dy);
-    const float m = (PROFILE == LR_PROFILE_POINT_MASS) ? pointmass_m(h, R2) : tnfw_m(h, R2);
-    // Kahan-compensated accumulation over subhalos
-    const float yx = fmaf(m, dx, -cx);
-    const float tx = sx + yx;
-    cx = (tx - sx) - yx;
-    sx = tx;
-    const float yy = fmaf(m, dy, -cy);
-    const float ty = sy + yy;
-    cy = (ty - sy) - yy;
-    sy = ty;
+    for (; t < t1; ++t) {
+      const SubRec h = sub_lane(recs2[t >> 1], t & 1);
+      const float dx = __fsub_rn(x, h.xh), dy = __fsub_rn(y, h.yh);
+      const float R2 = __fmaf_rn(dx, dx, __fmul_rn(dy, dy));
+      const float m = (PROFILE == LR_PROFILE_POINT_MASS) ? pointmass_m(h, R2) : tnfw_m(h, R2);
+      if (t & 1) {
+        ax.y = __fmaf_rn(m, dx, ax.y);
+        ay.y = __fmaf_rn(m, dy, ay.y);
+      } else {
+        ax.x = __fmaf_rn(m, dx, ax.x);
+        ay.x = __fmaf_rn(m, dy, ay.x);
+      }
+    }
+    kahan(sx, cx, __fadd_rn(ax.x, ax.y));
+    kahan(sy, cy, __fadd_rn(ay.x, ay.y));
   }
 }
 
 struct RtSmem {
   float raw[5 * kSubChunk];
-  SubRec recs[kSubChunk];
+  SubRec2 recs2[kSubChunk / 2];
   uint64_t bar;
 };
 
@@ -98,8 +106,8 @@ __device__ __forceinline__ void raytrace_body(const LensConst& L, const GridDev&
     float sx = 0.f, cx = 0.f, sy = 0.f, cy = 0.f;
     for (int h0 = 0; h0 < n_sub; h0 += kSubChunk) {
       const int cnt = min(kSubChunk, n_sub - h0);
-      if (!stage_subs(sub, h0, cnt, PROFILE, sm.raw, sm.recs, &sm.bar, phase, bulk_ok != 0, fault)) return;
-      add_subs<PROFILE>(sm.recs, cnt, p.x, p.y, sx, cx, sy, cy);
+      if (!stage_subs2(sub, h0, cnt, PROFILE, sm.raw, sm.recs2, &sm.bar, phase, bulk_ok != 0, fault)) return;
+      add_subs<PROFILE>(sm.recs2, cnt, p.x, p.y, sx, cx, sy, cy);
       __syncthreads();
     }
     ax += sx - cx;
@@ -249,6 +257,7 @@ lr_status launch_raytrace(const lr_points* p, float2* beta, float2* alpha, cudaS
   const unsigned blocks = (unsigned)((p->n + kRtThreads - 1) / kRtThreads);
   const float2* xi = reinterpret_cast<const float2*>(p->xy);
   const int ns = p->n_sub;
+  ktimer_begin(LR_KT_RAYTRACE, s);
   if (p->profile == LR_PROFILE_POINT_MASS)
     raytrace_kernel<LR_PROFILE_POINT_MASS><<<blocks, kRtThreads, 0, s>>>(L, g, xi, p->n, p->sub, ns, bulk_ok, beta,
                                                                          alpha, fault);
@@ -256,6 +265,7 @@ lr_status launch_raytrace(const lr_points* p, float2* beta, float2* alpha, cudaS
     raytrace_kernel<LR_PROFILE_TNFW><<<blocks, kRtThreads, 0, s>>>(L, g, xi, p->n, p->sub, ns, bulk_ok, beta, alpha,
                                                                    fault);
   LR_CHECK_CUDA(cudaGetLastError());
+  ktimer_end(LR_KT_RAYTRACE, s);
   return LR_OK;
 }
 

@@ -5,14 +5,20 @@
 //
 // The grid has at most one CTA per resident slot; CTA b takes the contiguous
 // point range [b n / nblk, (b + 1) n / nblk), so every CTA does the same work
-// to within one point and no wave is left partly empty. Points and their G
-// are staged through shared memory in tiles; each thread OWNS one subhalo
-// (threads loop over subhalo groups when there are more) and sweeps the
-// tile's points, reading each point as a shared-memory broadcast, so the
-// subhalo sums need no cross-thread reduction at all. The lens and shear
-// terms are per point: the thread that stages a point also evaluates them.
-// Per-CTA partials (FP64 lens terms, Kahan-compensated FP32 subhalo terms)
-// are added in fixed order by a final kernel, so results are deterministic.
+// to within one point and no wave is left partly empty. The CTA stages its
+// points and their G in shared memory (kVjChunk at a time; one chunk at the
+// usual sizes) and the thread that stages a point also evaluates its lens and
+// shear terms. The subhalo sums are split into slots (h, phase): with P
+// phases, slot (h, r) sums subhalo h over the staged points j = r (mod P).
+// Threads own slots, so a slot's sums need no cross-thread reduction and,
+// once the points are staged, a thread sweeps without block barriers. Points
+// are staged as packed pairs (2k, 2k + 1), so a slot evaluates two points per
+// step in f32x2 arithmetic; slot (h, r) takes the point pairs k = r (mod P).
+// P is
+// chosen on the host so that n_sub * P fills the CTA's threads nearly
+// evenly. Per-CTA partials (FP64 lens terms, Kahan-compensated FP32 slot
+// sums) are added in fixed order by a final kernel, so results are
+// deterministic.
 #include <math.h>
 
 #include "host.cuh"
@@ -21,8 +27,10 @@
 namespace lr {
 
 constexpr int kVjThreads = 128;
-constexpr int kVjTile = kVjThreads;  // points staged per tile (one per thread)
 constexpr int kVjWarps = kVjThreads / 32;
+constexpr int kVjChunk = 2048;    // points staged in shared memory at once
+constexpr int kVjMaxPhases = 8;
+constexpr int kVjFold = 16;       // point pairs summed plainly per slot before a Kahan fold
 
 __device__ __forceinline__ double warp_sum_d(double v) {
 #pragma unroll
@@ -31,136 +39,150 @@ __device__ __forceinline__ double warp_sum_d(double v) {
 }
 
 struct VjSmem {
-  float4 pts[2][kVjTile];  // (x, y, G_x, G_y)
+  float4 pos[kVjChunk / 2];   // point pair k: (x_2k, x_2k+1, y_2k, y_2k+1)
+  float4 grad[kVjChunk / 2];  // (G_x, G_x, G_y, G_y) of the same two points
   double lred[kVjWarps][7];
 };
 
-// One tNFW pair's terms of the four subhalo sums (with explicit roundings,
-// so every caller and every kernel that inlines it sums the same values).
-__device__ __forceinline__ void vj_accum(const SubRec& rec, float2 ex, float dx, float dy, float gx, float gy,
-                                         float R2, float Gt, float Ht, float& a0, float& a1, float& a2, float& a3) {
-  const float dg = fmaf(dx, gx, __fmul_rn(dy, gy));
-  const float hg = fmaf(-2.0f, Gt, Ht);
-  const float q = __fmul_rn(__fmul_rn(hg, dg), frcp(R2));
-  a0 = fmaf(rec.A, fmaf(Gt, gx, __fmul_rn(q, dx)), a0);
-  a1 = fmaf(rec.A, fmaf(Gt, gy, __fmul_rn(q, dy)), a1);
-  a2 = fmaf(-__fmul_rn(ex.x, Gt), dg, a2);
-  a3 = fmaf(__fmul_rn(__fmul_rn(rec.A, hg), dg), ex.y, a3);
+// One tNFW pair's terms of the four subhalo sums, for two points at once
+// (packed f32x2; iR2 = 1/R^2).
+__device__ __forceinline__ void vj_accum2(const SubRec2& H, float2 ex, float2 dx, float2 dy, float2 gx, float2 gy,
+                                          float2 iR2, float2 Gt, float2 Ht, float2& a0, float2& a1, float2& a2,
+                                          float2& a3) {
+  const float2 dg = __ffma2_rn(dx, gx, __fmul2_rn(dy, gy));
+  const float2 hg = __ffma2_rn(f2(-2.0f), Gt, Ht);
+  const float2 q = __fmul2_rn(__fmul2_rn(hg, dg), iR2);
+  a0 = __ffma2_rn(H.A, __ffma2_rn(Gt, gx, __fmul2_rn(q, dx)), a0);
+  a1 = __ffma2_rn(H.A, __ffma2_rn(Gt, gy, __fmul2_rn(q, dy)), a1);
+  a2 = __ffma2_rn(__fmul2_rn(f2(-ex.x), Gt), dg, a2);
+  a3 = __ffma2_rn(__fmul2_rn(__fmul2_rn(H.A, hg), dg), f2(ex.y), a3);
 }
 
 __device__ __forceinline__ void vj_kahan(float& s, float& c, float x) {
-  const float y = x - c;
-  const float t = s + y;
-  c = (t - s) - y;
+  const float y = __fsub_rn(x, c);
+  const float t = __fadd_rn(s, y);
+  c = __fsub_rn(__fsub_rn(t, s), y);
   s = t;
+}
+
+// Sums of one slot over the staged point pairs k = r, r + P, ... < npairs.
+template <int PROFILE>
+__device__ __forceinline__ void vj_sweep(const SubRec& rec, float2 ex, const float4* __restrict__ pos,
+                                         const float4* __restrict__ grad, int npairs, int r, int P, float* s,
+                                         float* c) {
+  const SubRec2 H = sub_pair(rec, rec);
+  for (int k = r; k < npairs;) {
+    const int kend = min(npairs, k + P * kVjFold);
+    float2 a0 = f2(0.f), a1 = f2(0.f), a2 = f2(0.f), a3 = f2(0.f);
+    for (; k < kend; k += P) {
+      const float4 Q = pos[k], D = grad[k];
+      const float2 dx = sub2(make_float2(Q.x, Q.y), H.xh), dy = sub2(make_float2(Q.z, Q.w), H.yh);
+      float2 gx = make_float2(D.x, D.y), gy = make_float2(D.z, D.w);
+      const float2 R2 = __ffma2_rn(dx, dx, __fmul2_rn(dy, dy));
+      if (PROFILE == LR_PROFILE_TNFW) {
+        // the far-side form for both points; the rare near ones are redone
+        // by the general form (the same bits where both apply)
+        const float2 x2 = __fmul2_rn(R2, H.its2);
+        float2 Gt, Ht, ix2;
+        tnfw_GH_far2(H, x2, Gt, Ht, ix2);
+        if (!tnfw_is_far(x2.x)) tnfw_GH(rec, R2.x, Gt.x, Ht.x, ix2.x);
+        if (!tnfw_is_far(x2.y)) tnfw_GH(rec, R2.y, Gt.y, Ht.y, ix2.y);
+        // a point on the subhalo centre adds nothing
+        if (!(R2.x > 1e-30f)) Gt.x = Ht.x = ix2.x = gx.x = gy.x = 0.f;
+        if (!(R2.y > 1e-30f)) Gt.y = Ht.y = ix2.y = gx.y = gy.y = 0.f;
+        vj_accum2(H, ex, dx, dy, gx, gy, __fmul2_rn(H.its2, ix2), Gt, Ht, a0, a1, a2, a3);
+      } else {
+        // point mass: alpha = theta^2 d / R^2 (its2 = theta^2, ex.y = theta)
+        float2 iR2 = make_float2(R2.x > 1e-30f ? frcp(R2.x) : 0.f, R2.y > 1e-30f ? frcp(R2.y) : 0.f);
+        const float2 dg = __ffma2_rn(dx, gx, __fmul2_rn(dy, gy));
+        const float2 m = __fmul2_rn(H.its2, iR2);
+        const float2 q = __fmul2_rn(__fmul2_rn(f2(-2.0f), dg), iR2);
+        a0 = __ffma2_rn(m, __ffma2_rn(q, dx, gx), a0);
+        a1 = __ffma2_rn(m, __ffma2_rn(q, dy, gy), a1);
+        a2 = __ffma2_rn(f2(-2.0f * ex.y), __fmul2_rn(dg, iR2), a2);
+      }
+    }
+    vj_kahan(s[0], c[0], __fadd_rn(a0.x, a0.y));
+    vj_kahan(s[1], c[1], __fadd_rn(a1.x, a1.y));
+    vj_kahan(s[2], c[2], __fadd_rn(a2.x, a2.y));
+    vj_kahan(s[3], c[3], __fadd_rn(a3.x, a3.y));
+  }
 }
 
 template <int PROFILE>
 __device__ __forceinline__ void vjp_body(const LensConst& L, const LensGradConst& LG, const GridDev& g,
                                          const float2* __restrict__ xi, int64_t n, const float* __restrict__ sub,
-                                         int n_sub, const float2* __restrict__ dbeta, double* __restrict__ lens_part,
-                                         float* __restrict__ sub_part, int64_t blk, int64_t nblk, VjSmem& sm) {
+                                         int n_sub, int P, const float2* __restrict__ dbeta,
+                                         double* __restrict__ lens_part, float* __restrict__ sub_part, int64_t blk,
+                                         int64_t nblk, VjSmem& sm) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t p0 = blk * n / nblk, p1 = (blk + 1) * n / nblk;
-  const int ntiles = (int)((p1 - p0 + kVjTile - 1) / kVjTile);
+  const int nchunks = (int)((p1 - p0 + kVjChunk - 1) / kVjChunk);
+  const int slots = n_sub * P;
+  const int ngroups = slots > 0 ? (slots + kVjThreads - 1) / kVjThreads : 1;
   float la[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-  const int ngroups = n_sub > 0 ? (n_sub + kVjThreads - 1) / kVjThreads : 1;
-
-  // stage point p0 + k kVjTile + tid; the first subhalo group also takes the
-  // point's lens and shear terms
-  auto load = [&](int k, bool lens_terms) -> float4 {
-    const int64_t i = p0 + (int64_t)k * kVjTile + tid;
-    if (i >= p1) return make_float4(0.f, 0.f, 0.f, 0.f);  // zero gradient: contributes nothing
-    const float2 p = xi ? xi[i] : grid_point(g, i);
-    const float2 d = dbeta[i];
-    if (lens_terms) {
-      float o5[5];
-      sple_vjp(L, LG, p.x, p.y, d.x, d.y, o5);
-#pragma unroll
-      for (int t = 0; t < 5; ++t) la[t] += o5[t];
-      la[5] -= fmaf(d.x, p.x, -d.y * p.y);  // dalpha/dg1 = (x, -y)
-      la[6] -= fmaf(d.x, p.y, d.y * p.x);   // dalpha/dg2 = (y, x)
-    }
-    return make_float4(p.x, p.y, d.x, d.y);
-  };
+  int staged = -1;
 
   for (int grp = 0; grp < ngroups; ++grp) {
-    const int h = grp * kVjThreads + tid;
-    const bool own = h < n_sub;
+    const int slot = grp * kVjThreads + tid;
+    const bool own = slot < slots;
+    const int h = own ? slot / P : 0;
+    const int r = own ? slot - h * P : 0;
     SubRec rec{};
     float2 ex = make_float2(0.f, 0.f);  // tNFW: (4T, 1/theta_s); point mass: (0, theta_pm)
     if (own) {
-      const float* r = sub + 5 * (int64_t)h;
-      rec = prep_sub(r, PROFILE);
+      const float* rr = sub + 5 * (int64_t)h;
+      rec = prep_sub(rr, PROFILE);
       if (PROFILE == LR_PROFILE_POINT_MASS) {
-        ex = make_float2(0.f, __ldg(r + 2));
+        ex = make_float2(0.f, __ldg(rr + 2));
       } else {
-        const float tau = __ldg(r + 4), t2 = tau * tau;
-        ex = make_float2(4.0f * t2 / ((t2 + 1.0f) * (t2 + 1.0f)), 1.0f / __ldg(r + 3));
+        const float tau = __ldg(rr + 4), t2 = tau * tau;
+        ex = make_float2(4.0f * t2 / ((t2 + 1.0f) * (t2 + 1.0f)), 1.0f / __ldg(rr + 3));
       }
     }
-    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f, c0 = 0.f, c1 = 0.f, c2 = 0.f, c3 = 0.f;
-    float4 P = ntiles > 0 ? load(0, grp == 0) : make_float4(0.f, 0.f, 0.f, 0.f);
-    sm.pts[0][tid] = P;
-    __syncthreads();
-    for (int k = 0; k < ntiles; ++k) {
-      const int buf = k & 1;
-      if (k + 1 < ntiles) P = load(k + 1, grp == 0);
-      const int cnt = (int)min((int64_t)kVjTile, p1 - p0 - (int64_t)k * kVjTile);
-      if (own) {
-        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-        int j = 0;
-        if (PROFILE == LR_PROFILE_TNFW) {
-          // two points per step on the straight-line far-side form (the rare
-          // near pairs are redone by the general form); same sums, same order
-          for (; j + 1 < cnt; j += 2) {
-            const float4 Qa = sm.pts[buf][j], Qb = sm.pts[buf][j + 1];
-            const float dxa = Qa.x - rec.xh, dya = Qa.y - rec.yh, dxb = Qb.x - rec.xh, dyb = Qb.y - rec.yh;
-            const float R2a = fmaf(dxa, dxa, dya * dya), R2b = fmaf(dxb, dxb, dyb * dyb);
-            const float x2a = R2a * rec.its2, x2b = R2b * rec.its2;
-            float Ga, Ha, Gb, Hb;
-            tnfw_GH_far(rec, x2a, Ga, Ha);
-            tnfw_GH_far(rec, x2b, Gb, Hb);
-            if (!tnfw_is_far(x2a)) tnfw_GH(rec, R2a, Ga, Ha);
-            if (!tnfw_is_far(x2b)) tnfw_GH(rec, R2b, Gb, Hb);
-            if (R2a > 1e-30f) vj_accum(rec, ex, dxa, dya, Qa.z, Qa.w, R2a, Ga, Ha, a0, a1, a2, a3);
-            if (R2b > 1e-30f) vj_accum(rec, ex, dxb, dyb, Qb.z, Qb.w, R2b, Gb, Hb, a0, a1, a2, a3);
+    float sc[4] = {0.f, 0.f, 0.f, 0.f}, cc[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int ch = 0; ch < nchunks; ++ch) {
+      const int64_t c0 = p0 + (int64_t)ch * kVjChunk;
+      const int cnt = (int)min((int64_t)kVjChunk, p1 - c0);
+      if (ch != staged) {  // uniform over the CTA
+        __syncthreads();   // the previous chunk's readers are done
+        for (int k = tid; k < cnt; k += kVjThreads) {
+          const int64_t i = c0 + k;
+          const float2 p = xi ? xi[i] : grid_point(g, i);
+          const float2 d = dbeta[i];
+          if (grp == 0) {  // each chunk is staged once in group 0: the point's lens and shear terms
+            float o5[5];
+            sple_vjp(L, LG, p.x, p.y, d.x, d.y, o5);
+#pragma unroll
+            for (int t = 0; t < 5; ++t) la[t] += o5[t];
+            la[5] -= fmaf(d.x, p.x, -d.y * p.y);  // dalpha/dg1 = (x, -y)
+            la[6] -= fmaf(d.x, p.y, d.y * p.x);   // dalpha/dg2 = (y, x)
+          }
+          float* ps = reinterpret_cast<float*>(&sm.pos[k >> 1]);
+          float* gs = reinterpret_cast<float*>(&sm.grad[k >> 1]);
+          const int lane2 = k & 1;
+          ps[lane2] = p.x;
+          ps[2 + lane2] = p.y;
+          gs[lane2] = d.x;
+          gs[2 + lane2] = d.y;
+          if (k == cnt - 1 && lane2 == 0) {  // odd count: a zero-gradient partner at the same position
+            ps[1] = p.x;
+            ps[3] = p.y;
+            gs[1] = 0.f;
+            gs[3] = 0.f;
           }
         }
-        for (; j < cnt; ++j) {
-          const float4 Q = sm.pts[buf][j];
-          const float dx = Q.x - rec.xh, dy = Q.y - rec.yh;
-          const float R2 = fmaf(dx, dx, dy * dy);
-          if (!(R2 > 1e-30f)) continue;
-          if (PROFILE == LR_PROFILE_TNFW) {
-            float Gt, Ht;
-            tnfw_GH(rec, R2, Gt, Ht);
-            vj_accum(rec, ex, dx, dy, Q.z, Q.w, R2, Gt, Ht, a0, a1, a2, a3);
-            continue;
-          }
-          // point mass
-          const float dg = fmaf(dx, Q.z, dy * Q.w);
-          const float iR2 = frcp(R2);
-          const float m = rec.its2 * iR2;
-          const float q = 2.0f * dg * iR2;
-          a0 += m * fmaf(-q, dx, Q.z);
-          a1 += m * fmaf(-q, dy, Q.w);
-          a2 -= 2.0f * ex.y * dg * iR2;
-        }
-        vj_kahan(s0, c0, a0);
-        vj_kahan(s1, c1, a1);
-        vj_kahan(s2, c2, a2);
-        vj_kahan(s3, c3, a3);
+        __syncthreads();
+        staged = ch;
       }
-      if (k + 1 < ntiles) sm.pts[buf ^ 1][tid] = P;
-      __syncthreads();
+      if (own) vj_sweep<PROFILE>(rec, ex, sm.pos, sm.grad, (cnt + 1) >> 1, r, P, sc, cc);
     }
     if (own) {
-      float* o = sub_part + (blk * n_sub + h) * 4;
-      o[0] = s0 - c0;
-      o[1] = s1 - c1;
-      o[2] = s2 - c2;
-      o[3] = s3 - c3;
+      float* o = sub_part + (blk * slots + slot) * 4;
+      o[0] = sc[0] - cc[0];
+      o[1] = sc[1] - cc[1];
+      o[2] = sc[2] - cc[2];
+      o[3] = sc[3] - cc[3];
     }
   }
 
@@ -179,33 +201,33 @@ __device__ __forceinline__ void vjp_body(const LensConst& L, const LensGradConst
 }
 
 template <int PROFILE>
-__global__ void __launch_bounds__(kVjThreads) raytrace_vjp_kernel(const __grid_constant__ LensConst L,
+__global__ void __launch_bounds__(kVjThreads, 6) raytrace_vjp_kernel(const __grid_constant__ LensConst L,
                                                                   const __grid_constant__ LensGradConst LG, GridDev g,
                                                                   const float2* __restrict__ xi, int64_t n,
-                                                                  const float* __restrict__ sub, int n_sub,
+                                                                  const float* __restrict__ sub, int n_sub, int P,
                                                                   const float2* __restrict__ dbeta,
                                                                   double* __restrict__ lens_part,
                                                                   float* __restrict__ sub_part) {
   __shared__ __align__(16) VjSmem sm;
-  vjp_body<PROFILE>(L, LG, g, xi, n, sub, n_sub, dbeta, lens_part, sub_part, blockIdx.x, gridDim.x, sm);
+  vjp_body<PROFILE>(L, LG, g, xi, n, sub, n_sub, P, dbeta, lens_part, sub_part, blockIdx.x, gridDim.x, sm);
 }
 
-__global__ void __launch_bounds__(kVjThreads) vjp_batched_kernel(const __grid_constant__ Batch<VjpP> B) {
+__global__ void __launch_bounds__(kVjThreads, 6) vjp_batched_kernel(const __grid_constant__ Batch<VjpP> B) {
   __shared__ __align__(16) VjSmem sm;
   const int k = batch_find(B, blockIdx.x);
   const VjpP& P = B.p[k];
   const int64_t blk = blockIdx.x - B.start[k];
   const int64_t nblk = B.start[k + 1] - B.start[k];
   if (P.profile == LR_PROFILE_POINT_MASS)
-    vjp_body<LR_PROFILE_POINT_MASS>(P.L, P.LG, P.g, P.xi, P.n, P.sub, P.n_sub, P.dbeta, P.lens_part, P.sub_part,
-                                    blk, nblk, sm);
+    vjp_body<LR_PROFILE_POINT_MASS>(P.L, P.LG, P.g, P.xi, P.n, P.sub, P.n_sub, P.phases, P.dbeta, P.lens_part,
+                                    P.sub_part, blk, nblk, sm);
   else
-    vjp_body<LR_PROFILE_TNFW>(P.L, P.LG, P.g, P.xi, P.n, P.sub, P.n_sub, P.dbeta, P.lens_part, P.sub_part, blk,
-                              nblk, sm);
+    vjp_body<LR_PROFILE_TNFW>(P.L, P.LG, P.g, P.xi, P.n, P.sub, P.n_sub, P.phases, P.dbeta, P.lens_part,
+                              P.sub_part, blk, nblk, sm);
 }
 
 // CTAs of the VJP for n points: one per resident slot of the device at most
-// (and at most one per kVjTile points), so a launch is a single full wave.
+// (and at most one per kVjThreads points), so a launch is a single full wave.
 int64_t vjp_blocks(int64_t n) {
   if (n <= 0) return 0;
   static int slots[64] = {0};
@@ -219,15 +241,37 @@ int64_t vjp_blocks(int64_t n) {
       occ = 1;
     slots[dev] = (occ > 0 ? occ : 1) * n_sm;
   }
-  const int64_t nb = (n + kVjTile - 1) / kVjTile;
+  const int64_t nb = (n + kVjThreads - 1) / kVjThreads;
   return nb < slots[dev] ? nb : slots[dev];
 }
 
-// Fixed-order FP64 sum of the per-CTA partials: one warp per output value
-// (7 lens values, then 4 per subhalo); lane l sums CTAs l, l + 32, ...; the
-// warp reduces by xor-shuffle.
+// Phases P of the subhalo sums: the P in [1, kVjMaxPhases] whose slot count
+// n_sub P wastes the fewest threads of the last group of kVjThreads (the
+// smallest such P), keeping at least 64 points per slot.
+int vjp_phases(int64_t n, int32_t n_sub) {
+  if (n_sub <= 0 || n <= 0) return 1;
+  const int64_t per_cta = (n + vjp_blocks(n) - 1) / vjp_blocks(n);
+  int best = 1;
+  double best_w = 1e30;
+  for (int P = 1; P <= kVjMaxPhases; ++P) {
+    if (P > 1 && per_cta / P < 64) break;
+    const int64_t sl = (int64_t)n_sub * P;
+    const int64_t padded = (sl + kVjThreads - 1) / kVjThreads * kVjThreads;
+    const double w = (double)padded / (double)sl;
+    if (w < best_w - 1e-9) {
+      best_w = w;
+      best = P;
+    }
+  }
+  return best;
+}
+
+// Fixed-order sum of the per-CTA partials: one warp per output value
+// (7 lens values, then 4 per subhalo); lane l sums CTAs l, l + 32, ... (and,
+// within a CTA, the subhalo's P slots in phase order); the warp reduces by
+// xor-shuffle.
 __device__ __forceinline__ void vjp_final_body(const double* __restrict__ lens_part,
-                                               const float* __restrict__ sub_part, int nblk, int n_sub,
+                                               const float* __restrict__ sub_part, int nblk, int n_sub, int P,
                                                double* __restrict__ d_lens, double* __restrict__ d_sub, int64_t blk) {
   const int o = (int)((blk * blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
@@ -236,8 +280,16 @@ __device__ __forceinline__ void vjp_final_body(const double* __restrict__ lens_p
   if (o < 7) {
     for (int b = lane; b < nblk; b += 32) s += lens_part[(int64_t)b * 7 + o];
   } else {
-    const int t = o - 7;
-    for (int b = lane; b < nblk; b += 32) s += (double)sub_part[(int64_t)b * n_sub * 4 + t];
+    // the lane's share in FP32 with Kahan compensation (FP64 arithmetic is
+    // slow on this GPU), the lanes in FP64
+    const int t = o - 7, h = t >> 2, v = t & 3;
+    const int64_t slots = (int64_t)n_sub * P;
+    float fs = 0.f, fc = 0.f;
+    for (int b = lane; b < nblk; b += 32) {
+      const float* q = sub_part + ((int64_t)b * slots + (int64_t)h * P) * 4 + v;
+      for (int r = 0; r < P; ++r) vj_kahan(fs, fc, q[4 * r]);
+    }
+    s = (double)fs - (double)fc;
   }
 #pragma unroll
   for (int k = 16; k > 0; k >>= 1) s += __shfl_xor_sync(0xffffffffu, s, k);
@@ -251,14 +303,14 @@ __device__ __forceinline__ void vjp_final_body(const double* __restrict__ lens_p
 }
 
 __global__ void vjp_final_kernel(const double* __restrict__ lens_part, const float* __restrict__ sub_part, int nblk,
-                                 int n_sub, double* __restrict__ d_lens, double* __restrict__ d_sub) {
-  vjp_final_body(lens_part, sub_part, nblk, n_sub, d_lens, d_sub, blockIdx.x);
+                                 int n_sub, int P, double* __restrict__ d_lens, double* __restrict__ d_sub) {
+  vjp_final_body(lens_part, sub_part, nblk, n_sub, P, d_lens, d_sub, blockIdx.x);
 }
 
 __global__ void vjp_final_batched_kernel(const __grid_constant__ Batch<VjpFinalP> B) {
   const int k = batch_find(B, blockIdx.x);
   const VjpFinalP& P = B.p[k];
-  vjp_final_body(P.lens_part, P.sub_part, P.nblk, P.n_sub, P.d_lens, P.d_sub, blockIdx.x - B.start[k]);
+  vjp_final_body(P.lens_part, P.sub_part, P.nblk, P.n_sub, P.phases, P.d_lens, P.d_sub, blockIdx.x - B.start[k]);
 }
 
 lr_status launch_vjp_batched(const VjpP* p, int count, cudaStream_t s) {
@@ -333,7 +385,8 @@ lr_status make_lens_grad_const(const lr_lens* lens, LensGradConst* out) {
 
 size_t raytrace_vjp_ws(int64_t n, int32_t n_sub) {
   const int64_t nblk = vjp_blocks(n);
-  return align256(sizeof(double) * 7 * (size_t)nblk) + align256(sizeof(float) * 4 * (size_t)n_sub * (size_t)nblk);
+  const int64_t slots = (int64_t)n_sub * vjp_phases(n, n_sub);
+  return align256(sizeof(double) * 7 * (size_t)nblk) + align256(sizeof(float) * 4 * (size_t)slots * (size_t)nblk);
 }
 
 lr_status launch_raytrace_vjp(const lr_points* p, const float2* dbeta, double* d_lens, double* d_sub, void* ws,
@@ -354,15 +407,18 @@ lr_status launch_raytrace_vjp(const lr_points* p, const float2* dbeta, double* d
   float* sub_part = reinterpret_cast<float*>(static_cast<char*>(ws) + align256(sizeof(double) * 7 * (size_t)nblk));
   const GridDev g = p->xy ? GridDev{} : grid_dev(p->grid);
   const float2* xi = reinterpret_cast<const float2*>(p->xy);
+  const int P = vjp_phases(p->n, p->n_sub);
+  ktimer_begin(LR_KT_RAYTRACE_VJP, s);
   if (p->profile == LR_PROFILE_POINT_MASS)
     raytrace_vjp_kernel<LR_PROFILE_POINT_MASS><<<(unsigned)nblk, kVjThreads, 0, s>>>(
-        L, G, g, xi, p->n, p->sub, p->n_sub, dbeta, lens_part, sub_part);
+        L, G, g, xi, p->n, p->sub, p->n_sub, P, dbeta, lens_part, sub_part);
   else
     raytrace_vjp_kernel<LR_PROFILE_TNFW><<<(unsigned)nblk, kVjThreads, 0, s>>>(
-        L, G, g, xi, p->n, p->sub, p->n_sub, dbeta, lens_part, sub_part);
+        L, G, g, xi, p->n, p->sub, p->n_sub, P, dbeta, lens_part, sub_part);
   LR_CHECK_CUDA(cudaGetLastError());
+  ktimer_end(LR_KT_RAYTRACE_VJP, s);
   const int64_t warps = 7 + 4 * (int64_t)p->n_sub;
-  vjp_final_kernel<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, s>>>(lens_part, sub_part, (int)nblk, p->n_sub,
+  vjp_final_kernel<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, s>>>(lens_part, sub_part, (int)nblk, p->n_sub, P,
                                                                         d_lens, p->n_sub ? d_sub : nullptr);
   LR_CHECK_CUDA(cudaGetLastError());
   return LR_OK;
@@ -384,6 +440,7 @@ lr_status make_vjp_problem(const lr_points* p, const float2* dbeta, double* d_le
   v.sub = p->sub;
   v.n_sub = p->n_sub;
   v.profile = p->profile;
+  v.phases = vjp_phases(p->n, p->n_sub);
   v.dbeta = dbeta;
   v.lens_part = static_cast<double*>(ws);
   v.sub_part = reinterpret_cast<float*>(static_cast<char*>(ws) + align256(sizeof(double) * 7 * (size_t)nblk));
@@ -392,6 +449,7 @@ lr_status make_vjp_problem(const lr_points* p, const float2* dbeta, double* d_le
   F->sub_part = v.sub_part;
   F->nblk = (int32_t)nblk;
   F->n_sub = p->n_sub;
+  F->phases = v.phases;
   F->d_lens = d_lens;
   F->d_sub = p->n_sub ? d_sub : nullptr;
   return LR_OK;

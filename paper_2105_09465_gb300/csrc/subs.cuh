@@ -7,10 +7,10 @@
 
 namespace lr {
 
-// Stages subhalo records [h0, h0 + cnt) into shared memory as SubRec.
-// Returns false (all threads) if the bulk-copy wait timed out.
-__device__ __forceinline__ bool stage_subs(const float* __restrict__ sub, int h0, int cnt, int profile, float* raw, SubRec* recs,
-                           uint64_t* bar, uint32_t& phase, bool bulk_ok, int* fault) {
+// Copies the raw records [h0, h0 + cnt) into shared memory. Returns false
+// (all threads) if the bulk-copy wait timed out.
+__device__ __forceinline__ bool stage_raw(const float* __restrict__ sub, int h0, int cnt, float* raw, uint64_t* bar,
+                                          uint32_t& phase, bool bulk_ok, int* fault) {
   const float* src = sub + 5 * (int64_t)h0;
   const uint32_t bytes = 20u * (uint32_t)cnt;
   const uint32_t bulk_bytes = bulk_ok ? (bytes & ~15u) : 0u;
@@ -26,8 +26,29 @@ __device__ __forceinline__ bool stage_subs(const float* __restrict__ sub, int h0
   if (bulk_bytes > 0) ok = mbar_wait_bounded(bar, phase, fault);
   phase ^= (bulk_bytes > 0) ? 1u : 0u;
   __syncthreads();
-  if (__syncthreads_or(!ok)) return false;
+  return !__syncthreads_or(!ok);
+}
+
+// Stages subhalo records [h0, h0 + cnt) into shared memory as SubRec.
+// Returns false (all threads) if the bulk-copy wait timed out.
+__device__ __forceinline__ bool stage_subs(const float* __restrict__ sub, int h0, int cnt, int profile, float* raw, SubRec* recs,
+                           uint64_t* bar, uint32_t& phase, bool bulk_ok, int* fault) {
+  if (!stage_raw(sub, h0, cnt, raw, bar, phase, bulk_ok, fault)) return false;
   for (int t = threadIdx.x; t < cnt; t += blockDim.x) recs[t] = prep_sub(raw + 5 * t, profile);
+  __syncthreads();
+  return true;
+}
+
+// The same as consecutive pairs: recs2[k] holds records 2k and 2k + 1 (the
+// second a zero record when cnt is odd).
+__device__ __forceinline__ bool stage_subs2(const float* __restrict__ sub, int h0, int cnt, int profile, float* raw,
+                                            SubRec2* recs2, uint64_t* bar, uint32_t& phase, bool bulk_ok, int* fault) {
+  if (!stage_raw(sub, h0, cnt, raw, bar, phase, bulk_ok, fault)) return false;
+  for (int t = threadIdx.x; 2 * t < cnt; t += blockDim.x) {
+    const SubRec a = prep_sub(raw + 10 * t, profile);
+    const SubRec b = 2 * t + 1 < cnt ? prep_sub(raw + 10 * t + 5, profile) : SubRec{};
+    recs2[t] = sub_pair(a, b);
+  }
   __syncthreads();
   return true;
 }

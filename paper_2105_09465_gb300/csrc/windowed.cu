@@ -327,11 +327,13 @@ extern "C" lr_status gp_windowed_matvec(const float* p, const float* z, int64_t 
   A.out = out;
   A.partial = static_cast<float*>(workspace);
   const unsigned grid = (unsigned)((int64_t)P.row_blocks * P.chunks);
+  ktimer_begin(LR_KT_WINDOWED, s);
   if (A.q)
     windowed_kernel<false><<<grid, kWnThreads, 0, s>>>(A);
   else
     windowed_kernel<true><<<grid, kWnThreads, 0, s>>>(A);
   LR_CHECK_CUDA(cudaGetLastError());
+  ktimer_end(LR_KT_WINDOWED, s);
   if (P.chunks > 1) {
     windowed_merge_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(A.partial, P.chunks, n, out);
     LR_CHECK_CUDA(cudaGetLastError());

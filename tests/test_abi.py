@@ -86,3 +86,14 @@ def test_matvec_rejects_bad_arguments_without_gpu(lib):
     q.n = -1
     assert lib.gp_kernel_matvec(ctypes.byref(q), None, None, 1, 0.1, 1.0, None, None, None, 0, None) == \
         abi.LR_ERR_INVALID_ARG
+
+
+def test_kernel_timer_without_gpu(lib):
+    n, ms, dropped = ctypes.c_int64(-1), ctypes.c_double(-1.0), ctypes.c_int64(-1)
+    assert lib.lr_kernel_timer_enable(0) == 0
+    assert lib.lr_kernel_timer_read(99, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(dropped)) == 1
+    assert lib.lr_kernel_timer_read(-1, ctypes.byref(n), ctypes.byref(ms), None) == 1
+    assert lib.lr_kernel_timer_read(0, None, ctypes.byref(ms), None) == 1
+    # nothing recorded: no event is touched
+    assert lib.lr_kernel_timer_read(0, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(dropped)) == 0
+    assert (n.value, ms.value, dropped.value) == (0, 0.0, 0)
