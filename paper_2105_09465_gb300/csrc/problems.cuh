@@ -180,13 +180,14 @@ struct VjpP {
   int32_t phases;  // slots per subhalo (see vjp_phases)
   const float2* dbeta;
   double* lens_part;
-  float* sub_part;
+  float* sub_part;   // [4 n_sub][CTA]
+  float* slot_part;  // [CTA][n_sub phases][4] when phases > 1
 };
 
 struct VjpFinalP {
   const double* lens_part;
   const float* sub_part;
-  int32_t nblk, n_sub, phases;
+  int32_t nblk, n_sub;
   double* d_lens;
   double* d_sub;
 };

@@ -16,7 +16,8 @@
 // step in f32x2 arithmetic; slot (h, r) takes the point pairs k = r (mod P).
 // P is
 // chosen on the host so that n_sub * P fills the CTA's threads nearly
-// evenly. Per-CTA partials (FP64 lens terms, Kahan-compensated FP32 slot
+// evenly. At the end the CTA adds each subhalo's P slot sums in phase order.
+// Per-CTA partials (FP64 lens terms, Kahan-compensated FP32 slot
 // sums) are added in fixed order by a final kernel, so results are
 // deterministic.
 #include <math.h>
@@ -113,8 +114,8 @@ template <int PROFILE>
 __device__ __forceinline__ void vjp_body(const LensConst& L, const LensGradConst& LG, const GridDev& g,
                                          const float2* __restrict__ xi, int64_t n, const float* __restrict__ sub,
                                          int n_sub, int P, const float2* __restrict__ dbeta,
-                                         double* __restrict__ lens_part, float* __restrict__ sub_part, int64_t blk,
-                                         int64_t nblk, VjSmem& sm) {
+                                         double* __restrict__ lens_part, float* __restrict__ sub_part,
+                                         float* __restrict__ slot_part, int64_t blk, int64_t nblk, VjSmem& sm) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t p0 = blk * n / nblk, p1 = (blk + 1) * n / nblk;
   const int nchunks = (int)((p1 - p0 + kVjChunk - 1) / kVjChunk);
@@ -178,11 +179,26 @@ __device__ __forceinline__ void vjp_body(const LensConst& L, const LensGradConst
       if (own) vj_sweep<PROFILE>(rec, ex, sm.pos, sm.grad, (cnt + 1) >> 1, r, P, sc, cc);
     }
     if (own) {
-      float* o = sub_part + (blk * slots + slot) * 4;
-      o[0] = sc[0] - cc[0];
-      o[1] = sc[1] - cc[1];
-      o[2] = sc[2] - cc[2];
-      o[3] = sc[3] - cc[3];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        const float x = sc[v] - cc[v];
+        if (P == 1)
+          sub_part[((int64_t)h * 4 + v) * nblk + blk] = x;  // [value][CTA]
+        else
+          slot_part[(blk * slots + slot) * 4 + v] = x;
+      }
+    }
+  }
+  if (P > 1) {
+    // each subhalo's P slots in phase order (written by this CTA's threads:
+    // visible to the whole CTA after the barrier)
+    __syncthreads();
+    for (int t = tid; t < 4 * n_sub; t += kVjThreads) {
+      const int hh = t >> 2, v = t & 3;
+      const float* q = slot_part + (blk * slots + (int64_t)hh * P) * 4 + v;
+      float a = 0.f, c = 0.f;
+      for (int rr = 0; rr < P; ++rr) vj_kahan(a, c, q[4 * rr]);
+      sub_part[(int64_t)t * nblk + blk] = a - c;
     }
   }
 
@@ -207,9 +223,11 @@ __global__ void __launch_bounds__(kVjThreads, 6) raytrace_vjp_kernel(const __gri
                                                                   const float* __restrict__ sub, int n_sub, int P,
                                                                   const float2* __restrict__ dbeta,
                                                                   double* __restrict__ lens_part,
-                                                                  float* __restrict__ sub_part) {
+                                                                  float* __restrict__ sub_part,
+                                                                  float* __restrict__ slot_part) {
   __shared__ __align__(16) VjSmem sm;
-  vjp_body<PROFILE>(L, LG, g, xi, n, sub, n_sub, P, dbeta, lens_part, sub_part, blockIdx.x, gridDim.x, sm);
+  vjp_body<PROFILE>(L, LG, g, xi, n, sub, n_sub, P, dbeta, lens_part, sub_part, slot_part, blockIdx.x, gridDim.x,
+                    sm);
 }
 
 __global__ void __launch_bounds__(kVjThreads, 6) vjp_batched_kernel(const __grid_constant__ Batch<VjpP> B) {
@@ -220,10 +238,10 @@ __global__ void __launch_bounds__(kVjThreads, 6) vjp_batched_kernel(const __grid
   const int64_t nblk = B.start[k + 1] - B.start[k];
   if (P.profile == LR_PROFILE_POINT_MASS)
     vjp_body<LR_PROFILE_POINT_MASS>(P.L, P.LG, P.g, P.xi, P.n, P.sub, P.n_sub, P.phases, P.dbeta, P.lens_part,
-                                    P.sub_part, blk, nblk, sm);
+                                    P.sub_part, P.slot_part, blk, nblk, sm);
   else
     vjp_body<LR_PROFILE_TNFW>(P.L, P.LG, P.g, P.xi, P.n, P.sub, P.n_sub, P.phases, P.dbeta, P.lens_part,
-                              P.sub_part, blk, nblk, sm);
+                              P.sub_part, P.slot_part, blk, nblk, sm);
 }
 
 // CTAs of the VJP for n points: one per resident slot of the device at most
@@ -267,11 +285,11 @@ int vjp_phases(int64_t n, int32_t n_sub) {
 }
 
 // Fixed-order sum of the per-CTA partials: one warp per output value
-// (7 lens values, then 4 per subhalo); lane l sums CTAs l, l + 32, ... (and,
-// within a CTA, the subhalo's P slots in phase order); the warp reduces by
-// xor-shuffle.
+// (7 lens values, then 4 per subhalo); lane l sums CTAs l, l + 32, ... (the
+// subhalo partials are stored [value][CTA], so the warp reads contiguous
+// memory); the warp reduces by xor-shuffle.
 __device__ __forceinline__ void vjp_final_body(const double* __restrict__ lens_part,
-                                               const float* __restrict__ sub_part, int nblk, int n_sub, int P,
+                                               const float* __restrict__ sub_part, int nblk, int n_sub,
                                                double* __restrict__ d_lens, double* __restrict__ d_sub, int64_t blk) {
   const int o = (int)((blk * blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
@@ -282,13 +300,9 @@ __device__ __forceinline__ void vjp_final_body(const double* __restrict__ lens_p
   } else {
     // the lane's share in FP32 with Kahan compensation (FP64 arithmetic is
     // slow on this GPU), the lanes in FP64
-    const int t = o - 7, h = t >> 2, v = t & 3;
-    const int64_t slots = (int64_t)n_sub * P;
+    const float* q = sub_part + (int64_t)(o - 7) * nblk;
     float fs = 0.f, fc = 0.f;
-    for (int b = lane; b < nblk; b += 32) {
-      const float* q = sub_part + ((int64_t)b * slots + (int64_t)h * P) * 4 + v;
-      for (int r = 0; r < P; ++r) vj_kahan(fs, fc, q[4 * r]);
-    }
+    for (int b = lane; b < nblk; b += 32) vj_kahan(fs, fc, q[b]);
     s = (double)fs - (double)fc;
   }
 #pragma unroll
@@ -303,14 +317,14 @@ __device__ __forceinline__ void vjp_final_body(const double* __restrict__ lens_p
 }
 
 __global__ void vjp_final_kernel(const double* __restrict__ lens_part, const float* __restrict__ sub_part, int nblk,
-                                 int n_sub, int P, double* __restrict__ d_lens, double* __restrict__ d_sub) {
-  vjp_final_body(lens_part, sub_part, nblk, n_sub, P, d_lens, d_sub, blockIdx.x);
+                                 int n_sub, double* __restrict__ d_lens, double* __restrict__ d_sub) {
+  vjp_final_body(lens_part, sub_part, nblk, n_sub, d_lens, d_sub, blockIdx.x);
 }
 
 __global__ void vjp_final_batched_kernel(const __grid_constant__ Batch<VjpFinalP> B) {
   const int k = batch_find(B, blockIdx.x);
   const VjpFinalP& P = B.p[k];
-  vjp_final_body(P.lens_part, P.sub_part, P.nblk, P.n_sub, P.phases, P.d_lens, P.d_sub, blockIdx.x - B.start[k]);
+  vjp_final_body(P.lens_part, P.sub_part, P.nblk, P.n_sub, P.d_lens, P.d_sub, blockIdx.x - B.start[k]);
 }
 
 lr_status launch_vjp_batched(const VjpP* p, int count, cudaStream_t s) {
@@ -383,11 +397,31 @@ lr_status make_lens_grad_const(const lr_lens* lens, LensGradConst* out) {
   return LR_OK;
 }
 
-size_t raytrace_vjp_ws(int64_t n, int32_t n_sub) {
+// Workspace: per-CTA lens partials [CTA][7] (FP64), subhalo partials
+// [4 n_sub][CTA], and with P > 1 the slot sums [CTA][n_sub P][4].
+struct VjWs {
+  double* lens_part;
+  float* sub_part;
+  float* slot_part;
+  size_t bytes;
+};
+
+static VjWs vjp_ws_layout(void* ws, int64_t n, int32_t n_sub) {
   const int64_t nblk = vjp_blocks(n);
-  const int64_t slots = (int64_t)n_sub * vjp_phases(n, n_sub);
-  return align256(sizeof(double) * 7 * (size_t)nblk) + align256(sizeof(float) * 4 * (size_t)slots * (size_t)nblk);
+  const int P = vjp_phases(n, n_sub);
+  const size_t b_lens = align256(sizeof(double) * 7 * (size_t)nblk);
+  const size_t b_sub = align256(sizeof(float) * 4 * (size_t)n_sub * (size_t)nblk);
+  const size_t b_slot = P > 1 ? align256(sizeof(float) * 4 * (size_t)n_sub * P * (size_t)nblk) : 0;
+  char* c = static_cast<char*>(ws);
+  VjWs w;
+  w.lens_part = reinterpret_cast<double*>(c);
+  w.sub_part = c ? reinterpret_cast<float*>(c + b_lens) : nullptr;
+  w.slot_part = (c && P > 1) ? reinterpret_cast<float*>(c + b_lens + b_sub) : nullptr;
+  w.bytes = b_lens + b_sub + b_slot;
+  return w;
 }
+
+size_t raytrace_vjp_ws(int64_t n, int32_t n_sub) { return vjp_ws_layout(nullptr, n, n_sub).bytes; }
 
 lr_status launch_raytrace_vjp(const lr_points* p, const float2* dbeta, double* d_lens, double* d_sub, void* ws,
                               cudaStream_t s) {
@@ -403,22 +437,23 @@ lr_status launch_raytrace_vjp(const lr_points* p, const float2* dbeta, double* d
     if (d_sub && p->n_sub) LR_CHECK_CUDA(cudaMemsetAsync(d_sub, 0, 4 * sizeof(double) * p->n_sub, s));
     return LR_OK;
   }
-  double* lens_part = static_cast<double*>(ws);
-  float* sub_part = reinterpret_cast<float*>(static_cast<char*>(ws) + align256(sizeof(double) * 7 * (size_t)nblk));
+  const VjWs w = vjp_ws_layout(ws, p->n, p->n_sub);
+  double* lens_part = w.lens_part;
+  float* sub_part = w.sub_part;
   const GridDev g = p->xy ? GridDev{} : grid_dev(p->grid);
   const float2* xi = reinterpret_cast<const float2*>(p->xy);
   const int P = vjp_phases(p->n, p->n_sub);
   ktimer_begin(LR_KT_RAYTRACE_VJP, s);
   if (p->profile == LR_PROFILE_POINT_MASS)
     raytrace_vjp_kernel<LR_PROFILE_POINT_MASS><<<(unsigned)nblk, kVjThreads, 0, s>>>(
-        L, G, g, xi, p->n, p->sub, p->n_sub, P, dbeta, lens_part, sub_part);
+        L, G, g, xi, p->n, p->sub, p->n_sub, P, dbeta, lens_part, sub_part, w.slot_part);
   else
     raytrace_vjp_kernel<LR_PROFILE_TNFW><<<(unsigned)nblk, kVjThreads, 0, s>>>(
-        L, G, g, xi, p->n, p->sub, p->n_sub, P, dbeta, lens_part, sub_part);
+        L, G, g, xi, p->n, p->sub, p->n_sub, P, dbeta, lens_part, sub_part, w.slot_part);
   LR_CHECK_CUDA(cudaGetLastError());
   ktimer_end(LR_KT_RAYTRACE_VJP, s);
   const int64_t warps = 7 + 4 * (int64_t)p->n_sub;
-  vjp_final_kernel<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, s>>>(lens_part, sub_part, (int)nblk, p->n_sub, P,
+  vjp_final_kernel<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, s>>>(lens_part, sub_part, (int)nblk, p->n_sub,
                                                                         d_lens, p->n_sub ? d_sub : nullptr);
   LR_CHECK_CUDA(cudaGetLastError());
   return LR_OK;
@@ -442,14 +477,15 @@ lr_status make_vjp_problem(const lr_points* p, const float2* dbeta, double* d_le
   v.profile = p->profile;
   v.phases = vjp_phases(p->n, p->n_sub);
   v.dbeta = dbeta;
-  v.lens_part = static_cast<double*>(ws);
-  v.sub_part = reinterpret_cast<float*>(static_cast<char*>(ws) + align256(sizeof(double) * 7 * (size_t)nblk));
+  const VjWs w = vjp_ws_layout(ws, p->n, p->n_sub);
+  v.lens_part = w.lens_part;
+  v.sub_part = w.sub_part;
+  v.slot_part = w.slot_part;
   *V = v;
   F->lens_part = v.lens_part;
   F->sub_part = v.sub_part;
   F->nblk = (int32_t)nblk;
   F->n_sub = p->n_sub;
-  F->phases = v.phases;
   F->d_lens = d_lens;
   F->d_sub = p->n_sub ? d_sub : nullptr;
   return LR_OK;
