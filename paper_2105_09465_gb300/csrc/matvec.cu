@@ -170,12 +170,15 @@ __device__ __forceinline__ void matvec_body(const MvArgs& A, int rb, int chunk, 
         dy2[r] = dy * dy;
       }
       const int nsg = (cnt + kSeg - 1) / kSeg;
+      // columns of this grid row within reach of the row block (all without info)
+      int clo = 0, chi = cnt - 1;
+      if (A.info) reach_cols(B, A.src.g, yt, A.sc, c0, cnt, clo, chi);
       if (!A.split) {
         // unsplit: dx' = q - x', exponent -(dx'^2 + dy'^2)
         for (int sg = 0; sg < nsg; ++sg) {
-          if (A.info && seg_far(B, grid_x(A.src.g, c0 + kSeg * sg),
-                                grid_x(A.src.g, c0 + min(kSeg * sg + kSeg, cnt) - 1), yt, A.sc))
-            continue;  // every pair's exp2 flushes to 0
+          int pl, ph;
+          seg_pair_range<kSeg>(clo, chi, kSeg * sg, pl, ph);
+          if (pl >= ph) continue;  // every pair's exp2 flushes to 0
           const float o = seg_origin(A.src.g, c0, sg);
           float2 qx[kMvR], d2[kMvR];
 #pragma unroll
@@ -185,24 +188,28 @@ __device__ __forceinline__ void matvec_body(const MvArgs& A, int rb, int chunk, 
             d2[r] = f2(dy2[r], dy2[r]);
           }
 #pragma unroll
-          for (int pp = 0; pp < kSeg / 2; ++pp) {
-            const float4 Q = sP[buf][sg * (kSeg / 2) + pp];
-            const float2 W = f2(Q.z, Q.w);
-            const float2 nx = f2(Q.x, Q.y);
+          for (int qq = 0; qq < kSeg / 2; qq += kQuarterPairs) {
+            if (qq < pl || qq >= ph) continue;  // a quarter out of reach: exactly zero
 #pragma unroll
-            for (int r = 0; r < kMvR; ++r) {
-              const float2 dx = __fadd2_rn(qx[r], nx);
-              const float2 t = __ffma2_rn(dx, dx, d2[r]);
-              const float2 k = f2(ex2_approx(-t.x), ex2_approx(-t.y));
-              acc[r] = __ffma2_rn(k, W, acc[r]);
+            for (int pp = qq; pp < qq + kQuarterPairs; ++pp) {
+              const float4 Q = sP[buf][sg * (kSeg / 2) + pp];
+              const float2 W = f2(Q.z, Q.w);
+              const float2 nx = f2(Q.x, Q.y);
+#pragma unroll
+              for (int r = 0; r < kMvR; ++r) {
+                const float2 dx = __fadd2_rn(qx[r], nx);
+                const float2 t = __ffma2_rn(dx, dx, d2[r]);
+                const float2 k = f2(ex2_approx(-t.x), ex2_approx(-t.y));
+                acc[r] = __ffma2_rn(k, W, acc[r]);
+              }
             }
           }
         }
       } else {
         for (int sg = 0; sg < nsg; ++sg) {
-          if (A.info && seg_far(B, grid_x(A.src.g, c0 + kSeg * sg),
-                                grid_x(A.src.g, c0 + min(kSeg * sg + kSeg, cnt) - 1), yt, A.sc))
-            continue;  // every pair's exp2 flushes to 0
+          int pl, ph;
+          seg_pair_range<kSeg>(clo, chi, kSeg * sg, pl, ph);
+          if (pl >= ph) continue;  // every pair's exp2 flushes to 0
           const float o = seg_origin(A.src.g, c0, sg);
           float2 q2[kMvR], ar[kMvR];
 #pragma unroll
@@ -213,15 +220,19 @@ __device__ __forceinline__ void matvec_body(const MvArgs& A, int rb, int chunk, 
             ar[r] = f2(a, a);
           }
 #pragma unroll
-          for (int pp = 0; pp < kSeg / 2; ++pp) {
-            const float4 Q = sP[buf][sg * (kSeg / 2) + pp];
-            const float2 W = f2(Q.z, Q.w);
-            const float2 X = f2(Q.x, Q.y);
+          for (int qq = 0; qq < kSeg / 2; qq += kQuarterPairs) {
+            if (qq < pl || qq >= ph) continue;  // a quarter out of reach: exactly zero
 #pragma unroll
-            for (int r = 0; r < kMvR; ++r) {
-              const float2 e = __ffma2_rn(q2[r], X, ar[r]);
-              const float2 k = f2(ex2_approx(e.x), ex2_approx(e.y));
-              acc[r] = __ffma2_rn(k, W, acc[r]);
+            for (int pp = qq; pp < qq + kQuarterPairs; ++pp) {
+              const float4 Q = sP[buf][sg * (kSeg / 2) + pp];
+              const float2 W = f2(Q.z, Q.w);
+              const float2 X = f2(Q.x, Q.y);
+#pragma unroll
+              for (int r = 0; r < kMvR; ++r) {
+                const float2 e = __ffma2_rn(q2[r], X, ar[r]);
+                const float2 k = f2(ex2_approx(e.x), ex2_approx(e.y));
+                acc[r] = __ffma2_rn(k, W, acc[r]);
+              }
             }
           }
         }

@@ -190,10 +190,14 @@ __device__ __forceinline__ void bwd_rows_body(const BwArgs& A, int rb, int chunk
       }
       constexpr bool fuse_dv = DV;
       const int nsg = (cnt + kBwSeg - 1) / kBwSeg;
+      // columns of this grid row within reach of the row block (all without info)
+      int clo = 0, chi = cnt - 1;
+      if (A.info) reach_cols(B, A.src.g, yt, A.sc, c0, cnt, clo, chi);
       if (SPLIT) {
       for (int sg = 0; sg < nsg; ++sg) {
-        if (A.info && seg_far(B, grid_x(A.src.g, c0 + kBwSeg * sg),
-                              grid_x(A.src.g, c0 + min(kBwSeg * sg + kBwSeg, cnt) - 1), yt, A.sc)) {
+        int pl, ph;
+        seg_pair_range<kBwSeg>(clo, chi, kBwSeg * sg, pl, ph);
+        if (pl >= ph) {
           // every pair's exp2 flushes to 0: nothing to add, zero column sums
           if (fuse_dv && (tid & 31) < kBwSeg) sm.dvred[tid >> 5][sg * kBwSeg + (tid & 31)] = 0.f;
           continue;
@@ -217,23 +221,31 @@ __device__ __forceinline__ void bwd_rows_body(const BwArgs& A, int rb, int chunk
         }
         float kgs[kBwSeg];
 #pragma unroll
-        for (int pp = 0; pp < kBwSeg / 2; ++pp) {
-          const int p = sg * (kBwSeg / 2) + pp;
-          const float4 Q = sP[buf][p];
-          const float2 X = f2(Q.x, Q.y), W0 = f2(Q.z, Q.w);
-          const float2 W1 = sV[buf][p], W2 = sG[buf][p];
-          float2 kg = f2(0.f, 0.f);
+        for (int qq = 0; qq < kBwSeg / 2; qq += kQuarterPairs) {
+          if (qq < pl || qq >= ph) {  // a quarter out of reach: exactly zero
 #pragma unroll
-          for (int r = 0; r < kBwR; ++r) {
-            const float2 e = __ffma2_rn(q2[r], X, ar[r]);
-            const float2 k = f2(ex2_approx(e.x), ex2_approx(e.y));
-            S0[r] = __ffma2_rn(k, W0, S0[r]);
-            S1[r] = __ffma2_rn(k, W1, S1[r]);
-            S2[r] = __ffma2_rn(k, W2, S2[r]);
-            if (fuse_dv) kg = __ffma2_rn(k, gq[r], kg);
+            for (int c = 2 * qq; c < 2 * (qq + kQuarterPairs); ++c) kgs[c] = 0.f;
+            continue;
           }
-          kgs[2 * pp] = kg.x;
-          kgs[2 * pp + 1] = kg.y;
+#pragma unroll
+          for (int pp = qq; pp < qq + kQuarterPairs; ++pp) {
+            const int p = sg * (kBwSeg / 2) + pp;
+            const float4 Q = sP[buf][p];
+            const float2 X = f2(Q.x, Q.y), W0 = f2(Q.z, Q.w);
+            const float2 W1 = sV[buf][p], W2 = sG[buf][p];
+            float2 kg = f2(0.f, 0.f);
+#pragma unroll
+            for (int r = 0; r < kBwR; ++r) {
+              const float2 e = __ffma2_rn(q2[r], X, ar[r]);
+              const float2 k = f2(ex2_approx(e.x), ex2_approx(e.y));
+              S0[r] = __ffma2_rn(k, W0, S0[r]);
+              S1[r] = __ffma2_rn(k, W1, S1[r]);
+              S2[r] = __ffma2_rn(k, W2, S2[r]);
+              if (fuse_dv) kg = __ffma2_rn(k, gq[r], kg);
+            }
+            kgs[2 * pp] = kg.x;
+            kgs[2 * pp + 1] = kg.y;
+          }
         }
 #pragma unroll
         for (int r = 0; r < kBwR; ++r) {
@@ -247,8 +259,9 @@ __device__ __forceinline__ void bwd_rows_body(const BwArgs& A, int rb, int chunk
       }
       } else {
       for (int sg = 0; sg < nsg; ++sg) {
-        if (A.info && seg_far(B, grid_x(A.src.g, c0 + kBwSeg * sg),
-                              grid_x(A.src.g, c0 + min(kBwSeg * sg + kBwSeg, cnt) - 1), yt, A.sc)) {
+        int pl, ph;
+        seg_pair_range<kBwSeg>(clo, chi, kBwSeg * sg, pl, ph);
+        if (pl >= ph) {
           if (fuse_dv && (tid & 31) < kBwSeg) sm.dvred[tid >> 5][sg * kBwSeg + (tid & 31)] = 0.f;
           continue;
         }
@@ -261,25 +274,33 @@ __device__ __forceinline__ void bwd_rows_body(const BwArgs& A, int rb, int chunk
         }
         float kgs[kBwSeg];  // fused d_v: per-thread sums of k g over its rows, per source of the sub-segment
 #pragma unroll
-        for (int pp = 0; pp < kBwSeg / 2; ++pp) {
-          const int p = sg * (kBwSeg / 2) + pp;
-          const float4 Q = sP[buf][p];
-          const float2 W = sV[buf][p];
-          const float2 nx = f2(Q.x, Q.y);
-          float2 kg = f2(0.f, 0.f);
+        for (int qq = 0; qq < kBwSeg / 2; qq += kQuarterPairs) {
+          if (qq < pl || qq >= ph) {  // a quarter out of reach: exactly zero
 #pragma unroll
-          for (int r = 0; r < kBwR; ++r) {
-            const float2 dx = __fadd2_rn(qx[r], nx);
-            const float2 t = __ffma2_rn(dx, dx, dy2[r]);
-            const float2 k = f2(ex2_approx(-t.x), ex2_approx(-t.y));
-            const float2 kv = __fmul2_rn(k, W);
-            acc[r][0] = __fadd2_rn(acc[r][0], kv);
-            acc[r][1] = __ffma2_rn(kv, dx, acc[r][1]);
-            acc[r][3] = __ffma2_rn(kv, t, acc[r][3]);
-            if (fuse_dv) kg = __ffma2_rn(k, gq[r], kg);
+            for (int c = 2 * qq; c < 2 * (qq + kQuarterPairs); ++c) kgs[c] = 0.f;
+            continue;
           }
-          kgs[2 * pp] = kg.x;
-          kgs[2 * pp + 1] = kg.y;
+#pragma unroll
+          for (int pp = qq; pp < qq + kQuarterPairs; ++pp) {
+            const int p = sg * (kBwSeg / 2) + pp;
+            const float4 Q = sP[buf][p];
+            const float2 W = sV[buf][p];
+            const float2 nx = f2(Q.x, Q.y);
+            float2 kg = f2(0.f, 0.f);
+#pragma unroll
+            for (int r = 0; r < kBwR; ++r) {
+              const float2 dx = __fadd2_rn(qx[r], nx);
+              const float2 t = __ffma2_rn(dx, dx, dy2[r]);
+              const float2 k = f2(ex2_approx(-t.x), ex2_approx(-t.y));
+              const float2 kv = __fmul2_rn(k, W);
+              acc[r][0] = __fadd2_rn(acc[r][0], kv);
+              acc[r][1] = __ffma2_rn(kv, dx, acc[r][1]);
+              acc[r][3] = __ffma2_rn(kv, t, acc[r][3]);
+              if (fuse_dv) kg = __ffma2_rn(k, gq[r], kg);
+            }
+            kgs[2 * pp] = kg.x;
+            kgs[2 * pp + 1] = kg.y;
+          }
         }
         if (fuse_dv) warp_reduce_scatter(kgs, tid & 31, &sm.dvred[tid >> 5][sg * kBwSeg]);
       }
@@ -358,10 +379,202 @@ __device__ __forceinline__ void bwd_rows_body(const BwArgs& A, int rb, int chunk
   }
 }
 
+// ---------------------------------------------------------------------------
+// Row pass for grid sources with the split exponent and no fused d_v (the
+// training forward, and the backward's row gradients without d_v): the row
+// sums A, B_x, B_y, C of row block rb over one chunk of its active tiles.
+//
+// Moments about the row block's centre: with x_c the centre of the block's
+// box, q0 = sc (x_i - x_c) per row and, for a source of sub-segment s,
+// u = sc (x_j - x_c) = x' + delta_s (delta_s = sc (o_s - x_c)), a pair's
+// dx' = q0 - u. So over a whole tile
+//   A = S0, B_x = q0 S0 - S1, B_y = dy S0, C = (q0^2 + dy'^2) S0 - 2 q0 S1 + S2
+// with S0 = sum k~ v~, S1 = sum k~ v~ u, S2 = sum k~ v~ u^2. The exponent
+// keeps the sub-segment form 2 q_s x' + a_s (q_s = q0 - delta_s,
+// a_s = -(q_s^2 + dy'^2), |x'| <= 5.5), so every sub-segment adds into the
+// same packed sums and the conversion to A, B, C runs once per row and tile.
+// The per-tile sums are added plainly for kTrainFold tiles, then folded into
+// Kahan sums kept in shared memory.
+//
+// The form needs a compact row block: q0 and u stay small only when the
+// block's box is narrow (image-tile row order). A wider box (rows in index
+// order of scattered points) takes the per-sub-segment form (bwd_rows_body),
+// whose exponent and moments are all relative to the sub-segment centre.
+constexpr int kTrainFold = 4;
+constexpr float kTrainCompact = 8.f;  // widest box, in scaled units sc x width
+
+__device__ __forceinline__ bool train_compact(const BwArgs& A, int rb) {
+  if (!A.info) return false;
+  const RowBlockInfo& B = A.info[rb];
+  return !(B.xlo <= B.xhi) || (B.xhi - B.xlo) * A.sc <= kTrainCompact;
+}
+
+__device__ __forceinline__ void train_load_pair(const BwArgs& A, int t, int p, float xc, float4& P, float2& V,
+                                                float2& G) {
+  int64_t j0;
+  int cnt, grow;
+  bw_tile_range(A.src, t, j0, cnt, grow);
+  const int a = 2 * p, b = 2 * p + 1;
+  const int c0 = (int)(j0 - (int64_t)grow * A.src.g.W);
+  const float o = grid_x(A.src.g, c0 + kBwSeg * (a / kBwSeg) + kBwSeg / 2);
+  const float gxa = grid_x(A.src.g, c0 + a), gxb = grid_x(A.src.g, c0 + b);
+  const float xa = (a < cnt) ? A.sc * (gxa - o) : 0.f;
+  const float xb = (b < cnt) ? A.sc * (gxb - o) : 0.f;
+  const float va = (a < cnt) ? __ldg(A.v + j0 + a) * ex2_approx(-xa * xa) : 0.f;
+  const float vb = (b < cnt) ? __ldg(A.v + j0 + b) * ex2_approx(-xb * xb) : 0.f;
+  const float ua = A.sc * (gxa - xc), ub = A.sc * (gxb - xc);
+  P = make_float4(xa, xb, va, vb);
+  V = f2(va * ua, vb * ub);
+  G = f2(va * ua * ua, vb * ub * ub);
+}
+
+template <int R>
+__device__ __forceinline__ void train_rows_body(const BwArgs& A, int rb, int chunk, BwSmem<R, 4>& sm) {
+  constexpr int kRows = kBwThreads * R;
+  RowBlockInfo B{};
+  int lo = 0, hi = A.src.n_tiles;
+  float xc = 0.f;
+  if (A.info) {
+    B = A.info[rb];
+    lo = B.t_lo;
+    hi = B.t_hi > B.t_lo ? B.t_hi : B.t_lo;
+    if (B.xlo <= B.xhi) xc = 0.5f * (B.xlo + B.xhi);
+  }
+  const int t0 = lo + (int)((int64_t)chunk * (hi - lo) / A.chunks);
+  const int t1 = lo + (int)((int64_t)(chunk + 1) * (hi - lo) / A.chunks);
+  const int tid = threadIdx.x;
+  const float inv_sc = 1.0f / A.sc, inv_h = 1.0f / A.src.g.h;
+
+  float yq[R], q0[R], m2q0[R];
+  float acc[R][4];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int64_t ir = map_row(A.map, A.n, kRows, rb, r * kBwThreads + tid);
+    const float2 p = __ldg(A.x + (ir >= 0 ? ir : 0));  // padding rows compute on row 0 and are not written
+    yq[r] = p.y;
+    q0[r] = A.sc * (p.x - xc);
+    m2q0[r] = -2.f * q0[r];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      acc[r][k] = 0.f;
+      sm.ksum[r][k][tid] = 0.f;
+      sm.kcomp[r][k][tid] = 0.f;
+    }
+  }
+
+  float4 P;
+  float2 V, G;
+  if (t0 < t1) {
+    train_load_pair(A, t0, tid, xc, P, V, G);
+    sm.sP[0][tid] = P;
+    sm.sV[0][tid] = V;
+    sm.sG[0][tid] = G;
+  }
+  __syncthreads();
+
+  for (int t = t0; t < t1; ++t) {
+    const int buf = (t - t0) & 1;
+    if (t + 1 < t1) train_load_pair(A, t + 1, tid, xc, P, V, G);
+    int64_t j0;
+    int cnt, grow;
+    bw_tile_range(A.src, t, j0, cnt, grow);
+    const float yt = grid_y(A.src.g, grow);
+    const int c0 = (int)(j0 - (int64_t)grow * A.src.g.W);
+    // columns of this grid row within reach of the row block
+    int clo = 0, chi = cnt - 1;
+    if (A.info) reach_cols_fast(B, A.src.g, yt, A.sc, inv_sc, inv_h, c0, cnt, clo, chi);
+    float dyr[R], ndy2[R];
+    float2 S0[R], S1[R], S2[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      dyr[r] = yq[r] - yt;
+      const float d = A.sc * dyr[r];
+      ndy2[r] = -d * d;
+      S0[r] = S1[r] = S2[r] = f2(0.f, 0.f);
+    }
+    const int nsg = (cnt + kBwSeg - 1) / kBwSeg;
+    for (int sg = 0; sg < nsg; ++sg) {
+      int pl, ph;
+      seg_pair_range<kBwSeg>(clo, chi, kBwSeg * sg, pl, ph);
+      if (pl >= ph) continue;  // every pair's exp2 flushes to 0
+      const float ds = A.sc * (grid_x(A.src.g, c0 + kBwSeg * sg + kBwSeg / 2) - xc);  // delta_s
+      float2 q2[R], ar[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const float q = q0[r] - ds;
+        const float a = fmaf(-q, q, ndy2[r]);
+        q2[r] = f2(q + q, q + q);
+        ar[r] = f2(a, a);
+      }
+#pragma unroll
+      for (int qq = 0; qq < kBwSeg / 2; qq += kQuarterPairs) {
+        if (qq < pl || qq >= ph) continue;  // a quarter out of reach: exactly zero
+#pragma unroll
+        for (int pp = qq; pp < qq + kQuarterPairs; ++pp) {
+          const int p = sg * (kBwSeg / 2) + pp;
+          const float4 Q = sm.sP[buf][p];
+          const float2 X = f2(Q.x, Q.y), W0 = f2(Q.z, Q.w);
+          const float2 W1 = sm.sV[buf][p], W2 = sm.sG[buf][p];
+#pragma unroll
+          for (int r = 0; r < R; ++r) {
+            const float2 e = __ffma2_rn(q2[r], X, ar[r]);
+            const float2 k = f2(ex2_approx(e.x), ex2_approx(e.y));
+            S0[r] = __ffma2_rn(k, W0, S0[r]);
+            S1[r] = __ffma2_rn(k, W1, S1[r]);
+            S2[r] = __ffma2_rn(k, W2, S2[r]);
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const float s0 = S0[r].x + S0[r].y, s1 = S1[r].x + S1[r].y, s2 = S2[r].x + S2[r].y;
+      acc[r][0] += s0;
+      acc[r][1] += fmaf(q0[r], s0, -s1);
+      acc[r][2] = fmaf(dyr[r], s0, acc[r][2]);
+      acc[r][3] += fmaf(fmaf(q0[r], q0[r], -ndy2[r]), s0, fmaf(m2q0[r], s1, s2));
+    }
+    if ((t - t0) % kTrainFold == kTrainFold - 1 || t + 1 == t1) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          float su = sm.ksum[r][k][tid], co = sm.kcomp[r][k][tid];
+          kahan(su, co, acc[r][k]);
+          sm.ksum[r][k][tid] = su;
+          sm.kcomp[r][k][tid] = co;
+          acc[r][k] = 0.f;
+        }
+      }
+    }
+    if (t + 1 < t1) {
+      sm.sP[buf ^ 1][tid] = P;
+      sm.sV[buf ^ 1][tid] = V;
+      sm.sG[buf ^ 1][tid] = G;
+    }
+    __syncthreads();
+  }
+
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int64_t i = map_row(A.map, A.n, kRows, rb, r * kBwThreads + tid);
+    if (i >= 0) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) A.partial[((int64_t)chunk * 4 + k) * A.n + i] = sm.ksum[r][k][tid] - sm.kcomp[r][k][tid];
+    }
+  }
+}
+
 template <bool GRID, bool SELF, bool DV, bool SPLIT = false>
 __global__ void __launch_bounds__(kBwThreads) bwd_rows_kernel(const __grid_constant__ BwArgs A) {
   __shared__ __align__(16) typename BwCfg<GRID, SELF, DV>::Smem sm;
   const int rb = blockIdx.x / A.chunks;
+  if constexpr (GRID && !SELF && !DV && SPLIT) {
+    if (train_compact(A, rb)) {
+      train_rows_body<BwCfg<GRID, SELF, DV>::R>(A, rb, blockIdx.x - rb * A.chunks, sm);
+      return;
+    }
+  }
   bwd_rows_body<GRID, SELF, DV, SPLIT>(A, rb, blockIdx.x - rb * A.chunks, sm);
 }
 
@@ -374,6 +587,12 @@ __global__ void __launch_bounds__(kBwThreads) bwd_rows_batched_kernel(const __gr
   const BwArgs& A = B.p[k];
   const int local = blockIdx.x - B.start[k];
   const int rb = local / A.chunks;
+  if constexpr (GRID && !SELF && !DV && SPLIT) {
+    if (train_compact(A, rb)) {
+      train_rows_body<BwCfg<GRID, SELF, DV>::R>(A, rb, local - rb * A.chunks, sm);
+      return;
+    }
+  }
   bwd_rows_body<GRID, SELF, DV, SPLIT>(A, rb, local - rb * A.chunks, sm);
 }
 
@@ -417,6 +636,7 @@ __device__ __forceinline__ void dv_rows_body(const BwArgs& A, int rb, int chunk,
   const int t0 = lo + (int)((int64_t)chunk * (hi - lo) / A.chunks);
   const int t1 = lo + (int)((int64_t)(chunk + 1) * (hi - lo) / A.chunks);
   const int tid = threadIdx.x;
+  const float inv_sc = 1.0f / A.sc, inv_h = 1.0f / A.src.g.h;
   float xq[kDvR], yq[kDvR];
   float2 gq[kDvR];
 #pragma unroll
@@ -450,9 +670,13 @@ __device__ __forceinline__ void dv_rows_body(const BwArgs& A, int rb, int chunk,
       dy2[r] = d * d;
     }
     const int nsg = (cnt + kBwSeg - 1) / kBwSeg;
+    // columns of this grid row within reach of the row block (all without info)
+    int clo = 0, chi = cnt - 1;
+    if (A.info) reach_cols_fast(B, A.src.g, yt, A.sc, inv_sc, inv_h, c0, cnt, clo, chi);
     for (int sg = 0; sg < nsg; ++sg) {
-      if (A.info && seg_far(B, grid_x(A.src.g, c0 + kBwSeg * sg),
-                            grid_x(A.src.g, c0 + min(kBwSeg * sg + kBwSeg, cnt) - 1), yt, A.sc)) {
+      int pl, ph;
+      seg_pair_range<kBwSeg>(clo, chi, kBwSeg * sg, pl, ph);
+      if (pl >= ph) {
         // every pair's exp2 flushes to 0: zero column sums for this sub-segment
         if ((tid & 31) < kBwSeg) sm.dvred[tid >> 5][sg * kBwSeg + (tid & 31)] = 0.f;
         continue;
@@ -464,7 +688,7 @@ __device__ __forceinline__ void dv_rows_body(const BwArgs& A, int rb, int chunk,
         const float q = A.sc * (xq[r] - o);
         if (SPLIT) {
           const float a = -fmaf(q, q, dy2[r]);
-          qa[r] = f2(2.f * q, 2.f * q);
+          qa[r] = f2(q + q, q + q);
           qb[r] = f2(a, a);
         } else {
           qa[r] = f2(q, q);
@@ -473,24 +697,32 @@ __device__ __forceinline__ void dv_rows_body(const BwArgs& A, int rb, int chunk,
       }
       float kgs[kBwSeg];
 #pragma unroll
-      for (int pp = 0; pp < kBwSeg / 2; ++pp) {
-        const float2 Xp = sm.sX[buf][sg * (kBwSeg / 2) + pp];
-        float2 kg = f2(0.f, 0.f);
+      for (int qq = 0; qq < kBwSeg / 2; qq += kQuarterPairs) {
+        if (qq < pl || qq >= ph) {  // a quarter out of reach: exactly zero
 #pragma unroll
-        for (int r = 0; r < kDvR; ++r) {
-          float2 k;
-          if (SPLIT) {
-            const float2 e = __ffma2_rn(qa[r], Xp, qb[r]);
-            k = f2(ex2_approx(e.x), ex2_approx(e.y));
-          } else {
-            const float2 dx = __fadd2_rn(qa[r], Xp);
-            const float2 tt = __ffma2_rn(dx, dx, qb[r]);
-            k = f2(ex2_approx(-tt.x), ex2_approx(-tt.y));
-          }
-          kg = __ffma2_rn(k, gq[r], kg);
+          for (int c = 2 * qq; c < 2 * (qq + kQuarterPairs); ++c) kgs[c] = 0.f;
+          continue;
         }
-        kgs[2 * pp] = kg.x;
-        kgs[2 * pp + 1] = kg.y;
+#pragma unroll
+        for (int pp = qq; pp < qq + kQuarterPairs; ++pp) {
+          const float2 Xp = sm.sX[buf][sg * (kBwSeg / 2) + pp];
+          float2 kg = f2(0.f, 0.f);
+#pragma unroll
+          for (int r = 0; r < kDvR; ++r) {
+            float2 k;
+            if (SPLIT) {
+              const float2 e = __ffma2_rn(qa[r], Xp, qb[r]);
+              k = f2(ex2_approx(e.x), ex2_approx(e.y));
+            } else {
+              const float2 dx = __fadd2_rn(qa[r], Xp);
+              const float2 tt = __ffma2_rn(dx, dx, qb[r]);
+              k = f2(ex2_approx(-tt.x), ex2_approx(-tt.y));
+            }
+            kg = __ffma2_rn(k, gq[r], kg);
+          }
+          kgs[2 * pp] = kg.x;
+          kgs[2 * pp + 1] = kg.y;
+        }
       }
       warp_reduce_scatter(kgs, tid & 31, &sm.dvred[tid >> 5][sg * kBwSeg]);
     }
@@ -514,14 +746,14 @@ __device__ __forceinline__ void dv_rows_body(const BwArgs& A, int rb, int chunk,
 }
 
 template <bool SPLIT>
-__global__ void __launch_bounds__(kBwThreads) dv_rows_kernel(const __grid_constant__ BwArgs A) {
+__global__ void __launch_bounds__(kBwThreads, 5) dv_rows_kernel(const __grid_constant__ BwArgs A) {
   __shared__ __align__(16) DvSmem sm;
   const int rb = blockIdx.x / A.chunks;
   dv_rows_body<SPLIT>(A, rb, blockIdx.x - rb * A.chunks, sm);
 }
 
 template <bool SPLIT>
-__global__ void __launch_bounds__(kBwThreads) dv_rows_batched_kernel(const __grid_constant__ Batch<BwArgs> B) {
+__global__ void __launch_bounds__(kBwThreads, 5) dv_rows_batched_kernel(const __grid_constant__ Batch<BwArgs> B) {
   __shared__ __align__(16) DvSmem sm;
   const int k = batch_find(B, blockIdx.x);
   const BwArgs& A = B.p[k];
@@ -670,9 +902,24 @@ __device__ __forceinline__ void dv_merge_body(const DvMergeP& P, int64_t blk) {
       const int64_t r = j / P.W;
       t = (int)(r * P.segs + (j - r * P.W) / kBwTile);
     }
-    for (int rb = y; rb < P.row_blocks; rb += kDvMergeGroups) {
-      if (P.info && !(P.info[rb].t_lo <= t && t < P.info[rb].t_hi)) continue;
-      kahan(s, c, P.dv_part[(int64_t)rb * P.m + j]);
+    // eight row blocks' loads in flight at a time, added in the same order
+    constexpr int kBatch = 8;
+    for (int rb0 = y; rb0 < P.row_blocks; rb0 += kBatch * kDvMergeGroups) {
+      float val[kBatch];
+      bool act[kBatch];
+#pragma unroll
+      for (int k = 0; k < kBatch; ++k) {
+        const int rb = rb0 + k * kDvMergeGroups;
+        act[k] = rb < P.row_blocks;
+        if (act[k] && P.info) {
+          const int2 r = *reinterpret_cast<const int2*>(&P.info[rb].t_lo);
+          act[k] = r.x <= t && t < r.y;
+        }
+        val[k] = act[k] ? P.dv_part[(int64_t)rb * P.m + j] : 0.f;
+      }
+#pragma unroll
+      for (int k = 0; k < kBatch; ++k)
+        if (act[k]) kahan(s, c, val[k]);
     }
   }
   part[y][x] = s - c;

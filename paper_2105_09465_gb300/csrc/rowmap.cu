@@ -50,11 +50,12 @@ lr_status launch_row_info_batched(const RowInfoP* p, int count, cudaStream_t s) 
 namespace lr {
 
 // Pairs the grid-source kernels evaluate for one row-block layout: per row
-// block, its valid rows times the source columns of every sub-segment that
-// is inside the active tile range and not far (the kernels' own tests).
+// block, its valid rows times, over the active tile range, the source columns
+// of the source pairs that meet the reachable columns (the kernels' own
+// tests: reach_cols and seg_pair_range per sub-segment).
 __global__ void __launch_bounds__(kRowPrepThreads) pair_count_kernel(const float2* __restrict__ x, int64_t n,
                                                                      RowMap map, int rows_per_cta, GridDev g,
-                                                                     int32_t segs, int32_t tile, int32_t sub,
+                                                                     int32_t segs, int32_t tile,
                                                                      float sc, const RowBlockInfo* __restrict__ info,
                                                                      unsigned long long* __restrict__ count) {
   const int64_t rb = blockIdx.x;
@@ -66,9 +67,15 @@ __global__ void __launch_bounds__(kRowPrepThreads) pair_count_kernel(const float
     const int grow = t / segs, c0 = (t - grow * segs) * tile;
     const int cnt = min(tile, g.W - c0);
     const float y = grid_y(g, grow);
-    for (int s0 = 0; s0 < cnt; s0 += sub) {
-      const int e = min(s0 + sub, cnt) - 1;
-      if (!seg_far(B, grid_x(g, c0 + s0), grid_x(g, c0 + e), y, sc)) cols += (unsigned long long)(e - s0 + 1);
+    int lo, hi;
+    reach_cols(B, g, y, sc, c0, cnt, lo, hi);
+    for (int s0 = 0; s0 < cnt; s0 += kSplitSeg) {
+      int pl, ph;
+      seg_pair_range<kSplitSeg>(lo, hi, s0, pl, ph);
+      // the kernels evaluate source pairs pl .. ph - 1, whole quarters of the
+      // sub-segment (a pair past the tile's last column is padding and
+      // counts nothing)
+      if (pl < ph) cols += (unsigned long long)(min(s0 + 2 * ph, cnt) - (s0 + 2 * pl));
     }
   }
   for (int o = 16; o; o >>= 1) {
@@ -123,7 +130,7 @@ extern "C" lr_status lr_grid_pairs_evaluated(const float* x, int64_t n, const lr
     return st != LR_OK ? st : cuda_status(cudaGetLastError(), "cudaMemsetAsync");
   }
   pair_count_kernel<<<(unsigned)nb, kRowPrepThreads, 0, s>>>(reinterpret_cast<const float2*>(x), n, map,
-                                                              rows_per_cta, g, segs, 256, 16, sc, info, cnt);
+                                                              rows_per_cta, g, segs, 256, sc, info, cnt);
   unsigned long long h = 0;
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaMemcpyAsync(&h, cnt, sizeof h, cudaMemcpyDeviceToHost, s);

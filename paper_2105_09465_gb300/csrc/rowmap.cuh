@@ -72,6 +72,68 @@ __device__ __forceinline__ bool seg_far(const RowBlockInfo& B, float xa, float x
   return fmaf(sx, sx, sy * sy) > kSkipT;
 }
 
+// Tile-local columns [lo, hi] of a source grid row at ordinate y that can
+// hold a pair with sc^2 d^2 <= kSkipT for some point of the box: every column
+// outside is far from the whole box (so are all columns when the row itself is
+// out of reach: then lo > hi). The tile covers columns c0 .. c0 + cnt - 1.
+// The bound is computed in FP32; one column of margin on each side absorbs its
+// rounding, and the threshold's own 14-unit margin covers the kernels'
+// rounding of the distances.
+__device__ __forceinline__ void reach_cols(const RowBlockInfo& B, const GridDev& g, float y, float sc, int c0, int cnt,
+                                           int& lo, int& hi) {
+  lo = 0x3fffffff;
+  hi = -1;
+  if (!(B.xlo <= B.xhi)) return;  // a row block without rows
+  const float dy = fmaxf(fmaxf(B.ylo - y, y - B.yhi), 0.f);
+  const float sy = sc * dy;
+  const float rem = kSkipT - sy * sy;
+  if (!(rem > 0.f)) return;
+  const float w = sqrtf(rem) / sc;  // reach along the row
+  const float cl = (B.xlo - w - g.cx) / g.h + g.c0x;
+  const float ch = (B.xhi + w - g.cx) / g.h + g.c0x;
+  // clamp in float first: the bounds can be far outside the int range
+  const float fl = fmaxf(floorf(cl) - 1.0f - (float)c0, 0.0f);
+  const float fh = fminf(ceilf(ch) + 1.0f - (float)c0, (float)(cnt - 1));
+  if (!(fl <= fh)) return;
+  lo = (int)fl;
+  hi = (int)fh;
+}
+
+// reach_cols with the divisions replaced by the reciprocals inv_sc = 1/sc and
+// inv_h = 1/h (their extra rounding is far inside the one-column margin).
+__device__ __forceinline__ void reach_cols_fast(const RowBlockInfo& B, const GridDev& g, float y, float sc,
+                                                float inv_sc, float inv_h, int c0, int cnt, int& lo, int& hi) {
+  lo = 0x3fffffff;
+  hi = -1;
+  if (!(B.xlo <= B.xhi)) return;  // a row block without rows
+  const float dy = fmaxf(fmaxf(B.ylo - y, y - B.yhi), 0.f);
+  const float sy = sc * dy;
+  const float rem = kSkipT - sy * sy;
+  if (!(rem > 0.f)) return;
+  const float w = sqrtf(rem) * inv_sc;  // reach along the row
+  const float cl = fmaf(B.xlo - w - g.cx, inv_h, g.c0x);
+  const float ch = fmaf(B.xhi + w - g.cx, inv_h, g.c0x);
+  const float fl = fmaxf(floorf(cl) - 1.0f - (float)c0, 0.0f);
+  const float fh = fminf(ceilf(ch) + 1.0f - (float)c0, (float)(cnt - 1));
+  if (!(fl <= fh)) return;
+  lo = (int)fl;
+  hi = (int)fh;
+}
+
+// The source pairs [pp_lo, pp_hi) of the sub-segment that starts at tile-local
+// column s0 (pair p = columns s0 + 2p, s0 + 2p + 1; SEG / 2 pairs) that meet
+// the reachable columns [lo, hi], widened to whole quarters of the
+// sub-segment (2 pairs, 4 columns): the kernels evaluate a quarter or skip
+// it as a block. Empty when pp_lo >= pp_hi.
+constexpr int kQuarterPairs = 2;
+
+template <int SEG>
+__device__ __forceinline__ void seg_pair_range(int lo, int hi, int s0, int& pp_lo, int& pp_hi) {
+  const int a = lo - s0, b = hi - s0;
+  pp_lo = a <= 0 ? 0 : (a >> 1) & ~(kQuarterPairs - 1);
+  pp_hi = b < 0 ? 0 : min(SEG / 2, ((b >> 1) + kQuarterPairs) & ~(kQuarterPairs - 1));
+}
+
 // One CTA (kRowPrepThreads) per row block: bounding box of its rows and the
 // active source-tile range (grid rows whose whole abscissa range is not far).
 constexpr int kRowPrepThreads = 128;
