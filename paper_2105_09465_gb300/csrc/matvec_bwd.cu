@@ -445,7 +445,7 @@ __device__ __forceinline__ void train_rows_body(const BwArgs& A, int rb, int chu
   const int tid = threadIdx.x;
   const float inv_sc = 1.0f / A.sc, inv_h = 1.0f / A.src.g.h;
 
-  float yq[R], q0[R], m2q0[R];
+  float yq[R], q0[R];
   float acc[R][4];
 #pragma unroll
   for (int r = 0; r < R; ++r) {
@@ -453,7 +453,6 @@ __device__ __forceinline__ void train_rows_body(const BwArgs& A, int rb, int chu
     const float2 p = __ldg(A.x + (ir >= 0 ? ir : 0));  // padding rows compute on row 0 and are not written
     yq[r] = p.y;
     q0[r] = A.sc * (p.x - xc);
-    m2q0[r] = -2.f * q0[r];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       acc[r][k] = 0.f;
@@ -532,7 +531,7 @@ __device__ __forceinline__ void train_rows_body(const BwArgs& A, int rb, int chu
       acc[r][0] += s0;
       acc[r][1] += fmaf(q0[r], s0, -s1);
       acc[r][2] = fmaf(dyr[r], s0, acc[r][2]);
-      acc[r][3] += fmaf(fmaf(q0[r], q0[r], -ndy2[r]), s0, fmaf(m2q0[r], s1, s2));
+      acc[r][3] += fmaf(fmaf(q0[r], q0[r], -ndy2[r]), s0, fmaf(-2.f * q0[r], s1, s2));
     }
     if ((t - t0) % kTrainFold == kTrainFold - 1 || t + 1 == t1) {
 #pragma unroll
@@ -565,8 +564,15 @@ __device__ __forceinline__ void train_rows_body(const BwArgs& A, int rb, int chu
   }
 }
 
+// Resident CTAs per SM the compiler must leave room for: the training
+// forward's row pass is latency-bound at 4, so its registers are capped for 5.
+template <bool GRID, bool SELF, bool DV, bool SPLIT>
+constexpr int bw_min_blocks() {
+  return (GRID && !SELF && !DV && SPLIT) ? 5 : 1;
+}
+
 template <bool GRID, bool SELF, bool DV, bool SPLIT = false>
-__global__ void __launch_bounds__(kBwThreads) bwd_rows_kernel(const __grid_constant__ BwArgs A) {
+__global__ void __launch_bounds__(kBwThreads, (bw_min_blocks<GRID, SELF, DV, SPLIT>())) bwd_rows_kernel(const __grid_constant__ BwArgs A) {
   __shared__ __align__(16) typename BwCfg<GRID, SELF, DV>::Smem sm;
   const int rb = blockIdx.x / A.chunks;
   if constexpr (GRID && !SELF && !DV && SPLIT) {
@@ -581,7 +587,8 @@ __global__ void __launch_bounds__(kBwThreads) bwd_rows_kernel(const __grid_const
 // Batched form; every problem of one launch has the same kind (grid with or
 // without the split exponent and fused d_v, explicit, explicit self-kernel).
 template <bool GRID, bool SELF, bool DV, bool SPLIT = false>
-__global__ void __launch_bounds__(kBwThreads) bwd_rows_batched_kernel(const __grid_constant__ Batch<BwArgs> B) {
+__global__ void __launch_bounds__(kBwThreads, (bw_min_blocks<GRID, SELF, DV, SPLIT>()))
+    bwd_rows_batched_kernel(const __grid_constant__ Batch<BwArgs> B) {
   __shared__ __align__(16) typename BwCfg<GRID, SELF, DV>::Smem sm;
   const int k = batch_find(B, blockIdx.x);
   const BwArgs& A = B.p[k];
