@@ -23,6 +23,18 @@ int* fault_ptr();
 void ktimer_begin(int id, cudaStream_t s);
 void ktimer_end(int id, cudaStream_t s);
 
+// Fork and join: fork_begin makes a per-device side stream wait for the work
+// enqueued on s so far (f->side is s itself when no side stream exists);
+// fork_end makes s wait for the side stream's work since. Under stream
+// capture the two become graph edges. Every fork_begin that returned LR_OK
+// must be followed by fork_end, also on error paths.
+struct Fork {
+  cudaStream_t side;
+  cudaEvent_t join;
+};
+lr_status fork_begin(cudaStream_t s, Fork* f);
+lr_status fork_end(cudaStream_t s, Fork* f);
+
 // Streams cross the ABI as lr_stream (an opaque CUstream_st*).
 inline cudaStream_t as_cuda(lr_stream s) { return reinterpret_cast<cudaStream_t>(s); }
 

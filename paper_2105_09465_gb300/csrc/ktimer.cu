@@ -118,3 +118,48 @@ extern "C" lr_status lr_kernel_timer_read(int32_t kernel, int64_t* launches, dou
   if (dropped) *dropped = g_dropped;
   return LR_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Fork and join of a second stream for independent branches of one entry
+// point (see common.cuh). The side stream is per device and non-blocking;
+// the events are per call, so concurrent callers never share one.
+namespace lr {
+
+cudaStream_t side_stream() {
+  static std::mutex mu;
+  static cudaStream_t streams[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lk(mu);
+  if (!streams[dev] && cudaStreamCreateWithFlags(&streams[dev], cudaStreamNonBlocking) != cudaSuccess)
+    streams[dev] = nullptr;
+  return streams[dev];
+}
+
+lr_status fork_begin(cudaStream_t s, Fork* f) {
+  f->side = s;
+  f->join = nullptr;
+  cudaStream_t side = side_stream();
+  if (!side) return LR_OK;  // no second stream: the branch runs on s
+  cudaEvent_t e = nullptr;
+  LR_CHECK_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  cudaError_t r = cudaEventRecord(e, s);
+  if (r == cudaSuccess) r = cudaStreamWaitEvent(side, e, 0);
+  cudaEventDestroy(e);
+  if (r != cudaSuccess) return cuda_status(r, "fork_begin");
+  LR_CHECK_CUDA(cudaEventCreateWithFlags(&f->join, cudaEventDisableTiming));
+  f->side = side;
+  return LR_OK;
+}
+
+lr_status fork_end(cudaStream_t s, Fork* f) {
+  if (!f->join) return LR_OK;
+  cudaError_t r = cudaEventRecord(f->join, f->side);
+  if (r == cudaSuccess) r = cudaStreamWaitEvent(s, f->join, 0);
+  cudaEventDestroy(f->join);
+  f->join = nullptr;
+  f->side = s;
+  return r == cudaSuccess ? LR_OK : cuda_status(r, "fork_end");
+}
+
+}  // namespace lr

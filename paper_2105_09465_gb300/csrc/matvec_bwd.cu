@@ -891,52 +891,73 @@ __global__ void __launch_bounds__(kMergeThreads) scalar_batched_kernel(const __g
 }
 
 // d_v merge: a CTA of kDvMergeCols x kDvMergeGroups threads takes
-// kDvMergeCols consecutive sources; thread group y sums the row blocks
-// y, y + kDvMergeGroups, ... (Kahan), and the groups' sums are added in
-// group order, so the result is deterministic. With row-block info, a row
-// block wrote source j only when j's tile is in its active range; elsewhere
-// its sum is exactly 0 and is not read.
-constexpr int kDvMergeCols = 32, kDvMergeGroups = 8;
+// kDvMergeCols consecutive sources of one source grid row (one tile). With
+// row-block info a row block wrote this tile only when the tile is in its
+// active range (elsewhere its sums are exactly 0 and are not read), so warp 0
+// first lists the active row blocks in ascending order in shared memory
+// (kDvMergeList at a time). Thread group y then sums list entries y,
+// y + kDvMergeGroups, ... (Kahan, four loads in flight), and the groups' sums
+// are added in group order: the result is deterministic.
+constexpr int kDvMergeCols = 32, kDvMergeGroups = 8, kDvMergeList = 2048;
 
 __device__ __forceinline__ void dv_merge_body(const DvMergeP& P, int64_t blk) {
   __shared__ float part[kDvMergeGroups][kDvMergeCols];
+  __shared__ int list[kDvMergeList];
+  __shared__ int count_sh;
   const int x = threadIdx.x % kDvMergeCols, y = threadIdx.x / kDvMergeCols;
-  const int64_t j = blk * kDvMergeCols + x;
-  float s = 0.f, c = 0.f;
-  if (j < P.m) {
-    int t = 0;
-    if (P.info) {
-      const int64_t r = j / P.W;
-      t = (int)(r * P.segs + (j - r * P.W) / kBwTile);
-    }
-    // eight row blocks' loads in flight at a time, added in the same order
-    constexpr int kBatch = 8;
-    for (int rb0 = y; rb0 < P.row_blocks; rb0 += kBatch * kDvMergeGroups) {
-      float val[kBatch];
-      bool act[kBatch];
-#pragma unroll
-      for (int k = 0; k < kBatch; ++k) {
-        const int rb = rb0 + k * kDvMergeGroups;
-        act[k] = rb < P.row_blocks;
-        if (act[k] && P.info) {
-          const int2 r = *reinterpret_cast<const int2*>(&P.info[rb].t_lo);
-          act[k] = r.x <= t && t < r.y;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int cw = (P.W + kDvMergeCols - 1) / kDvMergeCols;  // column chunks per grid row
+  const int64_t r = blk / cw;
+  const int c = (int)(blk - r * cw) * kDvMergeCols + x;
+  const bool valid = c < P.W;
+  const int64_t j = r * P.W + c;
+  const int t = (int)(r * P.segs + ((int64_t)(blk - r * cw) * kDvMergeCols) / kBwTile);
+  float s = 0.f, cc = 0.f;
+  for (int base = 0; base < P.row_blocks; base += kDvMergeList) {
+    const int nb = min(kDvMergeList, P.row_blocks - base);
+    if (warp == 0) {
+      int count = 0;
+      for (int b0 = 0; b0 < nb; b0 += 32) {
+        const int rb = base + b0 + lane;
+        bool act = b0 + lane < nb;
+        if (act && P.info) {
+          const int2 rr = *reinterpret_cast<const int2*>(&P.info[rb].t_lo);
+          act = rr.x <= t && t < rr.y;
         }
-        val[k] = act[k] ? P.dv_part[(int64_t)rb * P.m + j] : 0.f;
+        const unsigned m = __ballot_sync(0xffffffffu, act);
+        if (act) list[count + __popc(m & ((1u << lane) - 1u))] = rb;
+        count += __popc(m);
       }
-#pragma unroll
-      for (int k = 0; k < kBatch; ++k)
-        if (act[k]) kahan(s, c, val[k]);
+      if (lane == 0) count_sh = count;
     }
-  }
-  part[y][x] = s - c;
-  __syncthreads();
-  if (y == 0 && j < P.m) {
-    float t = 0.f, cc = 0.f;
+    __syncthreads();
+    const int count = count_sh;
+    if (valid) {
+      int i = y;
+      for (; i + 3 * kDvMergeGroups < count; i += 4 * kDvMergeGroups) {
+        float v[4];
 #pragma unroll
-    for (int k = 0; k < kDvMergeGroups; ++k) kahan(t, cc, part[k][x]);
-    P.d_v[j] = P.var * (t - cc);
+        for (int k = 0; k < 4; ++k) v[k] = P.dv_part[(int64_t)list[i + k * kDvMergeGroups] * P.m + j];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) kahan(s, cc, v[k]);
+      }
+      for (; i < count; i += kDvMergeGroups) kahan(s, cc, P.dv_part[(int64_t)list[i] * P.m + j]);
+    }
+    __syncthreads();  // the list is rewritten for the next window
   }
+  part[y][x] = s - cc;
+  __syncthreads();
+  if (y == 0 && valid) {
+    float a = 0.f, ca = 0.f;
+#pragma unroll
+    for (int k = 0; k < kDvMergeGroups; ++k) kahan(a, ca, part[k][x]);
+    P.d_v[j] = P.var * (a - ca);
+  }
+}
+
+// CTAs of the d_v merge: one per source grid row and kDvMergeCols columns.
+inline int64_t dv_merge_blocks(const DvMergeP& P) {
+  return P.W > 0 ? P.m / P.W * ((P.W + kDvMergeCols - 1) / kDvMergeCols) : 0;
 }
 
 __global__ void __launch_bounds__(kDvMergeCols * kDvMergeGroups) dv_merge_kernel(const __grid_constant__ DvMergeP P) {
@@ -957,7 +978,7 @@ lr_status launch_dv_merge_batched(const DvMergeP* p, int count, cudaStream_t s) 
     for (int k = 0; k < B.count; ++k) {
       B.p[k] = p[b0 + k];
       B.start[k] = (int32_t)tot;
-      tot += (p[b0 + k].m + kDvMergeCols - 1) / kDvMergeCols;
+      tot += dv_merge_blocks(p[b0 + k]);
     }
     B.start[B.count] = (int32_t)tot;
     if (tot == 0) continue;
@@ -1271,7 +1292,7 @@ static lr_status launch_rows(const float2* x, int64_t n, const lr_grid* qgrid, c
       LR_CHECK_CUDA(cudaGetLastError());
     }
     if (A.dv_part) {
-      dv_merge_kernel<<<(unsigned)((m + kDvMergeCols - 1) / kDvMergeCols), kDvMergeCols * kDvMergeGroups, 0, s>>>(D);
+      dv_merge_kernel<<<(unsigned)dv_merge_blocks(D), kDvMergeCols * kDvMergeGroups, 0, s>>>(D);
       LR_CHECK_CUDA(cudaGetLastError());
     }
     return LR_OK;
@@ -1435,7 +1456,7 @@ static lr_status launch_dv(const float2* x, int64_t n, const lr_grid* qgrid, con
     dv_rows_kernel<false><<<grid, kBwThreads, 0, s>>>(A);
   LR_CHECK_CUDA(cudaGetLastError());
   ktimer_end(LR_KT_DV_ROWS, s);
-  dv_merge_kernel<<<(unsigned)((D.m + kDvMergeCols - 1) / kDvMergeCols), kDvMergeCols * kDvMergeGroups, 0, s>>>(D);
+  dv_merge_kernel<<<(unsigned)dv_merge_blocks(D), kDvMergeCols * kDvMergeGroups, 0, s>>>(D);
   LR_CHECK_CUDA(cudaGetLastError());
   return LR_OK;
 }
@@ -1618,16 +1639,27 @@ extern "C" lr_status gp_kernel_matvec_bwd(const lr_points* query, const lr_point
   const lr_grid* qgrid = query_layout(query);
   float2* dx = P.need_dx ? (G.d_x ? reinterpret_cast<float2*>(G.d_x) : reinterpret_cast<float2*>(ws + P.off_dx))
                          : nullptr;
+  if (P.moments && P.s_grid) {
+    // grid sources with the training forward's moments: the row gradients
+    // (then the ray-trace VJP) and d_v from the d_v-only sweep are
+    // independent branches; the d_v one runs on a side stream so that the
+    // two overlap
+    Fork f{};
+    const bool side = G.d_v != nullptr;
+    if (side && (st = fork_begin(s, &f)) != LR_OK) return st;
+    if (side) st = launch_dv(xq, P.n, qgrid, yg, g_out, lengthscale, variance, G.d_v, ws + P.off_dv, f.side);
+    if (st == LR_OK)
+      st = launch_moment_rows(G.moments_in, P.n, true, g_out, v, lengthscale, variance, dx, G.d_lengthscale,
+                              G.d_variance, ws + P.off_rows, s);
+    if (st == LR_OK && P.want_lens) st = launch_raytrace_vjp(query, dx, G.d_lens, G.d_sub, ws + P.off_vjp, s);
+    const lr_status sj = side ? fork_end(s, &f) : LR_OK;
+    return st != LR_OK ? st : sj;
+  }
   if (P.moments) {
-    // row gradients from the training forward's moments; d_v of grid sources
-    // from the d_v-only sweep
+    // row gradients from the training forward's moments
     st = launch_moment_rows(G.moments_in, P.n, P.s_grid, g_out, v, lengthscale, variance, dx, G.d_lengthscale,
                             G.d_variance, ws + P.off_rows, s);
     if (st != LR_OK) return st;
-    if (P.s_grid && G.d_v) {
-      st = launch_dv(xq, P.n, qgrid, yg, g_out, lengthscale, variance, G.d_v, ws + P.off_dv, s);
-      if (st != LR_OK) return st;
-    }
   } else {
     // row pass: d_x (both roles for a self-kernel), self d_v, d_l, d_var
     st = launch_rows(xq, P.n, qgrid, ys, yg, P.m, v, P.self ? g_out : nullptr, g_out, v, lengthscale, variance, P.self,

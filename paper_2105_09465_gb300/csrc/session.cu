@@ -252,12 +252,19 @@ lr_status run_iteration(lr_session* S, const std::vector<Req*>& act) {
   if ((st = launch_bwd_rows_batched(train.data(), n, s)) != LR_OK) return st;
   if ((st = launch_moments_merge_batched(tmerge.data(), n, s)) != LR_OK) return st;
   if ((st = launch_axpy_batched(resid.data(), n, s)) != LR_OK) return st;
-  if ((st = launch_bwd_merge_batched(mrows.data(), n, s)) != LR_OK) return st;
-  if ((st = launch_scalar_batched(scal.data(), n, s)) != LR_OK) return st;
-  if ((st = launch_dv_rows_batched(dvs.data(), n, s)) != LR_OK) return st;
-  if ((st = launch_dv_merge_batched(dvm.data(), n, s)) != LR_OK) return st;
-  if ((st = launch_vjp_batched(vjp.data(), n, s)) != LR_OK) return st;
-  if ((st = launch_vjp_final_batched(vfin.data(), n, s)) != LR_OK) return st;
+  // d_v (side stream) and the row gradients with the ray-trace VJP are
+  // independent branches; the update waits for both
+  Fork f{};
+  if ((st = fork_begin(s, &f)) != LR_OK) return st;
+  st = launch_dv_rows_batched(dvs.data(), n, f.side);
+  if (st == LR_OK) st = launch_dv_merge_batched(dvm.data(), n, f.side);
+  if (st == LR_OK) st = launch_bwd_merge_batched(mrows.data(), n, s);
+  if (st == LR_OK) st = launch_scalar_batched(scal.data(), n, s);
+  if (st == LR_OK) st = launch_vjp_batched(vjp.data(), n, s);
+  if (st == LR_OK) st = launch_vjp_final_batched(vfin.data(), n, s);
+  const lr_status sj = fork_end(s, &f);
+  if (st != LR_OK) return st;
+  if (sj != LR_OK) return sj;
   if ((st = launch_axpy_batched(upd.data(), n, s)) != LR_OK) return st;
   const int groups = (n + kMaxBatch - 1) / kMaxBatch;
   S->launches += (uint64_t)groups * 11 + (uint64_t)((2 * n + kMaxBatch - 1) / kMaxBatch);

@@ -106,3 +106,37 @@ def test_deterministic_and_self_kernel_rejected():
     with pytest.raises(abi.LensGPError, match="non-self"):
         api.gp_kernel_matvec_bwd(api.Points(xy=x), None, dev(np.ones(8)), 0.1, 1.0, dev(np.ones(8)),
                                  moments=torch.zeros((4, 8), device="cuda"))
+
+
+def test_graph_capture_matches_direct_launches():
+    """The training step captured into a CUDA graph (the backward forks its
+    d_v branch onto a side stream) gives the bits of direct launches."""
+    p = W.realistic(seed=5, side=96, ss=2, n_sub=30, ygrid_side=48)
+    sub = torch.from_numpy(p.sub).cuda()
+    q, s = api.Points(grid=p.xgrid, lens=p.lens, sub=sub), api.Points(grid=p.ygrid)
+    v = torch.from_numpy(p.v).cuda()
+    g = torch.from_numpy(np.random.default_rng(3).standard_normal(p.n).astype(np.float32)).cuda()
+    want = ["v", "lengthscale", "variance", "lens", "sub"]
+    out = torch.empty(p.n, dtype=torch.float32, device="cuda")
+    beta = torch.empty((p.n, 2), dtype=torch.float32, device="cuda")
+    mom = torch.empty((4, p.n), dtype=torch.float32, device="cuda")
+    ws = torch.empty(max(api.train_workspace_size(q, s), 1), dtype=torch.uint8, device="cuda")
+
+    def step():
+        api.gp_kernel_matvec_train(q, s, v, p.lengthscale, p.variance, out=out, beta=beta, moments=mom, workspace=ws)
+        return api.gp_kernel_matvec_bwd(q, s, v, p.lengthscale, p.variance, g, want=want, beta=beta, moments=mom)
+
+    ref = {k: t.clone() for k, t in step().items()}
+    ref_out = out.clone()
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        G = step()
+    out.zero_()
+    for t in G.values():
+        t.zero_()
+    graph.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(out, ref_out)
+    for k in want:
+        assert torch.equal(G[k], ref[k]), k
