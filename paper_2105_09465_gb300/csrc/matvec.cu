@@ -170,12 +170,14 @@ __device__ __forceinline__ void matvec_body(const MvArgs& A, int rb, int chunk, 
         dy2[r] = dy * dy;
       }
       const int nsg = (cnt + kSeg - 1) / kSeg;
-      // columns of this grid row within reach of the row block (all without info)
+      // columns of this grid row within reach of the row block (all without
+      // info), and the sub-segments that meet them
       int clo = 0, chi = cnt - 1;
       if (A.info) reach_cols(B, A.src.g, yt, A.sc, c0, cnt, clo, chi);
+      const int sg_lo = clo <= chi ? clo / kSeg : nsg, sg_hi = clo <= chi ? chi / kSeg : -1;
       if (!A.split) {
         // unsplit: dx' = q - x', exponent -(dx'^2 + dy'^2)
-        for (int sg = 0; sg < nsg; ++sg) {
+        for (int sg = sg_lo; sg <= sg_hi; ++sg) {
           int pl, ph;
           seg_pair_range<kSeg>(clo, chi, kSeg * sg, pl, ph);
           if (pl >= ph) continue;  // every pair's exp2 flushes to 0
@@ -206,7 +208,7 @@ __device__ __forceinline__ void matvec_body(const MvArgs& A, int rb, int chunk, 
           }
         }
       } else {
-        for (int sg = 0; sg < nsg; ++sg) {
+        for (int sg = sg_lo; sg <= sg_hi; ++sg) {
           int pl, ph;
           seg_pair_range<kSeg>(clo, chi, kSeg * sg, pl, ph);
           if (pl >= ph) continue;  // every pair's exp2 flushes to 0

@@ -190,11 +190,13 @@ __device__ __forceinline__ void bwd_rows_body(const BwArgs& A, int rb, int chunk
       }
       constexpr bool fuse_dv = DV;
       const int nsg = (cnt + kBwSeg - 1) / kBwSeg;
-      // columns of this grid row within reach of the row block (all without info)
+      // columns of this grid row within reach of the row block (all without
+      // info), and the sub-segments that meet them
       int clo = 0, chi = cnt - 1;
       if (A.info) reach_cols(B, A.src.g, yt, A.sc, c0, cnt, clo, chi);
+      const int sg_lo = clo <= chi ? clo / kBwSeg : nsg, sg_hi = clo <= chi ? chi / kBwSeg : -1;
       if (SPLIT) {
-      for (int sg = 0; sg < nsg; ++sg) {
+      for (int sg = sg_lo; sg <= sg_hi; ++sg) {
         int pl, ph;
         seg_pair_range<kBwSeg>(clo, chi, kBwSeg * sg, pl, ph);
         if (pl >= ph) {
@@ -258,7 +260,7 @@ __device__ __forceinline__ void bwd_rows_body(const BwArgs& A, int rb, int chunk
         if (fuse_dv) warp_reduce_scatter(kgs, tid & 31, &sm.dvred[tid >> 5][sg * kBwSeg]);
       }
       } else {
-      for (int sg = 0; sg < nsg; ++sg) {
+      for (int sg = sg_lo; sg <= sg_hi; ++sg) {
         int pl, ph;
         seg_pair_range<kBwSeg>(clo, chi, kBwSeg * sg, pl, ph);
         if (pl >= ph) {
@@ -307,9 +309,14 @@ __device__ __forceinline__ void bwd_rows_body(const BwArgs& A, int rb, int chunk
       }
       if (fuse_dv) {
         __syncthreads();
-        // combine the warps in order; row block rb owns these columns of dv_part
+        // combine the warps in order; row block rb owns these columns of
+        // dv_part (exact zeros outside the sub-segments in reach)
         float* dst = A.dv_part + (int64_t)rb * A.src.m + j0;
         for (int j = tid; j < cnt; j += kBwThreads) {
+          if (j < sg_lo * kBwSeg || j >= (sg_hi + 1) * kBwSeg) {
+            dst[j] = 0.f;
+            continue;
+          }
           float sdv = sm.dvred[0][j];
 #pragma unroll
           for (int w = 1; w < kBwThreads / 32; ++w) sdv += sm.dvred[w][j];
@@ -479,7 +486,8 @@ __device__ __forceinline__ void train_rows_body(const BwArgs& A, int rb, int chu
     bw_tile_range(A.src, t, j0, cnt, grow);
     const float yt = grid_y(A.src.g, grow);
     const int c0 = (int)(j0 - (int64_t)grow * A.src.g.W);
-    // columns of this grid row within reach of the row block
+    // columns of this grid row within reach of the row block, and the
+    // sub-segments that meet them
     int clo = 0, chi = cnt - 1;
     if (A.info) reach_cols_fast(B, A.src.g, yt, A.sc, inv_sc, inv_h, c0, cnt, clo, chi);
     float dyr[R], ndy2[R];
@@ -492,7 +500,8 @@ __device__ __forceinline__ void train_rows_body(const BwArgs& A, int rb, int chu
       S0[r] = S1[r] = S2[r] = f2(0.f, 0.f);
     }
     const int nsg = (cnt + kBwSeg - 1) / kBwSeg;
-    for (int sg = 0; sg < nsg; ++sg) {
+    const int sg_lo = clo <= chi ? clo / kBwSeg : nsg, sg_hi = clo <= chi ? chi / kBwSeg : -1;
+    for (int sg = sg_lo; sg <= sg_hi; ++sg) {
       int pl, ph;
       seg_pair_range<kBwSeg>(clo, chi, kBwSeg * sg, pl, ph);
       if (pl >= ph) continue;  // every pair's exp2 flushes to 0
@@ -677,10 +686,12 @@ __device__ __forceinline__ void dv_rows_body(const BwArgs& A, int rb, int chunk,
       dy2[r] = d * d;
     }
     const int nsg = (cnt + kBwSeg - 1) / kBwSeg;
-    // columns of this grid row within reach of the row block (all without info)
+    // columns of this grid row within reach of the row block (all without
+    // info), and the sub-segments that meet them
     int clo = 0, chi = cnt - 1;
     if (A.info) reach_cols_fast(B, A.src.g, yt, A.sc, inv_sc, inv_h, c0, cnt, clo, chi);
-    for (int sg = 0; sg < nsg; ++sg) {
+    const int sg_lo = clo <= chi ? clo / kBwSeg : nsg, sg_hi = clo <= chi ? chi / kBwSeg : -1;
+    for (int sg = sg_lo; sg <= sg_hi; ++sg) {
       int pl, ph;
       seg_pair_range<kBwSeg>(clo, chi, kBwSeg * sg, pl, ph);
       if (pl >= ph) {
@@ -734,9 +745,14 @@ __device__ __forceinline__ void dv_rows_body(const BwArgs& A, int rb, int chunk,
       warp_reduce_scatter(kgs, tid & 31, &sm.dvred[tid >> 5][sg * kBwSeg]);
     }
     __syncthreads();
-    // combine the warps in order; row block rb owns these columns of dv_part
+    // combine the warps in order; row block rb owns these columns of
+    // dv_part (exact zeros outside the sub-segments in reach)
     float* dst = A.dv_part + (int64_t)rb * A.src.m + j0;
     for (int j = tid; j < cnt; j += kBwThreads) {
+      if (j < sg_lo * kBwSeg || j >= (sg_hi + 1) * kBwSeg) {
+        dst[j] = 0.f;
+        continue;
+      }
       float sdv = sm.dvred[0][j];
 #pragma unroll
       for (int w = 1; w < kBwThreads / 32; ++w) sdv += sm.dvred[w][j];
