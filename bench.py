@@ -29,16 +29,39 @@ sys.path.insert(0, str(ROOT))
 METRIC = "Gpair-evals/s fused raytrace+GP kernel matvec (fwd, fwd+bwd); p50/p99 req latency"
 UNIT = "Gpair/s"
 SM_MAX_MHZ_DEFAULT = 2070.0
-# Work per point-subhalo pair of the far-side tNFW form (x^2 >= 1.05, nearly
-# every pair), counted operation by operation from the kernels' source (FP32
-# lanes; packed f32x2 operations count 2 lanes for 2 pairs):
-# forward: 2 offsets, 3 for R^2 and x^2, 23 for the shared far terms (arctan
-# polynomial 12), 7 for the mass bracket, 2 to accumulate both components,
-# 1.25 for the Kahan fold after every 8 subhalos;
-# backward: 5 + 23, 13 for the G and H brackets, 1 for 1/R^2, 16 for the four
-# subhalo sums, 0.6 for the Kahan folds. MUFU: 2 rsqrt, 1 rcp, 1 lg2 each.
+# Work per point-subhalo pair, counted operation by operation from the
+# kernels' source (FP32 lanes; packed f32x2 operations count 2 lanes for 2
+# pairs). Forward, far-side closed form (x^2 >= 1.05): 2 offsets, 3 for R^2
+# and x^2, 23 for the shared far terms (arctan polynomial 12), 7 for the mass
+# bracket, 2 to accumulate both components, 1.25 for the Kahan fold after
+# every 8 subhalos; MUFU: 2 rsqrt, 1 rcp, 1 lg2. Forward, far-field series
+# (x >= 6 max(tau, 2)): 2 + 3, 1 for y^2, 7 + 1 for the Horner steps, 2 for
+# m = A y^2 Q, 2 + 1.25 to accumulate and fold; MUFU: 1 rsqrt. Backward
+# (closed form throughout): 5 + 23, 13 for the G and H brackets, 1 for 1/R^2,
+# 16 for the four subhalo sums, 0.6 for the Kahan folds; 4 MUFU.
 RT_MUFU, RT_LANES = 4, 38.3
+RT_SER_MUFU, RT_SER_LANES = 1, 19.25
 VJ_MUFU, VJ_LANES = 4, 58.6
+
+
+def series_fraction(p) -> float:
+    """Fraction of the workload's point-subhalo pairs in the far-field series
+    regime (x^2 >= 36 max(tau^2, 4)), over every 4th pixel row and column."""
+    g = p.xgrid
+    w = g.nx * g.ss
+    h = g.pix / g.ss
+    xs = ((np.arange(w) - (w - 1) / 2) * h + g.cx)[::4]
+    ys = ((np.arange(g.ny * g.ss) - (g.ny * g.ss - 1) / 2) * h + g.cy)[::4]
+    X, Y = np.meshgrid(xs, ys)
+    pts = np.stack([X.ravel(), Y.ravel()], 1)
+    sub = p.sub.astype(np.float64)
+    its2 = 1.0 / sub[:, 3] ** 2
+    xT2 = 36.0 * np.maximum(sub[:, 4] ** 2, 4.0)
+    far = 0
+    for c in range(0, len(pts), 4096):
+        d = pts[c:c + 4096, None, :] - sub[None, :, :2]
+        far += int(np.count_nonzero((d ** 2).sum(-1) * its2 >= xT2))
+    return far / (len(pts) * len(sub))
 
 
 def parse():
@@ -564,10 +587,14 @@ def run_ours(args):
     # the ray-trace kernels' unit is the point-subhalo pair; counts are those
     # of the far-side tNFW form that nearly every pair takes
     sub_pairs = p.n * len(p.sub)
+    fs = series_fraction(p)
+    rt_mufu = fs * RT_SER_MUFU + (1 - fs) * RT_MUFU
+    rt_lanes = fs * RT_SER_LANES + (1 - fs) * RT_LANES
     kern["raytrace_kernel<tNFW> (forward ray-trace; unit: point-subhalo pair)"] = (
-        rt_ms, rt_call_ms, sub_pairs, RT_MUFU, RT_LANES,
-        f"pairs: {RT_MUFU} MUFU + {RT_LANES} FP32 lanes each (far-side tNFW mass and its Kahan sum; the SPLE and "
-        "shear terms, once per point, are not counted)", True)
+        rt_ms, rt_call_ms, sub_pairs, rt_mufu, rt_lanes,
+        f"pairs: {rt_mufu:.2f} MUFU + {rt_lanes:.1f} FP32 lanes each on average: {fs:.3f} of the pairs in the "
+        f"far-field series regime ({RT_SER_MUFU} MUFU + {RT_SER_LANES} lanes), the rest the far-side closed form "
+        f"({RT_MUFU} MUFU + {RT_LANES} lanes); the SPLE and shear terms, once per point, are not counted", True)
     kern["raytrace_vjp_kernel<tNFW> (ray-trace backward; unit: point-subhalo pair)"] = (
         vjp_ms, vjp_call_ms, sub_pairs, VJ_MUFU, VJ_LANES,
         f"pairs: {VJ_MUFU} MUFU + {VJ_LANES} FP32 lanes each (far-side tNFW G and H brackets and the four subhalo "

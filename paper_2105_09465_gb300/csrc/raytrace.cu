@@ -15,6 +15,8 @@
 namespace lr {
 
 constexpr int kRtThreads = 256;
+constexpr int kRtTile = 16;  // grid input: a CTA takes a kRtTile x kRtTile tile of pixels
+static_assert(kRtTile * kRtTile == kRtThreads, "one thread per pixel of a tile");
 constexpr int kSubChunk = 256;  // subhalos staged per chunk (multiple of 4)
 
 __global__ void grid_points_kernel(GridDev g, int64_t n, float2* out) {
@@ -31,39 +33,162 @@ __device__ __forceinline__ void kahan(float& s, float& c, float x) {
   s = t;
 }
 
+// Staged subhalos, as consecutive pairs (a, b), field by field as packed
+// pairs. The hot words are all the series needs:
+//   [0] (xh, yh)  [1] (its2, A)  [2] (xT2, q0)  [3..6] (q2, q3) .. (q8, q9);
+// the cold words the closed forms: [0] (tau, tau2)  [1] (t2m1_t, C).
+constexpr int kRtHot = 7, kRtCold = 2;
+
+struct RtSmem {
+  float raw[5 * kSubChunk];
+  float4 hot[kSubChunk / 2][kRtHot];
+  float4 cold[kSubChunk / 2][kRtCold];
+  int order[kSubChunk];  // staged position -> subhalo of the chunk
+  unsigned char far[kSubChunk];
+  float box[4];          // the CTA's points: x_lo, y_lo, x_hi, y_hi
+  int nfar;
+  uint64_t bar;
+};
+
+__device__ __forceinline__ float2 lo2(float4 v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 hi2(float4 v) { return make_float2(v.z, v.w); }
+
+__device__ __forceinline__ SubRec2 rec_from(const float4* hot, const float4* cold) {
+  SubRec2 r;
+  r.xh = make_float2(hot[0].x, hot[0].y);
+  r.yh = make_float2(hot[0].z, hot[0].w);
+  r.its2 = lo2(hot[1]);
+  r.A = hi2(hot[1]);
+  r.tau = lo2(cold[0]);
+  r.tau2 = hi2(cold[0]);
+  r.t2m1_t = lo2(cold[1]);
+  r.C = hi2(cold[1]);
+  return r;
+}
+
+__device__ __forceinline__ SubSer ser_from(const float4* hot, int k) {
+  SubSer s;
+  s.xT2 = k ? hot[2].y : hot[2].x;
+  s.q[0] = k ? hot[2].w : hot[2].z;
+  s.q[1] = 0.f;
+#pragma unroll
+  for (int j = 2; j < kSerTerms; ++j) {
+    const float4 w = hot[3 + (j - 2) / 2];
+    s.q[j] = (j & 1) ? (k ? w.w : w.z) : (k ? w.y : w.x);
+  }
+  return s;
+}
+
+// Stages subhalos [h0, h0 + cnt). Subhalos whose centre is beyond the series
+// radius from the whole box of the CTA's points (every pair of them takes the
+// series) come first, each class in index order; sm.nfar counts them.
+// Returns false (all threads) if the bulk-copy wait timed out.
+__device__ __forceinline__ bool stage_rt(const float* __restrict__ sub, int h0, int cnt, int profile, RtSmem& sm,
+                                         uint32_t& phase, bool bulk_ok, int* fault) {
+  if (!stage_raw(sub, h0, cnt, sm.raw, &sm.bar, phase, bulk_ok, fault)) return false;
+  for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+    const SubRec h = prep_sub(sm.raw + 5 * t, profile);
+    const SubSer q = prep_series(h, profile);
+    const float dx = fmaxf(fmaxf(sm.box[0] - h.xh, h.xh - sm.box[2]), 0.f);
+    const float dy = fmaxf(fmaxf(sm.box[1] - h.yh, h.yh - sm.box[3]), 0.f);
+    sm.far[t] = __fmul_rn(fmaf(dx, dx, dy * dy), h.its2) >= q.xT2 ? 1 : 0;
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {  // stable partition: far first
+    const int lane = threadIdx.x;
+    int nf = 0;
+    for (int b = 0; b < cnt; b += 32) {
+      const bool f = b + lane < cnt && sm.far[b + lane];
+      const unsigned m = __ballot_sync(0xffffffffu, f);
+      if (f) sm.order[nf + __popc(m & ((1u << lane) - 1u))] = b + lane;
+      nf += __popc(m);
+    }
+    int nn = nf;
+    for (int b = 0; b < cnt; b += 32) {
+      const bool f = b + lane < cnt && !sm.far[b + lane];
+      const unsigned m = __ballot_sync(0xffffffffu, f);
+      if (f) sm.order[nn + __popc(m & ((1u << lane) - 1u))] = b + lane;
+      nn += __popc(m);
+    }
+    if (lane == 0) sm.nfar = nf;
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; 2 * k < cnt; k += blockDim.x) {
+    const SubRec a = prep_sub(sm.raw + 5 * sm.order[2 * k], profile);
+    const bool hb = 2 * k + 1 < cnt;
+    const SubRec b = hb ? prep_sub(sm.raw + 5 * sm.order[2 * k + 1], profile) : SubRec{};
+    const SubSer sa = prep_series(a, profile), sb = prep_series(b, hb ? profile : LR_PROFILE_POINT_MASS);
+    float4* hot = sm.hot[k];
+    hot[0] = make_float4(a.xh, b.xh, a.yh, b.yh);
+    hot[1] = make_float4(a.its2, b.its2, a.A, b.A);
+    hot[2] = make_float4(sa.xT2, sb.xT2, sa.q[0], sb.q[0]);
+#pragma unroll
+    for (int w = 0; w < 4; ++w)
+      hot[3 + w] = make_float4(sa.q[2 + 2 * w], sb.q[2 + 2 * w], sa.q[3 + 2 * w], sb.q[3 + 2 * w]);
+    sm.cold[k][0] = make_float4(a.tau, b.tau, a.tau2, b.tau2);
+    sm.cold[k][1] = make_float4(a.t2m1_t, b.t2m1_t, a.C, b.C);
+  }
+  __syncthreads();
+  return true;
+}
+
 // Deflection of the staged subhalos at (x, y), added to the Kahan sums
 // (sx, cx), (sy, cy). Blocks of kRtFold subhalos are summed plainly in two
-// packed lanes (even and odd subhalos) and folded into the Kahan sums; the
-// fold order is fixed, so every kernel that calls this gets the same bits.
+// packed lanes and folded into the Kahan sums; the order is fixed, so every
+// kernel that calls this gets the same bits.
 template <int PROFILE>
-__device__ __forceinline__ void add_subs(const SubRec2* recs2, int cnt, float x, float y, float& sx, float& cx,
+__device__ __forceinline__ void add_subs(const RtSmem& sm, int cnt, float x, float y, float& sx, float& cx,
                                          float& sy, float& cy) {
   const float2 X = f2(x), Y = f2(y);
+  const int nfe = sm.nfar & ~1;  // pairs below nfe: both subhalos are far from every point of the CTA
   for (int t0 = 0; t0 < cnt; t0 += kRtFold) {
     const int t1 = min(cnt, t0 + kRtFold);
     float2 ax = f2(0.f), ay = f2(0.f);
     int t = t0;
     if (PROFILE == LR_PROFILE_TNFW) {
-      // two subhalos per step on the packed far-side form (the rare near
-      // pairs are redone by the general form, which gives the same bits for
-      // far pairs)
       for (; t + 1 < t1; t += 2) {
-        const SubRec2 H = recs2[t >> 1];
-        const float2 dx = sub2(X, H.xh), dy = sub2(Y, H.yh);
+        const float4* hot = sm.hot[t >> 1];
+        const float4 w0 = hot[0], w1 = hot[1], w2 = hot[2];
+        const float2 dx = sub2(X, make_float2(w0.x, w0.y)), dy = sub2(Y, make_float2(w0.z, w0.w));
         const float2 R2 = __ffma2_rn(dx, dx, __fmul2_rn(dy, dy));
-        const float2 x2 = __fmul2_rn(R2, H.its2);
-        float2 m = tnfw_m_far2(H, x2);
-        if (!tnfw_is_far(x2.x)) m.x = tnfw_m(sub_lane(H, 0), R2.x);
-        if (!tnfw_is_far(x2.y)) m.y = tnfw_m(sub_lane(H, 1), R2.y);
+        const float2 x2 = __fmul2_rn(R2, lo2(w1));
+        float2 q[kSerTerms];
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+          const float4 c = hot[3 + w];
+          q[2 + 2 * w] = lo2(c);
+          q[3 + 2 * w] = hi2(c);
+        }
+        float2 m;
+        if (t + 1 < nfe) {
+          // both subhalos far from the whole CTA: the series, no tests
+          m = tnfw_m_series2(hi2(w1), hi2(w2), q, x2);
+        } else {
+          // the series where x^2 reaches its radius, else the packed far-side
+          // closed form, and the rare near pairs the general form (which
+          // gives the same bits for far pairs)
+          const SubRec2 H = rec_from(hot, sm.cold[t >> 1]);
+          const bool sa = x2.x >= w2.x, sb = x2.y >= w2.y;
+          m = tnfw_m_far2(H, x2);
+          if (!tnfw_is_far(x2.x)) m.x = tnfw_m(sub_lane(H, 0), R2.x);
+          if (!tnfw_is_far(x2.y)) m.y = tnfw_m(sub_lane(H, 1), R2.y);
+          if (sa || sb) {
+            const float2 ms = tnfw_m_series2(hi2(w1), hi2(w2), q, x2);
+            if (sa) m.x = ms.x;
+            if (sb) m.y = ms.y;
+          }
+        }
         ax = __ffma2_rn(m, dx, ax);
         ay = __ffma2_rn(m, dy, ay);
       }
     }
     for (; t < t1; ++t) {
-      const SubRec h = sub_lane(recs2[t >> 1], t & 1);
+      const float4* hot = sm.hot[t >> 1];
+      const SubRec h = sub_lane(rec_from(hot, sm.cold[t >> 1]), t & 1);
       const float dx = __fsub_rn(x, h.xh), dy = __fsub_rn(y, h.yh);
       const float R2 = __fmaf_rn(dx, dx, __fmul_rn(dy, dy));
-      const float m = (PROFILE == LR_PROFILE_POINT_MASS) ? pointmass_m(h, R2) : tnfw_m(h, R2);
+      const float m = (PROFILE == LR_PROFILE_POINT_MASS) ? pointmass_m(h, R2)
+                                                         : tnfw_m_any(h, ser_from(hot, t & 1), R2);
       if (t & 1) {
         ax.y = __fmaf_rn(m, dx, ax.y);
         ay.y = __fmaf_rn(m, dy, ay.y);
@@ -77,20 +202,27 @@ __device__ __forceinline__ void add_subs(const SubRec2* recs2, int cnt, float x,
   }
 }
 
-struct RtSmem {
-  float raw[5 * kSubChunk];
-  SubRec2 recs2[kSubChunk / 2];
-  uint64_t bar;
-};
-
 template <int PROFILE>
 __device__ __forceinline__ void raytrace_body(const LensConst& L, const GridDev& g, const float2* __restrict__ xi,
                                               int64_t n, const float* __restrict__ sub, int n_sub, int bulk_ok,
                                               float2* __restrict__ beta, float2* __restrict__ alpha_out, int* fault,
                                               int64_t blk, RtSmem& sm) {
-  const int64_t i = blk * kRtThreads + threadIdx.x;
-  const bool valid = i < n;
-  const int64_t ii = valid ? i : (n - 1);
+  // explicit points: kRtThreads consecutive ones; grid: a 2-D tile, so that
+  // the CTA's points are compact (padding threads repeat an edge point)
+  int64_t i, ii;
+  bool valid;
+  if (xi) {
+    i = blk * kRtThreads + threadIdx.x;
+    valid = i < n;
+    ii = valid ? i : (n - 1);
+  } else {
+    const int tw = (g.W + kRtTile - 1) / kRtTile;
+    const int ty = (int)(blk / tw), tx = (int)(blk - (int64_t)ty * tw);
+    const int row = ty * kRtTile + (int)threadIdx.x / kRtTile, col = tx * kRtTile + (int)threadIdx.x % kRtTile;
+    valid = row < g.H && col < g.W;
+    i = (int64_t)row * g.W + col;
+    ii = (int64_t)min(row, g.H - 1) * g.W + min(col, g.W - 1);
+  }
   const float2 p = xi ? xi[ii] : grid_point(g, ii);
 
   float ax, ay;
@@ -100,14 +232,44 @@ __device__ __forceinline__ void raytrace_body(const LensConst& L, const GridDev&
   ay = fmaf(L.g2, p.x, fmaf(-L.g1, p.y, ay));
 
   if (n_sub > 0) {
+    // the box of the CTA's points (the padding rows repeat the last point)
+    float b0 = p.x, b1 = p.y, b2 = p.x, b3 = p.y;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+      b0 = fminf(b0, __shfl_xor_sync(0xffffffffu, b0, o));
+      b1 = fminf(b1, __shfl_xor_sync(0xffffffffu, b1, o));
+      b2 = fmaxf(b2, __shfl_xor_sync(0xffffffffu, b2, o));
+      b3 = fmaxf(b3, __shfl_xor_sync(0xffffffffu, b3, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+      float* wb = sm.raw + 4 * (threadIdx.x >> 5);  // the raw records are staged only later
+      wb[0] = b0;
+      wb[1] = b1;
+      wb[2] = b2;
+      wb[3] = b3;
+    }
     if (threadIdx.x == 0) mbar_init(&sm.bar, 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      float c0 = sm.raw[0], c1 = sm.raw[1], c2 = sm.raw[2], c3 = sm.raw[3];
+      for (int w = 1; w < kRtThreads / 32; ++w) {
+        c0 = fminf(c0, sm.raw[4 * w]);
+        c1 = fminf(c1, sm.raw[4 * w + 1]);
+        c2 = fmaxf(c2, sm.raw[4 * w + 2]);
+        c3 = fmaxf(c3, sm.raw[4 * w + 3]);
+      }
+      sm.box[0] = c0;
+      sm.box[1] = c1;
+      sm.box[2] = c2;
+      sm.box[3] = c3;
+    }
     __syncthreads();
     uint32_t phase = 0;
     float sx = 0.f, cx = 0.f, sy = 0.f, cy = 0.f;
     for (int h0 = 0; h0 < n_sub; h0 += kSubChunk) {
       const int cnt = min(kSubChunk, n_sub - h0);
-      if (!stage_subs2(sub, h0, cnt, PROFILE, sm.raw, sm.recs2, &sm.bar, phase, bulk_ok != 0, fault)) return;
-      add_subs<PROFILE>(sm.recs2, cnt, p.x, p.y, sx, cx, sy, cy);
+      if (!stage_rt(sub, h0, cnt, PROFILE, sm, phase, bulk_ok != 0, fault)) return;
+      add_subs<PROFILE>(sm, cnt, p.x, p.y, sx, cx, sy, cy);
       __syncthreads();
     }
     ax += sx - cx;
@@ -120,7 +282,7 @@ __device__ __forceinline__ void raytrace_body(const LensConst& L, const GridDev&
 }
 
 template <int PROFILE>
-__global__ void __launch_bounds__(kRtThreads) raytrace_kernel(const __grid_constant__ LensConst L, GridDev g,
+__global__ void __launch_bounds__(kRtThreads, 3) raytrace_kernel(const __grid_constant__ LensConst L, GridDev g,
                                                               const float2* __restrict__ xi, int64_t n,
                                                               const float* __restrict__ sub, int n_sub, int bulk_ok,
                                                               float2* __restrict__ beta,
@@ -129,7 +291,7 @@ __global__ void __launch_bounds__(kRtThreads) raytrace_kernel(const __grid_const
   raytrace_body<PROFILE>(L, g, xi, n, sub, n_sub, bulk_ok, beta, alpha_out, fault, blockIdx.x, sm);
 }
 
-__global__ void __launch_bounds__(kRtThreads) raytrace_batched_kernel(const __grid_constant__ Batch<RtP> B,
+__global__ void __launch_bounds__(kRtThreads, 3) raytrace_batched_kernel(const __grid_constant__ Batch<RtP> B,
                                                                       int* fault) {
   __shared__ __align__(16) RtSmem sm;
   const int k = batch_find(B, blockIdx.x);
@@ -143,6 +305,12 @@ __global__ void __launch_bounds__(kRtThreads) raytrace_batched_kernel(const __gr
                                    sm);
 }
 
+// CTAs of the ray-trace: kRtThreads points each, or one per grid tile.
+static int64_t rt_blocks(bool explicit_points, const GridDev& g, int64_t n) {
+  if (explicit_points) return (n + kRtThreads - 1) / kRtThreads;
+  return (int64_t)((g.W + kRtTile - 1) / kRtTile) * ((g.H + kRtTile - 1) / kRtTile);
+}
+
 lr_status launch_raytrace_batched(const RtP* p, int count, cudaStream_t s) {
   int* fault = fault_ptr();
   LR_REQUIRE(fault != nullptr, "could not resolve the device fault word");
@@ -153,7 +321,7 @@ lr_status launch_raytrace_batched(const RtP* p, int count, cudaStream_t s) {
     for (int k = 0; k < B.count; ++k) {
       B.p[k] = p[b0 + k];
       B.start[k] = (int32_t)tot;
-      tot += (p[b0 + k].n + kRtThreads - 1) / kRtThreads;
+      tot += rt_blocks(p[b0 + k].xi != nullptr, p[b0 + k].g, p[b0 + k].n);
     }
     B.start[B.count] = (int32_t)tot;
     if (tot == 0) continue;
@@ -254,7 +422,7 @@ lr_status launch_raytrace(const lr_points* p, float2* beta, float2* alpha, cudaS
   LR_REQUIRE(fault != nullptr, "could not resolve the device fault word");
   const GridDev g = p->xy ? GridDev{} : grid_dev(p->grid);
   const int bulk_ok = (((uintptr_t)p->sub & 15u) == 0) ? 1 : 0;
-  const unsigned blocks = (unsigned)((p->n + kRtThreads - 1) / kRtThreads);
+  const unsigned blocks = (unsigned)rt_blocks(p->xy != nullptr, g, p->n);
   const float2* xi = reinterpret_cast<const float2*>(p->xy);
   const int ns = p->n_sub;
   ktimer_begin(LR_KT_RAYTRACE, s);

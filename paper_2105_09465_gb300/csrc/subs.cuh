@@ -39,18 +39,4 @@ __device__ __forceinline__ bool stage_subs(const float* __restrict__ sub, int h0
   return true;
 }
 
-// The same as consecutive pairs: recs2[k] holds records 2k and 2k + 1 (the
-// second a zero record when cnt is odd).
-__device__ __forceinline__ bool stage_subs2(const float* __restrict__ sub, int h0, int cnt, int profile, float* raw,
-                                            SubRec2* recs2, uint64_t* bar, uint32_t& phase, bool bulk_ok, int* fault) {
-  if (!stage_raw(sub, h0, cnt, raw, bar, phase, bulk_ok, fault)) return false;
-  for (int t = threadIdx.x; 2 * t < cnt; t += blockDim.x) {
-    const SubRec a = prep_sub(raw + 10 * t, profile);
-    const SubRec b = 2 * t + 1 < cnt ? prep_sub(raw + 10 * t + 5, profile) : SubRec{};
-    recs2[t] = sub_pair(a, b);
-  }
-  __syncthreads();
-  return true;
-}
-
 }  // namespace lr
