@@ -89,6 +89,24 @@ def test_subhalo_centred_on_pixels_and_near_x_equals_one(orc):
     check(a, b, ar, br)
 
 
+@pytest.mark.parametrize("tau", [0.7, 3.0, 10.0, 40.0])
+def test_tnfw_far_field_series_boundary(orc, tau):
+    """Pixels on both sides of the far-field series radius x = 6 max(tau, 2)
+    of heavy subhalos (the kernels switch from the closed form to the series
+    there; both must match the FP64 closed form), in tiles that are entirely
+    inside, entirely outside and across the radius."""
+    theta_s = 0.08
+    xT = 6 * max(tau, 2) * theta_s
+    g = W.Grid(96, 96, 2, 2.2 * xT / 96)
+    # one subhalo at the grid centre and three at the edges, with the
+    # realistic-size normalisation kappa_s of a 1e10 Msun halo
+    pos = [(0.0, 0.0), (0.9 * g.nx * g.pix / 2, 0.0), (0.0, -0.8 * g.ny * g.pix / 2), (0.31 * xT, 0.44 * xT)]
+    sub = np.array([[x, y, 0.05, theta_s, tau] for x, y in pos], np.float32)
+    lens = W.Lens(0.0, 0.0, 0.8, 0.3, 1.2, 2.0, 0.01, 0.02)
+    a, b, ar, br, _ = run_both(orc, g, lens, sub)
+    check(a, b, ar, br)
+
+
 def test_point_mass_profile(orc):
     rng = np.random.default_rng(5)
     lens = W.draw_lens(rng)
