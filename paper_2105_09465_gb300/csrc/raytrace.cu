@@ -170,8 +170,11 @@ __device__ __forceinline__ void add_subs(const RtSmem& sm, int cnt, float x, flo
           const SubRec2 H = rec_from(hot, sm.cold[t >> 1]);
           const bool sa = x2.x >= w2.x, sb = x2.y >= w2.y;
           m = tnfw_m_far2(H, x2);
-          if (!tnfw_is_far(x2.x)) m.x = tnfw_m(sub_lane(H, 0), R2.x);
-          if (!tnfw_is_far(x2.y)) m.y = tnfw_m(sub_lane(H, 1), R2.y);
+          const bool na = !tnfw_is_far(x2.x), nb = !tnfw_is_far(x2.y);
+          if (na || nb) {  // rare: one branch for both lanes
+            if (na) m.x = tnfw_m(sub_lane(H, 0), R2.x);
+            if (nb) m.y = tnfw_m(sub_lane(H, 1), R2.y);
+          }
           if (sa || sb) {
             const float2 ms = tnfw_m_series2(hi2(w1), hi2(w2), q, x2);
             if (sa) m.x = ms.x;
