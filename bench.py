@@ -38,10 +38,11 @@ SM_MAX_MHZ_DEFAULT = 2070.0
 # (x >= 6 max(tau, 2)): 2 + 3, 1 for y^2, 7 + 1 for the Horner steps, 2 for
 # m = A y^2 Q, 2 + 1.25 to accumulate and fold; MUFU: 1 rsqrt. Backward
 # (closed form throughout): 5 + 23, 13 for the G and H brackets, 1 for 1/R^2,
-# 16 for the four subhalo sums, 0.6 for the Kahan folds; 4 MUFU.
+# 11 for the four subhalo sums (their constant factors applied once per
+# subhalo), 0.6 for the Kahan folds; 4 MUFU.
 RT_MUFU, RT_LANES = 4, 38.3
 RT_SER_MUFU, RT_SER_LANES = 1, 19.25
-VJ_MUFU, VJ_LANES = 4, 58.6
+VJ_MUFU, VJ_LANES = 4, 53.6
 
 
 def series_fraction(p) -> float:

@@ -46,17 +46,28 @@ struct VjSmem {
 };
 
 // One tNFW pair's terms of the four subhalo sums, for two points at once
-// (packed f32x2; iR2 = 1/R^2).
-__device__ __forceinline__ void vj_accum2(const SubRec2& H, float2 ex, float2 dx, float2 dy, float2 gx, float2 gy,
-                                          float2 iR2, float2 Gt, float2 Ht, float2& a0, float2& a1, float2& a2,
-                                          float2& a3) {
+// (packed f32x2; iR2 = 1/R^2), without the subhalo's constant factors: with
+// dg = d.G and hg = H - 2G,
+//   a0 += G G_x + q dx, a1 += G G_y + q dy (q = hg dg / R^2), a2 += G dg,
+//   a3 += hg dg;
+// the slot's sums are scaled once by (A, A, -4T, A / theta_s) (vj_scale).
+__device__ __forceinline__ void vj_accum2(float2 dx, float2 dy, float2 gx, float2 gy, float2 iR2, float2 Gt,
+                                          float2 Ht, float2& a0, float2& a1, float2& a2, float2& a3) {
   const float2 dg = __ffma2_rn(dx, gx, __fmul2_rn(dy, gy));
   const float2 hg = __ffma2_rn(f2(-2.0f), Gt, Ht);
   const float2 q = __fmul2_rn(__fmul2_rn(hg, dg), iR2);
-  a0 = __ffma2_rn(H.A, __ffma2_rn(Gt, gx, __fmul2_rn(q, dx)), a0);
-  a1 = __ffma2_rn(H.A, __ffma2_rn(Gt, gy, __fmul2_rn(q, dy)), a1);
-  a2 = __ffma2_rn(__fmul2_rn(f2(-ex.x), Gt), dg, a2);
-  a3 = __ffma2_rn(__fmul2_rn(__fmul2_rn(H.A, hg), dg), f2(ex.y), a3);
+  a0 = __ffma2_rn(Gt, gx, __ffma2_rn(q, dx, a0));
+  a1 = __ffma2_rn(Gt, gy, __ffma2_rn(q, dy, a1));
+  a2 = __ffma2_rn(Gt, dg, a2);
+  a3 = __ffma2_rn(hg, dg, a3);
+}
+
+// The constant factors of a tNFW slot's four sums (1 for a point mass, whose
+// terms are accumulated whole).
+template <int PROFILE>
+__device__ __forceinline__ float vj_scale(const SubRec& rec, float2 ex, int v) {
+  if (PROFILE != LR_PROFILE_TNFW) return 1.0f;
+  return v == 0 || v == 1 ? rec.A : (v == 2 ? -ex.x : __fmul_rn(rec.A, ex.y));
 }
 
 __device__ __forceinline__ void vj_kahan(float& s, float& c, float x) {
@@ -86,12 +97,16 @@ __device__ __forceinline__ void vj_sweep(const SubRec& rec, float2 ex, const flo
         const float2 x2 = __fmul2_rn(R2, H.its2);
         float2 Gt, Ht, ix2;
         tnfw_GH_far2(H, x2, Gt, Ht, ix2);
-        if (!tnfw_is_far(x2.x)) tnfw_GH(rec, R2.x, Gt.x, Ht.x, ix2.x);
-        if (!tnfw_is_far(x2.y)) tnfw_GH(rec, R2.y, Gt.y, Ht.y, ix2.y);
-        // a point on the subhalo centre adds nothing
-        if (!(R2.x > 1e-30f)) Gt.x = Ht.x = ix2.x = gx.x = gy.x = 0.f;
-        if (!(R2.y > 1e-30f)) Gt.y = Ht.y = ix2.y = gx.y = gy.y = 0.f;
-        vj_accum2(H, ex, dx, dy, gx, gy, __fmul2_rn(H.its2, ix2), Gt, Ht, a0, a1, a2, a3);
+        const bool na = !tnfw_is_far(x2.x), nb = !tnfw_is_far(x2.y);
+        if (na || nb) {  // rare: one branch for both lanes
+          if (na) tnfw_GH(rec, R2.x, Gt.x, Ht.x, ix2.x);
+          if (nb) tnfw_GH(rec, R2.y, Gt.y, Ht.y, ix2.y);
+        }
+        // a point on the subhalo centre adds nothing: its G, H and 1/x^2 are
+        // finite (0 at x = 0), so a zero G makes every term 0
+        gx = make_float2(R2.x > 1e-30f ? gx.x : 0.f, R2.y > 1e-30f ? gx.y : 0.f);
+        gy = make_float2(R2.x > 1e-30f ? gy.x : 0.f, R2.y > 1e-30f ? gy.y : 0.f);
+        vj_accum2(dx, dy, gx, gy, __fmul2_rn(H.its2, ix2), Gt, Ht, a0, a1, a2, a3);
       } else {
         // point mass: alpha = theta^2 d / R^2 (its2 = theta^2, ex.y = theta)
         float2 iR2 = make_float2(R2.x > 1e-30f ? frcp(R2.x) : 0.f, R2.y > 1e-30f ? frcp(R2.y) : 0.f);
@@ -181,7 +196,7 @@ __device__ __forceinline__ void vjp_body(const LensConst& L, const LensGradConst
     if (own) {
 #pragma unroll
       for (int v = 0; v < 4; ++v) {
-        const float x = sc[v] - cc[v];
+        const float x = __fmul_rn(sc[v] - cc[v], vj_scale<PROFILE>(rec, ex, v));
         if (P == 1)
           sub_part[((int64_t)h * 4 + v) * nblk + blk] = x;  // [value][CTA]
         else
