@@ -98,9 +98,16 @@ __device__ __forceinline__ void bw_load_pair(const BwArgs& A, int t, int p, floa
 
 template <int R, int K>
 struct BwSmem {
-  float4 sP[2][kBwPairs];
-  float2 sV[2][kBwPairs];
-  float2 sG[2][kBwPairs];
+  union {
+    struct {
+      float4 sP[2][kBwPairs];
+      float2 sV[2][kBwPairs];
+      float2 sG[2][kBwPairs];
+    };
+    // the training forward's pair records: pair p at 2p (x'_a, x'_b, v~_a,
+    // v~_b) and 2p + 1 (v~u_a, v~u_b, v~u^2_a, v~u^2_b), one address per pair
+    float4 sT[2][2 * kBwPairs];
+  };
   float dvred[kBwThreads / 32][kBwTile];  // fused d_v: per-warp sums of k g per source
   float ksum[R][K][kBwThreads];            // per-thread Kahan running sums (touched once per tile)
   float kcomp[R][K][kBwThreads];
@@ -416,13 +423,13 @@ __device__ __forceinline__ bool train_compact(const BwArgs& A, int rb) {
   return !(B.xlo <= B.xhi) || (B.xhi - B.xlo) * A.sc <= kTrainCompact;
 }
 
-__device__ __forceinline__ void train_load_pair(const BwArgs& A, int t, int p, float xc, float4& P, float2& V,
-                                                float2& G) {
-  int64_t j0;
-  int cnt, grow;
-  bw_tile_range(A.src, t, j0, cnt, grow);
+// Pair p of the tile at grid row `grow`, segment `seg`.
+__device__ __forceinline__ void train_load_pair(const BwArgs& A, int grow, int seg, int p, float xc, float4& P,
+                                                float4& VG) {
+  const int c0 = seg * kBwTile;
+  const int cnt = min(kBwTile, A.src.g.W - c0);
+  const int64_t j0 = (int64_t)grow * A.src.g.W + c0;
   const int a = 2 * p, b = 2 * p + 1;
-  const int c0 = (int)(j0 - (int64_t)grow * A.src.g.W);
   const float o = grid_x(A.src.g, c0 + kBwSeg * (a / kBwSeg) + kBwSeg / 2);
   const float gxa = grid_x(A.src.g, c0 + a), gxb = grid_x(A.src.g, c0 + b);
   const float xa = (a < cnt) ? A.sc * (gxa - o) : 0.f;
@@ -431,8 +438,7 @@ __device__ __forceinline__ void train_load_pair(const BwArgs& A, int t, int p, f
   const float vb = (b < cnt) ? __ldg(A.v + j0 + b) * ex2_approx(-xb * xb) : 0.f;
   const float ua = A.sc * (gxa - xc), ub = A.sc * (gxb - xc);
   P = make_float4(xa, xb, va, vb);
-  V = f2(va * ua, vb * ub);
-  G = f2(va * ua * ua, vb * ub * ub);
+  VG = make_float4(va * ua, vb * ub, va * ua * ua, vb * ub * ub);
 }
 
 template <int R>
@@ -468,24 +474,25 @@ __device__ __forceinline__ void train_rows_body(const BwArgs& A, int rb, int chu
     }
   }
 
-  float4 P;
-  float2 V, G;
+  // tile t = grow * segs + seg, stepped without a division per tile
+  const int segs = A.src.segs;
+  int grow = t0 / segs, seg = t0 - grow * segs;
+  float4 P, VG;
   if (t0 < t1) {
-    train_load_pair(A, t0, tid, xc, P, V, G);
-    sm.sP[0][tid] = P;
-    sm.sV[0][tid] = V;
-    sm.sG[0][tid] = G;
+    train_load_pair(A, grow, seg, tid, xc, P, VG);
+    sm.sT[0][2 * tid] = P;
+    sm.sT[0][2 * tid + 1] = VG;
   }
   __syncthreads();
 
   for (int t = t0; t < t1; ++t) {
     const int buf = (t - t0) & 1;
-    if (t + 1 < t1) train_load_pair(A, t + 1, tid, xc, P, V, G);
-    int64_t j0;
-    int cnt, grow;
-    bw_tile_range(A.src, t, j0, cnt, grow);
+    const bool wrap = seg + 1 == segs;
+    const int ngrow = wrap ? grow + 1 : grow, nseg = wrap ? 0 : seg + 1;
+    if (t + 1 < t1) train_load_pair(A, ngrow, nseg, tid, xc, P, VG);
+    const int c0 = seg * kBwTile;
+    const int cnt = min(kBwTile, A.src.g.W - c0);
     const float yt = grid_y(A.src.g, grow);
-    const int c0 = (int)(j0 - (int64_t)grow * A.src.g.W);
     // columns of this grid row within reach of the row block, and the
     // sub-segments that meet them
     int clo = 0, chi = cnt - 1;
@@ -520,9 +527,9 @@ __device__ __forceinline__ void train_rows_body(const BwArgs& A, int rb, int chu
 #pragma unroll
         for (int pp = qq; pp < qq + kQuarterPairs; ++pp) {
           const int p = sg * (kBwSeg / 2) + pp;
-          const float4 Q = sm.sP[buf][p];
+          const float4 Q = sm.sT[buf][2 * p], U = sm.sT[buf][2 * p + 1];
           const float2 X = f2(Q.x, Q.y), W0 = f2(Q.z, Q.w);
-          const float2 W1 = sm.sV[buf][p], W2 = sm.sG[buf][p];
+          const float2 W1 = f2(U.x, U.y), W2 = f2(U.z, U.w);
 #pragma unroll
           for (int r = 0; r < R; ++r) {
             const float2 e = __ffma2_rn(q2[r], X, ar[r]);
@@ -556,10 +563,11 @@ __device__ __forceinline__ void train_rows_body(const BwArgs& A, int rb, int chu
       }
     }
     if (t + 1 < t1) {
-      sm.sP[buf ^ 1][tid] = P;
-      sm.sV[buf ^ 1][tid] = V;
-      sm.sG[buf ^ 1][tid] = G;
+      sm.sT[buf ^ 1][2 * tid] = P;
+      sm.sT[buf ^ 1][2 * tid + 1] = VG;
     }
+    grow = ngrow;
+    seg = nseg;
     __syncthreads();
   }
 
