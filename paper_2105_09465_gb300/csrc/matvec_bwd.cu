@@ -104,7 +104,7 @@ struct BwSmem {
       float2 sV[2][kBwPairs];
       float2 sG[2][kBwPairs];
     };
-    // the training forward's pair records: pair p at 2p (x'_a, x'_b, v~_a,
+    // the training forward's pair records: pair p at 2p (-2x'_a, -2x'_b, v~_a,
     // v~_b) and 2p + 1 (v~u_a, v~u_b, v~u^2_a, v~u^2_b), one address per pair
     float4 sT[2][2 * kBwPairs];
   };
@@ -407,6 +407,9 @@ __device__ __forceinline__ void bwd_rows_body(const BwArgs& A, int rb, int chunk
 // keeps the sub-segment form 2 q_s x' + a_s (q_s = q0 - delta_s,
 // a_s = -(q_s^2 + dy'^2), |x'| <= 5.5), so every sub-segment adds into the
 // same packed sums and the conversion to A, B, C runs once per row and tile.
+// The source records hold -2x', so the exponent is (delta_s - q0)(-2x') + a_s:
+// one subtraction and one FMA per row and sub-segment (the products are the
+// same as 2 q_s x', since the factor 2 is exact).
 // The per-tile sums are added plainly for kTrainFold tiles, then folded into
 // Kahan sums kept in shared memory.
 //
@@ -437,7 +440,7 @@ __device__ __forceinline__ void train_load_pair(const BwArgs& A, int grow, int s
   const float va = (a < cnt) ? __ldg(A.v + j0 + a) * ex2_approx(-xa * xa) : 0.f;
   const float vb = (b < cnt) ? __ldg(A.v + j0 + b) * ex2_approx(-xb * xb) : 0.f;
   const float ua = A.sc * (gxa - xc), ub = A.sc * (gxb - xc);
-  P = make_float4(xa, xb, va, vb);
+  P = make_float4(-2.f * xa, -2.f * xb, va, vb);
   VG = make_float4(va * ua, vb * ub, va * ua * ua, vb * ub * ub);
 }
 
@@ -516,9 +519,9 @@ __device__ __forceinline__ void train_rows_body(const BwArgs& A, int rb, int chu
       float2 q2[R], ar[R];
 #pragma unroll
       for (int r = 0; r < R; ++r) {
-        const float q = q0[r] - ds;
-        const float a = fmaf(-q, q, ndy2[r]);
-        q2[r] = f2(q + q, q + q);
+        const float nq = ds - q0[r];
+        const float a = fmaf(-nq, nq, ndy2[r]);
+        q2[r] = f2(nq, nq);
         ar[r] = f2(a, a);
       }
 #pragma unroll
@@ -636,16 +639,14 @@ struct DvSmem {
 };
 
 template <bool SPLIT>
-__device__ __forceinline__ void dv_load_pair(const BwArgs& A, int t, int p, float2& X) {
-  int64_t j0;
-  int cnt, grow;
-  bw_tile_range(A.src, t, j0, cnt, grow);
+__device__ __forceinline__ void dv_load_pair(const BwArgs& A, int seg, int p, float2& X) {
+  const int c0 = seg * kBwTile;
+  const int cnt = min(kBwTile, A.src.g.W - c0);
   const int a = 2 * p, b = 2 * p + 1;
-  const int c0 = (int)(j0 - (int64_t)grow * A.src.g.W);
   const float o = grid_x(A.src.g, c0 + kBwSeg * (a / kBwSeg) + kBwSeg / 2);
   const float xa = (a < cnt) ? A.sc * (grid_x(A.src.g, c0 + a) - o) : 0.f;
   const float xb = (b < cnt) ? A.sc * (grid_x(A.src.g, c0 + b) - o) : 0.f;
-  X = SPLIT ? f2(xa, xb) : f2(-xa, -xb);
+  X = SPLIT ? f2(-2.f * xa, -2.f * xb) : f2(-xa, -xb);
 }
 
 template <bool SPLIT>
@@ -673,20 +674,24 @@ __device__ __forceinline__ void dv_rows_body(const BwArgs& A, int rb, int chunk,
     const float gv = ir >= 0 ? __ldg(A.grow + ir) : 0.f;  // padding rows add nothing
     gq[r] = f2(gv, gv);
   }
+  // tile t = grow * segs + seg, stepped without a division per tile
+  const int segs = A.src.segs;
+  int grow = t0 / segs, seg = t0 - grow * segs;
   float2 X = f2(0.f, 0.f);
   if (t0 < t1) {
-    dv_load_pair<SPLIT>(A, t0, tid, X);
+    dv_load_pair<SPLIT>(A, seg, tid, X);
     sm.sX[0][tid] = X;
   }
   __syncthreads();
   for (int t = t0; t < t1; ++t) {
     const int buf = (t - t0) & 1;
-    if (t + 1 < t1) dv_load_pair<SPLIT>(A, t + 1, tid, X);
-    int64_t j0;
-    int cnt, grow;
-    bw_tile_range(A.src, t, j0, cnt, grow);
+    const bool wrap = seg + 1 == segs;
+    const int ngrow = wrap ? grow + 1 : grow, nseg = wrap ? 0 : seg + 1;
+    if (t + 1 < t1) dv_load_pair<SPLIT>(A, nseg, tid, X);
+    const int c0 = seg * kBwTile;
+    const int cnt = min(kBwTile, A.src.g.W - c0);
+    const int64_t j0 = (int64_t)grow * A.src.g.W + c0;
     const float yt = grid_y(A.src.g, grow);
-    const int c0 = (int)(j0 - (int64_t)grow * A.src.g.W);
     float dy2[kDvR];
 #pragma unroll
     for (int r = 0; r < kDvR; ++r) {
@@ -708,15 +713,17 @@ __device__ __forceinline__ void dv_rows_body(const BwArgs& A, int rb, int chunk,
         continue;
       }
       const float o = grid_x(A.src.g, c0 + kBwSeg * sg + kBwSeg / 2);
-      float2 qa[kDvR], qb[kDvR];  // split: (2q, -(q^2 + dy'^2)); unsplit: (q, dy'^2)
+      // split: (-q, -(q^2 + dy'^2)) against records -2x'; unsplit: (q, dy'^2)
+      float2 qa[kDvR], qb[kDvR];
 #pragma unroll
       for (int r = 0; r < kDvR; ++r) {
-        const float q = A.sc * (xq[r] - o);
         if (SPLIT) {
-          const float a = -fmaf(q, q, dy2[r]);
-          qa[r] = f2(q + q, q + q);
+          const float nq = A.sc * (o - xq[r]);
+          const float a = -fmaf(nq, nq, dy2[r]);
+          qa[r] = f2(nq, nq);
           qb[r] = f2(a, a);
         } else {
+          const float q = A.sc * (xq[r] - o);
           qa[r] = f2(q, q);
           qb[r] = f2(dy2[r], dy2[r]);
         }
@@ -766,12 +773,14 @@ __device__ __forceinline__ void dv_rows_body(const BwArgs& A, int rb, int chunk,
       for (int w = 1; w < kBwThreads / 32; ++w) sdv += sm.dvred[w][j];
       if (SPLIT) {
         const float2 Xp = sm.sX[buf][j >> 1];
-        const float xj = (j & 1) ? Xp.y : Xp.x;
+        const float xj = 0.5f * ((j & 1) ? Xp.y : Xp.x);  // the record holds -2x'
         sdv *= ex2_approx(-xj * xj);
       }
       dst[j] = sdv;
     }
     if (t + 1 < t1) sm.sX[buf ^ 1][tid] = X;
+    grow = ngrow;
+    seg = nseg;
     __syncthreads();
   }
 }
