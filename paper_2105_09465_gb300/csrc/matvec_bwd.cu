@@ -104,7 +104,7 @@ struct BwSmem {
       float2 sV[2][kBwPairs];
       float2 sG[2][kBwPairs];
     };
-    // the training forward's pair records: pair p at 2p (-2x'_a, -2x'_b, v~_a,
+    // the training forward's pair records: pair p at 2p (x'_a, x'_b, v~_a,
     // v~_b) and 2p + 1 (v~u_a, v~u_b, v~u^2_a, v~u^2_b), one address per pair
     float4 sT[2][2 * kBwPairs];
   };
@@ -407,9 +407,6 @@ __device__ __forceinline__ void bwd_rows_body(const BwArgs& A, int rb, int chunk
 // keeps the sub-segment form 2 q_s x' + a_s (q_s = q0 - delta_s,
 // a_s = -(q_s^2 + dy'^2), |x'| <= 5.5), so every sub-segment adds into the
 // same packed sums and the conversion to A, B, C runs once per row and tile.
-// The source records hold -2x', so the exponent is (delta_s - q0)(-2x') + a_s:
-// one subtraction and one FMA per row and sub-segment (the products are the
-// same as 2 q_s x', since the factor 2 is exact).
 // The per-tile sums are added plainly for kTrainFold tiles, then folded into
 // Kahan sums kept in shared memory.
 //
@@ -440,7 +437,7 @@ __device__ __forceinline__ void train_load_pair(const BwArgs& A, int grow, int s
   const float va = (a < cnt) ? __ldg(A.v + j0 + a) * ex2_approx(-xa * xa) : 0.f;
   const float vb = (b < cnt) ? __ldg(A.v + j0 + b) * ex2_approx(-xb * xb) : 0.f;
   const float ua = A.sc * (gxa - xc), ub = A.sc * (gxb - xc);
-  P = make_float4(-2.f * xa, -2.f * xb, va, vb);
+  P = make_float4(xa, xb, va, vb);
   VG = make_float4(va * ua, vb * ub, va * ua * ua, vb * ub * ub);
 }
 
@@ -519,9 +516,9 @@ __device__ __forceinline__ void train_rows_body(const BwArgs& A, int rb, int chu
       float2 q2[R], ar[R];
 #pragma unroll
       for (int r = 0; r < R; ++r) {
-        const float nq = ds - q0[r];
-        const float a = fmaf(-nq, nq, ndy2[r]);
-        q2[r] = f2(nq, nq);
+        const float q = q0[r] - ds;
+        const float a = fmaf(-q, q, ndy2[r]);
+        q2[r] = f2(q + q, q + q);
         ar[r] = f2(a, a);
       }
 #pragma unroll
