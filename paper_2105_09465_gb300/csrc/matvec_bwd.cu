@@ -441,6 +441,28 @@ __device__ __forceinline__ void train_load_pair(const BwArgs& A, int grow, int s
   VG = make_float4(va * ua, vb * ub, va * ua * ua, vb * ub * ub);
 }
 
+// NP consecutive source pairs (records T[0 .. 2 NP)) against the thread's R
+// rows: exponent, exp2 and the three packed moment sums.
+template <int R, int NP>
+__device__ __forceinline__ void train_pairs(const float4* __restrict__ T, const float2 (&q2)[R],
+                                            const float2 (&ar)[R], float2 (&S0)[R], float2 (&S1)[R],
+                                            float2 (&S2)[R]) {
+#pragma unroll
+  for (int pp = 0; pp < NP; ++pp) {
+    const float4 Q = T[2 * pp], U = T[2 * pp + 1];
+    const float2 X = f2(Q.x, Q.y), W0 = f2(Q.z, Q.w);
+    const float2 W1 = f2(U.x, U.y), W2 = f2(U.z, U.w);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const float2 e = __ffma2_rn(q2[r], X, ar[r]);
+      const float2 k = f2(ex2_approx(e.x), ex2_approx(e.y));
+      S0[r] = __ffma2_rn(k, W0, S0[r]);
+      S1[r] = __ffma2_rn(k, W1, S1[r]);
+      S2[r] = __ffma2_rn(k, W2, S2[r]);
+    }
+  }
+}
+
 template <int R>
 __device__ __forceinline__ void train_rows_body(const BwArgs& A, int rb, int chunk, BwSmem<R, 4>& sm) {
   constexpr int kRows = kBwThreads * R;
@@ -521,23 +543,15 @@ __device__ __forceinline__ void train_rows_body(const BwArgs& A, int rb, int chu
         q2[r] = f2(q + q, q + q);
         ar[r] = f2(a, a);
       }
+      const float4* T = &sm.sT[buf][2 * sg * (kBwSeg / 2)];
+      if (pl == 0 && ph == kBwSeg / 2) {
+        // a sub-segment wholly in reach: one block without quarter tests
+        train_pairs<R, kBwSeg / 2>(T, q2, ar, S0, S1, S2);
+      } else {
 #pragma unroll
-      for (int qq = 0; qq < kBwSeg / 2; qq += kQuarterPairs) {
-        if (qq < pl || qq >= ph) continue;  // a quarter out of reach: exactly zero
-#pragma unroll
-        for (int pp = qq; pp < qq + kQuarterPairs; ++pp) {
-          const int p = sg * (kBwSeg / 2) + pp;
-          const float4 Q = sm.sT[buf][2 * p], U = sm.sT[buf][2 * p + 1];
-          const float2 X = f2(Q.x, Q.y), W0 = f2(Q.z, Q.w);
-          const float2 W1 = f2(U.x, U.y), W2 = f2(U.z, U.w);
-#pragma unroll
-          for (int r = 0; r < R; ++r) {
-            const float2 e = __ffma2_rn(q2[r], X, ar[r]);
-            const float2 k = f2(ex2_approx(e.x), ex2_approx(e.y));
-            S0[r] = __ffma2_rn(k, W0, S0[r]);
-            S1[r] = __ffma2_rn(k, W1, S1[r]);
-            S2[r] = __ffma2_rn(k, W2, S2[r]);
-          }
+        for (int qq = 0; qq < kBwSeg / 2; qq += kQuarterPairs) {
+          if (qq < pl || qq >= ph) continue;  // a quarter out of reach: exactly zero
+          train_pairs<R, kQuarterPairs>(T + 2 * qq, q2, ar, S0, S1, S2);
         }
       }
     }
@@ -646,6 +660,33 @@ __device__ __forceinline__ void dv_load_pair(const BwArgs& A, int seg, int p, fl
   X = SPLIT ? f2(-2.f * xa, -2.f * xb) : f2(-xa, -xb);
 }
 
+// NP consecutive source pairs (records X[0 .. NP)) against the thread's rows:
+// kgs[2p], kgs[2p + 1] = sum over the rows of k g for the pair's two sources.
+template <bool SPLIT, int NP>
+__device__ __forceinline__ void dv_pairs(const float2* __restrict__ X, const float2 (&qa)[kDvR],
+                                         const float2 (&qb)[kDvR], const float2 (&gq)[kDvR], float* kgs) {
+#pragma unroll
+  for (int pp = 0; pp < NP; ++pp) {
+    const float2 Xp = X[pp];
+    float2 kg = f2(0.f, 0.f);
+#pragma unroll
+    for (int r = 0; r < kDvR; ++r) {
+      float2 k;
+      if (SPLIT) {
+        const float2 e = __ffma2_rn(qa[r], Xp, qb[r]);
+        k = f2(ex2_approx(e.x), ex2_approx(e.y));
+      } else {
+        const float2 dx = __fadd2_rn(qa[r], Xp);
+        const float2 tt = __ffma2_rn(dx, dx, qb[r]);
+        k = f2(ex2_approx(-tt.x), ex2_approx(-tt.y));
+      }
+      kg = __ffma2_rn(k, gq[r], kg);
+    }
+    kgs[2 * pp] = kg.x;
+    kgs[2 * pp + 1] = kg.y;
+  }
+}
+
 template <bool SPLIT>
 __device__ __forceinline__ void dv_rows_body(const BwArgs& A, int rb, int chunk, DvSmem& sm) {
   RowBlockInfo B{};
@@ -726,32 +767,19 @@ __device__ __forceinline__ void dv_rows_body(const BwArgs& A, int rb, int chunk,
         }
       }
       float kgs[kBwSeg];
+      const float2* Xs = &sm.sX[buf][sg * (kBwSeg / 2)];
+      if (pl == 0 && ph == kBwSeg / 2) {
+        // a sub-segment wholly in reach: one block without quarter tests
+        dv_pairs<SPLIT, kBwSeg / 2>(Xs, qa, qb, gq, kgs);
+      } else {
 #pragma unroll
-      for (int qq = 0; qq < kBwSeg / 2; qq += kQuarterPairs) {
-        if (qq < pl || qq >= ph) {  // a quarter out of reach: exactly zero
+        for (int qq = 0; qq < kBwSeg / 2; qq += kQuarterPairs) {
+          if (qq < pl || qq >= ph) {  // a quarter out of reach: exactly zero
 #pragma unroll
-          for (int c = 2 * qq; c < 2 * (qq + kQuarterPairs); ++c) kgs[c] = 0.f;
-          continue;
-        }
-#pragma unroll
-        for (int pp = qq; pp < qq + kQuarterPairs; ++pp) {
-          const float2 Xp = sm.sX[buf][sg * (kBwSeg / 2) + pp];
-          float2 kg = f2(0.f, 0.f);
-#pragma unroll
-          for (int r = 0; r < kDvR; ++r) {
-            float2 k;
-            if (SPLIT) {
-              const float2 e = __ffma2_rn(qa[r], Xp, qb[r]);
-              k = f2(ex2_approx(e.x), ex2_approx(e.y));
-            } else {
-              const float2 dx = __fadd2_rn(qa[r], Xp);
-              const float2 tt = __ffma2_rn(dx, dx, qb[r]);
-              k = f2(ex2_approx(-tt.x), ex2_approx(-tt.y));
-            }
-            kg = __ffma2_rn(k, gq[r], kg);
+            for (int c = 2 * qq; c < 2 * (qq + kQuarterPairs); ++c) kgs[c] = 0.f;
+            continue;
           }
-          kgs[2 * pp] = kg.x;
-          kgs[2 * pp + 1] = kg.y;
+          dv_pairs<SPLIT, kQuarterPairs>(Xs + qq, qa, qb, gq, kgs + 2 * qq);
         }
       }
       warp_reduce_scatter(kgs, tid & 31, &sm.dvred[tid >> 5][sg * kBwSeg]);
