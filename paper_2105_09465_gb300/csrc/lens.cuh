@@ -28,10 +28,11 @@ struct LensConst {
 
 // Subhalo record after per-CTA preparation (8 floats, 32 B).
 //  tNFW: x_h, y_h, 1/theta_s^2, A = 4 kappa_s tau^2/(tau^2+1)^2, tau, tau^2,
-//        (tau^2-1)/tau, C = tau pi + (tau^2-1) ln tau
+//        (tau^2-1)/tau * ln(2)/2, C = tau pi + (tau^2-1) ln tau
+//        (the ln(2)/2 turns log2 of x^2/(tau + st)^2 into ln(x/(tau + st)))
 //  point mass: x_h, y_h, theta_pm^2, 0...
 struct SubRec {
-  float xh, yh, its2, A, tau, tau2, t2m1_t, C;
+  float xh, yh, its2, A, tau, tau2, t2m1_l, C;
 };
 
 // R2^e in FP32 with the exponent product split into an integer part (applied
@@ -110,7 +111,6 @@ __device__ __forceinline__ float flg2(float x) {
   asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
   return r;
 }
-__device__ __forceinline__ float flog_half(float x) { return __fmul_rn(flg2(x), kHalfLn2); }
 
 // arctan(s) / s for s > 0, given is = 1/s. With t = min(s, 1/s) and u = t^2,
 // arctan(t) = t P(u), where P is a degree-8 polynomial fitted for this
@@ -196,9 +196,10 @@ __device__ __forceinline__ float tnfw_m(const SubRec& h, float R2) {
   const float st = fsqrt_pos(h.tau2 + x2);
   const float tp = h.tau + st;
   const float itp = frcp(tp);
-  const float L = flog(xx * itp);
+  const float l2 = flg2(xx * itp);  // ln(x/(tau + st)) = l2 ln 2
   float G;
   if (x2 < 0.25f) {
+    const float L = l2 * 0.69314718055994531f;
     const float is1 = frcp(1.0f + s);
     const float dlx2 = -fmaf(h.tau, is1, itp) * itp;
     const float dl = dlx2 * x2;
@@ -208,7 +209,7 @@ __device__ __forceinline__ float tnfw_m(const SubRec& h, float R2) {
              fmaf(2.0f, F, __fmul_rn(-kPi, itp)));
   } else {
     const float t2m1 = h.tau2 - 1.0f;
-    const float B = fmaf(st, fmaf(h.t2m1_t, L, -kPi), fmaf(fmaf(2.0f, x2, t2m1), F, h.C));
+    const float B = fmaf(st, fmaf(2.0f * h.t2m1_l, l2, -kPi), fmaf(fmaf(2.0f, x2, t2m1), F, h.C));
     G = B * frcp(x2);
   }
   return h.A * G;
@@ -228,9 +229,11 @@ __device__ __forceinline__ float pointmass_m(const SubRec& h, float R2) {
 // Four MUFU operations per pair: one reciprocal square root gives both
 // s = sqrt(eps) and 1/s (and 1/eps = (1/s)^2), one gives st = sqrt(tau^2 + x^2)
 // and 1/st, one reciprocal of x^2 (tau + st) gives both 1/(tau + st) and
-// 1/x^2, and ln(x/(tau + st)) = ln(x^2/(tau + st)^2)/2 needs no sqrt(x^2).
+// 1/x^2, and ln(x/(tau + st)) = log2(x^2/(tau + st)^2) ln(2)/2 needs no
+// sqrt(x^2) (L holds the log2; the record's (tau^2-1)/tau carries ln(2)/2).
 // Valid while x^2 (tau + st) stays finite in FP32 (x^2 < ~1e24).
-__device__ __forceinline__ bool tnfw_is_far(float x2) { return __fadd_rn(x2, -1.0f) >= 0.05f; }
+__device__ __forceinline__ bool tnfw_is_far_em1(float em1) { return em1 >= 0.05f; }
+__device__ __forceinline__ bool tnfw_is_far(float x2) { return tnfw_is_far_em1(__fadd_rn(x2, -1.0f)); }
 
 // Every step below is an explicitly rounded intrinsic, and the *2 forms
 // repeat the same steps on packed f32x2 pairs, so a pair gives the same bits
@@ -253,21 +256,21 @@ __device__ __forceinline__ TnfwFar tnfw_far_terms(const SubRec& h, float x2) {
   const float r = frcp(__fmul_rn(x2, tp));
   const float itp = __fmul_rn(x2, r);
   t.ix2 = __fmul_rn(tp, r);
-  t.L = flog_half(__fmul_rn(__fmul_rn(x2, itp), itp));
+  t.L = flg2(__fmul_rn(__fmul_rn(x2, itp), itp));  // log2(x^2/(tau + st)^2)
   return t;
 }
 
 __device__ __forceinline__ float tnfw_m_far(const SubRec& h, float x2) {
   const TnfwFar t = tnfw_far_terms(h, x2);
   const float t2m1 = __fadd_rn(h.tau2, -1.0f);
-  const float B = __fmaf_rn(t.st, __fmaf_rn(h.t2m1_t, t.L, -kPi),
+  const float B = __fmaf_rn(t.st, __fmaf_rn(h.t2m1_l, t.L, -kPi),
                             __fmaf_rn(__fmaf_rn(2.0f, x2, t2m1), t.F, h.C));
   return __fmul_rn(h.A, __fmul_rn(B, t.ix2));
 }
 
 // Two records (or one record twice) with every field as a packed pair.
 struct SubRec2 {
-  float2 xh, yh, its2, A, tau, tau2, t2m1_t, C;
+  float2 xh, yh, its2, A, tau, tau2, t2m1_l, C;
 };
 
 __device__ __forceinline__ SubRec2 sub_pair(const SubRec& a, const SubRec& b) {
@@ -278,7 +281,7 @@ __device__ __forceinline__ SubRec2 sub_pair(const SubRec& a, const SubRec& b) {
   r.A = make_float2(a.A, b.A);
   r.tau = make_float2(a.tau, b.tau);
   r.tau2 = make_float2(a.tau2, b.tau2);
-  r.t2m1_t = make_float2(a.t2m1_t, b.t2m1_t);
+  r.t2m1_l = make_float2(a.t2m1_l, b.t2m1_l);
   r.C = make_float2(a.C, b.C);
   return r;
 }
@@ -291,18 +294,19 @@ __device__ __forceinline__ SubRec sub_lane(const SubRec2& r, int k) {
   h.A = k ? r.A.y : r.A.x;
   h.tau = k ? r.tau.y : r.tau.x;
   h.tau2 = k ? r.tau2.y : r.tau2.x;
-  h.t2m1_t = k ? r.t2m1_t.y : r.t2m1_t.x;
+  h.t2m1_l = k ? r.t2m1_l.y : r.t2m1_l.x;
   h.C = k ? r.C.y : r.C.x;
   return h;
 }
 
 struct TnfwFar2 {
-  float2 F, is, st, ist, ix2, L;
+  float2 F, is, st, ist, ix2, L, em1;  // em1 = x^2 - 1, the bits tnfw_is_far tests
 };
 
 __device__ __forceinline__ TnfwFar2 tnfw_far_terms2(const SubRec2& h, float2 x2) {
   TnfwFar2 t;
   const float2 e = __fadd2_rn(x2, f2(-1.0f));
+  t.em1 = e;
   const float2 eps = make_float2(fmaxf(e.x, 0.05f), fmaxf(e.y, 0.05f));
   t.is = frsqrt2(eps);
   const float2 s = __fmul2_rn(eps, t.is);
@@ -315,14 +319,16 @@ __device__ __forceinline__ TnfwFar2 tnfw_far_terms2(const SubRec2& h, float2 x2)
   const float2 itp = __fmul2_rn(x2, r);
   t.ix2 = __fmul2_rn(tp, r);
   const float2 a = __fmul2_rn(__fmul2_rn(x2, itp), itp);
-  t.L = __fmul2_rn(make_float2(flg2(a.x), flg2(a.y)), f2(kHalfLn2));
+  t.L = make_float2(flg2(a.x), flg2(a.y));
   return t;
 }
 
-__device__ __forceinline__ float2 tnfw_m_far2(const SubRec2& h, float2 x2) {
+// em1 receives x^2 - 1 (tnfw_is_far_em1 tells the far lanes).
+__device__ __forceinline__ float2 tnfw_m_far2(const SubRec2& h, float2 x2, float2& em1) {
   const TnfwFar2 t = tnfw_far_terms2(h, x2);
+  em1 = t.em1;
   const float2 t2m1 = __fadd2_rn(h.tau2, f2(-1.0f));
-  const float2 B = __ffma2_rn(t.st, __ffma2_rn(h.t2m1_t, t.L, f2(-kPi)),
+  const float2 B = __ffma2_rn(t.st, __ffma2_rn(h.t2m1_l, t.L, f2(-kPi)),
                               __ffma2_rn(__ffma2_rn(f2(2.0f), x2, t2m1), t.F, h.C));
   return __fmul2_rn(h.A, __fmul2_rn(B, t.ix2));
 }
@@ -334,7 +340,7 @@ __device__ __forceinline__ SubRec prep_sub(const float* r, int profile) {
   h.yh = r[1];
   if (profile == LR_PROFILE_POINT_MASS) {
     h.its2 = r[2] * r[2];
-    h.A = h.tau = h.tau2 = h.t2m1_t = h.C = 0.f;
+    h.A = h.tau = h.tau2 = h.t2m1_l = h.C = 0.f;
   } else {
     const float ks = r[2], ts = r[3], tau = r[4];
     const float t2 = tau * tau;
@@ -342,7 +348,7 @@ __device__ __forceinline__ SubRec prep_sub(const float* r, int profile) {
     h.A = 4.0f * ks * t2 / ((t2 + 1.0f) * (t2 + 1.0f));
     h.tau = tau;
     h.tau2 = t2;
-    h.t2m1_t = (t2 - 1.0f) / tau;
+    h.t2m1_l = (t2 - 1.0f) / tau * kHalfLn2;
     h.C = fmaf(t2 - 1.0f, logf(tau), __fmul_rn(tau, kPi));  // explicit rounding: the same in every kernel
   }
   return h;
@@ -453,9 +459,11 @@ __device__ __forceinline__ void tnfw_GH(const SubRec& h, float R2, float& Gt, fl
   const float st = fsqrt_pos(h.tau2 + x2);
   const float tp = h.tau + st;
   const float itp = frcp(tp);
-  const float L = flog(xx * itp);
+  const float l2 = flg2(xx * itp);  // ln(x/(tau + st)) = l2 ln 2
+  const float lp = fmaf(2.0f * h.t2m1_l, l2, -kPi);
   const float t2m1 = h.tau2 - 1.0f;
   if (x2 < 0.25f) {
+    const float L = l2 * 0.69314718055994531f;
     const float is1 = frcp(1.0f + s);
     const float dlx2 = -fmaf(h.tau, is1, itp) * itp;
     const float dl = dlx2 * x2;
@@ -463,7 +471,7 @@ __device__ __forceinline__ void tnfw_GH(const SubRec& h, float R2, float& Gt, fl
     Gt = fmaf(t2m1, fmaf(F, is1, fmaf(dlx2, ratio, __fmul_rn(__fmul_rn(L, frcp(h.tau)), itp))),
               fmaf(2.0f, F, __fmul_rn(-kPi, itp)));
   } else {
-    const float B = fmaf(st, fmaf(h.t2m1_t, L, -kPi), fmaf(fmaf(2.0f, x2, t2m1), F, h.C));
+    const float B = fmaf(st, lp, fmaf(fmaf(2.0f, x2, t2m1), F, h.C));
     Gt = B * ix2;
   }
   const float eps = x2 - 1.0f;
@@ -480,14 +488,14 @@ __device__ __forceinline__ void tnfw_GH(const SubRec& h, float R2, float& Gt, fl
     omf = (1.0f - F) * frcp(eps);
   }
   const float ist = frcp(st);
-  Ht = fmaf(ist, fmaf(h.t2m1_t, L, -kPi), fmaf(2.0f, F, __fmul_rn(h.tau2 + 1.0f, omf)));
+  Ht = fmaf(ist, lp, fmaf(2.0f, F, __fmul_rn(h.tau2 + 1.0f, omf)));
 }
 
 // tnfw_GH on the far side (see tnfw_m_far), with 1/eps = (1/s)^2.
 __device__ __forceinline__ void tnfw_GH_far(const SubRec& h, float x2, float& Gt, float& Ht, float& ix2) {
   const TnfwFar t = tnfw_far_terms(h, x2);
   const float t2m1 = __fadd_rn(h.tau2, -1.0f);
-  const float lp = __fmaf_rn(h.t2m1_t, t.L, -kPi);
+  const float lp = __fmaf_rn(h.t2m1_l, t.L, -kPi);
   const float B = __fmaf_rn(t.st, lp, __fmaf_rn(__fmaf_rn(2.0f, x2, t2m1), t.F, h.C));
   Gt = __fmul_rn(B, t.ix2);
   ix2 = t.ix2;
@@ -495,10 +503,12 @@ __device__ __forceinline__ void tnfw_GH_far(const SubRec& h, float x2, float& Gt
   Ht = __fmaf_rn(t.ist, lp, __fmaf_rn(2.0f, t.F, __fmul_rn(__fadd_rn(h.tau2, 1.0f), omf)));
 }
 
-__device__ __forceinline__ void tnfw_GH_far2(const SubRec2& h, float2 x2, float2& Gt, float2& Ht, float2& ix2) {
+__device__ __forceinline__ void tnfw_GH_far2(const SubRec2& h, float2 x2, float2& Gt, float2& Ht, float2& ix2,
+                                             float2& em1) {
   const TnfwFar2 t = tnfw_far_terms2(h, x2);
+  em1 = t.em1;
   const float2 t2m1 = __fadd2_rn(h.tau2, f2(-1.0f));
-  const float2 lp = __ffma2_rn(h.t2m1_t, t.L, f2(-kPi));
+  const float2 lp = __ffma2_rn(h.t2m1_l, t.L, f2(-kPi));
   const float2 B = __ffma2_rn(t.st, lp, __ffma2_rn(__ffma2_rn(f2(2.0f), x2, t2m1), t.F, h.C));
   Gt = __fmul2_rn(B, t.ix2);
   ix2 = t.ix2;

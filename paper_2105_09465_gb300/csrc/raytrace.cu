@@ -36,7 +36,7 @@ __device__ __forceinline__ void kahan(float& s, float& c, float x) {
 // Staged subhalos, as consecutive pairs (a, b), field by field as packed
 // pairs. The hot words are all the series needs:
 //   [0] (xh, yh)  [1] (its2, A)  [2] (xT2, q0)  [3..6] (q2, q3) .. (q8, q9);
-// the cold words the closed forms: [0] (tau, tau2)  [1] (t2m1_t, C).
+// the cold words the closed forms: [0] (tau, tau2)  [1] (t2m1_l, C).
 constexpr int kRtHot = 7, kRtCold = 2;
 
 struct RtSmem {
@@ -61,7 +61,7 @@ __device__ __forceinline__ SubRec2 rec_from(const float4* hot, const float4* col
   r.A = hi2(hot[1]);
   r.tau = lo2(cold[0]);
   r.tau2 = hi2(cold[0]);
-  r.t2m1_t = lo2(cold[1]);
+  r.t2m1_l = lo2(cold[1]);
   r.C = hi2(cold[1]);
   return r;
 }
@@ -126,7 +126,7 @@ __device__ __forceinline__ bool stage_rt(const float* __restrict__ sub, int h0, 
     for (int w = 0; w < 4; ++w)
       hot[3 + w] = make_float4(sa.q[2 + 2 * w], sb.q[2 + 2 * w], sa.q[3 + 2 * w], sb.q[3 + 2 * w]);
     sm.cold[k][0] = make_float4(a.tau, b.tau, a.tau2, b.tau2);
-    sm.cold[k][1] = make_float4(a.t2m1_t, b.t2m1_t, a.C, b.C);
+    sm.cold[k][1] = make_float4(a.t2m1_l, b.t2m1_l, a.C, b.C);
   }
   __syncthreads();
   return true;
@@ -169,8 +169,9 @@ __device__ __forceinline__ void add_subs(const RtSmem& sm, int cnt, float x, flo
           // gives the same bits for far pairs)
           const SubRec2 H = rec_from(hot, sm.cold[t >> 1]);
           const bool sa = x2.x >= w2.x, sb = x2.y >= w2.y;
-          m = tnfw_m_far2(H, x2);
-          const bool na = !tnfw_is_far(x2.x), nb = !tnfw_is_far(x2.y);
+          float2 em1;
+          m = tnfw_m_far2(H, x2, em1);
+          const bool na = !tnfw_is_far_em1(em1.x), nb = !tnfw_is_far_em1(em1.y);
           if (na || nb) {  // rare: one branch for both lanes
             if (na) m.x = tnfw_m(sub_lane(H, 0), R2.x);
             if (nb) m.y = tnfw_m(sub_lane(H, 1), R2.y);

@@ -95,17 +95,18 @@ __device__ __forceinline__ void vj_sweep(const SubRec& rec, float2 ex, const flo
         // the far-side form for both points; the rare near ones are redone
         // by the general form (the same bits where both apply)
         const float2 x2 = __fmul2_rn(R2, H.its2);
-        float2 Gt, Ht, ix2;
-        tnfw_GH_far2(H, x2, Gt, Ht, ix2);
-        const bool na = !tnfw_is_far(x2.x), nb = !tnfw_is_far(x2.y);
+        float2 Gt, Ht, ix2, em1;
+        tnfw_GH_far2(H, x2, Gt, Ht, ix2, em1);
+        const bool na = !tnfw_is_far_em1(em1.x), nb = !tnfw_is_far_em1(em1.y);
         if (na || nb) {  // rare: one branch for both lanes
           if (na) tnfw_GH(rec, R2.x, Gt.x, Ht.x, ix2.x);
           if (nb) tnfw_GH(rec, R2.y, Gt.y, Ht.y, ix2.y);
+          // a point on the subhalo centre adds nothing: a zero gradient makes
+          // every term 0. R^2 <= 1e-30 is a near pair for any theta_s above
+          // 1e-15 (x^2 = R^2 / theta_s^2 < 1.05), so the test lives here.
+          gx = make_float2(R2.x > 1e-30f ? gx.x : 0.f, R2.y > 1e-30f ? gx.y : 0.f);
+          gy = make_float2(R2.x > 1e-30f ? gy.x : 0.f, R2.y > 1e-30f ? gy.y : 0.f);
         }
-        // a point on the subhalo centre adds nothing: its G, H and 1/x^2 are
-        // finite (0 at x = 0), so a zero G makes every term 0
-        gx = make_float2(R2.x > 1e-30f ? gx.x : 0.f, R2.y > 1e-30f ? gx.y : 0.f);
-        gy = make_float2(R2.x > 1e-30f ? gy.x : 0.f, R2.y > 1e-30f ? gy.y : 0.f);
         vj_accum2(dx, dy, gx, gy, __fmul2_rn(H.its2, ix2), Gt, Ht, a0, a1, a2, a3);
       } else {
         // point mass: alpha = theta^2 d / R^2 (its2 = theta^2, ex.y = theta)
