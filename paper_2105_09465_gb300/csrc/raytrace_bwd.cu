@@ -46,18 +46,23 @@ struct VjSmem {
 };
 
 // One tNFW pair's terms of the four subhalo sums, for two points at once
-// (packed f32x2; iR2 = 1/R^2), without the subhalo's constant factors: with
-// dg = d.G and hg = H - 2G,
-//   a0 += G G_x + q dx, a1 += G G_y + q dy (q = hg dg / R^2), a2 += G dg,
-//   a3 += hg dg;
-// the slot's sums are scaled once by (A, A, -4T, A / theta_s) (vj_scale).
-__device__ __forceinline__ void vj_accum2(float2 dx, float2 dy, float2 gx, float2 gy, float2 iR2, float2 Gt,
-                                          float2 Ht, float2& a0, float2& a1, float2& a2, float2& a3) {
+// (packed f32x2; ix2 = 1/x^2 = theta_s^2 / R^2), without the subhalo's
+// constant factors: with dg = d.G and hg = H - 2G,
+//   sum 0 = G G_x + q dx, sum 1 = G G_y + q dy (q = hg dg / R^2),
+//   sum 2 = G dg, sum 3 = hg dg.
+// The q terms are kept apart (b0, b1, with hg dg / x^2 in place of q) and
+// join sums 0 and 1 with the factor 1/theta_s^2 once per fold; the slot's
+// sums are scaled once by (A, A, -4T, A / theta_s) (vj_scale).
+__device__ __forceinline__ void vj_accum2(float2 dx, float2 dy, float2 gx, float2 gy, float2 ix2, float2 Gt,
+                                          float2 Ht, float2& a0, float2& a1, float2& a2, float2& a3, float2& b0,
+                                          float2& b1) {
   const float2 dg = __ffma2_rn(dx, gx, __fmul2_rn(dy, gy));
   const float2 hg = __ffma2_rn(f2(-2.0f), Gt, Ht);
-  const float2 q = __fmul2_rn(__fmul2_rn(hg, dg), iR2);
-  a0 = __ffma2_rn(Gt, gx, __ffma2_rn(q, dx, a0));
-  a1 = __ffma2_rn(Gt, gy, __ffma2_rn(q, dy, a1));
+  const float2 q = __fmul2_rn(__fmul2_rn(hg, dg), ix2);
+  b0 = __ffma2_rn(q, dx, b0);
+  b1 = __ffma2_rn(q, dy, b1);
+  a0 = __ffma2_rn(Gt, gx, a0);
+  a1 = __ffma2_rn(Gt, gy, a1);
   a2 = __ffma2_rn(Gt, dg, a2);
   a3 = __ffma2_rn(hg, dg, a3);
 }
@@ -85,7 +90,7 @@ __device__ __forceinline__ void vj_sweep(const SubRec& rec, float2 ex, const flo
   const SubRec2 H = sub_pair(rec, rec);
   for (int k = r; k < npairs;) {
     const int kend = min(npairs, k + P * kVjFold);
-    float2 a0 = f2(0.f), a1 = f2(0.f), a2 = f2(0.f), a3 = f2(0.f);
+    float2 a0 = f2(0.f), a1 = f2(0.f), a2 = f2(0.f), a3 = f2(0.f), b0 = f2(0.f), b1 = f2(0.f);
     for (; k < kend; k += P) {
       const float4 Q = pos[k], D = grad[k];
       const float2 dx = sub2(make_float2(Q.x, Q.y), H.xh), dy = sub2(make_float2(Q.z, Q.w), H.yh);
@@ -107,7 +112,7 @@ __device__ __forceinline__ void vj_sweep(const SubRec& rec, float2 ex, const flo
           gx = make_float2(R2.x > 1e-30f ? gx.x : 0.f, R2.y > 1e-30f ? gx.y : 0.f);
           gy = make_float2(R2.x > 1e-30f ? gy.x : 0.f, R2.y > 1e-30f ? gy.y : 0.f);
         }
-        vj_accum2(dx, dy, gx, gy, __fmul2_rn(H.its2, ix2), Gt, Ht, a0, a1, a2, a3);
+        vj_accum2(dx, dy, gx, gy, ix2, Gt, Ht, a0, a1, a2, a3, b0, b1);
       } else {
         // point mass: alpha = theta^2 d / R^2 (its2 = theta^2, ex.y = theta)
         float2 iR2 = make_float2(R2.x > 1e-30f ? frcp(R2.x) : 0.f, R2.y > 1e-30f ? frcp(R2.y) : 0.f);
@@ -118,6 +123,10 @@ __device__ __forceinline__ void vj_sweep(const SubRec& rec, float2 ex, const flo
         a1 = __ffma2_rn(m, __ffma2_rn(q, dy, gy), a1);
         a2 = __ffma2_rn(f2(-2.0f * ex.y), __fmul2_rn(dg, iR2), a2);
       }
+    }
+    if (PROFILE == LR_PROFILE_TNFW) {
+      a0.x = __fmaf_rn(rec.its2, __fadd_rn(b0.x, b0.y), a0.x);
+      a1.x = __fmaf_rn(rec.its2, __fadd_rn(b1.x, b1.y), a1.x);
     }
     vj_kahan(s[0], c[0], __fadd_rn(a0.x, a0.y));
     vj_kahan(s[1], c[1], __fadd_rn(a1.x, a1.y));
@@ -233,7 +242,7 @@ __device__ __forceinline__ void vjp_body(const LensConst& L, const LensGradConst
 }
 
 template <int PROFILE>
-__global__ void __launch_bounds__(kVjThreads, 6) raytrace_vjp_kernel(const __grid_constant__ LensConst L,
+__global__ void __launch_bounds__(kVjThreads, 5) raytrace_vjp_kernel(const __grid_constant__ LensConst L,
                                                                   const __grid_constant__ LensGradConst LG, GridDev g,
                                                                   const float2* __restrict__ xi, int64_t n,
                                                                   const float* __restrict__ sub, int n_sub, int P,
@@ -246,7 +255,7 @@ __global__ void __launch_bounds__(kVjThreads, 6) raytrace_vjp_kernel(const __gri
                     sm);
 }
 
-__global__ void __launch_bounds__(kVjThreads, 6) vjp_batched_kernel(const __grid_constant__ Batch<VjpP> B) {
+__global__ void __launch_bounds__(kVjThreads, 5) vjp_batched_kernel(const __grid_constant__ Batch<VjpP> B) {
   __shared__ __align__(16) VjSmem sm;
   const int k = batch_find(B, blockIdx.x);
   const VjpP& P = B.p[k];
