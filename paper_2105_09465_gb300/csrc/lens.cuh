@@ -224,7 +224,8 @@ __device__ __forceinline__ float pointmass_m(const SubRec& h, float R2) {
 // direct bracket), as straight-line code so that several pairs can be
 // interleaved. tnfw_m and tnfw_GH return exactly these values for far x^2
 // (they call the same code), so a pair gives the same bits on either path.
-// Other x^2 give a finite value that the caller replaces.
+// Other x^2 give a finite value (the packed *2 forms: any value, NaN for
+// x^2 < 1) that the caller replaces.
 //
 // Four MUFU operations per pair: one reciprocal square root gives both
 // s = sqrt(eps) and 1/s (and 1/eps = (1/s)^2), one gives st = sqrt(tau^2 + x^2)
@@ -307,7 +308,7 @@ __device__ __forceinline__ TnfwFar2 tnfw_far_terms2(const SubRec2& h, float2 x2)
   TnfwFar2 t;
   const float2 e = __fadd2_rn(x2, f2(-1.0f));
   t.em1 = e;
-  const float2 eps = make_float2(fmaxf(e.x, 0.05f), fmaxf(e.y, 0.05f));
+  const float2 eps = e;  // no clamp: a near lane's value (NaN for x^2 < 1) is replaced by the caller
   t.is = frsqrt2(eps);
   const float2 s = __fmul2_rn(eps, t.is);
   t.F = atan_over2(s, t.is);
