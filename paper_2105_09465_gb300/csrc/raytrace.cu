@@ -1,6 +1,6 @@
 // Pixel-grid generation and the lens ray-trace beta = xi - alpha(xi).
 //
-// One thread per image-plane point. The SPLE and shear terms are evaluated in
+// Two image-plane points per thread. The SPLE and shear terms are evaluated in
 // registers from per-lens constants passed as a kernel parameter; the
 // subhalo records are staged into shared memory in chunks by a bulk
 // asynchronous copy (the TMA engine's 1-D form) and reused by every point of
@@ -14,9 +14,11 @@
 
 namespace lr {
 
-constexpr int kRtThreads = 256;
+constexpr int kRtThreads = 128;
+constexpr int kRtPts = 2;                        // points per thread
+constexpr int kRtPoints = kRtThreads * kRtPts;   // points per CTA
 constexpr int kRtTile = 16;  // grid input: a CTA takes a kRtTile x kRtTile tile of pixels
-static_assert(kRtTile * kRtTile == kRtThreads, "one thread per pixel of a tile");
+static_assert(kRtTile * kRtTile == kRtPoints, "the CTA's points are one tile");
 constexpr int kSubChunk = 256;  // subhalos staged per chunk (multiple of 4)
 
 __global__ void grid_points_kernel(GridDev g, int64_t n, float2* out) {
@@ -132,26 +134,33 @@ __device__ __forceinline__ bool stage_rt(const float* __restrict__ sub, int h0, 
   return true;
 }
 
-// Deflection of the staged subhalos at (x, y), added to the Kahan sums
-// (sx, cx), (sy, cy). Blocks of kRtFold subhalos are summed plainly in two
-// packed lanes and folded into the Kahan sums; the order is fixed, so every
-// kernel that calls this gets the same bits.
+// Deflection of the staged subhalos at the thread's kRtPts points (x[j],
+// y[j]), added to the Kahan sums (sx, cx), (sy, cy) of each point. Blocks of
+// kRtFold subhalos are summed plainly in two packed lanes and folded into the
+// Kahan sums; the order is fixed, so a point's bits do not depend on the
+// other points of its thread. Each staged record is read once for all of
+// the thread's points.
 template <int PROFILE>
-__device__ __forceinline__ void add_subs(const RtSmem& sm, int cnt, float x, float y, float& sx, float& cx,
-                                         float& sy, float& cy) {
-  const float2 X = f2(x), Y = f2(y);
+__device__ __forceinline__ void add_subs(const RtSmem& sm, int cnt, const float (&x)[kRtPts],
+                                         const float (&y)[kRtPts], float (&sx)[kRtPts], float (&cx)[kRtPts],
+                                         float (&sy)[kRtPts], float (&cy)[kRtPts]) {
+  float2 X[kRtPts], Y[kRtPts];
+#pragma unroll
+  for (int j = 0; j < kRtPts; ++j) {
+    X[j] = f2(x[j]);
+    Y[j] = f2(y[j]);
+  }
   const int nfe = sm.nfar & ~1;  // pairs below nfe: both subhalos are far from every point of the CTA
   for (int t0 = 0; t0 < cnt; t0 += kRtFold) {
     const int t1 = min(cnt, t0 + kRtFold);
-    float2 ax = f2(0.f), ay = f2(0.f);
+    float2 ax[kRtPts], ay[kRtPts];
+#pragma unroll
+    for (int j = 0; j < kRtPts; ++j) ax[j] = ay[j] = f2(0.f);
     int t = t0;
     if (PROFILE == LR_PROFILE_TNFW) {
       for (; t + 1 < t1; t += 2) {
         const float4* hot = sm.hot[t >> 1];
         const float4 w0 = hot[0], w1 = hot[1], w2 = hot[2];
-        const float2 dx = sub2(X, make_float2(w0.x, w0.y)), dy = sub2(Y, make_float2(w0.z, w0.w));
-        const float2 R2 = __ffma2_rn(dx, dx, __fmul2_rn(dy, dy));
-        const float2 x2 = __fmul2_rn(R2, lo2(w1));
         float2 q[kSerTerms];
 #pragma unroll
         for (int w = 0; w < 4; ++w) {
@@ -159,50 +168,68 @@ __device__ __forceinline__ void add_subs(const RtSmem& sm, int cnt, float x, flo
           q[2 + 2 * w] = lo2(c);
           q[3 + 2 * w] = hi2(c);
         }
-        float2 m;
         if (t + 1 < nfe) {
           // both subhalos far from the whole CTA: the series, no tests
-          m = tnfw_m_series2(hi2(w1), hi2(w2), q, x2);
+#pragma unroll
+          for (int j = 0; j < kRtPts; ++j) {
+            const float2 dx = sub2(X[j], make_float2(w0.x, w0.y)), dy = sub2(Y[j], make_float2(w0.z, w0.w));
+            const float2 R2 = __ffma2_rn(dx, dx, __fmul2_rn(dy, dy));
+            const float2 m = tnfw_m_series2(hi2(w1), hi2(w2), q, __fmul2_rn(R2, lo2(w1)));
+            ax[j] = __ffma2_rn(m, dx, ax[j]);
+            ay[j] = __ffma2_rn(m, dy, ay[j]);
+          }
         } else {
           // the series where x^2 reaches its radius, else the packed far-side
           // closed form, and the rare near pairs the general form (which
           // gives the same bits for far pairs)
           const SubRec2 H = rec_from(hot, sm.cold[t >> 1]);
-          const bool sa = x2.x >= w2.x, sb = x2.y >= w2.y;
-          float2 em1;
-          m = tnfw_m_far2(H, x2, em1);
-          const bool na = !tnfw_is_far_em1(em1.x), nb = !tnfw_is_far_em1(em1.y);
-          if (na || nb) {  // rare: one branch for both lanes
-            if (na) m.x = tnfw_m(sub_lane(H, 0), R2.x);
-            if (nb) m.y = tnfw_m(sub_lane(H, 1), R2.y);
-          }
-          if (sa || sb) {
-            const float2 ms = tnfw_m_series2(hi2(w1), hi2(w2), q, x2);
-            if (sa) m.x = ms.x;
-            if (sb) m.y = ms.y;
+#pragma unroll
+          for (int j = 0; j < kRtPts; ++j) {
+            const float2 dx = sub2(X[j], make_float2(w0.x, w0.y)), dy = sub2(Y[j], make_float2(w0.z, w0.w));
+            const float2 R2 = __ffma2_rn(dx, dx, __fmul2_rn(dy, dy));
+            const float2 x2 = __fmul2_rn(R2, lo2(w1));
+            const bool sa = x2.x >= w2.x, sb = x2.y >= w2.y;
+            float2 em1;
+            float2 m = tnfw_m_far2(H, x2, em1);
+            const bool na = !tnfw_is_far_em1(em1.x), nb = !tnfw_is_far_em1(em1.y);
+            if (na || nb) {  // rare: one branch for both lanes
+              if (na) m.x = tnfw_m(sub_lane(H, 0), R2.x);
+              if (nb) m.y = tnfw_m(sub_lane(H, 1), R2.y);
+            }
+            if (sa || sb) {
+              const float2 ms = tnfw_m_series2(hi2(w1), hi2(w2), q, x2);
+              if (sa) m.x = ms.x;
+              if (sb) m.y = ms.y;
+            }
+            ax[j] = __ffma2_rn(m, dx, ax[j]);
+            ay[j] = __ffma2_rn(m, dy, ay[j]);
           }
         }
-        ax = __ffma2_rn(m, dx, ax);
-        ay = __ffma2_rn(m, dy, ay);
       }
     }
     for (; t < t1; ++t) {
       const float4* hot = sm.hot[t >> 1];
       const SubRec h = sub_lane(rec_from(hot, sm.cold[t >> 1]), t & 1);
-      const float dx = __fsub_rn(x, h.xh), dy = __fsub_rn(y, h.yh);
-      const float R2 = __fmaf_rn(dx, dx, __fmul_rn(dy, dy));
-      const float m = (PROFILE == LR_PROFILE_POINT_MASS) ? pointmass_m(h, R2)
-                                                         : tnfw_m_any(h, ser_from(hot, t & 1), R2);
-      if (t & 1) {
-        ax.y = __fmaf_rn(m, dx, ax.y);
-        ay.y = __fmaf_rn(m, dy, ay.y);
-      } else {
-        ax.x = __fmaf_rn(m, dx, ax.x);
-        ay.x = __fmaf_rn(m, dy, ay.x);
+#pragma unroll
+      for (int j = 0; j < kRtPts; ++j) {
+        const float dx = __fsub_rn(x[j], h.xh), dy = __fsub_rn(y[j], h.yh);
+        const float R2 = __fmaf_rn(dx, dx, __fmul_rn(dy, dy));
+        const float m = (PROFILE == LR_PROFILE_POINT_MASS) ? pointmass_m(h, R2)
+                                                           : tnfw_m_any(h, ser_from(hot, t & 1), R2);
+        if (t & 1) {
+          ax[j].y = __fmaf_rn(m, dx, ax[j].y);
+          ay[j].y = __fmaf_rn(m, dy, ay[j].y);
+        } else {
+          ax[j].x = __fmaf_rn(m, dx, ax[j].x);
+          ay[j].x = __fmaf_rn(m, dy, ay[j].x);
+        }
       }
     }
-    kahan(sx, cx, __fadd_rn(ax.x, ax.y));
-    kahan(sy, cy, __fadd_rn(ay.x, ay.y));
+#pragma unroll
+    for (int j = 0; j < kRtPts; ++j) {
+      kahan(sx[j], cx[j], __fadd_rn(ax[j].x, ax[j].y));
+      kahan(sy[j], cy[j], __fadd_rn(ay[j].x, ay[j].y));
+    }
   }
 }
 
@@ -211,33 +238,47 @@ __device__ __forceinline__ void raytrace_body(const LensConst& L, const GridDev&
                                               int64_t n, const float* __restrict__ sub, int n_sub, int bulk_ok,
                                               float2* __restrict__ beta, float2* __restrict__ alpha_out, int* fault,
                                               int64_t blk, RtSmem& sm) {
-  // explicit points: kRtThreads consecutive ones; grid: a 2-D tile, so that
-  // the CTA's points are compact (padding threads repeat an edge point)
-  int64_t i, ii;
-  bool valid;
-  if (xi) {
-    i = blk * kRtThreads + threadIdx.x;
-    valid = i < n;
-    ii = valid ? i : (n - 1);
-  } else {
-    const int tw = (g.W + kRtTile - 1) / kRtTile;
-    const int ty = (int)(blk / tw), tx = (int)(blk - (int64_t)ty * tw);
-    const int row = ty * kRtTile + (int)threadIdx.x / kRtTile, col = tx * kRtTile + (int)threadIdx.x % kRtTile;
-    valid = row < g.H && col < g.W;
-    i = (int64_t)row * g.W + col;
-    ii = (int64_t)min(row, g.H - 1) * g.W + min(col, g.W - 1);
+  // explicit points: kRtPoints consecutive ones; grid: a 2-D tile, so that
+  // the CTA's points are compact (padding points repeat an edge point).
+  // Thread t takes the CTA's points t + j kRtThreads (j < kRtPts).
+  int64_t i[kRtPts];
+  bool valid[kRtPts];
+  float px[kRtPts], py[kRtPts], ax[kRtPts], ay[kRtPts];
+#pragma unroll
+  for (int j = 0; j < kRtPts; ++j) {
+    const int w = (int)threadIdx.x + j * kRtThreads;
+    int64_t ii;
+    if (xi) {
+      i[j] = blk * kRtPoints + w;
+      valid[j] = i[j] < n;
+      ii = valid[j] ? i[j] : (n - 1);
+    } else {
+      const int tw = (g.W + kRtTile - 1) / kRtTile;
+      const int ty = (int)(blk / tw), tx = (int)(blk - (int64_t)ty * tw);
+      const int row = ty * kRtTile + w / kRtTile, col = tx * kRtTile + w % kRtTile;
+      valid[j] = row < g.H && col < g.W;
+      i[j] = (int64_t)row * g.W + col;
+      ii = (int64_t)min(row, g.H - 1) * g.W + min(col, g.W - 1);
+    }
+    const float2 p = xi ? xi[ii] : grid_point(g, ii);
+    px[j] = p.x;
+    py[j] = p.y;
+    sple_alpha(L, p.x, p.y, ax[j], ay[j]);
+    // external shear about the origin
+    ax[j] = fmaf(L.g1, p.x, fmaf(L.g2, p.y, ax[j]));
+    ay[j] = fmaf(L.g2, p.x, fmaf(-L.g1, p.y, ay[j]));
   }
-  const float2 p = xi ? xi[ii] : grid_point(g, ii);
-
-  float ax, ay;
-  sple_alpha(L, p.x, p.y, ax, ay);
-  // external shear about the origin
-  ax = fmaf(L.g1, p.x, fmaf(L.g2, p.y, ax));
-  ay = fmaf(L.g2, p.x, fmaf(-L.g1, p.y, ay));
 
   if (n_sub > 0) {
-    // the box of the CTA's points (the padding rows repeat the last point)
-    float b0 = p.x, b1 = p.y, b2 = p.x, b3 = p.y;
+    // the box of the CTA's points (the padding points repeat an edge point)
+    float b0 = px[0], b1 = py[0], b2 = px[0], b3 = py[0];
+#pragma unroll
+    for (int j = 1; j < kRtPts; ++j) {
+      b0 = fminf(b0, px[j]);
+      b1 = fminf(b1, py[j]);
+      b2 = fmaxf(b2, px[j]);
+      b3 = fmaxf(b3, py[j]);
+    }
 #pragma unroll
     for (int o = 16; o; o >>= 1) {
       b0 = fminf(b0, __shfl_xor_sync(0xffffffffu, b0, o));
@@ -269,24 +310,32 @@ __device__ __forceinline__ void raytrace_body(const LensConst& L, const GridDev&
     }
     __syncthreads();
     uint32_t phase = 0;
-    float sx = 0.f, cx = 0.f, sy = 0.f, cy = 0.f;
+    float sx[kRtPts], cx[kRtPts], sy[kRtPts], cy[kRtPts];
+#pragma unroll
+    for (int j = 0; j < kRtPts; ++j) sx[j] = cx[j] = sy[j] = cy[j] = 0.f;
     for (int h0 = 0; h0 < n_sub; h0 += kSubChunk) {
       const int cnt = min(kSubChunk, n_sub - h0);
       if (!stage_rt(sub, h0, cnt, PROFILE, sm, phase, bulk_ok != 0, fault)) return;
-      add_subs<PROFILE>(sm, cnt, p.x, p.y, sx, cx, sy, cy);
+      add_subs<PROFILE>(sm, cnt, px, py, sx, cx, sy, cy);
       __syncthreads();
     }
-    ax += sx - cx;
-    ay += sy - cy;
+#pragma unroll
+    for (int j = 0; j < kRtPts; ++j) {
+      ax[j] += sx[j] - cx[j];
+      ay[j] += sy[j] - cy[j];
+    }
   }
-  if (valid) {
-    beta[i] = make_float2(p.x - ax, p.y - ay);
-    if (alpha_out) alpha_out[i] = make_float2(ax, ay);
+#pragma unroll
+  for (int j = 0; j < kRtPts; ++j) {
+    if (valid[j]) {
+      beta[i[j]] = make_float2(px[j] - ax[j], py[j] - ay[j]);
+      if (alpha_out) alpha_out[i[j]] = make_float2(ax[j], ay[j]);
+    }
   }
 }
 
 template <int PROFILE>
-__global__ void __launch_bounds__(kRtThreads, 3) raytrace_kernel(const __grid_constant__ LensConst L, GridDev g,
+__global__ void __launch_bounds__(kRtThreads, 5) raytrace_kernel(const __grid_constant__ LensConst L, GridDev g,
                                                               const float2* __restrict__ xi, int64_t n,
                                                               const float* __restrict__ sub, int n_sub, int bulk_ok,
                                                               float2* __restrict__ beta,
@@ -295,7 +344,7 @@ __global__ void __launch_bounds__(kRtThreads, 3) raytrace_kernel(const __grid_co
   raytrace_body<PROFILE>(L, g, xi, n, sub, n_sub, bulk_ok, beta, alpha_out, fault, blockIdx.x, sm);
 }
 
-__global__ void __launch_bounds__(kRtThreads, 3) raytrace_batched_kernel(const __grid_constant__ Batch<RtP> B,
+__global__ void __launch_bounds__(kRtThreads, 5) raytrace_batched_kernel(const __grid_constant__ Batch<RtP> B,
                                                                       int* fault) {
   __shared__ __align__(16) RtSmem sm;
   const int k = batch_find(B, blockIdx.x);
@@ -309,9 +358,9 @@ __global__ void __launch_bounds__(kRtThreads, 3) raytrace_batched_kernel(const _
                                    sm);
 }
 
-// CTAs of the ray-trace: kRtThreads points each, or one per grid tile.
+// CTAs of the ray-trace: kRtPoints points each, or one per grid tile.
 static int64_t rt_blocks(bool explicit_points, const GridDev& g, int64_t n) {
-  if (explicit_points) return (n + kRtThreads - 1) / kRtThreads;
+  if (explicit_points) return (n + kRtPoints - 1) / kRtPoints;
   return (int64_t)((g.W + kRtTile - 1) / kRtTile) * ((g.H + kRtTile - 1) / kRtTile);
 }
 
