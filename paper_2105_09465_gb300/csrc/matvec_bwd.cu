@@ -51,6 +51,25 @@ __device__ __forceinline__ void warp_reduce_scatter(float (&kgs)[kBwSeg], int la
   if ((lane & 1) == 0) dvred_w[(lane >> 1) & 15] = kgs[0];
 }
 
+// The same reduction for kgs filled in the lane-permuted order of dv_pairs_perm
+// (slot pp of lane l holds source pair pp ^ ((l >> 2) & 7)): at every halving
+// the half a lane keeps is already its lower half, so only the last pair needs
+// a select. The lanes combine in the same tree as above, so the sums are the
+// same bits.
+__device__ __forceinline__ void warp_reduce_scatter_perm(float (&kgs)[kBwSeg], int lane, float* dvred_w) {
+#pragma unroll
+  for (int h = kBwSeg / 2, m = 16; h >= 2; h >>= 1, m >>= 1) {
+#pragma unroll
+    for (int i = 0; i < h; ++i) kgs[i] += __shfl_xor_sync(0xffffffffu, kgs[i + h], m);
+  }
+  const bool upper = (lane & 2) != 0;
+  const float send = upper ? kgs[0] : kgs[1];
+  const float keep = upper ? kgs[1] : kgs[0];
+  kgs[0] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
+  kgs[0] += __shfl_xor_sync(0xffffffffu, kgs[0], 1);
+  if ((lane & 1) == 0) dvred_w[(lane >> 1) & 15] = kgs[0];
+}
+
 __device__ __forceinline__ void bw_tile_range(const BwSrc& S, int t, int64_t& j0, int& cnt, int& grow) {
   if (S.xy) {
     j0 = (int64_t)t * kBwTile;
@@ -687,6 +706,20 @@ __device__ __forceinline__ void dv_pairs(const float2* __restrict__ X, const flo
   }
 }
 
+// All kBwSeg / 2 pairs of a sub-segment in the lane-permuted order that
+// warp_reduce_scatter_perm expects: slot pp of lane l takes pair
+// pp ^ ((l >> 2) & 7) (eight distinct records of one 64-byte block across
+// the warp: no bank conflict).
+template <bool SPLIT>
+__device__ __forceinline__ void dv_pairs_perm(const float2* __restrict__ X, const float2 (&qa)[kDvR],
+                                              const float2 (&qb)[kDvR], const float2 (&gq)[kDvR],
+                                              float (&kgs)[kBwSeg], int lane) {
+  static_assert(kBwSeg == 16, "the permutation spans the 8 pairs of a 16-column sub-segment");
+  const int kp = (lane >> 2) & 7;
+#pragma unroll
+  for (int pp = 0; pp < kBwSeg / 2; ++pp) dv_pairs<SPLIT, 1>(X + (pp ^ kp), qa, qb, gq, kgs + 2 * pp);
+}
+
 template <bool SPLIT>
 __device__ __forceinline__ void dv_rows_body(const BwArgs& A, int rb, int chunk, DvSmem& sm) {
   RowBlockInfo B{};
@@ -769,8 +802,10 @@ __device__ __forceinline__ void dv_rows_body(const BwArgs& A, int rb, int chunk,
       float kgs[kBwSeg];
       const float2* Xs = &sm.sX[buf][sg * (kBwSeg / 2)];
       if (pl == 0 && ph == kBwSeg / 2) {
-        // a sub-segment wholly in reach: one block without quarter tests
-        dv_pairs<SPLIT, kBwSeg / 2>(Xs, qa, qb, gq, kgs);
+        // a sub-segment wholly in reach: one block without quarter tests, in
+        // the lane-permuted order
+        dv_pairs_perm<SPLIT>(Xs, qa, qb, gq, kgs, tid & 31);
+        warp_reduce_scatter_perm(kgs, tid & 31, &sm.dvred[tid >> 5][sg * kBwSeg]);
       } else {
 #pragma unroll
         for (int qq = 0; qq < kBwSeg / 2; qq += kQuarterPairs) {
@@ -781,8 +816,8 @@ __device__ __forceinline__ void dv_rows_body(const BwArgs& A, int rb, int chunk,
           }
           dv_pairs<SPLIT, kQuarterPairs>(Xs + qq, qa, qb, gq, kgs + 2 * qq);
         }
+        warp_reduce_scatter(kgs, tid & 31, &sm.dvred[tid >> 5][sg * kBwSeg]);
       }
-      warp_reduce_scatter(kgs, tid & 31, &sm.dvred[tid >> 5][sg * kBwSeg]);
     }
     __syncthreads();
     // combine the warps in order; row block rb owns these columns of
