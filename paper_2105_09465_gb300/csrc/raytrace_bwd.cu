@@ -83,6 +83,22 @@ __device__ __forceinline__ void vj_kahan(float& s, float& c, float x) {
 }
 
 // Sums of one slot over the staged point pairs k = r, r + P, ... < npairs.
+// The rare near points of a tNFW step: the general form for the lanes with
+// x^2 - 1 < 0.05, and a zero gradient for a point on the subhalo centre (a
+// zero gradient makes every term 0; R^2 <= 1e-30 is a near pair for any
+// theta_s above 1e-15, since x^2 = R^2 / theta_s^2 < 1.05, so the test lives
+// here).
+__device__ __forceinline__ void vj_fix_near(const SubRec& rec, float2 R2, float2 em1, float2& gx, float2& gy,
+                                            float2& Gt, float2& Ht, float2& ix2) {
+  const bool na = !tnfw_is_far_em1(em1.x), nb = !tnfw_is_far_em1(em1.y);
+  if (na || nb) {  // rare: one branch for both lanes
+    if (na) tnfw_GH(rec, R2.x, Gt.x, Ht.x, ix2.x);
+    if (nb) tnfw_GH(rec, R2.y, Gt.y, Ht.y, ix2.y);
+    gx = make_float2(R2.x > 1e-30f ? gx.x : 0.f, R2.y > 1e-30f ? gx.y : 0.f);
+    gy = make_float2(R2.x > 1e-30f ? gy.x : 0.f, R2.y > 1e-30f ? gy.y : 0.f);
+  }
+}
+
 template <int PROFILE>
 __device__ __forceinline__ void vj_sweep(const SubRec& rec, float2 ex, const float4* __restrict__ pos,
                                          const float4* __restrict__ grad, int npairs, int r, int P, float* s,
@@ -91,6 +107,28 @@ __device__ __forceinline__ void vj_sweep(const SubRec& rec, float2 ex, const flo
   for (int k = r; k < npairs;) {
     const int kend = min(npairs, k + P * kVjFold);
     float2 a0 = f2(0.f), a1 = f2(0.f), a2 = f2(0.f), a3 = f2(0.f), b0 = f2(0.f), b1 = f2(0.f);
+    if (PROFILE == LR_PROFILE_TNFW) {
+      // two steps at a time: both far-side forms first (independent chains
+      // that can interleave), then the near fixes and the sums in step order
+      for (; k + P < kend; k += 2 * P) {
+        float2 dx[2], dy[2], gx[2], gy[2], R2[2], Gt[2], Ht[2], ix2[2], em1[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const float4 Q = pos[k + u * P], D = grad[k + u * P];
+          dx[u] = sub2(make_float2(Q.x, Q.y), H.xh);
+          dy[u] = sub2(make_float2(Q.z, Q.w), H.yh);
+          gx[u] = make_float2(D.x, D.y);
+          gy[u] = make_float2(D.z, D.w);
+          R2[u] = __ffma2_rn(dx[u], dx[u], __fmul2_rn(dy[u], dy[u]));
+          tnfw_GH_far2(H, __fmul2_rn(R2[u], H.its2), Gt[u], Ht[u], ix2[u], em1[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          vj_fix_near(rec, R2[u], em1[u], gx[u], gy[u], Gt[u], Ht[u], ix2[u]);
+          vj_accum2(dx[u], dy[u], gx[u], gy[u], ix2[u], Gt[u], Ht[u], a0, a1, a2, a3, b0, b1);
+        }
+      }
+    }
     for (; k < kend; k += P) {
       const float4 Q = pos[k], D = grad[k];
       const float2 dx = sub2(make_float2(Q.x, Q.y), H.xh), dy = sub2(make_float2(Q.z, Q.w), H.yh);
@@ -99,19 +137,9 @@ __device__ __forceinline__ void vj_sweep(const SubRec& rec, float2 ex, const flo
       if (PROFILE == LR_PROFILE_TNFW) {
         // the far-side form for both points; the rare near ones are redone
         // by the general form (the same bits where both apply)
-        const float2 x2 = __fmul2_rn(R2, H.its2);
         float2 Gt, Ht, ix2, em1;
-        tnfw_GH_far2(H, x2, Gt, Ht, ix2, em1);
-        const bool na = !tnfw_is_far_em1(em1.x), nb = !tnfw_is_far_em1(em1.y);
-        if (na || nb) {  // rare: one branch for both lanes
-          if (na) tnfw_GH(rec, R2.x, Gt.x, Ht.x, ix2.x);
-          if (nb) tnfw_GH(rec, R2.y, Gt.y, Ht.y, ix2.y);
-          // a point on the subhalo centre adds nothing: a zero gradient makes
-          // every term 0. R^2 <= 1e-30 is a near pair for any theta_s above
-          // 1e-15 (x^2 = R^2 / theta_s^2 < 1.05), so the test lives here.
-          gx = make_float2(R2.x > 1e-30f ? gx.x : 0.f, R2.y > 1e-30f ? gx.y : 0.f);
-          gy = make_float2(R2.x > 1e-30f ? gy.x : 0.f, R2.y > 1e-30f ? gy.y : 0.f);
-        }
+        tnfw_GH_far2(H, __fmul2_rn(R2, H.its2), Gt, Ht, ix2, em1);
+        vj_fix_near(rec, R2, em1, gx, gy, Gt, Ht, ix2);
         vj_accum2(dx, dy, gx, gy, ix2, Gt, Ht, a0, a1, a2, a3, b0, b1);
       } else {
         // point mass: alpha = theta^2 d / R^2 (its2 = theta^2, ex.y = theta)
@@ -242,7 +270,7 @@ __device__ __forceinline__ void vjp_body(const LensConst& L, const LensGradConst
 }
 
 template <int PROFILE>
-__global__ void __launch_bounds__(kVjThreads, 5) raytrace_vjp_kernel(const __grid_constant__ LensConst L,
+__global__ void __launch_bounds__(kVjThreads, 4) raytrace_vjp_kernel(const __grid_constant__ LensConst L,
                                                                   const __grid_constant__ LensGradConst LG, GridDev g,
                                                                   const float2* __restrict__ xi, int64_t n,
                                                                   const float* __restrict__ sub, int n_sub, int P,
@@ -255,7 +283,7 @@ __global__ void __launch_bounds__(kVjThreads, 5) raytrace_vjp_kernel(const __gri
                     sm);
 }
 
-__global__ void __launch_bounds__(kVjThreads, 5) vjp_batched_kernel(const __grid_constant__ Batch<VjpP> B) {
+__global__ void __launch_bounds__(kVjThreads, 4) vjp_batched_kernel(const __grid_constant__ Batch<VjpP> B) {
   __shared__ __align__(16) VjSmem sm;
   const int k = batch_find(B, blockIdx.x);
   const VjpP& P = B.p[k];
