@@ -32,17 +32,18 @@ SM_MAX_MHZ_DEFAULT = 2070.0
 # Work per point-subhalo pair, counted operation by operation from the
 # kernels' source (FP32 lanes; packed f32x2 operations count 2 lanes for 2
 # pairs). Forward, far-side closed form (x^2 >= 1.05): 2 offsets, 3 for R^2
-# and x^2, 23 for the shared far terms (arctan polynomial 12), 7 for the mass
-# bracket, 2 to accumulate both components, 1.25 for the Kahan fold after
-# every 8 subhalos; MUFU: 2 rsqrt, 1 rcp, 1 lg2. Forward, far-field series
+# and x^2, 22 for the shared far terms (arctan polynomial 12; the record's
+# (tau^2-1)/tau carries the ln(2)/2 of the log), 7 for the mass bracket, 2 to
+# accumulate both components, 1.25 for the Kahan fold after every 8
+# subhalos; MUFU: 2 rsqrt, 1 rcp, 1 lg2. Forward, far-field series
 # (x >= 6 max(tau, 2)): 2 + 3, 1 for y^2, 7 + 1 for the Horner steps, 2 for
 # m = A y^2 Q, 2 + 1.25 to accumulate and fold; MUFU: 1 rsqrt. Backward
-# (closed form throughout): 5 + 23, 13 for the G and H brackets, 1 for 1/R^2,
-# 11 for the four subhalo sums (their constant factors applied once per
-# subhalo), 0.6 for the Kahan folds; 4 MUFU.
-RT_MUFU, RT_LANES = 4, 38.3
+# (closed form throughout): 5 + 22, 13 for the G and H brackets, 11 for the
+# four subhalo sums (their constant factors, 1/theta_s^2 of the q terms
+# included, applied once per fold or slot), 0.6 for the Kahan folds; 4 MUFU.
+RT_MUFU, RT_LANES = 4, 37.3
 RT_SER_MUFU, RT_SER_LANES = 1, 19.25
-VJ_MUFU, VJ_LANES = 4, 53.6
+VJ_MUFU, VJ_LANES = 4, 51.6
 
 
 def series_fraction(p) -> float:
