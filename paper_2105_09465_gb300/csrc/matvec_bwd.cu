@@ -442,19 +442,55 @@ __device__ __forceinline__ bool train_compact(const BwArgs& A, int rb) {
   return !(B.xlo <= B.xhi) || (B.xhi - B.xlo) * A.sc <= kTrainCompact;
 }
 
-// Pair p of the tile at grid row `grow`, segment `seg`.
-__device__ __forceinline__ void train_load_pair(const BwArgs& A, int grow, int seg, int p, float xc, float4& P,
+// A tile of the training forward: grid row `grow`, columns c0 .. c0 + cnt - 1,
+// the columns [clo, chi] within reach of the row block (empty: clo > chi),
+// and cs, the tile-local column where the tile's records start: clo rounded
+// down to a quarter (4 columns). The sub-segments are laid from cs on, so
+// all but the last one in reach are whole.
+struct TrainTile {
+  int grow, c0, cnt, clo, chi, cs;
+  float yt;
+};
+
+__device__ __forceinline__ TrainTile train_tile(const BwArgs& A, const RowBlockInfo& B, int grow, int seg,
+                                                float inv_sc, float inv_h) {
+  TrainTile T;
+  T.grow = grow;
+  T.c0 = seg * kBwTile;
+  T.cnt = min(kBwTile, A.src.g.W - T.c0);
+  T.yt = grid_y(A.src.g, grow);
+  T.clo = 0;
+  T.chi = T.cnt - 1;
+  if (A.info) reach_cols_fast(B, A.src.g, T.yt, A.sc, inv_sc, inv_h, T.c0, T.cnt, T.clo, T.chi);
+  T.cs = T.clo <= T.chi ? (T.clo & ~(2 * kQuarterPairs - 1)) : 0;
+  return T;
+}
+
+// What the sweep of a tile needs: its quarters in reach from cs on (every
+// column outside is exactly zero), the grid column of cs, and the row's y.
+struct TrainRun {
+  int nq, ccs;
+  float yt;
+};
+
+__device__ __forceinline__ TrainRun train_run(const TrainTile& T) {
+  return TrainRun{T.clo <= T.chi ? (T.chi - T.cs) / (2 * kQuarterPairs) + 1 : 0, T.c0 + T.cs, T.yt};
+}
+
+// Pair p of tile T's records: columns cs + 2p and cs + 2p + 1 (zero past the
+// row's end), x' about the centre of their sub-segment.
+__device__ __forceinline__ void train_load_pair(const BwArgs& A, const TrainTile& T, int p, float xc, float4& P,
                                                 float4& VG) {
-  const int c0 = seg * kBwTile;
-  const int cnt = min(kBwTile, A.src.g.W - c0);
-  const int64_t j0 = (int64_t)grow * A.src.g.W + c0;
+  const int64_t j0 = (int64_t)T.grow * A.src.g.W + T.c0 + T.cs;
   const int a = 2 * p, b = 2 * p + 1;
-  const float o = grid_x(A.src.g, c0 + kBwSeg * (a / kBwSeg) + kBwSeg / 2);
-  const float gxa = grid_x(A.src.g, c0 + a), gxb = grid_x(A.src.g, c0 + b);
-  const float xa = (a < cnt) ? A.sc * (gxa - o) : 0.f;
-  const float xb = (b < cnt) ? A.sc * (gxb - o) : 0.f;
-  const float va = (a < cnt) ? __ldg(A.v + j0 + a) * ex2_approx(-xa * xa) : 0.f;
-  const float vb = (b < cnt) ? __ldg(A.v + j0 + b) * ex2_approx(-xb * xb) : 0.f;
+  const int c = T.c0 + T.cs;
+  const float o = grid_x(A.src.g, c + kBwSeg * (a / kBwSeg) + kBwSeg / 2);
+  const float gxa = grid_x(A.src.g, c + a), gxb = grid_x(A.src.g, c + b);
+  const bool ina = T.cs + a < T.cnt, inb = T.cs + b < T.cnt;
+  const float xa = ina ? A.sc * (gxa - o) : 0.f;
+  const float xb = inb ? A.sc * (gxb - o) : 0.f;
+  const float va = ina ? __ldg(A.v + j0 + a) * ex2_approx(-xa * xa) : 0.f;
+  const float vb = inb ? __ldg(A.v + j0 + b) * ex2_approx(-xb * xb) : 0.f;
   const float ua = A.sc * (gxa - xc), ub = A.sc * (gxb - xc);
   P = make_float4(xa, xb, va, vb);
   VG = make_float4(va * ua, vb * ub, va * ua * ua, vb * ub * ub);
@@ -515,12 +551,16 @@ __device__ __forceinline__ void train_rows_body(const BwArgs& A, int rb, int chu
     }
   }
 
-  // tile t = grow * segs + seg, stepped without a division per tile
+  // tile t = grow * segs + seg, stepped without a division per tile; each
+  // tile's reach is found one tile ahead, with its records
   const int segs = A.src.segs;
   int grow = t0 / segs, seg = t0 - grow * segs;
+  TrainRun run{0, 0, 0.f};
   float4 P, VG;
   if (t0 < t1) {
-    train_load_pair(A, grow, seg, tid, xc, P, VG);
+    const TrainTile T = train_tile(A, B, grow, seg, inv_sc, inv_h);
+    run = train_run(T);
+    train_load_pair(A, T, tid, xc, P, VG);
     sm.sT[0][2 * tid] = P;
     sm.sT[0][2 * tid + 1] = VG;
   }
@@ -529,15 +569,15 @@ __device__ __forceinline__ void train_rows_body(const BwArgs& A, int rb, int chu
   for (int t = t0; t < t1; ++t) {
     const int buf = (t - t0) & 1;
     const bool wrap = seg + 1 == segs;
-    const int ngrow = wrap ? grow + 1 : grow, nseg = wrap ? 0 : seg + 1;
-    if (t + 1 < t1) train_load_pair(A, ngrow, nseg, tid, xc, P, VG);
-    const int c0 = seg * kBwTile;
-    const int cnt = min(kBwTile, A.src.g.W - c0);
-    const float yt = grid_y(A.src.g, grow);
-    // columns of this grid row within reach of the row block, and the
-    // sub-segments that meet them
-    int clo = 0, chi = cnt - 1;
-    if (A.info) reach_cols_fast(B, A.src.g, yt, A.sc, inv_sc, inv_h, c0, cnt, clo, chi);
+    grow = wrap ? grow + 1 : grow;
+    seg = wrap ? 0 : seg + 1;
+    TrainRun next{0, 0, 0.f};
+    if (t + 1 < t1) {
+      const TrainTile T = train_tile(A, B, grow, seg, inv_sc, inv_h);
+      next = train_run(T);
+      train_load_pair(A, T, tid, xc, P, VG);
+    }
+    const float yt = run.yt;
     float dyr[R], ndy2[R];
     float2 S0[R], S1[R], S2[R];
 #pragma unroll
@@ -547,13 +587,11 @@ __device__ __forceinline__ void train_rows_body(const BwArgs& A, int rb, int chu
       ndy2[r] = -d * d;
       S0[r] = S1[r] = S2[r] = f2(0.f, 0.f);
     }
-    const int nsg = (cnt + kBwSeg - 1) / kBwSeg;
-    const int sg_lo = clo <= chi ? clo / kBwSeg : nsg, sg_hi = clo <= chi ? chi / kBwSeg : -1;
-    for (int sg = sg_lo; sg <= sg_hi; ++sg) {
-      int pl, ph;
-      seg_pair_range<kBwSeg>(clo, chi, kBwSeg * sg, pl, ph);
-      if (pl >= ph) continue;  // every pair's exp2 flushes to 0
-      const float ds = A.sc * (grid_x(A.src.g, c0 + kBwSeg * sg + kBwSeg / 2) - xc);  // delta_s
+    // sub-segments of 4 quarters from cs on: all whole but the last
+    const int nsg = (run.nq + 3) / 4;
+    for (int sg = 0; sg < nsg; ++sg) {
+      const int qn = min(4, run.nq - 4 * sg);
+      const float ds = A.sc * (grid_x(A.src.g, run.ccs + kBwSeg * sg + kBwSeg / 2) - xc);  // delta_s
       float2 q2[R], ar[R];
 #pragma unroll
       for (int r = 0; r < R; ++r) {
@@ -562,15 +600,15 @@ __device__ __forceinline__ void train_rows_body(const BwArgs& A, int rb, int chu
         q2[r] = f2(q + q, q + q);
         ar[r] = f2(a, a);
       }
-      const float4* T = &sm.sT[buf][2 * sg * (kBwSeg / 2)];
-      if (pl == 0 && ph == kBwSeg / 2) {
-        // a sub-segment wholly in reach: one block without quarter tests
-        train_pairs<R, kBwSeg / 2>(T, q2, ar, S0, S1, S2);
+      const float4* rec = &sm.sT[buf][2 * sg * (kBwSeg / 2)];
+      if (qn == 4) {
+        // a whole sub-segment: one block without quarter tests
+        train_pairs<R, kBwSeg / 2>(rec, q2, ar, S0, S1, S2);
       } else {
 #pragma unroll
-        for (int qq = 0; qq < kBwSeg / 2; qq += kQuarterPairs) {
-          if (qq < pl || qq >= ph) continue;  // a quarter out of reach: exactly zero
-          train_pairs<R, kQuarterPairs>(T + 2 * qq, q2, ar, S0, S1, S2);
+        for (int qq = 0; qq < 3; ++qq) {
+          if (qq >= qn) break;  // the quarters past the reach: exactly zero
+          train_pairs<R, kQuarterPairs>(rec + 4 * qq, q2, ar, S0, S1, S2);
         }
       }
     }
@@ -599,8 +637,7 @@ __device__ __forceinline__ void train_rows_body(const BwArgs& A, int rb, int chu
       sm.sT[buf ^ 1][2 * tid] = P;
       sm.sT[buf ^ 1][2 * tid + 1] = VG;
     }
-    grow = ngrow;
-    seg = nseg;
+    run = next;
     __syncthreads();
   }
 
@@ -615,10 +652,10 @@ __device__ __forceinline__ void train_rows_body(const BwArgs& A, int rb, int chu
 }
 
 // Resident CTAs per SM the compiler must leave room for: the training
-// forward's row pass is latency-bound at 4, so its registers are capped for 5.
+// forward's row pass ran fastest at 4 (128 registers; 5 and 6 ran slower).
 template <bool GRID, bool SELF, bool DV, bool SPLIT>
 constexpr int bw_min_blocks() {
-  return (GRID && !SELF && !DV && SPLIT) ? 5 : 1;
+  return (GRID && !SELF && !DV && SPLIT) ? 4 : 1;
 }
 
 template <bool GRID, bool SELF, bool DV, bool SPLIT = false>
