@@ -447,14 +447,14 @@ __device__ __forceinline__ bool train_compact(const BwArgs& A, int rb) {
 // and cs, the tile-local column where the tile's records start: clo rounded
 // down to a quarter (4 columns). The sub-segments are laid from cs on, so
 // all but the last one in reach are whole.
-struct TrainTile {
+struct GridTile {
   int grow, c0, cnt, clo, chi, cs;
   float yt;
 };
 
-__device__ __forceinline__ TrainTile train_tile(const BwArgs& A, const RowBlockInfo& B, int grow, int seg,
+__device__ __forceinline__ GridTile grid_tile(const BwArgs& A, const RowBlockInfo& B, int grow, int seg,
                                                 float inv_sc, float inv_h) {
-  TrainTile T;
+  GridTile T;
   T.grow = grow;
   T.c0 = seg * kBwTile;
   T.cnt = min(kBwTile, A.src.g.W - T.c0);
@@ -468,18 +468,18 @@ __device__ __forceinline__ TrainTile train_tile(const BwArgs& A, const RowBlockI
 
 // What the sweep of a tile needs: its quarters in reach from cs on (every
 // column outside is exactly zero), the grid column of cs, and the row's y.
-struct TrainRun {
+struct TileRun {
   int nq, ccs;
   float yt;
 };
 
-__device__ __forceinline__ TrainRun train_run(const TrainTile& T) {
-  return TrainRun{T.clo <= T.chi ? (T.chi - T.cs) / (2 * kQuarterPairs) + 1 : 0, T.c0 + T.cs, T.yt};
+__device__ __forceinline__ TileRun tile_run(const GridTile& T) {
+  return TileRun{T.clo <= T.chi ? (T.chi - T.cs) / (2 * kQuarterPairs) + 1 : 0, T.c0 + T.cs, T.yt};
 }
 
 // Pair p of tile T's records: columns cs + 2p and cs + 2p + 1 (zero past the
 // row's end), x' about the centre of their sub-segment.
-__device__ __forceinline__ void train_load_pair(const BwArgs& A, const TrainTile& T, int p, float xc, float4& P,
+__device__ __forceinline__ void train_load_pair(const BwArgs& A, const GridTile& T, int p, float xc, float4& P,
                                                 float4& VG) {
   const int64_t j0 = (int64_t)T.grow * A.src.g.W + T.c0 + T.cs;
   const int a = 2 * p, b = 2 * p + 1;
@@ -555,11 +555,11 @@ __device__ __forceinline__ void train_rows_body(const BwArgs& A, int rb, int chu
   // tile's reach is found one tile ahead, with its records
   const int segs = A.src.segs;
   int grow = t0 / segs, seg = t0 - grow * segs;
-  TrainRun run{0, 0, 0.f};
+  TileRun run{0, 0, 0.f};
   float4 P, VG;
   if (t0 < t1) {
-    const TrainTile T = train_tile(A, B, grow, seg, inv_sc, inv_h);
-    run = train_run(T);
+    const GridTile T = grid_tile(A, B, grow, seg, inv_sc, inv_h);
+    run = tile_run(T);
     train_load_pair(A, T, tid, xc, P, VG);
     sm.sT[0][2 * tid] = P;
     sm.sT[0][2 * tid + 1] = VG;
@@ -571,10 +571,10 @@ __device__ __forceinline__ void train_rows_body(const BwArgs& A, int rb, int chu
     const bool wrap = seg + 1 == segs;
     grow = wrap ? grow + 1 : grow;
     seg = wrap ? 0 : seg + 1;
-    TrainRun next{0, 0, 0.f};
+    TileRun next{0, 0, 0.f};
     if (t + 1 < t1) {
-      const TrainTile T = train_tile(A, B, grow, seg, inv_sc, inv_h);
-      next = train_run(T);
+      const GridTile T = grid_tile(A, B, grow, seg, inv_sc, inv_h);
+      next = tile_run(T);
       train_load_pair(A, T, tid, xc, P, VG);
     }
     const float yt = run.yt;
@@ -705,15 +705,27 @@ struct DvSmem {
   float dvred[kBwThreads / 32][kBwTile];
 };
 
+// Pair p of tile T's records (see GridTile): columns cs + 2p and cs + 2p + 1.
 template <bool SPLIT>
-__device__ __forceinline__ void dv_load_pair(const BwArgs& A, int seg, int p, float2& X) {
-  const int c0 = seg * kBwTile;
-  const int cnt = min(kBwTile, A.src.g.W - c0);
+__device__ __forceinline__ void dv_load_pair(const BwArgs& A, const GridTile& T, int p, float2& X) {
+  const int c = T.c0 + T.cs;
   const int a = 2 * p, b = 2 * p + 1;
-  const float o = grid_x(A.src.g, c0 + kBwSeg * (a / kBwSeg) + kBwSeg / 2);
-  const float xa = (a < cnt) ? A.sc * (grid_x(A.src.g, c0 + a) - o) : 0.f;
-  const float xb = (b < cnt) ? A.sc * (grid_x(A.src.g, c0 + b) - o) : 0.f;
+  const float o = grid_x(A.src.g, c + kBwSeg * (a / kBwSeg) + kBwSeg / 2);
+  const float xa = (T.cs + a < T.cnt) ? A.sc * (grid_x(A.src.g, c + a) - o) : 0.f;
+  const float xb = (T.cs + b < T.cnt) ? A.sc * (grid_x(A.src.g, c + b) - o) : 0.f;
   X = SPLIT ? f2(-2.f * xa, -2.f * xb) : f2(-xa, -xb);
+}
+
+// What the d_v sweep of a tile needs (see GridTile and TileRun).
+struct DvRun {
+  int nq, cs, c0, cnt;
+  int64_t j0;
+  float yt;
+};
+
+__device__ __forceinline__ DvRun dv_run(const BwArgs& A, const GridTile& T) {
+  return DvRun{T.clo <= T.chi ? (T.chi - T.cs) / (2 * kQuarterPairs) + 1 : 0, T.cs, T.c0, T.cnt,
+               (int64_t)T.grow * A.src.g.W + T.c0, T.yt};
 }
 
 // NP consecutive source pairs (records X[0 .. NP)) against the thread's rows:
@@ -782,45 +794,41 @@ __device__ __forceinline__ void dv_rows_body(const BwArgs& A, int rb, int chunk,
     const float gv = ir >= 0 ? __ldg(A.grow + ir) : 0.f;  // padding rows add nothing
     gq[r] = f2(gv, gv);
   }
-  // tile t = grow * segs + seg, stepped without a division per tile
+  // tile t = grow * segs + seg, stepped without a division per tile; each
+  // tile's reach is found one tile ahead, with its records, and its
+  // sub-segments are laid from cs on (all whole but the last)
   const int segs = A.src.segs;
   int grow = t0 / segs, seg = t0 - grow * segs;
+  DvRun run{0, 0, 0, 0, 0, 0.f};
   float2 X = f2(0.f, 0.f);
   if (t0 < t1) {
-    dv_load_pair<SPLIT>(A, seg, tid, X);
+    const GridTile T = grid_tile(A, B, grow, seg, inv_sc, inv_h);
+    run = dv_run(A, T);
+    dv_load_pair<SPLIT>(A, T, tid, X);
     sm.sX[0][tid] = X;
   }
   __syncthreads();
   for (int t = t0; t < t1; ++t) {
     const int buf = (t - t0) & 1;
     const bool wrap = seg + 1 == segs;
-    const int ngrow = wrap ? grow + 1 : grow, nseg = wrap ? 0 : seg + 1;
-    if (t + 1 < t1) dv_load_pair<SPLIT>(A, nseg, tid, X);
-    const int c0 = seg * kBwTile;
-    const int cnt = min(kBwTile, A.src.g.W - c0);
-    const int64_t j0 = (int64_t)grow * A.src.g.W + c0;
-    const float yt = grid_y(A.src.g, grow);
+    grow = wrap ? grow + 1 : grow;
+    seg = wrap ? 0 : seg + 1;
+    DvRun next{0, 0, 0, 0, 0, 0.f};
+    if (t + 1 < t1) {
+      const GridTile T = grid_tile(A, B, grow, seg, inv_sc, inv_h);
+      next = dv_run(A, T);
+      dv_load_pair<SPLIT>(A, T, tid, X);
+    }
     float dy2[kDvR];
 #pragma unroll
     for (int r = 0; r < kDvR; ++r) {
-      const float d = A.sc * (yq[r] - yt);
+      const float d = A.sc * (yq[r] - run.yt);
       dy2[r] = d * d;
     }
-    const int nsg = (cnt + kBwSeg - 1) / kBwSeg;
-    // columns of this grid row within reach of the row block (all without
-    // info), and the sub-segments that meet them
-    int clo = 0, chi = cnt - 1;
-    if (A.info) reach_cols_fast(B, A.src.g, yt, A.sc, inv_sc, inv_h, c0, cnt, clo, chi);
-    const int sg_lo = clo <= chi ? clo / kBwSeg : nsg, sg_hi = clo <= chi ? chi / kBwSeg : -1;
-    for (int sg = sg_lo; sg <= sg_hi; ++sg) {
-      int pl, ph;
-      seg_pair_range<kBwSeg>(clo, chi, kBwSeg * sg, pl, ph);
-      if (pl >= ph) {
-        // every pair's exp2 flushes to 0: zero column sums for this sub-segment
-        if ((tid & 31) < kBwSeg) sm.dvred[tid >> 5][sg * kBwSeg + (tid & 31)] = 0.f;
-        continue;
-      }
-      const float o = grid_x(A.src.g, c0 + kBwSeg * sg + kBwSeg / 2);
+    const int nsg = (run.nq + 3) / 4;
+    for (int sg = 0; sg < nsg; ++sg) {
+      const int qn = min(4, run.nq - 4 * sg);
+      const float o = grid_x(A.src.g, run.c0 + run.cs + kBwSeg * sg + kBwSeg / 2);
       // split: (-q, -(q^2 + dy'^2)) against records -2x'; unsplit: (q, dy'^2)
       float2 qa[kDvR], qb[kDvR];
 #pragma unroll
@@ -838,20 +846,20 @@ __device__ __forceinline__ void dv_rows_body(const BwArgs& A, int rb, int chunk,
       }
       float kgs[kBwSeg];
       const float2* Xs = &sm.sX[buf][sg * (kBwSeg / 2)];
-      if (pl == 0 && ph == kBwSeg / 2) {
-        // a sub-segment wholly in reach: one block without quarter tests, in
-        // the lane-permuted order
+      if (qn == 4) {
+        // a whole sub-segment: one block without quarter tests, in the
+        // lane-permuted order
         dv_pairs_perm<SPLIT>(Xs, qa, qb, gq, kgs, tid & 31);
         warp_reduce_scatter_perm(kgs, tid & 31, &sm.dvred[tid >> 5][sg * kBwSeg]);
       } else {
 #pragma unroll
-        for (int qq = 0; qq < kBwSeg / 2; qq += kQuarterPairs) {
-          if (qq < pl || qq >= ph) {  // a quarter out of reach: exactly zero
+        for (int qi = 0; qi < 4; ++qi) {
+          if (qi >= qn) {  // a quarter past the reach: exactly zero
 #pragma unroll
-            for (int c = 2 * qq; c < 2 * (qq + kQuarterPairs); ++c) kgs[c] = 0.f;
+            for (int c = 4 * qi; c < 4 * qi + 4; ++c) kgs[c] = 0.f;
             continue;
           }
-          dv_pairs<SPLIT, kQuarterPairs>(Xs + qq, qa, qb, gq, kgs + 2 * qq);
+          dv_pairs<SPLIT, kQuarterPairs>(Xs + 2 * qi, qa, qb, gq, kgs + 4 * qi);
         }
         warp_reduce_scatter(kgs, tid & 31, &sm.dvred[tid >> 5][sg * kBwSeg]);
       }
@@ -859,25 +867,25 @@ __device__ __forceinline__ void dv_rows_body(const BwArgs& A, int rb, int chunk,
     __syncthreads();
     // combine the warps in order; row block rb owns these columns of
     // dv_part (exact zeros outside the sub-segments in reach)
-    float* dst = A.dv_part + (int64_t)rb * A.src.m + j0;
-    for (int j = tid; j < cnt; j += kBwThreads) {
-      if (j < sg_lo * kBwSeg || j >= (sg_hi + 1) * kBwSeg) {
+    float* dst = A.dv_part + (int64_t)rb * A.src.m + run.j0;
+    for (int j = tid; j < run.cnt; j += kBwThreads) {
+      const int jj = j - run.cs;
+      if (jj < 0 || jj >= nsg * kBwSeg) {
         dst[j] = 0.f;
         continue;
       }
-      float sdv = sm.dvred[0][j];
+      float sdv = sm.dvred[0][jj];
 #pragma unroll
-      for (int w = 1; w < kBwThreads / 32; ++w) sdv += sm.dvred[w][j];
+      for (int w = 1; w < kBwThreads / 32; ++w) sdv += sm.dvred[w][jj];
       if (SPLIT) {
-        const float2 Xp = sm.sX[buf][j >> 1];
-        const float xj = 0.5f * ((j & 1) ? Xp.y : Xp.x);  // the record holds -2x'
+        const float2 Xp = sm.sX[buf][jj >> 1];
+        const float xj = 0.5f * ((jj & 1) ? Xp.y : Xp.x);  // the record holds -2x'
         sdv *= ex2_approx(-xj * xj);
       }
       dst[j] = sdv;
     }
     if (t + 1 < t1) sm.sX[buf ^ 1][tid] = X;
-    grow = ngrow;
-    seg = nseg;
+    run = next;
     __syncthreads();
   }
 }
