@@ -158,6 +158,38 @@ __device__ __forceinline__ void add_subs(const RtSmem& sm, int cnt, const float 
     for (int j = 0; j < kRtPts; ++j) ax[j] = ay[j] = f2(0.f);
     int t = t0;
     if (PROFILE == LR_PROFILE_TNFW) {
+      // two subhalo pairs at a time while all four are far from the whole
+      // CTA: four independent series chains per thread, added in order
+      for (; t + 3 < t1 && t + 3 < nfe; t += 4) {
+        float2 m[2][kRtPts], dxs[2][kRtPts], dys[2][kRtPts];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const float4* hot = sm.hot[(t >> 1) + u];
+          const float4 w0 = hot[0], w1 = hot[1], w2 = hot[2];
+          float2 q[kSerTerms];
+#pragma unroll
+          for (int w = 0; w < 4; ++w) {
+            const float4 c = hot[3 + w];
+            q[2 + 2 * w] = lo2(c);
+            q[3 + 2 * w] = hi2(c);
+          }
+#pragma unroll
+          for (int j = 0; j < kRtPts; ++j) {
+            dxs[u][j] = sub2(X[j], make_float2(w0.x, w0.y));
+            dys[u][j] = sub2(Y[j], make_float2(w0.z, w0.w));
+            const float2 R2 = __ffma2_rn(dxs[u][j], dxs[u][j], __fmul2_rn(dys[u][j], dys[u][j]));
+            m[u][j] = tnfw_m_series2(hi2(w1), hi2(w2), q, __fmul2_rn(R2, lo2(w1)));
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+#pragma unroll
+          for (int j = 0; j < kRtPts; ++j) {
+            ax[j] = __ffma2_rn(m[u][j], dxs[u][j], ax[j]);
+            ay[j] = __ffma2_rn(m[u][j], dys[u][j], ay[j]);
+          }
+        }
+      }
       for (; t + 1 < t1; t += 2) {
         const float4* hot = sm.hot[t >> 1];
         const float4 w0 = hot[0], w1 = hot[1], w2 = hot[2];
