@@ -38,12 +38,12 @@ SM_MAX_MHZ_DEFAULT = 2070.0
 # subhalos; MUFU: 2 rsqrt, 1 rcp, 1 lg2. Forward, far-field series
 # (x >= 6 max(tau, 2)): 2 + 3, 1 for y^2, 7 + 1 for the Horner steps, 2 for
 # m = A y^2 Q, 2 + 1.25 to accumulate and fold; MUFU: 1 rsqrt. Backward
-# (closed form throughout): 5 + 22, 13 for the G and H brackets, 11 for the
+# (closed form throughout): 5 + 22, 12 for the G and H brackets, 11 for the
 # four subhalo sums (their constant factors, 1/theta_s^2 of the q terms
 # included, applied once per fold or slot), 0.6 for the Kahan folds; 4 MUFU.
 RT_MUFU, RT_LANES = 4, 37.3
 RT_SER_MUFU, RT_SER_LANES = 1, 19.25
-VJ_MUFU, VJ_LANES = 4, 51.6
+VJ_MUFU, VJ_LANES = 4, 50.6
 
 
 def series_fraction(p) -> float:

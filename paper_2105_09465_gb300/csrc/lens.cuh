@@ -500,8 +500,9 @@ __device__ __forceinline__ void tnfw_GH_far(const SubRec& h, float x2, float& Gt
   const float B = __fmaf_rn(t.st, lp, __fmaf_rn(__fmaf_rn(2.0f, x2, t2m1), t.F, h.C));
   Gt = __fmul_rn(B, t.ix2);
   ix2 = t.ix2;
-  const float omf = __fmul_rn(__fsub_rn(1.0f, t.F), __fmul_rn(t.is, t.is));
-  Ht = __fmaf_rn(t.ist, lp, __fmaf_rn(2.0f, t.F, __fmul_rn(__fadd_rn(h.tau2, 1.0f), omf)));
+  // (tau^2 + 1)(1 - F)/eps as c - F c with c = (tau^2 + 1)/eps
+  const float c = __fmul_rn(__fmul_rn(t.is, t.is), __fadd_rn(h.tau2, 1.0f));
+  Ht = __fmaf_rn(t.ist, lp, __fmaf_rn(2.0f, t.F, __fmaf_rn(-t.F, c, c)));
 }
 
 __device__ __forceinline__ void tnfw_GH_far2(const SubRec2& h, float2 x2, float2& Gt, float2& Ht, float2& ix2,
@@ -513,8 +514,8 @@ __device__ __forceinline__ void tnfw_GH_far2(const SubRec2& h, float2 x2, float2
   const float2 B = __ffma2_rn(t.st, lp, __ffma2_rn(__ffma2_rn(f2(2.0f), x2, t2m1), t.F, h.C));
   Gt = __fmul2_rn(B, t.ix2);
   ix2 = t.ix2;
-  const float2 omf = __fmul2_rn(sub2(f2(1.0f), t.F), __fmul2_rn(t.is, t.is));
-  Ht = __ffma2_rn(t.ist, lp, __ffma2_rn(f2(2.0f), t.F, __fmul2_rn(__fadd2_rn(h.tau2, f2(1.0f)), omf)));
+  const float2 c = __fmul2_rn(__fmul2_rn(t.is, t.is), __fadd2_rn(h.tau2, f2(1.0f)));
+  Ht = __ffma2_rn(t.ist, lp, __ffma2_rn(f2(2.0f), t.F, __ffma2_rn(make_float2(-t.F.x, -t.F.y), c, c)));
 }
 
 // Per-lens constants for the SPLE gradient (host-prepared).

@@ -433,7 +433,7 @@ __device__ __forceinline__ void bwd_rows_body(const BwArgs& A, int rb, int chunk
 // block's box is narrow (image-tile row order). A wider box (rows in index
 // order of scattered points) takes the per-sub-segment form (bwd_rows_body),
 // whose exponent and moments are all relative to the sub-segment centre.
-constexpr int kTrainFold = 8;
+constexpr int kTrainFold = 16;
 constexpr float kTrainCompact = 8.f;  // widest box, in scaled units sc x width
 
 __device__ __forceinline__ bool train_compact(const BwArgs& A, int rb) {
