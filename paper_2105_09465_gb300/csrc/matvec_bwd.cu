@@ -442,7 +442,8 @@ __device__ __forceinline__ bool train_compact(const BwArgs& A, int rb) {
   return !(B.xlo <= B.xhi) || (B.xhi - B.xlo) * A.sc <= kTrainCompact;
 }
 
-// A tile of the training forward: grid row `grow`, columns c0 .. c0 + cnt - 1,
+// A tile of a grid-source sweep (the training forward and the d_v sweep):
+// grid row `grow`, columns c0 .. c0 + cnt - 1,
 // the columns [clo, chi] within reach of the row block (empty: clo > chi),
 // and cs, the tile-local column where the tile's records start: clo rounded
 // down to a quarter (4 columns). The sub-segments are laid from cs on, so
@@ -453,7 +454,7 @@ struct GridTile {
 };
 
 __device__ __forceinline__ GridTile grid_tile(const BwArgs& A, const RowBlockInfo& B, int grow, int seg,
-                                                float inv_sc, float inv_h) {
+                                              float inv_sc, float inv_h) {
   GridTile T;
   T.grow = grow;
   T.c0 = seg * kBwTile;
