@@ -42,6 +42,30 @@ def test_grid_source(orc, ratio):
     close(host(G["variance"]), [R["d_var"]], [R["d_var_abs"]], what="d_var")
 
 
+@pytest.mark.parametrize("ell", [0.03, 0.08])
+def test_grid_query_odd_source_grid(orc, ell):
+    """Pixel-grid queries (compact row blocks: the training forward's and the
+    d_v sweep's tiles laid from each reach start) against a source grid of odd
+    width and height, so that a tile's last quarter runs past the row end and
+    reach intervals start off the quarter boundaries."""
+    qg, sg = W.Grid(48, 40, 2, 0.05), W.Grid(131, 37, 1, 0.02)
+    rng = np.random.default_rng(int(1000 * ell))
+    v = rng.standard_normal(sg.n).astype(np.float32)
+    xq, yg = orc.grid_points(*qg.astuple()), orc.grid_points(*sg.astuple())
+    gout = rng.standard_normal(len(xq)).astype(np.float32)
+    q, s = api.Points(grid=qg), api.Points(grid=sg)
+    out, mom = api.gp_kernel_matvec_train(q, s, dev(v), ell, 0.9)
+    ref, ab = orc.kernel_matvec(xq, yg, v, ell, 0.9)
+    assert_matvec_close(host(out), ref, ab, what="train forward")
+    G = api.gp_kernel_matvec_bwd(q, s, dev(v), ell, 0.9, dev(gout), want=["v", "x", "lengthscale", "variance"],
+                                 moments=mom)
+    R = orc.kernel_matvec_vjp(xq, yg, v, ell, 0.9, gout.astype(np.float64), False, with_abs=True)
+    close(host(G["v"]), R["d_v"], R["d_v_abs"], what="d_v")
+    close(host(G["x"]), R["d_x"], R["d_x_abs"], what="d_x")
+    close(host(G["lengthscale"]), [R["d_len"]], [R["d_len_abs"]], what="d_len")
+    close(host(G["variance"]), [R["d_var"]], [R["d_var_abs"]], what="d_var")
+
+
 @pytest.mark.parametrize("n,m", [(1, 1), (700, 5003), (3001, 2500)])
 def test_explicit_sources(orc, n, m):
     rng = np.random.default_rng(n + m)
