@@ -495,8 +495,11 @@ def run_ours(args):
     cq, _k1 = api.to_c_points(q)
     cs, _k2 = api.to_c_points(s)
     gr = _abi.lr_grads()
-    gr.d_v, gr.d_lengthscale, gr.d_variance, gr.d_lens, gr.d_sub, gr.beta_in = 256, 256, 256, 256, 256, 256
-    gr.moments_in = 256
+    # the size query reads only which gradients are requested; real buffers
+    # stand for them so that no argument is a made-up address
+    _req = [torch.empty(64, dtype=torch.float64, device=dev) for _ in range(7)]
+    (gr.d_v, gr.d_lengthscale, gr.d_variance, gr.d_lens, gr.d_sub, gr.beta_in,
+     gr.moments_in) = [t.data_ptr() for t in _req]
     b = ctypes.c_size_t(0)
     _abi.check(_abi.load().lr_matvec_bwd_workspace_size(ctypes.byref(cq), ctypes.byref(cs), 1, ctypes.byref(gr),
                                                          ctypes.byref(b)), "lr_matvec_bwd_workspace_size")

@@ -569,9 +569,12 @@ lr_status solve_session_destroy(lr_session* s);
  *    exits. Problems whose workspace requirement (lr_matvec_workspace_size)
  *    exceeds it are rejected with LR_ERR_INVALID_ARG; nothing else is
  *    allocated (no cudaMalloc, cudaFree or allocating library call).
- *  - The first call on a device resolves the array's device address
- *    (cudaGetSymbolAddress, with that device current); make that first call
- *    before any stream capture.
+ *  - Every call resolves the array's device address in the current
+ *    device's context (cudaGetSymbolAddress, with that device current); the
+ *    first call on a device may load the library's device code, so make it
+ *    before any stream capture. Nothing is cached across calls, so a context
+ *    destroyed and created again (cudaDeviceReset) is served from its own
+ *    copy of the array.
  *  - All calls on a device share the one array, which keeps the last call's
  *    contents. Calls whose kernels overlap on the GPU (different streams, or
  *    host threads racing) corrupt each other's scratch: serialise them, for

@@ -18,8 +18,6 @@
 // fixed chunk order (Kahan), so results are deterministic.
 #include <math.h>
 
-#include <mutex>
-
 #include "batch.cuh"
 #include "host.cuh"
 #include "problems.cuh"
@@ -609,29 +607,19 @@ extern "C" lr_status gp_kernel_matvec(const lr_points* query, const lr_points* s
 namespace {
 
 constexpr size_t kStaticScratchBytes = size_t(48) << 20;  // 48 MiB per device
-constexpr int kMaxScratchDevices = 64;
-
 static __device__ __align__(256) unsigned char g_matvec_static_scratch[kStaticScratchBytes];
 
-std::mutex g_static_scratch_mu;
-void* g_static_scratch_ptr[kMaxScratchDevices] = {};
-
-// Device address of the static scratch on the current device. The first
-// call on a device resolves it with cudaGetSymbolAddress (with that device
-// current) and caches it; host code must never pass the array's name itself
-// to a kernel, since in host code it is only a host-side stand-in.
+// Device address of the static scratch in the current device's context,
+// resolved with cudaGetSymbolAddress on every call (it allocates nothing and
+// costs about a microsecond). Host code must never pass the array's name
+// itself to a kernel: in host code it is only a host-side stand-in. Nothing
+// is cached, so a context that was destroyed and created again (for example
+// after cudaDeviceReset) gets the address of its own copy of the array.
 lr_status static_scratch_address(void** out) {
-  int dev = 0;
-  LR_CHECK_CUDA(cudaGetDevice(&dev));
-  LR_REQUIRE(dev >= 0 && dev < kMaxScratchDevices, "static scratch: device ordinal %d out of range", dev);
-  std::lock_guard<std::mutex> lock(g_static_scratch_mu);
-  if (g_static_scratch_ptr[dev] == nullptr) {
-    void* p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_matvec_static_scratch);
-    if (e != cudaSuccess) return cuda_status(e, "cudaGetSymbolAddress(g_matvec_static_scratch)");
-    g_static_scratch_ptr[dev] = p;
-  }
-  *out = g_static_scratch_ptr[dev];
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_matvec_static_scratch);
+  if (e != cudaSuccess) return cuda_status(e, "cudaGetSymbolAddress(g_matvec_static_scratch)");
+  *out = p;
   return LR_OK;
 }
 

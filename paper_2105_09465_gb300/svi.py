@@ -18,9 +18,12 @@ Model for one draw:
 The lens priors are uniform (constant inside their domain) and left out;
 the transmission weights A_k are held fixed within a step.
 
-Every numerical step runs in the library's CUDA kernels; this module only
-orders the calls and moves the 7 drawn lens parameters to the host, where
-the ray-trace takes them as a parameter struct.
+The pair sweeps, draws, log densities and their VJPs run in the library's
+CUDA kernels. This module orders the calls, moves the 7 drawn lens
+parameters to the host (the ray-trace takes them as a parameter struct) and
+does a few elementwise steps in torch: the weight scaling (A y), the sum of
+the layers' fluxes, the accumulation of dL/dbeta over the layers and the
+source-plane prior gradient y_sp / alpha^2.
 """
 from __future__ import annotations
 

@@ -32,6 +32,27 @@ def lib():
     return abi.load()
 
 
+_KEEP = []
+
+
+def dbuf(offset=0):
+    """Address for an argument that validation must reject before any launch.
+
+    With a GPU present it points into a real 1 KiB device allocation (plus
+    `offset` bytes, e.g. 4 for a misaligned pointer), so that no call can
+    ever reach a made-up address. Without one no call reaches a device and a
+    placeholder stands in."""
+    try:
+        import torch
+        if torch.cuda.is_available():
+            t = torch.empty(1024, dtype=torch.uint8, device="cuda")
+            _KEEP.append(t)
+            return ctypes.c_void_p(t.data_ptr() + offset)
+    except ImportError:
+        pass
+    return ctypes.c_void_p(256 + offset)
+
+
 def test_library_exports_every_declared_symbol(lib):
     syms = declared_symbols()
     assert {"lens_raytrace", "gp_kernel_matvec", "lr_last_error"} <= syms
@@ -55,7 +76,7 @@ def test_raytrace_rejects_bad_arguments_without_gpu(lib):
     p.n = 99  # grid has 100 points
     L = abi.lr_lens(0, 0, 0.8, 0.5, 1.2, 2.0, 0, 0)
     p.lens = ctypes.pointer(L)
-    assert lib.lens_raytrace(ctypes.byref(p), ctypes.c_void_p(256), None, None) == abi.LR_ERR_INVALID_ARG
+    assert lib.lens_raytrace(ctypes.byref(p), dbuf(), None, None) == abi.LR_ERR_INVALID_ARG
     assert b"grid has 100 points" in lib.lr_last_error()
     p.n = 100
     for bad in [dict(q=0.0), dict(q=1.5), dict(gamma=3.0), dict(gamma=1.0), dict(theta_e=-1.0),
@@ -64,23 +85,23 @@ def test_raytrace_rejects_bad_arguments_without_gpu(lib):
         for k, val in bad.items():
             setattr(L2, k, val)
         p.lens = ctypes.pointer(L2)
-        assert lib.lens_raytrace(ctypes.byref(p), ctypes.c_void_p(256), None, None) == abi.LR_ERR_INVALID_ARG, bad
+        assert lib.lens_raytrace(ctypes.byref(p), dbuf(), None, None) == abi.LR_ERR_INVALID_ARG, bad
     p.lens = ctypes.pointer(L)
     p.n_sub = 3
     p.sub = None
-    assert lib.lens_raytrace(ctypes.byref(p), ctypes.c_void_p(256), None, None) == abi.LR_ERR_INVALID_ARG
+    assert lib.lens_raytrace(ctypes.byref(p), dbuf(), None, None) == abi.LR_ERR_INVALID_ARG
     p.n_sub = 0
     p.profile = 7
-    assert lib.lens_raytrace(ctypes.byref(p), ctypes.c_void_p(256), None, None) == abi.LR_ERR_INVALID_ARG
+    assert lib.lens_raytrace(ctypes.byref(p), dbuf(), None, None) == abi.LR_ERR_INVALID_ARG
 
 
 def test_matvec_rejects_bad_arguments_without_gpu(lib):
     q = abi.lr_points()
-    q.xy = ctypes.c_void_p(4)  # misaligned
+    q.xy = dbuf(4)  # misaligned
     q.n = 10
     assert lib.gp_kernel_matvec(ctypes.byref(q), None, None, 1, 0.1, 1.0, None, None, None, 0, None) == \
         abi.LR_ERR_INVALID_ARG
-    q.xy = ctypes.c_void_p(256)
+    q.xy = dbuf()
     assert lib.gp_kernel_matvec(ctypes.byref(q), None, None, 2, 0.1, 1.0, None, None, None, 0, None) == \
         abi.LR_ERR_INVALID_ARG  # nrhs
     q.n = -1
