@@ -95,6 +95,18 @@ enum {
 lr_status lr_kernel_timer_enable(int32_t enable);
 lr_status lr_kernel_timer_read(int32_t kernel, int64_t* launches, double* total_ms, int64_t* dropped);
 
+/*
+ * Exact skipping of far pairs in the reductions over explicit sources
+ * (gp_kernel_matvec, gp_kernel_matvec_bwd). A pair whose exponent is below
+ * -126 contributes exactly 0 (the hardware exp2 flushes it), so a row block
+ * leaves out every source chunk that is that far from all its rows.
+ * lr_set_pair_culling(0) makes those entry points evaluate every pair, in
+ * the same order; the results are bitwise the same, which is what it is for
+ * (checking that the skipping is exact). Process-wide, read at each call;
+ * on (1) by default.
+ */
+lr_status lr_set_pair_culling(int32_t enable);
+
 /* ------------------------------------------------------------------------ */
 /* Geometry and lens parameters                                               */
 
@@ -193,14 +205,20 @@ lr_status lens_jacobian(const lr_points* pts, float* jac_out, float* mu_out, lr_
  * reduced lazily without storing the n x m matrix, Sec. 3.3).
  *   query   the x_i; ray-traced first when query->lens != NULL
  *   source  the y_j, or NULL for a self-kernel (y = x after ray-tracing)
- *   v       device float[m][nrhs] (nrhs must be 1 in this version)
+ *   v       device float[m][nrhs]: nrhs right-hand sides reduced in one pass
+ *           (one exponential per pair, nrhs FMA): 1..4 for explicit,
+ *           ray-traced or self sources, 1 for grid sources
  *   out     device float[n][nrhs]
  *   beta_out device float[n][2] or NULL: receives the ray-traced query points
  *   workspace/workspace_bytes: caller-owned device scratch of at least
  *           lr_matvec_workspace_size() bytes (may be NULL when that is 0)
  * FP32 arithmetic: distances by FMA, exp through the hardware exp2, per-tile
  * partial sums merged with Kahan compensation. Deterministic: the same inputs
- * give bit-identical outputs.
+ * give bit-identical outputs. Pairs far enough apart that their FP32 kernel
+ * value is exactly 0 are left out (see lr_set_pair_culling); points that
+ * carry an image layout (a grid query, or explicit points whose lr_points
+ * grid matches their count, e.g. ray-traced pixels) are grouped by image
+ * tiles, which is what makes the skipping effective.
  * Errors: LR_ERR_INVALID_ARG (pointers, sizes, lengthscale <= 0, variance
  * not finite, workspace too small), LR_ERR_CUDA (launch failure).
  */
@@ -457,7 +475,10 @@ lr_status lr_matvec_train_workspace_size(const lr_points* query, const lr_points
  *   and subhalo parameters. Pair sums are FP32 with Kahan-merged tiles;
  *   parameter and hyperparameter sums are FP64. Deterministic.
  * Same arguments and conventions as gp_kernel_matvec; workspace of at least
- * lr_matvec_bwd_workspace_size() bytes, 256-byte aligned.
+ * lr_matvec_bwd_workspace_size() bytes, 256-byte aligned. With nrhs > 1
+ * (explicit or self sources, no moments_in) v, g_out and d_v are
+ * [.][nrhs]; d_x, d_y, d_lengthscale, d_variance and the lens gradients sum
+ * over the right-hand sides.
  * Errors: LR_ERR_INVALID_ARG also when d_y is requested for grid or
  * self-kernel sources, lens gradients without a ray-traced query, or a
  * ray-traced source set distinct from the query.

@@ -87,6 +87,7 @@ SIGNATURES = {
     "lr_fault_status": (ctypes.c_int32, [_P, ctypes.c_int32]),
     "lr_kernel_timer_enable": (ctypes.c_int32, [ctypes.c_int32]),
     "lr_kernel_timer_read": (ctypes.c_int32, [ctypes.c_int32, _P, _P, _P]),
+    "lr_set_pair_culling": (ctypes.c_int32, [ctypes.c_int32]),
     "lens_raytrace": (ctypes.c_int32, [ctypes.POINTER(lr_points), _P, _P, _P]),
     "lens_jacobian": (ctypes.c_int32, [ctypes.POINTER(lr_points), _P, _P, _P]),
     "gp_kernel_matvec": (ctypes.c_int32, [ctypes.POINTER(lr_points), ctypes.POINTER(lr_points), _P, ctypes.c_int32,

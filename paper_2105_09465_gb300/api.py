@@ -97,12 +97,17 @@ def lens_jacobian(pts: Points, stream=None):
     return jac.view(-1, 2, 2), mu
 
 
-def matvec_workspace_size(query: Points, source: Points | None) -> int:
+def _nrhs(v: torch.Tensor) -> int:
+    """Right-hand sides of a weight tensor: (m,) is one, (m, r) is r."""
+    return 1 if v.dim() == 1 else int(v.shape[1])
+
+
+def matvec_workspace_size(query: Points, source: Points | None, nrhs: int = 1) -> int:
     lib = abi.load()
     cq, k1 = to_c_points(query)
     cs, k2 = to_c_points(source)
     b = ctypes.c_size_t(0)
-    st = lib.lr_matvec_workspace_size(ctypes.byref(cq), ctypes.byref(cs) if cs is not None else None, 1,
+    st = lib.lr_matvec_workspace_size(ctypes.byref(cq), ctypes.byref(cs) if cs is not None else None, nrhs,
                                       ctypes.byref(b))
     abi.check(st, "lr_matvec_workspace_size")
     return int(b.value)
@@ -113,27 +118,30 @@ def gp_kernel_matvec(query: Points, source: Points | None, v: torch.Tensor, leng
                      workspace: torch.Tensor | None = None, stream=None, beta: torch.Tensor | None = None):
     """out_i = sum_j variance exp(-|x_i - y_j|^2 / (2 lengthscale^2)) v_j.
 
-    `source=None` is the self-kernel. Returns out (and the ray-traced query
-    points when want_beta and the query carries a lens or a grid). `beta`, if
-    given, is an (n, 2) float32 buffer that receives the ray-traced points."""
+    `source=None` is the self-kernel. `v` is (m,) or (m, nrhs) with up to four
+    right-hand sides (explicit sources); out then has shape (n,) or (n, nrhs).
+    Returns out (and the ray-traced query points when want_beta and the query
+    carries a lens or a grid). `beta`, if given, is an (n, 2) float32 buffer
+    that receives the ray-traced points."""
     lib = abi.load()
     _require_cuda(v, "v")
+    nrhs = _nrhs(v)
     cq, k1 = to_c_points(query)
     cs, k2 = to_c_points(source)
     n = cq.n
     dev = v.device
     if out is None:
-        out = torch.empty((n,), dtype=torch.float32, device=dev)
+        out = torch.empty((n,) if v.dim() == 1 else (n, nrhs), dtype=torch.float32, device=dev)
     if beta is None and want_beta:
         beta = torch.empty((n, 2), dtype=torch.float32, device=dev)
     _require_cuda(beta, "beta", (2,))
     b = ctypes.c_size_t(0)
-    abi.check(lib.lr_matvec_workspace_size(ctypes.byref(cq), ctypes.byref(cs) if cs is not None else None, 1,
+    abi.check(lib.lr_matvec_workspace_size(ctypes.byref(cq), ctypes.byref(cs) if cs is not None else None, nrhs,
                                            ctypes.byref(b)), "lr_matvec_workspace_size")
     need = int(b.value)
     if workspace is None or workspace.numel() < need:
         workspace = torch.empty((max(need, 1),), dtype=torch.uint8, device=dev)
-    st = lib.gp_kernel_matvec(ctypes.byref(cq), ctypes.byref(cs) if cs is not None else None, v.data_ptr(), 1,
+    st = lib.gp_kernel_matvec(ctypes.byref(cq), ctypes.byref(cs) if cs is not None else None, v.data_ptr(), nrhs,
                               float(lengthscale), float(variance), out.data_ptr(),
                               beta.data_ptr() if beta is not None else None, workspace.data_ptr(),
                               workspace.numel(), _stream_handle(stream))
@@ -422,18 +430,22 @@ def gp_kernel_matvec_bwd(query: Points, source: Points | None, v: torch.Tensor, 
     theta_e, g1, g2) and sub (S x 4). `beta` (optional) passes the query's
     ray-traced points from the forward pass instead of recomputing them;
     `moments` (optional) the row sums of gp_kernel_matvec_train, which leaves
-    only the column sums to sweep. Returns a dict of CUDA tensors (the scalar
-    and parameter gradients are float64)."""
+    only the column sums to sweep. `v` and `g_out` are (m,) and (n,), or
+    (m, nrhs) and (n, nrhs) (explicit sources); d_v has v's shape. Returns a
+    dict of CUDA tensors (the scalar and parameter gradients are float64)."""
     lib = abi.load()
     _require_cuda(v, "v")
     _require_cuda(g_out, "g_out")
+    nrhs = _nrhs(v)
+    if _nrhs(g_out) != nrhs:
+        raise ValueError("v and g_out must have the same number of right-hand sides")
     cq, k1 = to_c_points(query)
     cs, k2 = to_c_points(source)
     n, m = cq.n, (cs.n if cs is not None else cq.n)
     dev = v.device
     out = {}
     if "v" in want:
-        out["v"] = torch.empty(m, dtype=torch.float32, device=dev)
+        out["v"] = torch.empty((m,) if v.dim() == 1 else (m, nrhs), dtype=torch.float32, device=dev)
     if "x" in want:
         out["x"] = torch.empty((n, 2), dtype=torch.float32, device=dev)
     if "y" in want:
@@ -464,12 +476,12 @@ def gp_kernel_matvec_bwd(query: Points, source: Points | None, v: torch.Tensor, 
         gr.moments_in = moments.data_ptr()
     b = ctypes.c_size_t(0)
     ps = ctypes.byref(cs) if cs is not None else None
-    abi.check(lib.lr_matvec_bwd_workspace_size(ctypes.byref(cq), ps, 1, ctypes.byref(gr), ctypes.byref(b)),
+    abi.check(lib.lr_matvec_bwd_workspace_size(ctypes.byref(cq), ps, nrhs, ctypes.byref(gr), ctypes.byref(b)),
               "lr_matvec_bwd_workspace_size")
     need = int(b.value)
     if workspace is None or workspace.numel() < need:
         workspace = torch.empty((max(need, 1),), dtype=torch.uint8, device=dev)
-    st = lib.gp_kernel_matvec_bwd(ctypes.byref(cq), ps, v.data_ptr(), 1, float(lengthscale), float(variance),
+    st = lib.gp_kernel_matvec_bwd(ctypes.byref(cq), ps, v.data_ptr(), nrhs, float(lengthscale), float(variance),
                                   g_out.data_ptr(), ctypes.byref(gr), workspace.data_ptr(), workspace.numel(),
                                   _stream_handle(stream))
     abi.check(st, "gp_kernel_matvec_bwd")

@@ -1,0 +1,635 @@
+// Culled Gaussian-kernel reductions over explicit point sets (cull.cuh): the
+// forward reduction out_i = var sum_j exp(-|x_i - y_j|^2 / (2 l^2)) v_j with
+// up to four right-hand sides (Sec. 3.1 RBF kernel, Sec. 3.3 lazy T y), the
+// row moments of the backward, and the self-kernel backward (gradient flow
+// through the reduction, Sec. 3.3 and 3.6).
+//
+// One CTA per (row block, group range). The CTA keeps its rows in registers
+// and lists, in ascending order, the groups and then the chunks within reach
+// of its bounding box. The listed chunks' record blocks are copied into
+// shared memory by the bulk-copy engine (cp.async.bulk, completed through an
+// mbarrier with a bounded wait), two batches in flight: the next batch lands
+// while the warps work on the current one. Each warp then tests its own
+// bounding box against the chunk's and skips chunks out of its reach.
+// Per chunk a thread sums its rows' terms in plain FP32 (packed f32x2 over
+// source pairs) and folds the chunk sums into its row totals (Kahan for the
+// forward). The order of every sum is fixed by the problem alone.
+#include <atomic>
+
+#include "cull.cuh"
+#include "host.cuh"
+
+namespace lr {
+
+namespace {
+
+std::atomic<int> g_pair_culling{1};
+
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+
+__device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
+  const float y = x - c;
+  const float t = s + y;
+  c = (t - s) - y;
+  s = t;
+}
+
+__device__ __forceinline__ float4 box_merge(float4 a, float4 b) {
+  return make_float4(fminf(a.x, b.x), fminf(a.y, b.y), fmaxf(a.z, b.z), fmaxf(a.w, b.w));
+}
+
+__device__ __forceinline__ float4 warp_box(float4 b) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    float4 t;
+    t.x = __shfl_xor_sync(0xffffffffu, b.x, o);
+    t.y = __shfl_xor_sync(0xffffffffu, b.y, o);
+    t.z = __shfl_xor_sync(0xffffffffu, b.z, o);
+    t.w = __shfl_xor_sync(0xffffffffu, b.w, o);
+    b = box_merge(b, t);
+  }
+  return b;
+}
+
+constexpr float4 kEmptyBox = {INFINITY, INFINITY, -INFINITY, -INFINITY};
+
+// ---------------------------------------------------------------------------
+// Prepare: one warp per chunk (lane = slot) writes the chunk's box and record.
+__global__ void __launch_bounds__(256) cull_prep_kernel(const __grid_constant__ CullPrepP P) {
+  const int c = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (c >= P.L.n_chunks) return;  // warp-uniform
+  const int64_t i = chunk_point(P.L, c, lane);
+  const bool valid = i >= 0;
+  const float2 pv = valid ? P.pts[i] : f2(0.f, 0.f);
+  const float4 box = warp_box(valid ? make_float4(pv.x, pv.y, pv.x, pv.y) : kEmptyBox);
+  // an empty slot sits at its chunk's box corner with weight 0
+  const float2 p = valid ? pv : f2(box.x, box.y);
+  const int RB = rec_bytes(P.nw);
+  char* rec = P.rec + (int64_t)c * RB;
+  if (lane == 0) P.cbox[c] = box;
+  if (!(box.x <= box.z)) {  // an empty chunk: never within reach
+    float* w = reinterpret_cast<float*>(rec);
+    for (int k = lane; k < RB / 4; k += 32) w[k] = 0.f;
+    __syncwarp();
+    if (lane == 0) *reinterpret_cast<float4*>(rec) = box;
+    return;
+  }
+  if (lane == 0) {
+    *reinterpret_cast<float4*>(rec) = box;
+    *reinterpret_cast<float4*>(rec + 16) = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  // (xa, xb, ya, yb) per source pair: absolute positions, so that the
+  // kernels form x_j - x_i directly (correctly rounded: relative error u)
+  float* xy = reinterpret_cast<float*>(rec + kRecHead);
+  const int pr = lane >> 1, half = lane & 1;
+  xy[4 * pr + half] = p.x;
+  xy[4 * pr + 2 + half] = p.y;
+  float* w = reinterpret_cast<float*>(rec + kRecHead + kRecXY);  // [nw][32], pairs consecutive
+  if (P.kind == kCullOut) {
+    for (int k = 0; k < P.nw; ++k) w[k * kChunkPts + lane] = valid ? P.a[i * P.stride + k] : 0.f;
+  } else {
+    w[lane] = valid ? P.a[i * P.stride + P.col] : 0.f;
+    if (P.kind == kCullSelf) w[kChunkPts + lane] = valid ? P.b[i * P.stride + P.col] : 0.f;
+  }
+}
+
+// Group boxes: one warp per group.
+__global__ void __launch_bounds__(256) cull_group_box_kernel(const float4* __restrict__ cbox, int n_groups,
+                                                             float4* __restrict__ gbox) {
+  const int g = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (g >= n_groups) return;
+  float4 b = box_merge(cbox[(int64_t)g * kGroupChunks + lane], cbox[(int64_t)g * kGroupChunks + 32 + lane]);
+  b = warp_box(b);
+  if (lane == 0) gbox[g] = b;
+}
+
+// ---------------------------------------------------------------------------
+// The sweep.
+constexpr int kMaxList = 1024;  // listed chunks per window
+
+template <int KIND, int NW>
+struct CullTraits;
+template <int NW>
+struct CullTraits<kCullOut, NW> {
+  static constexpr int K = NW, R = NW <= 2 ? 4 : 2, BATCH = NW <= 2 ? 32 : 16;
+};
+template <>
+struct CullTraits<kCullMom, 1> {
+  static constexpr int K = 4, R = 2, BATCH = 32;
+};
+template <>
+struct CullTraits<kCullSelf, 2> {
+  static constexpr int K = 7, R = 2, BATCH = 32;
+};
+
+// Ordered compaction over the CTA: returns the number of true predicates;
+// those threads write `value` to out[base + rank] in thread order.
+__device__ __forceinline__ int cta_compact(bool pred, int value, int* out, int base, int* wcnt) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const unsigned m = __ballot_sync(0xffffffffu, pred);
+  if (lane == 0) wcnt[w] = __popc(m);
+  __syncthreads();
+  int off = base, total = 0;
+#pragma unroll
+  for (int k = 0; k < kCullThreads / 32; ++k) {
+    if (k < w) off += wcnt[k];
+    total += wcnt[k];
+  }
+  if (pred) out[off + __popc(m & ((1u << lane) - 1u))] = value;
+  __syncthreads();
+  return total;
+}
+
+// Row outputs of one row (totals t[K]) for splits == 1, or of the merge.
+// Returns the row's scalar-gradient terms (d_l, d_var) through sl, sv.
+template <int KIND, int K>
+__device__ __forceinline__ void cull_finalize(const CullArgs& A, int64_t i, const float* t, float& sl, float& sv) {
+  sl = 0.f;
+  sv = 0.f;
+  if (KIND == kCullOut) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) A.out[i * A.nrhs + k] = A.var * t[k];
+  } else if (KIND == kCullMom) {
+    if (A.g == nullptr) {
+      A.out[i] = A.var * t[0];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) A.mom[(int64_t)k * A.n + i] = t[k];
+    } else {
+      const float gi = A.g[i * A.stride + A.col];
+      if (A.d_x) {
+        float2 d = f2(A.dx_scale * gi * t[1], A.dx_scale * gi * t[2]);
+        if (A.dx_accumulate) {
+          const float2 o = A.d_x[i];
+          d = f2(o.x + d.x, o.y + d.y);
+        }
+        A.d_x[i] = d;
+      }
+      sl = __fmul_rn(__fmul_rn(gi, t[3]), A.dl_scale);
+      sv = __fmul_rn(gi, t[0]);
+    }
+  } else {  // kCullSelf
+    const float gi = A.g[i * A.stride + A.col], vi = A.vrow[i * A.stride + A.col];
+    if (A.d_v) A.d_v[i * A.stride + A.col] = A.var * t[4];
+    if (A.d_x) {
+      float2 d = f2(A.dx_scale * fmaf(gi, t[1], vi * t[5]), A.dx_scale * fmaf(gi, t[2], vi * t[6]));
+      if (A.dx_accumulate) {
+        const float2 o = A.d_x[i];
+        d = f2(o.x + d.x, o.y + d.y);
+      }
+      A.d_x[i] = d;
+    }
+    sl = __fmul_rn(__fmul_rn(gi, t[3]), A.dl_scale);
+    sv = __fmul_rn(gi, t[0]);
+  }
+}
+
+// Per-CTA FP64 partials of the two scalar gradients: FP32 per-row terms,
+// FP32 warp sums, FP64 across the warps in order.
+__device__ __forceinline__ void cta_scalar_partials(float sl, float sv, double* part, int64_t blk, float* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    sl += __shfl_xor_sync(0xffffffffu, sl, o);
+    sv += __shfl_xor_sync(0xffffffffu, sv, o);
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int nw = blockDim.x >> 5;
+  if (lane == 0) {
+    red[w] = sl;
+    red[nw + w] = sv;
+  }
+  __syncthreads();
+  if (threadIdx.x < 2) {
+    double t = 0.0;
+    for (int k = 0; k < nw; ++k) t += (double)red[threadIdx.x * nw + k];
+    part[blk * 2 + threadIdx.x] = t;
+  }
+}
+
+template <int KIND, int NW>
+struct CullSmem {
+  static constexpr int BATCH = CullTraits<KIND, NW>::BATCH;
+  alignas(128) char buf[2][BATCH * rec_bytes(NW)];
+  uint64_t bar[2];
+  float4 wbox[kCullThreads / 32];
+  int clist[kMaxList];
+  int gsel[kCullThreads];
+  int wcnt[kCullThreads / 32];
+  float red[2 * kCullThreads / 32];
+  int flag;
+};
+
+template <int KIND, int NW>
+__global__ void __launch_bounds__(kCullThreads) cull_kernel(const __grid_constant__ CullArgs A) {
+  using T = CullTraits<KIND, NW>;
+  constexpr int R = T::R, K = T::K, BATCH = T::BATCH, RB = rec_bytes(NW);
+  __shared__ CullSmem<KIND, NW> sm;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int rb = blockIdx.x / A.splits, split = blockIdx.x - rb * A.splits;
+
+  // rows
+  float xr[R], yr[R];
+  int64_t irow[R];
+  float4 mybox = kEmptyBox;
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    irow[r] = map_row(A.map, A.n, A.rows_per_cta, rb, tid * R + r);
+    const float2 p = irow[r] >= 0 ? A.x[irow[r]] : f2(0.f, 0.f);
+    xr[r] = p.x;
+    yr[r] = p.y;
+    if (irow[r] >= 0) mybox = box_merge(mybox, make_float4(p.x, p.y, p.x, p.y));
+  }
+  const float4 wb = warp_box(mybox);
+  float2 NQ[R], NP[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    NQ[r] = f2(-xr[r], -xr[r]);
+    NP[r] = f2(-yr[r], -yr[r]);
+  }
+  const float2 NC = f2(-A.c, -A.c);
+  if (lane == 0) sm.wbox[warp] = wb;
+  if (tid == 0) {
+    mbar_init(&sm.bar[0], 1);
+    mbar_init(&sm.bar[1], 1);
+  }
+  __syncthreads();
+  float4 cb = sm.wbox[0];
+#pragma unroll
+  for (int k = 1; k < kCullThreads / 32; ++k) cb = box_merge(cb, sm.wbox[k]);
+  const bool cull = A.cull != 0;
+
+  float tot[R][K], comp[R][K];
+#pragma unroll
+  for (int r = 0; r < R; ++r)
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      tot[r][k] = 0.f;
+      comp[r][k] = 0.f;
+    }
+
+  uint32_t phases = 0u;  // bit k: parity of buffer k's next completion
+  bool failed = false;
+  const int g_lo = (int)((int64_t)split * A.n_groups / A.splits);
+  const int g_hi = (int)((int64_t)(split + 1) * A.n_groups / A.splits);
+  int gpos = g_lo;
+  while (gpos < g_hi && !failed) {
+    // ---- list the chunks within reach, in ascending order, up to kMaxList
+    int count = 0;
+    bool full = false;
+    while (gpos < g_hi && !full) {
+      const int g = gpos + tid;
+      const bool gs = g < g_hi && !(cull && boxes_far(cb, A.gbox[g], A.sc));
+      const int ng = cta_compact(gs, g, sm.gsel, 0, sm.wcnt);
+      int k = 0;
+      for (; k < ng; ++k) {
+        if (count + kGroupChunks > kMaxList) break;
+        const int gg = sm.gsel[k];
+        const int c = gg * kGroupChunks + (tid & (kGroupChunks - 1));
+        const bool cs = tid < kGroupChunks && !(cull ? boxes_far(cb, A.cbox[c], A.sc)
+                                                     : !(A.cbox[c].x <= A.cbox[c].z));
+        count += cta_compact(cs, c, sm.clist, count, sm.wcnt);
+      }
+      if (k < ng) {
+        gpos = sm.gsel[k];
+        full = true;
+      } else {
+        gpos = min(gpos + kCullThreads, g_hi);
+      }
+      __syncthreads();  // gsel is rewritten by the next window
+    }
+    // ---- stream the listed chunks through shared memory, two batches in flight
+    const int nb = (count + BATCH - 1) / BATCH;
+    auto issue = [&](int b) {
+      const int c0 = b * BATCH, cn = min(BATCH, count - c0);
+      char* dst = sm.buf[b & 1];
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_expect_tx(&sm.bar[b & 1], (uint32_t)(cn * RB));
+      for (int k = 0; k < cn; ++k) bulk_g2s(dst + k * RB, A.rec + (int64_t)sm.clist[c0 + k] * RB, RB, &sm.bar[b & 1]);
+    };
+    if (tid == 0 && nb > 0) issue(0);
+    for (int b = 0; b < nb; ++b) {
+      if (tid == 0 && b + 1 < nb) issue(b + 1);
+      const uint32_t ph = (phases >> (b & 1)) & 1u;
+      const bool ok = mbar_wait_bounded(&sm.bar[b & 1], ph, A.fault);
+      if (__syncthreads_or(!ok)) {
+        failed = true;
+        // copies may still be in flight into either buffer: wait for them
+        // once more (bounded) before the CTA gives up its shared memory
+        if (!ok) mbar_wait_bounded(&sm.bar[b & 1], ph, nullptr);
+        if (b + 1 < nb) mbar_wait_bounded(&sm.bar[(b + 1) & 1], (phases >> ((b + 1) & 1)) & 1u, nullptr);
+        break;
+      }
+      phases ^= 1u << (b & 1);
+      const int cn = min(BATCH, count - b * BATCH);
+      const char* bb = sm.buf[b & 1];
+      for (int k = 0; k < cn; ++k) {
+        const char* rec = bb + k * RB;
+        const float4 box = *reinterpret_cast<const float4*>(rec);
+        if (cull && boxes_far(wb, box, A.sc)) continue;  // warp-uniform
+        const float4* xy = reinterpret_cast<const float4*>(rec + kRecHead);
+        const float2* wt = reinterpret_cast<const float2*>(rec + kRecHead + kRecXY);
+        if (KIND == kCullOut) {
+          // k v = 2^(-c |x_j - x_i|^2) v, c = sc^2: 6 FP32 lanes per pair
+          float2 acc[R][NW];
+#pragma unroll
+          for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int w = 0; w < NW; ++w) acc[r][w] = f2(0.f, 0.f);
+#pragma unroll 4
+          for (int pp = 0; pp < kChunkPairs; ++pp) {
+            const float4 P = xy[pp];
+            const float2 X = f2(P.x, P.y), Y = f2(P.z, P.w);
+            float2 W[NW];
+#pragma unroll
+            for (int w = 0; w < NW; ++w) W[w] = wt[w * kChunkPairs + pp];
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+              const float2 dx = __fadd2_rn(X, NQ[r]), dy = __fadd2_rn(Y, NP[r]);
+              const float2 e = __fmul2_rn(__ffma2_rn(dy, dy, __fmul2_rn(dx, dx)), NC);
+              const float2 kk = f2(ex2_approx(e.x), ex2_approx(e.y));
+#pragma unroll
+              for (int w = 0; w < NW; ++w) acc[r][w] = __ffma2_rn(kk, W[w], acc[r][w]);
+            }
+          }
+          // fold the chunk's sums into the row totals (only nonzero ones, so
+          // that a chunk left out and a chunk of exact zeros agree bitwise)
+#pragma unroll
+          for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int w = 0; w < NW; ++w) {
+              const float sum = acc[r][w].x + acc[r][w].y;
+              if (sum != 0.f) kahan_add(tot[r][w], comp[r][w], sum);
+            }
+        } else {
+          // row moments from per-pair differences d = x_j - x_i:
+          // A += k w, B += k w d, C += k w |d|^2 (and A, B of the second
+          // weight for the self-kernel). Differences, not moments about a
+          // reference point: a pair at d ~ 0 (the row's own point) adds
+          // nothing to B and C instead of two large terms that cancel.
+          constexpr int NA = KIND == kCullSelf ? 7 : 4;
+          float2 acc[R][NA];
+#pragma unroll
+          for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int k2 = 0; k2 < NA; ++k2) acc[r][k2] = f2(0.f, 0.f);
+#pragma unroll 4
+          for (int pp = 0; pp < kChunkPairs; ++pp) {
+            const float4 P = xy[pp];
+            const float2 X = f2(P.x, P.y), Y = f2(P.z, P.w);
+            const float2 W0 = wt[pp];
+            const float2 W1 = KIND == kCullSelf ? wt[kChunkPairs + pp] : f2(0.f, 0.f);
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+              const float2 dx = __fadd2_rn(X, NQ[r]), dy = __fadd2_rn(Y, NP[r]);
+              const float2 t = __ffma2_rn(dy, dy, __fmul2_rn(dx, dx));
+              const float2 e = __fmul2_rn(t, NC);
+              const float2 kk = f2(ex2_approx(e.x), ex2_approx(e.y));
+              const float2 kw = __fmul2_rn(kk, W0);
+              acc[r][0] = __fadd2_rn(acc[r][0], kw);
+              acc[r][1] = __ffma2_rn(kw, dx, acc[r][1]);
+              acc[r][2] = __ffma2_rn(kw, dy, acc[r][2]);
+              acc[r][3] = __ffma2_rn(kw, t, acc[r][3]);
+              if (KIND == kCullSelf) {
+                const float2 kg = __fmul2_rn(kk, W1);
+                acc[r][4] = __fadd2_rn(acc[r][4], kg);
+                acc[r][5] = __ffma2_rn(kg, dx, acc[r][5]);
+                acc[r][6] = __ffma2_rn(kg, dy, acc[r][6]);
+              }
+            }
+          }
+#pragma unroll
+          for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int k2 = 0; k2 < NA; ++k2) tot[r][k2] += acc[r][k2].x + acc[r][k2].y;
+        }
+      }
+      __syncthreads();  // the buffer is refilled two batches on
+    }
+  }
+  if (failed) return;
+
+  // ---- outputs
+  float sl = 0.f, sv = 0.f;
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    if (irow[r] < 0) continue;
+    float t[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) t[k] = KIND == kCullOut ? tot[r][k] - comp[r][k] : tot[r][k];
+    if (A.splits == 1) {
+      float a, b;
+      cull_finalize<KIND, K>(A, irow[r], t, a, b);
+      sl += a;
+      sv += b;
+    } else {
+#pragma unroll
+      for (int k = 0; k < K; ++k) A.partial[((int64_t)split * K + k) * A.n + irow[r]] = t[k];
+    }
+  }
+  if (A.splits == 1 && A.scal_part) cta_scalar_partials(sl, sv, A.scal_part, blockIdx.x, sm.red);
+}
+
+// Fixed-order merge of the group-range partials [splits][K][n], then the
+// outputs as the sweep would have written them.
+template <int KIND, int K>
+__global__ void __launch_bounds__(256) cull_merge_kernel(const __grid_constant__ CullArgs A) {
+  __shared__ float red[16];
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  float sl = 0.f, sv = 0.f;
+  if (i < A.n) {
+    float t[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      float s = 0.f, c = 0.f;
+      for (int sp = 0; sp < A.splits; ++sp) kahan_add(s, c, A.partial[((int64_t)sp * K + k) * A.n + i]);
+      t[k] = s - c;
+    }
+    cull_finalize<KIND, K>(A, i, t, sl, sv);
+  }
+  if (A.scal_part) cta_scalar_partials(sl, sv, A.scal_part, blockIdx.x, red);
+}
+
+// Fixed-order FP64 sum of scalar partials [nblk][2] into d_len, d_var.
+__global__ void __launch_bounds__(256) cull_scalar_final_kernel(const double* __restrict__ part, int64_t nblk,
+                                                                double* d_len, double* d_var) {
+  __shared__ double red[2][8];
+  double a = 0.0, b = 0.0;
+  for (int64_t k = threadIdx.x; k < nblk; k += 256) {
+    a += part[2 * k];
+    b += part[2 * k + 1];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = a;
+    red[1][threadIdx.x >> 5] = b;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double sa = 0.0, sb = 0.0;
+    for (int w = 0; w < 8; ++w) {
+      sa += red[0][w];
+      sb += red[1][w];
+    }
+    if (d_len) *d_len = sa;
+    if (d_var) *d_var = sb;
+  }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Host side
+
+int cull_enabled() { return g_pair_culling.load(std::memory_order_relaxed); }
+
+template <int KIND, int NW>
+static const void* cull_fn() {
+  return reinterpret_cast<const void*>(&cull_kernel<KIND, NW>);
+}
+
+static const void* cull_kernel_ptr(int kind, int nw) {
+  if (kind == kCullOut) {
+    switch (nw) {
+      case 1: return cull_fn<kCullOut, 1>();
+      case 2: return cull_fn<kCullOut, 2>();
+      case 3: return cull_fn<kCullOut, 3>();
+      default: return cull_fn<kCullOut, 4>();
+    }
+  }
+  return kind == kCullMom ? cull_fn<kCullMom, 1>() : cull_fn<kCullSelf, 2>();
+}
+
+static int cull_rows_per_thread(int kind, int nw) { return (kind == kCullOut && nw <= 2) ? 4 : 2; }
+
+lr_status plan_cull(int kind, int nrhs, int64_t n, const lr_grid* qlayout, int64_t m, const lr_grid* slayout,
+                    CullPlan* out) {
+  CullPlan P{};
+  P.kind = kind;
+  P.nw = cull_nw(kind, nrhs);
+  P.L = make_chunk_layout(slayout, m);
+  P.rows_per_cta = kCullThreads * cull_rows_per_thread(kind, P.nw);
+  if (qlayout) {
+    P.map.W = qlayout->nx * qlayout->ss;
+    P.map.H = qlayout->ny * qlayout->ss;
+    P.map.tw = kCullTileW;
+    P.map.th = P.rows_per_cta / kCullTileW;
+    P.map.TW = (P.map.W + P.map.tw - 1) / P.map.tw;
+    P.map.TH = (P.map.H + P.map.th - 1) / P.map.th;
+  }
+  P.row_blocks = row_block_count(P.map, n, P.rows_per_cta);
+  int dev = 0, n_sm = 1, occ = 1;
+  LR_CHECK_CUDA(cudaGetDevice(&dev));
+  LR_CHECK_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
+  LR_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, cull_kernel_ptr(kind, P.nw), kCullThreads, 0));
+  // group ranges per row block: only when the row blocks alone leave most of
+  // the resident CTA slots empty (small query sets)
+  const int64_t slots = (int64_t)(occ > 0 ? occ : 1) * n_sm;
+  int64_t splits = 1;
+  if (P.row_blocks > 0 && P.row_blocks < 2 * slots) splits = (2 * slots + P.row_blocks - 1) / P.row_blocks;
+  if (splits > P.L.n_groups) splits = P.L.n_groups > 0 ? P.L.n_groups : 1;
+  P.splits = (int32_t)splits;
+  P.K = kind == kCullOut ? P.nw : (kind == kCullMom ? 4 : 7);
+  size_t off = 0;
+  P.off_rec = off;
+  off += align256((size_t)P.L.n_chunks * rec_bytes(P.nw));
+  P.off_cbox = off;
+  off += align256(sizeof(float4) * (size_t)P.L.n_chunks);
+  P.off_gbox = off;
+  off += align256(sizeof(float4) * (size_t)(P.L.n_groups > 0 ? P.L.n_groups : 1));
+  P.off_partial = off;
+  if (P.splits > 1) off += align256(sizeof(float) * (size_t)P.splits * P.K * (size_t)n);
+  P.scal_blocks = P.splits > 1 ? (n + 255) / 256 : P.row_blocks * P.splits;
+  P.off_scal = off;
+  off += align256(sizeof(double) * 2 * (size_t)(P.scal_blocks > 0 ? P.scal_blocks : 1));
+  P.bytes = off;
+  *out = P;
+  return LR_OK;
+}
+
+lr_status launch_cull_prep(const CullPlan& P, const float2* pts, float sc, const float* a, const float* b,
+                           int32_t stride, int32_t col, char* ws, cudaStream_t s) {
+  CullPrepP Q{};
+  Q.pts = pts;
+  Q.L = P.L;
+  Q.sc = sc;
+  Q.kind = P.kind;
+  Q.nw = P.nw;
+  Q.a = a;
+  Q.b = b;
+  Q.stride = stride;
+  Q.col = col;
+  Q.rec = ws + P.off_rec;
+  Q.cbox = reinterpret_cast<float4*>(ws + P.off_cbox);
+  Q.gbox = reinterpret_cast<float4*>(ws + P.off_gbox);
+  if (P.L.n_chunks == 0) return LR_OK;
+  const int64_t warps = P.L.n_chunks;
+  cull_prep_kernel<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, s>>>(Q);
+  LR_CHECK_CUDA(cudaGetLastError());
+  cull_group_box_kernel<<<(unsigned)(((int64_t)P.L.n_groups * 32 + 255) / 256), 256, 0, s>>>(Q.cbox, P.L.n_groups,
+                                                                                              Q.gbox);
+  LR_CHECK_CUDA(cudaGetLastError());
+  return LR_OK;
+}
+
+template <int KIND, int NW>
+static lr_status launch_sweep_t(const CullPlan& P, const CullArgs& A, cudaStream_t s) {
+  const unsigned grid = (unsigned)(P.row_blocks * P.splits);
+  cull_kernel<KIND, NW><<<grid, kCullThreads, 0, s>>>(A);
+  LR_CHECK_CUDA(cudaGetLastError());
+  if (P.splits > 1) {
+    cull_merge_kernel<KIND, CullTraits<KIND, NW>::K><<<(unsigned)((A.n + 255) / 256), 256, 0, s>>>(A);
+    LR_CHECK_CUDA(cudaGetLastError());
+  }
+  return LR_OK;
+}
+
+lr_status launch_cull_sweep(const CullPlan& P, CullArgs A, char* ws, int timer_id, cudaStream_t s) {
+  if (P.row_blocks == 0) return LR_OK;
+  A.map = P.map;
+  A.rows_per_cta = P.rows_per_cta;
+  A.cull = cull_enabled();
+  A.rec = ws + P.off_rec;
+  A.cbox = reinterpret_cast<const float4*>(ws + P.off_cbox);
+  A.gbox = reinterpret_cast<const float4*>(ws + P.off_gbox);
+  A.n_chunks = P.L.n_chunks;
+  A.n_groups = P.L.n_groups;
+  A.splits = P.splits;
+  A.partial = reinterpret_cast<float*>(ws + P.off_partial);
+  A.fault = fault_ptr();
+  LR_REQUIRE(A.fault != nullptr, "could not resolve the device fault word");
+  if (timer_id >= 0) ktimer_begin(timer_id, s);
+  lr_status st;
+  if (P.kind == kCullOut) {
+    switch (P.nw) {
+      case 1: st = launch_sweep_t<kCullOut, 1>(P, A, s); break;
+      case 2: st = launch_sweep_t<kCullOut, 2>(P, A, s); break;
+      case 3: st = launch_sweep_t<kCullOut, 3>(P, A, s); break;
+      default: st = launch_sweep_t<kCullOut, 4>(P, A, s); break;
+    }
+  } else if (P.kind == kCullMom) {
+    st = launch_sweep_t<kCullMom, 1>(P, A, s);
+  } else {
+    st = launch_sweep_t<kCullSelf, 2>(P, A, s);
+  }
+  if (timer_id >= 0) ktimer_end(timer_id, s);
+  return st;
+}
+
+lr_status launch_cull_scalar_final(const double* part, int64_t nblk, double* d_len, double* d_var, cudaStream_t s) {
+  if (!d_len && !d_var) return LR_OK;
+  cull_scalar_final_kernel<<<1, 256, 0, s>>>(part, nblk, d_len, d_var);
+  LR_CHECK_CUDA(cudaGetLastError());
+  return LR_OK;
+}
+
+}  // namespace lr
+
+extern "C" lr_status lr_set_pair_culling(int32_t enable) {
+  lr::g_pair_culling.store(enable ? 1 : 0, std::memory_order_relaxed);
+  return LR_OK;
+}

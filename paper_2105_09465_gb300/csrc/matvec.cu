@@ -19,6 +19,7 @@
 #include <math.h>
 
 #include "batch.cuh"
+#include "cull.cuh"
 #include "host.cuh"
 #include "problems.cuh"
 
@@ -289,18 +290,6 @@ __global__ void __launch_bounds__(kMvThreads) matvec_kernel(const __grid_constan
   matvec_body<GRID>(A, rb, blockIdx.x - rb * A.chunks, sm);
 }
 
-// Batched form: CTA b runs task b of its problem; every problem of one
-// launch has the same source kind (grid or explicit).
-template <bool GRID>
-__global__ void __launch_bounds__(kMvThreads) matvec_batched_kernel(const __grid_constant__ Batch<MvArgs> B) {
-  __shared__ __align__(16) MvSmem sm;
-  const int k = batch_find(B, blockIdx.x);
-  const MvArgs& A = B.p[k];
-  const int local = blockIdx.x - B.start[k];
-  const int rb = local / A.chunks;
-  matvec_body<GRID>(A, rb, local - rb * A.chunks, sm);
-}
-
 // Fixed-order compensated merge of the chunk partials.
 __device__ __forceinline__ void merge_body(const float* __restrict__ partial, int chunks, int64_t n, float variance,
                                            float* __restrict__ out, int64_t i) {
@@ -313,13 +302,6 @@ __device__ __forceinline__ void merge_body(const float* __restrict__ partial, in
 __global__ void merge_chunks_kernel(const float* __restrict__ partial, int chunks, int64_t n, float variance,
                                     float* __restrict__ out) {
   merge_body(partial, chunks, n, variance, out, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
-}
-
-__global__ void merge_batched_kernel(const __grid_constant__ Batch<MergeP> B) {
-  const int k = batch_find(B, blockIdx.x);
-  const MergeP& M = B.p[k];
-  merge_body(M.partial, M.chunks, M.n, M.variance, M.out,
-             (int64_t)(blockIdx.x - B.start[k]) * blockDim.x + threadIdx.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -336,63 +318,17 @@ int32_t plan_chunks(int64_t row_blocks, int64_t n_tiles, int occupancy, int n_sm
   return (int32_t)chunks;
 }
 
-lr_status launch_matvec_batched(const MvArgs* p, int count, cudaStream_t s) {
-  for (int kind = 0; kind < 2; ++kind) {  // 0: explicit sources, 1: grid sources
-    Batch<MvArgs> B;
-    B.count = 0;
-    int64_t tot = 0;
-    for (int i = 0; i <= count; ++i) {
-      const bool flush = (i == count) || B.count == kMaxBatch;
-      if (flush && B.count > 0) {
-        B.start[B.count] = (int32_t)tot;
-        if (tot > 0) {
-          if (kind)
-            matvec_batched_kernel<true><<<(unsigned)tot, kMvThreads, 0, s>>>(B);
-          else
-            matvec_batched_kernel<false><<<(unsigned)tot, kMvThreads, 0, s>>>(B);
-          LR_CHECK_CUDA(cudaGetLastError());
-        }
-        B.count = 0;
-        tot = 0;
-      }
-      if (i == count) break;
-      if ((p[i].src.xy == nullptr) != (kind == 1)) continue;
-      B.p[B.count] = p[i];
-      B.start[B.count] = (int32_t)tot;
-      tot += row_block_count(p[i].map, p[i].n, kRowsPerCta) * p[i].chunks;
-      ++B.count;
-    }
-  }
-  return LR_OK;
-}
-
-lr_status launch_merge_batched(const MergeP* p, int count, cudaStream_t s) {
-  for (int b0 = 0; b0 < count; b0 += kMaxBatch) {
-    Batch<MergeP> B;
-    B.count = count - b0 < kMaxBatch ? count - b0 : kMaxBatch;
-    int64_t tot = 0;
-    for (int k = 0; k < B.count; ++k) {
-      B.p[k] = p[b0 + k];
-      B.start[k] = (int32_t)tot;
-      tot += (p[b0 + k].n + 255) / 256;
-    }
-    B.start[B.count] = (int32_t)tot;
-    if (tot == 0) continue;
-    merge_batched_kernel<<<(unsigned)tot, 256, 0, s>>>(B);
-    LR_CHECK_CUDA(cudaGetLastError());
-  }
-  return LR_OK;
-}
-
 struct MvPlan {
   int64_t n, m;
+  int32_t nrhs;
   bool self;
   bool q_raytrace, q_grid;   // query needs ray-tracing / grid materialisation
   bool s_raytrace;           // source needs ray-tracing
   bool s_grid;               // source read as a grid (no materialisation)
   int32_t n_tiles, segs, chunks, row_blocks;
   RowMap map;                // row blocks: image tiles of a grid query, else index order
-  size_t off_qbeta, off_sbeta, off_partial, off_info, bytes;
+  CullPlan cull;             // explicit sources: the culled sweep
+  size_t off_qbeta, off_sbeta, off_partial, off_info, off_cull, bytes;
 };
 
 static lr_status plan_matvec(const lr_points* q, const lr_points* s, int32_t nrhs, bool have_beta_out, MvPlan* P) {
@@ -402,9 +338,9 @@ static lr_status plan_matvec(const lr_points* q, const lr_points* s, int32_t nrh
     st = validate_points(s, "gp_kernel_matvec(source)", false);
     if (st != LR_OK) return st;
   }
-  LR_REQUIRE(nrhs == 1, "gp_kernel_matvec: nrhs = %d; this version supports nrhs = 1", nrhs);
   MvPlan p{};
   p.n = q->n;
+  p.nrhs = nrhs;
   p.self = (s == nullptr);
   p.m = p.self ? q->n : s->n;
   p.q_raytrace = q->lens != nullptr;
@@ -412,84 +348,46 @@ static lr_status plan_matvec(const lr_points* q, const lr_points* s, int32_t nrh
   p.s_raytrace = !p.self && s->lens != nullptr;
   p.s_grid = !p.self && !p.s_raytrace && s->xy == nullptr;
   if (p.s_grid) {
-    const int W = s->grid.nx * s->grid.ss;
-    p.segs = (W + kTile - 1) / kTile;
-    p.n_tiles = (int32_t)((int64_t)p.segs * s->grid.ny * s->grid.ss);
+    LR_REQUIRE(nrhs == 1, "gp_kernel_matvec: nrhs = %d; grid sources take nrhs = 1 (explicit sources: 1..4)", nrhs);
   } else {
-    p.segs = 0;
-    p.n_tiles = (int32_t)((p.m + kTile - 1) / kTile);
+    LR_REQUIRE(nrhs >= 1 && nrhs <= 4, "gp_kernel_matvec: nrhs = %d; explicit sources take nrhs = 1..4", nrhs);
   }
-  const lr_grid* layout = query_layout(q);
-  p.map = layout ? make_row_map(layout, kRowsPerCta) : RowMap{};
-  p.row_blocks = (int32_t)row_block_count(p.map, p.n, kRowsPerCta);
-  int dev = 0, n_sm = 1, occ = 1;
-  LR_CHECK_CUDA(cudaGetDevice(&dev));
-  LR_CHECK_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
-  LR_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, matvec_kernel<false>, kMvThreads, 0));
-  const int64_t chunks = plan_chunks(p.row_blocks, p.n_tiles, occ, n_sm, p.s_grid ? kSkipWaves : kChunkWaves);
-  p.chunks = (int32_t)chunks;
   size_t off = 0;
   const bool need_qbuf = (p.q_raytrace || p.q_grid) && !have_beta_out;
   p.off_qbeta = off;
   if (need_qbuf) off += align256(sizeof(float2) * (size_t)p.n);
   p.off_sbeta = off;
   if (p.s_raytrace) off += align256(sizeof(float2) * (size_t)p.m);
+  const lr_grid* layout = query_layout(q);
+  if (!p.s_grid) {
+    // explicit, ray-traced or self sources: the culled sweep
+    const lr_grid* slayout = p.self ? layout : query_layout(s);
+    st = plan_cull(kCullOut, nrhs, p.n, layout, p.m, slayout, &p.cull);
+    if (st != LR_OK) return st;
+    p.off_cull = off;
+    off += p.cull.bytes;
+    p.off_partial = p.off_info = off;
+    p.bytes = off;
+    *P = p;
+    return LR_OK;
+  }
+  const int W = s->grid.nx * s->grid.ss;
+  p.segs = (W + kTile - 1) / kTile;
+  p.n_tiles = (int32_t)((int64_t)p.segs * s->grid.ny * s->grid.ss);
+  p.map = layout ? make_row_map(layout, kRowsPerCta) : RowMap{};
+  p.row_blocks = (int32_t)row_block_count(p.map, p.n, kRowsPerCta);
+  int dev = 0, n_sm = 1, occ = 1;
+  LR_CHECK_CUDA(cudaGetDevice(&dev));
+  LR_CHECK_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
+  LR_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, matvec_kernel<true>, kMvThreads, 0));
+  p.chunks = plan_chunks(p.row_blocks, p.n_tiles, occ, n_sm, kSkipWaves);
   p.off_partial = off;
   if (p.chunks > 1) off += align256(sizeof(float) * (size_t)p.chunks * (size_t)p.n);
   p.off_info = off;
-  if (p.s_grid) off += row_info_bytes(p.map, p.n, kRowsPerCta);
+  off += row_info_bytes(p.map, p.n, kRowsPerCta);
+  p.off_cull = off;
   p.bytes = off;
   *P = p;
-  return LR_OK;
-}
-
-// Problem descriptor for a forward reduction of explicit query points against
-// explicit (ys) or grid (yg) sources, planned exactly as gp_kernel_matvec
-// plans it. With partial == NULL only *partial_bytes is filled in.
-lr_status make_mv_problem(const float2* x, int64_t n, const float2* ys, const lr_grid* yg, int64_t m, const float* v,
-                          float ell, float var, float* out, float* partial, MvArgs* A, MergeP* M,
-                          size_t* partial_bytes) {
-  lr_points q{}, src{};
-  q.xy = x ? reinterpret_cast<const float*>(x) : reinterpret_cast<const float*>(uintptr_t(256));
-  q.n = n;
-  if (ys || !yg) {
-    src.xy = ys ? reinterpret_cast<const float*>(ys) : reinterpret_cast<const float*>(uintptr_t(256));
-  } else {
-    src.grid = *yg;
-  }
-  src.n = m;
-  MvPlan P;
-  lr_status st = plan_matvec(&q, &src, 1, false, &P);
-  if (st != LR_OK) return st;
-  *partial_bytes = P.chunks > 1 ? align256(sizeof(float) * (size_t)P.chunks * (size_t)n) : 0;
-  if (A) {
-    MvArgs a{};
-    a.x = x;
-    a.n = n;
-    a.src.xy = ys;
-    a.src.g = ys ? GridDev{} : grid_dev(*yg);
-    a.src.m = m;
-    a.src.segs = P.segs;
-    a.src.n_tiles = P.n_tiles;
-    a.v = v;
-    a.neg_c = (float)(-1.4426950408889634 / (2.0 * (double)ell * (double)ell));
-    a.sc = (float)sqrt(1.4426950408889634 / (2.0 * (double)ell * (double)ell));
-    a.split = ys ? 0 : grid_split_ok(a.src.g, a.sc);
-    a.variance = var;
-    a.chunks = P.chunks;
-    a.out = out;
-    a.partial = partial;
-    a.map = RowMap{};
-    a.info = nullptr;
-    *A = a;
-  }
-  if (M) {
-    M->partial = partial;
-    M->chunks = P.chunks;
-    M->n = n;
-    M->variance = var;
-    M->out = out;
-  }
   return LR_OK;
 }
 
@@ -528,7 +426,7 @@ extern "C" lr_status gp_kernel_matvec(const lr_points* query, const lr_points* s
   cudaStream_t s = as_cuda(stream);
   if (P.n == 0) return LR_OK;
   if (P.m == 0) {
-    LR_CHECK_CUDA(cudaMemsetAsync(out, 0, sizeof(float) * (size_t)P.n, s));
+    LR_CHECK_CUDA(cudaMemsetAsync(out, 0, sizeof(float) * (size_t)P.n * (size_t)P.nrhs, s));
     return LR_OK;
   }
   char* ws = static_cast<char*>(workspace);
@@ -558,32 +456,42 @@ extern "C" lr_status gp_kernel_matvec(const lr_points* query, const lr_points* s
   } else {
     S.xy = reinterpret_cast<const float2*>(source->xy);
   }
+  const float sc = (float)sqrt(1.4426950408889634 / (2.0 * (double)lengthscale * (double)lengthscale));
+  if (!P.s_grid) {
+    // explicit, ray-traced or self sources: culled sweep over chunk records
+    char* cws = ws + P.off_cull;
+    st = launch_cull_prep(P.cull, S.xy, sc, v, nullptr, P.nrhs, 0, cws, s);
+    if (st != LR_OK) return st;
+    CullArgs C{};
+    C.x = xq;
+    C.n = P.n;
+    C.sc = sc;
+    C.c = (float)(1.4426950408889634 / (2.0 * (double)lengthscale * (double)lengthscale));
+    C.nrhs = P.nrhs;
+    C.var = variance;
+    C.out = out;
+    return launch_cull_sweep(P.cull, C, cws, LR_KT_MATVEC, s);
+  }
   MvArgs A;
   A.x = xq;
   A.n = P.n;
   A.src = S;
   A.v = v;
   A.neg_c = (float)(-1.4426950408889634 / (2.0 * (double)lengthscale * (double)lengthscale));
-  A.sc = (float)sqrt(1.4426950408889634 / (2.0 * (double)lengthscale * (double)lengthscale));
-  A.split = S.xy ? 0 : grid_split_ok(S.g, A.sc);
+  A.sc = sc;
+  A.split = grid_split_ok(S.g, A.sc);
   A.variance = variance;
   A.chunks = P.chunks;
   A.out = out;
   A.partial = reinterpret_cast<float*>(ws + P.off_partial);
   A.map = P.map;
-  A.info = nullptr;
-  if (P.s_grid) {
-    // row-block boxes: the exactly-zero pairs are left out
-    RowInfoP R{xq, P.n, P.map, kRowsPerCta, P.segs, S.g, A.sc, reinterpret_cast<RowBlockInfo*>(ws + P.off_info)};
-    if ((st = launch_row_info(R, s)) != LR_OK) return st;
-    A.info = R.info;
-  }
+  // row-block boxes: the exactly-zero pairs are left out
+  RowInfoP R{xq, P.n, P.map, kRowsPerCta, P.segs, S.g, A.sc, reinterpret_cast<RowBlockInfo*>(ws + P.off_info)};
+  if ((st = launch_row_info(R, s)) != LR_OK) return st;
+  A.info = R.info;
   const unsigned grid = (unsigned)((int64_t)P.row_blocks * P.chunks);
   ktimer_begin(LR_KT_MATVEC, s);
-  if (S.xy)
-    matvec_kernel<false><<<grid, kMvThreads, 0, s>>>(A);
-  else
-    matvec_kernel<true><<<grid, kMvThreads, 0, s>>>(A);
+  matvec_kernel<true><<<grid, kMvThreads, 0, s>>>(A);
   LR_CHECK_CUDA(cudaGetLastError());
   ktimer_end(LR_KT_MATVEC, s);
   if (P.chunks > 1) {

@@ -17,6 +17,7 @@
 #include <math.h>
 
 #include "host.cuh"
+#include "cull.cuh"
 #include "problems.cuh"
 
 namespace lr {
@@ -1627,14 +1628,19 @@ static size_t rows_ws(int64_t n, int64_t m, bool grid, const lr_grid* g, bool se
 
 struct BwPlan {
   int64_t n, m;
+  int32_t nrhs;
   bool self, q_raytrace, q_grid, s_raytrace, s_grid;
   bool want_lens;       // lens / subhalo gradients of the query's lens
   bool need_dx;         // d_x needed (requested or for the lens gradient)
   bool moments;         // row sums given by the training forward
-  size_t off_qbeta, off_sbeta, off_rows, off_dv, off_dx, off_sgrid, off_swap, off_swaprows, off_vjp, bytes;
+  bool culled;          // explicit or self sources without moments: culled sweeps
+  CullPlan cp_rows;     // culled: self backward, or the non-self row moments
+  CullPlan cp_dy;       // culled, non-self with d_y: row moments with the roles swapped
+  size_t off_qbeta, off_sbeta, off_rows, off_dv, off_dx, off_sgrid, off_swap, off_swaprows, off_vjp, off_scal, bytes;
+  size_t swap_bytes;    // workspace of the swapped forward (d_v of explicit sources)
 };
 
-static lr_status plan_bwd(const lr_points* q, const lr_points* s, const lr_grads* gr, BwPlan* P) {
+static lr_status plan_bwd(const lr_points* q, const lr_points* s, int32_t nrhs, const lr_grads* gr, BwPlan* P) {
   lr_status st = validate_points(q, "gp_kernel_matvec_bwd(query)", false);
   if (st != LR_OK) return st;
   if (s) {
@@ -1644,6 +1650,7 @@ static lr_status plan_bwd(const lr_points* q, const lr_points* s, const lr_grads
   LR_REQUIRE(gr != nullptr, "gp_kernel_matvec_bwd: grads is NULL");
   BwPlan p{};
   p.n = q->n;
+  p.nrhs = nrhs;
   p.self = s == nullptr;
   p.m = p.self ? q->n : s->n;
   p.q_raytrace = q->lens != nullptr;
@@ -1662,12 +1669,27 @@ static lr_status plan_bwd(const lr_points* q, const lr_points* s, const lr_grads
   const lr_grid* qg = query_layout(q);  // row blocks follow the image tiles
   LR_REQUIRE(!p.moments || !p.self, "gp_kernel_matvec_bwd: moments_in applies to non-self sources only");
   LR_REQUIRE(((uintptr_t)gr->moments_in & 3u) == 0, "gp_kernel_matvec_bwd: moments_in must be 4-byte aligned");
+  p.culled = !p.s_grid && !p.moments;
+  if (p.culled) {
+    LR_REQUIRE(nrhs >= 1 && nrhs <= 4, "gp_kernel_matvec_bwd: nrhs = %d; explicit sources take nrhs = 1..4", nrhs);
+  } else {
+    LR_REQUIRE(nrhs == 1, "gp_kernel_matvec_bwd: nrhs = %d; grid sources and moments_in take nrhs = 1", nrhs);
+  }
   size_t off = 0;
   p.off_qbeta = off;
   if ((p.q_raytrace && !gr->beta_in) || p.q_grid) off += align256(8 * (size_t)p.n);
   p.off_sbeta = off;
   p.off_rows = off;
-  if (p.moments) {
+  p.off_scal = off;
+  if (p.culled) {
+    const lr_grid* sg = p.self ? qg : query_layout(s);
+    st = plan_cull(p.self ? kCullSelf : kCullMom, 1, p.n, qg, p.m, sg, &p.cp_rows);
+    if (st != LR_OK) return st;
+    off += p.cp_rows.bytes;
+    // scalar partials of every right-hand side, summed once at the end
+    p.off_scal = off;
+    off += align256(sizeof(double) * 2 * (size_t)nrhs * (size_t)(p.cp_rows.scal_blocks > 0 ? p.cp_rows.scal_blocks : 1));
+  } else if (p.moments) {
     // scalar partials of the moment merge, then the d_v-only pass of grid sources
     off += align256(sizeof(double) * 2 * (size_t)((p.n + kMergeThreads - 1) / kMergeThreads + 1));
     p.off_dv = off;
@@ -1689,28 +1711,118 @@ static lr_status plan_bwd(const lr_points* q, const lr_points* s, const lr_grads
   p.off_swap = off;
   p.off_swaprows = off;
   if (!p.self && gr->d_v && !p.s_grid) {
-    p.off_swap = off;
-    // forward reduction with roles swapped: query = sources (explicit), source = query points (explicit)
-    lr_points qs{}, ss{};
-    qs.xy = reinterpret_cast<const float*>(uintptr_t(256));
-    qs.n = p.m;
-    ss.xy = reinterpret_cast<const float*>(uintptr_t(256));
-    ss.n = p.n;
-    size_t b = 0;
-    st = lr_matvec_workspace_size(&qs, &ss, 1, &b);
+    // d_v: the forward reduction with the roles swapped (query = the
+    // sources, source = the query points)
+    lr_points qs = *s, ss = *q;
+    qs.lens = nullptr;
+    ss.lens = nullptr;
+    ss.xy = reinterpret_cast<const float*>(uintptr_t(256));  // planning reads no point
+    st = lr_matvec_workspace_size(&qs, &ss, nrhs, &p.swap_bytes);
     if (st != LR_OK) return st;
-    off += align256(b);
+    off += align256(p.swap_bytes);
   }
   p.off_swaprows = off;
   if (!p.self && gr->d_y) {
-    size_t b = rows_ws(p.m, p.n, false, nullptr, false, false, nullptr, &st);
-    if (st != LR_OK) return st;
-    off += b;
+    if (p.culled) {
+      st = plan_cull(kCullMom, 1, p.m, query_layout(s), p.n, qg, &p.cp_dy);
+      if (st != LR_OK) return st;
+      off += p.cp_dy.bytes;
+    } else {
+      size_t b = rows_ws(p.m, p.n, false, nullptr, false, false, nullptr, &st);
+      if (st != LR_OK) return st;
+      off += b;
+    }
   }
   p.off_vjp = off;
   if (p.want_lens) off += raytrace_vjp_ws(p.n, q->n_sub);
   p.bytes = off;
   *P = p;
+  return LR_OK;
+}
+
+// The culled backward of explicit or self sources: per right-hand side the
+// self-kernel sweep (d_v, d_x of both roles, scalar partials) or the row
+// moments (d_x, scalar partials); then d_v and d_y of non-self sources with
+// the roles swapped; then d_l and d_var from every partial in fixed order.
+static lr_status launch_culled_bwd(const BwPlan& P, const lr_points* query, const lr_points* source,
+                                   const float2* xq, const float* v, float ell, float var, const float* g,
+                                   const lr_grads& G, float2* dx, char* ws, lr_stream stream) {
+  cudaStream_t s = as_cuda(stream);
+  const double c = 1.4426950408889634 / (2.0 * (double)ell * (double)ell);
+  const float sc = (float)sqrt(c);
+  const float dx_scale = (float)((double)var / ((double)ell * ell));
+  const float dl_scale = (float)((double)var / ((double)ell * ell * ell));
+  const float2* ys = P.self ? xq : reinterpret_cast<const float2*>(source->xy);
+  const bool want_scal = G.d_lengthscale || G.d_variance;
+  double* scal = reinterpret_cast<double*>(ws + P.off_scal);
+  const int64_t nblk = P.cp_rows.scal_blocks;
+  char* cws = ws + P.off_rows;
+  lr_status st;
+  const bool rows_needed = P.self ? (G.d_v || dx || want_scal) : (dx || want_scal);
+  for (int r = 0; r < P.nrhs && rows_needed; ++r) {
+    st = launch_cull_prep(P.cp_rows, ys, sc, v, P.self ? g : nullptr, P.nrhs, r, cws, s);
+    if (st != LR_OK) return st;
+    CullArgs A{};
+    A.x = xq;
+    A.n = P.n;
+    A.sc = sc;
+    A.c = (float)c;
+    A.nrhs = 1;
+    A.var = var;
+    A.dx_scale = dx_scale;
+    A.dl_scale = dl_scale;
+    A.g = g;
+    A.vrow = v;
+    A.stride = P.nrhs;
+    A.col = r;
+    A.d_x = dx;
+    A.dx_accumulate = r > 0;
+    A.d_v = P.self ? G.d_v : nullptr;
+    A.scal_part = want_scal ? scal + 2 * (size_t)r * (size_t)nblk : nullptr;
+    st = launch_cull_sweep(P.cp_rows, A, cws, LR_KT_BWD_ROWS, s);
+    if (st != LR_OK) return st;
+  }
+  if (want_scal) {
+    st = launch_cull_scalar_final(scal, (int64_t)P.nrhs * nblk, G.d_lengthscale, G.d_variance, s);
+    if (st != LR_OK) return st;
+  }
+  if (!P.self && G.d_v) {
+    // d_v_j = var sum_i k_ij g_i: the forward with the roles swapped
+    lr_points qs = *source, ss{};
+    qs.lens = nullptr;
+    ss.xy = reinterpret_cast<const float*>(xq);
+    ss.n = P.n;
+    const lr_grid* qg = query_layout(query);
+    if (qg) ss.grid = *qg;
+    st = gp_kernel_matvec(&qs, &ss, g, P.nrhs, ell, var, G.d_v, nullptr, ws + P.off_swap, P.swap_bytes, stream);
+    if (st != LR_OK) return st;
+  }
+  if (!P.self && G.d_y) {
+    // d_y_j = var/l^2 v_j sum_i k_ij g_i (x_i - y_j): row moments of g with
+    // the roles swapped, rows multiplied by their own v
+    char* dws = ws + P.off_swaprows;
+    for (int r = 0; r < P.nrhs; ++r) {
+      st = launch_cull_prep(P.cp_dy, xq, sc, g, nullptr, P.nrhs, r, dws, s);
+      if (st != LR_OK) return st;
+      CullArgs A{};
+      A.x = ys;
+      A.n = P.m;
+      A.sc = sc;
+      A.c = (float)c;
+      A.nrhs = 1;
+      A.var = var;
+      A.dx_scale = dx_scale;
+      A.dl_scale = dl_scale;
+      A.g = v;
+      A.stride = P.nrhs;
+      A.col = r;
+      A.d_x = reinterpret_cast<float2*>(G.d_y);
+      A.dx_accumulate = r > 0;
+      A.scal_part = nullptr;
+      st = launch_cull_sweep(P.cp_dy, A, dws, -1, s);
+      if (st != LR_OK) return st;
+    }
+  }
   return LR_OK;
 }
 
@@ -1721,9 +1833,8 @@ using namespace lr;
 extern "C" lr_status lr_matvec_bwd_workspace_size(const lr_points* query, const lr_points* source, int32_t nrhs,
                                                   const lr_grads* grads, size_t* bytes) {
   LR_REQUIRE(bytes != nullptr, "lr_matvec_bwd_workspace_size: bytes is NULL");
-  LR_REQUIRE(nrhs == 1, "lr_matvec_bwd_workspace_size: nrhs = %d; this version supports nrhs = 1", nrhs);
   BwPlan P;
-  lr_status st = plan_bwd(query, source, grads, &P);
+  lr_status st = plan_bwd(query, source, nrhs, grads, &P);
   if (st != LR_OK) return st;
   *bytes = P.bytes;
   return LR_OK;
@@ -1733,9 +1844,8 @@ extern "C" lr_status gp_kernel_matvec_bwd(const lr_points* query, const lr_point
                                           int32_t nrhs, float lengthscale, float variance, const float* g_out,
                                           const lr_grads* grads, void* workspace, size_t workspace_bytes,
                                           lr_stream stream) {
-  LR_REQUIRE(nrhs == 1, "gp_kernel_matvec_bwd: nrhs = %d; this version supports nrhs = 1", nrhs);
   BwPlan P;
-  lr_status st = plan_bwd(query, source, grads, &P);
+  lr_status st = plan_bwd(query, source, nrhs, grads, &P);
   if (st != LR_OK) return st;
   LR_REQUIRE(isfinite(lengthscale) && lengthscale > 0.f, "gp_kernel_matvec_bwd: lengthscale must be > 0");
   LR_REQUIRE(isfinite(variance), "gp_kernel_matvec_bwd: variance is not finite");
@@ -1754,7 +1864,7 @@ extern "C" lr_status gp_kernel_matvec_bwd(const lr_points* query, const lr_point
   char* ws = static_cast<char*>(workspace);
   if (P.n == 0 || P.m == 0) {
     // every gradient is an empty sum
-    if (G.d_v && P.m) LR_CHECK_CUDA(cudaMemsetAsync(G.d_v, 0, 4 * (size_t)P.m, s));
+    if (G.d_v && P.m) LR_CHECK_CUDA(cudaMemsetAsync(G.d_v, 0, 4 * (size_t)P.m * (size_t)P.nrhs, s));
     if (G.d_x && P.n) LR_CHECK_CUDA(cudaMemsetAsync(G.d_x, 0, 8 * (size_t)P.n, s));
     if (G.d_y && P.m) LR_CHECK_CUDA(cudaMemsetAsync(G.d_y, 0, 8 * (size_t)P.m, s));
     if (G.d_lengthscale) LR_CHECK_CUDA(cudaMemsetAsync(G.d_lengthscale, 0, 8, s));
@@ -1794,7 +1904,11 @@ extern "C" lr_status gp_kernel_matvec_bwd(const lr_points* query, const lr_point
     const lr_status sj = side ? fork_end(s, &f) : LR_OK;
     return st != LR_OK ? st : sj;
   }
-  if (P.moments) {
+  if (P.culled) {
+    // explicit or self sources: the culled sweeps (d_v and d_y included)
+    st = launch_culled_bwd(P, query, source, xq, v, lengthscale, variance, g_out, G, dx, ws, stream);
+    if (st != LR_OK) return st;
+  } else if (P.moments) {
     // row gradients from the training forward's moments
     st = launch_moment_rows(G.moments_in, P.n, P.s_grid, g_out, v, lengthscale, variance, dx, G.d_lengthscale,
                             G.d_variance, ws + P.off_rows, s);
@@ -1806,23 +1920,23 @@ extern "C" lr_status gp_kernel_matvec_bwd(const lr_points* query, const lr_point
                      (P.self || P.s_grid) ? G.d_v : nullptr, G.d_lengthscale, G.d_variance, ws + P.off_rows, s);
     if (st != LR_OK) return st;
   }
-  // d_v of explicit non-self sources: sum_i var k_ij g_i, the forward reduction
-  // with the point sets swapped (grid sources have it fused into the row pass)
-  if (!P.self && !P.s_grid && G.d_v) {
-    const float* ypts = source->xy;
-    lr_points qs{}, ss{};
-    qs.xy = ypts;
-    qs.n = P.m;
+  // d_v of explicit non-self sources after the training forward: sum_i var
+  // k_ij g_i, the forward reduction with the point sets swapped (grid sources
+  // have it fused into the row pass)
+  if (!P.culled && !P.self && !P.s_grid && G.d_v) {
+    lr_points qs = *source, ss{};
+    qs.lens = nullptr;
     ss.xy = reinterpret_cast<const float*>(xq);
     ss.n = P.n;
-    size_t b = 0;
-    st = lr_matvec_workspace_size(&qs, &ss, 1, &b);
-    if (st != LR_OK) return st;
-    st = gp_kernel_matvec(&qs, &ss, g_out, 1, lengthscale, variance, G.d_v, nullptr, ws + P.off_swap, b, stream);
+    const lr_grid* qg = query_layout(query);
+    if (qg) ss.grid = *qg;
+    st = gp_kernel_matvec(&qs, &ss, g_out, 1, lengthscale, variance, G.d_v, nullptr, ws + P.off_swap, P.swap_bytes,
+                          stream);
     if (st != LR_OK) return st;
   }
-  // d_y of explicit non-self sources: the row pass with the point sets swapped
-  if (!P.self && G.d_y) {
+  // d_y of explicit non-self sources after the training forward: the row pass
+  // with the point sets swapped
+  if (!P.culled && !P.self && G.d_y) {
     st = launch_rows(reinterpret_cast<const float2*>(source->xy), P.m, nullptr, xq, nullptr, P.n, g_out, nullptr, v,
                      g_out,
                      lengthscale, variance, false, reinterpret_cast<float2*>(G.d_y), nullptr, nullptr, nullptr,

@@ -203,8 +203,6 @@ struct AxpyP {
 
 // Batched launch helpers: each splits `count` problems into launches of at
 // most kMaxBatch problems, all on stream s.
-lr_status launch_matvec_batched(const MvArgs* p, int count, cudaStream_t s);
-lr_status launch_merge_batched(const MergeP* p, int count, cudaStream_t s);
 lr_status launch_raytrace_batched(const RtP* p, int count, cudaStream_t s);
 lr_status launch_bwd_rows_batched(const BwArgs* p, int count, cudaStream_t s);
 lr_status launch_bwd_merge_batched(const MergeArgs* p, int count, cudaStream_t s);
@@ -228,9 +226,7 @@ lr_status launch_vjp_batched(const VjpP* p, int count, cudaStream_t s);
 lr_status launch_vjp_final_batched(const VjpFinalP* p, int count, cudaStream_t s);
 
 // Problem constructors (planned exactly as the single-problem entry points).
-lr_status make_mv_problem(const float2* x, int64_t n, const float2* ys, const lr_grid* yg, int64_t m, const float* v,
-                          float ell, float var, float* out, float* partial, MvArgs* A, MergeP* M,
-                          size_t* partial_bytes);
+
 lr_status make_rows_problem(const float2* x, int64_t n, const lr_grid* qgrid, const float2* ys, const lr_grid* yg,
                             int64_t m, const float* v, const float* g, float ell, float var, float2* dx, double* d_len,
                             double* d_var, float* d_v, char* ws, BwArgs* A, MergeArgs* M, ScalP* S, DvMergeP* D,

@@ -102,8 +102,10 @@ def test_matvec_rejects_bad_arguments_without_gpu(lib):
     assert lib.gp_kernel_matvec(ctypes.byref(q), None, None, 1, 0.1, 1.0, None, None, None, 0, None) == \
         abi.LR_ERR_INVALID_ARG
     q.xy = dbuf()
-    assert lib.gp_kernel_matvec(ctypes.byref(q), None, None, 2, 0.1, 1.0, None, None, None, 0, None) == \
-        abi.LR_ERR_INVALID_ARG  # nrhs
+    for nrhs in (0, 5):
+        assert lib.gp_kernel_matvec(ctypes.byref(q), None, None, nrhs, 0.1, 1.0, None, None, None, 0, None) == \
+            abi.LR_ERR_INVALID_ARG  # nrhs outside 1..4
+        assert b"nrhs" in lib.lr_last_error()
     q.n = -1
     assert lib.gp_kernel_matvec(ctypes.byref(q), None, None, 1, 0.1, 1.0, None, None, None, 0, None) == \
         abi.LR_ERR_INVALID_ARG
