@@ -20,7 +20,10 @@ Parity status of each function (what pins it, see tests/test_oracle_pins.py):
   raytrace_vjp      — pinned: FP64 central differences of raytrace
   kernel_matvec     — pinned: dense long-double brute force, symmetry, PSD,
                       l -> infinity, two-point value, Riemann-sum integral
-  kernel_matvec_vjp — pinned: FP64 central differences of kernel_matvec
+  kernel_matvec_vjp — pinned: FP64 central differences of kernel_matvec; its
+                      input-error sensitivities by perturbing the points
+  self_vjp_rows     — pinned: FP64 central differences of kernel_matvec (both
+                      roles of the listed points)
 """
 from __future__ import annotations
 
@@ -83,6 +86,7 @@ def lib():
         L.orc_pixel_shapes_vjp.argtypes = [_P, _I32, _I32, _P, _P]
         L.orc_kernel_matvec.argtypes = [_P, _I64, _P, _I64, _P, _D, _D, _P, _I64, _P, _P, _P]
         L.orc_kernel_matvec_vjp.argtypes = [_P, _I64, _P, _I64, _P, _D, _D, _P, _I32, _P, _P, _P, _P, _P, _P]
+        L.orc_self_vjp_rows.argtypes = [_P, _I64, _P, _P, _D, _D, _P, _I64] + [_P] * 6
         L.orc_num_threads.restype = _I32
         _lib = L
     return _lib
@@ -274,7 +278,10 @@ def kernel_matvec_rows(x, rows, y, v, lengthscale, variance=1.0):
 
 def kernel_matvec_vjp(x, y, v, lengthscale, variance, g, self_kernel=False, with_abs=False):
     """Reduction gradients: dict with d_v, d_x, d_y (None for a self-kernel), d_len, d_var for Loss = sum_i g_i out_i.
-    With `with_abs`, also the matching sums of absolute terms under keys *_abs."""
+    With `with_abs`, also the matching sums of absolute terms under keys *_abs
+    and the input-error sensitivities under *_sens: if every point moves by at
+    most delta per coordinate, each output moves by at most
+    2 sqrt(2) delta * sens (first order)."""
     x, y = _pairs(x), _pairs(y)
     v = np.ascontiguousarray(v, dtype=np.float64).reshape(-1)
     g = np.ascontiguousarray(g, dtype=np.float64).reshape(-1)
@@ -284,12 +291,32 @@ def kernel_matvec_vjp(x, y, v, lengthscale, variance, g, self_kernel=False, with
     d_y = None if self_kernel else np.empty((m, 2), np.float64)
     d_len = np.zeros(1, np.float64)
     d_var = np.zeros(1, np.float64)
-    sc = [np.empty(m), np.empty((n, 2)), np.empty((m, 2)), np.zeros(1), np.zeros(1)]
-    arr = (ctypes.c_void_p * 5)(*[a.ctypes.data for a in sc]) if with_abs else None
+    sc = [np.empty(m), np.empty((n, 2)), np.empty((m, 2)), np.zeros(1), np.zeros(1),
+          np.empty(m), np.empty((n, 2)), np.empty((m, 2)), np.zeros(1), np.zeros(1)]
+    arr = (ctypes.c_void_p * 10)(*[a.ctypes.data for a in sc]) if with_abs else None
     lib().orc_kernel_matvec_vjp(_ptr(x), n, _ptr(y), m, _ptr(v), lengthscale, variance, _ptr(g), int(self_kernel),
                                 _ptr(d_v), _ptr(d_x), _ptr(d_y), _ptr(d_len), _ptr(d_var), arr)
     out = {"d_v": d_v, "d_x": d_x, "d_y": d_y, "d_len": float(d_len[0]), "d_var": float(d_var[0])}
     if with_abs:
         out.update({"d_v_abs": sc[0], "d_x_abs": sc[1], "d_y_abs": None if self_kernel else sc[2],
-                    "d_len_abs": float(sc[3][0]), "d_var_abs": float(sc[4][0])})
+                    "d_len_abs": float(sc[3][0]), "d_var_abs": float(sc[4][0]),
+                    "d_v_sens": sc[5], "d_x_sens": sc[6], "d_y_sens": None if self_kernel else sc[7],
+                    "d_len_sens": float(sc[8][0]), "d_var_sens": float(sc[9][0])})
     return out
+
+
+def self_vjp_rows(x, v, g, lengthscale, variance, rows):
+    """Self-kernel gradients on the listed rows only: dict with d_v (r,), d_x
+    (r, 2) (both roles of each listed point), their *_abs scales and *_sens
+    input-error sensitivities (as kernel_matvec_vjp)."""
+    x = _pairs(x)
+    v = np.ascontiguousarray(v, dtype=np.float64).reshape(-1)
+    g = np.ascontiguousarray(g, dtype=np.float64).reshape(-1)
+    rows = np.ascontiguousarray(rows, dtype=np.int64)
+    assert rows.size == 0 or (rows.min() >= 0 and rows.max() < x.shape[0])
+    k = rows.shape[0]
+    R = {"d_v": np.empty(k), "d_x": np.empty((k, 2)), "d_v_abs": np.empty(k), "d_x_abs": np.empty((k, 2)),
+         "d_v_sens": np.empty(k), "d_x_sens": np.empty((k, 2))}
+    lib().orc_self_vjp_rows(_ptr(x), x.shape[0], _ptr(v), _ptr(g), lengthscale, variance, _ptr(rows), k,
+                            *[_ptr(R[key]) for key in ("d_v", "d_x", "d_v_abs", "d_x_abs", "d_v_sens", "d_x_sens")])
+    return R

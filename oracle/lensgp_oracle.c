@@ -706,32 +706,45 @@ ORC_API void orc_knn_r2(const double* q, int64_t m, int32_t k, const int64_t* ro
  *   d_var   = sum_ij g_i v_j k_ij / var
  * For a self-kernel (x and y the same point set, `self` != 0) the point
  * gradient is the sum of both roles and is returned in d_x (d_y unused).
- * `scale` (optional, 5 arrays) receives the matching sums of absolute terms
+ * `scale` (optional, 10 arrays) receives the matching sums of absolute terms
  * (the scales of the parity tolerances): |d_v|, |d_x| (per component, both
  * roles), |d_y|, |d_len|, |d_var| in the order
  *   scale[0] = d_v_abs[m], scale[1] = d_x_abs[n][2], scale[2] = d_y_abs[m][2],
- *   scale[3] = d_len_abs[1], scale[4] = d_var_abs[1].
+ *   scale[3] = d_len_abs[1], scale[4] = d_var_abs[1],
+ * then the input-error sensitivities of the same outputs, scale[5..9]: if
+ * every point moves by at most delta per coordinate, so that each pair
+ * distance vector changes by at most D = 2 sqrt(2) delta, each output moves
+ * by at most D times its sensitivity (to first order in D). Per pair, with
+ * d = |d_ij| and k = var exp(-d^2 / (2 l^2)), |dk/dd| = k d / l^2, so
+ *   k w d_c  changes by at most |w| k D (1 + d |d_c| / l^2),
+ *   k w d^2  changes by at most |w| k D (2 d + d^3 / l^2),
+ *   k w      changes by at most |w| k D d / l^2;
+ * the sensitivities are these bounds without D, summed like the outputs.
  * Every output pointer may be NULL. */
 ORC_API void orc_kernel_matvec_vjp(const double* x, int64_t n, const double* y, int64_t m, const double* v,
                                    double lengthscale, double variance, const double* g, int32_t self, double* d_v,
                                    double* d_x /*[n][2]*/, double* d_y /*[m][2]*/, double* d_len, double* d_var,
-                                   double* const* scale /* [5] or NULL */) {
+                                   double* const* scale /* [10] or NULL */) {
   const double l2 = lengthscale * lengthscale, inv2l2 = 1.0 / (2.0 * l2);
   double* s_dv = scale ? scale[0] : NULL;
   double* s_dx = scale ? scale[1] : NULL;
   double* s_dy = scale ? scale[2] : NULL;
-  nsum tl = {0, 0}, tv = {0, 0}, tla = {0, 0}, tva = {0, 0};
+  double* e_dv = scale ? scale[5] : NULL;
+  double* e_dx = scale ? scale[6] : NULL;
+  double* e_dy = scale ? scale[7] : NULL;
+  nsum tl = {0, 0}, tv = {0, 0}, tla = {0, 0}, tva = {0, 0}, tle = {0, 0}, tve = {0, 0};
   /* row pass: d_x (row role), d_len, d_var */
 #pragma omp parallel
   {
-    nsum ll = {0, 0}, lv = {0, 0}, lla = {0, 0}, lva = {0, 0};
+    nsum ll = {0, 0}, lv = {0, 0}, lla = {0, 0}, lva = {0, 0}, lle = {0, 0}, lve = {0, 0};
 #pragma omp for schedule(dynamic, 64)
     for (int64_t i = 0; i < n; ++i) {
       const double xi = x[2 * i], yi = x[2 * i + 1];
       nsum sx = {0, 0}, sy = {0, 0}, sl = {0, 0}, sv = {0, 0}, ax = {0, 0}, ay = {0, 0}, al = {0, 0}, av = {0, 0};
+      nsum ex = {0, 0}, ey = {0, 0}, el = {0, 0}, ev = {0, 0};
       for (int64_t j = 0; j < m; ++j) {
         const double dx = y[2 * j] - xi, dy = y[2 * j + 1] - yi;
-        const double d2 = dx * dx + dy * dy;
+        const double d2 = dx * dx + dy * dy, d = sqrt(d2);
         const double kv = variance * exp(-d2 * inv2l2) * v[j];
         ns_add(&sx, kv * dx);
         ns_add(&sy, kv * dy);
@@ -741,6 +754,10 @@ ORC_API void orc_kernel_matvec_vjp(const double* x, int64_t n, const double* y, 
         ns_add(&ay, fabs(kv * dy));
         ns_add(&al, fabs(kv) * d2);
         ns_add(&av, fabs(kv));
+        ns_add(&ex, fabs(kv) * (1.0 + d * fabs(dx) / l2));
+        ns_add(&ey, fabs(kv) * (1.0 + d * fabs(dy) / l2));
+        ns_add(&el, fabs(kv) * (2.0 * d + d * d2 / l2));
+        ns_add(&ev, fabs(kv) * d / l2);
       }
       if (d_x) {
         d_x[2 * i] = g[i] * ns_val(&sx) / l2;
@@ -750,10 +767,16 @@ ORC_API void orc_kernel_matvec_vjp(const double* x, int64_t n, const double* y, 
         s_dx[2 * i] = fabs(g[i]) * ns_val(&ax) / l2;
         s_dx[2 * i + 1] = fabs(g[i]) * ns_val(&ay) / l2;
       }
+      if (e_dx) {
+        e_dx[2 * i] = fabs(g[i]) * ns_val(&ex) / l2;
+        e_dx[2 * i + 1] = fabs(g[i]) * ns_val(&ey) / l2;
+      }
       ns_add(&ll, g[i] * ns_val(&sl) / (l2 * lengthscale));
       ns_add(&lv, g[i] * ns_val(&sv) / variance);
       ns_add(&lla, fabs(g[i]) * ns_val(&al) / (l2 * lengthscale));
       ns_add(&lva, fabs(g[i]) * ns_val(&av) / fabs(variance));
+      ns_add(&lle, fabs(g[i]) * ns_val(&el) / (l2 * lengthscale));
+      ns_add(&lve, fabs(g[i]) * ns_val(&ev) / fabs(variance));
     }
 #pragma omp critical
     {
@@ -765,59 +788,143 @@ ORC_API void orc_kernel_matvec_vjp(const double* x, int64_t n, const double* y, 
       ns_add(&tla, lla.c);
       ns_add(&tva, lva.s);
       ns_add(&tva, lva.c);
+      ns_add(&tle, lle.s);
+      ns_add(&tle, lle.c);
+      ns_add(&tve, lve.s);
+      ns_add(&tve, lve.c);
     }
   }
   if (d_len) *d_len = ns_val(&tl);
   if (d_var) *d_var = ns_val(&tv);
   if (scale && scale[3]) *scale[3] = ns_val(&tla);
   if (scale && scale[4]) *scale[4] = ns_val(&tva);
+  if (scale && scale[8]) *scale[8] = ns_val(&tle);
+  if (scale && scale[9]) *scale[9] = ns_val(&tve);
   /* column pass: d_v, d_y (column role) */
-  double* col = (double*)calloc((size_t)(4 * m), sizeof(double));
+  double* col = (double*)calloc((size_t)(6 * m), sizeof(double));
 #pragma omp parallel for schedule(dynamic, 64)
   for (int64_t j = 0; j < m; ++j) {
     const double yj = y[2 * j], zj = y[2 * j + 1];
     nsum s = {0, 0}, sx = {0, 0}, sy = {0, 0}, as = {0, 0}, ax = {0, 0}, ay = {0, 0};
+    nsum es = {0, 0}, ex = {0, 0}, ey = {0, 0};
     for (int64_t i = 0; i < n; ++i) {
       const double dx = x[2 * i] - yj, dy = x[2 * i + 1] - zj;
-      const double gk = g[i] * variance * exp(-(dx * dx + dy * dy) * inv2l2);
+      const double d2 = dx * dx + dy * dy, d = sqrt(d2);
+      const double gk = g[i] * variance * exp(-d2 * inv2l2);
       ns_add(&s, gk);
       ns_add(&sx, gk * dx);
       ns_add(&sy, gk * dy);
       ns_add(&as, fabs(gk));
       ns_add(&ax, fabs(gk * dx));
       ns_add(&ay, fabs(gk * dy));
+      ns_add(&es, fabs(gk) * d / l2);
+      ns_add(&ex, fabs(gk) * (1.0 + d * fabs(dx) / l2));
+      ns_add(&ey, fabs(gk) * (1.0 + d * fabs(dy) / l2));
     }
     if (d_v) d_v[j] = ns_val(&s);
     if (s_dv) s_dv[j] = ns_val(&as);
-    col[4 * j] = v[j] * ns_val(&sx) / l2;
-    col[4 * j + 1] = v[j] * ns_val(&sy) / l2;
-    col[4 * j + 2] = fabs(v[j]) * ns_val(&ax) / l2;
-    col[4 * j + 3] = fabs(v[j]) * ns_val(&ay) / l2;
+    if (e_dv) e_dv[j] = ns_val(&es);
+    col[6 * j] = v[j] * ns_val(&sx) / l2;
+    col[6 * j + 1] = v[j] * ns_val(&sy) / l2;
+    col[6 * j + 2] = fabs(v[j]) * ns_val(&ax) / l2;
+    col[6 * j + 3] = fabs(v[j]) * ns_val(&ay) / l2;
+    col[6 * j + 4] = fabs(v[j]) * ns_val(&ex) / l2;
+    col[6 * j + 5] = fabs(v[j]) * ns_val(&ey) / l2;
   }
   if (self) {
     for (int64_t i = 0; i < n; ++i) {
       if (d_x) {
-        d_x[2 * i] += col[4 * i];
-        d_x[2 * i + 1] += col[4 * i + 1];
+        d_x[2 * i] += col[6 * i];
+        d_x[2 * i + 1] += col[6 * i + 1];
       }
       if (s_dx) {
-        s_dx[2 * i] += col[4 * i + 2];
-        s_dx[2 * i + 1] += col[4 * i + 3];
+        s_dx[2 * i] += col[6 * i + 2];
+        s_dx[2 * i + 1] += col[6 * i + 3];
+      }
+      if (e_dx) {
+        e_dx[2 * i] += col[6 * i + 4];
+        e_dx[2 * i + 1] += col[6 * i + 5];
       }
     }
   } else {
     for (int64_t j = 0; j < m; ++j) {
       if (d_y) {
-        d_y[2 * j] = col[4 * j];
-        d_y[2 * j + 1] = col[4 * j + 1];
+        d_y[2 * j] = col[6 * j];
+        d_y[2 * j + 1] = col[6 * j + 1];
       }
       if (s_dy) {
-        s_dy[2 * j] = col[4 * j + 2];
-        s_dy[2 * j + 1] = col[4 * j + 3];
+        s_dy[2 * j] = col[6 * j + 2];
+        s_dy[2 * j + 1] = col[6 * j + 3];
+      }
+      if (e_dy) {
+        e_dy[2 * j] = col[6 * j + 4];
+        e_dy[2 * j + 1] = col[6 * j + 5];
       }
     }
   }
   free(col);
+}
+
+/* The self-kernel gradients of orc_kernel_matvec_vjp (x = y, both roles) on
+ * the listed rows only, for sampled parity at sizes where the full n x n
+ * sweep is out of reach. For each listed row i, with k_ij = var
+ * exp(-|x_i - x_j|^2 / (2 l^2)) and d_ij = x_j - x_i:
+ *   d_v[r]  = sum_j k_ij g_j
+ *   d_x[r]  = [g_i sum_j k_ij v_j d_ij + v_i sum_j k_ij g_j d_ij] / l^2
+ * (the row role plus the column role of point i), the sums of absolute terms
+ * (s_dv, s_dx) and the input-error sensitivities (e_dv, e_dx) defined as for
+ * orc_kernel_matvec_vjp. Any output may be NULL. */
+ORC_API void orc_self_vjp_rows(const double* x, int64_t n, const double* v, const double* g, double lengthscale,
+                               double variance, const int64_t* rows, int64_t n_rows, double* d_v, double* d_x,
+                               double* s_dv, double* s_dx, double* e_dv, double* e_dx) {
+  const double l2 = lengthscale * lengthscale, inv2l2 = 1.0 / (2.0 * l2);
+#pragma omp parallel for schedule(dynamic, 4)
+  for (int64_t r = 0; r < n_rows; ++r) {
+    const int64_t i = rows[r];
+    const double xi = x[2 * i], yi = x[2 * i + 1];
+    nsum kg = {0, 0}, akg = {0, 0}, ekg = {0, 0};
+    nsum rx = {0, 0}, ry = {0, 0}, cx = {0, 0}, cy = {0, 0};
+    nsum arx = {0, 0}, ary = {0, 0}, acx = {0, 0}, acy = {0, 0};
+    nsum erx = {0, 0}, ery = {0, 0}, ecx = {0, 0}, ecy = {0, 0};
+    for (int64_t j = 0; j < n; ++j) {
+      const double dx = x[2 * j] - xi, dy = x[2 * j + 1] - yi;
+      const double d2 = dx * dx + dy * dy, d = sqrt(d2);
+      const double k = variance * exp(-d2 * inv2l2);
+      const double kv = k * v[j], kgj = k * g[j];
+      const double fx = 1.0 + d * fabs(dx) / l2, fy = 1.0 + d * fabs(dy) / l2;
+      ns_add(&kg, kgj);
+      ns_add(&akg, fabs(kgj));
+      ns_add(&ekg, fabs(kgj) * d / l2);
+      ns_add(&rx, kv * dx);
+      ns_add(&ry, kv * dy);
+      ns_add(&cx, kgj * dx);
+      ns_add(&cy, kgj * dy);
+      ns_add(&arx, fabs(kv * dx));
+      ns_add(&ary, fabs(kv * dy));
+      ns_add(&acx, fabs(kgj * dx));
+      ns_add(&acy, fabs(kgj * dy));
+      ns_add(&erx, fabs(kv) * fx);
+      ns_add(&ery, fabs(kv) * fy);
+      ns_add(&ecx, fabs(kgj) * fx);
+      ns_add(&ecy, fabs(kgj) * fy);
+    }
+    const double gi = g[i], vi = v[i];
+    if (d_v) d_v[r] = ns_val(&kg);
+    if (s_dv) s_dv[r] = ns_val(&akg);
+    if (e_dv) e_dv[r] = ns_val(&ekg);
+    if (d_x) {
+      d_x[2 * r] = (gi * ns_val(&rx) + vi * ns_val(&cx)) / l2;
+      d_x[2 * r + 1] = (gi * ns_val(&ry) + vi * ns_val(&cy)) / l2;
+    }
+    if (s_dx) {
+      s_dx[2 * r] = (fabs(gi) * ns_val(&arx) + fabs(vi) * ns_val(&acx)) / l2;
+      s_dx[2 * r + 1] = (fabs(gi) * ns_val(&ary) + fabs(vi) * ns_val(&acy)) / l2;
+    }
+    if (e_dx) {
+      e_dx[2 * r] = (fabs(gi) * ns_val(&erx) + fabs(vi) * ns_val(&ecx)) / l2;
+      e_dx[2 * r + 1] = (fabs(gi) * ns_val(&ery) + fabs(vi) * ns_val(&ecy)) / l2;
+    }
+  }
 }
 
 /* Number of OpenMP threads the oracle runs with (reported by the benchmark). */

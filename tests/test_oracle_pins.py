@@ -360,6 +360,80 @@ def test_matvec_vjp_against_central_differences(orc, self_kernel):
                 np.testing.assert_allclose(G["d_y"][j, c], fd, rtol=1e-6, atol=1e-8)
 
 
+def test_self_vjp_rows_against_central_differences(orc):
+    """The rows-only self-kernel gradients (used for sampled parity at full
+    size) against FP64 central differences of the forward oracle: moving point
+    p moves both its row and its column of the kernel."""
+    rng = np.random.default_rng(18)
+    n = 40
+    x = rng.uniform(-0.12, 0.12, (n, 2))
+    v, g = rng.standard_normal(n), rng.standard_normal(n)
+    ell, var = 0.06, 0.9
+
+    def loss(x_, v_):
+        return float(np.dot(g, orc.kernel_matvec(x_, x_, v_, ell, var)[0]))
+
+    rows = np.array([0, 3, 17, n - 1])
+    R = orc.self_vjp_rows(x, v, g, ell, var, rows)
+    h = 1e-6
+    for r, i in enumerate(rows):
+        vp, vm = v.copy(), v.copy()
+        vp[i] += h
+        vm[i] -= h
+        np.testing.assert_allclose(R["d_v"][r], (loss(x, vp) - loss(x, vm)) / (2 * h), rtol=1e-7, atol=1e-9)
+        for c in range(2):
+            xp, xm = x.copy(), x.copy()
+            xp[i, c] += h
+            xm[i, c] -= h
+            np.testing.assert_allclose(R["d_x"][r, c], (loss(xp, v) - loss(xm, v)) / (2 * h), rtol=1e-6, atol=1e-8)
+        assert np.all(R["d_x_abs"][r] >= np.abs(R["d_x"][r]))
+
+
+@pytest.mark.parametrize("self_kernel", [False, True])
+def test_matvec_vjp_sensitivities_bound_point_errors(orc, self_kernel):
+    """The input-error sensitivities bound how far each gradient moves when
+    every point moves by up to delta per coordinate (first order: with
+    delta = 1e-5 l the second-order rest is far below the 1 % slack)."""
+    rng = np.random.default_rng(28 + self_kernel)
+    n, m = 30, 34
+    x = rng.uniform(-0.2, 0.2, (n, 2))
+    y = x.copy() if self_kernel else rng.uniform(-0.2, 0.2, (m, 2))
+    v, g = rng.standard_normal(len(y)), rng.standard_normal(n)
+    ell, var = 0.07, 1.1
+    G = orc.kernel_matvec_vjp(x, y, v, ell, var, g, self_kernel, with_abs=True)
+    delta = 1e-5 * ell
+    D = 2 * np.sqrt(2) * delta
+    worst = {k: 0.0 for k in ("d_v", "d_x", "d_y", "d_len", "d_var")}
+    for trial in range(20):
+        dx = rng.uniform(-delta, delta, x.shape)
+        xp = x + dx
+        yp = xp.copy() if self_kernel else y + rng.uniform(-delta, delta, y.shape)
+        P = orc.kernel_matvec_vjp(xp, yp, v, ell, var, g, self_kernel)
+        for k in worst:
+            if G[k] is None:
+                continue
+            ratio = np.max(np.abs(np.asarray(P[k]) - np.asarray(G[k])) / (D * np.asarray(G[k + "_sens"]) + 1e-300))
+            worst[k] = max(worst[k], float(ratio))
+    assert all(r <= 1.01 for r in worst.values()), worst
+    # the per-point bounds are not vacuous: some perturbation moves those
+    # outputs by a sizeable fraction of them (the scalar sums' bounds add the
+    # pairs' worst cases, which random perturbations mostly cancel)
+    assert worst["d_x"] > 0.05 and worst["d_v"] > 0.05, worst
+
+
+def test_self_vjp_rows_sensitivities_match_full(orc):
+    rng = np.random.default_rng(38)
+    x = rng.uniform(-0.2, 0.2, (50, 2))
+    v, g = rng.standard_normal(50), rng.standard_normal(50)
+    F = orc.kernel_matvec_vjp(x, x, v, 0.05, 1.0, g, True, with_abs=True)
+    rows = np.arange(0, 50, 7)
+    R = orc.self_vjp_rows(x, v, g, 0.05, 1.0, rows)
+    for k in ("d_v", "d_x"):
+        np.testing.assert_allclose(R[k], F[k][rows], rtol=1e-12, atol=1e-14)
+        np.testing.assert_allclose(R[k + "_abs"], F[k + "_abs"][rows], rtol=1e-12)
+        np.testing.assert_allclose(R[k + "_sens"], F[k + "_sens"][rows], rtol=1e-12)
+
+
 # ---------------------------------------------------------------- planted mistakes
 def test_pins_catch_a_planted_sign_error(orc):
     """The divergence pin rejects a deflection with a flipped rotation (a
