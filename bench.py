@@ -1,13 +1,18 @@
 """Benchmark: fused lens ray-trace + Gaussian-kernel reduction on one GB300.
 
-One step = one pass of the hot path over the realistic workload: generate the
-400x400 image grid at 2x2 supersampling (640k points), ray-trace it through a
-power-law lens + shear + 200 truncated-NFW subhalos, and reduce the
-squared-exponential kernel of the ray-traced points against 16384 grid
-inducing points (1.05e10 pairs).
+Headline workload (the largest configuration that fits one GPU): one
+800x800 image at 2x2 supersampling (2.56M points), ray-traced through a
+power-law lens + shear + 2000 truncated-NFW subhalos; the squared-exponential
+self-kernel of the 2.56M ray-traced points (6.55e12 logical pairs), forward
+and backward down to the lens and subhalo parameters. One step = the forward
+call (ray-trace fused into it) and the backward call.
+
+A second section times the realistic workload (400x400 at 2x2 = 640k points,
+200 subhalos, against a 128x128 grid of inducing points) with its own kernel
+table, then the serving trace and the kernels beyond the step.
 
 Prints one JSON line (rank 0). `--impl reference` times the FP64 CPU oracle on
-a bounded sample of the same workload instead.
+a bounded sample of the headline workload instead.
 """
 from __future__ import annotations
 
@@ -41,6 +46,13 @@ SM_MAX_MHZ_DEFAULT = 2070.0
 # (closed form throughout): 5 + 22, 12 for the G and H brackets, 11 for the
 # four subhalo sums (their constant factors, 1/theta_s^2 of the q terms
 # included, applied once per fold or slot), 0.6 for the Kahan folds; 4 MUFU.
+# Culled reductions over explicit points (the self-kernel), per evaluated
+# pair: forward 2 differences, the squared distance (2), the scale (1) and
+# the accumulation (1); self-kernel backward the same 6 before the
+# accumulation, then k w and k g (2) and 7 accumulations (A, B, C of v; A, B
+# of g). One MUFU.EX2 each.
+CULL_FWD_MUFU, CULL_FWD_LANES = 1, 6.0
+CULL_SELF_MUFU, CULL_SELF_LANES = 1, 14.0
 RT_MUFU, RT_LANES = 4, 37.3
 RT_SER_MUFU, RT_SER_LANES = 1, 19.25
 VJ_MUFU, VJ_LANES = 4, 50.6
@@ -105,6 +117,15 @@ def workload_config(p) -> dict:
             "n_points": p.n, "m_inducing": p.m, "n_subhalos": int(len(p.sub)), "pairs_per_step": p.pairs,
             "lengthscale": p.lengthscale, "variance": p.variance,
             "l2": "flushed between timed steps (256 MiB device write outside the timed region)"}
+
+
+def large_config(p) -> dict:
+    return {"workload": f"large: {p.xgrid.nx}x{p.xgrid.ny} image, {p.xgrid.ss}x{p.xgrid.ss} supersampling "
+                        f"({p.n} points), power-law lens + shear + {len(p.sub)} tNFW subhalos "
+                        f"(1e6-1e10 Msun), self-kernel of the ray-traced points",
+            "n_points": p.n, "n_subhalos": int(len(p.sub)), "pairs_per_step": p.pairs,
+            "lengthscale": p.lengthscale, "variance": p.variance,
+            "l2": "inputs larger than L2 and a 256 MiB device write between timed steps (outside the timed region)"}
 
 
 # --------------------------------------------------------------------------
@@ -197,6 +218,60 @@ class OracleSampler:
                 f"ray-trace, reduction, reduction gradients and ray-trace gradients, {dt:.1f} s")
 
 
+class LargeOracleSampler:
+    """The FP64 oracle on row samples of the large workload: per sampled row,
+    the ray-trace through the lens and 2000 subhalos, the self-kernel row
+    against all 2.56M points (out, d_v and both roles of d_x), and the
+    ray-trace gradients of that row. The rows' sources are the pixels
+    ray-traced through the main lens and the shear (the subhalos move them by
+    milli-arcseconds, which leaves the reduction's cost unchanged); that
+    ray-trace is a fixed cost of the full problem counted once per step in
+    its share n_sample / n."""
+
+    def __init__(self, p, g=None):
+        import oracle
+
+        oracle.build()
+        self.oracle, self.p = oracle, p
+        self.xi_all = oracle.grid_points(*p.xgrid.astuple())
+        self.rng = np.random.default_rng(0)
+        self.g = self.rng.standard_normal(p.n) if g is None else g
+        _, self.beta_src = oracle.raytrace(self.xi_all, p.lens.astuple(), None)
+        self.run(self.rng.choice(p.n, 16, replace=False))  # warm-up
+
+    def run(self, rows) -> float:
+        o, p = self.oracle, self.p
+        t = time.perf_counter()
+        xi = self.xi_all[rows]
+        o.raytrace(xi, p.lens.astuple(), p.sub)
+        R = o.self_vjp_rows(self.beta_src, p.v, self.g, p.lengthscale, p.variance, rows)
+        o.raytrace_vjp(xi, p.lens.astuple(), p.sub, R["d_x"])
+        return time.perf_counter() - t
+
+    def rows_for(self, seconds: float) -> int:
+        dt = self.run(self.rng.choice(self.p.n, 64, replace=False))
+        return int(min(self.p.n, max(64, 64 * seconds / max(dt, 1e-3))))
+
+    def step(self, k: int) -> float:
+        return self.run(self.rng.choice(self.p.n, k, replace=False))
+
+    def describe(self, k: int, dt: float) -> str:
+        return (f"{k} random rows of the large workload x all {self.p.n} points ({k * self.p.n:.3e} pairs): "
+                f"ray-trace (2000 subhalos), self-kernel row with d_v and d_x, ray-trace gradients, {dt:.1f} s; "
+                f"extrapolated to all {self.p.n} rows")
+
+
+def cpu_sample_large(p, seconds: float, g=None) -> dict:
+    S = LargeOracleSampler(p, g)
+    k = S.rows_for(seconds)
+    total, done = 0.0, 0
+    while total < 0.8 * seconds and done < p.n:
+        total += S.step(k)
+        done += k
+    return {"value": done * p.n / total / 1e9, "unit": UNIT, "cores": S.oracle.num_threads(), "kind": "oracle",
+            "sample": S.describe(done, total), "seconds": total}
+
+
 def cpu_sample(p, seconds: float, g=None) -> dict:
     """Oracle throughput on a bounded sample of about `seconds` of CPU work."""
     S = OracleSampler(p, g)
@@ -213,31 +288,31 @@ def cpu_sample(p, seconds: float, g=None) -> dict:
 # --------------------------------------------------------------------------
 def run_reference(args):
     """The reference arm: the FP64 oracle as it stands, on the host cores. Each
-    of the W + K steps is a bounded row sample of the workload (the same rows
-    count every step, about ref_seconds / (W + K) seconds each); the K timed
-    steps give the whole-job rate, pairs over seconds."""
+    of the W + K steps is a bounded row sample of the large workload (the same
+    rows count every step, about ref_seconds / (W + K) seconds each); the K
+    timed steps give the whole-job rate, pairs over seconds."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     from paper_2105_09465_gb300 import workloads as W
 
-    p = W.realistic()
-    S = OracleSampler(p)
+    p = W.large()
+    S = LargeOracleSampler(p)
     per_step = min(2.0, max(0.2, args.ref_seconds / max(1, args.steps + args.warmup)))
     k = S.rows_for(per_step)
     for _ in range(args.warmup):
         S.step(k)
     secs = [S.step(k) for _ in range(args.steps)]
     total = float(np.sum(secs))
-    val = k * p.m * len(secs) / total / 1e9
+    val = k * p.n * len(secs) / total / 1e9
     ms = p.pairs / (val * 1e9) * 1e3
-    sample = (f"each step {k} random rows of the workload x all {p.m} inducing points ({k * p.m:.3e} pairs, "
-              f"{total / len(secs):.2f} s): ray-trace, reduction, reduction gradients and ray-trace gradients; "
-              f"ms_per_step is the full workload at this rate")
+    sample = (f"each step {k} random rows of the large workload x all {p.n} points ({k * p.n:.3e} pairs, "
+              f"{total / len(secs):.2f} s): ray-trace (2000 subhalos), self-kernel row with d_v and d_x, ray-trace "
+              f"gradients; ms_per_step is the full workload at this rate")
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_config(p),
+            "config": large_config(p),
             "cpu_baseline": {"kind": "oracle", "cores": S.oracle.num_threads(), "sample": sample, "value": val,
                              "unit": UNIT},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -439,24 +514,18 @@ def run_extensions(p, dev, rates, sm_max, flush, stream) -> dict:
     return out
 
 
-def run_ours(args):
+def run_realistic(args, dev, rates, clk) -> dict:
+    """The realistic workload's training step (grid inducing points, row
+    moments in the forward, the d_v-only sweep in the backward) with its
+    kernel table, timed like the headline step (one GPU)."""
     import torch
 
-    from paper_2105_09465_gb300 import replicas
+    from paper_2105_09465_gb300 import api, replicas, workloads as W
 
-    rank, local, world = replicas.world()
-    torch.cuda.set_device(local)
+    world = 1
     dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
-
-    from paper_2105_09465_gb300 import api, workloads as W
-
-    # each rank owns an independent lens system of the realistic recipe (weak scaling)
-    p = W.realistic(seed=replicas.rank_seed(rank))
-    dev = torch.device("cuda", local)
-    g_np = np.random.default_rng(100 + rank).standard_normal(p.n).astype(np.float32)
+    p = W.realistic()
+    g_np = np.random.default_rng(100).standard_normal(p.n).astype(np.float32)
     sub = torch.from_numpy(p.sub).to(dev)
     v = torch.from_numpy(p.v).to(dev)
     g = torch.from_numpy(g_np).to(dev)
@@ -522,21 +591,15 @@ def run_ours(args):
         run_step = graph.replay
 
     # ---- timed region: device-resident inputs, forward + backward per step
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    clocks = ClockSampler(local)
-    clocks.start()
-    if dist:
-        dist.barrier()
+    n_steps = max(20, min(args.steps, 200))
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_steps)]
     torch.cuda.synchronize()
-    for k in range(args.steps):
+    for k in range(n_steps):
         flush.fill_(k & 0xFF)
         ev[k][0].record(stream)
         run_step()
         ev[k][1].record(stream)
     torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    clk = clocks.stop()
     ms = replicas.max_over_ranks(float(np.mean([a.elapsed_time(b) for a, b in ev])), dev)
     value = replicas.aggregate_rate(p.pairs, ms * 1e-3, world) / 1e9
     nk = max(5, min(args.steps, 50))
@@ -672,13 +735,6 @@ def run_ours(args):
     h2d = (v_host.numel() + g_host.numel() + sub_host.numel()) * 4
     d2h = out_host.numel() * 4 + dv_host.numel() * 4 + (dl_host.numel() + ds_host.numel() + 2) * 8
 
-    rates = api.probe_pipe_rates(local)
-    if rank != 0:
-        if dist:
-            dist.barrier()
-            dist.destroy_process_group()
-        return
-
     sm_mhz = clk["sm_mhz"] or SM_MAX_MHZ_DEFAULT
     sm_max = clk["sm_max_mhz"] or SM_MAX_MHZ_DEFAULT
     nsm = rates["sm_count"]
@@ -698,11 +754,9 @@ def run_ours(args):
                                  "entry point (row-block pre-pass and merges included)"}
     dom = max((k for k in table if table[k]["in_step"]), key=lambda k: table[k]["ms"])
     d = table[dom]
-    line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded; see workloads.py)",
-        "config": dict(workload_config(p), parallelism=f"independent lens system per GPU x{world}"),
+    return {
+        "value": value, "unit": UNIT, "ms_per_step": ms, "steps": n_steps,
+        "config": workload_config(p),
         "pass": "forward + backward (grid, ray-trace, reduction with the row moments; gradients for v, "
                 "lengthscale, variance, 7 lens parameters, 200x4 subhalo parameters)",
         "fwd": {"ms": fwd_ms, "value": p.pairs / (fwd_ms * 1e-3) / 1e9, "unit": UNIT},
@@ -715,9 +769,8 @@ def run_ours(args):
         "roofline": {"bound": "alu", "achieved": d["achieved"], "peak": d["peak"], "unit": UNIT,
                      "frac": d["frac"], "traffic": measured_traffic(dom), "kernel": dom,
                      "peak_basis": f"min(MUFU {ex2:.2f}/clk/SM / MUFU per pair, FFMA2 {fma:.1f} lanes/clk/SM / lanes "
-                                   f"per pair) "
-                                   f"x {nsm} SMs x {sm_max:.0f} MHz (max clock; probe-measured rates); {d['note']}",
-                     "frac_at_measured_clock": d["frac"] * sm_max / sm_mhz},
+                                   f"per pair) x {nsm} SMs x {sm_max:.0f} MHz (max clock; probe-measured rates); "
+                                   f"{d['note']}"},
         "kernels": table,
         "step_breakdown_ms": breakdown,
         "raytrace": {"ms": rt_ms, "vjp_ms": vjp_ms, "vjp_call_ms": vjp_call_ms, "points": p.n,
@@ -725,26 +778,287 @@ def run_ours(args):
                      "hbm_gbs": p.n * 8 / (rt_ms * 1e-3) / 1e9,
                      "note": "ALU/XU-bound with subhalos (8 B written per point)"},
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "ms_per_step": e_ms, "ms_per_step_direct_launches": e_direct_ms},
+        "gpu_launches_per_step": 11,
+    }
+
+
+def run_large(args, rank, local, world, dist, dev):
+    """The headline step on the large workload; returns (line fields, rates,
+    clocks) on every rank."""
+    import torch
+
+    from paper_2105_09465_gb300 import api, replicas, workloads as W
+
+    # each rank owns an independent lens system of the large recipe (weak scaling)
+    p = W.large(seed=4 + rank)
+    g_np = np.random.default_rng(400 + rank).standard_normal(p.n).astype(np.float32)
+    sub = torch.from_numpy(p.sub).to(dev)
+    v = torch.from_numpy(p.v).to(dev)
+    g = torch.from_numpy(g_np).to(dev)
+    q = api.Points(grid=p.xgrid, lens=p.lens, sub=sub)
+    want = ("v", "lengthscale", "variance", "lens", "sub")
+    out = torch.empty(p.n, dtype=torch.float32, device=dev)
+    beta_buf = torch.empty((p.n, 2), dtype=torch.float32, device=dev)
+    ws = torch.empty(max(api.matvec_workspace_size(q, None), 1), dtype=torch.uint8, device=dev)
+    bws = torch.empty(max(api.matvec_bwd_workspace_size(q, None, want=want, beta=True), 1), dtype=torch.uint8,
+                      device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    grads = {}
+
+    def fwd():
+        api.gp_kernel_matvec(q, None, v, p.lengthscale, p.variance, out=out, beta=beta_buf, workspace=ws)
+
+    def bwd():
+        grads.update(api.gp_kernel_matvec_bwd(q, None, v, p.lengthscale, p.variance, g, want=want, workspace=bws,
+                                              beta=beta_buf))
+
+    def step():
+        fwd()
+        bwd()
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    run_step = step
+    if not args.no_graph:
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            step()
+        torch.cuda.synchronize()
+        for _ in range(2):
+            graph.replay()
+        torch.cuda.synchronize()
+        run_step = graph.replay
+
+    # ---- timed region: device-resident inputs, forward + backward per step
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)
+        ev[k][0].record(stream)
+        run_step()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = replicas.max_over_ranks(float(np.mean([a.elapsed_time(b) for a, b in ev])), dev)
+    value = replicas.aggregate_rate(p.pairs, ms * 1e-3, world) / 1e9
+    nk = max(5, min(args.steps, 30))
+    fwd_ms = replicas.max_over_ranks(event_time(fwd, nk, stream, flush), dev)
+    bwd_ms = event_time(bwd, nk, stream, flush)
+
+    # ---- where the step's time goes: the launch timer around each heavy
+    # kernel over nk directly launched steps
+    api.kernel_timer_enable(True)
+    direct_ms = event_time(step, nk, stream, flush)
+    api.kernel_timer_enable(False)
+    breakdown = {}
+    for kname in ("raytrace", "matvec", "bwd_rows", "raytrace_vjp"):
+        cnt, tot, _ = api.kernel_timer_read(kname)
+        breakdown[kname] = tot / cnt if cnt else None
+    breakdown["step (direct launches, timer on)"] = direct_ms
+    breakdown["note"] = ("matvec: the culled self-kernel forward sweep; bwd_rows: the culled self-kernel backward "
+                         "sweep; each kernel's own span (events on its stream)")
+
+    # ---- pairs the culled sweeps evaluate (the rest are exact zeros in FP32)
+    beta = api.lens_raytrace(q)
+    qx = api.Points(xy=beta, grid=p.xgrid)
+    pf, sf = api.cull_pairs_evaluated(qx, None, p.lengthscale, 0)
+    pb, sb = api.cull_pairs_evaluated(qx, None, p.lengthscale, 1)
+
+    # ---- kernels alone (same launch configuration as inside the step)
+    dbeta = torch.from_numpy(np.random.default_rng(7).standard_normal((p.n, 2)).astype(np.float32)).to(dev)
+    kern = {}
+    kern["cull_kernel<forward> (self-kernel forward)"] = (
+        *kernel_time(fwd, nk, stream, flush, "matvec"), pf, CULL_FWD_MUFU, CULL_FWD_LANES,
+        f"evaluated pairs ({sf:.3e} pair slots with row-block padding and empty chunk slots): 1 MUFU.EX2 + "
+        f"{CULL_FWD_LANES:g} FP32 lanes each; call_ms includes the ray-trace fused into the call", True)
+    kern["cull_kernel<self backward> (d_v, d_x both roles, d_l, d_var)"] = (
+        *kernel_time(bwd, nk, stream, flush, "bwd_rows"), pb, CULL_SELF_MUFU, CULL_SELF_LANES,
+        f"evaluated pairs ({sb:.3e} pair slots): 1 MUFU.EX2 + {CULL_SELF_LANES:g} FP32 lanes each; call_ms "
+        "includes the ray-trace VJP", True)
+    rt_ms, rt_call_ms = kernel_time(lambda: api.lens_raytrace(q), nk, stream, flush, "raytrace")
+    vjp_ms, vjp_call_ms = kernel_time(lambda: api.lens_raytrace_vjp(q, dbeta), nk, stream, flush, "raytrace_vjp")
+    sub_pairs = p.n * len(p.sub)
+    fs = series_fraction(p)
+    rt_mufu = fs * RT_SER_MUFU + (1 - fs) * RT_MUFU
+    rt_lanes = fs * RT_SER_LANES + (1 - fs) * RT_LANES
+    kern["raytrace_kernel<tNFW> (forward ray-trace; unit: point-subhalo pair)"] = (
+        rt_ms, rt_call_ms, sub_pairs, rt_mufu, rt_lanes,
+        f"pairs: {rt_mufu:.2f} MUFU + {rt_lanes:.1f} FP32 lanes each on average: {fs:.3f} of the pairs in the "
+        f"far-field series regime ({RT_SER_MUFU} MUFU + {RT_SER_LANES} lanes), the rest the far-side closed form "
+        f"({RT_MUFU} MUFU + {RT_LANES} lanes)", True)
+    kern["raytrace_vjp_kernel<tNFW> (ray-trace backward; unit: point-subhalo pair)"] = (
+        vjp_ms, vjp_call_ms, sub_pairs, VJ_MUFU, VJ_LANES,
+        f"pairs: {VJ_MUFU} MUFU + {VJ_LANES} FP32 lanes each (far-side tNFW G and H brackets and the four subhalo "
+        "sums)", True)
+
+    # ---- end to end through the public API with host buffers
+    v_host = torch.from_numpy(p.v).pin_memory()
+    g_host = torch.from_numpy(g_np).pin_memory()
+    sub_host = torch.from_numpy(p.sub).pin_memory()
+    out_host = torch.empty(p.n, dtype=torch.float32).pin_memory()
+    dv_host = torch.empty(p.n, dtype=torch.float32).pin_memory()
+    dl_host = torch.empty(7, dtype=torch.float64).pin_memory()
+    ds_host = torch.empty((len(p.sub), 4), dtype=torch.float64).pin_memory()
+    sc_host = torch.empty(2, dtype=torch.float64).pin_memory()
+    v_d, g_d, sub_d = torch.empty_like(v), torch.empty_like(g), torch.empty_like(sub)
+    qe = api.Points(grid=p.xgrid, lens=p.lens, sub=sub_d)
+    copy_stream = torch.cuda.Stream(device=dev)
+    ev_start, ev_g, ev_out, ev_out_done = (torch.cuda.Event() for _ in range(4))
+
+    def e2e_step():
+        # dL/dout (needed only by the backward) comes in on a second stream
+        # during the forward; out goes back during the backward
+        cur = torch.cuda.current_stream()
+        ev_start.record(cur)
+        v_d.copy_(v_host, non_blocking=True)
+        sub_d.copy_(sub_host, non_blocking=True)
+        with torch.cuda.stream(copy_stream):
+            copy_stream.wait_event(ev_start)
+            g_d.copy_(g_host, non_blocking=True)
+            ev_g.record(copy_stream)
+        api.gp_kernel_matvec(qe, None, v_d, p.lengthscale, p.variance, out=out, beta=beta_buf, workspace=ws)
+        ev_out.record(cur)
+        with torch.cuda.stream(copy_stream):
+            copy_stream.wait_event(ev_out)
+            out_host.copy_(out, non_blocking=True)
+            ev_out_done.record(copy_stream)
+        cur.wait_event(ev_g)
+        G = api.gp_kernel_matvec_bwd(qe, None, v_d, p.lengthscale, p.variance, g_d, want=want, workspace=bws,
+                                     beta=beta_buf)
+        dv_host.copy_(G["v"], non_blocking=True)
+        dl_host.copy_(G["lens"], non_blocking=True)
+        ds_host.copy_(G["sub"], non_blocking=True)
+        sc_host[0:1].copy_(G["lengthscale"], non_blocking=True)
+        sc_host[1:2].copy_(G["variance"], non_blocking=True)
+        cur.wait_event(ev_out_done)
+
+    for _ in range(3):
+        e2e_step()
+    torch.cuda.synchronize()
+    n_e2e = max(5, min(args.steps, 50))
+    e_direct_ms = replicas.max_over_ranks(event_time(e2e_step, n_e2e, stream, flush), dev)
+    run_e2e = e2e_step
+    if not args.no_graph:
+        e2e_graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(e2e_graph):
+            e2e_step()
+        torch.cuda.synchronize()
+        for _ in range(2):
+            e2e_graph.replay()
+        torch.cuda.synchronize()
+        run_e2e = e2e_graph.replay
+    e_ms = replicas.max_over_ranks(event_time(run_e2e, n_e2e, stream, flush), dev) if not args.no_graph else e_direct_ms
+    e2e_val = replicas.aggregate_rate(p.pairs, e_ms * 1e-3, world) / 1e9
+    h2d = (v_host.numel() + g_host.numel() + sub_host.numel()) * 4
+    d2h = out_host.numel() * 4 + dv_host.numel() * 4 + (dl_host.numel() + ds_host.numel() + 2) * 8
+
+    rates = api.probe_pipe_rates(local)
+    sm_mhz = clk["sm_mhz"] or SM_MAX_MHZ_DEFAULT
+    sm_max = clk["sm_max_mhz"] or SM_MAX_MHZ_DEFAULT
+    nsm, ex2, fma = rates["sm_count"], rates["ex2_per_clk"], rates["ffma2_lanes_per_clk"]
+    table = {}
+    for name, (kms, call_ms, pairs, mufu, lanes, note, in_step) in kern.items():
+        per_clk = min(ex2 / mufu, fma / lanes)
+        peak = per_clk * nsm * sm_max * 1e6 / 1e9
+        ach = pairs / (kms * 1e-3) / 1e9
+        table[name] = {"ms": kms, "call_ms": call_ms, "achieved": ach, "peak": peak, "frac": ach / peak,
+                       "per_sm_clk": per_clk, "pairs_evaluated": pairs,
+                       "pairs_logical": p.pairs if "raytrace" not in name else pairs, "note": note,
+                       "in_step": in_step,
+                       "timing": "kernel alone (launch-timer events around its launches); call_ms: the whole "
+                                 "entry point"}
+    dom = max((k for k in table if table[k]["in_step"]), key=lambda k: table[k]["ms"])
+    d = table[dom]
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded; see workloads.py)",
+        "config": dict(large_config(p), parallelism=f"independent lens system per GPU x{world}"),
+        "pass": "forward + backward: ray-trace fused into the forward call, the culled self-kernel forward, "
+                "the culled self-kernel backward (d_v, dL/dbeta of both roles, d_lengthscale, d_variance) and "
+                "the ray-trace backward (7 lens parameters, 2000x4 subhalo parameters)",
+        "fwd": {"ms": fwd_ms, "value": replicas.aggregate_rate(p.pairs, fwd_ms * 1e-3, world) / 1e9, "unit": UNIT,
+                "note": "forward alone: ray-trace + self-kernel reduction"},
+        "bwd": {"ms": bwd_ms},
+        "pairs": {"logical_per_step": p.pairs, "evaluated_forward": pf, "evaluated_backward": pb,
+                  "slots_forward": sf, "slots_backward": sb,
+                  "note": "value counts every logical (i, j) pair, as the metric defines it; the culled sweeps "
+                          "leave out the pairs whose FP32 exp2 flushes to exactly 0 (scaled distance^2 > 170), so "
+                          "results are bitwise those of evaluating all of them (tested); the roofline counts the "
+                          "evaluated pairs"},
+        "roofline": {"bound": "alu", "achieved": d["achieved"], "peak": d["peak"], "unit": UNIT,
+                     "frac": d["frac"], "traffic": measured_traffic(dom), "kernel": dom,
+                     "peak_basis": f"min(MUFU {ex2:.2f}/clk/SM / MUFU per pair, FFMA2 {fma:.1f} lanes/clk/SM / lanes "
+                                   f"per pair) x {nsm} SMs x {sm_max:.0f} MHz (max clock; probe-measured rates); "
+                                   f"{d['note']}",
+                     "frac_at_measured_clock": d["frac"] * sm_max / sm_mhz},
+        "kernels": table,
+        "step_breakdown_ms": breakdown,
+        "raytrace": {"ms": rt_ms, "vjp_ms": vjp_ms, "points": p.n, "subhalo_pairs": sub_pairs,
+                     "hbm_gbs": p.n * 8 / (rt_ms * 1e-3) / 1e9,
+                     "note": "ALU/XU-bound with subhalos (8 B written per point)"},
+        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "ms_per_step": e_ms, "ms_per_step_direct_launches": e_direct_ms,
                 "launch": ("CUDA graph of the step with its 3 host-to-device and 6 device-to-host copies, replayed"
-                           if not args.no_graph else "direct launches"),
-                "copies": "dL/dout copied in during the forward and out copied back during the backward, on a "
-                          "second stream; the rest on the step's stream"},
-        "gpu_launches": 11 * args.steps,
-        "launch": "CUDA graph of the step's 11 launches, replayed" if not args.no_graph else "direct launches",
+                           if not args.no_graph else "direct launches")},
+        "gpu_launches": LARGE_STEP_LAUNCHES * args.steps,
+        "launch": (f"CUDA graph of the step's {LARGE_STEP_LAUNCHES} launches, replayed" if not args.no_graph
+                   else "direct launches"),
         "clocks": clk,
         "pipe_rates": rates,
     }
-    if not args.no_extensions:
-        line["extensions"] = run_extensions(p, dev, rates, sm_max, flush, stream)
-    if world == 1 and not args.no_serving:
-        line["serving"] = run_serving(args.serving_requests, args.serving_iters)
-        line["p50_latency_s"] = line["serving"]["batched"]["p50_s"]
-        line["p99_latency_s"] = line["serving"]["batched"]["p99_s"]
-    if world == 1 and not args.no_cpu_baseline:
-        cb = cpu_sample(p, args.cpu_seconds, g_np.astype(np.float64))
-        cb.pop("seconds", None)
-        line["cpu_baseline"] = cb
+    return line, rates, clk, p, g_np
+
+
+# Kernels of one headline step: forward = ray-trace, chunk prepare, group
+# boxes, culled sweep; backward = chunk prepare, group boxes, culled sweep,
+# scalar sum, ray-trace VJP and its final sums.
+LARGE_STEP_LAUNCHES = 10
+
+
+def run_ours(args):
+    import torch
+
+    from paper_2105_09465_gb300 import replicas
+
+    rank, local, world = replicas.world()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    line, rates, clk, p, g_np = run_large(args, rank, local, world, dist, dev)
+    if rank != 0:
+        if dist:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+    if world == 1:
+        line["realistic"] = run_realistic(args, dev, rates, clk)
+        flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+        sm_max = clk["sm_max_mhz"] or SM_MAX_MHZ_DEFAULT
+        if not args.no_extensions:
+            from paper_2105_09465_gb300 import workloads as W
+            line["extensions"] = run_extensions(W.realistic(), dev, rates, sm_max, flush,
+                                                torch.cuda.current_stream())
+        if not args.no_serving:
+            line["serving"] = run_serving(args.serving_requests, args.serving_iters)
+            line["p50_latency_s"] = line["serving"]["batched"]["p50_s"]
+            line["p99_latency_s"] = line["serving"]["batched"]["p99_s"]
+        if not args.no_cpu_baseline:
+            cb = cpu_sample_large(p, args.cpu_seconds, g_np.astype(np.float64))
+            cb.pop("seconds", None)
+            line["cpu_baseline"] = cb
     print(json.dumps(line))
     if dist:
         dist.barrier()

@@ -403,6 +403,19 @@ lr_status gp_partial_mvn_vjp(const float* L, const float* sd, const float* eps, 
 lr_status lr_grid_pairs_evaluated(const float* x, int64_t n, const lr_grid* query_grid, const lr_grid* source_grid,
                                   float lengthscale, int32_t rows_per_cta, int64_t* pairs, lr_stream stream);
 
+/*
+ * Diagnostic: the pairs the culled sweeps over explicit, ray-traced or self
+ * sources evaluate for these point sets and this length scale; sweep 0 is the
+ * forward (gp_kernel_matvec), 1 the backward (gp_kernel_matvec_bwd, whose row
+ * blocks are smaller). *pairs counts valid (query, source) pairs; *slots
+ * (may be NULL) the pair slots the kernels compute, padding rows of a row
+ * block and empty slots of a source chunk included. Pairs left out are those
+ * whose FP32 exp2 flushes to exactly 0. Synchronises the stream; allocates
+ * and frees its own temporary device memory.
+ */
+lr_status lr_cull_pairs_evaluated(const lr_points* query, const lr_points* source, float lengthscale, int32_t sweep,
+                                  int64_t* pairs, int64_t* slots, lr_stream stream);
+
 /* Scratch bytes gp_kernel_matvec needs for these point sets on the current device. */
 lr_status lr_matvec_workspace_size(const lr_points* query, const lr_points* source, int32_t nrhs, size_t* bytes);
 

@@ -88,6 +88,9 @@ SIGNATURES = {
     "lr_kernel_timer_enable": (ctypes.c_int32, [ctypes.c_int32]),
     "lr_kernel_timer_read": (ctypes.c_int32, [ctypes.c_int32, _P, _P, _P]),
     "lr_set_pair_culling": (ctypes.c_int32, [ctypes.c_int32]),
+    "lr_cull_pairs_evaluated": (ctypes.c_int32, [ctypes.POINTER(lr_points), ctypes.POINTER(lr_points), ctypes.c_float,
+                                                 ctypes.c_int32, ctypes.POINTER(ctypes.c_int64),
+                                                 ctypes.POINTER(ctypes.c_int64), _P]),
     "lens_raytrace": (ctypes.c_int32, [ctypes.POINTER(lr_points), _P, _P, _P]),
     "lens_jacobian": (ctypes.c_int32, [ctypes.POINTER(lr_points), _P, _P, _P]),
     "gp_kernel_matvec": (ctypes.c_int32, [ctypes.POINTER(lr_points), ctypes.POINTER(lr_points), _P, ctypes.c_int32,

@@ -488,6 +488,43 @@ def gp_kernel_matvec_bwd(query: Points, source: Points | None, v: torch.Tensor, 
     return out
 
 
+def cull_pairs_evaluated(query: Points, source: Points | None, lengthscale: float, sweep: int = 0,
+                         stream=None) -> tuple[int, int]:
+    """(valid pairs, pair slots) the culled sweeps over explicit or self
+    sources evaluate; sweep 0 = forward, 1 = backward."""
+    lib = abi.load()
+    cq, k1 = to_c_points(query)
+    cs, k2 = to_c_points(source)
+    pr, sl = ctypes.c_int64(0), ctypes.c_int64(0)
+    abi.check(lib.lr_cull_pairs_evaluated(ctypes.byref(cq), ctypes.byref(cs) if cs is not None else None,
+                                          float(lengthscale), int(sweep), ctypes.byref(pr), ctypes.byref(sl),
+                                          _stream_handle(stream)), "lr_cull_pairs_evaluated")
+    return int(pr.value), int(sl.value)
+
+
+def matvec_bwd_workspace_size(query: Points, source: Points | None, want=("v", "x", "lengthscale", "variance"),
+                              beta: bool = False, moments: bool = False, nrhs: int = 1) -> int:
+    """Workspace bytes gp_kernel_matvec_bwd needs for these point sets, the
+    requested gradients (`want`, as in gp_kernel_matvec_bwd) and whether the
+    forward's points (`beta`) and row moments (`moments`) are passed. The
+    size depends only on which pointers are set: one small real device buffer
+    stands for all of them."""
+    lib = abi.load()
+    cq, k1 = to_c_points(query)
+    cs, k2 = to_c_points(source)
+    stand_in = torch.empty(64, dtype=torch.float64, device="cuda").data_ptr()
+    gr = abi.lr_grads()
+    for key, field in (("v", "d_v"), ("x", "d_x"), ("y", "d_y"), ("lengthscale", "d_lengthscale"),
+                       ("variance", "d_variance"), ("lens", "d_lens"), ("sub", "d_sub")):
+        setattr(gr, field, stand_in if key in want else None)
+    gr.beta_in = stand_in if beta else None
+    gr.moments_in = stand_in if moments else None
+    b = ctypes.c_size_t(0)
+    abi.check(lib.lr_matvec_bwd_workspace_size(ctypes.byref(cq), ctypes.byref(cs) if cs is not None else None, nrhs,
+                                               ctypes.byref(gr), ctypes.byref(b)), "lr_matvec_bwd_workspace_size")
+    return int(b.value)
+
+
 def lens_raytrace_vjp(pts: Points, d_beta: torch.Tensor, stream=None):
     """(d_lens[7], d_sub[S, 4]) float64 for Loss with dL/dbeta = d_beta."""
     lib = abi.load()

@@ -75,9 +75,10 @@ __global__ void __launch_bounds__(256) cull_prep_kernel(const __grid_constant__ 
     if (lane == 0) *reinterpret_cast<float4*>(rec) = box;
     return;
   }
+  const int n_valid = __popc(__ballot_sync(0xffffffffu, valid));
   if (lane == 0) {
     *reinterpret_cast<float4*>(rec) = box;
-    *reinterpret_cast<float4*>(rec + 16) = make_float4(0.f, 0.f, 0.f, 0.f);
+    *reinterpret_cast<float4*>(rec + 16) = make_float4((float)n_valid, 0.f, 0.f, 0.f);
   }
   // (xa, xb, ya, yb) per source pair: absolute positions, so that the
   // kernels form x_j - x_i directly (correctly rounded: relative error u)
@@ -241,6 +242,9 @@ __global__ void __launch_bounds__(kCullThreads) cull_kernel(const __grid_constan
     if (irow[r] >= 0) mybox = box_merge(mybox, make_float4(p.x, p.y, p.x, p.y));
   }
   const float4 wb = warp_box(mybox);
+  int warp_rows = 0;
+#pragma unroll
+  for (int r = 0; r < R; ++r) warp_rows += __popc(__ballot_sync(0xffffffffu, irow[r] >= 0));
   float2 NQ[R], NP[R];
 #pragma unroll
   for (int r = 0; r < R; ++r) {
@@ -327,6 +331,11 @@ __global__ void __launch_bounds__(kCullThreads) cull_kernel(const __grid_constan
         const char* rec = bb + k * RB;
         const float4 box = *reinterpret_cast<const float4*>(rec);
         if (cull && boxes_far(wb, box, A.sc)) continue;  // warp-uniform
+        if (A.count && lane == 0) {
+          const float nv = reinterpret_cast<const float4*>(rec + 16)->x;
+          atomicAdd(A.count, (unsigned long long)(warp_rows * (int)nv));
+          atomicAdd(A.count + 1, (unsigned long long)(32 * R * kChunkPts));
+        }
         const float4* xy = reinterpret_cast<const float4*>(rec + kRecHead);
         const float2* wt = reinterpret_cast<const float2*>(rec + kRecHead + kRecXY);
         if (KIND == kCullOut) {
@@ -407,7 +416,7 @@ __global__ void __launch_bounds__(kCullThreads) cull_kernel(const __grid_constan
       __syncthreads();  // the buffer is refilled two batches on
     }
   }
-  if (failed) return;
+  if (failed || A.count) return;
 
   // ---- outputs
   float sl = 0.f, sv = 0.f;
@@ -581,7 +590,7 @@ static lr_status launch_sweep_t(const CullPlan& P, const CullArgs& A, cudaStream
   const unsigned grid = (unsigned)(P.row_blocks * P.splits);
   cull_kernel<KIND, NW><<<grid, kCullThreads, 0, s>>>(A);
   LR_CHECK_CUDA(cudaGetLastError());
-  if (P.splits > 1) {
+  if (P.splits > 1 && !A.count) {
     cull_merge_kernel<KIND, CullTraits<KIND, NW>::K><<<(unsigned)((A.n + 255) / 256), 256, 0, s>>>(A);
     LR_CHECK_CUDA(cudaGetLastError());
   }
@@ -632,4 +641,85 @@ lr_status launch_cull_scalar_final(const double* part, int64_t nblk, double* d_l
 extern "C" lr_status lr_set_pair_culling(int32_t enable) {
   lr::g_pair_culling.store(enable ? 1 : 0, std::memory_order_relaxed);
   return LR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Diagnostic: pairs the culled sweeps evaluate.
+using namespace lr;
+
+extern "C" lr_status lr_cull_pairs_evaluated(const lr_points* query, const lr_points* source, float lengthscale,
+                                             int32_t sweep, int64_t* pairs, int64_t* slots, lr_stream stream) {
+  lr_status st = validate_points(query, "lr_cull_pairs_evaluated(query)", false);
+  if (st != LR_OK) return st;
+  if (source) {
+    st = validate_points(source, "lr_cull_pairs_evaluated(source)", false);
+    if (st != LR_OK) return st;
+    LR_REQUIRE(source->xy != nullptr || source->lens != nullptr,
+               "lr_cull_pairs_evaluated: grid sources take the grid sweeps (lr_grid_pairs_evaluated)");
+  }
+  LR_REQUIRE(pairs != nullptr, "lr_cull_pairs_evaluated: pairs is NULL");
+  LR_REQUIRE(sweep == 0 || sweep == 1, "lr_cull_pairs_evaluated: sweep = %d (0 forward, 1 backward)", sweep);
+  LR_REQUIRE(isfinite(lengthscale) && lengthscale > 0.f, "lr_cull_pairs_evaluated: lengthscale must be > 0");
+  cudaStream_t s = as_cuda(stream);
+  const bool self = source == nullptr;
+  const int64_t n = query->n, m = self ? n : source->n;
+  *pairs = 0;
+  if (slots) *slots = 0;
+  if (n == 0 || m == 0) return LR_OK;
+  const lr_grid* ql = query_layout(query);
+  const lr_grid* sl = self ? ql : query_layout(source);
+  const int kind = sweep == 0 ? kCullOut : (self ? kCullSelf : kCullMom);
+  CullPlan P;
+  st = plan_cull(kind, 1, n, ql, m, sl, &P);
+  if (st != LR_OK) return st;
+  // temporaries: points, zero weights, workspace, counters
+  const size_t b_q = align256(8 * (size_t)n), b_s = align256(8 * (size_t)m), b_w = align256(4 * (size_t)m);
+  char* buf = nullptr;
+  LR_CHECK_CUDA(cudaMalloc(&buf, b_q + b_s + b_w + P.bytes + 256));
+  auto done = [&](lr_status r) {
+    cudaFree(buf);
+    return r;
+  };
+  float2* xq = reinterpret_cast<float2*>(buf);
+  float2* ys = reinterpret_cast<float2*>(buf + b_q);
+  float* w = reinterpret_cast<float*>(buf + b_q + b_s);
+  char* ws = buf + b_q + b_s + b_w;
+  unsigned long long* cnt = reinterpret_cast<unsigned long long*>(ws + P.bytes);
+  if (query->lens)
+    st = launch_raytrace(query, xq, nullptr, s);
+  else if (query->xy == nullptr)
+    st = launch_grid_points(query->grid, xq, s);
+  else if (cudaMemcpyAsync(xq, query->xy, 8 * (size_t)n, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+    st = cuda_status(cudaGetLastError(), "cudaMemcpyAsync");
+  if (st != LR_OK) return done(st);
+  const float2* src = xq;
+  if (!self) {
+    if (source->lens)
+      st = launch_raytrace(source, ys, nullptr, s);
+    else if (cudaMemcpyAsync(ys, source->xy, 8 * (size_t)m, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+      st = cuda_status(cudaGetLastError(), "cudaMemcpyAsync");
+    if (st != LR_OK) return done(st);
+    src = ys;
+  }
+  if (cudaMemsetAsync(w, 0, 4 * (size_t)m, s) != cudaSuccess || cudaMemsetAsync(cnt, 0, 16, s) != cudaSuccess)
+    return done(cuda_status(cudaGetLastError(), "cudaMemsetAsync"));
+  const double c = 1.4426950408889634 / (2.0 * (double)lengthscale * (double)lengthscale);
+  st = launch_cull_prep(P, src, (float)sqrt(c), w, w, 1, 0, ws, s);
+  if (st != LR_OK) return done(st);
+  CullArgs A{};
+  A.x = xq;
+  A.n = n;
+  A.sc = (float)sqrt(c);
+  A.c = (float)c;
+  A.nrhs = 1;
+  A.stride = 1;
+  A.count = cnt;
+  st = launch_cull_sweep(P, A, ws, -1, s);
+  if (st != LR_OK) return done(st);
+  unsigned long long h[2] = {0, 0};
+  if (cudaMemcpyAsync(h, cnt, 16, cudaMemcpyDeviceToHost, s) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess)
+    return done(cuda_status(cudaGetLastError(), "lr_cull_pairs_evaluated"));
+  *pairs = (int64_t)h[0];
+  if (slots) *slots = (int64_t)h[1];
+  return done(LR_OK);
 }

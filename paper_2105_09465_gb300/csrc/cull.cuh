@@ -154,6 +154,8 @@ struct CullArgs {
   double* scal_part; // [partial blocks][2]: d_l, d_var partials
   float* partial;    // splits > 1: [splits][K][n]
   int* fault;        // device fault word (a bulk-copy wait that ran out)
+  unsigned long long* count;  // diagnostic: [0] valid pairs, [1] pair slots evaluated
+                              // (non-NULL: count only, no outputs written)
 };
 
 // Plan of one culled sweep: source chunks, query row blocks, group ranges per

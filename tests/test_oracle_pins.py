@@ -428,6 +428,9 @@ def test_self_vjp_rows_sensitivities_match_full(orc):
     F = orc.kernel_matvec_vjp(x, x, v, 0.05, 1.0, g, True, with_abs=True)
     rows = np.arange(0, 50, 7)
     R = orc.self_vjp_rows(x, v, g, 0.05, 1.0, rows)
+    out, ab = orc.kernel_matvec(x, x, v, 0.05, 1.0)
+    np.testing.assert_allclose(R["out"], out[rows], rtol=1e-12, atol=1e-14)
+    np.testing.assert_allclose(R["out_abs"], ab[rows], rtol=1e-12)
     for k in ("d_v", "d_x"):
         np.testing.assert_allclose(R[k], F[k][rows], rtol=1e-12, atol=1e-14)
         np.testing.assert_allclose(R[k + "_abs"], F[k + "_abs"][rows], rtol=1e-12)
