@@ -88,6 +88,8 @@ def parse():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-extensions", action="store_true", help="skip timing the kernels beyond the fused step")
     ap.add_argument("--no-graph", action="store_true", help="launch the step's kernels directly, not from a CUDA graph")
+    ap.add_argument("--profile", action="store_true",
+                    help="headline step only, direct launches: W warm-up and K timed steps, then exit (profiler runs)")
     ap.add_argument("--serving-requests", type=int, default=32)
     ap.add_argument("--serving-iters", type=int, default=50)
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="target oracle CPU time for cpu_baseline")
@@ -261,15 +263,28 @@ class LargeOracleSampler:
                 f"extrapolated to all {self.p.n} rows")
 
 
-def cpu_sample_large(p, seconds: float, g=None) -> dict:
+def cpu_sample_large(p, seconds: float, g=None, one_core_seconds: float = 0.0) -> dict:
+    """Oracle throughput on a bounded sample (about `seconds` of CPU work) on
+    all host cores, and, with one_core_seconds > 0, on one core."""
     S = LargeOracleSampler(p, g)
     k = S.rows_for(seconds)
     total, done = 0.0, 0
     while total < 0.8 * seconds and done < p.n:
         total += S.step(k)
         done += k
-    return {"value": done * p.n / total / 1e9, "unit": UNIT, "cores": S.oracle.num_threads(), "kind": "oracle",
-            "sample": S.describe(done, total), "seconds": total}
+    out = {"value": done * p.n / total / 1e9, "unit": UNIT, "cores": S.oracle.num_threads(), "kind": "oracle",
+           "sample": S.describe(done, total), "seconds": total}
+    if one_core_seconds > 0:
+        cores = S.oracle.num_threads()
+        S.oracle.set_num_threads(1)
+        try:
+            k1 = S.rows_for(one_core_seconds)
+            t1 = S.step(k1)
+        finally:
+            S.oracle.set_num_threads(cores)
+        out["one_core"] = {"value": k1 * p.n / t1 / 1e9, "unit": UNIT, "cores": 1,
+                           "sample": S.describe(k1, t1)}
+    return out
 
 
 def cpu_sample(p, seconds: float, g=None) -> dict:
@@ -767,7 +782,7 @@ def run_realistic(args, dev, rates, clk) -> dict:
                           "FP32 exp2 flushes to exactly 0 (scaled distance^2 > 170), so results are identical to "
                           "evaluating all of them; the roofline counts evaluated pairs"},
         "roofline": {"bound": "alu", "achieved": d["achieved"], "peak": d["peak"], "unit": UNIT,
-                     "frac": d["frac"], "traffic": measured_traffic(dom), "kernel": dom,
+                     "frac": d["frac"], "traffic": measured_traffic("realistic: " + dom), "kernel": dom,
                      "peak_basis": f"min(MUFU {ex2:.2f}/clk/SM / MUFU per pair, FFMA2 {fma:.1f} lanes/clk/SM / lanes "
                                    f"per pair) x {nsm} SMs x {sm_max:.0f} MHz (max clock; probe-measured rates); "
                                    f"{d['note']}"},
@@ -818,6 +833,19 @@ def run_large(args, rank, local, world, dist, dev):
         fwd()
         bwd()
 
+    if args.profile:
+        # the launch sequence a profiler sees: W warm-up steps, K timed steps
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return {"profile": True, "ms_per_step": e0.elapsed_time(e1) / max(args.steps, 1),
+                "launches_per_step": LARGE_STEP_LAUNCHES}, None, None, p, g_np
     for _ in range(max(3, args.warmup)):
         step()
     torch.cuda.synchronize()
@@ -996,7 +1024,7 @@ def run_large(args, rank, local, world, dist, dev):
                           "results are bitwise those of evaluating all of them (tested); the roofline counts the "
                           "evaluated pairs"},
         "roofline": {"bound": "alu", "achieved": d["achieved"], "peak": d["peak"], "unit": UNIT,
-                     "frac": d["frac"], "traffic": measured_traffic(dom), "kernel": dom,
+                     "frac": d["frac"], "traffic": measured_traffic("large: " + dom), "kernel": dom,
                      "peak_basis": f"min(MUFU {ex2:.2f}/clk/SM / MUFU per pair, FFMA2 {fma:.1f} lanes/clk/SM / lanes "
                                    f"per pair) x {nsm} SMs x {sm_max:.0f} MHz (max clock; probe-measured rates); "
                                    f"{d['note']}",
@@ -1038,6 +1066,12 @@ def run_ours(args):
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local)
     line, rates, clk, p, g_np = run_large(args, rank, local, world, dist, dev)
+    if args.profile:
+        if rank == 0:
+            print(json.dumps(line))
+        if dist:
+            dist.destroy_process_group()
+        return
     if rank != 0:
         if dist:
             dist.barrier()
@@ -1056,7 +1090,7 @@ def run_ours(args):
             line["p50_latency_s"] = line["serving"]["batched"]["p50_s"]
             line["p99_latency_s"] = line["serving"]["batched"]["p99_s"]
         if not args.no_cpu_baseline:
-            cb = cpu_sample_large(p, args.cpu_seconds, g_np.astype(np.float64))
+            cb = cpu_sample_large(p, args.cpu_seconds, g_np.astype(np.float64), one_core_seconds=args.cpu_seconds / 2)
             cb.pop("seconds", None)
             line["cpu_baseline"] = cb
     print(json.dumps(line))

@@ -69,6 +69,18 @@ lr_status lr_probe_pipe_rates(int32_t device, double* ffma_lanes_per_clk,
 lr_status lr_fault_status(int32_t* code, int32_t clear);
 
 /*
+ * Self-test of the bounded waits (no paper counterpart): launches one thread
+ * that arms an mbarrier for a bulk-copy transaction that never comes and
+ * waits for it with a budget of `budget_cycles` SM clocks (0 < budget <= 2e9).
+ * The wait runs out, the kernel records kFaultBarrierTimeout (1) in the
+ * fault word (read it with lr_fault_status) and returns; *code = 1 says it
+ * returned after giving up (2 would mean the wait completed). Nothing is in
+ * flight when it gives up, so the context stays usable. Synchronous;
+ * allocates 4 bytes of device memory.
+ */
+lr_status lr_selftest_bounded_wait(int64_t budget_cycles, int32_t* code);
+
+/*
  * Launch timer: device time of the library's pair-sweep kernels alone,
  * without the pre-pass and merge launches of the same entry point (the
  * denominator of a per-kernel roofline). lr_kernel_timer_enable(1) makes the

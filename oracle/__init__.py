@@ -86,8 +86,9 @@ def lib():
         L.orc_pixel_shapes_vjp.argtypes = [_P, _I32, _I32, _P, _P]
         L.orc_kernel_matvec.argtypes = [_P, _I64, _P, _I64, _P, _D, _D, _P, _I64, _P, _P, _P]
         L.orc_kernel_matvec_vjp.argtypes = [_P, _I64, _P, _I64, _P, _D, _D, _P, _I32, _P, _P, _P, _P, _P, _P]
-        L.orc_self_vjp_rows.argtypes = [_P, _I64, _P, _P, _D, _D, _P, _I64] + [_P] * 6
+        L.orc_self_vjp_rows.argtypes = [_P, _I64, _P, _P, _D, _D, _P, _I64] + [_P] * 8
         L.orc_num_threads.restype = _I32
+        L.orc_set_num_threads.argtypes = [_I32]
         _lib = L
     return _lib
 
@@ -120,6 +121,11 @@ def _subs(sub):
 
 def num_threads() -> int:
     return int(lib().orc_num_threads())
+
+
+def set_num_threads(n: int) -> None:
+    """Threads of the oracle's parallel loops from now on."""
+    lib().orc_set_num_threads(int(n))
 
 
 def grid_points(nx, ny, ss, pix, cx=0.0, cy=0.0) -> np.ndarray:
@@ -306,17 +312,18 @@ def kernel_matvec_vjp(x, y, v, lengthscale, variance, g, self_kernel=False, with
 
 
 def self_vjp_rows(x, v, g, lengthscale, variance, rows):
-    """Self-kernel gradients on the listed rows only: dict with d_v (r,), d_x
-    (r, 2) (both roles of each listed point), their *_abs scales and *_sens
-    input-error sensitivities (as kernel_matvec_vjp)."""
+    """Self-kernel reduction and gradients on the listed rows only: dict with
+    out (r,) and its out_abs scale, d_v (r,), d_x (r, 2) (both roles of each
+    listed point), their *_abs scales and *_sens input-error sensitivities
+    (as kernel_matvec_vjp)."""
     x = _pairs(x)
     v = np.ascontiguousarray(v, dtype=np.float64).reshape(-1)
     g = np.ascontiguousarray(g, dtype=np.float64).reshape(-1)
     rows = np.ascontiguousarray(rows, dtype=np.int64)
     assert rows.size == 0 or (rows.min() >= 0 and rows.max() < x.shape[0])
     k = rows.shape[0]
-    R = {"d_v": np.empty(k), "d_x": np.empty((k, 2)), "d_v_abs": np.empty(k), "d_x_abs": np.empty((k, 2)),
-         "d_v_sens": np.empty(k), "d_x_sens": np.empty((k, 2))}
+    keys = ("out", "out_abs", "d_v", "d_x", "d_v_abs", "d_x_abs", "d_v_sens", "d_x_sens")
+    R = {key: np.empty((k, 2) if key.startswith("d_x") else k) for key in keys}
     lib().orc_self_vjp_rows(_ptr(x), x.shape[0], _ptr(v), _ptr(g), lengthscale, variance, _ptr(rows), k,
-                            *[_ptr(R[key]) for key in ("d_v", "d_x", "d_v_abs", "d_x_abs", "d_v_sens", "d_x_sens")])
+                            *[_ptr(R[key]) for key in keys])
     return R

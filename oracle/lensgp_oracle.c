@@ -59,6 +59,12 @@ static inline void ns_add(nsum* a, double x) {
 }
 static inline double ns_val(const nsum* a) { return a->s + a->c; }
 
+/* exp(-a) is exactly 0.0 in FP64 once a > 745.14 (below the smallest
+ * subnormal); a pair whose kernel exponent is past EXP_ZERO therefore adds
+ * exactly nothing to any sum below (a Neumaier sum is unchanged by adding
+ * +0 or -0), and the loops skip it without changing a single result bit. */
+#define EXP_ZERO 750.0
+
 /* ------------------------------------------------------------------------ */
 /* Forward-mode dual numbers: value plus derivatives with respect to up to
  * ND parameters. Used for the analytic parameter gradients of the ray-trace. */
@@ -469,6 +475,7 @@ static void matvec_row(const double* x, int64_t i, const double* y, int64_t m, c
   for (int64_t j = 0; j < m; ++j) {
     const double dx = xi - y[2 * j], dy = yi - y[2 * j + 1];
     const double d2 = dx * dx + dy * dy;
+    if (d2 * inv2l2 > EXP_ZERO) continue;
     const double kv = variance * exp(-d2 * inv2l2) * v[j];
     ns_add(&s, kv);
     ns_add(&a, fabs(kv));
@@ -744,7 +751,9 @@ ORC_API void orc_kernel_matvec_vjp(const double* x, int64_t n, const double* y, 
       nsum ex = {0, 0}, ey = {0, 0}, el = {0, 0}, ev = {0, 0};
       for (int64_t j = 0; j < m; ++j) {
         const double dx = y[2 * j] - xi, dy = y[2 * j + 1] - yi;
-        const double d2 = dx * dx + dy * dy, d = sqrt(d2);
+        const double d2 = dx * dx + dy * dy;
+        if (d2 * inv2l2 > EXP_ZERO) continue;
+        const double d = sqrt(d2);
         const double kv = variance * exp(-d2 * inv2l2) * v[j];
         ns_add(&sx, kv * dx);
         ns_add(&sy, kv * dy);
@@ -809,7 +818,9 @@ ORC_API void orc_kernel_matvec_vjp(const double* x, int64_t n, const double* y, 
     nsum es = {0, 0}, ex = {0, 0}, ey = {0, 0};
     for (int64_t i = 0; i < n; ++i) {
       const double dx = x[2 * i] - yj, dy = x[2 * i + 1] - zj;
-      const double d2 = dx * dx + dy * dy, d = sqrt(d2);
+      const double d2 = dx * dx + dy * dy;
+      if (d2 * inv2l2 > EXP_ZERO) continue;
+      const double d = sqrt(d2);
       const double gk = g[i] * variance * exp(-d2 * inv2l2);
       ns_add(&s, gk);
       ns_add(&sx, gk * dx);
@@ -869,29 +880,34 @@ ORC_API void orc_kernel_matvec_vjp(const double* x, int64_t n, const double* y, 
  * the listed rows only, for sampled parity at sizes where the full n x n
  * sweep is out of reach. For each listed row i, with k_ij = var
  * exp(-|x_i - x_j|^2 / (2 l^2)) and d_ij = x_j - x_i:
+ *   out[r]  = sum_j k_ij v_j          (the forward reduction, with s_out = sum |k v|)
  *   d_v[r]  = sum_j k_ij g_j
  *   d_x[r]  = [g_i sum_j k_ij v_j d_ij + v_i sum_j k_ij g_j d_ij] / l^2
  * (the row role plus the column role of point i), the sums of absolute terms
  * (s_dv, s_dx) and the input-error sensitivities (e_dv, e_dx) defined as for
  * orc_kernel_matvec_vjp. Any output may be NULL. */
 ORC_API void orc_self_vjp_rows(const double* x, int64_t n, const double* v, const double* g, double lengthscale,
-                               double variance, const int64_t* rows, int64_t n_rows, double* d_v, double* d_x,
-                               double* s_dv, double* s_dx, double* e_dv, double* e_dx) {
+                               double variance, const int64_t* rows, int64_t n_rows, double* out, double* s_out,
+                               double* d_v, double* d_x, double* s_dv, double* s_dx, double* e_dv, double* e_dx) {
   const double l2 = lengthscale * lengthscale, inv2l2 = 1.0 / (2.0 * l2);
 #pragma omp parallel for schedule(dynamic, 4)
   for (int64_t r = 0; r < n_rows; ++r) {
     const int64_t i = rows[r];
     const double xi = x[2 * i], yi = x[2 * i + 1];
-    nsum kg = {0, 0}, akg = {0, 0}, ekg = {0, 0};
+    nsum kg = {0, 0}, akg = {0, 0}, ekg = {0, 0}, kvs = {0, 0}, akv = {0, 0};
     nsum rx = {0, 0}, ry = {0, 0}, cx = {0, 0}, cy = {0, 0};
     nsum arx = {0, 0}, ary = {0, 0}, acx = {0, 0}, acy = {0, 0};
     nsum erx = {0, 0}, ery = {0, 0}, ecx = {0, 0}, ecy = {0, 0};
     for (int64_t j = 0; j < n; ++j) {
       const double dx = x[2 * j] - xi, dy = x[2 * j + 1] - yi;
-      const double d2 = dx * dx + dy * dy, d = sqrt(d2);
+      const double d2 = dx * dx + dy * dy;
+      if (d2 * inv2l2 > EXP_ZERO) continue;
+      const double d = sqrt(d2);
       const double k = variance * exp(-d2 * inv2l2);
       const double kv = k * v[j], kgj = k * g[j];
       const double fx = 1.0 + d * fabs(dx) / l2, fy = 1.0 + d * fabs(dy) / l2;
+      ns_add(&kvs, kv);
+      ns_add(&akv, fabs(kv));
       ns_add(&kg, kgj);
       ns_add(&akg, fabs(kgj));
       ns_add(&ekg, fabs(kgj) * d / l2);
@@ -909,6 +925,8 @@ ORC_API void orc_self_vjp_rows(const double* x, int64_t n, const double* v, cons
       ns_add(&ecy, fabs(kgj) * fy);
     }
     const double gi = g[i], vi = v[i];
+    if (out) out[r] = ns_val(&kvs);
+    if (s_out) s_out[r] = ns_val(&akv);
     if (d_v) d_v[r] = ns_val(&kg);
     if (s_dv) s_dv[r] = ns_val(&akg);
     if (e_dv) e_dv[r] = ns_val(&ekg);
@@ -926,6 +944,10 @@ ORC_API void orc_self_vjp_rows(const double* x, int64_t n, const double* v, cons
     }
   }
 }
+
+/* Threads of the oracle's OpenMP loops from here on (the benchmark's
+ * one-core timing sets 1, then restores the default). */
+ORC_API void orc_set_num_threads(int32_t n) { omp_set_num_threads(n > 0 ? n : 1); }
 
 /* Number of OpenMP threads the oracle runs with (reported by the benchmark). */
 ORC_API int32_t orc_num_threads(void) {

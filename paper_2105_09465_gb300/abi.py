@@ -85,6 +85,7 @@ SIGNATURES = {
     "lr_status_name": (ctypes.c_char_p, [ctypes.c_int32]),
     "lr_probe_pipe_rates": (ctypes.c_int32, [ctypes.c_int32, _P, _P, _P, _P]),
     "lr_fault_status": (ctypes.c_int32, [_P, ctypes.c_int32]),
+    "lr_selftest_bounded_wait": (ctypes.c_int32, [ctypes.c_int64, ctypes.POINTER(ctypes.c_int32)]),
     "lr_kernel_timer_enable": (ctypes.c_int32, [ctypes.c_int32]),
     "lr_kernel_timer_read": (ctypes.c_int32, [ctypes.c_int32, _P, _P, _P]),
     "lr_set_pair_culling": (ctypes.c_int32, [ctypes.c_int32]),

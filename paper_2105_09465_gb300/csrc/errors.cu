@@ -3,6 +3,7 @@
 #include <stdarg.h>
 #include <string.h>
 #include "common.cuh"
+#include "tma.cuh"
 
 namespace lr {
 
@@ -70,4 +71,46 @@ extern "C" lr_status lr_fault_status(int32_t* code, int32_t clear) {
   *code = v;
   if (clear) LR_CHECK_CUDA(cudaMemset(p, 0, sizeof(int)));
   return LR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Self-test of the bounded wait: one thread arms an mbarrier for 16 bytes of
+// transactions that never come (no copy is issued), waits with the given
+// budget, and returns after recording the time-out. Nothing is in flight when
+// it gives up, so the context stays usable.
+namespace {
+
+__global__ void bounded_wait_selftest_kernel(long long budget, int* fault, int* returned) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x != 0) return;
+  lr::mbar_init(&bar, 1);
+  lr::mbar_expect_tx(&bar, 16);  // arrive, and expect 16 bytes that no copy delivers
+  const bool ok = lr::mbar_wait_bounded(&bar, 0, fault, budget);
+  *returned = ok ? 2 : 1;
+}
+
+}  // namespace
+
+extern "C" lr_status lr_selftest_bounded_wait(int64_t budget_cycles, int32_t* code) {
+  LR_REQUIRE(code != nullptr, "lr_selftest_bounded_wait: code is NULL");
+  LR_REQUIRE(budget_cycles > 0 && budget_cycles <= 2000000000LL,
+             "lr_selftest_bounded_wait: budget of %lld cycles outside (0, 2e9]", (long long)budget_cycles);
+  int* fault = lr::fault_ptr();
+  LR_REQUIRE(fault != nullptr, "could not resolve the device fault word");
+  int* ret = nullptr;
+  LR_CHECK_CUDA(cudaMalloc(&ret, sizeof(int)));
+  lr_status st = LR_OK;
+  int h = 0;
+  if (cudaMemset(ret, 0, sizeof(int)) != cudaSuccess) st = lr::cuda_status(cudaGetLastError(), "cudaMemset");
+  if (st == LR_OK) {
+    bounded_wait_selftest_kernel<<<1, 32>>>((long long)budget_cycles, fault, ret);
+    const cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) st = lr::cuda_status(e, "bounded_wait_selftest_kernel");
+  }
+  if (st == LR_OK && cudaMemcpy(&h, ret, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+    st = lr::cuda_status(cudaGetLastError(), "cudaMemcpy");
+  cudaFree(ret);
+  // 1: the kernel gave up the wait and returned; the fault word says why
+  *code = h;
+  return st;
 }

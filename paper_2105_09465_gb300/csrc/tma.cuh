@@ -48,13 +48,14 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return done != 0;
 }
 
-// Waits for phase `parity` of `bar` to complete, for at most
-// kWaitBudgetCycles; on time-out writes kFaultBarrierTimeout to *fault and
-// returns false.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, int* fault) {
+// Waits for phase `parity` of `bar` to complete, for at most `budget`
+// cycles (kWaitBudgetCycles by default); on time-out writes
+// kFaultBarrierTimeout to *fault and returns false.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, int* fault,
+                                                  long long budget = kWaitBudgetCycles) {
   const long long t0 = clock64();
   while (!mbar_try_wait(bar, parity)) {
-    if (clock64() - t0 > kWaitBudgetCycles) {
+    if (clock64() - t0 > budget) {
       if (fault) atomicExch(fault, kFaultBarrierTimeout);
       return false;
     }
