@@ -199,6 +199,14 @@ typedef struct {
 lr_status lens_raytrace(const lr_points* pts, float* beta_out, float* alpha_out, lr_stream stream);
 
 /*
+ * The FP32 points of a grid (the pixel centres P of Table 1, supersampled as
+ * lr_grid defines them) into out (device float[n][2], row-major). Exactly
+ * the points every entry point generates for a grid argument, e.g. for
+ * splitting an image's rows across GPUs.
+ */
+lr_status lr_grid_points(const lr_grid* grid, float* out, lr_stream stream);
+
+/*
  * Lens Jacobian and magnification (Sec. 2.1, lens-Jacobian and magnification
  * equations): for every point of `pts` (which must carry a lens),
  *   jac_out[i] = d beta / d xi = I - d alpha / d xi, row-major float[4]
@@ -457,6 +465,20 @@ lr_status lr_matvec_workspace_size(const lr_points* query, const lr_points* sour
  *                               scale (non-self sources only); when given the
  *                               row sums are not recomputed and only the
  *                               column sums for d_v (and d_y) sweep the pairs
+ * and a mode for a self-kernel split by rows (one rank's share of the pairs
+ * when the rows are partitioned across GPUs):
+ *   source_rows    nonzero: the query points are the points
+ *                  [row0, row0 + n) of the explicit source set, i.e. rows
+ *                  of the self-kernel of the sources. g_out and v then cover
+ *                  the whole source set ([m][nrhs]); d_x receives both roles
+ *                  of the query points (as for a self-kernel), d_v the
+ *                  query rows only ([n][nrhs]: d_v_i = var sum_j k_ij g_j),
+ *                  and d_lengthscale, d_variance the query rows' share.
+ *                  Summing the shares of a partition of the rows (and
+ *                  gathering the rows' d_v, d_x) gives the whole
+ *                  self-kernel's gradients; the query's lens gradients are
+ *                  the query rows' share too. Not with moments_in or d_y.
+ *   row0           first row of the query in the source set
  */
 typedef struct {
   float* d_v;
@@ -468,6 +490,9 @@ typedef struct {
   double* d_sub;
   const float* beta_in;
   const float* moments_in;
+  int32_t source_rows;
+  int32_t reserved;
+  int64_t row0;
 } lr_grads;
 
 /*

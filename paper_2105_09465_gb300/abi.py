@@ -50,7 +50,8 @@ class lr_grads(ctypes.Structure):
     _fields_ = [("d_v", ctypes.c_void_p), ("d_x", ctypes.c_void_p), ("d_y", ctypes.c_void_p),
                 ("d_lengthscale", ctypes.c_void_p), ("d_variance", ctypes.c_void_p), ("d_lens", ctypes.c_void_p),
                 ("d_sub", ctypes.c_void_p), ("beta_in", ctypes.c_void_p),
-                ("moments_in", ctypes.c_void_p)]
+                ("moments_in", ctypes.c_void_p), ("source_rows", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("row0", ctypes.c_int64)]
 
 
 class lr_session_cfg(ctypes.Structure):
@@ -93,6 +94,7 @@ SIGNATURES = {
                                                  ctypes.c_int32, ctypes.POINTER(ctypes.c_int64),
                                                  ctypes.POINTER(ctypes.c_int64), _P]),
     "lens_raytrace": (ctypes.c_int32, [ctypes.POINTER(lr_points), _P, _P, _P]),
+    "lr_grid_points": (ctypes.c_int32, [ctypes.POINTER(lr_grid), _P, _P]),
     "lens_jacobian": (ctypes.c_int32, [ctypes.POINTER(lr_points), _P, _P, _P]),
     "gp_kernel_matvec": (ctypes.c_int32, [ctypes.POINTER(lr_points), ctypes.POINTER(lr_points), _P, ctypes.c_int32,
                                           ctypes.c_float, ctypes.c_float, _P, _P, _P, ctypes.c_size_t, _P]),

@@ -85,6 +85,15 @@ def lens_raytrace(pts: Points, want_alpha: bool = False, stream=None):
     return (beta, alpha) if want_alpha else beta
 
 
+def grid_points(grid: Grid, stream=None) -> torch.Tensor:
+    """(n, 2) float32 CUDA tensor of the grid's points, as the kernels generate them."""
+    lib = abi.load()
+    out = torch.empty((grid.n, 2), dtype=torch.float32, device=torch.device("cuda", torch.cuda.current_device()))
+    g = abi.lr_grid(*grid.astuple())
+    abi.check(lib.lr_grid_points(ctypes.byref(g), out.data_ptr(), _stream_handle(stream)), "lr_grid_points")
+    return out
+
+
 def lens_jacobian(pts: Points, stream=None):
     """(jac (n, 2, 2) = d beta / d xi, mu (n,) magnification) for every point (pts.lens required)."""
     lib = abi.load()
@@ -422,7 +431,7 @@ def gp_kernel_matvec_train(query: Points, source: Points, v: torch.Tensor, lengt
 def gp_kernel_matvec_bwd(query: Points, source: Points | None, v: torch.Tensor, lengthscale: float,
                          variance: float, g_out: torch.Tensor, want=("v", "x", "lengthscale", "variance"),
                          workspace: torch.Tensor | None = None, stream=None, beta: torch.Tensor | None = None,
-                         moments: torch.Tensor | None = None) -> dict:
+                         moments: torch.Tensor | None = None, source_rows: int | None = None) -> dict:
     """Gradients of Loss = sum_i g_out_i out_i (recompute-only backward).
 
     `want` selects among v, x (query points after ray-tracing), y (explicit
@@ -431,8 +440,12 @@ def gp_kernel_matvec_bwd(query: Points, source: Points | None, v: torch.Tensor, 
     ray-traced points from the forward pass instead of recomputing them;
     `moments` (optional) the row sums of gp_kernel_matvec_train, which leaves
     only the column sums to sweep. `v` and `g_out` are (m,) and (n,), or
-    (m, nrhs) and (n, nrhs) (explicit sources); d_v has v's shape. Returns a
-    dict of CUDA tensors (the scalar and parameter gradients are float64)."""
+    (m, nrhs) and (n, nrhs) (explicit sources); d_v has v's shape.
+    `source_rows=r0` says the query points are the points r0 .. r0 + n - 1
+    of `source` (one rank's rows of a self-kernel split by rows): g_out then
+    covers all m source points, x gets both roles of the query points and v
+    (the gradient) the query rows only. Returns a dict of CUDA tensors (the
+    scalar and parameter gradients are float64)."""
     lib = abi.load()
     _require_cuda(v, "v")
     _require_cuda(g_out, "g_out")
@@ -444,8 +457,9 @@ def gp_kernel_matvec_bwd(query: Points, source: Points | None, v: torch.Tensor, 
     n, m = cq.n, (cs.n if cs is not None else cq.n)
     dev = v.device
     out = {}
+    nv = n if source_rows is not None else m
     if "v" in want:
-        out["v"] = torch.empty((m,) if v.dim() == 1 else (m, nrhs), dtype=torch.float32, device=dev)
+        out["v"] = torch.empty((nv,) if v.dim() == 1 else (nv, nrhs), dtype=torch.float32, device=dev)
     if "x" in want:
         out["x"] = torch.empty((n, 2), dtype=torch.float32, device=dev)
     if "y" in want:
@@ -474,6 +488,9 @@ def gp_kernel_matvec_bwd(query: Points, source: Points | None, v: torch.Tensor, 
         if moments.numel() != 4 * n:
             raise ValueError("moments must hold 4 x n values")
         gr.moments_in = moments.data_ptr()
+    if source_rows is not None:
+        gr.source_rows = 1
+        gr.row0 = int(source_rows)
     b = ctypes.c_size_t(0)
     ps = ctypes.byref(cs) if cs is not None else None
     abi.check(lib.lr_matvec_bwd_workspace_size(ctypes.byref(cq), ps, nrhs, ctypes.byref(gr), ctypes.byref(b)),

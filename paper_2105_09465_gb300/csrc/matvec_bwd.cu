@@ -1634,6 +1634,8 @@ struct BwPlan {
   bool need_dx;         // d_x needed (requested or for the lens gradient)
   bool moments;         // row sums given by the training forward
   bool culled;          // explicit or self sources without moments: culled sweeps
+  bool slice;           // the query is rows [row0, row0 + n) of the source set (self-kernel rows)
+  int64_t row0;
   CullPlan cp_rows;     // culled: self backward, or the non-self row moments
   CullPlan cp_dy;       // culled, non-self with d_y: row moments with the roles swapped
   size_t off_qbeta, off_sbeta, off_rows, off_dv, off_dx, off_sgrid, off_swap, off_swaprows, off_vjp, off_scal, bytes;
@@ -1669,6 +1671,14 @@ static lr_status plan_bwd(const lr_points* q, const lr_points* s, int32_t nrhs, 
   const lr_grid* qg = query_layout(q);  // row blocks follow the image tiles
   LR_REQUIRE(!p.moments || !p.self, "gp_kernel_matvec_bwd: moments_in applies to non-self sources only");
   LR_REQUIRE(((uintptr_t)gr->moments_in & 3u) == 0, "gp_kernel_matvec_bwd: moments_in must be 4-byte aligned");
+  p.slice = gr->source_rows != 0;
+  if (p.slice) {
+    LR_REQUIRE(!p.self && !p.s_grid, "gp_kernel_matvec_bwd: source_rows needs explicit source points");
+    LR_REQUIRE(!p.moments && gr->d_y == nullptr, "gp_kernel_matvec_bwd: source_rows excludes moments_in and d_y");
+    LR_REQUIRE(gr->row0 >= 0 && gr->row0 + p.n <= p.m,
+               "gp_kernel_matvec_bwd: rows [%lld, %lld) outside the %lld source points", (long long)gr->row0,
+               (long long)(gr->row0 + p.n), (long long)p.m);
+  }
   p.culled = !p.s_grid && !p.moments;
   if (p.culled) {
     LR_REQUIRE(nrhs >= 1 && nrhs <= 4, "gp_kernel_matvec_bwd: nrhs = %d; explicit sources take nrhs = 1..4", nrhs);
@@ -1683,7 +1693,8 @@ static lr_status plan_bwd(const lr_points* q, const lr_points* s, int32_t nrhs, 
   p.off_scal = off;
   if (p.culled) {
     const lr_grid* sg = p.self ? qg : query_layout(s);
-    st = plan_cull(p.self ? kCullSelf : kCullMom, 1, p.n, qg, p.m, sg, &p.cp_rows);
+    p.row0 = p.slice ? gr->row0 : 0;
+    st = plan_cull((p.self || p.slice) ? kCullSelf : kCullMom, 1, p.n, qg, p.m, sg, &p.cp_rows);
     if (st != LR_OK) return st;
     off += p.cp_rows.bytes;
     // scalar partials of every right-hand side, summed once at the end
@@ -1710,7 +1721,7 @@ static lr_status plan_bwd(const lr_points* q, const lr_points* s, int32_t nrhs, 
   p.off_sgrid = off;
   p.off_swap = off;
   p.off_swaprows = off;
-  if (!p.self && gr->d_v && !p.s_grid) {
+  if (!p.self && !p.slice && gr->d_v && !p.s_grid) {
     // d_v: the forward reduction with the roles swapped (query = the
     // sources, source = the query points)
     lr_points qs = *s, ss = *q;
@@ -1758,9 +1769,11 @@ static lr_status launch_culled_bwd(const BwPlan& P, const lr_points* query, cons
   const int64_t nblk = P.cp_rows.scal_blocks;
   char* cws = ws + P.off_rows;
   lr_status st;
-  const bool rows_needed = P.self ? (G.d_v || dx || want_scal) : (dx || want_scal);
+  // a self-kernel, or rows [row0, row0 + n) of one: both roles of the rows
+  const bool both = P.self || P.slice;
+  const bool rows_needed = both ? (G.d_v || dx || want_scal) : (dx || want_scal);
   for (int r = 0; r < P.nrhs && rows_needed; ++r) {
-    st = launch_cull_prep(P.cp_rows, ys, sc, v, P.self ? g : nullptr, P.nrhs, r, cws, s);
+    st = launch_cull_prep(P.cp_rows, ys, sc, v, both ? g : nullptr, P.nrhs, r, cws, s);
     if (st != LR_OK) return st;
     CullArgs A{};
     A.x = xq;
@@ -1771,13 +1784,14 @@ static lr_status launch_culled_bwd(const BwPlan& P, const lr_points* query, cons
     A.var = var;
     A.dx_scale = dx_scale;
     A.dl_scale = dl_scale;
-    A.g = g;
-    A.vrow = v;
+    // the rows' own g and v: the first n, or rows row0.. of the source set
+    A.g = g + (size_t)P.row0 * P.nrhs;
+    A.vrow = v + (size_t)P.row0 * P.nrhs;
     A.stride = P.nrhs;
     A.col = r;
     A.d_x = dx;
     A.dx_accumulate = r > 0;
-    A.d_v = P.self ? G.d_v : nullptr;
+    A.d_v = both ? G.d_v : nullptr;
     A.scal_part = want_scal ? scal + 2 * (size_t)r * (size_t)nblk : nullptr;
     st = launch_cull_sweep(P.cp_rows, A, cws, LR_KT_BWD_ROWS, s);
     if (st != LR_OK) return st;
@@ -1786,7 +1800,7 @@ static lr_status launch_culled_bwd(const BwPlan& P, const lr_points* query, cons
     st = launch_cull_scalar_final(scal, (int64_t)P.nrhs * nblk, G.d_lengthscale, G.d_variance, s);
     if (st != LR_OK) return st;
   }
-  if (!P.self && G.d_v) {
+  if (!P.self && !P.slice && G.d_v) {
     // d_v_j = var sum_i k_ij g_i: the forward with the roles swapped
     lr_points qs = *source, ss{};
     qs.lens = nullptr;
@@ -1864,7 +1878,8 @@ extern "C" lr_status gp_kernel_matvec_bwd(const lr_points* query, const lr_point
   char* ws = static_cast<char*>(workspace);
   if (P.n == 0 || P.m == 0) {
     // every gradient is an empty sum
-    if (G.d_v && P.m) LR_CHECK_CUDA(cudaMemsetAsync(G.d_v, 0, 4 * (size_t)P.m * (size_t)P.nrhs, s));
+    const int64_t nv = P.slice ? P.n : P.m;  // d_v covers the query rows in the slice mode
+    if (G.d_v && nv) LR_CHECK_CUDA(cudaMemsetAsync(G.d_v, 0, 4 * (size_t)nv * (size_t)P.nrhs, s));
     if (G.d_x && P.n) LR_CHECK_CUDA(cudaMemsetAsync(G.d_x, 0, 8 * (size_t)P.n, s));
     if (G.d_y && P.m) LR_CHECK_CUDA(cudaMemsetAsync(G.d_y, 0, 8 * (size_t)P.m, s));
     if (G.d_lengthscale) LR_CHECK_CUDA(cudaMemsetAsync(G.d_lengthscale, 0, 8, s));

@@ -550,3 +550,11 @@ extern "C" lr_status lens_raytrace(const lr_points* pts, float* beta_out, float*
   return lr::launch_raytrace(pts, reinterpret_cast<float2*>(beta_out), reinterpret_cast<float2*>(alpha_out),
                              lr::as_cuda(stream));
 }
+
+extern "C" lr_status lr_grid_points(const lr_grid* grid, float* out, lr_stream stream) {
+  LR_REQUIRE(grid != nullptr, "lr_grid_points: grid is NULL");
+  LR_REQUIRE(grid->nx >= 0 && grid->ny >= 0 && grid->ss >= 1, "lr_grid_points: invalid grid");
+  LR_REQUIRE(out != nullptr || lr::grid_count(*grid) == 0, "lr_grid_points: out is NULL");
+  LR_REQUIRE(((uintptr_t)out & 7u) == 0, "lr_grid_points: out must be 8-byte aligned");
+  return lr::launch_grid_points(*grid, reinterpret_cast<float2*>(out), lr::as_cuda(stream));
+}
