@@ -895,6 +895,29 @@ def run_large(args, rank, local, world, dist, dev):
     breakdown["note"] = ("matvec: the culled self-kernel forward sweep; bwd_rows: the culled self-kernel backward "
                          "sweep; each kernel's own span (events on its stream)")
 
+    # ---- four right-hand sides in one pass (one exp2 per pair for all four):
+    # the step with v and dL/dout of four draws that share the lens
+    v4 = torch.from_numpy(np.random.default_rng(40).standard_normal((p.n, 4)).astype(np.float32)).to(dev)
+    g4 = torch.from_numpy(np.random.default_rng(41).standard_normal((p.n, 4)).astype(np.float32)).to(dev)
+    out4 = torch.empty((p.n, 4), dtype=torch.float32, device=dev)
+    ws4 = torch.empty(max(api.matvec_workspace_size(q, None, nrhs=4), 1), dtype=torch.uint8, device=dev)
+    bws4 = torch.empty(max(api.matvec_bwd_workspace_size(q, None, want=want, beta=True, nrhs=4), 1),
+                       dtype=torch.uint8, device=dev)
+
+    def step4():
+        api.gp_kernel_matvec(q, None, v4, p.lengthscale, p.variance, out=out4, beta=beta_buf, workspace=ws4)
+        api.gp_kernel_matvec_bwd(q, None, v4, p.lengthscale, p.variance, g4, want=want, workspace=bws4,
+                                 beta=beta_buf)
+
+    step4()
+    ms4 = event_time(step4, nk, stream, flush)
+    ms1 = event_time(step, nk, stream, flush)
+    multi_rhs = {"nrhs": 4, "ms_per_step": ms4, "ms_one_rhs": ms1, "ms_four_one_rhs_steps": 4 * ms1,
+                 "speedup_vs_four_steps": 4 * ms1 / ms4,
+                 "note": "v and dL/dout with 4 columns that share the ray-traced points: the forward and the "
+                         "self-kernel backward evaluate each pair's exp2 once for all four; the ray-trace and its "
+                         "VJP (dL/dbeta summed over the columns) run once; direct launches"}
+
     # ---- pairs the culled sweeps evaluate (the rest are exact zeros in FP32)
     beta = api.lens_raytrace(q)
     qx = api.Points(xy=beta, grid=p.xgrid)
@@ -1031,6 +1054,7 @@ def run_large(args, rank, local, world, dist, dev):
                      "frac_at_measured_clock": d["frac"] * sm_max / sm_mhz},
         "kernels": table,
         "step_breakdown_ms": breakdown,
+        "multi_rhs": multi_rhs,
         "raytrace": {"ms": rt_ms, "vjp_ms": vjp_ms, "points": p.n, "subhalo_pairs": sub_pairs,
                      "hbm_gbs": p.n * 8 / (rt_ms * 1e-3) / 1e9,
                      "note": "ALU/XU-bound with subhalos (8 B written per point)"},

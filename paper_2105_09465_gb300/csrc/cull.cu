@@ -89,9 +89,15 @@ __global__ void __launch_bounds__(256) cull_prep_kernel(const __grid_constant__ 
   float* w = reinterpret_cast<float*>(rec + kRecHead + kRecXY);  // [nw][32], pairs consecutive
   if (P.kind == kCullOut) {
     for (int k = 0; k < P.nw; ++k) w[k * kChunkPts + lane] = valid ? P.a[i * P.stride + k] : 0.f;
-  } else {
+  } else if (P.kind == kCullMom) {
     w[lane] = valid ? P.a[i * P.stride + P.col] : 0.f;
-    if (P.kind == kCullSelf) w[kChunkPts + lane] = valid ? P.b[i * P.stride + P.col] : 0.f;
+  } else {
+    // self-kernel: the nrhs columns of a (v), then those of b (g)
+    const int nr = P.nw / 2;
+    for (int k = 0; k < nr; ++k) {
+      w[k * kChunkPts + lane] = valid ? P.a[i * P.stride + k] : 0.f;
+      w[(nr + k) * kChunkPts + lane] = valid ? P.b[i * P.stride + k] : 0.f;
+    }
   }
 }
 
@@ -120,9 +126,9 @@ template <>
 struct CullTraits<kCullMom, 1> {
   static constexpr int K = 4, R = 2, BATCH = 32;
 };
-template <>
-struct CullTraits<kCullSelf, 2> {
-  static constexpr int K = 7, R = 2, BATCH = 32;
+template <int NW>
+struct CullTraits<kCullSelf, NW> {  // NW / 2 right-hand sides
+  static constexpr int K = 7 * (NW / 2), R = NW == 2 ? 2 : 1, BATCH = NW == 2 ? 32 : 16;
 };
 
 // Ordered compaction over the CTA: returns the number of true predicates;
@@ -170,19 +176,26 @@ __device__ __forceinline__ void cull_finalize(const CullArgs& A, int64_t i, cons
       sl = __fmul_rn(__fmul_rn(gi, t[3]), A.dl_scale);
       sv = __fmul_rn(gi, t[0]);
     }
-  } else {  // kCullSelf
-    const float gi = A.g[i * A.stride + A.col], vi = A.vrow[i * A.stride + A.col];
-    if (A.d_v) A.d_v[i * A.stride + A.col] = A.var * t[4];
+  } else {  // kCullSelf: K / 7 right-hand sides, 7 sums each
+    float dxx = 0.f, dxy = 0.f;
+#pragma unroll
+    for (int h = 0; h < K / 7; ++h) {
+      const float gi = A.g[i * A.stride + h], vi = A.vrow[i * A.stride + h];
+      const float* th = t + 7 * h;
+      if (A.d_v) A.d_v[i * A.stride + h] = A.var * th[4];
+      dxx = fmaf(gi, th[1], fmaf(vi, th[5], dxx));
+      dxy = fmaf(gi, th[2], fmaf(vi, th[6], dxy));
+      sl = fmaf(__fmul_rn(gi, th[3]), A.dl_scale, sl);
+      sv = fmaf(gi, th[0], sv);
+    }
     if (A.d_x) {
-      float2 d = f2(A.dx_scale * fmaf(gi, t[1], vi * t[5]), A.dx_scale * fmaf(gi, t[2], vi * t[6]));
+      float2 d = f2(A.dx_scale * dxx, A.dx_scale * dxy);
       if (A.dx_accumulate) {
         const float2 o = A.d_x[i];
         d = f2(o.x + d.x, o.y + d.y);
       }
       A.d_x[i] = d;
     }
-    sl = __fmul_rn(__fmul_rn(gi, t[3]), A.dl_scale);
-    sv = __fmul_rn(gi, t[0]);
   }
 }
 
@@ -376,34 +389,41 @@ __global__ void __launch_bounds__(kCullThreads) cull_kernel(const __grid_constan
           // weight for the self-kernel). Differences, not moments about a
           // reference point: a pair at d ~ 0 (the row's own point) adds
           // nothing to B and C instead of two large terms that cancel.
-          constexpr int NA = KIND == kCullSelf ? 7 : 4;
+          constexpr int NRH = KIND == kCullSelf ? NW / 2 : 1;  // right-hand sides
+          constexpr int NA = KIND == kCullSelf ? 7 * NRH : 4;
           float2 acc[R][NA];
 #pragma unroll
           for (int r = 0; r < R; ++r)
 #pragma unroll
             for (int k2 = 0; k2 < NA; ++k2) acc[r][k2] = f2(0.f, 0.f);
-#pragma unroll 4
+#pragma unroll 2
           for (int pp = 0; pp < kChunkPairs; ++pp) {
             const float4 P = xy[pp];
             const float2 X = f2(P.x, P.y), Y = f2(P.z, P.w);
-            const float2 W0 = wt[pp];
-            const float2 W1 = KIND == kCullSelf ? wt[kChunkPairs + pp] : f2(0.f, 0.f);
+            float2 W[NW];
+#pragma unroll
+            for (int w = 0; w < NW; ++w) W[w] = wt[w * kChunkPairs + pp];
 #pragma unroll
             for (int r = 0; r < R; ++r) {
+              // the pair's distance and exp2 once, for every right-hand side
               const float2 dx = __fadd2_rn(X, NQ[r]), dy = __fadd2_rn(Y, NP[r]);
               const float2 t = __ffma2_rn(dy, dy, __fmul2_rn(dx, dx));
               const float2 e = __fmul2_rn(t, NC);
               const float2 kk = f2(ex2_approx(e.x), ex2_approx(e.y));
-              const float2 kw = __fmul2_rn(kk, W0);
-              acc[r][0] = __fadd2_rn(acc[r][0], kw);
-              acc[r][1] = __ffma2_rn(kw, dx, acc[r][1]);
-              acc[r][2] = __ffma2_rn(kw, dy, acc[r][2]);
-              acc[r][3] = __ffma2_rn(kw, t, acc[r][3]);
-              if (KIND == kCullSelf) {
-                const float2 kg = __fmul2_rn(kk, W1);
-                acc[r][4] = __fadd2_rn(acc[r][4], kg);
-                acc[r][5] = __ffma2_rn(kg, dx, acc[r][5]);
-                acc[r][6] = __ffma2_rn(kg, dy, acc[r][6]);
+#pragma unroll
+              for (int h = 0; h < NRH; ++h) {
+                float2* a = acc[r] + 7 * h;
+                const float2 kw = __fmul2_rn(kk, W[h]);
+                a[0] = __fadd2_rn(a[0], kw);
+                a[1] = __ffma2_rn(kw, dx, a[1]);
+                a[2] = __ffma2_rn(kw, dy, a[2]);
+                a[3] = __ffma2_rn(kw, t, a[3]);
+                if (KIND == kCullSelf) {
+                  const float2 kg = __fmul2_rn(kk, W[NRH + h]);
+                  a[4] = __fadd2_rn(a[4], kg);
+                  a[5] = __ffma2_rn(kg, dx, a[5]);
+                  a[6] = __ffma2_rn(kg, dy, a[6]);
+                }
               }
             }
           }
@@ -510,10 +530,19 @@ static const void* cull_kernel_ptr(int kind, int nw) {
       default: return cull_fn<kCullOut, 4>();
     }
   }
-  return kind == kCullMom ? cull_fn<kCullMom, 1>() : cull_fn<kCullSelf, 2>();
+  if (kind == kCullMom) return cull_fn<kCullMom, 1>();
+  switch (nw) {
+    case 2: return cull_fn<kCullSelf, 2>();
+    case 4: return cull_fn<kCullSelf, 4>();
+    case 6: return cull_fn<kCullSelf, 6>();
+    default: return cull_fn<kCullSelf, 8>();
+  }
 }
 
-static int cull_rows_per_thread(int kind, int nw) { return (kind == kCullOut && nw <= 2) ? 4 : 2; }
+static int cull_rows_per_thread(int kind, int nw) {
+  if (kind == kCullOut) return nw <= 2 ? 4 : 2;
+  return (kind == kCullSelf && nw > 2) ? 1 : 2;
+}
 
 lr_status plan_cull(int kind, int nrhs, int64_t n, const lr_grid* qlayout, int64_t m, const lr_grid* slayout,
                     CullPlan* out) {
@@ -542,7 +571,7 @@ lr_status plan_cull(int kind, int nrhs, int64_t n, const lr_grid* qlayout, int64
   if (P.row_blocks > 0 && P.row_blocks < 2 * slots) splits = (2 * slots + P.row_blocks - 1) / P.row_blocks;
   if (splits > P.L.n_groups) splits = P.L.n_groups > 0 ? P.L.n_groups : 1;
   P.splits = (int32_t)splits;
-  P.K = kind == kCullOut ? P.nw : (kind == kCullMom ? 4 : 7);
+  P.K = kind == kCullOut ? P.nw : (kind == kCullMom ? 4 : 7 * (P.nw / 2));
   size_t off = 0;
   P.off_rec = off;
   off += align256((size_t)P.L.n_chunks * rec_bytes(P.nw));
@@ -623,7 +652,12 @@ lr_status launch_cull_sweep(const CullPlan& P, CullArgs A, char* ws, int timer_i
   } else if (P.kind == kCullMom) {
     st = launch_sweep_t<kCullMom, 1>(P, A, s);
   } else {
-    st = launch_sweep_t<kCullSelf, 2>(P, A, s);
+    switch (P.nw) {
+      case 2: st = launch_sweep_t<kCullSelf, 2>(P, A, s); break;
+      case 4: st = launch_sweep_t<kCullSelf, 4>(P, A, s); break;
+      case 6: st = launch_sweep_t<kCullSelf, 6>(P, A, s); break;
+      default: st = launch_sweep_t<kCullSelf, 8>(P, A, s); break;
+    }
   }
   if (timer_id >= 0) ktimer_end(timer_id, s);
   return st;

@@ -97,11 +97,11 @@ __device__ __forceinline__ bool boxes_far(float4 a, float4 b, float sc) {
 enum CullKind : int32_t {
   kCullOut = 0,   // nrhs weights: the columns of v   (forward)
   kCullMom = 1,   // one weight a                     (row moments of a)
-  kCullSelf = 2,  // two weights a, b                 (self-kernel backward)
+  kCullSelf = 2,  // a (v) and b (g), nrhs columns each  (self-kernel backward)
 };
 
 __host__ __device__ constexpr int cull_nw(int kind, int nrhs) {
-  return kind == kCullOut ? nrhs : (kind == kCullMom ? 1 : 2);
+  return kind == kCullOut ? nrhs : (kind == kCullMom ? 1 : 2 * nrhs);
 }
 
 struct CullPrepP {
@@ -124,8 +124,9 @@ struct CullPrepP {
 //             with g == NULL they are written to mom [4][n] (and out = var A);
 //             else the row gradients d_x = var/l^2 g_i (Bx, By) and the
 //             scalar partials (d_l, d_var) of g_i C, g_i A
-//  kCullSelf: self-kernel backward: d_v = var sum_j k g_j, d_x both roles,
-//             scalar partials.
+//  kCullSelf: self-kernel backward for nrhs right-hand sides in one sweep
+//             (the pair's exp2 shared): d_v = var sum_j k g_j per column,
+//             d_x both roles summed over the columns, scalar partials.
 struct CullArgs {
   const float2* x;   // [n] query points
   int64_t n;

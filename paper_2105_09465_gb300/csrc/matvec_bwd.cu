@@ -1694,7 +1694,10 @@ static lr_status plan_bwd(const lr_points* q, const lr_points* s, int32_t nrhs, 
   if (p.culled) {
     const lr_grid* sg = p.self ? qg : query_layout(s);
     p.row0 = p.slice ? gr->row0 : 0;
-    st = plan_cull((p.self || p.slice) ? kCullSelf : kCullMom, 1, p.n, qg, p.m, sg, &p.cp_rows);
+    // the self-kernel sweep takes every right-hand side at once; the
+    // non-self row moments one at a time
+    const bool both = p.self || p.slice;
+    st = plan_cull(both ? kCullSelf : kCullMom, both ? nrhs : 1, p.n, qg, p.m, sg, &p.cp_rows);
     if (st != LR_OK) return st;
     off += p.cp_rows.bytes;
     // scalar partials of every right-hand side, summed once at the end
@@ -1772,8 +1775,9 @@ static lr_status launch_culled_bwd(const BwPlan& P, const lr_points* query, cons
   // a self-kernel, or rows [row0, row0 + n) of one: both roles of the rows
   const bool both = P.self || P.slice;
   const bool rows_needed = both ? (G.d_v || dx || want_scal) : (dx || want_scal);
-  for (int r = 0; r < P.nrhs && rows_needed; ++r) {
-    st = launch_cull_prep(P.cp_rows, ys, sc, v, both ? g : nullptr, P.nrhs, r, cws, s);
+  const int sweeps = both ? 1 : P.nrhs;  // the self-kernel sweep takes every column at once
+  for (int r = 0; r < sweeps && rows_needed; ++r) {
+    st = launch_cull_prep(P.cp_rows, ys, sc, v, both ? g : nullptr, P.nrhs, both ? 0 : r, cws, s);
     if (st != LR_OK) return st;
     CullArgs A{};
     A.x = xq;
@@ -1788,7 +1792,7 @@ static lr_status launch_culled_bwd(const BwPlan& P, const lr_points* query, cons
     A.g = g + (size_t)P.row0 * P.nrhs;
     A.vrow = v + (size_t)P.row0 * P.nrhs;
     A.stride = P.nrhs;
-    A.col = r;
+    A.col = both ? 0 : r;
     A.d_x = dx;
     A.dx_accumulate = r > 0;
     A.d_v = both ? G.d_v : nullptr;
@@ -1797,7 +1801,7 @@ static lr_status launch_culled_bwd(const BwPlan& P, const lr_points* query, cons
     if (st != LR_OK) return st;
   }
   if (want_scal) {
-    st = launch_cull_scalar_final(scal, (int64_t)P.nrhs * nblk, G.d_lengthscale, G.d_variance, s);
+    st = launch_cull_scalar_final(scal, (int64_t)sweeps * nblk, G.d_lengthscale, G.d_variance, s);
     if (st != LR_OK) return st;
   }
   if (!P.self && !P.slice && G.d_v) {
