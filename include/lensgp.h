@@ -225,9 +225,10 @@ lr_status lens_jacobian(const lr_points* pts, float* jac_out, float* mu_out, lr_
  * reduced lazily without storing the n x m matrix, Sec. 3.3).
  *   query   the x_i; ray-traced first when query->lens != NULL
  *   source  the y_j, or NULL for a self-kernel (y = x after ray-tracing)
- *   v       device float[m][nrhs]: nrhs right-hand sides reduced in one pass
- *           (one exponential per pair, nrhs FMA): 1..4 for explicit,
- *           ray-traced or self sources, 1 for grid sources
+ *   v       device float[m][nrhs]: nrhs = 1..4 right-hand sides reduced in
+ *           one pass (one exponential per pair, nrhs FMA); with grid sources
+ *           and nrhs > 1 the grid's points are written to the workspace and
+ *           reduced like explicit sources
  *   out     device float[n][nrhs]
  *   beta_out device float[n][2] or NULL: receives the ray-traced query points
  *   workspace/workspace_bytes: caller-owned device scratch of at least
@@ -526,9 +527,11 @@ lr_status lr_matvec_train_workspace_size(const lr_points* query, const lr_points
  *   parameter and hyperparameter sums are FP64. Deterministic.
  * Same arguments and conventions as gp_kernel_matvec; workspace of at least
  * lr_matvec_bwd_workspace_size() bytes, 256-byte aligned. With nrhs > 1
- * (explicit or self sources, no moments_in) v, g_out and d_v are
- * [.][nrhs]; d_x, d_y, d_lengthscale, d_variance and the lens gradients sum
- * over the right-hand sides.
+ * (1..4, not with moments_in) v, g_out and d_v are [.][nrhs]; d_x, d_y,
+ * d_lengthscale, d_variance and the lens gradients sum over the right-hand
+ * sides. A self-kernel shares each pair's exp2 across the columns; the d_v
+ * sweep of other sources does too (grid sources are then written out as
+ * points), while their d_x row moments take one sweep per column.
  * Errors: LR_ERR_INVALID_ARG also when d_y is requested for grid or
  * self-kernel sources, lens gradients without a ray-traced query, or a
  * ray-traced source set distinct from the query.

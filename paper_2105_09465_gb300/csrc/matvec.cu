@@ -325,6 +325,7 @@ struct MvPlan {
   bool q_raytrace, q_grid;   // query needs ray-tracing / grid materialisation
   bool s_raytrace;           // source needs ray-tracing
   bool s_grid;               // source read as a grid (no materialisation)
+  bool s_mat;                // grid source written out as points (several right-hand sides)
   int32_t n_tiles, segs, chunks, row_blocks;
   RowMap map;                // row blocks: image tiles of a grid query, else index order
   CullPlan cull;             // explicit sources: the culled sweep
@@ -347,17 +348,18 @@ static lr_status plan_matvec(const lr_points* q, const lr_points* s, int32_t nrh
   p.q_grid = !p.q_raytrace && q->xy == nullptr;
   p.s_raytrace = !p.self && s->lens != nullptr;
   p.s_grid = !p.self && !p.s_raytrace && s->xy == nullptr;
-  if (p.s_grid) {
-    LR_REQUIRE(nrhs == 1, "gp_kernel_matvec: nrhs = %d; grid sources take nrhs = 1 (explicit sources: 1..4)", nrhs);
-  } else {
-    LR_REQUIRE(nrhs >= 1 && nrhs <= 4, "gp_kernel_matvec: nrhs = %d; explicit sources take nrhs = 1..4", nrhs);
-  }
+  LR_REQUIRE(nrhs >= 1 && nrhs <= 4, "gp_kernel_matvec: nrhs = %d; 1..4 right-hand sides", nrhs);
+  // several right-hand sides over grid sources: the grid's points are
+  // written out and reduced by the culled sweep, which shares each pair's
+  // exp2 across the right-hand sides
+  p.s_mat = p.s_grid && nrhs > 1;
+  if (p.s_mat) p.s_grid = false;
   size_t off = 0;
   const bool need_qbuf = (p.q_raytrace || p.q_grid) && !have_beta_out;
   p.off_qbeta = off;
   if (need_qbuf) off += align256(sizeof(float2) * (size_t)p.n);
   p.off_sbeta = off;
-  if (p.s_raytrace) off += align256(sizeof(float2) * (size_t)p.m);
+  if (p.s_raytrace || p.s_mat) off += align256(sizeof(float2) * (size_t)p.m);
   const lr_grid* layout = query_layout(q);
   if (!p.s_grid) {
     // explicit, ray-traced or self sources: the culled sweep
@@ -445,9 +447,9 @@ extern "C" lr_status gp_kernel_matvec(const lr_points* query, const lr_points* s
   S.segs = P.segs;
   if (P.self) {
     S.xy = xq;
-  } else if (P.s_raytrace) {
+  } else if (P.s_raytrace || P.s_mat) {
     float2* sb = reinterpret_cast<float2*>(ws + P.off_sbeta);
-    st = launch_raytrace(source, sb, nullptr, s);
+    st = P.s_raytrace ? launch_raytrace(source, sb, nullptr, s) : launch_grid_points(source->grid, sb, s);
     if (st != LR_OK) return st;
     S.xy = sb;
   } else if (P.s_grid) {

@@ -1635,6 +1635,7 @@ struct BwPlan {
   bool moments;         // row sums given by the training forward
   bool culled;          // explicit or self sources without moments: culled sweeps
   bool slice;           // the query is rows [row0, row0 + n) of the source set (self-kernel rows)
+  bool s_mat;           // grid source written out as points (several right-hand sides)
   int64_t row0;
   CullPlan cp_rows;     // culled: self backward, or the non-self row moments
   CullPlan cp_dy;       // culled, non-self with d_y: row moments with the roles swapped
@@ -1662,6 +1663,10 @@ static lr_status plan_bwd(const lr_points* q, const lr_points* s, int32_t nrhs, 
   LR_REQUIRE(!p.s_raytrace, "gp_kernel_matvec_bwd: a ray-traced source set distinct from the query is not supported");
   LR_REQUIRE(!(gr->d_y && (p.self || p.s_grid)),
              "gp_kernel_matvec_bwd: d_y applies to explicit non-self source points only");
+  // several right-hand sides over grid sources: the grid's points are written
+  // out and the culled sweeps take them as explicit points
+  p.s_mat = p.s_grid && nrhs > 1 && gr->moments_in == nullptr;
+  if (p.s_mat) p.s_grid = false;
   p.want_lens = (gr->d_lens || gr->d_sub);
   LR_REQUIRE(!p.want_lens || p.q_raytrace, "gp_kernel_matvec_bwd: lens gradients need a ray-traced query");
   p.need_dx = gr->d_x || p.want_lens;
@@ -1681,14 +1686,15 @@ static lr_status plan_bwd(const lr_points* q, const lr_points* s, int32_t nrhs, 
   }
   p.culled = !p.s_grid && !p.moments;
   if (p.culled) {
-    LR_REQUIRE(nrhs >= 1 && nrhs <= 4, "gp_kernel_matvec_bwd: nrhs = %d; explicit sources take nrhs = 1..4", nrhs);
+    LR_REQUIRE(nrhs >= 1 && nrhs <= 4, "gp_kernel_matvec_bwd: nrhs = %d; 1..4 right-hand sides", nrhs);
   } else {
-    LR_REQUIRE(nrhs == 1, "gp_kernel_matvec_bwd: nrhs = %d; grid sources and moments_in take nrhs = 1", nrhs);
+    LR_REQUIRE(nrhs == 1, "gp_kernel_matvec_bwd: nrhs = %d; moments_in takes nrhs = 1", nrhs);
   }
   size_t off = 0;
   p.off_qbeta = off;
   if ((p.q_raytrace && !gr->beta_in) || p.q_grid) off += align256(8 * (size_t)p.n);
   p.off_sbeta = off;
+  if (p.s_mat) off += align256(8 * (size_t)p.m);
   p.off_rows = off;
   p.off_scal = off;
   if (p.culled) {
@@ -1759,14 +1765,13 @@ static lr_status plan_bwd(const lr_points* q, const lr_points* s, int32_t nrhs, 
 // moments (d_x, scalar partials); then d_v and d_y of non-self sources with
 // the roles swapped; then d_l and d_var from every partial in fixed order.
 static lr_status launch_culled_bwd(const BwPlan& P, const lr_points* query, const lr_points* source,
-                                   const float2* xq, const float* v, float ell, float var, const float* g,
-                                   const lr_grads& G, float2* dx, char* ws, lr_stream stream) {
+                                   const float2* xq, const float2* ys, const float* v, float ell, float var,
+                                   const float* g, const lr_grads& G, float2* dx, char* ws, lr_stream stream) {
   cudaStream_t s = as_cuda(stream);
   const double c = 1.4426950408889634 / (2.0 * (double)ell * (double)ell);
   const float sc = (float)sqrt(c);
   const float dx_scale = (float)((double)var / ((double)ell * ell));
   const float dl_scale = (float)((double)var / ((double)ell * ell * ell));
-  const float2* ys = P.self ? xq : reinterpret_cast<const float2*>(source->xy);
   const bool want_scal = G.d_lengthscale || G.d_variance;
   double* scal = reinterpret_cast<double*>(ws + P.off_scal);
   const int64_t nblk = P.cp_rows.scal_blocks;
@@ -1903,6 +1908,11 @@ extern "C" lr_status gp_kernel_matvec_bwd(const lr_points* query, const lr_point
     xq = qb;
   }
   const float2* ys = P.self ? xq : (P.s_grid ? nullptr : reinterpret_cast<const float2*>(source->xy));
+  if (P.s_mat) {
+    float2* sb = reinterpret_cast<float2*>(ws + P.off_sbeta);
+    if ((st = launch_grid_points(source->grid, sb, s)) != LR_OK) return st;
+    ys = sb;
+  }
   const lr_grid* yg = P.s_grid ? &source->grid : nullptr;
   const lr_grid* qgrid = query_layout(query);
   float2* dx = P.need_dx ? (G.d_x ? reinterpret_cast<float2*>(G.d_x) : reinterpret_cast<float2*>(ws + P.off_dx))
@@ -1925,7 +1935,7 @@ extern "C" lr_status gp_kernel_matvec_bwd(const lr_points* query, const lr_point
   }
   if (P.culled) {
     // explicit or self sources: the culled sweeps (d_v and d_y included)
-    st = launch_culled_bwd(P, query, source, xq, v, lengthscale, variance, g_out, G, dx, ws, stream);
+    st = launch_culled_bwd(P, query, source, xq, ys, v, lengthscale, variance, g_out, G, dx, ws, stream);
     if (st != LR_OK) return st;
   } else if (P.moments) {
     // row gradients from the training forward's moments

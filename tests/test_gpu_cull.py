@@ -1,9 +1,10 @@
 """Culled reductions over explicit point sets against the FP64 oracle.
 
 Covers several right-hand sides in one pass (forward and backward, each
-column against the oracle), ray-traced pixels that carry their image layout
-(where the exact-zero skipping leaves out most pairs), ragged layouts, both
-exponent forms, and the skipping itself: the same bits with
+column against the oracle, explicit, self and grid sources), ray-traced
+pixels that carry their image layout (where the exact-zero skipping leaves
+out most pairs), ragged layouts, length scales well above and well below the
+point spacing, and the skipping itself: the same bits with
 lr_set_pair_culling(0) as with it on."""
 import ctypes
 
@@ -116,8 +117,10 @@ def test_multi_rhs_backward_explicit(orc, nrhs):
 @pytest.mark.parametrize("nx,ny,ell", [(77, 45, 0.05), (64, 32, 0.05), (50, 90, 0.002), (33, 33, 0.4)])
 def test_layout_self_kernel_forward_backward(orc, nx, ny, ell):
     """Ragged image layouts (not multiples of the chunk, group or row-block
-    tile), the split form (l well above the point spacing) and the unsplit one
-    (l = 2 mas, below the 25 mas spacing: every chunk too wide to split)."""
+    tile); length scales well above the point spacing and at 2 mas, far
+    below the 25 mas spacing, where a row's sum beyond its own point is made
+    of far pairs (scaled distance^2 of 30 to 120) and a chunk spans many
+    length scales."""
     lens = W.Lens(0.05, -0.03, 0.75, 0.4, 1.1, 2.05, 0.02, -0.01)
     g = W.Grid(nx, ny, 2, 0.05)
     _, b = orc.raytrace(orc.grid_points(*g.astuple()), lens.astuple())
@@ -215,9 +218,33 @@ def test_rejects_nrhs_outside_range():
     x = dev(np.zeros((4, 2)))
     with pytest.raises(abi.LensGPError):
         api.gp_kernel_matvec(api.Points(xy=x), None, torch.zeros((4, 5), device="cuda"), 0.1)
-    with pytest.raises(abi.LensGPError):  # grid sources take one right-hand side
+    with pytest.raises(abi.LensGPError):
         api.gp_kernel_matvec(api.Points(xy=x), api.Points(grid=W.Grid(4, 4, 1, 0.1)),
-                             torch.zeros((16, 2), device="cuda"), 0.1)
+                             torch.zeros((16, 5), device="cuda"), 0.1)
+
+
+@pytest.mark.parametrize("nrhs", [2, 4])
+def test_multi_rhs_grid_sources(orc, nrhs):
+    """Ray-traced pixels against a grid of inducing points with several
+    right-hand sides: forward and backward, each column against the oracle."""
+    p = W.realistic(seed=91, side=60, ss=2, n_sub=12, ygrid_side=40)
+    b = traced(orc, p)
+    rng = np.random.default_rng(nrhs)
+    v = rng.standard_normal((p.m, nrhs)).astype(np.float32)
+    g = rng.standard_normal((p.n, nrhs)).astype(np.float32)
+    q, s = api.Points(xy=dev(b), grid=p.xgrid), api.Points(grid=p.ygrid)
+    got = host(api.gp_kernel_matvec(q, s, dev(v), p.lengthscale, p.variance))
+    yg = orc.grid_points(*p.ygrid.astuple())
+    for r in range(nrhs):
+        ref, ab = orc.kernel_matvec(b, yg, v[:, r], p.lengthscale, p.variance)
+        assert_matvec_close(got[:, r], ref, ab, what=f"grid rhs {r}")
+    G = api.gp_kernel_matvec_bwd(q, s, dev(v), p.lengthscale, p.variance, dev(g),
+                                 want=("v", "x", "lengthscale", "variance"))
+    R = oracle_bwd(orc, b, yg, v, g, p.lengthscale, p.variance, False)
+    close(host(G["v"]), R["d_v"], R["d_v_abs"], what="d_v")
+    close(host(G["x"]), R["d_x"], R["d_x_abs"], what="d_x")
+    close(host(G["lengthscale"]), [R["d_len"]], [R["d_len_abs"]], what="d_len")
+    close(host(G["variance"]), [R["d_var"]], [R["d_var_abs"]], what="d_var")
 
 
 def test_no_fault_recorded():
