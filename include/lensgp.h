@@ -171,6 +171,7 @@ enum { LR_PROFILE_TNFW = 0, LR_PROFILE_POINT_MASS = 1 };
  *   xy      device float[n][2], or NULL to use `grid`
  *   grid    used when xy == NULL (then n must equal its point count)
  *   lens    host pointer; NULL = no ray-trace (positions used as given)
+ *           unless lens_record is set
  *   sub, n_sub, profile   subhalos, used only when lens != NULL
  */
 typedef struct {
@@ -181,7 +182,27 @@ typedef struct {
   const float* sub;
   int32_t n_sub;
   int32_t profile;
+  const void* lens_record; /* or: a DEVICE lens record (lr_lens_prepare) in place of `lens` */
 } lr_points;
+
+/*
+ * Device-resident lens parameters (a lens drawn on the device, e.g. by
+ * gp_partial_mvn_draw, never copied to the host). lr_lens_prepare computes,
+ * on `stream`, the lens constants of the ray-trace and of its gradient from
+ * theta7 (device float[7]: x0, y0, q, phi, theta_e, g1, g2, the slope held
+ * fixed at `gamma`) into `record` (device memory of lr_lens_record_bytes()
+ * bytes, 16-byte aligned, owned by the caller). A point set with
+ * lens_record = record is then ray-traced (lens_raytrace, gp_kernel_matvec*,
+ * gp_kernel_matvec_bwd, lens_raytrace_vjp) with that lens and no host
+ * synchronisation. Parameters outside their domain (q not in (0, 1], slope
+ * not in (1, 3), theta_e < 0, a non-finite value, or q too small for the
+ * series) cannot be rejected when the call is made: the record is marked
+ * invalid, the ray-trace kernels record fault code 2 in the device fault
+ * word (lr_fault_status), and their outputs, finite but not to be used, are
+ * those of a main deflector and shear that deflect nothing.
+ */
+size_t lr_lens_record_bytes(void);
+lr_status lr_lens_prepare(const float* theta7, float gamma, void* record, lr_stream stream);
 
 /* ------------------------------------------------------------------------ */
 /* Ray-trace (Sec. 2.1 raytracing equation; Sec. 2.2 lens model)              */
@@ -553,6 +574,22 @@ lr_status lr_matvec_bwd_workspace_size(const lr_points* query, const lr_points* 
 lr_status lens_raytrace_vjp(const lr_points* pts, const float* d_beta, double* d_lens, double* d_sub,
                             void* workspace, size_t workspace_bytes, lr_stream stream);
 lr_status lr_raytrace_vjp_workspace_size(const lr_points* pts, size_t* bytes);
+
+/* ------------------------------------------------------------------------ */
+/* Elementwise steps of a training step composed from the library (weight     */
+/* folding A y, Sec. 3.4; the sum of the layers, Sec. 3.1; dL/dbeta summed    */
+/* over the layers and the prior gradient, Sec. 3.6). Device arrays,          */
+/* stream-ordered, FP32 unless stated; out may alias an input.                */
+
+/* out = a x + b y (y may be NULL: out = a x), n elements. */
+lr_status lr_vec_axpby(int64_t n, float a, const float* x, float b, const float* y, float* out, lr_stream stream);
+/* out = a * b elementwise, n elements. */
+lr_status lr_vec_mul(int64_t n, const float* a, const float* b, float* out, lr_stream stream);
+/* out[0:nh] = (float)head (FP64), out[nh:nh+nt] = tail. */
+lr_status lr_vec_pack(const double* head, int32_t nh, const float* tail, int64_t nt, float* out, lr_stream stream);
+/* *out = sum of the n (<= 16) device doubles *parts[k] (parts: a HOST array
+ * of device pointers), in that order. */
+lr_status lr_sum_scalars(const double* const* parts, int32_t n, double* out, lr_stream stream);
 
 /* ------------------------------------------------------------------------ */
 /* Serving: device-resident request loop with continuous batching             */

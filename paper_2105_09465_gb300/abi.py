@@ -43,7 +43,7 @@ class lr_lens(ctypes.Structure):
 class lr_points(ctypes.Structure):
     _fields_ = [("xy", ctypes.c_void_p), ("grid", lr_grid), ("n", ctypes.c_int64),
                 ("lens", ctypes.POINTER(lr_lens)), ("sub", ctypes.c_void_p), ("n_sub", ctypes.c_int32),
-                ("profile", ctypes.c_int32)]
+                ("profile", ctypes.c_int32), ("lens_record", ctypes.c_void_p)]
 
 
 class lr_grads(ctypes.Structure):
@@ -95,6 +95,12 @@ SIGNATURES = {
                                                  ctypes.POINTER(ctypes.c_int64), _P]),
     "lens_raytrace": (ctypes.c_int32, [ctypes.POINTER(lr_points), _P, _P, _P]),
     "lr_grid_points": (ctypes.c_int32, [ctypes.POINTER(lr_grid), _P, _P]),
+    "lr_lens_record_bytes": (ctypes.c_size_t, []),
+    "lr_lens_prepare": (ctypes.c_int32, [_P, ctypes.c_float, _P, _P]),
+    "lr_vec_axpby": (ctypes.c_int32, [ctypes.c_int64, ctypes.c_float, _P, ctypes.c_float, _P, _P, _P]),
+    "lr_vec_mul": (ctypes.c_int32, [ctypes.c_int64, _P, _P, _P, _P]),
+    "lr_vec_pack": (ctypes.c_int32, [_P, ctypes.c_int32, _P, ctypes.c_int64, _P, _P]),
+    "lr_sum_scalars": (ctypes.c_int32, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int32, _P, _P]),
     "lens_jacobian": (ctypes.c_int32, [ctypes.POINTER(lr_points), _P, _P, _P]),
     "gp_kernel_matvec": (ctypes.c_int32, [ctypes.POINTER(lr_points), ctypes.POINTER(lr_points), _P, ctypes.c_int32,
                                           ctypes.c_float, ctypes.c_float, _P, _P, _P, ctypes.c_size_t, _P]),

@@ -24,6 +24,7 @@ class Points:
     lens: Lens | None = None
     sub: torch.Tensor | None = None   # (S, 5) float32 CUDA
     profile: int = abi.LR_PROFILE_TNFW
+    lens_record: torch.Tensor | None = None  # a device lens (lens_prepare) in place of `lens`
 
     @property
     def n(self) -> int:
@@ -61,10 +62,13 @@ def to_c_points(p: Points | None):
         c.xy = None
         c.grid = abi.lr_grid(*p.grid.astuple())
         c.n = p.grid.n
-    if p.lens is not None:
-        L = abi.lr_lens(*p.lens.astuple())
-        keep.append(L)
-        c.lens = ctypes.pointer(L)
+    if p.lens is not None or p.lens_record is not None:
+        if p.lens is not None:
+            L = abi.lr_lens(*p.lens.astuple())
+            keep.append(L)
+            c.lens = ctypes.pointer(L)
+        else:
+            c.lens_record = p.lens_record.data_ptr()
         c.sub = p.sub.data_ptr() if (p.sub is not None and p.sub.numel()) else None
         c.n_sub = int(p.sub.shape[0]) if p.sub is not None else 0
         c.profile = int(p.profile)
@@ -91,6 +95,75 @@ def grid_points(grid: Grid, stream=None) -> torch.Tensor:
     out = torch.empty((grid.n, 2), dtype=torch.float32, device=torch.device("cuda", torch.cuda.current_device()))
     g = abi.lr_grid(*grid.astuple())
     abi.check(lib.lr_grid_points(ctypes.byref(g), out.data_ptr(), _stream_handle(stream)), "lr_grid_points")
+    return out
+
+
+def lens_prepare(theta7: torch.Tensor, gamma: float, record: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Device lens record from device-resident parameters theta7 (x0, y0, q,
+    phi, theta_e, g1, g2; float32 CUDA, 7 values) with the slope fixed at
+    gamma: pass it as Points(lens_record=...). No host synchronisation."""
+    lib = abi.load()
+    _require_cuda(theta7, "theta7")
+    if theta7.numel() != 7:
+        raise ValueError("theta7 must hold 7 values")
+    nb = int(lib.lr_lens_record_bytes())
+    if record is None:
+        record = torch.empty((nb + 15) // 16 * 4, dtype=torch.float32, device=theta7.device)
+    abi.check(lib.lr_lens_prepare(theta7.data_ptr(), float(gamma), record.data_ptr(), _stream_handle(stream)),
+              "lr_lens_prepare")
+    return record
+
+
+def vec_axpby(a: float, x: torch.Tensor, b: float = 0.0, y: torch.Tensor | None = None,
+              out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """a x + b y (or a x) elementwise, in the library."""
+    lib = abi.load()
+    _require_cuda(x, "x")
+    _require_cuda(y, "y")
+    if y is not None and y.numel() != x.numel():
+        raise ValueError("x and y differ in size")
+    out = torch.empty_like(x) if out is None else out
+    abi.check(lib.lr_vec_axpby(x.numel(), float(a), x.data_ptr(), float(b), y.data_ptr() if y is not None else None,
+                               out.data_ptr(), _stream_handle(stream)), "lr_vec_axpby")
+    return out
+
+
+def vec_mul(a: torch.Tensor, b: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """a * b elementwise, in the library."""
+    lib = abi.load()
+    _require_cuda(a, "a")
+    _require_cuda(b, "b")
+    if a.numel() != b.numel():
+        raise ValueError("a and b differ in size")
+    out = torch.empty_like(a) if out is None else out
+    abi.check(lib.lr_vec_mul(a.numel(), a.data_ptr(), b.data_ptr(), out.data_ptr(), _stream_handle(stream)),
+              "lr_vec_mul")
+    return out
+
+
+def vec_pack(head: torch.Tensor, tail: torch.Tensor, stream=None) -> torch.Tensor:
+    """[float32(head), tail] with head float64, tail float32 (CUDA)."""
+    lib = abi.load()
+    _require_cuda(tail, "tail")
+    if head.dtype != torch.float64 or not head.is_cuda or not head.is_contiguous():
+        raise ValueError("head must be a contiguous float64 CUDA tensor")
+    out = torch.empty(head.numel() + tail.numel(), dtype=torch.float32, device=tail.device)
+    abi.check(lib.lr_vec_pack(head.data_ptr(), head.numel(), tail.data_ptr(), tail.numel(), out.data_ptr(),
+                              _stream_handle(stream)), "lr_vec_pack")
+    return out
+
+
+def sum_scalars(parts, stream=None) -> torch.Tensor:
+    """(1,) float64 CUDA tensor: the sum of the first element of each float64
+    CUDA tensor in `parts`, in order, in the library."""
+    lib = abi.load()
+    ptrs = (ctypes.c_void_p * max(len(parts), 1))(*[t.data_ptr() for t in parts])
+    dev = parts[0].device if parts else torch.device("cuda", torch.cuda.current_device())
+    out = torch.empty(1, dtype=torch.float64, device=dev)
+    for t in parts:
+        if t.dtype != torch.float64 or not t.is_cuda:
+            raise ValueError("parts must be float64 CUDA tensors")
+    abi.check(lib.lr_sum_scalars(ptrs, len(parts), out.data_ptr(), _stream_handle(stream)), "lr_sum_scalars")
     return out
 
 

@@ -688,7 +688,7 @@ extern "C" lr_status lr_cull_pairs_evaluated(const lr_points* query, const lr_po
   if (source) {
     st = validate_points(source, "lr_cull_pairs_evaluated(source)", false);
     if (st != LR_OK) return st;
-    LR_REQUIRE(source->xy != nullptr || source->lens != nullptr,
+    LR_REQUIRE(source->xy != nullptr || has_lens(source),
                "lr_cull_pairs_evaluated: grid sources take the grid sweeps (lr_grid_pairs_evaluated)");
   }
   LR_REQUIRE(pairs != nullptr, "lr_cull_pairs_evaluated: pairs is NULL");
@@ -719,7 +719,7 @@ extern "C" lr_status lr_cull_pairs_evaluated(const lr_points* query, const lr_po
   float* w = reinterpret_cast<float*>(buf + b_q + b_s);
   char* ws = buf + b_q + b_s + b_w;
   unsigned long long* cnt = reinterpret_cast<unsigned long long*>(ws + P.bytes);
-  if (query->lens)
+  if (has_lens(query))
     st = launch_raytrace(query, xq, nullptr, s);
   else if (query->xy == nullptr)
     st = launch_grid_points(query->grid, xq, s);
@@ -728,7 +728,7 @@ extern "C" lr_status lr_cull_pairs_evaluated(const lr_points* query, const lr_po
   if (st != LR_OK) return done(st);
   const float2* src = xq;
   if (!self) {
-    if (source->lens)
+    if (has_lens(source))
       st = launch_raytrace(source, ys, nullptr, s);
     else if (cudaMemcpyAsync(ys, source->xy, 8 * (size_t)m, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
       st = cuda_status(cudaGetLastError(), "cudaMemcpyAsync");

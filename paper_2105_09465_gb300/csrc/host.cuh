@@ -16,6 +16,9 @@ size_t raytrace_vjp_ws(int64_t n, int32_t n_sub);
 lr_status launch_raytrace_vjp(const lr_points* p, const float2* dbeta, double* d_lens, double* d_sub, void* ws,
                               cudaStream_t s);
 
+// A point set is ray-traced when it carries a lens, host struct or device record.
+inline bool has_lens(const lr_points* p) { return p->lens != nullptr || p->lens_record != nullptr; }
+
 // Rounds a byte count up to a multiple of 256 (workspace sub-allocation).
 inline size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 

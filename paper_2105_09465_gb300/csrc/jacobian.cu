@@ -85,6 +85,7 @@ extern "C" lr_status lens_jacobian(const lr_points* pts, float* jac_out, float* 
   LR_REQUIRE(((uintptr_t)jac_out & 15u) == 0 && ((uintptr_t)mu_out & 3u) == 0,
              "lens_jacobian: jac_out must be 16-byte and mu_out 4-byte aligned");
   lr::LensConst L;
+  LR_REQUIRE(pts->lens != nullptr, "lens_jacobian: takes a host lens (lr_lens), not a device lens record");
   if ((st = lr::make_lens_const(pts->lens, &L)) != LR_OK) return st;
   lr::LensGradConst G;
   if ((st = lr::make_lens_grad_const(pts->lens, &G)) != LR_OK) return st;

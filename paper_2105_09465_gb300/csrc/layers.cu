@@ -194,14 +194,14 @@ static lr_status plan_layers(const lr_points* q, const lr_points* s, int32_t L, 
   if (st != LR_OK) return st;
   if (s) {
     if ((st = validate_points(s, "gp_kernel_matvec_layers(source)", false)) != LR_OK) return st;
-    LR_REQUIRE(s->lens == nullptr, "gp_kernel_matvec_layers: sources must not be ray-traced (use a self-kernel)");
+    LR_REQUIRE(!has_lens(s), "gp_kernel_matvec_layers: sources must not be ray-traced (use a self-kernel)");
   }
   LR_REQUIRE(L >= 1 && L <= kLyMax, "gp_kernel_matvec_layers: n_layers = %d outside [1, %d]", L, kLyMax);
   LyPlan p{};
   p.n = q->n;
   p.self = s == nullptr;
   p.m = p.self ? q->n : s->n;
-  p.q_raytrace = q->lens != nullptr;
+  p.q_raytrace = has_lens(q);
   p.q_grid = !p.q_raytrace && q->xy == nullptr;
   p.s_grid = !p.self && s->xy == nullptr;
   if (p.s_grid) {

@@ -532,6 +532,88 @@ struct LensGradConst {
   float hco[kMaxSeriesTerms];
 };
 
+// Both constant sets from the 8 lens parameters (x0, y0, q, phi, theta_e,
+// gamma, g1, g2) in FP64, on the host or on the device: returns 0, 1 when a
+// parameter is outside its domain or not finite, 2 when q is too small for
+// the deflection series (more than kMaxSeriesTerms terms), 3 for the
+// gradient series. Either output may be NULL.
+__host__ __device__ inline int lens_constants(const float* p, LensConst* Lout, LensGradConst* Gout) {
+  for (int k = 0; k < 8; ++k)
+    if (!(p[k] == p[k]) || p[k] - p[k] != 0.0f) return 1;  // NaN or infinite
+  const double q = p[2], phi = p[3], te = p[4], gam = p[5];
+  if (!(q > 0.0 && q <= 1.0) || !(gam > 1.0 && gam < 3.0) || !(te >= 0.0)) return 1;
+  const double a = 0.5 * (gam - 1.0), b = 0.5 * (5.0 - gam), fq = (1.0 - q) / (1.0 + q);
+  if (Lout) {
+    LensConst L;
+    for (int k = 0; k < kMaxSeriesTerms; ++k) L.d[k] = 0.f;
+    L.x0 = p[0];
+    L.y0 = p[1];
+    L.c = (float)cos(phi);
+    L.s = (float)sin(phi);
+    L.sq = (float)sqrt(q);
+    L.isq = (float)(1.0 / sqrt(q));
+    L.pre = (float)(pow(te, gam - 1.0) * 2.0 * sqrt(q) / (1.0 + q));
+    L.half_expo = (float)(0.5 * (1.0 - gam));
+    L.g1 = p[6];
+    L.g2 = p[7];
+    L.pad_ = 0;
+    // 2F1(1, a; b; -f w) = sum_n c_n (-f)^n w^n, c_n = prod_{k<=n} (a+k-1)/(b+k-1)
+    double c = 1.0, fn = 1.0;
+    int n = 0;
+    L.d[0] = 1.0f;
+    for (n = 1; n < kMaxSeriesTerms; ++n) {
+      // tail bound: |d_n| f / (1 - f) (coefficient ratios are below 1 for gamma < 3)
+      if (fq == 0.0 || fabs(c * fn) * fq / (1.0 - fq) < 1e-9) break;
+      c *= (a + n - 1.0) / (b + n - 1.0);
+      fn *= -fq;
+      L.d[n] = (float)(c * fn);
+    }
+    if (!(fq == 0.0 || fabs(c * fn) * fq / (1.0 - fq) < 1e-9)) return 2;
+    L.nterms = n;
+    *Lout = L;
+  }
+  if (Gout) {
+    LensGradConst G;
+    for (int k = 0; k < kMaxSeriesTerms; ++k) G.hco[k] = 0.f;
+    G.e = (float)(0.5 * (1.0 - gam));
+    G.f = (float)fq;
+    G.dlnpre_dq = (float)(0.5 / q - 1.0 / (1.0 + q));
+    G.df_dq = (float)(-2.0 / ((1.0 + q) * (1.0 + q)));
+    G.inv2q = (float)(0.5 / q);
+    G.dlnte = te > 0.0 ? (float)((gam - 1.0) / te) : 0.f;
+    G.pad_ = 0;
+    // h_n = (n+1) c_{n+1} (-f)^n, c_n = prod_{k<=n} (a+k-1)/(b+k-1)
+    double c = 1.0, fn = 1.0;  // c_{n+1}, (-f)^n
+    int n = 0;
+    for (n = 0; n < kMaxSeriesTerms; ++n) {
+      c *= (a + n) / (b + n);  // c_{n+1}
+      const double hn = (n + 1.0) * c * fn;
+      G.hco[n] = (float)hn;
+      // tail bound for sum_{k>n} |h_k|: |h_n| f (n+2)/(n+1) / (1 - f)^2
+      if (fq == 0.0 || fabs(hn) * fq * (n + 2.0) / (n + 1.0) / ((1.0 - fq) * (1.0 - fq)) < 1e-9) {
+        ++n;
+        break;
+      }
+      fn *= -fq;
+    }
+    if (n > kMaxSeriesTerms) return 3;
+    G.nterms = n < 1 ? 1 : n;
+    *Gout = G;
+  }
+  return 0;
+}
+
+// A lens prepared on the device from device-resident parameters (the
+// lr_lens_prepare entry point): both constant sets and the status of
+// lens_constants (nonzero: the parameters were outside their domain and the
+// constants are not to be used).
+struct LensRecord {
+  LensConst L;
+  LensGradConst G;
+  int32_t status;
+  int32_t pad_[3];
+};
+
 struct cf {
   float re, im;
 };

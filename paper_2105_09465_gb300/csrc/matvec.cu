@@ -344,9 +344,9 @@ static lr_status plan_matvec(const lr_points* q, const lr_points* s, int32_t nrh
   p.nrhs = nrhs;
   p.self = (s == nullptr);
   p.m = p.self ? q->n : s->n;
-  p.q_raytrace = q->lens != nullptr;
+  p.q_raytrace = has_lens(q);
   p.q_grid = !p.q_raytrace && q->xy == nullptr;
-  p.s_raytrace = !p.self && s->lens != nullptr;
+  p.s_raytrace = !p.self && has_lens(s);
   p.s_grid = !p.self && !p.s_raytrace && s->xy == nullptr;
   LR_REQUIRE(nrhs >= 1 && nrhs <= 4, "gp_kernel_matvec: nrhs = %d; 1..4 right-hand sides", nrhs);
   // several right-hand sides over grid sources: the grid's points are

@@ -1656,9 +1656,9 @@ static lr_status plan_bwd(const lr_points* q, const lr_points* s, int32_t nrhs, 
   p.nrhs = nrhs;
   p.self = s == nullptr;
   p.m = p.self ? q->n : s->n;
-  p.q_raytrace = q->lens != nullptr;
+  p.q_raytrace = has_lens(q);
   p.q_grid = !p.q_raytrace && q->xy == nullptr;
-  p.s_raytrace = !p.self && s->lens != nullptr;
+  p.s_raytrace = !p.self && has_lens(s);
   p.s_grid = !p.self && !p.s_raytrace && s->xy == nullptr;
   LR_REQUIRE(!p.s_raytrace, "gp_kernel_matvec_bwd: a ray-traced source set distinct from the query is not supported");
   LR_REQUIRE(!(gr->d_y && (p.self || p.s_grid)),
@@ -1735,7 +1735,9 @@ static lr_status plan_bwd(const lr_points* q, const lr_points* s, int32_t nrhs, 
     // sources, source = the query points)
     lr_points qs = *s, ss = *q;
     qs.lens = nullptr;
+    qs.lens_record = nullptr;
     ss.lens = nullptr;
+    ss.lens_record = nullptr;
     ss.xy = reinterpret_cast<const float*>(uintptr_t(256));  // planning reads no point
     st = lr_matvec_workspace_size(&qs, &ss, nrhs, &p.swap_bytes);
     if (st != LR_OK) return st;
@@ -1813,6 +1815,7 @@ static lr_status launch_culled_bwd(const BwPlan& P, const lr_points* query, cons
     // d_v_j = var sum_i k_ij g_i: the forward with the roles swapped
     lr_points qs = *source, ss{};
     qs.lens = nullptr;
+    qs.lens_record = nullptr;
     ss.xy = reinterpret_cast<const float*>(xq);
     ss.n = P.n;
     const lr_grid* qg = query_layout(query);
@@ -1955,6 +1958,7 @@ extern "C" lr_status gp_kernel_matvec_bwd(const lr_points* query, const lr_point
   if (!P.culled && !P.self && !P.s_grid && G.d_v) {
     lr_points qs = *source, ss{};
     qs.lens = nullptr;
+    qs.lens_record = nullptr;
     ss.xy = reinterpret_cast<const float*>(xq);
     ss.n = P.n;
     const lr_grid* qg = query_layout(query);
@@ -1999,11 +2003,11 @@ static lr_status plan_train(const lr_points* q, const lr_points* s, TrainPlan* T
   LR_REQUIRE(s != nullptr, "gp_kernel_matvec_train: a self-kernel (source == NULL) is not supported");
   st = validate_points(s, "gp_kernel_matvec_train(source)", false);
   if (st != LR_OK) return st;
-  LR_REQUIRE(s->lens == nullptr, "gp_kernel_matvec_train: ray-traced sources are not supported");
+  LR_REQUIRE(!has_lens(s), "gp_kernel_matvec_train: ray-traced sources are not supported");
   TrainPlan p{};
   p.n = q->n;
   p.m = s->n;
-  p.q_raytrace = q->lens != nullptr;
+  p.q_raytrace = has_lens(q);
   p.q_grid = !p.q_raytrace && q->xy == nullptr;
   p.s_grid = s->xy == nullptr;
   size_t off = 0;

@@ -376,6 +376,38 @@ __global__ void __launch_bounds__(kRtThreads, 5) raytrace_kernel(const __grid_co
   raytrace_body<PROFILE>(L, g, xi, n, sub, n_sub, bulk_ok, beta, alpha_out, fault, blockIdx.x, sm);
 }
 
+// The same with the lens read from a device record (lr_lens_prepare); an
+// invalid record is reported in the fault word.
+template <int PROFILE>
+__global__ void __launch_bounds__(kRtThreads, 5) raytrace_rec_kernel(const LensRecord* __restrict__ rec, GridDev g,
+                                                                  const float2* __restrict__ xi, int64_t n,
+                                                                  const float* __restrict__ sub, int n_sub,
+                                                                  int bulk_ok, float2* __restrict__ beta,
+                                                                  float2* __restrict__ alpha_out, int* fault) {
+  __shared__ __align__(16) RtSmem sm;
+  if (rec->status != 0 && blockIdx.x == 0 && threadIdx.x == 0) atomicExch(fault, kFaultBadLens);
+  raytrace_body<PROFILE>(rec->L, g, xi, n, sub, n_sub, bulk_ok, beta, alpha_out, fault, blockIdx.x, sm);
+}
+
+__global__ void lens_prepare_kernel(const float* __restrict__ theta7, float gamma, LensRecord* __restrict__ rec) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const float p[8] = {theta7[0], theta7[1], theta7[2], theta7[3], theta7[4], gamma, theta7[5], theta7[6]};
+  LensRecord r;
+  r.status = lens_constants(p, &r.L, &r.G);
+  if (r.status != 0) {
+    // rejected parameters: a lens that deflects nothing, so that every loop
+    // over the series coefficients stays within its arrays
+    for (int k = 0; k < kMaxSeriesTerms; ++k) r.L.d[k] = r.G.hco[k] = 0.f;
+    r.L.x0 = r.L.y0 = r.L.s = r.L.pre = r.L.half_expo = r.L.g1 = r.L.g2 = 0.f;
+    r.L.c = r.L.sq = r.L.isq = 1.f;
+    r.L.nterms = r.G.nterms = 1;
+    r.L.pad_ = r.G.pad_ = 0;
+    r.G.e = r.G.f = r.G.dlnpre_dq = r.G.df_dq = r.G.inv2q = r.G.dlnte = 0.f;
+  }
+  r.pad_[0] = r.pad_[1] = r.pad_[2] = 0;
+  *rec = r;
+}
+
 __global__ void __launch_bounds__(kRtThreads, 5) raytrace_batched_kernel(const __grid_constant__ Batch<RtP> B,
                                                                       int* fault) {
   __shared__ __align__(16) RtSmem sm;
@@ -428,35 +460,9 @@ lr_status make_lens_const(const lr_lens* lens, LensConst* out) {
   LR_REQUIRE(lens->q > 0.f && lens->q <= 1.f, "lens q = %g outside (0, 1]", (double)lens->q);
   LR_REQUIRE(lens->gamma > 1.f && lens->gamma < 3.f, "lens gamma = %g outside (1, 3)", (double)lens->gamma);
   LR_REQUIRE(lens->theta_e >= 0.f, "lens theta_e = %g < 0", (double)lens->theta_e);
-  const double q = lens->q, gam = lens->gamma, te = lens->theta_e, phi = lens->phi;
-  LensConst L;
-  memset(&L, 0, sizeof L);
-  L.x0 = lens->x0;
-  L.y0 = lens->y0;
-  L.c = (float)cos(phi);
-  L.s = (float)sin(phi);
-  L.sq = (float)sqrt(q);
-  L.isq = (float)(1.0 / sqrt(q));
-  L.pre = (float)(pow(te, gam - 1.0) * 2.0 * sqrt(q) / (1.0 + q));
-  L.half_expo = (float)(0.5 * (1.0 - gam));
-  L.g1 = lens->g1;
-  L.g2 = lens->g2;
-  // 2F1(1, a; b; -f w) = sum_n c_n (-f)^n w^n, c_n = prod_{k<=n} (a+k-1)/(b+k-1)
-  const double a = 0.5 * (gam - 1.0), b = 0.5 * (5.0 - gam), fq = (1.0 - q) / (1.0 + q);
-  double c = 1.0, fn = 1.0;
-  int n = 0;
-  L.d[0] = 1.0f;
-  for (n = 1; n < kMaxSeriesTerms; ++n) {
-    // tail bound: |d_n| f / (1 - f) (coefficient ratios are below 1 for gamma < 3)
-    if (fq == 0.0 || fabs(c * fn) * fq / (1.0 - fq) < 1e-9) break;
-    c *= (a + n - 1.0) / (b + n - 1.0);
-    fn *= -fq;
-    L.d[n] = (float)(c * fn);
-  }
-  LR_REQUIRE(fq == 0.0 || fabs(c * fn) * fq / (1.0 - fq) < 1e-9,
-             "lens q = %g too small: the deflection series needs more than %d terms", q, kMaxSeriesTerms);
-  L.nterms = n;
-  *out = L;
+  const int st = lens_constants(f, out, nullptr);
+  LR_REQUIRE(st == 0, "lens q = %g too small: the deflection series needs more than %d terms", (double)lens->q,
+             kMaxSeriesTerms);
   return LR_OK;
 }
 
@@ -479,8 +485,9 @@ lr_status validate_points(const lr_points* p, const char* what, bool need_lens) 
   } else {
     LR_REQUIRE(((uintptr_t)p->xy & 7u) == 0, "%s: xy must be 8-byte aligned", what);
   }
-  if (need_lens) LR_REQUIRE(p->lens != nullptr, "%s: a lens is required", what);
-  if (p->lens) {
+  if (need_lens) LR_REQUIRE(has_lens(p), "%s: a lens is required", what);
+  LR_REQUIRE(((uintptr_t)p->lens_record & 15u) == 0, "%s: lens_record must be 16-byte aligned", what);
+  if (has_lens(p)) {
     LR_REQUIRE(p->n_sub >= 0, "%s: n_sub < 0", what);
     LR_REQUIRE(p->n_sub == 0 || p->sub != nullptr, "%s: sub is NULL with n_sub = %d", what, p->n_sub);
     LR_REQUIRE(p->sub == nullptr || ((uintptr_t)p->sub & 3u) == 0, "%s: sub must be 4-byte aligned", what);
@@ -500,8 +507,11 @@ lr_status launch_grid_points(const lr_grid& g, float2* out, cudaStream_t s) {
 
 lr_status launch_raytrace(const lr_points* p, float2* beta, float2* alpha, cudaStream_t s) {
   LensConst L;
-  lr_status st = make_lens_const(p->lens, &L);
-  if (st != LR_OK) return st;
+  const auto* rec = static_cast<const LensRecord*>(p->lens_record);
+  if (!rec) {
+    lr_status st = make_lens_const(p->lens, &L);
+    if (st != LR_OK) return st;
+  }
   if (p->n == 0) return LR_OK;
   int* fault = fault_ptr();
   LR_REQUIRE(fault != nullptr, "could not resolve the device fault word");
@@ -511,7 +521,13 @@ lr_status launch_raytrace(const lr_points* p, float2* beta, float2* alpha, cudaS
   const float2* xi = reinterpret_cast<const float2*>(p->xy);
   const int ns = p->n_sub;
   ktimer_begin(LR_KT_RAYTRACE, s);
-  if (p->profile == LR_PROFILE_POINT_MASS)
+  if (rec && p->profile == LR_PROFILE_POINT_MASS)
+    raytrace_rec_kernel<LR_PROFILE_POINT_MASS><<<blocks, kRtThreads, 0, s>>>(rec, g, xi, p->n, p->sub, ns, bulk_ok,
+                                                                             beta, alpha, fault);
+  else if (rec)
+    raytrace_rec_kernel<LR_PROFILE_TNFW><<<blocks, kRtThreads, 0, s>>>(rec, g, xi, p->n, p->sub, ns, bulk_ok, beta,
+                                                                       alpha, fault);
+  else if (p->profile == LR_PROFILE_POINT_MASS)
     raytrace_kernel<LR_PROFILE_POINT_MASS><<<blocks, kRtThreads, 0, s>>>(L, g, xi, p->n, p->sub, ns, bulk_ok, beta,
                                                                          alpha, fault);
   else
@@ -523,6 +539,7 @@ lr_status launch_raytrace(const lr_points* p, float2* beta, float2* alpha, cudaS
 }
 
 lr_status make_rt_problem(const lr_points* p, float2* beta, float2* alpha, RtP* R) {
+  LR_REQUIRE(p->lens_record == nullptr, "batched ray-trace problems take a host lens");
   RtP r{};
   lr_status st = make_lens_const(p->lens, &r.L);
   if (st != LR_OK) return st;
@@ -557,4 +574,16 @@ extern "C" lr_status lr_grid_points(const lr_grid* grid, float* out, lr_stream s
   LR_REQUIRE(out != nullptr || lr::grid_count(*grid) == 0, "lr_grid_points: out is NULL");
   LR_REQUIRE(((uintptr_t)out & 7u) == 0, "lr_grid_points: out must be 8-byte aligned");
   return lr::launch_grid_points(*grid, reinterpret_cast<float2*>(out), lr::as_cuda(stream));
+}
+
+extern "C" size_t lr_lens_record_bytes(void) { return sizeof(lr::LensRecord); }
+
+extern "C" lr_status lr_lens_prepare(const float* theta7, float gamma, void* record, lr_stream stream) {
+  LR_REQUIRE(theta7 != nullptr && record != nullptr, "lr_lens_prepare: NULL argument");
+  LR_REQUIRE(((uintptr_t)theta7 & 3u) == 0 && ((uintptr_t)record & 15u) == 0,
+             "lr_lens_prepare: misaligned pointer (theta7: 4 bytes, record: 16 bytes)");
+  LR_REQUIRE(gamma > 1.f && gamma < 3.f, "lr_lens_prepare: gamma = %g outside (1, 3)", (double)gamma);
+  lr::lens_prepare_kernel<<<1, 32, 0, lr::as_cuda(stream)>>>(theta7, gamma, static_cast<lr::LensRecord*>(record));
+  LR_CHECK_CUDA(cudaGetLastError());
+  return LR_OK;
 }

@@ -24,6 +24,7 @@
 
 #include "host.cuh"
 #include "problems.cuh"
+#include "tma.cuh"
 
 namespace lr {
 
@@ -283,6 +284,21 @@ __global__ void __launch_bounds__(kVjThreads, 4) raytrace_vjp_kernel(const __gri
                     sm);
 }
 
+// The same with the lens read from a device record (lr_lens_prepare).
+template <int PROFILE>
+__global__ void __launch_bounds__(kVjThreads, 4) raytrace_vjp_rec_kernel(const LensRecord* __restrict__ rec, GridDev g,
+                                                                      const float2* __restrict__ xi, int64_t n,
+                                                                      const float* __restrict__ sub, int n_sub, int P,
+                                                                      const float2* __restrict__ dbeta,
+                                                                      double* __restrict__ lens_part,
+                                                                      float* __restrict__ sub_part,
+                                                                      float* __restrict__ slot_part, int* fault) {
+  __shared__ __align__(16) VjSmem sm;
+  if (rec->status != 0 && blockIdx.x == 0 && threadIdx.x == 0) atomicExch(fault, kFaultBadLens);
+  vjp_body<PROFILE>(rec->L, rec->G, g, xi, n, sub, n_sub, P, dbeta, lens_part, sub_part, slot_part, blockIdx.x,
+                    gridDim.x, sm);
+}
+
 __global__ void __launch_bounds__(kVjThreads, 4) vjp_batched_kernel(const __grid_constant__ Batch<VjpP> B) {
   __shared__ __align__(16) VjSmem sm;
   const int k = batch_find(B, blockIdx.x);
@@ -419,34 +435,9 @@ lr_status launch_vjp_final_batched(const VjpFinalP* p, int count, cudaStream_t s
 // Host side
 
 lr_status make_lens_grad_const(const lr_lens* lens, LensGradConst* out) {
-  const double q = lens->q, gam = lens->gamma, te = lens->theta_e;
-  LensGradConst G;
-  memset(&G, 0, sizeof G);
-  G.e = (float)(0.5 * (1.0 - gam));
-  const double f = (1.0 - q) / (1.0 + q);
-  G.f = (float)f;
-  G.dlnpre_dq = (float)(0.5 / q - 1.0 / (1.0 + q));
-  G.df_dq = (float)(-2.0 / ((1.0 + q) * (1.0 + q)));
-  G.inv2q = (float)(0.5 / q);
-  G.dlnte = te > 0.0 ? (float)((gam - 1.0) / te) : 0.f;
-  // h_n = (n+1) c_{n+1} (-f)^n, c_n = prod_{k<=n} (a+k-1)/(b+k-1)
-  const double a = 0.5 * (gam - 1.0), b = 0.5 * (5.0 - gam);
-  double c = 1.0, fn = 1.0;  // c_{n+1}, (-f)^n
-  int n = 0;
-  for (n = 0; n < kMaxSeriesTerms; ++n) {
-    c *= (a + n) / (b + n);  // c_{n+1}
-    const double hn = (n + 1.0) * c * fn;
-    G.hco[n] = (float)hn;
-    // tail bound for sum_{k>n} |h_k|: |h_n| f (n+2)/(n+1) / (1 - f)^2
-    if (f == 0.0 || fabs(hn) * f * (n + 2.0) / (n + 1.0) / ((1.0 - f) * (1.0 - f)) < 1e-9) {
-      ++n;
-      break;
-    }
-    fn *= -f;
-  }
-  LR_REQUIRE(n <= kMaxSeriesTerms, "lens q = %g too small for the gradient series", q);
-  G.nterms = n < 1 ? 1 : n;
-  *out = G;
+  LR_REQUIRE(lens != nullptr, "lens is NULL");
+  const int st = lens_constants(&lens->x0, nullptr, out);
+  LR_REQUIRE(st == 0, "lens q = %g outside its domain or too small for the gradient series", (double)lens->q);
   return LR_OK;
 }
 
@@ -478,12 +469,15 @@ size_t raytrace_vjp_ws(int64_t n, int32_t n_sub) { return vjp_ws_layout(nullptr,
 
 lr_status launch_raytrace_vjp(const lr_points* p, const float2* dbeta, double* d_lens, double* d_sub, void* ws,
                               cudaStream_t s) {
-  LensConst L;
-  lr_status st = make_lens_const(p->lens, &L);
-  if (st != LR_OK) return st;
-  LensGradConst G;
-  st = make_lens_grad_const(p->lens, &G);
-  if (st != LR_OK) return st;
+  LensConst L{};
+  LensGradConst G{};
+  const auto* rec = static_cast<const LensRecord*>(p->lens_record);
+  if (!rec) {
+    lr_status st = make_lens_const(p->lens, &L);
+    if (st != LR_OK) return st;
+    st = make_lens_grad_const(p->lens, &G);
+    if (st != LR_OK) return st;
+  }
   const int64_t nblk = vjp_blocks(p->n);
   if (nblk == 0) {
     if (d_lens) LR_CHECK_CUDA(cudaMemsetAsync(d_lens, 0, 7 * sizeof(double), s));
@@ -496,8 +490,16 @@ lr_status launch_raytrace_vjp(const lr_points* p, const float2* dbeta, double* d
   const GridDev g = p->xy ? GridDev{} : grid_dev(p->grid);
   const float2* xi = reinterpret_cast<const float2*>(p->xy);
   const int P = vjp_phases(p->n, p->n_sub);
+  int* fault = fault_ptr();
+  LR_REQUIRE(fault != nullptr, "could not resolve the device fault word");
   ktimer_begin(LR_KT_RAYTRACE_VJP, s);
-  if (p->profile == LR_PROFILE_POINT_MASS)
+  if (rec && p->profile == LR_PROFILE_POINT_MASS)
+    raytrace_vjp_rec_kernel<LR_PROFILE_POINT_MASS><<<(unsigned)nblk, kVjThreads, 0, s>>>(
+        rec, g, xi, p->n, p->sub, p->n_sub, P, dbeta, lens_part, sub_part, w.slot_part, fault);
+  else if (rec)
+    raytrace_vjp_rec_kernel<LR_PROFILE_TNFW><<<(unsigned)nblk, kVjThreads, 0, s>>>(
+        rec, g, xi, p->n, p->sub, p->n_sub, P, dbeta, lens_part, sub_part, w.slot_part, fault);
+  else if (p->profile == LR_PROFILE_POINT_MASS)
     raytrace_vjp_kernel<LR_PROFILE_POINT_MASS><<<(unsigned)nblk, kVjThreads, 0, s>>>(
         L, G, g, xi, p->n, p->sub, p->n_sub, P, dbeta, lens_part, sub_part, w.slot_part);
   else
@@ -516,6 +518,7 @@ lr_status launch_raytrace_vjp(const lr_points* p, const float2* dbeta, double* d
 // the per-CTA partials.
 lr_status make_vjp_problem(const lr_points* p, const float2* dbeta, double* d_lens, double* d_sub, void* ws, VjpP* V,
                            VjpFinalP* F) {
+  LR_REQUIRE(p->lens_record == nullptr, "batched ray-trace VJP problems take a host lens");
   VjpP v{};
   lr_status st = make_lens_const(p->lens, &v.L);
   if (st != LR_OK) return st;

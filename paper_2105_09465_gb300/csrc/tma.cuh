@@ -8,7 +8,7 @@
 namespace lr {
 
 // Fault codes written to the library's device fault word.
-enum : int { kFaultNone = 0, kFaultBarrierTimeout = 1 };
+enum : int { kFaultNone = 0, kFaultBarrierTimeout = 1, kFaultBadLens = 2 };
 
 // ~1 s at 2 GHz: far above any legitimate copy latency.
 constexpr long long kWaitBudgetCycles = 2000000000LL;

@@ -248,7 +248,7 @@ struct WnPlan {
 static lr_status plan_windowed(int64_t n, const lr_points* s, WnPlan* P) {
   lr_status st = validate_points(s, "gp_windowed_matvec(source)", false);
   if (st != LR_OK) return st;
-  LR_REQUIRE(s->lens == nullptr, "gp_windowed_matvec: sources must not carry a lens");
+  LR_REQUIRE(!has_lens(s), "gp_windowed_matvec: sources must not carry a lens");
   LR_REQUIRE(n >= 0 && n < (int64_t(1) << 31), "gp_windowed_matvec: n out of range");
   WnPlan p{};
   if (s->xy == nullptr) {

@@ -413,7 +413,7 @@ struct WbPlan {
 static lr_status plan_windowed_bwd(int64_t n, const lr_points* s, WbPlan* P) {
   lr_status st = validate_points(s, "gp_windowed_matvec_bwd(source)", false);
   if (st != LR_OK) return st;
-  LR_REQUIRE(s->lens == nullptr && s->xy != nullptr, "gp_windowed_matvec_bwd: sources must be explicit points");
+  LR_REQUIRE(!has_lens(s) && s->xy != nullptr, "gp_windowed_matvec_bwd: sources must be explicit points");
   LR_REQUIRE(n >= 0 && n < (int64_t(1) << 31), "gp_windowed_matvec_bwd: n out of range");
   const int64_t m = s->n;
   WbPlan p{};

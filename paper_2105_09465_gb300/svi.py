@@ -18,12 +18,13 @@ Model for one draw:
 The lens priors are uniform (constant inside their domain) and left out;
 the transmission weights A_k are held fixed within a step.
 
-The pair sweeps, draws, log densities and their VJPs run in the library's
-CUDA kernels. This module orders the calls, moves the 7 drawn lens
-parameters to the host (the ray-trace takes them as a parameter struct) and
-does a few elementwise steps in torch: the weight scaling (A y), the sum of
-the layers' fluxes, the accumulation of dL/dbeta over the layers and the
-source-plane prior gradient y_sp / alpha^2.
+Every numerical step runs in the library's CUDA kernels, the elementwise
+ones (A y, the sum of the layers, dL/dbeta summed over the layers, the
+source-plane prior gradient y_sp / alpha^2, the loss's sum of terms)
+included; the 7 drawn lens parameters stay on the device (lens_prepare turns
+them into the ray-trace's lens record). This module only orders the calls
+and allocates their outputs; nothing is copied to the host, so a step can be
+timed with CUDA events or captured in a graph.
 """
 from __future__ import annotations
 
@@ -68,70 +69,89 @@ def lens_from(theta: list[float], gamma: float) -> Lens:
     return Lens(x0, y0, q, phi, te, gamma, g1, g2)
 
 
+_UNIT = {}
+
+
+def _unit_draw(M: int, dev) -> tuple[torch.Tensor, torch.Tensor]:
+    """(ones, zeros) of length M: the draw y = y_sp with sd 1 and eps 0 gives
+    the source-plane prior term -ln p(y_sp | alpha_sp)."""
+    key = (M, str(dev))
+    if key not in _UNIT:
+        _UNIT[key] = (torch.ones(M, device=dev), torch.zeros(M, device=dev))
+    return _UNIT[key]
+
+
 def loss_and_grads(cfg: ModelConfig, guide: Guide, data: torch.Tensor, eps_sp: torch.Tensor,
-                   eps_layers: list[torch.Tensor]) -> tuple[float, dict]:
-    """Loss of one reparameterised draw (given the standard-normal draws) and
-    its gradients with respect to every guide parameter."""
+                   eps_layers: list[torch.Tensor]) -> tuple[torch.Tensor, dict]:
+    """Loss of one reparameterised draw (given the standard-normal draws), as
+    a (1,) float64 device tensor, and its gradients with respect to every
+    guide parameter."""
     dev = data.device
     M = guide.sd_sp.numel()
+    W, H = cfg.pixels.nx, cfg.pixels.ny
     # ---- draws and their log densities
     x, logq_sp = api.partial_mvn_draw(guide.mu, guide.L, guide.C, guide.sd_sp, eps_sp)
-    theta = x[:N_LENS].double().cpu().tolist()
-    y_sp = x[N_LENS:].contiguous()
-    lens = lens_from(theta, cfg.gamma)
+    lens_rec = api.lens_prepare(x[:N_LENS], cfg.gamma)
+    y_sp = x[N_LENS:]
     ys, terms = [], []
     for mu, sd, e, a in zip(guide.mu_layers, guide.sd_layers, eps_layers, cfg.alpha_layers):
         y, t = api.diag_normal_draw(mu, sd, e, a)
         ys.append(y)
         terms.append(t)
-    ones_sp = torch.ones(M, device=dev)
-    _, prior_sp = api.diag_normal_draw(y_sp, ones_sp, torch.zeros(M, device=dev), cfg.alpha_sp)
+    ones_sp, zeros_sp = _unit_draw(M, dev)
+    _, prior_sp = api.diag_normal_draw(y_sp, ones_sp, zeros_sp, cfg.alpha_sp)
 
     # ---- forward
-    pix = api.Points(grid=cfg.pixels, lens=lens)
+    pix = api.Points(grid=cfg.pixels, lens_record=lens_rec)
     beta = api.lens_raytrace(pix)
     h = cfg.source_grid.pix / cfg.source_grid.ss
     a_sp = math.sqrt(2.0 * math.pi) * cfg.sigma_sp * h / (math.pi * cfg.sigma_sp ** 2)  # A |pi Sigma|^-1/2
     src = api.Points(grid=cfg.source_grid)
-    w_sp = (a_sp * y_sp).contiguous()
+    w_sp = api.vec_axpby(a_sp, y_sp)
     f = api.gp_kernel_matvec(api.Points(xy=beta), src, w_sp, cfg.sigma_sp / math.sqrt(2.0), 1.0)
-    z = api.pixel_shapes(beta, cfg.pixels.nx, cfg.pixels.ny)
+    z = api.pixel_shapes(beta, W, H)
     self_pts = api.Points(xy=beta)
     a_layers, w_layers = [], []
     for y, s in zip(ys, cfg.sigma_layers):
         a_k = api.knn_density(beta, cfg.knn_k, lengthscale=s, want_r2=False)
-        w = (a_k * y).contiguous()
-        f = f + api.gp_windowed_matvec(beta, z, self_pts, w, s)
+        w = api.vec_mul(a_k, y)
+        api.vec_axpby(1.0, f, 1.0, api.gp_windowed_matvec(beta, z, self_pts, w, s), out=f)
         a_layers.append(a_k)
         w_layers.append(w)
-    nll, g, _ = api.gaussian_nll(f.contiguous(), data, cfg.noise)
+    nll, g, _ = api.gaussian_nll(f, data, cfg.noise)
 
-    # ---- backward
-    d_beta = torch.zeros_like(beta)
-    d_z = torch.zeros_like(z)
+    # ---- backward: dL/dbeta summed over the layers (in place)
+    d_beta = d_z = None
     grads = {"layers_mu": [], "layers_sd": []}
     for y, s, a_k, w, mu, sd, e, al in zip(ys, cfg.sigma_layers, a_layers, w_layers, guide.mu_layers,
                                            guide.sd_layers, eps_layers, cfg.alpha_layers):
         G = api.gp_windowed_matvec_bwd(beta, z, self_pts, w, s, g, want=("v", "p", "q", "z"))
-        d_beta += G["p"] + G["q"]
-        d_z += G["z"]
-        d_y = (a_k * G["v"]).contiguous()
-        d_mu, d_sd, _ = api.diag_normal_vjp(mu, sd, e, al, d_y, 1.0, 1.0)
+        if d_beta is None:
+            d_beta = api.vec_axpby(1.0, G["p"], 1.0, G["q"])
+            d_z = G["z"]
+        else:
+            api.vec_axpby(1.0, d_beta, 1.0, G["p"], out=d_beta)
+            api.vec_axpby(1.0, d_beta, 1.0, G["q"], out=d_beta)
+            api.vec_axpby(1.0, d_z, 1.0, G["z"], out=d_z)
+        d_mu, d_sd, _ = api.diag_normal_vjp(mu, sd, e, al, api.vec_mul(a_k, G["v"]), 1.0, 1.0)
         grads["layers_mu"].append(d_mu)
         grads["layers_sd"].append(d_sd)
-    d_beta += api.pixel_shapes_vjp(beta, cfg.pixels.nx, cfg.pixels.ny, d_z.contiguous())
     Gs = api.gp_kernel_matvec_bwd(api.Points(xy=beta), src, w_sp, cfg.sigma_sp / math.sqrt(2.0), 1.0, g,
                                   want=("v", "x"))
-    d_beta += Gs["x"]
-    d_lens, _ = api.lens_raytrace_vjp(pix, d_beta.contiguous())
-    # the source-plane layer's prior: d(-ln p)/dy_sp = y_sp / alpha^2
-    d_ysp = a_sp * Gs["v"] + y_sp / (cfg.alpha_sp ** 2)
-    d_x = torch.cat([d_lens.float(), d_ysp]).contiguous()
+    if d_beta is None:
+        d_beta = api.vec_axpby(1.0, Gs["x"])
+    else:
+        api.vec_axpby(1.0, d_beta, 1.0, api.pixel_shapes_vjp(beta, W, H, d_z), out=d_beta)
+        api.vec_axpby(1.0, d_beta, 1.0, Gs["x"], out=d_beta)
+    d_lens, _ = api.lens_raytrace_vjp(pix, d_beta)
+    # the source-plane layer's weights and its prior: d(-ln p)/dy_sp = y_sp / alpha^2
+    d_ysp = api.vec_axpby(a_sp, Gs["v"], 1.0 / cfg.alpha_sp ** 2, y_sp)
+    d_x = api.vec_pack(d_lens, d_ysp)
     d_mu, d_L, d_C, d_sd = api.partial_mvn_vjp(guide.L, guide.sd_sp, eps_sp, d_x, 1.0)
     grads.update(mu=d_mu, L=d_L, C=d_C, sd_sp=d_sd, d_lens=d_lens, d_beta=d_beta)
 
-    loss = float(nll) + float(prior_sp[0]) + float(logq_sp)
+    parts = [nll.reshape(1), prior_sp[0:1], logq_sp.reshape(1)]
     for t in terms:
-        tt = t.cpu()
-        loss += float(tt[0]) + float(tt[1])
+        parts += [t[0:1], t[1:2]]
+    loss = api.sum_scalars(parts)
     return loss, grads

@@ -40,7 +40,8 @@ def test_svi_step_matches_the_oracle(orc):
            for k, v in guide.items()}
     ref, R = osvi.loss_and_grads(orc, cfg, g64, data, eps_sp, eps_l)
     # an FP32 chain (ray-trace, three reductions, windows) against FP64
-    assert loss == pytest.approx(ref, rel=1e-5)
+    assert loss.dtype == torch.float64 and loss.is_cuda
+    assert float(loss.item()) == pytest.approx(ref, rel=1e-5)
     close(host(G["d_lens"]), R["d_lens"], 2e-4, "d_lens")
     close(host(G["mu"]), R["mu"], 2e-4, "d_mu")
     close(host(G["L"]), R["L"], 2e-4, "d_L")
