@@ -463,15 +463,27 @@ def run_extensions(p, dev, rates, sm_max, flush, stream) -> dict:
                                         workload=f"{pix.nx}x{pix.ny} ray-traced pixel centres with their "
                                                  f"window covariances x {p.ygrid.nx}x{p.ygrid.ny} grid")
     out["pixel_shapes"] = {"ms": event_time(lambda: api.pixel_shapes(bp, pix.nx, pix.ny), nk, stream, flush)}
-    # the image-plane layer: the pixels' own windowed reduction (explicit sources = the pixels)
+    # the image-plane layer: the pixels' own windowed reduction (explicit
+    # sources = the pixels, in their image layout), at the workloads' 0.05
+    # arcsec and at the paper's narrowest image-plane kernel, 2 mas; pairs
+    # whose exponent is below -126 are skipped, so the roofline counts the
+    # evaluated pairs (forward 8 lanes, backward rows 16, columns 12 per pair)
     vp = torch.randn(pix.n, generator=torch.Generator().manual_seed(6)).to(dev)
     gp = torch.randn(pix.n, generator=torch.Generator().manual_seed(7)).to(dev)
-    selfp = api.Points(xy=bp)
-    ms = event_time(lambda: api.gp_windowed_matvec(bp, z, selfp, vp, 0.05), 5, stream, flush)
-    out["windowed_matvec<explicit> image-plane layer"] = dict(roof(pix.n * pix.n, ms, 1, 8), n=pix.n, m=pix.n)
-    ms = event_time(lambda: api.gp_windowed_matvec_bwd(bp, z, selfp, vp, 0.05, gp), 3, stream, flush)
-    out["windowed backward (rows + columns) image-plane layer"] = dict(
-        roof(2 * pix.n * pix.n, ms, 1, 15), note="two sweeps; pairs counted per sweep; ~17 and ~13 lanes per pair")
+    selfp = api.Points(xy=bp, grid=pix)
+    for ell in (0.05, 0.002):
+        ev = [api.windowed_pairs_evaluated(bp, z, selfp, ell, sw, layout=pix)[0] for sw in (0, 1, 2)]
+        ms = event_time(lambda: api.gp_windowed_matvec(bp, z, selfp, vp, ell, layout=pix), nk, stream, flush)
+        out[f"windowed_matvec<explicit> image-plane layer l={ell}"] = dict(
+            roof(ev[0], ms, 1, 8), n=pix.n, m=pix.n, logical_pairs=pix.n * pix.n, evaluated_pairs=ev[0])
+        ms = event_time(lambda: api.gp_windowed_matvec_bwd(bp, z, selfp, vp, ell, gp, layout=pix), nk, stream,
+                        flush)
+        rr, rc = roof(ev[1], 1.0, 1, 16), roof(ev[2], 1.0, 1, 12)
+        bound_ms = ev[1] / (rr["peak"] * 1e9) * 1e3 + ev[2] / (rc["peak"] * 1e9) * 1e3
+        out[f"windowed backward (rows + columns) image-plane layer l={ell}"] = {
+            "ms": ms, "frac": bound_ms / ms, "evaluated_pairs": {"rows": ev[1], "columns": ev[2]},
+            "logical_pairs": 2 * pix.n * pix.n,
+            "basis": "time at the FMA bound of both sweeps (16 and 12 lanes per evaluated pair) / measured"}
     # one SVI step of the model at this size: every step on the device, no host wait inside
     from paper_2105_09465_gb300 import svi
     mc = svi.ModelConfig(pixels=pix, source_grid=p.ygrid, sigma_sp=p.lengthscale * 1.4142135, sigma_layers=[0.05],

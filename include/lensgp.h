@@ -306,11 +306,19 @@ lr_status gp_pixel_shapes(const float* p, int32_t W, int32_t H, float* z, lr_str
  * (device float[n][3], from gp_pixel_shapes; zeros give point pixels) and
  * sources q (explicit or grid, no lens). The caller folds the transmission
  * weights A_k into v_k. Workspace of lr_windowed_workspace_size() bytes.
+ *   layout  NULL, or the image grid the n query points come from (row-major,
+ *           nx*ss x ny*ss == n; only its shape is read): the sweeps then take
+ *           the rows in compact image tiles. Explicit sources are ordered the
+ *           same way when source->grid describes them (lr_points).
+ * Explicit sources: pairs whose exponent is below -126 (they contribute
+ * exactly 0 in FP32) are skipped by bounding boxes, with the reach of each
+ * row's widest window direction; lr_set_pair_culling(0) evaluates them all,
+ * with bitwise the same results.
  */
-lr_status gp_windowed_matvec(const float* p, const float* z, int64_t n, const lr_points* source, const float* v,
-                             float lengthscale, float* out, void* workspace, size_t workspace_bytes,
-                             lr_stream stream);
-lr_status lr_windowed_workspace_size(int64_t n, const lr_points* source, size_t* bytes);
+lr_status gp_windowed_matvec(const float* p, const float* z, int64_t n, const lr_grid* layout,
+                             const lr_points* source, const float* v, float lengthscale, float* out, void* workspace,
+                             size_t workspace_bytes, lr_stream stream);
+lr_status lr_windowed_workspace_size(int64_t n, const lr_grid* layout, const lr_points* source, size_t* bytes);
 
 /*
  * Gradients of Loss = sum_i g_i out_i through gp_windowed_matvec
@@ -327,12 +335,25 @@ lr_status lr_windowed_workspace_size(int64_t n, const lr_points* source, size_t*
  * For an image-plane layer with q = p the total gradient of a point is
  * d_p + d_q + gp_pixel_shapes_vjp(d_z). Every output may be NULL; the row
  * sweep runs for d_p, d_z or d_lengthscale, the column sweep for d_v or d_q.
- * Workspace of lr_windowed_bwd_workspace_size() bytes, 256-byte aligned.
+ * `layout` and the skipping of exact zeros as for gp_windowed_matvec (both
+ * sweeps). Workspace of lr_windowed_bwd_workspace_size() bytes, 256-byte
+ * aligned.
  */
-lr_status gp_windowed_matvec_bwd(const float* p, const float* z, int64_t n, const lr_points* source, const float* v,
-                                 float lengthscale, const float* g, float* d_v, float* d_p, float* d_q, float* d_z,
-                                 double* d_lengthscale, void* workspace, size_t workspace_bytes, lr_stream stream);
-lr_status lr_windowed_bwd_workspace_size(int64_t n, const lr_points* source, size_t* bytes);
+lr_status gp_windowed_matvec_bwd(const float* p, const float* z, int64_t n, const lr_grid* layout,
+                                 const lr_points* source, const float* v, float lengthscale, const float* g,
+                                 float* d_v, float* d_p, float* d_q, float* d_z, double* d_lengthscale,
+                                 void* workspace, size_t workspace_bytes, lr_stream stream);
+lr_status lr_windowed_bwd_workspace_size(int64_t n, const lr_grid* layout, const lr_points* source, size_t* bytes);
+
+/*
+ * Diagnostic: the pairs the windowed sweeps over explicit sources evaluate
+ * (sweep 0: gp_windowed_matvec; 1: the backward's row sweep; 2: its column
+ * sweep), counted like lr_cull_pairs_evaluated. Synchronises the stream;
+ * allocates and frees its own temporary device memory.
+ */
+lr_status lr_windowed_pairs_evaluated(const float* p, const float* z, int64_t n, const lr_grid* layout,
+                                      const lr_points* source, float lengthscale, int32_t sweep, int64_t* pairs,
+                                      int64_t* slots, lr_stream stream);
 
 /*
  * Gradient through gp_pixel_shapes: dp (device float[W*H][2], overwritten)

@@ -83,6 +83,7 @@ def lib():
         L.orc_windowed_matvec.argtypes = [_P, _P, _I64, _P, _I64, _P, _D, _P, _P, _P]
         L.orc_knn_r2.argtypes = [_P, _I64, _I32, _P, _I64, _P]
         L.orc_windowed_vjp.argtypes = [_P, _P, _I64, _P, _I64, _P, _D, _P] + [_P] * 10
+        L.orc_windowed_rounding.argtypes = [_P, _P, _I64, _P, _I64, _P, _D, _P] + [_P] * 6
         L.orc_pixel_shapes_vjp.argtypes = [_P, _I32, _I32, _P, _P]
         L.orc_kernel_matvec.argtypes = [_P, _I64, _P, _I64, _P, _D, _D, _P, _I64, _P, _P, _P]
         L.orc_kernel_matvec_vjp.argtypes = [_P, _I64, _P, _I64, _P, _D, _D, _P, _I32, _P, _P, _P, _P, _P, _P]
@@ -223,6 +224,24 @@ def windowed_vjp(p, z, q, v, lengthscale, g, with_abs=False):
         A["d_len_abs"] = float(A["d_len_abs"][0])
         R.update(A)
     return R
+
+
+def windowed_rounding(p, z, q, v, lengthscale, g=None):
+    """FP32 rounding sensitivities (in units of u = 2^-24) of windowed_matvec
+    and windowed_vjp: dict s_out (n), s_v (m), s_p (n, 2), s_q (m, 2),
+    s_z (n, 3), s_len; the gradient entries need g. Test infrastructure: a
+    tolerance term, not the method."""
+    p, q = _pairs(p), _pairs(q)
+    z = np.ascontiguousarray(z, np.float64)
+    v = np.ascontiguousarray(v, np.float64).reshape(-1)
+    g = None if g is None else np.ascontiguousarray(g, np.float64).reshape(-1)
+    n, m = p.shape[0], q.shape[0]
+    S = {"s_out": np.empty(n), "s_v": np.empty(m), "s_p": np.empty((n, 2)), "s_q": np.empty((m, 2)),
+         "s_z": np.empty((n, 3)), "s_len": np.empty(1)}
+    lib().orc_windowed_rounding(_ptr(p), _ptr(z), n, _ptr(q), m, _ptr(v), lengthscale, _ptr(g),
+                                *[_ptr(S[k]) for k in ("s_out", "s_v", "s_p", "s_q", "s_z", "s_len")])
+    S["s_len"] = float(S["s_len"][0])
+    return S
 
 
 def pixel_shapes_vjp(p, W, H, dz):

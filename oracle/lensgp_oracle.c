@@ -591,11 +591,16 @@ ORC_API void orc_windowed_vjp(const double* p, const double* z, int64_t n, const
       ns_add(&zxx, cx);
       ns_add(&zxy, 2.0 * cxy2);
       ns_add(&zyy, cy);
-      azxx += fabs(cx);
-      azxy += 2.0 * fabs(cxy2);
-      azyy += fabs(cy);
+      /* scales: both parts of u u^T - M, which nearly cancel for a pair at
+       * d^T M d ~ 1 */
+      const double hg = 0.5 * fabs(gGv);
+      const double sx = hg * (ux * ux + fabs(mxx)), sxy = hg * (fabs(ux * uy) + fabs(mxy)),
+                   sy = hg * (uy * uy + fabs(myy));
+      azxx += sx;
+      azxy += 2.0 * sxy;
+      azyy += sy;
       ns_add(&len, lengthscale * (cx + cy));
-      ns_add(&len_a, lengthscale * (fabs(cx) + fabs(cy)));
+      ns_add(&len_a, lengthscale * (sx + sy));
       /* column role (sequential over i: fixed order) */
       dq_acc[k] += gG;
       dq_acc[m + k] += gGv * ux;
@@ -639,6 +644,85 @@ ORC_API void orc_windowed_vjp(const double* p, const double* z, int64_t n, const
   if (abs_len) *abs_len = ns_val(&len_a);
   free(dq_acc);
   free(dq_abs);
+}
+
+/* Rounding sensitivities of the windowed reduction and its gradients, for
+ * the tolerance of an FP32 evaluation (test infrastructure, not the method).
+ * An FP32 pair evaluation rounds the difference d = p_i - q_k and the
+ * window constants (each to relative error u), so the upper Cholesky factor
+ * R of M = C_i^-1 (M = R^T R) applied to d, w = R d, is off by at most
+ * 2u w^ with w^ = (|r11 dx| + |r12 dy|, |r22 dy|). With q = |w|^2 the
+ * Gaussian factor exp(-q/2) is then off by a relative
+ *   rho = 2 (|w1| w^1 + |w2| w^2) + q   (in units of u; q for the roundings
+ * of the squares and their sum), and u = M d = R^T w by
+ *   du_x = 2 |r11| w^1,  du_y = 2 (|r12| w^1 + |r22| w^2).
+ * For a window elongated by a condition number kappa, rho grows like
+ * q sqrt(kappa): far pairs of narrow windows carry the largest error. The
+ * outputs (each may be NULL) sum, over the terms of each output, |term| rho
+ * plus the terms' share through du:
+ *   s_out[n]:   sum_k |G v| rho
+ *   s_v[m]:     sum_i |g G| rho
+ *   s_p[n][2], s_q[m][2]: sum |g G v| (|u| rho + du)
+ *   s_z[n][3]:  (1/2) sum |g G v| ((u u^T + |M|) rho + d(u u^T)), the
+ *               off-diagonal entry twice as in orc_windowed_vjp
+ *   s_len[1]:   l sum_i (s_z[i][0] + s_z[i][2]). */
+ORC_API void orc_windowed_rounding(const double* p, const double* z, int64_t n, const double* q, int64_t m,
+                                   const double* v, double lengthscale, const double* g, double* s_out,
+                                   double* s_v, double* s_p, double* s_q, double* s_z, double* s_len) {
+  const double half_s = 0.5 * lengthscale * lengthscale;
+  double* col = (double*)calloc((size_t)(3 * m + 1), sizeof(double));
+  double len = 0.0;
+  for (int64_t i = 0; i < n; ++i) {
+    const double cxx = z[3 * i] + half_s, cxy = z[3 * i + 1], cyy = z[3 * i + 2] + half_s;
+    const double det = cxx * cyy - cxy * cxy;
+    const double mxx = cyy / det, mxy = -cxy / det, myy = cxx / det;
+    const double r11 = sqrt(cyy / det), r12 = -cxy / sqrt(cyy * det), r22 = 1.0 / sqrt(cyy);
+    const double norm = 1.0 / (2.0 * PI * sqrt(det));
+    const double gi = g ? fabs(g[i]) : 0.0;
+    double so = 0, spx = 0, spy = 0, szx = 0, szxy = 0, szy = 0;
+    for (int64_t k = 0; k < m; ++k) {
+      const double dx = p[2 * i] - q[2 * k], dy = p[2 * i + 1] - q[2 * k + 1];
+      const double w1 = r11 * dx + r12 * dy, w2 = r22 * dy;
+      const double h1 = fabs(r11 * dx) + fabs(r12 * dy), h2 = fabs(r22 * dy);
+      const double qq = w1 * w1 + w2 * w2;
+      const double rho = 2.0 * (fabs(w1) * h1 + fabs(w2) * h2) + qq;
+      const double G = norm * exp(-0.5 * qq);
+      const double ux = mxx * dx + mxy * dy, uy = mxy * dx + myy * dy;
+      const double dux = 2.0 * fabs(r11) * h1, duy = 2.0 * (fabs(r12) * h1 + fabs(r22) * h2);
+      const double av = v ? fabs(v[k]) : 0.0;
+      const double t = fabs(G) * av, tg = gi * t;
+      so += t * rho;
+      const double px = tg * (fabs(ux) * rho + dux), py = tg * (fabs(uy) * rho + duy);
+      spx += px;
+      spy += py;
+      szx += 0.5 * tg * ((ux * ux + fabs(mxx)) * rho + 2.0 * fabs(ux) * dux);
+      szxy += tg * ((fabs(ux * uy) + fabs(mxy)) * rho + fabs(ux) * duy + fabs(uy) * dux);
+      szy += 0.5 * tg * ((uy * uy + fabs(myy)) * rho + 2.0 * fabs(uy) * duy);
+      col[k] += gi * fabs(G) * rho;
+      col[m + k] += px;
+      col[2 * m + k] += py;
+    }
+    if (s_out) s_out[i] = so;
+    if (s_p) {
+      s_p[2 * i] = spx;
+      s_p[2 * i + 1] = spy;
+    }
+    if (s_z) {
+      s_z[3 * i] = szx;
+      s_z[3 * i + 1] = szxy;
+      s_z[3 * i + 2] = szy;
+    }
+    len += lengthscale * (szx + szy);
+  }
+  for (int64_t k = 0; k < m; ++k) {
+    if (s_v) s_v[k] = col[k];
+    if (s_q) {
+      s_q[2 * k] = col[m + k];
+      s_q[2 * k + 1] = col[2 * m + k];
+    }
+  }
+  if (s_len) *s_len = len;
+  free(col);
 }
 
 /* Gradient of Loss through the pixel windows: given dL/dZ (n x 3, the

@@ -111,8 +111,8 @@ SIGNATURES = {
                                                          _P]),
     "lr_static_scratch_bytes": (ctypes.c_size_t, []),
     "gp_pixel_shapes": (ctypes.c_int32, [_P, ctypes.c_int32, ctypes.c_int32, _P, _P]),
-    "gp_windowed_matvec": (ctypes.c_int32, [_P, _P, ctypes.c_int64, ctypes.POINTER(lr_points), _P, ctypes.c_float, _P,
-                                            _P, ctypes.c_size_t, _P]),
+    "gp_windowed_matvec": (ctypes.c_int32, [_P, _P, ctypes.c_int64, ctypes.POINTER(lr_grid), ctypes.POINTER(lr_points),
+                                            _P, ctypes.c_float, _P, _P, ctypes.c_size_t, _P]),
     "gp_knn_density": (ctypes.c_int32, [_P, ctypes.c_int64, ctypes.c_int32, ctypes.c_float, _P, _P, _P,
                                         ctypes.c_size_t, _P]),
     "lr_knn_workspace_size": (ctypes.c_int32, [ctypes.c_int64, ctypes.POINTER(ctypes.c_size_t)]),
@@ -134,13 +134,18 @@ SIGNATURES = {
                                              ctypes.c_size_t, _P]),
     "gp_partial_mvn_vjp": (ctypes.c_int32, [_P, _P, _P, ctypes.c_int32, ctypes.c_int64, _P, ctypes.c_double, _P, _P,
                                             _P, _P, _P]),
-    "gp_windowed_matvec_bwd": (ctypes.c_int32, [_P, _P, ctypes.c_int64, ctypes.POINTER(lr_points), _P, ctypes.c_float,
-                                                _P, _P, _P, _P, _P, _P, _P, ctypes.c_size_t, _P]),
-    "lr_windowed_bwd_workspace_size": (ctypes.c_int32, [ctypes.c_int64, ctypes.POINTER(lr_points),
-                                                        ctypes.POINTER(ctypes.c_size_t)]),
+    "gp_windowed_matvec_bwd": (ctypes.c_int32, [_P, _P, ctypes.c_int64, ctypes.POINTER(lr_grid),
+                                                ctypes.POINTER(lr_points), _P, ctypes.c_float, _P, _P, _P, _P, _P, _P,
+                                                _P, ctypes.c_size_t, _P]),
+    "lr_windowed_bwd_workspace_size": (ctypes.c_int32, [ctypes.c_int64, ctypes.POINTER(lr_grid),
+                                                        ctypes.POINTER(lr_points), ctypes.POINTER(ctypes.c_size_t)]),
+    "lr_windowed_pairs_evaluated": (ctypes.c_int32, [_P, _P, ctypes.c_int64, ctypes.POINTER(lr_grid),
+                                                     ctypes.POINTER(lr_points), ctypes.c_float, ctypes.c_int32,
+                                                     ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
+                                                     _P]),
     "gp_pixel_shapes_vjp": (ctypes.c_int32, [_P, ctypes.c_int32, ctypes.c_int32, _P, _P, _P]),
-    "lr_windowed_workspace_size": (ctypes.c_int32, [ctypes.c_int64, ctypes.POINTER(lr_points),
-                                                    ctypes.POINTER(ctypes.c_size_t)]),
+    "lr_windowed_workspace_size": (ctypes.c_int32, [ctypes.c_int64, ctypes.POINTER(lr_grid),
+                                                    ctypes.POINTER(lr_points), ctypes.POINTER(ctypes.c_size_t)]),
     "gp_kernel_matvec_layers": (ctypes.c_int32, [ctypes.POINTER(lr_points), ctypes.POINTER(lr_points), ctypes.c_int32,
                                                  _P, _P, _P, _P, _P, _P, ctypes.c_size_t, _P]),
     "lr_matvec_layers_workspace_size": (ctypes.c_int32, [ctypes.POINTER(lr_points), ctypes.POINTER(lr_points),

@@ -268,9 +268,14 @@ def pixel_shapes(p: torch.Tensor, W: int, H: int, stream=None) -> torch.Tensor:
     return z
 
 
+def _layout(layout: Grid | None):
+    return ctypes.byref(abi.lr_grid(*layout.astuple())) if layout is not None else None
+
+
 def gp_windowed_matvec(p: torch.Tensor, z: torch.Tensor, source: Points, v: torch.Tensor, lengthscale: float,
-                       stream=None) -> torch.Tensor:
-    """out_i = sum_k G(p_i - q_k, Z_i + l^2/2 I) v_k (windowed transmission)."""
+                       layout: Grid | None = None, stream=None) -> torch.Tensor:
+    """out_i = sum_k G(p_i - q_k, Z_i + l^2/2 I) v_k (windowed transmission);
+    layout: the image grid the query points p come from (orders the work)."""
     lib = abi.load()
     _require_cuda(p, "p", (2,))
     _require_cuda(z, "z", (3,))
@@ -279,10 +284,11 @@ def gp_windowed_matvec(p: torch.Tensor, z: torch.Tensor, source: Points, v: torc
     n = p.shape[0]
     out = torch.empty(n, dtype=torch.float32, device=p.device)
     b = ctypes.c_size_t(0)
-    abi.check(lib.lr_windowed_workspace_size(n, ctypes.byref(cs), ctypes.byref(b)), "lr_windowed_workspace_size")
+    abi.check(lib.lr_windowed_workspace_size(n, _layout(layout), ctypes.byref(cs), ctypes.byref(b)),
+              "lr_windowed_workspace_size")
     ws = torch.empty(max(int(b.value), 1), dtype=torch.uint8, device=p.device)
-    st = lib.gp_windowed_matvec(p.data_ptr(), z.data_ptr(), n, ctypes.byref(cs), v.data_ptr(), float(lengthscale),
-                                out.data_ptr(), ws.data_ptr(), ws.numel(), _stream_handle(stream))
+    st = lib.gp_windowed_matvec(p.data_ptr(), z.data_ptr(), n, _layout(layout), ctypes.byref(cs), v.data_ptr(),
+                                float(lengthscale), out.data_ptr(), ws.data_ptr(), ws.numel(), _stream_handle(stream))
     abi.check(st, "gp_windowed_matvec")
     return out
 
@@ -408,7 +414,8 @@ def partial_mvn_vjp(L, sd, eps, d_x, w_q: float = 1.0, stream=None):
 
 
 def gp_windowed_matvec_bwd(p: torch.Tensor, z: torch.Tensor, source: Points, v: torch.Tensor, lengthscale: float,
-                           g: torch.Tensor, want=("v", "p", "q", "z", "lengthscale"), stream=None) -> dict:
+                           g: torch.Tensor, want=("v", "p", "q", "z", "lengthscale"), layout: Grid | None = None,
+                           stream=None) -> dict:
     """Gradients of sum_i g_i out_i through gp_windowed_matvec (explicit sources)."""
     lib = abi.load()
     _require_cuda(p, "p", (2,))
@@ -423,14 +430,31 @@ def gp_windowed_matvec_bwd(p: torch.Tensor, z: torch.Tensor, source: Points, v: 
     if "lengthscale" in want:
         out["lengthscale"] = torch.empty(1, dtype=torch.float64, device=dev_)
     b = ctypes.c_size_t(0)
-    abi.check(lib.lr_windowed_bwd_workspace_size(n, ctypes.byref(cs), ctypes.byref(b)), "lr_windowed_bwd_workspace_size")
+    abi.check(lib.lr_windowed_bwd_workspace_size(n, _layout(layout), ctypes.byref(cs), ctypes.byref(b)),
+              "lr_windowed_bwd_workspace_size")
     ws = torch.empty(max(int(b.value), 1), dtype=torch.uint8, device=dev_)
     ptr = lambda key: out[key].data_ptr() if key in out else None
-    st = lib.gp_windowed_matvec_bwd(p.data_ptr(), z.data_ptr(), n, ctypes.byref(cs), v.data_ptr(), float(lengthscale),
-                                    g.data_ptr(), ptr("v"), ptr("p"), ptr("q"), ptr("z"), ptr("lengthscale"),
-                                    ws.data_ptr(), ws.numel(), _stream_handle(stream))
+    st = lib.gp_windowed_matvec_bwd(p.data_ptr(), z.data_ptr(), n, _layout(layout), ctypes.byref(cs), v.data_ptr(),
+                                    float(lengthscale), g.data_ptr(), ptr("v"), ptr("p"), ptr("q"), ptr("z"),
+                                    ptr("lengthscale"), ws.data_ptr(), ws.numel(), _stream_handle(stream))
     abi.check(st, "gp_windowed_matvec_bwd")
     return out
+
+
+def windowed_pairs_evaluated(p: torch.Tensor, z: torch.Tensor, source: Points, lengthscale: float, sweep: int = 0,
+                             layout: Grid | None = None, stream=None) -> tuple[int, int]:
+    """(pairs, slots) the windowed sweeps over explicit sources evaluate
+    (sweep 0: forward; 1: backward rows; 2: backward columns)."""
+    lib = abi.load()
+    _require_cuda(p, "p", (2,))
+    _require_cuda(z, "z", (3,))
+    cs, k = to_c_points(source)
+    pairs, slots = ctypes.c_int64(0), ctypes.c_int64(0)
+    abi.check(lib.lr_windowed_pairs_evaluated(p.data_ptr(), z.data_ptr(), p.shape[0], _layout(layout),
+                                              ctypes.byref(cs), float(lengthscale), int(sweep), ctypes.byref(pairs),
+                                              ctypes.byref(slots), _stream_handle(stream)),
+              "lr_windowed_pairs_evaluated")
+    return int(pairs.value), int(slots.value)
 
 
 def pixel_shapes_vjp(p: torch.Tensor, W: int, H: int, dz: torch.Tensor, stream=None) -> torch.Tensor:

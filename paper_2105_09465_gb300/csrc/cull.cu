@@ -1,8 +1,9 @@
 // Culled Gaussian-kernel reductions over explicit point sets (cull.cuh): the
 // forward reduction out_i = var sum_j exp(-|x_i - y_j|^2 / (2 l^2)) v_j with
 // up to four right-hand sides (Sec. 3.1 RBF kernel, Sec. 3.3 lazy T y), the
-// row moments of the backward, and the self-kernel backward (gradient flow
-// through the reduction, Sec. 3.3 and 3.6).
+// row moments of the backward, the self-kernel backward (gradient flow
+// through the reduction, Sec. 3.3 and 3.6), and the windowed transmission of
+// the image-plane layers with its backward (Sec. 3.4, windows of Sec. 3.2).
 //
 // One CTA per (row block, group range). The CTA keeps its rows in registers
 // and lists, in ascending order, the groups and then the chunks within reach
@@ -72,13 +73,29 @@ __global__ void __launch_bounds__(256) cull_prep_kernel(const __grid_constant__ 
     float* w = reinterpret_cast<float*>(rec);
     for (int k = lane; k < RB / 4; k += 32) w[k] = 0.f;
     __syncwarp();
-    if (lane == 0) *reinterpret_cast<float4*>(rec) = box;
+    if (lane == 0) {
+      *reinterpret_cast<float4*>(rec) = box;
+      if (P.csc) P.csc[c] = INFINITY;
+    }
     return;
   }
   const int n_valid = __popc(__ballot_sync(0xffffffffu, valid));
+  // kCullWinCols: the points' window constants and the chunk's reach scale
+  float wm[4] = {0.f, 0.f, 0.f, 0.f}, reach = INFINITY;
+  if (P.kind == kCullWinCols && valid) {
+    const float4 wc = P.wcoef[i];
+    wm[0] = wc.x;
+    wm[1] = wc.y;
+    wm[2] = wc.z;
+    wm[3] = P.a[i] * wc.w;
+    reach = P.wreach[i];
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) reach = fminf(reach, __shfl_xor_sync(0xffffffffu, reach, o));
   if (lane == 0) {
     *reinterpret_cast<float4*>(rec) = box;
-    *reinterpret_cast<float4*>(rec + 16) = make_float4((float)n_valid, 0.f, 0.f, 0.f);
+    *reinterpret_cast<float4*>(rec + 16) = make_float4((float)n_valid, reach, 0.f, 0.f);
+    if (P.csc) P.csc[c] = reach;
   }
   // (xa, xb, ya, yb) per source pair: absolute positions, so that the
   // kernels form x_j - x_i directly (correctly rounded: relative error u)
@@ -89,6 +106,10 @@ __global__ void __launch_bounds__(256) cull_prep_kernel(const __grid_constant__ 
   float* w = reinterpret_cast<float*>(rec + kRecHead + kRecXY);  // [nw][32], pairs consecutive
   if (P.kind == kCullOut) {
     for (int k = 0; k < P.nw; ++k) w[k * kChunkPts + lane] = valid ? P.a[i * P.stride + k] : 0.f;
+  } else if (P.kind == kCullWin || P.kind == kCullWinRows) {
+    w[lane] = valid ? P.a[i] : 0.f;
+  } else if (P.kind == kCullWinCols) {
+    for (int k = 0; k < 4; ++k) w[k * kChunkPts + lane] = wm[k];
   } else if (P.kind == kCullMom) {
     w[lane] = valid ? P.a[i * P.stride + P.col] : 0.f;
   } else {
@@ -101,21 +122,50 @@ __global__ void __launch_bounds__(256) cull_prep_kernel(const __grid_constant__ 
   }
 }
 
-// Group boxes: one warp per group.
-__global__ void __launch_bounds__(256) cull_group_box_kernel(const float4* __restrict__ cbox, int n_groups,
-                                                             float4* __restrict__ gbox) {
+// Window constants, one thread per point. C = Z + (l^2/2) I and det C are
+// formed in FP64 (det cancels by a factor of the condition number); the rest
+// is well-conditioned (products, quotients and square roots of positive
+// numbers) and runs in FP32 from them: the upper Cholesky factor R of C^-1,
+// r11 = sqrt(cyy / det), r12 = -cxy / sqrt(cyy det), r22 = 1 / sqrt(cyy), so
+// that d^T C^-1 d = |R d|^2, and lambda_max(C) for the reach.
+__global__ void __launch_bounds__(256) window_prep_kernel(const float* __restrict__ z, int64_t n, double half_s,
+                                                          float4* __restrict__ wcoef, float* __restrict__ wreach) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double cxx_d = (double)z[3 * i] + half_s, cyy_d = (double)z[3 * i + 2] + half_s;
+  const float cxy = z[3 * i + 1];
+  const float det = (float)(cxx_d * cyy_d - (double)cxy * (double)cxy);
+  const float cxx = (float)cxx_d, cyy = (float)cyy_d;
+  const float k = 0.84932180028801904f;  // sqrt(log2(e) / 2)
+  const float r11 = sqrtf(cyy / det), r12 = -cxy / sqrtf(cyy * det), r22 = 1.0f / sqrtf(cyy);
+  wcoef[i] = make_float4(k * r11, k * r12, k * r22, 0.15915494309189535f / sqrtf(det));  // N = 1/(2 pi sqrt(det))
+  const float h = 0.5f * (cxx - cyy);
+  const float lmax = 0.5f * (cxx + cyy) + sqrtf(fmaf(h, h, cxy * cxy));
+  wreach[i] = sqrtf(0.72134752044448170f / lmax);  // sqrt(log2(e) / (2 lambda_max))
+}
+
+// Group boxes (and, with csc, the groups' smallest reach scales): one warp
+// per group.
+__global__ void __launch_bounds__(256) cull_group_box_kernel(const float4* __restrict__ cbox,
+                                                             const float* __restrict__ csc, int n_groups,
+                                                             float4* __restrict__ gbox, float* __restrict__ gsc) {
   const int g = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
   if (g >= n_groups) return;
-  float4 b = box_merge(cbox[(int64_t)g * kGroupChunks + lane], cbox[(int64_t)g * kGroupChunks + 32 + lane]);
+  const int64_t c0 = (int64_t)g * kGroupChunks;
+  float4 b = box_merge(cbox[c0 + lane], cbox[c0 + 32 + lane]);
   b = warp_box(b);
   if (lane == 0) gbox[g] = b;
+  if (csc) {
+    float r = fminf(csc[c0 + lane], csc[c0 + 32 + lane]);
+#pragma unroll
+    for (int o = 16; o; o >>= 1) r = fminf(r, __shfl_xor_sync(0xffffffffu, r, o));
+    if (lane == 0) gsc[g] = r;
+  }
 }
 
 // ---------------------------------------------------------------------------
 // The sweep.
-constexpr int kMaxList = 1024;  // listed chunks per window
-
 template <int KIND, int NW>
 struct CullTraits;
 template <int NW>
@@ -130,24 +180,18 @@ template <int NW>
 struct CullTraits<kCullSelf, NW> {  // NW / 2 right-hand sides
   static constexpr int K = 7 * (NW / 2), R = NW == 2 ? 2 : 1, BATCH = NW == 2 ? 32 : 16;
 };
-
-// Ordered compaction over the CTA: returns the number of true predicates;
-// those threads write `value` to out[base + rank] in thread order.
-__device__ __forceinline__ int cta_compact(bool pred, int value, int* out, int base, int* wcnt) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const unsigned m = __ballot_sync(0xffffffffu, pred);
-  if (lane == 0) wcnt[w] = __popc(m);
-  __syncthreads();
-  int off = base, total = 0;
-#pragma unroll
-  for (int k = 0; k < kCullThreads / 32; ++k) {
-    if (k < w) off += wcnt[k];
-    total += wcnt[k];
-  }
-  if (pred) out[off + __popc(m & ((1u << lane) - 1u))] = value;
-  __syncthreads();
-  return total;
-}
+template <>
+struct CullTraits<kCullWin, 1> {
+  static constexpr int K = 1, R = 4, BATCH = 32;
+};
+template <>
+struct CullTraits<kCullWinRows, 1> {
+  static constexpr int K = 6, R = 2, BATCH = 32;
+};
+template <>
+struct CullTraits<kCullWinCols, 4> {
+  static constexpr int K = 3, R = 4, BATCH = 16;
+};
 
 // Row outputs of one row (totals t[K]) for splits == 1, or of the merge.
 // Returns the row's scalar-gradient terms (d_l, d_var) through sl, sv.
@@ -155,10 +199,12 @@ template <int KIND, int K>
 __device__ __forceinline__ void cull_finalize(const CullArgs& A, int64_t i, const float* t, float& sl, float& sv) {
   sl = 0.f;
   sv = 0.f;
-  if (KIND == kCullOut) {
+  if constexpr (KIND == kCullOut) {
 #pragma unroll
     for (int k = 0; k < K; ++k) A.out[i * A.nrhs + k] = A.var * t[k];
-  } else if (KIND == kCullMom) {
+  } else if constexpr (KIND == kCullWin) {
+    A.out[i] = A.wcoef[i].w * t[0];
+  } else if constexpr (KIND == kCullMom) {
     if (A.g == nullptr) {
       A.out[i] = A.var * t[0];
 #pragma unroll
@@ -176,7 +222,7 @@ __device__ __forceinline__ void cull_finalize(const CullArgs& A, int64_t i, cons
       sl = __fmul_rn(__fmul_rn(gi, t[3]), A.dl_scale);
       sv = __fmul_rn(gi, t[0]);
     }
-  } else {  // kCullSelf: K / 7 right-hand sides, 7 sums each
+  } else if constexpr (KIND == kCullSelf) {  // K / 7 right-hand sides, 7 sums each
     float dxx = 0.f, dxy = 0.f;
 #pragma unroll
     for (int h = 0; h < K / 7; ++h) {
@@ -221,23 +267,45 @@ __device__ __forceinline__ void cta_scalar_partials(float sl, float sv, double* 
   }
 }
 
+constexpr int kMaxList = 1024;  // listed chunks per window
+
+// Ordered compaction over the CTA: returns the number of true predicates;
+// those threads write `value` to out[base + rank] in thread order.
+__device__ __forceinline__ int cta_compact(bool pred, int value, int* out, int base, int* wcnt) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const unsigned m = __ballot_sync(0xffffffffu, pred);
+  if (lane == 0) wcnt[w] = __popc(m);
+  __syncthreads();
+  int off = base, total = 0;
+#pragma unroll
+  for (int k = 0; k < kCullThreads / 32; ++k) {
+    if (k < w) off += wcnt[k];
+    total += wcnt[k];
+  }
+  if (pred) out[off + __popc(m & ((1u << lane) - 1u))] = value;
+  __syncthreads();
+  return total;
+}
+
 template <int KIND, int NW>
 struct CullSmem {
   static constexpr int BATCH = CullTraits<KIND, NW>::BATCH;
   alignas(128) char buf[2][BATCH * rec_bytes(NW)];
   uint64_t bar[2];
   float4 wbox[kCullThreads / 32];
+  float wsc[kCullThreads / 32];
   int clist[kMaxList];
   int gsel[kCullThreads];
   int wcnt[kCullThreads / 32];
   float red[2 * kCullThreads / 32];
-  int flag;
 };
 
 template <int KIND, int NW>
 __global__ void __launch_bounds__(kCullThreads) cull_kernel(const __grid_constant__ CullArgs A) {
   using T = CullTraits<KIND, NW>;
   constexpr int R = T::R, K = T::K, BATCH = T::BATCH, RB = rec_bytes(NW);
+  constexpr bool WROW = KIND == kCullWin || KIND == kCullWinRows;  // rows carry windows
+  constexpr bool WBWD = KIND == kCullWinRows || KIND == kCullWinCols;
   __shared__ CullSmem<KIND, NW> sm;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int rb = blockIdx.x / A.splits, split = blockIdx.x - rb * A.splits;
@@ -265,6 +333,32 @@ __global__ void __launch_bounds__(kCullThreads) cull_kernel(const __grid_constan
     NP[r] = f2(-yr[r], -yr[r]);
   }
   const float2 NC = f2(-A.c, -A.c);
+  // windowed rows: the scaled Cholesky factor (a, b, c) of C_i^-1 and the
+  // reach scales of the skipping test (the smallest over the warp's and the
+  // CTA's rows)
+  float2 MA[R], MB[R], MC[R];
+  float sc_w = A.sc, sc_b = A.sc;
+  if constexpr (WROW) {
+    float rs = INFINITY;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      float a = 0.f, b = 0.f, c = 0.f;
+      if (irow[r] >= 0) {
+        const float4 wc = A.wcoef[irow[r]];
+        a = wc.x;
+        b = wc.y;
+        c = wc.z;
+        rs = fminf(rs, A.wreach[irow[r]]);
+      }
+      MA[r] = f2(a, a);
+      MB[r] = f2(b, b);
+      MC[r] = f2(c, c);
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) rs = fminf(rs, __shfl_xor_sync(0xffffffffu, rs, o));
+    sc_w = rs;
+    if (lane == 0) sm.wsc[warp] = rs;
+  }
   if (lane == 0) sm.wbox[warp] = wb;
   if (tid == 0) {
     mbar_init(&sm.bar[0], 1);
@@ -274,6 +368,11 @@ __global__ void __launch_bounds__(kCullThreads) cull_kernel(const __grid_constan
   float4 cb = sm.wbox[0];
 #pragma unroll
   for (int k = 1; k < kCullThreads / 32; ++k) cb = box_merge(cb, sm.wbox[k]);
+  if constexpr (WROW) {
+    sc_b = sm.wsc[0];
+#pragma unroll
+    for (int k = 1; k < kCullThreads / 32; ++k) sc_b = fminf(sc_b, sm.wsc[k]);
+  }
   const bool cull = A.cull != 0;
 
   float tot[R][K], comp[R][K];
@@ -296,15 +395,16 @@ __global__ void __launch_bounds__(kCullThreads) cull_kernel(const __grid_constan
     bool full = false;
     while (gpos < g_hi && !full) {
       const int g = gpos + tid;
-      const bool gs = g < g_hi && !(cull && boxes_far(cb, A.gbox[g], A.sc));
+      const bool gs = g < g_hi && !(cull && boxes_far(cb, A.gbox[g], KIND == kCullWinCols ? A.gsc[g] : sc_b));
       const int ng = cta_compact(gs, g, sm.gsel, 0, sm.wcnt);
       int k = 0;
       for (; k < ng; ++k) {
         if (count + kGroupChunks > kMaxList) break;
         const int gg = sm.gsel[k];
         const int c = gg * kGroupChunks + (tid & (kGroupChunks - 1));
-        const bool cs = tid < kGroupChunks && !(cull ? boxes_far(cb, A.cbox[c], A.sc)
-                                                     : !(A.cbox[c].x <= A.cbox[c].z));
+        const bool cs = tid < kGroupChunks &&
+                        !(cull ? boxes_far(cb, A.cbox[c], KIND == kCullWinCols ? A.csc[c] : sc_b)
+                               : !(A.cbox[c].x <= A.cbox[c].z));
         count += cta_compact(cs, c, sm.clist, count, sm.wcnt);
       }
       if (k < ng) {
@@ -343,15 +443,16 @@ __global__ void __launch_bounds__(kCullThreads) cull_kernel(const __grid_constan
       for (int k = 0; k < cn; ++k) {
         const char* rec = bb + k * RB;
         const float4 box = *reinterpret_cast<const float4*>(rec);
-        if (cull && boxes_far(wb, box, A.sc)) continue;  // warp-uniform
+        const float4 head = *reinterpret_cast<const float4*>(rec + 16);  // (valid points, reach scale)
+        if (cull && boxes_far(wb, box, KIND == kCullWinCols ? head.y : sc_w)) continue;  // warp-uniform
         if (A.count && lane == 0) {
-          const float nv = reinterpret_cast<const float4*>(rec + 16)->x;
+          const float nv = head.x;
           atomicAdd(A.count, (unsigned long long)(warp_rows * (int)nv));
           atomicAdd(A.count + 1, (unsigned long long)(32 * R * kChunkPts));
         }
         const float4* xy = reinterpret_cast<const float4*>(rec + kRecHead);
         const float2* wt = reinterpret_cast<const float2*>(rec + kRecHead + kRecXY);
-        if (KIND == kCullOut) {
+        if constexpr (KIND == kCullOut) {
           // k v = 2^(-c |x_j - x_i|^2) v, c = sc^2: 6 FP32 lanes per pair
           float2 acc[R][NW];
 #pragma unroll
@@ -383,6 +484,98 @@ __global__ void __launch_bounds__(kCullThreads) cull_kernel(const __grid_constan
               const float sum = acc[r][w].x + acc[r][w].y;
               if (sum != 0.f) kahan_add(tot[r][w], comp[r][w], sum);
             }
+        } else if constexpr (KIND == kCullWin) {
+          // G' v = 2^(-|w|^2) v, w = (a d_x + b d_y, c d_y), d = x_j - x_i:
+          // 8 FP32 lanes per pair
+          float2 acc[R];
+#pragma unroll
+          for (int r = 0; r < R; ++r) acc[r] = f2(0.f, 0.f);
+#pragma unroll 2
+          for (int pp = 0; pp < kChunkPairs; ++pp) {
+            const float4 P = xy[pp];
+            const float2 X = f2(P.x, P.y), Y = f2(P.z, P.w);
+            const float2 W = wt[pp];
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+              const float2 dx = __fadd2_rn(X, NQ[r]), dy = __fadd2_rn(Y, NP[r]);
+              const float2 w1 = __ffma2_rn(MA[r], dx, __fmul2_rn(MB[r], dy)), w2 = __fmul2_rn(MC[r], dy);
+              const float2 t = __ffma2_rn(w1, w1, __fmul2_rn(w2, w2));
+              const float2 kk = f2(ex2_approx(-t.x), ex2_approx(-t.y));
+              acc[r] = __ffma2_rn(kk, W, acc[r]);
+            }
+          }
+#pragma unroll
+          for (int r = 0; r < R; ++r) {
+            const float sum = acc[r].x + acc[r].y;
+            if (sum != 0.f) kahan_add(tot[r][0], comp[r][0], sum);
+          }
+        } else if constexpr (KIND == kCullWinRows) {
+          // with w = R_i d (scaled), d = x_j - x_i and u = R_i^T w =
+          // k^2 C_i^-1 d (= M'_i (x_i - x_j) with M' = -k^2 C^-1, the merge's
+          // form): S += v G', P += v G' u, Q += v G' u u^T
+          float2 acc[R][6];
+#pragma unroll
+          for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int k2 = 0; k2 < 6; ++k2) acc[r][k2] = f2(0.f, 0.f);
+#pragma unroll 2
+          for (int pp = 0; pp < kChunkPairs; ++pp) {
+            const float4 P = xy[pp];
+            const float2 X = f2(P.x, P.y), Y = f2(P.z, P.w);
+            const float2 W = wt[pp];
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+              const float2 dx = __fadd2_rn(X, NQ[r]), dy = __fadd2_rn(Y, NP[r]);
+              const float2 w1 = __ffma2_rn(MA[r], dx, __fmul2_rn(MB[r], dy)), w2 = __fmul2_rn(MC[r], dy);
+              const float2 t = __ffma2_rn(w1, w1, __fmul2_rn(w2, w2));
+              const float2 ux = __fmul2_rn(MA[r], w1), uy = __ffma2_rn(MB[r], w1, __fmul2_rn(MC[r], w2));
+              const float2 kv = __fmul2_rn(f2(ex2_approx(-t.x), ex2_approx(-t.y)), W);
+              const float2 kx = __fmul2_rn(kv, ux), ky = __fmul2_rn(kv, uy);
+              float2* a = acc[r];
+              a[0] = __fadd2_rn(a[0], kv);
+              a[1] = __fadd2_rn(a[1], kx);
+              a[2] = __fadd2_rn(a[2], ky);
+              a[3] = __ffma2_rn(kx, ux, a[3]);
+              a[4] = __ffma2_rn(kx, uy, a[4]);
+              a[5] = __ffma2_rn(ky, uy, a[5]);
+            }
+          }
+#pragma unroll
+          for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int k2 = 0; k2 < 6; ++k2) tot[r][k2] += acc[r][k2].x + acc[r][k2].y;
+        } else if constexpr (KIND == kCullWinCols) {
+          // the sources carry the windows: with w = R_j d (scaled),
+          // d = x_j - x_i and u = R_j^T w = k^2 C_j^-1 d (= M'_j (x_i - x_j)):
+          // T += gN G', U += gN G' u
+          float2 acc[R][3];
+#pragma unroll
+          for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int k2 = 0; k2 < 3; ++k2) acc[r][k2] = f2(0.f, 0.f);
+#pragma unroll 2
+          for (int pp = 0; pp < kChunkPairs; ++pp) {
+            const float4 P = xy[pp];
+            const float2 X = f2(P.x, P.y), Y = f2(P.z, P.w);
+            const float2 ca = wt[pp], cb = wt[kChunkPairs + pp], cc = wt[2 * kChunkPairs + pp],
+                         gn = wt[3 * kChunkPairs + pp];
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+              const float2 dx = __fadd2_rn(X, NQ[r]), dy = __fadd2_rn(Y, NP[r]);
+              const float2 w1 = __ffma2_rn(ca, dx, __fmul2_rn(cb, dy)), w2 = __fmul2_rn(cc, dy);
+              const float2 t = __ffma2_rn(w1, w1, __fmul2_rn(w2, w2));
+              const float2 kg = __fmul2_rn(f2(ex2_approx(-t.x), ex2_approx(-t.y)), gn);
+              const float2 ux = __fmul2_rn(ca, w1), uy = __ffma2_rn(cb, w1, __fmul2_rn(cc, w2));
+              float2* a = acc[r];
+              a[0] = __fadd2_rn(a[0], kg);
+              a[1] = __ffma2_rn(kg, ux, a[1]);
+              a[2] = __ffma2_rn(kg, uy, a[2]);
+            }
+          }
+#pragma unroll
+          for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int k2 = 0; k2 < 3; ++k2) tot[r][k2] += acc[r][k2].x + acc[r][k2].y;
         } else {
           // row moments from per-pair differences d = x_j - x_i:
           // A += k w, B += k w d, C += k w |d|^2 (and A, B of the second
@@ -432,6 +625,7 @@ __global__ void __launch_bounds__(kCullThreads) cull_kernel(const __grid_constan
 #pragma unroll
             for (int k2 = 0; k2 < NA; ++k2) tot[r][k2] += acc[r][k2].x + acc[r][k2].y;
         }
+    
       }
       __syncthreads();  // the buffer is refilled two batches on
     }
@@ -445,8 +639,11 @@ __global__ void __launch_bounds__(kCullThreads) cull_kernel(const __grid_constan
     if (irow[r] < 0) continue;
     float t[K];
 #pragma unroll
-    for (int k = 0; k < K; ++k) t[k] = KIND == kCullOut ? tot[r][k] - comp[r][k] : tot[r][k];
-    if (A.splits == 1) {
+    for (int k = 0; k < K; ++k) t[k] = (KIND == kCullOut || KIND == kCullWin) ? tot[r][k] - comp[r][k] : tot[r][k];
+    if constexpr (WBWD) {
+#pragma unroll
+      for (int k = 0; k < K; ++k) A.partial[((int64_t)split * K + k) * A.n + irow[r]] = t[k];
+    } else if (A.splits == 1) {
       float a, b;
       cull_finalize<KIND, K>(A, irow[r], t, a, b);
       sl += a;
@@ -531,6 +728,9 @@ static const void* cull_kernel_ptr(int kind, int nw) {
     }
   }
   if (kind == kCullMom) return cull_fn<kCullMom, 1>();
+  if (kind == kCullWin) return cull_fn<kCullWin, 1>();
+  if (kind == kCullWinRows) return cull_fn<kCullWinRows, 1>();
+  if (kind == kCullWinCols) return cull_fn<kCullWinCols, 4>();
   switch (nw) {
     case 2: return cull_fn<kCullSelf, 2>();
     case 4: return cull_fn<kCullSelf, 4>();
@@ -541,6 +741,7 @@ static const void* cull_kernel_ptr(int kind, int nw) {
 
 static int cull_rows_per_thread(int kind, int nw) {
   if (kind == kCullOut) return nw <= 2 ? 4 : 2;
+  if (kind == kCullWin || kind == kCullWinCols) return 4;
   return (kind == kCullSelf && nw > 2) ? 1 : 2;
 }
 
@@ -565,13 +766,18 @@ lr_status plan_cull(int kind, int nrhs, int64_t n, const lr_grid* qlayout, int64
   LR_CHECK_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
   LR_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, cull_kernel_ptr(kind, P.nw), kCullThreads, 0));
   // group ranges per row block: only when the row blocks alone leave most of
-  // the resident CTA slots empty (small query sets)
+  // the resident CTA slots empty (small query sets). Rows that carry windows
+  // differ in reach by orders of magnitude (pixels next to the lens centre
+  // reach arcseconds, half the image), so the work of a row block does too:
+  // there many more group ranges spread the widest row blocks over the GPU.
   const int64_t slots = (int64_t)(occ > 0 ? occ : 1) * n_sm;
+  const int64_t target = (kind == kCullWin || kind == kCullWinRows) ? 16 * slots : 2 * slots;
   int64_t splits = 1;
-  if (P.row_blocks > 0 && P.row_blocks < 2 * slots) splits = (2 * slots + P.row_blocks - 1) / P.row_blocks;
+  if (P.row_blocks > 0 && P.row_blocks < target) splits = (target + P.row_blocks - 1) / P.row_blocks;
   if (splits > P.L.n_groups) splits = P.L.n_groups > 0 ? P.L.n_groups : 1;
   P.splits = (int32_t)splits;
-  P.K = kind == kCullOut ? P.nw : (kind == kCullMom ? 4 : 7 * (P.nw / 2));
+  P.K = cull_k(kind, P.nw);
+  const bool wbwd = kind == kCullWinRows || kind == kCullWinCols;
   size_t off = 0;
   P.off_rec = off;
   off += align256((size_t)P.L.n_chunks * rec_bytes(P.nw));
@@ -579,8 +785,14 @@ lr_status plan_cull(int kind, int nrhs, int64_t n, const lr_grid* qlayout, int64
   off += align256(sizeof(float4) * (size_t)P.L.n_chunks);
   P.off_gbox = off;
   off += align256(sizeof(float4) * (size_t)(P.L.n_groups > 0 ? P.L.n_groups : 1));
+  P.off_csc = P.off_gsc = off;
+  if (kind == kCullWinCols) {
+    off += align256(sizeof(float) * (size_t)P.L.n_chunks);
+    P.off_gsc = off;
+    off += align256(sizeof(float) * (size_t)(P.L.n_groups > 0 ? P.L.n_groups : 1));
+  }
   P.off_partial = off;
-  if (P.splits > 1) off += align256(sizeof(float) * (size_t)P.splits * P.K * (size_t)n);
+  if (P.splits > 1 || wbwd) off += align256(sizeof(float) * (size_t)P.splits * P.K * (size_t)n);
   P.scal_blocks = P.splits > 1 ? (n + 255) / 256 : P.row_blocks * P.splits;
   P.off_scal = off;
   off += align256(sizeof(double) * 2 * (size_t)(P.scal_blocks > 0 ? P.scal_blocks : 1));
@@ -589,8 +801,18 @@ lr_status plan_cull(int kind, int nrhs, int64_t n, const lr_grid* qlayout, int64
   return LR_OK;
 }
 
+lr_status launch_window_prep(const float* z, int64_t n, float lengthscale, float4* wcoef, float* wreach,
+                             cudaStream_t s) {
+  if (n == 0) return LR_OK;
+  const double ell = (double)lengthscale;
+  window_prep_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(z, n, 0.5 * ell * ell, wcoef, wreach);
+  LR_CHECK_CUDA(cudaGetLastError());
+  return LR_OK;
+}
+
 lr_status launch_cull_prep(const CullPlan& P, const float2* pts, float sc, const float* a, const float* b,
-                           int32_t stride, int32_t col, char* ws, cudaStream_t s) {
+                           int32_t stride, int32_t col, char* ws, cudaStream_t s, const float4* wcoef,
+                           const float* wreach) {
   CullPrepP Q{};
   Q.pts = pts;
   Q.L = P.L;
@@ -604,12 +826,18 @@ lr_status launch_cull_prep(const CullPlan& P, const float2* pts, float sc, const
   Q.rec = ws + P.off_rec;
   Q.cbox = reinterpret_cast<float4*>(ws + P.off_cbox);
   Q.gbox = reinterpret_cast<float4*>(ws + P.off_gbox);
+  Q.wcoef = wcoef;
+  Q.wreach = wreach;
+  if (P.kind == kCullWinCols) {
+    Q.csc = reinterpret_cast<float*>(ws + P.off_csc);
+    Q.gsc = reinterpret_cast<float*>(ws + P.off_gsc);
+  }
   if (P.L.n_chunks == 0) return LR_OK;
   const int64_t warps = P.L.n_chunks;
   cull_prep_kernel<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, s>>>(Q);
   LR_CHECK_CUDA(cudaGetLastError());
-  cull_group_box_kernel<<<(unsigned)(((int64_t)P.L.n_groups * 32 + 255) / 256), 256, 0, s>>>(Q.cbox, P.L.n_groups,
-                                                                                              Q.gbox);
+  cull_group_box_kernel<<<(unsigned)(((int64_t)P.L.n_groups * 32 + 255) / 256), 256, 0, s>>>(
+      Q.cbox, Q.csc, P.L.n_groups, Q.gbox, Q.gsc);
   LR_CHECK_CUDA(cudaGetLastError());
   return LR_OK;
 }
@@ -619,9 +847,12 @@ static lr_status launch_sweep_t(const CullPlan& P, const CullArgs& A, cudaStream
   const unsigned grid = (unsigned)(P.row_blocks * P.splits);
   cull_kernel<KIND, NW><<<grid, kCullThreads, 0, s>>>(A);
   LR_CHECK_CUDA(cudaGetLastError());
-  if (P.splits > 1 && !A.count) {
-    cull_merge_kernel<KIND, CullTraits<KIND, NW>::K><<<(unsigned)((A.n + 255) / 256), 256, 0, s>>>(A);
-    LR_CHECK_CUDA(cudaGetLastError());
+  // the windowed backward kinds leave their partials to the caller's merge
+  if constexpr (KIND != kCullWinRows && KIND != kCullWinCols) {
+    if (P.splits > 1 && !A.count) {
+      cull_merge_kernel<KIND, CullTraits<KIND, NW>::K><<<(unsigned)((A.n + 255) / 256), 256, 0, s>>>(A);
+      LR_CHECK_CUDA(cudaGetLastError());
+    }
   }
   return LR_OK;
 }
@@ -638,6 +869,10 @@ lr_status launch_cull_sweep(const CullPlan& P, CullArgs A, char* ws, int timer_i
   A.n_groups = P.L.n_groups;
   A.splits = P.splits;
   A.partial = reinterpret_cast<float*>(ws + P.off_partial);
+  if (P.kind == kCullWinCols) {
+    A.csc = reinterpret_cast<const float*>(ws + P.off_csc);
+    A.gsc = reinterpret_cast<const float*>(ws + P.off_gsc);
+  }
   A.fault = fault_ptr();
   LR_REQUIRE(A.fault != nullptr, "could not resolve the device fault word");
   if (timer_id >= 0) ktimer_begin(timer_id, s);
@@ -651,6 +886,12 @@ lr_status launch_cull_sweep(const CullPlan& P, CullArgs A, char* ws, int timer_i
     }
   } else if (P.kind == kCullMom) {
     st = launch_sweep_t<kCullMom, 1>(P, A, s);
+  } else if (P.kind == kCullWin) {
+    st = launch_sweep_t<kCullWin, 1>(P, A, s);
+  } else if (P.kind == kCullWinRows) {
+    st = launch_sweep_t<kCullWinRows, 1>(P, A, s);
+  } else if (P.kind == kCullWinCols) {
+    st = launch_sweep_t<kCullWinCols, 4>(P, A, s);
   } else {
     switch (P.nw) {
       case 2: st = launch_sweep_t<kCullSelf, 2>(P, A, s); break;

@@ -8,7 +8,8 @@
 // together in the source plane. Without a layout chunks are consecutive indices.
 // A prepare kernel writes, per chunk, its bounding box and a record block:
 //   float4 box       (xlo, ylo, xhi, yhi)
-//   float4 unused
+//   float4 head      (points in the chunk, smallest reach scale s of its
+//                    windowed points (kCullWinCols), 0, 0)
 //   float4 xy[16]    source pair p = points (2p, 2p+1): (xa, xb, ya, yb)
 //   float2 w[NW][16] the pairs' weights
 // Positions are stored as they are: the sweeps form x_j - x_i directly, which
@@ -28,6 +29,27 @@
 // they are nonzero (the forward) or add them plainly (the moments, where
 // adding +0 changes nothing), so culled and unculled sweeps give the same
 // bits.
+//
+// Windowed kinds (the image-plane transmission, Sec. 3.4): the pair's
+// exponent is -(log2 e / 2) d^T C_i^-1 d with the covariance C_i = Z_i +
+// (l^2/2) I of the windowed point i, at most -s_i^2 |d|^2 with
+// s_i = sqrt(log2(e) / (2 lambda_max(C_i))). The same box test then runs with
+// the smallest s_i of the points involved: of the rows (a warp's or a CTA's)
+// when the rows carry the windows, of the chunk (stored with its box) when
+// the sources do.
+//
+// Window precision. At the paper's narrow image-plane kernels (2 to 10 mas)
+// the windows of magnified pixels are thin ellipses: C_i has a condition
+// number kappa of order 100. Forming det C_i or the quadratic form
+// mxx dx^2 + 2 mxy dx dy + myy dy^2 in FP32 loses about u kappa |exponent|,
+// past the 2e-5 bound. So a prepare kernel forms C_i = Z_i + (l^2/2) I and
+// det C_i in FP64 (the sums and the one cancelling difference; the rest is
+// well-conditioned in FP32) and writes, per point, the upper Cholesky factor
+// R of C_i^-1 scaled by
+// k = sqrt(log2(e) / 2), (a, b, c) = k (r11, r12, r22), the normalisation
+// N_i = 1 / (2 pi sqrt(det C_i)) and s_i. A pair then evaluates
+// w = (a dx + b dy, c dy), exponent -|w|^2 (a sum of squares: error about
+// u sqrt(kappa) |exponent|), and k^2 C^-1 d = R^T w = (a w1, b w1 + c w2).
 #pragma once
 #include "rowmap.cuh"
 #include "tma.cuh"
@@ -41,7 +63,7 @@ constexpr int kGroupChunks = 64;
 constexpr int kChunkW = 8, kChunkH = 4;  // chunk of an image layout (pixels)
 constexpr int kGroupW = 8, kGroupH = 8;  // group of an image layout (chunks)
 constexpr int kCullTileW = 16;           // row blocks: 16-pixel-wide image tiles
-constexpr int kRecHead = 32;             // box + unused
+constexpr int kRecHead = 32;             // box + head
 constexpr int kRecXY = 16 * kChunkPairs;  // float4 per source pair
 
 __host__ __device__ constexpr int rec_bytes(int nw) { return kRecHead + kRecXY + 8 * kChunkPairs * nw; }
@@ -95,14 +117,34 @@ __device__ __forceinline__ bool boxes_far(float4 a, float4 b, float sc) {
 
 // What a sweep computes and its chunk records' weights hold.
 enum CullKind : int32_t {
-  kCullOut = 0,   // nrhs weights: the columns of v   (forward)
-  kCullMom = 1,   // one weight a                     (row moments of a)
-  kCullSelf = 2,  // a (v) and b (g), nrhs columns each  (self-kernel backward)
+  kCullOut = 0,      // nrhs weights: the columns of v   (forward)
+  kCullMom = 1,      // one weight a                     (row moments of a)
+  kCullSelf = 2,     // a (v) and b (g), nrhs columns each  (self-kernel backward)
+  kCullWin = 3,      // windowed forward: rows carry windows, weight v
+  kCullWinRows = 4,  // windowed backward, row sums: rows carry windows, weight v
+  kCullWinCols = 5,  // windowed backward, column sums: the sources (the
+                     // windowed points) carry their window constants (a, b, c)
+                     // and g N as their four weights
 };
 
 __host__ __device__ constexpr int cull_nw(int kind, int nrhs) {
-  return kind == kCullOut ? nrhs : (kind == kCullMom ? 1 : 2 * nrhs);
+  return kind == kCullOut ? nrhs
+                          : (kind == kCullSelf ? 2 * nrhs : (kind == kCullWinCols ? 4 : 1));
 }
+
+// Sums per row of a sweep.
+__host__ __device__ constexpr int cull_k(int kind, int nw) {
+  return kind == kCullOut ? nw
+                          : kind == kCullMom ? 4
+                          : kind == kCullSelf ? 7 * (nw / 2)
+                          : kind == kCullWin ? 1
+                          : kind == kCullWinRows ? 6 : 3;
+}
+
+// Per-point window constants (see "Window precision" above): wcoef[i] =
+// (a, b, c, N) and wreach[i] = s_i from the windows z [n][3] and l.
+lr_status launch_window_prep(const float* z, int64_t n, float lengthscale, float4* wcoef, float* wreach,
+                             cudaStream_t s);
 
 struct CullPrepP {
   const float2* pts;  // [n] source points
@@ -115,6 +157,12 @@ struct CullPrepP {
   char* rec;          // [n_chunks][rec_bytes(nw)]
   float4* cbox;       // [n_chunks]
   float4* gbox;       // [n_groups]
+  // kCullWinCols: the points' window constants (launch_window_prep; a = g);
+  // the chunks' and groups' smallest reach scales
+  const float4* wcoef;
+  const float* wreach;
+  float* csc;         // [n_chunks]
+  float* gsc;         // [n_groups]
 };
 
 // Outputs of a culled sweep, by kind:
@@ -127,6 +175,13 @@ struct CullPrepP {
 //  kCullSelf: self-kernel backward for nrhs right-hand sides in one sweep
 //             (the pair's exp2 shared): d_v = var sum_j k g_j per column,
 //             d_x both roles summed over the columns, scalar partials.
+//  kCullWin:  out[i] = N_i sum_j G'_ij v_j, G' = 2^(-|R_i d|^2 k^2)
+//  kCullWinRows: per row, with d = x_i - y_j and u = k^2 C_i^-1 d, the six
+//             sums S = sum v G', P = sum v G' u, Q = sum v G' u u^T (xx, xy, yy)
+//  kCullWinCols: per row (a source of the windowed reduction), with
+//             d = x_i - y_j and u = k^2 C_j^-1 d, T = sum gN G', U = sum gN G' u
+//             The two backward kinds write partial[split][K][n] whatever the
+//             split count; the windowed backward merges them.
 struct CullArgs {
   const float2* x;   // [n] query points
   int64_t n;
@@ -154,6 +209,10 @@ struct CullArgs {
   float* d_v;        // kCullSelf: [n][stride] at column col
   double* scal_part; // [partial blocks][2]: d_l, d_var partials
   float* partial;    // splits > 1: [splits][K][n]
+  const float4* wcoef;  // kCullWin, kCullWinRows: the rows' window constants (a, b, c, N)
+  const float* wreach;  // and reach scales (launch_window_prep)
+  const float* csc;  // kCullWinCols: reach scales of the chunks and groups
+  const float* gsc;
   int* fault;        // device fault word (a bulk-copy wait that ran out)
   unsigned long long* count;  // diagnostic: [0] valid pairs, [1] pair slots evaluated
                               // (non-NULL: count only, no outputs written)
@@ -169,7 +228,7 @@ struct CullPlan {
   int64_t row_blocks;
   int32_t splits;
   int64_t scal_blocks;  // blocks that write scalar partials
-  size_t off_rec, off_cbox, off_gbox, off_partial, off_scal, bytes;
+  size_t off_rec, off_cbox, off_gbox, off_csc, off_gsc, off_partial, off_scal, bytes;
 };
 
 // 1 unless lr_set_pair_culling(0) switched exact skipping off.
@@ -180,9 +239,11 @@ lr_status plan_cull(int kind, int nrhs, int64_t n, const lr_grid* qlayout, int64
                     CullPlan* P);
 // Writes the source chunks' boxes and records into ws (offsets of P):
 // kCullOut weights a [m][stride] (all nrhs columns), kCullMom column col of a,
-// kCullSelf column col of a and of b.
+// kCullSelf column col of a and of b, kCullWin / kCullWinRows a [m],
+// kCullWinCols the points' window constants (wcoef, wreach) and g = a [m].
 lr_status launch_cull_prep(const CullPlan& P, const float2* pts, float sc, const float* a, const float* b,
-                           int32_t stride, int32_t col, char* ws, cudaStream_t s);
+                           int32_t stride, int32_t col, char* ws, cudaStream_t s, const float4* wcoef = nullptr,
+                           const float* wreach = nullptr);
 // The sweep (and merge when P.splits > 1); A carries the kind's outputs.
 // timer_id: an LR_KT_* launch-timer id, or -1.
 lr_status launch_cull_sweep(const CullPlan& P, CullArgs A, char* ws, int timer_id, cudaStream_t s);

@@ -7,10 +7,14 @@
 // with the transmission weights A_k folded into v_k by the caller. Each
 // query row carries its own 2x2 inverse covariance (three coefficients,
 // pre-scaled for exp2) and normalisation; per pair the exponent is a
-// quadratic form in (dx, dy). Same tiling, chunking and fixed-order merge as
-// the stationary reduction.
+// quadratic form in (dx, dy). Grid sources: the grid tiling, chunking and
+// fixed-order merge of the stationary reduction (windowed_kernel). Explicit
+// sources (the image-plane layers, the pixels against themselves): the
+// culled sweep of cull.cu, which leaves out the pairs whose exponent is below
+// -126 by bounding boxes.
 #include <math.h>
 
+#include "cull.cuh"
 #include "host.cuh"
 #include "problems.cuh"
 
@@ -44,8 +48,7 @@ struct WnArgs {
   const float2* p;
   const float* z;
   int64_t n;
-  const float2* q;  // explicit sources, or NULL for the grid
-  GridDev g;
+  GridDev g;        // the source grid
   int64_t m;
   int32_t segs, n_tiles, chunks;
   const float* v;
@@ -56,40 +59,26 @@ struct WnArgs {
 
 __device__ __forceinline__ float2 wf2(float a, float b) { return make_float2(a, b); }
 
+// Source tile t: a 256-column segment of one grid row.
 __device__ __forceinline__ void wn_tile(const WnArgs& A, int t, int64_t& j0, int& cnt, int& grow) {
-  if (A.q) {
-    j0 = (int64_t)t * kWnTile;
-    const int64_t rem = A.m - j0;
-    cnt = rem < kWnTile ? (int)rem : kWnTile;
-    grow = 0;
-  } else {
-    grow = t / A.segs;
-    const int c0 = (t - grow * A.segs) * kWnTile;
-    cnt = min(kWnTile, A.g.W - c0);
-    j0 = (int64_t)grow * A.g.W + c0;
-  }
+  grow = t / A.segs;
+  const int c0 = (t - grow * A.segs) * kWnTile;
+  cnt = min(kWnTile, A.g.W - c0);
+  j0 = (int64_t)grow * A.g.W + c0;
 }
 
-template <bool GRID>
 __device__ __forceinline__ void wn_load(const WnArgs& A, int t, int p, float4& P, float2& V) {
   int64_t j0;
   int cnt, grow;
   wn_tile(A, t, j0, cnt, grow);
   const int a = 2 * p, b = 2 * p + 1;
-  if (GRID) {
-    // abscissae relative to the centre column of their 16-column sub-segment
-    const int c0 = (int)(j0 - (int64_t)grow * A.g.W);
-    const float o = grid_x(A.g, c0 + kWnSeg * (a / kWnSeg) + kWnSeg / 2);
-    P = make_float4((a < cnt) ? grid_x(A.g, c0 + a) - o : 0.f, (b < cnt) ? grid_x(A.g, c0 + b) - o : 0.f, 0.f, 0.f);
-  } else {
-    const float2 qa = (a < cnt) ? __ldg(A.q + j0 + a) : wf2(0.f, 0.f);
-    const float2 qb = (b < cnt) ? __ldg(A.q + j0 + b) : wf2(0.f, 0.f);
-    P = make_float4(-qa.x, -qb.x, -qa.y, -qb.y);
-  }
+  // abscissae relative to the centre column of their 16-column sub-segment
+  const int c0 = (int)(j0 - (int64_t)grow * A.g.W);
+  const float o = grid_x(A.g, c0 + kWnSeg * (a / kWnSeg) + kWnSeg / 2);
+  P = make_float4((a < cnt) ? grid_x(A.g, c0 + a) - o : 0.f, (b < cnt) ? grid_x(A.g, c0 + b) - o : 0.f, 0.f, 0.f);
   V = wf2((a < cnt) ? __ldg(A.v + j0 + a) : 0.f, (b < cnt) ? __ldg(A.v + j0 + b) : 0.f);
 }
 
-template <bool GRID>
 __global__ void __launch_bounds__(kWnThreads) windowed_kernel(const __grid_constant__ WnArgs A) {
   __shared__ __align__(16) float4 sP[2][kWnPairs];
   __shared__ __align__(16) float2 sV[2][kWnPairs];
@@ -125,19 +114,18 @@ __global__ void __launch_bounds__(kWnThreads) windowed_kernel(const __grid_const
   float4 P;
   float2 V;
   if (t0 < t1) {
-    wn_load<GRID>(A, t0, tid, P, V);
+    wn_load(A, t0, tid, P, V);
     sP[0][tid] = P;
     sV[0][tid] = V;
   }
   __syncthreads();
   for (int t = t0; t < t1; ++t) {
     const int buf = (t - t0) & 1;
-    if (t + 1 < t1) wn_load<GRID>(A, t + 1, tid, P, V);
+    if (t + 1 < t1) wn_load(A, t + 1, tid, P, V);
     int64_t j0;
     int cnt, grow;
     wn_tile(A, t, j0, cnt, grow);
-    const int np = (cnt + 1) >> 1;
-    if (GRID) {
+    {
       // Uniform y on a grid row: completing the square in dx,
       //   -e = -mxx (dx + kap dy)^2 + lam dy^2,  kap = mxy2 / (2 mxx),
       //   lam = mxy2^2 / (4 mxx) - myy >= 0,
@@ -180,22 +168,6 @@ __global__ void __launch_bounds__(kWnThreads) windowed_kernel(const __grid_const
             const float2 k = wf2(ex2_approx(-t.x), ex2_approx(-t.y));
             acc[r] = __ffma2_rn(k, W, acc[r]);
           }
-        }
-      }
-    } else {
-#pragma unroll 2
-      for (int p = 0; p < np; ++p) {
-        const float4 Q = sP[buf][p];
-        const float2 W = sV[buf][p];
-        const float2 nx = wf2(Q.x, Q.y), ny = wf2(Q.z, Q.w);
-#pragma unroll
-        for (int r = 0; r < kWnR; ++r) {
-          const float2 dx = __fadd2_rn(xq[r], nx);
-          const float2 dy = __fadd2_rn(yq[r], ny);
-          const float2 u = __ffma2_rn(mxx[r], dx, __fmul2_rn(mxy2[r], dy));
-          const float2 e = __ffma2_rn(dx, u, __fmul2_rn(__fmul2_rn(myy[r], dy), dy));
-          const float2 k = wf2(ex2_approx(e.x), ex2_approx(e.y));
-          acc[r] = __ffma2_rn(k, W, acc[r]);
         }
       }
     }
@@ -241,28 +213,48 @@ __global__ void windowed_merge_kernel(const float* __restrict__ partial, int chu
 }
 
 struct WnPlan {
-  int32_t n_tiles, segs, chunks, row_blocks;
+  int32_t n_tiles, segs, chunks, row_blocks;  // grid sources
+  int32_t culled;                             // explicit sources: the culled sweep
+  CullPlan C;
+  size_t off_wcoef, off_wreach;               // the rows' window constants
   size_t bytes;
 };
 
-static lr_status plan_windowed(int64_t n, const lr_points* s, WnPlan* P) {
+// The query layout, when given, must describe exactly the n query points.
+static lr_status check_layout(const lr_grid* layout, int64_t n, const char* what) {
+  if (!layout) return LR_OK;
+  LR_REQUIRE(layout->nx > 0 && layout->ny > 0 && layout->ss > 0 &&
+                 (int64_t)layout->nx * layout->ss * layout->ny * layout->ss == n,
+             "%s: the layout (%d x %d x %d^2) does not hold the %lld query points", what, layout->nx, layout->ny,
+             layout->ss, (long long)n);
+  return LR_OK;
+}
+
+static lr_status plan_windowed(int64_t n, const lr_grid* layout, const lr_points* s, WnPlan* P) {
   lr_status st = validate_points(s, "gp_windowed_matvec(source)", false);
   if (st != LR_OK) return st;
   LR_REQUIRE(!has_lens(s), "gp_windowed_matvec: sources must not carry a lens");
   LR_REQUIRE(n >= 0 && n < (int64_t(1) << 31), "gp_windowed_matvec: n out of range");
+  if ((st = check_layout(layout, n, "gp_windowed_matvec")) != LR_OK) return st;
   WnPlan p{};
-  if (s->xy == nullptr) {
-    const int W = s->grid.nx * s->grid.ss;
-    p.segs = (W + kWnTile - 1) / kWnTile;
-    p.n_tiles = (int32_t)((int64_t)p.segs * s->grid.ny * s->grid.ss);
-  } else {
-    p.n_tiles = (int32_t)((s->n + kWnTile - 1) / kWnTile);
+  if (s->xy != nullptr) {
+    p.culled = 1;
+    st = plan_cull(kCullWin, 1, n, layout, s->n, query_layout(s), &p.C);
+    if (st != LR_OK) return st;
+    p.off_wcoef = align256(p.C.bytes);
+    p.off_wreach = p.off_wcoef + align256(16 * (size_t)n);
+    p.bytes = p.off_wreach + align256(4 * (size_t)n);
+    *P = p;
+    return LR_OK;
   }
+  const int W = s->grid.nx * s->grid.ss;
+  p.segs = (W + kWnTile - 1) / kWnTile;
+  p.n_tiles = (int32_t)((int64_t)p.segs * s->grid.ny * s->grid.ss);
   p.row_blocks = (int32_t)((n + kWnRows - 1) / kWnRows);
   int dev = 0, n_sm = 1, occ = 1;
   LR_CHECK_CUDA(cudaGetDevice(&dev));
   LR_CHECK_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
-  LR_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, windowed_kernel<false>, kWnThreads, 0));
+  LR_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, windowed_kernel, kWnThreads, 0));
   p.chunks = plan_chunks(p.row_blocks, p.n_tiles, occ, n_sm);
   p.bytes = p.chunks > 1 ? align256(4 * (size_t)p.chunks * (size_t)n) : 0;
   *P = p;
@@ -284,20 +276,21 @@ extern "C" lr_status gp_pixel_shapes(const float* p, int32_t W, int32_t H, float
   return LR_OK;
 }
 
-extern "C" lr_status lr_windowed_workspace_size(int64_t n, const lr_points* source, size_t* bytes) {
+extern "C" lr_status lr_windowed_workspace_size(int64_t n, const lr_grid* layout, const lr_points* source,
+                                                size_t* bytes) {
   LR_REQUIRE(bytes != nullptr, "lr_windowed_workspace_size: bytes is NULL");
   WnPlan P;
-  lr_status st = plan_windowed(n, source, &P);
+  lr_status st = plan_windowed(n, layout, source, &P);
   if (st != LR_OK) return st;
   *bytes = P.bytes;
   return LR_OK;
 }
 
-extern "C" lr_status gp_windowed_matvec(const float* p, const float* z, int64_t n, const lr_points* source,
-                                        const float* v, float lengthscale, float* out, void* workspace,
-                                        size_t workspace_bytes, lr_stream stream) {
+extern "C" lr_status gp_windowed_matvec(const float* p, const float* z, int64_t n, const lr_grid* layout,
+                                        const lr_points* source, const float* v, float lengthscale, float* out,
+                                        void* workspace, size_t workspace_bytes, lr_stream stream) {
   WnPlan P;
-  lr_status st = plan_windowed(n, source, &P);
+  lr_status st = plan_windowed(n, layout, source, &P);
   if (st != LR_OK) return st;
   LR_REQUIRE(isfinite(lengthscale) && lengthscale > 0.f, "gp_windowed_matvec: lengthscale must be > 0");
   LR_REQUIRE(n == 0 || (p != nullptr && z != nullptr && out != nullptr), "gp_windowed_matvec: NULL pointer");
@@ -312,26 +305,40 @@ extern "C" lr_status gp_windowed_matvec(const float* p, const float* z, int64_t 
     LR_CHECK_CUDA(cudaMemsetAsync(out, 0, 4 * (size_t)n, s));
     return LR_OK;
   }
+  const float half_s = 0.5f * lengthscale * lengthscale;
+  if (P.culled) {
+    char* ws = static_cast<char*>(workspace);
+    float4* wcoef = reinterpret_cast<float4*>(ws + P.off_wcoef);
+    float* wreach = reinterpret_cast<float*>(ws + P.off_wreach);
+    if ((st = launch_window_prep(z, n, lengthscale, wcoef, wreach, s)) != LR_OK) return st;
+    st = launch_cull_prep(P.C, reinterpret_cast<const float2*>(source->xy), 0.f, v, nullptr, 1, 0, ws, s);
+    if (st != LR_OK) return st;
+    CullArgs A{};
+    A.x = reinterpret_cast<const float2*>(p);
+    A.n = n;
+    A.nrhs = 1;
+    A.stride = 1;
+    A.wcoef = wcoef;
+    A.wreach = wreach;
+    A.out = out;
+    return launch_cull_sweep(P.C, A, ws, LR_KT_WINDOWED, s);
+  }
   WnArgs A{};
   A.p = reinterpret_cast<const float2*>(p);
   A.z = z;
   A.n = n;
-  A.q = reinterpret_cast<const float2*>(source->xy);
-  A.g = source->xy ? GridDev{} : grid_dev(source->grid);
+  A.g = grid_dev(source->grid);
   A.m = source->n;
   A.segs = P.segs;
   A.n_tiles = P.n_tiles;
   A.chunks = P.chunks;
   A.v = v;
-  A.half_s = 0.5f * lengthscale * lengthscale;
+  A.half_s = half_s;
   A.out = out;
   A.partial = static_cast<float*>(workspace);
   const unsigned grid = (unsigned)((int64_t)P.row_blocks * P.chunks);
   ktimer_begin(LR_KT_WINDOWED, s);
-  if (A.q)
-    windowed_kernel<false><<<grid, kWnThreads, 0, s>>>(A);
-  else
-    windowed_kernel<true><<<grid, kWnThreads, 0, s>>>(A);
+  windowed_kernel<<<grid, kWnThreads, 0, s>>>(A);
   LR_CHECK_CUDA(cudaGetLastError());
   ktimer_end(LR_KT_WINDOWED, s);
   if (P.chunks > 1) {

@@ -110,12 +110,12 @@ def loss_and_grads(cfg: ModelConfig, guide: Guide, data: torch.Tensor, eps_sp: t
     w_sp = api.vec_axpby(a_sp, y_sp)
     f = api.gp_kernel_matvec(api.Points(xy=beta), src, w_sp, cfg.sigma_sp / math.sqrt(2.0), 1.0)
     z = api.pixel_shapes(beta, W, H)
-    self_pts = api.Points(xy=beta)
+    self_pts = api.Points(xy=beta, grid=cfg.pixels)  # the pixels in their image layout
     a_layers, w_layers = [], []
     for y, s in zip(ys, cfg.sigma_layers):
         a_k = api.knn_density(beta, cfg.knn_k, lengthscale=s, want_r2=False)
         w = api.vec_mul(a_k, y)
-        api.vec_axpby(1.0, f, 1.0, api.gp_windowed_matvec(beta, z, self_pts, w, s), out=f)
+        api.vec_axpby(1.0, f, 1.0, api.gp_windowed_matvec(beta, z, self_pts, w, s, layout=cfg.pixels), out=f)
         a_layers.append(a_k)
         w_layers.append(w)
     nll, g, _ = api.gaussian_nll(f, data, cfg.noise)
@@ -125,7 +125,7 @@ def loss_and_grads(cfg: ModelConfig, guide: Guide, data: torch.Tensor, eps_sp: t
     grads = {"layers_mu": [], "layers_sd": []}
     for y, s, a_k, w, mu, sd, e, al in zip(ys, cfg.sigma_layers, a_layers, w_layers, guide.mu_layers,
                                            guide.sd_layers, eps_layers, cfg.alpha_layers):
-        G = api.gp_windowed_matvec_bwd(beta, z, self_pts, w, s, g, want=("v", "p", "q", "z"))
+        G = api.gp_windowed_matvec_bwd(beta, z, self_pts, w, s, g, want=("v", "p", "q", "z"), layout=cfg.pixels)
         if d_beta is None:
             d_beta = api.vec_axpby(1.0, G["p"], 1.0, G["q"])
             d_z = G["z"]

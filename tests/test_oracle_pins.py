@@ -674,3 +674,57 @@ def test_pixel_shapes_vjp_by_central_differences(orc):
     dz = rng.normal(size=(W * H, 3))
     f = lambda a: np.sum(dz * orc.pixel_shapes(a, W, H))
     np.testing.assert_allclose(orc.pixel_shapes_vjp(P, W, H, dz), _cd(f, P, 1e-6), rtol=1e-7, atol=1e-9)
+
+
+# ---- FP32 rounding sensitivities of the windowed reduction (a tolerance term)
+
+def test_windowed_rounding_isotropic_closed_form(orc):
+    """Without windows (Z = 0, C = l^2/2 I) R is diagonal, w^ = |w| and the
+    relative error bound of a Gaussian factor is rho = 3 q with q = 2 |d|^2 / l^2."""
+    rng = np.random.default_rng(1)
+    p = rng.uniform(-0.3, 0.3, (40, 2))
+    q = rng.uniform(-0.3, 0.3, (25, 2))
+    v = rng.standard_normal(25)
+    ell = 0.07
+    S = orc.windowed_rounding(p, np.zeros((40, 3)), q, v, ell)
+    d2 = ((p[:, None, :] - q[None, :, :]) ** 2).sum(-1)
+    qq = 2.0 * d2 / ell ** 2
+    G = np.exp(-0.5 * qq) / (np.pi * ell ** 2)
+    np.testing.assert_allclose(S["s_out"], (np.abs(G * v) * 3 * qq).sum(1), rtol=1e-12)
+
+
+def test_windowed_rounding_bounds_an_fp32_evaluation(orc):
+    """The bound holds for a plain FP32 evaluation of the Cholesky form with
+    rounded differences and constants, on thin windows (condition numbers up
+    to 1e3) and pairs out to exponents near the FP32 range."""
+    rng = np.random.default_rng(2)
+    n, m, ell = 60, 400, 0.002
+    p = rng.uniform(-0.2, 0.2, (n, 2)).astype(np.float32)
+    q = rng.uniform(-0.2, 0.2, (m, 2)).astype(np.float32)
+    th = rng.uniform(0, np.pi, n)
+    l1, l2 = 10 ** rng.uniform(-4, -3, n), 10 ** rng.uniform(-7, -5, n)
+    c, s_ = np.cos(th), np.sin(th)
+    z = np.stack([l1 * c * c + l2 * s_ * s_, (l1 - l2) * c * s_, l1 * s_ * s_ + l2 * c * c], 1).astype(np.float32)
+    v = rng.standard_normal(m).astype(np.float32)
+    ref, _ = orc.windowed_matvec(p, z, q, v, ell)
+    S = orc.windowed_rounding(p, z, q, v, ell)
+    # FP32: constants from FP64 rounded once, differences and the form in FP32
+    zz = z.astype(np.float64)
+    hs = 0.5 * ell * ell
+    cxx, cxy, cyy = zz[:, 0] + hs, zz[:, 1], zz[:, 2] + hs
+    det = cxx * cyy - cxy * cxy
+    k = np.sqrt(np.log2(np.e) / 2)
+    a = (k * np.sqrt(cyy / det)).astype(np.float32)
+    b = (-k * cxy / np.sqrt(cyy * det)).astype(np.float32)
+    cc = (k / np.sqrt(cyy)).astype(np.float32)
+    N = 1.0 / (2 * np.pi * np.sqrt(det))
+    dx = (q[None, :, 0] - p[:, None, 0]).astype(np.float32)
+    dy = (q[None, :, 1] - p[:, None, 1]).astype(np.float32)
+    w1 = (a[:, None] * dx + b[:, None] * dy).astype(np.float32)
+    w2 = (cc[:, None] * dy).astype(np.float32)
+    t = (w1 * w1 + w2 * w2).astype(np.float32)
+    G = np.exp2(-t.astype(np.float64)) * N[:, None]
+    out = (G * v[None, :].astype(np.float64)).sum(1)
+    err = np.abs(out - ref)
+    assert np.all(err <= 2 * 2.0 ** -24 * S["s_out"] + 1e-300)
+    assert np.max(err / (2 * 2.0 ** -24 * S["s_out"] + 1e-300)) > 1e-3  # the bound is not vacuous
