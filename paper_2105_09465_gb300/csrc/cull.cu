@@ -766,12 +766,16 @@ lr_status plan_cull(int kind, int nrhs, int64_t n, const lr_grid* qlayout, int64
   LR_CHECK_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
   LR_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, cull_kernel_ptr(kind, P.nw), kCullThreads, 0));
   // group ranges per row block: only when the row blocks alone leave most of
-  // the resident CTA slots empty (small query sets). Rows that carry windows
-  // differ in reach by orders of magnitude (pixels next to the lens centre
-  // reach arcseconds, half the image), so the work of a row block does too:
-  // there many more group ranges spread the widest row blocks over the GPU.
+  // the resident CTA slots empty (small query sets). Windowed points differ
+  // in reach by orders of magnitude (pixels next to the lens centre reach
+  // arcseconds, half the image), so the work of a row block does too: there
+  // many more group ranges spread the heaviest row blocks over the GPU.
   const int64_t slots = (int64_t)(occ > 0 ? occ : 1) * n_sm;
-  const int64_t target = (kind == kCullWin || kind == kCullWinRows) ? 16 * slots : 2 * slots;
+  // (measured on the 400 x 400 image: 48 for the sweeps whose rows carry the
+  // windows, 16 for the column sweep, against 2 for the stationary sweeps)
+  const int64_t target = (kind == kCullWin || kind == kCullWinRows) ? 48 * slots
+                         : kind == kCullWinCols                       ? 16 * slots
+                                                                      : 2 * slots;
   int64_t splits = 1;
   if (P.row_blocks > 0 && P.row_blocks < target) splits = (target + P.row_blocks - 1) / P.row_blocks;
   if (splits > P.L.n_groups) splits = P.L.n_groups > 0 ? P.L.n_groups : 1;
