@@ -84,7 +84,7 @@ def lib():
         L.orc_knn_r2.argtypes = [_P, _I64, _I32, _P, _I64, _P]
         L.orc_windowed_vjp.argtypes = [_P, _P, _I64, _P, _I64, _P, _D, _P] + [_P] * 10
         L.orc_windowed_rounding.argtypes = [_P, _P, _I64, _P, _I64, _P, _D, _P] + [_P] * 6
-        L.orc_pixel_shapes_vjp.argtypes = [_P, _I32, _I32, _P, _P]
+        L.orc_pixel_shapes_vjp.argtypes = [_P, _I32, _I32, _P, _P, _P]
         L.orc_kernel_matvec.argtypes = [_P, _I64, _P, _I64, _P, _D, _D, _P, _I64, _P, _P, _P]
         L.orc_kernel_matvec_vjp.argtypes = [_P, _I64, _P, _I64, _P, _D, _D, _P, _I32, _P, _P, _P, _P, _P, _P]
         L.orc_self_vjp_rows.argtypes = [_P, _I64, _P, _P, _D, _D, _P, _I64] + [_P] * 8
@@ -244,13 +244,15 @@ def windowed_rounding(p, z, q, v, lengthscale, g=None):
     return S
 
 
-def pixel_shapes_vjp(p, W, H, dz):
-    """dL/dp (W*H, 2) through pixel_shapes given dL/dZ (W*H, 3)."""
+def pixel_shapes_vjp(p, W, H, dz, with_abs=False):
+    """dL/dp (W*H, 2) through pixel_shapes given dL/dZ (W*H, 3); with
+    `with_abs`, also the sums of absolute terms (a tolerance scale)."""
     p = _pairs(p)
     dz = np.ascontiguousarray(dz, np.float64)
     dp = np.empty((W * H, 2), np.float64)
-    lib().orc_pixel_shapes_vjp(_ptr(p), W, H, _ptr(dz), _ptr(dp))
-    return dp
+    ab = np.empty((W * H, 2), np.float64) if with_abs else None
+    lib().orc_pixel_shapes_vjp(_ptr(p), W, H, _ptr(dz), _ptr(dp), _ptr(ab))
+    return (dp, ab) if with_abs else dp
 
 
 def knn_r2(q, k, rows=None):

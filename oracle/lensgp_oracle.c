@@ -730,9 +730,11 @@ ORC_API void orc_windowed_rounding(const double* p, const double* z, int64_t n, 
  * (n x 2) for the W x H grid of projected centres of orc_pixel_shapes, by
  * differentiating Z_i = (a a^T + b b^T)/(4 pi) and scattering the window
  * vectors' gradients onto the neighbours they are differences of. */
-ORC_API void orc_pixel_shapes_vjp(const double* p, int32_t W, int32_t H, const double* dz, double* dp) {
+ORC_API void orc_pixel_shapes_vjp(const double* p, int32_t W, int32_t H, const double* dz, double* dp,
+                                  double* dp_abs) {
   (void)p;
   memset(dp, 0, sizeof(double) * 2 * (size_t)W * (size_t)H);
+  if (dp_abs) memset(dp_abs, 0, sizeof(double) * 2 * (size_t)W * (size_t)H);
   for (int64_t r = 0; r < H; ++r)
     for (int64_t c = 0; c < W; ++c) {
       const int64_t i = r * W + c;
@@ -754,6 +756,17 @@ ORC_API void orc_pixel_shapes_vjp(const double* p, int32_t W, int32_t H, const d
       dp[2 * ru + 1] += sb * dby;
       dp[2 * rd] -= sb * dbx;
       dp[2 * rd + 1] -= sb * dby;
+      if (dp_abs) {
+        /* scales: the absolute terms of the same scatter */
+        const double ax_ = k * (2.0 * fabs(gxx * ax) + fabs(gxy * ay)), ay_ = k * (fabs(gxy * ax) + 2.0 * fabs(gyy * ay));
+        const double bx_ = k * (2.0 * fabs(gxx * bx) + fabs(gxy * by)), by_ = k * (fabs(gxy * bx) + 2.0 * fabs(gyy * by));
+        const int64_t js[4] = {cr, cl, ru, rd};
+        const double wx[4] = {sa * ax_, sa * ax_, sb * bx_, sb * bx_}, wy[4] = {sa * ay_, sa * ay_, sb * by_, sb * by_};
+        for (int t = 0; t < 4; ++t) {
+          dp_abs[2 * js[t]] += wx[t];
+          dp_abs[2 * js[t] + 1] += wy[t];
+        }
+      }
     }
 }
 

@@ -82,10 +82,12 @@ def _unit_draw(M: int, dev) -> tuple[torch.Tensor, torch.Tensor]:
 
 
 def loss_and_grads(cfg: ModelConfig, guide: Guide, data: torch.Tensor, eps_sp: torch.Tensor,
-                   eps_layers: list[torch.Tensor]) -> tuple[torch.Tensor, dict]:
+                   eps_layers: list[torch.Tensor], trace: dict | None = None) -> tuple[torch.Tensor, dict]:
     """Loss of one reparameterised draw (given the standard-normal draws), as
     a (1,) float64 device tensor, and its gradients with respect to every
-    guide parameter."""
+    guide parameter. `trace`, when given, receives the step's intermediate
+    device tensors (the draw, the ray-traced pixels, windows, weights, model
+    fluxes, dL/df and the layers' gradients) for inspection."""
     dev = data.device
     M = guide.sd_sp.numel()
     W, H = cfg.pixels.nx, cfg.pixels.ny
@@ -119,6 +121,9 @@ def loss_and_grads(cfg: ModelConfig, guide: Guide, data: torch.Tensor, eps_sp: t
         a_layers.append(a_k)
         w_layers.append(w)
     nll, g, _ = api.gaussian_nll(f, data, cfg.noise)
+    if trace is not None:
+        trace.update(x=x, beta=beta, z=z, f=f, g=g, nll=nll, ys=ys, a_layers=a_layers, w_layers=w_layers,
+                     w_sp=w_sp)
 
     # ---- backward: dL/dbeta summed over the layers (in place)
     d_beta = d_z = None
@@ -133,6 +138,8 @@ def loss_and_grads(cfg: ModelConfig, guide: Guide, data: torch.Tensor, eps_sp: t
             api.vec_axpby(1.0, d_beta, 1.0, G["p"], out=d_beta)
             api.vec_axpby(1.0, d_beta, 1.0, G["q"], out=d_beta)
             api.vec_axpby(1.0, d_z, 1.0, G["z"], out=d_z)
+        if trace is not None:
+            trace.setdefault("layer_grads", []).append(G)
         d_mu, d_sd, _ = api.diag_normal_vjp(mu, sd, e, al, api.vec_mul(a_k, G["v"]), 1.0, 1.0)
         grads["layers_mu"].append(d_mu)
         grads["layers_sd"].append(d_sd)
@@ -144,9 +151,13 @@ def loss_and_grads(cfg: ModelConfig, guide: Guide, data: torch.Tensor, eps_sp: t
         api.vec_axpby(1.0, d_beta, 1.0, api.pixel_shapes_vjp(beta, W, H, d_z), out=d_beta)
         api.vec_axpby(1.0, d_beta, 1.0, Gs["x"], out=d_beta)
     d_lens, _ = api.lens_raytrace_vjp(pix, d_beta)
+    if trace is not None:
+        trace.update(source_grads=Gs)
     # the source-plane layer's weights and its prior: d(-ln p)/dy_sp = y_sp / alpha^2
     d_ysp = api.vec_axpby(a_sp, Gs["v"], 1.0 / cfg.alpha_sp ** 2, y_sp)
     d_x = api.vec_pack(d_lens, d_ysp)
+    if trace is not None:
+        trace.update(d_x=d_x)
     d_mu, d_L, d_C, d_sd = api.partial_mvn_vjp(guide.L, guide.sd_sp, eps_sp, d_x, 1.0)
     grads.update(mu=d_mu, L=d_L, C=d_C, sd_sp=d_sd, d_lens=d_lens, d_beta=d_beta)
 

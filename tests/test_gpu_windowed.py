@@ -117,8 +117,9 @@ def test_pixel_shapes_vjp(orc):
     g_, b = lensed_grid(orc, side=40)
     dz = np.random.default_rng(22).standard_normal((len(b), 3)).astype(np.float32)
     got = host(api.pixel_shapes_vjp(dev(b), g_.nx, g_.ny, dev(dz)))
-    ref = orc.pixel_shapes_vjp(b, g_.nx, g_.ny, dz)
-    np.testing.assert_allclose(got, ref, rtol=1e-4, atol=1e-5 * np.abs(ref).max())
+    ref, ab = orc.pixel_shapes_vjp(b, g_.nx, g_.ny, dz, with_abs=True)
+    # FP32 products and a gather of up to four neighbours' terms: 16 u of the absolute terms
+    _close(got, ref, ab, 16 * 2.0 ** -24, "pixel-window VJP")
 
 
 # ---- the image-plane layer with exact skipping of far pairs
