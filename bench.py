@@ -32,6 +32,7 @@ ROOT = Path(__file__).resolve().parent
 sys.path.insert(0, str(ROOT))
 
 METRIC = "Gpair-evals/s fused raytrace+GP kernel matvec (fwd, fwd+bwd); p50/p99 req latency"
+FILL_PAIRS = 8_000_000_000  # pairs per iteration that fill the GPU (about a 384-px request at 2x2 on 128^2)
 UNIT = "Gpair/s"
 SM_MAX_MHZ_DEFAULT = 2070.0
 # Work per point-subhalo pair, counted operation by operation from the
@@ -343,7 +344,7 @@ def run_serving(n_req: int, iters: int) -> dict:
     grid, `iters` fwd+bwd+update iterations each) through the session engine:
     all requests at t = 0 with continuous batching (16 slots) and one at a
     time (1 slot, per-request launches), then Poisson arrivals at 70 % of the
-    measured batched capacity."""
+    measured batched capacity through both."""
     import threading as th
 
     from paper_2105_09465_gb300 import workloads as W
@@ -366,8 +367,12 @@ def run_serving(n_req: int, iters: int) -> dict:
     with Session(max_slots=2) as S:  # warm-up (module load, pools)
         p = trace[0]["problem"]
         S.poll(S.submit(p, datas[0], 2, step))
-    for mode, slots in (("batched", 16), ("unbatched", 1)):
-        with Session(max_slots=slots) as S:
+    # three engines: 16 slots; one request at a time; 16 slots admitted only
+    # while the active requests' pairs per iteration stay within FILL_PAIRS
+    # (requests that fill the GPU alone run alone, small ones share it)
+    modes = (("batched", 16, 0), ("unbatched", 1, 0), ("filled", 16, FILL_PAIRS))
+    for mode, slots, fill in modes:
+        with Session(max_slots=slots, fill_pairs=fill) as S:
             t0 = time.perf_counter()
             ts = [S.submit(r["problem"], d, iters, step) for r, d in zip(trace, datas)]
             res = [S.poll(t, timeout_s=600, want=()) for t in ts]
@@ -378,31 +383,39 @@ def run_serving(n_req: int, iters: int) -> dict:
         out[mode] = {"value": pairs / wall / 1e9, "wall_s": wall, "req_per_s": n_req / wall,
                      "batched_launches": st["launches"], "iterations": st["iterations"], **pct(lat)}
     out["speedup_batched_vs_unbatched"] = out["batched"]["value"] / out["unbatched"]["value"]
-    # Poisson arrivals at 70 % of the measured batched capacity
+    # Poisson arrivals (the serving workload's stream, its rate scaled to this
+    # GPU: 70 % of the measured batched capacity), the same arrival times for
+    # the batched engine and for one request at a time
     rate = 0.7 * out["batched"]["req_per_s"]
     arr = np.cumsum(np.random.default_rng(5).exponential(1.0 / rate, n_req))
-    with Session(max_slots=16) as S:
-        tickets = [None] * n_req
-        t0 = time.perf_counter()
+    for mode, slots, fill in modes:
+        with Session(max_slots=slots, fill_pairs=fill) as S:
+            tickets = [None] * n_req
+            t0 = time.perf_counter()
 
-        def feeder():
-            for k, (r, d) in enumerate(zip(trace, datas)):
-                dt = arr[k] - (time.perf_counter() - t0)
-                if dt > 0:
-                    time.sleep(dt)
-                tickets[k] = S.submit(r["problem"], d, iters, step)
+            def feeder():
+                for k, (r, d) in enumerate(zip(trace, datas)):
+                    dt = arr[k] - (time.perf_counter() - t0)
+                    if dt > 0:
+                        time.sleep(dt)
+                    tickets[k] = S.submit(r["problem"], d, iters, step)
 
-        f = th.Thread(target=feeder)
-        f.start()
-        res = []
-        for k in range(n_req):
-            while tickets[k] is None:
-                time.sleep(0.0005)
-            res.append(S.poll(tickets[k], timeout_s=600, want=()))
-        f.join()
-        wall = time.perf_counter() - t0
-    out["poisson_70pct"] = {"rate_req_per_s": rate, "value": pairs / wall / 1e9, "wall_s": wall,
-                            **pct([r.latency for r in res])}
+            f = th.Thread(target=feeder)
+            f.start()
+            res = []
+            for k in range(n_req):
+                while tickets[k] is None:
+                    time.sleep(0.0005)
+                res.append(S.poll(tickets[k], timeout_s=600, want=()))
+            f.join()
+            wall = time.perf_counter() - t0
+        assert all(r.status == 0 for r in res), [r.status for r in res]
+        out[f"poisson_70pct_{mode}"] = {"rate_req_per_s": rate, "value": pairs / wall / 1e9, "wall_s": wall,
+                                        **pct([r.latency for r in res])}
+    out["speedup_filled_vs_unbatched"] = out["filled"]["value"] / out["unbatched"]["value"]
+    out["latency_note"] = ("most requests of this trace fill the GPU alone, so sharing it among 16 stretches each "
+                           "one (all-at-once p50 above one-at-a-time FIFO's); admission by pairs per iteration "
+                           "batches only the small ones")
     return out
 
 
@@ -516,6 +529,14 @@ def run_extensions(p, dev, rates, sm_max, flush, stream) -> dict:
                     stream, flush)
     out["matvec_layers<grid> x3"] = dict(roof(p.pairs, ms, 3, 10), layers=3,
                                          note="pairs counted once; 3 exponentials per pair")
+    # four draws of the three layers' weights in one pass (the exponentials
+    # shared) beside four one-draw passes
+    vl4 = torch.randn((3, p.m, 4), generator=torch.Generator().manual_seed(9)).to(dev)
+    ms4 = event_time(lambda: api.gp_kernel_matvec_layers(api.Points(xy=beta), s, vl4, ls, [1.0, 0.5, 0.25]), nk,
+                     stream, flush)
+    out["matvec_layers<grid> x3, 4 right-hand sides"] = {
+        "ms": ms4, "ms_four_single_passes": 4 * ms, "speedup": 4 * ms / ms4,
+        "note": "v (3 layers, m, 4): one exp2 per pair and layer, 4 FMAs"}
     out["knn_density k=20"] = {"ms": event_time(lambda: api.knn_density(beta, 20, lengthscale=p.lengthscale), nk,
                                                 stream, flush), "points": p.n}
     qj = api.Points(grid=p.xgrid, lens=p.lens, sub=sub)
@@ -1163,8 +1184,10 @@ def run_ours(args):
                                                 torch.cuda.current_stream())
         if not args.no_serving:
             line["serving"] = run_serving(args.serving_requests, args.serving_iters)
-            line["p50_latency_s"] = line["serving"]["batched"]["p50_s"]
-            line["p99_latency_s"] = line["serving"]["batched"]["p99_s"]
+            # request latency as a service sees it: Poisson arrivals, the
+            # engine that admits by pairs per iteration
+            line["p50_latency_s"] = line["serving"]["poisson_70pct_filled"]["p50_s"]
+            line["p99_latency_s"] = line["serving"]["poisson_70pct_filled"]["p99_s"]
         if not args.no_cpu_baseline:
             cb = cpu_sample_large(p, args.cpu_seconds, g_np.astype(np.float64), one_core_seconds=args.cpu_seconds / 2)
             cb.pop("seconds", None)

@@ -270,19 +270,23 @@ lr_status gp_kernel_matvec(const lr_points* query, const lr_points* source, cons
 
 /*
  * Multi-layer reduction (Sec. 3.1, sum of RBF layers with fixed length
- * scales and per-layer variances): with L = n_layers in [1, 4],
- *   out_i = sum_l variances[l] sum_j exp(-|x_i - y_j|^2 / (2 lengthscales[l]^2)) v[l][j].
- * The pair distance is formed once for all layers. lengthscales and
- * variances are HOST float[L]; v is device float[L][m] (layer-major).
- * Sources may be explicit or a grid, or NULL for a self-kernel (the paper's
- * image-plane GP); they may not carry a lens. Other arguments as
- * gp_kernel_matvec; workspace of lr_matvec_layers_workspace_size() bytes.
+ * scales and per-layer variances): with L = n_layers in [1, 4] and nrhs in
+ * [1, 4] right-hand sides (e.g. several draws of the layers' weights),
+ *   out[i][h] = sum_l variances[l] sum_j exp(-|x_i - y_j|^2 / (2 lengthscales[l]^2)) v[l][j][h].
+ * The pair distance is formed once for all layers, and each layer's exp2
+ * once for all right-hand sides. lengthscales and variances are HOST
+ * float[L]; v is device float[L][m][nrhs] (layer-major), out device
+ * float[n][nrhs]. Sources may be explicit or a grid, or NULL for a
+ * self-kernel (the paper's image-plane GP); they may not carry a lens.
+ * Other arguments as gp_kernel_matvec; workspace of
+ * lr_matvec_layers_workspace_size() bytes.
  */
 lr_status gp_kernel_matvec_layers(const lr_points* query, const lr_points* source, int32_t n_layers,
-                                  const float* lengthscales, const float* variances, const float* v, float* out,
-                                  float* beta_out, void* workspace, size_t workspace_bytes, lr_stream stream);
+                                  const float* lengthscales, const float* variances, const float* v, int32_t nrhs,
+                                  float* out, float* beta_out, void* workspace, size_t workspace_bytes,
+                                  lr_stream stream);
 lr_status lr_matvec_layers_workspace_size(const lr_points* query, const lr_points* source, int32_t n_layers,
-                                          size_t* bytes);
+                                          int32_t nrhs, size_t* bytes);
 
 /* ------------------------------------------------------------------------ */
 /* Pixel windows (Sec. 3.2) and the windowed transmission (Sec. 3.4)          */
@@ -636,6 +640,9 @@ typedef struct {
   size_t hbm_budget_bytes; /* device memory admitted requests may hold; 0 = 120 GiB */
   int32_t max_slots;       /* requests iterating at once (1 = one at a time) */
   int32_t device;          /* CUDA device ordinal */
+  int64_t fill_pairs;      /* 0, or admit a request only while the active requests' pairs per
+                              iteration (n x m each) stay within fill_pairs, or none is active:
+                              requests that fill the GPU alone run alone, small ones share it */
 } lr_session_cfg;
 
 typedef struct {

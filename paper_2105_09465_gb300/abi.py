@@ -55,7 +55,8 @@ class lr_grads(ctypes.Structure):
 
 
 class lr_session_cfg(ctypes.Structure):
-    _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_slots", ctypes.c_int32), ("device", ctypes.c_int32)]
+    _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_slots", ctypes.c_int32), ("device", ctypes.c_int32),
+                ("fill_pairs", ctypes.c_int64)]
 
 
 class lr_request(ctypes.Structure):
@@ -147,9 +148,10 @@ SIGNATURES = {
     "lr_windowed_workspace_size": (ctypes.c_int32, [ctypes.c_int64, ctypes.POINTER(lr_grid),
                                                     ctypes.POINTER(lr_points), ctypes.POINTER(ctypes.c_size_t)]),
     "gp_kernel_matvec_layers": (ctypes.c_int32, [ctypes.POINTER(lr_points), ctypes.POINTER(lr_points), ctypes.c_int32,
-                                                 _P, _P, _P, _P, _P, _P, ctypes.c_size_t, _P]),
+                                                 _P, _P, _P, ctypes.c_int32, _P, _P, _P, ctypes.c_size_t, _P]),
     "lr_matvec_layers_workspace_size": (ctypes.c_int32, [ctypes.POINTER(lr_points), ctypes.POINTER(lr_points),
-                                                         ctypes.c_int32, ctypes.POINTER(ctypes.c_size_t)]),
+                                                         ctypes.c_int32, ctypes.c_int32,
+                                                         ctypes.POINTER(ctypes.c_size_t)]),
     "gp_kernel_matvec_bwd": (ctypes.c_int32, [ctypes.POINTER(lr_points), ctypes.POINTER(lr_points), _P,
                                               ctypes.c_int32, ctypes.c_float, ctypes.c_float, _P,
                                               ctypes.POINTER(lr_grads), _P, ctypes.c_size_t, _P]),

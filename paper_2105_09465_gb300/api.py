@@ -233,11 +233,13 @@ def gp_kernel_matvec(query: Points, source: Points | None, v: torch.Tensor, leng
 
 def gp_kernel_matvec_layers(query: Points, source: Points | None, v: torch.Tensor, lengthscales, variances,
                             want_beta: bool = False, stream=None):
-    """out_i = sum_l variances[l] sum_j exp(-|x_i - y_j|^2 / (2 lengthscales[l]^2)) v[l, j]; v is (L, m)."""
+    """out[i, h] = sum_l variances[l] sum_j exp(-|x_i - y_j|^2 / (2 lengthscales[l]^2)) v[l, j, h];
+    v is (L, m) (one right-hand side, out (n,)) or (L, m, nrhs) (out (n, nrhs))."""
     import numpy as np
 
     lib = abi.load()
     L = int(v.shape[0])
+    nrhs = int(v.shape[2]) if v.dim() == 3 else 1
     _require_cuda(v, "v")
     cq, k1 = to_c_points(query)
     cs, k2 = to_c_points(source)
@@ -245,14 +247,14 @@ def gp_kernel_matvec_layers(query: Points, source: Points | None, v: torch.Tenso
     vs = np.ascontiguousarray(variances, np.float32)
     assert ls.shape == (L,) and vs.shape == (L,)
     n = cq.n
-    out = torch.empty(n, dtype=torch.float32, device=v.device)
+    out = torch.empty((n, nrhs) if v.dim() == 3 else (n,), dtype=torch.float32, device=v.device)
     beta = torch.empty((n, 2), dtype=torch.float32, device=v.device) if want_beta else None
     ps = ctypes.byref(cs) if cs is not None else None
     b = ctypes.c_size_t(0)
-    abi.check(lib.lr_matvec_layers_workspace_size(ctypes.byref(cq), ps, L, ctypes.byref(b)),
+    abi.check(lib.lr_matvec_layers_workspace_size(ctypes.byref(cq), ps, L, nrhs, ctypes.byref(b)),
               "lr_matvec_layers_workspace_size")
     ws = torch.empty(max(int(b.value), 1), dtype=torch.uint8, device=v.device)
-    st = lib.gp_kernel_matvec_layers(ctypes.byref(cq), ps, L, ls.ctypes.data, vs.ctypes.data, v.data_ptr(),
+    st = lib.gp_kernel_matvec_layers(ctypes.byref(cq), ps, L, ls.ctypes.data, vs.ctypes.data, v.data_ptr(), nrhs,
                                      out.data_ptr(), beta.data_ptr() if beta is not None else None, ws.data_ptr(),
                                      ws.numel(), _stream_handle(stream))
     abi.check(st, "gp_kernel_matvec_layers")

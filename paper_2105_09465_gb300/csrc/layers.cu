@@ -13,12 +13,14 @@
 namespace lr {
 
 constexpr int kLyMax = 4;
+constexpr int kLyMaxRhs = 4;
 constexpr int kLyThreads = 128;
-constexpr int kLyR = 4;                            // query rows per thread
-constexpr int kLyRows = kLyThreads * kLyR;         // 512 rows per CTA
 constexpr int kLyTile = 256;
 constexpr int kLyPairs = kLyTile / 2;
 static_assert(kLyPairs == kLyThreads, "one source pair per thread when staging");
+
+// Query rows per thread: 4, or 2 with more than two right-hand sides.
+__host__ __device__ constexpr int ly_rows_per_thread(int nrhs) { return nrhs <= 2 ? 4 : 2; }
 
 struct LyArgs {
   const float2* x;
@@ -26,13 +28,13 @@ struct LyArgs {
   const float2* y;  // explicit sources, or NULL for the grid
   GridDev g;
   int64_t m;
-  int32_t segs, n_tiles, chunks, L;
-  const float* v;          // [L][m]
+  int32_t segs, n_tiles, chunks, L, nrhs;
+  const float* v;          // [L][m][nrhs]
   float neg_c0;            // -log2(e)/(2 l_0^2)
   float ratio[kLyMax];     // (l_0 / l_l)^2
   float var[kLyMax];
-  float* out;              // [n] when chunks == 1
-  float* partial;          // [chunks][n]
+  float* out;              // [n][nrhs] when chunks == 1
+  float* partial;          // [chunks][n][nrhs]
 };
 
 __device__ __forceinline__ float2 lf2(float a, float b) { return make_float2(a, b); }
@@ -51,9 +53,10 @@ __device__ __forceinline__ void ly_tile(const LyArgs& A, int t, int64_t& j0, int
   }
 }
 
-// Pair p of tile t: negated coordinates and the per-layer weights.
-template <int L>
-__device__ __forceinline__ void ly_load(const LyArgs& A, int t, int p, float4& P, float2 (&V)[L]) {
+// Pair p of tile t: negated coordinates and, per layer and right-hand side,
+// the weights scaled by the layer's variance.
+template <int L, int H>
+__device__ __forceinline__ void ly_load(const LyArgs& A, int t, int p, float4& P, float2 (&V)[L][H]) {
   int64_t j0;
   int cnt, grow;
   ly_tile(A, t, j0, cnt, grow);
@@ -71,46 +74,56 @@ __device__ __forceinline__ void ly_load(const LyArgs& A, int t, int p, float4& P
   P = make_float4(-pa.x, -pb.x, -pa.y, -pb.y);
 #pragma unroll
   for (int l = 0; l < L; ++l)
-    V[l] = lf2((a < cnt) ? __ldg(A.v + l * A.m + j0 + a) : 0.f, (b < cnt) ? __ldg(A.v + l * A.m + j0 + b) : 0.f);
+#pragma unroll
+    for (int h = 0; h < H; ++h) {
+      const float* vl = A.v + ((int64_t)l * A.m + j0) * H + h;
+      V[l][h] = lf2((a < cnt) ? A.var[l] * __ldg(vl + (int64_t)a * H) : 0.f,
+                    (b < cnt) ? A.var[l] * __ldg(vl + (int64_t)b * H) : 0.f);
+    }
 }
 
-template <int L>
+template <int L, int H>
 __global__ void __launch_bounds__(kLyThreads) layers_kernel(const __grid_constant__ LyArgs A) {
+  constexpr int R = ly_rows_per_thread(H), ROWS = kLyThreads * R;
   __shared__ __align__(16) float4 sP[2][kLyPairs];
-  __shared__ __align__(16) float2 sV[2][L][kLyPairs];
-  __shared__ float ksum[kLyR][kLyThreads], kcomp[kLyR][kLyThreads];
+  __shared__ __align__(16) float2 sV[2][L][H][kLyPairs];
+  __shared__ float ksum[R][H][kLyThreads], kcomp[R][H][kLyThreads];
   const int rb = blockIdx.x / A.chunks;
   const int chunk = blockIdx.x - rb * A.chunks;
   const int t0 = (int)((int64_t)chunk * A.n_tiles / A.chunks);
   const int t1 = (int)((int64_t)(chunk + 1) * A.n_tiles / A.chunks);
   const int tid = threadIdx.x;
 
-  float2 xq[kLyR], yq[kLyR], acc[kLyR][L];
+  float2 xq[R], yq[R], acc[R][H];
 #pragma unroll
-  for (int r = 0; r < kLyR; ++r) {
-    int64_t i = (int64_t)rb * kLyRows + r * kLyThreads + tid;
+  for (int r = 0; r < R; ++r) {
+    int64_t i = (int64_t)rb * ROWS + r * kLyThreads + tid;
     if (i >= A.n) i = A.n - 1;
     const float2 p = __ldg(A.x + i);
     xq[r] = lf2(p.x, p.x);
     yq[r] = lf2(p.y, p.y);
 #pragma unroll
-    for (int l = 0; l < L; ++l) acc[r][l] = lf2(0.f, 0.f);
-    ksum[r][tid] = 0.f;
-    kcomp[r][tid] = 0.f;
+    for (int h = 0; h < H; ++h) {
+      acc[r][h] = lf2(0.f, 0.f);
+      ksum[r][h][tid] = 0.f;
+      kcomp[r][h][tid] = 0.f;
+    }
   }
   const float2 nc = lf2(A.neg_c0, A.neg_c0);
   float4 P;
-  float2 V[L];
+  float2 V[L][H];
   if (t0 < t1) {
-    ly_load<L>(A, t0, tid, P, V);
+    ly_load<L, H>(A, t0, tid, P, V);
     sP[0][tid] = P;
 #pragma unroll
-    for (int l = 0; l < L; ++l) sV[0][l][tid] = V[l];
+    for (int l = 0; l < L; ++l)
+#pragma unroll
+      for (int h = 0; h < H; ++h) sV[0][l][h][tid] = V[l][h];
   }
   __syncthreads();
   for (int t = t0; t < t1; ++t) {
     const int buf = (t - t0) & 1;
-    if (t + 1 < t1) ly_load<L>(A, t + 1, tid, P, V);
+    if (t + 1 < t1) ly_load<L, H>(A, t + 1, tid, P, V);
     int64_t j0;
     int cnt, grow;
     ly_tile(A, t, j0, cnt, grow);
@@ -118,63 +131,69 @@ __global__ void __launch_bounds__(kLyThreads) layers_kernel(const __grid_constan
 #pragma unroll 2
     for (int p = 0; p < np; ++p) {
       const float4 Q = sP[buf][p];
-      float2 W[L];
+      float2 W[L][H];
 #pragma unroll
-      for (int l = 0; l < L; ++l) W[l] = sV[buf][l][p];
+      for (int l = 0; l < L; ++l)
+#pragma unroll
+        for (int h = 0; h < H; ++h) W[l][h] = sV[buf][l][h][p];
       const float2 nx = lf2(Q.x, Q.y), ny = lf2(Q.z, Q.w);
 #pragma unroll
-      for (int r = 0; r < kLyR; ++r) {
+      for (int r = 0; r < R; ++r) {
         const float2 dx = __fadd2_rn(xq[r], nx);
         const float2 dy = __fadd2_rn(yq[r], ny);
         const float2 e0 = __fmul2_rn(__ffma2_rn(dy, dy, __fmul2_rn(dx, dx)), nc);  // layer-0 exponent
 #pragma unroll
         for (int l = 0; l < L; ++l) {
+          // one exp2 per pair and layer, shared by the right-hand sides
           const float2 e = (l == 0) ? e0 : __fmul2_rn(e0, lf2(A.ratio[l], A.ratio[l]));
           const float2 k = lf2(ex2_approx(e.x), ex2_approx(e.y));
-          acc[r][l] = __ffma2_rn(k, W[l], acc[r][l]);
+#pragma unroll
+          for (int h = 0; h < H; ++h) acc[r][h] = __ffma2_rn(k, W[l][h], acc[r][h]);
         }
       }
     }
 #pragma unroll
-    for (int r = 0; r < kLyR; ++r) {
-      float tile = 0.f;
+    for (int r = 0; r < R; ++r)
 #pragma unroll
-      for (int l = 0; l < L; ++l) {
-        tile = fmaf(A.var[l], acc[r][l].x + acc[r][l].y, tile);
-        acc[r][l] = lf2(0.f, 0.f);
+      for (int h = 0; h < H; ++h) {
+        const float y = (acc[r][h].x + acc[r][h].y) - kcomp[r][h][tid];
+        const float s = ksum[r][h][tid] + y;
+        kcomp[r][h][tid] = (s - ksum[r][h][tid]) - y;
+        ksum[r][h][tid] = s;
+        acc[r][h] = lf2(0.f, 0.f);
       }
-      const float y = tile - kcomp[r][tid];
-      const float s = ksum[r][tid] + y;
-      kcomp[r][tid] = (s - ksum[r][tid]) - y;
-      ksum[r][tid] = s;
-    }
     if (t + 1 < t1) {
       sP[buf ^ 1][tid] = P;
 #pragma unroll
-      for (int l = 0; l < L; ++l) sV[buf ^ 1][l][tid] = V[l];
+      for (int l = 0; l < L; ++l)
+#pragma unroll
+        for (int h = 0; h < H; ++h) sV[buf ^ 1][l][h][tid] = V[l][h];
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int r = 0; r < kLyR; ++r) {
-    const int64_t i = (int64_t)rb * kLyRows + r * kLyThreads + tid;
-    if (i < A.n) {
-      const float total = ksum[r][tid] - kcomp[r][tid];
-      if (A.chunks == 1)
-        A.out[i] = total;
-      else
-        A.partial[(int64_t)chunk * A.n + i] = total;
-    }
+  for (int r = 0; r < R; ++r) {
+    const int64_t i = (int64_t)rb * ROWS + r * kLyThreads + tid;
+    if (i < A.n)
+#pragma unroll
+      for (int h = 0; h < H; ++h) {
+        const float total = ksum[r][h][tid] - kcomp[r][h][tid];
+        if (A.chunks == 1)
+          A.out[i * H + h] = total;
+        else
+          A.partial[((int64_t)chunk * A.n + i) * H + h] = total;
+      }
   }
 }
 
-__global__ void layers_merge_kernel(const float* __restrict__ partial, int chunks, int64_t n,
+// Fixed-order (Kahan) merge of the chunk partials [chunks][n * nrhs].
+__global__ void layers_merge_kernel(const float* __restrict__ partial, int chunks, int64_t count,
                                     float* __restrict__ out) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+  if (i >= count) return;
   float s = 0.f, c = 0.f;
   for (int k = 0; k < chunks; ++k) {
-    const float y = partial[(int64_t)k * n + i] - c;
+    const float y = partial[(int64_t)k * count + i] - c;
     const float t = s + y;
     c = (t - s) - y;
     s = t;
@@ -185,11 +204,21 @@ __global__ void layers_merge_kernel(const float* __restrict__ partial, int chunk
 struct LyPlan {
   int64_t n, m;
   bool q_raytrace, q_grid, self, s_grid;
-  int32_t n_tiles, segs, chunks, row_blocks;
+  int32_t n_tiles, segs, chunks, row_blocks, nrhs;
   size_t off_q, off_partial, bytes;
 };
 
-static lr_status plan_layers(const lr_points* q, const lr_points* s, int32_t L, bool have_beta_out, LyPlan* P) {
+static const void* layers_kernel_ptr(int nrhs) {
+  switch (nrhs) {
+    case 1: return reinterpret_cast<const void*>(&layers_kernel<kLyMax, 1>);
+    case 2: return reinterpret_cast<const void*>(&layers_kernel<kLyMax, 2>);
+    case 3: return reinterpret_cast<const void*>(&layers_kernel<kLyMax, 3>);
+    default: return reinterpret_cast<const void*>(&layers_kernel<kLyMax, 4>);
+  }
+}
+
+static lr_status plan_layers(const lr_points* q, const lr_points* s, int32_t L, int32_t nrhs, bool have_beta_out,
+                             LyPlan* P) {
   lr_status st = validate_points(q, "gp_kernel_matvec_layers(query)", false);
   if (st != LR_OK) return st;
   if (s) {
@@ -197,6 +226,7 @@ static lr_status plan_layers(const lr_points* q, const lr_points* s, int32_t L, 
     LR_REQUIRE(!has_lens(s), "gp_kernel_matvec_layers: sources must not be ray-traced (use a self-kernel)");
   }
   LR_REQUIRE(L >= 1 && L <= kLyMax, "gp_kernel_matvec_layers: n_layers = %d outside [1, %d]", L, kLyMax);
+  LR_REQUIRE(nrhs >= 1 && nrhs <= kLyMaxRhs, "gp_kernel_matvec_layers: nrhs = %d outside [1, %d]", nrhs, kLyMaxRhs);
   LyPlan p{};
   p.n = q->n;
   p.self = s == nullptr;
@@ -211,17 +241,19 @@ static lr_status plan_layers(const lr_points* q, const lr_points* s, int32_t L, 
   } else {
     p.n_tiles = (int32_t)((p.m + kLyTile - 1) / kLyTile);
   }
-  p.row_blocks = (int32_t)((p.n + kLyRows - 1) / kLyRows);
+  const int64_t rows = (int64_t)kLyThreads * ly_rows_per_thread(nrhs);
+  p.nrhs = nrhs;
+  p.row_blocks = (int32_t)((p.n + rows - 1) / rows);
   int dev = 0, n_sm = 1, occ = 1;
   LR_CHECK_CUDA(cudaGetDevice(&dev));
   LR_CHECK_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
-  LR_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, layers_kernel<kLyMax>, kLyThreads, 0));
+  LR_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, layers_kernel_ptr(nrhs), kLyThreads, 0));
   p.chunks = plan_chunks(p.row_blocks, p.n_tiles, occ, n_sm);
   size_t off = 0;
   p.off_q = off;
   if ((p.q_raytrace || p.q_grid) && !have_beta_out) off += align256(8 * (size_t)p.n);
   p.off_partial = off;
-  if (p.chunks > 1) off += align256(4 * (size_t)p.chunks * (size_t)p.n);
+  if (p.chunks > 1) off += align256(4 * (size_t)p.chunks * (size_t)p.n * (size_t)nrhs);
   p.bytes = off;
   *P = p;
   return LR_OK;
@@ -229,7 +261,12 @@ static lr_status plan_layers(const lr_points* q, const lr_points* s, int32_t L, 
 
 template <int L>
 static void launch_layers(const LyArgs& A, unsigned grid, cudaStream_t s) {
-  layers_kernel<L><<<grid, kLyThreads, 0, s>>>(A);
+  switch (A.nrhs) {
+    case 1: layers_kernel<L, 1><<<grid, kLyThreads, 0, s>>>(A); break;
+    case 2: layers_kernel<L, 2><<<grid, kLyThreads, 0, s>>>(A); break;
+    case 3: layers_kernel<L, 3><<<grid, kLyThreads, 0, s>>>(A); break;
+    default: layers_kernel<L, 4><<<grid, kLyThreads, 0, s>>>(A); break;
+  }
 }
 
 }  // namespace lr
@@ -237,10 +274,10 @@ static void launch_layers(const LyArgs& A, unsigned grid, cudaStream_t s) {
 using namespace lr;
 
 extern "C" lr_status lr_matvec_layers_workspace_size(const lr_points* query, const lr_points* source, int32_t n_layers,
-                                                     size_t* bytes) {
+                                                     int32_t nrhs, size_t* bytes) {
   LR_REQUIRE(bytes != nullptr, "lr_matvec_layers_workspace_size: bytes is NULL");
   LyPlan P;
-  lr_status st = plan_layers(query, source, n_layers, false, &P);
+  lr_status st = plan_layers(query, source, n_layers, nrhs, false, &P);
   if (st != LR_OK) return st;
   *bytes = P.bytes;
   return LR_OK;
@@ -248,10 +285,10 @@ extern "C" lr_status lr_matvec_layers_workspace_size(const lr_points* query, con
 
 extern "C" lr_status gp_kernel_matvec_layers(const lr_points* query, const lr_points* source, int32_t n_layers,
                                              const float* lengthscales, const float* variances, const float* v,
-                                             float* out, float* beta_out, void* workspace, size_t workspace_bytes,
-                                             lr_stream stream) {
+                                             int32_t nrhs, float* out, float* beta_out, void* workspace,
+                                             size_t workspace_bytes, lr_stream stream) {
   LyPlan P;
-  lr_status st = plan_layers(query, source, n_layers, beta_out != nullptr, &P);
+  lr_status st = plan_layers(query, source, n_layers, nrhs, beta_out != nullptr, &P);
   if (st != LR_OK) return st;
   LR_REQUIRE(lengthscales != nullptr && variances != nullptr, "gp_kernel_matvec_layers: NULL hyperparameters");
   for (int l = 0; l < n_layers; ++l) {
@@ -268,7 +305,7 @@ extern "C" lr_status gp_kernel_matvec_layers(const lr_points* query, const lr_po
   cudaStream_t s = as_cuda(stream);
   if (P.n == 0) return LR_OK;
   if (P.m == 0) {
-    LR_CHECK_CUDA(cudaMemsetAsync(out, 0, 4 * (size_t)P.n, s));
+    LR_CHECK_CUDA(cudaMemsetAsync(out, 0, 4 * (size_t)P.n * (size_t)nrhs, s));
     return LR_OK;
   }
   char* ws = static_cast<char*>(workspace);
@@ -289,6 +326,7 @@ extern "C" lr_status gp_kernel_matvec_layers(const lr_points* query, const lr_po
   A.n_tiles = P.n_tiles;
   A.chunks = P.chunks;
   A.L = n_layers;
+  A.nrhs = nrhs;
   A.v = v;
   const double l0 = lengthscales[0];
   A.neg_c0 = (float)(-1.4426950408889634 / (2.0 * l0 * l0));
@@ -308,7 +346,8 @@ extern "C" lr_status gp_kernel_matvec_layers(const lr_points* query, const lr_po
   }
   LR_CHECK_CUDA(cudaGetLastError());
   if (P.chunks > 1) {
-    layers_merge_kernel<<<(unsigned)((P.n + 255) / 256), 256, 0, s>>>(A.partial, P.chunks, P.n, out);
+    const int64_t count = P.n * nrhs;
+    layers_merge_kernel<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(A.partial, P.chunks, count, out);
     LR_CHECK_CUDA(cudaGetLastError());
   }
   return LR_OK;

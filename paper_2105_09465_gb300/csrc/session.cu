@@ -307,10 +307,15 @@ void worker_main(lr_session* S) {
       S->cv_work.wait_for(lock, std::chrono::milliseconds(20),
                           [&] { return S->stop || !S->pending.empty() || !S->active.empty(); });
       if (S->stop) break;
-      // admission: FIFO while a slot and the memory budget allow
+      // admission: FIFO while a slot, the memory budget and (when set) the
+      // pairs per iteration allow
+      int64_t work = 0;
+      for (const Req* a : S->active) work += a->n * a->m;
       while (!S->pending.empty() && (int)S->active.size() < S->cfg.max_slots) {
         Req* r = S->pending.front();
         if (S->used + r->bytes > S->cfg.hbm_budget_bytes) break;
+        if (S->cfg.fill_pairs > 0 && !S->active.empty() && work + r->n * r->m > S->cfg.fill_pairs) break;
+        work += r->n * r->m;
         S->pending.pop_front();
         S->used += r->bytes;
         r->state = RState::Active;
@@ -365,6 +370,7 @@ void worker_main(lr_session* S) {
 extern "C" lr_status solve_session_create(const lr_session_cfg* cfg, lr_session** out) {
   LR_REQUIRE(cfg != nullptr && out != nullptr, "solve_session_create: NULL argument");
   LR_REQUIRE(cfg->max_slots >= 1, "solve_session_create: max_slots = %d must be >= 1", cfg->max_slots);
+  LR_REQUIRE(cfg->fill_pairs >= 0, "solve_session_create: fill_pairs < 0");
   auto S = std::make_unique<lr_session>();
   S->cfg = *cfg;
   if (S->cfg.hbm_budget_bytes == 0) S->cfg.hbm_budget_bytes = size_t(120) << 30;

@@ -36,9 +36,9 @@ class Result:
 
 
 class Session:
-    def __init__(self, max_slots: int = 16, hbm_budget_bytes: int = 0, device: int = 0):
+    def __init__(self, max_slots: int = 16, hbm_budget_bytes: int = 0, device: int = 0, fill_pairs: int = 0):
         self.lib = abi.load()
-        cfg = abi.lr_session_cfg(hbm_budget_bytes, max_slots, device)
+        cfg = abi.lr_session_cfg(hbm_budget_bytes, max_slots, device, int(fill_pairs))
         h = ctypes.c_void_p()
         abi.check(self.lib.solve_session_create(ctypes.byref(cfg), ctypes.byref(h)), "solve_session_create")
         self.h = h

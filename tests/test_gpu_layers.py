@@ -73,3 +73,25 @@ def test_one_layer_matches_single_layer_entry_point():
     a = host(api.gp_kernel_matvec_layers(api.Points(xy=dev(x)), None, dev(v[None, :]), [0.04], [1.3]))
     b = host(api.gp_kernel_matvec(api.Points(xy=dev(x)), None, dev(v), 0.04, 1.3))
     np.testing.assert_allclose(a, b, rtol=3e-6, atol=1e-6 * np.abs(b).max())
+
+
+@pytest.mark.parametrize("L,nrhs", [(1, 2), (3, 4), (4, 3), (2, 4)])
+@pytest.mark.parametrize("source", ["grid", "explicit", "self"])
+def test_several_right_hand_sides(orc, L, nrhs, source):
+    """v of shape (L, m, nrhs): every column of out against the oracle's sum
+    of layers for that column (one exp2 per pair and layer serves all the
+    right-hand sides); ragged sizes that leave partial tiles and row blocks."""
+    rng = np.random.default_rng(10 * L + nrhs)
+    g = W.Grid(61, 37, 1, 0.035)
+    yg = orc.grid_points(*g.astuple())
+    x = rng.uniform(-1.0, 1.0, (2777, 2)).astype(np.float32)
+    src = {"grid": api.Points(grid=g), "explicit": api.Points(xy=dev(yg)), "self": None}[source]
+    y = x if source == "self" else yg
+    v = rng.standard_normal((L, len(y), nrhs)).astype(np.float32)
+    ls = list(np.float32(0.04 * 1.6 ** np.arange(L)))
+    vs = list(np.float32(1.0 + 0.25 * np.arange(L)))
+    got = host(api.gp_kernel_matvec_layers(api.Points(xy=dev(x)), src, dev(v), ls, vs))
+    assert got.shape == (len(x), nrhs)
+    for h in range(nrhs):
+        ref, ab = oracle_layers(orc, x, y, np.ascontiguousarray(v[:, :, h]), ls, vs)
+        assert_matvec_close(got[:, h], ref, ab, what=f"{L} layers, {source}, right-hand side {h}")
