@@ -552,8 +552,11 @@ typedef struct {
  * Pass them unchanged as grads->moments_in to gp_kernel_matvec_bwd with the
  * same arguments. The pair sweep costs a few more FP32 operations per pair
  * than gp_kernel_matvec and saves the backward's row sweep. Sources: grid or
- * explicit, not a self-kernel (source != NULL) and not ray-traced. Workspace
- * of lr_matvec_train_workspace_size() bytes, 256-byte aligned.
+ * explicit, not a self-kernel (source != NULL) and not ray-traced. nrhs must
+ * be 1 (LR_ERR_INVALID_ARG otherwise): this is the one-draw training path;
+ * several draws share each pair's exp2 through gp_kernel_matvec and
+ * gp_kernel_matvec_bwd with nrhs up to 4. Workspace of
+ * lr_matvec_train_workspace_size() bytes, 256-byte aligned.
  */
 lr_status gp_kernel_matvec_train(const lr_points* query, const lr_points* source, const float* v, int32_t nrhs,
                                  float lengthscale, float variance, float* out, float* beta_out, float* moments_out,
