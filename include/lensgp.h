@@ -325,6 +325,23 @@ lr_status gp_windowed_matvec(const float* p, const float* z, int64_t n, const lr
 lr_status lr_windowed_workspace_size(int64_t n, const lr_grid* layout, const lr_points* source, size_t* bytes);
 
 /*
+ * The windowed reduction with the Gaussian pixel likelihood (Sec. 3.3) in its
+ * epilogue, for the last layer of the model: with one value per pixel,
+ *   out_i = f_in_i + sum_k G(p_i - q_k, Z_i + (l^2/2) I) v_k   (f_in may be NULL: 0),
+ *   g_i   = (out_i - data_i) / sigma^2                          (dL/dout),
+ *   nll   = sum_i (out_i - data_i)^2 / (2 sigma^2) + n ln sigma + (n/2) ln 2 pi
+ * (device double[1]; FP32 per row, FP64 across rows, fixed order). The rows'
+ * terms are formed where the reduction finishes each row, so the model total
+ * is never re-read. Explicit sources only; other arguments, the workspace
+ * (lr_windowed_workspace_size) and the skipping of exact zeros as for
+ * gp_windowed_matvec. out, g: device float[n]; data device float[n].
+ */
+lr_status gp_windowed_matvec_nll(const float* p, const float* z, int64_t n, const lr_grid* layout,
+                                 const lr_points* source, const float* v, float lengthscale, const float* f_in,
+                                 const float* data, float sigma, float* out, float* g, double* nll, void* workspace,
+                                 size_t workspace_bytes, lr_stream stream);
+
+/*
  * Gradients of Loss = sum_i g_i out_i through gp_windowed_matvec
  * (recompute-only). With d = p_i - q_k, C_i = Z_i + (l^2/2) I, M = C_i^-1,
  * u = M d and G = G(d, C_i):

@@ -145,6 +145,9 @@ SIGNATURES = {
                                                      ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
                                                      _P]),
     "gp_pixel_shapes_vjp": (ctypes.c_int32, [_P, ctypes.c_int32, ctypes.c_int32, _P, _P, _P]),
+    "gp_windowed_matvec_nll": (ctypes.c_int32, [_P, _P, ctypes.c_int64, ctypes.POINTER(lr_grid),
+                                                ctypes.POINTER(lr_points), _P, ctypes.c_float, _P, _P, ctypes.c_float,
+                                                _P, _P, _P, _P, ctypes.c_size_t, _P]),
     "lr_windowed_workspace_size": (ctypes.c_int32, [ctypes.c_int64, ctypes.POINTER(lr_grid),
                                                     ctypes.POINTER(lr_points), ctypes.POINTER(ctypes.c_size_t)]),
     "gp_kernel_matvec_layers": (ctypes.c_int32, [ctypes.POINTER(lr_points), ctypes.POINTER(lr_points), ctypes.c_int32,

@@ -295,6 +295,35 @@ def gp_windowed_matvec(p: torch.Tensor, z: torch.Tensor, source: Points, v: torc
     return out
 
 
+def gp_windowed_matvec_nll(p: torch.Tensor, z: torch.Tensor, source: Points, v: torch.Tensor, lengthscale: float,
+                           data: torch.Tensor, sigma: float, f_in: torch.Tensor | None = None,
+                           layout: Grid | None = None, stream=None):
+    """(out, g, nll): out = f_in + the windowed reduction, g = (out - data) / sigma^2,
+    nll (float64 0-d device tensor) the Gaussian likelihood's negative log, formed
+    in the reduction's epilogue."""
+    lib = abi.load()
+    _require_cuda(p, "p", (2,))
+    _require_cuda(z, "z", (3,))
+    _require_cuda(v, "v")
+    _require_cuda(data, "data")
+    _require_cuda(f_in, "f_in")
+    cs, k = to_c_points(source)
+    n = p.shape[0]
+    out = torch.empty(n, dtype=torch.float32, device=p.device)
+    g = torch.empty(n, dtype=torch.float32, device=p.device)
+    nll = torch.empty((), dtype=torch.float64, device=p.device)
+    b = ctypes.c_size_t(0)
+    abi.check(lib.lr_windowed_workspace_size(n, _layout(layout), ctypes.byref(cs), ctypes.byref(b)),
+              "lr_windowed_workspace_size")
+    ws = torch.empty(max(int(b.value), 1), dtype=torch.uint8, device=p.device)
+    st = lib.gp_windowed_matvec_nll(p.data_ptr(), z.data_ptr(), n, _layout(layout), ctypes.byref(cs), v.data_ptr(),
+                                    float(lengthscale), f_in.data_ptr() if f_in is not None else None,
+                                    data.data_ptr(), float(sigma), out.data_ptr(), g.data_ptr(), nll.data_ptr(),
+                                    ws.data_ptr(), ws.numel(), _stream_handle(stream))
+    abi.check(st, "gp_windowed_matvec_nll")
+    return out, g, nll
+
+
 def knn_density(q: torch.Tensor, k: int = 20, lengthscale: float | None = None, want_r2: bool = True,
                 workspace: torch.Tensor | None = None, stream=None):
     """k-th-neighbour squared radius r2 (and, with a lengthscale, the

@@ -203,7 +203,15 @@ __device__ __forceinline__ void cull_finalize(const CullArgs& A, int64_t i, cons
 #pragma unroll
     for (int k = 0; k < K; ++k) A.out[i * A.nrhs + k] = A.var * t[k];
   } else if constexpr (KIND == kCullWin) {
-    A.out[i] = A.wcoef[i].w * t[0];
+    float o = A.wcoef[i].w * t[0];
+    if (A.lik_data) {
+      // the likelihood epilogue: the model total and its residual
+      if (A.f_in) o = A.f_in[i] + o;
+      const float r = o - A.lik_data[i];
+      A.lik_g[i] = r * A.lik_isig2;
+      sl = 0.5f * (r * r) * A.lik_isig2;
+    }
+    A.out[i] = o;
   } else if constexpr (KIND == kCullMom) {
     if (A.g == nullptr) {
       A.out[i] = A.var * t[0];

@@ -211,6 +211,13 @@ struct CullArgs {
   float* partial;    // splits > 1: [splits][K][n]
   const float4* wcoef;  // kCullWin, kCullWinRows: the rows' window constants (a, b, c, N)
   const float* wreach;  // and reach scales (launch_window_prep)
+  // kCullWin with a Gaussian likelihood in the epilogue (lik_data != NULL):
+  // out = f_in (or 0) + this reduction, lik_g = (out - data) / sigma^2, and
+  // the rows' (out - data)^2 / (2 sigma^2) summed into scal_part
+  const float* f_in;
+  const float* lik_data;
+  float lik_isig2;      // 1 / sigma^2
+  float* lik_g;
   const float* csc;  // kCullWinCols: reach scales of the chunks and groups
   const float* gsc;
   int* fault;        // device fault word (a bulk-copy wait that ran out)

@@ -212,6 +212,11 @@ __global__ void windowed_merge_kernel(const float* __restrict__ partial, int chu
   out[i] = s - c;
 }
 
+// nll += c (the likelihood's constant terms), one thread.
+__global__ void add_const_kernel(double* __restrict__ x, double c) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *x += c;
+}
+
 struct WnPlan {
   int32_t n_tiles, segs, chunks, row_blocks;  // grid sources
   int32_t culled;                             // explicit sources: the culled sweep
@@ -345,5 +350,53 @@ extern "C" lr_status gp_windowed_matvec(const float* p, const float* z, int64_t 
     windowed_merge_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(A.partial, P.chunks, n, out);
     LR_CHECK_CUDA(cudaGetLastError());
   }
+  return LR_OK;
+}
+
+extern "C" lr_status gp_windowed_matvec_nll(const float* p, const float* z, int64_t n, const lr_grid* layout,
+                                            const lr_points* source, const float* v, float lengthscale,
+                                            const float* f_in, const float* data, float sigma, float* out, float* g,
+                                            double* nll, void* workspace, size_t workspace_bytes, lr_stream stream) {
+  WnPlan P;
+  lr_status st = plan_windowed(n, layout, source, &P);
+  if (st != LR_OK) return st;
+  LR_REQUIRE(P.culled, "gp_windowed_matvec_nll: sources must be explicit points");
+  LR_REQUIRE(isfinite(lengthscale) && lengthscale > 0.f, "gp_windowed_matvec_nll: lengthscale must be > 0");
+  LR_REQUIRE(isfinite(sigma) && sigma > 0.f, "gp_windowed_matvec_nll: sigma must be > 0");
+  LR_REQUIRE(nll != nullptr && ((uintptr_t)nll & 7u) == 0, "gp_windowed_matvec_nll: nll is NULL or misaligned");
+  LR_REQUIRE(n == 0 || (p && z && data && out && g), "gp_windowed_matvec_nll: NULL pointer");
+  LR_REQUIRE(((uintptr_t)p & 7u) == 0 && ((uintptr_t)z & 3u) == 0, "gp_windowed_matvec_nll: misaligned p or z");
+  LR_REQUIRE(v != nullptr || source->n == 0, "gp_windowed_matvec_nll: v is NULL");
+  LR_REQUIRE(workspace_bytes >= P.bytes && (P.bytes == 0 || workspace != nullptr),
+             "gp_windowed_matvec_nll: workspace of %zu bytes, %zu needed", workspace_bytes, P.bytes);
+  LR_REQUIRE(((uintptr_t)workspace & 255u) == 0, "gp_windowed_matvec_nll: workspace must be 256-byte aligned");
+  cudaStream_t s = as_cuda(stream);
+  LR_CHECK_CUDA(cudaMemsetAsync(nll, 0, sizeof(double), s));
+  if (n == 0) return LR_OK;
+  char* ws = static_cast<char*>(workspace);
+  float4* wcoef = reinterpret_cast<float4*>(ws + P.off_wcoef);
+  float* wreach = reinterpret_cast<float*>(ws + P.off_wreach);
+  if ((st = launch_window_prep(z, n, lengthscale, wcoef, wreach, s)) != LR_OK) return st;
+  st = launch_cull_prep(P.C, reinterpret_cast<const float2*>(source->xy), 0.f, v, nullptr, 1, 0, ws, s);
+  if (st != LR_OK) return st;
+  CullArgs A{};
+  A.x = reinterpret_cast<const float2*>(p);
+  A.n = n;
+  A.nrhs = 1;
+  A.stride = 1;
+  A.wcoef = wcoef;
+  A.wreach = wreach;
+  A.out = out;
+  A.f_in = f_in;
+  A.lik_data = data;
+  A.lik_isig2 = (float)(1.0 / ((double)sigma * (double)sigma));
+  A.lik_g = g;
+  double* part = reinterpret_cast<double*>(ws + P.C.off_scal);
+  A.scal_part = part;
+  if ((st = launch_cull_sweep(P.C, A, ws, LR_KT_WINDOWED, s)) != LR_OK) return st;
+  if ((st = launch_cull_scalar_final(part, P.C.scal_blocks, nll, nullptr, s)) != LR_OK) return st;
+  // the constant terms: n ln sigma + (n / 2) ln 2 pi
+  add_const_kernel<<<1, 32, 0, s>>>(nll, (double)n * (log((double)sigma) + 0.91893853320467274));
+  LR_CHECK_CUDA(cudaGetLastError());
   return LR_OK;
 }

@@ -21,9 +21,10 @@ the transmission weights A_k are held fixed within a step.
 Every numerical step runs in the library's CUDA kernels, the elementwise
 ones (A y, the sum of the layers, dL/dbeta summed over the layers, the
 source-plane prior gradient y_sp / alpha^2, the loss's sum of terms)
-included; the 7 drawn lens parameters stay on the device (lens_prepare turns
-them into the ray-trace's lens record). This module only orders the calls
-and allocates their outputs; nothing is copied to the host, so a step can be
+included; the last image-plane layer forms the likelihood in its epilogue.
+The 7 drawn lens parameters stay on the device (lens_prepare turns them
+into the ray-trace's lens record). This module only orders the calls and
+allocates their outputs; nothing is copied to the host, so a step can be
 timed with CUDA events or captured in a graph.
 """
 from __future__ import annotations
@@ -114,13 +115,20 @@ def loss_and_grads(cfg: ModelConfig, guide: Guide, data: torch.Tensor, eps_sp: t
     z = api.pixel_shapes(beta, W, H)
     self_pts = api.Points(xy=beta, grid=cfg.pixels)  # the pixels in their image layout
     a_layers, w_layers = [], []
-    for y, s in zip(ys, cfg.sigma_layers):
+    nll = g = None
+    for li, (y, s) in enumerate(zip(ys, cfg.sigma_layers)):
         a_k = api.knn_density(beta, cfg.knn_k, lengthscale=s, want_r2=False)
         w = api.vec_mul(a_k, y)
-        api.vec_axpby(1.0, f, 1.0, api.gp_windowed_matvec(beta, z, self_pts, w, s, layout=cfg.pixels), out=f)
+        if li + 1 < len(ys):
+            api.vec_axpby(1.0, f, 1.0, api.gp_windowed_matvec(beta, z, self_pts, w, s, layout=cfg.pixels), out=f)
+        else:
+            # the last layer: the model total, dL/df and the likelihood in its epilogue
+            f, g, nll = api.gp_windowed_matvec_nll(beta, z, self_pts, w, s, data, cfg.noise, f_in=f,
+                                                   layout=cfg.pixels)
         a_layers.append(a_k)
         w_layers.append(w)
-    nll, g, _ = api.gaussian_nll(f, data, cfg.noise)
+    if nll is None:
+        nll, g, _ = api.gaussian_nll(f, data, cfg.noise)
     if trace is not None:
         trace.update(x=x, beta=beta, z=z, f=f, g=g, nll=nll, ys=ys, a_layers=a_layers, w_layers=w_layers,
                      w_sp=w_sp)

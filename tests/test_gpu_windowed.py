@@ -274,3 +274,28 @@ def test_windowed_pairs_evaluated(orc):
         q = (c[2] * d[:, 0] ** 2 - 2 * c[1] * d[:, 0] * d[:, 1] + c[0] * d[:, 1] ** 2) / det
         need += int(np.count_nonzero(0.5 * np.log2(np.e) * q <= 126.0))
     assert counts[0][0] >= need * (n / 300) * 0.5
+
+
+@pytest.mark.parametrize("with_f_in", [False, True])
+def test_likelihood_in_the_epilogue(orc, with_f_in):
+    """gp_windowed_matvec_nll: the model total, dL/df and the Gaussian nll
+    formed where the windowed reduction finishes each row, against the
+    oracle's windowed reduction and Gaussian likelihood (Sec. 3.3)."""
+    g_, b, zr, v, _ = image_layer(orc, 70, 0.01, seed=60)
+    rng = np.random.default_rng(61)
+    n = len(b)
+    f_in = rng.standard_normal(n).astype(np.float32) if with_f_in else None
+    data = rng.standard_normal(n).astype(np.float32)
+    sigma = 0.3
+    src = api.Points(xy=dev(b), grid=g_)
+    out, g, nll = api.gp_windowed_matvec_nll(dev(b), dev(zr), src, dev(v), 0.01, dev(data), sigma,
+                                             f_in=dev(f_in) if with_f_in else None, layout=g_)
+    R, T = windowed_tols(orc, b, zr, b, v, np.zeros(n), 0.01)
+    ref = R["out"] + (f_in.astype(np.float64) if with_f_in else 0.0)
+    tol_out = T["out"] + 4 * 2.0 ** -24 * (np.abs(f_in) if with_f_in else 0.0)
+    _close(host(out), ref, 0.0, 0.0, "model total", tol_out)
+    r = ref - data.astype(np.float64)
+    _close(host(g), r / sigma ** 2, 0.0, 0.0, "dL/df", (tol_out + 4 * 2.0 ** -24 * np.abs(r)) / sigma ** 2)
+    ref_nll = float(np.sum(0.5 * r * r) / sigma ** 2 + n * np.log(sigma) + 0.5 * n * np.log(2 * np.pi))
+    tol_nll = float(np.sum(np.abs(r) * tol_out) / sigma ** 2) + 1e-6 * abs(ref_nll)
+    assert abs(float(nll) - ref_nll) <= tol_nll, (float(nll), ref_nll, tol_nll)
