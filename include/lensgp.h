@@ -695,6 +695,8 @@ typedef struct {
   size_t used_bytes;
   uint64_t iterations;           /* batched iterations run */
   uint64_t launches;             /* batched kernel launches issued */
+  int64_t active_pairs;          /* pairs per iteration (n x m) of the active requests */
+  int64_t peak_active_pairs;     /* the largest active_pairs since the session began */
 } lr_session_stats;
 
 lr_status solve_session_create(const lr_session_cfg* cfg, lr_session** out);

@@ -75,7 +75,8 @@ class lr_result(ctypes.Structure):
 
 class lr_session_stats(ctypes.Structure):
     _fields_ = [("pending", ctypes.c_int64), ("active", ctypes.c_int64), ("held", ctypes.c_int64),
-                ("used_bytes", ctypes.c_size_t), ("iterations", ctypes.c_uint64), ("launches", ctypes.c_uint64)]
+                ("used_bytes", ctypes.c_size_t), ("iterations", ctypes.c_uint64), ("launches", ctypes.c_uint64),
+                ("active_pairs", ctypes.c_int64), ("peak_active_pairs", ctypes.c_int64)]
 
 
 _P = ctypes.c_void_p

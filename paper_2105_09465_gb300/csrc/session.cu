@@ -119,6 +119,7 @@ struct lr_session {
   bool stop = false;
   bool fault_pending = false;
   uint64_t iterations = 0, launches = 0;
+  int64_t peak_pairs = 0;
   std::chrono::steady_clock::time_point t0;
   std::string worker_error;
 
@@ -316,6 +317,7 @@ void worker_main(lr_session* S) {
         if (S->used + r->bytes > S->cfg.hbm_budget_bytes) break;
         if (S->cfg.fill_pairs > 0 && !S->active.empty() && work + r->n * r->m > S->cfg.fill_pairs) break;
         work += r->n * r->m;
+        if (work > S->peak_pairs) S->peak_pairs = work;
         S->pending.pop_front();
         S->used += r->bytes;
         r->state = RState::Active;
@@ -547,6 +549,9 @@ extern "C" lr_status solve_session_stats(lr_session* S, lr_session_stats* st) {
   st->used_bytes = S->used;
   st->iterations = S->iterations;
   st->launches = S->launches;
+  st->active_pairs = 0;
+  for (const Req* r : S->active) st->active_pairs += r->n * r->m;
+  st->peak_active_pairs = S->peak_pairs;
   return LR_OK;
 }
 

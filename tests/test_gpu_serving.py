@@ -130,8 +130,8 @@ def test_one_iteration_equals_single_problem_calls():
     assert R.d_lengthscale == G["lengthscale"].item() and R.d_variance == G["variance"].item()
 
 
-def run(reqs, max_slots, iters=4, step=0.02, budget=0):
-    with Session(max_slots=max_slots, hbm_budget_bytes=budget) as S:
+def run(reqs, max_slots, iters=4, step=0.02, budget=0, fill_pairs=0):
+    with Session(max_slots=max_slots, hbm_budget_bytes=budget, fill_pairs=fill_pairs) as S:
         ts = [S.submit(p, d, iters, step) for p, d in reqs]
         return [S.poll(t) for t in ts]
 
@@ -153,6 +153,25 @@ def test_alone_vs_mix_vs_one_at_a_time_bit_identical():
         assert same(mix[k], fifo[k]), k
     for k in range(3):
         assert same(mix[k], alone[k]), k
+
+
+def test_admission_by_pairs_per_iteration():
+    """With fill_pairs the active requests' pairs per iteration stay within
+    the limit (a request larger than it runs alone); results are bitwise
+    those of one request at a time."""
+    reqs = [problem(80 + k, side, ns, ys) for k, (side, ns, ys) in
+            enumerate([(64, 10, 128), (16, 2, 32), (20, 0, 32), (48, 6, 64), (12, 3, 16), (40, 8, 64)])]
+    work = [p.n * p.m for p, _ in reqs]
+    fill = sorted(work)[-2] + min(work)  # the largest runs alone, smaller ones share
+    with Session(max_slots=8, fill_pairs=fill) as S:
+        ts = [S.submit(p, d, 6, 0.02) for p, d in reqs]
+        res = [S.poll(t) for t in ts]
+        peak = S.stats()["peak_active_pairs"]
+    # the largest request alone, or requests within the limit, never more
+    assert peak <= max(fill, max(work)) and peak >= max(work)
+    fifo = run(reqs, max_slots=1, iters=6)
+    for a, b in zip(res, fifo):
+        assert a.status == abi.LR_OK and same(a, b)
 
 
 def test_more_requests_than_one_batched_launch():
