@@ -170,7 +170,7 @@ template <int KIND, int NW>
 struct CullTraits;
 template <int NW>
 struct CullTraits<kCullOut, NW> {
-  static constexpr int K = NW, R = NW <= 2 ? 4 : 2, BATCH = NW <= 2 ? 32 : 16;
+  static constexpr int K = NW, R = NW <= 2 ? 4 : 2, BATCH = NW == 1 ? 48 : (NW == 2 ? 32 : 16);
 };
 template <>
 struct CullTraits<kCullMom, 1> {
