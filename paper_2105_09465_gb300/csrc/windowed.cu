@@ -5,9 +5,10 @@
 //   out_i = sum_k G(p_i - q_k, Z_i + (l^2/2) I) v_k,
 //   G(d, C) = exp(-d^T C^-1 d / 2) / (2 pi sqrt(det C)),
 // with the transmission weights A_k folded into v_k by the caller. Each
-// query row carries its own 2x2 inverse covariance (three coefficients,
-// pre-scaled for exp2) and normalisation; per pair the exponent is a
-// quadratic form in (dx, dy). Grid sources: the grid tiling, chunking and
+// query row carries its own window constants, prepared once with C and
+// det C in FP64 (launch_window_prep): the Cholesky factor (a, b, c) of C^-1
+// pre-scaled for exp2 and the normalisation; per pair the exponent is
+// -((a dx + b dy)^2 + (c dy)^2). Grid sources: the grid tiling, chunking and
 // fixed-order merge of the stationary reduction (windowed_kernel). Explicit
 // sources (the image-plane layers, the pixels against themselves): the
 // culled sweep of cull.cu, which leaves out the pairs whose exponent is below
@@ -46,13 +47,12 @@ __global__ void pixel_shapes_kernel(const float2* __restrict__ p, int32_t W, int
 
 struct WnArgs {
   const float2* p;
-  const float* z;
+  const float4* wcoef;  // the rows' window constants (launch_window_prep)
   int64_t n;
   GridDev g;        // the source grid
   int64_t m;
   int32_t segs, n_tiles, chunks;
   const float* v;
-  float half_s;     // l^2 / 2
   float* out;
   float* partial;
 };
@@ -88,25 +88,23 @@ __global__ void __launch_bounds__(kWnThreads) windowed_kernel(const __grid_const
   const int t0 = (int)((int64_t)chunk * A.n_tiles / A.chunks);
   const int t1 = (int)((int64_t)(chunk + 1) * A.n_tiles / A.chunks);
   const int tid = threadIdx.x;
-  // per row: exponent = dx (mxx dx + mxy2 dy) + myy dy^2 with the inverse
-  // covariance pre-scaled by -log2(e)/2
-  float2 xq[kWnR], yq[kWnR], mxx[kWnR], mxy2[kWnR], myy[kWnR], acc[kWnR];
-  float norm[kWnR];
+  // per row: the scaled Cholesky factor (a, b, c) of C^-1 and N (window
+  // constants prepared with C and det C in FP64: cull.cuh), so that the
+  // exponent is -((a dx + b dy)^2 + (c dy)^2) with d = x_i - y_j
+  float2 xq[kWnR], yq[kWnR], acc[kWnR];
+  float ca[kWnR], boa[kWnR], cc[kWnR], norm[kWnR];
 #pragma unroll
   for (int r = 0; r < kWnR; ++r) {
     int64_t i = (int64_t)rb * kWnRows + r * kWnThreads + tid;
     if (i >= A.n) i = A.n - 1;
     const float2 pp = __ldg(A.p + i);
-    const float cxx = __ldg(A.z + 3 * i) + A.half_s, cxy = __ldg(A.z + 3 * i + 1),
-                cyy = __ldg(A.z + 3 * i + 2) + A.half_s;
-    const float det = fmaf(cxx, cyy, -cxy * cxy);
-    const float s = -0.72134752044448170f / det;  // -log2(e) / (2 det)
+    const float4 wc = A.wcoef[i];
     xq[r] = wf2(pp.x, pp.x);
     yq[r] = wf2(pp.y, pp.y);
-    mxx[r] = wf2(s * cyy, s * cyy);
-    mxy2[r] = wf2(-2.0f * s * cxy, -2.0f * s * cxy);
-    myy[r] = wf2(s * cxx, s * cxx);
-    norm[r] = 0.15915494309189535f * rsqrtf(det);  // 1 / (2 pi sqrt(det))
+    ca[r] = wc.x;
+    boa[r] = wc.y / wc.x;
+    cc[r] = wc.z;
+    norm[r] = wc.w;
     acc[r] = wf2(0.f, 0.f);
     ksum[r][tid] = 0.f;
     kcomp[r][tid] = 0.f;
@@ -126,24 +124,21 @@ __global__ void __launch_bounds__(kWnThreads) windowed_kernel(const __grid_const
     int cnt, grow;
     wn_tile(A, t, j0, cnt, grow);
     {
-      // Uniform y on a grid row: completing the square in dx,
-      //   -e = -mxx (dx + kap dy)^2 + lam dy^2,  kap = mxy2 / (2 mxx),
-      //   lam = mxy2^2 / (4 mxx) - myy >= 0,
-      // so with s = sqrt(-mxx) and w = s ((x_i - o) + kap dy) - s (x_j - o)
-      // the pair needs one packed FMA for w of two pairs, one for
-      // t = w^2 + lam dy^2, the exp2 of -t and one packed FMA to accumulate.
+      // Uniform y on a grid row: the Cholesky form is a completed square in
+      // dx, t = a^2 (dx + (b/a) dy)^2 + (c dy)^2, so with
+      // w = a ((x_i - o) + (b/a) dy) - a (x_j - o) the pair needs one packed
+      // FMA for w of two pairs, one for t = w^2 + (c dy)^2, the exp2 of -t
+      // and one packed FMA to accumulate.
       const float yt = grid_y(A.g, grow);
       const int c0 = (int)(j0 - (int64_t)grow * A.g.W);
       float kdy[kWnR], sr[kWnR];
       float2 t0[kWnR], ns[kWnR];
 #pragma unroll
       for (int r = 0; r < kWnR; ++r) {
-        const float a2 = mxx[r].x, dy = yq[r].x - yt;
-        const float kap = mxy2[r].x / (2.0f * a2);
-        const float lam = fmaxf(fmaf(mxy2[r].x, kap * 0.5f, -myy[r].x), 0.f);
-        sr[r] = sqrtf(-a2);
-        kdy[r] = kap * dy;
-        t0[r] = wf2(lam * dy * dy, lam * dy * dy);
+        const float dy = yq[r].x - yt, cdy = cc[r] * dy;
+        sr[r] = ca[r];
+        kdy[r] = boa[r] * dy;
+        t0[r] = wf2(cdy * cdy, cdy * cdy);
         ns[r] = wf2(-sr[r], -sr[r]);
       }
       const int nsg = (cnt + kWnSeg - 1) / kWnSeg;
@@ -261,7 +256,9 @@ static lr_status plan_windowed(int64_t n, const lr_grid* layout, const lr_points
   LR_CHECK_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
   LR_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, windowed_kernel, kWnThreads, 0));
   p.chunks = plan_chunks(p.row_blocks, p.n_tiles, occ, n_sm);
-  p.bytes = p.chunks > 1 ? align256(4 * (size_t)p.chunks * (size_t)n) : 0;
+  p.off_wcoef = p.chunks > 1 ? align256(4 * (size_t)p.chunks * (size_t)n) : 0;
+  p.off_wreach = p.off_wcoef + align256(16 * (size_t)n);
+  p.bytes = p.off_wreach + align256(4 * (size_t)n);
   *P = p;
   return LR_OK;
 }
@@ -310,12 +307,11 @@ extern "C" lr_status gp_windowed_matvec(const float* p, const float* z, int64_t 
     LR_CHECK_CUDA(cudaMemsetAsync(out, 0, 4 * (size_t)n, s));
     return LR_OK;
   }
-  const float half_s = 0.5f * lengthscale * lengthscale;
+  char* ws = static_cast<char*>(workspace);
+  float4* wcoef = reinterpret_cast<float4*>(ws + P.off_wcoef);
+  float* wreach = reinterpret_cast<float*>(ws + P.off_wreach);
+  if ((st = launch_window_prep(z, n, lengthscale, wcoef, wreach, s)) != LR_OK) return st;
   if (P.culled) {
-    char* ws = static_cast<char*>(workspace);
-    float4* wcoef = reinterpret_cast<float4*>(ws + P.off_wcoef);
-    float* wreach = reinterpret_cast<float*>(ws + P.off_wreach);
-    if ((st = launch_window_prep(z, n, lengthscale, wcoef, wreach, s)) != LR_OK) return st;
     st = launch_cull_prep(P.C, reinterpret_cast<const float2*>(source->xy), 0.f, v, nullptr, 1, 0, ws, s);
     if (st != LR_OK) return st;
     CullArgs A{};
@@ -330,7 +326,7 @@ extern "C" lr_status gp_windowed_matvec(const float* p, const float* z, int64_t 
   }
   WnArgs A{};
   A.p = reinterpret_cast<const float2*>(p);
-  A.z = z;
+  A.wcoef = wcoef;
   A.n = n;
   A.g = grid_dev(source->grid);
   A.m = source->n;
@@ -338,9 +334,8 @@ extern "C" lr_status gp_windowed_matvec(const float* p, const float* z, int64_t 
   A.n_tiles = P.n_tiles;
   A.chunks = P.chunks;
   A.v = v;
-  A.half_s = half_s;
   A.out = out;
-  A.partial = static_cast<float*>(workspace);
+  A.partial = reinterpret_cast<float*>(ws);
   const unsigned grid = (unsigned)((int64_t)P.row_blocks * P.chunks);
   ktimer_begin(LR_KT_WINDOWED, s);
   windowed_kernel<<<grid, kWnThreads, 0, s>>>(A);

@@ -212,6 +212,25 @@ def test_image_plane_layer_at_the_papers_scales(orc, ell, layout):
     check_windowed(G, got, R, T, f"image-plane layer l = {ell}")
 
 
+@pytest.mark.parametrize("ell", [0.002, 0.00447, 0.01])
+def test_grid_sources_with_narrow_kernels(orc, ell):
+    """Grid sources at the image-plane layers' kernel sizes (10, 4.47 and
+    2 mas), spaced 3/4 of the length scale, 270 columns (two tiles, the
+    second ragged) by 10 rows, against a lensed 60 x 60 image whose
+    windows are most elongated relative to the kernel there: every output
+    against the FP64 oracle within the derived FP32 tolerance."""
+    g, b, zr, v, _ = image_layer(orc, 60, ell, seed=33)
+    yg = W.Grid(270, 10, 1, 0.75 * ell)
+    q = orc.grid_points(*yg.astuple())
+    w = np.random.default_rng(34).standard_normal(len(q)).astype(np.float32)
+    got = host(api.gp_windowed_matvec(dev(b), dev(zr), api.Points(grid=yg), dev(w), ell))
+    R, T = windowed_tols(orc, b, zr, q, w, np.zeros(len(b), np.float32), ell)
+    near = R["out"] != 0
+    assert int(np.sum(np.abs(R["out"]) > 1e-3 * np.abs(R["out"]).max())) >= 20  # rows that meet the grid
+    _close(got, R["out"], 0.0, 0.0, f"grid sources l = {ell}", T["out"])
+    assert np.all(got[~near] == 0)
+
+
 @pytest.mark.parametrize("ell", [0.002, 0.05])
 def test_skipping_is_exact_bitwise(orc, ell):
     """With exact skipping switched off every pair is evaluated, in the same
