@@ -43,10 +43,14 @@ SM_MAX_MHZ_DEFAULT = 2070.0
 # accumulate both components, 1.25 for the Kahan fold after every 8
 # subhalos; MUFU: 2 rsqrt, 1 rcp, 1 lg2. Forward, far-field series
 # (x >= 6 max(tau, 2)): 2 + 3, 1 for y^2, 7 + 1 for the Horner steps, 2 for
-# m = A y^2 Q, 2 + 1.25 to accumulate and fold; MUFU: 1 rsqrt. Backward
-# (closed form throughout): 5 + 22, 12 for the G and H brackets, 11 for the
-# four subhalo sums (their constant factors, 1/theta_s^2 of the q terms
-# included, applied once per fold or slot), 0.6 for the Kahan folds; 4 MUFU.
+# m = A y^2 Q, 2 + 1.25 to accumulate and fold; MUFU: 1 rsqrt. Backward,
+# subhalos near the CTA's points (far-side closed form): 5 + 22, 12 for the G
+# and H brackets, 11 for the four subhalo sums (their constant factors,
+# 1/theta_s^2 of the q terms included, applied once per fold or slot), 0.6
+# for the Kahan folds; 4 MUFU. Backward, subhalos whose series radius clears
+# every point of the CTA (far-field series of G and of x dG/dx): 5, 1 for
+# y^2, 7 + 7 for the two Horner chains, 2 + 2 for G and x dG/dx, 10 for the
+# four sums, 0.6 for the folds; 1 MUFU.
 # Culled reductions over explicit points (the self-kernel), per evaluated
 # pair: forward 2 differences, the squared distance (2), the scale (1) and
 # the accumulation (1); self-kernel backward the same 6 before the
@@ -57,6 +61,7 @@ CULL_SELF_MUFU, CULL_SELF_LANES = 1, 14.0
 RT_MUFU, RT_LANES = 4, 37.3
 RT_SER_MUFU, RT_SER_LANES = 1, 19.25
 VJ_MUFU, VJ_LANES = 4, 50.6
+VJ_SER_MUFU, VJ_SER_LANES = 1, 34.6
 
 
 def series_fraction(p) -> float:
@@ -79,6 +84,42 @@ def series_fraction(p) -> float:
     return far / (len(pts) * len(sub))
 
 
+def vjp_series_fraction(p, nblk: int) -> float:
+    """Fraction of the point-subhalo pairs that the ray-trace backward sums by
+    the far-field series: CTA b of nblk takes the points [b n / nblk,
+    (b + 1) n / nblk) in row-major order, and a subhalo takes the series for
+    all of them when the bounding box of those points is beyond its series
+    radius (x^2 >= 36 max(tau^2, 4))."""
+    g = p.xgrid
+    w, hgt = g.nx * g.ss, g.ny * g.ss
+    h = g.pix / g.ss
+    xs = (np.arange(w) - (w - 1) / 2) * h + g.cx
+    ys = (np.arange(hgt) - (hgt - 1) / 2) * h + g.cy
+    n = w * hgt
+    b = np.arange(nblk, dtype=np.int64)
+    p0, p1 = b * n // nblk, (b + 1) * n // nblk
+    cnt = p1 - p0
+    r0, r1 = p0 // w, np.maximum(p1 - 1, p0) // w
+    c0, c1 = p0 % w, np.maximum(p1 - 1, p0) % w
+    one = r0 == r1
+    xlo = np.where(one, xs[c0], xs[0])
+    xhi = np.where(one, xs[c1], xs[-1])
+    ylo, yhi = ys[r0], ys[r1]
+    sub = p.sub.astype(np.float64)
+    its2 = 1.0 / sub[:, 3] ** 2
+    xT2 = 36.0 * np.maximum(sub[:, 4] ** 2, 4.0)
+    dx = np.maximum(np.maximum(xlo[:, None] - sub[None, :, 0], sub[None, :, 0] - xhi[:, None]), 0.0)
+    dy = np.maximum(np.maximum(ylo[:, None] - sub[None, :, 1], sub[None, :, 1] - yhi[:, None]), 0.0)
+    far = (dx * dx + dy * dy) * its2[None, :] >= xT2[None, :]
+    return float((far.sum(1) * cnt).sum()) / float(n * len(sub))
+
+
+def vjp_blocks(dev) -> int:
+    """CTAs of the ray-trace backward at 4 resident per SM (128 registers and
+    41 KB of shared memory each), one per 128 points at most."""
+    return 4 * torch.cuda.get_device_properties(dev).multi_processor_count
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -91,6 +132,9 @@ def parse():
     ap.add_argument("--no-graph", action="store_true", help="launch the step's kernels directly, not from a CUDA graph")
     ap.add_argument("--profile", action="store_true",
                     help="headline step only, direct launches: W warm-up and K timed steps, then exit (profiler runs)")
+    ap.add_argument("--profile-side", type=int, default=800,
+                    help="with --profile: pixels per side of the large workload's image (800: the workload itself; "
+                         "smaller sides give profiler captures of the same recipe)")
     ap.add_argument("--profile-layer", action="store_true",
                     help="the image-plane layer's windowed forward and backward only (400x400 ray-traced pixels "
                          "against themselves, l = 0.05 arcsec): W warm-up and K timed calls, then exit (profiler runs)")
@@ -745,10 +789,15 @@ def run_realistic(args, dev, rates, clk) -> dict:
         f"pairs: {rt_mufu:.2f} MUFU + {rt_lanes:.1f} FP32 lanes each on average: {fs:.3f} of the pairs in the "
         f"far-field series regime ({RT_SER_MUFU} MUFU + {RT_SER_LANES} lanes), the rest the far-side closed form "
         f"({RT_MUFU} MUFU + {RT_LANES} lanes); the SPLE and shear terms, once per point, are not counted", True)
+    fv = vjp_series_fraction(p, min(vjp_blocks(dev), (p.n + 127) // 128))
+    vj_mufu = fv * VJ_SER_MUFU + (1 - fv) * VJ_MUFU
+    vj_lanes = fv * VJ_SER_LANES + (1 - fv) * VJ_LANES
     kern["raytrace_vjp_kernel<tNFW> (ray-trace backward; unit: point-subhalo pair)"] = (
-        vjp_ms, vjp_call_ms, sub_pairs, VJ_MUFU, VJ_LANES,
-        f"pairs: {VJ_MUFU} MUFU + {VJ_LANES} FP32 lanes each (far-side tNFW G and H brackets and the four subhalo "
-        "sums; the per-point SPLE and shear gradient terms are not counted)", True)
+        vjp_ms, vjp_call_ms, sub_pairs, vj_mufu, vj_lanes,
+        f"pairs: {vj_mufu:.2f} MUFU + {vj_lanes:.1f} FP32 lanes each on average: {fv:.3f} of the pairs from "
+        f"subhalos whose series radius clears the CTA's points (far-field series, {VJ_SER_MUFU} MUFU + "
+        f"{VJ_SER_LANES} lanes), the rest the far-side closed form ({VJ_MUFU} MUFU + {VJ_LANES} lanes); the "
+        "per-point SPLE and shear gradient terms are not counted", True)
 
     # ---- end to end through the public API with host buffers
     v_host = torch.from_numpy(p.v).pin_memory()
@@ -873,7 +922,7 @@ def run_large(args, rank, local, world, dist, dev):
     from paper_2105_09465_gb300 import api, replicas, workloads as W
 
     # each rank owns an independent lens system of the large recipe (weak scaling)
-    p = W.large(seed=4 + rank)
+    p = W.large(seed=4 + rank, side=args.profile_side if args.profile else 800)
     g_np = np.random.default_rng(400 + rank).standard_normal(p.n).astype(np.float32)
     sub = torch.from_numpy(p.sub).to(dev)
     v = torch.from_numpy(p.v).to(dev)
@@ -1013,10 +1062,14 @@ def run_large(args, rank, local, world, dist, dev):
         f"pairs: {rt_mufu:.2f} MUFU + {rt_lanes:.1f} FP32 lanes each on average: {fs:.3f} of the pairs in the "
         f"far-field series regime ({RT_SER_MUFU} MUFU + {RT_SER_LANES} lanes), the rest the far-side closed form "
         f"({RT_MUFU} MUFU + {RT_LANES} lanes)", True)
+    fv = vjp_series_fraction(p, min(vjp_blocks(dev), (p.n + 127) // 128))
+    vj_mufu = fv * VJ_SER_MUFU + (1 - fv) * VJ_MUFU
+    vj_lanes = fv * VJ_SER_LANES + (1 - fv) * VJ_LANES
     kern["raytrace_vjp_kernel<tNFW> (ray-trace backward; unit: point-subhalo pair)"] = (
-        vjp_ms, vjp_call_ms, sub_pairs, VJ_MUFU, VJ_LANES,
-        f"pairs: {VJ_MUFU} MUFU + {VJ_LANES} FP32 lanes each (far-side tNFW G and H brackets and the four subhalo "
-        "sums)", True)
+        vjp_ms, vjp_call_ms, sub_pairs, vj_mufu, vj_lanes,
+        f"pairs: {vj_mufu:.2f} MUFU + {vj_lanes:.1f} FP32 lanes each on average: {fv:.3f} of the pairs from "
+        f"subhalos whose series radius clears the CTA's points (far-field series of G and x dG/dx, {VJ_SER_MUFU} "
+        f"MUFU + {VJ_SER_LANES} lanes), the rest the far-side closed form ({VJ_MUFU} MUFU + {VJ_LANES} lanes)", True)
 
     # ---- end to end through the public API with host buffers
     v_host = torch.from_numpy(p.v).pin_memory()

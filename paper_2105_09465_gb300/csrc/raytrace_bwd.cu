@@ -20,6 +20,13 @@
 // Per-CTA partials (FP64 lens terms, Kahan-compensated FP32 slot
 // sums) are added in fixed order by a final kernel, so results are
 // deterministic.
+//
+// tNFW subhalos whose far-field series radius (x >= 6 max(tau, 2)) clears
+// the bounding box of all of a CTA's points sum by the series of G and of
+// x dG/dx (1 rsqrt and two degree-7 polynomials per pair) with no per-pair
+// test; the others take the far-side closed form per pair and the general
+// form for the rare near pairs. Each CTA orders its subhalos far-first
+// (vj_order), so that whole warps take one path.
 #include <math.h>
 
 #include "host.cuh"
@@ -33,6 +40,7 @@ constexpr int kVjWarps = kVjThreads / 32;
 constexpr int kVjChunk = 2048;    // points staged in shared memory at once
 constexpr int kVjMaxPhases = 8;
 constexpr int kVjFold = 16;       // point pairs summed plainly per slot before a Kahan fold
+constexpr int kVjMaxOrd = 4096;   // subhalo counts up to which a CTA orders its slots far-first
 
 __device__ __forceinline__ double warp_sum_d(double v) {
 #pragma unroll
@@ -44,21 +52,23 @@ struct VjSmem {
   float4 pos[kVjChunk / 2];   // point pair k: (x_2k, x_2k+1, y_2k, y_2k+1)
   float4 grad[kVjChunk / 2];  // (G_x, G_x, G_y, G_y) of the same two points
   double lred[kVjWarps][7];
+  unsigned short ord[kVjMaxOrd];  // slot subhalo -> subhalo: far from the CTA's points first
+  float wbox[kVjWarps][4];        // per-warp bounds of the CTA's points
+  float box[4];                   // x_lo, y_lo, x_hi, y_hi of the CTA's points
 };
 
 // One tNFW pair's terms of the four subhalo sums, for two points at once
 // (packed f32x2; ix2 = 1/x^2 = theta_s^2 / R^2), without the subhalo's
-// constant factors: with dg = d.G and hg = H - 2G,
+// constant factors: with dg = d.G and hg = H - 2G (= x dG/dx),
 //   sum 0 = G G_x + q dx, sum 1 = G G_y + q dy (q = hg dg / R^2),
 //   sum 2 = G dg, sum 3 = hg dg.
 // The q terms are kept apart (b0, b1, with hg dg / x^2 in place of q) and
 // join sums 0 and 1 with the factor 1/theta_s^2 once per fold; the slot's
 // sums are scaled once by (A, A, -4T, A / theta_s) (vj_scale).
 __device__ __forceinline__ void vj_accum2(float2 dx, float2 dy, float2 gx, float2 gy, float2 ix2, float2 Gt,
-                                          float2 Ht, float2& a0, float2& a1, float2& a2, float2& a3, float2& b0,
+                                          float2 hg, float2& a0, float2& a1, float2& a2, float2& a3, float2& b0,
                                           float2& b1) {
   const float2 dg = __ffma2_rn(dx, gx, __fmul2_rn(dy, gy));
-  const float2 hg = __ffma2_rn(f2(-2.0f), Gt, Ht);
   const float2 q = __fmul2_rn(__fmul2_rn(hg, dg), ix2);
   b0 = __ffma2_rn(q, dx, b0);
   b1 = __ffma2_rn(q, dy, b1);
@@ -100,15 +110,82 @@ __device__ __forceinline__ void vj_fix_near(const SubRec& rec, float2 R2, float2
   }
 }
 
+// The far field of a tNFW subhalo for the gradient: with y = 1/x and the
+// deflection's series G = y^2 Q(y), Q = q0 + sum_{j>=2} q_j y^j (prep_series),
+//   hg = x dG/dx = -y^2 (2 Q + y Q'(y)) = y^2 (s0 + sum_{j>=2} s_j y^j),
+//   s0 = -2 q0, s_j = -(j + 2) q_j.
+// Against the closed form in extended precision, at the series radius
+// x = 6 max(tau, 2) the truncated hg is within 3e-9 relative (G within
+// 5e-10) for tau in [2, 20], and the error falls as x^-10 beyond it.
+struct VjSer {
+  float2 q0, s0;
+  float2 q[kSerTerms - 2], s[kSerTerms - 2];  // index j - 2
+};
+
+__device__ __forceinline__ VjSer vj_series_coeffs(const SubSer& c) {
+  VjSer v;
+  v.q0 = f2(c.q[0]);
+  v.s0 = f2(-2.0f * c.q[0]);
+#pragma unroll
+  for (int j = 2; j < kSerTerms; ++j) {
+    v.q[j - 2] = f2(c.q[j]);
+    v.s[j - 2] = f2(-(float)(j + 2) * c.q[j]);
+  }
+  return v;
+}
+
+// G, hg and 1/x^2 = y^2 of two points by the series (x^2 at or beyond the
+// series radius for both).
+__device__ __forceinline__ void vj_series2(const VjSer& c, float2 x2, float2& Gt, float2& hg, float2& ix2) {
+  const float2 y = frsqrt2(x2), y2 = __fmul2_rn(y, y);
+  float2 r = c.q[kSerTerms - 3], t = c.s[kSerTerms - 3];
+#pragma unroll
+  for (int j = kSerTerms - 4; j >= 0; --j) {
+    r = __ffma2_rn(r, y, c.q[j]);
+    t = __ffma2_rn(t, y, c.s[j]);
+  }
+  Gt = __fmul2_rn(y2, __ffma2_rn(r, y2, c.q0));
+  hg = __fmul2_rn(y2, __ffma2_rn(t, y2, c.s0));
+  ix2 = y2;
+}
+
+// far: every staged point of the CTA is at or beyond the subhalo's series
+// radius (tNFW only), so the series serves every pair without a test.
 template <int PROFILE>
-__device__ __forceinline__ void vj_sweep(const SubRec& rec, float2 ex, const float4* __restrict__ pos,
-                                         const float4* __restrict__ grad, int npairs, int r, int P, float* s,
-                                         float* c) {
+__device__ __forceinline__ void vj_sweep(const SubRec& rec, float2 ex, const VjSer& ser, bool far,
+                                         const float4* __restrict__ pos, const float4* __restrict__ grad, int npairs,
+                                         int r, int P, float* s, float* c) {
   const SubRec2 H = sub_pair(rec, rec);
   for (int k = r; k < npairs;) {
     const int kend = min(npairs, k + P * kVjFold);
     float2 a0 = f2(0.f), a1 = f2(0.f), a2 = f2(0.f), a3 = f2(0.f), b0 = f2(0.f), b1 = f2(0.f);
-    if (PROFILE == LR_PROFILE_TNFW) {
+    if (PROFILE == LR_PROFILE_TNFW && far) {
+      for (; k + P < kend; k += 2 * P) {
+        float2 dx[2], dy[2], gx[2], gy[2], Gt[2], hg[2], ix2[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const float4 Q = pos[k + u * P], D = grad[k + u * P];
+          dx[u] = sub2(make_float2(Q.x, Q.y), H.xh);
+          dy[u] = sub2(make_float2(Q.z, Q.w), H.yh);
+          gx[u] = make_float2(D.x, D.y);
+          gy[u] = make_float2(D.z, D.w);
+          const float2 R2 = __ffma2_rn(dx[u], dx[u], __fmul2_rn(dy[u], dy[u]));
+          vj_series2(ser, __fmul2_rn(R2, H.its2), Gt[u], hg[u], ix2[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u)
+          vj_accum2(dx[u], dy[u], gx[u], gy[u], ix2[u], Gt[u], hg[u], a0, a1, a2, a3, b0, b1);
+      }
+      if (k < kend) {
+        const float4 Q = pos[k], D = grad[k];
+        const float2 dx = sub2(make_float2(Q.x, Q.y), H.xh), dy = sub2(make_float2(Q.z, Q.w), H.yh);
+        const float2 R2 = __ffma2_rn(dx, dx, __fmul2_rn(dy, dy));
+        float2 Gt, hg, ix2;
+        vj_series2(ser, __fmul2_rn(R2, H.its2), Gt, hg, ix2);
+        vj_accum2(dx, dy, make_float2(D.x, D.y), make_float2(D.z, D.w), ix2, Gt, hg, a0, a1, a2, a3, b0, b1);
+        k += P;
+      }
+    } else if (PROFILE == LR_PROFILE_TNFW) {
       // two steps at a time: both far-side forms first (independent chains
       // that can interleave), then the near fixes and the sums in step order
       for (; k + P < kend; k += 2 * P) {
@@ -126,7 +203,8 @@ __device__ __forceinline__ void vj_sweep(const SubRec& rec, float2 ex, const flo
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
           vj_fix_near(rec, R2[u], em1[u], gx[u], gy[u], Gt[u], Ht[u], ix2[u]);
-          vj_accum2(dx[u], dy[u], gx[u], gy[u], ix2[u], Gt[u], Ht[u], a0, a1, a2, a3, b0, b1);
+          vj_accum2(dx[u], dy[u], gx[u], gy[u], ix2[u], Gt[u], __ffma2_rn(f2(-2.0f), Gt[u], Ht[u]), a0, a1, a2, a3,
+                    b0, b1);
         }
       }
     }
@@ -141,7 +219,7 @@ __device__ __forceinline__ void vj_sweep(const SubRec& rec, float2 ex, const flo
         float2 Gt, Ht, ix2, em1;
         tnfw_GH_far2(H, __fmul2_rn(R2, H.its2), Gt, Ht, ix2, em1);
         vj_fix_near(rec, R2, em1, gx, gy, Gt, Ht, ix2);
-        vj_accum2(dx, dy, gx, gy, ix2, Gt, Ht, a0, a1, a2, a3, b0, b1);
+        vj_accum2(dx, dy, gx, gy, ix2, Gt, __ffma2_rn(f2(-2.0f), Gt, Ht), a0, a1, a2, a3, b0, b1);
       } else {
         // point mass: alpha = theta^2 d / R^2 (its2 = theta^2, ex.y = theta)
         float2 iR2 = make_float2(R2.x > 1e-30f ? frcp(R2.x) : 0.f, R2.y > 1e-30f ? frcp(R2.y) : 0.f);
@@ -164,6 +242,69 @@ __device__ __forceinline__ void vj_sweep(const SubRec& rec, float2 ex, const flo
   }
 }
 
+// Whether every point in the box (x_lo, y_lo, x_hi, y_hi) is at or beyond the
+// subhalo's series radius: x^2 of the box's nearest point reaches xT2.
+__device__ __forceinline__ bool vj_far(const SubRec& h, const SubSer& q, const float* box) {
+  const float dx = fmaxf(fmaxf(box[0] - h.xh, h.xh - box[2]), 0.f);
+  const float dy = fmaxf(fmaxf(box[1] - h.yh, h.yh - box[3]), 0.f);
+  return __fmul_rn(fmaf(dx, dx, dy * dy), h.its2) >= q.xT2;
+}
+
+// The CTA's prologue for a tNFW sum: the bounds of its points [p0, p1), then
+// (ordered) the subhalos far from all of them (vj_far) in index order,
+// followed by the others, in sm.ord, so that the far ones, whose slots sweep
+// by the series alone, fill whole warps. The slots' sums do not depend on
+// the order.
+__device__ __forceinline__ void vj_order(const GridDev& g, const float2* __restrict__ xi, int64_t p0, int64_t p1,
+                                         const float* __restrict__ sub, int n_sub, bool ordered, VjSmem& sm) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  float b0 = INFINITY, b1 = INFINITY, b2 = -INFINITY, b3 = -INFINITY;
+  for (int64_t i = p0 + tid; i < p1; i += kVjThreads) {
+    const float2 p = xi ? xi[i] : grid_point(g, i);
+    b0 = fminf(b0, p.x);
+    b1 = fminf(b1, p.y);
+    b2 = fmaxf(b2, p.x);
+    b3 = fmaxf(b3, p.y);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    b0 = fminf(b0, __shfl_xor_sync(0xffffffffu, b0, o));
+    b1 = fminf(b1, __shfl_xor_sync(0xffffffffu, b1, o));
+    b2 = fmaxf(b2, __shfl_xor_sync(0xffffffffu, b2, o));
+    b3 = fmaxf(b3, __shfl_xor_sync(0xffffffffu, b3, o));
+  }
+  if (lane == 0) {
+    sm.wbox[warp][0] = b0;
+    sm.wbox[warp][1] = b1;
+    sm.wbox[warp][2] = b2;
+    sm.wbox[warp][3] = b3;
+  }
+  __syncthreads();
+  if (tid < 4) {
+    float v = sm.wbox[0][tid];
+    for (int w = 1; w < kVjWarps; ++w) v = tid < 2 ? fminf(v, sm.wbox[w][tid]) : fmaxf(v, sm.wbox[w][tid]);
+    sm.box[tid] = v;
+  }
+  __syncthreads();
+  if (!ordered) return;
+  if (warp == 0) {  // stable partition: far first
+    int nf = 0;
+    for (int pass = 0; pass < 2; ++pass) {
+      for (int b = 0; b < n_sub; b += 32) {
+        bool f = false;
+        if (b + lane < n_sub) {
+          const SubRec h = prep_sub(sub + 5 * (int64_t)(b + lane), LR_PROFILE_TNFW);
+          f = vj_far(h, prep_series(h, LR_PROFILE_TNFW), sm.box) == (pass == 0);
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, f);
+        if (f) sm.ord[nf + __popc(m & ((1u << lane) - 1u))] = (unsigned short)(b + lane);
+        nf += __popc(m);
+      }
+    }
+  }
+  __syncthreads();
+}
+
 template <int PROFILE>
 __device__ __forceinline__ void vjp_body(const LensConst& L, const LensGradConst& LG, const GridDev& g,
                                          const float2* __restrict__ xi, int64_t n, const float* __restrict__ sub,
@@ -177,17 +318,27 @@ __device__ __forceinline__ void vjp_body(const LensConst& L, const LensGradConst
   const int ngroups = slots > 0 ? (slots + kVjThreads - 1) / kVjThreads : 1;
   float la[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   int staged = -1;
+  const bool ordered = PROFILE == LR_PROFILE_TNFW && n_sub > 0 && n_sub <= kVjMaxOrd;
+  if (PROFILE == LR_PROFILE_TNFW) vj_order(g, xi, p0, p1, sub, n_sub, ordered, sm);
 
   for (int grp = 0; grp < ngroups; ++grp) {
     const int slot = grp * kVjThreads + tid;
     const bool own = slot < slots;
-    const int h = own ? slot / P : 0;
-    const int r = own ? slot - h * P : 0;
+    const int hs = own ? slot / P : 0;  // the slot's subhalo in the CTA's order
+    const int r = own ? slot - hs * P : 0;
+    const int h = ordered ? (int)sm.ord[hs] : hs;
     SubRec rec{};
+    VjSer ser{};
+    bool far = false;
     float2 ex = make_float2(0.f, 0.f);  // tNFW: (4T, 1/theta_s); point mass: (0, theta_pm)
     if (own) {
       const float* rr = sub + 5 * (int64_t)h;
       rec = prep_sub(rr, PROFILE);
+      if (PROFILE == LR_PROFILE_TNFW) {
+        const SubSer q = prep_series(rec, PROFILE);
+        far = vj_far(rec, q, sm.box);
+        if (far) ser = vj_series_coeffs(q);
+      }
       if (PROFILE == LR_PROFILE_POINT_MASS) {
         ex = make_float2(0.f, __ldg(rr + 2));
       } else {
@@ -230,14 +381,14 @@ __device__ __forceinline__ void vjp_body(const LensConst& L, const LensGradConst
         __syncthreads();
         staged = ch;
       }
-      if (own) vj_sweep<PROFILE>(rec, ex, sm.pos, sm.grad, (cnt + 1) >> 1, r, P, sc, cc);
+      if (own) vj_sweep<PROFILE>(rec, ex, ser, far, sm.pos, sm.grad, (cnt + 1) >> 1, r, P, sc, cc);
     }
     if (own) {
 #pragma unroll
       for (int v = 0; v < 4; ++v) {
         const float x = __fmul_rn(sc[v] - cc[v], vj_scale<PROFILE>(rec, ex, v));
         if (P == 1)
-          sub_part[((int64_t)h * 4 + v) * nblk + blk] = x;  // [value][CTA]
+          sub_part[((int64_t)h * 4 + v) * nblk + blk] = x;  // [value][CTA], h the subhalo itself
         else
           slot_part[(blk * slots + slot) * 4 + v] = x;
       }
@@ -248,11 +399,12 @@ __device__ __forceinline__ void vjp_body(const LensConst& L, const LensGradConst
     // visible to the whole CTA after the barrier)
     __syncthreads();
     for (int t = tid; t < 4 * n_sub; t += kVjThreads) {
-      const int hh = t >> 2, v = t & 3;
+      const int hh = t >> 2, v = t & 3;  // hh: the CTA's order
       const float* q = slot_part + (blk * slots + (int64_t)hh * P) * 4 + v;
       float a = 0.f, c = 0.f;
       for (int rr = 0; rr < P; ++rr) vj_kahan(a, c, q[4 * rr]);
-      sub_part[(int64_t)t * nblk + blk] = a - c;
+      const int64_t hreal = ordered ? (int64_t)sm.ord[hh] : (int64_t)hh;
+      sub_part[(hreal * 4 + v) * nblk + blk] = a - c;
     }
   }
 

@@ -100,6 +100,24 @@ def test_raytrace_vjp(orc, profile):
     close(host(d_sub), rs, asub, what="d_sub")
 
 
+@pytest.mark.parametrize("n_sub", [3, 4097])
+def test_raytrace_vjp_subhalo_counts(orc, n_sub):
+    """A few subhalos (several phases per subhalo) and more subhalos than a
+    CTA orders far-first (every slot in index order): the far-field series
+    and the closed forms both serve the sums, every gradient element against
+    the oracle."""
+    rng = np.random.default_rng(44)
+    lens = W.draw_lens(rng)
+    sub = W.draw_subhalos(rng, n_sub, lens, 1e6, 1e10)
+    g = W.Grid(24, 24, 2, 0.1)
+    xi = orc.grid_points(*g.astuple())
+    db = rng.standard_normal((g.n, 2)).astype(np.float32)
+    d_lens, d_sub = api.lens_raytrace_vjp(api.Points(grid=g, lens=lens, sub=dev(sub)), dev(db))
+    rl, rs, al, asub = orc.raytrace_vjp(xi, lens.astuple(), sub, db, 0, with_abs=True)
+    close(host(d_lens), rl, al, what="d_lens")
+    close(host(d_sub), rs, asub, what="d_sub")
+
+
 @pytest.mark.parametrize("name", ["hoags_object", "ngc4414"])
 def test_raytrace_vjp_printed_lenses(orc, name):
     from tests.golden.lenses import paper_lenses
