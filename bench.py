@@ -47,10 +47,11 @@ SM_MAX_MHZ_DEFAULT = 2070.0
 # subhalos near the CTA's points (far-side closed form): 5 + 22, 12 for the G
 # and H brackets, 11 for the four subhalo sums (their constant factors,
 # 1/theta_s^2 of the q terms included, applied once per fold or slot), 0.6
-# for the Kahan folds; 4 MUFU. Backward, subhalos whose series radius clears
-# every point of the CTA (far-field series of G and of x dG/dx): 5, 1 for
-# y^2, 7 + 7 for the two Horner chains, 2 + 2 for G and x dG/dx, 10 for the
-# four sums, 0.6 for the folds; 1 MUFU.
+# for the Kahan folds; 4 MUFU. Backward, subhalos whose gradient series
+# radius (x >= 8 max(tau, 2)) clears every point of the CTA (far-field series
+# of G and of x dG/dx to y^7): 5, 1 for y^2, 5 + 5 for the two Horner
+# chains, 2 + 2 for G and x dG/dx, 10 for the four sums, 0.6 for the folds;
+# 1 MUFU.
 # Culled reductions over explicit points (the self-kernel), per evaluated
 # pair: forward 2 differences, the squared distance (2), the scale (1) and
 # the accumulation (1); self-kernel backward the same 6 before the
@@ -61,7 +62,7 @@ CULL_SELF_MUFU, CULL_SELF_LANES = 1, 14.0
 RT_MUFU, RT_LANES = 4, 37.3
 RT_SER_MUFU, RT_SER_LANES = 1, 19.25
 VJ_MUFU, VJ_LANES = 4, 50.6
-VJ_SER_MUFU, VJ_SER_LANES = 1, 34.6
+VJ_SER_MUFU, VJ_SER_LANES = 1, 30.6
 
 
 def series_fraction(p) -> float:
@@ -88,8 +89,8 @@ def vjp_series_fraction(p, nblk: int) -> float:
     """Fraction of the point-subhalo pairs that the ray-trace backward sums by
     the far-field series: CTA b of nblk takes the points [b n / nblk,
     (b + 1) n / nblk) in row-major order, and a subhalo takes the series for
-    all of them when the bounding box of those points is beyond its series
-    radius (x^2 >= 36 max(tau^2, 4))."""
+    all of them when the bounding box of those points is beyond its gradient
+    series radius (x^2 >= 64 max(tau^2, 4))."""
     g = p.xgrid
     w, hgt = g.nx * g.ss, g.ny * g.ss
     h = g.pix / g.ss
@@ -107,7 +108,7 @@ def vjp_series_fraction(p, nblk: int) -> float:
     ylo, yhi = ys[r0], ys[r1]
     sub = p.sub.astype(np.float64)
     its2 = 1.0 / sub[:, 3] ** 2
-    xT2 = 36.0 * np.maximum(sub[:, 4] ** 2, 4.0)
+    xT2 = 64.0 * np.maximum(sub[:, 4] ** 2, 4.0)
     dx = np.maximum(np.maximum(xlo[:, None] - sub[None, :, 0], sub[None, :, 0] - xhi[:, None]), 0.0)
     dy = np.maximum(np.maximum(ylo[:, None] - sub[None, :, 1], sub[None, :, 1] - yhi[:, None]), 0.0)
     far = (dx * dx + dy * dy) * its2[None, :] >= xT2[None, :]

@@ -21,9 +21,9 @@
 // sums) are added in fixed order by a final kernel, so results are
 // deterministic.
 //
-// tNFW subhalos whose far-field series radius (x >= 6 max(tau, 2)) clears
+// tNFW subhalos whose far-field series radius (x >= 8 max(tau, 2)) clears
 // the bounding box of all of a CTA's points sum by the series of G and of
-// x dG/dx (1 rsqrt and two degree-7 polynomials per pair) with no per-pair
+// x dG/dx (1 rsqrt and two degree-5 polynomials per pair) with no per-pair
 // test; the others take the far-side closed form per pair and the general
 // form for the rare near pairs. Each CTA orders its subhalos far-first
 // (vj_order), so that whole warps take one path.
@@ -114,12 +114,16 @@ __device__ __forceinline__ void vj_fix_near(const SubRec& rec, float2 R2, float2
 // deflection's series G = y^2 Q(y), Q = q0 + sum_{j>=2} q_j y^j (prep_series),
 //   hg = x dG/dx = -y^2 (2 Q + y Q'(y)) = y^2 (s0 + sum_{j>=2} s_j y^j),
 //   s0 = -2 q0, s_j = -(j + 2) q_j.
-// Against the closed form in extended precision, at the series radius
-// x = 6 max(tau, 2) the truncated hg is within 3e-9 relative (G within
-// 5e-10) for tau in [2, 20], and the error falls as x^-10 beyond it.
+// The gradient takes the terms up to y^7 from x = 8 max(tau, 2) on: against
+// the closed form in extended precision both G and hg are within 1.2e-8
+// relative there for tau in [2, 20] (2e-9 from 10 max(tau, 2)), a fifth of
+// the FP32 unit roundoff.
+constexpr int kVjSerTerms = 8;         // q0 .. q7 (q1 = 0)
+constexpr float kVjSerRadius2 = 64.f;  // x^2 >= 64 max(tau^2, 4)
+
 struct VjSer {
   float2 q0, s0;
-  float2 q[kSerTerms - 2], s[kSerTerms - 2];  // index j - 2
+  float2 q[kVjSerTerms - 2], s[kVjSerTerms - 2];  // index j - 2
 };
 
 __device__ __forceinline__ VjSer vj_series_coeffs(const SubSer& c) {
@@ -127,20 +131,26 @@ __device__ __forceinline__ VjSer vj_series_coeffs(const SubSer& c) {
   v.q0 = f2(c.q[0]);
   v.s0 = f2(-2.0f * c.q[0]);
 #pragma unroll
-  for (int j = 2; j < kSerTerms; ++j) {
+  for (int j = 2; j < kVjSerTerms; ++j) {
     v.q[j - 2] = f2(c.q[j]);
     v.s[j - 2] = f2(-(float)(j + 2) * c.q[j]);
   }
   return v;
 }
 
+// x^2 from which the gradient takes the series (+inf where the deflection's
+// series is not in use for the subhalo).
+__device__ __forceinline__ float vj_radius2(const SubRec& h, const SubSer& q) {
+  return isinf(q.xT2) ? INFINITY : kVjSerRadius2 * fmaxf(h.tau2, 4.0f);
+}
+
 // G, hg and 1/x^2 = y^2 of two points by the series (x^2 at or beyond the
 // series radius for both).
 __device__ __forceinline__ void vj_series2(const VjSer& c, float2 x2, float2& Gt, float2& hg, float2& ix2) {
   const float2 y = frsqrt2(x2), y2 = __fmul2_rn(y, y);
-  float2 r = c.q[kSerTerms - 3], t = c.s[kSerTerms - 3];
+  float2 r = c.q[kVjSerTerms - 3], t = c.s[kVjSerTerms - 3];
 #pragma unroll
-  for (int j = kSerTerms - 4; j >= 0; --j) {
+  for (int j = kVjSerTerms - 4; j >= 0; --j) {
     r = __ffma2_rn(r, y, c.q[j]);
     t = __ffma2_rn(t, y, c.s[j]);
   }
@@ -149,7 +159,7 @@ __device__ __forceinline__ void vj_series2(const VjSer& c, float2 x2, float2& Gt
   ix2 = y2;
 }
 
-// far: every staged point of the CTA is at or beyond the subhalo's series
+// far: every staged point of the CTA is at or beyond the gradient's series
 // radius (tNFW only), so the series serves every pair without a test.
 template <int PROFILE>
 __device__ __forceinline__ void vj_sweep(const SubRec& rec, float2 ex, const VjSer& ser, bool far,
@@ -243,11 +253,11 @@ __device__ __forceinline__ void vj_sweep(const SubRec& rec, float2 ex, const VjS
 }
 
 // Whether every point in the box (x_lo, y_lo, x_hi, y_hi) is at or beyond the
-// subhalo's series radius: x^2 of the box's nearest point reaches xT2.
+// gradient's series radius: x^2 of the box's nearest point reaches it.
 __device__ __forceinline__ bool vj_far(const SubRec& h, const SubSer& q, const float* box) {
   const float dx = fmaxf(fmaxf(box[0] - h.xh, h.xh - box[2]), 0.f);
   const float dy = fmaxf(fmaxf(box[1] - h.yh, h.yh - box[3]), 0.f);
-  return __fmul_rn(fmaf(dx, dx, dy * dy), h.its2) >= q.xT2;
+  return __fmul_rn(fmaf(dx, dx, dy * dy), h.its2) >= vj_radius2(h, q);
 }
 
 // The CTA's prologue for a tNFW sum: the bounds of its points [p0, p1), then
