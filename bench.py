@@ -118,6 +118,8 @@ def vjp_series_fraction(p, nblk: int) -> float:
 def vjp_blocks(dev) -> int:
     """CTAs of the ray-trace backward at 4 resident per SM (128 registers and
     41 KB of shared memory each), one per 128 points at most."""
+    import torch
+
     return 4 * torch.cuda.get_device_properties(dev).multi_processor_count
 
 
