@@ -41,17 +41,17 @@ SM_MAX_MHZ_DEFAULT = 2070.0
 # and x^2, 22 for the shared far terms (arctan polynomial 12; the record's
 # (tau^2-1)/tau carries the ln(2)/2 of the log), 7 for the mass bracket, 2 to
 # accumulate both components, 1.25 for the Kahan fold after every 8
-# subhalos; MUFU: 2 rsqrt, 1 rcp, 1 lg2. Forward, far-field series
-# (x >= 6 max(tau, 2)): 2 + 3, 1 for y^2, 7 + 1 for the Horner steps, 2 for
-# m = A y^2 Q, 2 + 1.25 to accumulate and fold; MUFU: 1 rsqrt. Backward,
-# subhalos near the CTA's points (far-side closed form): 5 + 22, 12 for the G
-# and H brackets, 11 for the four subhalo sums (their constant factors,
-# 1/theta_s^2 of the q terms included, applied once per fold or slot), 0.6
-# for the Kahan folds; 4 MUFU. Backward, subhalos whose gradient series
-# radius (x >= 8 max(tau, 2)) clears every point of the CTA (far-field series
-# of G and of x dG/dx to y^7): 5, 1 for y^2, 5 + 5 for the two Horner
-# chains, 2 + 2 for G and x dG/dx, 10 for the four sums, 0.6 for the folds;
-# 1 MUFU.
+# subhalos; MUFU: 2 rsqrt, 1 rcp, 1 lg2. Forward, far-field series to y^K
+# (a subhalo whose series radius clears the CTA's whole tile): 2 + 3, 1 for
+# y^2, K - 2 + 1 for the Horner steps, 2 for m = A y^2 Q, 2 to accumulate
+# and 0.31 for the Kahan fold after every 32 subhalos; MUFU: 1 rsqrt.
+# Backward, subhalos near the tile's points (far-side closed form): 5 + 22,
+# 12 for the G and H brackets, 11 for the four subhalo sums (their constant
+# factors, 1/theta_s^2 of the q terms included, applied once per fold or
+# slot), 0.3 for the Kahan folds; 4 MUFU. Backward, subhalos whose gradient
+# series radius clears every point of the tile (far-field series of G and of
+# x dG/dx to y^K): 5, 1 for y^2, 2 (K - 2) for the two Horner chains, 2 + 2
+# for G and x dG/dx, 10 for the four sums, 0.3 for the folds; 1 MUFU.
 # Culled reductions over explicit points (the self-kernel), per evaluated
 # pair: forward 2 differences, the squared distance (2), the scale (1) and
 # the accumulation (1); self-kernel backward the same 6 before the
@@ -60,67 +60,126 @@ SM_MAX_MHZ_DEFAULT = 2070.0
 CULL_FWD_MUFU, CULL_FWD_LANES = 1, 6.0
 CULL_SELF_MUFU, CULL_SELF_LANES = 1, 14.0
 RT_MUFU, RT_LANES = 4, 37.3
-RT_SER_MUFU, RT_SER_LANES = 1, 19.25
-VJ_MUFU, VJ_LANES = 4, 50.6
-VJ_SER_MUFU, VJ_SER_LANES = 1, 30.6
+VJ_MUFU, VJ_LANES = 4, 50.3
+SER_MUFU = 1
+# series degrees K and the x^2 / max(tau^2, 4) from which each serves a
+# whole CTA (fewest terms first)
+RT_DEGREES = ((3, 6400.0), (4, 1024.0), (5, 324.0), (7, 64.0), (9, 36.0))
+VJ_DEGREES = ((3, 6400.0), (4, 1024.0), (5, 324.0), (7, 64.0))
 
 
-def series_fraction(p) -> float:
-    """Fraction of the workload's point-subhalo pairs in the far-field series
-    regime (x^2 >= 36 max(tau^2, 4)), over every 4th pixel row and column."""
-    g = p.xgrid
-    w = g.nx * g.ss
-    h = g.pix / g.ss
-    xs = ((np.arange(w) - (w - 1) / 2) * h + g.cx)[::4]
-    ys = ((np.arange(g.ny * g.ss) - (g.ny * g.ss - 1) / 2) * h + g.cy)[::4]
-    X, Y = np.meshgrid(xs, ys)
-    pts = np.stack([X.ravel(), Y.ravel()], 1)
-    sub = p.sub.astype(np.float64)
-    its2 = 1.0 / sub[:, 3] ** 2
-    xT2 = 36.0 * np.maximum(sub[:, 4] ** 2, 4.0)
-    far = 0
-    for c in range(0, len(pts), 4096):
-        d = pts[c:c + 4096, None, :] - sub[None, :, :2]
-        far += int(np.count_nonzero((d ** 2).sum(-1) * its2 >= xT2))
-    return far / (len(pts) * len(sub))
+def rt_ser_lanes(k: int) -> float:
+    return 9.31 + k
 
 
-def vjp_series_fraction(p, nblk: int) -> float:
-    """Fraction of the point-subhalo pairs that the ray-trace backward sums by
-    the far-field series: CTA b of nblk takes the points [b n / nblk,
-    (b + 1) n / nblk) in row-major order, and a subhalo takes the series for
-    all of them when the bounding box of those points is beyond its gradient
-    series radius (x^2 >= 64 max(tau^2, 4))."""
-    g = p.xgrid
+def vj_ser_lanes(k: int) -> float:
+    return 20.3 + 2 * (k - 2)
+
+
+def _grid_axes(g):
     w, hgt = g.nx * g.ss, g.ny * g.ss
     h = g.pix / g.ss
     xs = (np.arange(w) - (w - 1) / 2) * h + g.cx
     ys = (np.arange(hgt) - (hgt - 1) / 2) * h + g.cy
-    n = w * hgt
-    b = np.arange(nblk, dtype=np.int64)
-    p0, p1 = b * n // nblk, (b + 1) * n // nblk
-    cnt = p1 - p0
-    r0, r1 = p0 // w, np.maximum(p1 - 1, p0) // w
-    c0, c1 = p0 % w, np.maximum(p1 - 1, p0) % w
-    one = r0 == r1
-    xlo = np.where(one, xs[c0], xs[0])
-    xhi = np.where(one, xs[c1], xs[-1])
-    ylo, yhi = ys[r0], ys[r1]
+    return w, hgt, xs, ys
+
+
+def _degree_shares(p, boxes, counts, degrees) -> dict:
+    """Share of the point-subhalo pairs by the series degree that serves a
+    CTA's whole box (x_lo, y_lo, x_hi, y_hi) of `counts` points; 0: the
+    closed forms."""
     sub = p.sub.astype(np.float64)
     its2 = 1.0 / sub[:, 3] ** 2
-    xT2 = 64.0 * np.maximum(sub[:, 4] ** 2, 4.0)
-    dx = np.maximum(np.maximum(xlo[:, None] - sub[None, :, 0], sub[None, :, 0] - xhi[:, None]), 0.0)
-    dy = np.maximum(np.maximum(ylo[:, None] - sub[None, :, 1], sub[None, :, 1] - yhi[:, None]), 0.0)
-    far = (dx * dx + dy * dy) * its2[None, :] >= xT2[None, :]
-    return float((far.sum(1) * cnt).sum()) / float(n * len(sub))
+    m = np.maximum(sub[:, 4] ** 2, 4.0)
+    tot = {k: 0.0 for k, _ in degrees}
+    tot[0] = 0.0
+    for c in range(0, len(boxes), 1024):
+        bx, cn = boxes[c:c + 1024], counts[c:c + 1024].astype(np.float64)
+        dx = np.maximum(np.maximum(bx[:, 0, None] - sub[None, :, 0], sub[None, :, 0] - bx[:, 2, None]), 0.0)
+        dy = np.maximum(np.maximum(bx[:, 1, None] - sub[None, :, 1], sub[None, :, 1] - bx[:, 3, None]), 0.0)
+        x2 = (dx * dx + dy * dy) * its2[None, :] / m[None, :]
+        left = np.ones(x2.shape, dtype=bool)
+        for k, r2 in degrees:
+            hit = left & (x2 >= r2)
+            tot[k] += float((hit.sum(1) * cn).sum())
+            left &= ~hit
+        tot[0] += float((left.sum(1) * cn).sum())
+    n = float(counts.sum()) * len(sub)
+    return {k: v / n for k, v in tot.items()}
 
 
-def vjp_blocks(dev) -> int:
-    """CTAs of the ray-trace backward at 4 resident per SM (128 registers and
-    41 KB of shared memory each), one per 128 points at most."""
+def raytrace_cost(p):
+    """(MUFU, FP32 lanes) per point-subhalo pair of the forward ray-trace on
+    a pixel grid, and the pairs' shares by series degree: a CTA takes a
+    16 x 16 tile of pixels, a subhalo takes the series of the degree that
+    serves the whole tile, the others the far-side closed form."""
+    w, hgt, xs, ys = _grid_axes(p.xgrid)
+    tw, th = (w + 15) // 16, (hgt + 15) // 16
+    ty, tx = np.divmod(np.arange(tw * th), tw)
+    r0, c0 = ty * 16, tx * 16
+    r1, c1 = np.minimum(r0 + 16, hgt) - 1, np.minimum(c0 + 16, w) - 1
+    boxes = np.stack([xs[c0], ys[r0], xs[c1], ys[r1]], 1)
+    sh = _degree_shares(p, boxes, (r1 - r0 + 1) * (c1 - c0 + 1), RT_DEGREES)
+    mufu = sh[0] * RT_MUFU + (1 - sh[0]) * SER_MUFU
+    lanes = sh[0] * RT_LANES + sum(sh[k] * rt_ser_lanes(k) for k, _ in RT_DEGREES)
+    return mufu, lanes, sh
+
+
+def vjp_bands(nblk: int, w: int, hgt: int) -> int:
+    """Bands of image rows of the ray-trace backward's CTA tiles: the divisor
+    R of nblk whose tiles are closest to square, preferring equal bands."""
+    best, best_s = 1, float("inf")
+    for r in range(1, min(nblk, hgt) + 1):
+        if nblk % r:
+            continue
+        th, tw = hgt / r, w * r / nblk
+        sc = abs(float(np.log(th / tw))) + 2.0 * (((hgt + r - 1) // r) / th - 1.0)
+        if sc < best_s:
+            best, best_s = r, sc
+    return best
+
+
+def vjp_cost(p, nblk: int):
+    """(MUFU, FP32 lanes) per point-subhalo pair of the ray-trace backward on
+    a pixel grid, and the pairs' shares by series degree: nblk tiles (bands
+    of rows, each band's points split in column-major order), a subhalo takes
+    the gradient series of the degree that serves the whole tile's bounding
+    box, the others the far-side closed form."""
+    w, hgt, xs, ys = _grid_axes(p.xgrid)
+    bands = vjp_bands(nblk, w, hgt)
+    per = nblk // bands
+    b, c = np.divmod(np.arange(nblk, dtype=np.int64), per)
+    row0 = b * hgt // bands
+    rows = (b + 1) * hgt // bands - row0
+    nb = rows * w
+    u0, u1 = c * nb // per, (c + 1) * nb // per
+    col0, col1 = u0 // rows, (u1 - 1) // rows
+    one = col0 == col1
+    rlo = np.where(one, u0 % rows, 0)
+    rhi = np.where(one, (u1 - 1) % rows, rows - 1)
+    boxes = np.stack([xs[col0], ys[row0 + rlo], xs[col1], ys[row0 + rhi]], 1)
+    sh = _degree_shares(p, boxes, u1 - u0, VJ_DEGREES)
+    mufu = sh[0] * VJ_MUFU + (1 - sh[0]) * SER_MUFU
+    lanes = sh[0] * VJ_LANES + sum(sh[k] * vj_ser_lanes(k) for k, _ in VJ_DEGREES)
+    return mufu, lanes, sh
+
+
+def _shares_text(sh: dict) -> str:
+    return ", ".join(f"y^{k}: {v:.3f}" for k, v in sh.items() if k) + f"; closed form: {sh[0]:.3f}"
+
+
+def vjp_tiles(dev, n: int) -> int:
+    """Tiles (CTAs) of the ray-trace backward for n points, with 4 CTAs
+    resident per SM (128 registers and 45 KB of shared memory each): one per
+    128 points below a full wave, above it whole waves (at most 8) of tiles
+    of at least 512 points."""
     import torch
 
-    return 4 * torch.cuda.get_device_properties(dev).multi_processor_count
+    slots = 4 * torch.cuda.get_device_properties(dev).multi_processor_count
+    nb = (n + 127) // 128
+    if nb < slots:
+        return nb
+    return min(max(n // (slots * 512), 1), 8) * slots
 
 
 def parse():
@@ -784,22 +843,19 @@ def run_realistic(args, dev, rates, clk) -> dict:
     # the ray-trace kernels' unit is the point-subhalo pair; counts are those
     # of the far-side tNFW form that nearly every pair takes
     sub_pairs = p.n * len(p.sub)
-    fs = series_fraction(p)
-    rt_mufu = fs * RT_SER_MUFU + (1 - fs) * RT_MUFU
-    rt_lanes = fs * RT_SER_LANES + (1 - fs) * RT_LANES
+    rt_mufu, rt_lanes, rt_sh = raytrace_cost(p)
     kern["raytrace_kernel<tNFW> (forward ray-trace; unit: point-subhalo pair)"] = (
         rt_ms, rt_call_ms, sub_pairs, rt_mufu, rt_lanes,
-        f"pairs: {rt_mufu:.2f} MUFU + {rt_lanes:.1f} FP32 lanes each on average: {fs:.3f} of the pairs in the "
-        f"far-field series regime ({RT_SER_MUFU} MUFU + {RT_SER_LANES} lanes), the rest the far-side closed form "
-        f"({RT_MUFU} MUFU + {RT_LANES} lanes); the SPLE and shear terms, once per point, are not counted", True)
-    fv = vjp_series_fraction(p, min(vjp_blocks(dev), (p.n + 127) // 128))
-    vj_mufu = fv * VJ_SER_MUFU + (1 - fv) * VJ_MUFU
-    vj_lanes = fv * VJ_SER_LANES + (1 - fv) * VJ_LANES
+        f"pairs: {rt_mufu:.2f} MUFU + {rt_lanes:.1f} FP32 lanes each on average; shares of the pairs by the "
+        f"far-field series degree that serves the CTA's tile ({SER_MUFU} MUFU + 9.31 + K lanes) and the far-side "
+        f"closed form ({RT_MUFU} MUFU + {RT_LANES} lanes): {_shares_text(rt_sh)}; the SPLE and shear terms, once "
+        "per point, are not counted", True)
+    vj_mufu, vj_lanes, vj_sh = vjp_cost(p, vjp_tiles(dev, p.n))
     kern["raytrace_vjp_kernel<tNFW> (ray-trace backward; unit: point-subhalo pair)"] = (
         vjp_ms, vjp_call_ms, sub_pairs, vj_mufu, vj_lanes,
-        f"pairs: {vj_mufu:.2f} MUFU + {vj_lanes:.1f} FP32 lanes each on average: {fv:.3f} of the pairs from "
-        f"subhalos whose series radius clears the CTA's points (far-field series, {VJ_SER_MUFU} MUFU + "
-        f"{VJ_SER_LANES} lanes), the rest the far-side closed form ({VJ_MUFU} MUFU + {VJ_LANES} lanes); the "
+        f"pairs: {vj_mufu:.2f} MUFU + {vj_lanes:.1f} FP32 lanes each on average; shares of the pairs by the "
+        f"degree of the series of G and x dG/dx that serves the CTA's tile ({SER_MUFU} MUFU + 20.3 + 2 (K - 2) "
+        f"lanes) and the far-side closed form ({VJ_MUFU} MUFU + {VJ_LANES} lanes): {_shares_text(vj_sh)}; the "
         "per-point SPLE and shear gradient terms are not counted", True)
 
     # ---- end to end through the public API with host buffers
@@ -913,7 +969,7 @@ def run_realistic(args, dev, rates, clk) -> dict:
                      "note": "ALU/XU-bound with subhalos (8 B written per point)"},
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "ms_per_step": e_ms, "ms_per_step_direct_launches": e_direct_ms},
-        "gpu_launches_per_step": 11,
+        "gpu_launches_per_step": 13,
     }
 
 
@@ -1057,22 +1113,18 @@ def run_large(args, rank, local, world, dist, dev):
     rt_ms, rt_call_ms = kernel_time(lambda: api.lens_raytrace(q), nk, stream, flush, "raytrace")
     vjp_ms, vjp_call_ms = kernel_time(lambda: api.lens_raytrace_vjp(q, dbeta), nk, stream, flush, "raytrace_vjp")
     sub_pairs = p.n * len(p.sub)
-    fs = series_fraction(p)
-    rt_mufu = fs * RT_SER_MUFU + (1 - fs) * RT_MUFU
-    rt_lanes = fs * RT_SER_LANES + (1 - fs) * RT_LANES
+    rt_mufu, rt_lanes, rt_sh = raytrace_cost(p)
     kern["raytrace_kernel<tNFW> (forward ray-trace; unit: point-subhalo pair)"] = (
         rt_ms, rt_call_ms, sub_pairs, rt_mufu, rt_lanes,
-        f"pairs: {rt_mufu:.2f} MUFU + {rt_lanes:.1f} FP32 lanes each on average: {fs:.3f} of the pairs in the "
-        f"far-field series regime ({RT_SER_MUFU} MUFU + {RT_SER_LANES} lanes), the rest the far-side closed form "
-        f"({RT_MUFU} MUFU + {RT_LANES} lanes)", True)
-    fv = vjp_series_fraction(p, min(vjp_blocks(dev), (p.n + 127) // 128))
-    vj_mufu = fv * VJ_SER_MUFU + (1 - fv) * VJ_MUFU
-    vj_lanes = fv * VJ_SER_LANES + (1 - fv) * VJ_LANES
+        f"pairs: {rt_mufu:.2f} MUFU + {rt_lanes:.1f} FP32 lanes each on average; shares of the pairs by the "
+        f"far-field series degree that serves the CTA's tile ({SER_MUFU} MUFU + 9.31 + K lanes) and the far-side "
+        f"closed form ({RT_MUFU} MUFU + {RT_LANES} lanes): {_shares_text(rt_sh)}", True)
+    vj_mufu, vj_lanes, vj_sh = vjp_cost(p, vjp_tiles(dev, p.n))
     kern["raytrace_vjp_kernel<tNFW> (ray-trace backward; unit: point-subhalo pair)"] = (
         vjp_ms, vjp_call_ms, sub_pairs, vj_mufu, vj_lanes,
-        f"pairs: {vj_mufu:.2f} MUFU + {vj_lanes:.1f} FP32 lanes each on average: {fv:.3f} of the pairs from "
-        f"subhalos whose series radius clears the CTA's points (far-field series of G and x dG/dx, {VJ_SER_MUFU} "
-        f"MUFU + {VJ_SER_LANES} lanes), the rest the far-side closed form ({VJ_MUFU} MUFU + {VJ_LANES} lanes)", True)
+        f"pairs: {vj_mufu:.2f} MUFU + {vj_lanes:.1f} FP32 lanes each on average; shares of the pairs by the "
+        f"degree of the series of G and x dG/dx that serves the CTA's tile ({SER_MUFU} MUFU + 20.3 + 2 (K - 2) "
+        f"lanes) and the far-side closed form ({VJ_MUFU} MUFU + {VJ_LANES} lanes): {_shares_text(vj_sh)}", True)
 
     # ---- end to end through the public API with host buffers
     v_host = torch.from_numpy(p.v).pin_memory()
@@ -1197,7 +1249,7 @@ def run_large(args, rank, local, world, dist, dev):
 # Kernels of one headline step: forward = ray-trace, chunk prepare, group
 # boxes, culled sweep; backward = chunk prepare, group boxes, culled sweep,
 # scalar sum, ray-trace VJP and its final sums.
-LARGE_STEP_LAUNCHES = 10
+LARGE_STEP_LAUNCHES = 12
 
 
 def run_ours(args):

@@ -178,6 +178,7 @@ struct VjpP {
   const float* sub;
   int32_t n_sub, profile;
   int32_t phases;  // slots per subhalo (see vjp_phases)
+  int32_t bands;   // grid points: bands of image rows of the CTAs' tiles (see vjp_bands)
   const float2* dbeta;
   double* lens_part;
   float* sub_part;   // [4 n_sub][CTA]

@@ -26,7 +26,8 @@ __global__ void grid_points_kernel(GridDev g, int64_t n, float2* out) {
   if (i < n) out[i] = grid_point(g, i);
 }
 
-constexpr int kRtFold = 8;  // subhalos summed plainly before a Kahan fold
+constexpr int kRtFold = 8;        // subhalos summed plainly before a Kahan fold (closed forms)
+constexpr int kRtFoldPairs = 16;  // staged pairs summed plainly before a Kahan fold (series runs)
 
 __device__ __forceinline__ void kahan(float& s, float& c, float x) {
   const float y = __fsub_rn(x, c);
@@ -46,7 +47,9 @@ struct RtSmem {
   float4 hot[kSubChunk / 2][kRtHot];
   float4 cold[kSubChunk / 2][kRtCold];
   int order[kSubChunk];  // staged position -> subhalo of the chunk
-  unsigned char far[kSubChunk];
+  unsigned char deg[kSubChunk];  // series degree for the CTA's points of each subhalo of the chunk (0: none)
+  int ndeg[5];                   // staged subhalos served by the series to y^3, y^4, y^5, y^7, y^9
+  int wcnt[kRtThreads / 32][6];  // per warp's quarter of the chunk: subhalos by degree class
   float box[4];          // the CTA's points: x_lo, y_lo, x_hi, y_hi
   int nfar;
   uint64_t bar;
@@ -81,10 +84,28 @@ __device__ __forceinline__ SubSer ser_from(const float4* hot, int k) {
   return s;
 }
 
+// The degree K of the deflection's far-field series (prep_series) that
+// serves every pair of a subhalo with points at x^2 >= x2min, with m =
+// max(tau^2, 4): the terms up to y^K from x = r_K max(tau, 2) on, K = 9 from
+// r = 6, 7 from 8, 5 from 18, 4 from 32, 3 from 80 (the truncated terms fall
+// as (tau / x)^(K + 1); against the closed form in extended precision within
+// 5e-10 relative for K = 9 and 1.4e-8 for the others, tau in [0.5, 30]).
+// 0 below 6 max(tau, 2).
+__device__ __forceinline__ int rt_degree(float x2min, float m) {
+  return x2min >= 6400.0f * m   ? 3
+         : x2min >= 1024.0f * m ? 4
+         : x2min >= 324.0f * m  ? 5
+         : x2min >= 64.0f * m   ? 7
+         : x2min >= 36.0f * m   ? 9
+                                : 0;
+}
+
 // Stages subhalos [h0, h0 + cnt). Subhalos whose centre is beyond the series
 // radius from the whole box of the CTA's points (every pair of them takes the
-// series) come first, each class in index order; sm.nfar counts them.
-// Returns false (all threads) if the bulk-copy wait timed out.
+// series) come first, ordered by the degree that serves the whole box
+// (rt_degree, fewest terms first), each degree in index order; sm.ndeg
+// counts them by degree and sm.nfar in all. Returns false (all threads) if
+// the bulk-copy wait timed out.
 __device__ __forceinline__ bool stage_rt(const float* __restrict__ sub, int h0, int cnt, int profile, RtSmem& sm,
                                          uint32_t& phase, bool bulk_ok, int* fault) {
   if (!stage_raw(sub, h0, cnt, sm.raw, &sm.bar, phase, bulk_ok, fault)) return false;
@@ -93,26 +114,46 @@ __device__ __forceinline__ bool stage_rt(const float* __restrict__ sub, int h0, 
     const SubSer q = prep_series(h, profile);
     const float dx = fmaxf(fmaxf(sm.box[0] - h.xh, h.xh - sm.box[2]), 0.f);
     const float dy = fmaxf(fmaxf(sm.box[1] - h.yh, h.yh - sm.box[3]), 0.f);
-    sm.far[t] = __fmul_rn(fmaf(dx, dx, dy * dy), h.its2) >= q.xT2 ? 1 : 0;
+    sm.deg[t] = isinf(q.xT2) ? 0
+                             : (unsigned char)rt_degree(__fmul_rn(fmaf(dx, dx, dy * dy), h.its2), fmaxf(h.tau2, 4.0f));
   }
   __syncthreads();
-  if (threadIdx.x < 32) {  // stable partition: far first
-    const int lane = threadIdx.x;
-    int nf = 0;
-    for (int b = 0; b < cnt; b += 32) {
-      const bool f = b + lane < cnt && sm.far[b + lane];
-      const unsigned m = __ballot_sync(0xffffffffu, f);
-      if (f) sm.order[nf + __popc(m & ((1u << lane) - 1u))] = b + lane;
-      nf += __popc(m);
+  // stable partition by degree class: 3, 4, 5, 7, 9, then 0 (not far). Warp
+  // w takes the chunk's positions [w q, (w + 1) q), q = kSubChunk / warps:
+  // it counts its subhalos per class, then scatters them after the classes
+  // before theirs and the warps before it.
+  constexpr int kW = kRtThreads / 32, kQ = kSubChunk / kW;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll 1
+  for (int pass = 0; pass < 6; ++pass) {
+    const int want = pass == 5 ? 0 : (pass < 3 ? 3 + pass : 2 * pass + 1);
+    int nc = 0;
+    for (int b = warp * kQ; b < (warp + 1) * kQ; b += 32)
+      nc += __popc(__ballot_sync(0xffffffffu, b + lane < cnt && sm.deg[b + lane] == want));
+    if (lane == 0) sm.wcnt[warp][pass] = nc;
+  }
+  __syncthreads();
+  int nf = 0;  // this warp's first position of the class
+#pragma unroll 1
+  for (int pass = 0; pass < 6; ++pass) {
+    const int want = pass == 5 ? 0 : (pass < 3 ? 3 + pass : 2 * pass + 1);
+    int tot = 0, before = 0;
+    for (int w = 0; w < kW; ++w) {
+      tot += sm.wcnt[w][pass];
+      if (w < warp) before += sm.wcnt[w][pass];
     }
-    int nn = nf;
-    for (int b = 0; b < cnt; b += 32) {
-      const bool f = b + lane < cnt && !sm.far[b + lane];
-      const unsigned m = __ballot_sync(0xffffffffu, f);
-      if (f) sm.order[nn + __popc(m & ((1u << lane) - 1u))] = b + lane;
-      nn += __popc(m);
+    if (threadIdx.x == 0) {
+      if (pass < 5) sm.ndeg[pass] = tot;
+      if (pass == 5) sm.nfar = nf;  // thread 0 is in warp 0: nf is the count of all far classes
     }
-    if (lane == 0) sm.nfar = nf;
+    int pos = nf + before;
+    for (int b = warp * kQ; b < (warp + 1) * kQ; b += 32) {
+      const bool f = b + lane < cnt && sm.deg[b + lane] == want;
+      const unsigned m = __ballot_sync(0xffffffffu, f);
+      if (f) sm.order[pos + __popc(m & ((1u << lane) - 1u))] = b + lane;
+      pos += __popc(m);
+    }
+    nf += tot;
   }
   __syncthreads();
   for (int k = threadIdx.x; 2 * k < cnt; k += blockDim.x) {
@@ -134,12 +175,114 @@ __device__ __forceinline__ bool stage_rt(const float* __restrict__ sub, int h0, 
   return true;
 }
 
+// m = A y^2 Q(y) of two subhalos (or one twice) by the series to y^K: q[j]
+// for j = 2 .. K (explicitly rounded; K = 9 is tnfw_m_series2).
+template <int K>
+__device__ __forceinline__ float2 rt_series2(float2 A, float2 q0, const float2* q, float2 x2) {
+  const float2 y = frsqrt2(x2), y2 = __fmul2_rn(y, y);
+  float2 p = q[K];
+#pragma unroll
+  for (int j = K - 1; j >= 2; --j) p = __ffma2_rn(p, y, q[j]);
+  return __fmul2_rn(A, __fmul2_rn(y2, __ffma2_rn(p, y2, q0)));
+}
+
+// The series coefficients q[2 .. K] of a staged pair.
+template <int K>
+__device__ __forceinline__ void rt_coeffs(const float4* hot, float2 (&q)[kSerTerms]) {
+#pragma unroll
+  for (int j = 2; j <= K; ++j) {
+    const float4 c = hot[3 + (j - 2) / 2];
+    q[j] = (j & 1) ? hi2(c) : lo2(c);
+  }
+}
+
+// Staged pairs kp and kp + 1 (four subhalos, all far from every point of the
+// CTA) by the series to y^K: four independent chains per thread, added in
+// order.
+template <int K>
+__device__ __forceinline__ void rt_far4(const RtSmem& sm, int kp, const float2 (&X)[kRtPts],
+                                        const float2 (&Y)[kRtPts], float2 (&ax)[kRtPts], float2 (&ay)[kRtPts]) {
+  float2 m[2][kRtPts], dxs[2][kRtPts], dys[2][kRtPts];
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {
+    const float4* hot = sm.hot[kp + u];
+    const float4 w0 = hot[0], w1 = hot[1], w2 = hot[2];
+    float2 q[kSerTerms];
+    rt_coeffs<K>(hot, q);
+#pragma unroll
+    for (int j = 0; j < kRtPts; ++j) {
+      dxs[u][j] = sub2(X[j], make_float2(w0.x, w0.y));
+      dys[u][j] = sub2(Y[j], make_float2(w0.z, w0.w));
+      const float2 R2 = __ffma2_rn(dxs[u][j], dxs[u][j], __fmul2_rn(dys[u][j], dys[u][j]));
+      m[u][j] = rt_series2<K>(hi2(w1), hi2(w2), q, __fmul2_rn(R2, lo2(w1)));
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {
+#pragma unroll
+    for (int j = 0; j < kRtPts; ++j) {
+      ax[j] = __ffma2_rn(m[u][j], dxs[u][j], ax[j]);
+      ay[j] = __ffma2_rn(m[u][j], dys[u][j], ay[j]);
+    }
+  }
+}
+
+// Staged pair kp (both subhalos far from every point of the CTA) by the
+// series to y^K.
+template <int K>
+__device__ __forceinline__ void rt_far2(const RtSmem& sm, int kp, const float2 (&X)[kRtPts],
+                                        const float2 (&Y)[kRtPts], float2 (&ax)[kRtPts], float2 (&ay)[kRtPts]) {
+  const float4* hot = sm.hot[kp];
+  const float4 w0 = hot[0], w1 = hot[1], w2 = hot[2];
+  float2 q[kSerTerms];
+  rt_coeffs<K>(hot, q);
+#pragma unroll
+  for (int j = 0; j < kRtPts; ++j) {
+    const float2 dx = sub2(X[j], make_float2(w0.x, w0.y)), dy = sub2(Y[j], make_float2(w0.z, w0.w));
+    const float2 R2 = __ffma2_rn(dx, dx, __fmul2_rn(dy, dy));
+    const float2 m = rt_series2<K>(hi2(w1), hi2(w2), q, __fmul2_rn(R2, lo2(w1)));
+    ax[j] = __ffma2_rn(m, dx, ax[j]);
+    ay[j] = __ffma2_rn(m, dy, ay[j]);
+  }
+}
+
+__device__ __forceinline__ void fold(const float2 (&ax)[kRtPts], const float2 (&ay)[kRtPts], float (&sx)[kRtPts],
+                                     float (&cx)[kRtPts], float (&sy)[kRtPts], float (&cy)[kRtPts]) {
+#pragma unroll
+  for (int j = 0; j < kRtPts; ++j) {
+    kahan(sx[j], cx[j], __fadd_rn(ax[j].x, ax[j].y));
+    kahan(sy[j], cy[j], __fadd_rn(ay[j].x, ay[j].y));
+  }
+}
+
+// Staged pairs [ka, kb), every subhalo of them far from the whole CTA and
+// served by the series to y^K (a pair that straddles two degrees takes the
+// larger): two pairs per step, kRtFoldPairs pairs summed plainly per fold.
+template <int K>
+__device__ __forceinline__ void rt_far_run(const RtSmem& sm, int ka, int kb, const float2 (&X)[kRtPts],
+                                           const float2 (&Y)[kRtPts], float (&sx)[kRtPts], float (&cx)[kRtPts],
+                                           float (&sy)[kRtPts], float (&cy)[kRtPts]) {
+  for (int k = ka; k < kb;) {
+    const int kend = min(kb, k + kRtFoldPairs);
+    float2 ax[kRtPts], ay[kRtPts];
+#pragma unroll
+    for (int j = 0; j < kRtPts; ++j) ax[j] = ay[j] = f2(0.f);
+    for (; k + 1 < kend; k += 2) rt_far4<K>(sm, k, X, Y, ax, ay);
+    if (k < kend) {
+      rt_far2<K>(sm, k, X, Y, ax, ay);
+      ++k;
+    }
+    fold(ax, ay, sx, cx, sy, cy);
+  }
+}
+
 // Deflection of the staged subhalos at the thread's kRtPts points (x[j],
-// y[j]), added to the Kahan sums (sx, cx), (sy, cy) of each point. Blocks of
-// kRtFold subhalos are summed plainly in two packed lanes and folded into the
-// Kahan sums; the order is fixed, so a point's bits do not depend on the
-// other points of its thread. Each staged record is read once for all of
-// the thread's points.
+// y[j]), added to the Kahan sums (sx, cx), (sy, cy) of each point. The
+// subhalos far from the whole CTA come first, in runs of one series degree
+// (rt_far_run); the rest in blocks of kRtFold subhalos. Each block is summed
+// plainly in two packed lanes and folded into the Kahan sums; the order is
+// fixed, so a point's bits do not depend on the other points of its thread.
+// Each staged record is read once for all of the thread's points.
 template <int PROFILE>
 __device__ __forceinline__ void add_subs(const RtSmem& sm, int cnt, const float (&x)[kRtPts],
                                          const float (&y)[kRtPts], float (&sx)[kRtPts], float (&cx)[kRtPts],
@@ -150,67 +293,39 @@ __device__ __forceinline__ void add_subs(const RtSmem& sm, int cnt, const float 
     X[j] = f2(x[j]);
     Y[j] = f2(y[j]);
   }
-  const int nfe = sm.nfar & ~1;  // pairs below nfe: both subhalos are far from every point of the CTA
-  for (int t0 = 0; t0 < cnt; t0 += kRtFold) {
+  int tfar = 0;  // staged subhalos [0, tfar): pairs far from every point of the CTA
+  if (PROFILE == LR_PROFILE_TNFW) {
+    // the run of pairs whose larger degree is K: [c_{<K} / 2, c_{<=K} / 2)
+    // with c the staged counts by degree (both rounded down)
+    int c = 0;
+#pragma unroll
+    for (int di = 0; di < 5; ++di) {
+      const int ka = c >> 1;
+      c += sm.ndeg[di];
+      const int kb = c >> 1;
+      if (kb > ka) {
+        if (di == 0) rt_far_run<3>(sm, ka, kb, X, Y, sx, cx, sy, cy);
+        if (di == 1) rt_far_run<4>(sm, ka, kb, X, Y, sx, cx, sy, cy);
+        if (di == 2) rt_far_run<5>(sm, ka, kb, X, Y, sx, cx, sy, cy);
+        if (di == 3) rt_far_run<7>(sm, ka, kb, X, Y, sx, cx, sy, cy);
+        if (di == 4) rt_far_run<9>(sm, ka, kb, X, Y, sx, cx, sy, cy);
+      }
+    }
+    tfar = c & ~1;
+  }
+  for (int t0 = tfar; t0 < cnt; t0 += kRtFold) {
     const int t1 = min(cnt, t0 + kRtFold);
     float2 ax[kRtPts], ay[kRtPts];
 #pragma unroll
     for (int j = 0; j < kRtPts; ++j) ax[j] = ay[j] = f2(0.f);
     int t = t0;
     if (PROFILE == LR_PROFILE_TNFW) {
-      // two subhalo pairs at a time while all four are far from the whole
-      // CTA: four independent series chains per thread, added in order
-      for (; t + 3 < t1 && t + 3 < nfe; t += 4) {
-        float2 m[2][kRtPts], dxs[2][kRtPts], dys[2][kRtPts];
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
-          const float4* hot = sm.hot[(t >> 1) + u];
+      for (; t + 1 < t1; t += 2) {
+        {
+          const float4* hot = sm.hot[t >> 1];
           const float4 w0 = hot[0], w1 = hot[1], w2 = hot[2];
           float2 q[kSerTerms];
-#pragma unroll
-          for (int w = 0; w < 4; ++w) {
-            const float4 c = hot[3 + w];
-            q[2 + 2 * w] = lo2(c);
-            q[3 + 2 * w] = hi2(c);
-          }
-#pragma unroll
-          for (int j = 0; j < kRtPts; ++j) {
-            dxs[u][j] = sub2(X[j], make_float2(w0.x, w0.y));
-            dys[u][j] = sub2(Y[j], make_float2(w0.z, w0.w));
-            const float2 R2 = __ffma2_rn(dxs[u][j], dxs[u][j], __fmul2_rn(dys[u][j], dys[u][j]));
-            m[u][j] = tnfw_m_series2(hi2(w1), hi2(w2), q, __fmul2_rn(R2, lo2(w1)));
-          }
-        }
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
-#pragma unroll
-          for (int j = 0; j < kRtPts; ++j) {
-            ax[j] = __ffma2_rn(m[u][j], dxs[u][j], ax[j]);
-            ay[j] = __ffma2_rn(m[u][j], dys[u][j], ay[j]);
-          }
-        }
-      }
-      for (; t + 1 < t1; t += 2) {
-        const float4* hot = sm.hot[t >> 1];
-        const float4 w0 = hot[0], w1 = hot[1], w2 = hot[2];
-        float2 q[kSerTerms];
-#pragma unroll
-        for (int w = 0; w < 4; ++w) {
-          const float4 c = hot[3 + w];
-          q[2 + 2 * w] = lo2(c);
-          q[3 + 2 * w] = hi2(c);
-        }
-        if (t + 1 < nfe) {
-          // both subhalos far from the whole CTA: the series, no tests
-#pragma unroll
-          for (int j = 0; j < kRtPts; ++j) {
-            const float2 dx = sub2(X[j], make_float2(w0.x, w0.y)), dy = sub2(Y[j], make_float2(w0.z, w0.w));
-            const float2 R2 = __ffma2_rn(dx, dx, __fmul2_rn(dy, dy));
-            const float2 m = tnfw_m_series2(hi2(w1), hi2(w2), q, __fmul2_rn(R2, lo2(w1)));
-            ax[j] = __ffma2_rn(m, dx, ax[j]);
-            ay[j] = __ffma2_rn(m, dy, ay[j]);
-          }
-        } else {
+          rt_coeffs<kSerTerms - 1>(hot, q);
           // the series where x^2 reaches its radius, else the packed far-side
           // closed form, and the rare near pairs the general form (which
           // gives the same bits for far pairs)

@@ -3,9 +3,16 @@
 // of the lens and dL/d(x_h, y_h, kappa_s | theta_pm, theta_s) of every
 // subhalo, with dL/dp = -sum_i G_i . dalpha_i/dp (beta = xi - alpha).
 //
-// The grid has at most one CTA per resident slot; CTA b takes the contiguous
-// point range [b n / nblk, (b + 1) n / nblk), so every CTA does the same work
-// to within one point and no wave is left partly empty. The CTA stages its
+// The points are cut into tiles, one CTA each, of equal point counts to
+// within one image row: explicit points into contiguous index ranges; pixel
+// grids into bands of image rows whose tiles split the band's points in
+// column-major order (vjp_bands), so that a tile's points are compact and
+// far from most subhalos. Below a full wave of the resident CTA slots there
+// is a tile per kVjThreads points; above it whole waves, up to kVjWaves
+// (vjp_tiles), because tiles inside the subhalo population cost several
+// times the average: with more tiles than slots the CTA scheduler balances
+// them, and a plan (vjp_plan_kernel, vjp_rank_kernel) launches them
+// heaviest first. The CTA stages its
 // points and their G in shared memory (kVjChunk at a time; one chunk at the
 // usual sizes) and the thread that stages a point also evaluates its lens and
 // shear terms. The subhalo sums are split into slots (h, phase): with P
@@ -14,19 +21,20 @@
 // once the points are staged, a thread sweeps without block barriers. Points
 // are staged as packed pairs (2k, 2k + 1), so a slot evaluates two points per
 // step in f32x2 arithmetic; slot (h, r) takes the point pairs k = r (mod P).
-// P is
-// chosen on the host so that n_sub * P fills the CTA's threads nearly
+// P is chosen on the host so that n_sub * P fills the CTA's threads nearly
 // evenly. At the end the CTA adds each subhalo's P slot sums in phase order.
-// Per-CTA partials (FP64 lens terms, Kahan-compensated FP32 slot
-// sums) are added in fixed order by a final kernel, so results are
-// deterministic.
+// Per-tile partials (FP64 lens terms, Kahan-compensated FP32 slot sums) are
+// added in fixed order (the lens terms by tile, the subhalo sums by launch
+// position) by a final kernel, so results are deterministic.
 //
 // tNFW subhalos whose far-field series radius (x >= 8 max(tau, 2)) clears
-// the bounding box of all of a CTA's points sum by the series of G and of
-// x dG/dx (1 rsqrt and two degree-5 polynomials per pair) with no per-pair
-// test; the others take the far-side closed form per pair and the general
-// form for the rare near pairs. Each CTA orders its subhalos far-first
-// (vj_order), so that whole warps take one path.
+// the bounding box of all of a tile's points sum by the series of G and of
+// x dG/dx (1 rsqrt and two short polynomials per pair) with no per-pair
+// test, with as few terms as the box's distance allows (vj_degree); the
+// others take the far-side closed form per pair and the general form for the
+// rare near pairs. The subhalos of a tile are ordered by that choice, fewest
+// terms first and the closed forms last (vj_sort, by the plan or by the CTA
+// itself), so that whole warps take one path.
 #include <math.h>
 
 #include "host.cuh"
@@ -39,8 +47,10 @@ constexpr int kVjThreads = 128;
 constexpr int kVjWarps = kVjThreads / 32;
 constexpr int kVjChunk = 2048;    // points staged in shared memory at once
 constexpr int kVjMaxPhases = 8;
-constexpr int kVjFold = 16;       // point pairs summed plainly per slot before a Kahan fold
-constexpr int kVjMaxOrd = 4096;   // subhalo counts up to which a CTA orders its slots far-first
+constexpr int kVjFold = 32;       // point pairs summed plainly per slot before a Kahan fold
+constexpr int kVjMaxOrd = 4096;   // subhalo counts up to which a CTA orders its slots by series degree
+constexpr int kVjWaves = 8;       // large inputs: tiles per resident CTA slot
+constexpr int kVjTilePts = 512;   // ... while every tile keeps at least this many points
 
 __device__ __forceinline__ double warp_sum_d(double v) {
 #pragma unroll
@@ -52,9 +62,22 @@ struct VjSmem {
   float4 pos[kVjChunk / 2];   // point pair k: (x_2k, x_2k+1, y_2k, y_2k+1)
   float4 grad[kVjChunk / 2];  // (G_x, G_x, G_y, G_y) of the same two points
   double lred[kVjWarps][7];
-  unsigned short ord[kVjMaxOrd];  // slot subhalo -> subhalo: far from the CTA's points first
+  unsigned short ord[kVjMaxOrd];  // slot subhalo -> subhalo, by series degree (vj_order)
+  unsigned char deg[kVjMaxOrd];   // series degree of each subhalo for the CTA's points (0: closed forms)
   float wbox[kVjWarps][4];        // per-warp bounds of the CTA's points
   float box[4];                   // x_lo, y_lo, x_hi, y_hi of the CTA's points
+  int cnt[4];                     // subhalos served by the series to y^3, y^4, y^5, y^7
+};
+
+// The optional plan of a launch (vjp_plan_kernel, vjp_rank_kernel): CTA b
+// takes tile perm[b] (the tiles heaviest first), whose subhalos in series
+// degree order are ord[tile n_sub ..], cnt[4 tile ..] of them served by the
+// series to y^3, y^4, y^5, y^7. All NULL: CTA b takes tile b and orders its
+// subhalos itself.
+struct VjPlan {
+  const int* perm;
+  const unsigned short* ord;
+  const int* cnt;
 };
 
 // One tNFW pair's terms of the four subhalo sums, for two points at once
@@ -114,43 +137,43 @@ __device__ __forceinline__ void vj_fix_near(const SubRec& rec, float2 R2, float2
 // deflection's series G = y^2 Q(y), Q = q0 + sum_{j>=2} q_j y^j (prep_series),
 //   hg = x dG/dx = -y^2 (2 Q + y Q'(y)) = y^2 (s0 + sum_{j>=2} s_j y^j),
 //   s0 = -2 q0, s_j = -(j + 2) q_j.
-// The gradient takes the terms up to y^7 from x = 8 max(tau, 2) on: against
-// the closed form in extended precision both G and hg are within 1.2e-8
-// relative there for tau in [2, 20] (2e-9 from 10 max(tau, 2)), a fifth of
-// the FP32 unit roundoff.
-constexpr int kVjSerTerms = 8;         // q0 .. q7 (q1 = 0)
-constexpr float kVjSerRadius2 = 64.f;  // x^2 >= 64 max(tau^2, 4)
-
+// The terms up to y^K serve from x = r_K max(tau, 2) on:
+//   K = 7 from r = 8, K = 5 from 18, K = 4 from 32, K = 3 from 80.
+// Against the closed form in extended precision both G and hg are then
+// within 1.4e-8 relative for tau in [0.5, 30] (the truncated terms fall as
+// (tau / x)^(K + 1)), a quarter of the FP32 unit roundoff.
+template <int K>
 struct VjSer {
   float2 q0, s0;
-  float2 q[kVjSerTerms - 2], s[kVjSerTerms - 2];  // index j - 2
+  float2 q[K - 1], s[K - 1];  // index j - 2, j = 2 .. K
 };
 
-__device__ __forceinline__ VjSer vj_series_coeffs(const SubSer& c) {
-  VjSer v;
+template <int K>
+__device__ __forceinline__ VjSer<K> vj_series_coeffs(const SubSer& c) {
+  VjSer<K> v;
   v.q0 = f2(c.q[0]);
   v.s0 = f2(-2.0f * c.q[0]);
 #pragma unroll
-  for (int j = 2; j < kVjSerTerms; ++j) {
+  for (int j = 2; j <= K; ++j) {
     v.q[j - 2] = f2(c.q[j]);
     v.s[j - 2] = f2(-(float)(j + 2) * c.q[j]);
   }
   return v;
 }
 
-// x^2 from which the gradient takes the series (+inf where the deflection's
-// series is not in use for the subhalo).
-__device__ __forceinline__ float vj_radius2(const SubRec& h, const SubSer& q) {
-  return isinf(q.xT2) ? INFINITY : kVjSerRadius2 * fmaxf(h.tau2, 4.0f);
+// The series degree K that serves every pair of a subhalo with points at
+// x^2 >= x2min (m = max(tau^2, 4)); 0 where x is below 8 max(tau, 2).
+__device__ __forceinline__ int vj_degree(float x2min, float m) {
+  return x2min >= 6400.0f * m ? 3 : x2min >= 1024.0f * m ? 4 : x2min >= 324.0f * m ? 5 : x2min >= 64.0f * m ? 7 : 0;
 }
 
-// G, hg and 1/x^2 = y^2 of two points by the series (x^2 at or beyond the
-// series radius for both).
-__device__ __forceinline__ void vj_series2(const VjSer& c, float2 x2, float2& Gt, float2& hg, float2& ix2) {
+// G, hg and 1/x^2 = y^2 of two points by the series of degree K.
+template <int K>
+__device__ __forceinline__ void vj_series2(const VjSer<K>& c, float2 x2, float2& Gt, float2& hg, float2& ix2) {
   const float2 y = frsqrt2(x2), y2 = __fmul2_rn(y, y);
-  float2 r = c.q[kVjSerTerms - 3], t = c.s[kVjSerTerms - 3];
+  float2 r = c.q[K - 2], t = c.s[K - 2];
 #pragma unroll
-  for (int j = kVjSerTerms - 4; j >= 0; --j) {
+  for (int j = K - 3; j >= 0; --j) {
     r = __ffma2_rn(r, y, c.q[j]);
     t = __ffma2_rn(t, y, c.s[j]);
   }
@@ -159,17 +182,22 @@ __device__ __forceinline__ void vj_series2(const VjSer& c, float2 x2, float2& Gt
   ix2 = y2;
 }
 
-// far: every staged point of the CTA is at or beyond the gradient's series
-// radius (tNFW only), so the series serves every pair without a test.
-template <int PROFILE>
-__device__ __forceinline__ void vj_sweep(const SubRec& rec, float2 ex, const VjSer& ser, bool far,
+// K > 0: every staged point of the CTA is at or beyond the radius of the
+// gradient's series of degree K (tNFW only), so that series serves every
+// pair without a test; K = 0: the closed forms. P1: one phase (P = 1), so
+// that consecutive steps read neighbouring point pairs.
+template <int PROFILE, int K, bool P1>
+__device__ __forceinline__ void vj_sweep(const SubRec& rec, float2 ex, const SubSer& q,
                                          const float4* __restrict__ pos, const float4* __restrict__ grad, int npairs,
-                                         int r, int P, float* s, float* c) {
+                                         int r, int Pr, float* s, float* c) {
+  const int P = P1 ? 1 : Pr;  // the slot's stride over the point pairs
   const SubRec2 H = sub_pair(rec, rec);
+  constexpr bool kSeries = PROFILE == LR_PROFILE_TNFW && K > 0;
+  const VjSer<kSeries ? K : 3> ser = vj_series_coeffs<kSeries ? K : 3>(q);
   for (int k = r; k < npairs;) {
     const int kend = min(npairs, k + P * kVjFold);
     float2 a0 = f2(0.f), a1 = f2(0.f), a2 = f2(0.f), a3 = f2(0.f), b0 = f2(0.f), b1 = f2(0.f);
-    if (PROFILE == LR_PROFILE_TNFW && far) {
+    if constexpr (kSeries) {
       for (; k + P < kend; k += 2 * P) {
         float2 dx[2], dy[2], gx[2], gy[2], Gt[2], hg[2], ix2[2];
 #pragma unroll
@@ -252,25 +280,59 @@ __device__ __forceinline__ void vj_sweep(const SubRec& rec, float2 ex, const VjS
   }
 }
 
-// Whether every point in the box (x_lo, y_lo, x_hi, y_hi) is at or beyond the
-// gradient's series radius: x^2 of the box's nearest point reaches it.
-__device__ __forceinline__ bool vj_far(const SubRec& h, const SubSer& q, const float* box) {
+// The series degree (vj_degree) that serves every point of the box (x_lo,
+// y_lo, x_hi, y_hi): x^2 of the box's nearest point. 0 where the deflection's
+// series is not in use for the subhalo.
+__device__ __forceinline__ int vj_degree_box(const SubRec& h, const SubSer& q, const float* box) {
+  if (isinf(q.xT2)) return 0;
   const float dx = fmaxf(fmaxf(box[0] - h.xh, h.xh - box[2]), 0.f);
   const float dy = fmaxf(fmaxf(box[1] - h.yh, h.yh - box[3]), 0.f);
-  return __fmul_rn(fmaf(dx, dx, dy * dy), h.its2) >= vj_radius2(h, q);
+  return vj_degree(__fmul_rn(fmaf(dx, dx, dy * dy), h.its2), fmaxf(h.tau2, 4.0f));
 }
 
-// The CTA's prologue for a tNFW sum: the bounds of its points [p0, p1), then
-// (ordered) the subhalos far from all of them (vj_far) in index order,
-// followed by the others, in sm.ord, so that the far ones, whose slots sweep
-// by the series alone, fill whole warps. The slots' sums do not depend on
-// the order.
-__device__ __forceinline__ void vj_order(const GridDev& g, const float2* __restrict__ xi, int64_t p0, int64_t p1,
-                                         const float* __restrict__ sub, int n_sub, bool ordered, VjSmem& sm) {
+// The CTA's points: u in [u0, u1) indexes explicit points directly; on a
+// pixel grid it indexes the points of the band of rows [row0, row0 + rows)
+// in column-major order.
+struct VjMap {
+  int64_t u0, u1;
+  int32_t row0, rows;
+};
+
+__device__ __forceinline__ VjMap vj_map(const GridDev& g, bool grid, int64_t n, int bands, int64_t blk,
+                                        int64_t nblk) {
+  VjMap m;
+  if (!grid) {
+    m.u0 = blk * n / nblk;
+    m.u1 = (blk + 1) * n / nblk;
+    m.row0 = m.rows = 0;
+    return m;
+  }
+  const int64_t per = nblk / bands;  // CTAs per band
+  const int64_t b = blk / per, c = blk - b * per;
+  m.row0 = (int32_t)(b * g.H / bands);
+  m.rows = (int32_t)((b + 1) * g.H / bands) - m.row0;
+  const int64_t nb = (int64_t)m.rows * g.W;
+  m.u0 = c * nb / per;
+  m.u1 = (c + 1) * nb / per;
+  return m;
+}
+
+// Index of the CTA's point u (explicit points: u itself).
+__device__ __forceinline__ int64_t vj_index(const GridDev& g, const VjMap& m, bool grid, int64_t u) {
+  if (!grid) return u;
+  const int32_t col = (int32_t)(u / m.rows);
+  const int32_t row = m.row0 + (int32_t)(u - (int64_t)col * m.rows);
+  return (int64_t)row * g.W + col;
+}
+
+// The bounding box (x_lo, y_lo, x_hi, y_hi) of the tile's points into box,
+// by all of the CTA's threads (wbox: per-warp scratch).
+__device__ __forceinline__ void vj_box(const GridDev& g, const float2* __restrict__ xi, const VjMap& mp,
+                                       float (*wbox)[4], float* box) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   float b0 = INFINITY, b1 = INFINITY, b2 = -INFINITY, b3 = -INFINITY;
-  for (int64_t i = p0 + tid; i < p1; i += kVjThreads) {
-    const float2 p = xi ? xi[i] : grid_point(g, i);
+  for (int64_t u = mp.u0 + tid; u < mp.u1; u += kVjThreads) {
+    const float2 p = xi ? xi[u] : grid_point(g, vj_index(g, mp, true, u));
     b0 = fminf(b0, p.x);
     b1 = fminf(b1, p.y);
     b2 = fmaxf(b2, p.x);
@@ -284,70 +346,118 @@ __device__ __forceinline__ void vj_order(const GridDev& g, const float2* __restr
     b3 = fmaxf(b3, __shfl_xor_sync(0xffffffffu, b3, o));
   }
   if (lane == 0) {
-    sm.wbox[warp][0] = b0;
-    sm.wbox[warp][1] = b1;
-    sm.wbox[warp][2] = b2;
-    sm.wbox[warp][3] = b3;
+    wbox[warp][0] = b0;
+    wbox[warp][1] = b1;
+    wbox[warp][2] = b2;
+    wbox[warp][3] = b3;
   }
   __syncthreads();
   if (tid < 4) {
-    float v = sm.wbox[0][tid];
-    for (int w = 1; w < kVjWarps; ++w) v = tid < 2 ? fminf(v, sm.wbox[w][tid]) : fmaxf(v, sm.wbox[w][tid]);
-    sm.box[tid] = v;
+    float v = wbox[0][tid];
+    for (int w = 1; w < kVjWarps; ++w) v = tid < 2 ? fminf(v, wbox[w][tid]) : fmaxf(v, wbox[w][tid]);
+    box[tid] = v;
   }
   __syncthreads();
-  if (!ordered) return;
-  if (warp == 0) {  // stable partition: far first
+}
+
+// FP32 lanes per pair of a subhalo sum by the series of degree K (0: the
+// closed forms): the weight of a tile's work.
+__device__ __forceinline__ float vj_cost(int K) { return K ? 20.3f + 2.0f * (float)(K - 2) : 50.3f; }
+
+// The tNFW subhalos (n_sub <= kVjMaxOrd) by the series degree that serves
+// every point of the box, fewest terms first, each degree in index order,
+// those that need the closed forms last: ord[rank] = subhalo, cnt[0..3] the
+// numbers served by the series to y^3, y^4, y^5, y^7 (shared or global
+// memory). deg: per-subhalo scratch in shared memory. Returns the thread's
+// share of the tile's work per point (sum of vj_cost over its subhalos).
+__device__ __forceinline__ float vj_sort(const float* __restrict__ sub, int n_sub, const float* box,
+                                         unsigned char* deg, unsigned short* ord, int* cnt) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  float cost = 0.f;
+  for (int h = tid; h < n_sub; h += kVjThreads) {
+    const SubRec r = prep_sub(sub + 5 * (int64_t)h, LR_PROFILE_TNFW);
+    const int d = vj_degree_box(r, prep_series(r, LR_PROFILE_TNFW), box);
+    deg[h] = (unsigned char)d;
+    cost += vj_cost(d);
+  }
+  __syncthreads();
+  if (warp == 0) {  // stable partition by degree: 3, 4, 5, 7, then 0
     int nf = 0;
-    for (int pass = 0; pass < 2; ++pass) {
+    for (int pass = 0; pass < 5; ++pass) {
+      const int want = pass < 4 ? (pass < 3 ? 3 + pass : 7) : 0;
+      const int nf0 = nf;
       for (int b = 0; b < n_sub; b += 32) {
-        bool f = false;
-        if (b + lane < n_sub) {
-          const SubRec h = prep_sub(sub + 5 * (int64_t)(b + lane), LR_PROFILE_TNFW);
-          f = vj_far(h, prep_series(h, LR_PROFILE_TNFW), sm.box) == (pass == 0);
-        }
+        const bool f = b + lane < n_sub && deg[b + lane] == want;
         const unsigned m = __ballot_sync(0xffffffffu, f);
-        if (f) sm.ord[nf + __popc(m & ((1u << lane) - 1u))] = (unsigned short)(b + lane);
+        if (f) ord[nf + __popc(m & ((1u << lane) - 1u))] = (unsigned short)(b + lane);
         nf += __popc(m);
       }
+      if (pass < 4 && lane == 0) cnt[pass] = nf - nf0;
     }
   }
   __syncthreads();
+  return cost;
+}
+
+// The series degree of the subhalo at rank hs of the degree order.
+__device__ __forceinline__ int vj_rank_degree(int hs, int c3, int c4, int c5, int c7) {
+  return hs < c3 ? 3 : hs < c3 + c4 ? 4 : hs < c3 + c4 + c5 ? 5 : hs < c3 + c4 + c5 + c7 ? 7 : 0;
 }
 
 template <int PROFILE>
 __device__ __forceinline__ void vjp_body(const LensConst& L, const LensGradConst& LG, const GridDev& g,
                                          const float2* __restrict__ xi, int64_t n, const float* __restrict__ sub,
-                                         int n_sub, int P, const float2* __restrict__ dbeta,
-                                         double* __restrict__ lens_part, float* __restrict__ sub_part,
-                                         float* __restrict__ slot_part, int64_t blk, int64_t nblk, VjSmem& sm) {
+                                         int n_sub, int P, int bands, const VjPlan& plan,
+                                         const float2* __restrict__ dbeta, double* __restrict__ lens_part,
+                                         float* __restrict__ sub_part, float* __restrict__ slot_part, int64_t blk,
+                                         int64_t nblk, VjSmem& sm) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int64_t p0 = blk * n / nblk, p1 = (blk + 1) * n / nblk;
+  const bool grid = xi == nullptr;
+  // the lens partials are indexed by tile, the subhalo and slot partials by
+  // launch position: CTAs that run together write neighbouring words
+  const int64_t tile = plan.perm ? (int64_t)plan.perm[blk] : blk;
+  const VjMap mp = vj_map(g, grid, n, bands, tile, nblk);
+  const int64_t p0 = mp.u0, p1 = mp.u1;
   const int nchunks = (int)((p1 - p0 + kVjChunk - 1) / kVjChunk);
   const int slots = n_sub * P;
   const int ngroups = slots > 0 ? (slots + kVjThreads - 1) / kVjThreads : 1;
   float la[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   int staged = -1;
+  // tNFW: the subhalos in series degree order, from the plan or sorted here
+  // for the tile's box; more than kVjMaxOrd subhalos: index order, each
+  // slot choosing its degree for the box
   const bool ordered = PROFILE == LR_PROFILE_TNFW && n_sub > 0 && n_sub <= kVjMaxOrd;
-  if (PROFILE == LR_PROFILE_TNFW) vj_order(g, xi, p0, p1, sub, n_sub, ordered, sm);
+  const unsigned short* ord = plan.ord ? plan.ord + tile * n_sub : sm.ord;
+  int c3 = 0, c4 = 0, c5 = 0, c7 = 0;
+  if (PROFILE == LR_PROFILE_TNFW) {
+    if (plan.ord) {
+      const int* c = plan.cnt + 4 * tile;
+      c3 = c[0], c4 = c[1], c5 = c[2], c7 = c[3];
+    } else {
+      vj_box(g, xi, mp, sm.wbox, sm.box);
+      if (ordered) {
+        vj_sort(sub, n_sub, sm.box, sm.deg, sm.ord, sm.cnt);
+        c3 = sm.cnt[0], c4 = sm.cnt[1], c5 = sm.cnt[2], c7 = sm.cnt[3];
+      }
+    }
+  }
 
   for (int grp = 0; grp < ngroups; ++grp) {
     const int slot = grp * kVjThreads + tid;
     const bool own = slot < slots;
     const int hs = own ? slot / P : 0;  // the slot's subhalo in the CTA's order
     const int r = own ? slot - hs * P : 0;
-    const int h = ordered ? (int)sm.ord[hs] : hs;
+    const int h = ordered ? (int)ord[hs] : hs;
     SubRec rec{};
-    VjSer ser{};
-    bool far = false;
+    SubSer q{};
+    int deg = 0;  // series degree serving all of the CTA's points (0: closed forms)
     float2 ex = make_float2(0.f, 0.f);  // tNFW: (4T, 1/theta_s); point mass: (0, theta_pm)
     if (own) {
       const float* rr = sub + 5 * (int64_t)h;
       rec = prep_sub(rr, PROFILE);
       if (PROFILE == LR_PROFILE_TNFW) {
-        const SubSer q = prep_series(rec, PROFILE);
-        far = vj_far(rec, q, sm.box);
-        if (far) ser = vj_series_coeffs(q);
+        q = prep_series(rec, PROFILE);
+        deg = ordered ? vj_rank_degree(hs, c3, c4, c5, c7) : vj_degree_box(rec, q, sm.box);
       }
       if (PROFILE == LR_PROFILE_POINT_MASS) {
         ex = make_float2(0.f, __ldg(rr + 2));
@@ -363,7 +473,7 @@ __device__ __forceinline__ void vjp_body(const LensConst& L, const LensGradConst
       if (ch != staged) {  // uniform over the CTA
         __syncthreads();   // the previous chunk's readers are done
         for (int k = tid; k < cnt; k += kVjThreads) {
-          const int64_t i = c0 + k;
+          const int64_t i = vj_index(g, mp, grid, c0 + k);
           const float2 p = xi ? xi[i] : grid_point(g, i);
           const float2 d = dbeta[i];
           if (grp == 0) {  // each chunk is staged once in group 0: the point's lens and shear terms
@@ -391,7 +501,44 @@ __device__ __forceinline__ void vjp_body(const LensConst& L, const LensGradConst
         __syncthreads();
         staged = ch;
       }
-      if (own) vj_sweep<PROFILE>(rec, ex, ser, far, sm.pos, sm.grad, (cnt + 1) >> 1, r, P, sc, cc);
+      if (own) {
+        const int np = (cnt + 1) >> 1;
+        if (P == 1) {
+          switch (deg) {
+            case 3:
+              vj_sweep<PROFILE, 3, true>(rec, ex, q, sm.pos, sm.grad, np, r, 1, sc, cc);
+              break;
+            case 4:
+              vj_sweep<PROFILE, 4, true>(rec, ex, q, sm.pos, sm.grad, np, r, 1, sc, cc);
+              break;
+            case 5:
+              vj_sweep<PROFILE, 5, true>(rec, ex, q, sm.pos, sm.grad, np, r, 1, sc, cc);
+              break;
+            case 7:
+              vj_sweep<PROFILE, 7, true>(rec, ex, q, sm.pos, sm.grad, np, r, 1, sc, cc);
+              break;
+            default:
+              vj_sweep<PROFILE, 0, true>(rec, ex, q, sm.pos, sm.grad, np, r, 1, sc, cc);
+          }
+        } else {
+          switch (deg) {
+            case 3:
+              vj_sweep<PROFILE, 3, false>(rec, ex, q, sm.pos, sm.grad, np, r, P, sc, cc);
+              break;
+            case 4:
+              vj_sweep<PROFILE, 4, false>(rec, ex, q, sm.pos, sm.grad, np, r, P, sc, cc);
+              break;
+            case 5:
+              vj_sweep<PROFILE, 5, false>(rec, ex, q, sm.pos, sm.grad, np, r, P, sc, cc);
+              break;
+            case 7:
+              vj_sweep<PROFILE, 7, false>(rec, ex, q, sm.pos, sm.grad, np, r, P, sc, cc);
+              break;
+            default:
+              vj_sweep<PROFILE, 0, false>(rec, ex, q, sm.pos, sm.grad, np, r, P, sc, cc);
+          }
+        }
+      }
     }
     if (own) {
 #pragma unroll
@@ -413,7 +560,7 @@ __device__ __forceinline__ void vjp_body(const LensConst& L, const LensGradConst
       const float* q = slot_part + (blk * slots + (int64_t)hh * P) * 4 + v;
       float a = 0.f, c = 0.f;
       for (int rr = 0; rr < P; ++rr) vj_kahan(a, c, q[4 * rr]);
-      const int64_t hreal = ordered ? (int64_t)sm.ord[hh] : (int64_t)hh;
+      const int64_t hreal = ordered ? (int64_t)ord[hh] : (int64_t)hh;
       sub_part[(hreal * 4 + v) * nblk + blk] = a - c;
     }
   }
@@ -428,7 +575,7 @@ __device__ __forceinline__ void vjp_body(const LensConst& L, const LensGradConst
   if (tid < 7) {
     double v = 0.0;
     for (int w = 0; w < kVjWarps; ++w) v += sm.lred[w][tid];
-    lens_part[blk * 7 + tid] = v;
+    lens_part[tile * 7 + tid] = v;
   }
 }
 
@@ -437,13 +584,14 @@ __global__ void __launch_bounds__(kVjThreads, 4) raytrace_vjp_kernel(const __gri
                                                                   const __grid_constant__ LensGradConst LG, GridDev g,
                                                                   const float2* __restrict__ xi, int64_t n,
                                                                   const float* __restrict__ sub, int n_sub, int P,
+                                                                  int bands, const VjPlan plan,
                                                                   const float2* __restrict__ dbeta,
                                                                   double* __restrict__ lens_part,
                                                                   float* __restrict__ sub_part,
                                                                   float* __restrict__ slot_part) {
   __shared__ __align__(16) VjSmem sm;
-  vjp_body<PROFILE>(L, LG, g, xi, n, sub, n_sub, P, dbeta, lens_part, sub_part, slot_part, blockIdx.x, gridDim.x,
-                    sm);
+  vjp_body<PROFILE>(L, LG, g, xi, n, sub, n_sub, P, bands, plan, dbeta, lens_part, sub_part, slot_part,
+                    blockIdx.x, gridDim.x, sm);
 }
 
 // The same with the lens read from a device record (lr_lens_prepare).
@@ -451,14 +599,61 @@ template <int PROFILE>
 __global__ void __launch_bounds__(kVjThreads, 4) raytrace_vjp_rec_kernel(const LensRecord* __restrict__ rec, GridDev g,
                                                                       const float2* __restrict__ xi, int64_t n,
                                                                       const float* __restrict__ sub, int n_sub, int P,
+                                                                      int bands, const VjPlan plan,
                                                                       const float2* __restrict__ dbeta,
                                                                       double* __restrict__ lens_part,
                                                                       float* __restrict__ sub_part,
                                                                       float* __restrict__ slot_part, int* fault) {
   __shared__ __align__(16) VjSmem sm;
   if (rec->status != 0 && blockIdx.x == 0 && threadIdx.x == 0) atomicExch(fault, kFaultBadLens);
-  vjp_body<PROFILE>(rec->L, rec->G, g, xi, n, sub, n_sub, P, dbeta, lens_part, sub_part, slot_part, blockIdx.x,
-                    gridDim.x, sm);
+  vjp_body<PROFILE>(rec->L, rec->G, g, xi, n, sub, n_sub, P, bands, plan, dbeta, lens_part, sub_part, slot_part,
+                    blockIdx.x, gridDim.x, sm);
+}
+
+// The plan of a tNFW launch with more tiles than resident CTA slots: one
+// CTA per tile sorts the subhalos by the series degree that serves the
+// tile's box (vj_sort) into ord and cnt, and writes the tile's work
+// (FP32 lanes over its point-subhalo pairs) to weight.
+__global__ void __launch_bounds__(kVjThreads) vjp_plan_kernel(GridDev g, const float2* __restrict__ xi, int64_t n,
+                                                              const float* __restrict__ sub, int n_sub, int bands,
+                                                              int64_t ntiles, unsigned short* __restrict__ ord,
+                                                              int* __restrict__ cnt, float* __restrict__ weight) {
+  __shared__ float wbox[kVjWarps][4], box[4], wsum[kVjWarps];
+  __shared__ unsigned char deg[kVjMaxOrd];
+  const int64_t tile = blockIdx.x;
+  const VjMap mp = vj_map(g, xi == nullptr, n, bands, tile, ntiles);
+  vj_box(g, xi, mp, wbox, box);
+  float c = vj_sort(sub, n_sub, box, deg, ord + tile * n_sub, cnt + 4 * tile);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float t = 0.f;
+    for (int w = 0; w < kVjWarps; ++w) t += wsum[w];
+    weight[tile] = t * (float)(mp.u1 - mp.u0);
+  }
+}
+
+// perm[rank] = tile, the tiles by weight, heaviest first (ties by index):
+// one warp per tile counts the heavier tiles. Dynamic shared memory: the
+// ntiles weights.
+__global__ void __launch_bounds__(128) vjp_rank_kernel(const float* __restrict__ weight, int ntiles,
+                                                       int* __restrict__ perm) {
+  extern __shared__ float wsh[];
+  for (int t = threadIdx.x; t < ntiles; t += blockDim.x) wsh[t] = weight[t];
+  __syncthreads();
+  const int t = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (t >= ntiles) return;
+  const float wt = wsh[t];
+  int r = 0;
+  for (int u = lane; u < ntiles; u += 32) {
+    const float wu = wsh[u];
+    r += (wu > wt || (wu == wt && u < t)) ? 1 : 0;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+  if (lane == 0) perm[r] = t;
 }
 
 __global__ void __launch_bounds__(kVjThreads, 4) vjp_batched_kernel(const __grid_constant__ Batch<VjpP> B) {
@@ -468,17 +663,15 @@ __global__ void __launch_bounds__(kVjThreads, 4) vjp_batched_kernel(const __grid
   const int64_t blk = blockIdx.x - B.start[k];
   const int64_t nblk = B.start[k + 1] - B.start[k];
   if (P.profile == LR_PROFILE_POINT_MASS)
-    vjp_body<LR_PROFILE_POINT_MASS>(P.L, P.LG, P.g, P.xi, P.n, P.sub, P.n_sub, P.phases, P.dbeta, P.lens_part,
-                                    P.sub_part, P.slot_part, blk, nblk, sm);
+    vjp_body<LR_PROFILE_POINT_MASS>(P.L, P.LG, P.g, P.xi, P.n, P.sub, P.n_sub, P.phases, P.bands, VjPlan{},
+                                    P.dbeta, P.lens_part, P.sub_part, P.slot_part, blk, nblk, sm);
   else
-    vjp_body<LR_PROFILE_TNFW>(P.L, P.LG, P.g, P.xi, P.n, P.sub, P.n_sub, P.phases, P.dbeta, P.lens_part,
-                              P.sub_part, P.slot_part, blk, nblk, sm);
+    vjp_body<LR_PROFILE_TNFW>(P.L, P.LG, P.g, P.xi, P.n, P.sub, P.n_sub, P.phases, P.bands, VjPlan{}, P.dbeta,
+                              P.lens_part, P.sub_part, P.slot_part, blk, nblk, sm);
 }
 
-// CTAs of the VJP for n points: one per resident slot of the device at most
-// (and at most one per kVjThreads points), so a launch is a single full wave.
-int64_t vjp_blocks(int64_t n) {
-  if (n <= 0) return 0;
+// Resident CTA slots of the VJP kernels on the current device.
+static int64_t vjp_slots() {
   static int slots[64] = {0};
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
@@ -490,26 +683,76 @@ int64_t vjp_blocks(int64_t n) {
       occ = 1;
     slots[dev] = (occ > 0 ? occ : 1) * n_sm;
   }
+  return slots[dev];
+}
+
+// Tiles (one CTA each) of the VJP for n points: one per kVjThreads points
+// below a full wave of the resident slots; above it whole waves, up to
+// kVjWaves of them while every tile keeps kVjTilePts points, so that the
+// CTA scheduler can balance tiles of uneven work (a plan launches them
+// heaviest first).
+int64_t vjp_tiles(int64_t n) {
+  if (n <= 0) return 0;
+  const int64_t slots = vjp_slots();
   const int64_t nb = (n + kVjThreads - 1) / kVjThreads;
-  return nb < slots[dev] ? nb : slots[dev];
+  if (nb < slots) return nb;
+  int64_t w = n / (slots * kVjTilePts);
+  w = w < 1 ? 1 : (w > kVjWaves ? kVjWaves : w);
+  return w * slots;
+}
+
+// Whether the workspace holds a plan: subhalos that a CTA can order (at most
+// kVjMaxOrd), more than one wave of tiles, and their weights within the
+// rank kernel's shared memory.
+static bool plan_fits(int64_t ntiles, int32_t n_sub) {
+  return n_sub > 0 && n_sub <= kVjMaxOrd && ntiles > vjp_slots() && ntiles <= 12288;
+}
+
+// Whether a launch over ntiles tiles takes a plan: tNFW subhalos and a
+// workspace that holds it.
+static bool vjp_planned(int64_t ntiles, const lr_points* p) {
+  return p->profile == LR_PROFILE_TNFW && plan_fits(ntiles, p->n_sub);
 }
 
 // Phases P of the subhalo sums: the P in [1, kVjMaxPhases] whose slot count
 // n_sub P wastes the fewest threads of the last group of kVjThreads (the
-// smallest such P), keeping at least 64 points per slot.
+// smallest such P), keeping at least 128 points per slot.
 int vjp_phases(int64_t n, int32_t n_sub) {
   if (n_sub <= 0 || n <= 0) return 1;
-  const int64_t per_cta = (n + vjp_blocks(n) - 1) / vjp_blocks(n);
+  const int64_t per_cta = (n + vjp_tiles(n) - 1) / vjp_tiles(n);
   int best = 1;
   double best_w = 1e30;
   for (int P = 1; P <= kVjMaxPhases; ++P) {
-    if (P > 1 && per_cta / P < 64) break;
+    if (P > 1 && per_cta / P < 128) break;
     const int64_t sl = (int64_t)n_sub * P;
     const int64_t padded = (sl + kVjThreads - 1) / kVjThreads * kVjThreads;
     const double w = (double)padded / (double)sl;
     if (w < best_w - 1e-9) {
       best_w = w;
       best = P;
+    }
+  }
+  return best;
+}
+
+// Bands of image rows for the CTAs of a pixel grid of W x H points: the
+// divisor R of nblk (R <= H) whose tiles, H / R rows by W R / nblk columns,
+// are closest to square, preferring bands of equal height; the nblk / R CTAs
+// of a band split its points evenly in column-major order. 1 for explicit
+// points (unused).
+int vjp_bands(int64_t nblk, const lr_points* p) {
+  if (p->xy || nblk <= 0) return 1;
+  const GridDev g = grid_dev(p->grid);
+  int best = 1;
+  double best_s = 1e300;
+  for (int64_t R = 1; R <= nblk && R <= g.H; ++R) {
+    if (nblk % R) continue;
+    const double th = (double)g.H / (double)R, tw = (double)g.W * (double)R / (double)nblk;
+    const double uneven = (double)((g.H + R - 1) / R) / th - 1.0;
+    const double sc = fabs(log(th / tw)) + 2.0 * uneven;
+    if (sc < best_s) {
+      best_s = sc;
+      best = (int)R;
     }
   }
   return best;
@@ -566,7 +809,7 @@ lr_status launch_vjp_batched(const VjpP* p, int count, cudaStream_t s) {
     for (int k = 0; k < B.count; ++k) {
       B.p[k] = p[b0 + k];
       B.start[k] = (int32_t)tot;
-      tot += vjp_blocks(p[b0 + k].n);
+      tot += vjp_tiles(p[b0 + k].n);
     }
     B.start[B.count] = (int32_t)tot;
     if (tot == 0) continue;
@@ -603,27 +846,48 @@ lr_status make_lens_grad_const(const lr_lens* lens, LensGradConst* out) {
   return LR_OK;
 }
 
-// Workspace: per-CTA lens partials [CTA][7] (FP64), subhalo partials
-// [4 n_sub][CTA], and with P > 1 the slot sums [CTA][n_sub P][4].
+// Workspace: per-tile lens partials [tile][7] (FP64), subhalo partials
+// [4 n_sub][CTA], with P > 1 the slot sums [CTA][n_sub P][4], and where a
+// plan fits (plan_fits) its subhalo orders [tile][n_sub] (16 bit), degree
+// counts [tile][4], tile weights and the permutation of the tiles.
 struct VjWs {
   double* lens_part;
   float* sub_part;
   float* slot_part;
+  unsigned short* ord;
+  int* cnt;
+  float* weight;
+  int* perm;
   size_t bytes;
 };
 
 static VjWs vjp_ws_layout(void* ws, int64_t n, int32_t n_sub) {
-  const int64_t nblk = vjp_blocks(n);
+  const int64_t nt = vjp_tiles(n);
   const int P = vjp_phases(n, n_sub);
-  const size_t b_lens = align256(sizeof(double) * 7 * (size_t)nblk);
-  const size_t b_sub = align256(sizeof(float) * 4 * (size_t)n_sub * (size_t)nblk);
-  const size_t b_slot = P > 1 ? align256(sizeof(float) * 4 * (size_t)n_sub * P * (size_t)nblk) : 0;
+  const bool plan = plan_fits(nt, n_sub);
+  const size_t b_lens = align256(sizeof(double) * 7 * (size_t)nt);
+  const size_t b_sub = align256(sizeof(float) * 4 * (size_t)n_sub * (size_t)nt);
+  const size_t b_slot = P > 1 ? align256(sizeof(float) * 4 * (size_t)n_sub * P * (size_t)nt) : 0;
+  const size_t b_ord = plan ? align256(sizeof(unsigned short) * (size_t)n_sub * (size_t)nt) : 0;
+  const size_t b_cnt = plan ? align256(sizeof(int) * 4 * (size_t)nt) : 0;
+  const size_t b_w = plan ? align256(sizeof(float) * (size_t)nt) : 0;
+  const size_t b_perm = plan ? align256(sizeof(int) * (size_t)nt) : 0;
   char* c = static_cast<char*>(ws);
+  size_t off = 0;
+  auto at = [&](size_t bytes) -> char* {
+    char* r = (c && bytes) ? c + off : nullptr;
+    off += bytes;
+    return r;
+  };
   VjWs w;
-  w.lens_part = reinterpret_cast<double*>(c);
-  w.sub_part = c ? reinterpret_cast<float*>(c + b_lens) : nullptr;
-  w.slot_part = (c && P > 1) ? reinterpret_cast<float*>(c + b_lens + b_sub) : nullptr;
-  w.bytes = b_lens + b_sub + b_slot;
+  w.lens_part = reinterpret_cast<double*>(at(b_lens));
+  w.sub_part = reinterpret_cast<float*>(at(b_sub));
+  w.slot_part = reinterpret_cast<float*>(at(b_slot));
+  w.ord = reinterpret_cast<unsigned short*>(at(b_ord));
+  w.cnt = reinterpret_cast<int*>(at(b_cnt));
+  w.weight = reinterpret_cast<float*>(at(b_w));
+  w.perm = reinterpret_cast<int*>(at(b_perm));
+  w.bytes = off;
   return w;
 }
 
@@ -640,7 +904,7 @@ lr_status launch_raytrace_vjp(const lr_points* p, const float2* dbeta, double* d
     st = make_lens_grad_const(p->lens, &G);
     if (st != LR_OK) return st;
   }
-  const int64_t nblk = vjp_blocks(p->n);
+  const int64_t nblk = vjp_tiles(p->n);
   if (nblk == 0) {
     if (d_lens) LR_CHECK_CUDA(cudaMemsetAsync(d_lens, 0, 7 * sizeof(double), s));
     if (d_sub && p->n_sub) LR_CHECK_CUDA(cudaMemsetAsync(d_sub, 0, 4 * sizeof(double) * p->n_sub, s));
@@ -652,21 +916,32 @@ lr_status launch_raytrace_vjp(const lr_points* p, const float2* dbeta, double* d
   const GridDev g = p->xy ? GridDev{} : grid_dev(p->grid);
   const float2* xi = reinterpret_cast<const float2*>(p->xy);
   const int P = vjp_phases(p->n, p->n_sub);
+  const int bands = vjp_bands(nblk, p);
   int* fault = fault_ptr();
   LR_REQUIRE(fault != nullptr, "could not resolve the device fault word");
+  VjPlan plan{};
+  if (vjp_planned(nblk, p)) {
+    vjp_plan_kernel<<<(unsigned)nblk, kVjThreads, 0, s>>>(g, xi, p->n, p->sub, p->n_sub, bands, nblk, w.ord, w.cnt,
+                                                          w.weight);
+    LR_CHECK_CUDA(cudaGetLastError());
+    vjp_rank_kernel<<<(unsigned)((nblk + 3) / 4), 128, sizeof(float) * (size_t)nblk, s>>>(w.weight, (int)nblk,
+                                                                                          w.perm);
+    LR_CHECK_CUDA(cudaGetLastError());
+    plan = VjPlan{w.perm, w.ord, w.cnt};
+  }
   ktimer_begin(LR_KT_RAYTRACE_VJP, s);
   if (rec && p->profile == LR_PROFILE_POINT_MASS)
     raytrace_vjp_rec_kernel<LR_PROFILE_POINT_MASS><<<(unsigned)nblk, kVjThreads, 0, s>>>(
-        rec, g, xi, p->n, p->sub, p->n_sub, P, dbeta, lens_part, sub_part, w.slot_part, fault);
+        rec, g, xi, p->n, p->sub, p->n_sub, P, bands, plan, dbeta, lens_part, sub_part, w.slot_part, fault);
   else if (rec)
     raytrace_vjp_rec_kernel<LR_PROFILE_TNFW><<<(unsigned)nblk, kVjThreads, 0, s>>>(
-        rec, g, xi, p->n, p->sub, p->n_sub, P, dbeta, lens_part, sub_part, w.slot_part, fault);
+        rec, g, xi, p->n, p->sub, p->n_sub, P, bands, plan, dbeta, lens_part, sub_part, w.slot_part, fault);
   else if (p->profile == LR_PROFILE_POINT_MASS)
     raytrace_vjp_kernel<LR_PROFILE_POINT_MASS><<<(unsigned)nblk, kVjThreads, 0, s>>>(
-        L, G, g, xi, p->n, p->sub, p->n_sub, P, dbeta, lens_part, sub_part, w.slot_part);
+        L, G, g, xi, p->n, p->sub, p->n_sub, P, bands, plan, dbeta, lens_part, sub_part, w.slot_part);
   else
     raytrace_vjp_kernel<LR_PROFILE_TNFW><<<(unsigned)nblk, kVjThreads, 0, s>>>(
-        L, G, g, xi, p->n, p->sub, p->n_sub, P, dbeta, lens_part, sub_part, w.slot_part);
+        L, G, g, xi, p->n, p->sub, p->n_sub, P, bands, plan, dbeta, lens_part, sub_part, w.slot_part);
   LR_CHECK_CUDA(cudaGetLastError());
   ktimer_end(LR_KT_RAYTRACE_VJP, s);
   const int64_t warps = 7 + 4 * (int64_t)p->n_sub;
@@ -686,7 +961,7 @@ lr_status make_vjp_problem(const lr_points* p, const float2* dbeta, double* d_le
   if (st != LR_OK) return st;
   st = make_lens_grad_const(p->lens, &v.LG);
   if (st != LR_OK) return st;
-  const int64_t nblk = vjp_blocks(p->n);
+  const int64_t nblk = vjp_tiles(p->n);
   v.g = p->xy ? GridDev{} : grid_dev(p->grid);
   v.xi = reinterpret_cast<const float2*>(p->xy);
   v.n = p->n;
@@ -694,6 +969,7 @@ lr_status make_vjp_problem(const lr_points* p, const float2* dbeta, double* d_le
   v.n_sub = p->n_sub;
   v.profile = p->profile;
   v.phases = vjp_phases(p->n, p->n_sub);
+  v.bands = vjp_bands(nblk, p);
   v.dbeta = dbeta;
   const VjWs w = vjp_ws_layout(ws, p->n, p->n_sub);
   v.lens_part = w.lens_part;
