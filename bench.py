@@ -76,6 +76,14 @@ def vj_ser_lanes(k: int) -> float:
     return 20.3 + 2 * (k - 2)
 
 
+# The backward's local expansion of a far subhalo about a tile's centre: 36
+# terms of 40 FP32 operations (7 series terms of the coefficient, 4 real
+# parts of products with the tile's moments, the next power of u) per tile
+# and subhalo, whatever the tile's point count; its moments add about 31
+# operations per point and term, once per tile (not counted).
+VJ_EXP_LANES = 1470.0
+
+
 def _grid_axes(g):
     w, hgt = g.nx * g.ss, g.ny * g.ss
     h = g.pix / g.ss
@@ -84,21 +92,31 @@ def _grid_axes(g):
     return w, hgt, xs, ys
 
 
-def _degree_shares(p, boxes, counts, degrees) -> dict:
+def _degree_shares(p, boxes, counts, degrees, expand=False) -> dict:
     """Share of the point-subhalo pairs by the series degree that serves a
     CTA's whole box (x_lo, y_lo, x_hi, y_hi) of `counts` points; 0: the
-    closed forms."""
+    closed forms. With `expand`, the pairs of a far subhalo whose distance
+    from the box's centre is at least 12.5 half-diagonals go to the key
+    "expansion" (the ray-trace backward's local expansion)."""
     sub = p.sub.astype(np.float64)
     its2 = 1.0 / sub[:, 3] ** 2
     m = np.maximum(sub[:, 4] ** 2, 4.0)
     tot = {k: 0.0 for k, _ in degrees}
     tot[0] = 0.0
+    tot["expansion"] = 0.0
     for c in range(0, len(boxes), 1024):
         bx, cn = boxes[c:c + 1024], counts[c:c + 1024].astype(np.float64)
         dx = np.maximum(np.maximum(bx[:, 0, None] - sub[None, :, 0], sub[None, :, 0] - bx[:, 2, None]), 0.0)
         dy = np.maximum(np.maximum(bx[:, 1, None] - sub[None, :, 1], sub[None, :, 1] - bx[:, 3, None]), 0.0)
         x2 = (dx * dx + dy * dy) * its2[None, :] / m[None, :]
         left = np.ones(x2.shape, dtype=bool)
+        if expand:
+            hd2 = 0.25 * ((bx[:, 2] - bx[:, 0]) ** 2 + (bx[:, 3] - bx[:, 1]) ** 2)
+            cx = 0.5 * (bx[:, 0] + bx[:, 2])[:, None] - sub[None, :, 0]
+            cy = 0.5 * (bx[:, 1] + bx[:, 3])[:, None] - sub[None, :, 1]
+            hit = (x2 >= degrees[-1][1]) & (hd2[:, None] <= 0.0064 * (cx * cx + cy * cy)) & (cn[:, None] <= 2048)
+            tot["expansion"] += float((hit.sum(1) * cn).sum())
+            left &= ~hit
         for k, r2 in degrees:
             hit = left & (x2 >= r2)
             tot[k] += float((hit.sum(1) * cn).sum())
@@ -139,6 +157,25 @@ def vjp_bands(nblk: int, w: int, hgt: int) -> int:
     return best
 
 
+def vjp_phases(n: int, nblk: int, n_sub: int) -> int:
+    """Slots per subhalo of the ray-trace backward: 1 when n_sub slots waste
+    at most 5 % of the last 128 threads, else the P in [1, 8] whose n_sub P
+    wastes the fewest of them, keeping 128 points per slot (the local
+    expansion needs P = 1)."""
+    per = -(-n // nblk)
+    if -(-n_sub // 128) * 128 <= 1.05 * n_sub:
+        return 1
+    best, best_w = 1, float("inf")
+    for P in range(1, 9):
+        if P > 1 and per // P < 128:
+            break
+        sl = n_sub * P
+        w = (-(-sl // 128) * 128) / sl
+        if w < best_w - 1e-9:
+            best, best_w = P, w
+    return best
+
+
 def vjp_cost(p, nblk: int):
     """(MUFU, FP32 lanes) per point-subhalo pair of the ray-trace backward on
     a pixel grid, and the pairs' shares by series degree: nblk tiles (bands
@@ -158,14 +195,18 @@ def vjp_cost(p, nblk: int):
     rlo = np.where(one, u0 % rows, 0)
     rhi = np.where(one, (u1 - 1) % rows, rows - 1)
     boxes = np.stack([xs[col0], ys[row0 + rlo], xs[col1], ys[row0 + rhi]], 1)
-    sh = _degree_shares(p, boxes, u1 - u0, VJ_DEGREES)
-    mufu = sh[0] * VJ_MUFU + (1 - sh[0]) * SER_MUFU
-    lanes = sh[0] * VJ_LANES + sum(sh[k] * vj_ser_lanes(k) for k, _ in VJ_DEGREES)
+    npts = float(np.mean(u1 - u0))
+    sh = _degree_shares(p, boxes, u1 - u0, VJ_DEGREES, expand=vjp_phases(p.n, nblk, len(p.sub)) == 1)
+    mufu = sh[0] * VJ_MUFU + sum(sh[k] for k, _ in VJ_DEGREES) * SER_MUFU
+    lanes = (sh[0] * VJ_LANES + sum(sh[k] * vj_ser_lanes(k) for k, _ in VJ_DEGREES)
+             + sh["expansion"] * VJ_EXP_LANES / npts)
     return mufu, lanes, sh
 
 
 def _shares_text(sh: dict) -> str:
-    return ", ".join(f"y^{k}: {v:.3f}" for k, v in sh.items() if k) + f"; closed form: {sh[0]:.3f}"
+    ser = ", ".join(f"y^{k}: {v:.3f}" for k, v in sh.items() if isinstance(k, int) and k)
+    exp = f"local expansion: {sh['expansion']:.3f}, " if "expansion" in sh else ""
+    return exp + ser + f"; closed form: {sh[0]:.3f}"
 
 
 def vjp_tiles(dev, n: int) -> int:

@@ -30,11 +30,16 @@
 // tNFW subhalos whose far-field series radius (x >= 8 max(tau, 2)) clears
 // the bounding box of all of a tile's points sum by the series of G and of
 // x dG/dx (1 rsqrt and two short polynomials per pair) with no per-pair
-// test, with as few terms as the box's distance allows (vj_degree); the
-// others take the far-side closed form per pair and the general form for the
-// rare near pairs. The subhalos of a tile are ordered by that choice, fewest
-// terms first and the closed forms last (vj_sort, by the plan or by the CTA
-// itself), so that whole warps take one path.
+// test, with as few terms as the box's distance allows (vj_degree). Where
+// the tile is also small against its distance from the subhalo (half-
+// diagonal within 0.08 of it) and a tile is swept in one phase, the same
+// series is summed by its local expansion about the tile's centre
+// (vj_expand): the tile's gradient moments are formed once (vj_moments), and
+// each such subhalo costs a fixed 36 terms instead of a pass over the points.
+// The others take the far-side closed form per pair and the general form for
+// the rare near pairs. The subhalos of a tile are ordered by that choice,
+// the expansion first and the closed forms last (vj_sort, by the plan or by
+// the CTA itself), so that whole warps take one path.
 #include <math.h>
 
 #include "host.cuh"
@@ -48,9 +53,13 @@ constexpr int kVjWarps = kVjThreads / 32;
 constexpr int kVjChunk = 2048;    // points staged in shared memory at once
 constexpr int kVjMaxPhases = 8;
 constexpr int kVjFold = 32;       // point pairs summed plainly per slot before a Kahan fold
-constexpr int kVjMaxOrd = 4096;   // subhalo counts up to which a CTA orders its slots by series degree
+constexpr int kVjMaxOrd = 4096;   // subhalo counts up to which a CTA orders its slots by class (vj_sort)
 constexpr int kVjWaves = 8;       // large inputs: tiles per resident CTA slot
 constexpr int kVjTilePts = 512;   // ... while every tile keeps at least this many points
+constexpr int kVjExpN = 7;        // local expansion: terms delta^k conj(delta)^l with k + l <= kVjExpN
+constexpr int kVjExpTerms = (kVjExpN + 1) * (kVjExpN + 2) / 2;
+constexpr float kVjExpRatio2 = 0.0064f;  // (tile half-diagonal / distance)^2 up to which it serves (0.08^2)
+constexpr int kVjExpFlag = 16;           // class code: series degree | flag, the expansion serves the tile
 
 __device__ __forceinline__ double warp_sum_d(double v) {
 #pragma unroll
@@ -63,21 +72,19 @@ struct VjSmem {
   float4 grad[kVjChunk / 2];  // (G_x, G_x, G_y, G_y) of the same two points
   double lred[kVjWarps][7];
   unsigned short ord[kVjMaxOrd];  // slot subhalo -> subhalo, by series degree (vj_order)
-  unsigned char deg[kVjMaxOrd];   // series degree of each subhalo for the CTA's points (0: closed forms)
+  unsigned char deg[kVjMaxOrd];   // class of each subhalo for the tile (vj_class)
   float wbox[kVjWarps][4];        // per-warp bounds of the CTA's points
   float box[4];                   // x_lo, y_lo, x_hi, y_hi of the CTA's points
-  int cnt[4];                     // subhalos served by the series to y^3, y^4, y^5, y^7
+  float2 wm[3][kVjExpTerms];      // the tile's moments for the local expansion (vj_moments): W, W_x, W_y
 };
 
 // The optional plan of a launch (vjp_plan_kernel, vjp_rank_kernel): CTA b
-// takes tile perm[b] (the tiles heaviest first), whose subhalos in series
-// degree order are ord[tile n_sub ..], cnt[4 tile ..] of them served by the
-// series to y^3, y^4, y^5, y^7. All NULL: CTA b takes tile b and orders its
-// subhalos itself.
+// takes tile perm[b] (the tiles heaviest first), whose subhalos in the
+// order of vj_sort are ord[tile n_sub ..]. Both NULL: CTA b takes tile b and
+// orders its subhalos itself.
 struct VjPlan {
   const int* perm;
   const unsigned short* ord;
-  const int* cnt;
 };
 
 // One tNFW pair's terms of the four subhalo sums, for two points at once
@@ -290,6 +297,165 @@ __device__ __forceinline__ int vj_degree_box(const SubRec& h, const SubSer& q, c
   return vj_degree(__fmul_rn(fmaf(dx, dx, dy * dy), h.its2), fmaxf(h.tau2, 4.0f));
 }
 
+// ---------------------------------------------------------------------------
+// Local expansion of a far subhalo's deflection about a tile's centre.
+//
+// With z = xi - xi_h as a complex number, the far-field series gives
+//   alpha(z) = A sum_j q_j theta_s^(j+2) |z|^-(j+2) z
+//            = A theta_s^2 sum_j q_j (theta_s / |c|)^j conj(c)^-1
+//              (1 + delta/c)^(-j/2) (1 + conj(delta)/conj(c))^(-(j+2)/2)
+// about the tile's centre, z = c + delta. The binomial series of the two
+// factors converge for |delta| < |c|; truncated at k + l <= kVjExpN they
+// give alpha as a polynomial in delta and conj(delta) whose coefficients
+// depend on the subhalo alone:
+//   alpha(c + delta) = A theta_s^2 sum_{k,l} c_kl u^k conj(u)^(l+1) delta^k conj(delta)^l,
+//   c_kl = sum_j q_j (theta_s / |c|)^j C(-j/2, k) C(-(j+2)/2, l), u = 1/c.
+// The four gradient sums over the tile's points then need only the tile's
+// moments W_kl = sum_i conj(G_i) delta_i^k conj(delta_i)^l (vj_moments):
+//   sum_i G_i . alpha_i = Re sum_kl M_kl W_kl, with M_kl the coefficients,
+//   and d/dxi_x, d/dxi_y of delta^k conj(delta)^l give the moments
+//   W_x = k W_(k-1,l) + l W_(k,l-1), W_y = i (k W_(k-1,l) - l W_(k,l-1)).
+// With the tile's half-diagonal at most 0.08 |c| and kVjExpN = 7, the
+// truncation stays below 4e-9 of the sums of absolute terms (checked against
+// the analytic FP64 gradients for theta_s from 0.015 to 0.2 arcsec and
+// series degrees 3 to 7).
+
+// Generalised binomial coefficients C(-j/2, k) and C(-(j+2)/2, k), j < 8.
+struct VjBin {
+  float a[8][kVjExpN + 1];
+  float b[8][kVjExpN + 1];
+};
+
+constexpr VjBin vj_make_bin() {
+  VjBin t{};
+  for (int j = 0; j < 8; ++j) {
+    double ca = 1.0, cb = 1.0;
+    for (int k = 0; k <= kVjExpN; ++k) {
+      t.a[j][k] = (float)ca;
+      t.b[j][k] = (float)cb;
+      ca *= (-0.5 * j - k) / (k + 1.0);
+      cb *= (-0.5 * (j + 2) - k) / (k + 1.0);
+    }
+  }
+  return t;
+}
+
+__constant__ VjBin kVjBin = vj_make_bin();
+
+__device__ __forceinline__ float2 c2mul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+
+// Term index of delta^k conj(delta)^l: by total order s = k + l, then k.
+__device__ __forceinline__ int vj_term(int k, int l) { return (k + l) * (k + l + 1) / 2 + k; }
+
+// The class of a subhalo for a tile: its series degree (vj_degree_box), with
+// kVjExpFlag added where exp_ok and the tile's half-diagonal is within 0.08
+// of the distance from its centre.
+__device__ __forceinline__ int vj_class(const SubRec& h, const SubSer& q, const float* box, bool exp_ok) {
+  const int d = vj_degree_box(h, q, box);
+  if (d == 0 || !exp_ok) return d;
+  const float hx = 0.5f * (box[2] - box[0]), hy = 0.5f * (box[3] - box[1]);
+  const float cx = 0.5f * (box[0] + box[2]) - h.xh, cy = 0.5f * (box[1] + box[3]) - h.yh;
+  return fmaf(hx, hx, hy * hy) <= kVjExpRatio2 * fmaf(cx, cx, cy * cy) ? (d | kVjExpFlag) : d;
+}
+
+// The tile's moments about cen over its staged points (one chunk of cnt
+// points): W into sm.wm[0], W_x into sm.wm[1], W_y into sm.wm[2]. All
+// threads of the CTA take part; three threads per term sum a third of the
+// points each (Kahan-compensated), and the thirds are added in order.
+__device__ __forceinline__ void vj_moments(VjSmem& sm, int cnt, float2 cen) {
+  const int t = threadIdx.x;
+  if (t < 3 * kVjExpTerms) {
+    const int m = t % kVjExpTerms, part = t / kVjExpTerms;
+    int s = 0;
+    while ((s + 1) * (s + 2) / 2 <= m) ++s;
+    const int k = m - s * (s + 1) / 2, l = s - k;
+    float2 acc = make_float2(0.f, 0.f), cmp = make_float2(0.f, 0.f);
+    for (int i = part; i < cnt; i += 3) {
+      const float4 P = sm.pos[i >> 1], D = sm.grad[i >> 1];
+      const bool b = i & 1;
+      const float2 d = make_float2((b ? P.y : P.x) - cen.x, (b ? P.w : P.z) - cen.y);
+      float2 pw = make_float2(1.f, 0.f);
+      for (int a = 0; a < k; ++a) pw = c2mul(pw, d);
+      for (int a = 0; a < l; ++a) pw = c2mul(pw, make_float2(d.x, -d.y));
+      const float2 term = c2mul(make_float2(b ? D.y : D.x, -(b ? D.w : D.z)), pw);
+      vj_kahan(acc.x, cmp.x, term.x);
+      vj_kahan(acc.y, cmp.y, term.y);
+    }
+    sm.wm[part][m] = make_float2(acc.x - cmp.x, acc.y - cmp.y);
+  }
+  __syncthreads();
+  if (t < kVjExpTerms) {
+    const float2 a = sm.wm[0][t], b = sm.wm[1][t], c = sm.wm[2][t];
+    sm.wm[0][t] = make_float2(a.x + b.x + c.x, a.y + b.y + c.y);
+  }
+  __syncthreads();
+  if (t < kVjExpTerms) {
+    int s = 0;
+    while ((s + 1) * (s + 2) / 2 <= t) ++s;
+    const int k = t - s * (s + 1) / 2, l = s - k;
+    const float2 wa = k > 0 ? sm.wm[0][vj_term(k - 1, l)] : make_float2(0.f, 0.f);
+    const float2 wb = l > 0 ? sm.wm[0][vj_term(k, l - 1)] : make_float2(0.f, 0.f);
+    const float fk = (float)k, fl = (float)l;
+    sm.wm[1][t] = make_float2(fmaf(fk, wa.x, fl * wb.x), fmaf(fk, wa.y, fl * wb.y));
+    // i (k W_(k-1,l) - l W_(k,l-1))
+    sm.wm[2][t] = make_float2(-fmaf(fk, wa.y, -fl * wb.y), fmaf(fk, wa.x, -fl * wb.x));
+  }
+  __syncthreads();
+}
+
+// The tile's four subhalo sums by the local expansion: dL/d(x_h, y_h,
+// kappa_s, theta_s) of one tNFW subhalo (K: its series degree for the tile),
+// from the tile's moments about cen. The term loops stay rolled: unrolled
+// inside the sweep's kernel they spill, and a separate (not inlined) unrolled
+// function measured slower.
+__device__ __forceinline__ float4 vj_expand(const SubRec& rec, const SubSer& q, float kappa, float ts, int K,
+                                            float2 cen, const VjSmem& sm) {
+  const float2 c = make_float2(cen.x - rec.xh, cen.y - rec.yh);
+  const float ir2 = 1.0f / fmaf(c.x, c.x, c.y * c.y);
+  const float2 u = make_float2(c.x * ir2, -c.y * ir2), ub = make_float2(u.x, -u.y);
+  const float yc = ts * sqrtf(ir2);
+  float qy[8];
+  float yj = 1.f;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    qy[j] = (j == 1 || j > K) ? 0.f : q.q[j] * yj;
+    yj *= yc;
+  }
+  // Q = u^k conj(u)^(l+1) for the terms of total order s = k + l: from
+  // conj(u)^(s+1) at k = 0, each step in k times u / conj(u) = c^2 / |c|^2
+  const float2 rot = make_float2((c.x * c.x - c.y * c.y) * ir2, 2.0f * c.x * c.y * ir2);
+  float2 us = ub;  // conj(u)^(s+1)
+  float L = 0.f, Lt = 0.f, X = 0.f, Y = 0.f;
+#pragma unroll 1
+  for (int s = 0; s <= kVjExpN; ++s) {
+    float2 Q = us;
+#pragma unroll 1
+    for (int k = 0; k <= s; ++k) {
+      const int l = s - k, m = s * (s + 1) / 2 + k;
+      float ckl = 0.f, ctl = 0.f;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        if (j == 1) continue;
+        const float w = qy[j] * (kVjBin.a[j][k] * kVjBin.b[j][l]);
+        ckl += w;
+        ctl = fmaf(w, (float)(j + 2), ctl);
+      }
+      const float2 W = sm.wm[0][m], Wx = sm.wm[1][m], Wy = sm.wm[2][m];
+      const float rw = fmaf(Q.x, W.x, -Q.y * W.y);
+      L = fmaf(ckl, rw, L);
+      Lt = fmaf(ctl, rw, Lt);
+      X = fmaf(ckl, fmaf(Q.x, Wx.x, -Q.y * Wx.y), X);
+      Y = fmaf(ckl, fmaf(Q.x, Wy.x, -Q.y * Wy.y), Y);
+      Q = c2mul(Q, rot);
+    }
+    us = c2mul(us, ub);
+  }
+  const float sc = rec.A * ts * ts;
+  return make_float4(sc * X, sc * Y, -sc * L / kappa, -sc * Lt / ts);
+}
+
 // The CTA's points: u in [u0, u1) indexes explicit points directly; on a
 // pixel grid it indexes the points of the band of rows [row0, row0 + rows)
 // in column-major order.
@@ -360,48 +526,72 @@ __device__ __forceinline__ void vj_box(const GridDev& g, const float2* __restric
   __syncthreads();
 }
 
-// FP32 lanes per pair of a subhalo sum by the series of degree K (0: the
-// closed forms): the weight of a tile's work.
-__device__ __forceinline__ float vj_cost(int K) { return K ? 20.3f + 2.0f * (float)(K - 2) : 50.3f; }
+// The sort key of a class: every expansion class (any series degree) alike.
+__device__ __forceinline__ int vj_cls_key(int c) { return (c & kVjExpFlag) ? kVjExpFlag : c; }
 
-// The tNFW subhalos (n_sub <= kVjMaxOrd) by the series degree that serves
-// every point of the box, fewest terms first, each degree in index order,
-// those that need the closed forms last: ord[rank] = subhalo, cnt[0..3] the
-// numbers served by the series to y^3, y^4, y^5, y^7 (shared or global
-// memory). deg: per-subhalo scratch in shared memory. Returns the thread's
-// share of the tile's work per point (sum of vj_cost over its subhalos).
-__device__ __forceinline__ float vj_sort(const float* __restrict__ sub, int n_sub, const float* box,
-                                         unsigned char* deg, unsigned short* ord, int* cnt) {
+// FP32 lanes per point of a subhalo's sums for a tile of npts points, by its
+// class (vj_class): the series of degree K, the closed forms (0), or the
+// local expansion (about 1,600 lanes per tile): the weight of a tile's work.
+__device__ __forceinline__ float vj_cost(int cls, int npts) {
+  if (cls & kVjExpFlag) return 1600.0f / (float)max(npts, 1);
+  return cls ? 20.3f + 2.0f * (float)(cls - 2) : 50.3f;
+}
+
+// The tNFW subhalos (n_sub <= kVjMaxOrd) by their class for the tile's box
+// (vj_class): those served by the local expansion first, then by the series
+// of degree 3, 4, 5, 7, each class in index order, those that need the
+// closed forms last: ord[rank] = subhalo (shared or global memory). cls:
+// per-subhalo scratch in shared memory. Returns the thread's share of the
+// tile's work per point (sum of vj_cost over its subhalos).
+__device__ __forceinline__ float vj_sort(const float* __restrict__ sub, int n_sub, const float* box, bool exp_ok,
+                                         int npts, unsigned char* cls, unsigned short* ord) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   float cost = 0.f;
   for (int h = tid; h < n_sub; h += kVjThreads) {
     const SubRec r = prep_sub(sub + 5 * (int64_t)h, LR_PROFILE_TNFW);
-    const int d = vj_degree_box(r, prep_series(r, LR_PROFILE_TNFW), box);
-    deg[h] = (unsigned char)d;
-    cost += vj_cost(d);
+    const int d = vj_class(r, prep_series(r, LR_PROFILE_TNFW), box, exp_ok);
+    cls[h] = (unsigned char)d;
+    cost += vj_cost(d, npts);
   }
   __syncthreads();
-  if (warp == 0) {  // stable partition by degree: 3, 4, 5, 7, then 0
-    int nf = 0;
-    for (int pass = 0; pass < 5; ++pass) {
-      const int want = pass < 4 ? (pass < 3 ? 3 + pass : 7) : 0;
-      const int nf0 = nf;
-      for (int b = 0; b < n_sub; b += 32) {
-        const bool f = b + lane < n_sub && deg[b + lane] == want;
-        const unsigned m = __ballot_sync(0xffffffffu, f);
-        if (f) ord[nf + __popc(m & ((1u << lane) - 1u))] = (unsigned short)(b + lane);
-        nf += __popc(m);
-      }
-      if (pass < 4 && lane == 0) cnt[pass] = nf - nf0;
+  // stable counting sort by class: the expansion (any series degree), then
+  // the series of degree 3, 4, 5, 7, then 0. Warp w takes the
+  // subhalos [w q, (w + 1) q), q = n_sub / warps rounded up to 32: it counts
+  // its subhalos per class, then scatters them after the classes before
+  // theirs and the warps before it.
+  constexpr int kClasses = 6;
+  const int qn = (n_sub + kVjWarps * 32 - 1) / (kVjWarps * 32) * 32;
+  const int h0 = warp * qn, h1 = min(n_sub, h0 + qn);
+  __shared__ int wcnt[kVjWarps][kClasses];
+#pragma unroll 1
+  for (int pass = 0; pass < kClasses; ++pass) {
+    const int want = pass == 0 ? kVjExpFlag : (pass < 4 ? 2 + pass : (pass == 4 ? 7 : 0));
+    int nc = 0;
+    for (int b = h0; b < h1; b += 32)
+      nc += __popc(__ballot_sync(0xffffffffu, b + lane < h1 && vj_cls_key(cls[b + lane]) == want));
+    if (lane == 0) wcnt[warp][pass] = nc;
+  }
+  __syncthreads();
+  int nf = 0;
+#pragma unroll 1
+  for (int pass = 0; pass < kClasses; ++pass) {
+    const int want = pass == 0 ? kVjExpFlag : (pass < 4 ? 2 + pass : (pass == 4 ? 7 : 0));
+    int tot = 0, before = 0;
+    for (int w = 0; w < kVjWarps; ++w) {
+      tot += wcnt[w][pass];
+      if (w < warp) before += wcnt[w][pass];
     }
+    int pos = nf + before;
+    for (int b = h0; b < h1; b += 32) {
+      const bool f = b + lane < h1 && vj_cls_key(cls[b + lane]) == want;
+      const unsigned m = __ballot_sync(0xffffffffu, f);
+      if (f) ord[pos + __popc(m & ((1u << lane) - 1u))] = (unsigned short)(b + lane);
+      pos += __popc(m);
+    }
+    nf += tot;
   }
   __syncthreads();
   return cost;
-}
-
-// The series degree of the subhalo at rank hs of the degree order.
-__device__ __forceinline__ int vj_rank_degree(int hs, int c3, int c4, int c5, int c7) {
-  return hs < c3 ? 3 : hs < c3 + c4 ? 4 : hs < c3 + c4 + c5 ? 5 : hs < c3 + c4 + c5 + c7 ? 7 : 0;
 }
 
 template <int PROFILE>
@@ -423,24 +613,18 @@ __device__ __forceinline__ void vjp_body(const LensConst& L, const LensGradConst
   const int ngroups = slots > 0 ? (slots + kVjThreads - 1) / kVjThreads : 1;
   float la[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   int staged = -1;
-  // tNFW: the subhalos in series degree order, from the plan or sorted here
-  // for the tile's box; more than kVjMaxOrd subhalos: index order, each
-  // slot choosing its degree for the box
+  // tNFW: the subhalos in the order of their classes for the tile's box
+  // (vj_sort), from the plan or sorted here; more than kVjMaxOrd subhalos:
+  // index order. Each slot finds its subhalo's class itself (vj_class). The
+  // local expansion needs one phase and one staged chunk.
   const bool ordered = PROFILE == LR_PROFILE_TNFW && n_sub > 0 && n_sub <= kVjMaxOrd;
+  const bool exp_ok = ordered && P == 1 && nchunks == 1;
   const unsigned short* ord = plan.ord ? plan.ord + tile * n_sub : sm.ord;
-  int c3 = 0, c4 = 0, c5 = 0, c7 = 0;
   if (PROFILE == LR_PROFILE_TNFW) {
-    if (plan.ord) {
-      const int* c = plan.cnt + 4 * tile;
-      c3 = c[0], c4 = c[1], c5 = c[2], c7 = c[3];
-    } else {
-      vj_box(g, xi, mp, sm.wbox, sm.box);
-      if (ordered) {
-        vj_sort(sub, n_sub, sm.box, sm.deg, sm.ord, sm.cnt);
-        c3 = sm.cnt[0], c4 = sm.cnt[1], c5 = sm.cnt[2], c7 = sm.cnt[3];
-      }
-    }
+    vj_box(g, xi, mp, sm.wbox, sm.box);
+    if (ordered && !plan.ord) vj_sort(sub, n_sub, sm.box, exp_ok, (int)(p1 - p0), sm.deg, sm.ord);
   }
+  const float2 cen = make_float2(0.5f * (sm.box[0] + sm.box[2]), 0.5f * (sm.box[1] + sm.box[3]));
 
   for (int grp = 0; grp < ngroups; ++grp) {
     const int slot = grp * kVjThreads + tid;
@@ -450,14 +634,14 @@ __device__ __forceinline__ void vjp_body(const LensConst& L, const LensGradConst
     const int h = ordered ? (int)ord[hs] : hs;
     SubRec rec{};
     SubSer q{};
-    int deg = 0;  // series degree serving all of the CTA's points (0: closed forms)
+    int deg = 0;  // class for the tile (vj_class): series degree, 0 the closed forms, | kVjExpFlag
     float2 ex = make_float2(0.f, 0.f);  // tNFW: (4T, 1/theta_s); point mass: (0, theta_pm)
     if (own) {
       const float* rr = sub + 5 * (int64_t)h;
       rec = prep_sub(rr, PROFILE);
       if (PROFILE == LR_PROFILE_TNFW) {
         q = prep_series(rec, PROFILE);
-        deg = ordered ? vj_rank_degree(hs, c3, c4, c5, c7) : vj_degree_box(rec, q, sm.box);
+        deg = vj_class(rec, q, sm.box, exp_ok);
       }
       if (PROFILE == LR_PROFILE_POINT_MASS) {
         ex = make_float2(0.f, __ldg(rr + 2));
@@ -500,8 +684,18 @@ __device__ __forceinline__ void vjp_body(const LensConst& L, const LensGradConst
         }
         __syncthreads();
         staged = ch;
+        if (exp_ok && grp == 0) vj_moments(sm, cnt, cen);  // uniform over the CTA
       }
-      if (own) {
+      if (own && (deg & kVjExpFlag)) {
+        // the local expansion about the tile's centre: the four sums whole
+        const float* rr = sub + 5 * (int64_t)h;
+        const float kap = __ldg(rr + 2), ts = __ldg(rr + 3);
+        const float4 e = vj_expand(rec, q, kap, ts, deg & (kVjExpFlag - 1), cen, sm);
+        sc[0] = e.x;
+        sc[1] = e.y;
+        sc[2] = e.z;
+        sc[3] = e.w;
+      } else if (own) {
         const int np = (cnt + 1) >> 1;
         if (P == 1) {
           switch (deg) {
@@ -541,9 +735,10 @@ __device__ __forceinline__ void vjp_body(const LensConst& L, const LensGradConst
       }
     }
     if (own) {
+      const bool expd = (deg & kVjExpFlag) != 0;  // sc holds the expansion's sums, already scaled
 #pragma unroll
       for (int v = 0; v < 4; ++v) {
-        const float x = __fmul_rn(sc[v] - cc[v], vj_scale<PROFILE>(rec, ex, v));
+        const float x = expd ? sc[v] : __fmul_rn(sc[v] - cc[v], vj_scale<PROFILE>(rec, ex, v));
         if (P == 1)
           sub_part[((int64_t)h * 4 + v) * nblk + blk] = x;  // [value][CTA], h the subhalo itself
         else
@@ -611,19 +806,23 @@ __global__ void __launch_bounds__(kVjThreads, 4) raytrace_vjp_rec_kernel(const L
 }
 
 // The plan of a tNFW launch with more tiles than resident CTA slots: one
-// CTA per tile sorts the subhalos by the series degree that serves the
-// tile's box (vj_sort) into ord and cnt, and writes the tile's work
-// (FP32 lanes over its point-subhalo pairs) to weight.
+// CTA per tile sorts the subhalos by their class for the tile's box
+// (vj_sort) into ord, and writes the tile's work (FP32 lanes over its
+// point-subhalo pairs, the expansion's per tile) to weight.
 __global__ void __launch_bounds__(kVjThreads) vjp_plan_kernel(GridDev g, const float2* __restrict__ xi, int64_t n,
-                                                              const float* __restrict__ sub, int n_sub, int bands,
-                                                              int64_t ntiles, unsigned short* __restrict__ ord,
-                                                              int* __restrict__ cnt, float* __restrict__ weight) {
+                                                              const float* __restrict__ sub, int n_sub, int P,
+                                                              int bands, int64_t ntiles,
+                                                              unsigned short* __restrict__ ord,
+                                                              float* __restrict__ weight) {
   __shared__ float wbox[kVjWarps][4], box[4], wsum[kVjWarps];
-  __shared__ unsigned char deg[kVjMaxOrd];
+  __shared__ unsigned char cls[kVjMaxOrd];
   const int64_t tile = blockIdx.x;
   const VjMap mp = vj_map(g, xi == nullptr, n, bands, tile, ntiles);
   vj_box(g, xi, mp, wbox, box);
-  float c = vj_sort(sub, n_sub, box, deg, ord + tile * n_sub, cnt + 4 * tile);
+  const int npts = (int)(mp.u1 - mp.u0);
+  // the same choice as the sweep's (vjp_body): one phase and one staged chunk
+  const bool exp_ok = P == 1 && npts > 0 && npts <= kVjChunk;
+  float c = vj_sort(sub, n_sub, box, exp_ok, npts, cls, ord + tile * n_sub);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
   if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = c;
@@ -714,12 +913,16 @@ static bool vjp_planned(int64_t ntiles, const lr_points* p) {
   return p->profile == LR_PROFILE_TNFW && plan_fits(ntiles, p->n_sub);
 }
 
-// Phases P of the subhalo sums: the P in [1, kVjMaxPhases] whose slot count
-// n_sub P wastes the fewest threads of the last group of kVjThreads (the
-// smallest such P), keeping at least 128 points per slot.
+// Phases P of the subhalo sums: 1 when n_sub slots waste at most 5 % of the
+// last group of kVjThreads (one phase sweeps with a constant stride and
+// allows the local expansion), else the P in [1, kVjMaxPhases] whose slot
+// count n_sub P wastes the fewest threads of the last group (the smallest
+// such P), keeping at least 128 points per slot.
 int vjp_phases(int64_t n, int32_t n_sub) {
   if (n_sub <= 0 || n <= 0) return 1;
   const int64_t per_cta = (n + vjp_tiles(n) - 1) / vjp_tiles(n);
+  const int64_t pad1 = ((int64_t)n_sub + kVjThreads - 1) / kVjThreads * kVjThreads;
+  if ((double)pad1 <= 1.05 * (double)n_sub) return 1;
   int best = 1;
   double best_w = 1e30;
   for (int P = 1; P <= kVjMaxPhases; ++P) {
@@ -848,14 +1051,13 @@ lr_status make_lens_grad_const(const lr_lens* lens, LensGradConst* out) {
 
 // Workspace: per-tile lens partials [tile][7] (FP64), subhalo partials
 // [4 n_sub][CTA], with P > 1 the slot sums [CTA][n_sub P][4], and where a
-// plan fits (plan_fits) its subhalo orders [tile][n_sub] (16 bit), degree
-// counts [tile][4], tile weights and the permutation of the tiles.
+// plan fits (plan_fits) its subhalo orders [tile][n_sub] (16 bit), tile
+// weights and the permutation of the tiles.
 struct VjWs {
   double* lens_part;
   float* sub_part;
   float* slot_part;
   unsigned short* ord;
-  int* cnt;
   float* weight;
   int* perm;
   size_t bytes;
@@ -869,7 +1071,6 @@ static VjWs vjp_ws_layout(void* ws, int64_t n, int32_t n_sub) {
   const size_t b_sub = align256(sizeof(float) * 4 * (size_t)n_sub * (size_t)nt);
   const size_t b_slot = P > 1 ? align256(sizeof(float) * 4 * (size_t)n_sub * P * (size_t)nt) : 0;
   const size_t b_ord = plan ? align256(sizeof(unsigned short) * (size_t)n_sub * (size_t)nt) : 0;
-  const size_t b_cnt = plan ? align256(sizeof(int) * 4 * (size_t)nt) : 0;
   const size_t b_w = plan ? align256(sizeof(float) * (size_t)nt) : 0;
   const size_t b_perm = plan ? align256(sizeof(int) * (size_t)nt) : 0;
   char* c = static_cast<char*>(ws);
@@ -884,7 +1085,6 @@ static VjWs vjp_ws_layout(void* ws, int64_t n, int32_t n_sub) {
   w.sub_part = reinterpret_cast<float*>(at(b_sub));
   w.slot_part = reinterpret_cast<float*>(at(b_slot));
   w.ord = reinterpret_cast<unsigned short*>(at(b_ord));
-  w.cnt = reinterpret_cast<int*>(at(b_cnt));
   w.weight = reinterpret_cast<float*>(at(b_w));
   w.perm = reinterpret_cast<int*>(at(b_perm));
   w.bytes = off;
@@ -921,13 +1121,13 @@ lr_status launch_raytrace_vjp(const lr_points* p, const float2* dbeta, double* d
   LR_REQUIRE(fault != nullptr, "could not resolve the device fault word");
   VjPlan plan{};
   if (vjp_planned(nblk, p)) {
-    vjp_plan_kernel<<<(unsigned)nblk, kVjThreads, 0, s>>>(g, xi, p->n, p->sub, p->n_sub, bands, nblk, w.ord, w.cnt,
+    vjp_plan_kernel<<<(unsigned)nblk, kVjThreads, 0, s>>>(g, xi, p->n, p->sub, p->n_sub, P, bands, nblk, w.ord,
                                                           w.weight);
     LR_CHECK_CUDA(cudaGetLastError());
     vjp_rank_kernel<<<(unsigned)((nblk + 3) / 4), 128, sizeof(float) * (size_t)nblk, s>>>(w.weight, (int)nblk,
                                                                                           w.perm);
     LR_CHECK_CUDA(cudaGetLastError());
-    plan = VjPlan{w.perm, w.ord, w.cnt};
+    plan = VjPlan{w.perm, w.ord};
   }
   ktimer_begin(LR_KT_RAYTRACE_VJP, s);
   if (rec && p->profile == LR_PROFILE_POINT_MASS)

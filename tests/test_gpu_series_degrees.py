@@ -4,7 +4,8 @@ A CTA sums a subhalo by the terms of its far-field series up to y^K (y =
 1/x, x = R / theta_s) when the whole bounding box of the CTA's points lies
 beyond that degree's radius: the forward from x = 6, 8, 18, 32, 80
 max(tau, 2) with K = 9, 7, 5, 4, 3, the backward from 8, 18, 32, 80 with
-K = 7, 5, 4, 3. Here one heavy subhalo sits at the origin and a small image
+K = 7, 5, 4, 3. Where the tile is small against its distance, the backward
+sums the same series by its local expansion about the tile's centre. Here one heavy subhalo sits at the origin and a small image
 grid lies wholly inside one distance band at a time; the main deflector is
 negligible (theta_E = 1e-9) and the shear zero, so every deflection is the
 subhalo's. The FP64 oracle evaluates the closed form (Baltz, Marshall & Oguri
@@ -54,9 +55,14 @@ def test_forward_series_degree(orc, cx):
     assert err.max() <= 1.5e-6, f"max relative deflection error {err.max():.3e}"
 
 
+@pytest.mark.parametrize("copies", [1, 4097])
 @pytest.mark.parametrize("cx", CENTRES)
-def test_vjp_series_degree(orc, cx):
+def test_vjp_series_degree(orc, cx, copies):
+    """One subhalo: the backward's local expansion about each tile's centre
+    serves every band but the nearest; 4097 copies of it (more than a tile
+    orders): every pair takes the series or the closed forms directly."""
     g, lens, sub = setup(cx)
+    sub = np.repeat(sub, copies, axis=0)
     xi = orc.grid_points(*g.astuple())
     rng = np.random.default_rng(3)
     db = rng.uniform(0.5, 1.5, (g.n, 2)).astype(np.float32)
