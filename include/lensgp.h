@@ -611,10 +611,18 @@ lr_status lr_matvec_bwd_workspace_size(const lr_points* query, const lr_points* 
                                        const lr_grads* grads, size_t* bytes);
 
 /*
- * Ray-trace backward alone: given d_beta = dL/dbeta (device float[n][2]) for
- * the points of `pts` (which must carry a lens), writes d_lens (double[7],
- * dL/d(x0, y0, q, phi, theta_e, g1, g2)) and d_sub (double[S][4]); either may
- * be NULL. Workspace of lr_raytrace_vjp_workspace_size() bytes.
+ * Ray-trace backward alone (the vector-Jacobian product of the raytracing
+ * equation beta = xi - alpha(xi), Sec. 2.1, with the deflectors of Sec. 2.2):
+ * given d_beta = dL/dbeta (device float[n][2]) for the points of `pts` (which
+ * must carry a lens), writes d_lens (double[7], dL/d(x0, y0, q, phi, theta_e,
+ * g1, g2)) and d_sub (double[S][4], dL/d(x_h, y_h, kappa_s, theta_s), or
+ * (x_h, y_h, theta_pm, -) for point masses); either may be NULL. Workspace of
+ * lr_raytrace_vjp_workspace_size() bytes, 256-byte aligned, caller-owned.
+ * The points are cut into tiles; a tNFW subhalo far from a tile is summed by
+ * its far-field series, or by that series' local expansion about the tile's
+ * centre, within 4e-9 of the sums of absolute terms, and per-tile partials
+ * are added in a fixed order (deterministic). Asynchronous on `stream`;
+ * LR_ERR_INVALID_ARG for a missing lens, misaligned or short buffers.
  */
 lr_status lens_raytrace_vjp(const lr_points* pts, const float* d_beta, double* d_lens, double* d_sub,
                             void* workspace, size_t workspace_bytes, lr_stream stream);
