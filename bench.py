@@ -76,12 +76,13 @@ def vj_ser_lanes(k: int) -> float:
     return 20.3 + 2 * (k - 2)
 
 
-# The backward's local expansion of a far subhalo about a tile's centre: 36
-# terms of 40 FP32 operations (7 series terms of the coefficient, 4 real
-# parts of products with the tile's moments, the next power of u) per tile
-# and subhalo, whatever the tile's point count; its moments add about 31
-# operations per point and term, once per tile (not counted).
-VJ_EXP_LANES = 1470.0
+# The backward's local expansion of a far subhalo about a tile's centre: 15
+# to 36 terms (by the tile's size against its distance) of 40 FP32
+# operations each (7 series terms of the coefficient, 4 real parts of
+# products with the tile's moments, the next power of u) and 30 to set up,
+# per tile and subhalo, whatever the tile's point count; its moments add
+# about 31 operations per point and term, once per tile (not counted).
+VJ_EXP_LANES_PER_TERM = 40.0
 
 
 def _grid_axes(g):
@@ -104,6 +105,7 @@ def _degree_shares(p, boxes, counts, degrees, expand=False) -> dict:
     tot = {k: 0.0 for k, _ in degrees}
     tot[0] = 0.0
     tot["expansion"] = 0.0
+    exp_lanes = 0.0
     for c in range(0, len(boxes), 1024):
         bx, cn = boxes[c:c + 1024], counts[c:c + 1024].astype(np.float64)
         dx = np.maximum(np.maximum(bx[:, 0, None] - sub[None, :, 0], sub[None, :, 0] - bx[:, 2, None]), 0.0)
@@ -114,8 +116,13 @@ def _degree_shares(p, boxes, counts, degrees, expand=False) -> dict:
             hd2 = 0.25 * ((bx[:, 2] - bx[:, 0]) ** 2 + (bx[:, 3] - bx[:, 1]) ** 2)
             cx = 0.5 * (bx[:, 0] + bx[:, 2])[:, None] - sub[None, :, 0]
             cy = 0.5 * (bx[:, 1] + bx[:, 3])[:, None] - sub[None, :, 1]
-            hit = (x2 >= degrees[-1][1]) & (hd2[:, None] <= 0.0064 * (cx * cx + cy * cy)) & (cn[:, None] <= 2048)
+            c2 = cx * cx + cy * cy
+            hit = (x2 >= degrees[-1][1]) & (hd2[:, None] <= 0.0064 * c2) & (cn[:, None] <= 2048)
             tot["expansion"] += float((hit.sum(1) * cn).sum())
+            # terms of the expansion's order: 15, 21, 28 or 36 for (half-diagonal / |c|) up to 0.01, 0.03, 0.05, 0.08
+            r2 = hd2[:, None] / c2
+            terms = np.where(r2 <= 1e-4, 15, np.where(r2 <= 9e-4, 21, np.where(r2 <= 2.5e-3, 28, 36)))
+            exp_lanes += float(np.sum(np.where(hit, VJ_EXP_LANES_PER_TERM * terms + 30.0, 0.0)))
             left &= ~hit
         for k, r2 in degrees:
             hit = left & (x2 >= r2)
@@ -123,7 +130,9 @@ def _degree_shares(p, boxes, counts, degrees, expand=False) -> dict:
             left &= ~hit
         tot[0] += float((left.sum(1) * cn).sum())
     n = float(counts.sum()) * len(sub)
-    return {k: v / n for k, v in tot.items()}
+    out = {k: v / n for k, v in tot.items()}
+    out["expansion_lanes"] = exp_lanes / n
+    return out
 
 
 def raytrace_cost(p):
@@ -195,11 +204,9 @@ def vjp_cost(p, nblk: int):
     rlo = np.where(one, u0 % rows, 0)
     rhi = np.where(one, (u1 - 1) % rows, rows - 1)
     boxes = np.stack([xs[col0], ys[row0 + rlo], xs[col1], ys[row0 + rhi]], 1)
-    npts = float(np.mean(u1 - u0))
     sh = _degree_shares(p, boxes, u1 - u0, VJ_DEGREES, expand=vjp_phases(p.n, nblk, len(p.sub)) == 1)
     mufu = sh[0] * VJ_MUFU + sum(sh[k] for k, _ in VJ_DEGREES) * SER_MUFU
-    lanes = (sh[0] * VJ_LANES + sum(sh[k] * vj_ser_lanes(k) for k, _ in VJ_DEGREES)
-             + sh["expansion"] * VJ_EXP_LANES / npts)
+    lanes = (sh[0] * VJ_LANES + sum(sh[k] * vj_ser_lanes(k) for k, _ in VJ_DEGREES) + sh["expansion_lanes"])
     return mufu, lanes, sh
 
 

@@ -315,10 +315,11 @@ __device__ __forceinline__ int vj_degree_box(const SubRec& h, const SubSer& q, c
 //   sum_i G_i . alpha_i = Re sum_kl M_kl W_kl, with M_kl the coefficients,
 //   and d/dxi_x, d/dxi_y of delta^k conj(delta)^l give the moments
 //   W_x = k W_(k-1,l) + l W_(k,l-1), W_y = i (k W_(k-1,l) - l W_(k,l-1)).
-// With the tile's half-diagonal at most 0.08 |c| and kVjExpN = 7, the
-// truncation stays below 4e-9 of the sums of absolute terms (checked against
-// the analytic FP64 gradients for theta_s from 0.015 to 0.2 arcsec and
-// series degrees 3 to 7).
+// The order of the truncation follows the ratio of the tile's half-diagonal
+// to |c|: 4 up to 0.01, 5 up to 0.03, 6 up to 0.05, 7 (kVjExpN) up to 0.08.
+// Each keeps the truncation below 4e-9 of the sums of absolute terms
+// (checked against the analytic FP64 gradients for theta_s from 0.015 to
+// 0.2 arcsec and series degrees 3 to 7).
 
 // Generalised binomial coefficients C(-j/2, k) and C(-(j+2)/2, k), j < 8.
 struct VjBin {
@@ -411,9 +412,11 @@ __device__ __forceinline__ void vj_moments(VjSmem& sm, int cnt, float2 cen) {
 // inside the sweep's kernel they spill, and a separate (not inlined) unrolled
 // function measured slower.
 __device__ __forceinline__ float4 vj_expand(const SubRec& rec, const SubSer& q, float kappa, float ts, int K,
-                                            float2 cen, const VjSmem& sm) {
+                                            float2 cen, float hd2, const VjSmem& sm) {
   const float2 c = make_float2(cen.x - rec.xh, cen.y - rec.yh);
-  const float ir2 = 1.0f / fmaf(c.x, c.x, c.y * c.y);
+  const float r2 = fmaf(c.x, c.x, c.y * c.y), ir2 = 1.0f / r2;
+  // the truncation order for (half-diagonal / |c|)^2 = hd2 / r2
+  const int nmax = hd2 <= 1e-4f * r2 ? 4 : hd2 <= 9e-4f * r2 ? 5 : hd2 <= 2.5e-3f * r2 ? 6 : kVjExpN;
   const float2 u = make_float2(c.x * ir2, -c.y * ir2), ub = make_float2(u.x, -u.y);
   const float yc = ts * sqrtf(ir2);
   float qy[8];
@@ -429,7 +432,7 @@ __device__ __forceinline__ float4 vj_expand(const SubRec& rec, const SubSer& q, 
   float2 us = ub;  // conj(u)^(s+1)
   float L = 0.f, Lt = 0.f, X = 0.f, Y = 0.f;
 #pragma unroll 1
-  for (int s = 0; s <= kVjExpN; ++s) {
+  for (int s = 0; s <= nmax; ++s) {
     float2 Q = us;
 #pragma unroll 1
     for (int k = 0; k <= s; ++k) {
@@ -531,7 +534,8 @@ __device__ __forceinline__ int vj_cls_key(int c) { return (c & kVjExpFlag) ? kVj
 
 // FP32 lanes per point of a subhalo's sums for a tile of npts points, by its
 // class (vj_class): the series of degree K, the closed forms (0), or the
-// local expansion (about 1,600 lanes per tile): the weight of a tile's work.
+// local expansion (up to about 1,600 lanes per tile): the weight of a tile's
+// work.
 __device__ __forceinline__ float vj_cost(int cls, int npts) {
   if (cls & kVjExpFlag) return 1600.0f / (float)max(npts, 1);
   return cls ? 20.3f + 2.0f * (float)(cls - 2) : 50.3f;
@@ -625,6 +629,8 @@ __device__ __forceinline__ void vjp_body(const LensConst& L, const LensGradConst
     if (ordered && !plan.ord) vj_sort(sub, n_sub, sm.box, exp_ok, (int)(p1 - p0), sm.deg, sm.ord);
   }
   const float2 cen = make_float2(0.5f * (sm.box[0] + sm.box[2]), 0.5f * (sm.box[1] + sm.box[3]));
+  const float hx = 0.5f * (sm.box[2] - sm.box[0]), hy = 0.5f * (sm.box[3] - sm.box[1]);
+  const float hd2 = fmaf(hx, hx, hy * hy);  // the tile's half-diagonal squared
 
   for (int grp = 0; grp < ngroups; ++grp) {
     const int slot = grp * kVjThreads + tid;
@@ -690,7 +696,7 @@ __device__ __forceinline__ void vjp_body(const LensConst& L, const LensGradConst
         // the local expansion about the tile's centre: the four sums whole
         const float* rr = sub + 5 * (int64_t)h;
         const float kap = __ldg(rr + 2), ts = __ldg(rr + 3);
-        const float4 e = vj_expand(rec, q, kap, ts, deg & (kVjExpFlag - 1), cen, sm);
+        const float4 e = vj_expand(rec, q, kap, ts, deg & (kVjExpFlag - 1), cen, hd2, sm);
         sc[0] = e.x;
         sc[1] = e.y;
         sc[2] = e.z;
