@@ -334,6 +334,48 @@ __device__ __forceinline__ float2 tnfw_m_far2(const SubRec2& h, float2 x2, float
   return __fmul2_rn(h.A, __fmul2_rn(B, t.ix2));
 }
 
+// ---------------------------------------------------------------------------
+// Local expansions of a far subhalo's series about a tile's centre (both
+// ray-trace kernels): with z = c + delta,
+//   |z|^-(j+2) z = |c|^-j conj(c)^-1 (1 + delta/c)^(-j/2) (1 + conj(delta)/conj(c))^(-(j+2)/2),
+// whose two binomial series converge for |delta| < |c|.
+constexpr int kExpN = 7;  // the highest total order k + l of delta^k conj(delta)^l
+
+// Generalised binomial coefficients C(-j/2, k) and C(-(j+2)/2, k), j < 8.
+struct ExpBin {
+  float a[8][kExpN + 1];
+  float b[8][kExpN + 1];
+};
+
+constexpr ExpBin exp_make_bin() {
+  ExpBin t{};
+  for (int j = 0; j < 8; ++j) {
+    double ca = 1.0, cb = 1.0;
+    for (int k = 0; k <= kExpN; ++k) {
+      t.a[j][k] = (float)ca;
+      t.b[j][k] = (float)cb;
+      ca *= (-0.5 * j - k) / (k + 1.0);
+      cb *= (-0.5 * (j + 2) - k) / (k + 1.0);
+    }
+  }
+  return t;
+}
+
+static __constant__ ExpBin kExpBin = exp_make_bin();
+
+__device__ __forceinline__ float2 c2mul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+
+// The truncation order of an expansion for (tile half-diagonal / |c|)^2 =
+// hd2 / r2: 4 up to a ratio of 0.01, 5 up to 0.03, 6 up to 0.05, 7 up to
+// 0.08 (the largest served). Each keeps the truncation below 4e-9 of the
+// sums of absolute terms.
+constexpr float kExpRatio2 = 0.0064f;
+__device__ __forceinline__ int exp_order(float hd2, float r2) {
+  return hd2 <= 1e-4f * r2 ? 4 : hd2 <= 9e-4f * r2 ? 5 : hd2 <= 2.5e-3f * r2 ? 6 : kExpN;
+}
+
 // Converts a raw subhalo record (5 floats) into the prepared form.
 __device__ __forceinline__ SubRec prep_sub(const float* r, int profile) {
   SubRec h;

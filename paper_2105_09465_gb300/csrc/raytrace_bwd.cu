@@ -56,9 +56,9 @@ constexpr int kVjFold = 32;       // point pairs summed plainly per slot before 
 constexpr int kVjMaxOrd = 4096;   // subhalo counts up to which a CTA orders its slots by class (vj_sort)
 constexpr int kVjWaves = 8;       // large inputs: tiles per resident CTA slot
 constexpr int kVjTilePts = 512;   // ... while every tile keeps at least this many points
-constexpr int kVjExpN = 7;        // local expansion: terms delta^k conj(delta)^l with k + l <= kVjExpN
+constexpr int kVjExpN = kExpN;     // local expansion: terms delta^k conj(delta)^l with k + l <= kVjExpN
 constexpr int kVjExpTerms = (kVjExpN + 1) * (kVjExpN + 2) / 2;
-constexpr float kVjExpRatio2 = 0.0064f;  // (tile half-diagonal / distance)^2 up to which it serves (0.08^2)
+constexpr float kVjExpRatio2 = kExpRatio2;  // (tile half-diagonal / distance)^2 up to which it serves (0.08^2)
 constexpr int kVjExpFlag = 16;           // class code: series degree | flag, the expansion serves the tile
 
 __device__ __forceinline__ double warp_sum_d(double v) {
@@ -321,32 +321,6 @@ __device__ __forceinline__ int vj_degree_box(const SubRec& h, const SubSer& q, c
 // (checked against the analytic FP64 gradients for theta_s from 0.015 to
 // 0.2 arcsec and series degrees 3 to 7).
 
-// Generalised binomial coefficients C(-j/2, k) and C(-(j+2)/2, k), j < 8.
-struct VjBin {
-  float a[8][kVjExpN + 1];
-  float b[8][kVjExpN + 1];
-};
-
-constexpr VjBin vj_make_bin() {
-  VjBin t{};
-  for (int j = 0; j < 8; ++j) {
-    double ca = 1.0, cb = 1.0;
-    for (int k = 0; k <= kVjExpN; ++k) {
-      t.a[j][k] = (float)ca;
-      t.b[j][k] = (float)cb;
-      ca *= (-0.5 * j - k) / (k + 1.0);
-      cb *= (-0.5 * (j + 2) - k) / (k + 1.0);
-    }
-  }
-  return t;
-}
-
-__constant__ VjBin kVjBin = vj_make_bin();
-
-__device__ __forceinline__ float2 c2mul(float2 a, float2 b) {
-  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
-}
-
 // Term index of delta^k conj(delta)^l: by total order s = k + l, then k.
 __device__ __forceinline__ int vj_term(int k, int l) { return (k + l) * (k + l + 1) / 2 + k; }
 
@@ -416,7 +390,7 @@ __device__ __forceinline__ float4 vj_expand(const SubRec& rec, const SubSer& q, 
   const float2 c = make_float2(cen.x - rec.xh, cen.y - rec.yh);
   const float r2 = fmaf(c.x, c.x, c.y * c.y), ir2 = 1.0f / r2;
   // the truncation order for (half-diagonal / |c|)^2 = hd2 / r2
-  const int nmax = hd2 <= 1e-4f * r2 ? 4 : hd2 <= 9e-4f * r2 ? 5 : hd2 <= 2.5e-3f * r2 ? 6 : kVjExpN;
+  const int nmax = exp_order(hd2, r2);
   const float2 u = make_float2(c.x * ir2, -c.y * ir2), ub = make_float2(u.x, -u.y);
   const float yc = ts * sqrtf(ir2);
   float qy[8];
@@ -427,8 +401,8 @@ __device__ __forceinline__ float4 vj_expand(const SubRec& rec, const SubSer& q, 
     yj *= yc;
   }
   // Q = u^k conj(u)^(l+1) for the terms of total order s = k + l: from
-  // conj(u)^(s+1) at k = 0, each step in k times u / conj(u) = c^2 / |c|^2
-  const float2 rot = make_float2((c.x * c.x - c.y * c.y) * ir2, 2.0f * c.x * c.y * ir2);
+  // conj(u)^(s+1) at k = 0, each step in k times u / conj(u) = conj(c)^2 / |c|^2
+  const float2 rot = make_float2((c.x * c.x - c.y * c.y) * ir2, -2.0f * c.x * c.y * ir2);
   float2 us = ub;  // conj(u)^(s+1)
   float L = 0.f, Lt = 0.f, X = 0.f, Y = 0.f;
 #pragma unroll 1
@@ -441,7 +415,7 @@ __device__ __forceinline__ float4 vj_expand(const SubRec& rec, const SubSer& q, 
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
         if (j == 1) continue;
-        const float w = qy[j] * (kVjBin.a[j][k] * kVjBin.b[j][l]);
+        const float w = qy[j] * (kExpBin.a[j][k] * kExpBin.b[j][l]);
         ckl += w;
         ctl = fmaf(w, (float)(j + 2), ctl);
       }

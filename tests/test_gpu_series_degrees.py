@@ -73,3 +73,27 @@ def test_vjp_series_degree(orc, cx, copies):
     assert np.all(np.abs(rs) >= 0.999 * asub)
     err = np.abs(got - rs) / asub
     assert err.max() <= 4e-6, f"relative subhalo-gradient errors {err}"
+
+
+# Off-axis tiles near the local expansion's limit: a light subhalo (theta_s =
+# 0.01 arcsec) with the grid's centre at distance D in direction 40 degrees,
+# so that the tiles' half-diagonals are 0.01 to 0.08 of their distance and
+# every term delta^k conj(delta)^l of the expansion, and its phase, counts.
+@pytest.mark.parametrize("dist", [3.6, 8.0, 25.0])
+def test_expansion_off_axis(orc, dist):
+    ang = np.deg2rad(40.0)
+    g = W.Grid(16, 16, 2, 0.05, dist * np.cos(ang), dist * np.sin(ang))
+    lens = W.Lens(0.0, 0.0, 0.9, 0.2, 1e-9, 2.0, 0.0, 0.0)
+    sub = np.array([[0.0, 0.0, 0.3, 0.01, TAU]], np.float32)
+    xi = orc.grid_points(*g.astuple())
+    _, alpha = api.lens_raytrace(api.Points(grid=g, lens=lens, sub=dev(sub)), want_alpha=True)
+    a_ref, _ = orc.raytrace(xi, lens.astuple(), sub, 0)
+    a = host(alpha).astype(np.float64)
+    err = np.hypot(*(a - a_ref).T) / np.hypot(*a_ref.T)
+    assert err.max() <= 1.5e-6, f"max relative deflection error {err.max():.3e}"
+    db = np.random.default_rng(5).uniform(0.5, 1.5, (g.n, 2)).astype(np.float32)
+    _, d_sub = api.lens_raytrace_vjp(api.Points(grid=g, lens=lens, sub=dev(sub)), dev(db))
+    _, rs, _, asub = orc.raytrace_vjp(xi, lens.astuple(), sub, db, 0, with_abs=True)
+    got, rs, asub = host(d_sub).astype(np.float64).ravel(), np.ravel(rs), np.ravel(asub)
+    err = np.abs(got - rs) / asub
+    assert err.max() <= 4e-6, f"relative subhalo-gradient errors {err}"
