@@ -620,7 +620,7 @@ lr_status lr_matvec_bwd_workspace_size(const lr_points* query, const lr_points* 
  * lr_raytrace_vjp_workspace_size() bytes, 256-byte aligned, caller-owned.
  * The points are cut into tiles; a tNFW subhalo far from a tile is summed by
  * its far-field series, or by that series' local expansion about the tile's
- * centre, within 4e-9 of the sums of absolute terms, and per-tile partials
+ * centre, within 5e-9 of the sums of absolute terms, and per-tile partials
  * are added in a fixed order (deterministic). Asynchronous on `stream`;
  * LR_ERR_INVALID_ARG for a missing lens, misaligned or short buffers.
  */

@@ -369,7 +369,7 @@ __device__ __forceinline__ float2 c2mul(float2 a, float2 b) {
 
 // The truncation order of an expansion for (tile half-diagonal / |c|)^2 =
 // hd2 / r2: 4 up to a ratio of 0.01, 5 up to 0.03, 6 up to 0.05, 7 up to
-// 0.08 (the largest served). Each keeps the truncation below 4e-9 of the
+// 0.08 (the largest served). Each keeps the truncation below 5e-9 of the
 // sums of absolute terms.
 constexpr float kExpRatio2 = 0.0064f;
 __device__ __forceinline__ int exp_order(float hd2, float r2) {

@@ -317,7 +317,7 @@ __device__ __forceinline__ int vj_degree_box(const SubRec& h, const SubSer& q, c
 //   W_x = k W_(k-1,l) + l W_(k,l-1), W_y = i (k W_(k-1,l) - l W_(k,l-1)).
 // The order of the truncation follows the ratio of the tile's half-diagonal
 // to |c|: 4 up to 0.01, 5 up to 0.03, 6 up to 0.05, 7 (kVjExpN) up to 0.08.
-// Each keeps the truncation below 4e-9 of the sums of absolute terms
+// Each keeps the truncation below 5e-9 of the sums of absolute terms
 // (checked against the analytic FP64 gradients for theta_s from 0.015 to
 // 0.2 arcsec and series degrees 3 to 7).
 
