@@ -71,7 +71,7 @@ struct VjSmem {
   float4 pos[kVjChunk / 2];   // point pair k: (x_2k, x_2k+1, y_2k, y_2k+1)
   float4 grad[kVjChunk / 2];  // (G_x, G_x, G_y, G_y) of the same two points
   double lred[kVjWarps][7];
-  unsigned short ord[kVjMaxOrd];  // slot subhalo -> subhalo, by series degree (vj_order)
+  unsigned short ord[kVjMaxOrd];  // slot subhalo -> subhalo, in the order of vj_sort
   unsigned char deg[kVjMaxOrd];   // class of each subhalo for the tile (vj_class)
   float wbox[kVjWarps][4];        // per-warp bounds of the CTA's points
   float box[4];                   // x_lo, y_lo, x_hi, y_hi of the CTA's points

@@ -103,9 +103,9 @@ def test_raytrace_vjp(orc, profile):
 @pytest.mark.parametrize("n_sub", [3, 4097])
 def test_raytrace_vjp_subhalo_counts(orc, n_sub):
     """A few subhalos (several phases per subhalo) and more subhalos than a
-    CTA orders far-first (every slot in index order): the far-field series
-    and the closed forms both serve the sums, every gradient element against
-    the oracle."""
+    CTA orders by class (every slot in index order): the far-field series,
+    the local expansion and the closed forms serve the sums, every gradient
+    element against the oracle."""
     rng = np.random.default_rng(44)
     lens = W.draw_lens(rng)
     sub = W.draw_subhalos(rng, n_sub, lens, 1e6, 1e10)
