@@ -1,10 +1,15 @@
 // Pixel-grid generation and the lens ray-trace beta = xi - alpha(xi).
 //
-// Two image-plane points per thread. The SPLE and shear terms are evaluated in
-// registers from per-lens constants passed as a kernel parameter; the
-// subhalo records are staged into shared memory in chunks by a bulk
-// asynchronous copy (the TMA engine's 1-D form) and reused by every point of
-// the CTA. Stores are coalesced float2 writes.
+// Two image-plane points per thread; a CTA takes a 16 x 16 tile of a pixel
+// grid (or 256 consecutive explicit points). The SPLE and shear terms are
+// evaluated in registers from per-lens constants passed as a kernel
+// parameter; the subhalo records are staged into shared memory in chunks by a
+// bulk asynchronous copy (the TMA engine's 1-D form) and reused by every
+// point of the CTA. Each chunk is sorted by the degree of the far-field
+// series that serves the whole tile (rt_degree, fewest terms first), and each
+// degree's run is swept without per-pair tests; the rest take a per-pair
+// choice of series, far-side closed form or general form. Stores are
+// coalesced float2 writes.
 #include <math.h>
 
 #include "host.cuh"
